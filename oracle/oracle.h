@@ -1,0 +1,117 @@
+/*
+ * Plain FP64 CPU oracle for the periodic treecode force path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code: only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no code, header or table with the CUDA
+ * library under paper_1407_2600_gb300/csrc.
+ *
+ * Units: unit periodic box (positions in [0,1)), G = 1, accelerations are
+ * those of unit-mass sources unless masses are given.  The method is the pure
+ * treecode of Sec. 2.1 ("2HOT"): Morton keys, a key-implied oct-tree, a
+ * truncated multipole expansion of cells, a multipole acceptance test,
+ * grouped sinks and periodic boundaries.
+ */
+#ifndef ORACLE_H
+#define ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- Ewald summation (unit cube, neutralising background) ---------------- */
+typedef struct {
+  double alpha;  /* splitting parameter */
+  double rcut;   /* real-space cutoff on |r - n| */
+  int h2max;     /* reciprocal-space cutoff on |h|^2 */
+} or_ewald_cfg;
+
+void or_ewald_default(or_ewald_cfg *c);
+/* Periodic acceleration at separation r (sink - source) from a unit source,
+ * with the uniform neutralising background (Hernquist, Bouchet & Suto 1991). */
+void or_ewald_acc(const double r[3], const or_ewald_cfg *c, double a[3]);
+/* Periodic potential, zero-mean convention. */
+double or_ewald_pot(const double r[3], const or_ewald_cfg *c);
+/* Derivatives of the smooth remainder potential
+ *   phi~(r) = phi_E(r) + 1/|r| + (2 pi / 3)|r|^2
+ * whose field C~ = -grad phi~ = a_E - a_N - (4 pi/3) r is the field of all
+ * images n != 0 with the background removed.  out[0] = phi~, out[1..3] =
+ * d_i, out[4..9] = d_ij (xx,xy,xz,yy,yz,zz), out[10..19] = d_ijk
+ * (xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz). */
+void or_phitilde(const double r[3], const or_ewald_cfg *c, double out[20]);
+
+/* All derivatives d^m phi~ with |m| <= P (P <= 7), in multi-index order
+ * (order-major; within an order nx descending, then ny descending). */
+void or_phitilde_mi(const double r[3], const or_ewald_cfg *c, int P, double *out);
+/* Exact phi~ derivatives (|m| <= P) at the lattice nodes (i,j,k) 2^-lg with
+ * 0 <= i,j,k <= 2^(lg-1) + 1; nmom(P) values per node. */
+int or_phitilde_lattice(int lg, int P, double *tab);
+/* Value at a signed lattice point (parity folding). */
+void or_phitilde_lattice_get(const double *tab, int lg, int P, const int64_t ir[3], double *out);
+
+/* Accurate tricubic table of C~ only (3 values per node) for the direct
+ * oracle; nodes from -h to 1/2 + 2h with h = 1/(2 n1). */
+int or_ctilde_table_build(int n1, double *tab /* (n1+4)^3 * 3 */);
+void or_ctilde_table_eval(const double *tab, int n1, const double r[3], double out[3]);
+/* Same layout for the 6 second derivatives of phi~ (used by the adjoint). */
+int or_ctilde_grad_table_build(int n1, double *tab /* (n1+4)^3 * 6 */);
+void or_ctilde_grad_table_eval(const double *tab, int n1, const double r[3], double out[6]);
+
+/* ---- O1: direct summation with Ewald images --------------------------------
+ * a_i = sum_{j != i} m_j [ a_E(r_ij) - a_N(r*_ij) + a_P(r*_ij) ]
+ * (Plummer softening for the minimum-image pair only).  ctab == NULL uses the
+ * exact Ewald sum per pair; otherwise the tricubic C~ table.  targets == NULL
+ * means all particles.  acc is SoA 3 x ntarget. */
+int or_direct_forces(int64_t n, const double *pos, const double *mass, double eps,
+                     int64_t ntarget, const int64_t *targets, const double *ctab,
+                     int n1, double *acc);
+/* Vector-Jacobian product of O1: given lam (3 x n SoA, cotangent of the
+ * accelerations of all particles), out = (d a / d x)^T lam (3 x n SoA). */
+int or_direct_vjp(int64_t n, const double *pos, const double *mass, double eps,
+                  const double *gtab, int n1, const double *lam, double *out);
+
+/* ---- O2: CPU tree ------------------------------------------------------- */
+typedef struct {
+  double eps;     /* Plummer softening, box units */
+  double theta;   /* opening angle */
+  int order;      /* multipole order p, 0..4 */
+  int n_leaf;     /* a cell with more particles is split */
+  int n_group;    /* sinks per group (consecutive in key order) */
+  int n_direct;   /* accepted cells with <= n_direct particles use P2P */
+  int lmax;       /* deepest level, <= 21 */
+  int ewald;      /* 0: no periodic correction; else the order p_E of the
+                     per-group local expansion of the image field */
+  int ew_level;   /* level of the fixed source cells of the image field */
+  int ew_grid;    /* expansion points snap to the lattice 2^-ew_grid */
+} or_tree_params;
+
+/* stats[0] = P2P pair interactions, stats[1] = M2P interactions,
+ * stats[2] = Ewald (group, cell) terms, stats[3] = cells, stats[4] = groups */
+int or_tree_forces(int64_t n, const double *pos, const double *mass,
+                   const or_tree_params *p, const double *tab, int64_t ntarget,
+                   const int64_t *targets, double *acc, double *stats);
+
+/* Tree topology export for structural parity: cell placeholder keys
+ * (1 << 3l | prefix), particle ranges, in breadth-first (level, key) order.
+ * Returns the number of cells or -(needed) if cap is too small. */
+int64_t or_tree_cells(int64_t n, const double *pos, int n_leaf, int lmax, int64_t cap,
+                      uint64_t *key, int32_t *level, int64_t *start, int64_t *count);
+/* Morton keys (63 bits) and the stable sort permutation. */
+void or_morton_keys(int64_t n, const double *pos, uint64_t *keys);
+void or_sort_perm(int64_t n, const uint64_t *keys, int64_t *perm);
+
+/* Multipole helpers exposed for pins. */
+int or_nmom(int p);
+void or_p2m(int64_t n, const double *pos, const double *mass, const double c[3], int p, double *M);
+void or_m2m(const double *Mc, const double c[3], const double cp[3], int p, double *Mp);
+/* d^m g for |m| <= pmax of g = (|R|^2 + eps^2)^-1/2, Hermite-product form. */
+void or_dtensor(const double R[3], double eps, int pmax, double *D);
+/* acceleration at R from a cell with moments M (order p), softened */
+void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,141 @@
+"""Seeded synthetic inputs (shared by the oracle tests and the CUDA path).
+
+This module holds none of the force method's arithmetic: it only draws the
+particle distributions the workloads are defined on.  Everything is FP64,
+seeded, in box units (unit periodic cube).
+
+* Zel'dovich displacements: white noise from ``numpy.random.Generator(PCG64(seed))``
+  on an ng^3 grid, FFT, multiplication by sqrt(P(k)) with P(k) ~ k^n, a
+  spherical cut at the grid Nyquist |k| <= pi ng (Nyquist planes zeroed),
+  psi_k = i k delta_k / k^2, inverse FFT, rescaled so that the rms of |psi|
+  equals the requested fraction of the grid spacing.
+* NFW haloes: counts log-uniform in [nmin, nmax], concentration uniform in
+  [cmin, cmax], r200 from 200 times the mean density, radii by inverting the
+  enclosed-mass profile ln(1+x) - x/(1+x) for x <= c, isotropic directions,
+  centres uniform; halo particles replace distinct random grid particles so
+  that N is unchanged.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def lattice(ng: int) -> np.ndarray:
+    """Grid points q = (i + 1/2)/ng, (ng^3, 3), x fastest-varying last."""
+    g = (np.arange(ng, dtype=np.float64) + 0.5) / ng
+    qx, qy, qz = np.meshgrid(g, g, g, indexing="ij")
+    return np.stack([qx.ravel(), qy.ravel(), qz.ravel()], axis=1)
+
+
+def zeldovich_displacement(ng: int, n_index: float, rms_spacing: float, seed: int) -> np.ndarray:
+    """Displacement field psi (ng^3, 3) in box units with rms |psi| =
+    rms_spacing / ng; power spectrum P(k) ~ k^n_index."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    white = rng.standard_normal((ng, ng, ng))
+    dk = np.fft.rfftn(white)
+    kx = np.fft.fftfreq(ng, d=1.0 / ng) * 2.0 * math.pi
+    kz = np.fft.rfftfreq(ng, d=1.0 / ng) * 2.0 * math.pi
+    KX, KY, KZ = np.meshgrid(kx, kx, kz, indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    kk = np.sqrt(k2)
+    kny = math.pi * ng
+    amp = np.zeros_like(kk)
+    ok = (kk > 0) & (kk <= kny)
+    amp[ok] = kk[ok] ** (n_index / 2.0)
+    # zero the Nyquist planes
+    nyq = ng // 2 if ng % 2 == 0 else None
+    if nyq is not None:
+        amp[nyq, :, :] = 0.0
+        amp[:, nyq, :] = 0.0
+        amp[:, :, -1] = 0.0
+    dk = dk * amp
+    k2s = np.where(k2 > 0, k2, 1.0)
+    psi = []
+    for K in (KX, KY, KZ):
+        comp = np.fft.irfftn(1j * K * dk / k2s, s=(ng, ng, ng), axes=(0, 1, 2))
+        psi.append(comp.ravel())
+    psi = np.stack(psi, axis=1)
+    rms = math.sqrt(np.mean(np.sum(psi * psi, axis=1)))
+    if rms > 0:
+        psi *= (rms_spacing / ng) / rms
+    return psi
+
+
+def zeldovich_particles(ng: int, n_index: float, rms_spacing: float, seed: int):
+    """Lagrangian grid q and displacement psi, both (ng^3, 3)."""
+    return lattice(ng), zeldovich_displacement(ng, n_index, rms_spacing, seed)
+
+
+def nfw_radii(rng, count: int, c: float, r200: float) -> np.ndarray:
+    """Radii drawn from the NFW enclosed-mass profile truncated at r200."""
+    def mu(x):
+        return np.log1p(x) - x / (1.0 + x)
+
+    u = rng.uniform(0.0, 1.0, count) * mu(c)
+    lo = np.zeros(count)
+    hi = np.full(count, c)
+    for _ in range(80):  # bisection of mu(x) = u on [0, c]
+        mid = 0.5 * (lo + hi)
+        f = mu(mid) - u
+        lo = np.where(f < 0, mid, lo)
+        hi = np.where(f < 0, hi, mid)
+    return 0.5 * (lo + hi) * (r200 / c)
+
+
+def add_nfw_haloes(x: np.ndarray, n_halo: int, nmin: int, nmax: int, cmin: float, cmax: float,
+                   seed: int):
+    """Replace random distinct particles of x (n,3) by NFW haloes.
+
+    Returns (x_new, halo_member_index, halo_table) where halo_table rows are
+    (count, concentration, r200, cx, cy, cz)."""
+    n = x.shape[0]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    counts = np.exp(rng.uniform(math.log(nmin), math.log(nmax), n_halo)).astype(np.int64)
+    total = int(counts.sum())
+    if total > n:
+        raise ValueError("haloes need more particles than exist")
+    conc = rng.uniform(cmin, cmax, n_halo)
+    centres = rng.uniform(0.0, 1.0, (n_halo, 3))
+    chosen = rng.permutation(n)[:total]
+    xn = x.copy()
+    table = []
+    off = 0
+    for h in range(n_halo):
+        cnt = int(counts[h])
+        # mean density of the box is n particles per unit volume
+        r200 = (3.0 * cnt / (4.0 * math.pi * 200.0 * n)) ** (1.0 / 3.0)
+        r = nfw_radii(rng, cnt, conc[h], r200)
+        v = rng.standard_normal((cnt, 3))
+        v /= np.linalg.norm(v, axis=1, keepdims=True)
+        xn[chosen[off:off + cnt]] = np.mod(centres[h] + r[:, None] * v, 1.0)
+        table.append((cnt, conc[h], r200, *centres[h]))
+        off += cnt
+    return xn, chosen, np.array(table)
+
+
+def config_small(seed: int = 1):
+    """16^3 particles, P(k) ~ k^-2, rms displacement 0.25 spacing;
+    eps = spacing/30; positions (n,3) in [0,1)."""
+    ng = 16
+    q, psi = zeldovich_particles(ng, -2.0, 0.25, seed)
+    x = np.mod(q + psi, 1.0)
+    return x, 1.0 / (30.0 * ng)
+
+
+def config_haloes(ng: int = 128, seed: int = 1, n_halo: int = 64, rms: float = 0.6,
+                  nmin: int = 2000, nmax: int = 50000):
+    """ng^3 particles, P(k) ~ k^-2, rms displacement `rms` spacing, plus
+    `n_halo` NFW haloes (nmin..nmax particles, log-uniform; c in [5,15])
+    replacing random grid particles; eps = spacing/30."""
+    q, psi = zeldovich_particles(ng, -2.0, rms, seed)
+    x = np.mod(q + psi, 1.0)
+    if n_halo > 0:
+        x, _, _ = add_nfw_haloes(x, n_halo, nmin, nmax, 5.0, 15.0, seed + 1000)
+    return x, 1.0 / (30.0 * ng)
+
+
+def random_targets(n: int, k: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed + 7))
+    return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)

@@ -1,0 +1,294 @@
+"""Pins of the FP64 CPU oracle to facts outside itself (CPU only).
+
+Each test checks the oracle against mathematics the paper's method rests on:
+Ewald sums (alpha independence, symmetry zeros, the r -> 0 background limit,
+the Madelung constant of the simple cubic lattice, harmonicity), exact
+symmetry of direct summation (lattice, momentum), the multipole algebra
+(M2M exactness, derivative tensors vs finite differences, one-particle
+cells), convergence of the tree to direct summation, the integrator's
+closed forms and linear growth, and the CIC loss gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1407_2600_gb300 import ics
+
+RNG = np.random.default_rng(12345)
+
+
+# ---- Ewald ---------------------------------------------------------------------
+def test_ewald_alpha_independence():
+    pts = RNG.uniform(-0.5, 0.5, (6, 3))
+    for r in pts:
+        a = [O.ewald_acc(r, O.ewald_cfg(al)) for al in (1.5, 2.0, 3.0)]
+        scale = np.abs(a[1]).max()
+        assert np.abs(a[0] - a[1]).max() <= 1e-12 * max(scale, 1.0)
+        assert np.abs(a[2] - a[1]).max() <= 1e-12 * max(scale, 1.0)
+
+
+def test_ewald_symmetry_zeros_and_parity():
+    for r in ([0.5, 0, 0], [0.5, 0.5, 0], [0.5, 0.5, 0.5], [0, 0.5, 0.5]):
+        assert np.abs(O.ewald_acc(np.array(r, float))).max() <= 1e-13
+    r = np.array([0.21, -0.13, 0.34])
+    a = O.ewald_acc(r)
+    b = O.ewald_acc(r * np.array([-1, 1, 1]))
+    assert abs(a[0] + b[0]) <= 1e-13 and abs(a[1] - b[1]) <= 1e-13 and abs(a[2] - b[2]) <= 1e-13
+    c = O.ewald_acc(r[[1, 2, 0]])  # cubic symmetry: permuting axes permutes components
+    assert np.abs(c - a[[1, 2, 0]]).max() <= 1e-12
+
+
+def test_ewald_small_r_background_limit():
+    # a_E - a_N -> +(4 pi / 3) r as r -> 0: the neutralising background's
+    # repulsion; the lattice tidal term vanishes by cubic symmetry
+    d = np.array([0.3, -0.5, 0.8])
+    d /= np.linalg.norm(d)
+    for h in (1e-2, 3e-3):
+        r = h * d
+        diff = O.ewald_acc(r) + r / h ** 3
+        assert np.abs(diff / r - 4 * math.pi / 3).max() <= 5 * h ** 2 * 10
+
+
+def test_madelung_constant():
+    # simple cubic lattice with neutralising background (Nijboer & de Wette):
+    # lim_{r->0} [psi(r) - 1/r] = -2.8372974794806 for the Coulomb-sign potential
+    r = 1e-4 * np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
+    val = -(O.ewald_pot(r) + 1.0 / np.linalg.norm(r))
+    assert abs(val - (-2.8372974794806)) <= 1e-7
+
+
+def test_phitilde_consistency_and_harmonic():
+    cfg = O.ewald_cfg()
+    mi = O.multi_indices(5)
+    idx = {m: i for i, m in enumerate(mi)}
+    for r in RNG.uniform(-0.5, 0.5, (3, 3)):
+        D = O.phitilde_mi(r, 5)
+        # C~ = -grad phi~ equals a_E - a_N - (4 pi/3) r (independent code path)
+        ae = O.ewald_acc(r)
+        ct = ae + r / np.linalg.norm(r) ** 3 - 4 * math.pi / 3 * r
+        assert np.abs(-D[1:4] - ct).max() <= 1e-11
+        # phi~ is harmonic: every Laplacian-trace of its derivatives vanishes
+        for m in mi:
+            if sum(m) > 3:
+                continue
+            lap = sum(D[idx[tuple(m[k] + (2 if k == d else 0) for k in range(3))]] for d in range(3))
+            assert abs(lap) <= 1e-8 * (1 + np.abs(D).max())
+        # order-k derivatives are finite differences of order k-1
+        h = 1e-5
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = h
+            Dp, Dm = O.phitilde_mi(r + e, 4), O.phitilde_mi(r - e, 4)
+            for m in mi:
+                if sum(m) > 4:
+                    continue
+                up = tuple(m[k] + (1 if k == d else 0) for k in range(3))
+                fd = (Dp[idx[m]] - Dm[idx[m]]) / (2 * h)
+                assert abs(fd - D[idx[up]]) <= 1e-5 * (1 + abs(D[idx[up]]))
+        # the generic-order routine agrees with the explicit orders 0..3
+        E = O.phitilde(r, cfg)
+        assert np.abs(E[:4] - D[:4]).max() <= 1e-12 * (1 + np.abs(E).max())
+
+
+# ---- O1 direct summation ------------------------------------------------------------
+def test_direct_lattice_zero_and_momentum():
+    q = ics.lattice(7)  # odd lattice: no pair sits exactly half a box apart
+    a = O.direct_forces(q, None, 1.0 / 70, table_n1=None)
+    assert np.abs(a).max() <= 1e-11
+    x, eps = ics.config_small(3)
+    a = O.direct_forces(x, None, eps, table_n1=64)
+    assert np.abs(a.sum(axis=0)).max() <= 1e-13 * np.abs(a).sum(axis=0).max()
+
+
+def test_direct_table_matches_exact_ewald():
+    x, eps = ics.config_small(2)
+    tg = ics.random_targets(len(x), 24, 2)
+    a_ex = O.direct_forces(x, None, eps, targets=tg, table_n1=None)
+    a_tb = O.direct_forces(x, None, eps, targets=tg, table_n1=64)
+    rel = np.linalg.norm(a_ex - a_tb, axis=1) / np.linalg.norm(a_ex, axis=1)
+    assert rel.max() <= 1e-6
+
+
+def test_direct_pair_matches_definition():
+    # two particles: a_1 = m_2 [a_E(r) - a_N(r*) + a_P(r*)]
+    x = np.array([[0.1, 0.2, 0.3], [0.7, 0.25, 0.28]])
+    eps = 0.02
+    a = O.direct_forces(x, np.array([0.3, 0.7]), eps, table_n1=None)
+    r = x[0] - x[1]
+    rs = r - np.round(r)
+    q = np.linalg.norm(rs)
+    ref = 0.7 * (O.ewald_acc(r) + rs / q ** 3 - rs / (q * q + eps * eps) ** 1.5)
+    assert np.abs(a[0] - ref).max() <= 1e-13
+    assert np.abs(0.3 * a[0] + 0.7 * a[1]).max() <= 1e-13  # Newton's third law
+
+
+def test_direct_plane_wave_linear_force():
+    # small single-mode displacement on a lattice: force = 4 pi G rho psi up
+    # to the lattice's discreteness correction, which falls as (k/k_Ny)^2
+    ratios = []
+    for ng in (8, 16):
+        q = ics.lattice(ng)
+        A = 1e-3 / ng
+        x = q.copy()
+        x[:, 0] += A * np.sin(2 * math.pi * q[:, 0])
+        a = O.direct_forces(x, None, 1e-6, table_n1=64)
+        pred = 4 * math.pi * A * np.sin(2 * math.pi * q[:, 0])
+        i = int(np.argmax(np.abs(pred)))
+        ratios.append(a[i, 0] / pred[i])
+        assert np.abs(a[:, 1:]).max() <= 1e-5 * abs(pred[i])
+    assert abs(ratios[1] - 1) <= 0.01
+    assert 3.5 <= (ratios[0] - 1) / (ratios[1] - 1) <= 4.5
+
+
+# ---- multipoles and tree ----------------------------------------------------------------
+def test_m2m_exact():
+    pts = RNG.uniform(0.1, 0.3, (3, 40))
+    m = RNG.uniform(0.5, 1.5, 40)
+    c, cp = np.array([0.2, 0.2, 0.2]), np.array([0.25, 0.15, 0.2])
+    for p in range(5):
+        direct = O.p2m(pts, m, cp, p)
+        shifted = O.m2m(O.p2m(pts, m, c, p), c, cp, p)
+        assert np.abs(direct - shifted).max() <= 1e-14 * np.abs(direct).max()
+
+
+def test_dtensor_finite_differences():
+    R = np.array([0.31, -0.22, 0.17])
+    eps = 0.05
+    mi = O.multi_indices(6)
+    idx = {m: i for i, m in enumerate(mi)}
+    D = O.dtensor(R, eps, 6)
+    assert abs(D[0] - 1 / math.sqrt(R @ R + eps * eps)) <= 1e-15
+    h = 1e-6
+    for d in range(3):
+        e = np.zeros(3)
+        e[d] = h
+        Dp, Dm = O.dtensor(R + e, eps, 5), O.dtensor(R - e, eps, 5)
+        for m in mi:
+            if sum(m) > 5:
+                continue
+            up = tuple(m[k] + (1 if k == d else 0) for k in range(3))
+            fd = (Dp[idx[m]] - Dm[idx[m]]) / (2 * h)
+            assert abs(fd - D[idx[up]]) <= 1e-6 * (1 + abs(D[idx[up]]))
+
+
+def test_one_particle_cell_m2p_equals_p2p():
+    c = np.array([0.5, 0.5, 0.5])
+    y = np.array([[0.51], [0.49], [0.505]])
+    x = np.array([0.8, 0.1, 0.6])
+    eps = 0.01
+    r = y[:, 0] - x
+    p2p = 0.7 * r / (r @ r + eps * eps) ** 1.5
+    for p in (2, 4):
+        M = O.p2m(y, np.array([0.7]), c, p)
+        a = O.m2p(M, p, x - c, eps)
+        # the expansion about c converges to the softened particle force
+        assert np.abs(a - p2p).max() <= 5e-3 * np.abs(p2p).max() * (0.02 / 0.6) ** (p - 1)
+    M = O.p2m(c[:, None], np.array([0.7]), c, 4)  # particle at the centre: exact
+    assert np.abs(O.m2p(M, 4, x - c, eps) - 0.7 * (c - x) / ((c - x) @ (c - x) + eps * eps) ** 1.5).max() <= 1e-15
+
+
+def test_tree_topology_invariants():
+    x, _ = ics.config_haloes(16, seed=4, n_halo=3, nmin=100, nmax=400)
+    key, lev, st, ct = O.tree_cells(x, n_leaf=8)
+    n = len(x)
+    assert ct[0] == n and lev[0] == 0
+    # cells of one level are disjoint and sorted; a cell's count equals its prefix range
+    okeys = O.morton_keys(x)[O.sort_perm(O.morton_keys(x))]
+    for c in range(0, len(key), 7):
+        l = int(lev[c])
+        pre = int(key[c]) ^ (1 << (3 * l))
+        span = okeys[st[c]:st[c] + ct[c]] >> np.uint64(3 * (21 - l)) if l > 0 else np.zeros(ct[c], np.uint64)
+        assert np.all(span == np.uint64(pre))
+    # leaves: no cell may have a child if it has <= n_leaf particles
+    for l in range(int(lev.max())):
+        par = (lev == l) & (ct <= 8)
+        kids = lev == l + 1
+        pk = set((key[par] ^ np.uint64(0)).tolist())
+        kp = set(((key[kids] >> np.uint64(3))).tolist())
+        assert not (pk & kp)
+
+
+def test_tree_converges_to_direct():
+    x, eps = ics.config_small(1)
+    ad = O.direct_forces(x, None, eps, table_n1=64)
+
+    def med(th, p):
+        at = O.tree_forces(x, None, O.tree_params(eps, th, p, ewald=4))
+        return np.median(np.linalg.norm(at - ad, axis=1) / np.linalg.norm(ad, axis=1))
+
+    # with no cell accepted only the image-field expansion remains
+    assert med(1e-3, 2) <= 1e-4
+    # truncation error of an order-p expansion falls at least like theta^(p+1)
+    assert med(0.6, 2) / med(0.3, 2) >= 2 ** 3
+    assert med(0.9, 4) / med(0.45, 4) >= 2 ** 5
+
+
+def test_image_field_order_convergence():
+    x, eps = ics.config_small(6)
+    ad = O.direct_forces(x, None, eps, table_n1=64)
+    med = []
+    for pe in (1, 2, 4):
+        at = O.tree_forces(x, None, O.tree_params(eps, 1e-3, 2, ewald=pe))
+        med.append(np.median(np.linalg.norm(at - ad, axis=1) / np.linalg.norm(ad, axis=1)))
+    assert med[0] > med[1] > med[2]
+
+
+# ---- O3 integrator ---------------------------------------------------------------
+def test_kick_drift_factors_quadrature():
+    from scipy.integrate import quad
+    a0, a1 = 0.05, 0.2
+    H = lambda a: O.H0 * a ** -1.5
+    k = quad(lambda a: 1.0 / (a * a * H(a)), a0, a1, epsabs=0, epsrel=2e-14)[0]
+    d = quad(lambda a: 1.0 / (a ** 3 * H(a)), a0, a1, epsabs=0, epsrel=2e-14)[0]
+    assert abs(O.kick_factor(a0, a1) - k) <= 1e-13 * k
+    assert abs(O.drift_factor(a0, a1) - d) <= 1e-13 * d
+
+
+def test_linear_growth_second_order():
+    # with the linear-theory force g = 4 pi (x - q) the growing mode is D = a
+    q = np.full((1, 3), 0.5)
+    psi = np.array([[1e-3, -2e-3, 5e-4]])
+    errs = []
+    for S in (8, 16):
+        a0, a1 = 0.05, 0.1
+        x, p = O.zeldovich_state(q, psi, a0)
+        force = lambda xx: 4 * math.pi * (xx - 0.5)
+        g = force(x)
+        al = a0 * np.exp(np.arange(S + 1) * math.log(a1 / a0) / S)
+        for k in range(S):
+            x, p, g = O.kdk_step(x, p, g, al[k], al[k + 1], force)
+        errs.append(np.abs((x - 0.5) / psi / a1 - 1).max())
+    assert errs[1] <= 1e-3
+    assert 3.5 <= errs[0] / errs[1] <= 4.5
+
+
+# ---- CIC loss and the direct adjoint ---------------------------------------------------------
+def test_cic_loss_and_gradient():
+    ng = 8
+    q = ics.lattice(ng)
+    L, g = O.cic_loss(q, None, ng)  # particles at cell centres: delta = 0
+    assert L <= 1e-20 and np.abs(g).max() <= 1e-12
+    x = np.mod(q + 0.03 * RNG.standard_normal(q.shape), 1.0)
+    L, g = O.cic_loss(x, None, ng)
+    h = 1e-7
+    for i in (0, 17, 300):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            fd = (O.cic_loss(xp, None, ng)[0] - O.cic_loss(xm, None, ng)[0]) / (2 * h)
+            assert abs(fd - g[i, d]) <= 1e-5 * (1 + abs(g[i, d]))
+
+
+def test_direct_vjp_dot_product():
+    x = np.mod(ics.lattice(4) + 0.02 * RNG.standard_normal((64, 3)), 1.0)
+    eps = 0.02
+    v = RNG.standard_normal(x.shape)
+    w = RNG.standard_normal(x.shape)
+    h = 1e-6
+    jv = (O.direct_forces(x + h * v, None, eps, table_n1=64) -
+          O.direct_forces(x - h * v, None, eps, table_n1=64)) / (2 * h)
+    jtw = O.direct_vjp(x, w, None, eps, n1=64)
+    assert abs(np.sum(jv * w) - np.sum(v * jtw)) <= 1e-4 * abs(np.sum(jv * w))
