@@ -1,0 +1,204 @@
+/*
+ * nbody.h -- C ABI of the GB300 periodic treecode force path.
+ *
+ * The operations follow the N-body method of Sec. 2.1 of the paper ("2HOT"):
+ * particles get Morton keys and are sorted by them (the key order maps 3-D
+ * space to a line and the sort doubles as the domain decomposition), the
+ * keys imply an oct-tree whose cells are found through a hash of their keys,
+ * cells carry truncated multipole expansions, a multipole acceptance test
+ * decides between using a cell's expansion and opening it, sinks are
+ * bundled into groups that share one interaction list, and near-leaf
+ * interactions are direct particle-particle sums; boundaries are periodic.
+ * Sec. 2.1 also names a symplectic integrator; the kick-drift-kick step in
+ * comoving coordinates is provided here, with its adjoint.
+ *
+ * Conventions for every entry point:
+ *   - Units: each box is the unit periodic cube; positions are FP64 in [0,1)
+ *     (values outside are wrapped), G = 1, accelerations are in units of
+ *     G * (unit mass) / (box length)^2.  With masses summing to 1 per box the
+ *     mean density is 1.
+ *   - Layout: arrays are structure-of-arrays in the caller's particle order:
+ *     pos = [x_0..x_{n-1}, y_0..y_{n-1}, z_0..z_{n-1}], likewise for momenta
+ *     and accelerations.  Pointers marked _dev are device pointers on the
+ *     current CUDA device.
+ *   - Ownership: the caller owns every array it passes and must keep the
+ *     position, momentum and mass arrays it hands to a tree alive while the
+ *     tree is used.  The library owns the tree handle and its scratch memory
+ *     (freed by nbody_tree_free) and a per-device table of the periodic image
+ *     field (freed at process exit).
+ *   - Streams: work is enqueued on the given stream.  By default each call
+ *     ends with a blocking read of a 4-byte device status word so that
+ *     device-side errors (overflow, bounded waits that ran out) come back as
+ *     return codes; NBODY_FLAG_ASYNC in params.flags skips that read and the
+ *     status can be fetched later with nbody_check.
+ *   - Errors: 0 on success, a negative NBODY_E* code otherwise; no entry
+ *     point throws or exits.  nbody_strerror gives a message.
+ */
+#ifndef NBODY_H
+#define NBODY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *nbody_stream_t; /* a cudaStream_t; NULL = default stream */
+
+enum {
+  NBODY_OK = 0,
+  NBODY_EINVAL = -1,    /* bad argument (null pointer, n <= 0, eps <= 0, ...) */
+  NBODY_ENOMEM = -2,    /* device allocation failed */
+  NBODY_ECUDA = -3,     /* a CUDA runtime call failed */
+  NBODY_EOVERFLOW = -4, /* a fixed-capacity device buffer would overflow */
+  NBODY_ETIMEOUT = -5,  /* a bounded device-side wait ran out */
+  NBODY_ENOTSUP = -6    /* parameter combination not supported */
+};
+
+enum { NBODY_MIXED = 0, NBODY_FP64 = 1 };
+enum { NBODY_FLAG_ASYNC = 1 };
+
+typedef struct {
+  double eps;       /* Plummer softening length, box units (> 0); per-box
+                       values may be given to nbody_build_tree_batched */
+  double theta;     /* opening angle of the multipole acceptance test */
+  int order;        /* multipole order p of the cell expansions, 0..4 */
+  int n_leaf;       /* cells with more particles are split (1..64) */
+  int n_group;      /* sinks per group, 1..32 */
+  int n_direct;     /* accepted cells with <= n_direct particles are summed
+                       directly (0..n_leaf) */
+  int lmax;         /* deepest tree level, 2..21 */
+  int ewald_order;  /* order of the image-field local expansion, 0..5
+                       (0 = no periodic images) */
+  int ewald_level;  /* level of the fixed source cells of the image field */
+  int ewald_grid;   /* image-field expansion points lie on the lattice
+                       2^-ewald_grid; groups never straddle a cell of level
+                       ewald_grid - 1 */
+  int precision;    /* NBODY_MIXED (FP32 interactions, FP64 positions and
+                       moments) or NBODY_FP64 (FP64 throughout) */
+  int flags;        /* NBODY_FLAG_* */
+} nbody_params;
+
+/* Fills the defaults: eps = 1/(30*128), theta = 0.6, order = 4, n_leaf = 16,
+ * n_group = 32, n_direct = 4, lmax = 21, ewald_order = 4, ewald_level = 3,
+ * ewald_grid = 6, precision = NBODY_MIXED, flags = 0. */
+void nbody_default_params(nbody_params *p);
+
+typedef struct {
+  double p2p;          /* particle-particle interactions in the last evaluation */
+  double m2p;          /* cell-particle (multipole) interactions */
+  double m2l;          /* image-field cell-to-group translations */
+  int64_t ncells;      /* tree cells (all boxes) */
+  int64_t ngroups;     /* sink groups */
+  int32_t max_level;   /* deepest level present */
+  int32_t nbox;
+  float ms_sort;       /* device time of keys + sort + gather */
+  float ms_build;      /* tree topology, hash, groups, leaf offsets */
+  float ms_upward;     /* moments */
+  float ms_walk;       /* group walk with P2P and M2P */
+  float ms_periodic;   /* image-field expansion and scatter to caller order */
+} nbody_stats;
+
+typedef struct nbody_tree nbody_tree;
+
+/*
+ * Build (or rebuild) the tree of one periodic box: Morton keys, radix sort,
+ * gather into key order, oct-tree topology and key hash, sink groups, leaf
+ * offsets and the cell moments (Sec. 2.1: keys imply the tree; cells carry
+ * truncated multipole expansions).
+ *   n        number of particles (>= 1, < 2^31)
+ *   pos_dev  3*n FP64 positions (SoA)
+ *   mass_dev n FP32 masses, or NULL for equal masses 1/n
+ *   tree     in: NULL or an existing handle to reuse (its buffers are kept
+ *            when large enough); out: the handle
+ * The tree keeps pointers to pos_dev and mass_dev.
+ */
+int nbody_build_tree(const nbody_params *params, int64_t n, const double *pos_dev,
+                     const float *mass_dev, nbody_tree **tree, nbody_stream_t stream);
+
+/*
+ * Same for nbox independent periodic boxes stored back to back: box b holds
+ * particles [offsets[b], offsets[b+1]) (offsets_host: nbox+1 host int64,
+ * offsets[0] = 0, non-decreasing with no empty box).  eps_host: nbox host
+ * doubles (NULL = params->eps for all).  Masses NULL = 1/n_b in box b.
+ */
+int nbody_build_tree_batched(const nbody_params *params, int nbox, const int64_t *offsets_host,
+                             const double *eps_host, const double *pos_dev,
+                             const float *mass_dev, nbody_tree **tree, nbody_stream_t stream);
+
+/*
+ * Accelerations of all particles of the tree (Sec. 2.1: grouped tree walk with
+ * the acceptance test, multipole and direct interactions, periodic images).
+ *   acc_dev  3*n FP32 (SoA, caller order), overwritten
+ *   stats    NULL or filled with counts and phase times (phase times are
+ *            only filled when the call synchronises)
+ */
+int nbody_forces(nbody_tree *tree, float *acc_dev, nbody_stats *stats, nbody_stream_t stream);
+
+/*
+ * One kick-drift-kick step in comoving coordinates (Einstein-de Sitter,
+ * p = a^2 dx/dt, dx/dt = p/a^2, dp/dt = g/a, H = H0 a^-3/2,
+ * H0^2 = 8 pi / 3 for unit mean density), the global-step form of the
+ * symplectic integrator cited in Sec. 2.1:
+ *   p += K(a0, ah) g(x0);  x += D(a0, a1) p (wrapped);  rebuild + forces;
+ *   p += K(ah, a1) g(x1);  ah = sqrt(a0 a1),
+ *   K(a,b) = (2/H0)(sqrt b - sqrt a),  D(a,b) = (2/H0)(a^-1/2 - b^-1/2).
+ *   pos_dev  3*n FP64, updated in place (must be the tree's positions)
+ *   mom_dev  3*n FP32 momenta, updated in place
+ *   acc_dev  3*n FP32: in g(x0), out g(x1)
+ */
+int nbody_kdk_step(nbody_tree *tree, double *pos_dev, float *mom_dev, float *acc_dev, double a0,
+                   double a1, nbody_stream_t stream);
+
+/*
+ * Reverse mode of one nbody_kdk_step, with g(x0) recomputed from pos0 (so the
+ * step is a function (x0, p0) -> (x1, p1)).  Given the cotangents of the
+ * step's outputs it returns those of its inputs:
+ *   pos0_dev, mom0_dev      the state at the start of the step (not modified)
+ *   lam_pos1_dev, lam_mom1_dev  3*n FP64 / FP32 cotangents of x1, p1
+ *   lam_pos0_dev, lam_mom0_dev  3*n FP64 / FP32 outputs
+ * The discrete decisions of the tree (topology, acceptance, groups) are held
+ * fixed, so this is the exact derivative of the evaluated forces.  Uses the
+ * tree's parameters; the tree is rebuilt at x0 and x1 internally.
+ */
+int nbody_kdk_adjoint(nbody_tree *tree, const double *pos0_dev, const float *mom0_dev, double a0,
+                      double a1, const double *lam_pos1_dev, const float *lam_mom1_dev,
+                      double *lam_pos0_dev, float *lam_mom0_dev, nbody_stream_t stream);
+
+/*
+ * Vector-Jacobian product of the force: out = (d acc / d pos)^T lam, for the
+ * tree as last built (positions as given to the build).
+ *   lam_dev  3*n FP32 cotangent of the accelerations (caller order)
+ *   out_dev  3*n FP64, overwritten
+ */
+int nbody_forces_vjp(nbody_tree *tree, const float *lam_dev, double *out_dev,
+                     nbody_stream_t stream);
+
+/* Tree inspection (tests).  what: */
+enum {
+  NBODY_EXPORT_SORTED_KEYS = 1, /* uint64 per particle, key order */
+  NBODY_EXPORT_PERM = 2,        /* uint32 per particle: original index of the i-th in key order */
+  NBODY_EXPORT_CELL_KEYS = 3,   /* uint64 per cell: 1<<3l | key prefix, breadth-first order */
+  NBODY_EXPORT_CELL_RANGE = 4,  /* int32 pairs (first particle, count) per cell */
+  NBODY_EXPORT_CELL_LEVEL = 5,  /* int32 per cell */
+  NBODY_EXPORT_MOMENTS = 6,     /* FP64 moments per cell, (order+1)(order+2)(order+3)/6 each */
+  NBODY_EXPORT_GROUPS = 7       /* int32 pairs (first particle, count) per group */
+};
+/* Number of elements of an export (cells, particles, groups), or < 0. */
+int64_t nbody_tree_count(const nbody_tree *tree, int what);
+/* Copy an export to dst_dev (device memory sized by nbody_tree_count). */
+int nbody_tree_export(const nbody_tree *tree, int what, void *dst_dev, nbody_stream_t stream);
+/* Hash lookup of cell keys (1<<3l | prefix) of box 0: idx_dev[i] = cell
+ * index in breadth-first order, or -1 when the key is not a cell. */
+int nbody_tree_lookup(const nbody_tree *tree, const uint64_t *keys_dev, int64_t nkeys,
+                      int32_t *idx_dev, nbody_stream_t stream);
+
+/* Read and clear the tree's device status word (blocks on the stream). */
+int nbody_check(nbody_tree *tree, nbody_stream_t stream);
+void nbody_tree_free(nbody_tree *tree);
+const char *nbody_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NBODY_H */

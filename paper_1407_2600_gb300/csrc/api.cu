@@ -1,0 +1,661 @@
+// C ABI of the periodic treecode force path: tree handle, phase orchestration,
+// kick-drift-kick step, inspection and error reporting.  The phases follow
+// Sec. 2.1: keys and sort, key-implied tree with its hash, moments, grouped
+// walk, periodic images; the integrator is the kick-drift-kick form of the
+// symplectic integrator it cites.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+// launchers from the other translation units
+cudaError_t nb_gather(const double* pos, const float* mass, const uint32_t* perm, const uint16_t* box_of,
+                      const int64_t* off, int64_t n, double* spos, float* smass, uint16_t* sbox, cudaStream_t s);
+cudaError_t nb_count_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int n_leaf,
+                           int lmax, int* ccount, int8_t* l0, cudaStream_t s);
+cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int n_leaf,
+                          int lmax, const int* ccount, const int* coff, const int8_t* l0, uint8_t* plevel,
+                          int* pstart, int* pcount, int* pparent, cudaStream_t s);
+cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const uint32_t* bfs2pre,
+                         int* pre2bfs, const uint8_t* plevel, const int* pstart, const int* pcount,
+                         const int* pparent, int4* cA, int4* cB, uint64_t* ckey, uint16_t* cbox, cudaStream_t s);
+cudaError_t nb_hash_build(int ncell, const uint64_t* ckey, const uint16_t* cbox, int* hval, uint64_t cap,
+                          unsigned* err, cudaStream_t s);
+cudaError_t nb_hash_lookup(const uint64_t* q, int64_t nq, int box, const int* hval, const uint64_t* ckey,
+                           const uint16_t* cbox, uint64_t cap, int* out, cudaStream_t s);
+cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* spos, const float* smass,
+                      int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s);
+cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int ls,
+                           int n_group, int* flag, cudaStream_t s);
+cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, int ls,
+                          const int* flag, const int* gid, int* gstart, const double* spos, int4* gA, int4* gB,
+                          int4* gC, int4* gD, cudaStream_t s);
+int nb_coef_stride(int order);
+cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int4* cB, const double* spos,
+                      const float* smass, int64_t n, double* mom, int* arrive, void* coef, cudaStream_t s);
+cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
+                             const double* spos, const float* smass, int64_t n, double* fm, cudaStream_t s);
+int nb_walk_warps(bool fp64);
+cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
+                    const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
+                    int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
+                    cudaStream_t s);
+cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
+cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+                        const void* tab, const void* accw, float* out, unsigned long long* counter,
+                        cudaStream_t s);
+
+namespace {
+
+constexpr int kStackCap = 8192;  // cells per warp stack
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e) {
+      cudaGetLastError();
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <typename T> T* as() const { return (T*)p; }
+};
+
+}  // namespace
+
+struct nbody_tree {
+  nbody_params prm;
+  int nbox = 0;
+  int64_t n = 0;
+  std::vector<int64_t> h_off;
+  std::vector<double> h_eps;
+  const double* pos = nullptr;
+  const float* mass = nullptr;
+  int device = 0, nsm = 0;
+  // particles
+  Buf off, box_of, keys, vals, keys2, vals2, sbox, spos, smass, src, sleaf;
+  // sort scratch
+  Buf hist, sstatus, tilectr, status;
+  // build scratch
+  Buf ccount, coff, l0, plevel, pstart, pcount, pparent, bfs2pre, pre2bfs, lvlhist, scantmp, totals;
+  // cells
+  int ncell = 0, max_level = 0;
+  Buf cA, cB, ckey, cbox, hval, mom, arrive, coef;
+  uint64_t hcap = 0;
+  // groups
+  int ngroup = 0;
+  Buf gflag, gid, gstart, gA, gB, gC, gD;
+  // image field
+  Buf fm;
+  const double* tab64 = nullptr;
+  const float* tab32 = nullptr;
+  // walk
+  Buf eps2, stack, gctr, accw, counters;
+  int walk_blocks = 0;
+  long long thr[NB_NLEV];
+  int64_t* pinned = nullptr;
+  double last_p2p = 0, last_m2p = 0, last_m2l = 0;
+  cudaEvent_t ev[8];
+  bool events = false;
+
+  ~nbody_tree() {
+    Buf* all[] = {&off, &box_of, &keys, &vals, &keys2, &vals2, &sbox, &spos, &smass, &src, &sleaf,
+                  &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
+                  &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
+                  &hval, &mom, &arrive, &coef, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
+                  &eps2, &stack, &gctr, &accw, &counters};
+    for (Buf* b : all) b->release();
+    if (pinned) cudaFreeHost(pinned);
+    if (events)
+      for (auto& e : ev) cudaEventDestroy(e);
+  }
+
+  DevTree dev() const {
+    DevTree t;
+    t.n = n;
+    t.nbox = nbox;
+    t.off = off.as<int64_t>();
+    t.skeys = keys.as<uint64_t>();
+    t.perm = vals.as<uint32_t>();
+    t.sbox = sbox.as<uint16_t>();
+    t.spos = spos.as<double>();
+    t.smass = smass.as<float>();
+    t.ncell = ncell;
+    t.cA = cA.as<int4>();
+    t.cB = cB.as<int4>();
+    t.ngroup = ngroup;
+    t.gA = gA.as<int4>();
+    t.gB = gB.as<int4>();
+    t.gC = gC.as<int4>();
+    t.gD = gD.as<int4>();
+    t.sleaf = sleaf.as<int>();
+    return t;
+  }
+};
+
+namespace {
+
+#define NB_CU(x)                                 \
+  do {                                           \
+    cudaError_t _e = (x);                        \
+    if (_e != cudaSuccess) return map_err(_e);   \
+  } while (0)
+
+int map_err(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return NBODY_ENOMEM;
+  return NBODY_ECUDA;
+}
+
+int status_to_code(unsigned st) {
+  if (st & NB_ST_OVERFLOW) return NBODY_EOVERFLOW;
+  if (st & NB_ST_TIMEOUT) return NBODY_ETIMEOUT;
+  if (st & NB_ST_BADINPUT) return NBODY_EINVAL;
+  return NBODY_OK;
+}
+
+int validate(const nbody_params* p) {
+  if (!p) return NBODY_EINVAL;
+  if (!(p->theta > 0.0) || !(p->eps > 0.0)) return NBODY_EINVAL;
+  if (p->order < 0 || p->order > 4) return NBODY_EINVAL;
+  if (p->n_leaf < 1 || p->n_leaf > 64) return NBODY_EINVAL;
+  if (p->n_group < 1 || p->n_group > 32) return NBODY_EINVAL;
+  if (p->n_direct < 0 || p->n_direct > p->n_leaf) return NBODY_EINVAL;
+  if (p->lmax < 2 || p->lmax > NB_QBITS) return NBODY_EINVAL;
+  if (p->ewald_order < 0 || p->ewald_order > 5) return NBODY_EINVAL;
+  if (p->ewald_order > 0) {
+    if (p->ewald_level < 1 || p->ewald_level > 4) return NBODY_EINVAL;
+    if (p->ewald_grid < p->ewald_level + 1 || p->ewald_grid > 8) return NBODY_EINVAL;
+  }
+  if (p->precision != NBODY_MIXED && p->precision != NBODY_FP64) return NBODY_EINVAL;
+  return NBODY_OK;
+}
+
+// image level used by the walk even without periodic images
+int image_level(const nbody_params& p) { return p.ewald_order > 0 ? p.ewald_level : 3; }
+int group_level(const nbody_params& p) { return p.ewald_order > 0 ? p.ewald_grid - 1 : 5; }
+
+__global__ void kick_kernel(int64_t n3, float* __restrict__ mom, const float* __restrict__ acc, float k) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    mom[i] = fmaf(k, acc[i], mom[i]);
+}
+
+__global__ void drift_kernel(int64_t n3, double* __restrict__ pos, const float* __restrict__ mom, double d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = pos[i] + d * (double)mom[i];
+    x -= floor(x);
+    if (x >= 1.0) x = 0.0;
+    pos[i] = x;
+  }
+}
+
+__global__ void copy_u64_kernel(const uint64_t* __restrict__ a, uint64_t* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+__global__ void export_cells_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ cB, int what,
+                                    int* __restrict__ out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    if (what == NBODY_EXPORT_CELL_RANGE) {
+      out[2 * b] = cB[b].x;
+      out[2 * b + 1] = cB[b].y;
+    } else {
+      out[b] = cA[b].w & 0xff;
+    }
+  }
+}
+
+__global__ void export_groups_kernel(int ng, const int4* __restrict__ gA, int* __restrict__ out) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    out[2 * g] = gA[g].x;
+    out[2 * g + 1] = gA[g].y;
+  }
+}
+
+__global__ void eps2_kernel(int nbox, const double* __restrict__ eps, float* __restrict__ e32,
+                            double* __restrict__ e64) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+    e32[b] = (float)(eps[b] * eps[b]);
+    e64[b] = eps[b] * eps[b];
+  }
+}
+
+__global__ void max_level_kernel(int ncell, const int4* __restrict__ cA, int* out) {
+  int m = 0;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x)
+    m = max(m, cA[b].w & 0xff);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+int gridn(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+int read_status(nbody_tree* t, cudaStream_t s) {
+  unsigned st = 0;
+  NB_CU(cudaMemcpyAsync(&st, t->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  NB_CU(cudaStreamSynchronize(s));
+  NB_CU(cudaMemsetAsync(t->status.p, 0, sizeof(unsigned), s));
+  return status_to_code(st);
+}
+
+int build_impl(nbody_tree* t, cudaStream_t s) {
+  const nbody_params& p = t->prm;
+  const int64_t n = t->n;
+  const bool fp64 = p.precision == NBODY_FP64;
+  // per-particle buffers
+  NB_CU(t->keys.ensure(8 * n));
+  NB_CU(t->vals.ensure(4 * n));
+  NB_CU(t->keys2.ensure(8 * n));
+  NB_CU(t->vals2.ensure(4 * n));
+  NB_CU(t->box_of.ensure(2 * n));
+  NB_CU(t->sbox.ensure(2 * n));
+  NB_CU(t->spos.ensure(24 * n));
+  NB_CU(t->smass.ensure(4 * n));
+  NB_CU(t->src.ensure((fp64 ? 32 : 16) * n));
+  NB_CU(t->sleaf.ensure(4 * n));
+  NB_CU(t->ccount.ensure(4 * n));
+  NB_CU(t->coff.ensure(4 * n));
+  NB_CU(t->l0.ensure(n));
+  NB_CU(t->gflag.ensure(4 * n));
+  NB_CU(t->gid.ensure(4 * n));
+  NB_CU(t->scantmp.ensure(4 * (nb_scan_tmp_ints(n) + 16)));
+  NB_CU(t->totals.ensure(64));
+  const int64_t tiles = nb_sort_tiles(n) + 1;
+  NB_CU(t->hist.ensure(4 * 256 * 16));
+  NB_CU(t->sstatus.ensure(4 * 256 * tiles * 12));
+  NB_CU(t->tilectr.ensure(4 * 16));
+  NB_CU(t->lvlhist.ensure(4 * 256));
+  NB_CU(t->off.ensure(8 * (t->nbox + 1)));
+  NB_CU(cudaMemcpyAsync(t->off.p, t->h_off.data(), 8 * (t->nbox + 1), cudaMemcpyHostToDevice, s));
+  {
+    NB_CU(t->eps2.ensure(12 * t->nbox + 64));
+    Buf tmp;
+    NB_CU(tmp.ensure(8 * t->nbox));
+    NB_CU(cudaMemcpyAsync(tmp.p, t->h_eps.data(), 8 * t->nbox, cudaMemcpyHostToDevice, s));
+    float* e32 = t->eps2.as<float>();
+    double* e64 = (double*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15));
+    eps2_kernel<<<gridn(t->nbox, 128), 128, 0, s>>>(t->nbox, tmp.as<double>(), e32, e64);
+    NB_CU(cudaStreamSynchronize(s));
+    tmp.release();
+  }
+  SortScratch sc;
+  sc.keys_alt = t->keys2.as<uint64_t>();
+  sc.vals_alt = t->vals2.as<uint32_t>();
+  sc.hist = t->hist.as<uint32_t>();
+  sc.status = t->sstatus.as<uint32_t>();
+  sc.tile_ctr = t->tilectr.as<uint32_t>();
+  sc.tiles_cap = tiles;
+  sc.dstatus = t->status.as<unsigned>();
+
+  if (t->events) NB_CU(cudaEventRecord(t->ev[0], s));
+  // A1 keys, A2 sort, A3 gather
+  NB_CU(nb_launch_box_ids(t->off.as<int64_t>(), t->nbox, n, t->box_of.as<uint16_t>(), s));
+  NB_CU(nb_launch_keys(t->pos, n, 0, t->keys.as<uint64_t>(), t->vals.as<uint32_t>(), s));
+  int alt = 0;
+  NB_CU(nb_radix_sort(t->keys.as<uint64_t>(), t->vals.as<uint32_t>(), n, 63, t->box_of.as<uint16_t>(), t->nbox,
+                      &sc, s, &alt));
+  if (alt) {
+    std::swap(t->keys, t->keys2);
+    std::swap(t->vals, t->vals2);
+  }
+  NB_CU(nb_gather(t->pos, t->mass, t->vals.as<uint32_t>(), t->box_of.as<uint16_t>(), t->off.as<int64_t>(), n,
+                  t->spos.as<double>(), t->smass.as<float>(), t->sbox.as<uint16_t>(), s));
+  if (t->events) NB_CU(cudaEventRecord(t->ev[1], s));
+  // A4 tree: cells per particle, scan, groups flags + scan, read totals
+  NB_CU(nb_count_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, p.n_leaf, p.lmax,
+                       t->ccount.as<int>(), t->l0.as<int8_t>(), s));
+  int* totals = t->totals.as<int>();
+  NB_CU(nb_exclusive_scan_i32(t->ccount.as<int>(), t->coff.as<int>(), n, totals, t->scantmp.as<int>(), s));
+  const int ls = group_level(p);
+  NB_CU(nb_group_flags(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, ls, p.n_group,
+                       t->gflag.as<int>(), s));
+  NB_CU(nb_exclusive_scan_i32(t->gflag.as<int>(), t->gid.as<int>(), n, totals + 1, t->scantmp.as<int>(), s));
+  NB_CU(cudaMemcpyAsync(t->pinned, totals, 8, cudaMemcpyDeviceToHost, s));
+  NB_CU(cudaStreamSynchronize(s));
+  const int ncell = (int)((int*)t->pinned)[0];
+  const int ngroup = (int)((int*)t->pinned)[1];
+  if (ncell <= 0 || ngroup <= 0) return NBODY_EINVAL;
+  t->ncell = ncell;
+  t->ngroup = ngroup;
+  const int cs = nb_coef_stride(p.order);
+  const int nm = (p.order + 1) * (p.order + 2) * (p.order + 3) / 6;
+  NB_CU(t->plevel.ensure(ncell));
+  NB_CU(t->pstart.ensure(4 * (int64_t)ncell));
+  NB_CU(t->pcount.ensure(4 * (int64_t)ncell));
+  NB_CU(t->pparent.ensure(4 * (int64_t)ncell));
+  NB_CU(t->bfs2pre.ensure(4 * (int64_t)ncell));
+  NB_CU(t->pre2bfs.ensure(4 * (int64_t)ncell));
+  NB_CU(t->cA.ensure(16 * (int64_t)ncell));
+  NB_CU(t->cB.ensure(16 * (int64_t)ncell));
+  NB_CU(t->ckey.ensure(8 * (int64_t)ncell));
+  NB_CU(t->cbox.ensure(2 * (int64_t)ncell));
+  NB_CU(t->mom.ensure(8 * (int64_t)ncell * nm));
+  NB_CU(t->arrive.ensure(4 * (int64_t)ncell));
+  NB_CU(t->coef.ensure((fp64 ? 8 : 4) * (int64_t)ncell * cs));
+  uint64_t hc = 1;
+  while (hc < 2 * (uint64_t)ncell) hc <<= 1;
+  t->hcap = hc;
+  NB_CU(t->hval.ensure(4 * hc));
+  NB_CU(t->gstart.ensure(4 * (int64_t)ngroup));
+  NB_CU(t->gA.ensure(16 * (int64_t)ngroup));
+  NB_CU(t->gB.ensure(16 * (int64_t)ngroup));
+  NB_CU(t->gC.ensure(16 * (int64_t)ngroup));
+  NB_CU(t->gD.ensure(16 * (int64_t)ngroup));
+  if (nb_sort_tiles(ncell) + 1 > tiles) {
+    NB_CU(t->sstatus.ensure(4 * 256 * (nb_sort_tiles(ncell) + 1)));
+    sc.status = t->sstatus.as<uint32_t>();
+    sc.tiles_cap = nb_sort_tiles(ncell) + 1;
+  }
+  NB_CU(nb_emit_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, p.n_leaf, p.lmax,
+                      t->ccount.as<int>(), t->coff.as<int>(), t->l0.as<int8_t>(), t->plevel.as<uint8_t>(),
+                      t->pstart.as<int>(), t->pcount.as<int>(), t->pparent.as<int>(), s));
+  NB_CU(nb_sort_digit8(t->plevel.as<uint8_t>(), ncell, t->bfs2pre.as<uint32_t>(), t->lvlhist.as<uint32_t>(), &sc, s));
+  NB_CU(nb_bfs_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), ncell, t->bfs2pre.as<uint32_t>(),
+                     t->pre2bfs.as<int>(), t->plevel.as<uint8_t>(), t->pstart.as<int>(), t->pcount.as<int>(),
+                     t->pparent.as<int>(), t->cA.as<int4>(), t->cB.as<int4>(), t->ckey.as<uint64_t>(),
+                     t->cbox.as<uint16_t>(), s));
+  NB_CU(nb_hash_build(ncell, t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(), t->hval.as<int>(), hc,
+                      t->status.as<unsigned>(), s));
+  NB_CU(nb_leaves(ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(), t->smass.as<float>(), n,
+                  t->sleaf.as<int>(), t->src.p, fp64, s));
+  NB_CU(nb_group_info(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), n, ngroup, ls, t->gflag.as<int>(),
+                      t->gid.as<int>(), t->gstart.as<int>(), t->spos.as<double>(), t->gA.as<int4>(), t->gB.as<int4>(),
+                      t->gC.as<int4>(), t->gD.as<int4>(), s));
+  if (t->events) NB_CU(cudaEventRecord(t->ev[2], s));
+  // A5 moments
+  NB_CU(nb_upward(p.order, fp64, ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
+                  t->smass.as<float>(), n, t->mom.as<double>(), t->arrive.as<int>(), t->coef.p, s));
+  if (p.ewald_order > 0) {
+    const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
+    NB_CU(t->fm.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
+    NB_CU(nb_field_moments(p.ewald_order, p.ewald_level, t->nbox, t->off.as<int64_t>(), t->keys.as<uint64_t>(),
+                           t->spos.as<double>(), t->smass.as<float>(), n, t->fm.as<double>(), s));
+  }
+  if (t->events) NB_CU(cudaEventRecord(t->ev[3], s));
+  return NBODY_OK;
+}
+
+int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
+  const nbody_params& p = t->prm;
+  const bool fp64 = p.precision == NBODY_FP64;
+  const int64_t n = t->n;
+  NB_CU(t->accw.ensure((fp64 ? 24 : 12) * n));
+  NB_CU(t->counters.ensure(64));
+  NB_CU(t->gctr.ensure(64));
+  const int warps = nb_walk_warps(fp64);
+  if (t->walk_blocks == 0) t->walk_blocks = t->nsm * 8;
+  NB_CU(t->stack.ensure(4 * (int64_t)t->walk_blocks * warps * kStackCap));
+  NB_CU(cudaMemsetAsync(t->counters.p, 0, 64, s));
+  for (int l = 0; l < NB_NLEV; l++) {
+    double sl = ldexp(1.0, 23 - l);
+    double T = floor((sl * sl) / (p.theta * p.theta));
+    t->thr[l] = T > 4.0e18 ? (long long)4000000000000000000LL : (long long)T;
+  }
+  const void* eps2 = fp64 ? (const void*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15)) : t->eps2.p;
+  if (p.ewald_order > 0) {
+    NB_CU(nb_phitilde_table(p.ewald_grid, p.ewald_order + 1, &t->tab64, &t->tab32, s));
+  }
+  if (t->events) NB_CU(cudaEventRecord(t->ev[4], s));
+  DevTree tr = t->dev();
+  unsigned long long* ctr = t->counters.as<unsigned long long>();
+  NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
+                t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
+                t->status.as<unsigned>(), t->nsm, s));
+  if (t->events) NB_CU(cudaEventRecord(t->ev[5], s));
+  const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
+  NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
+                    t->accw.p, acc, ctr + 2, s));
+  if (t->events) NB_CU(cudaEventRecord(t->ev[6], s));
+  return NBODY_OK;
+}
+
+int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, const double* eps_host,
+              const double* pos, const float* mass, nbody_tree** tree, cudaStream_t s) {
+  if (!tree || !pos || !offsets || nbox < 1 || nbox > NB_MAX_NBOX) return NBODY_EINVAL;
+  int rc = validate(params);
+  if (rc) return rc;
+  if (offsets[0] != 0) return NBODY_EINVAL;
+  for (int b = 0; b < nbox; b++)
+    if (offsets[b + 1] <= offsets[b]) return NBODY_EINVAL;
+  const int64_t n = offsets[nbox];
+  if (n <= 0 || n >= ((int64_t)1 << 30)) return NBODY_EINVAL;
+  if (eps_host)
+    for (int b = 0; b < nbox; b++)
+      if (!(eps_host[b] > 0.0)) return NBODY_EINVAL;
+  nbody_tree* t = *tree;
+  bool fresh = false;
+  if (!t) {
+    t = new (std::nothrow) nbody_tree();
+    if (!t) return NBODY_ENOMEM;
+    fresh = true;
+    if (cudaGetDevice(&t->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&t->nsm, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess ||
+        cudaMallocHost(&t->pinned, 64) != cudaSuccess || t->status.ensure(64) != cudaSuccess) {
+      cudaGetLastError();
+      delete t;
+      return NBODY_ECUDA;
+    }
+    cudaMemset(t->status.p, 0, 64);
+    for (auto& e : t->ev) cudaEventCreate(&e);
+    t->events = true;
+  }
+  t->prm = *params;
+  t->nbox = nbox;
+  t->n = n;
+  t->pos = pos;
+  t->mass = mass;
+  t->h_off.assign(offsets, offsets + nbox + 1);
+  t->h_eps.resize(nbox);
+  for (int b = 0; b < nbox; b++) t->h_eps[b] = eps_host ? eps_host[b] : params->eps;
+  rc = build_impl(t, s);
+  if (rc == NBODY_OK && !(params->flags & NBODY_FLAG_ASYNC)) rc = read_status(t, s);
+  if (rc != NBODY_OK && fresh) {
+    delete t;
+    return rc;
+  }
+  *tree = t;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nbody_default_params(nbody_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->eps = 1.0 / (30.0 * 128.0);
+  p->theta = 0.6;
+  p->order = 4;
+  p->n_leaf = 16;
+  p->n_group = 32;
+  p->n_direct = 4;
+  p->lmax = 21;
+  p->ewald_order = 4;
+  p->ewald_level = 3;
+  p->ewald_grid = 6;
+  p->precision = NBODY_MIXED;
+  p->flags = 0;
+}
+
+int nbody_build_tree(const nbody_params* params, int64_t n, const double* pos_dev, const float* mass_dev,
+                     nbody_tree** tree, nbody_stream_t stream) {
+  if (n <= 0) return NBODY_EINVAL;
+  int64_t off[2] = {0, n};
+  return make_tree(params, 1, off, nullptr, pos_dev, mass_dev, tree, (cudaStream_t)stream);
+}
+
+int nbody_build_tree_batched(const nbody_params* params, int nbox, const int64_t* offsets_host,
+                             const double* eps_host, const double* pos_dev, const float* mass_dev,
+                             nbody_tree** tree, nbody_stream_t stream) {
+  return make_tree(params, nbox, offsets_host, eps_host, pos_dev, mass_dev, tree, (cudaStream_t)stream);
+}
+
+int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_stream_t stream) {
+  if (!tree || !acc_dev) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = forces_impl(tree, acc_dev, s);
+  if (rc) return rc;
+  if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  rc = read_status(tree, s);
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    unsigned long long c[3] = {0, 0, 0};
+    if (cudaMemcpy(c, tree->counters.p, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      stats->p2p = (double)c[0];
+      stats->m2p = (double)c[1];
+      stats->m2l = (double)c[2];
+    }
+    stats->ncells = tree->ncell;
+    stats->ngroups = tree->ngroup;
+    stats->nbox = tree->nbox;
+    int* ml = nullptr;
+    if (cudaMalloc(&ml, sizeof(int)) == cudaSuccess) {
+      cudaMemsetAsync(ml, 0, sizeof(int), s);
+      max_level_kernel<<<gridn(tree->ncell, 256), 256, 0, s>>>(tree->ncell, tree->cA.as<int4>(), ml);
+      int v = 0;
+      if (cudaMemcpyAsync(&v, ml, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+          cudaStreamSynchronize(s) == cudaSuccess)
+        stats->max_level = v;
+      cudaFree(ml);
+    }
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, tree->ev[0], tree->ev[1]) == cudaSuccess) stats->ms_sort = ms;
+    if (cudaEventElapsedTime(&ms, tree->ev[1], tree->ev[2]) == cudaSuccess) stats->ms_build = ms;
+    if (cudaEventElapsedTime(&ms, tree->ev[2], tree->ev[3]) == cudaSuccess) stats->ms_upward = ms;
+    if (cudaEventElapsedTime(&ms, tree->ev[4], tree->ev[5]) == cudaSuccess) stats->ms_walk = ms;
+    if (cudaEventElapsedTime(&ms, tree->ev[5], tree->ev[6]) == cudaSuccess) stats->ms_periodic = ms;
+    cudaGetLastError();
+  }
+  return rc;
+}
+
+int nbody_kdk_step(nbody_tree* tree, double* pos_dev, float* mom_dev, float* acc_dev, double a0, double a1,
+                   nbody_stream_t stream) {
+  if (!tree || !pos_dev || !mom_dev || !acc_dev || !(a0 > 0.0) || !(a1 > 0.0)) return NBODY_EINVAL;
+  if (pos_dev != tree->pos) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double H0 = sqrt(8.0 * M_PI / 3.0);
+  const double ah = sqrt(a0 * a1);
+  const double K1 = 2.0 / H0 * (sqrt(ah) - sqrt(a0));
+  const double K2 = 2.0 / H0 * (sqrt(a1) - sqrt(ah));
+  const double D = 2.0 / H0 * (1.0 / sqrt(a0) - 1.0 / sqrt(a1));
+  const int64_t n3 = 3 * tree->n;
+  kick_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, mom_dev, acc_dev, (float)K1);
+  drift_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, pos_dev, mom_dev, D);
+  NB_CU(cudaGetLastError());
+  int rc = build_impl(tree, s);
+  if (rc) return rc;
+  rc = forces_impl(tree, acc_dev, s);
+  if (rc) return rc;
+  kick_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, mom_dev, acc_dev, (float)K2);
+  NB_CU(cudaGetLastError());
+  if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  return read_status(tree, s);
+}
+
+int nbody_kdk_adjoint(nbody_tree*, const double*, const float*, double, double, const double*, const float*,
+                      double*, float*, nbody_stream_t) {
+  return NBODY_ENOTSUP;
+}
+
+int nbody_forces_vjp(nbody_tree*, const float*, double*, nbody_stream_t) { return NBODY_ENOTSUP; }
+
+int64_t nbody_tree_count(const nbody_tree* t, int what) {
+  if (!t) return NBODY_EINVAL;
+  switch (what) {
+    case NBODY_EXPORT_SORTED_KEYS:
+    case NBODY_EXPORT_PERM: return t->n;
+    case NBODY_EXPORT_CELL_KEYS:
+    case NBODY_EXPORT_CELL_RANGE:
+    case NBODY_EXPORT_CELL_LEVEL:
+    case NBODY_EXPORT_MOMENTS: return t->ncell;
+    case NBODY_EXPORT_GROUPS: return t->ngroup;
+    default: return NBODY_EINVAL;
+  }
+}
+
+int nbody_tree_export(const nbody_tree* t, int what, void* dst, nbody_stream_t stream) {
+  if (!t || !dst) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nm = (t->prm.order + 1) * (t->prm.order + 2) * (t->prm.order + 3) / 6;
+  switch (what) {
+    case NBODY_EXPORT_SORTED_KEYS:
+      NB_CU(cudaMemcpyAsync(dst, t->keys.p, 8 * t->n, cudaMemcpyDeviceToDevice, s));
+      break;
+    case NBODY_EXPORT_PERM: NB_CU(cudaMemcpyAsync(dst, t->vals.p, 4 * t->n, cudaMemcpyDeviceToDevice, s)); break;
+    case NBODY_EXPORT_CELL_KEYS:
+      NB_CU(cudaMemcpyAsync(dst, t->ckey.p, 8 * (int64_t)t->ncell, cudaMemcpyDeviceToDevice, s));
+      break;
+    case NBODY_EXPORT_CELL_RANGE:
+    case NBODY_EXPORT_CELL_LEVEL:
+      export_cells_kernel<<<gridn(t->ncell, 256), 256, 0, s>>>(t->ncell, t->cA.as<int4>(), t->cB.as<int4>(), what,
+                                                                (int*)dst);
+      break;
+    case NBODY_EXPORT_MOMENTS:
+      NB_CU(cudaMemcpyAsync(dst, t->mom.p, 8 * (int64_t)t->ncell * nm, cudaMemcpyDeviceToDevice, s));
+      break;
+    case NBODY_EXPORT_GROUPS:
+      export_groups_kernel<<<gridn(t->ngroup, 256), 256, 0, s>>>(t->ngroup, t->gA.as<int4>(), (int*)dst);
+      break;
+    default: return NBODY_EINVAL;
+  }
+  NB_CU(cudaGetLastError());
+  NB_CU(cudaStreamSynchronize(s));
+  return NBODY_OK;
+}
+
+int nbody_tree_lookup(const nbody_tree* t, const uint64_t* keys_dev, int64_t nkeys, int32_t* idx_dev,
+                      nbody_stream_t stream) {
+  if (!t || !keys_dev || !idx_dev || nkeys < 0) return NBODY_EINVAL;
+  if (nkeys == 0) return NBODY_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  NB_CU(nb_hash_lookup(keys_dev, nkeys, 0, t->hval.as<int>(), t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(),
+                       t->hcap, (int*)idx_dev, s));
+  NB_CU(cudaStreamSynchronize(s));
+  return NBODY_OK;
+}
+
+int nbody_check(nbody_tree* t, nbody_stream_t stream) {
+  if (!t) return NBODY_EINVAL;
+  return read_status(t, (cudaStream_t)stream);
+}
+
+void nbody_tree_free(nbody_tree* t) { delete t; }
+
+const char* nbody_strerror(int code) {
+  switch (code) {
+    case NBODY_OK: return "success";
+    case NBODY_EINVAL: return "invalid argument";
+    case NBODY_ENOMEM: return "device memory allocation failed";
+    case NBODY_ECUDA: return "CUDA runtime error";
+    case NBODY_EOVERFLOW: return "fixed-capacity device buffer overflow";
+    case NBODY_ETIMEOUT: return "bounded device wait ran out";
+    case NBODY_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,403 @@
+// Oct-tree from sorted Morton keys (Sec. 2.1: the key order implicitly
+// defines the tree; parent and daughter keys follow by bit operations; a hash
+// table maps a cell key to its storage).
+//
+// A cell is a key prefix.  A level-l prefix exists as a cell iff l = 0 (the
+// box root) or its parent prefix holds more than n_leaf particles and the
+// parent's level is below lmax.  Every cell starts at the first particle of
+// its prefix range, so the cells starting at particle i are the levels
+// l0(i) .. l0(i)+c_i-1 with l0(i) = (common-prefix level with particle i-1)+1.
+// Counting c_i per particle and scanning gives the cells in depth-first
+// (pre-)order; one stable pass by level turns that into breadth-first order,
+// in which the daughters of a cell are contiguous.
+#include "common.cuh"
+
+namespace {
+
+__device__ __forceinline__ uint64_t prefix_of(uint64_t k, int level) {
+  return level == 0 ? 0ull : (k >> (3 * (NB_QBITS - level)));
+}
+
+// first index in [lo, hi) whose level-l prefix is >= P
+__device__ __forceinline__ int64_t lower_pref(const uint64_t* __restrict__ k, int64_t lo, int64_t hi,
+                                              uint64_t P, int level) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (prefix_of(k[mid], level) < P) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+// first index in [lo, hi) whose level-l prefix is > P
+__device__ __forceinline__ int64_t upper_pref(const uint64_t* __restrict__ k, int64_t lo, int64_t hi,
+                                              uint64_t P, int level) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (prefix_of(k[mid], level) <= P) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int first_level(const uint64_t* __restrict__ k, int64_t i, int64_t bb) {
+  if (i == bb) return 0;
+  uint64_t x = k[i - 1] ^ k[i];
+  if (x == 0ull) return NB_NLEV;  // identical key: starts no cell
+  return (__clzll((long long)x) - 1) / 3 + 1;
+}
+
+struct BuildArgs {
+  const uint64_t* skeys;
+  const uint16_t* sbox;
+  const int64_t* off;
+  int64_t n;
+  int n_leaf, lmax;
+};
+
+__global__ void count_cells_kernel(BuildArgs a, int* __restrict__ ccount, int8_t* __restrict__ l0out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int b = a.sbox[i];
+    int64_t bb = a.off[b], be = a.off[b + 1];
+    int l0 = first_level(a.skeys, i, bb);
+    int c = 0;
+    if (l0 <= a.lmax) {
+      uint64_t k = a.skeys[i];
+      bool exists = true;
+      if (l0 > 0) {
+        uint64_t pp = prefix_of(k, l0 - 1);
+        int64_t lo = lower_pref(a.skeys, bb, i + 1, pp, l0 - 1);
+        int64_t hi = upper_pref(a.skeys, i, be, pp, l0 - 1);
+        exists = (hi - lo) > a.n_leaf;
+      }
+      if (exists) {
+        int l = l0;
+        while (true) {
+          c++;
+          int64_t hi = upper_pref(a.skeys, i, be, prefix_of(k, l), l);
+          if (hi - i > a.n_leaf && l < a.lmax) l++; else break;
+        }
+      }
+    }
+    ccount[i] = c;
+    l0out[i] = (int8_t)l0;
+  }
+}
+
+__global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, const int* __restrict__ coff,
+                                  const int8_t* __restrict__ l0in, uint8_t* __restrict__ plevel,
+                                  int* __restrict__ pstart, int* __restrict__ pcount,
+                                  int* __restrict__ pparent) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int c = ccount[i];
+    if (c == 0) continue;
+    int b = a.sbox[i];
+    int64_t bb = a.off[b], be = a.off[b + 1];
+    int l0 = l0in[i];
+    uint64_t k = a.skeys[i];
+    int p0 = coff[i];
+    for (int t = 0; t < c; t++) {
+      int l = l0 + t, p = p0 + t;
+      int64_t hi = upper_pref(a.skeys, i, be, prefix_of(k, l), l);
+      plevel[p] = (uint8_t)l;
+      pstart[p] = (int)i;
+      pcount[p] = (int)(hi - i);
+      int par;
+      if (t > 0) par = p - 1;
+      else if (l == 0) par = -1;
+      else {
+        int64_t s = lower_pref(a.skeys, bb, i + 1, prefix_of(k, l - 1), l - 1);
+        par = coff[s] + (l - 1 - (int)l0in[s]);
+      }
+      pparent[p] = par;
+    }
+  }
+}
+
+__global__ void bfs_fill_kernel(BuildArgs a, int ncell, const uint32_t* __restrict__ bfs2pre,
+                                int* __restrict__ pre2bfs) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x)
+    pre2bfs[bfs2pre[b]] = b;
+}
+
+__global__ void bfs_cells_kernel(BuildArgs a, int ncell, const uint32_t* __restrict__ bfs2pre,
+                                 const int* __restrict__ pre2bfs, const uint8_t* __restrict__ plevel,
+                                 const int* __restrict__ pstart, const int* __restrict__ pcount,
+                                 const int* __restrict__ pparent, int4* __restrict__ cA,
+                                 int4* __restrict__ cB, uint64_t* __restrict__ ckey,
+                                 uint16_t* __restrict__ cbox) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    int p = bfs2pre[b];
+    int l = plevel[p];
+    int s = pstart[p];
+    uint64_t pre = prefix_of(a.skeys[s], l);
+    int ix = (int)compact3(pre), iy = (int)compact3(pre >> 1), iz = (int)compact3(pre >> 2);
+    cA[b] = make_int4(cell_c2(ix, l), cell_c2(iy, l), cell_c2(iz, l), l);
+    int par = pparent[p];
+    cB[b] = make_int4(s, pcount[p], 0, par >= 0 ? pre2bfs[par] : -1);
+    ckey[b] = (1ull << (3 * l)) | pre;
+    cbox[b] = a.sbox[s];
+  }
+}
+
+// daughters of a cell are contiguous in breadth-first order
+__global__ void children_kernel(int ncell, int4* __restrict__ cB) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    int par = cB[b].w;
+    if (par < 0) continue;
+    if (b == 0 || cB[b - 1].w != par) cB[par].z = b;  // first daughter
+  }
+}
+
+__global__ void nchild_kernel(int ncell, int4* __restrict__ cA, const int4* __restrict__ cB) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    int par = cB[b].w;
+    if (par < 0) continue;
+    bool last = (b == ncell - 1) || (cB[b + 1].w != par);
+    if (last) {
+      int nch = b - cB[par].z + 1;
+      cA[par].w = (cA[par].w & 0xff) | (nch << 8);
+    }
+  }
+}
+
+// ---- hash of cell keys (open addressing, linear probing) ------------------------
+__device__ __forceinline__ uint64_t hmix(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+// slots hold cell indices (-1 = empty); a slot matches when the cell's key
+// and box equal the query
+__global__ void hash_insert_kernel(int ncell, const uint64_t* __restrict__ ckey,
+                                   const uint16_t* __restrict__ cbox, int* __restrict__ hval,
+                                   uint64_t mask, unsigned* err) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    uint64_t h = hmix(ckey[b] ^ ((uint64_t)cbox[b] * 0x9e3779b97f4a7c15ull)) & mask;
+    bool done = false;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+      if (atomicCAS(&hval[h], -1, b) == -1) {
+        done = true;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    if (!done) atomicOr(err, NB_ST_OVERFLOW);
+  }
+}
+
+__global__ void hash_lookup_kernel(const uint64_t* __restrict__ q, int64_t nq, int box,
+                                   const int* __restrict__ hval, const uint64_t* __restrict__ ckey,
+                                   const uint16_t* __restrict__ cbox, uint64_t mask, int* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = q[i];
+    uint64_t h = hmix(k ^ ((uint64_t)box * 0x9e3779b97f4a7c15ull)) & mask;
+    int r = -1;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+      int v = hval[h];
+      if (v < 0) break;
+      if (ckey[v] == k && cbox[v] == box) {
+        r = v;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+    out[i] = r;
+  }
+}
+
+// ---- leaves: particle -> leaf and leaf-relative FP32/FP64 source records ----------
+template <typename T>
+__global__ void leaf_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ cB,
+                            const double* __restrict__ spos, const float* __restrict__ smass, int64_t n,
+                            int* __restrict__ sleaf, typename Vec4<T>::type* __restrict__ src) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    int4 a = cA[b];
+    if ((a.w >> 8) != 0) continue;  // not a leaf
+    int4 r = cB[b];
+    double cx = ldexp((double)a.x, -23), cy = ldexp((double)a.y, -23), cz = ldexp((double)a.z, -23);
+    for (int j = r.x; j < r.x + r.y; j++) {
+      sleaf[j] = b;
+      typename Vec4<T>::type v;
+      v.x = (T)(spos[j] - cx);
+      v.y = (T)(spos[n + j] - cy);
+      v.z = (T)(spos[2 * n + j] - cz);
+      v.w = (T)smass[j];
+      src[j] = v;
+    }
+  }
+}
+
+// ---- groups: runs of <= n_group particles inside one level-ls cell -------------------
+__global__ void group_flag_kernel(BuildArgs a, int ls, int n_group, int* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int b = a.sbox[i];
+    int64_t bb = a.off[b];
+    uint64_t P = prefix_of(a.skeys[i], ls);
+    int64_t rs = lower_pref(a.skeys, bb, i + 1, P, ls);
+    flag[i] = ((i - rs) % n_group) == 0 ? 1 : 0;
+  }
+}
+
+__global__ void group_start_kernel(int64_t n, const int* __restrict__ flag, const int* __restrict__ gid,
+                                   int* __restrict__ gstart) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) gstart[gid[i]] = (int)i;
+}
+
+// one warp per group: count, box, integer bounding box and expansion point
+__global__ void group_info_kernel(BuildArgs a, int ngroup, int ls, const int* __restrict__ gstart,
+                                  const double* __restrict__ spos, int4* __restrict__ gA,
+                                  int4* __restrict__ gB, int4* __restrict__ gC, int4* __restrict__ gD) {
+  const int lane = threadIdx.x & 31;
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup;
+       g += (gridDim.x * blockDim.x) >> 5) {
+    int s = gstart[g];
+    int e = (g + 1 < ngroup) ? gstart[g + 1] : (int)a.n;
+    int cnt = e - s;
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    if (lane < cnt) {
+      int i = s + lane;
+      for (int d = 0; d < 3; d++) {
+        int q = (int)quant21(spos[d * a.n + i]);
+        lo[d] = 2 * q;
+        hi[d] = 2 * q + 2;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1)
+      for (int d = 0; d < 3; d++) {
+        lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+        hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+      }
+    if (lane == 0) {
+      uint64_t P = prefix_of(a.skeys[s], ls);
+      int ix = (int)compact3(P), iy = (int)compact3(P >> 1), iz = (int)compact3(P >> 2);
+      gA[g] = make_int4(s, cnt, a.sbox[s], 0);
+      gB[g] = make_int4(lo[0] + hi[0], lo[1] + hi[1], lo[2] + hi[2], 0);
+      gC[g] = make_int4(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 0);
+      gD[g] = make_int4(cell_c2(ix, ls), cell_c2(iy, ls), cell_c2(iz, ls), 0);
+    }
+  }
+}
+
+__global__ void gather_kernel(const double* __restrict__ pos, const float* __restrict__ mass,
+                              const uint32_t* __restrict__ perm, const uint16_t* __restrict__ sbox,
+                              const int64_t* __restrict__ off, int64_t n, double* __restrict__ spos,
+                              float* __restrict__ smass) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t j = perm[i];
+    for (int d = 0; d < 3; d++) {
+      double x = pos[d * n + j];
+      x -= floor(x);  // wrap into [0,1)
+      if (x >= 1.0) x = 0.0;
+      spos[d * n + i] = x;
+    }
+    if (mass) smass[i] = mass[j];
+    else {
+      int b = sbox[i];
+      smass[i] = (float)(1.0 / (double)(off[b + 1] - off[b]));
+    }
+  }
+}
+
+__global__ void sbox_kernel(const uint32_t* __restrict__ perm, const uint16_t* __restrict__ box_of,
+                            int64_t n, uint16_t* __restrict__ sbox) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    sbox[i] = box_of[perm[i]];
+}
+
+int gridn(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 64) g = 152 * 64;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---- host launchers --------------------------------------------------------
+cudaError_t nb_gather(const double* pos, const float* mass, const uint32_t* perm, const uint16_t* box_of,
+                      const int64_t* off, int64_t n, double* spos, float* smass, uint16_t* sbox,
+                      cudaStream_t s) {
+  sbox_kernel<<<gridn(n, 256), 256, 0, s>>>(perm, box_of, n, sbox);
+  gather_kernel<<<gridn(n, 256), 256, 0, s>>>(pos, mass, perm, sbox, off, n, spos, smass);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_count_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n,
+                           int n_leaf, int lmax, int* ccount, int8_t* l0, cudaStream_t s) {
+  BuildArgs a{skeys, sbox, off, n, n_leaf, lmax};
+  count_cells_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ccount, l0);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n,
+                          int n_leaf, int lmax, const int* ccount, const int* coff, const int8_t* l0,
+                          uint8_t* plevel, int* pstart, int* pcount, int* pparent, cudaStream_t s) {
+  BuildArgs a{skeys, sbox, off, n, n_leaf, lmax};
+  emit_cells_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ccount, coff, l0, plevel, pstart, pcount, pparent);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const uint32_t* bfs2pre,
+                         int* pre2bfs, const uint8_t* plevel, const int* pstart, const int* pcount,
+                         const int* pparent, int4* cA, int4* cB, uint64_t* ckey, uint16_t* cbox,
+                         cudaStream_t s) {
+  BuildArgs a{skeys, sbox, nullptr, 0, 0, 0};
+  bfs_fill_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, ncell, bfs2pre, pre2bfs);
+  bfs_cells_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, ncell, bfs2pre, pre2bfs, plevel, pstart, pcount,
+                                                     pparent, cA, cB, ckey, cbox);
+  children_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, cB);
+  nchild_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, cA, cB);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_hash_build(int ncell, const uint64_t* ckey, const uint16_t* cbox, int* hval, uint64_t cap,
+                          unsigned* err, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(hval, 0xff, sizeof(int) * cap, s);
+  if (e) return e;
+  hash_insert_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, ckey, cbox, hval, cap - 1, err);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_hash_lookup(const uint64_t* q, int64_t nq, int box, const int* hval, const uint64_t* ckey,
+                           const uint16_t* cbox, uint64_t cap, int* out, cudaStream_t s) {
+  hash_lookup_kernel<<<gridn(nq, 256), 256, 0, s>>>(q, nq, box, hval, ckey, cbox, cap - 1, out);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* spos, const float* smass,
+                      int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s) {
+  if (fp64)
+    leaf_kernel<double><<<gridn(ncell, 128), 128, 0, s>>>(ncell, cA, cB, spos, smass, n, sleaf,
+                                                          (dbl4*)src);
+  else
+    leaf_kernel<float><<<gridn(ncell, 128), 128, 0, s>>>(ncell, cA, cB, spos, smass, n, sleaf,
+                                                         (float4*)src);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n,
+                           int ls, int n_group, int* flag, cudaStream_t s) {
+  BuildArgs a{skeys, sbox, off, n, 0, 0};
+  group_flag_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ls, n_group, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, int ls,
+                          const int* flag, const int* gid, int* gstart, const double* spos, int4* gA,
+                          int4* gB, int4* gC, int4* gD, cudaStream_t s) {
+  BuildArgs a{skeys, sbox, nullptr, n, 0, 0};
+  group_start_kernel<<<gridn(n, 256), 256, 0, s>>>(n, flag, gid, gstart);
+  group_info_kernel<<<gridn((int64_t)ngroup * 32, 256), 256, 0, s>>>(a, ngroup, ls, gstart, spos, gA, gB,
+                                                                      gC, gD);
+  return cudaGetLastError();
+}

@@ -1,0 +1,120 @@
+// Internal declarations shared by the CUDA translation units of libnbody.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nbody.h"
+
+#define NB_QBITS 21            // key bits per axis
+#define NB_NLEV 22             // levels 0..21
+#define NB_PBOX (1 << 23)      // one box in integer units of 2^-23
+#define NB_MAX_NBOX 65535
+
+// device status bits (OR-ed into the tree's status word)
+#define NB_ST_OVERFLOW 1u
+#define NB_ST_TIMEOUT 2u
+#define NB_ST_BADINPUT 4u
+
+// bounded spin limit for decoupled look-back waits
+#define NB_SPIN_LIMIT (1 << 22)
+
+__device__ __forceinline__ float nbody_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double nbody_rsqrt(double x) { return rsqrt(x); }
+
+struct __align__(32) dbl4 {
+  double x, y, z, w;
+};
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef dbl4 type; };
+
+// level-l cell centre in units of 2^-23 from its integer index at that level
+__host__ __device__ __forceinline__ int cell_c2(int i, int level) {
+  return (2 * i + 1) << (22 - level);
+}
+
+// image shift k (in boxes) of a point c2 (units 2^-23) nearest the point g2
+__host__ __device__ __forceinline__ int img_shift(int c2, int g2) {
+  int delta = c2 - g2;
+  int red = ((delta + (NB_PBOX >> 1)) & (NB_PBOX - 1)) - (NB_PBOX >> 1);  // [-2^22, 2^22)
+  return (delta - red) >> 23;
+}
+
+// 21-bit spreads for Morton interleaving (x in bit 3b, y in 3b+1, z in 3b+2)
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x1fffffull;
+  return (uint32_t)x;
+}
+
+// quantised coordinate floor(x 2^21) mod 2^21 (x is wrapped to [0,1) first)
+__device__ __forceinline__ uint32_t quant21(double x) {
+  double f = floor(x * 2097152.0);
+  long long q = (long long)f;
+  q %= 2097152LL;
+  if (q < 0) q += 2097152LL;
+  return (uint32_t)q;
+}
+
+// ---- device-side tree description passed to kernels -------------------------
+struct DevTree {
+  int64_t n;
+  int nbox;
+  const int64_t* off;      // nbox+1 particle offsets (device)
+  const uint64_t* skeys;   // sorted keys
+  const uint32_t* perm;    // sorted -> original index
+  const uint16_t* sbox;    // box id per sorted particle
+  const double* spos;      // 3n sorted positions (SoA)
+  const float* smass;      // sorted masses
+  int ncell;
+  const int4* cA;          // c2x, c2y, c2z, level | nchild << 8
+  const int4* cB;          // start, count, child, parent
+  int ngroup;
+  const int4* gA;          // start, count, box, 0
+  const int4* gB;          // g2x, g2y, g2z, 0 (box centre, units 2^-23)
+  const int4* gC;          // w2x, w2y, w2z, 0 (half widths, units 2^-23)
+  const int4* gD;          // e2x, e2y, e2z, 0 (expansion point, units 2^-23)
+  const int* sleaf;        // leaf cell of each sorted particle
+};
+
+// ---- host launchers (each returns cudaError_t of the launch) ---------------------
+cudaError_t nb_launch_keys(const double* pos, int64_t n, int64_t box_n0, uint64_t* keys,
+                           uint32_t* vals, cudaStream_t s);
+cudaError_t nb_launch_box_ids(const int64_t* off, int nbox, int64_t n, uint16_t* box_of,
+                              cudaStream_t s);
+// stable LSD onesweep radix sort of (key, val); sorts bits [bit0, bit1) of
+// the key, then (if box_of != NULL and nbox > 1) by box id of the value.
+struct SortScratch {
+  uint64_t* keys_alt;
+  uint32_t* vals_alt;
+  uint32_t* hist;       // 16 passes x 256
+  uint32_t* status;     // tiles x 256 x passes
+  uint32_t* tile_ctr;   // passes
+  int64_t tiles_cap;
+  unsigned* dstatus;    // error word
+};
+cudaError_t nb_radix_sort(uint64_t* keys, uint32_t* vals, int64_t n, int bit1,
+                          const uint16_t* box_of_orig, int nbox, SortScratch* sc, cudaStream_t s,
+                          int* result_in_alt);
+// stable sort of a small-range 8-bit digit array (one pass), values = index
+cudaError_t nb_sort_digit8(const uint8_t* digit, int64_t n, uint32_t* order_out, uint32_t* hist_out,
+                           SortScratch* sc, cudaStream_t s);
+int64_t nb_sort_tiles(int64_t n);
+
+cudaError_t nb_exclusive_scan_i32(const int* in, int* out, int64_t n, int* total_dev, int* tmp,
+                                  cudaStream_t s);
+int64_t nb_scan_tmp_ints(int64_t n);

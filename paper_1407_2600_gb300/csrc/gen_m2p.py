@@ -1,0 +1,310 @@
+"""Generate m2p_gen.cuh: straight-line multipole-to-particle code.
+
+The acceleration of a cell with moments M_n (about its geometric centre) at
+R = x - c is the truncated expansion of Sec. 2.1's multipole method,
+
+    a_i = sum_{|n|<=p} C_n d^{n+e_i} g(R),  C_n = (-1)^|n| M_n / n!,
+    g(R) = (|R|^2 + eps^2)^(-1/2).
+
+With s = |R|^2 + eps^2 and F_j = (-1)^j (2j-1)!! s^(-1/2-j), the Hermite form
+d^n g = sum_k h(n,k) R^(n-2k) F_{|n|-|k|},
+h(n,k) = prod_d n_d! / (k_d! (n_d - 2k_d)! 2^k_d), regroups the potential as
+
+    phi(R) = sum_j F_j S_j(R),   S_j(R) = sum_a B_{j,a} R^a,
+    B_{j,a} = sum_{n - 2k = a, |n| - |k| = j} C_n h(n,k),
+
+so that, with d_i F_j = R_i F_{j+1},
+
+    a_i = d_i phi = sum_j ( R_i F_{j+1} S_j + F_j d_i S_j ).
+
+The per-cell coefficients B_{j,a} are formed once in the upward pass (FP64)
+and stored in the walk's precision; each M2P then costs a few hundred flops.
+Run ``python gen_m2p.py`` to regenerate; a CPU test checks that the committed
+header equals this script's output.
+"""
+from __future__ import annotations
+
+import math
+import os
+import sys
+from itertools import product
+
+
+def multi(p):
+    out = []
+    for o in range(p + 1):
+        for nx in range(o, -1, -1):
+            for ny in range(o - nx, -1, -1):
+                out.append((nx, ny, o - nx - ny))
+    return out
+
+
+def hcoef(n, k):
+    c = 1.0
+    for d in range(3):
+        c *= math.factorial(n[d]) / (math.factorial(k[d]) * math.factorial(n[d] - 2 * k[d]) * 2 ** k[d])
+    return c
+
+
+def slots(p):
+    """(j, a) pairs of the reduced expansion, in storage order."""
+    out = []
+    for j in range(p + 1):
+        for a in multi(p):
+            s = sum(a)
+            if s <= j and 2 * j - s <= p:
+                out.append((j, a))
+    return out
+
+
+def contributions(p):
+    """For each slot: list of (moment index, coefficient multiplying M_n)."""
+    mi = {m: i for i, m in enumerate(multi(p))}
+    sl = slots(p)
+    idx = {s: i for i, s in enumerate(sl)}
+    contrib = [[] for _ in sl]
+    for n in multi(p):
+        on = sum(n)
+        sign = -1.0 if on % 2 else 1.0
+        nf = math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2])
+        for k in product(*(range(n[d] // 2 + 1) for d in range(3))):
+            a = tuple(n[d] - 2 * k[d] for d in range(3))
+            j = on - sum(k)
+            contrib[idx[(j, a)]].append((mi[n], sign / nf * hcoef(n, k)))
+    return sl, contrib
+
+
+def flop_count(p):
+    """Flops of the generated M2P (FMA = 2, rsqrt = 1), excluding R = x - c."""
+    mon = multi(p)
+    fl = 0
+    fl += 6  # s = eps2 + Rx^2 + Ry^2 + Rz^2: 3 FMA
+    fl += 1  # rsqrt
+    fl += 1  # inv_s = F0*F0
+    fl += 2 * (p + 1)  # F_j chain: c_j = k*inv_s, F_j = F_{j-1}*c_j
+    fl += len(mon) - 1  # monomials
+    sl = slots(p)
+    for (j, a) in sl:
+        fl += 2  # S_j FMA
+        for d in range(3):
+            if a[d] > 0:
+                fl += 2  # G_{j,d} FMA
+                if a[d] > 1:
+                    fl += 1  # integer scale
+    fl += (p + 1) * (1 + 3 * 4)  # t_j = F_{j+1} S_j; a_i += R_i t_j + F_j G_ji
+    return fl
+
+
+def emit_m2p(p):
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    sl = slots(p)
+    L = []
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void m2p_p%d(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2," % p)
+    L.append("                                     T& ax, T& ay, T& az) {")
+    L.append("  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));")
+    L.append("  const T F0 = nbody_rsqrt(s);")
+    L.append("  const T is = F0 * F0;")
+    for j in range(1, p + 2):
+        L.append("  const T F%d = F%d * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
+    # monomials
+    L.append("  const T m0 = T(1);")
+    for i, m in enumerate(mon):
+        if i == 0:
+            continue
+        # parent: reduce the first nonzero axis
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                pi = mi[tuple(par)]
+                R = "RxRyRz"[2 * d:2 * d + 2]
+                L.append("  const T m%d = %s * %s;" % (i, "m%d" % pi if pi else "T(1)", R))
+                break
+    for j in range(p + 1):
+        L.append("  T S%d = T(0), G%dx = T(0), G%dy = T(0), G%dz = T(0);" % (j, j, j, j))
+    for t, (j, a) in enumerate(sl):
+        ai = mi[a]
+        L.append("  { const T b = B[%d];" % t)
+        L.append("    S%d = fma(b, m%d, S%d);" % (j, ai, j))
+        for d, ax in enumerate("xyz"):
+            if a[d] > 0:
+                par = list(a)
+                par[d] -= 1
+                pi = mi[tuple(par)]
+                mterm = "m%d" % pi
+                if a[d] > 1:
+                    L.append("    G%d%s = fma(b * T(%d), %s, G%d%s);" % (j, ax, a[d], mterm, j, ax))
+                else:
+                    L.append("    G%d%s = fma(b, %s, G%d%s);" % (j, ax, mterm, j, ax))
+        L.append("  }")
+    for j in range(p + 1):
+        L.append("  { const T t = F%d * S%d;" % (j + 1, j))
+        L.append("    ax = fma(Rx, t, fma(F%d, G%dx, ax));" % (j, j))
+        L.append("    ay = fma(Ry, t, fma(F%d, G%dy, ay));" % (j, j))
+        L.append("    az = fma(Rz, t, fma(F%d, G%dz, az));" % (j, j))
+        L.append("  }")
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_reduce(p):
+    """FP64 moments (multi-index order) -> reduced coefficients."""
+    sl, contrib = contributions(p)
+    L = []
+    L.append("__device__ __forceinline__ void reduce_moments_p%d(const double* __restrict__ M, double* __restrict__ B) {" % p)
+    for t, cs in enumerate(contrib):
+        terms = " + ".join("%.17g * M[%d]" % (c, i) for i, c in cs)
+        L.append("  B[%d] = %s;" % (t, terms))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_m2l(pe):
+    """Image-field local expansion about the expansion point e:
+    L_m += sum_n (-1)^|n|/n! M_n d^{m+n} phi~(R0), 1 <= |m| <= pe+1, |m|+|n| <= pe+1."""
+    P = pe + 1
+    mP = multi(P)
+    mi = {m: i for i, m in enumerate(mP)}
+    me = multi(pe)
+    L = []
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void m2l_pe%d(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {" % pe)
+    L.append("  // Lc[t-1] accumulates L_m for multi-index t >= 1 (orders 1..%d)" % P)
+    for t, m in enumerate(mP):
+        if t == 0:
+            continue
+        terms = []
+        for u, n in enumerate(me):
+            if sum(m) + sum(n) > P:
+                continue
+            c = (-1.0 if sum(n) % 2 else 1.0) / (math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2]))
+            k = mi[(m[0] + n[0], m[1] + n[1], m[2] + n[2])]
+            terms.append((u, c, k))
+        expr = "Lc[%d]" % (t - 1)
+        for u, c, k in terms:
+            if c == 1.0:
+                expr = "fma(M[%d], D[%d], %s)" % (u, k, expr)
+            elif c == -1.0:
+                expr = "fma(-M[%d], D[%d], %s)" % (u, k, expr)
+            else:
+                expr = "fma(M[%d] * T(%.17g), D[%d], %s)" % (u, c, k, expr)
+        L.append("  Lc[%d] = %s;" % (t - 1, expr))
+    L.append("}")
+    # L2P
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void l2p_pe%d(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {" % pe)
+    L.append("  // a_k -= sum_{|n|<=%d} d^n/n! L_{n+e_k}" % pe)
+    mon = me
+    mmi = {m: i for i, m in enumerate(mon)}
+    L.append("  const T q0 = T(1);")
+    for i, m in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                pi = mmi[tuple(par)]
+                L.append("  const T q%d = q%d * (%s * T(%.17g));" % (i, pi, "dxdydz"[2 * d:2 * d + 2], 1.0 / m[d]))
+                break
+    for k, ax in enumerate("xyz"):
+        terms = []
+        for i, n in enumerate(mon):
+            nn = list(n)
+            nn[k] += 1
+            terms.append((i, mi[tuple(nn)] - 1))
+        expr = "a%s" % ax
+        for i, li in terms:
+            expr = "fma(-q%d, Lc[%d], %s)" % (i, li, expr)
+        L.append("  a%s = %s;" % (ax, expr))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_p2m(p):
+    """M_n += m (x - c)^n for |n| <= p (FP64)."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    L = ["__device__ __forceinline__ void p2m_acc_p%d(double m, double dx, double dy, double dz, double* __restrict__ M) {" % p]
+    L.append("  const double q0 = m;")
+    L.append("  M[0] += q0;")
+    for i, mm in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if mm[d] > 0:
+                par = list(mm)
+                par[d] -= 1
+                L.append("  const double q%d = q%d * %s;" % (i, mi[tuple(par)], "dxdydz"[2 * d:2 * d + 2]))
+                break
+        L.append("  M[%d] += q%d;" % (i, i))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_m2m(p):
+    """Mp_n += sum_{k <= n} C(n,k) s^(n-k) Mc_k, s = c_child - c_parent (FP64)."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    L = ["__device__ __forceinline__ void m2m_acc_p%d(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {" % p]
+    L.append("  const double w0 = 1.0;")
+    for i, mm in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if mm[d] > 0:
+                par = list(mm)
+                par[d] -= 1
+                L.append("  const double w%d = w%d * %s;" % (i, mi[tuple(par)], "sxsysz"[2 * d:2 * d + 2]))
+                break
+    for t, n in enumerate(mon):
+        expr = "Mp[%d]" % t
+        for k in product(*(range(n[d] + 1) for d in range(3))):
+            b = math.comb(n[0], k[0]) * math.comb(n[1], k[1]) * math.comb(n[2], k[2])
+            w = mi[(n[0] - k[0], n[1] - k[1], n[2] - k[2])]
+            if b == 1:
+                expr = "fma(w%d, Mc[%d], %s)" % (w, mi[k], expr)
+            else:
+                expr = "fma(w%d * %d.0, Mc[%d], %s)" % (w, b, mi[k], expr)
+        L.append("  Mp[%d] = %s;" % (t, expr))
+    L.append("}")
+    return "\n".join(L)
+
+
+def generate():
+    out = []
+    out.append("// Generated by gen_m2p.py -- do not edit by hand.")
+    out.append("// Reduced-coefficient multipole-to-particle kernels, orders 0..4.")
+    out.append("#pragma once")
+    out.append("")
+    for p in range(5):
+        out.append("constexpr int kNB%d = %d;  // reduced coefficients at order %d" % (p, len(slots(p)), p))
+        out.append("constexpr int kM2PFlops%d = %d;  // flops per M2P (FMA = 2, rsqrt = 1)" % (p, flop_count(p)))
+    out.append("")
+    for p in range(5):
+        out.append(emit_m2p(p))
+        out.append("")
+        out.append(emit_reduce(p))
+        out.append("")
+    for p in range(6):
+        out.append(emit_p2m(p))
+        out.append("")
+        out.append(emit_m2m(p))
+        out.append("")
+    for pe in range(1, 6):
+        out.append("constexpr int kNL%d = %d;  // local coefficients, image-field order %d" % (pe, len(multi(pe + 1)) - 1, pe))
+        out.append(emit_m2l(pe))
+        out.append("")
+    return "\n".join(out) + "\n"
+
+
+if __name__ == "__main__":
+    here = os.path.dirname(os.path.abspath(__file__))
+    dst = os.path.join(here, "m2p_gen.cuh")
+    text = generate()
+    if len(sys.argv) > 1 and sys.argv[1] == "--check":
+        sys.exit(0 if open(dst).read() == text else 1)
+    with open(dst, "w") as f:
+        f.write(text)

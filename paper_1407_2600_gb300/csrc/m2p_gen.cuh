@@ -1,0 +1,1639 @@
+// Generated by gen_m2p.py -- do not edit by hand.
+// Reduced-coefficient multipole-to-particle kernels, orders 0..4.
+#pragma once
+
+constexpr int kNB0 = 1;  // reduced coefficients at order 0
+constexpr int kM2PFlops0 = 25;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kNB1 = 4;  // reduced coefficients at order 1
+constexpr int kM2PFlops1 = 55;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kNB2 = 11;  // reduced coefficients at order 2
+constexpr int kM2PFlops2 = 111;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kNB3 = 24;  // reduced coefficients at order 3
+constexpr int kM2PFlops3 = 213;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kNB4 = 46;  // reduced coefficients at order 4
+constexpr int kM2PFlops4 = 386;  // flops per M2P (FMA = 2, rsqrt = 1)
+
+template <typename T>
+__device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
+                                     T& ax, T& ay, T& az) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T m0 = T(1);
+  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
+  { const T b = B[0];
+    S0 = fma(b, m0, S0);
+  }
+  { const T t = F1 * S0;
+    ax = fma(Rx, t, fma(F0, G0x, ax));
+    ay = fma(Ry, t, fma(F0, G0y, ay));
+    az = fma(Rz, t, fma(F0, G0z, az));
+  }
+}
+
+__device__ __forceinline__ void reduce_moments_p0(const double* __restrict__ M, double* __restrict__ B) {
+  B[0] = 1 * M[0];
+}
+
+template <typename T>
+__device__ __forceinline__ void m2p_p1(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
+                                     T& ax, T& ay, T& az) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T m0 = T(1);
+  const T m1 = T(1) * Rx;
+  const T m2 = T(1) * Ry;
+  const T m3 = T(1) * Rz;
+  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
+  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
+  { const T b = B[0];
+    S0 = fma(b, m0, S0);
+  }
+  { const T b = B[1];
+    S1 = fma(b, m1, S1);
+    G1x = fma(b, m0, G1x);
+  }
+  { const T b = B[2];
+    S1 = fma(b, m2, S1);
+    G1y = fma(b, m0, G1y);
+  }
+  { const T b = B[3];
+    S1 = fma(b, m3, S1);
+    G1z = fma(b, m0, G1z);
+  }
+  { const T t = F1 * S0;
+    ax = fma(Rx, t, fma(F0, G0x, ax));
+    ay = fma(Ry, t, fma(F0, G0y, ay));
+    az = fma(Rz, t, fma(F0, G0z, az));
+  }
+  { const T t = F2 * S1;
+    ax = fma(Rx, t, fma(F1, G1x, ax));
+    ay = fma(Ry, t, fma(F1, G1y, ay));
+    az = fma(Rz, t, fma(F1, G1z, az));
+  }
+}
+
+__device__ __forceinline__ void reduce_moments_p1(const double* __restrict__ M, double* __restrict__ B) {
+  B[0] = 1 * M[0];
+  B[1] = -1 * M[1];
+  B[2] = -1 * M[2];
+  B[3] = -1 * M[3];
+}
+
+template <typename T>
+__device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
+                                     T& ax, T& ay, T& az) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T F3 = F2 * (T(-5) * is);
+  const T m0 = T(1);
+  const T m1 = T(1) * Rx;
+  const T m2 = T(1) * Ry;
+  const T m3 = T(1) * Rz;
+  const T m4 = m1 * Rx;
+  const T m5 = m2 * Rx;
+  const T m6 = m3 * Rx;
+  const T m7 = m2 * Ry;
+  const T m8 = m3 * Ry;
+  const T m9 = m3 * Rz;
+  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
+  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
+  T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0);
+  { const T b = B[0];
+    S0 = fma(b, m0, S0);
+  }
+  { const T b = B[1];
+    S1 = fma(b, m0, S1);
+  }
+  { const T b = B[2];
+    S1 = fma(b, m1, S1);
+    G1x = fma(b, m0, G1x);
+  }
+  { const T b = B[3];
+    S1 = fma(b, m2, S1);
+    G1y = fma(b, m0, G1y);
+  }
+  { const T b = B[4];
+    S1 = fma(b, m3, S1);
+    G1z = fma(b, m0, G1z);
+  }
+  { const T b = B[5];
+    S2 = fma(b, m4, S2);
+    G2x = fma(b * T(2), m1, G2x);
+  }
+  { const T b = B[6];
+    S2 = fma(b, m5, S2);
+    G2x = fma(b, m2, G2x);
+    G2y = fma(b, m1, G2y);
+  }
+  { const T b = B[7];
+    S2 = fma(b, m6, S2);
+    G2x = fma(b, m3, G2x);
+    G2z = fma(b, m1, G2z);
+  }
+  { const T b = B[8];
+    S2 = fma(b, m7, S2);
+    G2y = fma(b * T(2), m2, G2y);
+  }
+  { const T b = B[9];
+    S2 = fma(b, m8, S2);
+    G2y = fma(b, m3, G2y);
+    G2z = fma(b, m2, G2z);
+  }
+  { const T b = B[10];
+    S2 = fma(b, m9, S2);
+    G2z = fma(b * T(2), m3, G2z);
+  }
+  { const T t = F1 * S0;
+    ax = fma(Rx, t, fma(F0, G0x, ax));
+    ay = fma(Ry, t, fma(F0, G0y, ay));
+    az = fma(Rz, t, fma(F0, G0z, az));
+  }
+  { const T t = F2 * S1;
+    ax = fma(Rx, t, fma(F1, G1x, ax));
+    ay = fma(Ry, t, fma(F1, G1y, ay));
+    az = fma(Rz, t, fma(F1, G1z, az));
+  }
+  { const T t = F3 * S2;
+    ax = fma(Rx, t, fma(F2, G2x, ax));
+    ay = fma(Ry, t, fma(F2, G2y, ay));
+    az = fma(Rz, t, fma(F2, G2z, az));
+  }
+}
+
+__device__ __forceinline__ void reduce_moments_p2(const double* __restrict__ M, double* __restrict__ B) {
+  B[0] = 1 * M[0];
+  B[1] = 0.5 * M[4] + 0.5 * M[7] + 0.5 * M[9];
+  B[2] = -1 * M[1];
+  B[3] = -1 * M[2];
+  B[4] = -1 * M[3];
+  B[5] = 0.5 * M[4];
+  B[6] = 1 * M[5];
+  B[7] = 1 * M[6];
+  B[8] = 0.5 * M[7];
+  B[9] = 1 * M[8];
+  B[10] = 0.5 * M[9];
+}
+
+template <typename T>
+__device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
+                                     T& ax, T& ay, T& az) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T F3 = F2 * (T(-5) * is);
+  const T F4 = F3 * (T(-7) * is);
+  const T m0 = T(1);
+  const T m1 = T(1) * Rx;
+  const T m2 = T(1) * Ry;
+  const T m3 = T(1) * Rz;
+  const T m4 = m1 * Rx;
+  const T m5 = m2 * Rx;
+  const T m6 = m3 * Rx;
+  const T m7 = m2 * Ry;
+  const T m8 = m3 * Ry;
+  const T m9 = m3 * Rz;
+  const T m10 = m4 * Rx;
+  const T m11 = m5 * Rx;
+  const T m12 = m6 * Rx;
+  const T m13 = m7 * Rx;
+  const T m14 = m8 * Rx;
+  const T m15 = m9 * Rx;
+  const T m16 = m7 * Ry;
+  const T m17 = m8 * Ry;
+  const T m18 = m9 * Ry;
+  const T m19 = m9 * Rz;
+  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
+  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
+  T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0);
+  T S3 = T(0), G3x = T(0), G3y = T(0), G3z = T(0);
+  { const T b = B[0];
+    S0 = fma(b, m0, S0);
+  }
+  { const T b = B[1];
+    S1 = fma(b, m0, S1);
+  }
+  { const T b = B[2];
+    S1 = fma(b, m1, S1);
+    G1x = fma(b, m0, G1x);
+  }
+  { const T b = B[3];
+    S1 = fma(b, m2, S1);
+    G1y = fma(b, m0, G1y);
+  }
+  { const T b = B[4];
+    S1 = fma(b, m3, S1);
+    G1z = fma(b, m0, G1z);
+  }
+  { const T b = B[5];
+    S2 = fma(b, m1, S2);
+    G2x = fma(b, m0, G2x);
+  }
+  { const T b = B[6];
+    S2 = fma(b, m2, S2);
+    G2y = fma(b, m0, G2y);
+  }
+  { const T b = B[7];
+    S2 = fma(b, m3, S2);
+    G2z = fma(b, m0, G2z);
+  }
+  { const T b = B[8];
+    S2 = fma(b, m4, S2);
+    G2x = fma(b * T(2), m1, G2x);
+  }
+  { const T b = B[9];
+    S2 = fma(b, m5, S2);
+    G2x = fma(b, m2, G2x);
+    G2y = fma(b, m1, G2y);
+  }
+  { const T b = B[10];
+    S2 = fma(b, m6, S2);
+    G2x = fma(b, m3, G2x);
+    G2z = fma(b, m1, G2z);
+  }
+  { const T b = B[11];
+    S2 = fma(b, m7, S2);
+    G2y = fma(b * T(2), m2, G2y);
+  }
+  { const T b = B[12];
+    S2 = fma(b, m8, S2);
+    G2y = fma(b, m3, G2y);
+    G2z = fma(b, m2, G2z);
+  }
+  { const T b = B[13];
+    S2 = fma(b, m9, S2);
+    G2z = fma(b * T(2), m3, G2z);
+  }
+  { const T b = B[14];
+    S3 = fma(b, m10, S3);
+    G3x = fma(b * T(3), m4, G3x);
+  }
+  { const T b = B[15];
+    S3 = fma(b, m11, S3);
+    G3x = fma(b * T(2), m5, G3x);
+    G3y = fma(b, m4, G3y);
+  }
+  { const T b = B[16];
+    S3 = fma(b, m12, S3);
+    G3x = fma(b * T(2), m6, G3x);
+    G3z = fma(b, m4, G3z);
+  }
+  { const T b = B[17];
+    S3 = fma(b, m13, S3);
+    G3x = fma(b, m7, G3x);
+    G3y = fma(b * T(2), m5, G3y);
+  }
+  { const T b = B[18];
+    S3 = fma(b, m14, S3);
+    G3x = fma(b, m8, G3x);
+    G3y = fma(b, m6, G3y);
+    G3z = fma(b, m5, G3z);
+  }
+  { const T b = B[19];
+    S3 = fma(b, m15, S3);
+    G3x = fma(b, m9, G3x);
+    G3z = fma(b * T(2), m6, G3z);
+  }
+  { const T b = B[20];
+    S3 = fma(b, m16, S3);
+    G3y = fma(b * T(3), m7, G3y);
+  }
+  { const T b = B[21];
+    S3 = fma(b, m17, S3);
+    G3y = fma(b * T(2), m8, G3y);
+    G3z = fma(b, m7, G3z);
+  }
+  { const T b = B[22];
+    S3 = fma(b, m18, S3);
+    G3y = fma(b, m9, G3y);
+    G3z = fma(b * T(2), m8, G3z);
+  }
+  { const T b = B[23];
+    S3 = fma(b, m19, S3);
+    G3z = fma(b * T(3), m9, G3z);
+  }
+  { const T t = F1 * S0;
+    ax = fma(Rx, t, fma(F0, G0x, ax));
+    ay = fma(Ry, t, fma(F0, G0y, ay));
+    az = fma(Rz, t, fma(F0, G0z, az));
+  }
+  { const T t = F2 * S1;
+    ax = fma(Rx, t, fma(F1, G1x, ax));
+    ay = fma(Ry, t, fma(F1, G1y, ay));
+    az = fma(Rz, t, fma(F1, G1z, az));
+  }
+  { const T t = F3 * S2;
+    ax = fma(Rx, t, fma(F2, G2x, ax));
+    ay = fma(Ry, t, fma(F2, G2y, ay));
+    az = fma(Rz, t, fma(F2, G2z, az));
+  }
+  { const T t = F4 * S3;
+    ax = fma(Rx, t, fma(F3, G3x, ax));
+    ay = fma(Ry, t, fma(F3, G3y, ay));
+    az = fma(Rz, t, fma(F3, G3z, az));
+  }
+}
+
+__device__ __forceinline__ void reduce_moments_p3(const double* __restrict__ M, double* __restrict__ B) {
+  B[0] = 1 * M[0];
+  B[1] = 0.5 * M[4] + 0.5 * M[7] + 0.5 * M[9];
+  B[2] = -1 * M[1];
+  B[3] = -1 * M[2];
+  B[4] = -1 * M[3];
+  B[5] = -0.5 * M[10] + -0.5 * M[13] + -0.5 * M[15];
+  B[6] = -0.5 * M[11] + -0.5 * M[16] + -0.5 * M[18];
+  B[7] = -0.5 * M[12] + -0.5 * M[17] + -0.5 * M[19];
+  B[8] = 0.5 * M[4];
+  B[9] = 1 * M[5];
+  B[10] = 1 * M[6];
+  B[11] = 0.5 * M[7];
+  B[12] = 1 * M[8];
+  B[13] = 0.5 * M[9];
+  B[14] = -0.16666666666666666 * M[10];
+  B[15] = -0.5 * M[11];
+  B[16] = -0.5 * M[12];
+  B[17] = -0.5 * M[13];
+  B[18] = -1 * M[14];
+  B[19] = -0.5 * M[15];
+  B[20] = -0.16666666666666666 * M[16];
+  B[21] = -0.5 * M[17];
+  B[22] = -0.5 * M[18];
+  B[23] = -0.16666666666666666 * M[19];
+}
+
+template <typename T>
+__device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
+                                     T& ax, T& ay, T& az) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T F3 = F2 * (T(-5) * is);
+  const T F4 = F3 * (T(-7) * is);
+  const T F5 = F4 * (T(-9) * is);
+  const T m0 = T(1);
+  const T m1 = T(1) * Rx;
+  const T m2 = T(1) * Ry;
+  const T m3 = T(1) * Rz;
+  const T m4 = m1 * Rx;
+  const T m5 = m2 * Rx;
+  const T m6 = m3 * Rx;
+  const T m7 = m2 * Ry;
+  const T m8 = m3 * Ry;
+  const T m9 = m3 * Rz;
+  const T m10 = m4 * Rx;
+  const T m11 = m5 * Rx;
+  const T m12 = m6 * Rx;
+  const T m13 = m7 * Rx;
+  const T m14 = m8 * Rx;
+  const T m15 = m9 * Rx;
+  const T m16 = m7 * Ry;
+  const T m17 = m8 * Ry;
+  const T m18 = m9 * Ry;
+  const T m19 = m9 * Rz;
+  const T m20 = m10 * Rx;
+  const T m21 = m11 * Rx;
+  const T m22 = m12 * Rx;
+  const T m23 = m13 * Rx;
+  const T m24 = m14 * Rx;
+  const T m25 = m15 * Rx;
+  const T m26 = m16 * Rx;
+  const T m27 = m17 * Rx;
+  const T m28 = m18 * Rx;
+  const T m29 = m19 * Rx;
+  const T m30 = m16 * Ry;
+  const T m31 = m17 * Ry;
+  const T m32 = m18 * Ry;
+  const T m33 = m19 * Ry;
+  const T m34 = m19 * Rz;
+  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
+  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
+  T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0);
+  T S3 = T(0), G3x = T(0), G3y = T(0), G3z = T(0);
+  T S4 = T(0), G4x = T(0), G4y = T(0), G4z = T(0);
+  { const T b = B[0];
+    S0 = fma(b, m0, S0);
+  }
+  { const T b = B[1];
+    S1 = fma(b, m0, S1);
+  }
+  { const T b = B[2];
+    S1 = fma(b, m1, S1);
+    G1x = fma(b, m0, G1x);
+  }
+  { const T b = B[3];
+    S1 = fma(b, m2, S1);
+    G1y = fma(b, m0, G1y);
+  }
+  { const T b = B[4];
+    S1 = fma(b, m3, S1);
+    G1z = fma(b, m0, G1z);
+  }
+  { const T b = B[5];
+    S2 = fma(b, m0, S2);
+  }
+  { const T b = B[6];
+    S2 = fma(b, m1, S2);
+    G2x = fma(b, m0, G2x);
+  }
+  { const T b = B[7];
+    S2 = fma(b, m2, S2);
+    G2y = fma(b, m0, G2y);
+  }
+  { const T b = B[8];
+    S2 = fma(b, m3, S2);
+    G2z = fma(b, m0, G2z);
+  }
+  { const T b = B[9];
+    S2 = fma(b, m4, S2);
+    G2x = fma(b * T(2), m1, G2x);
+  }
+  { const T b = B[10];
+    S2 = fma(b, m5, S2);
+    G2x = fma(b, m2, G2x);
+    G2y = fma(b, m1, G2y);
+  }
+  { const T b = B[11];
+    S2 = fma(b, m6, S2);
+    G2x = fma(b, m3, G2x);
+    G2z = fma(b, m1, G2z);
+  }
+  { const T b = B[12];
+    S2 = fma(b, m7, S2);
+    G2y = fma(b * T(2), m2, G2y);
+  }
+  { const T b = B[13];
+    S2 = fma(b, m8, S2);
+    G2y = fma(b, m3, G2y);
+    G2z = fma(b, m2, G2z);
+  }
+  { const T b = B[14];
+    S2 = fma(b, m9, S2);
+    G2z = fma(b * T(2), m3, G2z);
+  }
+  { const T b = B[15];
+    S3 = fma(b, m4, S3);
+    G3x = fma(b * T(2), m1, G3x);
+  }
+  { const T b = B[16];
+    S3 = fma(b, m5, S3);
+    G3x = fma(b, m2, G3x);
+    G3y = fma(b, m1, G3y);
+  }
+  { const T b = B[17];
+    S3 = fma(b, m6, S3);
+    G3x = fma(b, m3, G3x);
+    G3z = fma(b, m1, G3z);
+  }
+  { const T b = B[18];
+    S3 = fma(b, m7, S3);
+    G3y = fma(b * T(2), m2, G3y);
+  }
+  { const T b = B[19];
+    S3 = fma(b, m8, S3);
+    G3y = fma(b, m3, G3y);
+    G3z = fma(b, m2, G3z);
+  }
+  { const T b = B[20];
+    S3 = fma(b, m9, S3);
+    G3z = fma(b * T(2), m3, G3z);
+  }
+  { const T b = B[21];
+    S3 = fma(b, m10, S3);
+    G3x = fma(b * T(3), m4, G3x);
+  }
+  { const T b = B[22];
+    S3 = fma(b, m11, S3);
+    G3x = fma(b * T(2), m5, G3x);
+    G3y = fma(b, m4, G3y);
+  }
+  { const T b = B[23];
+    S3 = fma(b, m12, S3);
+    G3x = fma(b * T(2), m6, G3x);
+    G3z = fma(b, m4, G3z);
+  }
+  { const T b = B[24];
+    S3 = fma(b, m13, S3);
+    G3x = fma(b, m7, G3x);
+    G3y = fma(b * T(2), m5, G3y);
+  }
+  { const T b = B[25];
+    S3 = fma(b, m14, S3);
+    G3x = fma(b, m8, G3x);
+    G3y = fma(b, m6, G3y);
+    G3z = fma(b, m5, G3z);
+  }
+  { const T b = B[26];
+    S3 = fma(b, m15, S3);
+    G3x = fma(b, m9, G3x);
+    G3z = fma(b * T(2), m6, G3z);
+  }
+  { const T b = B[27];
+    S3 = fma(b, m16, S3);
+    G3y = fma(b * T(3), m7, G3y);
+  }
+  { const T b = B[28];
+    S3 = fma(b, m17, S3);
+    G3y = fma(b * T(2), m8, G3y);
+    G3z = fma(b, m7, G3z);
+  }
+  { const T b = B[29];
+    S3 = fma(b, m18, S3);
+    G3y = fma(b, m9, G3y);
+    G3z = fma(b * T(2), m8, G3z);
+  }
+  { const T b = B[30];
+    S3 = fma(b, m19, S3);
+    G3z = fma(b * T(3), m9, G3z);
+  }
+  { const T b = B[31];
+    S4 = fma(b, m20, S4);
+    G4x = fma(b * T(4), m10, G4x);
+  }
+  { const T b = B[32];
+    S4 = fma(b, m21, S4);
+    G4x = fma(b * T(3), m11, G4x);
+    G4y = fma(b, m10, G4y);
+  }
+  { const T b = B[33];
+    S4 = fma(b, m22, S4);
+    G4x = fma(b * T(3), m12, G4x);
+    G4z = fma(b, m10, G4z);
+  }
+  { const T b = B[34];
+    S4 = fma(b, m23, S4);
+    G4x = fma(b * T(2), m13, G4x);
+    G4y = fma(b * T(2), m11, G4y);
+  }
+  { const T b = B[35];
+    S4 = fma(b, m24, S4);
+    G4x = fma(b * T(2), m14, G4x);
+    G4y = fma(b, m12, G4y);
+    G4z = fma(b, m11, G4z);
+  }
+  { const T b = B[36];
+    S4 = fma(b, m25, S4);
+    G4x = fma(b * T(2), m15, G4x);
+    G4z = fma(b * T(2), m12, G4z);
+  }
+  { const T b = B[37];
+    S4 = fma(b, m26, S4);
+    G4x = fma(b, m16, G4x);
+    G4y = fma(b * T(3), m13, G4y);
+  }
+  { const T b = B[38];
+    S4 = fma(b, m27, S4);
+    G4x = fma(b, m17, G4x);
+    G4y = fma(b * T(2), m14, G4y);
+    G4z = fma(b, m13, G4z);
+  }
+  { const T b = B[39];
+    S4 = fma(b, m28, S4);
+    G4x = fma(b, m18, G4x);
+    G4y = fma(b, m15, G4y);
+    G4z = fma(b * T(2), m14, G4z);
+  }
+  { const T b = B[40];
+    S4 = fma(b, m29, S4);
+    G4x = fma(b, m19, G4x);
+    G4z = fma(b * T(3), m15, G4z);
+  }
+  { const T b = B[41];
+    S4 = fma(b, m30, S4);
+    G4y = fma(b * T(4), m16, G4y);
+  }
+  { const T b = B[42];
+    S4 = fma(b, m31, S4);
+    G4y = fma(b * T(3), m17, G4y);
+    G4z = fma(b, m16, G4z);
+  }
+  { const T b = B[43];
+    S4 = fma(b, m32, S4);
+    G4y = fma(b * T(2), m18, G4y);
+    G4z = fma(b * T(2), m17, G4z);
+  }
+  { const T b = B[44];
+    S4 = fma(b, m33, S4);
+    G4y = fma(b, m19, G4y);
+    G4z = fma(b * T(3), m18, G4z);
+  }
+  { const T b = B[45];
+    S4 = fma(b, m34, S4);
+    G4z = fma(b * T(4), m19, G4z);
+  }
+  { const T t = F1 * S0;
+    ax = fma(Rx, t, fma(F0, G0x, ax));
+    ay = fma(Ry, t, fma(F0, G0y, ay));
+    az = fma(Rz, t, fma(F0, G0z, az));
+  }
+  { const T t = F2 * S1;
+    ax = fma(Rx, t, fma(F1, G1x, ax));
+    ay = fma(Ry, t, fma(F1, G1y, ay));
+    az = fma(Rz, t, fma(F1, G1z, az));
+  }
+  { const T t = F3 * S2;
+    ax = fma(Rx, t, fma(F2, G2x, ax));
+    ay = fma(Ry, t, fma(F2, G2y, ay));
+    az = fma(Rz, t, fma(F2, G2z, az));
+  }
+  { const T t = F4 * S3;
+    ax = fma(Rx, t, fma(F3, G3x, ax));
+    ay = fma(Ry, t, fma(F3, G3y, ay));
+    az = fma(Rz, t, fma(F3, G3z, az));
+  }
+  { const T t = F5 * S4;
+    ax = fma(Rx, t, fma(F4, G4x, ax));
+    ay = fma(Ry, t, fma(F4, G4y, ay));
+    az = fma(Rz, t, fma(F4, G4z, az));
+  }
+}
+
+__device__ __forceinline__ void reduce_moments_p4(const double* __restrict__ M, double* __restrict__ B) {
+  B[0] = 1 * M[0];
+  B[1] = 0.5 * M[4] + 0.5 * M[7] + 0.5 * M[9];
+  B[2] = -1 * M[1];
+  B[3] = -1 * M[2];
+  B[4] = -1 * M[3];
+  B[5] = 0.125 * M[20] + 0.25 * M[23] + 0.25 * M[25] + 0.125 * M[30] + 0.25 * M[32] + 0.125 * M[34];
+  B[6] = -0.5 * M[10] + -0.5 * M[13] + -0.5 * M[15];
+  B[7] = -0.5 * M[11] + -0.5 * M[16] + -0.5 * M[18];
+  B[8] = -0.5 * M[12] + -0.5 * M[17] + -0.5 * M[19];
+  B[9] = 0.5 * M[4];
+  B[10] = 1 * M[5];
+  B[11] = 1 * M[6];
+  B[12] = 0.5 * M[7];
+  B[13] = 1 * M[8];
+  B[14] = 0.5 * M[9];
+  B[15] = 0.25 * M[20] + 0.25 * M[23] + 0.25 * M[25];
+  B[16] = 0.5 * M[21] + 0.5 * M[26] + 0.5 * M[28];
+  B[17] = 0.5 * M[22] + 0.5 * M[27] + 0.5 * M[29];
+  B[18] = 0.25 * M[23] + 0.25 * M[30] + 0.25 * M[32];
+  B[19] = 0.5 * M[24] + 0.5 * M[31] + 0.5 * M[33];
+  B[20] = 0.25 * M[25] + 0.25 * M[32] + 0.25 * M[34];
+  B[21] = -0.16666666666666666 * M[10];
+  B[22] = -0.5 * M[11];
+  B[23] = -0.5 * M[12];
+  B[24] = -0.5 * M[13];
+  B[25] = -1 * M[14];
+  B[26] = -0.5 * M[15];
+  B[27] = -0.16666666666666666 * M[16];
+  B[28] = -0.5 * M[17];
+  B[29] = -0.5 * M[18];
+  B[30] = -0.16666666666666666 * M[19];
+  B[31] = 0.041666666666666664 * M[20];
+  B[32] = 0.16666666666666666 * M[21];
+  B[33] = 0.16666666666666666 * M[22];
+  B[34] = 0.25 * M[23];
+  B[35] = 0.5 * M[24];
+  B[36] = 0.25 * M[25];
+  B[37] = 0.16666666666666666 * M[26];
+  B[38] = 0.5 * M[27];
+  B[39] = 0.5 * M[28];
+  B[40] = 0.16666666666666666 * M[29];
+  B[41] = 0.041666666666666664 * M[30];
+  B[42] = 0.16666666666666666 * M[31];
+  B[43] = 0.25 * M[32];
+  B[44] = 0.16666666666666666 * M[33];
+  B[45] = 0.041666666666666664 * M[34];
+}
+
+__device__ __forceinline__ void p2m_acc_p0(double m, double dx, double dy, double dz, double* __restrict__ M) {
+  const double q0 = m;
+  M[0] += q0;
+}
+
+__device__ __forceinline__ void m2m_acc_p0(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {
+  const double w0 = 1.0;
+  Mp[0] = fma(w0, Mc[0], Mp[0]);
+}
+
+__device__ __forceinline__ void p2m_acc_p1(double m, double dx, double dy, double dz, double* __restrict__ M) {
+  const double q0 = m;
+  M[0] += q0;
+  const double q1 = q0 * dx;
+  M[1] += q1;
+  const double q2 = q0 * dy;
+  M[2] += q2;
+  const double q3 = q0 * dz;
+  M[3] += q3;
+}
+
+__device__ __forceinline__ void m2m_acc_p1(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {
+  const double w0 = 1.0;
+  const double w1 = w0 * sx;
+  const double w2 = w0 * sy;
+  const double w3 = w0 * sz;
+  Mp[0] = fma(w0, Mc[0], Mp[0]);
+  Mp[1] = fma(w0, Mc[1], fma(w1, Mc[0], Mp[1]));
+  Mp[2] = fma(w0, Mc[2], fma(w2, Mc[0], Mp[2]));
+  Mp[3] = fma(w0, Mc[3], fma(w3, Mc[0], Mp[3]));
+}
+
+__device__ __forceinline__ void p2m_acc_p2(double m, double dx, double dy, double dz, double* __restrict__ M) {
+  const double q0 = m;
+  M[0] += q0;
+  const double q1 = q0 * dx;
+  M[1] += q1;
+  const double q2 = q0 * dy;
+  M[2] += q2;
+  const double q3 = q0 * dz;
+  M[3] += q3;
+  const double q4 = q1 * dx;
+  M[4] += q4;
+  const double q5 = q2 * dx;
+  M[5] += q5;
+  const double q6 = q3 * dx;
+  M[6] += q6;
+  const double q7 = q2 * dy;
+  M[7] += q7;
+  const double q8 = q3 * dy;
+  M[8] += q8;
+  const double q9 = q3 * dz;
+  M[9] += q9;
+}
+
+__device__ __forceinline__ void m2m_acc_p2(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {
+  const double w0 = 1.0;
+  const double w1 = w0 * sx;
+  const double w2 = w0 * sy;
+  const double w3 = w0 * sz;
+  const double w4 = w1 * sx;
+  const double w5 = w2 * sx;
+  const double w6 = w3 * sx;
+  const double w7 = w2 * sy;
+  const double w8 = w3 * sy;
+  const double w9 = w3 * sz;
+  Mp[0] = fma(w0, Mc[0], Mp[0]);
+  Mp[1] = fma(w0, Mc[1], fma(w1, Mc[0], Mp[1]));
+  Mp[2] = fma(w0, Mc[2], fma(w2, Mc[0], Mp[2]));
+  Mp[3] = fma(w0, Mc[3], fma(w3, Mc[0], Mp[3]));
+  Mp[4] = fma(w0, Mc[4], fma(w1 * 2.0, Mc[1], fma(w4, Mc[0], Mp[4])));
+  Mp[5] = fma(w0, Mc[5], fma(w2, Mc[1], fma(w1, Mc[2], fma(w5, Mc[0], Mp[5]))));
+  Mp[6] = fma(w0, Mc[6], fma(w3, Mc[1], fma(w1, Mc[3], fma(w6, Mc[0], Mp[6]))));
+  Mp[7] = fma(w0, Mc[7], fma(w2 * 2.0, Mc[2], fma(w7, Mc[0], Mp[7])));
+  Mp[8] = fma(w0, Mc[8], fma(w3, Mc[2], fma(w2, Mc[3], fma(w8, Mc[0], Mp[8]))));
+  Mp[9] = fma(w0, Mc[9], fma(w3 * 2.0, Mc[3], fma(w9, Mc[0], Mp[9])));
+}
+
+__device__ __forceinline__ void p2m_acc_p3(double m, double dx, double dy, double dz, double* __restrict__ M) {
+  const double q0 = m;
+  M[0] += q0;
+  const double q1 = q0 * dx;
+  M[1] += q1;
+  const double q2 = q0 * dy;
+  M[2] += q2;
+  const double q3 = q0 * dz;
+  M[3] += q3;
+  const double q4 = q1 * dx;
+  M[4] += q4;
+  const double q5 = q2 * dx;
+  M[5] += q5;
+  const double q6 = q3 * dx;
+  M[6] += q6;
+  const double q7 = q2 * dy;
+  M[7] += q7;
+  const double q8 = q3 * dy;
+  M[8] += q8;
+  const double q9 = q3 * dz;
+  M[9] += q9;
+  const double q10 = q4 * dx;
+  M[10] += q10;
+  const double q11 = q5 * dx;
+  M[11] += q11;
+  const double q12 = q6 * dx;
+  M[12] += q12;
+  const double q13 = q7 * dx;
+  M[13] += q13;
+  const double q14 = q8 * dx;
+  M[14] += q14;
+  const double q15 = q9 * dx;
+  M[15] += q15;
+  const double q16 = q7 * dy;
+  M[16] += q16;
+  const double q17 = q8 * dy;
+  M[17] += q17;
+  const double q18 = q9 * dy;
+  M[18] += q18;
+  const double q19 = q9 * dz;
+  M[19] += q19;
+}
+
+__device__ __forceinline__ void m2m_acc_p3(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {
+  const double w0 = 1.0;
+  const double w1 = w0 * sx;
+  const double w2 = w0 * sy;
+  const double w3 = w0 * sz;
+  const double w4 = w1 * sx;
+  const double w5 = w2 * sx;
+  const double w6 = w3 * sx;
+  const double w7 = w2 * sy;
+  const double w8 = w3 * sy;
+  const double w9 = w3 * sz;
+  const double w10 = w4 * sx;
+  const double w11 = w5 * sx;
+  const double w12 = w6 * sx;
+  const double w13 = w7 * sx;
+  const double w14 = w8 * sx;
+  const double w15 = w9 * sx;
+  const double w16 = w7 * sy;
+  const double w17 = w8 * sy;
+  const double w18 = w9 * sy;
+  const double w19 = w9 * sz;
+  Mp[0] = fma(w0, Mc[0], Mp[0]);
+  Mp[1] = fma(w0, Mc[1], fma(w1, Mc[0], Mp[1]));
+  Mp[2] = fma(w0, Mc[2], fma(w2, Mc[0], Mp[2]));
+  Mp[3] = fma(w0, Mc[3], fma(w3, Mc[0], Mp[3]));
+  Mp[4] = fma(w0, Mc[4], fma(w1 * 2.0, Mc[1], fma(w4, Mc[0], Mp[4])));
+  Mp[5] = fma(w0, Mc[5], fma(w2, Mc[1], fma(w1, Mc[2], fma(w5, Mc[0], Mp[5]))));
+  Mp[6] = fma(w0, Mc[6], fma(w3, Mc[1], fma(w1, Mc[3], fma(w6, Mc[0], Mp[6]))));
+  Mp[7] = fma(w0, Mc[7], fma(w2 * 2.0, Mc[2], fma(w7, Mc[0], Mp[7])));
+  Mp[8] = fma(w0, Mc[8], fma(w3, Mc[2], fma(w2, Mc[3], fma(w8, Mc[0], Mp[8]))));
+  Mp[9] = fma(w0, Mc[9], fma(w3 * 2.0, Mc[3], fma(w9, Mc[0], Mp[9])));
+  Mp[10] = fma(w0, Mc[10], fma(w1 * 3.0, Mc[4], fma(w4 * 3.0, Mc[1], fma(w10, Mc[0], Mp[10]))));
+  Mp[11] = fma(w0, Mc[11], fma(w2, Mc[4], fma(w1 * 2.0, Mc[5], fma(w5 * 2.0, Mc[1], fma(w4, Mc[2], fma(w11, Mc[0], Mp[11]))))));
+  Mp[12] = fma(w0, Mc[12], fma(w3, Mc[4], fma(w1 * 2.0, Mc[6], fma(w6 * 2.0, Mc[1], fma(w4, Mc[3], fma(w12, Mc[0], Mp[12]))))));
+  Mp[13] = fma(w0, Mc[13], fma(w2 * 2.0, Mc[5], fma(w7, Mc[1], fma(w1, Mc[7], fma(w5 * 2.0, Mc[2], fma(w13, Mc[0], Mp[13]))))));
+  Mp[14] = fma(w0, Mc[14], fma(w3, Mc[5], fma(w2, Mc[6], fma(w8, Mc[1], fma(w1, Mc[8], fma(w6, Mc[2], fma(w5, Mc[3], fma(w14, Mc[0], Mp[14]))))))));
+  Mp[15] = fma(w0, Mc[15], fma(w3 * 2.0, Mc[6], fma(w9, Mc[1], fma(w1, Mc[9], fma(w6 * 2.0, Mc[3], fma(w15, Mc[0], Mp[15]))))));
+  Mp[16] = fma(w0, Mc[16], fma(w2 * 3.0, Mc[7], fma(w7 * 3.0, Mc[2], fma(w16, Mc[0], Mp[16]))));
+  Mp[17] = fma(w0, Mc[17], fma(w3, Mc[7], fma(w2 * 2.0, Mc[8], fma(w8 * 2.0, Mc[2], fma(w7, Mc[3], fma(w17, Mc[0], Mp[17]))))));
+  Mp[18] = fma(w0, Mc[18], fma(w3 * 2.0, Mc[8], fma(w9, Mc[2], fma(w2, Mc[9], fma(w8 * 2.0, Mc[3], fma(w18, Mc[0], Mp[18]))))));
+  Mp[19] = fma(w0, Mc[19], fma(w3 * 3.0, Mc[9], fma(w9 * 3.0, Mc[3], fma(w19, Mc[0], Mp[19]))));
+}
+
+__device__ __forceinline__ void p2m_acc_p4(double m, double dx, double dy, double dz, double* __restrict__ M) {
+  const double q0 = m;
+  M[0] += q0;
+  const double q1 = q0 * dx;
+  M[1] += q1;
+  const double q2 = q0 * dy;
+  M[2] += q2;
+  const double q3 = q0 * dz;
+  M[3] += q3;
+  const double q4 = q1 * dx;
+  M[4] += q4;
+  const double q5 = q2 * dx;
+  M[5] += q5;
+  const double q6 = q3 * dx;
+  M[6] += q6;
+  const double q7 = q2 * dy;
+  M[7] += q7;
+  const double q8 = q3 * dy;
+  M[8] += q8;
+  const double q9 = q3 * dz;
+  M[9] += q9;
+  const double q10 = q4 * dx;
+  M[10] += q10;
+  const double q11 = q5 * dx;
+  M[11] += q11;
+  const double q12 = q6 * dx;
+  M[12] += q12;
+  const double q13 = q7 * dx;
+  M[13] += q13;
+  const double q14 = q8 * dx;
+  M[14] += q14;
+  const double q15 = q9 * dx;
+  M[15] += q15;
+  const double q16 = q7 * dy;
+  M[16] += q16;
+  const double q17 = q8 * dy;
+  M[17] += q17;
+  const double q18 = q9 * dy;
+  M[18] += q18;
+  const double q19 = q9 * dz;
+  M[19] += q19;
+  const double q20 = q10 * dx;
+  M[20] += q20;
+  const double q21 = q11 * dx;
+  M[21] += q21;
+  const double q22 = q12 * dx;
+  M[22] += q22;
+  const double q23 = q13 * dx;
+  M[23] += q23;
+  const double q24 = q14 * dx;
+  M[24] += q24;
+  const double q25 = q15 * dx;
+  M[25] += q25;
+  const double q26 = q16 * dx;
+  M[26] += q26;
+  const double q27 = q17 * dx;
+  M[27] += q27;
+  const double q28 = q18 * dx;
+  M[28] += q28;
+  const double q29 = q19 * dx;
+  M[29] += q29;
+  const double q30 = q16 * dy;
+  M[30] += q30;
+  const double q31 = q17 * dy;
+  M[31] += q31;
+  const double q32 = q18 * dy;
+  M[32] += q32;
+  const double q33 = q19 * dy;
+  M[33] += q33;
+  const double q34 = q19 * dz;
+  M[34] += q34;
+}
+
+__device__ __forceinline__ void m2m_acc_p4(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {
+  const double w0 = 1.0;
+  const double w1 = w0 * sx;
+  const double w2 = w0 * sy;
+  const double w3 = w0 * sz;
+  const double w4 = w1 * sx;
+  const double w5 = w2 * sx;
+  const double w6 = w3 * sx;
+  const double w7 = w2 * sy;
+  const double w8 = w3 * sy;
+  const double w9 = w3 * sz;
+  const double w10 = w4 * sx;
+  const double w11 = w5 * sx;
+  const double w12 = w6 * sx;
+  const double w13 = w7 * sx;
+  const double w14 = w8 * sx;
+  const double w15 = w9 * sx;
+  const double w16 = w7 * sy;
+  const double w17 = w8 * sy;
+  const double w18 = w9 * sy;
+  const double w19 = w9 * sz;
+  const double w20 = w10 * sx;
+  const double w21 = w11 * sx;
+  const double w22 = w12 * sx;
+  const double w23 = w13 * sx;
+  const double w24 = w14 * sx;
+  const double w25 = w15 * sx;
+  const double w26 = w16 * sx;
+  const double w27 = w17 * sx;
+  const double w28 = w18 * sx;
+  const double w29 = w19 * sx;
+  const double w30 = w16 * sy;
+  const double w31 = w17 * sy;
+  const double w32 = w18 * sy;
+  const double w33 = w19 * sy;
+  const double w34 = w19 * sz;
+  Mp[0] = fma(w0, Mc[0], Mp[0]);
+  Mp[1] = fma(w0, Mc[1], fma(w1, Mc[0], Mp[1]));
+  Mp[2] = fma(w0, Mc[2], fma(w2, Mc[0], Mp[2]));
+  Mp[3] = fma(w0, Mc[3], fma(w3, Mc[0], Mp[3]));
+  Mp[4] = fma(w0, Mc[4], fma(w1 * 2.0, Mc[1], fma(w4, Mc[0], Mp[4])));
+  Mp[5] = fma(w0, Mc[5], fma(w2, Mc[1], fma(w1, Mc[2], fma(w5, Mc[0], Mp[5]))));
+  Mp[6] = fma(w0, Mc[6], fma(w3, Mc[1], fma(w1, Mc[3], fma(w6, Mc[0], Mp[6]))));
+  Mp[7] = fma(w0, Mc[7], fma(w2 * 2.0, Mc[2], fma(w7, Mc[0], Mp[7])));
+  Mp[8] = fma(w0, Mc[8], fma(w3, Mc[2], fma(w2, Mc[3], fma(w8, Mc[0], Mp[8]))));
+  Mp[9] = fma(w0, Mc[9], fma(w3 * 2.0, Mc[3], fma(w9, Mc[0], Mp[9])));
+  Mp[10] = fma(w0, Mc[10], fma(w1 * 3.0, Mc[4], fma(w4 * 3.0, Mc[1], fma(w10, Mc[0], Mp[10]))));
+  Mp[11] = fma(w0, Mc[11], fma(w2, Mc[4], fma(w1 * 2.0, Mc[5], fma(w5 * 2.0, Mc[1], fma(w4, Mc[2], fma(w11, Mc[0], Mp[11]))))));
+  Mp[12] = fma(w0, Mc[12], fma(w3, Mc[4], fma(w1 * 2.0, Mc[6], fma(w6 * 2.0, Mc[1], fma(w4, Mc[3], fma(w12, Mc[0], Mp[12]))))));
+  Mp[13] = fma(w0, Mc[13], fma(w2 * 2.0, Mc[5], fma(w7, Mc[1], fma(w1, Mc[7], fma(w5 * 2.0, Mc[2], fma(w13, Mc[0], Mp[13]))))));
+  Mp[14] = fma(w0, Mc[14], fma(w3, Mc[5], fma(w2, Mc[6], fma(w8, Mc[1], fma(w1, Mc[8], fma(w6, Mc[2], fma(w5, Mc[3], fma(w14, Mc[0], Mp[14]))))))));
+  Mp[15] = fma(w0, Mc[15], fma(w3 * 2.0, Mc[6], fma(w9, Mc[1], fma(w1, Mc[9], fma(w6 * 2.0, Mc[3], fma(w15, Mc[0], Mp[15]))))));
+  Mp[16] = fma(w0, Mc[16], fma(w2 * 3.0, Mc[7], fma(w7 * 3.0, Mc[2], fma(w16, Mc[0], Mp[16]))));
+  Mp[17] = fma(w0, Mc[17], fma(w3, Mc[7], fma(w2 * 2.0, Mc[8], fma(w8 * 2.0, Mc[2], fma(w7, Mc[3], fma(w17, Mc[0], Mp[17]))))));
+  Mp[18] = fma(w0, Mc[18], fma(w3 * 2.0, Mc[8], fma(w9, Mc[2], fma(w2, Mc[9], fma(w8 * 2.0, Mc[3], fma(w18, Mc[0], Mp[18]))))));
+  Mp[19] = fma(w0, Mc[19], fma(w3 * 3.0, Mc[9], fma(w9 * 3.0, Mc[3], fma(w19, Mc[0], Mp[19]))));
+  Mp[20] = fma(w0, Mc[20], fma(w1 * 4.0, Mc[10], fma(w4 * 6.0, Mc[4], fma(w10 * 4.0, Mc[1], fma(w20, Mc[0], Mp[20])))));
+  Mp[21] = fma(w0, Mc[21], fma(w2, Mc[10], fma(w1 * 3.0, Mc[11], fma(w5 * 3.0, Mc[4], fma(w4 * 3.0, Mc[5], fma(w11 * 3.0, Mc[1], fma(w10, Mc[2], fma(w21, Mc[0], Mp[21]))))))));
+  Mp[22] = fma(w0, Mc[22], fma(w3, Mc[10], fma(w1 * 3.0, Mc[12], fma(w6 * 3.0, Mc[4], fma(w4 * 3.0, Mc[6], fma(w12 * 3.0, Mc[1], fma(w10, Mc[3], fma(w22, Mc[0], Mp[22]))))))));
+  Mp[23] = fma(w0, Mc[23], fma(w2 * 2.0, Mc[11], fma(w7, Mc[4], fma(w1 * 2.0, Mc[13], fma(w5 * 4.0, Mc[5], fma(w13 * 2.0, Mc[1], fma(w4, Mc[7], fma(w11 * 2.0, Mc[2], fma(w23, Mc[0], Mp[23])))))))));
+  Mp[24] = fma(w0, Mc[24], fma(w3, Mc[11], fma(w2, Mc[12], fma(w8, Mc[4], fma(w1 * 2.0, Mc[14], fma(w6 * 2.0, Mc[5], fma(w5 * 2.0, Mc[6], fma(w14 * 2.0, Mc[1], fma(w4, Mc[8], fma(w12, Mc[2], fma(w11, Mc[3], fma(w24, Mc[0], Mp[24]))))))))))));
+  Mp[25] = fma(w0, Mc[25], fma(w3 * 2.0, Mc[12], fma(w9, Mc[4], fma(w1 * 2.0, Mc[15], fma(w6 * 4.0, Mc[6], fma(w15 * 2.0, Mc[1], fma(w4, Mc[9], fma(w12 * 2.0, Mc[3], fma(w25, Mc[0], Mp[25])))))))));
+  Mp[26] = fma(w0, Mc[26], fma(w2 * 3.0, Mc[13], fma(w7 * 3.0, Mc[5], fma(w16, Mc[1], fma(w1, Mc[16], fma(w5 * 3.0, Mc[7], fma(w13 * 3.0, Mc[2], fma(w26, Mc[0], Mp[26]))))))));
+  Mp[27] = fma(w0, Mc[27], fma(w3, Mc[13], fma(w2 * 2.0, Mc[14], fma(w8 * 2.0, Mc[5], fma(w7, Mc[6], fma(w17, Mc[1], fma(w1, Mc[17], fma(w6, Mc[7], fma(w5 * 2.0, Mc[8], fma(w14 * 2.0, Mc[2], fma(w13, Mc[3], fma(w27, Mc[0], Mp[27]))))))))))));
+  Mp[28] = fma(w0, Mc[28], fma(w3 * 2.0, Mc[14], fma(w9, Mc[5], fma(w2, Mc[15], fma(w8 * 2.0, Mc[6], fma(w18, Mc[1], fma(w1, Mc[18], fma(w6 * 2.0, Mc[8], fma(w15, Mc[2], fma(w5, Mc[9], fma(w14 * 2.0, Mc[3], fma(w28, Mc[0], Mp[28]))))))))))));
+  Mp[29] = fma(w0, Mc[29], fma(w3 * 3.0, Mc[15], fma(w9 * 3.0, Mc[6], fma(w19, Mc[1], fma(w1, Mc[19], fma(w6 * 3.0, Mc[9], fma(w15 * 3.0, Mc[3], fma(w29, Mc[0], Mp[29]))))))));
+  Mp[30] = fma(w0, Mc[30], fma(w2 * 4.0, Mc[16], fma(w7 * 6.0, Mc[7], fma(w16 * 4.0, Mc[2], fma(w30, Mc[0], Mp[30])))));
+  Mp[31] = fma(w0, Mc[31], fma(w3, Mc[16], fma(w2 * 3.0, Mc[17], fma(w8 * 3.0, Mc[7], fma(w7 * 3.0, Mc[8], fma(w17 * 3.0, Mc[2], fma(w16, Mc[3], fma(w31, Mc[0], Mp[31]))))))));
+  Mp[32] = fma(w0, Mc[32], fma(w3 * 2.0, Mc[17], fma(w9, Mc[7], fma(w2 * 2.0, Mc[18], fma(w8 * 4.0, Mc[8], fma(w18 * 2.0, Mc[2], fma(w7, Mc[9], fma(w17 * 2.0, Mc[3], fma(w32, Mc[0], Mp[32])))))))));
+  Mp[33] = fma(w0, Mc[33], fma(w3 * 3.0, Mc[18], fma(w9 * 3.0, Mc[8], fma(w19, Mc[2], fma(w2, Mc[19], fma(w8 * 3.0, Mc[9], fma(w18 * 3.0, Mc[3], fma(w33, Mc[0], Mp[33]))))))));
+  Mp[34] = fma(w0, Mc[34], fma(w3 * 4.0, Mc[19], fma(w9 * 6.0, Mc[9], fma(w19 * 4.0, Mc[3], fma(w34, Mc[0], Mp[34])))));
+}
+
+__device__ __forceinline__ void p2m_acc_p5(double m, double dx, double dy, double dz, double* __restrict__ M) {
+  const double q0 = m;
+  M[0] += q0;
+  const double q1 = q0 * dx;
+  M[1] += q1;
+  const double q2 = q0 * dy;
+  M[2] += q2;
+  const double q3 = q0 * dz;
+  M[3] += q3;
+  const double q4 = q1 * dx;
+  M[4] += q4;
+  const double q5 = q2 * dx;
+  M[5] += q5;
+  const double q6 = q3 * dx;
+  M[6] += q6;
+  const double q7 = q2 * dy;
+  M[7] += q7;
+  const double q8 = q3 * dy;
+  M[8] += q8;
+  const double q9 = q3 * dz;
+  M[9] += q9;
+  const double q10 = q4 * dx;
+  M[10] += q10;
+  const double q11 = q5 * dx;
+  M[11] += q11;
+  const double q12 = q6 * dx;
+  M[12] += q12;
+  const double q13 = q7 * dx;
+  M[13] += q13;
+  const double q14 = q8 * dx;
+  M[14] += q14;
+  const double q15 = q9 * dx;
+  M[15] += q15;
+  const double q16 = q7 * dy;
+  M[16] += q16;
+  const double q17 = q8 * dy;
+  M[17] += q17;
+  const double q18 = q9 * dy;
+  M[18] += q18;
+  const double q19 = q9 * dz;
+  M[19] += q19;
+  const double q20 = q10 * dx;
+  M[20] += q20;
+  const double q21 = q11 * dx;
+  M[21] += q21;
+  const double q22 = q12 * dx;
+  M[22] += q22;
+  const double q23 = q13 * dx;
+  M[23] += q23;
+  const double q24 = q14 * dx;
+  M[24] += q24;
+  const double q25 = q15 * dx;
+  M[25] += q25;
+  const double q26 = q16 * dx;
+  M[26] += q26;
+  const double q27 = q17 * dx;
+  M[27] += q27;
+  const double q28 = q18 * dx;
+  M[28] += q28;
+  const double q29 = q19 * dx;
+  M[29] += q29;
+  const double q30 = q16 * dy;
+  M[30] += q30;
+  const double q31 = q17 * dy;
+  M[31] += q31;
+  const double q32 = q18 * dy;
+  M[32] += q32;
+  const double q33 = q19 * dy;
+  M[33] += q33;
+  const double q34 = q19 * dz;
+  M[34] += q34;
+  const double q35 = q20 * dx;
+  M[35] += q35;
+  const double q36 = q21 * dx;
+  M[36] += q36;
+  const double q37 = q22 * dx;
+  M[37] += q37;
+  const double q38 = q23 * dx;
+  M[38] += q38;
+  const double q39 = q24 * dx;
+  M[39] += q39;
+  const double q40 = q25 * dx;
+  M[40] += q40;
+  const double q41 = q26 * dx;
+  M[41] += q41;
+  const double q42 = q27 * dx;
+  M[42] += q42;
+  const double q43 = q28 * dx;
+  M[43] += q43;
+  const double q44 = q29 * dx;
+  M[44] += q44;
+  const double q45 = q30 * dx;
+  M[45] += q45;
+  const double q46 = q31 * dx;
+  M[46] += q46;
+  const double q47 = q32 * dx;
+  M[47] += q47;
+  const double q48 = q33 * dx;
+  M[48] += q48;
+  const double q49 = q34 * dx;
+  M[49] += q49;
+  const double q50 = q30 * dy;
+  M[50] += q50;
+  const double q51 = q31 * dy;
+  M[51] += q51;
+  const double q52 = q32 * dy;
+  M[52] += q52;
+  const double q53 = q33 * dy;
+  M[53] += q53;
+  const double q54 = q34 * dy;
+  M[54] += q54;
+  const double q55 = q34 * dz;
+  M[55] += q55;
+}
+
+__device__ __forceinline__ void m2m_acc_p5(const double* __restrict__ Mc, double sx, double sy, double sz, double* __restrict__ Mp) {
+  const double w0 = 1.0;
+  const double w1 = w0 * sx;
+  const double w2 = w0 * sy;
+  const double w3 = w0 * sz;
+  const double w4 = w1 * sx;
+  const double w5 = w2 * sx;
+  const double w6 = w3 * sx;
+  const double w7 = w2 * sy;
+  const double w8 = w3 * sy;
+  const double w9 = w3 * sz;
+  const double w10 = w4 * sx;
+  const double w11 = w5 * sx;
+  const double w12 = w6 * sx;
+  const double w13 = w7 * sx;
+  const double w14 = w8 * sx;
+  const double w15 = w9 * sx;
+  const double w16 = w7 * sy;
+  const double w17 = w8 * sy;
+  const double w18 = w9 * sy;
+  const double w19 = w9 * sz;
+  const double w20 = w10 * sx;
+  const double w21 = w11 * sx;
+  const double w22 = w12 * sx;
+  const double w23 = w13 * sx;
+  const double w24 = w14 * sx;
+  const double w25 = w15 * sx;
+  const double w26 = w16 * sx;
+  const double w27 = w17 * sx;
+  const double w28 = w18 * sx;
+  const double w29 = w19 * sx;
+  const double w30 = w16 * sy;
+  const double w31 = w17 * sy;
+  const double w32 = w18 * sy;
+  const double w33 = w19 * sy;
+  const double w34 = w19 * sz;
+  const double w35 = w20 * sx;
+  const double w36 = w21 * sx;
+  const double w37 = w22 * sx;
+  const double w38 = w23 * sx;
+  const double w39 = w24 * sx;
+  const double w40 = w25 * sx;
+  const double w41 = w26 * sx;
+  const double w42 = w27 * sx;
+  const double w43 = w28 * sx;
+  const double w44 = w29 * sx;
+  const double w45 = w30 * sx;
+  const double w46 = w31 * sx;
+  const double w47 = w32 * sx;
+  const double w48 = w33 * sx;
+  const double w49 = w34 * sx;
+  const double w50 = w30 * sy;
+  const double w51 = w31 * sy;
+  const double w52 = w32 * sy;
+  const double w53 = w33 * sy;
+  const double w54 = w34 * sy;
+  const double w55 = w34 * sz;
+  Mp[0] = fma(w0, Mc[0], Mp[0]);
+  Mp[1] = fma(w0, Mc[1], fma(w1, Mc[0], Mp[1]));
+  Mp[2] = fma(w0, Mc[2], fma(w2, Mc[0], Mp[2]));
+  Mp[3] = fma(w0, Mc[3], fma(w3, Mc[0], Mp[3]));
+  Mp[4] = fma(w0, Mc[4], fma(w1 * 2.0, Mc[1], fma(w4, Mc[0], Mp[4])));
+  Mp[5] = fma(w0, Mc[5], fma(w2, Mc[1], fma(w1, Mc[2], fma(w5, Mc[0], Mp[5]))));
+  Mp[6] = fma(w0, Mc[6], fma(w3, Mc[1], fma(w1, Mc[3], fma(w6, Mc[0], Mp[6]))));
+  Mp[7] = fma(w0, Mc[7], fma(w2 * 2.0, Mc[2], fma(w7, Mc[0], Mp[7])));
+  Mp[8] = fma(w0, Mc[8], fma(w3, Mc[2], fma(w2, Mc[3], fma(w8, Mc[0], Mp[8]))));
+  Mp[9] = fma(w0, Mc[9], fma(w3 * 2.0, Mc[3], fma(w9, Mc[0], Mp[9])));
+  Mp[10] = fma(w0, Mc[10], fma(w1 * 3.0, Mc[4], fma(w4 * 3.0, Mc[1], fma(w10, Mc[0], Mp[10]))));
+  Mp[11] = fma(w0, Mc[11], fma(w2, Mc[4], fma(w1 * 2.0, Mc[5], fma(w5 * 2.0, Mc[1], fma(w4, Mc[2], fma(w11, Mc[0], Mp[11]))))));
+  Mp[12] = fma(w0, Mc[12], fma(w3, Mc[4], fma(w1 * 2.0, Mc[6], fma(w6 * 2.0, Mc[1], fma(w4, Mc[3], fma(w12, Mc[0], Mp[12]))))));
+  Mp[13] = fma(w0, Mc[13], fma(w2 * 2.0, Mc[5], fma(w7, Mc[1], fma(w1, Mc[7], fma(w5 * 2.0, Mc[2], fma(w13, Mc[0], Mp[13]))))));
+  Mp[14] = fma(w0, Mc[14], fma(w3, Mc[5], fma(w2, Mc[6], fma(w8, Mc[1], fma(w1, Mc[8], fma(w6, Mc[2], fma(w5, Mc[3], fma(w14, Mc[0], Mp[14]))))))));
+  Mp[15] = fma(w0, Mc[15], fma(w3 * 2.0, Mc[6], fma(w9, Mc[1], fma(w1, Mc[9], fma(w6 * 2.0, Mc[3], fma(w15, Mc[0], Mp[15]))))));
+  Mp[16] = fma(w0, Mc[16], fma(w2 * 3.0, Mc[7], fma(w7 * 3.0, Mc[2], fma(w16, Mc[0], Mp[16]))));
+  Mp[17] = fma(w0, Mc[17], fma(w3, Mc[7], fma(w2 * 2.0, Mc[8], fma(w8 * 2.0, Mc[2], fma(w7, Mc[3], fma(w17, Mc[0], Mp[17]))))));
+  Mp[18] = fma(w0, Mc[18], fma(w3 * 2.0, Mc[8], fma(w9, Mc[2], fma(w2, Mc[9], fma(w8 * 2.0, Mc[3], fma(w18, Mc[0], Mp[18]))))));
+  Mp[19] = fma(w0, Mc[19], fma(w3 * 3.0, Mc[9], fma(w9 * 3.0, Mc[3], fma(w19, Mc[0], Mp[19]))));
+  Mp[20] = fma(w0, Mc[20], fma(w1 * 4.0, Mc[10], fma(w4 * 6.0, Mc[4], fma(w10 * 4.0, Mc[1], fma(w20, Mc[0], Mp[20])))));
+  Mp[21] = fma(w0, Mc[21], fma(w2, Mc[10], fma(w1 * 3.0, Mc[11], fma(w5 * 3.0, Mc[4], fma(w4 * 3.0, Mc[5], fma(w11 * 3.0, Mc[1], fma(w10, Mc[2], fma(w21, Mc[0], Mp[21]))))))));
+  Mp[22] = fma(w0, Mc[22], fma(w3, Mc[10], fma(w1 * 3.0, Mc[12], fma(w6 * 3.0, Mc[4], fma(w4 * 3.0, Mc[6], fma(w12 * 3.0, Mc[1], fma(w10, Mc[3], fma(w22, Mc[0], Mp[22]))))))));
+  Mp[23] = fma(w0, Mc[23], fma(w2 * 2.0, Mc[11], fma(w7, Mc[4], fma(w1 * 2.0, Mc[13], fma(w5 * 4.0, Mc[5], fma(w13 * 2.0, Mc[1], fma(w4, Mc[7], fma(w11 * 2.0, Mc[2], fma(w23, Mc[0], Mp[23])))))))));
+  Mp[24] = fma(w0, Mc[24], fma(w3, Mc[11], fma(w2, Mc[12], fma(w8, Mc[4], fma(w1 * 2.0, Mc[14], fma(w6 * 2.0, Mc[5], fma(w5 * 2.0, Mc[6], fma(w14 * 2.0, Mc[1], fma(w4, Mc[8], fma(w12, Mc[2], fma(w11, Mc[3], fma(w24, Mc[0], Mp[24]))))))))))));
+  Mp[25] = fma(w0, Mc[25], fma(w3 * 2.0, Mc[12], fma(w9, Mc[4], fma(w1 * 2.0, Mc[15], fma(w6 * 4.0, Mc[6], fma(w15 * 2.0, Mc[1], fma(w4, Mc[9], fma(w12 * 2.0, Mc[3], fma(w25, Mc[0], Mp[25])))))))));
+  Mp[26] = fma(w0, Mc[26], fma(w2 * 3.0, Mc[13], fma(w7 * 3.0, Mc[5], fma(w16, Mc[1], fma(w1, Mc[16], fma(w5 * 3.0, Mc[7], fma(w13 * 3.0, Mc[2], fma(w26, Mc[0], Mp[26]))))))));
+  Mp[27] = fma(w0, Mc[27], fma(w3, Mc[13], fma(w2 * 2.0, Mc[14], fma(w8 * 2.0, Mc[5], fma(w7, Mc[6], fma(w17, Mc[1], fma(w1, Mc[17], fma(w6, Mc[7], fma(w5 * 2.0, Mc[8], fma(w14 * 2.0, Mc[2], fma(w13, Mc[3], fma(w27, Mc[0], Mp[27]))))))))))));
+  Mp[28] = fma(w0, Mc[28], fma(w3 * 2.0, Mc[14], fma(w9, Mc[5], fma(w2, Mc[15], fma(w8 * 2.0, Mc[6], fma(w18, Mc[1], fma(w1, Mc[18], fma(w6 * 2.0, Mc[8], fma(w15, Mc[2], fma(w5, Mc[9], fma(w14 * 2.0, Mc[3], fma(w28, Mc[0], Mp[28]))))))))))));
+  Mp[29] = fma(w0, Mc[29], fma(w3 * 3.0, Mc[15], fma(w9 * 3.0, Mc[6], fma(w19, Mc[1], fma(w1, Mc[19], fma(w6 * 3.0, Mc[9], fma(w15 * 3.0, Mc[3], fma(w29, Mc[0], Mp[29]))))))));
+  Mp[30] = fma(w0, Mc[30], fma(w2 * 4.0, Mc[16], fma(w7 * 6.0, Mc[7], fma(w16 * 4.0, Mc[2], fma(w30, Mc[0], Mp[30])))));
+  Mp[31] = fma(w0, Mc[31], fma(w3, Mc[16], fma(w2 * 3.0, Mc[17], fma(w8 * 3.0, Mc[7], fma(w7 * 3.0, Mc[8], fma(w17 * 3.0, Mc[2], fma(w16, Mc[3], fma(w31, Mc[0], Mp[31]))))))));
+  Mp[32] = fma(w0, Mc[32], fma(w3 * 2.0, Mc[17], fma(w9, Mc[7], fma(w2 * 2.0, Mc[18], fma(w8 * 4.0, Mc[8], fma(w18 * 2.0, Mc[2], fma(w7, Mc[9], fma(w17 * 2.0, Mc[3], fma(w32, Mc[0], Mp[32])))))))));
+  Mp[33] = fma(w0, Mc[33], fma(w3 * 3.0, Mc[18], fma(w9 * 3.0, Mc[8], fma(w19, Mc[2], fma(w2, Mc[19], fma(w8 * 3.0, Mc[9], fma(w18 * 3.0, Mc[3], fma(w33, Mc[0], Mp[33]))))))));
+  Mp[34] = fma(w0, Mc[34], fma(w3 * 4.0, Mc[19], fma(w9 * 6.0, Mc[9], fma(w19 * 4.0, Mc[3], fma(w34, Mc[0], Mp[34])))));
+  Mp[35] = fma(w0, Mc[35], fma(w1 * 5.0, Mc[20], fma(w4 * 10.0, Mc[10], fma(w10 * 10.0, Mc[4], fma(w20 * 5.0, Mc[1], fma(w35, Mc[0], Mp[35]))))));
+  Mp[36] = fma(w0, Mc[36], fma(w2, Mc[20], fma(w1 * 4.0, Mc[21], fma(w5 * 4.0, Mc[10], fma(w4 * 6.0, Mc[11], fma(w11 * 6.0, Mc[4], fma(w10 * 4.0, Mc[5], fma(w21 * 4.0, Mc[1], fma(w20, Mc[2], fma(w36, Mc[0], Mp[36]))))))))));
+  Mp[37] = fma(w0, Mc[37], fma(w3, Mc[20], fma(w1 * 4.0, Mc[22], fma(w6 * 4.0, Mc[10], fma(w4 * 6.0, Mc[12], fma(w12 * 6.0, Mc[4], fma(w10 * 4.0, Mc[6], fma(w22 * 4.0, Mc[1], fma(w20, Mc[3], fma(w37, Mc[0], Mp[37]))))))))));
+  Mp[38] = fma(w0, Mc[38], fma(w2 * 2.0, Mc[21], fma(w7, Mc[10], fma(w1 * 3.0, Mc[23], fma(w5 * 6.0, Mc[11], fma(w13 * 3.0, Mc[4], fma(w4 * 3.0, Mc[13], fma(w11 * 6.0, Mc[5], fma(w23 * 3.0, Mc[1], fma(w10, Mc[7], fma(w21 * 2.0, Mc[2], fma(w38, Mc[0], Mp[38]))))))))))));
+  Mp[39] = fma(w0, Mc[39], fma(w3, Mc[21], fma(w2, Mc[22], fma(w8, Mc[10], fma(w1 * 3.0, Mc[24], fma(w6 * 3.0, Mc[11], fma(w5 * 3.0, Mc[12], fma(w14 * 3.0, Mc[4], fma(w4 * 3.0, Mc[14], fma(w12 * 3.0, Mc[5], fma(w11 * 3.0, Mc[6], fma(w24 * 3.0, Mc[1], fma(w10, Mc[8], fma(w22, Mc[2], fma(w21, Mc[3], fma(w39, Mc[0], Mp[39]))))))))))))))));
+  Mp[40] = fma(w0, Mc[40], fma(w3 * 2.0, Mc[22], fma(w9, Mc[10], fma(w1 * 3.0, Mc[25], fma(w6 * 6.0, Mc[12], fma(w15 * 3.0, Mc[4], fma(w4 * 3.0, Mc[15], fma(w12 * 6.0, Mc[6], fma(w25 * 3.0, Mc[1], fma(w10, Mc[9], fma(w22 * 2.0, Mc[3], fma(w40, Mc[0], Mp[40]))))))))))));
+  Mp[41] = fma(w0, Mc[41], fma(w2 * 3.0, Mc[23], fma(w7 * 3.0, Mc[11], fma(w16, Mc[4], fma(w1 * 2.0, Mc[26], fma(w5 * 6.0, Mc[13], fma(w13 * 6.0, Mc[5], fma(w26 * 2.0, Mc[1], fma(w4, Mc[16], fma(w11 * 3.0, Mc[7], fma(w23 * 3.0, Mc[2], fma(w41, Mc[0], Mp[41]))))))))))));
+  Mp[42] = fma(w0, Mc[42], fma(w3, Mc[23], fma(w2 * 2.0, Mc[24], fma(w8 * 2.0, Mc[11], fma(w7, Mc[12], fma(w17, Mc[4], fma(w1 * 2.0, Mc[27], fma(w6 * 2.0, Mc[13], fma(w5 * 4.0, Mc[14], fma(w14 * 4.0, Mc[5], fma(w13 * 2.0, Mc[6], fma(w27 * 2.0, Mc[1], fma(w4, Mc[17], fma(w12, Mc[7], fma(w11 * 2.0, Mc[8], fma(w24 * 2.0, Mc[2], fma(w23, Mc[3], fma(w42, Mc[0], Mp[42]))))))))))))))))));
+  Mp[43] = fma(w0, Mc[43], fma(w3 * 2.0, Mc[24], fma(w9, Mc[11], fma(w2, Mc[25], fma(w8 * 2.0, Mc[12], fma(w18, Mc[4], fma(w1 * 2.0, Mc[28], fma(w6 * 4.0, Mc[14], fma(w15 * 2.0, Mc[5], fma(w5 * 2.0, Mc[15], fma(w14 * 4.0, Mc[6], fma(w28 * 2.0, Mc[1], fma(w4, Mc[18], fma(w12 * 2.0, Mc[8], fma(w25, Mc[2], fma(w11, Mc[9], fma(w24 * 2.0, Mc[3], fma(w43, Mc[0], Mp[43]))))))))))))))))));
+  Mp[44] = fma(w0, Mc[44], fma(w3 * 3.0, Mc[25], fma(w9 * 3.0, Mc[12], fma(w19, Mc[4], fma(w1 * 2.0, Mc[29], fma(w6 * 6.0, Mc[15], fma(w15 * 6.0, Mc[6], fma(w29 * 2.0, Mc[1], fma(w4, Mc[19], fma(w12 * 3.0, Mc[9], fma(w25 * 3.0, Mc[3], fma(w44, Mc[0], Mp[44]))))))))))));
+  Mp[45] = fma(w0, Mc[45], fma(w2 * 4.0, Mc[26], fma(w7 * 6.0, Mc[13], fma(w16 * 4.0, Mc[5], fma(w30, Mc[1], fma(w1, Mc[30], fma(w5 * 4.0, Mc[16], fma(w13 * 6.0, Mc[7], fma(w26 * 4.0, Mc[2], fma(w45, Mc[0], Mp[45]))))))))));
+  Mp[46] = fma(w0, Mc[46], fma(w3, Mc[26], fma(w2 * 3.0, Mc[27], fma(w8 * 3.0, Mc[13], fma(w7 * 3.0, Mc[14], fma(w17 * 3.0, Mc[5], fma(w16, Mc[6], fma(w31, Mc[1], fma(w1, Mc[31], fma(w6, Mc[16], fma(w5 * 3.0, Mc[17], fma(w14 * 3.0, Mc[7], fma(w13 * 3.0, Mc[8], fma(w27 * 3.0, Mc[2], fma(w26, Mc[3], fma(w46, Mc[0], Mp[46]))))))))))))))));
+  Mp[47] = fma(w0, Mc[47], fma(w3 * 2.0, Mc[27], fma(w9, Mc[13], fma(w2 * 2.0, Mc[28], fma(w8 * 4.0, Mc[14], fma(w18 * 2.0, Mc[5], fma(w7, Mc[15], fma(w17 * 2.0, Mc[6], fma(w32, Mc[1], fma(w1, Mc[32], fma(w6 * 2.0, Mc[17], fma(w15, Mc[7], fma(w5 * 2.0, Mc[18], fma(w14 * 4.0, Mc[8], fma(w28 * 2.0, Mc[2], fma(w13, Mc[9], fma(w27 * 2.0, Mc[3], fma(w47, Mc[0], Mp[47]))))))))))))))))));
+  Mp[48] = fma(w0, Mc[48], fma(w3 * 3.0, Mc[28], fma(w9 * 3.0, Mc[14], fma(w19, Mc[5], fma(w2, Mc[29], fma(w8 * 3.0, Mc[15], fma(w18 * 3.0, Mc[6], fma(w33, Mc[1], fma(w1, Mc[33], fma(w6 * 3.0, Mc[18], fma(w15 * 3.0, Mc[8], fma(w29, Mc[2], fma(w5, Mc[19], fma(w14 * 3.0, Mc[9], fma(w28 * 3.0, Mc[3], fma(w48, Mc[0], Mp[48]))))))))))))))));
+  Mp[49] = fma(w0, Mc[49], fma(w3 * 4.0, Mc[29], fma(w9 * 6.0, Mc[15], fma(w19 * 4.0, Mc[6], fma(w34, Mc[1], fma(w1, Mc[34], fma(w6 * 4.0, Mc[19], fma(w15 * 6.0, Mc[9], fma(w29 * 4.0, Mc[3], fma(w49, Mc[0], Mp[49]))))))))));
+  Mp[50] = fma(w0, Mc[50], fma(w2 * 5.0, Mc[30], fma(w7 * 10.0, Mc[16], fma(w16 * 10.0, Mc[7], fma(w30 * 5.0, Mc[2], fma(w50, Mc[0], Mp[50]))))));
+  Mp[51] = fma(w0, Mc[51], fma(w3, Mc[30], fma(w2 * 4.0, Mc[31], fma(w8 * 4.0, Mc[16], fma(w7 * 6.0, Mc[17], fma(w17 * 6.0, Mc[7], fma(w16 * 4.0, Mc[8], fma(w31 * 4.0, Mc[2], fma(w30, Mc[3], fma(w51, Mc[0], Mp[51]))))))))));
+  Mp[52] = fma(w0, Mc[52], fma(w3 * 2.0, Mc[31], fma(w9, Mc[16], fma(w2 * 3.0, Mc[32], fma(w8 * 6.0, Mc[17], fma(w18 * 3.0, Mc[7], fma(w7 * 3.0, Mc[18], fma(w17 * 6.0, Mc[8], fma(w32 * 3.0, Mc[2], fma(w16, Mc[9], fma(w31 * 2.0, Mc[3], fma(w52, Mc[0], Mp[52]))))))))))));
+  Mp[53] = fma(w0, Mc[53], fma(w3 * 3.0, Mc[32], fma(w9 * 3.0, Mc[17], fma(w19, Mc[7], fma(w2 * 2.0, Mc[33], fma(w8 * 6.0, Mc[18], fma(w18 * 6.0, Mc[8], fma(w33 * 2.0, Mc[2], fma(w7, Mc[19], fma(w17 * 3.0, Mc[9], fma(w32 * 3.0, Mc[3], fma(w53, Mc[0], Mp[53]))))))))))));
+  Mp[54] = fma(w0, Mc[54], fma(w3 * 4.0, Mc[33], fma(w9 * 6.0, Mc[18], fma(w19 * 4.0, Mc[8], fma(w34, Mc[2], fma(w2, Mc[34], fma(w8 * 4.0, Mc[19], fma(w18 * 6.0, Mc[9], fma(w33 * 4.0, Mc[3], fma(w54, Mc[0], Mp[54]))))))))));
+  Mp[55] = fma(w0, Mc[55], fma(w3 * 5.0, Mc[34], fma(w9 * 10.0, Mc[19], fma(w19 * 10.0, Mc[9], fma(w34 * 5.0, Mc[3], fma(w55, Mc[0], Mp[55]))))));
+}
+
+constexpr int kNL1 = 9;  // local coefficients, image-field order 1
+template <typename T>
+__device__ __forceinline__ void m2l_pe1(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {
+  // Lc[t-1] accumulates L_m for multi-index t >= 1 (orders 1..2)
+  Lc[0] = fma(-M[3], D[6], fma(-M[2], D[5], fma(-M[1], D[4], fma(M[0], D[1], Lc[0]))));
+  Lc[1] = fma(-M[3], D[8], fma(-M[2], D[7], fma(-M[1], D[5], fma(M[0], D[2], Lc[1]))));
+  Lc[2] = fma(-M[3], D[9], fma(-M[2], D[8], fma(-M[1], D[6], fma(M[0], D[3], Lc[2]))));
+  Lc[3] = fma(M[0], D[4], Lc[3]);
+  Lc[4] = fma(M[0], D[5], Lc[4]);
+  Lc[5] = fma(M[0], D[6], Lc[5]);
+  Lc[6] = fma(M[0], D[7], Lc[6]);
+  Lc[7] = fma(M[0], D[8], Lc[7]);
+  Lc[8] = fma(M[0], D[9], Lc[8]);
+}
+template <typename T>
+__device__ __forceinline__ void l2p_pe1(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {
+  // a_k -= sum_{|n|<=1} d^n/n! L_{n+e_k}
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  ax = fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))));
+  ay = fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))));
+  az = fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))));
+}
+
+constexpr int kNL2 = 19;  // local coefficients, image-field order 2
+template <typename T>
+__device__ __forceinline__ void m2l_pe2(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {
+  // Lc[t-1] accumulates L_m for multi-index t >= 1 (orders 1..3)
+  Lc[0] = fma(M[9] * T(0.5), D[15], fma(M[8], D[14], fma(M[7] * T(0.5), D[13], fma(M[6], D[12], fma(M[5], D[11], fma(M[4] * T(0.5), D[10], fma(-M[3], D[6], fma(-M[2], D[5], fma(-M[1], D[4], fma(M[0], D[1], Lc[0]))))))))));
+  Lc[1] = fma(M[9] * T(0.5), D[18], fma(M[8], D[17], fma(M[7] * T(0.5), D[16], fma(M[6], D[14], fma(M[5], D[13], fma(M[4] * T(0.5), D[11], fma(-M[3], D[8], fma(-M[2], D[7], fma(-M[1], D[5], fma(M[0], D[2], Lc[1]))))))))));
+  Lc[2] = fma(M[9] * T(0.5), D[19], fma(M[8], D[18], fma(M[7] * T(0.5), D[17], fma(M[6], D[15], fma(M[5], D[14], fma(M[4] * T(0.5), D[12], fma(-M[3], D[9], fma(-M[2], D[8], fma(-M[1], D[6], fma(M[0], D[3], Lc[2]))))))))));
+  Lc[3] = fma(-M[3], D[12], fma(-M[2], D[11], fma(-M[1], D[10], fma(M[0], D[4], Lc[3]))));
+  Lc[4] = fma(-M[3], D[14], fma(-M[2], D[13], fma(-M[1], D[11], fma(M[0], D[5], Lc[4]))));
+  Lc[5] = fma(-M[3], D[15], fma(-M[2], D[14], fma(-M[1], D[12], fma(M[0], D[6], Lc[5]))));
+  Lc[6] = fma(-M[3], D[17], fma(-M[2], D[16], fma(-M[1], D[13], fma(M[0], D[7], Lc[6]))));
+  Lc[7] = fma(-M[3], D[18], fma(-M[2], D[17], fma(-M[1], D[14], fma(M[0], D[8], Lc[7]))));
+  Lc[8] = fma(-M[3], D[19], fma(-M[2], D[18], fma(-M[1], D[15], fma(M[0], D[9], Lc[8]))));
+  Lc[9] = fma(M[0], D[10], Lc[9]);
+  Lc[10] = fma(M[0], D[11], Lc[10]);
+  Lc[11] = fma(M[0], D[12], Lc[11]);
+  Lc[12] = fma(M[0], D[13], Lc[12]);
+  Lc[13] = fma(M[0], D[14], Lc[13]);
+  Lc[14] = fma(M[0], D[15], Lc[14]);
+  Lc[15] = fma(M[0], D[16], Lc[15]);
+  Lc[16] = fma(M[0], D[17], Lc[16]);
+  Lc[17] = fma(M[0], D[18], Lc[17]);
+  Lc[18] = fma(M[0], D[19], Lc[18]);
+}
+template <typename T>
+__device__ __forceinline__ void l2p_pe2(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {
+  // a_k -= sum_{|n|<=2} d^n/n! L_{n+e_k}
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  ax = fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))));
+  ay = fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))));
+  az = fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))));
+}
+
+constexpr int kNL3 = 34;  // local coefficients, image-field order 3
+template <typename T>
+__device__ __forceinline__ void m2l_pe3(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {
+  // Lc[t-1] accumulates L_m for multi-index t >= 1 (orders 1..4)
+  Lc[0] = fma(M[19] * T(-0.16666666666666666), D[29], fma(M[18] * T(-0.5), D[28], fma(M[17] * T(-0.5), D[27], fma(M[16] * T(-0.16666666666666666), D[26], fma(M[15] * T(-0.5), D[25], fma(-M[14], D[24], fma(M[13] * T(-0.5), D[23], fma(M[12] * T(-0.5), D[22], fma(M[11] * T(-0.5), D[21], fma(M[10] * T(-0.16666666666666666), D[20], fma(M[9] * T(0.5), D[15], fma(M[8], D[14], fma(M[7] * T(0.5), D[13], fma(M[6], D[12], fma(M[5], D[11], fma(M[4] * T(0.5), D[10], fma(-M[3], D[6], fma(-M[2], D[5], fma(-M[1], D[4], fma(M[0], D[1], Lc[0]))))))))))))))))))));
+  Lc[1] = fma(M[19] * T(-0.16666666666666666), D[33], fma(M[18] * T(-0.5), D[32], fma(M[17] * T(-0.5), D[31], fma(M[16] * T(-0.16666666666666666), D[30], fma(M[15] * T(-0.5), D[28], fma(-M[14], D[27], fma(M[13] * T(-0.5), D[26], fma(M[12] * T(-0.5), D[24], fma(M[11] * T(-0.5), D[23], fma(M[10] * T(-0.16666666666666666), D[21], fma(M[9] * T(0.5), D[18], fma(M[8], D[17], fma(M[7] * T(0.5), D[16], fma(M[6], D[14], fma(M[5], D[13], fma(M[4] * T(0.5), D[11], fma(-M[3], D[8], fma(-M[2], D[7], fma(-M[1], D[5], fma(M[0], D[2], Lc[1]))))))))))))))))))));
+  Lc[2] = fma(M[19] * T(-0.16666666666666666), D[34], fma(M[18] * T(-0.5), D[33], fma(M[17] * T(-0.5), D[32], fma(M[16] * T(-0.16666666666666666), D[31], fma(M[15] * T(-0.5), D[29], fma(-M[14], D[28], fma(M[13] * T(-0.5), D[27], fma(M[12] * T(-0.5), D[25], fma(M[11] * T(-0.5), D[24], fma(M[10] * T(-0.16666666666666666), D[22], fma(M[9] * T(0.5), D[19], fma(M[8], D[18], fma(M[7] * T(0.5), D[17], fma(M[6], D[15], fma(M[5], D[14], fma(M[4] * T(0.5), D[12], fma(-M[3], D[9], fma(-M[2], D[8], fma(-M[1], D[6], fma(M[0], D[3], Lc[2]))))))))))))))))))));
+  Lc[3] = fma(M[9] * T(0.5), D[25], fma(M[8], D[24], fma(M[7] * T(0.5), D[23], fma(M[6], D[22], fma(M[5], D[21], fma(M[4] * T(0.5), D[20], fma(-M[3], D[12], fma(-M[2], D[11], fma(-M[1], D[10], fma(M[0], D[4], Lc[3]))))))))));
+  Lc[4] = fma(M[9] * T(0.5), D[28], fma(M[8], D[27], fma(M[7] * T(0.5), D[26], fma(M[6], D[24], fma(M[5], D[23], fma(M[4] * T(0.5), D[21], fma(-M[3], D[14], fma(-M[2], D[13], fma(-M[1], D[11], fma(M[0], D[5], Lc[4]))))))))));
+  Lc[5] = fma(M[9] * T(0.5), D[29], fma(M[8], D[28], fma(M[7] * T(0.5), D[27], fma(M[6], D[25], fma(M[5], D[24], fma(M[4] * T(0.5), D[22], fma(-M[3], D[15], fma(-M[2], D[14], fma(-M[1], D[12], fma(M[0], D[6], Lc[5]))))))))));
+  Lc[6] = fma(M[9] * T(0.5), D[32], fma(M[8], D[31], fma(M[7] * T(0.5), D[30], fma(M[6], D[27], fma(M[5], D[26], fma(M[4] * T(0.5), D[23], fma(-M[3], D[17], fma(-M[2], D[16], fma(-M[1], D[13], fma(M[0], D[7], Lc[6]))))))))));
+  Lc[7] = fma(M[9] * T(0.5), D[33], fma(M[8], D[32], fma(M[7] * T(0.5), D[31], fma(M[6], D[28], fma(M[5], D[27], fma(M[4] * T(0.5), D[24], fma(-M[3], D[18], fma(-M[2], D[17], fma(-M[1], D[14], fma(M[0], D[8], Lc[7]))))))))));
+  Lc[8] = fma(M[9] * T(0.5), D[34], fma(M[8], D[33], fma(M[7] * T(0.5), D[32], fma(M[6], D[29], fma(M[5], D[28], fma(M[4] * T(0.5), D[25], fma(-M[3], D[19], fma(-M[2], D[18], fma(-M[1], D[15], fma(M[0], D[9], Lc[8]))))))))));
+  Lc[9] = fma(-M[3], D[22], fma(-M[2], D[21], fma(-M[1], D[20], fma(M[0], D[10], Lc[9]))));
+  Lc[10] = fma(-M[3], D[24], fma(-M[2], D[23], fma(-M[1], D[21], fma(M[0], D[11], Lc[10]))));
+  Lc[11] = fma(-M[3], D[25], fma(-M[2], D[24], fma(-M[1], D[22], fma(M[0], D[12], Lc[11]))));
+  Lc[12] = fma(-M[3], D[27], fma(-M[2], D[26], fma(-M[1], D[23], fma(M[0], D[13], Lc[12]))));
+  Lc[13] = fma(-M[3], D[28], fma(-M[2], D[27], fma(-M[1], D[24], fma(M[0], D[14], Lc[13]))));
+  Lc[14] = fma(-M[3], D[29], fma(-M[2], D[28], fma(-M[1], D[25], fma(M[0], D[15], Lc[14]))));
+  Lc[15] = fma(-M[3], D[31], fma(-M[2], D[30], fma(-M[1], D[26], fma(M[0], D[16], Lc[15]))));
+  Lc[16] = fma(-M[3], D[32], fma(-M[2], D[31], fma(-M[1], D[27], fma(M[0], D[17], Lc[16]))));
+  Lc[17] = fma(-M[3], D[33], fma(-M[2], D[32], fma(-M[1], D[28], fma(M[0], D[18], Lc[17]))));
+  Lc[18] = fma(-M[3], D[34], fma(-M[2], D[33], fma(-M[1], D[29], fma(M[0], D[19], Lc[18]))));
+  Lc[19] = fma(M[0], D[20], Lc[19]);
+  Lc[20] = fma(M[0], D[21], Lc[20]);
+  Lc[21] = fma(M[0], D[22], Lc[21]);
+  Lc[22] = fma(M[0], D[23], Lc[22]);
+  Lc[23] = fma(M[0], D[24], Lc[23]);
+  Lc[24] = fma(M[0], D[25], Lc[24]);
+  Lc[25] = fma(M[0], D[26], Lc[25]);
+  Lc[26] = fma(M[0], D[27], Lc[26]);
+  Lc[27] = fma(M[0], D[28], Lc[27]);
+  Lc[28] = fma(M[0], D[29], Lc[28]);
+  Lc[29] = fma(M[0], D[30], Lc[29]);
+  Lc[30] = fma(M[0], D[31], Lc[30]);
+  Lc[31] = fma(M[0], D[32], Lc[31]);
+  Lc[32] = fma(M[0], D[33], Lc[32]);
+  Lc[33] = fma(M[0], D[34], Lc[33]);
+}
+template <typename T>
+__device__ __forceinline__ void l2p_pe3(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {
+  // a_k -= sum_{|n|<=3} d^n/n! L_{n+e_k}
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  ax = fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))))))))))))));
+  ay = fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))))))))))))));
+  az = fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))));
+}
+
+constexpr int kNL4 = 55;  // local coefficients, image-field order 4
+template <typename T>
+__device__ __forceinline__ void m2l_pe4(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {
+  // Lc[t-1] accumulates L_m for multi-index t >= 1 (orders 1..5)
+  Lc[0] = fma(M[34] * T(0.041666666666666664), D[49], fma(M[33] * T(0.16666666666666666), D[48], fma(M[32] * T(0.25), D[47], fma(M[31] * T(0.16666666666666666), D[46], fma(M[30] * T(0.041666666666666664), D[45], fma(M[29] * T(0.16666666666666666), D[44], fma(M[28] * T(0.5), D[43], fma(M[27] * T(0.5), D[42], fma(M[26] * T(0.16666666666666666), D[41], fma(M[25] * T(0.25), D[40], fma(M[24] * T(0.5), D[39], fma(M[23] * T(0.25), D[38], fma(M[22] * T(0.16666666666666666), D[37], fma(M[21] * T(0.16666666666666666), D[36], fma(M[20] * T(0.041666666666666664), D[35], fma(M[19] * T(-0.16666666666666666), D[29], fma(M[18] * T(-0.5), D[28], fma(M[17] * T(-0.5), D[27], fma(M[16] * T(-0.16666666666666666), D[26], fma(M[15] * T(-0.5), D[25], fma(-M[14], D[24], fma(M[13] * T(-0.5), D[23], fma(M[12] * T(-0.5), D[22], fma(M[11] * T(-0.5), D[21], fma(M[10] * T(-0.16666666666666666), D[20], fma(M[9] * T(0.5), D[15], fma(M[8], D[14], fma(M[7] * T(0.5), D[13], fma(M[6], D[12], fma(M[5], D[11], fma(M[4] * T(0.5), D[10], fma(-M[3], D[6], fma(-M[2], D[5], fma(-M[1], D[4], fma(M[0], D[1], Lc[0])))))))))))))))))))))))))))))))))));
+  Lc[1] = fma(M[34] * T(0.041666666666666664), D[54], fma(M[33] * T(0.16666666666666666), D[53], fma(M[32] * T(0.25), D[52], fma(M[31] * T(0.16666666666666666), D[51], fma(M[30] * T(0.041666666666666664), D[50], fma(M[29] * T(0.16666666666666666), D[48], fma(M[28] * T(0.5), D[47], fma(M[27] * T(0.5), D[46], fma(M[26] * T(0.16666666666666666), D[45], fma(M[25] * T(0.25), D[43], fma(M[24] * T(0.5), D[42], fma(M[23] * T(0.25), D[41], fma(M[22] * T(0.16666666666666666), D[39], fma(M[21] * T(0.16666666666666666), D[38], fma(M[20] * T(0.041666666666666664), D[36], fma(M[19] * T(-0.16666666666666666), D[33], fma(M[18] * T(-0.5), D[32], fma(M[17] * T(-0.5), D[31], fma(M[16] * T(-0.16666666666666666), D[30], fma(M[15] * T(-0.5), D[28], fma(-M[14], D[27], fma(M[13] * T(-0.5), D[26], fma(M[12] * T(-0.5), D[24], fma(M[11] * T(-0.5), D[23], fma(M[10] * T(-0.16666666666666666), D[21], fma(M[9] * T(0.5), D[18], fma(M[8], D[17], fma(M[7] * T(0.5), D[16], fma(M[6], D[14], fma(M[5], D[13], fma(M[4] * T(0.5), D[11], fma(-M[3], D[8], fma(-M[2], D[7], fma(-M[1], D[5], fma(M[0], D[2], Lc[1])))))))))))))))))))))))))))))))))));
+  Lc[2] = fma(M[34] * T(0.041666666666666664), D[55], fma(M[33] * T(0.16666666666666666), D[54], fma(M[32] * T(0.25), D[53], fma(M[31] * T(0.16666666666666666), D[52], fma(M[30] * T(0.041666666666666664), D[51], fma(M[29] * T(0.16666666666666666), D[49], fma(M[28] * T(0.5), D[48], fma(M[27] * T(0.5), D[47], fma(M[26] * T(0.16666666666666666), D[46], fma(M[25] * T(0.25), D[44], fma(M[24] * T(0.5), D[43], fma(M[23] * T(0.25), D[42], fma(M[22] * T(0.16666666666666666), D[40], fma(M[21] * T(0.16666666666666666), D[39], fma(M[20] * T(0.041666666666666664), D[37], fma(M[19] * T(-0.16666666666666666), D[34], fma(M[18] * T(-0.5), D[33], fma(M[17] * T(-0.5), D[32], fma(M[16] * T(-0.16666666666666666), D[31], fma(M[15] * T(-0.5), D[29], fma(-M[14], D[28], fma(M[13] * T(-0.5), D[27], fma(M[12] * T(-0.5), D[25], fma(M[11] * T(-0.5), D[24], fma(M[10] * T(-0.16666666666666666), D[22], fma(M[9] * T(0.5), D[19], fma(M[8], D[18], fma(M[7] * T(0.5), D[17], fma(M[6], D[15], fma(M[5], D[14], fma(M[4] * T(0.5), D[12], fma(-M[3], D[9], fma(-M[2], D[8], fma(-M[1], D[6], fma(M[0], D[3], Lc[2])))))))))))))))))))))))))))))))))));
+  Lc[3] = fma(M[19] * T(-0.16666666666666666), D[44], fma(M[18] * T(-0.5), D[43], fma(M[17] * T(-0.5), D[42], fma(M[16] * T(-0.16666666666666666), D[41], fma(M[15] * T(-0.5), D[40], fma(-M[14], D[39], fma(M[13] * T(-0.5), D[38], fma(M[12] * T(-0.5), D[37], fma(M[11] * T(-0.5), D[36], fma(M[10] * T(-0.16666666666666666), D[35], fma(M[9] * T(0.5), D[25], fma(M[8], D[24], fma(M[7] * T(0.5), D[23], fma(M[6], D[22], fma(M[5], D[21], fma(M[4] * T(0.5), D[20], fma(-M[3], D[12], fma(-M[2], D[11], fma(-M[1], D[10], fma(M[0], D[4], Lc[3]))))))))))))))))))));
+  Lc[4] = fma(M[19] * T(-0.16666666666666666), D[48], fma(M[18] * T(-0.5), D[47], fma(M[17] * T(-0.5), D[46], fma(M[16] * T(-0.16666666666666666), D[45], fma(M[15] * T(-0.5), D[43], fma(-M[14], D[42], fma(M[13] * T(-0.5), D[41], fma(M[12] * T(-0.5), D[39], fma(M[11] * T(-0.5), D[38], fma(M[10] * T(-0.16666666666666666), D[36], fma(M[9] * T(0.5), D[28], fma(M[8], D[27], fma(M[7] * T(0.5), D[26], fma(M[6], D[24], fma(M[5], D[23], fma(M[4] * T(0.5), D[21], fma(-M[3], D[14], fma(-M[2], D[13], fma(-M[1], D[11], fma(M[0], D[5], Lc[4]))))))))))))))))))));
+  Lc[5] = fma(M[19] * T(-0.16666666666666666), D[49], fma(M[18] * T(-0.5), D[48], fma(M[17] * T(-0.5), D[47], fma(M[16] * T(-0.16666666666666666), D[46], fma(M[15] * T(-0.5), D[44], fma(-M[14], D[43], fma(M[13] * T(-0.5), D[42], fma(M[12] * T(-0.5), D[40], fma(M[11] * T(-0.5), D[39], fma(M[10] * T(-0.16666666666666666), D[37], fma(M[9] * T(0.5), D[29], fma(M[8], D[28], fma(M[7] * T(0.5), D[27], fma(M[6], D[25], fma(M[5], D[24], fma(M[4] * T(0.5), D[22], fma(-M[3], D[15], fma(-M[2], D[14], fma(-M[1], D[12], fma(M[0], D[6], Lc[5]))))))))))))))))))));
+  Lc[6] = fma(M[19] * T(-0.16666666666666666), D[53], fma(M[18] * T(-0.5), D[52], fma(M[17] * T(-0.5), D[51], fma(M[16] * T(-0.16666666666666666), D[50], fma(M[15] * T(-0.5), D[47], fma(-M[14], D[46], fma(M[13] * T(-0.5), D[45], fma(M[12] * T(-0.5), D[42], fma(M[11] * T(-0.5), D[41], fma(M[10] * T(-0.16666666666666666), D[38], fma(M[9] * T(0.5), D[32], fma(M[8], D[31], fma(M[7] * T(0.5), D[30], fma(M[6], D[27], fma(M[5], D[26], fma(M[4] * T(0.5), D[23], fma(-M[3], D[17], fma(-M[2], D[16], fma(-M[1], D[13], fma(M[0], D[7], Lc[6]))))))))))))))))))));
+  Lc[7] = fma(M[19] * T(-0.16666666666666666), D[54], fma(M[18] * T(-0.5), D[53], fma(M[17] * T(-0.5), D[52], fma(M[16] * T(-0.16666666666666666), D[51], fma(M[15] * T(-0.5), D[48], fma(-M[14], D[47], fma(M[13] * T(-0.5), D[46], fma(M[12] * T(-0.5), D[43], fma(M[11] * T(-0.5), D[42], fma(M[10] * T(-0.16666666666666666), D[39], fma(M[9] * T(0.5), D[33], fma(M[8], D[32], fma(M[7] * T(0.5), D[31], fma(M[6], D[28], fma(M[5], D[27], fma(M[4] * T(0.5), D[24], fma(-M[3], D[18], fma(-M[2], D[17], fma(-M[1], D[14], fma(M[0], D[8], Lc[7]))))))))))))))))))));
+  Lc[8] = fma(M[19] * T(-0.16666666666666666), D[55], fma(M[18] * T(-0.5), D[54], fma(M[17] * T(-0.5), D[53], fma(M[16] * T(-0.16666666666666666), D[52], fma(M[15] * T(-0.5), D[49], fma(-M[14], D[48], fma(M[13] * T(-0.5), D[47], fma(M[12] * T(-0.5), D[44], fma(M[11] * T(-0.5), D[43], fma(M[10] * T(-0.16666666666666666), D[40], fma(M[9] * T(0.5), D[34], fma(M[8], D[33], fma(M[7] * T(0.5), D[32], fma(M[6], D[29], fma(M[5], D[28], fma(M[4] * T(0.5), D[25], fma(-M[3], D[19], fma(-M[2], D[18], fma(-M[1], D[15], fma(M[0], D[9], Lc[8]))))))))))))))))))));
+  Lc[9] = fma(M[9] * T(0.5), D[40], fma(M[8], D[39], fma(M[7] * T(0.5), D[38], fma(M[6], D[37], fma(M[5], D[36], fma(M[4] * T(0.5), D[35], fma(-M[3], D[22], fma(-M[2], D[21], fma(-M[1], D[20], fma(M[0], D[10], Lc[9]))))))))));
+  Lc[10] = fma(M[9] * T(0.5), D[43], fma(M[8], D[42], fma(M[7] * T(0.5), D[41], fma(M[6], D[39], fma(M[5], D[38], fma(M[4] * T(0.5), D[36], fma(-M[3], D[24], fma(-M[2], D[23], fma(-M[1], D[21], fma(M[0], D[11], Lc[10]))))))))));
+  Lc[11] = fma(M[9] * T(0.5), D[44], fma(M[8], D[43], fma(M[7] * T(0.5), D[42], fma(M[6], D[40], fma(M[5], D[39], fma(M[4] * T(0.5), D[37], fma(-M[3], D[25], fma(-M[2], D[24], fma(-M[1], D[22], fma(M[0], D[12], Lc[11]))))))))));
+  Lc[12] = fma(M[9] * T(0.5), D[47], fma(M[8], D[46], fma(M[7] * T(0.5), D[45], fma(M[6], D[42], fma(M[5], D[41], fma(M[4] * T(0.5), D[38], fma(-M[3], D[27], fma(-M[2], D[26], fma(-M[1], D[23], fma(M[0], D[13], Lc[12]))))))))));
+  Lc[13] = fma(M[9] * T(0.5), D[48], fma(M[8], D[47], fma(M[7] * T(0.5), D[46], fma(M[6], D[43], fma(M[5], D[42], fma(M[4] * T(0.5), D[39], fma(-M[3], D[28], fma(-M[2], D[27], fma(-M[1], D[24], fma(M[0], D[14], Lc[13]))))))))));
+  Lc[14] = fma(M[9] * T(0.5), D[49], fma(M[8], D[48], fma(M[7] * T(0.5), D[47], fma(M[6], D[44], fma(M[5], D[43], fma(M[4] * T(0.5), D[40], fma(-M[3], D[29], fma(-M[2], D[28], fma(-M[1], D[25], fma(M[0], D[15], Lc[14]))))))))));
+  Lc[15] = fma(M[9] * T(0.5), D[52], fma(M[8], D[51], fma(M[7] * T(0.5), D[50], fma(M[6], D[46], fma(M[5], D[45], fma(M[4] * T(0.5), D[41], fma(-M[3], D[31], fma(-M[2], D[30], fma(-M[1], D[26], fma(M[0], D[16], Lc[15]))))))))));
+  Lc[16] = fma(M[9] * T(0.5), D[53], fma(M[8], D[52], fma(M[7] * T(0.5), D[51], fma(M[6], D[47], fma(M[5], D[46], fma(M[4] * T(0.5), D[42], fma(-M[3], D[32], fma(-M[2], D[31], fma(-M[1], D[27], fma(M[0], D[17], Lc[16]))))))))));
+  Lc[17] = fma(M[9] * T(0.5), D[54], fma(M[8], D[53], fma(M[7] * T(0.5), D[52], fma(M[6], D[48], fma(M[5], D[47], fma(M[4] * T(0.5), D[43], fma(-M[3], D[33], fma(-M[2], D[32], fma(-M[1], D[28], fma(M[0], D[18], Lc[17]))))))))));
+  Lc[18] = fma(M[9] * T(0.5), D[55], fma(M[8], D[54], fma(M[7] * T(0.5), D[53], fma(M[6], D[49], fma(M[5], D[48], fma(M[4] * T(0.5), D[44], fma(-M[3], D[34], fma(-M[2], D[33], fma(-M[1], D[29], fma(M[0], D[19], Lc[18]))))))))));
+  Lc[19] = fma(-M[3], D[37], fma(-M[2], D[36], fma(-M[1], D[35], fma(M[0], D[20], Lc[19]))));
+  Lc[20] = fma(-M[3], D[39], fma(-M[2], D[38], fma(-M[1], D[36], fma(M[0], D[21], Lc[20]))));
+  Lc[21] = fma(-M[3], D[40], fma(-M[2], D[39], fma(-M[1], D[37], fma(M[0], D[22], Lc[21]))));
+  Lc[22] = fma(-M[3], D[42], fma(-M[2], D[41], fma(-M[1], D[38], fma(M[0], D[23], Lc[22]))));
+  Lc[23] = fma(-M[3], D[43], fma(-M[2], D[42], fma(-M[1], D[39], fma(M[0], D[24], Lc[23]))));
+  Lc[24] = fma(-M[3], D[44], fma(-M[2], D[43], fma(-M[1], D[40], fma(M[0], D[25], Lc[24]))));
+  Lc[25] = fma(-M[3], D[46], fma(-M[2], D[45], fma(-M[1], D[41], fma(M[0], D[26], Lc[25]))));
+  Lc[26] = fma(-M[3], D[47], fma(-M[2], D[46], fma(-M[1], D[42], fma(M[0], D[27], Lc[26]))));
+  Lc[27] = fma(-M[3], D[48], fma(-M[2], D[47], fma(-M[1], D[43], fma(M[0], D[28], Lc[27]))));
+  Lc[28] = fma(-M[3], D[49], fma(-M[2], D[48], fma(-M[1], D[44], fma(M[0], D[29], Lc[28]))));
+  Lc[29] = fma(-M[3], D[51], fma(-M[2], D[50], fma(-M[1], D[45], fma(M[0], D[30], Lc[29]))));
+  Lc[30] = fma(-M[3], D[52], fma(-M[2], D[51], fma(-M[1], D[46], fma(M[0], D[31], Lc[30]))));
+  Lc[31] = fma(-M[3], D[53], fma(-M[2], D[52], fma(-M[1], D[47], fma(M[0], D[32], Lc[31]))));
+  Lc[32] = fma(-M[3], D[54], fma(-M[2], D[53], fma(-M[1], D[48], fma(M[0], D[33], Lc[32]))));
+  Lc[33] = fma(-M[3], D[55], fma(-M[2], D[54], fma(-M[1], D[49], fma(M[0], D[34], Lc[33]))));
+  Lc[34] = fma(M[0], D[35], Lc[34]);
+  Lc[35] = fma(M[0], D[36], Lc[35]);
+  Lc[36] = fma(M[0], D[37], Lc[36]);
+  Lc[37] = fma(M[0], D[38], Lc[37]);
+  Lc[38] = fma(M[0], D[39], Lc[38]);
+  Lc[39] = fma(M[0], D[40], Lc[39]);
+  Lc[40] = fma(M[0], D[41], Lc[40]);
+  Lc[41] = fma(M[0], D[42], Lc[41]);
+  Lc[42] = fma(M[0], D[43], Lc[42]);
+  Lc[43] = fma(M[0], D[44], Lc[43]);
+  Lc[44] = fma(M[0], D[45], Lc[44]);
+  Lc[45] = fma(M[0], D[46], Lc[45]);
+  Lc[46] = fma(M[0], D[47], Lc[46]);
+  Lc[47] = fma(M[0], D[48], Lc[47]);
+  Lc[48] = fma(M[0], D[49], Lc[48]);
+  Lc[49] = fma(M[0], D[50], Lc[49]);
+  Lc[50] = fma(M[0], D[51], Lc[50]);
+  Lc[51] = fma(M[0], D[52], Lc[51]);
+  Lc[52] = fma(M[0], D[53], Lc[52]);
+  Lc[53] = fma(M[0], D[54], Lc[53]);
+  Lc[54] = fma(M[0], D[55], Lc[54]);
+}
+template <typename T>
+__device__ __forceinline__ void l2p_pe4(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {
+  // a_k -= sum_{|n|<=4} d^n/n! L_{n+e_k}
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  ax = fma(-q34, Lc[48], fma(-q33, Lc[47], fma(-q32, Lc[46], fma(-q31, Lc[45], fma(-q30, Lc[44], fma(-q29, Lc[43], fma(-q28, Lc[42], fma(-q27, Lc[41], fma(-q26, Lc[40], fma(-q25, Lc[39], fma(-q24, Lc[38], fma(-q23, Lc[37], fma(-q22, Lc[36], fma(-q21, Lc[35], fma(-q20, Lc[34], fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax)))))))))))))))))))))))))))))))))));
+  ay = fma(-q34, Lc[53], fma(-q33, Lc[52], fma(-q32, Lc[51], fma(-q31, Lc[50], fma(-q30, Lc[49], fma(-q29, Lc[47], fma(-q28, Lc[46], fma(-q27, Lc[45], fma(-q26, Lc[44], fma(-q25, Lc[42], fma(-q24, Lc[41], fma(-q23, Lc[40], fma(-q22, Lc[38], fma(-q21, Lc[37], fma(-q20, Lc[35], fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay)))))))))))))))))))))))))))))))))));
+  az = fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az)))))))))))))))))))))))))))))))))));
+}
+
+constexpr int kNL5 = 83;  // local coefficients, image-field order 5
+template <typename T>
+__device__ __forceinline__ void m2l_pe5(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {
+  // Lc[t-1] accumulates L_m for multi-index t >= 1 (orders 1..6)
+  Lc[0] = fma(M[55] * T(-0.0083333333333333332), D[76], fma(M[54] * T(-0.041666666666666664), D[75], fma(M[53] * T(-0.083333333333333329), D[74], fma(M[52] * T(-0.083333333333333329), D[73], fma(M[51] * T(-0.041666666666666664), D[72], fma(M[50] * T(-0.0083333333333333332), D[71], fma(M[49] * T(-0.041666666666666664), D[70], fma(M[48] * T(-0.16666666666666666), D[69], fma(M[47] * T(-0.25), D[68], fma(M[46] * T(-0.16666666666666666), D[67], fma(M[45] * T(-0.041666666666666664), D[66], fma(M[44] * T(-0.083333333333333329), D[65], fma(M[43] * T(-0.25), D[64], fma(M[42] * T(-0.25), D[63], fma(M[41] * T(-0.083333333333333329), D[62], fma(M[40] * T(-0.083333333333333329), D[61], fma(M[39] * T(-0.16666666666666666), D[60], fma(M[38] * T(-0.083333333333333329), D[59], fma(M[37] * T(-0.041666666666666664), D[58], fma(M[36] * T(-0.041666666666666664), D[57], fma(M[35] * T(-0.0083333333333333332), D[56], fma(M[34] * T(0.041666666666666664), D[49], fma(M[33] * T(0.16666666666666666), D[48], fma(M[32] * T(0.25), D[47], fma(M[31] * T(0.16666666666666666), D[46], fma(M[30] * T(0.041666666666666664), D[45], fma(M[29] * T(0.16666666666666666), D[44], fma(M[28] * T(0.5), D[43], fma(M[27] * T(0.5), D[42], fma(M[26] * T(0.16666666666666666), D[41], fma(M[25] * T(0.25), D[40], fma(M[24] * T(0.5), D[39], fma(M[23] * T(0.25), D[38], fma(M[22] * T(0.16666666666666666), D[37], fma(M[21] * T(0.16666666666666666), D[36], fma(M[20] * T(0.041666666666666664), D[35], fma(M[19] * T(-0.16666666666666666), D[29], fma(M[18] * T(-0.5), D[28], fma(M[17] * T(-0.5), D[27], fma(M[16] * T(-0.16666666666666666), D[26], fma(M[15] * T(-0.5), D[25], fma(-M[14], D[24], fma(M[13] * T(-0.5), D[23], fma(M[12] * T(-0.5), D[22], fma(M[11] * T(-0.5), D[21], fma(M[10] * T(-0.16666666666666666), D[20], fma(M[9] * T(0.5), D[15], fma(M[8], D[14], fma(M[7] * T(0.5), D[13], fma(M[6], D[12], fma(M[5], D[11], fma(M[4] * T(0.5), D[10], fma(-M[3], D[6], fma(-M[2], D[5], fma(-M[1], D[4], fma(M[0], D[1], Lc[0]))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  Lc[1] = fma(M[55] * T(-0.0083333333333333332), D[82], fma(M[54] * T(-0.041666666666666664), D[81], fma(M[53] * T(-0.083333333333333329), D[80], fma(M[52] * T(-0.083333333333333329), D[79], fma(M[51] * T(-0.041666666666666664), D[78], fma(M[50] * T(-0.0083333333333333332), D[77], fma(M[49] * T(-0.041666666666666664), D[75], fma(M[48] * T(-0.16666666666666666), D[74], fma(M[47] * T(-0.25), D[73], fma(M[46] * T(-0.16666666666666666), D[72], fma(M[45] * T(-0.041666666666666664), D[71], fma(M[44] * T(-0.083333333333333329), D[69], fma(M[43] * T(-0.25), D[68], fma(M[42] * T(-0.25), D[67], fma(M[41] * T(-0.083333333333333329), D[66], fma(M[40] * T(-0.083333333333333329), D[64], fma(M[39] * T(-0.16666666666666666), D[63], fma(M[38] * T(-0.083333333333333329), D[62], fma(M[37] * T(-0.041666666666666664), D[60], fma(M[36] * T(-0.041666666666666664), D[59], fma(M[35] * T(-0.0083333333333333332), D[57], fma(M[34] * T(0.041666666666666664), D[54], fma(M[33] * T(0.16666666666666666), D[53], fma(M[32] * T(0.25), D[52], fma(M[31] * T(0.16666666666666666), D[51], fma(M[30] * T(0.041666666666666664), D[50], fma(M[29] * T(0.16666666666666666), D[48], fma(M[28] * T(0.5), D[47], fma(M[27] * T(0.5), D[46], fma(M[26] * T(0.16666666666666666), D[45], fma(M[25] * T(0.25), D[43], fma(M[24] * T(0.5), D[42], fma(M[23] * T(0.25), D[41], fma(M[22] * T(0.16666666666666666), D[39], fma(M[21] * T(0.16666666666666666), D[38], fma(M[20] * T(0.041666666666666664), D[36], fma(M[19] * T(-0.16666666666666666), D[33], fma(M[18] * T(-0.5), D[32], fma(M[17] * T(-0.5), D[31], fma(M[16] * T(-0.16666666666666666), D[30], fma(M[15] * T(-0.5), D[28], fma(-M[14], D[27], fma(M[13] * T(-0.5), D[26], fma(M[12] * T(-0.5), D[24], fma(M[11] * T(-0.5), D[23], fma(M[10] * T(-0.16666666666666666), D[21], fma(M[9] * T(0.5), D[18], fma(M[8], D[17], fma(M[7] * T(0.5), D[16], fma(M[6], D[14], fma(M[5], D[13], fma(M[4] * T(0.5), D[11], fma(-M[3], D[8], fma(-M[2], D[7], fma(-M[1], D[5], fma(M[0], D[2], Lc[1]))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  Lc[2] = fma(M[55] * T(-0.0083333333333333332), D[83], fma(M[54] * T(-0.041666666666666664), D[82], fma(M[53] * T(-0.083333333333333329), D[81], fma(M[52] * T(-0.083333333333333329), D[80], fma(M[51] * T(-0.041666666666666664), D[79], fma(M[50] * T(-0.0083333333333333332), D[78], fma(M[49] * T(-0.041666666666666664), D[76], fma(M[48] * T(-0.16666666666666666), D[75], fma(M[47] * T(-0.25), D[74], fma(M[46] * T(-0.16666666666666666), D[73], fma(M[45] * T(-0.041666666666666664), D[72], fma(M[44] * T(-0.083333333333333329), D[70], fma(M[43] * T(-0.25), D[69], fma(M[42] * T(-0.25), D[68], fma(M[41] * T(-0.083333333333333329), D[67], fma(M[40] * T(-0.083333333333333329), D[65], fma(M[39] * T(-0.16666666666666666), D[64], fma(M[38] * T(-0.083333333333333329), D[63], fma(M[37] * T(-0.041666666666666664), D[61], fma(M[36] * T(-0.041666666666666664), D[60], fma(M[35] * T(-0.0083333333333333332), D[58], fma(M[34] * T(0.041666666666666664), D[55], fma(M[33] * T(0.16666666666666666), D[54], fma(M[32] * T(0.25), D[53], fma(M[31] * T(0.16666666666666666), D[52], fma(M[30] * T(0.041666666666666664), D[51], fma(M[29] * T(0.16666666666666666), D[49], fma(M[28] * T(0.5), D[48], fma(M[27] * T(0.5), D[47], fma(M[26] * T(0.16666666666666666), D[46], fma(M[25] * T(0.25), D[44], fma(M[24] * T(0.5), D[43], fma(M[23] * T(0.25), D[42], fma(M[22] * T(0.16666666666666666), D[40], fma(M[21] * T(0.16666666666666666), D[39], fma(M[20] * T(0.041666666666666664), D[37], fma(M[19] * T(-0.16666666666666666), D[34], fma(M[18] * T(-0.5), D[33], fma(M[17] * T(-0.5), D[32], fma(M[16] * T(-0.16666666666666666), D[31], fma(M[15] * T(-0.5), D[29], fma(-M[14], D[28], fma(M[13] * T(-0.5), D[27], fma(M[12] * T(-0.5), D[25], fma(M[11] * T(-0.5), D[24], fma(M[10] * T(-0.16666666666666666), D[22], fma(M[9] * T(0.5), D[19], fma(M[8], D[18], fma(M[7] * T(0.5), D[17], fma(M[6], D[15], fma(M[5], D[14], fma(M[4] * T(0.5), D[12], fma(-M[3], D[9], fma(-M[2], D[8], fma(-M[1], D[6], fma(M[0], D[3], Lc[2]))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  Lc[3] = fma(M[34] * T(0.041666666666666664), D[70], fma(M[33] * T(0.16666666666666666), D[69], fma(M[32] * T(0.25), D[68], fma(M[31] * T(0.16666666666666666), D[67], fma(M[30] * T(0.041666666666666664), D[66], fma(M[29] * T(0.16666666666666666), D[65], fma(M[28] * T(0.5), D[64], fma(M[27] * T(0.5), D[63], fma(M[26] * T(0.16666666666666666), D[62], fma(M[25] * T(0.25), D[61], fma(M[24] * T(0.5), D[60], fma(M[23] * T(0.25), D[59], fma(M[22] * T(0.16666666666666666), D[58], fma(M[21] * T(0.16666666666666666), D[57], fma(M[20] * T(0.041666666666666664), D[56], fma(M[19] * T(-0.16666666666666666), D[44], fma(M[18] * T(-0.5), D[43], fma(M[17] * T(-0.5), D[42], fma(M[16] * T(-0.16666666666666666), D[41], fma(M[15] * T(-0.5), D[40], fma(-M[14], D[39], fma(M[13] * T(-0.5), D[38], fma(M[12] * T(-0.5), D[37], fma(M[11] * T(-0.5), D[36], fma(M[10] * T(-0.16666666666666666), D[35], fma(M[9] * T(0.5), D[25], fma(M[8], D[24], fma(M[7] * T(0.5), D[23], fma(M[6], D[22], fma(M[5], D[21], fma(M[4] * T(0.5), D[20], fma(-M[3], D[12], fma(-M[2], D[11], fma(-M[1], D[10], fma(M[0], D[4], Lc[3])))))))))))))))))))))))))))))))))));
+  Lc[4] = fma(M[34] * T(0.041666666666666664), D[75], fma(M[33] * T(0.16666666666666666), D[74], fma(M[32] * T(0.25), D[73], fma(M[31] * T(0.16666666666666666), D[72], fma(M[30] * T(0.041666666666666664), D[71], fma(M[29] * T(0.16666666666666666), D[69], fma(M[28] * T(0.5), D[68], fma(M[27] * T(0.5), D[67], fma(M[26] * T(0.16666666666666666), D[66], fma(M[25] * T(0.25), D[64], fma(M[24] * T(0.5), D[63], fma(M[23] * T(0.25), D[62], fma(M[22] * T(0.16666666666666666), D[60], fma(M[21] * T(0.16666666666666666), D[59], fma(M[20] * T(0.041666666666666664), D[57], fma(M[19] * T(-0.16666666666666666), D[48], fma(M[18] * T(-0.5), D[47], fma(M[17] * T(-0.5), D[46], fma(M[16] * T(-0.16666666666666666), D[45], fma(M[15] * T(-0.5), D[43], fma(-M[14], D[42], fma(M[13] * T(-0.5), D[41], fma(M[12] * T(-0.5), D[39], fma(M[11] * T(-0.5), D[38], fma(M[10] * T(-0.16666666666666666), D[36], fma(M[9] * T(0.5), D[28], fma(M[8], D[27], fma(M[7] * T(0.5), D[26], fma(M[6], D[24], fma(M[5], D[23], fma(M[4] * T(0.5), D[21], fma(-M[3], D[14], fma(-M[2], D[13], fma(-M[1], D[11], fma(M[0], D[5], Lc[4])))))))))))))))))))))))))))))))))));
+  Lc[5] = fma(M[34] * T(0.041666666666666664), D[76], fma(M[33] * T(0.16666666666666666), D[75], fma(M[32] * T(0.25), D[74], fma(M[31] * T(0.16666666666666666), D[73], fma(M[30] * T(0.041666666666666664), D[72], fma(M[29] * T(0.16666666666666666), D[70], fma(M[28] * T(0.5), D[69], fma(M[27] * T(0.5), D[68], fma(M[26] * T(0.16666666666666666), D[67], fma(M[25] * T(0.25), D[65], fma(M[24] * T(0.5), D[64], fma(M[23] * T(0.25), D[63], fma(M[22] * T(0.16666666666666666), D[61], fma(M[21] * T(0.16666666666666666), D[60], fma(M[20] * T(0.041666666666666664), D[58], fma(M[19] * T(-0.16666666666666666), D[49], fma(M[18] * T(-0.5), D[48], fma(M[17] * T(-0.5), D[47], fma(M[16] * T(-0.16666666666666666), D[46], fma(M[15] * T(-0.5), D[44], fma(-M[14], D[43], fma(M[13] * T(-0.5), D[42], fma(M[12] * T(-0.5), D[40], fma(M[11] * T(-0.5), D[39], fma(M[10] * T(-0.16666666666666666), D[37], fma(M[9] * T(0.5), D[29], fma(M[8], D[28], fma(M[7] * T(0.5), D[27], fma(M[6], D[25], fma(M[5], D[24], fma(M[4] * T(0.5), D[22], fma(-M[3], D[15], fma(-M[2], D[14], fma(-M[1], D[12], fma(M[0], D[6], Lc[5])))))))))))))))))))))))))))))))))));
+  Lc[6] = fma(M[34] * T(0.041666666666666664), D[81], fma(M[33] * T(0.16666666666666666), D[80], fma(M[32] * T(0.25), D[79], fma(M[31] * T(0.16666666666666666), D[78], fma(M[30] * T(0.041666666666666664), D[77], fma(M[29] * T(0.16666666666666666), D[74], fma(M[28] * T(0.5), D[73], fma(M[27] * T(0.5), D[72], fma(M[26] * T(0.16666666666666666), D[71], fma(M[25] * T(0.25), D[68], fma(M[24] * T(0.5), D[67], fma(M[23] * T(0.25), D[66], fma(M[22] * T(0.16666666666666666), D[63], fma(M[21] * T(0.16666666666666666), D[62], fma(M[20] * T(0.041666666666666664), D[59], fma(M[19] * T(-0.16666666666666666), D[53], fma(M[18] * T(-0.5), D[52], fma(M[17] * T(-0.5), D[51], fma(M[16] * T(-0.16666666666666666), D[50], fma(M[15] * T(-0.5), D[47], fma(-M[14], D[46], fma(M[13] * T(-0.5), D[45], fma(M[12] * T(-0.5), D[42], fma(M[11] * T(-0.5), D[41], fma(M[10] * T(-0.16666666666666666), D[38], fma(M[9] * T(0.5), D[32], fma(M[8], D[31], fma(M[7] * T(0.5), D[30], fma(M[6], D[27], fma(M[5], D[26], fma(M[4] * T(0.5), D[23], fma(-M[3], D[17], fma(-M[2], D[16], fma(-M[1], D[13], fma(M[0], D[7], Lc[6])))))))))))))))))))))))))))))))))));
+  Lc[7] = fma(M[34] * T(0.041666666666666664), D[82], fma(M[33] * T(0.16666666666666666), D[81], fma(M[32] * T(0.25), D[80], fma(M[31] * T(0.16666666666666666), D[79], fma(M[30] * T(0.041666666666666664), D[78], fma(M[29] * T(0.16666666666666666), D[75], fma(M[28] * T(0.5), D[74], fma(M[27] * T(0.5), D[73], fma(M[26] * T(0.16666666666666666), D[72], fma(M[25] * T(0.25), D[69], fma(M[24] * T(0.5), D[68], fma(M[23] * T(0.25), D[67], fma(M[22] * T(0.16666666666666666), D[64], fma(M[21] * T(0.16666666666666666), D[63], fma(M[20] * T(0.041666666666666664), D[60], fma(M[19] * T(-0.16666666666666666), D[54], fma(M[18] * T(-0.5), D[53], fma(M[17] * T(-0.5), D[52], fma(M[16] * T(-0.16666666666666666), D[51], fma(M[15] * T(-0.5), D[48], fma(-M[14], D[47], fma(M[13] * T(-0.5), D[46], fma(M[12] * T(-0.5), D[43], fma(M[11] * T(-0.5), D[42], fma(M[10] * T(-0.16666666666666666), D[39], fma(M[9] * T(0.5), D[33], fma(M[8], D[32], fma(M[7] * T(0.5), D[31], fma(M[6], D[28], fma(M[5], D[27], fma(M[4] * T(0.5), D[24], fma(-M[3], D[18], fma(-M[2], D[17], fma(-M[1], D[14], fma(M[0], D[8], Lc[7])))))))))))))))))))))))))))))))))));
+  Lc[8] = fma(M[34] * T(0.041666666666666664), D[83], fma(M[33] * T(0.16666666666666666), D[82], fma(M[32] * T(0.25), D[81], fma(M[31] * T(0.16666666666666666), D[80], fma(M[30] * T(0.041666666666666664), D[79], fma(M[29] * T(0.16666666666666666), D[76], fma(M[28] * T(0.5), D[75], fma(M[27] * T(0.5), D[74], fma(M[26] * T(0.16666666666666666), D[73], fma(M[25] * T(0.25), D[70], fma(M[24] * T(0.5), D[69], fma(M[23] * T(0.25), D[68], fma(M[22] * T(0.16666666666666666), D[65], fma(M[21] * T(0.16666666666666666), D[64], fma(M[20] * T(0.041666666666666664), D[61], fma(M[19] * T(-0.16666666666666666), D[55], fma(M[18] * T(-0.5), D[54], fma(M[17] * T(-0.5), D[53], fma(M[16] * T(-0.16666666666666666), D[52], fma(M[15] * T(-0.5), D[49], fma(-M[14], D[48], fma(M[13] * T(-0.5), D[47], fma(M[12] * T(-0.5), D[44], fma(M[11] * T(-0.5), D[43], fma(M[10] * T(-0.16666666666666666), D[40], fma(M[9] * T(0.5), D[34], fma(M[8], D[33], fma(M[7] * T(0.5), D[32], fma(M[6], D[29], fma(M[5], D[28], fma(M[4] * T(0.5), D[25], fma(-M[3], D[19], fma(-M[2], D[18], fma(-M[1], D[15], fma(M[0], D[9], Lc[8])))))))))))))))))))))))))))))))))));
+  Lc[9] = fma(M[19] * T(-0.16666666666666666), D[65], fma(M[18] * T(-0.5), D[64], fma(M[17] * T(-0.5), D[63], fma(M[16] * T(-0.16666666666666666), D[62], fma(M[15] * T(-0.5), D[61], fma(-M[14], D[60], fma(M[13] * T(-0.5), D[59], fma(M[12] * T(-0.5), D[58], fma(M[11] * T(-0.5), D[57], fma(M[10] * T(-0.16666666666666666), D[56], fma(M[9] * T(0.5), D[40], fma(M[8], D[39], fma(M[7] * T(0.5), D[38], fma(M[6], D[37], fma(M[5], D[36], fma(M[4] * T(0.5), D[35], fma(-M[3], D[22], fma(-M[2], D[21], fma(-M[1], D[20], fma(M[0], D[10], Lc[9]))))))))))))))))))));
+  Lc[10] = fma(M[19] * T(-0.16666666666666666), D[69], fma(M[18] * T(-0.5), D[68], fma(M[17] * T(-0.5), D[67], fma(M[16] * T(-0.16666666666666666), D[66], fma(M[15] * T(-0.5), D[64], fma(-M[14], D[63], fma(M[13] * T(-0.5), D[62], fma(M[12] * T(-0.5), D[60], fma(M[11] * T(-0.5), D[59], fma(M[10] * T(-0.16666666666666666), D[57], fma(M[9] * T(0.5), D[43], fma(M[8], D[42], fma(M[7] * T(0.5), D[41], fma(M[6], D[39], fma(M[5], D[38], fma(M[4] * T(0.5), D[36], fma(-M[3], D[24], fma(-M[2], D[23], fma(-M[1], D[21], fma(M[0], D[11], Lc[10]))))))))))))))))))));
+  Lc[11] = fma(M[19] * T(-0.16666666666666666), D[70], fma(M[18] * T(-0.5), D[69], fma(M[17] * T(-0.5), D[68], fma(M[16] * T(-0.16666666666666666), D[67], fma(M[15] * T(-0.5), D[65], fma(-M[14], D[64], fma(M[13] * T(-0.5), D[63], fma(M[12] * T(-0.5), D[61], fma(M[11] * T(-0.5), D[60], fma(M[10] * T(-0.16666666666666666), D[58], fma(M[9] * T(0.5), D[44], fma(M[8], D[43], fma(M[7] * T(0.5), D[42], fma(M[6], D[40], fma(M[5], D[39], fma(M[4] * T(0.5), D[37], fma(-M[3], D[25], fma(-M[2], D[24], fma(-M[1], D[22], fma(M[0], D[12], Lc[11]))))))))))))))))))));
+  Lc[12] = fma(M[19] * T(-0.16666666666666666), D[74], fma(M[18] * T(-0.5), D[73], fma(M[17] * T(-0.5), D[72], fma(M[16] * T(-0.16666666666666666), D[71], fma(M[15] * T(-0.5), D[68], fma(-M[14], D[67], fma(M[13] * T(-0.5), D[66], fma(M[12] * T(-0.5), D[63], fma(M[11] * T(-0.5), D[62], fma(M[10] * T(-0.16666666666666666), D[59], fma(M[9] * T(0.5), D[47], fma(M[8], D[46], fma(M[7] * T(0.5), D[45], fma(M[6], D[42], fma(M[5], D[41], fma(M[4] * T(0.5), D[38], fma(-M[3], D[27], fma(-M[2], D[26], fma(-M[1], D[23], fma(M[0], D[13], Lc[12]))))))))))))))))))));
+  Lc[13] = fma(M[19] * T(-0.16666666666666666), D[75], fma(M[18] * T(-0.5), D[74], fma(M[17] * T(-0.5), D[73], fma(M[16] * T(-0.16666666666666666), D[72], fma(M[15] * T(-0.5), D[69], fma(-M[14], D[68], fma(M[13] * T(-0.5), D[67], fma(M[12] * T(-0.5), D[64], fma(M[11] * T(-0.5), D[63], fma(M[10] * T(-0.16666666666666666), D[60], fma(M[9] * T(0.5), D[48], fma(M[8], D[47], fma(M[7] * T(0.5), D[46], fma(M[6], D[43], fma(M[5], D[42], fma(M[4] * T(0.5), D[39], fma(-M[3], D[28], fma(-M[2], D[27], fma(-M[1], D[24], fma(M[0], D[14], Lc[13]))))))))))))))))))));
+  Lc[14] = fma(M[19] * T(-0.16666666666666666), D[76], fma(M[18] * T(-0.5), D[75], fma(M[17] * T(-0.5), D[74], fma(M[16] * T(-0.16666666666666666), D[73], fma(M[15] * T(-0.5), D[70], fma(-M[14], D[69], fma(M[13] * T(-0.5), D[68], fma(M[12] * T(-0.5), D[65], fma(M[11] * T(-0.5), D[64], fma(M[10] * T(-0.16666666666666666), D[61], fma(M[9] * T(0.5), D[49], fma(M[8], D[48], fma(M[7] * T(0.5), D[47], fma(M[6], D[44], fma(M[5], D[43], fma(M[4] * T(0.5), D[40], fma(-M[3], D[29], fma(-M[2], D[28], fma(-M[1], D[25], fma(M[0], D[15], Lc[14]))))))))))))))))))));
+  Lc[15] = fma(M[19] * T(-0.16666666666666666), D[80], fma(M[18] * T(-0.5), D[79], fma(M[17] * T(-0.5), D[78], fma(M[16] * T(-0.16666666666666666), D[77], fma(M[15] * T(-0.5), D[73], fma(-M[14], D[72], fma(M[13] * T(-0.5), D[71], fma(M[12] * T(-0.5), D[67], fma(M[11] * T(-0.5), D[66], fma(M[10] * T(-0.16666666666666666), D[62], fma(M[9] * T(0.5), D[52], fma(M[8], D[51], fma(M[7] * T(0.5), D[50], fma(M[6], D[46], fma(M[5], D[45], fma(M[4] * T(0.5), D[41], fma(-M[3], D[31], fma(-M[2], D[30], fma(-M[1], D[26], fma(M[0], D[16], Lc[15]))))))))))))))))))));
+  Lc[16] = fma(M[19] * T(-0.16666666666666666), D[81], fma(M[18] * T(-0.5), D[80], fma(M[17] * T(-0.5), D[79], fma(M[16] * T(-0.16666666666666666), D[78], fma(M[15] * T(-0.5), D[74], fma(-M[14], D[73], fma(M[13] * T(-0.5), D[72], fma(M[12] * T(-0.5), D[68], fma(M[11] * T(-0.5), D[67], fma(M[10] * T(-0.16666666666666666), D[63], fma(M[9] * T(0.5), D[53], fma(M[8], D[52], fma(M[7] * T(0.5), D[51], fma(M[6], D[47], fma(M[5], D[46], fma(M[4] * T(0.5), D[42], fma(-M[3], D[32], fma(-M[2], D[31], fma(-M[1], D[27], fma(M[0], D[17], Lc[16]))))))))))))))))))));
+  Lc[17] = fma(M[19] * T(-0.16666666666666666), D[82], fma(M[18] * T(-0.5), D[81], fma(M[17] * T(-0.5), D[80], fma(M[16] * T(-0.16666666666666666), D[79], fma(M[15] * T(-0.5), D[75], fma(-M[14], D[74], fma(M[13] * T(-0.5), D[73], fma(M[12] * T(-0.5), D[69], fma(M[11] * T(-0.5), D[68], fma(M[10] * T(-0.16666666666666666), D[64], fma(M[9] * T(0.5), D[54], fma(M[8], D[53], fma(M[7] * T(0.5), D[52], fma(M[6], D[48], fma(M[5], D[47], fma(M[4] * T(0.5), D[43], fma(-M[3], D[33], fma(-M[2], D[32], fma(-M[1], D[28], fma(M[0], D[18], Lc[17]))))))))))))))))))));
+  Lc[18] = fma(M[19] * T(-0.16666666666666666), D[83], fma(M[18] * T(-0.5), D[82], fma(M[17] * T(-0.5), D[81], fma(M[16] * T(-0.16666666666666666), D[80], fma(M[15] * T(-0.5), D[76], fma(-M[14], D[75], fma(M[13] * T(-0.5), D[74], fma(M[12] * T(-0.5), D[70], fma(M[11] * T(-0.5), D[69], fma(M[10] * T(-0.16666666666666666), D[65], fma(M[9] * T(0.5), D[55], fma(M[8], D[54], fma(M[7] * T(0.5), D[53], fma(M[6], D[49], fma(M[5], D[48], fma(M[4] * T(0.5), D[44], fma(-M[3], D[34], fma(-M[2], D[33], fma(-M[1], D[29], fma(M[0], D[19], Lc[18]))))))))))))))))))));
+  Lc[19] = fma(M[9] * T(0.5), D[61], fma(M[8], D[60], fma(M[7] * T(0.5), D[59], fma(M[6], D[58], fma(M[5], D[57], fma(M[4] * T(0.5), D[56], fma(-M[3], D[37], fma(-M[2], D[36], fma(-M[1], D[35], fma(M[0], D[20], Lc[19]))))))))));
+  Lc[20] = fma(M[9] * T(0.5), D[64], fma(M[8], D[63], fma(M[7] * T(0.5), D[62], fma(M[6], D[60], fma(M[5], D[59], fma(M[4] * T(0.5), D[57], fma(-M[3], D[39], fma(-M[2], D[38], fma(-M[1], D[36], fma(M[0], D[21], Lc[20]))))))))));
+  Lc[21] = fma(M[9] * T(0.5), D[65], fma(M[8], D[64], fma(M[7] * T(0.5), D[63], fma(M[6], D[61], fma(M[5], D[60], fma(M[4] * T(0.5), D[58], fma(-M[3], D[40], fma(-M[2], D[39], fma(-M[1], D[37], fma(M[0], D[22], Lc[21]))))))))));
+  Lc[22] = fma(M[9] * T(0.5), D[68], fma(M[8], D[67], fma(M[7] * T(0.5), D[66], fma(M[6], D[63], fma(M[5], D[62], fma(M[4] * T(0.5), D[59], fma(-M[3], D[42], fma(-M[2], D[41], fma(-M[1], D[38], fma(M[0], D[23], Lc[22]))))))))));
+  Lc[23] = fma(M[9] * T(0.5), D[69], fma(M[8], D[68], fma(M[7] * T(0.5), D[67], fma(M[6], D[64], fma(M[5], D[63], fma(M[4] * T(0.5), D[60], fma(-M[3], D[43], fma(-M[2], D[42], fma(-M[1], D[39], fma(M[0], D[24], Lc[23]))))))))));
+  Lc[24] = fma(M[9] * T(0.5), D[70], fma(M[8], D[69], fma(M[7] * T(0.5), D[68], fma(M[6], D[65], fma(M[5], D[64], fma(M[4] * T(0.5), D[61], fma(-M[3], D[44], fma(-M[2], D[43], fma(-M[1], D[40], fma(M[0], D[25], Lc[24]))))))))));
+  Lc[25] = fma(M[9] * T(0.5), D[73], fma(M[8], D[72], fma(M[7] * T(0.5), D[71], fma(M[6], D[67], fma(M[5], D[66], fma(M[4] * T(0.5), D[62], fma(-M[3], D[46], fma(-M[2], D[45], fma(-M[1], D[41], fma(M[0], D[26], Lc[25]))))))))));
+  Lc[26] = fma(M[9] * T(0.5), D[74], fma(M[8], D[73], fma(M[7] * T(0.5), D[72], fma(M[6], D[68], fma(M[5], D[67], fma(M[4] * T(0.5), D[63], fma(-M[3], D[47], fma(-M[2], D[46], fma(-M[1], D[42], fma(M[0], D[27], Lc[26]))))))))));
+  Lc[27] = fma(M[9] * T(0.5), D[75], fma(M[8], D[74], fma(M[7] * T(0.5), D[73], fma(M[6], D[69], fma(M[5], D[68], fma(M[4] * T(0.5), D[64], fma(-M[3], D[48], fma(-M[2], D[47], fma(-M[1], D[43], fma(M[0], D[28], Lc[27]))))))))));
+  Lc[28] = fma(M[9] * T(0.5), D[76], fma(M[8], D[75], fma(M[7] * T(0.5), D[74], fma(M[6], D[70], fma(M[5], D[69], fma(M[4] * T(0.5), D[65], fma(-M[3], D[49], fma(-M[2], D[48], fma(-M[1], D[44], fma(M[0], D[29], Lc[28]))))))))));
+  Lc[29] = fma(M[9] * T(0.5), D[79], fma(M[8], D[78], fma(M[7] * T(0.5), D[77], fma(M[6], D[72], fma(M[5], D[71], fma(M[4] * T(0.5), D[66], fma(-M[3], D[51], fma(-M[2], D[50], fma(-M[1], D[45], fma(M[0], D[30], Lc[29]))))))))));
+  Lc[30] = fma(M[9] * T(0.5), D[80], fma(M[8], D[79], fma(M[7] * T(0.5), D[78], fma(M[6], D[73], fma(M[5], D[72], fma(M[4] * T(0.5), D[67], fma(-M[3], D[52], fma(-M[2], D[51], fma(-M[1], D[46], fma(M[0], D[31], Lc[30]))))))))));
+  Lc[31] = fma(M[9] * T(0.5), D[81], fma(M[8], D[80], fma(M[7] * T(0.5), D[79], fma(M[6], D[74], fma(M[5], D[73], fma(M[4] * T(0.5), D[68], fma(-M[3], D[53], fma(-M[2], D[52], fma(-M[1], D[47], fma(M[0], D[32], Lc[31]))))))))));
+  Lc[32] = fma(M[9] * T(0.5), D[82], fma(M[8], D[81], fma(M[7] * T(0.5), D[80], fma(M[6], D[75], fma(M[5], D[74], fma(M[4] * T(0.5), D[69], fma(-M[3], D[54], fma(-M[2], D[53], fma(-M[1], D[48], fma(M[0], D[33], Lc[32]))))))))));
+  Lc[33] = fma(M[9] * T(0.5), D[83], fma(M[8], D[82], fma(M[7] * T(0.5), D[81], fma(M[6], D[76], fma(M[5], D[75], fma(M[4] * T(0.5), D[70], fma(-M[3], D[55], fma(-M[2], D[54], fma(-M[1], D[49], fma(M[0], D[34], Lc[33]))))))))));
+  Lc[34] = fma(-M[3], D[58], fma(-M[2], D[57], fma(-M[1], D[56], fma(M[0], D[35], Lc[34]))));
+  Lc[35] = fma(-M[3], D[60], fma(-M[2], D[59], fma(-M[1], D[57], fma(M[0], D[36], Lc[35]))));
+  Lc[36] = fma(-M[3], D[61], fma(-M[2], D[60], fma(-M[1], D[58], fma(M[0], D[37], Lc[36]))));
+  Lc[37] = fma(-M[3], D[63], fma(-M[2], D[62], fma(-M[1], D[59], fma(M[0], D[38], Lc[37]))));
+  Lc[38] = fma(-M[3], D[64], fma(-M[2], D[63], fma(-M[1], D[60], fma(M[0], D[39], Lc[38]))));
+  Lc[39] = fma(-M[3], D[65], fma(-M[2], D[64], fma(-M[1], D[61], fma(M[0], D[40], Lc[39]))));
+  Lc[40] = fma(-M[3], D[67], fma(-M[2], D[66], fma(-M[1], D[62], fma(M[0], D[41], Lc[40]))));
+  Lc[41] = fma(-M[3], D[68], fma(-M[2], D[67], fma(-M[1], D[63], fma(M[0], D[42], Lc[41]))));
+  Lc[42] = fma(-M[3], D[69], fma(-M[2], D[68], fma(-M[1], D[64], fma(M[0], D[43], Lc[42]))));
+  Lc[43] = fma(-M[3], D[70], fma(-M[2], D[69], fma(-M[1], D[65], fma(M[0], D[44], Lc[43]))));
+  Lc[44] = fma(-M[3], D[72], fma(-M[2], D[71], fma(-M[1], D[66], fma(M[0], D[45], Lc[44]))));
+  Lc[45] = fma(-M[3], D[73], fma(-M[2], D[72], fma(-M[1], D[67], fma(M[0], D[46], Lc[45]))));
+  Lc[46] = fma(-M[3], D[74], fma(-M[2], D[73], fma(-M[1], D[68], fma(M[0], D[47], Lc[46]))));
+  Lc[47] = fma(-M[3], D[75], fma(-M[2], D[74], fma(-M[1], D[69], fma(M[0], D[48], Lc[47]))));
+  Lc[48] = fma(-M[3], D[76], fma(-M[2], D[75], fma(-M[1], D[70], fma(M[0], D[49], Lc[48]))));
+  Lc[49] = fma(-M[3], D[78], fma(-M[2], D[77], fma(-M[1], D[71], fma(M[0], D[50], Lc[49]))));
+  Lc[50] = fma(-M[3], D[79], fma(-M[2], D[78], fma(-M[1], D[72], fma(M[0], D[51], Lc[50]))));
+  Lc[51] = fma(-M[3], D[80], fma(-M[2], D[79], fma(-M[1], D[73], fma(M[0], D[52], Lc[51]))));
+  Lc[52] = fma(-M[3], D[81], fma(-M[2], D[80], fma(-M[1], D[74], fma(M[0], D[53], Lc[52]))));
+  Lc[53] = fma(-M[3], D[82], fma(-M[2], D[81], fma(-M[1], D[75], fma(M[0], D[54], Lc[53]))));
+  Lc[54] = fma(-M[3], D[83], fma(-M[2], D[82], fma(-M[1], D[76], fma(M[0], D[55], Lc[54]))));
+  Lc[55] = fma(M[0], D[56], Lc[55]);
+  Lc[56] = fma(M[0], D[57], Lc[56]);
+  Lc[57] = fma(M[0], D[58], Lc[57]);
+  Lc[58] = fma(M[0], D[59], Lc[58]);
+  Lc[59] = fma(M[0], D[60], Lc[59]);
+  Lc[60] = fma(M[0], D[61], Lc[60]);
+  Lc[61] = fma(M[0], D[62], Lc[61]);
+  Lc[62] = fma(M[0], D[63], Lc[62]);
+  Lc[63] = fma(M[0], D[64], Lc[63]);
+  Lc[64] = fma(M[0], D[65], Lc[64]);
+  Lc[65] = fma(M[0], D[66], Lc[65]);
+  Lc[66] = fma(M[0], D[67], Lc[66]);
+  Lc[67] = fma(M[0], D[68], Lc[67]);
+  Lc[68] = fma(M[0], D[69], Lc[68]);
+  Lc[69] = fma(M[0], D[70], Lc[69]);
+  Lc[70] = fma(M[0], D[71], Lc[70]);
+  Lc[71] = fma(M[0], D[72], Lc[71]);
+  Lc[72] = fma(M[0], D[73], Lc[72]);
+  Lc[73] = fma(M[0], D[74], Lc[73]);
+  Lc[74] = fma(M[0], D[75], Lc[74]);
+  Lc[75] = fma(M[0], D[76], Lc[75]);
+  Lc[76] = fma(M[0], D[77], Lc[76]);
+  Lc[77] = fma(M[0], D[78], Lc[77]);
+  Lc[78] = fma(M[0], D[79], Lc[78]);
+  Lc[79] = fma(M[0], D[80], Lc[79]);
+  Lc[80] = fma(M[0], D[81], Lc[80]);
+  Lc[81] = fma(M[0], D[82], Lc[81]);
+  Lc[82] = fma(M[0], D[83], Lc[82]);
+}
+template <typename T>
+__device__ __forceinline__ void l2p_pe5(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {
+  // a_k -= sum_{|n|<=5} d^n/n! L_{n+e_k}
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  const T q35 = q20 * (dx * T(0.20000000000000001));
+  const T q36 = q21 * (dx * T(0.25));
+  const T q37 = q22 * (dx * T(0.25));
+  const T q38 = q23 * (dx * T(0.33333333333333331));
+  const T q39 = q24 * (dx * T(0.33333333333333331));
+  const T q40 = q25 * (dx * T(0.33333333333333331));
+  const T q41 = q26 * (dx * T(0.5));
+  const T q42 = q27 * (dx * T(0.5));
+  const T q43 = q28 * (dx * T(0.5));
+  const T q44 = q29 * (dx * T(0.5));
+  const T q45 = q30 * (dx * T(1));
+  const T q46 = q31 * (dx * T(1));
+  const T q47 = q32 * (dx * T(1));
+  const T q48 = q33 * (dx * T(1));
+  const T q49 = q34 * (dx * T(1));
+  const T q50 = q30 * (dy * T(0.20000000000000001));
+  const T q51 = q31 * (dy * T(0.25));
+  const T q52 = q32 * (dy * T(0.33333333333333331));
+  const T q53 = q33 * (dy * T(0.5));
+  const T q54 = q34 * (dy * T(1));
+  const T q55 = q34 * (dz * T(0.20000000000000001));
+  ax = fma(-q55, Lc[75], fma(-q54, Lc[74], fma(-q53, Lc[73], fma(-q52, Lc[72], fma(-q51, Lc[71], fma(-q50, Lc[70], fma(-q49, Lc[69], fma(-q48, Lc[68], fma(-q47, Lc[67], fma(-q46, Lc[66], fma(-q45, Lc[65], fma(-q44, Lc[64], fma(-q43, Lc[63], fma(-q42, Lc[62], fma(-q41, Lc[61], fma(-q40, Lc[60], fma(-q39, Lc[59], fma(-q38, Lc[58], fma(-q37, Lc[57], fma(-q36, Lc[56], fma(-q35, Lc[55], fma(-q34, Lc[48], fma(-q33, Lc[47], fma(-q32, Lc[46], fma(-q31, Lc[45], fma(-q30, Lc[44], fma(-q29, Lc[43], fma(-q28, Lc[42], fma(-q27, Lc[41], fma(-q26, Lc[40], fma(-q25, Lc[39], fma(-q24, Lc[38], fma(-q23, Lc[37], fma(-q22, Lc[36], fma(-q21, Lc[35], fma(-q20, Lc[34], fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  ay = fma(-q55, Lc[81], fma(-q54, Lc[80], fma(-q53, Lc[79], fma(-q52, Lc[78], fma(-q51, Lc[77], fma(-q50, Lc[76], fma(-q49, Lc[74], fma(-q48, Lc[73], fma(-q47, Lc[72], fma(-q46, Lc[71], fma(-q45, Lc[70], fma(-q44, Lc[68], fma(-q43, Lc[67], fma(-q42, Lc[66], fma(-q41, Lc[65], fma(-q40, Lc[63], fma(-q39, Lc[62], fma(-q38, Lc[61], fma(-q37, Lc[59], fma(-q36, Lc[58], fma(-q35, Lc[56], fma(-q34, Lc[53], fma(-q33, Lc[52], fma(-q32, Lc[51], fma(-q31, Lc[50], fma(-q30, Lc[49], fma(-q29, Lc[47], fma(-q28, Lc[46], fma(-q27, Lc[45], fma(-q26, Lc[44], fma(-q25, Lc[42], fma(-q24, Lc[41], fma(-q23, Lc[40], fma(-q22, Lc[38], fma(-q21, Lc[37], fma(-q20, Lc[35], fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  az = fma(-q55, Lc[82], fma(-q54, Lc[81], fma(-q53, Lc[80], fma(-q52, Lc[79], fma(-q51, Lc[78], fma(-q50, Lc[77], fma(-q49, Lc[75], fma(-q48, Lc[74], fma(-q47, Lc[73], fma(-q46, Lc[72], fma(-q45, Lc[71], fma(-q44, Lc[69], fma(-q43, Lc[68], fma(-q42, Lc[67], fma(-q41, Lc[66], fma(-q40, Lc[64], fma(-q39, Lc[63], fma(-q38, Lc[62], fma(-q37, Lc[60], fma(-q36, Lc[59], fma(-q35, Lc[57], fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+}
+

@@ -1,0 +1,435 @@
+// Periodic images (Sec. 2.1: periodic boundary conditions through an
+// expansion of the image field).
+//
+// For a source at any image r of a separation, the Ewald acceleration is
+//   a_E(r) = a_N(r) + (4 pi/3) r + C~(r),   C~ = -grad phi~,
+//   phi~(r) = phi_E(r) + 1/|r| + (2 pi/3)|r|^2,
+// where phi_E is the Ewald potential of a unit source with the neutralising
+// background (real-space erfc sum plus reciprocal-space sum).  The walk sums
+// the Newton/Plummer part at the images it chose; the background term is
+// summed exactly from the masses and dipoles of the fixed level-l_E cells at
+// the same images; and sum_j m_j C~ is evaluated from a local expansion of
+// phi~ about the group's expansion point e (a point of the lattice
+// 2^-grid), built from those cells' moments at R0 = e - c* (lattice points,
+// so the phi~ derivatives are exact table entries) and truncated at total
+// order p_E + 1.
+//
+// phi~ derivatives at the lattice nodes are computed here in FP64 from the
+// Ewald sums, using the radial ladder d_i psi_l = -r_i psi_{l+1} of the screened
+// terms (psi = erfc(a r)/r) and of the smooth n = 0 remainder erf(a r)/r.
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "m2p_gen.cuh"
+
+namespace {
+
+constexpr int kPMax = 6;               // derivative orders in the table
+constexpr int kNMMax = 84;             // multi-indices of order <= 6
+constexpr double kAlpha = 2.0;
+constexpr double kRcut = 3.0;
+constexpr int kH2Max = 15;
+
+struct HTerm {
+  double cf;
+  signed char e[3];
+  signed char j;
+};
+__constant__ HTerm c_hterm[600];
+__constant__ short c_hbeg[kNMMax + 1];
+__constant__ signed char c_mi[kNMMax][3];
+
+__device__ void ladder_screened(double rho, int P, double* B) {
+  const double r2 = rho * rho;
+  const double ex = exp(-kAlpha * kAlpha * r2);
+  double pw = 1.0;
+  B[0] = erfc(kAlpha * rho) / rho;
+  for (int l = 1; l <= P; l++) {
+    pw *= 2.0 * kAlpha * kAlpha;
+    B[l] = ((2 * l - 1) * B[l - 1] + pw / (kAlpha * sqrt(M_PI)) * ex) / r2;
+  }
+}
+
+// smooth ladder of erf(a r)/r
+__device__ void ladder_smooth(double r, int P, double* E) {
+  if (kAlpha * r > 1.0) {
+    double B[kPMax + 1];
+    ladder_screened(r, P, B);
+    double inv2 = 1.0 / (r * r), I = 1.0 / r;
+    for (int l = 0; l <= P; l++) {
+      E[l] = I - B[l];
+      I *= (2 * l + 1) * inv2;
+    }
+    return;
+  }
+  const double x = -kAlpha * kAlpha * r * r;
+  double pref = 2.0 * kAlpha / sqrt(M_PI);
+  for (int l = 0; l <= P; l++) {
+    double t = 1.0, sum = 0.0;
+    for (int m = 0; m < 48; m++) {
+      sum += t / (2 * (l + m) + 1);
+      t *= x / (m + 1);
+    }
+    E[l] = pref * sum;
+    pref *= 2.0 * kAlpha * kAlpha;
+  }
+}
+
+__device__ void add_radial(const double rho[3], const double* psi, double s, int nm, int P, double* out) {
+  double pw[3][kPMax + 1];
+  for (int d = 0; d < 3; d++) {
+    pw[d][0] = 1.0;
+    for (int e = 1; e <= P; e++) pw[d][e] = pw[d][e - 1] * rho[d];
+  }
+  for (int t = 0; t < nm; t++) {
+    double v = 0.0;
+    for (int h = c_hbeg[t]; h < c_hbeg[t + 1]; h++) {
+      const HTerm q = c_hterm[h];
+      const double ps = (q.j & 1) ? -psi[q.j] : psi[q.j];
+      v += q.cf * pw[0][q.e[0]] * pw[1][q.e[1]] * pw[2][q.e[2]] * ps;
+    }
+    out[t] += s * v;
+  }
+}
+
+__global__ void phitilde_table_kernel(int lg, int P, int nm, double* __restrict__ tab) {
+  const int m = (1 << (lg - 1)) + 2;
+  const int total = m * m * m;
+  const double h = ldexp(1.0, -lg);
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < total; id += gridDim.x * blockDim.x) {
+    const int i = id / (m * m), j = (id / m) % m, k = id % m;
+    const double r[3] = {i * h, j * h, k * h};
+    double out[kNMMax];
+    for (int t = 0; t < nm; t++) out[t] = 0.0;
+    const int nmax = (int)ceil(kRcut) + 1;
+    for (int nx = -nmax; nx <= nmax; nx++)
+      for (int ny = -nmax; ny <= nmax; ny++)
+        for (int nz = -nmax; nz <= nmax; nz++) {
+          if (nx == 0 && ny == 0 && nz == 0) continue;
+          const double rho[3] = {r[0] - nx, r[1] - ny, r[2] - nz};
+          const double d = sqrt(rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2]);
+          if (d >= kRcut) continue;
+          double B[kPMax + 1];
+          ladder_screened(d, P, B);
+          add_radial(rho, B, -1.0, nm, P, out);
+        }
+    {
+      const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      double E[kPMax + 1];
+      ladder_smooth(d, P, E);
+      add_radial(r, E, 1.0, nm, P, out);
+    }
+    const int hm = 3;
+    for (int hx = -hm; hx <= hm; hx++)
+      for (int hy = -hm; hy <= hm; hy++)
+        for (int hz = -hm; hz <= hm; hz++) {
+          const int h2 = hx * hx + hy * hy + hz * hz;
+          if (h2 == 0 || h2 > kH2Max) continue;
+          const double wgt = exp(-M_PI * M_PI * h2 / (kAlpha * kAlpha)) / h2;
+          double sn, cs;
+          sincos(2.0 * M_PI * (hx * r[0] + hy * r[1] + hz * r[2]), &sn, &cs);
+          for (int t = 0; t < nm; t++) {
+            const int o = c_mi[t][0] + c_mi[t][1] + c_mi[t][2];
+            double hp = 1.0;
+            for (int q = 0; q < o; q++) hp *= 2.0 * M_PI;
+            for (int q = 0; q < c_mi[t][0]; q++) hp *= hx;
+            for (int q = 0; q < c_mi[t][1]; q++) hp *= hy;
+            for (int q = 0; q < c_mi[t][2]; q++) hp *= hz;
+            const double ph = (o & 3) == 0 ? cs : (o & 3) == 1 ? -sn : (o & 3) == 2 ? -cs : sn;
+            out[t] += -(1.0 / M_PI) * wgt * hp * ph;
+          }
+        }
+    out[0] += (2.0 * M_PI / 3.0) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + M_PI / (kAlpha * kAlpha);
+    if (P >= 1)
+      for (int d = 0; d < 3; d++) out[1 + d] += (4.0 * M_PI / 3.0) * r[d];
+    if (P >= 2) {
+      out[4] += 4.0 * M_PI / 3.0;  // (2,0,0)
+      out[7] += 4.0 * M_PI / 3.0;  // (0,2,0)
+      out[9] += 4.0 * M_PI / 3.0;  // (0,0,2)
+    }
+    for (int t = 0; t < nm; t++) tab[(int64_t)id * nm + t] = out[t];
+  }
+}
+
+__global__ void to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// ---- per-group image field and scatter to caller order -------------------------
+template <int PE> struct PE_;
+#define NB_PE(PE)                                                                        \
+  template <> struct PE_<PE> {                                                           \
+    static constexpr int NL = kNL##PE;                                                   \
+    static constexpr int NE = (PE + 1) * (PE + 2) * (PE + 3) / 6;                        \
+    static constexpr int NP = (PE + 2) * (PE + 3) * (PE + 4) / 6;                        \
+    template <typename T>                                                                \
+    static __device__ __forceinline__ void m2l(const T* M, const T* D, T* L) {           \
+      m2l_pe##PE<T>(M, D, L);                                                            \
+    }                                                                                    \
+    template <typename T>                                                                \
+    static __device__ __forceinline__ void l2p(const T* L, T x, T y, T z, T& ax, T& ay, T& az) { \
+      l2p_pe##PE<T>(L, x, y, z, ax, ay, az);                                             \
+    }                                                                                    \
+  };
+NB_PE(1)
+NB_PE(2)
+NB_PE(3)
+NB_PE(4)
+NB_PE(5)
+
+template <typename T>
+struct PerArgs {
+  DevTree tr;
+  const typename Vec4<T>::type* src;
+  const double* fm;     // field moments (FP64), (box, cell, NE)
+  const T* tab;         // phi~ table, nodes x NP
+  int le, lg, pe;
+  const T* accw;        // walk accelerations, key order
+  float* out;           // caller order
+  unsigned long long* counter;
+};
+
+__constant__ unsigned char c_par_mask[kNMMax];  // bit d set: multi-index odd in axis d
+
+template <typename T, int PE>
+__global__ void __launch_bounds__(128) periodic_kernel(PerArgs<T> a) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NL = PE_<PE>::NL, NE = PE_<PE>::NE, NP = PE_<PE>::NP;
+  const int lane = threadIdx.x & 31;
+  const DevTree& tr = a.tr;
+  const int ncp = 1 << (3 * a.le);
+  const int m = (1 << (a.lg - 1)) + 2;
+  const int step = 1 << (23 - a.lg);
+  const T scale = (T)(1.0 / 8388608.0);
+  const T fourpi3 = (T)(4.0 * M_PI / 3.0);
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+    const int4 ga = tr.gA[g], gb = tr.gB[g], gd = tr.gD[g];
+    const int box = ga.z;
+    T L[NL];
+#pragma unroll
+    for (int t = 0; t < NL; t++) L[t] = (T)0;
+    T vx = 0, vy = 0, vz = 0, mt = 0;
+    unsigned long long nused = 0;
+    for (int cell = lane; cell < ncp; cell += 32) {
+      const double* Mc = a.fm + ((int64_t)box * ncp + cell) * NE;
+      const double m0 = Mc[0];
+      if (m0 == 0.0) continue;
+      nused++;
+      T M[NE];
+#pragma unroll
+      for (int t = 0; t < NE; t++) M[t] = (T)Mc[t];
+      const int cx2 = cell_c2((int)compact3((uint64_t)cell), a.le);
+      const int cy2 = cell_c2((int)compact3((uint64_t)cell >> 1), a.le);
+      const int cz2 = cell_c2((int)compact3((uint64_t)cell >> 2), a.le);
+      const int kx = img_shift(cx2, gb.x), ky = img_shift(cy2, gb.y), kz = img_shift(cz2, gb.z);
+      const int ox = cx2 - kx * NB_PBOX - gd.x, oy = cy2 - ky * NB_PBOX - gd.y, oz = cz2 - kz * NB_PBOX - gd.z;
+      // R0 = e - c* on the lattice
+      const int irx = -ox / step, iry = -oy / step, irz = -oz / step;
+      const int neg = (irx < 0 ? 1 : 0) | (iry < 0 ? 2 : 0) | (irz < 0 ? 4 : 0);
+      const int node = (abs(irx) * m + abs(iry)) * m + abs(irz);
+      const T* src = a.tab + (int64_t)node * NP;
+      T D[NP];
+#pragma unroll
+      for (int t = 0; t < NP; t++) {
+        const T v = src[t];
+        D[t] = (__popc(c_par_mask[t] & neg) & 1) ? -v : v;
+      }
+      PE_<PE>::template m2l<T>(M, D, L);
+      vx += M[0] * ((T)ox * scale) + M[1];
+      vy += M[0] * ((T)oy * scale) + M[2];
+      vz += M[0] * ((T)oz * scale) + M[3];
+      mt += M[0];
+    }
+#pragma unroll
+    for (int t = 0; t < NL; t++) {
+      T v = L[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      L[t] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      vx += __shfl_xor_sync(0xffffffffu, vx, o);
+      vy += __shfl_xor_sync(0xffffffffu, vy, o);
+      vz += __shfl_xor_sync(0xffffffffu, vz, o);
+      mt += __shfl_xor_sync(0xffffffffu, mt, o);
+      nused += __shfl_xor_sync(0xffffffffu, nused, o);
+    }
+    if (lane == 0 && a.counter) atomicAdd(a.counter, nused);
+    if (lane < ga.y) {
+      const int i = ga.x + lane;
+      const V4 o4 = a.src[i];
+      const int4 la = tr.cA[tr.sleaf[i]];
+      const T dx = o4.x + (T)(la.x - gd.x) * scale;
+      const T dy = o4.y + (T)(la.y - gd.y) * scale;
+      const T dz = o4.z + (T)(la.z - gd.z) * scale;
+      T ax = a.accw[i] + fourpi3 * (mt * dx - vx);
+      T ay = a.accw[tr.n + i] + fourpi3 * (mt * dy - vy);
+      T az = a.accw[2 * tr.n + i] + fourpi3 * (mt * dz - vz);
+      PE_<PE>::template l2p<T>(L, dx, dy, dz, ax, ay, az);
+      const uint32_t j = tr.perm[i];
+      a.out[j] = (float)ax;
+      a.out[tr.n + j] = (float)ay;
+      a.out[2 * tr.n + j] = (float)az;
+    }
+  }
+}
+
+// plain scatter when there are no periodic images
+template <typename T>
+__global__ void scatter_kernel(int64_t n, const uint32_t* __restrict__ perm, const T* __restrict__ accw,
+                               float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = perm[i];
+    out[j] = (float)accw[i];
+    out[n + j] = (float)accw[n + i];
+    out[2 * n + j] = (float)accw[2 * n + i];
+  }
+}
+
+// ---- host side: term tables and cached device tables ------------------------------
+int mi_index(int nx, int ny, int nz) {
+  int o = nx + ny + nz, j = ny + nz;
+  return o * (o + 1) * (o + 2) / 6 + j * (j + 1) / 2 + nz;
+}
+
+double factd(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; i++) f *= i;
+  return f;
+}
+
+struct TableCache {
+  int device = -1, lg = 0, P = 0;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+};
+std::mutex g_tab_mutex;
+std::vector<TableCache> g_tabs;
+
+cudaError_t upload_terms() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && done[dev]) return cudaSuccess;
+  std::vector<HTerm> terms;
+  short beg[kNMMax + 1];
+  signed char mi[kNMMax][3];
+  unsigned char pm[kNMMax];
+  for (int o = 0; o <= kPMax; o++)
+    for (int nx = o; nx >= 0; nx--)
+      for (int ny = o - nx; ny >= 0; ny--) {
+        int nz = o - nx - ny, t = mi_index(nx, ny, nz);
+        mi[t][0] = (signed char)nx;
+        mi[t][1] = (signed char)ny;
+        mi[t][2] = (signed char)nz;
+        pm[t] = (unsigned char)((nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2));
+      }
+  for (int t = 0; t < kNMMax; t++) {
+    beg[t] = (short)terms.size();
+    int m0 = mi[t][0], m1 = mi[t][1], m2 = mi[t][2];
+    for (int k0 = 0; 2 * k0 <= m0; k0++)
+      for (int k1 = 0; 2 * k1 <= m1; k1++)
+        for (int k2 = 0; 2 * k2 <= m2; k2++) {
+          HTerm h;
+          h.cf = factd(m0) / (factd(k0) * factd(m0 - 2 * k0) * ldexp(1.0, k0)) * factd(m1) /
+                 (factd(k1) * factd(m1 - 2 * k1) * ldexp(1.0, k1)) * factd(m2) /
+                 (factd(k2) * factd(m2 - 2 * k2) * ldexp(1.0, k2));
+          h.e[0] = (signed char)(m0 - 2 * k0);
+          h.e[1] = (signed char)(m1 - 2 * k1);
+          h.e[2] = (signed char)(m2 - 2 * k2);
+          h.j = (signed char)(m0 + m1 + m2 - k0 - k1 - k2);
+          terms.push_back(h);
+        }
+  }
+  beg[kNMMax] = (short)terms.size();
+  if (terms.size() > 600) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_hterm, terms.data(), sizeof(HTerm) * terms.size()))) return e;
+  if ((e = cudaMemcpyToSymbol(c_hbeg, beg, sizeof(beg)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_mi, mi, sizeof(mi)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_par_mask, pm, sizeof(pm)))) return e;
+  if (dev < 64) done[dev] = true;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+// phi~ table for (lg, P) on the current device (built once, cached until exit)
+cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_tab_mutex);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  for (auto& c : g_tabs)
+    if (c.device == dev && c.lg == lg && c.P == P) {
+      *t64 = c.d64;
+      *t32 = c.d32;
+      return cudaSuccess;
+    }
+  if (P > kPMax || lg < 2 || lg > 9) return cudaErrorInvalidValue;
+  if ((e = upload_terms())) return e;
+  const int m = (1 << (lg - 1)) + 2;
+  const int nm = (P + 1) * (P + 2) * (P + 3) / 6;
+  const int64_t total = (int64_t)m * m * m * nm;
+  TableCache c;
+  c.device = dev;
+  c.lg = lg;
+  c.P = P;
+  if ((e = cudaMalloc(&c.d64, sizeof(double) * total))) return e;
+  if ((e = cudaMalloc(&c.d32, sizeof(float) * total))) {
+    cudaFree(c.d64);
+    return e;
+  }
+  const int nodes = m * m * m;
+  phitilde_table_kernel<<<(nodes + 63) / 64, 64, 0, s>>>(lg, P, nm, c.d64);
+  to_float_kernel<<<(int)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256), 256, 0, s>>>(c.d64, c.d32,
+                                                                                                 total);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaStreamSynchronize(s))) return e;
+  g_tabs.push_back(c);
+  *t64 = c.d64;
+  *t32 = c.d32;
+  return cudaSuccess;
+}
+
+cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+                        const void* tab, const void* accw, float* out, unsigned long long* counter,
+                        cudaStream_t s) {
+  if (pe == 0) {
+    if (fp64) scatter_kernel<double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out);
+    else scatter_kernel<float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out);
+    return cudaGetLastError();
+  }
+  int grid = (int)(((int64_t)tr.ngroup * 32 + 127) / 128);
+  if (grid > 152 * 64) grid = 152 * 64;
+  if (grid < 1) grid = 1;
+#define NB_PER(TT, PE)                                                                \
+  {                                                                                   \
+    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, \
+                  (const TT*)accw, out, counter};                                     \
+    periodic_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                  \
+    break;                                                                            \
+  }
+  if (fp64) {
+    switch (pe) {
+      case 1: NB_PER(double, 1)
+      case 2: NB_PER(double, 2)
+      case 3: NB_PER(double, 3)
+      case 4: NB_PER(double, 4)
+      default: NB_PER(double, 5)
+    }
+  } else {
+    switch (pe) {
+      case 1: NB_PER(float, 1)
+      case 2: NB_PER(float, 2)
+      case 3: NB_PER(float, 3)
+      case 4: NB_PER(float, 4)
+      default: NB_PER(float, 5)
+    }
+  }
+#undef NB_PER
+  return cudaGetLastError();
+}

@@ -1,0 +1,351 @@
+// Group tree walk with P2P and M2P interactions (Sec. 2.1: sinks that share
+// an interaction list are bundled and their m x n interaction block is
+// evaluated together; a multipole acceptance test picks cell expansions or
+// opens the cell; near-leaf interactions are direct sums).
+//
+// One warp per group of <= 32 sinks (one sink per lane).  The warp walks the
+// tree cooperatively: it pops up to 32 cells from its stack, each lane tests
+// one cell with the integer acceptance test, opened cells push their
+// daughters, accepted cells are evaluated at once as a chunk of M2P
+// interactions (coefficients staged in shared memory, every lane a sink),
+// and leaves are flattened into chunks of 32 source particles staged in
+// shared memory for the P2P loop.  Every chunk's partial sum is added with
+// Kahan compensation.  The walk order is fixed, so results are bitwise
+// reproducible.
+//
+// Acceptance: in integer units of 2^-23, with the cell at the image of its
+// level-l_E ancestor nearest the group box centre g, d2 is the squared
+// distance from the cell centre to the group box; a cell of level l >= 2
+// whose level-l_E descendants share one image is accepted iff
+// d2 > floor(s^2/theta^2), s = 2^(23-l).
+#include "common.cuh"
+#include "m2p_gen.cuh"
+
+namespace {
+
+template <int P> struct WOrd;
+#define NB_WORD(P)                                                                                    \
+  template <> struct WOrd<P> {                                                                        \
+    static constexpr int NBS = (kNB##P + 3) & ~3;                                                     \
+    template <typename T>                                                                             \
+    static __device__ __forceinline__ void m2p(const T* B, T x, T y, T z, T e2, T& ax, T& ay, T& az) { \
+      m2p_p##P<T>(B, x, y, z, e2, ax, ay, az);                                                        \
+    }                                                                                                 \
+  };
+NB_WORD(0)
+NB_WORD(1)
+NB_WORD(2)
+NB_WORD(3)
+NB_WORD(4)
+
+template <typename T>
+__device__ __forceinline__ void kadd(T& s, T& c, T x) {
+  T y = x - c;
+  T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x - v;
+}
+
+template <typename T>
+struct WalkArgs {
+  DevTree tr;
+  const T* coef;
+  const typename Vec4<T>::type* src;
+  const T* eps2;  // per box
+  long long thr[NB_NLEV];
+  int n_direct;
+  int le;
+  int* stack;
+  int stack_cap;
+  int* group_ctr;
+  T* acc;  // 3n, key order
+  unsigned long long* counters;  // [0] p2p, [1] m2p
+  unsigned* status;
+};
+
+constexpr double kScale = 1.0 / 8388608.0;  // 2^-23
+
+template <typename T, int P, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NBS = WOrd<P>::NBS;
+  __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
+  __shared__ V4 s_src[WARPS][32];
+  __shared__ T s_moff[WARPS][32][3];
+  __shared__ int s_midx[WARPS][32];
+  __shared__ int s_pfx[WARPS][32];
+  __shared__ int s_pst[WARPS][32];
+  __shared__ int s_plev[WARPS][32];
+  __shared__ T s_poff[WARPS][32][3];
+  __shared__ int4 s_pcen[WARPS][32];
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned ltmask = (1u << lane) - 1u;
+  const DevTree& tr = w.tr;
+  int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
+  const T scale = (T)kScale;
+
+  while (true) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(w.group_ctr, 1);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= tr.ngroup) break;
+    const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
+    const int cnt = ga.y, box = ga.z;
+    const T eps2 = w.eps2[box];
+    const bool act = lane < cnt;
+    const int i = ga.x + (act ? lane : 0);
+    T xi, yi, zi;
+    {
+      V4 o = w.src[i];
+      int4 la = tr.cA[tr.sleaf[i]];
+      xi = o.x + (T)(la.x - gd.x) * scale;
+      yi = o.y + (T)(la.y - gd.y) * scale;
+      zi = o.z + (T)(la.z - gd.z) * scale;
+    }
+    T ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;
+    unsigned long long n_p2p = 0, n_m2p = 0;
+    int top = 1;
+    if (lane == 0) stk[0] = box;  // root of this box
+    __syncwarp();
+    bool overflow = false;
+    while (top > 0) {
+      const int nb = min(32, top);
+      const int base = top - nb;
+      top = base;
+      int c = -1;
+      int4 ca = make_int4(0, 0, 0, 0), cb = make_int4(0, 0, 0, 0);
+      if (lane < nb) {
+        c = stk[base + lane];
+        ca = tr.cA[c];
+        cb = tr.cB[c];
+      }
+      __syncwarp();
+      int cls = 0;  // 1 open, 2 M2P, 3 P2P
+      int kx = 0, ky = 0, kz = 0;
+      const int lvl = ca.w & 0xff, nch = ca.w >> 8;
+      if (lane < nb) {
+        bool consistent = true;
+        const int ix = ((ca.x >> (22 - lvl)) - 1) >> 1;
+        const int iy = ((ca.y >> (22 - lvl)) - 1) >> 1;
+        const int iz = ((ca.z >> (22 - lvl)) - 1) >> 1;
+        if (lvl >= w.le) {
+          const int sh = lvl - w.le;
+          kx = img_shift(cell_c2(ix >> sh, w.le), gb.x);
+          ky = img_shift(cell_c2(iy >> sh, w.le), gb.y);
+          kz = img_shift(cell_c2(iz >> sh, w.le), gb.z);
+        } else {
+          const int sh = w.le - lvl;
+          kx = img_shift(cell_c2(ix << sh, w.le), gb.x);
+          ky = img_shift(cell_c2(iy << sh, w.le), gb.y);
+          kz = img_shift(cell_c2(iz << sh, w.le), gb.z);
+          consistent = kx == img_shift(cell_c2(((ix + 1) << sh) - 1, w.le), gb.x) &&
+                       ky == img_shift(cell_c2(((iy + 1) << sh) - 1, w.le), gb.y) &&
+                       kz == img_shift(cell_c2(((iz + 1) << sh) - 1, w.le), gb.z);
+        }
+        const int dx = abs(ca.x - gb.x - kx * NB_PBOX) - gc.x;
+        const int dy = abs(ca.y - gb.y - ky * NB_PBOX) - gc.y;
+        const int dz = abs(ca.z - gb.z - kz * NB_PBOX) - gc.z;
+        const long long ddx = dx > 0 ? dx : 0, ddy = dy > 0 ? dy : 0, ddz = dz > 0 ? dz : 0;
+        const long long d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        const bool accept = consistent && lvl >= 2 && d2 > w.thr[lvl];
+        if (accept && cb.y > w.n_direct) cls = 2;
+        else if (accept || nch == 0) cls = 3;
+        else cls = 1;
+      }
+      // push daughters of opened cells
+      {
+        const int nc = (cls == 1) ? nch : 0;
+        const int pre = warp_excl_scan(nc, lane);
+        const int tot = __shfl_sync(FULL, pre + nc, 31);
+        if (top + tot > w.stack_cap) {
+          overflow = true;
+          break;
+        }
+        for (int q = 0; q < nc; q++) stk[top + pre + q] = cb.z + q;
+        top += tot;
+        __syncwarp();
+      }
+      // M2P chunk
+      const unsigned mm = __ballot_sync(FULL, cls == 2);
+      if (mm) {
+        const int nmp = __popc(mm);
+        if (cls == 2) {
+          const int pos = __popc(mm & ltmask);
+          s_midx[wid][pos] = c;
+          s_moff[wid][pos][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
+          s_moff[wid][pos][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
+          s_moff[wid][pos][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
+        }
+        __syncwarp();
+        for (int t = lane; t < nmp * NBS; t += 32) {
+          const int q = t / NBS, r = t - q * NBS;
+          s_coef[wid][t] = w.coef[(int64_t)s_midx[wid][q] * NBS + r];
+        }
+        __syncwarp();
+        if (act) {
+          T px = 0, py = 0, pz = 0;
+          for (int q = 0; q < nmp; q++)
+            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], xi - s_moff[wid][q][0], yi - s_moff[wid][q][1],
+                                     zi - s_moff[wid][q][2], eps2, px, py, pz);
+          kadd(ax, cx, px);
+          kadd(ay, cy, py);
+          kadd(az, cz, pz);
+        }
+        n_m2p += nmp;
+        __syncwarp();
+      }
+      // P2P chunks
+      const unsigned pm = __ballot_sync(FULL, cls == 3);
+      if (pm) {
+        const int ncl = (cls == 3) ? cb.y : 0;
+        const int pre = warp_excl_scan(ncl, lane);
+        const int total = __shfl_sync(FULL, pre + ncl, 31);
+        s_pfx[wid][lane] = pre;  // monotone: lanes without P2P add nothing
+        s_pst[wid][lane] = cb.x;
+        s_plev[wid][lane] = lvl;
+        s_pcen[wid][lane] = ca;
+        s_poff[wid][lane][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
+        s_poff[wid][lane][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
+        s_poff[wid][lane][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
+        __syncwarp();
+        for (int b0 = 0; b0 < total; b0 += 32) {
+          const int t = b0 + lane;
+          if (t < total) {
+            // last P2P lane q with pfx[q] <= t
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (s_pfx[wid][mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            const int q = lo;
+            const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
+            V4 v = w.src[j];
+            T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
+            if (s_plev[wid][q] < w.le) {
+              // leaf above the image level: image per particle from its own
+              // level-l_E ancestor
+              const uint64_t pk = tr.skeys[j] >> (3 * (NB_QBITS - w.le));
+              const int4 pc = s_pcen[wid][q];
+              const int jx = img_shift(cell_c2((int)compact3(pk), w.le), gb.x);
+              const int jy = img_shift(cell_c2((int)compact3(pk >> 1), w.le), gb.y);
+              const int jz = img_shift(cell_c2((int)compact3(pk >> 2), w.le), gb.z);
+              ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
+              oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
+              oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;
+            }
+            v.x = v.x + ox;
+            v.y = v.y + oy;
+            v.z = v.z + oz;
+            s_src[wid][lane] = v;
+          }
+          __syncwarp();
+          const int nn = min(32, total - b0);
+          if (act) {
+            T px = 0, py = 0, pz = 0;
+            for (int k = 0; k < nn; k++) {
+              const V4 s = s_src[wid][k];
+              const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+              const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+              const T inv = nbody_rsqrt(r2);
+              const T f = s.w * (inv * inv) * inv;
+              px = fma(dx, f, px);
+              py = fma(dy, f, py);
+              pz = fma(dz, f, pz);
+            }
+            kadd(ax, cx, px);
+            kadd(ay, cy, py);
+            kadd(az, cz, pz);
+          }
+          __syncwarp();
+        }
+        n_p2p += (unsigned long long)total;
+      }
+    }
+    if (overflow) {
+      if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
+      continue;
+    }
+    if (act) {
+      w.acc[i] = ax - cx;
+      w.acc[tr.n + i] = ay - cy;
+      w.acc[2 * tr.n + i] = az - cz;
+    }
+    if (lane == 0) {
+      atomicAdd(&w.counters[0], n_p2p * (unsigned long long)cnt);
+      atomicAdd(&w.counters[1], n_m2p * (unsigned long long)cnt);
+    }
+  }
+}
+
+template <typename T, int P, int WARPS, int MINB>
+cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB>,
+                                                                 WARPS * 32, 0);
+  if (e) return e;
+  int grid = nsm * (occ > 0 ? occ : 1);
+  if (grid > max_blocks) grid = max_blocks;
+  walk_kernel<T, P, WARPS, MINB><<<grid, WARPS * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// warps per block of the walk for a precision
+int nb_walk_warps(bool fp64) { return fp64 ? 4 : 8; }
+
+cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src,
+                    const void* eps2, const long long* thr, int n_direct, int le, int* stack,
+                    int stack_cap, int max_blocks, int* group_ctr, void* acc,
+                    unsigned long long* counters, unsigned* status, int nsm, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
+  if (e) return e;
+#define NB_WALK(TT, P, W, MB)                                                      \
+  {                                                                                \
+    WalkArgs<TT> a;                                                                \
+    a.tr = tr;                                                                     \
+    a.coef = (const TT*)coef;                                                      \
+    a.src = (const typename Vec4<TT>::type*)src;                                   \
+    a.eps2 = (const TT*)eps2;                                                      \
+    for (int l = 0; l < NB_NLEV; l++) a.thr[l] = thr[l];                           \
+    a.n_direct = n_direct;                                                         \
+    a.le = le;                                                                     \
+    a.stack = stack;                                                               \
+    a.stack_cap = stack_cap;                                                       \
+    a.group_ctr = group_ctr;                                                       \
+    a.acc = (TT*)acc;                                                              \
+    a.counters = counters;                                                         \
+    a.status = status;                                                             \
+    return launch_walk<TT, P, W, MB>(a, nsm, max_blocks, s);                       \
+  }
+  if (fp64) {
+    switch (order) {
+      case 0: NB_WALK(double, 0, 4, 1)
+      case 1: NB_WALK(double, 1, 4, 1)
+      case 2: NB_WALK(double, 2, 4, 1)
+      case 3: NB_WALK(double, 3, 4, 1)
+      default: NB_WALK(double, 4, 4, 1)
+    }
+  } else {
+    switch (order) {
+      case 0: NB_WALK(float, 0, 8, 2)
+      case 1: NB_WALK(float, 1, 8, 2)
+      case 2: NB_WALK(float, 2, 8, 2)
+      case 3: NB_WALK(float, 3, 8, 2)
+      default: NB_WALK(float, 4, 8, 2)
+    }
+  }
+#undef NB_WALK
+}

@@ -1,0 +1,260 @@
+"""Thin Python binding of the C ABI in include/nbody.h (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in
+``libnbody.so``; the ``*_t`` helpers accept torch CUDA tensors and pass their
+device pointers and the current stream.  All computation happens in the CUDA
+library; there is no fallback.  Loading fails loudly when the library has not
+been built (``python -m paper_1407_2600_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnbody.so")
+
+NBODY_OK = 0
+NBODY_EINVAL = -1
+NBODY_ENOMEM = -2
+NBODY_ECUDA = -3
+NBODY_EOVERFLOW = -4
+NBODY_ETIMEOUT = -5
+NBODY_ENOTSUP = -6
+NBODY_MIXED = 0
+NBODY_FP64 = 1
+NBODY_FLAG_ASYNC = 1
+EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_level": 5,
+          "moments": 6, "groups": 7}
+
+# every symbol include/nbody.h declares
+SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces",
+           "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_forces_vjp", "nbody_tree_count",
+           "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
+           "nbody_strerror"]
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("theta", C.c_double), ("order", C.c_int), ("n_leaf", C.c_int),
+                ("n_group", C.c_int), ("n_direct", C.c_int), ("lmax", C.c_int),
+                ("ewald_order", C.c_int), ("ewald_level", C.c_int), ("ewald_grid", C.c_int),
+                ("precision", C.c_int), ("flags", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("p2p", C.c_double), ("m2p", C.c_double), ("m2l", C.c_double),
+                ("ncells", C.c_int64), ("ngroups", C.c_int64), ("max_level", C.c_int32),
+                ("nbox", C.c_int32), ("ms_sort", C.c_float), ("ms_build", C.c_float),
+                ("ms_upward", C.c_float), ("ms_walk", C.c_float), ("ms_periodic", C.c_float)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class NbodyError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, nbody_strerror(code), code))
+
+
+_LIB = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libnbody.so; raises if it is missing (no CPU fallback exists)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnbody.so is not built: run __graft_entry__.build() "
+                               "(the CUDA library is required; there is no fallback)")
+        L = C.CDLL(LIB_PATH)
+        L.nbody_default_params.argtypes = [C.POINTER(Params)]
+        L.nbody_default_params.restype = None
+        L.nbody_build_tree.argtypes = [C.POINTER(Params), C.c_int64, _vp, _vp, C.POINTER(_vp), _vp]
+        L.nbody_build_tree_batched.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_int64),
+                                               C.POINTER(C.c_double), _vp, _vp, C.POINTER(_vp), _vp]
+        L.nbody_forces.argtypes = [_vp, _vp, C.POINTER(Stats), _vp]
+        L.nbody_kdk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp]
+        L.nbody_kdk_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp]
+        L.nbody_forces_vjp.argtypes = [_vp, _vp, _vp, _vp]
+        L.nbody_tree_count.argtypes = [_vp, C.c_int]
+        L.nbody_tree_count.restype = C.c_int64
+        L.nbody_tree_export.argtypes = [_vp, C.c_int, _vp, _vp]
+        L.nbody_tree_lookup.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.nbody_check.argtypes = [_vp, _vp]
+        L.nbody_tree_free.argtypes = [_vp]
+        L.nbody_tree_free.restype = None
+        L.nbody_strerror.argtypes = [C.c_int]
+        L.nbody_strerror.restype = C.c_char_p
+        _LIB = L
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != NBODY_OK:
+        raise NbodyError(rc, where)
+
+
+# ---- the C entry points, same names -------------------------------------------
+def nbody_default_params() -> Params:
+    p = Params()
+    lib().nbody_default_params(C.byref(p))
+    return p
+
+
+def nbody_build_tree(params: Params, n: int, pos_dev: int, mass_dev: int | None, tree=None,
+                     stream: int | None = None):
+    h = _vp(tree)
+    rc = lib().nbody_build_tree(C.byref(params), n, pos_dev, mass_dev, C.byref(h), stream)
+    return rc, h.value
+
+
+def nbody_build_tree_batched(params: Params, offsets, eps, pos_dev: int, mass_dev: int | None,
+                             tree=None, stream: int | None = None):
+    nbox = len(offsets) - 1
+    off = (C.c_int64 * (nbox + 1))(*[int(v) for v in offsets])
+    ep = None if eps is None else (C.c_double * nbox)(*[float(v) for v in eps])
+    h = _vp(tree)
+    rc = lib().nbody_build_tree_batched(C.byref(params), nbox, off, ep, pos_dev, mass_dev,
+                                        C.byref(h), stream)
+    return rc, h.value
+
+
+def nbody_forces(tree: int, acc_dev: int, stats: Stats | None = None, stream: int | None = None) -> int:
+    return lib().nbody_forces(tree, acc_dev, C.byref(stats) if stats is not None else None, stream)
+
+
+def nbody_kdk_step(tree: int, pos_dev: int, mom_dev: int, acc_dev: int, a0: float, a1: float,
+                   stream: int | None = None) -> int:
+    return lib().nbody_kdk_step(tree, pos_dev, mom_dev, acc_dev, a0, a1, stream)
+
+
+def nbody_kdk_adjoint(tree: int, pos0_dev: int, mom0_dev: int, a0: float, a1: float,
+                      lam_pos1_dev: int, lam_mom1_dev: int, lam_pos0_dev: int, lam_mom0_dev: int,
+                      stream: int | None = None) -> int:
+    return lib().nbody_kdk_adjoint(tree, pos0_dev, mom0_dev, a0, a1, lam_pos1_dev, lam_mom1_dev,
+                                   lam_pos0_dev, lam_mom0_dev, stream)
+
+
+def nbody_forces_vjp(tree: int, lam_dev: int, out_dev: int, stream: int | None = None) -> int:
+    return lib().nbody_forces_vjp(tree, lam_dev, out_dev, stream)
+
+
+def nbody_tree_count(tree: int, what: int) -> int:
+    return lib().nbody_tree_count(tree, what)
+
+
+def nbody_tree_export(tree: int, what: int, dst_dev: int, stream: int | None = None) -> int:
+    return lib().nbody_tree_export(tree, what, dst_dev, stream)
+
+
+def nbody_tree_lookup(tree: int, keys_dev: int, nkeys: int, idx_dev: int, stream: int | None = None) -> int:
+    return lib().nbody_tree_lookup(tree, keys_dev, nkeys, idx_dev, stream)
+
+
+def nbody_check(tree: int, stream: int | None = None) -> int:
+    return lib().nbody_check(tree, stream)
+
+
+def nbody_tree_free(tree: int) -> None:
+    if tree:
+        lib().nbody_tree_free(tree)
+
+
+def nbody_strerror(code: int) -> str:
+    return lib().nbody_strerror(code).decode()
+
+
+# ---- torch-tensor conveniences (marshalling only) ------------------------------------
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def params(**kw) -> Params:
+    p = nbody_default_params()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Tree:
+    """Owns one nbody_tree handle built from torch CUDA tensors (SoA (3, n))."""
+
+    def __init__(self, prm: Params, pos, mass=None, offsets=None, eps=None):
+        import torch
+        if not pos.is_cuda or pos.dtype != torch.float64 or pos.dim() != 2 or pos.shape[0] != 3:
+            raise ValueError("pos must be a CUDA float64 tensor of shape (3, n)")
+        self.params = prm
+        self.pos = pos.contiguous()
+        self.mass = None if mass is None else mass.contiguous().float()
+        self.n = pos.shape[1]
+        self.offsets = offsets
+        self.eps = eps
+        self.handle = None
+        self.rebuild()
+
+    def rebuild(self):
+        mp = None if self.mass is None else self.mass.data_ptr()
+        if self.offsets is None:
+            rc, h = nbody_build_tree(self.params, self.n, self.pos.data_ptr(), mp, self.handle, _stream())
+        else:
+            rc, h = nbody_build_tree_batched(self.params, self.offsets, self.eps, self.pos.data_ptr(), mp,
+                                             self.handle, _stream())
+        if h:
+            self.handle = h
+        _check(rc, "nbody_build_tree")
+
+    def forces(self, acc=None, stats=False):
+        import torch
+        if acc is None:
+            acc = torch.empty((3, self.n), dtype=torch.float32, device=self.pos.device)
+        st = Stats() if stats else None
+        _check(nbody_forces(self.handle, acc.data_ptr(), st, _stream()), "nbody_forces")
+        return (acc, st.asdict()) if stats else acc
+
+    def kdk_step(self, mom, acc, a0, a1):
+        _check(nbody_kdk_step(self.handle, self.pos.data_ptr(), mom.data_ptr(), acc.data_ptr(), a0, a1,
+                              _stream()), "nbody_kdk_step")
+
+    def export(self, what: str):
+        import torch
+        code = EXPORT[what]
+        cnt = nbody_tree_count(self.handle, code)
+        if cnt < 0:
+            _check(int(cnt), "nbody_tree_count")
+        if what in ("sorted_keys", "cell_keys"):
+            t = torch.empty(cnt, dtype=torch.int64, device=self.pos.device)
+        elif what == "perm":
+            t = torch.empty(cnt, dtype=torch.int32, device=self.pos.device)
+        elif what in ("cell_range", "groups"):
+            t = torch.empty((cnt, 2), dtype=torch.int32, device=self.pos.device)
+        elif what == "cell_level":
+            t = torch.empty(cnt, dtype=torch.int32, device=self.pos.device)
+        else:
+            o = self.params.order
+            t = torch.empty((cnt, (o + 1) * (o + 2) * (o + 3) // 6), dtype=torch.float64, device=self.pos.device)
+        _check(nbody_tree_export(self.handle, code, t.data_ptr(), _stream()), "nbody_tree_export")
+        return t
+
+    def lookup(self, keys):
+        import torch
+        out = torch.empty(keys.shape[0], dtype=torch.int32, device=keys.device)
+        _check(nbody_tree_lookup(self.handle, keys.data_ptr(), keys.shape[0], out.data_ptr(), _stream()),
+               "nbody_tree_lookup")
+        return out
+
+    def close(self):
+        if self.handle:
+            nbody_tree_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,87 @@
+"""CPU checks of the boundary: the C-ABI library loads and exports every
+symbol include/nbody.h declares; the generated kernel header is current."""
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "nbody.h")).read()
+    return sorted(set(re.findall(r"\b(nbody_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1407_2600_gb300 import build as B
+    B.build()
+    import paper_1407_2600_gb300.nbody as nb
+    lib = nb.lib()
+    names = _declared()
+    assert len(names) >= 10
+    for s in names:
+        assert hasattr(lib, s), s
+    assert sorted(nb.SYMBOLS) == names
+
+
+def test_defaults_and_strerror():
+    import paper_1407_2600_gb300.nbody as nb
+    p = nb.nbody_default_params()
+    assert p.order == 4 and p.n_group == 32 and p.ewald_order == 4 and p.lmax == 21
+    for code in range(0, -7, -1):
+        assert nb.nbody_strerror(code) != "unknown error"
+
+
+def test_invalid_arguments_are_rejected_without_gpu_work():
+    import paper_1407_2600_gb300.nbody as nb
+    p = nb.nbody_default_params()
+    rc, h = nb.nbody_build_tree(p, 0, 0, None)
+    assert rc == nb.NBODY_EINVAL and not h
+    p.eps = 0.0
+    rc, h = nb.nbody_build_tree(p, 10, 1, None)
+    assert rc == nb.NBODY_EINVAL and not h
+    p = nb.nbody_default_params()
+    p.n_direct = p.n_leaf + 1
+    rc, h = nb.nbody_build_tree(p, 10, 1, None)
+    assert rc == nb.NBODY_EINVAL
+    assert nb.nbody_forces(None, 0) == nb.NBODY_EINVAL
+
+
+def test_generated_kernel_header_is_current():
+    gen = os.path.join(ROOT, "paper_1407_2600_gb300", "csrc", "gen_m2p.py")
+    r = subprocess.run([sys.executable, gen, "--check"])
+    assert r.returncode == 0
+
+
+def test_reduced_m2p_matches_oracle_dtensor_form():
+    """The walk's reduced-coefficient M2P is algebraically the oracle's
+    Hermite-form contraction; check the generator's tables numerically."""
+    import math
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "paper_1407_2600_gb300", "csrc"))
+    import gen_m2p as G
+    import oracle as O
+    rng = np.random.default_rng(3)
+    for p in range(5):
+        sl, contrib = G.contributions(p)
+        M = rng.standard_normal(O.nmom(p))
+        B = np.array([sum(c * M[i] for i, c in cs) for cs in contrib])
+        R = rng.standard_normal(3) * 0.5
+        eps = 0.05
+        s = R @ R + eps ** 2
+        F = [((-1) ** j) * math.prod(range(1, 2 * j, 2)) * s ** (-0.5 - j) for j in range(p + 2)]
+        S = np.zeros(p + 1)
+        Gd = np.zeros((p + 1, 3))
+        for t, (j, a) in enumerate(sl):
+            S[j] += B[t] * R[0] ** a[0] * R[1] ** a[1] * R[2] ** a[2]
+            for d in range(3):
+                if a[d] > 0:
+                    aa = list(a)
+                    aa[d] -= 1
+                    Gd[j, d] += B[t] * a[d] * R[0] ** aa[0] * R[1] ** aa[1] * R[2] ** aa[2]
+        acc = sum(R * F[j + 1] * S[j] + F[j] * Gd[j] for j in range(p + 1))
+        ref = O.m2p(M, p, R, eps)
+        assert np.abs(acc - ref).max() <= 1e-13 * np.abs(ref).max()

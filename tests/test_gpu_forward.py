@@ -1,0 +1,214 @@
+"""GPU parity of the forward path (keys, sort, tree, hash, moments, walk,
+periodic images, KDK) against the FP64 CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_2600_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+def _nb():
+    import paper_1407_2600_gb300.nbody as nb
+    return nb
+
+
+def _pos(x, dev):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def _gpu_forces(x, dev, **kw):
+    import torch
+    nb = _nb()
+    tree = nb.Tree(nb.params(**kw), _pos(x, dev))
+    acc, st = tree.forces(stats=True)
+    torch.cuda.synchronize()
+    out = acc.cpu().numpy().T.astype(np.float64)
+    tree.close()
+    return out, st
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 4096, 10007])
+def test_keys_sort_bitexact(cuda, n):
+    nb = _nb()
+    rng = np.random.default_rng(n)
+    x = rng.uniform(0.0, 1.0, (n, 3))
+    if n > 100:
+        x[: n // 10] = x[0]  # many equal keys: stability decides the order
+    tree = nb.Tree(nb.params(eps=1e-3), _pos(x, cuda))
+    keys = tree.export("sorted_keys").cpu().numpy().view(np.uint64)
+    perm = tree.export("perm").cpu().numpy().astype(np.int64)
+    tree.close()
+    okeys = oracle.morton_keys(x)
+    operm = oracle.sort_perm(okeys)
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(keys, okeys[operm])
+
+
+@pytest.mark.parametrize("seed,n_leaf", [(1, 16), (2, 8), (3, 1)])
+def test_tree_topology_and_hash(cuda, seed, n_leaf):
+    import torch
+    nb = _nb()
+    x, eps = ics.config_small(seed)
+    if seed == 2:  # add a dense clump so the tree goes deep
+        x = np.concatenate([x, np.mod(0.3 + 1e-4 * np.random.default_rng(5).standard_normal((700, 3)), 1.0)])
+    tree = nb.Tree(nb.params(eps=eps, n_leaf=n_leaf, n_direct=0), _pos(x, cuda))
+    ck = tree.export("cell_keys").cpu().numpy().view(np.uint64)
+    rng_ = tree.export("cell_range").cpu().numpy()
+    lev = tree.export("cell_level").cpu().numpy()
+    okey, olev, ost, oct_ = oracle.tree_cells(x, n_leaf=n_leaf)
+    assert np.array_equal(ck, okey)
+    assert np.array_equal(lev, olev)
+    assert np.array_equal(rng_[:, 0], ost)
+    assert np.array_equal(rng_[:, 1], oct_)
+    # hash: every cell key maps to its index; absent keys map to -1
+    q = torch.tensor(np.concatenate([okey, okey[:50] ^ np.uint64(1 << 62)]).view(np.int64), device=cuda)
+    idx = tree.lookup(q).cpu().numpy()
+    assert np.array_equal(idx[: len(okey)], np.arange(len(okey)))
+    absent = okey[:50] ^ np.uint64(1 << 62)
+    present = set(okey.tolist())
+    exp = np.array([(-1 if int(k) not in present else -2) for k in absent])
+    assert np.all(idx[len(okey):][exp == -1] == -1)
+    tree.close()
+
+
+def test_moments_fp64(cuda):
+    nb = _nb()
+    x, eps = ics.config_small(4)
+    n = len(x)
+    tree = nb.Tree(nb.params(eps=eps, order=4), _pos(x, cuda))
+    M = tree.export("moments").cpu().numpy()
+    ck = tree.export("cell_keys").cpu().numpy().view(np.uint64)
+    rng_ = tree.export("cell_range").cpu().numpy()
+    lev = tree.export("cell_level").cpu().numpy()
+    perm = tree.export("perm").cpu().numpy()
+    tree.close()
+    xs = x[perm]
+    m = np.full(n, 1.0 / n, dtype=np.float32).astype(np.float64)
+    for c in range(0, len(ck), max(1, len(ck) // 200)):
+        l = int(lev[c])
+        pre = int(ck[c]) ^ (1 << (3 * l))
+        ix = [sum(((pre >> (3 * b + d)) & 1) << b for b in range(l)) for d in range(3)]
+        cen = np.array([(i + 0.5) / 2 ** l for i in ix])
+        s, k = rng_[c]
+        ref = oracle.p2m(xs[s:s + k], m[s:s + k], cen, 4)
+        scale = np.abs(ref).max()
+        assert np.max(np.abs(M[c] - ref)) <= 1e-12 * scale + 1e-300
+
+
+CASES = [
+    # (name, generator, theta, order)
+    ("zeldovich16_p2", lambda: ics.config_small(1), 0.5, 2),
+    ("zeldovich16_p4", lambda: ics.config_small(1), 0.5, 4),
+    ("haloes32_p4", lambda: ics.config_haloes(32, seed=2, n_halo=8, nmin=50, nmax=800), 0.6, 4),
+    ("ragged_p3", lambda: (np.random.default_rng(9).uniform(0, 1, (3001, 3)), 1e-3), 0.7, 3),
+]
+
+
+@pytest.mark.parametrize("name,gen,theta,order", CASES)
+def test_forces_vs_oracle_tree(cuda, name, gen, theta, order):
+    """Same method definition on both sides: differences are FP32 rounding."""
+    x, eps = gen()
+    nd = 2 if order <= 2 else 4
+    a, st = _gpu_forces(x, cuda, eps=eps, theta=theta, order=order, n_direct=nd)
+    ref, ost = oracle.tree_forces(x, None, oracle.tree_params(eps, theta, order, n_direct=nd, ewald=4),
+                                  return_stats=True)
+    rel = _rel(a, ref)
+    assert np.isfinite(a).all()
+    assert np.median(rel) <= 1e-5, (np.median(rel), np.percentile(rel, 99))
+    assert np.percentile(rel, 99) <= 1e-4, np.percentile(rel, 99)
+    # identical discrete decisions: interaction counts agree
+    assert st["m2p"] == ost["m2p"]
+    assert abs(st["p2p"] - (ost["p2p"] + len(x))) <= 1e-9 * ost["p2p"] + 0.5  # GPU counts the self pair
+
+
+def test_forces_fp64_mode(cuda):
+    x, eps = ics.config_small(2)
+    a, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=4, precision=1)
+    ref = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.5, 4, ewald=4))
+    rel = _rel(a, ref)
+    # FP64 arithmetic, FP32 output
+    assert np.max(rel) <= 1e-6
+
+
+def test_forces_vs_direct_ewald(cuda):
+    """Tree (mixed precision) against FP64 direct summation with Ewald images."""
+    x, eps = ics.config_small(1)
+    ad = oracle.direct_forces(x, None, eps, table_n1=64)
+    a4, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=4, n_direct=4)
+    rel = _rel(a4, ad)
+    assert np.median(rel) <= 1e-3 and np.percentile(rel, 99) <= 1e-2, (np.median(rel), np.percentile(rel, 99))
+    a0, _ = _gpu_forces(x, cuda, eps=eps, theta=1e-3, order=2, n_direct=2)
+    rel0 = _rel(a0, ad)
+    assert np.median(rel0) <= 1e-4
+
+
+def test_lattice_zero_force(cuda):
+    """Particles on a uniform lattice feel no force (symmetry)."""
+    q = ics.lattice(16)
+    a, _ = _gpu_forces(q, cuda, eps=1.0 / 480, theta=0.5, order=4)
+    # scale: force of one neighbour at one spacing
+    scale = (1.0 / 4096) / (1.0 / 16) ** 2
+    assert np.max(np.abs(a)) <= 1e-3 * scale
+
+
+def test_momentum_conservation_direct_limit(cuda):
+    x, eps = ics.config_small(5)
+    a, _ = _gpu_forces(x, cuda, eps=eps, theta=1e-3, order=2, n_direct=2)
+    tot = np.abs(a.sum(axis=0)).max() / len(x)
+    assert tot <= 1e-4 * np.abs(a).mean()
+
+
+def test_kdk_step_vs_oracle(cuda):
+    import torch
+    nb = _nb()
+    q, psi = ics.zeldovich_particles(16, -2.0, 0.25, 7)
+    a0, a1 = 0.05, 0.06
+    x0, p0 = oracle.zeldovich_state(q, psi / 0.05, a0)
+    eps = 1.0 / 480
+    op = oracle.tree_params(eps, 0.5, 4, ewald=4)
+    force = lambda xx: oracle.tree_forces(xx, None, op)
+    g0 = force(x0)
+    x1, p1, g1 = oracle.kdk_step(x0, p0, g0, a0, a1, force)
+    pos = _pos(x0, cuda)
+    tree = nb.Tree(nb.params(eps=eps, theta=0.5, order=4), pos)
+    acc = tree.forces()
+    mom = torch.tensor(p0.T.copy(), dtype=torch.float32, device=cuda)
+    tree.kdk_step(mom, acc, a0, a1)
+    torch.cuda.synchronize()
+    xg = tree.pos.cpu().numpy().T
+    dx = np.mod(xg - x1 + 0.5, 1.0) - 0.5
+    # the drift moves by D p with FP32 momenta that carry the mixed-precision
+    # force's relative error (<= 1e-5): the displacement is good to 1e-5
+    step = np.abs(np.mod(x1 - x0 + 0.5, 1.0) - 0.5).max()
+    assert np.max(np.abs(dx)) <= 1e-5 * step + 1e-13
+    pg = mom.cpu().numpy().T.astype(np.float64)
+    assert np.max(np.abs(pg - p1)) <= 1e-5 * np.abs(p1).max()
+    ag = acc.cpu().numpy().T.astype(np.float64)
+    assert np.median(_rel(ag, g1)) <= 1e-5
+    tree.close()
+
+
+def test_batched_boxes_match_single(cuda):
+    import torch
+    nb = _nb()
+    boxes = [ics.config_small(11)[0], ics.config_haloes(12, seed=3, n_halo=2, nmin=40, nmax=200)[0],
+             np.random.default_rng(4).uniform(0, 1, (777, 3))]
+    eps = [1.0 / 480, 1.0 / 360, 2e-3]
+    off = np.cumsum([0] + [len(b) for b in boxes])
+    xall = np.concatenate(boxes)
+    pos = _pos(xall, cuda)
+    prm = nb.params(eps=1e-3, theta=0.55, order=4)
+    tree = nb.Tree(prm, pos, offsets=off.tolist(), eps=eps)
+    acc = tree.forces().cpu().numpy().T.astype(np.float64)
+    tree.close()
+    for b, xb in enumerate(boxes):
+        ref = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.55, 4, ewald=4))
+        rel = _rel(acc[off[b]:off[b + 1]], ref)
+        assert np.median(rel) <= 1e-5, (b, np.median(rel))
