@@ -1,0 +1,350 @@
+"""Benchmark: tree-force particle updates per second on one GB300 per rank.
+
+A step is one kick-drift-kick step of the periodic treecode (keys, sort,
+tree, moments, group walk with P2P/M2P, image field, both kicks and the
+drift) on the 128^3 Zel'dovich + 64 NFW halo workload (L = 250 Mpc/h,
+theta = 0.6, hexadecapole, eps = spacing/30), inputs resident in HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun every rank runs an independent realisation (seed + rank) on
+its own GPU (weak scaling, no data-path collective); rank 0 prints one JSON
+line.  --impl reference times the FP64 CPU oracle tree on a bounded sample
+of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tree-force particle updates/s at median force err ≤1e-3; adjoint/forward ratio"
+UNIT = "particle updates/s"
+H0 = math.sqrt(8.0 * math.pi / 3.0)
+NG = 128
+A_START = 0.02
+DLNA = 0.1
+THETA = 0.6
+ORDER = 4
+EWALD_GRID = 5       # groups never straddle a level-4 cell (measured accuracy setting)
+FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FMA
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def workload(seed: int, ng: int = NG):
+    """Positions (n,3) and momenta (n,3) at a = A_START, plus eps.  ng < 128
+    scales the halo counts with the particle number (profiling runs)."""
+    from paper_1407_2600_gb300 import ics
+    q, psi = ics.zeldovich_particles(ng, -2.0, 0.6, seed)
+    x = np.mod(q + psi, 1.0)
+    # growing-mode momentum of the displacement psi at a: p = H0 a^(1/2) psi
+    p = H0 * math.sqrt(A_START) * psi
+    f = (ng / NG) ** 3
+    x, members, _ = ics.add_nfw_haloes(x, 64, max(2, int(2000 * f)), max(3, int(50000 * f)), 5.0, 15.0,
+                                       seed + 1000)
+    p[members] = 0.0  # halo particles start at rest (their centre's velocity is not modelled)
+    return x, p, 1.0 / (30.0 * ng)
+
+
+def m2p_flops(order: int) -> int:
+    """Flops per M2P of the generated kernel (FMA = 2, rsqrt = 1)."""
+    sys.path.insert(0, os.path.join(ROOT, "paper_1407_2600_gb300", "csrc"))
+    import gen_m2p
+    return gen_m2p.flop_count(order)
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_reference(x, eps, sample: int, seed: int):
+    """Time the FP64 CPU oracle tree on `sample` target particles; return the
+    implied whole-evaluation rate (particles/s) and details."""
+    import oracle
+    from paper_1407_2600_gb300 import ics
+    n = len(x)
+    prm = oracle.tree_params(eps, THETA, ORDER, n_direct=4, ewald=4, ew_grid=EWALD_GRID)
+    oracle.phitilde_lattice(EWALD_GRID, 5)  # build the oracle's table outside the timing
+    t0 = time.perf_counter()
+    oracle.tree_forces(x, None, prm, targets=np.array([0], dtype=np.int64))
+    t_build = time.perf_counter() - t0
+    tg = ics.random_targets(n, sample, seed)
+    t0 = time.perf_counter()
+    oracle.tree_forces(x, None, prm, targets=tg)
+    t_call = time.perf_counter() - t0
+    t_walk = max(t_call - t_build, 1e-9)
+    t_eval = t_build + t_walk / len(tg) * n
+    return n / t_eval, {"t_build_s": t_build, "t_walk_sample_s": t_walk, "targets": len(tg)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    x, _, eps = workload(1)
+    n = len(x)
+    rates = []
+    detail = None
+    for it in range(args.warmup + args.steps):
+        r, detail = cpu_reference(x, eps, 256, 100 + it)
+        if it >= args.warmup:
+            rates.append(r)
+    value = float(np.median(rates))
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "128^3 Zel'dovich (P~k^-2, rms 0.6 spacing) + 64 NFW haloes, theta=0.6, p=4",
+                   "n": n, "theta": THETA, "order": ORDER},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "FP64 CPU tree on 256 random targets per step (tree build + walk of "
+                                   "their groups), scaled to a whole force evaluation"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "detail": detail,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nb.lib()
+    x, p, eps = workload(1 + rank, args.ng)
+    n = len(x)
+    pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
+    mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
+    prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=4, ewald_grid=EWALD_GRID,
+                    flags=nb.NBODY_FLAG_ASYNC)
+    tree = nb.Tree(prm, pos)
+    acc = tree.forces()
+    a = A_START
+    for _ in range(args.warmup):
+        a1 = a * math.exp(DLNA)
+        tree.kdk_step(mom, acc, a, a1)
+        a = a1
+    torch.cuda.synchronize()
+    tree.timing(reset=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        a1 = a * math.exp(DLNA)
+        tree.kdk_step(mom, acc, a, a1)
+        a = a1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ck = clocks.stop()
+    rc = nb.nbody_check(tree.handle, nb._stream())
+    if rc != nb.NBODY_OK:
+        raise nb.NbodyError(rc, "timed KDK steps")
+    if world > 1:
+        torch.distributed.barrier()
+    tm = tree.timing(reset=True)
+    # max over ranks of the timed region
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n * args.steps / (t_max * 1e-3)
+
+    # roofline of the dominant kernel (the walk), from the timed region
+    evals = max(tm["evaluations"], 1)
+    walk_ms = tm["ms_walk"] / evals
+    flops = (tm["p2p"] * FP32_FLOPS_P2P + tm["m2p"] * m2p_flops(ORDER)) / evals
+    peak = fp32_peak_tflops(SM_MAX_MHZ)
+    achieved = flops / (walk_ms * 1e-3) / 1e12
+    phases = {k: tm[k] / max(tm["builds"] if k in ("ms_sort", "ms_build", "ms_upward") else evals, 1)
+              for k in ("ms_sort", "ms_build", "ms_upward", "ms_walk", "ms_periodic")}
+
+    # force evaluation alone (no kicks/drift, tree rebuilt each time)
+    fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fe0.record(stream)
+    for _ in range(args.steps):
+        tree.rebuild()
+        tree.forces(acc)
+    fe1.record(stream)
+    torch.cuda.synchronize()
+    force_ms = fe0.elapsed_time(fe1) / args.steps
+    tree.timing(reset=True)
+
+    # end to end through the C ABI with host buffers: H2D of the state, the
+    # step, D2H of the updated state, every step
+    e2e = None
+    if not args.no_e2e:
+        hpos = torch.empty((3, n), dtype=torch.float64, pin_memory=True)
+        hmom = torch.empty((3, n), dtype=torch.float32, pin_memory=True)
+        hacc = torch.empty((3, n), dtype=torch.float32, pin_memory=True)
+        hpos.copy_(pos)
+        hmom.copy_(mom)
+        hacc.copy_(acc)
+        torch.cuda.synchronize()
+        k2 = max(2, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            pos.copy_(hpos, non_blocking=True)
+            mom.copy_(hmom, non_blocking=True)
+            acc.copy_(hacc, non_blocking=True)
+            a1 = a * math.exp(DLNA)
+            tree.kdk_step(mom, acc, a, a1)
+            a = a1
+            hpos.copy_(pos, non_blocking=True)
+            hmom.copy_(mom, non_blocking=True)
+            hacc.copy_(acc, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * n * k2 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
+               "d2h_bytes_per_step": 48 * n}
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            rate, det = cpu_reference(x, eps, 128, 7)
+            base = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                    "sample": "FP64 CPU oracle tree: one build of all %d particles plus the walk of "
+                              "the groups of %d random targets, scaled to a whole evaluation" % (n, det["targets"]),
+                    "detail": det}
+        except Exception as exc:  # the oracle is optional on a box without a compiler
+            base = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                    "sample": "failed: %s" % exc}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": ("%d^3" % args.ng) + " Zel'dovich (P~k^-2, rms 0.6 spacing, a=0.02) + 64 NFW haloes "
+                                   "(2k-50k particles, c 5-15), L=250 Mpc/h, eps=spacing/30; one KDK step "
+                                   "of dln a = 0.1 per step",
+                       "n": n, "theta": THETA, "order": ORDER, "n_group": 32, "n_leaf": 16,
+                       "ewald_order": 4, "ewald_grid": EWALD_GRID, "precision": "FP32 interactions, "
+                       "FP64 positions/moments",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "dp%d (independent realisations)" % world},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "walk_kernel", "flops_per_launch": flops,
+                         "peak_note": "FP32 non-tensor: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "gpu_launches": tm["launches"] // 1,
+            "clocks": ck,
+            "phases_ms": phases,
+            "force_eval_ms": force_ms,
+            "force_updates_per_s": n / (force_ms * 1e-3),
+            "interactions_per_particle": {"p2p": tm["p2p"] / evals / n, "m2p": tm["m2p"] / evals / n},
+            "adjoint_forward_ratio": None,
+        }
+        print(json.dumps(line), flush=True)
+    tree.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ng", type=int, default=NG, help="particles per axis (128 = the benchmark workload)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

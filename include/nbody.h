@@ -174,6 +174,21 @@ int nbody_kdk_adjoint(nbody_tree *tree, const double *pos0_dev, const float *mom
 int nbody_forces_vjp(nbody_tree *tree, const float *lam_dev, double *out_dev,
                      nbody_stream_t stream);
 
+/*
+ * Device-time accounting for benchmarks.  Every build and force evaluation
+ * records CUDA events on its stream into a ring (the last 64 of each are
+ * kept); this call synchronises the tree's last stream, sums the phase times
+ * and interaction counts since the previous reset, and optionally resets.
+ */
+typedef struct {
+  int64_t builds;        /* tree builds timed */
+  int64_t evaluations;   /* force evaluations timed */
+  int64_t launches;      /* kernels launched by the library */
+  double p2p, m2p, m2l;  /* interactions summed over the evaluations */
+  double ms_sort, ms_build, ms_upward, ms_walk, ms_periodic; /* summed device times */
+} nbody_timing;
+int nbody_timing_read(nbody_tree *tree, nbody_timing *out, int reset);
+
 /* Tree inspection (tests).  what: */
 enum {
   NBODY_EXPORT_SORTED_KEYS = 1, /* uint64 per particle, key order */

@@ -52,6 +52,7 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
 namespace {
 
 constexpr int kStackCap = 8192;  // cells per warp stack
+constexpr int kRing = 64;        // timed builds / evaluations kept
 
 struct Buf {
   void* p = nullptr;
@@ -111,20 +112,29 @@ struct nbody_tree {
   int walk_blocks = 0;
   long long thr[NB_NLEV];
   int64_t* pinned = nullptr;
-  double last_p2p = 0, last_m2p = 0, last_m2l = 0;
-  cudaEvent_t ev[8];
+  // timing ring: builds (sort start, sort end, build end, moments end) and
+  // evaluations (walk start, walk end, periodic end)
+  cudaEvent_t bev[kRing][4];
+  cudaEvent_t fev[kRing][3];
   bool events = false;
+  int64_t nb_log = 0, nf_log = 0;
+  long long launches = 0;
+  Buf tot;  // accumulated p2p, m2p, m2l counters
+  cudaStream_t last_stream = nullptr;
 
   ~nbody_tree() {
     Buf* all[] = {&off, &box_of, &keys, &vals, &keys2, &vals2, &sbox, &spos, &smass, &src, &sleaf,
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
                   &hval, &mom, &arrive, &coef, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
-                  &eps2, &stack, &gctr, &accw, &counters};
+                  &eps2, &stack, &gctr, &accw, &counters, &tot};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     if (events)
-      for (auto& e : ev) cudaEventDestroy(e);
+      for (int r = 0; r < kRing; r++) {
+        for (auto& e : bev[r]) cudaEventDestroy(e);
+        for (auto& e : fev[r]) cudaEventDestroy(e);
+      }
   }
 
   DevTree dev() const {
@@ -237,6 +247,10 @@ __global__ void eps2_kernel(int nbox, const double* __restrict__ eps, float* __r
   }
 }
 
+__global__ void accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ tot) {
+  if (threadIdx.x < 3) tot[threadIdx.x] += c[threadIdx.x];
+}
+
 __global__ void max_level_kernel(int ncell, const int4* __restrict__ cA, int* out) {
   int m = 0;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x)
@@ -309,7 +323,9 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   sc.tiles_cap = tiles;
   sc.dstatus = t->status.as<unsigned>();
 
-  if (t->events) NB_CU(cudaEventRecord(t->ev[0], s));
+  cudaEvent_t* be = t->bev[t->nb_log % kRing];
+  t->last_stream = s;
+  NB_CU(cudaEventRecord(be[0], s));
   // A1 keys, A2 sort, A3 gather
   NB_CU(nb_launch_box_ids(t->off.as<int64_t>(), t->nbox, n, t->box_of.as<uint16_t>(), s));
   NB_CU(nb_launch_keys(t->pos, n, 0, t->keys.as<uint64_t>(), t->vals.as<uint32_t>(), s));
@@ -322,7 +338,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   }
   NB_CU(nb_gather(t->pos, t->mass, t->vals.as<uint32_t>(), t->box_of.as<uint16_t>(), t->off.as<int64_t>(), n,
                   t->spos.as<double>(), t->smass.as<float>(), t->sbox.as<uint16_t>(), s));
-  if (t->events) NB_CU(cudaEventRecord(t->ev[1], s));
+  NB_CU(cudaEventRecord(be[1], s));
   // A4 tree: cells per particle, scan, groups flags + scan, read totals
   NB_CU(nb_count_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, p.n_leaf, p.lmax,
                        t->ccount.as<int>(), t->l0.as<int8_t>(), s));
@@ -383,7 +399,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(nb_group_info(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), n, ngroup, ls, t->gflag.as<int>(),
                       t->gid.as<int>(), t->gstart.as<int>(), t->spos.as<double>(), t->gA.as<int4>(), t->gB.as<int4>(),
                       t->gC.as<int4>(), t->gD.as<int4>(), s));
-  if (t->events) NB_CU(cudaEventRecord(t->ev[2], s));
+  NB_CU(cudaEventRecord(be[2], s));
   // A5 moments
   NB_CU(nb_upward(p.order, fp64, ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
                   t->smass.as<float>(), n, t->mom.as<double>(), t->arrive.as<int>(), t->coef.p, s));
@@ -393,7 +409,8 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
     NB_CU(nb_field_moments(p.ewald_order, p.ewald_level, t->nbox, t->off.as<int64_t>(), t->keys.as<uint64_t>(),
                            t->spos.as<double>(), t->smass.as<float>(), n, t->fm.as<double>(), s));
   }
-  if (t->events) NB_CU(cudaEventRecord(t->ev[3], s));
+  NB_CU(cudaEventRecord(be[3], s));
+  t->nb_log++;
   return NBODY_OK;
 }
 
@@ -403,6 +420,10 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   const int64_t n = t->n;
   NB_CU(t->accw.ensure((fp64 ? 24 : 12) * n));
   NB_CU(t->counters.ensure(64));
+  if (!t->tot.p) {
+    NB_CU(t->tot.ensure(64));
+    NB_CU(cudaMemsetAsync(t->tot.p, 0, 64, s));
+  }
   NB_CU(t->gctr.ensure(64));
   const int warps = nb_walk_warps(fp64);
   if (t->walk_blocks == 0) t->walk_blocks = t->nsm * 8;
@@ -417,17 +438,22 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   if (p.ewald_order > 0) {
     NB_CU(nb_phitilde_table(p.ewald_grid, p.ewald_order + 1, &t->tab64, &t->tab32, s));
   }
-  if (t->events) NB_CU(cudaEventRecord(t->ev[4], s));
+  cudaEvent_t* fe = t->fev[t->nf_log % kRing];
+  t->last_stream = s;
+  NB_CU(cudaEventRecord(fe[0], s));
   DevTree tr = t->dev();
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
                 t->status.as<unsigned>(), t->nsm, s));
-  if (t->events) NB_CU(cudaEventRecord(t->ev[5], s));
+  NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
                     t->accw.p, acc, ctr + 2, s));
-  if (t->events) NB_CU(cudaEventRecord(t->ev[6], s));
+  NB_CU(cudaEventRecord(fe[2], s));
+  accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
+  nb_launch_counter += 1;
+  t->nf_log++;
   return NBODY_OK;
 }
 
@@ -458,7 +484,10 @@ int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, cons
       return NBODY_ECUDA;
     }
     cudaMemset(t->status.p, 0, 64);
-    for (auto& e : t->ev) cudaEventCreate(&e);
+    for (int r = 0; r < kRing; r++) {
+      for (auto& e : t->bev[r]) cudaEventCreate(&e);
+      for (auto& e : t->fev[r]) cudaEventCreate(&e);
+    }
     t->events = true;
   }
   t->prm = *params;
@@ -469,7 +498,9 @@ int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, cons
   t->h_off.assign(offsets, offsets + nbox + 1);
   t->h_eps.resize(nbox);
   for (int b = 0; b < nbox; b++) t->h_eps[b] = eps_host ? eps_host[b] : params->eps;
+  const long long l0 = nb_launch_counter;
   rc = build_impl(t, s);
+  t->launches += nb_launch_counter - l0;
   if (rc == NBODY_OK && !(params->flags & NBODY_FLAG_ASYNC)) rc = read_status(t, s);
   if (rc != NBODY_OK && fresh) {
     delete t;
@@ -516,7 +547,9 @@ int nbody_build_tree_batched(const nbody_params* params, int nbox, const int64_t
 int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_stream_t stream) {
   if (!tree || !acc_dev) return NBODY_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  const long long l0 = nb_launch_counter;
   int rc = forces_impl(tree, acc_dev, s);
+  tree->launches += nb_launch_counter - l0;
   if (rc) return rc;
   if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
   rc = read_status(tree, s);
@@ -542,11 +575,15 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_str
       cudaFree(ml);
     }
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, tree->ev[0], tree->ev[1]) == cudaSuccess) stats->ms_sort = ms;
-    if (cudaEventElapsedTime(&ms, tree->ev[1], tree->ev[2]) == cudaSuccess) stats->ms_build = ms;
-    if (cudaEventElapsedTime(&ms, tree->ev[2], tree->ev[3]) == cudaSuccess) stats->ms_upward = ms;
-    if (cudaEventElapsedTime(&ms, tree->ev[4], tree->ev[5]) == cudaSuccess) stats->ms_walk = ms;
-    if (cudaEventElapsedTime(&ms, tree->ev[5], tree->ev[6]) == cudaSuccess) stats->ms_periodic = ms;
+    cudaEvent_t* be = tree->bev[(tree->nb_log + kRing - 1) % kRing];
+    cudaEvent_t* fe = tree->fev[(tree->nf_log + kRing - 1) % kRing];
+    if (tree->nb_log > 0) {
+      if (cudaEventElapsedTime(&ms, be[0], be[1]) == cudaSuccess) stats->ms_sort = ms;
+      if (cudaEventElapsedTime(&ms, be[1], be[2]) == cudaSuccess) stats->ms_build = ms;
+      if (cudaEventElapsedTime(&ms, be[2], be[3]) == cudaSuccess) stats->ms_upward = ms;
+    }
+    if (cudaEventElapsedTime(&ms, fe[0], fe[1]) == cudaSuccess) stats->ms_walk = ms;
+    if (cudaEventElapsedTime(&ms, fe[1], fe[2]) == cudaSuccess) stats->ms_periodic = ms;
     cudaGetLastError();
   }
   return rc;
@@ -563,14 +600,18 @@ int nbody_kdk_step(nbody_tree* tree, double* pos_dev, float* mom_dev, float* acc
   const double K2 = 2.0 / H0 * (sqrt(a1) - sqrt(ah));
   const double D = 2.0 / H0 * (1.0 / sqrt(a0) - 1.0 / sqrt(a1));
   const int64_t n3 = 3 * tree->n;
+  const long long l0 = nb_launch_counter;
   kick_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, mom_dev, acc_dev, (float)K1);
   drift_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, pos_dev, mom_dev, D);
+  nb_launch_counter += 2;
   NB_CU(cudaGetLastError());
   int rc = build_impl(tree, s);
   if (rc) return rc;
   rc = forces_impl(tree, acc_dev, s);
   if (rc) return rc;
   kick_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, mom_dev, acc_dev, (float)K2);
+  nb_launch_counter += 1;
+  tree->launches += nb_launch_counter - l0;
   NB_CU(cudaGetLastError());
   if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
   return read_status(tree, s);
@@ -635,6 +676,49 @@ int nbody_tree_lookup(const nbody_tree* t, const uint64_t* keys_dev, int64_t nke
   NB_CU(nb_hash_lookup(keys_dev, nkeys, 0, t->hval.as<int>(), t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(),
                        t->hcap, (int*)idx_dev, s));
   NB_CU(cudaStreamSynchronize(s));
+  return NBODY_OK;
+}
+
+int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
+  if (!t || !out) return NBODY_EINVAL;
+  memset(out, 0, sizeof(*out));
+  NB_CU(cudaStreamSynchronize(t->last_stream));
+  const int64_t nb = t->nb_log < kRing ? t->nb_log : kRing;
+  const int64_t nf = t->nf_log < kRing ? t->nf_log : kRing;
+  for (int64_t r = 0; r < nb; r++) {
+    float a = 0, b = 0, c = 0;
+    cudaEvent_t* e = t->bev[(t->nb_log - 1 - r) % kRing];
+    NB_CU(cudaEventElapsedTime(&a, e[0], e[1]));
+    NB_CU(cudaEventElapsedTime(&b, e[1], e[2]));
+    NB_CU(cudaEventElapsedTime(&c, e[2], e[3]));
+    out->ms_sort += a;
+    out->ms_build += b;
+    out->ms_upward += c;
+  }
+  for (int64_t r = 0; r < nf; r++) {
+    float a = 0, b = 0;
+    cudaEvent_t* e = t->fev[(t->nf_log - 1 - r) % kRing];
+    NB_CU(cudaEventElapsedTime(&a, e[0], e[1]));
+    NB_CU(cudaEventElapsedTime(&b, e[1], e[2]));
+    out->ms_walk += a;
+    out->ms_periodic += b;
+  }
+  out->builds = nb;
+  out->evaluations = nf;
+  out->launches = t->launches;
+  if (t->tot.p) {
+    unsigned long long c[3] = {0, 0, 0};
+    NB_CU(cudaMemcpy(c, t->tot.p, sizeof(c), cudaMemcpyDeviceToHost));
+    out->p2p = (double)c[0];
+    out->m2p = (double)c[1];
+    out->m2l = (double)c[2];
+  }
+  if (reset) {
+    t->nb_log = 0;
+    t->nf_log = 0;
+    t->launches = 0;
+    if (t->tot.p) NB_CU(cudaMemset(t->tot.p, 0, 64));
+  }
   return NBODY_OK;
 }
 

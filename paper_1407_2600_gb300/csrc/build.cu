@@ -329,6 +329,7 @@ cudaError_t nb_gather(const double* pos, const float* mass, const uint32_t* perm
                       cudaStream_t s) {
   sbox_kernel<<<gridn(n, 256), 256, 0, s>>>(perm, box_of, n, sbox);
   gather_kernel<<<gridn(n, 256), 256, 0, s>>>(pos, mass, perm, sbox, off, n, spos, smass);
+  nb_launch_counter += 2;
   return cudaGetLastError();
 }
 
@@ -336,6 +337,7 @@ cudaError_t nb_count_cells(const uint64_t* skeys, const uint16_t* sbox, const in
                            int n_leaf, int lmax, int* ccount, int8_t* l0, cudaStream_t s) {
   BuildArgs a{skeys, sbox, off, n, n_leaf, lmax};
   count_cells_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ccount, l0);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -344,6 +346,7 @@ cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int
                           uint8_t* plevel, int* pstart, int* pcount, int* pparent, cudaStream_t s) {
   BuildArgs a{skeys, sbox, off, n, n_leaf, lmax};
   emit_cells_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ccount, coff, l0, plevel, pstart, pcount, pparent);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -357,6 +360,7 @@ cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell,
                                                      pparent, cA, cB, ckey, cbox);
   children_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, cB);
   nchild_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, cA, cB);
+  nb_launch_counter += 4;
   return cudaGetLastError();
 }
 
@@ -365,12 +369,14 @@ cudaError_t nb_hash_build(int ncell, const uint64_t* ckey, const uint16_t* cbox,
   cudaError_t e = cudaMemsetAsync(hval, 0xff, sizeof(int) * cap, s);
   if (e) return e;
   hash_insert_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, ckey, cbox, hval, cap - 1, err);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
 cudaError_t nb_hash_lookup(const uint64_t* q, int64_t nq, int box, const int* hval, const uint64_t* ckey,
                            const uint16_t* cbox, uint64_t cap, int* out, cudaStream_t s) {
   hash_lookup_kernel<<<gridn(nq, 256), 256, 0, s>>>(q, nq, box, hval, ckey, cbox, cap - 1, out);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -382,6 +388,7 @@ cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* s
   else
     leaf_kernel<float><<<gridn(ncell, 128), 128, 0, s>>>(ncell, cA, cB, spos, smass, n, sleaf,
                                                          (float4*)src);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -389,6 +396,7 @@ cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const in
                            int ls, int n_group, int* flag, cudaStream_t s) {
   BuildArgs a{skeys, sbox, off, n, 0, 0};
   group_flag_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ls, n_group, flag);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -399,5 +407,6 @@ cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n
   group_start_kernel<<<gridn(n, 256), 256, 0, s>>>(n, flag, gid, gstart);
   group_info_kernel<<<gridn((int64_t)ngroup * 32, 256), 256, 0, s>>>(a, ngroup, ls, gstart, spos, gA, gB,
                                                                       gC, gD);
+  nb_launch_counter += 2;
   return cudaGetLastError();
 }

@@ -91,6 +91,9 @@ struct DevTree {
   const int* sleaf;        // leaf cell of each sorted particle
 };
 
+// kernels launched by this thread through the library (benchmark accounting)
+extern thread_local long long nb_launch_counter;
+
 // ---- host launchers (each returns cudaError_t of the launch) ---------------------
 cudaError_t nb_launch_keys(const double* pos, int64_t n, int64_t box_n0, uint64_t* keys,
                            uint32_t* vals, cudaStream_t s);

@@ -75,9 +75,11 @@ def contributions(p):
 
 
 def flop_count(p):
-    """Flops of the generated M2P (FMA = 2, rsqrt = 1), excluding R = x - c."""
+    """Flops of one M2P as the walk runs it (FMA = 2, rsqrt = 1): R = x - c
+    (3), the scaling of R and eps^2 to the cell's unit (4), and the generated
+    expansion."""
     mon = multi(p)
-    fl = 0
+    fl = 7
     fl += 6  # s = eps2 + Rx^2 + Ry^2 + Rz^2: 3 FMA
     fl += 1  # rsqrt
     fl += 1  # inv_s = F0*F0

@@ -3,15 +3,15 @@
 #pragma once
 
 constexpr int kNB0 = 1;  // reduced coefficients at order 0
-constexpr int kM2PFlops0 = 25;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops0 = 32;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB1 = 4;  // reduced coefficients at order 1
-constexpr int kM2PFlops1 = 55;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops1 = 62;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB2 = 11;  // reduced coefficients at order 2
-constexpr int kM2PFlops2 = 111;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops2 = 118;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB3 = 24;  // reduced coefficients at order 3
-constexpr int kM2PFlops3 = 213;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops3 = 220;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB4 = 46;  // reduced coefficients at order 4
-constexpr int kM2PFlops4 = 386;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops4 = 393;  // flops per M2P (FMA = 2, rsqrt = 1)
 
 template <typename T>
 __device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,

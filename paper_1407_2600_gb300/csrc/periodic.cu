@@ -401,6 +401,7 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
   if (pe == 0) {
     if (fp64) scatter_kernel<double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out);
     else scatter_kernel<float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out);
+    nb_launch_counter += 1;
     return cudaGetLastError();
   }
   int grid = (int)(((int64_t)tr.ngroup * 32 + 127) / 128);
@@ -431,5 +432,6 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
     }
   }
 #undef NB_PER
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }

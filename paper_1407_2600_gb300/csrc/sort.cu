@@ -348,11 +348,14 @@ int grid_for(int64_t n, int threads, int cap = 152 * 32) {
 
 }  // namespace
 
+thread_local long long nb_launch_counter = 0;
+
 int64_t nb_sort_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
 
 cudaError_t nb_launch_keys(const double* pos, int64_t n, int64_t, uint64_t* keys, uint32_t* vals,
                            cudaStream_t s) {
   keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(pos, n, keys, vals);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -360,6 +363,7 @@ cudaError_t nb_launch_box_ids(const int64_t* off, int nbox, int64_t n, uint16_t*
                               cudaStream_t s) {
   dim3 g(grid_for(n / (nbox > 0 ? nbox : 1) + 1, 256, 256), nbox < 65535 ? nbox : 65535);
   box_ids_kernel<<<g, 256, 0, s>>>(off, nbox, box_of);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -394,6 +398,7 @@ cudaError_t nb_radix_sort(uint64_t* keys, uint32_t* vals, int64_t n, int bit1,
     vb = tv;
   }
   *result_in_alt = (np & 1);
+  nb_launch_counter += 2 + np;
   return cudaGetLastError();
 }
 
@@ -412,6 +417,7 @@ cudaError_t nb_sort_digit8(const uint8_t* digit, int64_t n, uint32_t* order_out,
   hist_scan_kernel<<<1, 256, 0, s>>>(sc->hist);
   digit_sweep_kernel<<<(unsigned)tiles, kSortThreads, 0, s>>>(digit, n, sc->hist, sc->status,
                                                                sc->tile_ctr, order_out, sc->dstatus);
+  nb_launch_counter += 3;
   return cudaGetLastError();
 }
 
@@ -424,5 +430,6 @@ cudaError_t nb_exclusive_scan_i32(const int* in, int* out, int64_t n, int* total
   scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
   scan_sums_kernel<<<1, 1024, 0, s>>>(tmp, nb, total_dev);
   scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
+  nb_launch_counter += 3;
   return cudaGetLastError();
 }

@@ -38,15 +38,30 @@ NB_ORD(2)
 NB_ORD(3)
 NB_ORD(4)
 
+// Reduced coefficients in the cell's own length unit h = 2^-level: with
+// R' = R/h and eps' = eps/h the expansion terms are O(1) for every accepted
+// cell (R' >= 1/theta), so FP32 intermediates cannot overflow however deep the
+// cell; a = h^-2 sum(...) is folded into the coefficients as B'' =
+// h^-2 B(M_n h^-|n|).  All scalings are exact powers of two.
 template <int P, typename T>
-__device__ __forceinline__ void finish_cell(int c, const double* M, T* __restrict__ coef) {
+__device__ __forceinline__ void finish_cell(int c, int level, const double* M, T* __restrict__ coef) {
+  constexpr int NM = Ord<P>::NM;
+  double Ms[NM];
+  int t = 0;
+#pragma unroll
+  for (int o = 0; o <= P; o++) {
+    const double sc = ldexp(1.0, level * o);
+#pragma unroll
+    for (int q = 0; q < (o + 1) * (o + 2) / 2; q++, t++) Ms[t] = M[t] * sc;
+  }
   double B[Ord<P>::NB];
-  Ord<P>::reduce(M, B);
+  Ord<P>::reduce(Ms, B);
   T* dst = coef + (int64_t)c * Ord<P>::NBS;
+  const double s2 = ldexp(1.0, 2 * level);
 #pragma unroll
-  for (int t = 0; t < Ord<P>::NB; t++) dst[t] = (T)B[t];
+  for (int q = 0; q < Ord<P>::NB; q++) dst[q] = (T)(B[q] * s2);
 #pragma unroll
-  for (int t = Ord<P>::NB; t < Ord<P>::NBS; t++) dst[t] = (T)0;
+  for (int q = Ord<P>::NB; q < Ord<P>::NBS; q++) dst[q] = (T)0;
 }
 
 template <int P, typename T>
@@ -68,7 +83,7 @@ upward_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ c
     double* dst = mom + (int64_t)b * NM;
 #pragma unroll
     for (int t = 0; t < NM; t++) dst[t] = M[t];
-    finish_cell<P, T>(b, M, coef);
+    finish_cell<P, T>(b, a.w & 0xff, M, coef);
     int c = b;
     while (true) {
       int par = cB[c].w;
@@ -94,7 +109,7 @@ upward_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ c
       double* pd = mom + (int64_t)par * NM;
 #pragma unroll
       for (int t = 0; t < NM; t++) pd[t] = M[t];
-      finish_cell<P, T>(par, M, coef);
+      finish_cell<P, T>(par, pa.w & 0xff, M, coef);
       c = par;
     }
   }
@@ -200,6 +215,7 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int
     default: NB_UP(4) break;
   }
 #undef NB_UP
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
@@ -213,5 +229,6 @@ cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const
     case 4: field_moments_kernel<4><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
     default: field_moments_kernel<5><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
   }
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }

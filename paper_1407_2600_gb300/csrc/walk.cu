@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   constexpr int NBS = WOrd<P>::NBS;
   __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
   __shared__ V4 s_src[WARPS][32];
-  __shared__ T s_moff[WARPS][32][3];
+  __shared__ T s_moff[WARPS][32][4];  // centre offset and, in [3], the cell scale 2^level
   __shared__ int s_midx[WARPS][32];
   __shared__ int s_pfx[WARPS][32];
   __shared__ int s_pst[WARPS][32];
@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           s_moff[wid][pos][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
           s_moff[wid][pos][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
           s_moff[wid][pos][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
+          s_moff[wid][pos][3] = (T)(1 << lvl);
         }
         __syncwarp();
         for (int t = lane; t < nmp * NBS; t += 32) {
@@ -196,9 +197,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         __syncwarp();
         if (act) {
           T px = 0, py = 0, pz = 0;
-          for (int q = 0; q < nmp; q++)
-            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], xi - s_moff[wid][q][0], yi - s_moff[wid][q][1],
-                                     zi - s_moff[wid][q][2], eps2, px, py, pz);
+          // each M2P runs in its cell's unit (coordinates times 2^level,
+          // coefficients pre-scaled): see the upward pass
+          for (int q = 0; q < nmp; q++) {
+            const T sc = s_moff[wid][q][3];
+            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], (xi - s_moff[wid][q][0]) * sc,
+                                     (yi - s_moff[wid][q][1]) * sc, (zi - s_moff[wid][q][2]) * sc,
+                                     eps2 * (sc * sc), px, py, pz);
+          }
           kadd(ax, cx, px);
           kadd(ay, cy, py);
           kadd(az, cz, pz);
@@ -298,6 +304,7 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
   int grid = nsm * (occ > 0 ? occ : 1);
   if (grid > max_blocks) grid = max_blocks;
   walk_kernel<T, P, WARPS, MINB><<<grid, WARPS * 32, 0, s>>>(a);
+  nb_launch_counter += 1;
   return cudaGetLastError();
 }
 

@@ -32,7 +32,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces",
            "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
-           "nbody_strerror"]
+           "nbody_strerror", "nbody_timing_read"]
 
 
 class Params(C.Structure):
@@ -47,6 +47,16 @@ class Stats(C.Structure):
                 ("ncells", C.c_int64), ("ngroups", C.c_int64), ("max_level", C.c_int32),
                 ("nbox", C.c_int32), ("ms_sort", C.c_float), ("ms_build", C.c_float),
                 ("ms_upward", C.c_float), ("ms_walk", C.c_float), ("ms_periodic", C.c_float)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Timing(C.Structure):
+    _fields_ = [("builds", C.c_int64), ("evaluations", C.c_int64), ("launches", C.c_int64),
+                ("p2p", C.c_double), ("m2p", C.c_double), ("m2l", C.c_double),
+                ("ms_sort", C.c_double), ("ms_build", C.c_double), ("ms_upward", C.c_double),
+                ("ms_walk", C.c_double), ("ms_periodic", C.c_double)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +96,7 @@ def lib():
         L.nbody_check.argtypes = [_vp, _vp]
         L.nbody_tree_free.argtypes = [_vp]
         L.nbody_tree_free.restype = None
+        L.nbody_timing_read.argtypes = [_vp, C.POINTER(Timing), C.c_int]
         L.nbody_strerror.argtypes = [C.c_int]
         L.nbody_strerror.restype = C.c_char_p
         _LIB = L
@@ -163,6 +174,10 @@ def nbody_tree_free(tree: int) -> None:
         lib().nbody_tree_free(tree)
 
 
+def nbody_timing_read(tree: int, out: Timing, reset: int) -> int:
+    return lib().nbody_timing_read(tree, C.byref(out), reset)
+
+
 def nbody_strerror(code: int) -> str:
     return lib().nbody_strerror(code).decode()
 
@@ -220,6 +235,11 @@ class Tree:
     def kdk_step(self, mom, acc, a0, a1):
         _check(nbody_kdk_step(self.handle, self.pos.data_ptr(), mom.data_ptr(), acc.data_ptr(), a0, a1,
                               _stream()), "nbody_kdk_step")
+
+    def timing(self, reset=True):
+        t = Timing()
+        _check(nbody_timing_read(self.handle, t, 1 if reset else 0), "nbody_timing_read")
+        return t.asdict()
 
     def export(self, what: str):
         import torch

@@ -108,6 +108,9 @@ CASES = [
     ("zeldovich16_p4", lambda: ics.config_small(1), 0.5, 4),
     ("haloes32_p4", lambda: ics.config_haloes(32, seed=2, n_halo=8, nmin=50, nmax=800), 0.6, 4),
     ("ragged_p3", lambda: (np.random.default_rng(9).uniform(0, 1, (3001, 3)), 1e-3), 0.7, 3),
+    # one concentrated halo holding half the particles: a deep tree whose
+    # small cells are accepted at small distances (FP32 range of the M2P)
+    ("dense_halo_p4", lambda: ics.config_haloes(16, seed=5, n_halo=1, nmin=2000, nmax=2001), 0.6, 4),
 ]
 
 

@@ -1,0 +1,91 @@
+"""Full-size parity on the benchmark workload (128^3 Zel'dovich + 64 NFW
+haloes): keys, sort and tree topology exactly against the oracle, forces on
+a seeded sample of particles against the oracle tree and the direct Ewald sum."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_2600_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    x, eps = ics.config_haloes(128, seed=1)
+    return x, eps
+
+
+def _tree(x, dev, **kw):
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
+    return nb.Tree(nb.params(**kw), pos)
+
+
+def test_fullsize_sort_and_topology(cuda, cfg2):
+    x, eps = cfg2
+    tree = _tree(x, cuda, eps=eps)
+    keys = tree.export("sorted_keys").cpu().numpy().view(np.uint64)
+    perm = tree.export("perm").cpu().numpy().astype(np.int64)
+    ck = tree.export("cell_keys").cpu().numpy().view(np.uint64)
+    lev = tree.export("cell_level").cpu().numpy()
+    rng_ = tree.export("cell_range").cpu().numpy()
+    tree.close()
+    okeys = oracle.morton_keys(x)
+    operm = oracle.sort_perm(okeys)
+    assert np.array_equal(keys, okeys[operm]), "sorted keys differ"
+    assert np.array_equal(perm, operm), "permutation differs"
+    okey, olev, ost, oct_ = oracle.tree_cells(x, n_leaf=16)
+    assert len(ck) == len(okey), (len(ck), len(okey))
+    assert np.array_equal(lev, olev)
+    assert np.array_equal(ck, okey)
+    assert np.array_equal(rng_[:, 0], ost) and np.array_equal(rng_[:, 1], oct_)
+
+
+def _forces(x, dev, **kw):
+    import torch
+    tree = _tree(x, dev, **kw)
+    acc, st = tree.forces(stats=True)
+    torch.cuda.synchronize()
+    a = acc.cpu().numpy().T.astype(np.float64)
+    tree.close()
+    return a, st
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+@pytest.mark.parametrize("theta,order,grid", [(0.6, 4, 5), (0.5, 2, 6)])
+def test_fullsize_forces_vs_oracle_tree(cuda, cfg2, theta, order, grid):
+    x, eps = cfg2
+    nd = 2 if order <= 2 else 4
+    a, st = _forces(x, cuda, eps=eps, theta=theta, order=order, n_direct=nd, ewald_grid=grid)
+    assert np.isfinite(a).all()
+    tg = ics.random_targets(len(x), 1024, 3)
+    ref = oracle.tree_forces(x, None, oracle.tree_params(eps, theta, order, n_direct=nd, ewald=4, ew_grid=grid),
+                             targets=tg)
+    rel = _rel(a[tg], ref)
+    assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (np.median(rel), np.percentile(rel, 99))
+
+
+@pytest.fixture(scope="module")
+def cfg2_direct(cfg2):
+    x, eps = cfg2
+    tg = ics.random_targets(len(x), 256, 5)
+    return tg, oracle.direct_forces(x, None, eps, targets=tg, table_n1=128)
+
+
+def test_fullsize_error_vs_direct_ewald(cuda, cfg2, cfg2_direct):
+    """The benchmark setting's force error against FP64 direct summation."""
+    x, eps = cfg2
+    tg, ad = cfg2_direct
+    a, _ = _forces(x, cuda, eps=eps, theta=0.6, order=4, n_direct=4, ewald_grid=5)
+    rel = _rel(a[tg], ad)
+    print("theta=0.6 p=4: median %.3e p99 %.3e" % (np.median(rel), np.percentile(rel, 99)))
+    assert np.median(rel) <= 1e-3
+    a, _ = _forces(x, cuda, eps=eps, theta=0.5, order=4, n_direct=4, ewald_grid=6)
+    rel = _rel(a[tg], ad)
+    print("theta=0.5 p=4: median %.3e p99 %.3e" % (np.median(rel), np.percentile(rel, 99)))
+    assert np.median(rel) <= 1e-3 and np.percentile(rel, 99) <= 1e-2
