@@ -39,6 +39,10 @@ THETA = 0.6
 ORDER = 4
 EWALD_GRID = 5       # groups never straddle a level-4 cell (measured accuracy setting)
 FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FMA
+# DRAM traffic of one walk launch from the ncu capture summarised in
+# profiles/walk_kernel_haloes96.md, scaled to 2^21 particles; valid only while
+# the walk's sources are unchanged since that capture
+WALK_TRAFFIC = {"bytes": 124e6, "source_sha": "66456c7f86ad5907"}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -64,6 +68,14 @@ def m2p_flops(order: int) -> int:
     sys.path.insert(0, os.path.join(ROOT, "paper_1407_2600_gb300", "csrc"))
     import gen_m2p
     return gen_m2p.flop_count(order)
+
+
+def walk_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("walk.cu", "m2p_gen.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1407_2600_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def fp32_peak_tflops(mhz: float) -> float:
@@ -301,7 +313,9 @@ def run_gpu(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "dp%d (independent realisations)" % world},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (WALK_TRAFFIC["bytes"] if args.ng == NG and
+                                     walk_source_sha() == WALK_TRAFFIC["source_sha"] else None),
                          "kernel": "walk_kernel", "flops_per_launch": flops,
                          "peak_note": "FP32 non-tensor: 152 SMs x 128 lanes x 2 x 2070 MHz"},
             "cpu_baseline": base,

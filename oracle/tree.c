@@ -22,9 +22,10 @@
  *           centre to the nearest image of the group box; a cell of level
  *           l >= 2 is accepted iff d2 > floor(s*s/(theta*theta)), s = 2^(23-l).
  *  images   every particle is used at the image of its level-ew_level
- *           ancestor cell nearest the group centre g; a cell above that level
- *           is accepted only if all its level-ew_level descendants share one
- *           image (else it is opened), and the MAC distance uses that image.
+ *           ancestor cell nearest e, the centre of the group's
+ *           level-(ew_grid-1) cell; a cell above that level is accepted only
+ *           if all its level-ew_level descendants share one image (else it is
+ *           opened), and the MAC distance uses that image.
  *  M2P      a_k = sum_{|n|<=p} ((-1)^|n|/n!) M_n d^{n+e_k} g(R), R = x - c*,
  *           g = (|R|^2 + eps^2)^-1/2, moments about the geometric centre.
  *  P2P      a += m_j r / (|r|^2 + eps^2)^(3/2), r = x_j* - x_i, j != i.
@@ -322,11 +323,11 @@ static int cell_image(const walkctx *w, const tgroup *G, int level, const int64_
   for (int d = 0; d < 3; d++) {
     if (level >= le) {
       int64_t a = ix[d] >> (level - le);
-      k[d] = img_shift(2 * centre_u(a, le), G->g2[d]);
+      k[d] = img_shift(2 * centre_u(a, le), G->cell2[d]);
     } else {
       int64_t lo = ix[d] << (le - level), hi = ((ix[d] + 1) << (le - level)) - 1;
-      int64_t klo = img_shift(2 * centre_u(lo, le), G->g2[d]);
-      int64_t khi = img_shift(2 * centre_u(hi, le), G->g2[d]);
+      int64_t klo = img_shift(2 * centre_u(lo, le), G->cell2[d]);
+      int64_t khi = img_shift(2 * centre_u(hi, le), G->cell2[d]);
       if (klo != khi) return 0;
       k[d] = klo;
     }
@@ -377,7 +378,7 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
         int64_t jx[3] = {quant(w->X[j]) >> (QBITS - le), quant(w->Y[j]) >> (QBITS - le),
                          quant(w->Z[j]) >> (QBITS - le)};
         int64_t kj[3];
-        for (int d = 0; d < 3; d++) kj[d] = img_shift(2 * centre_u(jx[d], le), G->g2[d]);
+        for (int d = 0; d < 3; d++) kj[d] = img_shift(2 * centre_u(jx[d], le), G->cell2[d]);
         double r[3] = {w->X[j] - (double)kj[0] - xi[0], w->Y[j] - (double)kj[1] - xi[1],
                        w->Z[j] - (double)kj[2] - xi[2]};
         double q = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + e2;
@@ -412,7 +413,7 @@ static void periodic_group(const walkctx *w, const tgroup *G, double *acc, wstat
     double cst[3];
     for (int d = 0; d < 3; d++) {
       int64_t c2 = 2 * centre_u(ix[d], le);
-      k[d] = img_shift(c2, G->g2[d]);
+      k[d] = img_shift(c2, e2[d]);
       ir[d] = (e2[d] - (c2 - k[d] * PBOX)) / step;
       cst[d] = ldexp((double)c2, -23) - (double)k[d];
     }

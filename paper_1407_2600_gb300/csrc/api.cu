@@ -31,6 +31,8 @@ cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* s
                       int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s);
 cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int ls,
                            int n_group, int* flag, cudaStream_t s);
+cudaError_t nb_group_runs(int ngroup, int4* gA, int4* gD, int* flag, int* excl, int* total, int* tmp,
+                          cudaStream_t s);
 cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, int ls,
                           const int* flag, const int* gid, int* gstart, const double* spos, int4* gA, int4* gB,
                           int4* gC, int4* gD, cudaStream_t s);
@@ -45,8 +47,9 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
                     cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
+int nb_field_stride(int pe);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
-                        const void* tab, const void* accw, float* out, unsigned long long* counter,
+                        const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         cudaStream_t s);
 
 namespace {
@@ -108,7 +111,7 @@ struct nbody_tree {
   const double* tab64 = nullptr;
   const float* tab32 = nullptr;
   // walk
-  Buf eps2, stack, gctr, accw, counters;
+  Buf eps2, stack, gctr, accw, counters, lbuf;
   int walk_blocks = 0;
   long long thr[NB_NLEV];
   int64_t* pinned = nullptr;
@@ -127,7 +130,7 @@ struct nbody_tree {
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
                   &hval, &mom, &arrive, &coef, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
-                  &eps2, &stack, &gctr, &accw, &counters, &tot};
+                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     if (events)
@@ -399,6 +402,8 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(nb_group_info(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), n, ngroup, ls, t->gflag.as<int>(),
                       t->gid.as<int>(), t->gstart.as<int>(), t->spos.as<double>(), t->gA.as<int4>(), t->gB.as<int4>(),
                       t->gC.as<int4>(), t->gD.as<int4>(), s));
+  NB_CU(nb_group_runs(ngroup, t->gA.as<int4>(), t->gD.as<int4>(), t->gflag.as<int>(), t->gid.as<int>(),
+                      totals + 2, t->scantmp.as<int>(), s));
   NB_CU(cudaEventRecord(be[2], s));
   // A5 moments
   NB_CU(nb_upward(p.order, fp64, ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
@@ -448,8 +453,10 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
                 t->status.as<unsigned>(), t->nsm, s));
   NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
+  if (p.ewald_order > 0)
+    NB_CU(t->lbuf.ensure((fp64 ? 8 : 4) * (int64_t)t->ngroup * nb_field_stride(p.ewald_order)));
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
-                    t->accw.p, acc, ctr + 2, s));
+                    t->lbuf.p, t->accw.p, acc, ctr + 2, s));
   NB_CU(cudaEventRecord(fe[2], s));
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
   nb_launch_counter += 1;

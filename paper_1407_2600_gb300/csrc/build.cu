@@ -286,6 +286,27 @@ __global__ void group_info_kernel(BuildArgs a, int ngroup, int ls, const int* __
   }
 }
 
+// groups sharing an expansion cell (same box, same level-(grid-1) cell) form
+// a run; gA.w = 1 marks a run's first group, gD.w receives the run index
+__global__ void run_flag_kernel(int ngroup, int4* __restrict__ gA, const int4* __restrict__ gD,
+                                int* __restrict__ flag) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x) {
+    bool first = g == 0;
+    if (!first) {
+      const int4 a = gD[g], b = gD[g - 1];
+      first = a.x != b.x || a.y != b.y || a.z != b.z || gA[g].z != gA[g - 1].z;
+    }
+    gA[g].w = first ? 1 : 0;
+    flag[g] = first ? 1 : 0;
+  }
+}
+
+__global__ void run_index_kernel(int ngroup, const int* __restrict__ flag, const int* __restrict__ excl,
+                                 int4* __restrict__ gD) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x)
+    gD[g].w = excl[g] + flag[g] - 1;
+}
+
 __global__ void gather_kernel(const double* __restrict__ pos, const float* __restrict__ mass,
                               const uint32_t* __restrict__ perm, const uint16_t* __restrict__ sbox,
                               const int64_t* __restrict__ off, int64_t n, double* __restrict__ spos,
@@ -388,6 +409,17 @@ cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* s
   else
     leaf_kernel<float><<<gridn(ncell, 128), 128, 0, s>>>(ncell, cA, cB, spos, smass, n, sleaf,
                                                          (float4*)src);
+  nb_launch_counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t nb_group_runs(int ngroup, int4* gA, int4* gD, int* flag, int* excl, int* total, int* tmp,
+                          cudaStream_t s) {
+  run_flag_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(ngroup, gA, gD, flag);
+  nb_launch_counter += 1;
+  cudaError_t e = nb_exclusive_scan_i32(flag, excl, ngroup, total, tmp, s);
+  if (e) return e;
+  run_index_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(ngroup, flag, excl, gD);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }

@@ -17,8 +17,11 @@ so that, with d_i F_j = R_i F_{j+1},
 
     a_i = d_i phi = sum_j ( R_i F_{j+1} S_j + F_j d_i S_j ).
 
-The per-cell coefficients B_{j,a} are formed once in the upward pass (FP64)
-and stored in the walk's precision; each M2P then costs a few hundred flops.
+The per-cell coefficients are stored as a! B_{j,a} with the divided monomials
+mu_a = R^a / a!, so that d_i mu_a = mu_{a - e_i} exactly and the gradient sums
+need no integer factors (every term is one fused multiply-add).  They are
+formed once in the upward pass (FP64) and stored in the walk's precision;
+each M2P then costs a few hundred flops.
 Run ``python gen_m2p.py`` to regenerate; a CPU test checks that the committed
 header equals this script's output.
 """
@@ -75,24 +78,21 @@ def contributions(p):
 
 
 def flop_count(p):
-    """Flops of one M2P as the walk runs it (FMA = 2, rsqrt = 1): R = x - c
-    (3), the scaling of R and eps^2 to the cell's unit (4), and the generated
-    expansion."""
+    """Flops of one M2P as the walk runs it (FMA = 2, rsqrt = 1): the scaled
+    separation R = (x - c) 2^level as 3 FMA, eps^2 scaled per cell (0), and
+    the generated expansion."""
     mon = multi(p)
-    fl = 7
-    fl += 6  # s = eps2 + Rx^2 + Ry^2 + Rz^2: 3 FMA
-    fl += 1  # rsqrt
-    fl += 1  # inv_s = F0*F0
+    fl = 6            # R: 3 FMA
+    fl += 6           # s = eps2 + Rx^2 + Ry^2 + Rz^2: 3 FMA
+    fl += 1           # rsqrt
+    fl += 1           # inv_s = F0*F0
     fl += 2 * (p + 1)  # F_j chain: c_j = k*inv_s, F_j = F_{j-1}*c_j
-    fl += len(mon) - 1  # monomials
+    fl += 3 * max(p - 1, 0)  # R_d / k for k = 2..p
+    fl += len(mon) - 1  # divided monomials
     sl = slots(p)
     for (j, a) in sl:
         fl += 2  # S_j FMA
-        for d in range(3):
-            if a[d] > 0:
-                fl += 2  # G_{j,d} FMA
-                if a[d] > 1:
-                    fl += 1  # integer scale
+        fl += 2 * sum(1 for d in range(3) if a[d] > 0)  # G_{j,d} FMA
     fl += (p + 1) * (1 + 3 * 4)  # t_j = F_{j+1} S_j; a_i += R_i t_j + F_j G_ji
     return fl
 
@@ -110,19 +110,21 @@ def emit_m2p(p):
     L.append("  const T is = F0 * F0;")
     for j in range(1, p + 2):
         L.append("  const T F%d = F%d * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
-    # monomials
+    for d, R in enumerate(("Rx", "Ry", "Rz")):
+        for k in range(2, p + 1):
+            L.append("  const T %s_%d = %s * T(%.17g);" % (R, k, R, 1.0 / k))
     L.append("  const T m0 = T(1);")
     for i, m in enumerate(mon):
         if i == 0:
             continue
-        # parent: reduce the first nonzero axis
         for d in range(3):
             if m[d] > 0:
                 par = list(m)
                 par[d] -= 1
                 pi = mi[tuple(par)]
-                R = "RxRyRz"[2 * d:2 * d + 2]
-                L.append("  const T m%d = %s * %s;" % (i, "m%d" % pi if pi else "T(1)", R))
+                R = ("Rx", "Ry", "Rz")[d]
+                fac = R if m[d] == 1 else "%s_%d" % (R, m[d])
+                L.append("  const T m%d = %s;" % (i, fac if pi == 0 else "m%d * %s" % (pi, fac)))
                 break
     for j in range(p + 1):
         L.append("  T S%d = T(0), G%dx = T(0), G%dy = T(0), G%dz = T(0);" % (j, j, j, j))
@@ -134,12 +136,7 @@ def emit_m2p(p):
             if a[d] > 0:
                 par = list(a)
                 par[d] -= 1
-                pi = mi[tuple(par)]
-                mterm = "m%d" % pi
-                if a[d] > 1:
-                    L.append("    G%d%s = fma(b * T(%d), %s, G%d%s);" % (j, ax, a[d], mterm, j, ax))
-                else:
-                    L.append("    G%d%s = fma(b, %s, G%d%s);" % (j, ax, mterm, j, ax))
+                L.append("    G%d%s = fma(b, m%d, G%d%s);" % (j, ax, mi[tuple(par)], j, ax))
         L.append("  }")
     for j in range(p + 1):
         L.append("  { const T t = F%d * S%d;" % (j + 1, j))
@@ -152,12 +149,14 @@ def emit_m2p(p):
 
 
 def emit_reduce(p):
-    """FP64 moments (multi-index order) -> reduced coefficients."""
+    """FP64 moments (multi-index order) -> stored coefficients a! B_{j,a}."""
     sl, contrib = contributions(p)
     L = []
     L.append("__device__ __forceinline__ void reduce_moments_p%d(const double* __restrict__ M, double* __restrict__ B) {" % p)
     for t, cs in enumerate(contrib):
-        terms = " + ".join("%.17g * M[%d]" % (c, i) for i, c in cs)
+        a = sl[t][1]
+        af = math.factorial(a[0]) * math.factorial(a[1]) * math.factorial(a[2])
+        terms = " + ".join("%.17g * M[%d]" % (c * af, i) for i, c in cs)
         L.append("  B[%d] = %s;" % (t, terms))
     L.append("}")
     return "\n".join(L)

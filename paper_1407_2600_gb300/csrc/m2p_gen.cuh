@@ -3,15 +3,15 @@
 #pragma once
 
 constexpr int kNB0 = 1;  // reduced coefficients at order 0
-constexpr int kM2PFlops0 = 32;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops0 = 31;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB1 = 4;  // reduced coefficients at order 1
-constexpr int kM2PFlops1 = 62;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops1 = 61;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB2 = 11;  // reduced coefficients at order 2
-constexpr int kM2PFlops2 = 118;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops2 = 117;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB3 = 24;  // reduced coefficients at order 3
-constexpr int kM2PFlops3 = 220;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops3 = 213;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB4 = 46;  // reduced coefficients at order 4
-constexpr int kM2PFlops4 = 393;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops4 = 368;  // flops per M2P (FMA = 2, rsqrt = 1)
 
 template <typename T>
 __device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
@@ -45,9 +45,9 @@ __device__ __forceinline__ void m2p_p1(const T* __restrict__ B, T Rx, T Ry, T Rz
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
   const T m0 = T(1);
-  const T m1 = T(1) * Rx;
-  const T m2 = T(1) * Ry;
-  const T m3 = T(1) * Rz;
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
   T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
   T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
   { const T b = B[0];
@@ -93,16 +93,19 @@ __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
   const T F3 = F2 * (T(-5) * is);
+  const T Rx_2 = Rx * T(0.5);
+  const T Ry_2 = Ry * T(0.5);
+  const T Rz_2 = Rz * T(0.5);
   const T m0 = T(1);
-  const T m1 = T(1) * Rx;
-  const T m2 = T(1) * Ry;
-  const T m3 = T(1) * Rz;
-  const T m4 = m1 * Rx;
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  const T m4 = m1 * Rx_2;
   const T m5 = m2 * Rx;
   const T m6 = m3 * Rx;
-  const T m7 = m2 * Ry;
+  const T m7 = m2 * Ry_2;
   const T m8 = m3 * Ry;
-  const T m9 = m3 * Rz;
+  const T m9 = m3 * Rz_2;
   T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
   T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
   T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0);
@@ -126,7 +129,7 @@ __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[5];
     S2 = fma(b, m4, S2);
-    G2x = fma(b * T(2), m1, G2x);
+    G2x = fma(b, m1, G2x);
   }
   { const T b = B[6];
     S2 = fma(b, m5, S2);
@@ -140,7 +143,7 @@ __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[8];
     S2 = fma(b, m7, S2);
-    G2y = fma(b * T(2), m2, G2y);
+    G2y = fma(b, m2, G2y);
   }
   { const T b = B[9];
     S2 = fma(b, m8, S2);
@@ -149,7 +152,7 @@ __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[10];
     S2 = fma(b, m9, S2);
-    G2z = fma(b * T(2), m3, G2z);
+    G2z = fma(b, m3, G2z);
   }
   { const T t = F1 * S0;
     ax = fma(Rx, t, fma(F0, G0x, ax));
@@ -174,12 +177,12 @@ __device__ __forceinline__ void reduce_moments_p2(const double* __restrict__ M, 
   B[2] = -1 * M[1];
   B[3] = -1 * M[2];
   B[4] = -1 * M[3];
-  B[5] = 0.5 * M[4];
+  B[5] = 1 * M[4];
   B[6] = 1 * M[5];
   B[7] = 1 * M[6];
-  B[8] = 0.5 * M[7];
+  B[8] = 1 * M[7];
   B[9] = 1 * M[8];
-  B[10] = 0.5 * M[9];
+  B[10] = 1 * M[9];
 }
 
 template <typename T>
@@ -192,26 +195,32 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
   const T F2 = F1 * (T(-3) * is);
   const T F3 = F2 * (T(-5) * is);
   const T F4 = F3 * (T(-7) * is);
+  const T Rx_2 = Rx * T(0.5);
+  const T Rx_3 = Rx * T(0.33333333333333331);
+  const T Ry_2 = Ry * T(0.5);
+  const T Ry_3 = Ry * T(0.33333333333333331);
+  const T Rz_2 = Rz * T(0.5);
+  const T Rz_3 = Rz * T(0.33333333333333331);
   const T m0 = T(1);
-  const T m1 = T(1) * Rx;
-  const T m2 = T(1) * Ry;
-  const T m3 = T(1) * Rz;
-  const T m4 = m1 * Rx;
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  const T m4 = m1 * Rx_2;
   const T m5 = m2 * Rx;
   const T m6 = m3 * Rx;
-  const T m7 = m2 * Ry;
+  const T m7 = m2 * Ry_2;
   const T m8 = m3 * Ry;
-  const T m9 = m3 * Rz;
-  const T m10 = m4 * Rx;
-  const T m11 = m5 * Rx;
-  const T m12 = m6 * Rx;
+  const T m9 = m3 * Rz_2;
+  const T m10 = m4 * Rx_3;
+  const T m11 = m5 * Rx_2;
+  const T m12 = m6 * Rx_2;
   const T m13 = m7 * Rx;
   const T m14 = m8 * Rx;
   const T m15 = m9 * Rx;
-  const T m16 = m7 * Ry;
-  const T m17 = m8 * Ry;
+  const T m16 = m7 * Ry_3;
+  const T m17 = m8 * Ry_2;
   const T m18 = m9 * Ry;
-  const T m19 = m9 * Rz;
+  const T m19 = m9 * Rz_3;
   T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
   T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
   T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0);
@@ -248,7 +257,7 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[8];
     S2 = fma(b, m4, S2);
-    G2x = fma(b * T(2), m1, G2x);
+    G2x = fma(b, m1, G2x);
   }
   { const T b = B[9];
     S2 = fma(b, m5, S2);
@@ -262,7 +271,7 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[11];
     S2 = fma(b, m7, S2);
-    G2y = fma(b * T(2), m2, G2y);
+    G2y = fma(b, m2, G2y);
   }
   { const T b = B[12];
     S2 = fma(b, m8, S2);
@@ -271,26 +280,26 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[13];
     S2 = fma(b, m9, S2);
-    G2z = fma(b * T(2), m3, G2z);
+    G2z = fma(b, m3, G2z);
   }
   { const T b = B[14];
     S3 = fma(b, m10, S3);
-    G3x = fma(b * T(3), m4, G3x);
+    G3x = fma(b, m4, G3x);
   }
   { const T b = B[15];
     S3 = fma(b, m11, S3);
-    G3x = fma(b * T(2), m5, G3x);
+    G3x = fma(b, m5, G3x);
     G3y = fma(b, m4, G3y);
   }
   { const T b = B[16];
     S3 = fma(b, m12, S3);
-    G3x = fma(b * T(2), m6, G3x);
+    G3x = fma(b, m6, G3x);
     G3z = fma(b, m4, G3z);
   }
   { const T b = B[17];
     S3 = fma(b, m13, S3);
     G3x = fma(b, m7, G3x);
-    G3y = fma(b * T(2), m5, G3y);
+    G3y = fma(b, m5, G3y);
   }
   { const T b = B[18];
     S3 = fma(b, m14, S3);
@@ -301,25 +310,25 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
   { const T b = B[19];
     S3 = fma(b, m15, S3);
     G3x = fma(b, m9, G3x);
-    G3z = fma(b * T(2), m6, G3z);
+    G3z = fma(b, m6, G3z);
   }
   { const T b = B[20];
     S3 = fma(b, m16, S3);
-    G3y = fma(b * T(3), m7, G3y);
+    G3y = fma(b, m7, G3y);
   }
   { const T b = B[21];
     S3 = fma(b, m17, S3);
-    G3y = fma(b * T(2), m8, G3y);
+    G3y = fma(b, m8, G3y);
     G3z = fma(b, m7, G3z);
   }
   { const T b = B[22];
     S3 = fma(b, m18, S3);
     G3y = fma(b, m9, G3y);
-    G3z = fma(b * T(2), m8, G3z);
+    G3z = fma(b, m8, G3z);
   }
   { const T b = B[23];
     S3 = fma(b, m19, S3);
-    G3z = fma(b * T(3), m9, G3z);
+    G3z = fma(b, m9, G3z);
   }
   { const T t = F1 * S0;
     ax = fma(Rx, t, fma(F0, G0x, ax));
@@ -352,22 +361,22 @@ __device__ __forceinline__ void reduce_moments_p3(const double* __restrict__ M, 
   B[5] = -0.5 * M[10] + -0.5 * M[13] + -0.5 * M[15];
   B[6] = -0.5 * M[11] + -0.5 * M[16] + -0.5 * M[18];
   B[7] = -0.5 * M[12] + -0.5 * M[17] + -0.5 * M[19];
-  B[8] = 0.5 * M[4];
+  B[8] = 1 * M[4];
   B[9] = 1 * M[5];
   B[10] = 1 * M[6];
-  B[11] = 0.5 * M[7];
+  B[11] = 1 * M[7];
   B[12] = 1 * M[8];
-  B[13] = 0.5 * M[9];
-  B[14] = -0.16666666666666666 * M[10];
-  B[15] = -0.5 * M[11];
-  B[16] = -0.5 * M[12];
-  B[17] = -0.5 * M[13];
+  B[13] = 1 * M[9];
+  B[14] = -1 * M[10];
+  B[15] = -1 * M[11];
+  B[16] = -1 * M[12];
+  B[17] = -1 * M[13];
   B[18] = -1 * M[14];
-  B[19] = -0.5 * M[15];
-  B[20] = -0.16666666666666666 * M[16];
-  B[21] = -0.5 * M[17];
-  B[22] = -0.5 * M[18];
-  B[23] = -0.16666666666666666 * M[19];
+  B[19] = -1 * M[15];
+  B[20] = -1 * M[16];
+  B[21] = -1 * M[17];
+  B[22] = -1 * M[18];
+  B[23] = -1 * M[19];
 }
 
 template <typename T>
@@ -381,41 +390,50 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   const T F3 = F2 * (T(-5) * is);
   const T F4 = F3 * (T(-7) * is);
   const T F5 = F4 * (T(-9) * is);
+  const T Rx_2 = Rx * T(0.5);
+  const T Rx_3 = Rx * T(0.33333333333333331);
+  const T Rx_4 = Rx * T(0.25);
+  const T Ry_2 = Ry * T(0.5);
+  const T Ry_3 = Ry * T(0.33333333333333331);
+  const T Ry_4 = Ry * T(0.25);
+  const T Rz_2 = Rz * T(0.5);
+  const T Rz_3 = Rz * T(0.33333333333333331);
+  const T Rz_4 = Rz * T(0.25);
   const T m0 = T(1);
-  const T m1 = T(1) * Rx;
-  const T m2 = T(1) * Ry;
-  const T m3 = T(1) * Rz;
-  const T m4 = m1 * Rx;
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  const T m4 = m1 * Rx_2;
   const T m5 = m2 * Rx;
   const T m6 = m3 * Rx;
-  const T m7 = m2 * Ry;
+  const T m7 = m2 * Ry_2;
   const T m8 = m3 * Ry;
-  const T m9 = m3 * Rz;
-  const T m10 = m4 * Rx;
-  const T m11 = m5 * Rx;
-  const T m12 = m6 * Rx;
+  const T m9 = m3 * Rz_2;
+  const T m10 = m4 * Rx_3;
+  const T m11 = m5 * Rx_2;
+  const T m12 = m6 * Rx_2;
   const T m13 = m7 * Rx;
   const T m14 = m8 * Rx;
   const T m15 = m9 * Rx;
-  const T m16 = m7 * Ry;
-  const T m17 = m8 * Ry;
+  const T m16 = m7 * Ry_3;
+  const T m17 = m8 * Ry_2;
   const T m18 = m9 * Ry;
-  const T m19 = m9 * Rz;
-  const T m20 = m10 * Rx;
-  const T m21 = m11 * Rx;
-  const T m22 = m12 * Rx;
-  const T m23 = m13 * Rx;
-  const T m24 = m14 * Rx;
-  const T m25 = m15 * Rx;
+  const T m19 = m9 * Rz_3;
+  const T m20 = m10 * Rx_4;
+  const T m21 = m11 * Rx_3;
+  const T m22 = m12 * Rx_3;
+  const T m23 = m13 * Rx_2;
+  const T m24 = m14 * Rx_2;
+  const T m25 = m15 * Rx_2;
   const T m26 = m16 * Rx;
   const T m27 = m17 * Rx;
   const T m28 = m18 * Rx;
   const T m29 = m19 * Rx;
-  const T m30 = m16 * Ry;
-  const T m31 = m17 * Ry;
-  const T m32 = m18 * Ry;
+  const T m30 = m16 * Ry_4;
+  const T m31 = m17 * Ry_3;
+  const T m32 = m18 * Ry_2;
   const T m33 = m19 * Ry;
-  const T m34 = m19 * Rz;
+  const T m34 = m19 * Rz_4;
   T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0);
   T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0);
   T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0);
@@ -456,7 +474,7 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[9];
     S2 = fma(b, m4, S2);
-    G2x = fma(b * T(2), m1, G2x);
+    G2x = fma(b, m1, G2x);
   }
   { const T b = B[10];
     S2 = fma(b, m5, S2);
@@ -470,7 +488,7 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[12];
     S2 = fma(b, m7, S2);
-    G2y = fma(b * T(2), m2, G2y);
+    G2y = fma(b, m2, G2y);
   }
   { const T b = B[13];
     S2 = fma(b, m8, S2);
@@ -479,11 +497,11 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[14];
     S2 = fma(b, m9, S2);
-    G2z = fma(b * T(2), m3, G2z);
+    G2z = fma(b, m3, G2z);
   }
   { const T b = B[15];
     S3 = fma(b, m4, S3);
-    G3x = fma(b * T(2), m1, G3x);
+    G3x = fma(b, m1, G3x);
   }
   { const T b = B[16];
     S3 = fma(b, m5, S3);
@@ -497,7 +515,7 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[18];
     S3 = fma(b, m7, S3);
-    G3y = fma(b * T(2), m2, G3y);
+    G3y = fma(b, m2, G3y);
   }
   { const T b = B[19];
     S3 = fma(b, m8, S3);
@@ -506,26 +524,26 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   }
   { const T b = B[20];
     S3 = fma(b, m9, S3);
-    G3z = fma(b * T(2), m3, G3z);
+    G3z = fma(b, m3, G3z);
   }
   { const T b = B[21];
     S3 = fma(b, m10, S3);
-    G3x = fma(b * T(3), m4, G3x);
+    G3x = fma(b, m4, G3x);
   }
   { const T b = B[22];
     S3 = fma(b, m11, S3);
-    G3x = fma(b * T(2), m5, G3x);
+    G3x = fma(b, m5, G3x);
     G3y = fma(b, m4, G3y);
   }
   { const T b = B[23];
     S3 = fma(b, m12, S3);
-    G3x = fma(b * T(2), m6, G3x);
+    G3x = fma(b, m6, G3x);
     G3z = fma(b, m4, G3z);
   }
   { const T b = B[24];
     S3 = fma(b, m13, S3);
     G3x = fma(b, m7, G3x);
-    G3y = fma(b * T(2), m5, G3y);
+    G3y = fma(b, m5, G3y);
   }
   { const T b = B[25];
     S3 = fma(b, m14, S3);
@@ -536,100 +554,100 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   { const T b = B[26];
     S3 = fma(b, m15, S3);
     G3x = fma(b, m9, G3x);
-    G3z = fma(b * T(2), m6, G3z);
+    G3z = fma(b, m6, G3z);
   }
   { const T b = B[27];
     S3 = fma(b, m16, S3);
-    G3y = fma(b * T(3), m7, G3y);
+    G3y = fma(b, m7, G3y);
   }
   { const T b = B[28];
     S3 = fma(b, m17, S3);
-    G3y = fma(b * T(2), m8, G3y);
+    G3y = fma(b, m8, G3y);
     G3z = fma(b, m7, G3z);
   }
   { const T b = B[29];
     S3 = fma(b, m18, S3);
     G3y = fma(b, m9, G3y);
-    G3z = fma(b * T(2), m8, G3z);
+    G3z = fma(b, m8, G3z);
   }
   { const T b = B[30];
     S3 = fma(b, m19, S3);
-    G3z = fma(b * T(3), m9, G3z);
+    G3z = fma(b, m9, G3z);
   }
   { const T b = B[31];
     S4 = fma(b, m20, S4);
-    G4x = fma(b * T(4), m10, G4x);
+    G4x = fma(b, m10, G4x);
   }
   { const T b = B[32];
     S4 = fma(b, m21, S4);
-    G4x = fma(b * T(3), m11, G4x);
+    G4x = fma(b, m11, G4x);
     G4y = fma(b, m10, G4y);
   }
   { const T b = B[33];
     S4 = fma(b, m22, S4);
-    G4x = fma(b * T(3), m12, G4x);
+    G4x = fma(b, m12, G4x);
     G4z = fma(b, m10, G4z);
   }
   { const T b = B[34];
     S4 = fma(b, m23, S4);
-    G4x = fma(b * T(2), m13, G4x);
-    G4y = fma(b * T(2), m11, G4y);
+    G4x = fma(b, m13, G4x);
+    G4y = fma(b, m11, G4y);
   }
   { const T b = B[35];
     S4 = fma(b, m24, S4);
-    G4x = fma(b * T(2), m14, G4x);
+    G4x = fma(b, m14, G4x);
     G4y = fma(b, m12, G4y);
     G4z = fma(b, m11, G4z);
   }
   { const T b = B[36];
     S4 = fma(b, m25, S4);
-    G4x = fma(b * T(2), m15, G4x);
-    G4z = fma(b * T(2), m12, G4z);
+    G4x = fma(b, m15, G4x);
+    G4z = fma(b, m12, G4z);
   }
   { const T b = B[37];
     S4 = fma(b, m26, S4);
     G4x = fma(b, m16, G4x);
-    G4y = fma(b * T(3), m13, G4y);
+    G4y = fma(b, m13, G4y);
   }
   { const T b = B[38];
     S4 = fma(b, m27, S4);
     G4x = fma(b, m17, G4x);
-    G4y = fma(b * T(2), m14, G4y);
+    G4y = fma(b, m14, G4y);
     G4z = fma(b, m13, G4z);
   }
   { const T b = B[39];
     S4 = fma(b, m28, S4);
     G4x = fma(b, m18, G4x);
     G4y = fma(b, m15, G4y);
-    G4z = fma(b * T(2), m14, G4z);
+    G4z = fma(b, m14, G4z);
   }
   { const T b = B[40];
     S4 = fma(b, m29, S4);
     G4x = fma(b, m19, G4x);
-    G4z = fma(b * T(3), m15, G4z);
+    G4z = fma(b, m15, G4z);
   }
   { const T b = B[41];
     S4 = fma(b, m30, S4);
-    G4y = fma(b * T(4), m16, G4y);
+    G4y = fma(b, m16, G4y);
   }
   { const T b = B[42];
     S4 = fma(b, m31, S4);
-    G4y = fma(b * T(3), m17, G4y);
+    G4y = fma(b, m17, G4y);
     G4z = fma(b, m16, G4z);
   }
   { const T b = B[43];
     S4 = fma(b, m32, S4);
-    G4y = fma(b * T(2), m18, G4y);
-    G4z = fma(b * T(2), m17, G4z);
+    G4y = fma(b, m18, G4y);
+    G4z = fma(b, m17, G4z);
   }
   { const T b = B[44];
     S4 = fma(b, m33, S4);
     G4y = fma(b, m19, G4y);
-    G4z = fma(b * T(3), m18, G4z);
+    G4z = fma(b, m18, G4z);
   }
   { const T b = B[45];
     S4 = fma(b, m34, S4);
-    G4z = fma(b * T(4), m19, G4z);
+    G4z = fma(b, m19, G4z);
   }
   { const T t = F1 * S0;
     ax = fma(Rx, t, fma(F0, G0x, ax));
@@ -668,43 +686,43 @@ __device__ __forceinline__ void reduce_moments_p4(const double* __restrict__ M, 
   B[6] = -0.5 * M[10] + -0.5 * M[13] + -0.5 * M[15];
   B[7] = -0.5 * M[11] + -0.5 * M[16] + -0.5 * M[18];
   B[8] = -0.5 * M[12] + -0.5 * M[17] + -0.5 * M[19];
-  B[9] = 0.5 * M[4];
+  B[9] = 1 * M[4];
   B[10] = 1 * M[5];
   B[11] = 1 * M[6];
-  B[12] = 0.5 * M[7];
+  B[12] = 1 * M[7];
   B[13] = 1 * M[8];
-  B[14] = 0.5 * M[9];
-  B[15] = 0.25 * M[20] + 0.25 * M[23] + 0.25 * M[25];
+  B[14] = 1 * M[9];
+  B[15] = 0.5 * M[20] + 0.5 * M[23] + 0.5 * M[25];
   B[16] = 0.5 * M[21] + 0.5 * M[26] + 0.5 * M[28];
   B[17] = 0.5 * M[22] + 0.5 * M[27] + 0.5 * M[29];
-  B[18] = 0.25 * M[23] + 0.25 * M[30] + 0.25 * M[32];
+  B[18] = 0.5 * M[23] + 0.5 * M[30] + 0.5 * M[32];
   B[19] = 0.5 * M[24] + 0.5 * M[31] + 0.5 * M[33];
-  B[20] = 0.25 * M[25] + 0.25 * M[32] + 0.25 * M[34];
-  B[21] = -0.16666666666666666 * M[10];
-  B[22] = -0.5 * M[11];
-  B[23] = -0.5 * M[12];
-  B[24] = -0.5 * M[13];
+  B[20] = 0.5 * M[25] + 0.5 * M[32] + 0.5 * M[34];
+  B[21] = -1 * M[10];
+  B[22] = -1 * M[11];
+  B[23] = -1 * M[12];
+  B[24] = -1 * M[13];
   B[25] = -1 * M[14];
-  B[26] = -0.5 * M[15];
-  B[27] = -0.16666666666666666 * M[16];
-  B[28] = -0.5 * M[17];
-  B[29] = -0.5 * M[18];
-  B[30] = -0.16666666666666666 * M[19];
-  B[31] = 0.041666666666666664 * M[20];
-  B[32] = 0.16666666666666666 * M[21];
-  B[33] = 0.16666666666666666 * M[22];
-  B[34] = 0.25 * M[23];
-  B[35] = 0.5 * M[24];
-  B[36] = 0.25 * M[25];
-  B[37] = 0.16666666666666666 * M[26];
-  B[38] = 0.5 * M[27];
-  B[39] = 0.5 * M[28];
-  B[40] = 0.16666666666666666 * M[29];
-  B[41] = 0.041666666666666664 * M[30];
-  B[42] = 0.16666666666666666 * M[31];
-  B[43] = 0.25 * M[32];
-  B[44] = 0.16666666666666666 * M[33];
-  B[45] = 0.041666666666666664 * M[34];
+  B[26] = -1 * M[15];
+  B[27] = -1 * M[16];
+  B[28] = -1 * M[17];
+  B[29] = -1 * M[18];
+  B[30] = -1 * M[19];
+  B[31] = 1 * M[20];
+  B[32] = 1 * M[21];
+  B[33] = 1 * M[22];
+  B[34] = 1 * M[23];
+  B[35] = 1 * M[24];
+  B[36] = 1 * M[25];
+  B[37] = 1 * M[26];
+  B[38] = 1 * M[27];
+  B[39] = 1 * M[28];
+  B[40] = 1 * M[29];
+  B[41] = 1 * M[30];
+  B[42] = 1 * M[31];
+  B[43] = 1 * M[32];
+  B[44] = 1 * M[33];
+  B[45] = 1 * M[34];
 }
 
 __device__ __forceinline__ void p2m_acc_p0(double m, double dx, double dy, double dz, double* __restrict__ M) {

@@ -188,6 +188,8 @@ struct PerArgs {
   const double* fm;     // field moments (FP64), (box, cell, NE)
   const T* tab;         // phi~ table, nodes x NP
   int le, lg, pe;
+  T* lbuf;              // per run: L (NL), V (3), M_total
+  int lstride;
   const T* accw;        // walk accelerations, key order
   float* out;           // caller order
   unsigned long long* counter;
@@ -195,9 +197,10 @@ struct PerArgs {
 
 __constant__ unsigned char c_par_mask[kNMMax];  // bit d set: multi-index odd in axis d
 
+// One warp per run of groups sharing an expansion point e: the local
+// expansion of the image field, the background term's V and the total mass.
 template <typename T, int PE>
-__global__ void __launch_bounds__(128) periodic_kernel(PerArgs<T> a) {
-  using V4 = typename Vec4<T>::type;
+__global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
   constexpr int NL = PE_<PE>::NL, NE = PE_<PE>::NE, NP = PE_<PE>::NP;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
@@ -205,9 +208,10 @@ __global__ void __launch_bounds__(128) periodic_kernel(PerArgs<T> a) {
   const int m = (1 << (a.lg - 1)) + 2;
   const int step = 1 << (23 - a.lg);
   const T scale = (T)(1.0 / 8388608.0);
-  const T fourpi3 = (T)(4.0 * M_PI / 3.0);
   for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
-    const int4 ga = tr.gA[g], gb = tr.gB[g], gd = tr.gD[g];
+    const int4 ga = tr.gA[g];
+    if (ga.w == 0) continue;  // not the first group of its run
+    const int4 gd = tr.gD[g];
     const int box = ga.z;
     T L[NL];
 #pragma unroll
@@ -216,8 +220,7 @@ __global__ void __launch_bounds__(128) periodic_kernel(PerArgs<T> a) {
     unsigned long long nused = 0;
     for (int cell = lane; cell < ncp; cell += 32) {
       const double* Mc = a.fm + ((int64_t)box * ncp + cell) * NE;
-      const double m0 = Mc[0];
-      if (m0 == 0.0) continue;
+      if (Mc[0] == 0.0) continue;
       nused++;
       T M[NE];
 #pragma unroll
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(128) periodic_kernel(PerArgs<T> a) {
       const int cx2 = cell_c2((int)compact3((uint64_t)cell), a.le);
       const int cy2 = cell_c2((int)compact3((uint64_t)cell >> 1), a.le);
       const int cz2 = cell_c2((int)compact3((uint64_t)cell >> 2), a.le);
-      const int kx = img_shift(cx2, gb.x), ky = img_shift(cy2, gb.y), kz = img_shift(cz2, gb.z);
+      const int kx = img_shift(cx2, gd.x), ky = img_shift(cy2, gd.y), kz = img_shift(cz2, gd.z);
       const int ox = cx2 - kx * NB_PBOX - gd.x, oy = cy2 - ky * NB_PBOX - gd.y, oz = cz2 - kz * NB_PBOX - gd.z;
       // R0 = e - c* on the lattice
       const int irx = -ox / step, iry = -oy / step, irz = -oz / step;
@@ -257,23 +260,56 @@ __global__ void __launch_bounds__(128) periodic_kernel(PerArgs<T> a) {
       mt += __shfl_xor_sync(0xffffffffu, mt, o);
       nused += __shfl_xor_sync(0xffffffffu, nused, o);
     }
-    if (lane == 0 && a.counter) atomicAdd(a.counter, nused);
-    if (lane < ga.y) {
-      const int i = ga.x + lane;
-      const V4 o4 = a.src[i];
-      const int4 la = tr.cA[tr.sleaf[i]];
-      const T dx = o4.x + (T)(la.x - gd.x) * scale;
-      const T dy = o4.y + (T)(la.y - gd.y) * scale;
-      const T dz = o4.z + (T)(la.z - gd.z) * scale;
-      T ax = a.accw[i] + fourpi3 * (mt * dx - vx);
-      T ay = a.accw[tr.n + i] + fourpi3 * (mt * dy - vy);
-      T az = a.accw[2 * tr.n + i] + fourpi3 * (mt * dz - vz);
-      PE_<PE>::template l2p<T>(L, dx, dy, dz, ax, ay, az);
-      const uint32_t j = tr.perm[i];
-      a.out[j] = (float)ax;
-      a.out[tr.n + j] = (float)ay;
-      a.out[2 * tr.n + j] = (float)az;
+    T* dst = a.lbuf + (int64_t)gd.w * a.lstride;
+    for (int t = lane; t < NL; t += 32) {
+      T v = L[0];
+#pragma unroll
+      for (int q = 1; q < NL; q++)
+        if (q == t) v = L[q];
+      dst[t] = v;
     }
+    if (lane == 0) {
+      dst[NL] = vx;
+      dst[NL + 1] = vy;
+      dst[NL + 2] = vz;
+      dst[NL + 3] = mt;
+      if (a.counter) atomicAdd(a.counter, nused);
+    }
+  }
+}
+
+// One warp per group, one sink per lane: walk acceleration + background term
+// + image field, scattered to the caller's order.
+template <typename T, int PE>
+__global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NL = PE_<PE>::NL;
+  const int lane = threadIdx.x & 31;
+  const DevTree& tr = a.tr;
+  const T scale = (T)(1.0 / 8388608.0);
+  const T fourpi3 = (T)(4.0 * M_PI / 3.0);
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+    const int4 ga = tr.gA[g], gd = tr.gD[g];
+    if (lane >= ga.y) continue;
+    const T* Lr = a.lbuf + (int64_t)gd.w * a.lstride;
+    T L[NL];
+#pragma unroll
+    for (int t = 0; t < NL; t++) L[t] = Lr[t];
+    const T vx = Lr[NL], vy = Lr[NL + 1], vz = Lr[NL + 2], mt = Lr[NL + 3];
+    const int i = ga.x + lane;
+    const V4 o4 = a.src[i];
+    const int4 la = tr.cA[tr.sleaf[i]];
+    const T dx = o4.x + (T)(la.x - gd.x) * scale;
+    const T dy = o4.y + (T)(la.y - gd.y) * scale;
+    const T dz = o4.z + (T)(la.z - gd.z) * scale;
+    T ax = a.accw[i] + fourpi3 * (mt * dx - vx);
+    T ay = a.accw[tr.n + i] + fourpi3 * (mt * dy - vy);
+    T az = a.accw[2 * tr.n + i] + fourpi3 * (mt * dz - vz);
+    PE_<PE>::template l2p<T>(L, dx, dy, dz, ax, ay, az);
+    const uint32_t j = tr.perm[i];
+    a.out[j] = (float)ax;
+    a.out[tr.n + j] = (float)ay;
+    a.out[2 * tr.n + j] = (float)az;
   }
 }
 
@@ -395,8 +431,13 @@ cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t
   return cudaSuccess;
 }
 
+int nb_field_stride(int pe) {
+  const int nl = (pe + 2) * (pe + 3) * (pe + 4) / 6 - 1;
+  return (nl + 4 + 3) & ~3;
+}
+
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
-                        const void* tab, const void* accw, float* out, unsigned long long* counter,
+                        const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         cudaStream_t s) {
   if (pe == 0) {
     if (fp64) scatter_kernel<double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out);
@@ -407,12 +448,14 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
   int grid = (int)(((int64_t)tr.ngroup * 32 + 127) / 128);
   if (grid > 152 * 64) grid = 152 * 64;
   if (grid < 1) grid = 1;
-#define NB_PER(TT, PE)                                                                \
-  {                                                                                   \
-    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, \
-                  (const TT*)accw, out, counter};                                     \
-    periodic_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                  \
-    break;                                                                            \
+  const int ls = nb_field_stride(pe);
+#define NB_PER(TT, PE)                                                                              \
+  {                                                                                                 \
+    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
+                  (const TT*)accw, out, counter};                                                   \
+    field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
+    field_l2p_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
+    break;                                                                                          \
   }
   if (fp64) {
     switch (pe) {
@@ -432,6 +475,6 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
     }
   }
 #undef NB_PER
-  nb_launch_counter += 1;
+  nb_launch_counter += 2;
   return cudaGetLastError();
 }

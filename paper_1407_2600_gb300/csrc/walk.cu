@@ -14,10 +14,14 @@
 // reproducible.
 //
 // Acceptance: in integer units of 2^-23, with the cell at the image of its
-// level-l_E ancestor nearest the group box centre g, d2 is the squared
+// level-l_E ancestor nearest the group's expansion point e (the centre of
+// its level-(grid-1) cell), d2 is the squared
 // distance from the cell centre to the group box; a cell of level l >= 2
 // whose level-l_E descendants share one image is accepted iff
 // d2 > floor(s^2/theta^2), s = 2^(23-l).
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "m2p_gen.cuh"
 
@@ -83,6 +87,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   __shared__ V4 s_src[WARPS][32];
   __shared__ T s_moff[WARPS][32][4];  // centre offset and, in [3], the cell scale 2^level
   __shared__ int s_midx[WARPS][32];
+  __shared__ T s_meps[WARPS][32];
   __shared__ int s_pfx[WARPS][32];
   __shared__ int s_pst[WARPS][32];
   __shared__ int s_plev[WARPS][32];
@@ -142,17 +147,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         const int iz = ((ca.z >> (22 - lvl)) - 1) >> 1;
         if (lvl >= w.le) {
           const int sh = lvl - w.le;
-          kx = img_shift(cell_c2(ix >> sh, w.le), gb.x);
-          ky = img_shift(cell_c2(iy >> sh, w.le), gb.y);
-          kz = img_shift(cell_c2(iz >> sh, w.le), gb.z);
+          kx = img_shift(cell_c2(ix >> sh, w.le), gd.x);
+          ky = img_shift(cell_c2(iy >> sh, w.le), gd.y);
+          kz = img_shift(cell_c2(iz >> sh, w.le), gd.z);
         } else {
           const int sh = w.le - lvl;
-          kx = img_shift(cell_c2(ix << sh, w.le), gb.x);
-          ky = img_shift(cell_c2(iy << sh, w.le), gb.y);
-          kz = img_shift(cell_c2(iz << sh, w.le), gb.z);
-          consistent = kx == img_shift(cell_c2(((ix + 1) << sh) - 1, w.le), gb.x) &&
-                       ky == img_shift(cell_c2(((iy + 1) << sh) - 1, w.le), gb.y) &&
-                       kz == img_shift(cell_c2(((iz + 1) << sh) - 1, w.le), gb.z);
+          kx = img_shift(cell_c2(ix << sh, w.le), gd.x);
+          ky = img_shift(cell_c2(iy << sh, w.le), gd.y);
+          kz = img_shift(cell_c2(iz << sh, w.le), gd.z);
+          consistent = kx == img_shift(cell_c2(((ix + 1) << sh) - 1, w.le), gd.x) &&
+                       ky == img_shift(cell_c2(((iy + 1) << sh) - 1, w.le), gd.y) &&
+                       kz == img_shift(cell_c2(((iz + 1) << sh) - 1, w.le), gd.z);
         }
         const int dx = abs(ca.x - gb.x - kx * NB_PBOX) - gc.x;
         const int dy = abs(ca.y - gb.y - ky * NB_PBOX) - gc.y;
@@ -184,10 +189,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         if (cls == 2) {
           const int pos = __popc(mm & ltmask);
           s_midx[wid][pos] = c;
-          s_moff[wid][pos][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
-          s_moff[wid][pos][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
-          s_moff[wid][pos][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
-          s_moff[wid][pos][3] = (T)(1 << lvl);
+          // -(c* - e) 2^level and eps^2 4^level: the cell's unit (exact scalings)
+          const T sc = (T)(1 << lvl);
+          s_moff[wid][pos][0] = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
+          s_moff[wid][pos][1] = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
+          s_moff[wid][pos][2] = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
+          s_moff[wid][pos][3] = sc;
+          s_meps[wid][pos] = eps2 * (sc * sc);
         }
         __syncwarp();
         for (int t = lane; t < nmp * NBS; t += 32) {
@@ -201,9 +209,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           // coefficients pre-scaled): see the upward pass
           for (int q = 0; q < nmp; q++) {
             const T sc = s_moff[wid][q][3];
-            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], (xi - s_moff[wid][q][0]) * sc,
-                                     (yi - s_moff[wid][q][1]) * sc, (zi - s_moff[wid][q][2]) * sc,
-                                     eps2 * (sc * sc), px, py, pz);
+            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], fma(xi, sc, s_moff[wid][q][0]),
+                                     fma(yi, sc, s_moff[wid][q][1]), fma(zi, sc, s_moff[wid][q][2]),
+                                     s_meps[wid][q], px, py, pz);
           }
           kadd(ax, cx, px);
           kadd(ay, cy, py);
@@ -244,9 +252,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
               // level-l_E ancestor
               const uint64_t pk = tr.skeys[j] >> (3 * (NB_QBITS - w.le));
               const int4 pc = s_pcen[wid][q];
-              const int jx = img_shift(cell_c2((int)compact3(pk), w.le), gb.x);
-              const int jy = img_shift(cell_c2((int)compact3(pk >> 1), w.le), gb.y);
-              const int jz = img_shift(cell_c2((int)compact3(pk >> 2), w.le), gb.z);
+              const int jx = img_shift(cell_c2((int)compact3(pk), w.le), gd.x);
+              const int jy = img_shift(cell_c2((int)compact3(pk >> 1), w.le), gd.y);
+              const int jz = img_shift(cell_c2((int)compact3(pk >> 2), w.le), gd.z);
               ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
               oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
               oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;
@@ -308,10 +316,85 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
   return cudaGetLastError();
 }
 
+// launch variants (warps per block, minimum resident blocks per SM); the
+// register budget per thread follows from them
+template <typename T, int P>
+cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
+  if (sizeof(T) == 8) return launch_walk<T, P, 4, 1>(a, nsm, max_blocks, s);
+  if (v == 0) return launch_walk<T, P, 8, 2>(a, nsm, max_blocks, s);
+  return launch_walk<T, P, 8, 3>(a, nsm, max_blocks, s);
+}
+constexpr int kVariants = 2;
+
+struct TuneEntry {
+  int device, order, fp64, variant;
+};
+std::mutex g_tune_mutex;
+std::vector<TuneEntry> g_tune;
+
+// Autotuner: the first walk of a (device, precision, order) times every
+// variant on the real data and keeps the fastest; results do not depend on
+// the variant (each group's walk is the same computation).
+template <typename T, int P>
+cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int fp = sizeof(T) == 8;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (const auto& t : g_tune)
+      if (t.device == dev && t.order == P && t.fp64 == fp) return launch_variant<T, P>(t.variant, a, nsm, max_blocks, s);
+  }
+  if (fp) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune.push_back({dev, P, fp, 0});
+    return launch_variant<T, P>(0, a, nsm, max_blocks, s);
+  }
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0))) return e;
+  if ((e = cudaEventCreate(&e1))) return e;
+  float best = 1e30f;
+  int bv = 0;
+  for (int v = 0; v < kVariants; v++) {
+    if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
+    if ((e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s))) return e;
+    cudaEventRecord(e0, s);
+    if ((e = launch_variant<T, P>(v, a, nsm, max_blocks, s))) return e;
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1))) return e;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune.push_back({dev, P, fp, bv});
+  }
+  if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
+  if ((e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s))) return e;
+  return launch_variant<T, P>(bv, a, nsm, max_blocks, s);
+}
+
 }  // namespace
 
-// warps per block of the walk for a precision
+// warps per block of the walk for a precision (stack slots are sized for the largest)
 int nb_walk_warps(bool fp64) { return fp64 ? 4 : 8; }
+
+// the variant the autotuner chose for (precision, order) on this device, or -1
+int nb_walk_variant(bool fp64, int order) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  for (const auto& t : g_tune)
+    if (t.device == dev && t.order == order && t.fp64 == (fp64 ? 1 : 0)) return t.variant;
+  return -1;
+}
 
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src,
                     const void* eps2, const long long* thr, int n_direct, int le, int* stack,
@@ -319,7 +402,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     unsigned long long* counters, unsigned* status, int nsm, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
-#define NB_WALK(TT, P, W, MB)                                                      \
+#define NB_WALK(TT, P)                                                             \
   {                                                                                \
     WalkArgs<TT> a;                                                                \
     a.tr = tr;                                                                     \
@@ -335,23 +418,23 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.acc = (TT*)acc;                                                              \
     a.counters = counters;                                                         \
     a.status = status;                                                             \
-    return launch_walk<TT, P, W, MB>(a, nsm, max_blocks, s);                       \
+    return run_walk<TT, P>(a, nsm, max_blocks, s);                                 \
   }
   if (fp64) {
     switch (order) {
-      case 0: NB_WALK(double, 0, 4, 1)
-      case 1: NB_WALK(double, 1, 4, 1)
-      case 2: NB_WALK(double, 2, 4, 1)
-      case 3: NB_WALK(double, 3, 4, 1)
-      default: NB_WALK(double, 4, 4, 1)
+      case 0: NB_WALK(double, 0)
+      case 1: NB_WALK(double, 1)
+      case 2: NB_WALK(double, 2)
+      case 3: NB_WALK(double, 3)
+      default: NB_WALK(double, 4)
     }
   } else {
     switch (order) {
-      case 0: NB_WALK(float, 0, 8, 2)
-      case 1: NB_WALK(float, 1, 8, 2)
-      case 2: NB_WALK(float, 2, 8, 2)
-      case 3: NB_WALK(float, 3, 8, 2)
-      default: NB_WALK(float, 4, 8, 2)
+      case 0: NB_WALK(float, 0)
+      case 1: NB_WALK(float, 1)
+      case 2: NB_WALK(float, 2)
+      case 3: NB_WALK(float, 3)
+      default: NB_WALK(float, 4)
     }
   }
 #undef NB_WALK

@@ -68,20 +68,23 @@ def test_reduced_m2p_matches_oracle_dtensor_form():
     for p in range(5):
         sl, contrib = G.contributions(p)
         M = rng.standard_normal(O.nmom(p))
-        B = np.array([sum(c * M[i] for i, c in cs) for cs in contrib])
+        # stored coefficients are a! B_{j,a}; monomials are R^a / a!
+        fa = lambda a: math.factorial(a[0]) * math.factorial(a[1]) * math.factorial(a[2])
+        B = np.array([fa(sl[t][1]) * sum(c * M[i] for i, c in cs) for t, cs in enumerate(contrib)])
         R = rng.standard_normal(3) * 0.5
         eps = 0.05
         s = R @ R + eps ** 2
         F = [((-1) ** j) * math.prod(range(1, 2 * j, 2)) * s ** (-0.5 - j) for j in range(p + 2)]
+        mu = lambda a: R[0] ** a[0] * R[1] ** a[1] * R[2] ** a[2] / fa(a)
         S = np.zeros(p + 1)
         Gd = np.zeros((p + 1, 3))
         for t, (j, a) in enumerate(sl):
-            S[j] += B[t] * R[0] ** a[0] * R[1] ** a[1] * R[2] ** a[2]
+            S[j] += B[t] * mu(a)
             for d in range(3):
                 if a[d] > 0:
                     aa = list(a)
                     aa[d] -= 1
-                    Gd[j, d] += B[t] * a[d] * R[0] ** aa[0] * R[1] ** aa[1] * R[2] ** aa[2]
+                    Gd[j, d] += B[t] * mu(aa)
         acc = sum(R * F[j + 1] * S[j] + F[j] * Gd[j] for j in range(p + 1))
         ref = O.m2p(M, p, R, eps)
         assert np.abs(acc - ref).max() <= 1e-13 * np.abs(ref).max()
