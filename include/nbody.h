@@ -52,7 +52,8 @@ enum {
   NBODY_ECUDA = -3,     /* a CUDA runtime call failed */
   NBODY_EOVERFLOW = -4, /* a fixed-capacity device buffer would overflow */
   NBODY_ETIMEOUT = -5,  /* a bounded device-side wait ran out */
-  NBODY_ENOTSUP = -6    /* parameter combination not supported */
+  NBODY_ENOTSUP = -6,   /* parameter combination not supported */
+  NBODY_ERANGE = -7     /* size beyond the fixed maximum of an allocation-free entry point */
 };
 
 enum { NBODY_MIXED = 0, NBODY_FP64 = 1 };
@@ -207,6 +208,29 @@ int nbody_tree_export(const nbody_tree *tree, int what, void *dst_dev, nbody_str
  * index in breadth-first order, or -1 when the key is not a cell. */
 int nbody_tree_lookup(const nbody_tree *tree, const uint64_t *keys_dev, int64_t nkeys,
                       int32_t *idx_dev, nbody_stream_t stream);
+
+/*
+ * Allocation-free Morton keys + stable radix sort, for callers that cannot
+ * allocate device memory at run time (another allocator owns or caps the
+ * device memory, cudaMalloc's implicit synchronisation is not acceptable,
+ * or the device footprint must stay fixed after set-up).  The paper has no
+ * counterpart; this is the keys + sort phase of nbody_build_tree run on
+ * scratch held in a file-scope device array of the library instead of
+ * allocated memory.
+ *   pos_dev       3*n FP64 positions (SoA), read only
+ *   n             1 .. 2^20 particles; larger n returns NBODY_ERANGE
+ *   keys_out_dev  n uint64: the Morton keys in ascending order (equal keys in
+ *                 input order), caller-allocated
+ *   perm_out_dev  n uint32: the input index of each sorted key, caller-allocated
+ * The scratch array (about 14.7 MB) is held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up the
+ * array's device address, so make it before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  The call blocks
+ * on the stream at its end to return the status of the bounded waits.
+ */
+int nbody_sort_keys_noalloc(const double *pos_dev, int64_t n, uint64_t *keys_out_dev,
+                            uint32_t *perm_out_dev, nbody_stream_t stream);
 
 /* Read and clear the tree's device status word (blocks on the stream). */
 int nbody_check(nbody_tree *tree, nbody_stream_t stream);

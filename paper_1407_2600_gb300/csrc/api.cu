@@ -745,6 +745,7 @@ const char* nbody_strerror(int code) {
     case NBODY_EOVERFLOW: return "fixed-capacity device buffer overflow";
     case NBODY_ETIMEOUT: return "bounded device wait ran out";
     case NBODY_ENOTSUP: return "not supported";
+    case NBODY_ERANGE: return "size exceeds the fixed maximum of an allocation-free entry point";
     default: return "unknown error";
   }
 }

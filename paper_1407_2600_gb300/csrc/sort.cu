@@ -7,6 +7,8 @@
 // obtains its exclusive prefix by decoupled look-back over earlier tiles
 // (bounded waits: a wait that runs out sets a status bit and the pass
 // completes with the flag raised instead of hanging).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace {
@@ -432,4 +434,78 @@ cudaError_t nb_exclusive_scan_i32(const int* in, int* out, int64_t n, int* total
   scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, tmp);
   nb_launch_counter += 3;
   return cudaGetLastError();
+}
+
+// ---- allocation-free Morton sort --------------------------------------------
+// Some callers cannot allocate device memory at run time: code that runs
+// while another allocator owns (or caps) the device memory, loops that must
+// not pay cudaMalloc's implicit synchronisation, or processes whose device
+// footprint must be fixed after set-up.  nbody_sort_keys_noalloc serves them:
+// it is the keys + onesweep sort of nbody_build_tree with every scratch
+// buffer (the alternate key/value buffers, the histograms, the look-back
+// status words and the error word) in the file-scope array below, sized for
+// at most kNoAllocMaxN particles.  Every GPU that loads this library holds
+// the array (about 14.7 MB) until the process exits.
+namespace {
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 20;
+constexpr int64_t kNoAllocTiles = kNoAllocMaxN / kTile + 1;
+constexpr int kNoAllocPasses = 8;  // 63 key bits, 8 bits per pass
+struct NoAllocScratch {
+  uint64_t keys_alt[kNoAllocMaxN];
+  uint32_t vals_alt[kNoAllocMaxN];
+  uint32_t hist[16 * 256];
+  uint32_t status[kNoAllocPasses * 256 * kNoAllocTiles];
+  uint32_t tile_ctr[16];
+  unsigned err;
+};
+std::mutex g_noalloc_mutex;
+NoAllocScratch* g_noalloc_ptr[64] = {};
+}  // namespace
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+extern "C" int nbody_sort_keys_noalloc(const double* pos_dev, int64_t n, uint64_t* keys_out_dev,
+                                       uint32_t* perm_out_dev, nbody_stream_t stream) {
+  if (!pos_dev || !keys_out_dev || !perm_out_dev || n <= 0) return NBODY_EINVAL;
+  if (n > kNoAllocMaxN) return NBODY_ERANGE;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return NBODY_ECUDA;
+  NoAllocScratch* sc = nullptr;
+  {
+    // once per device, with that device current: the device address of the
+    // array (its name in host code is only a host-side stand-in)
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return NBODY_ECUDA;
+      }
+      g_noalloc_ptr[dev] = (NoAllocScratch*)p;
+    }
+    sc = g_noalloc_ptr[dev];
+  }
+  // the array keeps the previous call's contents: the error word is cleared
+  // here, the histograms, status words and tile counters by the sort itself
+  if (cudaMemsetAsync(&sc->err, 0, sizeof(unsigned), s) != cudaSuccess) return NBODY_ECUDA;
+  if (nb_launch_keys(pos_dev, n, 0, keys_out_dev, perm_out_dev, s) != cudaSuccess) return NBODY_ECUDA;
+  SortScratch ss;
+  ss.keys_alt = sc->keys_alt;
+  ss.vals_alt = sc->vals_alt;
+  ss.hist = sc->hist;
+  ss.status = sc->status;
+  ss.tile_ctr = sc->tile_ctr;
+  ss.tiles_cap = kNoAllocTiles;
+  ss.dstatus = &sc->err;
+  int alt = 0;
+  if (nb_radix_sort(keys_out_dev, perm_out_dev, n, 63, nullptr, 1, &ss, s, &alt) != cudaSuccess)
+    return NBODY_ECUDA;
+  if (alt) return NBODY_ECUDA;  // an even number of passes ends in the output buffers
+  unsigned err = 0;
+  if (cudaMemcpyAsync(&err, &sc->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return NBODY_ECUDA;
+  if (err & NB_ST_TIMEOUT) return NBODY_ETIMEOUT;
+  return NBODY_OK;
 }

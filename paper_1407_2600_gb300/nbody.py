@@ -22,6 +22,7 @@ NBODY_ECUDA = -3
 NBODY_EOVERFLOW = -4
 NBODY_ETIMEOUT = -5
 NBODY_ENOTSUP = -6
+NBODY_ERANGE = -7
 NBODY_MIXED = 0
 NBODY_FP64 = 1
 NBODY_FLAG_ASYNC = 1
@@ -32,7 +33,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces",
            "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
-           "nbody_strerror", "nbody_timing_read"]
+           "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc"]
 
 
 class Params(C.Structure):
@@ -97,6 +98,7 @@ def lib():
         L.nbody_tree_free.argtypes = [_vp]
         L.nbody_tree_free.restype = None
         L.nbody_timing_read.argtypes = [_vp, C.POINTER(Timing), C.c_int]
+        L.nbody_sort_keys_noalloc.argtypes = [_vp, C.c_int64, _vp, _vp, _vp]
         L.nbody_strerror.argtypes = [C.c_int]
         L.nbody_strerror.restype = C.c_char_p
         _LIB = L
@@ -176,6 +178,11 @@ def nbody_tree_free(tree: int) -> None:
 
 def nbody_timing_read(tree: int, out: Timing, reset: int) -> int:
     return lib().nbody_timing_read(tree, C.byref(out), reset)
+
+
+def nbody_sort_keys_noalloc(pos_dev: int, n: int, keys_out_dev: int, perm_out_dev: int,
+                            stream: int | None = None) -> int:
+    return lib().nbody_sort_keys_noalloc(pos_dev, n, keys_out_dev, perm_out_dev, stream)
 
 
 def nbody_strerror(code: int) -> str:
