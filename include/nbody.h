@@ -190,6 +190,19 @@ typedef struct {
 } nbody_timing;
 int nbody_timing_read(nbody_tree *tree, nbody_timing *out, int reset);
 
+/*
+ * CIC density contrast loss of one box (the loss of the differentiable
+ * trajectory; the paper has no such loss, it uses CIC grids for its power
+ * spectra in Sec. 4): grid cell c of ng^3 has centre (c + 1/2)/ng,
+ * delta_c = ng^3 sum_j m_j w_jc - 1, L = sum_c delta_c^2.
+ *   pos_dev   3*n FP64 positions;  mass_dev  n FP32 or NULL (1/n)
+ *   grid_dev  ng^3 FP64 caller workspace; holds delta on return
+ *   loss_dev  one FP64 (device), the loss
+ *   grad_dev  3*n FP64 dL/dpos (SoA) or NULL
+ */
+int nbody_cic_loss(const double *pos_dev, const float *mass_dev, int64_t n, int ng, double *grid_dev,
+                   double *loss_dev, double *grad_dev, nbody_stream_t stream);
+
 /* Tree inspection (tests).  what: */
 enum {
   NBODY_EXPORT_SORTED_KEYS = 1, /* uint64 per particle, key order */

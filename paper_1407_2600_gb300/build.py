@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnbody.so")
-UNITS = ["sort.cu", "build.cu", "upward.cu", "walk.cu", "periodic.cu", "api.cu"]
+UNITS = ["sort.cu", "build.cu", "upward.cu", "walk.cu", "periodic.cu", "adjoint.cu", "cic.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

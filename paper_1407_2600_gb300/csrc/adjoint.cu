@@ -1,0 +1,696 @@
+// Reverse mode of the force evaluation (vector-Jacobian product).  Not in the
+// paper: the adjoint differentiates the tree force with its discrete decisions
+// (tree, groups, images, acceptance) held fixed, so it is the exact derivative
+// of the accelerations the forward kernels compute.
+//
+// For cotangents lam of the accelerations, mu = (da/dx)^T lam collects
+//  * per sink: the Hessian-vector products of every M2P expansion used by its
+//    group, minus the P2P tidal terms, plus the image field's local Hessian;
+//  * per source particle: the P2P tidal terms of every group that summed it
+//    directly (a diagonal pairing over the warp, one atomic per source and group);
+//  * through the moments: the cotangents of the scaled M2P expansions per cell
+//    (atomics), carried down the tree by the transposed shifts (M2M^T) and
+//    onto the particles (P2M^T); likewise the image field's cotangents onto
+//    the level-3 cells and their particles.
+#include <math.h>
+
+#include "common.cuh"
+#include "m2p_gen.cuh"
+#include "adj_gen.cuh"
+#include "walk_common.cuh"
+
+namespace {
+
+template <int P> struct AOrd;
+#define NB_AORD(P)                                                                                      \
+  template <> struct AOrd<P> {                                                                          \
+    static constexpr int NBS = (kNB##P + 3) & ~3;                                                       \
+    static constexpr int NM = (P + 1) * (P + 2) * (P + 3) / 6;                                          \
+    template <typename T>                                                                               \
+    static __device__ __forceinline__ void self(const T* B, T x, T y, T z, T e2, T lx, T ly, T lz, T& ox, \
+                                                T& oy, T& oz) {                                         \
+      m2p_adj_self_p##P<T>(B, x, y, z, e2, lx, ly, lz, ox, oy, oz);                                     \
+    }                                                                                                   \
+    template <typename T>                                                                               \
+    static __device__ __forceinline__ void src(T x, T y, T z, T e2, T lx, T ly, T lz, T* nu) {          \
+      m2p_adj_src_p##P<T>(x, y, z, e2, lx, ly, lz, nu);                                                 \
+    }                                                                                                   \
+    static __device__ __forceinline__ void m2madj(const double* nup, double x, double y, double z,      \
+                                                  double* nuc) {                                        \
+      m2m_adj_acc_p##P(nup, x, y, z, nuc);                                                              \
+    }                                                                                                   \
+    static __device__ __forceinline__ void p2madj(double m, double x, double y, double z, const double* nu, \
+                                                  double& gx, double& gy, double& gz) {                 \
+      p2m_adj_p##P(m, x, y, z, nu, gx, gy, gz);                                                         \
+    }                                                                                                   \
+  };
+NB_AORD(0)
+NB_AORD(1)
+NB_AORD(2)
+NB_AORD(3)
+NB_AORD(4)
+
+template <typename T>
+struct AdjArgs {
+  DevTree tr;
+  const T* coef;
+  const typename Vec4<T>::type* src;
+  const T* eps2;
+  long long thr[NB_NLEV];
+  int n_direct, le;
+  int* stack;
+  int stack_cap;
+  int* group_ctr;
+  const float* lam;  // 3n, key order
+  double* mu;        // 3n, key order
+  float* nuc;        // per cell NM, scaled cotangents of the moments
+  unsigned* status;
+};
+
+constexpr double kScale = 1.0 / 8388608.0;
+
+template <typename T, int P, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NBS = AOrd<P>::NBS, NM = AOrd<P>::NM;
+  __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
+  __shared__ V4 s_src[WARPS][32];
+  __shared__ int s_jidx[WARPS][32];
+  __shared__ T s_moff[WARPS][32][4];
+  __shared__ T s_meps[WARPS][32];
+  __shared__ int s_midx[WARPS][32];
+  __shared__ int s_pfx[WARPS][32], s_pst[WARPS][32], s_plev[WARPS][32];
+  __shared__ T s_poff[WARPS][32][3];
+  __shared__ int4 s_pcen[WARPS][32];
+  __shared__ T s_sx[WARPS][32][3];
+  __shared__ T s_sl[WARPS][32][3];
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned ltmask = (1u << lane) - 1u;
+  const DevTree& tr = w.tr;
+  int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
+  const T scale = (T)kScale;
+
+  while (true) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(w.group_ctr, 1);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= tr.ngroup) break;
+    const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
+    const int cnt = ga.y, box = ga.z;
+    const T eps2 = w.eps2[box];
+    const bool act = lane < cnt;
+    const int i = ga.x + (act ? lane : 0);
+    T xi, yi, zi, lx = 0, ly = 0, lz = 0;
+    {
+      V4 o = w.src[i];
+      int4 la = tr.cA[tr.sleaf[i]];
+      xi = o.x + (T)(la.x - gd.x) * scale;
+      yi = o.y + (T)(la.y - gd.y) * scale;
+      zi = o.z + (T)(la.z - gd.z) * scale;
+      if (act) {
+        lx = (T)w.lam[i];
+        ly = (T)w.lam[tr.n + i];
+        lz = (T)w.lam[2 * tr.n + i];
+      }
+    }
+    s_sx[wid][lane][0] = xi;
+    s_sx[wid][lane][1] = yi;
+    s_sx[wid][lane][2] = zi;
+    s_sl[wid][lane][0] = lx;
+    s_sl[wid][lane][1] = ly;
+    s_sl[wid][lane][2] = lz;
+    T mx = 0, my = 0, mz = 0;  // sink cotangent
+    int top = 1;
+    if (lane == 0) stk[0] = box;
+    __syncwarp();
+    bool overflow = false;
+    while (top > 0) {
+      const int nb = min(32, top);
+      const int base = top - nb;
+      top = base;
+      int c = -1;
+      int4 ca = make_int4(0, 0, 0, 0), cb = make_int4(0, 0, 0, 0);
+      if (lane < nb) {
+        c = stk[base + lane];
+        ca = tr.cA[c];
+        cb = tr.cB[c];
+      }
+      __syncwarp();
+      int cls = NB_CELL_NONE, kx = 0, ky = 0, kz = 0;
+      const int lvl = ca.w & 0xff, nch = ca.w >> 8;
+      if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, kx, ky, kz);
+      {
+        const int nc = (cls == NB_CELL_OPEN) ? nch : 0;
+        const int pre = warp_excl_scan(nc, lane);
+        const int tot = __shfl_sync(FULL, pre + nc, 31);
+        if (top + tot > w.stack_cap) {
+          overflow = true;
+          break;
+        }
+        for (int q = 0; q < nc; q++) stk[top + pre + q] = cb.z + q;
+        top += tot;
+        __syncwarp();
+      }
+      const unsigned mm = __ballot_sync(FULL, cls == NB_CELL_M2P);
+      if (mm) {
+        const int nmp = __popc(mm);
+        if (cls == NB_CELL_M2P) {
+          const int pos = __popc(mm & ltmask);
+          const T sc = (T)(1 << lvl);
+          s_midx[wid][pos] = c;
+          s_moff[wid][pos][0] = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
+          s_moff[wid][pos][1] = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
+          s_moff[wid][pos][2] = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
+          s_moff[wid][pos][3] = sc;
+          s_meps[wid][pos] = eps2 * (sc * sc);
+        }
+        __syncwarp();
+        for (int t = lane; t < nmp * NBS; t += 32) {
+          const int q = t / NBS, r = t - q * NBS;
+          s_coef[wid][t] = w.coef[(int64_t)s_midx[wid][q] * NBS + r];
+        }
+        __syncwarp();
+        // sink side: Hessian-vector products (in the cell unit, times 2^level)
+        if (act) {
+          for (int q = 0; q < nmp; q++) {
+            const T sc = s_moff[wid][q][3];
+            T ox = 0, oy = 0, oz = 0;
+            AOrd<P>::template self<T>(&s_coef[wid][q * NBS], fma(xi, sc, s_moff[wid][q][0]),
+                                      fma(yi, sc, s_moff[wid][q][1]), fma(zi, sc, s_moff[wid][q][2]),
+                                      s_meps[wid][q], lx, ly, lz, ox, oy, oz);
+            mx = fma(ox, sc, mx);
+            my = fma(oy, sc, my);
+            mz = fma(oz, sc, mz);
+          }
+        }
+        // source side: lane q owns cell q and sums over the group's sinks
+        if (lane < nmp) {
+          const T sc = s_moff[wid][lane][3];
+          const T ox = s_moff[wid][lane][0], oy = s_moff[wid][lane][1], oz = s_moff[wid][lane][2];
+          const T e2 = s_meps[wid][lane];
+          T nu[NM];
+#pragma unroll
+          for (int t = 0; t < NM; t++) nu[t] = (T)0;
+          for (int sk = 0; sk < cnt; sk++)
+            AOrd<P>::template src<T>(fma(s_sx[wid][sk][0], sc, ox), fma(s_sx[wid][sk][1], sc, oy),
+                                     fma(s_sx[wid][sk][2], sc, oz), e2, s_sl[wid][sk][0], s_sl[wid][sk][1],
+                                     s_sl[wid][sk][2], nu);
+          float* dst = w.nuc + (int64_t)s_midx[wid][lane] * NM;
+#pragma unroll
+          for (int t = 0; t < NM; t++) atomicAdd(dst + t, (float)nu[t]);
+        }
+        __syncwarp();
+      }
+      const unsigned pm = __ballot_sync(FULL, cls == NB_CELL_P2P);
+      if (pm) {
+        const int ncl = (cls == NB_CELL_P2P) ? cb.y : 0;
+        const int pre = warp_excl_scan(ncl, lane);
+        const int total = __shfl_sync(FULL, pre + ncl, 31);
+        s_pfx[wid][lane] = pre;
+        s_pst[wid][lane] = cb.x;
+        s_plev[wid][lane] = lvl;
+        s_pcen[wid][lane] = ca;
+        s_poff[wid][lane][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
+        s_poff[wid][lane][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
+        s_poff[wid][lane][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
+        __syncwarp();
+        for (int b0 = 0; b0 < total; b0 += 32) {
+          const int t = b0 + lane;
+          int jsrc = -1;
+          if (t < total) {
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (s_pfx[wid][mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            const int q = lo;
+            const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
+            V4 v = w.src[j];
+            T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
+            if (s_plev[wid][q] < w.le) {
+              const int4 pc = s_pcen[wid][q];
+              int jx, jy, jz;
+              particle_image(tr.skeys[j], w.le, gd, jx, jy, jz);
+              ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
+              oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
+              oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;
+            }
+            v.x = v.x + ox;
+            v.y = v.y + oy;
+            v.z = v.z + oz;
+            s_src[wid][lane] = v;
+            jsrc = j;
+          }
+          s_jidx[wid][lane] = jsrc;
+          __syncwarp();
+          const int nn = min(32, total - b0);
+          // diagonal pairing: in round k lane l takes source (l+k) mod 32 and
+          // passes the source-side term to the lane that owns that source
+          T sx = 0, sy = 0, sz = 0;
+          for (int k = 0; k < 32; k++) {
+            const int q = (lane + k) & 31;
+            T wx = 0, wy = 0, wz = 0;
+            if (act && q < nn && s_jidx[wid][q] != i) {
+              const V4 s = s_src[wid][q];
+              const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+              const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+              const T inv = nbody_rsqrt(r2);
+              const T f = (inv * inv) * inv;
+              const T g5 = f * (inv * inv) * (T)3;
+              const T rl = fma(dx, lx, fma(dy, ly, dz * lz));
+              const T a = s.w * f, b = s.w * g5 * rl;
+              wx = fma(a, lx, -b * dx);
+              wy = fma(a, ly, -b * dy);
+              wz = fma(a, lz, -b * dz);
+            }
+            mx -= wx;
+            my -= wy;
+            mz -= wz;
+            const int from = (lane - k) & 31;
+            sx += __shfl_sync(FULL, wx, from);
+            sy += __shfl_sync(FULL, wy, from);
+            sz += __shfl_sync(FULL, wz, from);
+          }
+          if (lane < nn) {
+            const int j = s_jidx[wid][lane];
+            atomicAdd(&w.mu[j], (double)sx);
+            atomicAdd(&w.mu[tr.n + j], (double)sy);
+            atomicAdd(&w.mu[2 * tr.n + j], (double)sz);
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (overflow) {
+      if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
+      continue;
+    }
+    if (act) {
+      atomicAdd(&w.mu[i], (double)mx);
+      atomicAdd(&w.mu[tr.n + i], (double)my);
+      atomicAdd(&w.mu[2 * tr.n + i], (double)mz);
+    }
+  }
+}
+
+// ---- image field --------------------------------------------------------------------
+template <int PE> struct AFE;
+#define NB_AFE(PE)                                                                                  \
+  template <> struct AFE<PE> {                                                                      \
+    static constexpr int NL = kNL##PE;                                                              \
+    static constexpr int NE = (PE + 1) * (PE + 2) * (PE + 3) / 6;                                   \
+    static constexpr int NP = (PE + 2) * (PE + 3) * (PE + 4) / 6;                                   \
+    template <typename T>                                                                           \
+    static __device__ __forceinline__ void hess(const T* L, T x, T y, T z, T lx, T ly, T lz, T& ox, T& oy, \
+                                                T& oz) {                                            \
+      l2p_hess_pe##PE<T>(L, x, y, z, lx, ly, lz, ox, oy, oz);                                       \
+    }                                                                                               \
+    template <typename T>                                                                           \
+    static __device__ __forceinline__ void ladj(T x, T y, T z, T lx, T ly, T lz, T* Lb) {           \
+      l2p_adj_pe##PE<T>(x, y, z, lx, ly, lz, Lb);                                                   \
+    }                                                                                               \
+    template <typename T>                                                                           \
+    static __device__ __forceinline__ void madj(const T* Lb, const T* D, T* nu) {                   \
+      m2l_adj_pe##PE<T>(Lb, D, nu);                                                                 \
+    }                                                                                               \
+    static __device__ __forceinline__ void p2madj(double m, double x, double y, double z, const double* nu, \
+                                                  double& gx, double& gy, double& gz) {             \
+      p2m_adj_p##PE(m, x, y, z, nu, gx, gy, gz);                                                    \
+    }                                                                                               \
+  };
+NB_AFE(1)
+NB_AFE(2)
+NB_AFE(3)
+NB_AFE(4)
+
+__constant__ unsigned char c_apar[84];  // bit d set: multi-index odd in axis d
+
+template <typename T>
+struct AFArgs {
+  DevTree tr;
+  const typename Vec4<T>::type* src;
+  const double* fm;   // field moments (box, cell, NE)
+  const T* tab;       // phi~ table
+  int le, lg;
+  const T* lbuf;      // forward per-run expansion (NL, V, Mt)
+  int lstride;
+  double* lbar;       // per run cotangents (NL + 3)
+  int bstride;
+  const float* lam;
+  double* mu;
+  double* nue;        // field-moment cotangents (box, cell, NE)
+};
+
+// per group, lane = sink: local Hessian (sink side) and the run's cotangents
+template <typename T, int PE>
+__global__ void __launch_bounds__(128) adj_field_local_kernel(AFArgs<T> a) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NL = AFE<PE>::NL;
+  const int lane = threadIdx.x & 31;
+  const DevTree& tr = a.tr;
+  const T scale = (T)kScale;
+  const T fourpi3 = (T)(4.0 * M_PI / 3.0);
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+    const int4 ga = tr.gA[g], gd = tr.gD[g];
+    const bool act = lane < ga.y;
+    const T* Lr = a.lbuf + (int64_t)gd.w * a.lstride;
+    T Lb[NL];
+#pragma unroll
+    for (int t = 0; t < NL; t++) Lb[t] = (T)0;
+    T lx = 0, ly = 0, lz = 0;
+    if (act) {
+      const int i = ga.x + lane;
+      lx = (T)a.lam[i];
+      ly = (T)a.lam[tr.n + i];
+      lz = (T)a.lam[2 * tr.n + i];
+      const V4 o4 = a.src[i];
+      const int4 la = tr.cA[tr.sleaf[i]];
+      const T dx = o4.x + (T)(la.x - gd.x) * scale;
+      const T dy = o4.y + (T)(la.y - gd.y) * scale;
+      const T dz = o4.z + (T)(la.z - gd.z) * scale;
+      T L[NL];
+#pragma unroll
+      for (int t = 0; t < NL; t++) L[t] = Lr[t];
+      const T mt = Lr[NL + 3];
+      T ox = fourpi3 * mt * lx, oy = fourpi3 * mt * ly, oz = fourpi3 * mt * lz;
+      AFE<PE>::template hess<T>(L, dx, dy, dz, lx, ly, lz, ox, oy, oz);
+      a.mu[i] += (double)ox;  // one thread per sink: plain adds after the walk's atomics
+      a.mu[tr.n + i] += (double)oy;
+      a.mu[2 * tr.n + i] += (double)oz;
+      AFE<PE>::template ladj<T>(dx, dy, dz, lx, ly, lz, Lb);
+    }
+    double* dst = a.lbar + (int64_t)gd.w * a.bstride;
+#pragma unroll
+    for (int t = 0; t < NL; t++) {
+      T v = Lb[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) atomicAdd(dst + t, (double)v);
+    }
+    T vx = -fourpi3 * lx, vy = -fourpi3 * ly, vz = -fourpi3 * lz;
+    for (int o = 16; o > 0; o >>= 1) {
+      vx += __shfl_xor_sync(0xffffffffu, vx, o);
+      vy += __shfl_xor_sync(0xffffffffu, vy, o);
+      vz += __shfl_xor_sync(0xffffffffu, vz, o);
+    }
+    if (lane == 0) {
+      atomicAdd(dst + NL, (double)vx);
+      atomicAdd(dst + NL + 1, (double)vy);
+      atomicAdd(dst + NL + 2, (double)vz);
+    }
+  }
+}
+
+// per run (first group), lane = level-le cell: transposed M2L onto the cells
+template <typename T, int PE>
+__global__ void __launch_bounds__(128) adj_field_m2l_kernel(AFArgs<T> a) {
+  constexpr int NL = AFE<PE>::NL, NE = AFE<PE>::NE, NP = AFE<PE>::NP;
+  const int lane = threadIdx.x & 31;
+  const DevTree& tr = a.tr;
+  const int ncp = 1 << (3 * a.le);
+  const int m = (1 << (a.lg - 1)) + 2;
+  const int step = 1 << (23 - a.lg);
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+    const int4 ga = tr.gA[g];
+    if (ga.w == 0) continue;
+    const int4 gd = tr.gD[g];
+    const int box = ga.z;
+    const double* Lbr = a.lbar + (int64_t)gd.w * a.bstride;
+    T Lb[NL];
+#pragma unroll
+    for (int t = 0; t < NL; t++) Lb[t] = (T)Lbr[t];
+    const T vbx = (T)Lbr[NL], vby = (T)Lbr[NL + 1], vbz = (T)Lbr[NL + 2];
+    for (int cell = lane; cell < ncp; cell += 32) {
+      const double* Mc = a.fm + ((int64_t)box * ncp + cell) * NE;
+      if (Mc[0] == 0.0) continue;
+      const int cx2 = cell_c2((int)compact3((uint64_t)cell), a.le);
+      const int cy2 = cell_c2((int)compact3((uint64_t)cell >> 1), a.le);
+      const int cz2 = cell_c2((int)compact3((uint64_t)cell >> 2), a.le);
+      const int kx = img_shift(cx2, gd.x), ky = img_shift(cy2, gd.y), kz = img_shift(cz2, gd.z);
+      const int ox = cx2 - kx * NB_PBOX - gd.x, oy = cy2 - ky * NB_PBOX - gd.y, oz = cz2 - kz * NB_PBOX - gd.z;
+      const int irx = -ox / step, iry = -oy / step, irz = -oz / step;
+      const int neg = (irx < 0 ? 1 : 0) | (iry < 0 ? 2 : 0) | (irz < 0 ? 4 : 0);
+      const int node = (abs(irx) * m + abs(iry)) * m + abs(irz);
+      const T* srcp = a.tab + (int64_t)node * NP;
+      T D[NP];
+#pragma unroll
+      for (int t = 0; t < NP; t++) {
+        const T v = srcp[t];
+        D[t] = (__popc(c_apar[t] & neg) & 1) ? -v : v;
+      }
+      T nu[NE];
+#pragma unroll
+      for (int t = 0; t < NE; t++) nu[t] = (T)0;
+      AFE<PE>::template madj<T>(Lb, D, nu);
+      nu[1] += vbx;  // the background term's dipole (V = sum m (c*-e) + D)
+      nu[2] += vby;
+      nu[3] += vbz;
+      double* dst = a.nue + ((int64_t)box * ncp + cell) * NE;
+#pragma unroll
+      for (int t = 0; t < NE; t++) atomicAdd(dst + t, (double)nu[t]);
+    }
+  }
+}
+
+// one thread per particle: field-moment cotangents onto the particle
+template <int PE>
+__global__ void adj_field_p2m_kernel(DevTree tr, int le, const double* __restrict__ nue, double* __restrict__ mu) {
+  constexpr int NE = AFE<PE>::NE;
+  const int ncp = 1 << (3 * le);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < tr.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int box = tr.sbox[j];
+    const int cell = (int)(tr.skeys[j] >> (3 * (NB_QBITS - le)));
+    const double* nu = nue + ((int64_t)box * ncp + cell) * NE;
+    double nl[NE];
+#pragma unroll
+    for (int t = 0; t < NE; t++) nl[t] = nu[t];
+    const double cx = ldexp((double)cell_c2((int)compact3((uint64_t)cell), le), -23);
+    const double cy = ldexp((double)cell_c2((int)compact3((uint64_t)cell >> 1), le), -23);
+    const double cz = ldexp((double)cell_c2((int)compact3((uint64_t)cell >> 2), le), -23);
+    double gx = 0, gy = 0, gz = 0;
+    AFE<PE>::p2madj((double)tr.smass[j], tr.spos[j] - cx, tr.spos[tr.n + j] - cy, tr.spos[2 * tr.n + j] - cz, nl,
+                    gx, gy, gz);
+    mu[j] += gx;
+    mu[tr.n + j] += gy;
+    mu[2 * tr.n + j] += gz;
+  }
+}
+
+// ---- moments: unscale, down the tree, onto the particles --------------------------------
+template <int P>
+__global__ void adj_unscale_kernel(int ncell, const int4* __restrict__ cA, const float* __restrict__ nuc,
+                                   double* __restrict__ nu) {
+  constexpr int NM = AOrd<P>::NM;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const int lvl = cA[c].w & 0xff;
+    int t = 0;
+    for (int o = 0; o <= P; o++) {
+      // nu_n = nu'_n (-1)^|n| / n! h^(-2-|n|), h = 2^-level
+      const double sc = ldexp(1.0, lvl * (2 + o)) * ((o & 1) ? -1.0 : 1.0);
+      for (int nx = o; nx >= 0; nx--)
+        for (int ny = o - nx; ny >= 0; ny--, t++) {
+          const int nz = o - nx - ny;
+          double f = 1.0;
+          for (int q = 2; q <= nx; q++) f *= q;
+          for (int q = 2; q <= ny; q++) f *= q;
+          for (int q = 2; q <= nz; q++) f *= q;
+          nu[(int64_t)c * NM + t] = (double)nuc[(int64_t)c * NM + t] * sc / f;
+        }
+    }
+  }
+}
+
+template <int P>
+__global__ void adj_down_kernel(int ncell, int level, const int4* __restrict__ cA, const int4* __restrict__ cB,
+                                double* __restrict__ nu) {
+  constexpr int NM = AOrd<P>::NM;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const int4 a = cA[c];
+    if ((a.w & 0xff) != level) continue;
+    const int par = cB[c].w;
+    if (par < 0) continue;
+    const int4 pa = cA[par];
+    double nup[NM], nc[NM];
+#pragma unroll
+    for (int t = 0; t < NM; t++) {
+      nup[t] = nu[(int64_t)par * NM + t];
+      nc[t] = nu[(int64_t)c * NM + t];
+    }
+    AOrd<P>::m2madj(nup, ldexp((double)(a.x - pa.x), -23), ldexp((double)(a.y - pa.y), -23),
+                    ldexp((double)(a.z - pa.z), -23), nc);
+#pragma unroll
+    for (int t = 0; t < NM; t++) nu[(int64_t)c * NM + t] = nc[t];
+  }
+}
+
+template <int P>
+__global__ void adj_p2m_kernel(DevTree tr, const double* __restrict__ nu, double* __restrict__ mu) {
+  constexpr int NM = AOrd<P>::NM;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < tr.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int leaf = tr.sleaf[j];
+    const int4 a = tr.cA[leaf];
+    double nl[NM];
+#pragma unroll
+    for (int t = 0; t < NM; t++) nl[t] = nu[(int64_t)leaf * NM + t];
+    double gx = 0, gy = 0, gz = 0;
+    AOrd<P>::p2madj((double)tr.smass[j], tr.spos[j] - ldexp((double)a.x, -23), tr.spos[tr.n + j] - ldexp((double)a.y, -23),
+                    tr.spos[2 * tr.n + j] - ldexp((double)a.z, -23), nl, gx, gy, gz);
+    mu[j] += gx;
+    mu[tr.n + j] += gy;
+    mu[2 * tr.n + j] += gz;
+  }
+}
+
+__global__ void adj_prep_kernel(int64_t n, const uint32_t* __restrict__ perm, const float* __restrict__ lam,
+                                float* __restrict__ lam_s, double* __restrict__ mu) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = perm[i];
+    for (int d = 0; d < 3; d++) {
+      lam_s[d * n + i] = lam[d * n + j];
+      mu[d * n + i] = 0.0;
+    }
+  }
+}
+
+__global__ void adj_scatter_kernel(int64_t n, const uint32_t* __restrict__ perm, const double* __restrict__ mu,
+                                   double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t j = perm[i];
+    for (int d = 0; d < 3; d++) out[d * n + j] = mu[d * n + i];
+  }
+}
+
+int gridv(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)g;
+}
+
+bool g_apar_done[64] = {false};
+
+}  // namespace
+
+struct AdjBuffers {
+  float* lam_s;
+  double* mu;
+  float* nuc;
+  double* nu;
+  double* lbar;
+  double* nue;
+  int* group_ctr;
+};
+
+int nb_adj_coef_nm(int order) { return (order + 1) * (order + 2) * (order + 3) / 6; }
+int nb_adj_lbar_stride(int pe) { return pe > 0 ? ((pe + 2) * (pe + 3) * (pe + 4) / 6 - 1) + 3 : 0; }
+
+cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int le, int lg, const void* coef,
+                          const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
+                          int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
+                          int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
+                          unsigned* status, int nsm, cudaStream_t s) {
+  if (fp64) return cudaErrorNotSupported;  // the reverse mode runs the mixed-precision walk
+  if (pe > 4) return cudaErrorNotSupported;
+  cudaError_t e;
+  const int NM = nb_adj_coef_nm(order);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !g_apar_done[dev]) {
+    unsigned char pm[84];
+    for (int o = 0, t = 0; o <= 6; o++)
+      for (int nx = o; nx >= 0; nx--)
+        for (int ny = o - nx; ny >= 0; ny--, t++) pm[t] = (unsigned char)((nx & 1) | ((ny & 1) << 1) | (((o - nx - ny) & 1) << 2));
+    if ((e = cudaMemcpyToSymbol(c_apar, pm, sizeof(pm)))) return e;
+    g_apar_done[dev] = true;
+  }
+  adj_prep_kernel<<<gridv(tr.n, 256), 256, 0, s>>>(tr.n, tr.perm, lam, B.lam_s, B.mu);
+  if ((e = cudaMemsetAsync(B.nuc, 0, sizeof(float) * (size_t)tr.ncell * NM, s))) return e;
+  if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;
+  nb_launch_counter += 1;
+  {
+    AdjArgs<float> a;
+    a.tr = tr;
+    a.coef = (const float*)coef;
+    a.src = (const float4*)src;
+    a.eps2 = (const float*)eps2;
+    for (int l = 0; l < NB_NLEV; l++) a.thr[l] = thr[l];
+    a.n_direct = n_direct;
+    a.le = le;
+    a.stack = stack;
+    a.stack_cap = stack_cap;
+    a.group_ctr = B.group_ctr;
+    a.lam = B.lam_s;
+    a.mu = B.mu;
+    a.nuc = B.nuc;
+    a.status = status;
+    constexpr int W = 4;
+    int occ = 0;
+#define NB_ADJW(P)                                                                                         \
+  {                                                                                                        \
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_walk_kernel<float, P, W>, W * 32, 0))) \
+      return e;                                                                                            \
+    int grid = nsm * (occ > 0 ? occ : 1);                                                                  \
+    if (grid * W > max_blocks * 8) grid = max_blocks * 8 / W;                                              \
+    adj_walk_kernel<float, P, W><<<grid, W * 32, 0, s>>>(a);                                               \
+    break;                                                                                                 \
+  }
+    switch (order) {
+      case 0: NB_ADJW(0)
+      case 1: NB_ADJW(1)
+      case 2: NB_ADJW(2)
+      case 3: NB_ADJW(3)
+      default: NB_ADJW(4)
+    }
+#undef NB_ADJW
+    nb_launch_counter += 1;
+  }
+  if ((e = cudaGetLastError())) return e;
+  if (pe > 0) {
+    const int ncp = 1 << (3 * le);
+    if ((e = cudaMemsetAsync(B.lbar, 0, sizeof(double) * (size_t)tr.ngroup * nb_adj_lbar_stride(pe), s))) return e;
+    const int NE = (pe + 1) * (pe + 2) * (pe + 3) / 6;
+    if ((e = cudaMemsetAsync(B.nue, 0, sizeof(double) * (size_t)tr.nbox * ncp * NE, s))) return e;
+    AFArgs<float> a{tr, (const float4*)src, fm, (const float*)tab, le, lg, (const float*)lbuf, lstride, B.lbar,
+                    nb_adj_lbar_stride(pe), B.lam_s, B.mu, B.nue};
+    int grid = (int)(((int64_t)tr.ngroup * 32 + 127) / 128);
+    if (grid > 152 * 64) grid = 152 * 64;
+    if (grid < 1) grid = 1;
+#define NB_ADJF(PE)                                                                          \
+  {                                                                                          \
+    adj_field_local_kernel<float, PE><<<grid, 128, 0, s>>>(a);                               \
+    adj_field_m2l_kernel<float, PE><<<grid, 128, 0, s>>>(a);                                 \
+    adj_field_p2m_kernel<PE><<<gridv(tr.n, 128), 128, 0, s>>>(tr, le, B.nue, B.mu);          \
+    break;                                                                                   \
+  }
+    switch (pe) {
+      case 1: NB_ADJF(1)
+      case 2: NB_ADJF(2)
+      case 3: NB_ADJF(3)
+      default: NB_ADJF(4)
+    }
+#undef NB_ADJF
+    nb_launch_counter += 3;
+    if ((e = cudaGetLastError())) return e;
+  }
+#define NB_ADJD(P)                                                                                   \
+  {                                                                                                  \
+    adj_unscale_kernel<P><<<gridv(tr.ncell, 128), 128, 0, s>>>(tr.ncell, tr.cA, B.nuc, B.nu);         \
+    for (int l = 1; l <= max_level; l++)                                                             \
+      adj_down_kernel<P><<<gridv(tr.ncell, 128), 128, 0, s>>>(tr.ncell, l, tr.cA, tr.cB, B.nu);       \
+    adj_p2m_kernel<P><<<gridv(tr.n, 128), 128, 0, s>>>(tr, B.nu, B.mu);                               \
+    break;                                                                                           \
+  }
+  switch (order) {
+    case 0: NB_ADJD(0)
+    case 1: NB_ADJD(1)
+    case 2: NB_ADJD(2)
+    case 3: NB_ADJD(3)
+    default: NB_ADJD(4)
+  }
+#undef NB_ADJD
+  nb_launch_counter += 2 + max_level;
+  adj_scatter_kernel<<<gridv(tr.n, 256), 256, 0, s>>>(tr.n, tr.perm, B.mu, out);
+  nb_launch_counter += 1;
+  return cudaGetLastError();
+}

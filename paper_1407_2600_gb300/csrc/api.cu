@@ -48,6 +48,22 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
+struct AdjBuffers {
+  float* lam_s;
+  double* mu;
+  float* nuc;
+  double* nu;
+  double* lbar;
+  double* nue;
+  int* group_ctr;
+};
+int nb_adj_coef_nm(int order);
+int nb_adj_lbar_stride(int pe);
+cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int le, int lg, const void* coef,
+                          const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
+                          int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
+                          int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
+                          unsigned* status, int nsm, cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         cudaStream_t s);
@@ -112,6 +128,10 @@ struct nbody_tree {
   const float* tab32 = nullptr;
   // walk
   Buf eps2, stack, gctr, accw, counters, lbuf;
+  // reverse mode
+  Buf a_lam, a_mu, a_nuc, a_nu, a_lbar, a_nue, a_x0, a_x1, a_ph, a_g, a_lg, a_lx, a_lp, a_out;
+  bool forces_valid = false;
+  nbody_tree* aux = nullptr;  // second tree of the KDK adjoint (state at the step's end)
   int walk_blocks = 0;
   long long thr[NB_NLEV];
   int64_t* pinned = nullptr;
@@ -130,9 +150,12 @@ struct nbody_tree {
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
                   &hval, &mom, &arrive, &coef, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
-                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf};
+                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf,
+                  &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
+                  &a_lx, &a_lp, &a_out};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
+    delete aux;
     if (events)
       for (int r = 0; r < kRing; r++) {
         for (auto& e : bev[r]) cudaEventDestroy(e);
@@ -247,6 +270,43 @@ __global__ void eps2_kernel(int nbox, const double* __restrict__ eps, float* __r
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
     e32[b] = (float)(eps[b] * eps[b]);
     e64[b] = eps[b] * eps[b];
+  }
+}
+
+// elementwise pieces of the KDK step and its reverse
+__global__ void lin_kernel(int64_t n3, int mode, const float* __restrict__ a, const float* __restrict__ b,
+                           const float* __restrict__ g, double k, float* __restrict__ out, void*, void*) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a ? (float)((double)a[i] + k * (double)g[i]) : (float)(k * (double)b[i]);
+}
+
+__global__ void drift_from_kernel(int64_t n3, const double* __restrict__ x0, const float* __restrict__ p, double d,
+                                  double* __restrict__ x1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = x0[i] + d * (double)p[i];
+    x -= floor(x);
+    if (x >= 1.0) x = 0.0;
+    x1[i] = x;
+  }
+}
+
+__global__ void lin64_kernel(int64_t n3, const double* __restrict__ lx1, const double* __restrict__ mu,
+                             const float* __restrict__ lp1, double d, double k1, double* __restrict__ lx,
+                             double* __restrict__ lp, float* __restrict__ lg) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = lx1[i] + mu[i];
+    const double p = (double)lp1[i] + d * x;
+    lx[i] = x;
+    lp[i] = p;
+    lg[i] = (float)(k1 * p);
+  }
+}
+
+__global__ void fin_kernel(int64_t n3, const double* __restrict__ lx, const double* __restrict__ mu,
+                           const double* __restrict__ lp, double* __restrict__ lx0, float* __restrict__ lp0) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    lx0[i] = lx[i] + mu[i];
+    lp0[i] = (float)lp[i];
   }
 }
 
@@ -416,6 +476,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   }
   NB_CU(cudaEventRecord(be[3], s));
   t->nb_log++;
+  t->forces_valid = false;
   return NBODY_OK;
 }
 
@@ -461,6 +522,43 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
   nb_launch_counter += 1;
   t->nf_log++;
+  t->forces_valid = true;
+  return NBODY_OK;
+}
+
+// out = (d acc / d pos)^T lam for the tree as last built (forces refreshed if needed)
+int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
+  const nbody_params& p = t->prm;
+  if (p.precision != NBODY_MIXED || p.ewald_order > 4) return NBODY_ENOTSUP;
+  const int64_t n = t->n;
+  if (!t->forces_valid) {
+    NB_CU(t->a_g.ensure(12 * n));
+    int rc = forces_impl(t, t->a_g.as<float>(), s);
+    if (rc) return rc;
+  }
+  const int nm = nb_adj_coef_nm(p.order);
+  NB_CU(t->a_lam.ensure(12 * n));
+  NB_CU(t->a_mu.ensure(24 * n));
+  NB_CU(t->a_nuc.ensure(4 * (int64_t)t->ncell * nm));
+  NB_CU(t->a_nu.ensure(8 * (int64_t)t->ncell * nm));
+  if (p.ewald_order > 0) {
+    const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
+    NB_CU(t->a_lbar.ensure(8 * (int64_t)t->ngroup * nb_adj_lbar_stride(p.ewald_order)));
+    NB_CU(t->a_nue.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
+  }
+  AdjBuffers B;
+  B.lam_s = t->a_lam.as<float>();
+  B.mu = t->a_mu.as<double>();
+  B.nuc = t->a_nuc.as<float>();
+  B.nu = t->a_nu.as<double>();
+  B.lbar = t->a_lbar.as<double>();
+  B.nue = t->a_nue.as<double>();
+  B.group_ctr = t->gctr.as<int>();
+  DevTree tr = t->dev();
+  NB_CU(nb_forces_vjp(tr, false, p.order, p.ewald_order, p.ewald_level, p.ewald_grid, t->coef.p, t->src.p,
+                      t->eps2.p, t->thr, p.n_direct, t->stack.as<int>(), kStackCap, t->walk_blocks,
+                      t->fm.as<double>(), t->tab32, t->lbuf.p, nb_field_stride(p.ewald_order), p.lmax, lam, out,
+                      B, t->status.as<unsigned>(), t->nsm, s));
   return NBODY_OK;
 }
 
@@ -599,8 +697,8 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_str
 int nbody_kdk_step(nbody_tree* tree, double* pos_dev, float* mom_dev, float* acc_dev, double a0, double a1,
                    nbody_stream_t stream) {
   if (!tree || !pos_dev || !mom_dev || !acc_dev || !(a0 > 0.0) || !(a1 > 0.0)) return NBODY_EINVAL;
-  if (pos_dev != tree->pos) return NBODY_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  tree->pos = pos_dev;
   const double H0 = sqrt(8.0 * M_PI / 3.0);
   const double ah = sqrt(a0 * a1);
   const double K1 = 2.0 / H0 * (sqrt(ah) - sqrt(a0));
@@ -624,12 +722,101 @@ int nbody_kdk_step(nbody_tree* tree, double* pos_dev, float* mom_dev, float* acc
   return read_status(tree, s);
 }
 
-int nbody_kdk_adjoint(nbody_tree*, const double*, const float*, double, double, const double*, const float*,
-                      double*, float*, nbody_stream_t) {
-  return NBODY_ENOTSUP;
+int nbody_forces_vjp(nbody_tree* t, const float* lam_dev, double* out_dev, nbody_stream_t stream) {
+  if (!t || !lam_dev || !out_dev) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long l0 = nb_launch_counter;
+  int rc = vjp_impl(t, lam_dev, out_dev, s);
+  t->launches += nb_launch_counter - l0;
+  if (rc) return rc;
+  if (t->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  return read_status(t, s);
 }
 
-int nbody_forces_vjp(nbody_tree*, const float*, double*, nbody_stream_t) { return NBODY_ENOTSUP; }
+int nbody_kdk_adjoint(nbody_tree* t, const double* pos0, const float* mom0, double a0, double a1,
+                      const double* lam_pos1, const float* lam_mom1, double* lam_pos0, float* lam_mom0,
+                      nbody_stream_t stream) {
+  if (!t || !pos0 || !mom0 || !lam_pos1 || !lam_mom1 || !lam_pos0 || !lam_mom0 || !(a0 > 0.0) || !(a1 > 0.0))
+    return NBODY_EINVAL;
+  if (t->prm.precision != NBODY_MIXED || t->prm.ewald_order > 4) return NBODY_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long l0 = nb_launch_counter;
+  const int64_t n = t->n, n3 = 3 * n;
+  const double H0 = sqrt(8.0 * M_PI / 3.0);
+  const double ah = sqrt(a0 * a1);
+  const double K1 = 2.0 / H0 * (sqrt(ah) - sqrt(a0));
+  const double K2 = 2.0 / H0 * (sqrt(a1) - sqrt(ah));
+  const double D = 2.0 / H0 * (1.0 / sqrt(a0) - 1.0 / sqrt(a1));
+  NB_CU(t->a_x0.ensure(8 * n3));
+  NB_CU(t->a_x1.ensure(8 * n3));
+  NB_CU(t->a_ph.ensure(4 * n3));
+  NB_CU(t->a_g.ensure(4 * n3));
+  NB_CU(t->a_lg.ensure(4 * n3));
+  NB_CU(t->a_lx.ensure(8 * n3));
+  NB_CU(t->a_lp.ensure(8 * n3));
+  NB_CU(t->a_out.ensure(8 * n3));
+  double* X0 = t->a_x0.as<double>();
+  double* X1 = t->a_x1.as<double>();
+  float* PH = t->a_ph.as<float>();
+  float* G = t->a_g.as<float>();
+  float* LG = t->a_lg.as<float>();
+  double* LX = t->a_lx.as<double>();
+  double* LP = t->a_lp.as<double>();
+  double* MU = t->a_out.as<double>();
+  NB_CU(cudaMemcpyAsync(X0, pos0, 8 * n3, cudaMemcpyDeviceToDevice, s));
+  // forward recompute: tree at x0, g(x0), half kick, drift
+  t->pos = X0;
+  int rc = build_impl(t, s);
+  if (rc) return rc;
+  if ((rc = forces_impl(t, G, s))) return rc;
+  lin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, 0, mom0, nullptr, G, K1, PH, nullptr, nullptr);
+  drift_from_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, X0, PH, D, X1);
+  nb_launch_counter += 2;
+  // second tree at x1 (the step's end state) for its force and reverse mode
+  if (!t->aux) {
+    t->aux = new (std::nothrow) nbody_tree();
+    if (!t->aux) return NBODY_ENOMEM;
+    nbody_tree* x = t->aux;
+    x->device = t->device;
+    x->nsm = t->nsm;
+    if (cudaMallocHost(&x->pinned, 64) != cudaSuccess || x->status.ensure(64) != cudaSuccess) {
+      cudaGetLastError();
+      return NBODY_ECUDA;
+    }
+    cudaMemsetAsync(x->status.p, 0, 64, s);
+    for (int r = 0; r < kRing; r++) {
+      for (auto& e : x->bev[r]) cudaEventCreate(&e);
+      for (auto& e : x->fev[r]) cudaEventCreate(&e);
+    }
+    x->events = true;
+  }
+  nbody_tree* x = t->aux;
+  x->prm = t->prm;
+  x->nbox = t->nbox;
+  x->n = t->n;
+  x->pos = X1;
+  x->mass = t->mass;
+  x->h_off = t->h_off;
+  x->h_eps = t->h_eps;
+  if ((rc = build_impl(x, s))) return rc;
+  if ((rc = forces_impl(x, G, s))) return rc;
+  // reverse: p1 = ph + K2 g(x1)
+  lin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, 0, nullptr, lam_mom1, nullptr, K2, LG, nullptr, nullptr);
+  nb_launch_counter += 1;
+  if ((rc = vjp_impl(x, LG, MU, s))) return rc;
+  // lx1 = lam_x1 + g(x1)^T-term; lph = lam_p1 + D lx1; lam_g0 = K1 lph
+  lin64_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, lam_pos1, MU, lam_mom1, D, K1, LX, LP, LG);
+  nb_launch_counter += 1;
+  if ((rc = vjp_impl(t, LG, MU, s))) return rc;
+  fin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, LX, MU, LP, lam_pos0, lam_mom0);
+  nb_launch_counter += 1;
+  NB_CU(cudaGetLastError());
+  t->launches += nb_launch_counter - l0;
+  if (t->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  rc = read_status(x, s);
+  if (rc) return rc;
+  return read_status(t, s);
+}
 
 int64_t nbody_tree_count(const nbody_tree* t, int what) {
   if (!t) return NBODY_EINVAL;

@@ -301,11 +301,306 @@ def generate():
     return "\n".join(out) + "\n"
 
 
+
+
+# ---- reverse-mode (adjoint) kernels -------------------------------------------------
+def emit_m2p_adj_self(p):
+    """J lam with J = dA/dR (symmetric) of the reduced M2P A(R) = sum_j (R F_{j+1} S_j + F_j G_j):
+    (J lam)_k = sum_j [F_{j+1} S_j lam_k + R_k F_{j+2} S_j (R.lam) + R_k F_{j+1} (G_j.lam)
+                       + F_{j+1} G_{j,k} (R.lam) + F_j (H_j lam)_k],
+    (H_j lam)_k = sum_a B_{j,a} Lmu_{a-e_k},  Lmu_c = sum_l lam_l mu_{c-e_l}."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    sl = slots(p)
+    L = ["template <typename T>",
+         "__device__ __forceinline__ void m2p_adj_self_p%d(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2," % p,
+         "                                          T lx, T ly, T lz, T& ox, T& oy, T& oz) {",
+         "  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));",
+         "  const T F0 = nbody_rsqrt(s);",
+         "  const T is = F0 * F0;"]
+    for j in range(1, p + 3):
+        L.append("  const T F%d = F%d * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
+    for d, R in enumerate(("Rx", "Ry", "Rz")):
+        for k in range(2, p + 1):
+            L.append("  const T %s_%d = %s * T(%.17g);" % (R, k, R, 1.0 / k))
+    L.append("  const T m0 = T(1);")
+    for i, m in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                pi = mi[tuple(par)]
+                R = ("Rx", "Ry", "Rz")[d]
+                fac = R if m[d] == 1 else "%s_%d" % (R, m[d])
+                L.append("  const T m%d = %s;" % (i, fac if pi == 0 else "m%d * %s" % (pi, fac)))
+                break
+    # Lmu_c for |c| <= p-1
+    lam = ("lx", "ly", "lz")
+    # q_c = sum_l lam_l mu_{c-e_l}, so that (H_j lam)_k = sum_a B_{j,a} q_{a-e_k}
+    for i, c in enumerate(mon):
+        if sum(c) > p - 1:
+            continue
+        L.append("  T q%d = T(0);" % i)
+    for i, c in enumerate(mon):
+        if sum(c) > p - 1:
+            continue
+        for d in range(3):
+            if c[d] > 0:
+                cc = list(c)
+                cc[d] -= 1
+                L.append("  q%d = fma(%s, m%d, q%d);" % (i, lam[d], mi[tuple(cc)], i))
+    for j in range(p + 1):
+        L.append("  T S%d = T(0), G%dx = T(0), G%dy = T(0), G%dz = T(0), H%dx = T(0), H%dy = T(0), H%dz = T(0);"
+                 % ((j,) * 7))
+    for t, (j, a) in enumerate(sl):
+        L.append("  { const T b = B[%d];" % t)
+        L.append("    S%d = fma(b, m%d, S%d);" % (j, mi[a], j))
+        for d, ax in enumerate("xyz"):
+            if a[d] > 0:
+                par = list(a)
+                par[d] -= 1
+                L.append("    G%d%s = fma(b, m%d, G%d%s);" % (j, ax, mi[tuple(par)], j, ax))
+                if sum(par) > 0:
+                    L.append("    H%d%s = fma(b, q%d, H%d%s);" % (j, ax, mi[tuple(par)], j, ax))
+        L.append("  }")
+    L.append("  const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));")
+    L.append("  T ax = T(0), ay = T(0), az = T(0);")
+    for j in range(p + 1):
+        L.append("  { const T a1 = F%d * S%d;  // F_{j+1} S_j" % (j + 1, j))
+        L.append("    const T gl = fma(G%dx, lx, fma(G%dy, ly, G%dz * lz));" % (j, j, j))
+        L.append("    const T c1 = fma(F%d * S%d, rl, F%d * gl);  // R_k coefficient" % (j + 2, j, j + 1))
+        L.append("    const T c2 = F%d * rl;  // G_{j,k} coefficient" % (j + 1))
+        for ax, Rv, lv in (("x", "Rx", "lx"), ("y", "Ry", "ly"), ("z", "Rz", "lz")):
+            L.append("    a%s = fma(a1, %s, fma(%s, c1, fma(c2, G%d%s, fma(F%d, H%d%s, a%s))));"
+                     % (ax, lv, Rv, j, ax, j, j, ax, ax))
+        L.append("  }")
+    L.append("  ox += ax;")
+    L.append("  oy += ay;")
+    L.append("  oz += az;")
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_m2p_adj_src(p):
+    """nu_n += sum_l lam_l d^{n+e_l} g(R), |n| <= p, via nu_n = (lam.R) E_n + sum_d n_d lam_d E_{n-e_d},
+    E_m = d^m F_1 = sum_k h(m,k) R^(m-2k) F_{1+|m|-|k|}."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    L = ["template <typename T>",
+         "__device__ __forceinline__ void m2p_adj_src_p%d(T Rx, T Ry, T Rz, T eps2, T lx, T ly, T lz," % p,
+         "                                         T* __restrict__ nu) {",
+         "  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));",
+         "  const T F0 = nbody_rsqrt(s);",
+         "  const T is = F0 * F0;"]
+    for j in range(1, p + 2):
+        L.append("  const T F%d = F%d * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
+    L.append("  const T r0 = T(1);")
+    for i, m in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                pi = mi[tuple(par)]
+                R = ("Rx", "Ry", "Rz")[d]
+                L.append("  const T r%d = %s;" % (i, R if pi == 0 else "r%d * %s" % (pi, R)))
+                break
+    # E_m
+    for i, m in enumerate(mon):
+        byj = {}
+        for k in product(*(range(m[d] // 2 + 1) for d in range(3))):
+            a = tuple(m[d] - 2 * k[d] for d in range(3))
+            j = 1 + sum(m) - sum(k)
+            byj.setdefault(j, []).append((hcoef(m, k), mi[a]))
+        parts = []
+        for j, terms in sorted(byj.items()):
+            expr = None
+            for c, ai in terms:
+                if expr is None:
+                    expr = "r%d * T(%.17g)" % (ai, c) if c != 1.0 else "r%d" % ai
+                else:
+                    expr = "fma(r%d, T(%.17g), %s)" % (ai, c, expr)
+            parts.append((j, expr))
+        e = None
+        for j, expr in parts:
+            e = "F%d * (%s)" % (j, expr) if e is None else "fma(F%d, %s, %s)" % (j, expr, e)
+        L.append("  const T E%d = %s;" % (i, e))
+    L.append("  const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));")
+    lam = ("lx", "ly", "lz")
+    for i, n in enumerate(mon):
+        expr = "fma(rl, E%d, nu[%d])" % (i, i)
+        for d in range(3):
+            if n[d] > 0:
+                nn = list(n)
+                nn[d] -= 1
+                fac = lam[d] if n[d] == 1 else "(%s * T(%d))" % (lam[d], n[d])
+                expr = "fma(%s, E%d, %s)" % (fac, mi[tuple(nn)], expr)
+        L.append("  nu[%d] = %s;" % (i, expr))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_m2m_adj(p):
+    """nuc_k += sum_{n >= k} C(n,k) s^(n-k) nup_n (transpose of the M2M shift), FP64."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    L = ["__device__ __forceinline__ void m2m_adj_acc_p%d(const double* __restrict__ nup, double sx, double sy, double sz, double* __restrict__ nuc) {" % p,
+         "  const double w0 = 1.0;"]
+    for i, mm in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if mm[d] > 0:
+                par = list(mm)
+                par[d] -= 1
+                L.append("  const double w%d = w%d * %s;" % (i, mi[tuple(par)], "sxsysz"[2 * d:2 * d + 2]))
+                break
+    for kk, k in enumerate(mon):
+        expr = "nuc[%d]" % kk
+        for n in mon:
+            if all(n[d] >= k[d] for d in range(3)):
+                b = math.comb(n[0], k[0]) * math.comb(n[1], k[1]) * math.comb(n[2], k[2])
+                w = mi[(n[0] - k[0], n[1] - k[1], n[2] - k[2])]
+                expr = ("fma(w%d, nup[%d], %s)" % (w, mi[n], expr)) if b == 1 else \
+                       ("fma(w%d * %d.0, nup[%d], %s)" % (w, b, mi[n], expr))
+        L.append("  nuc[%d] = %s;" % (kk, expr))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_p2m_adj(p):
+    """g += m sum_n nu_n grad (d^n) (transpose of P2M), FP64."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    L = ["__device__ __forceinline__ void p2m_adj_p%d(double m, double dx, double dy, double dz, const double* __restrict__ nu, double& gx, double& gy, double& gz) {" % p,
+         "  const double q0 = 1.0;"]
+    for i, mm in enumerate(mon):
+        if i == 0 or sum(mm) > p - 1:
+            continue
+        for d in range(3):
+            if mm[d] > 0:
+                par = list(mm)
+                par[d] -= 1
+                L.append("  const double q%d = q%d * %s;" % (i, mi[tuple(par)], "dxdydz"[2 * d:2 * d + 2]))
+                break
+    for d, gv in enumerate(("gx", "gy", "gz")):
+        expr = "0.0"
+        for i, n in enumerate(mon):
+            if n[d] == 0:
+                continue
+            nn = list(n)
+            nn[d] -= 1
+            c = n[d]
+            expr = ("fma(nu[%d], q%d, %s)" % (i, mi[tuple(nn)], expr)) if c == 1 else \
+                   ("fma(nu[%d] * %d.0, q%d, %s)" % (i, c, mi[tuple(nn)], expr))
+        L.append("  %s = fma(m, %s, %s);" % (gv, expr, gv))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_field_adj(pe):
+    """Image-field reverse kernels: Hessian-vector of the local expansion, the
+    cotangent of its coefficients, and the transposed M2L."""
+    P = pe + 1
+    mP = multi(P)
+    miP = {m: i for i, m in enumerate(mP)}
+    me = multi(pe)
+    L = []
+    # (a) hess: o_k -= sum_l lam_l sum_{|c| <= pe-1} d^c/c! L_{c+e_k+e_l}
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void l2p_hess_pe%d(const T* __restrict__ Lc, T dx, T dy, T dz, T lx, T ly, T lz, T& ox, T& oy, T& oz) {" % pe)
+    mc = [c for c in me if sum(c) <= pe - 1]
+    mci = {c: i for i, c in enumerate(me)}
+    L.append("  const T q0 = T(1);")
+    for i, m in enumerate(me):
+        if i == 0 or sum(m) > pe - 1:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                L.append("  const T q%d = q%d * (%s * T(%.17g));" % (i, mci[tuple(par)], "dxdydz"[2 * d:2 * d + 2], 1.0 / m[d]))
+                break
+    lam = ("lx", "ly", "lz")
+    for k, ov in enumerate(("ox", "oy", "oz")):
+        expr = ov
+        for l in range(3):
+            for c in mc:
+                t = list(c)
+                t[k] += 1
+                t[l] += 1
+                expr = "fma(-%s * q%d, Lc[%d], %s)" % (lam[l], mci[c], miP[tuple(t)] - 1, expr)
+        L.append("  %s = %s;" % (ov, expr))
+    L.append("}")
+    # (b) cotangent of L: Lbar_m -= sum_{l: m_l>=1} lam_l d^{m-e_l}/(m-e_l)!
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void l2p_adj_pe%d(T dx, T dy, T dz, T lx, T ly, T lz, T* __restrict__ Lbar) {" % pe)
+    L.append("  const T q0 = T(1);")
+    for i, m in enumerate(me):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                L.append("  const T q%d = q%d * (%s * T(%.17g));" % (i, mci[tuple(par)], "dxdydz"[2 * d:2 * d + 2], 1.0 / m[d]))
+                break
+    for t, m in enumerate(mP):
+        if t == 0:
+            continue
+        expr = "Lbar[%d]" % (t - 1)
+        for l in range(3):
+            if m[l] >= 1:
+                c = list(m)
+                c[l] -= 1
+                if sum(c) <= pe:
+                    expr = "fma(-%s, q%d, %s)" % (lam[l], mci[tuple(c)], expr)
+        L.append("  Lbar[%d] = %s;" % (t - 1, expr))
+    L.append("}")
+    # (c) transposed M2L: nu_n += (-1)^|n|/n! sum_m Lbar_m D_{m+n}
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void m2l_adj_pe%d(const T* __restrict__ Lbar, const T* __restrict__ D, T* __restrict__ nu) {" % pe)
+    for u, n in enumerate(me):
+        c = (-1.0 if sum(n) % 2 else 1.0) / (math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2]))
+        expr = None
+        for t, m in enumerate(mP):
+            if t == 0 or sum(m) + sum(n) > P:
+                continue
+            k = miP[(m[0] + n[0], m[1] + n[1], m[2] + n[2])]
+            expr = ("Lbar[%d] * D[%d]" % (t - 1, k)) if expr is None else ("fma(Lbar[%d], D[%d], %s)" % (t - 1, k, expr))
+        L.append("  nu[%d] = fma(T(%.17g), %s, nu[%d]);" % (u, c, expr, u))
+    L.append("}")
+    return "\n".join(L)
+
+
+def generate_adjoint():
+    out = ["// Generated by gen_m2p.py -- do not edit by hand.",
+           "// Reverse-mode (adjoint) kernels of the M2P, M2M, P2M and image-field expansions.",
+           "#pragma once", ""]
+    for p in range(5):
+        out.append(emit_m2p_adj_self(p))
+        out.append("")
+        out.append(emit_m2p_adj_src(p))
+        out.append("")
+        out.append(emit_m2m_adj(p))
+        out.append("")
+        out.append(emit_p2m_adj(p))
+        out.append("")
+    for pe in range(1, 6):
+        out.append(emit_field_adj(pe))
+        out.append("")
+    return "\n".join(out) + "\n"
+
+
 if __name__ == "__main__":
     here = os.path.dirname(os.path.abspath(__file__))
-    dst = os.path.join(here, "m2p_gen.cuh")
-    text = generate()
+    outputs = {os.path.join(here, "m2p_gen.cuh"): generate(),
+               os.path.join(here, "adj_gen.cuh"): generate_adjoint()}
     if len(sys.argv) > 1 and sys.argv[1] == "--check":
-        sys.exit(0 if open(dst).read() == text else 1)
-    with open(dst, "w") as f:
-        f.write(text)
+        sys.exit(0 if all(os.path.exists(k) and open(k).read() == v for k, v in outputs.items()) else 1)
+    for k, v in outputs.items():
+        with open(k, "w") as f:
+            f.write(v)

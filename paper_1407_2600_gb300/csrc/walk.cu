@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "m2p_gen.cuh"
+#include "walk_common.cuh"
 
 namespace {
 
@@ -41,24 +42,6 @@ NB_WORD(1)
 NB_WORD(2)
 NB_WORD(3)
 NB_WORD(4)
-
-template <typename T>
-__device__ __forceinline__ void kadd(T& s, T& c, T x) {
-  T y = x - c;
-  T t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
-__device__ __forceinline__ int warp_excl_scan(int v, int lane) {
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  return x - v;
-}
 
 template <typename T>
 struct WalkArgs {
@@ -137,38 +120,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         cb = tr.cB[c];
       }
       __syncwarp();
-      int cls = 0;  // 1 open, 2 M2P, 3 P2P
+      int cls = NB_CELL_NONE;
       int kx = 0, ky = 0, kz = 0;
       const int lvl = ca.w & 0xff, nch = ca.w >> 8;
-      if (lane < nb) {
-        bool consistent = true;
-        const int ix = ((ca.x >> (22 - lvl)) - 1) >> 1;
-        const int iy = ((ca.y >> (22 - lvl)) - 1) >> 1;
-        const int iz = ((ca.z >> (22 - lvl)) - 1) >> 1;
-        if (lvl >= w.le) {
-          const int sh = lvl - w.le;
-          kx = img_shift(cell_c2(ix >> sh, w.le), gd.x);
-          ky = img_shift(cell_c2(iy >> sh, w.le), gd.y);
-          kz = img_shift(cell_c2(iz >> sh, w.le), gd.z);
-        } else {
-          const int sh = w.le - lvl;
-          kx = img_shift(cell_c2(ix << sh, w.le), gd.x);
-          ky = img_shift(cell_c2(iy << sh, w.le), gd.y);
-          kz = img_shift(cell_c2(iz << sh, w.le), gd.z);
-          consistent = kx == img_shift(cell_c2(((ix + 1) << sh) - 1, w.le), gd.x) &&
-                       ky == img_shift(cell_c2(((iy + 1) << sh) - 1, w.le), gd.y) &&
-                       kz == img_shift(cell_c2(((iz + 1) << sh) - 1, w.le), gd.z);
-        }
-        const int dx = abs(ca.x - gb.x - kx * NB_PBOX) - gc.x;
-        const int dy = abs(ca.y - gb.y - ky * NB_PBOX) - gc.y;
-        const int dz = abs(ca.z - gb.z - kz * NB_PBOX) - gc.z;
-        const long long ddx = dx > 0 ? dx : 0, ddy = dy > 0 ? dy : 0, ddz = dz > 0 ? dz : 0;
-        const long long d2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        const bool accept = consistent && lvl >= 2 && d2 > w.thr[lvl];
-        if (accept && cb.y > w.n_direct) cls = 2;
-        else if (accept || nch == 0) cls = 3;
-        else cls = 1;
-      }
+      if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, kx, ky, kz);
       // push daughters of opened cells
       {
         const int nc = (cls == 1) ? nch : 0;
@@ -250,11 +205,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             if (s_plev[wid][q] < w.le) {
               // leaf above the image level: image per particle from its own
               // level-l_E ancestor
-              const uint64_t pk = tr.skeys[j] >> (3 * (NB_QBITS - w.le));
               const int4 pc = s_pcen[wid][q];
-              const int jx = img_shift(cell_c2((int)compact3(pk), w.le), gd.x);
-              const int jy = img_shift(cell_c2((int)compact3(pk >> 1), w.le), gd.y);
-              const int jz = img_shift(cell_c2((int)compact3(pk >> 2), w.le), gd.z);
+              int jx, jy, jz;
+              particle_image(tr.skeys[j], w.le, gd, jx, jy, jz);
               ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
               oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
               oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;

@@ -33,7 +33,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces",
            "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
-           "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc"]
+           "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
 
 
 class Params(C.Structure):
@@ -99,6 +99,7 @@ def lib():
         L.nbody_tree_free.restype = None
         L.nbody_timing_read.argtypes = [_vp, C.POINTER(Timing), C.c_int]
         L.nbody_sort_keys_noalloc.argtypes = [_vp, C.c_int64, _vp, _vp, _vp]
+        L.nbody_cic_loss.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, _vp]
         L.nbody_strerror.argtypes = [C.c_int]
         L.nbody_strerror.restype = C.c_char_p
         _LIB = L
@@ -185,6 +186,11 @@ def nbody_sort_keys_noalloc(pos_dev: int, n: int, keys_out_dev: int, perm_out_de
     return lib().nbody_sort_keys_noalloc(pos_dev, n, keys_out_dev, perm_out_dev, stream)
 
 
+def nbody_cic_loss(pos_dev: int, mass_dev: int | None, n: int, ng: int, grid_dev: int, loss_dev: int,
+                   grad_dev: int | None, stream: int | None = None) -> int:
+    return lib().nbody_cic_loss(pos_dev, mass_dev, n, ng, grid_dev, loss_dev, grad_dev, stream)
+
+
 def nbody_strerror(code: int) -> str:
     return lib().nbody_strerror(code).decode()
 
@@ -243,6 +249,26 @@ class Tree:
         _check(nbody_kdk_step(self.handle, self.pos.data_ptr(), mom.data_ptr(), acc.data_ptr(), a0, a1,
                               _stream()), "nbody_kdk_step")
 
+    def forces_vjp(self, lam, out=None):
+        """(d acc / d pos)^T lam for the tree as last built (lam: (3, n) float32)."""
+        import torch
+        if out is None:
+            out = torch.empty((3, self.n), dtype=torch.float64, device=self.pos.device)
+        lam = lam.contiguous().float()
+        _check(nbody_forces_vjp(self.handle, lam.data_ptr(), out.data_ptr(), _stream()), "nbody_forces_vjp")
+        return out
+
+    def kdk_adjoint(self, pos0, mom0, a0, a1, lam_pos1, lam_mom1):
+        """Cotangents of (pos0, mom0) of one KDK step given those of its outputs."""
+        import torch
+        lx0 = torch.empty((3, self.n), dtype=torch.float64, device=self.pos.device)
+        lp0 = torch.empty((3, self.n), dtype=torch.float32, device=self.pos.device)
+        _check(nbody_kdk_adjoint(self.handle, pos0.contiguous().data_ptr(), mom0.contiguous().data_ptr(), a0, a1,
+                                 lam_pos1.contiguous().double().data_ptr(),
+                                 lam_mom1.contiguous().float().data_ptr(), lx0.data_ptr(), lp0.data_ptr(),
+                                 _stream()), "nbody_kdk_adjoint")
+        return lx0, lp0
+
     def timing(self, reset=True):
         t = Timing()
         _check(nbody_timing_read(self.handle, t, 1 if reset else 0), "nbody_timing_read")
@@ -285,3 +311,17 @@ class Tree:
             self.close()
         except Exception:
             pass
+
+
+def cic_loss(pos, ng, mass=None, grad=True):
+    """CIC delta^2 loss of positions pos ((3, n) float64 CUDA tensor); returns
+    (loss tensor of shape (), dL/dpos or None)."""
+    import torch
+    n = pos.shape[1]
+    grid = torch.empty(ng ** 3, dtype=torch.float64, device=pos.device)
+    loss = torch.empty((), dtype=torch.float64, device=pos.device)
+    g = torch.empty((3, n), dtype=torch.float64, device=pos.device) if grad else None
+    m = None if mass is None else mass.contiguous().float()
+    _check(nbody_cic_loss(pos.contiguous().data_ptr(), None if m is None else m.data_ptr(), n, ng, grid.data_ptr(),
+                          loss.data_ptr(), None if g is None else g.data_ptr(), _stream()), "nbody_cic_loss")
+    return loss, g
