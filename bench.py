@@ -288,6 +288,43 @@ def run_gpu(args, rank, world, local_rank):
         e2e = {"value": world * n * k2 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
                "d2h_bytes_per_step": 48 * n}
 
+    # reverse mode: a checkpointed trajectory of S steps (checkpoints every 4)
+    # forward, then its reverse sweep (states recomputed from the checkpoints,
+    # steps reversed by chained nbody_kdk_adjoint_acc calls), as the
+    # differentiable-trajectory wrapper runs them
+    adj = None
+    if not args.no_adjoint:
+        from paper_1407_2600_gb300.autograd import forward_steps, reverse_steps
+        S = args.adjoint_steps
+        a_list = [a * math.exp(DLNA * k) for k in range(S + 1)]
+        g = torch.Generator(device=dev)
+        g.manual_seed(17 + rank)
+        lx = torch.randn((3, n), dtype=torch.float64, device=dev, generator=g)
+        lp = torch.randn((3, n), dtype=torch.float32, device=dev, generator=g)
+        torch.cuda.synchronize()
+        tree.timing(reset=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        ckpt = forward_steps(tree, pos, mom, acc, a_list, 4)
+        ev[1].record(stream)
+        ev[2].record(stream)
+        lx0, lp0 = reverse_steps(tree, ckpt, a_list, lx, lp)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        rc = nb.nbody_check(tree.handle, nb._stream())
+        if rc != nb.NBODY_OK:
+            raise nb.NbodyError(rc, "timed reverse sweep")
+        ta = tree.timing(reset=True)
+        t_fwd = ev[0].elapsed_time(ev[1]) / S
+        t_bwd = ev[2].elapsed_time(ev[3]) / S
+        adj = {"backward_ms_per_step": t_bwd, "forward_ms_per_step": t_fwd, "ratio": t_bwd / t_fwd,
+               "steps": S, "checkpoint_every": 4, "adjoint_calls": ta["adjoint_steps"],
+               "adjoint_calls_reusing": ta["adjoint_reused"],
+               "finite": bool(torch.isfinite(lx0).all().item() and torch.isfinite(lp0).all().item()),
+               "note": "backward = reverse sweep incl. the recompute of every state from its checkpoint; "
+                       "forward = the same trajectory's KDK steps with checkpoint copies"}
+        a = a_list[-1]
+
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -326,7 +363,8 @@ def run_gpu(args, rank, world, local_rank):
             "force_eval_ms": force_ms,
             "force_updates_per_s": n / (force_ms * 1e-3),
             "interactions_per_particle": {"p2p": tm["p2p"] / evals / n, "m2p": tm["m2p"] / evals / n},
-            "adjoint_forward_ratio": None,
+            "adjoint_forward_ratio": adj["ratio"] if adj else None,
+            "adjoint": adj,
         }
         print(json.dumps(line), flush=True)
     tree.close()
@@ -341,6 +379,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")
     ap.add_argument("--ng", type=int, default=NG, help="particles per axis (128 = the benchmark workload)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

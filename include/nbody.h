@@ -160,11 +160,38 @@ int nbody_kdk_step(nbody_tree *tree, double *pos_dev, float *mom_dev, float *acc
  *   lam_pos0_dev, lam_mom0_dev  3*n FP64 / FP32 outputs
  * The discrete decisions of the tree (topology, acceptance, groups) are held
  * fixed, so this is the exact derivative of the evaluated forces.  Uses the
- * tree's parameters; the tree is rebuilt at x0 and x1 internally.
+ * tree's parameters; the tree is rebuilt at x0 internally (its positions are
+ * then an internal copy of pos0).
+ *
+ * Chaining.  The step needs J(x1)^T lam_mom1 (J = d acc / d pos) and
+ * J(x0)^T lam_ph; the second is kept, with x0 and lam_mom0.  When the next
+ * call is the previous step of the same trajectory (its recomputed x1 equals
+ * this call's x0 bit for bit and its lam_mom1 is this call's lam_mom0, which is
+ * what a reverse sweep passes), the kept product is reused and that call
+ * evaluates one tree instead of two.  The test is an exact comparison on the
+ * device, so any other sequence of calls gives the same results, only
+ * without the reuse.  The recompute uses the same FP32 kick and FP64 drift as
+ * nbody_kdk_step, so a trajectory stepped by nbody_kdk_step chains.
+ * Errors: EINVAL (NULL pointer, a0 or a1 <= 0), ENOTSUP (FP64 precision or
+ * an image field of order > 4), plus those of nbody_build_tree.
  */
 int nbody_kdk_adjoint(nbody_tree *tree, const double *pos0_dev, const float *mom0_dev, double a0,
                       double a1, const double *lam_pos1_dev, const float *lam_mom1_dev,
                       double *lam_pos0_dev, float *lam_mom0_dev, nbody_stream_t stream);
+
+/*
+ * nbody_kdk_adjoint with g(x0) supplied by the caller instead of recomputed:
+ *   acc0_dev  3*n FP32, the accelerations at pos0 exactly as nbody_forces or
+ *             nbody_kdk_step returned them for these positions (caller order;
+ *             not modified).  The tree walk at x0 is then skipped: the call
+ *             builds the tree, its moments and its image field only.
+ * Results are bitwise those of nbody_kdk_adjoint when acc0 is that g(x0).
+ * A checkpointed reverse sweep has g(x) of every recomputed state at hand.
+ */
+int nbody_kdk_adjoint_acc(nbody_tree *tree, const double *pos0_dev, const float *mom0_dev,
+                          const float *acc0_dev, double a0, double a1, const double *lam_pos1_dev,
+                          const float *lam_mom1_dev, double *lam_pos0_dev, float *lam_mom0_dev,
+                          nbody_stream_t stream);
 
 /*
  * Vector-Jacobian product of the force: out = (d acc / d pos)^T lam, for the
@@ -187,6 +214,8 @@ typedef struct {
   int64_t launches;      /* kernels launched by the library */
   double p2p, m2p, m2l;  /* interactions summed over the evaluations */
   double ms_sort, ms_build, ms_upward, ms_walk, ms_periodic; /* summed device times */
+  int64_t adjoint_steps;   /* nbody_kdk_adjoint(_acc) calls */
+  int64_t adjoint_reused;  /* of which reused the previous call's J(x0)^T lam_ph */
 } nbody_timing;
 int nbody_timing_read(nbody_tree *tree, nbody_timing *out, int reset);
 

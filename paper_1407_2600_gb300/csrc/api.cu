@@ -64,6 +64,8 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
                           int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
                           unsigned* status, int nsm, cudaStream_t s);
+cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+                           const void* tab, void* lbuf, cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         cudaStream_t s);
@@ -130,7 +132,12 @@ struct nbody_tree {
   Buf eps2, stack, gctr, accw, counters, lbuf;
   // reverse mode
   Buf a_lam, a_mu, a_nuc, a_nu, a_lbar, a_nue, a_x0, a_x1, a_ph, a_g, a_lg, a_lx, a_lp, a_out;
-  bool forces_valid = false;
+  // the KDK adjoint's kept product J(x0)^T lam_ph with its x0 and lam_p0
+  Buf a_xc, a_lc, a_muc, a_eq;
+  bool adj_cache = false;
+  long long adj_steps = 0, adj_reused = 0;
+  bool forces_valid = false;  // walk + image field of the last build evaluated
+  bool field_valid = false;   // image-field local expansions of the last build formed
   nbody_tree* aux = nullptr;  // second tree of the KDK adjoint (state at the step's end)
   int walk_blocks = 0;
   long long thr[NB_NLEV];
@@ -152,7 +159,7 @@ struct nbody_tree {
                   &hval, &mom, &arrive, &coef, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
-                  &a_lx, &a_lp, &a_out};
+                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     delete aux;
@@ -273,13 +280,7 @@ __global__ void eps2_kernel(int nbox, const double* __restrict__ eps, float* __r
   }
 }
 
-// elementwise pieces of the KDK step and its reverse
-__global__ void lin_kernel(int64_t n3, int mode, const float* __restrict__ a, const float* __restrict__ b,
-                           const float* __restrict__ g, double k, float* __restrict__ out, void*, void*) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = a ? (float)((double)a[i] + k * (double)g[i]) : (float)(k * (double)b[i]);
-}
-
+// elementwise pieces of the KDK adjoint
 __global__ void drift_from_kernel(int64_t n3, const double* __restrict__ x0, const float* __restrict__ p, double d,
                                   double* __restrict__ x1) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
@@ -290,24 +291,36 @@ __global__ void drift_from_kernel(int64_t n3, const double* __restrict__ x0, con
   }
 }
 
-__global__ void lin64_kernel(int64_t n3, const double* __restrict__ lx1, const double* __restrict__ mu,
-                             const float* __restrict__ lp1, double d, double k1, double* __restrict__ lx,
-                             double* __restrict__ lp, float* __restrict__ lg) {
+// lam_x1' = lam_x1 + k2 mu1;  lam_ph = lam_p1 + d lam_x1' (FP64 and its FP32 rounding)
+__global__ void adj_mid_kernel(int64_t n3, const double* __restrict__ lx1, const double* __restrict__ mu1,
+                               const float* __restrict__ lp1, double k2, double d, double* __restrict__ lx,
+                               double* __restrict__ lp, float* __restrict__ lp32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = lx1[i] + mu[i];
+    const double x = lx1[i] + k2 * mu1[i];
     const double p = (double)lp1[i] + d * x;
     lx[i] = x;
     lp[i] = p;
-    lg[i] = (float)(k1 * p);
+    lp32[i] = (float)p;
   }
 }
 
-__global__ void fin_kernel(int64_t n3, const double* __restrict__ lx, const double* __restrict__ mu,
-                           const double* __restrict__ lp, double* __restrict__ lx0, float* __restrict__ lp0) {
+// lam_x0 = lam_x1' + k1 mu0;  lam_p0 = lam_ph
+__global__ void adj_fin_kernel(int64_t n3, const double* __restrict__ lx, const double* __restrict__ mu0, double k1,
+                               const float* __restrict__ lp32, double* __restrict__ lx0, float* __restrict__ lp0) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
-    lx0[i] = lx[i] + mu[i];
-    lp0[i] = (float)lp[i];
+    lx0[i] = lx[i] + k1 * mu0[i];
+    lp0[i] = lp32[i];
   }
+}
+
+// *flag = 1 unless a == b and c == d bit for bit (n3 doubles, n3 floats)
+__global__ void differ_kernel(int64_t n3, const unsigned long long* __restrict__ a,
+                              const unsigned long long* __restrict__ b, const unsigned* __restrict__ c,
+                              const unsigned* __restrict__ d, int* flag) {
+  bool diff = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    diff |= (a[i] != b[i]) | (c[i] != d[i]);
+  if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
 __global__ void accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ tot) {
@@ -477,14 +490,14 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(cudaEventRecord(be[3], s));
   t->nb_log++;
   t->forces_valid = false;
+  t->field_valid = false;
   return NBODY_OK;
 }
 
-int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
+// state shared by the walk and the reverse walk: thresholds, stacks, tables
+int eval_prep(nbody_tree* t, cudaStream_t s) {
   const nbody_params& p = t->prm;
   const bool fp64 = p.precision == NBODY_FP64;
-  const int64_t n = t->n;
-  NB_CU(t->accw.ensure((fp64 ? 24 : 12) * n));
   NB_CU(t->counters.ensure(64));
   if (!t->tot.p) {
     NB_CU(t->tot.ensure(64));
@@ -494,16 +507,41 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   const int warps = nb_walk_warps(fp64);
   if (t->walk_blocks == 0) t->walk_blocks = t->nsm * 8;
   NB_CU(t->stack.ensure(4 * (int64_t)t->walk_blocks * warps * kStackCap));
-  NB_CU(cudaMemsetAsync(t->counters.p, 0, 64, s));
   for (int l = 0; l < NB_NLEV; l++) {
     double sl = ldexp(1.0, 23 - l);
     double T = floor((sl * sl) / (p.theta * p.theta));
     t->thr[l] = T > 4.0e18 ? (long long)4000000000000000000LL : (long long)T;
   }
-  const void* eps2 = fp64 ? (const void*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15)) : t->eps2.p;
   if (p.ewald_order > 0) {
     NB_CU(nb_phitilde_table(p.ewald_grid, p.ewald_order + 1, &t->tab64, &t->tab32, s));
+    NB_CU(t->lbuf.ensure((fp64 ? 8 : 4) * (int64_t)t->ngroup * nb_field_stride(p.ewald_order)));
   }
+  return NBODY_OK;
+}
+
+// image-field local expansions of the last build, without the walk
+int field_impl(nbody_tree* t, cudaStream_t s) {
+  const nbody_params& p = t->prm;
+  const bool fp64 = p.precision == NBODY_FP64;
+  int rc = eval_prep(t, s);
+  if (rc) return rc;
+  const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
+  if (p.ewald_order > 0)
+    NB_CU(nb_field_local(t->dev(), fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p,
+                         t->fm.as<double>(), tab, t->lbuf.p, s));
+  t->field_valid = true;
+  return NBODY_OK;
+}
+
+int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
+  const nbody_params& p = t->prm;
+  const bool fp64 = p.precision == NBODY_FP64;
+  const int64_t n = t->n;
+  NB_CU(t->accw.ensure((fp64 ? 24 : 12) * n));
+  int rc = eval_prep(t, s);
+  if (rc) return rc;
+  NB_CU(cudaMemsetAsync(t->counters.p, 0, 64, s));
+  const void* eps2 = fp64 ? (const void*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15)) : t->eps2.p;
   cudaEvent_t* fe = t->fev[t->nf_log % kRing];
   t->last_stream = s;
   NB_CU(cudaEventRecord(fe[0], s));
@@ -514,8 +552,6 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
                 t->status.as<unsigned>(), t->nsm, s));
   NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
-  if (p.ewald_order > 0)
-    NB_CU(t->lbuf.ensure((fp64 ? 8 : 4) * (int64_t)t->ngroup * nb_field_stride(p.ewald_order)));
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
                     t->lbuf.p, t->accw.p, acc, ctr + 2, s));
   NB_CU(cudaEventRecord(fe[2], s));
@@ -523,6 +559,7 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   nb_launch_counter += 1;
   t->nf_log++;
   t->forces_valid = true;
+  t->field_valid = true;
   return NBODY_OK;
 }
 
@@ -531,9 +568,8 @@ int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   const nbody_params& p = t->prm;
   if (p.precision != NBODY_MIXED || p.ewald_order > 4) return NBODY_ENOTSUP;
   const int64_t n = t->n;
-  if (!t->forces_valid) {
-    NB_CU(t->a_g.ensure(12 * n));
-    int rc = forces_impl(t, t->a_g.as<float>(), s);
+  if (!t->field_valid) {
+    int rc = field_impl(t, s);
     if (rc) return rc;
   }
   const int nm = nb_adj_coef_nm(p.order);
@@ -733,13 +769,35 @@ int nbody_forces_vjp(nbody_tree* t, const float* lam_dev, double* out_dev, nbody
   return read_status(t, s);
 }
 
-int nbody_kdk_adjoint(nbody_tree* t, const double* pos0, const float* mom0, double a0, double a1,
-                      const double* lam_pos1, const float* lam_mom1, double* lam_pos0, float* lam_mom0,
-                      nbody_stream_t stream) {
+namespace {
+
+// second tree of the KDK adjoint (the step's end state), created on first use
+int ensure_aux(nbody_tree* t, cudaStream_t s) {
+  if (t->aux) return NBODY_OK;
+  t->aux = new (std::nothrow) nbody_tree();
+  if (!t->aux) return NBODY_ENOMEM;
+  nbody_tree* x = t->aux;
+  x->device = t->device;
+  x->nsm = t->nsm;
+  if (cudaMallocHost(&x->pinned, 64) != cudaSuccess || x->status.ensure(64) != cudaSuccess) {
+    cudaGetLastError();
+    return NBODY_ECUDA;
+  }
+  NB_CU(cudaMemsetAsync(x->status.p, 0, 64, s));
+  for (int r = 0; r < kRing; r++) {
+    for (auto& e : x->bev[r]) cudaEventCreate(&e);
+    for (auto& e : x->fev[r]) cudaEventCreate(&e);
+  }
+  x->events = true;
+  return NBODY_OK;
+}
+
+int kdk_adjoint_impl(nbody_tree* t, const double* pos0, const float* mom0, const float* acc0, double a0, double a1,
+                     const double* lam_pos1, const float* lam_mom1, double* lam_pos0, float* lam_mom0,
+                     cudaStream_t s) {
   if (!t || !pos0 || !mom0 || !lam_pos1 || !lam_mom1 || !lam_pos0 || !lam_mom0 || !(a0 > 0.0) || !(a1 > 0.0))
     return NBODY_EINVAL;
   if (t->prm.precision != NBODY_MIXED || t->prm.ewald_order > 4) return NBODY_ENOTSUP;
-  cudaStream_t s = (cudaStream_t)stream;
   const long long l0 = nb_launch_counter;
   const int64_t n = t->n, n3 = 3 * n;
   const double H0 = sqrt(8.0 * M_PI / 3.0);
@@ -755,67 +813,98 @@ int nbody_kdk_adjoint(nbody_tree* t, const double* pos0, const float* mom0, doub
   NB_CU(t->a_lx.ensure(8 * n3));
   NB_CU(t->a_lp.ensure(8 * n3));
   NB_CU(t->a_out.ensure(8 * n3));
+  NB_CU(t->a_xc.ensure(8 * n3));
+  NB_CU(t->a_lc.ensure(4 * n3));
+  NB_CU(t->a_muc.ensure(8 * n3));
+  NB_CU(t->a_eq.ensure(64));
   double* X0 = t->a_x0.as<double>();
   double* X1 = t->a_x1.as<double>();
   float* PH = t->a_ph.as<float>();
-  float* G = t->a_g.as<float>();
   float* LG = t->a_lg.as<float>();
   double* LX = t->a_lx.as<double>();
   double* LP = t->a_lp.as<double>();
-  double* MU = t->a_out.as<double>();
   NB_CU(cudaMemcpyAsync(X0, pos0, 8 * n3, cudaMemcpyDeviceToDevice, s));
-  // forward recompute: tree at x0, g(x0), half kick, drift
+  // forward recompute with the arithmetic of nbody_kdk_step: tree at x0,
+  // g(x0), the FP32 half kick and the FP64 drift
   t->pos = X0;
   int rc = build_impl(t, s);
   if (rc) return rc;
-  if ((rc = forces_impl(t, G, s))) return rc;
-  lin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, 0, mom0, nullptr, G, K1, PH, nullptr, nullptr);
+  const float* G = acc0;
+  if (!G) {
+    if ((rc = forces_impl(t, t->a_g.as<float>(), s))) return rc;
+    G = t->a_g.as<float>();
+  }
+  NB_CU(cudaMemcpyAsync(PH, mom0, 4 * n3, cudaMemcpyDeviceToDevice, s));
+  kick_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, PH, G, (float)K1);
   drift_from_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, X0, PH, D, X1);
   nb_launch_counter += 2;
-  // second tree at x1 (the step's end state) for its force and reverse mode
-  if (!t->aux) {
-    t->aux = new (std::nothrow) nbody_tree();
-    if (!t->aux) return NBODY_ENOMEM;
-    nbody_tree* x = t->aux;
-    x->device = t->device;
-    x->nsm = t->nsm;
-    if (cudaMallocHost(&x->pinned, 64) != cudaSuccess || x->status.ensure(64) != cudaSuccess) {
-      cudaGetLastError();
-      return NBODY_ECUDA;
-    }
-    cudaMemsetAsync(x->status.p, 0, 64, s);
-    for (int r = 0; r < kRing; r++) {
-      for (auto& e : x->bev[r]) cudaEventCreate(&e);
-      for (auto& e : x->fev[r]) cudaEventCreate(&e);
-    }
-    x->events = true;
+  // J(x1)^T lam_p1: the product kept by the previous call when it was taken at
+  // this x1 with this cotangent, else from a tree at x1
+  bool reuse = false;
+  if (t->adj_cache) {
+    int* eq = t->a_eq.as<int>();
+    NB_CU(cudaMemsetAsync(eq, 0, sizeof(int), s));
+    differ_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, (const unsigned long long*)X1,
+                                                   t->a_xc.as<unsigned long long>(), (const unsigned*)lam_mom1,
+                                                   t->a_lc.as<unsigned>(), eq);
+    nb_launch_counter += 1;
+    NB_CU(cudaMemcpyAsync(t->pinned, eq, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NB_CU(cudaStreamSynchronize(s));
+    reuse = ((int*)t->pinned)[0] == 0;
   }
-  nbody_tree* x = t->aux;
-  x->prm = t->prm;
-  x->nbox = t->nbox;
-  x->n = t->n;
-  x->pos = X1;
-  x->mass = t->mass;
-  x->h_off = t->h_off;
-  x->h_eps = t->h_eps;
-  if ((rc = build_impl(x, s))) return rc;
-  if ((rc = forces_impl(x, G, s))) return rc;
-  // reverse: p1 = ph + K2 g(x1)
-  lin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, 0, nullptr, lam_mom1, nullptr, K2, LG, nullptr, nullptr);
+  const double* MU1 = t->a_muc.as<double>();
+  if (!reuse) {
+    if ((rc = ensure_aux(t, s))) return rc;
+    nbody_tree* x = t->aux;
+    x->prm = t->prm;
+    x->nbox = t->nbox;
+    x->n = t->n;
+    x->pos = X1;
+    x->mass = t->mass;
+    x->h_off = t->h_off;
+    x->h_eps = t->h_eps;
+    if ((rc = build_impl(x, s))) return rc;
+    if ((rc = vjp_impl(x, lam_mom1, t->a_out.as<double>(), s))) return rc;
+    MU1 = t->a_out.as<double>();
+  }
+  // lam_x1' = lam_x1 + K2 mu1;  lam_ph = lam_p1 + D lam_x1'
+  adj_mid_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, lam_pos1, MU1, lam_mom1, K2, D, LX, LP, LG);
   nb_launch_counter += 1;
-  if ((rc = vjp_impl(x, LG, MU, s))) return rc;
-  // lx1 = lam_x1 + g(x1)^T-term; lph = lam_p1 + D lx1; lam_g0 = K1 lph
-  lin64_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, lam_pos1, MU, lam_mom1, D, K1, LX, LP, LG);
+  // J(x0)^T lam_ph, kept for the next call (a_out is free once MU1 is used)
+  double* MU0 = reuse ? t->a_out.as<double>() : t->a_muc.as<double>();
+  if ((rc = vjp_impl(t, LG, MU0, s))) return rc;
+  // lam_x0 = lam_x1' + K1 mu0;  lam_p0 = lam_ph (FP32)
+  adj_fin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, LX, MU0, K1, LG, lam_pos0, lam_mom0);
   nb_launch_counter += 1;
-  if ((rc = vjp_impl(t, LG, MU, s))) return rc;
-  fin_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, LX, MU, LP, lam_pos0, lam_mom0);
-  nb_launch_counter += 1;
+  NB_CU(cudaMemcpyAsync(t->a_lc.p, LG, 4 * n3, cudaMemcpyDeviceToDevice, s));
+  if (reuse) std::swap(t->a_out, t->a_muc);
+  std::swap(t->a_x0, t->a_xc);
+  t->pos = t->a_xc.as<double>();
+  t->adj_cache = true;
+  t->adj_steps += 1;
+  t->adj_reused += reuse ? 1 : 0;
   NB_CU(cudaGetLastError());
   t->launches += nb_launch_counter - l0;
   if (t->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
-  rc = read_status(x, s);
-  if (rc) return rc;
+  if (!reuse && (rc = read_status(t->aux, s))) return rc;
   return read_status(t, s);
+}
+
+}  // namespace
+
+int nbody_kdk_adjoint(nbody_tree* t, const double* pos0, const float* mom0, double a0, double a1,
+                      const double* lam_pos1, const float* lam_mom1, double* lam_pos0, float* lam_mom0,
+                      nbody_stream_t stream) {
+  return kdk_adjoint_impl(t, pos0, mom0, nullptr, a0, a1, lam_pos1, lam_mom1, lam_pos0, lam_mom0,
+                          (cudaStream_t)stream);
+}
+
+int nbody_kdk_adjoint_acc(nbody_tree* t, const double* pos0, const float* mom0, const float* acc0, double a0,
+                          double a1, const double* lam_pos1, const float* lam_mom1, double* lam_pos0,
+                          float* lam_mom0, nbody_stream_t stream) {
+  if (!acc0) return NBODY_EINVAL;
+  return kdk_adjoint_impl(t, pos0, mom0, acc0, a0, a1, lam_pos1, lam_mom1, lam_pos0, lam_mom0,
+                          (cudaStream_t)stream);
 }
 
 int64_t nbody_tree_count(const nbody_tree* t, int what) {
@@ -900,6 +989,8 @@ int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
   out->builds = nb;
   out->evaluations = nf;
   out->launches = t->launches;
+  out->adjoint_steps = t->adj_steps;
+  out->adjoint_reused = t->adj_reused;
   if (t->tot.p) {
     unsigned long long c[3] = {0, 0, 0};
     NB_CU(cudaMemcpy(c, t->tot.p, sizeof(c), cudaMemcpyDeviceToHost));
@@ -911,6 +1002,8 @@ int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
     t->nb_log = 0;
     t->nf_log = 0;
     t->launches = 0;
+    t->adj_steps = 0;
+    t->adj_reused = 0;
     if (t->tot.p) NB_CU(cudaMemset(t->tot.p, 0, 64));
   }
   return NBODY_OK;

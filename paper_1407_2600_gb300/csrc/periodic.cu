@@ -478,3 +478,41 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
   nb_launch_counter += 2;
   return cudaGetLastError();
 }
+
+// Local expansions of the image field only (one per run of groups), for the
+// reverse mode, which needs them without evaluating the forces.
+cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+                           const void* tab, void* lbuf, cudaStream_t s) {
+  if (pe == 0) return cudaSuccess;
+  int grid = (int)(((int64_t)tr.ngroup * 32 + 127) / 128);
+  if (grid > 152 * 64) grid = 152 * 64;
+  if (grid < 1) grid = 1;
+  const int ls = nb_field_stride(pe);
+#define NB_LOC(TT, PE)                                                                              \
+  {                                                                                                 \
+    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
+                  nullptr, nullptr, nullptr};                                                       \
+    field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
+    break;                                                                                          \
+  }
+  if (fp64) {
+    switch (pe) {
+      case 1: NB_LOC(double, 1)
+      case 2: NB_LOC(double, 2)
+      case 3: NB_LOC(double, 3)
+      case 4: NB_LOC(double, 4)
+      default: NB_LOC(double, 5)
+    }
+  } else {
+    switch (pe) {
+      case 1: NB_LOC(float, 1)
+      case 2: NB_LOC(float, 2)
+      case 3: NB_LOC(float, 3)
+      case 4: NB_LOC(float, 4)
+      default: NB_LOC(float, 5)
+    }
+  }
+#undef NB_LOC
+  nb_launch_counter += 1;
+  return cudaGetLastError();
+}

@@ -31,7 +31,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 
 # every symbol include/nbody.h declares
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces",
-           "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_forces_vjp", "nbody_tree_count",
+           "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
            "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
 
@@ -57,7 +57,8 @@ class Timing(C.Structure):
     _fields_ = [("builds", C.c_int64), ("evaluations", C.c_int64), ("launches", C.c_int64),
                 ("p2p", C.c_double), ("m2p", C.c_double), ("m2l", C.c_double),
                 ("ms_sort", C.c_double), ("ms_build", C.c_double), ("ms_upward", C.c_double),
-                ("ms_walk", C.c_double), ("ms_periodic", C.c_double)]
+                ("ms_walk", C.c_double), ("ms_periodic", C.c_double),
+                ("adjoint_steps", C.c_int64), ("adjoint_reused", C.c_int64)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +90,8 @@ def lib():
         L.nbody_forces.argtypes = [_vp, _vp, C.POINTER(Stats), _vp]
         L.nbody_kdk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp]
         L.nbody_kdk_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp]
+        L.nbody_kdk_adjoint_acc.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp,
+                                            _vp]
         L.nbody_forces_vjp.argtypes = [_vp, _vp, _vp, _vp]
         L.nbody_tree_count.argtypes = [_vp, C.c_int]
         L.nbody_tree_count.restype = C.c_int64
@@ -150,6 +153,13 @@ def nbody_kdk_adjoint(tree: int, pos0_dev: int, mom0_dev: int, a0: float, a1: fl
                       stream: int | None = None) -> int:
     return lib().nbody_kdk_adjoint(tree, pos0_dev, mom0_dev, a0, a1, lam_pos1_dev, lam_mom1_dev,
                                    lam_pos0_dev, lam_mom0_dev, stream)
+
+
+def nbody_kdk_adjoint_acc(tree: int, pos0_dev: int, mom0_dev: int, acc0_dev: int, a0: float, a1: float,
+                          lam_pos1_dev: int, lam_mom1_dev: int, lam_pos0_dev: int, lam_mom0_dev: int,
+                          stream: int | None = None) -> int:
+    return lib().nbody_kdk_adjoint_acc(tree, pos0_dev, mom0_dev, acc0_dev, a0, a1, lam_pos1_dev, lam_mom1_dev,
+                                       lam_pos0_dev, lam_mom0_dev, stream)
 
 
 def nbody_forces_vjp(tree: int, lam_dev: int, out_dev: int, stream: int | None = None) -> int:
@@ -258,15 +268,28 @@ class Tree:
         _check(nbody_forces_vjp(self.handle, lam.data_ptr(), out.data_ptr(), _stream()), "nbody_forces_vjp")
         return out
 
-    def kdk_adjoint(self, pos0, mom0, a0, a1, lam_pos1, lam_mom1):
-        """Cotangents of (pos0, mom0) of one KDK step given those of its outputs."""
+    def kdk_adjoint(self, pos0, mom0, a0, a1, lam_pos1, lam_mom1, acc0=None):
+        """Cotangents of (pos0, mom0) of one KDK step given those of its outputs.
+        With acc0 (g(x0) as nbody_forces / nbody_kdk_step returned it) the walk
+        at x0 is skipped (nbody_kdk_adjoint_acc)."""
         import torch
-        lx0 = torch.empty((3, self.n), dtype=torch.float64, device=self.pos.device)
-        lp0 = torch.empty((3, self.n), dtype=torch.float32, device=self.pos.device)
-        _check(nbody_kdk_adjoint(self.handle, pos0.contiguous().data_ptr(), mom0.contiguous().data_ptr(), a0, a1,
-                                 lam_pos1.contiguous().double().data_ptr(),
-                                 lam_mom1.contiguous().float().data_ptr(), lx0.data_ptr(), lp0.data_ptr(),
-                                 _stream()), "nbody_kdk_adjoint")
+        dev = self.pos.device
+        # keep every converted input alive until the call has been issued
+        x0 = pos0.contiguous()
+        p0 = mom0.contiguous()
+        lx1 = lam_pos1.to(torch.float64).contiguous()
+        lp1 = lam_mom1.to(torch.float32).contiguous()
+        lx0 = torch.empty((3, self.n), dtype=torch.float64, device=dev)
+        lp0 = torch.empty((3, self.n), dtype=torch.float32, device=dev)
+        if acc0 is None:
+            _check(nbody_kdk_adjoint(self.handle, x0.data_ptr(), p0.data_ptr(), a0, a1, lx1.data_ptr(),
+                                     lp1.data_ptr(), lx0.data_ptr(), lp0.data_ptr(), _stream()),
+                   "nbody_kdk_adjoint")
+        else:
+            g0 = acc0.contiguous()
+            _check(nbody_kdk_adjoint_acc(self.handle, x0.data_ptr(), p0.data_ptr(), g0.data_ptr(), a0, a1,
+                                         lx1.data_ptr(), lp1.data_ptr(), lx0.data_ptr(), lp0.data_ptr(),
+                                         _stream()), "nbody_kdk_adjoint_acc")
         return lx0, lp0
 
     def timing(self, reset=True):
@@ -322,6 +345,7 @@ def cic_loss(pos, ng, mass=None, grad=True):
     loss = torch.empty((), dtype=torch.float64, device=pos.device)
     g = torch.empty((3, n), dtype=torch.float64, device=pos.device) if grad else None
     m = None if mass is None else mass.contiguous().float()
-    _check(nbody_cic_loss(pos.contiguous().data_ptr(), None if m is None else m.data_ptr(), n, ng, grid.data_ptr(),
+    x = pos.contiguous()
+    _check(nbody_cic_loss(x.data_ptr(), None if m is None else m.data_ptr(), n, ng, grid.data_ptr(),
                           loss.data_ptr(), None if g is None else g.data_ptr(), _stream()), "nbody_cic_loss")
     return loss, g

@@ -203,3 +203,56 @@ def test_trajectory_gradient_vs_direct_sum_adjoint(cuda):
     gd = a_init * lx + oracle.H0 * a_init ** 1.5 * lp
     rel = np.linalg.norm(g - gd, axis=1) / np.linalg.norm(gd, axis=1)
     assert np.median(rel) <= 5e-3, np.median(rel)
+
+
+def _trajectory_states(nb, tree, x, p, a_list):
+    """States (x, p, g(x)) of a short trajectory stepped by nbody_kdk_step."""
+    acc = tree.forces()
+    states = [(x.clone(), p.clone(), acc.clone())]
+    for k in range(len(a_list) - 1):
+        tree.kdk_step(p, acc, a_list[k], a_list[k + 1])
+        states.append((x.clone(), p.clone(), acc.clone()))
+    return states
+
+
+def test_kdk_adjoint_chain_reuses_and_matches_unchained(cuda):
+    """A reverse sweep of nbody_kdk_adjoint_acc calls reuses each previous
+    call's product (every call after the first), and gives the results of
+    unchained calls (a fresh tree per step) up to the reverse walk's atomic
+    summation order; nbody_kdk_adjoint (g(x0) recomputed) agrees too."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    q, psi = ics.zeldovich_particles(16, -2.0, 0.25, 9)
+    a_list = [0.05 * 1.1 ** k for k in range(5)]
+    x0, p0 = oracle.zeldovich_state(q, psi / a_list[0], a_list[0])
+    prm = _prm(1.0 / 480, 0.5, 4)
+    x = _t(x0, cuda)
+    p = _t(p0, cuda, torch.float32)
+    tree = nb.Tree(prm, x)
+    states = _trajectory_states(nb, tree, x, p, a_list)
+    rng = np.random.default_rng(2)
+    n = len(q)
+    lx_end = _t(rng.standard_normal((n, 3)), cuda)
+    lp_end = _t(rng.standard_normal((n, 3)), cuda, torch.float32)
+
+    tree.timing(reset=True)
+    lx, lp = lx_end.clone(), lp_end.clone()
+    for k in range(len(a_list) - 2, -1, -1):
+        xs, ps, gs = states[k]
+        lx, lp = tree.kdk_adjoint(xs, ps, a_list[k], a_list[k + 1], lx, lp, acc0=gs)
+    tm = tree.timing(reset=True)
+    assert tm["adjoint_steps"] == len(a_list) - 1
+    assert tm["adjoint_reused"] == len(a_list) - 2
+
+    ux, up = lx_end.clone(), lp_end.clone()
+    for k in range(len(a_list) - 2, -1, -1):
+        xs, ps, _ = states[k]
+        fresh = nb.Tree(prm, xs.clone())
+        ux, up = fresh.kdk_adjoint(xs, ps, a_list[k], a_list[k + 1], ux, up)
+        assert fresh.timing(reset=True)["adjoint_reused"] == 0
+        fresh.close()
+    tree.close()
+    for a, b in ((lx, ux), (lp.double(), up.double())):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        rms = np.sqrt(np.mean(b ** 2))
+        assert np.abs(a - b).max() <= 1e-5 * rms, np.abs(a - b).max() / rms
