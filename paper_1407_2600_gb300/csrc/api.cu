@@ -38,7 +38,8 @@ cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n
                           int4* gC, int4* gD, cudaStream_t s);
 int nb_coef_stride(int order);
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int4* cB, const double* spos,
-                      const float* smass, int64_t n, double* mom, int* arrive, void* coef, cudaStream_t s);
+                      const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey, uint32_t* uorder,
+                      uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s);
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, double* fm, cudaStream_t s);
 int nb_walk_warps(bool fp64);
@@ -119,7 +120,7 @@ struct nbody_tree {
   Buf ccount, coff, l0, plevel, pstart, pcount, pparent, bfs2pre, pre2bfs, lvlhist, scantmp, totals;
   // cells
   int ncell = 0, max_level = 0;
-  Buf cA, cB, ckey, cbox, hval, mom, arrive, coef;
+  Buf cA, cB, ckey, cbox, hval, mom, uorder, coef, ukey, urng;
   uint64_t hcap = 0;
   // groups
   int ngroup = 0;
@@ -156,7 +157,7 @@ struct nbody_tree {
     Buf* all[] = {&off, &box_of, &keys, &vals, &keys2, &vals2, &sbox, &spos, &smass, &src, &sleaf,
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
-                  &hval, &mom, &arrive, &coef, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
+                  &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
                   &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq};
@@ -444,7 +445,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(t->ckey.ensure(8 * (int64_t)ncell));
   NB_CU(t->cbox.ensure(2 * (int64_t)ncell));
   NB_CU(t->mom.ensure(8 * (int64_t)ncell * nm));
-  NB_CU(t->arrive.ensure(4 * (int64_t)ncell));
+  NB_CU(t->uorder.ensure(4 * (int64_t)ncell));
   NB_CU(t->coef.ensure((fp64 ? 8 : 4) * (int64_t)ncell * cs));
   uint64_t hc = 1;
   while (hc < 2 * (uint64_t)ncell) hc <<= 1;
@@ -479,8 +480,11 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
                       totals + 2, t->scantmp.as<int>(), s));
   NB_CU(cudaEventRecord(be[2], s));
   // A5 moments
+  NB_CU(t->ukey.ensure((int64_t)ncell));
+  NB_CU(t->urng.ensure(4 * (256 + 32)));
   NB_CU(nb_upward(p.order, fp64, ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
-                  t->smass.as<float>(), n, t->mom.as<double>(), t->arrive.as<int>(), t->coef.p, s));
+                  t->smass.as<float>(), n, t->mom.as<double>(), t->coef.p, t->ukey.as<uint8_t>(),
+                  t->uorder.as<uint32_t>(), t->urng.as<uint32_t>(), t->urng.as<int>() + 256, &sc, s));
   if (p.ewald_order > 0) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
     NB_CU(t->fm.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));

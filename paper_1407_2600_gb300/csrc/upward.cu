@@ -38,6 +38,28 @@ NB_ORD(2)
 NB_ORD(3)
 NB_ORD(4)
 
+// Exact scalings by powers of two on the integer pipe: GB300's FP64 pipe is
+// narrow, and these run once per moment of every cell.
+// v * 2^e for |v| < 2^31 (exact)
+__device__ __forceinline__ double i2d_pow2(int v, int e) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ULL : 0ULL;
+  const unsigned u = v < 0 ? (unsigned)(-(long long)v) : (unsigned)v;
+  const int msb = 31 - __clz(u);
+  const unsigned long long mant = ((unsigned long long)u << (52 - msb)) & 0x000fffffffffffffULL;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + msb + e) << 52) | mant));
+}
+
+// x * 2^k (exact unless the result under- or overflows); the exponent field
+// is adjusted directly when x and the result are normal numbers
+__device__ __forceinline__ double mul_pow2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex > 0 && ex + k > 0 && ex + k < 0x7ff) return __longlong_as_double(b + ((long long)k << 52));
+  if (ex == 0 && (b & 0x000fffffffffffffLL) == 0) return x;  // +-0
+  return x * __longlong_as_double((long long)(1023 + k) << 52);
+}
+
 // Reduced coefficients in the cell's own length unit h = 2^-level: with
 // R' = R/h and eps' = eps/h the expansion terms are O(1) for every accepted
 // cell (R' >= 1/theta), so FP32 intermediates cannot overflow however deep the
@@ -50,68 +72,99 @@ __device__ __forceinline__ void finish_cell(int c, int level, const double* M, T
   int t = 0;
 #pragma unroll
   for (int o = 0; o <= P; o++) {
-    const double sc = ldexp(1.0, level * o);
 #pragma unroll
-    for (int q = 0; q < (o + 1) * (o + 2) / 2; q++, t++) Ms[t] = M[t] * sc;
+    for (int q = 0; q < (o + 1) * (o + 2) / 2; q++, t++) Ms[t] = mul_pow2(M[t], level * o);
   }
   double B[Ord<P>::NB];
   Ord<P>::reduce(Ms, B);
   T* dst = coef + (int64_t)c * Ord<P>::NBS;
-  const double s2 = ldexp(1.0, 2 * level);
 #pragma unroll
-  for (int q = 0; q < Ord<P>::NB; q++) dst[q] = (T)(B[q] * s2);
+  for (int q = 0; q < Ord<P>::NB; q++) dst[q] = (T)mul_pow2(B[q], 2 * level);
 #pragma unroll
   for (int q = Ord<P>::NB; q < Ord<P>::NBS; q++) dst[q] = (T)0;
 }
 
+// Schedule of the upward pass.  Every cell gets an 8-bit key: leaves sort by
+// particle count (0..63) and come first; cells with daughters follow by level,
+// deepest first, and by daughter count within a level.  After a stable sort by
+// this key, one launch forms all leaves (threads of a warp have similar
+// counts) and one launch per level forms that level's parents from their
+// finished daughters (similar daughter counts), so the FP64 work runs on
+// full warps and no thread waits for another.
+__global__ void upkey_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ cB,
+                             uint8_t* __restrict__ key) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+    const int4 a = cA[b];
+    const int nch = a.w >> 8, lvl = a.w & 0xff;
+    key[b] = nch == 0 ? (uint8_t)min(cB[b].y, 63) : (uint8_t)(64 + (NB_QBITS - lvl) * 8 + (nch - 1));
+  }
+}
+
+// r[0] = number of leaves; cells with daughters at level NB_QBITS - j occupy
+// [r[j], r[j + 1]) of the sorted order, j = 0..NB_QBITS
+__global__ void urange_kernel(const uint32_t* __restrict__ hist, int* __restrict__ r) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int pos = 0;
+  for (int k = 0; k < 64; k++) pos += (int)hist[k];
+  r[0] = pos;
+  for (int j = 0; j <= NB_QBITS; j++) {
+    for (int k = 64 + 8 * j; k < 64 + 8 * (j + 1); k++) pos += (int)hist[k];
+    r[j + 1] = pos;
+  }
+}
+
+// P2M of the leaves
 template <int P, typename T>
 __global__ void __launch_bounds__(128)
-upward_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ cB,
-              const double* __restrict__ spos, const float* __restrict__ smass, int64_t n,
-              double* __restrict__ mom, int* __restrict__ arrive, T* __restrict__ coef) {
+leaf_moments_kernel(const uint32_t* __restrict__ order, const int* __restrict__ r, const int4* __restrict__ cA,
+                    const int4* __restrict__ cB, const double* __restrict__ spos, const float* __restrict__ smass,
+                    int64_t n, double* __restrict__ mom, T* __restrict__ coef) {
   constexpr int NM = Ord<P>::NM;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
-    int4 a = cA[b];
-    if ((a.w >> 8) != 0) continue;  // only leaves start a climb
-    int4 r = cB[b];
+  const int nleaf = r[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nleaf; i += gridDim.x * blockDim.x) {
+    const int b = (int)order[i];
+    const int4 a = cA[b];
+    const int4 rg = cB[b];
     double M[NM];
 #pragma unroll
     for (int t = 0; t < NM; t++) M[t] = 0.0;
-    double cx = ldexp((double)a.x, -23), cy = ldexp((double)a.y, -23), cz = ldexp((double)a.z, -23);
-    for (int j = r.x; j < r.x + r.y; j++)
+    const double cx = i2d_pow2(a.x, -23), cy = i2d_pow2(a.y, -23), cz = i2d_pow2(a.z, -23);
+    for (int j = rg.x; j < rg.x + rg.y; j++)
       Ord<P>::p2m((double)smass[j], spos[j] - cx, spos[n + j] - cy, spos[2 * n + j] - cz, M);
     double* dst = mom + (int64_t)b * NM;
 #pragma unroll
     for (int t = 0; t < NM; t++) dst[t] = M[t];
     finish_cell<P, T>(b, a.w & 0xff, M, coef);
-    int c = b;
-    while (true) {
-      int par = cB[c].w;
-      if (par < 0) break;
-      __threadfence();
-      int nch = cA[par].w >> 8;
-      int old = atomicAdd(&arrive[par], 1);
-      if (old != nch - 1) break;
-      __threadfence();
-      int4 pa = cA[par];
-      int first = cB[par].z;
+  }
+}
+
+// M2M of the parents of one level from their daughters (formed by earlier launches)
+template <int P, typename T>
+__global__ void __launch_bounds__(128)
+level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __restrict__ r,
+                     const int4* __restrict__ cA, const int4* __restrict__ cB, double* __restrict__ mom,
+                     T* __restrict__ coef) {
+  constexpr int NM = Ord<P>::NM;
+  const int lo = r[j], hi = r[j + 1];
+  for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
+    const int b = (int)order[i];
+    const int4 pa = cA[b];
+    const int first = cB[b].z, nch = pa.w >> 8;
+    double M[NM];
 #pragma unroll
-      for (int t = 0; t < NM; t++) M[t] = 0.0;
-      for (int ch = first; ch < first + nch; ch++) {
-        int4 ca = __ldcg(&cA[ch]);
-        double Mc[NM];
-        const double* src = mom + (int64_t)ch * NM;
+    for (int t = 0; t < NM; t++) M[t] = 0.0;
+    for (int ch = first; ch < first + nch; ch++) {
+      const int4 ca = cA[ch];
+      double Mc[NM];
+      const double* src = mom + (int64_t)ch * NM;
 #pragma unroll
-        for (int t = 0; t < NM; t++) Mc[t] = __ldcg(src + t);
-        Ord<P>::m2m(Mc, ldexp((double)(ca.x - pa.x), -23), ldexp((double)(ca.y - pa.y), -23),
-                    ldexp((double)(ca.z - pa.z), -23), M);
-      }
-      double* pd = mom + (int64_t)par * NM;
-#pragma unroll
-      for (int t = 0; t < NM; t++) pd[t] = M[t];
-      finish_cell<P, T>(par, pa.w & 0xff, M, coef);
-      c = par;
+      for (int t = 0; t < NM; t++) Mc[t] = src[t];
+      Ord<P>::m2m(Mc, i2d_pow2(ca.x - pa.x, -23), i2d_pow2(ca.y - pa.y, -23), i2d_pow2(ca.z - pa.z, -23), M);
     }
+    double* pd = mom + (int64_t)b * NM;
+#pragma unroll
+    for (int t = 0; t < NM; t++) pd[t] = M[t];
+    finish_cell<P, T>(b, pa.w & 0xff, M, coef);
   }
 }
 
@@ -198,24 +251,34 @@ int nb_coef_stride(int order) {
 }
 
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int4* cB, const double* spos,
-                      const float* smass, int64_t n, double* mom, int* arrive, void* coef, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(arrive, 0, sizeof(int) * ncell, s);
-  if (e) return e;
-  int g = gridc(ncell, 128);
-#define NB_UP(P)                                                                                      \
-  if (fp64)                                                                                           \
-    upward_kernel<P, double><<<g, 128, 0, s>>>(ncell, cA, cB, spos, smass, n, mom, arrive, (double*)coef); \
-  else                                                                                                \
-    upward_kernel<P, float><<<g, 128, 0, s>>>(ncell, cA, cB, spos, smass, n, mom, arrive, (float*)coef);
-  switch (order) {
-    case 0: NB_UP(0) break;
-    case 1: NB_UP(1) break;
-    case 2: NB_UP(2) break;
-    case 3: NB_UP(3) break;
-    default: NB_UP(4) break;
-  }
-#undef NB_UP
+                      const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey, uint32_t* uorder,
+                      uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s) {
+  upkey_kernel<<<gridc(ncell, 256), 256, 0, s>>>(ncell, cA, cB, ukey);
   nb_launch_counter += 1;
+  cudaError_t e = nb_sort_digit8(ukey, ncell, uorder, uhist, sc, s);
+  if (e) return e;
+  urange_kernel<<<1, 32, 0, s>>>(uhist, urange);
+  nb_launch_counter += 1;
+  const int g = gridc(ncell, 128);
+  const int gl = g < 152 * 8 ? g : 152 * 8;
+#define NB_UP(P, TT)                                                                                        \
+  {                                                                                                         \
+    leaf_moments_kernel<P, TT><<<g, 128, 0, s>>>(uorder, urange, cA, cB, spos, smass, n, mom, (TT*)coef);   \
+    for (int j = 0; j <= NB_QBITS; j++)                                                                     \
+      level_moments_kernel<P, TT><<<gl, 128, 0, s>>>(j, uorder, urange, cA, cB, mom, (TT*)coef);           \
+  }
+#define NB_UPP(P) \
+  if (fp64) NB_UP(P, double) else NB_UP(P, float)
+  switch (order) {
+    case 0: NB_UPP(0) break;
+    case 1: NB_UPP(1) break;
+    case 2: NB_UPP(2) break;
+    case 3: NB_UPP(3) break;
+    default: NB_UPP(4) break;
+  }
+#undef NB_UPP
+#undef NB_UP
+  nb_launch_counter += 2 + NB_QBITS;
   return cudaGetLastError();
 }
 
