@@ -73,12 +73,14 @@ template <typename T, int P, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
   using V4 = typename Vec4<T>::type;
   constexpr int NBS = AOrd<P>::NBS, NM = AOrd<P>::NM;
+  constexpr int C16 = NBS * (int)sizeof(T) / 16;
   __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
   __shared__ V4 s_src[WARPS][32];
   __shared__ int s_jidx[WARPS][32];
-  __shared__ T s_moff[WARPS][32][4];
-  __shared__ T s_meps[WARPS][32];
-  __shared__ int s_midx[WARPS][32];
+  // M2P queue (up to 31 carried + 32 new), as in the forward walk
+  __shared__ V4 s_moff[WARPS][64];
+  __shared__ T s_meps[WARPS][64];
+  __shared__ int s_midx[WARPS][64];
   __shared__ int s_pfx[WARPS][32], s_pst[WARPS][32], s_plev[WARPS][32];
   __shared__ T s_poff[WARPS][32][3];
   __shared__ int4 s_pcen[WARPS][32];
@@ -122,6 +124,45 @@ __global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
     s_sl[wid][lane][1] = ly;
     s_sl[wid][lane][2] = lz;
     T mx = 0, my = 0, mz = 0;  // sink cotangent
+    int qn = 0;                // queued M2P cells
+    // the first nmp queued M2P cells: sink side (Hessian-vector products, in
+    // the cell unit, times 2^level) and source side (lane q owns cell q and
+    // sums its moment cotangents over the group's sinks)
+    auto m2p_chunk = [&](int nmp) {
+      const int4* gsrc = reinterpret_cast<const int4*>(w.coef);
+      int4* sdst = reinterpret_cast<int4*>(&s_coef[wid][0]);
+      for (int t = lane; t < nmp * C16; t += 32) {
+        const int q = t / C16, r = t - q * C16;
+        sdst[t] = gsrc[(int64_t)s_midx[wid][q] * C16 + r];
+      }
+      __syncwarp();
+      if (act) {
+        for (int q = 0; q < nmp; q++) {
+          const V4 mo = s_moff[wid][q];
+          T ox = 0, oy = 0, oz = 0;
+          AOrd<P>::template self<T>(&s_coef[wid][q * NBS], fma(xi, mo.w, mo.x), fma(yi, mo.w, mo.y),
+                                    fma(zi, mo.w, mo.z), s_meps[wid][q], lx, ly, lz, ox, oy, oz);
+          mx = fma(ox, mo.w, mx);
+          my = fma(oy, mo.w, my);
+          mz = fma(oz, mo.w, mz);
+        }
+      }
+      if (lane < nmp) {
+        const V4 mo = s_moff[wid][lane];
+        const T e2 = s_meps[wid][lane];
+        T nu[NM];
+#pragma unroll
+        for (int t = 0; t < NM; t++) nu[t] = (T)0;
+        for (int sk = 0; sk < cnt; sk++)
+          AOrd<P>::template src<T>(fma(s_sx[wid][sk][0], mo.w, mo.x), fma(s_sx[wid][sk][1], mo.w, mo.y),
+                                   fma(s_sx[wid][sk][2], mo.w, mo.z), e2, s_sl[wid][sk][0], s_sl[wid][sk][1],
+                                   s_sl[wid][sk][2], nu);
+        float* dst = w.nuc + (int64_t)s_midx[wid][lane] * NM;
+#pragma unroll
+        for (int t = 0; t < NM; t++) atomicAdd(dst + t, (float)nu[t]);
+      }
+      __syncwarp();
+    };
     int top = 1;
     if (lane == 0) stk[0] = box;
     __syncwarp();
@@ -155,51 +196,28 @@ __global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
       }
       const unsigned mm = __ballot_sync(FULL, cls == NB_CELL_M2P);
       if (mm) {
-        const int nmp = __popc(mm);
         if (cls == NB_CELL_M2P) {
-          const int pos = __popc(mm & ltmask);
+          const int pos = qn + __popc(mm & ltmask);
           const T sc = (T)(1 << lvl);
           s_midx[wid][pos] = c;
-          s_moff[wid][pos][0] = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
-          s_moff[wid][pos][1] = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
-          s_moff[wid][pos][2] = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
-          s_moff[wid][pos][3] = sc;
+          V4 mo;
+          mo.x = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
+          mo.y = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
+          mo.z = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
+          mo.w = sc;
+          s_moff[wid][pos] = mo;
           s_meps[wid][pos] = eps2 * (sc * sc);
         }
-        __syncwarp();
-        for (int t = lane; t < nmp * NBS; t += 32) {
-          const int q = t / NBS, r = t - q * NBS;
-          s_coef[wid][t] = w.coef[(int64_t)s_midx[wid][q] * NBS + r];
-        }
-        __syncwarp();
-        // sink side: Hessian-vector products (in the cell unit, times 2^level)
-        if (act) {
-          for (int q = 0; q < nmp; q++) {
-            const T sc = s_moff[wid][q][3];
-            T ox = 0, oy = 0, oz = 0;
-            AOrd<P>::template self<T>(&s_coef[wid][q * NBS], fma(xi, sc, s_moff[wid][q][0]),
-                                      fma(yi, sc, s_moff[wid][q][1]), fma(zi, sc, s_moff[wid][q][2]),
-                                      s_meps[wid][q], lx, ly, lz, ox, oy, oz);
-            mx = fma(ox, sc, mx);
-            my = fma(oy, sc, my);
-            mz = fma(oz, sc, mz);
+        qn += __popc(mm);
+        if (qn >= 32) {
+          __syncwarp();
+          m2p_chunk(32);
+          if (lane < qn - 32) {
+            s_midx[wid][lane] = s_midx[wid][32 + lane];
+            s_moff[wid][lane] = s_moff[wid][32 + lane];
+            s_meps[wid][lane] = s_meps[wid][32 + lane];
           }
-        }
-        // source side: lane q owns cell q and sums over the group's sinks
-        if (lane < nmp) {
-          const T sc = s_moff[wid][lane][3];
-          const T ox = s_moff[wid][lane][0], oy = s_moff[wid][lane][1], oz = s_moff[wid][lane][2];
-          const T e2 = s_meps[wid][lane];
-          T nu[NM];
-#pragma unroll
-          for (int t = 0; t < NM; t++) nu[t] = (T)0;
-          for (int sk = 0; sk < cnt; sk++)
-            AOrd<P>::template src<T>(fma(s_sx[wid][sk][0], sc, ox), fma(s_sx[wid][sk][1], sc, oy),
-                                     fma(s_sx[wid][sk][2], sc, oz), e2, s_sl[wid][sk][0], s_sl[wid][sk][1],
-                                     s_sl[wid][sk][2], nu);
-          float* dst = w.nuc + (int64_t)s_midx[wid][lane] * NM;
-#pragma unroll
-          for (int t = 0; t < NM; t++) atomicAdd(dst + t, (float)nu[t]);
+          qn -= 32;
         }
         __syncwarp();
       }
@@ -287,6 +305,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
     }
+    if (qn > 0) m2p_chunk(qn);
     if (act) {
       atomicAdd(&w.mu[i], (double)mx);
       atomicAdd(&w.mu[tr.n + i], (double)my);

@@ -6,12 +6,12 @@
 // One warp per group of <= 32 sinks (one sink per lane).  The warp walks the
 // tree cooperatively: it pops up to 32 cells from its stack, each lane tests
 // one cell with the integer acceptance test, opened cells push their
-// daughters, accepted cells are evaluated at once as a chunk of M2P
-// interactions (coefficients staged in shared memory, every lane a sink),
-// and leaves are flattened into chunks of 32 source particles staged in
-// shared memory for the P2P loop.  Every chunk's partial sum is added with
-// Kahan compensation.  The walk order is fixed, so results are bitwise
-// reproducible.
+// daughters, accepted cells join a queue of M2P interactions that is
+// evaluated 32 cells at a time (coefficients staged in shared memory, every
+// lane a sink), and leaves are flattened into chunks of 32 source particles
+// staged in shared memory for the P2P loop.  Every chunk's partial sum is
+// added with Kahan compensation.  The walk order is fixed, so results are
+// bitwise reproducible.
 //
 // Acceptance: in integer units of 2^-23, with the cell at the image of its
 // level-l_E ancestor nearest the group's expansion point e (the centre of
@@ -66,11 +66,14 @@ template <typename T, int P, int WARPS, int MINB>
 __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   using V4 = typename Vec4<T>::type;
   constexpr int NBS = WOrd<P>::NBS;
+  constexpr int C16 = NBS * (int)sizeof(T) / 16;  // 16-byte pieces per cell's coefficients
   __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
   __shared__ V4 s_src[WARPS][32];
-  __shared__ T s_moff[WARPS][32][4];  // centre offset and, in [3], the cell scale 2^level
-  __shared__ int s_midx[WARPS][32];
-  __shared__ T s_meps[WARPS][32];
+  // M2P queue (up to 31 carried + 32 new): centre offset and, in .w, the
+  // cell scale 2^level; eps^2 in the cell unit; cell index
+  __shared__ V4 s_moff[WARPS][64];
+  __shared__ int s_midx[WARPS][64];
+  __shared__ T s_meps[WARPS][64];
   __shared__ int s_pfx[WARPS][32];
   __shared__ int s_pst[WARPS][32];
   __shared__ int s_plev[WARPS][32];
@@ -104,6 +107,32 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     }
     T ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;
     unsigned long long n_p2p = 0, n_m2p = 0;
+    int qn = 0;  // queued M2P cells
+    // evaluate the first nmp queued M2P cells for every sink of the group
+    auto m2p_chunk = [&](int nmp) {
+      const int4* gsrc = reinterpret_cast<const int4*>(w.coef);
+      int4* sdst = reinterpret_cast<int4*>(&s_coef[wid][0]);
+      for (int t = lane; t < nmp * C16; t += 32) {
+        const int q = t / C16, r = t - q * C16;
+        sdst[t] = gsrc[(int64_t)s_midx[wid][q] * C16 + r];
+      }
+      __syncwarp();
+      if (act) {
+        T px = 0, py = 0, pz = 0;
+        // each M2P runs in its cell's unit (coordinates times 2^level,
+        // coefficients pre-scaled): see the upward pass
+        for (int q = 0; q < nmp; q++) {
+          const V4 mo = s_moff[wid][q];
+          WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], fma(xi, mo.w, mo.x), fma(yi, mo.w, mo.y),
+                                   fma(zi, mo.w, mo.z), s_meps[wid][q], px, py, pz);
+        }
+        kadd(ax, cx, px);
+        kadd(ay, cy, py);
+        kadd(az, cz, pz);
+      }
+      n_m2p += nmp;
+      __syncwarp();
+    };
     int top = 1;
     if (lane == 0) stk[0] = box;  // root of this box
     __syncwarp();
@@ -137,42 +166,34 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         top += tot;
         __syncwarp();
       }
-      // M2P chunk
-      const unsigned mm = __ballot_sync(FULL, cls == 2);
+      // queue the accepted cells; evaluate whenever 32 are queued
+      const unsigned mm = __ballot_sync(FULL, cls == NB_CELL_M2P);
       if (mm) {
-        const int nmp = __popc(mm);
-        if (cls == 2) {
-          const int pos = __popc(mm & ltmask);
+        if (cls == NB_CELL_M2P) {
+          const int pos = qn + __popc(mm & ltmask);
           s_midx[wid][pos] = c;
           // -(c* - e) 2^level and eps^2 4^level: the cell's unit (exact scalings)
           const T sc = (T)(1 << lvl);
-          s_moff[wid][pos][0] = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
-          s_moff[wid][pos][1] = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
-          s_moff[wid][pos][2] = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
-          s_moff[wid][pos][3] = sc;
+          V4 mo;
+          mo.x = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
+          mo.y = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
+          mo.z = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
+          mo.w = sc;
+          s_moff[wid][pos] = mo;
           s_meps[wid][pos] = eps2 * (sc * sc);
         }
-        __syncwarp();
-        for (int t = lane; t < nmp * NBS; t += 32) {
-          const int q = t / NBS, r = t - q * NBS;
-          s_coef[wid][t] = w.coef[(int64_t)s_midx[wid][q] * NBS + r];
-        }
-        __syncwarp();
-        if (act) {
-          T px = 0, py = 0, pz = 0;
-          // each M2P runs in its cell's unit (coordinates times 2^level,
-          // coefficients pre-scaled): see the upward pass
-          for (int q = 0; q < nmp; q++) {
-            const T sc = s_moff[wid][q][3];
-            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], fma(xi, sc, s_moff[wid][q][0]),
-                                     fma(yi, sc, s_moff[wid][q][1]), fma(zi, sc, s_moff[wid][q][2]),
-                                     s_meps[wid][q], px, py, pz);
+        qn += __popc(mm);
+        if (qn >= 32) {
+          __syncwarp();
+          m2p_chunk(32);
+          // carry the remainder to the front of the queue
+          if (lane < qn - 32) {
+            s_midx[wid][lane] = s_midx[wid][32 + lane];
+            s_moff[wid][lane] = s_moff[wid][32 + lane];
+            s_meps[wid][lane] = s_meps[wid][32 + lane];
           }
-          kadd(ax, cx, px);
-          kadd(ay, cy, py);
-          kadd(az, cz, pz);
+          qn -= 32;
         }
-        n_m2p += nmp;
         __syncwarp();
       }
       // P2P chunks
@@ -244,6 +265,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
     }
+    if (qn > 0) m2p_chunk(qn);
     if (act) {
       w.acc[i] = ax - cx;
       w.acc[tr.n + i] = ay - cy;
