@@ -363,6 +363,9 @@ def run_gpu(args, rank, world, local_rank):
             "force_eval_ms": force_ms,
             "force_updates_per_s": n / (force_ms * 1e-3),
             "interactions_per_particle": {"p2p": tm["p2p"] / evals / n, "m2p": tm["m2p"] / evals / n},
+            "walk_autotune": {"variant": tm["walk_variant"], "tuning_ms": tm["walk_tune_ms"][:4],
+                              "variants": ["scalar M2P, 8 warps x 2 blocks/SM", "scalar M2P, 8 x 3",
+                                           "packed FP32x2 M2P, 8 x 2", "packed FP32x2 M2P, 4 x 5"]},
             "adjoint_forward_ratio": adj["ratio"] if adj else None,
             "adjoint": adj,
         }

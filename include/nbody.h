@@ -58,6 +58,13 @@ enum {
 
 enum { NBODY_MIXED = 0, NBODY_FP64 = 1 };
 enum { NBODY_FLAG_ASYNC = 1 };
+/* flags bits 8..11: walk launch variant + 1 to use instead of the autotuned
+ * one (0 = autotune).  Mixed precision has variants 0..3 (one M2P per
+ * instruction stream with 8 warps x 2 or 3 blocks per SM; two M2P at once in
+ * packed FP32 pairs with 8 x 2 or 4 x 5); FP64 has only variant 0.
+ * Every variant computes the same interactions; results differ by the
+ * summation order only. */
+#define NBODY_FLAG_WALK_VARIANT(v) (((v) + 1) << 8)
 
 typedef struct {
   double eps;       /* Plummer softening length, box units (> 0); per-box
@@ -216,6 +223,9 @@ typedef struct {
   double ms_sort, ms_build, ms_upward, ms_walk, ms_periodic; /* summed device times */
   int64_t adjoint_steps;   /* nbody_kdk_adjoint(_acc) calls */
   int64_t adjoint_reused;  /* of which reused the previous call's J(x0)^T lam_ph */
+  int64_t walk_variant;    /* walk launch variant the autotuner chose for this tree's
+                              precision and order on this device (-1: not tuned yet) */
+  double walk_tune_ms[8];  /* each variant's time in the tuning run (0: not timed) */
 } nbody_timing;
 int nbody_timing_read(nbody_tree *tree, nbody_timing *out, int reset);
 

@@ -36,6 +36,7 @@ cudaError_t nb_group_runs(int ngroup, int4* gA, int4* gD, int* flag, int* excl, 
 cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, int ls,
                           const int* flag, const int* gid, int* gstart, const double* spos, int4* gA, int4* gB,
                           int4* gC, int4* gD, cudaStream_t s);
+int nb_walk_variant(bool fp64, int order, double* ms);
 int nb_coef_stride(int order);
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int4* cB, const double* spos,
                       const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey, uint32_t* uorder,
@@ -46,7 +47,7 @@ int nb_walk_warps(bool fp64);
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
-                    cudaStream_t s);
+                    int forced_variant, cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -228,6 +229,7 @@ int validate(const nbody_params* p) {
     if (p->ewald_grid < p->ewald_level + 1 || p->ewald_grid > 8) return NBODY_EINVAL;
   }
   if (p->precision != NBODY_MIXED && p->precision != NBODY_FP64) return NBODY_EINVAL;
+  if (((p->flags >> 8) & 0xf) > 4) return NBODY_EINVAL;  // walk variant override 0..3
   return NBODY_OK;
 }
 
@@ -553,7 +555,7 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
-                t->status.as<unsigned>(), t->nsm, s));
+                t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, s));
   NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
@@ -993,6 +995,7 @@ int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
   out->builds = nb;
   out->evaluations = nf;
   out->launches = t->launches;
+  out->walk_variant = nb_walk_variant(t->prm.precision == NBODY_FP64, t->prm.order, out->walk_tune_ms);
   out->adjoint_steps = t->adj_steps;
   out->adjoint_reused = t->adj_reused;
   if (t->tot.p) {

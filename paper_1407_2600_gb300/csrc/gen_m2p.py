@@ -15,7 +15,7 @@ h(n,k) = prod_d n_d! / (k_d! (n_d - 2k_d)! 2^k_d), regroups the potential as
 
 so that, with d_i F_j = R_i F_{j+1},
 
-    a_i = d_i phi = sum_j ( R_i F_{j+1} S_j + F_j d_i S_j ).
+    a_i = d_i phi = R_i sum_j F_{j+1} S_j + sum_j F_j d_i S_j.
 
 The per-cell coefficients are stored as a! B_{j,a} with the divided monomials
 mu_a = R^a / a!, so that d_i mu_a = mu_{a - e_i} exactly and the gradient sums
@@ -93,7 +93,8 @@ def flop_count(p):
     for (j, a) in sl:
         fl += 2  # S_j FMA
         fl += 2 * sum(1 for d in range(3) if a[d] > 0)  # G_{j,d} FMA
-    fl += (p + 1) * (1 + 3 * 4)  # t_j = F_{j+1} S_j; a_i += R_i t_j + F_j G_ji
+    fl += 1 + 2 * p  # t = sum_j F_{j+1} S_j
+    fl += 3 * 2 * (p + 1)  # a_i += R_i t + sum_{j>=1} F_j G_ji
     return fl
 
 
@@ -138,12 +139,90 @@ def emit_m2p(p):
                 par[d] -= 1
                 L.append("    G%d%s = fma(b, m%d, G%d%s);" % (j, ax, mi[tuple(par)], j, ax))
         L.append("  }")
+    # a = R sum_j F_{j+1} S_j + sum_{j>=1} F_j G_j  (G_0 = 0)
+    L.append("  T t = F1 * S0;")
+    for j in range(1, p + 1):
+        L.append("  t = fma(F%d, S%d, t);" % (j + 1, j))
+    for c in "xyz":
+        e = "a%s" % c
+        for j in range(p, 0, -1):
+            e = "fma(F%d, G%d%s, %s)" % (j, j, c, e)
+        L.append("  a%s = fma(R%s, t, %s);" % (c, c, e))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_m2p2(p):
+    """The M2P of two cells at once for one sink, in packed FP32 pairs (the
+    .x and .y halves are the two cells; B holds the two cells' coefficients
+    interleaved).  Every half performs the operations of m2p_p<p> in the
+    same order, so each cell's result equals the scalar one bit for bit."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    sl = slots(p)
+    L = []
+    L.append("__device__ __forceinline__ void m2p2_p%d(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz," % p)
+    L.append("                                       float2 eps2, float2& ax, float2& ay, float2& az) {")
+    L.append("  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));")
+    L.append("  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));")
+    L.append("  const float2 is = __fmul2_rn(F0, F0);")
+    for j in range(1, p + 2):
+        c = -(2 * j - 1)
+        L.append("  const float2 F%d = __fmul2_rn(F%d, __fmul2_rn(make_float2(%d.0f, %d.0f), is));" % (j, j - 1, c, c))
+    for d, R in enumerate(("Rx", "Ry", "Rz")):
+        for k in range(2, p + 1):
+            c = "%.9gf" % (1.0 / k)
+            L.append("  const float2 %s_%d = __fmul2_rn(%s, make_float2(%s, %s));" % (R, k, R, c, c))
+    for i, m in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                pi = mi[tuple(par)]
+                R = ("Rx", "Ry", "Rz")[d]
+                fac = R if m[d] == 1 else "%s_%d" % (R, m[d])
+                L.append("  const float2 m%d = %s;" % (i, fac if pi == 0 else "__fmul2_rn(m%d, %s)" % (pi, fac)))
+                break
+    started = set()
+
+    def acc(name, b, mono):
+        if name not in started:  # first term: the accumulator starts from zero
+            started.add(name)
+            return "    %s = %s;" % (name, b if mono == 0 else "__fmul2_rn(%s, m%d)" % (b, mono))
+        if mono == 0:
+            return "    %s = __fadd2_rn(%s, %s);" % (name, b, name)
+        return "    %s = __ffma2_rn(%s, m%d, %s);" % (name, b, mono, name)
+
+    names = []
     for j in range(p + 1):
-        L.append("  { const T t = F%d * S%d;" % (j + 1, j))
-        L.append("    ax = fma(Rx, t, fma(F%d, G%dx, ax));" % (j, j))
-        L.append("    ay = fma(Ry, t, fma(F%d, G%dy, ay));" % (j, j))
-        L.append("    az = fma(Rz, t, fma(F%d, G%dz, az));" % (j, j))
+        names += ["S%d" % j] + ["G%d%s" % (j, c) for c in "xyz"]
+    used = set()
+    for (j, a) in sl:
+        used.add("S%d" % j)
+        for d, c in enumerate("xyz"):
+            if a[d] > 0:
+                used.add("G%d%s" % (j, c))
+    L.append("  float2 %s;" % ", ".join(n for n in names if n in used))
+    for t, (j, a) in enumerate(sl):
+        ai = mi[a]
+        L.append("  { const float2 b = B[%d];" % t)
+        L.append(acc("S%d" % j, "b", ai))
+        for d, c in enumerate("xyz"):
+            if a[d] > 0:
+                par = list(a)
+                par[d] -= 1
+                L.append(acc("G%d%s" % (j, c), "b", mi[tuple(par)]))
         L.append("  }")
+    L.append("  float2 t = __fmul2_rn(F1, S0);")
+    for j in range(1, p + 1):
+        L.append("  t = __ffma2_rn(F%d, S%d, t);" % (j + 1, j))
+    for c in "xyz":
+        e = "a%s" % c
+        for j in range(p, 0, -1):
+            e = "__ffma2_rn(F%d, G%d%s, %s)" % (j, j, c, e)
+        L.append("  a%s = __ffma2_rn(R%s, t, %s);" % (c, c, e))
     L.append("}")
     return "\n".join(L)
 
@@ -286,6 +365,8 @@ def generate():
     out.append("")
     for p in range(5):
         out.append(emit_m2p(p))
+        out.append("")
+        out.append(emit_m2p2(p))
         out.append("")
         out.append(emit_reduce(p))
         out.append("")

@@ -3,15 +3,15 @@
 #pragma once
 
 constexpr int kNB0 = 1;  // reduced coefficients at order 0
-constexpr int kM2PFlops0 = 31;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops0 = 25;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB1 = 4;  // reduced coefficients at order 1
-constexpr int kM2PFlops1 = 61;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops1 = 50;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB2 = 11;  // reduced coefficients at order 2
-constexpr int kM2PFlops2 = 117;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops2 = 101;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB3 = 24;  // reduced coefficients at order 3
-constexpr int kM2PFlops3 = 213;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops3 = 192;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB4 = 46;  // reduced coefficients at order 4
-constexpr int kM2PFlops4 = 368;  // flops per M2P (FMA = 2, rsqrt = 1)
+constexpr int kM2PFlops4 = 342;  // flops per M2P (FMA = 2, rsqrt = 1)
 
 template <typename T>
 __device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
@@ -25,11 +25,26 @@ __device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz
   { const T b = B[0];
     S0 = fma(b, m0, S0);
   }
-  { const T t = F1 * S0;
-    ax = fma(Rx, t, fma(F0, G0x, ax));
-    ay = fma(Ry, t, fma(F0, G0y, ay));
-    az = fma(Rz, t, fma(F0, G0z, az));
+  T t = F1 * S0;
+  ax = fma(Rx, t, ax);
+  ay = fma(Ry, t, ay);
+  az = fma(Rz, t, az);
+}
+
+__device__ __forceinline__ void m2p2_p0(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
+                                       float2 eps2, float2& ax, float2& ay, float2& az) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  float2 S0;
+  { const float2 b = B[0];
+    S0 = b;
   }
+  float2 t = __fmul2_rn(F1, S0);
+  ax = __ffma2_rn(Rx, t, ax);
+  ay = __ffma2_rn(Ry, t, ay);
+  az = __ffma2_rn(Rz, t, az);
 }
 
 __device__ __forceinline__ void reduce_moments_p0(const double* __restrict__ M, double* __restrict__ B) {
@@ -65,16 +80,44 @@ __device__ __forceinline__ void m2p_p1(const T* __restrict__ B, T Rx, T Ry, T Rz
     S1 = fma(b, m3, S1);
     G1z = fma(b, m0, G1z);
   }
-  { const T t = F1 * S0;
-    ax = fma(Rx, t, fma(F0, G0x, ax));
-    ay = fma(Ry, t, fma(F0, G0y, ay));
-    az = fma(Rz, t, fma(F0, G0z, az));
+  T t = F1 * S0;
+  t = fma(F2, S1, t);
+  ax = fma(Rx, t, fma(F1, G1x, ax));
+  ay = fma(Ry, t, fma(F1, G1y, ay));
+  az = fma(Rz, t, fma(F1, G1z, az));
+}
+
+__device__ __forceinline__ void m2p2_p1(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
+                                       float2 eps2, float2& ax, float2& ay, float2& az) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  float2 S0, S1, G1x, G1y, G1z;
+  { const float2 b = B[0];
+    S0 = b;
   }
-  { const T t = F2 * S1;
-    ax = fma(Rx, t, fma(F1, G1x, ax));
-    ay = fma(Ry, t, fma(F1, G1y, ay));
-    az = fma(Rz, t, fma(F1, G1z, az));
+  { const float2 b = B[1];
+    S1 = __fmul2_rn(b, m1);
+    G1x = b;
   }
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
+  }
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  float2 t = __fmul2_rn(F1, S0);
+  t = __ffma2_rn(F2, S1, t);
+  ax = __ffma2_rn(Rx, t, __ffma2_rn(F1, G1x, ax));
+  ay = __ffma2_rn(Ry, t, __ffma2_rn(F1, G1y, ay));
+  az = __ffma2_rn(Rz, t, __ffma2_rn(F1, G1z, az));
 }
 
 __device__ __forceinline__ void reduce_moments_p1(const double* __restrict__ M, double* __restrict__ B) {
@@ -154,21 +197,86 @@ __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz
     S2 = fma(b, m9, S2);
     G2z = fma(b, m3, G2z);
   }
-  { const T t = F1 * S0;
-    ax = fma(Rx, t, fma(F0, G0x, ax));
-    ay = fma(Ry, t, fma(F0, G0y, ay));
-    az = fma(Rz, t, fma(F0, G0z, az));
+  T t = F1 * S0;
+  t = fma(F2, S1, t);
+  t = fma(F3, S2, t);
+  ax = fma(Rx, t, fma(F1, G1x, fma(F2, G2x, ax)));
+  ay = fma(Ry, t, fma(F1, G1y, fma(F2, G2y, ay)));
+  az = fma(Rz, t, fma(F1, G1z, fma(F2, G2z, az)));
+}
+
+__device__ __forceinline__ void m2p2_p2(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
+                                       float2 eps2, float2& ax, float2& ay, float2& az) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 Rx_2 = __fmul2_rn(Rx, make_float2(0.5f, 0.5f));
+  const float2 Ry_2 = __fmul2_rn(Ry, make_float2(0.5f, 0.5f));
+  const float2 Rz_2 = __fmul2_rn(Rz, make_float2(0.5f, 0.5f));
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  const float2 m4 = __fmul2_rn(m1, Rx_2);
+  const float2 m5 = __fmul2_rn(m2, Rx);
+  const float2 m6 = __fmul2_rn(m3, Rx);
+  const float2 m7 = __fmul2_rn(m2, Ry_2);
+  const float2 m8 = __fmul2_rn(m3, Ry);
+  const float2 m9 = __fmul2_rn(m3, Rz_2);
+  float2 S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z;
+  { const float2 b = B[0];
+    S0 = b;
   }
-  { const T t = F2 * S1;
-    ax = fma(Rx, t, fma(F1, G1x, ax));
-    ay = fma(Ry, t, fma(F1, G1y, ay));
-    az = fma(Rz, t, fma(F1, G1z, az));
+  { const float2 b = B[1];
+    S1 = b;
   }
-  { const T t = F3 * S2;
-    ax = fma(Rx, t, fma(F2, G2x, ax));
-    ay = fma(Ry, t, fma(F2, G2y, ay));
-    az = fma(Rz, t, fma(F2, G2z, az));
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m1, S1);
+    G1x = b;
   }
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
+  }
+  { const float2 b = B[4];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  { const float2 b = B[5];
+    S2 = __fmul2_rn(b, m4);
+    G2x = __fmul2_rn(b, m1);
+  }
+  { const float2 b = B[6];
+    S2 = __ffma2_rn(b, m5, S2);
+    G2x = __ffma2_rn(b, m2, G2x);
+    G2y = __fmul2_rn(b, m1);
+  }
+  { const float2 b = B[7];
+    S2 = __ffma2_rn(b, m6, S2);
+    G2x = __ffma2_rn(b, m3, G2x);
+    G2z = __fmul2_rn(b, m1);
+  }
+  { const float2 b = B[8];
+    S2 = __ffma2_rn(b, m7, S2);
+    G2y = __ffma2_rn(b, m2, G2y);
+  }
+  { const float2 b = B[9];
+    S2 = __ffma2_rn(b, m8, S2);
+    G2y = __ffma2_rn(b, m3, G2y);
+    G2z = __ffma2_rn(b, m2, G2z);
+  }
+  { const float2 b = B[10];
+    S2 = __ffma2_rn(b, m9, S2);
+    G2z = __ffma2_rn(b, m3, G2z);
+  }
+  float2 t = __fmul2_rn(F1, S0);
+  t = __ffma2_rn(F2, S1, t);
+  t = __ffma2_rn(F3, S2, t);
+  ax = __ffma2_rn(Rx, t, __ffma2_rn(F1, G1x, __ffma2_rn(F2, G2x, ax)));
+  ay = __ffma2_rn(Ry, t, __ffma2_rn(F1, G1y, __ffma2_rn(F2, G2y, ay)));
+  az = __ffma2_rn(Rz, t, __ffma2_rn(F1, G1z, __ffma2_rn(F2, G2z, az)));
 }
 
 __device__ __forceinline__ void reduce_moments_p2(const double* __restrict__ M, double* __restrict__ B) {
@@ -330,26 +438,162 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
     S3 = fma(b, m19, S3);
     G3z = fma(b, m9, G3z);
   }
-  { const T t = F1 * S0;
-    ax = fma(Rx, t, fma(F0, G0x, ax));
-    ay = fma(Ry, t, fma(F0, G0y, ay));
-    az = fma(Rz, t, fma(F0, G0z, az));
+  T t = F1 * S0;
+  t = fma(F2, S1, t);
+  t = fma(F3, S2, t);
+  t = fma(F4, S3, t);
+  ax = fma(Rx, t, fma(F1, G1x, fma(F2, G2x, fma(F3, G3x, ax))));
+  ay = fma(Ry, t, fma(F1, G1y, fma(F2, G2y, fma(F3, G3y, ay))));
+  az = fma(Rz, t, fma(F1, G1z, fma(F2, G2z, fma(F3, G3z, az))));
+}
+
+__device__ __forceinline__ void m2p2_p3(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
+                                       float2 eps2, float2& ax, float2& ay, float2& az) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 F4 = __fmul2_rn(F3, __fmul2_rn(make_float2(-7.0f, -7.0f), is));
+  const float2 Rx_2 = __fmul2_rn(Rx, make_float2(0.5f, 0.5f));
+  const float2 Rx_3 = __fmul2_rn(Rx, make_float2(0.333333333f, 0.333333333f));
+  const float2 Ry_2 = __fmul2_rn(Ry, make_float2(0.5f, 0.5f));
+  const float2 Ry_3 = __fmul2_rn(Ry, make_float2(0.333333333f, 0.333333333f));
+  const float2 Rz_2 = __fmul2_rn(Rz, make_float2(0.5f, 0.5f));
+  const float2 Rz_3 = __fmul2_rn(Rz, make_float2(0.333333333f, 0.333333333f));
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  const float2 m4 = __fmul2_rn(m1, Rx_2);
+  const float2 m5 = __fmul2_rn(m2, Rx);
+  const float2 m6 = __fmul2_rn(m3, Rx);
+  const float2 m7 = __fmul2_rn(m2, Ry_2);
+  const float2 m8 = __fmul2_rn(m3, Ry);
+  const float2 m9 = __fmul2_rn(m3, Rz_2);
+  const float2 m10 = __fmul2_rn(m4, Rx_3);
+  const float2 m11 = __fmul2_rn(m5, Rx_2);
+  const float2 m12 = __fmul2_rn(m6, Rx_2);
+  const float2 m13 = __fmul2_rn(m7, Rx);
+  const float2 m14 = __fmul2_rn(m8, Rx);
+  const float2 m15 = __fmul2_rn(m9, Rx);
+  const float2 m16 = __fmul2_rn(m7, Ry_3);
+  const float2 m17 = __fmul2_rn(m8, Ry_2);
+  const float2 m18 = __fmul2_rn(m9, Ry);
+  const float2 m19 = __fmul2_rn(m9, Rz_3);
+  float2 S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z, S3, G3x, G3y, G3z;
+  { const float2 b = B[0];
+    S0 = b;
   }
-  { const T t = F2 * S1;
-    ax = fma(Rx, t, fma(F1, G1x, ax));
-    ay = fma(Ry, t, fma(F1, G1y, ay));
-    az = fma(Rz, t, fma(F1, G1z, az));
+  { const float2 b = B[1];
+    S1 = b;
   }
-  { const T t = F3 * S2;
-    ax = fma(Rx, t, fma(F2, G2x, ax));
-    ay = fma(Ry, t, fma(F2, G2y, ay));
-    az = fma(Rz, t, fma(F2, G2z, az));
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m1, S1);
+    G1x = b;
   }
-  { const T t = F4 * S3;
-    ax = fma(Rx, t, fma(F3, G3x, ax));
-    ay = fma(Ry, t, fma(F3, G3y, ay));
-    az = fma(Rz, t, fma(F3, G3z, az));
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
   }
+  { const float2 b = B[4];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  { const float2 b = B[5];
+    S2 = __fmul2_rn(b, m1);
+    G2x = b;
+  }
+  { const float2 b = B[6];
+    S2 = __ffma2_rn(b, m2, S2);
+    G2y = b;
+  }
+  { const float2 b = B[7];
+    S2 = __ffma2_rn(b, m3, S2);
+    G2z = b;
+  }
+  { const float2 b = B[8];
+    S2 = __ffma2_rn(b, m4, S2);
+    G2x = __ffma2_rn(b, m1, G2x);
+  }
+  { const float2 b = B[9];
+    S2 = __ffma2_rn(b, m5, S2);
+    G2x = __ffma2_rn(b, m2, G2x);
+    G2y = __ffma2_rn(b, m1, G2y);
+  }
+  { const float2 b = B[10];
+    S2 = __ffma2_rn(b, m6, S2);
+    G2x = __ffma2_rn(b, m3, G2x);
+    G2z = __ffma2_rn(b, m1, G2z);
+  }
+  { const float2 b = B[11];
+    S2 = __ffma2_rn(b, m7, S2);
+    G2y = __ffma2_rn(b, m2, G2y);
+  }
+  { const float2 b = B[12];
+    S2 = __ffma2_rn(b, m8, S2);
+    G2y = __ffma2_rn(b, m3, G2y);
+    G2z = __ffma2_rn(b, m2, G2z);
+  }
+  { const float2 b = B[13];
+    S2 = __ffma2_rn(b, m9, S2);
+    G2z = __ffma2_rn(b, m3, G2z);
+  }
+  { const float2 b = B[14];
+    S3 = __fmul2_rn(b, m10);
+    G3x = __fmul2_rn(b, m4);
+  }
+  { const float2 b = B[15];
+    S3 = __ffma2_rn(b, m11, S3);
+    G3x = __ffma2_rn(b, m5, G3x);
+    G3y = __fmul2_rn(b, m4);
+  }
+  { const float2 b = B[16];
+    S3 = __ffma2_rn(b, m12, S3);
+    G3x = __ffma2_rn(b, m6, G3x);
+    G3z = __fmul2_rn(b, m4);
+  }
+  { const float2 b = B[17];
+    S3 = __ffma2_rn(b, m13, S3);
+    G3x = __ffma2_rn(b, m7, G3x);
+    G3y = __ffma2_rn(b, m5, G3y);
+  }
+  { const float2 b = B[18];
+    S3 = __ffma2_rn(b, m14, S3);
+    G3x = __ffma2_rn(b, m8, G3x);
+    G3y = __ffma2_rn(b, m6, G3y);
+    G3z = __ffma2_rn(b, m5, G3z);
+  }
+  { const float2 b = B[19];
+    S3 = __ffma2_rn(b, m15, S3);
+    G3x = __ffma2_rn(b, m9, G3x);
+    G3z = __ffma2_rn(b, m6, G3z);
+  }
+  { const float2 b = B[20];
+    S3 = __ffma2_rn(b, m16, S3);
+    G3y = __ffma2_rn(b, m7, G3y);
+  }
+  { const float2 b = B[21];
+    S3 = __ffma2_rn(b, m17, S3);
+    G3y = __ffma2_rn(b, m8, G3y);
+    G3z = __ffma2_rn(b, m7, G3z);
+  }
+  { const float2 b = B[22];
+    S3 = __ffma2_rn(b, m18, S3);
+    G3y = __ffma2_rn(b, m9, G3y);
+    G3z = __ffma2_rn(b, m8, G3z);
+  }
+  { const float2 b = B[23];
+    S3 = __ffma2_rn(b, m19, S3);
+    G3z = __ffma2_rn(b, m9, G3z);
+  }
+  float2 t = __fmul2_rn(F1, S0);
+  t = __ffma2_rn(F2, S1, t);
+  t = __ffma2_rn(F3, S2, t);
+  t = __ffma2_rn(F4, S3, t);
+  ax = __ffma2_rn(Rx, t, __ffma2_rn(F1, G1x, __ffma2_rn(F2, G2x, __ffma2_rn(F3, G3x, ax))));
+  ay = __ffma2_rn(Ry, t, __ffma2_rn(F1, G1y, __ffma2_rn(F2, G2y, __ffma2_rn(F3, G3y, ay))));
+  az = __ffma2_rn(Rz, t, __ffma2_rn(F1, G1z, __ffma2_rn(F2, G2z, __ffma2_rn(F3, G3z, az))));
 }
 
 __device__ __forceinline__ void reduce_moments_p3(const double* __restrict__ M, double* __restrict__ B) {
@@ -649,31 +893,288 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
     S4 = fma(b, m34, S4);
     G4z = fma(b, m19, G4z);
   }
-  { const T t = F1 * S0;
-    ax = fma(Rx, t, fma(F0, G0x, ax));
-    ay = fma(Ry, t, fma(F0, G0y, ay));
-    az = fma(Rz, t, fma(F0, G0z, az));
+  T t = F1 * S0;
+  t = fma(F2, S1, t);
+  t = fma(F3, S2, t);
+  t = fma(F4, S3, t);
+  t = fma(F5, S4, t);
+  ax = fma(Rx, t, fma(F1, G1x, fma(F2, G2x, fma(F3, G3x, fma(F4, G4x, ax)))));
+  ay = fma(Ry, t, fma(F1, G1y, fma(F2, G2y, fma(F3, G3y, fma(F4, G4y, ay)))));
+  az = fma(Rz, t, fma(F1, G1z, fma(F2, G2z, fma(F3, G3z, fma(F4, G4z, az)))));
+}
+
+__device__ __forceinline__ void m2p2_p4(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
+                                       float2 eps2, float2& ax, float2& ay, float2& az) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 F4 = __fmul2_rn(F3, __fmul2_rn(make_float2(-7.0f, -7.0f), is));
+  const float2 F5 = __fmul2_rn(F4, __fmul2_rn(make_float2(-9.0f, -9.0f), is));
+  const float2 Rx_2 = __fmul2_rn(Rx, make_float2(0.5f, 0.5f));
+  const float2 Rx_3 = __fmul2_rn(Rx, make_float2(0.333333333f, 0.333333333f));
+  const float2 Rx_4 = __fmul2_rn(Rx, make_float2(0.25f, 0.25f));
+  const float2 Ry_2 = __fmul2_rn(Ry, make_float2(0.5f, 0.5f));
+  const float2 Ry_3 = __fmul2_rn(Ry, make_float2(0.333333333f, 0.333333333f));
+  const float2 Ry_4 = __fmul2_rn(Ry, make_float2(0.25f, 0.25f));
+  const float2 Rz_2 = __fmul2_rn(Rz, make_float2(0.5f, 0.5f));
+  const float2 Rz_3 = __fmul2_rn(Rz, make_float2(0.333333333f, 0.333333333f));
+  const float2 Rz_4 = __fmul2_rn(Rz, make_float2(0.25f, 0.25f));
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  const float2 m4 = __fmul2_rn(m1, Rx_2);
+  const float2 m5 = __fmul2_rn(m2, Rx);
+  const float2 m6 = __fmul2_rn(m3, Rx);
+  const float2 m7 = __fmul2_rn(m2, Ry_2);
+  const float2 m8 = __fmul2_rn(m3, Ry);
+  const float2 m9 = __fmul2_rn(m3, Rz_2);
+  const float2 m10 = __fmul2_rn(m4, Rx_3);
+  const float2 m11 = __fmul2_rn(m5, Rx_2);
+  const float2 m12 = __fmul2_rn(m6, Rx_2);
+  const float2 m13 = __fmul2_rn(m7, Rx);
+  const float2 m14 = __fmul2_rn(m8, Rx);
+  const float2 m15 = __fmul2_rn(m9, Rx);
+  const float2 m16 = __fmul2_rn(m7, Ry_3);
+  const float2 m17 = __fmul2_rn(m8, Ry_2);
+  const float2 m18 = __fmul2_rn(m9, Ry);
+  const float2 m19 = __fmul2_rn(m9, Rz_3);
+  const float2 m20 = __fmul2_rn(m10, Rx_4);
+  const float2 m21 = __fmul2_rn(m11, Rx_3);
+  const float2 m22 = __fmul2_rn(m12, Rx_3);
+  const float2 m23 = __fmul2_rn(m13, Rx_2);
+  const float2 m24 = __fmul2_rn(m14, Rx_2);
+  const float2 m25 = __fmul2_rn(m15, Rx_2);
+  const float2 m26 = __fmul2_rn(m16, Rx);
+  const float2 m27 = __fmul2_rn(m17, Rx);
+  const float2 m28 = __fmul2_rn(m18, Rx);
+  const float2 m29 = __fmul2_rn(m19, Rx);
+  const float2 m30 = __fmul2_rn(m16, Ry_4);
+  const float2 m31 = __fmul2_rn(m17, Ry_3);
+  const float2 m32 = __fmul2_rn(m18, Ry_2);
+  const float2 m33 = __fmul2_rn(m19, Ry);
+  const float2 m34 = __fmul2_rn(m19, Rz_4);
+  float2 S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z, S3, G3x, G3y, G3z, S4, G4x, G4y, G4z;
+  { const float2 b = B[0];
+    S0 = b;
   }
-  { const T t = F2 * S1;
-    ax = fma(Rx, t, fma(F1, G1x, ax));
-    ay = fma(Ry, t, fma(F1, G1y, ay));
-    az = fma(Rz, t, fma(F1, G1z, az));
+  { const float2 b = B[1];
+    S1 = b;
   }
-  { const T t = F3 * S2;
-    ax = fma(Rx, t, fma(F2, G2x, ax));
-    ay = fma(Ry, t, fma(F2, G2y, ay));
-    az = fma(Rz, t, fma(F2, G2z, az));
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m1, S1);
+    G1x = b;
   }
-  { const T t = F4 * S3;
-    ax = fma(Rx, t, fma(F3, G3x, ax));
-    ay = fma(Ry, t, fma(F3, G3y, ay));
-    az = fma(Rz, t, fma(F3, G3z, az));
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
   }
-  { const T t = F5 * S4;
-    ax = fma(Rx, t, fma(F4, G4x, ax));
-    ay = fma(Ry, t, fma(F4, G4y, ay));
-    az = fma(Rz, t, fma(F4, G4z, az));
+  { const float2 b = B[4];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
   }
+  { const float2 b = B[5];
+    S2 = b;
+  }
+  { const float2 b = B[6];
+    S2 = __ffma2_rn(b, m1, S2);
+    G2x = b;
+  }
+  { const float2 b = B[7];
+    S2 = __ffma2_rn(b, m2, S2);
+    G2y = b;
+  }
+  { const float2 b = B[8];
+    S2 = __ffma2_rn(b, m3, S2);
+    G2z = b;
+  }
+  { const float2 b = B[9];
+    S2 = __ffma2_rn(b, m4, S2);
+    G2x = __ffma2_rn(b, m1, G2x);
+  }
+  { const float2 b = B[10];
+    S2 = __ffma2_rn(b, m5, S2);
+    G2x = __ffma2_rn(b, m2, G2x);
+    G2y = __ffma2_rn(b, m1, G2y);
+  }
+  { const float2 b = B[11];
+    S2 = __ffma2_rn(b, m6, S2);
+    G2x = __ffma2_rn(b, m3, G2x);
+    G2z = __ffma2_rn(b, m1, G2z);
+  }
+  { const float2 b = B[12];
+    S2 = __ffma2_rn(b, m7, S2);
+    G2y = __ffma2_rn(b, m2, G2y);
+  }
+  { const float2 b = B[13];
+    S2 = __ffma2_rn(b, m8, S2);
+    G2y = __ffma2_rn(b, m3, G2y);
+    G2z = __ffma2_rn(b, m2, G2z);
+  }
+  { const float2 b = B[14];
+    S2 = __ffma2_rn(b, m9, S2);
+    G2z = __ffma2_rn(b, m3, G2z);
+  }
+  { const float2 b = B[15];
+    S3 = __fmul2_rn(b, m4);
+    G3x = __fmul2_rn(b, m1);
+  }
+  { const float2 b = B[16];
+    S3 = __ffma2_rn(b, m5, S3);
+    G3x = __ffma2_rn(b, m2, G3x);
+    G3y = __fmul2_rn(b, m1);
+  }
+  { const float2 b = B[17];
+    S3 = __ffma2_rn(b, m6, S3);
+    G3x = __ffma2_rn(b, m3, G3x);
+    G3z = __fmul2_rn(b, m1);
+  }
+  { const float2 b = B[18];
+    S3 = __ffma2_rn(b, m7, S3);
+    G3y = __ffma2_rn(b, m2, G3y);
+  }
+  { const float2 b = B[19];
+    S3 = __ffma2_rn(b, m8, S3);
+    G3y = __ffma2_rn(b, m3, G3y);
+    G3z = __ffma2_rn(b, m2, G3z);
+  }
+  { const float2 b = B[20];
+    S3 = __ffma2_rn(b, m9, S3);
+    G3z = __ffma2_rn(b, m3, G3z);
+  }
+  { const float2 b = B[21];
+    S3 = __ffma2_rn(b, m10, S3);
+    G3x = __ffma2_rn(b, m4, G3x);
+  }
+  { const float2 b = B[22];
+    S3 = __ffma2_rn(b, m11, S3);
+    G3x = __ffma2_rn(b, m5, G3x);
+    G3y = __ffma2_rn(b, m4, G3y);
+  }
+  { const float2 b = B[23];
+    S3 = __ffma2_rn(b, m12, S3);
+    G3x = __ffma2_rn(b, m6, G3x);
+    G3z = __ffma2_rn(b, m4, G3z);
+  }
+  { const float2 b = B[24];
+    S3 = __ffma2_rn(b, m13, S3);
+    G3x = __ffma2_rn(b, m7, G3x);
+    G3y = __ffma2_rn(b, m5, G3y);
+  }
+  { const float2 b = B[25];
+    S3 = __ffma2_rn(b, m14, S3);
+    G3x = __ffma2_rn(b, m8, G3x);
+    G3y = __ffma2_rn(b, m6, G3y);
+    G3z = __ffma2_rn(b, m5, G3z);
+  }
+  { const float2 b = B[26];
+    S3 = __ffma2_rn(b, m15, S3);
+    G3x = __ffma2_rn(b, m9, G3x);
+    G3z = __ffma2_rn(b, m6, G3z);
+  }
+  { const float2 b = B[27];
+    S3 = __ffma2_rn(b, m16, S3);
+    G3y = __ffma2_rn(b, m7, G3y);
+  }
+  { const float2 b = B[28];
+    S3 = __ffma2_rn(b, m17, S3);
+    G3y = __ffma2_rn(b, m8, G3y);
+    G3z = __ffma2_rn(b, m7, G3z);
+  }
+  { const float2 b = B[29];
+    S3 = __ffma2_rn(b, m18, S3);
+    G3y = __ffma2_rn(b, m9, G3y);
+    G3z = __ffma2_rn(b, m8, G3z);
+  }
+  { const float2 b = B[30];
+    S3 = __ffma2_rn(b, m19, S3);
+    G3z = __ffma2_rn(b, m9, G3z);
+  }
+  { const float2 b = B[31];
+    S4 = __fmul2_rn(b, m20);
+    G4x = __fmul2_rn(b, m10);
+  }
+  { const float2 b = B[32];
+    S4 = __ffma2_rn(b, m21, S4);
+    G4x = __ffma2_rn(b, m11, G4x);
+    G4y = __fmul2_rn(b, m10);
+  }
+  { const float2 b = B[33];
+    S4 = __ffma2_rn(b, m22, S4);
+    G4x = __ffma2_rn(b, m12, G4x);
+    G4z = __fmul2_rn(b, m10);
+  }
+  { const float2 b = B[34];
+    S4 = __ffma2_rn(b, m23, S4);
+    G4x = __ffma2_rn(b, m13, G4x);
+    G4y = __ffma2_rn(b, m11, G4y);
+  }
+  { const float2 b = B[35];
+    S4 = __ffma2_rn(b, m24, S4);
+    G4x = __ffma2_rn(b, m14, G4x);
+    G4y = __ffma2_rn(b, m12, G4y);
+    G4z = __ffma2_rn(b, m11, G4z);
+  }
+  { const float2 b = B[36];
+    S4 = __ffma2_rn(b, m25, S4);
+    G4x = __ffma2_rn(b, m15, G4x);
+    G4z = __ffma2_rn(b, m12, G4z);
+  }
+  { const float2 b = B[37];
+    S4 = __ffma2_rn(b, m26, S4);
+    G4x = __ffma2_rn(b, m16, G4x);
+    G4y = __ffma2_rn(b, m13, G4y);
+  }
+  { const float2 b = B[38];
+    S4 = __ffma2_rn(b, m27, S4);
+    G4x = __ffma2_rn(b, m17, G4x);
+    G4y = __ffma2_rn(b, m14, G4y);
+    G4z = __ffma2_rn(b, m13, G4z);
+  }
+  { const float2 b = B[39];
+    S4 = __ffma2_rn(b, m28, S4);
+    G4x = __ffma2_rn(b, m18, G4x);
+    G4y = __ffma2_rn(b, m15, G4y);
+    G4z = __ffma2_rn(b, m14, G4z);
+  }
+  { const float2 b = B[40];
+    S4 = __ffma2_rn(b, m29, S4);
+    G4x = __ffma2_rn(b, m19, G4x);
+    G4z = __ffma2_rn(b, m15, G4z);
+  }
+  { const float2 b = B[41];
+    S4 = __ffma2_rn(b, m30, S4);
+    G4y = __ffma2_rn(b, m16, G4y);
+  }
+  { const float2 b = B[42];
+    S4 = __ffma2_rn(b, m31, S4);
+    G4y = __ffma2_rn(b, m17, G4y);
+    G4z = __ffma2_rn(b, m16, G4z);
+  }
+  { const float2 b = B[43];
+    S4 = __ffma2_rn(b, m32, S4);
+    G4y = __ffma2_rn(b, m18, G4y);
+    G4z = __ffma2_rn(b, m17, G4z);
+  }
+  { const float2 b = B[44];
+    S4 = __ffma2_rn(b, m33, S4);
+    G4y = __ffma2_rn(b, m19, G4y);
+    G4z = __ffma2_rn(b, m18, G4z);
+  }
+  { const float2 b = B[45];
+    S4 = __ffma2_rn(b, m34, S4);
+    G4z = __ffma2_rn(b, m19, G4z);
+  }
+  float2 t = __fmul2_rn(F1, S0);
+  t = __ffma2_rn(F2, S1, t);
+  t = __ffma2_rn(F3, S2, t);
+  t = __ffma2_rn(F4, S3, t);
+  t = __ffma2_rn(F5, S4, t);
+  ax = __ffma2_rn(Rx, t, __ffma2_rn(F1, G1x, __ffma2_rn(F2, G2x, __ffma2_rn(F3, G3x, __ffma2_rn(F4, G4x, ax)))));
+  ay = __ffma2_rn(Ry, t, __ffma2_rn(F1, G1y, __ffma2_rn(F2, G2y, __ffma2_rn(F3, G3y, __ffma2_rn(F4, G4y, ay)))));
+  az = __ffma2_rn(Rz, t, __ffma2_rn(F1, G1z, __ffma2_rn(F2, G2z, __ffma2_rn(F3, G3z, __ffma2_rn(F4, G4z, az)))));
 }
 
 __device__ __forceinline__ void reduce_moments_p4(const double* __restrict__ M, double* __restrict__ B) {

@@ -36,6 +36,10 @@ template <int P> struct WOrd;
     static __device__ __forceinline__ void m2p(const T* B, T x, T y, T z, T e2, T& ax, T& ay, T& az) { \
       m2p_p##P<T>(B, x, y, z, e2, ax, ay, az);                                                        \
     }                                                                                                 \
+    static __device__ __forceinline__ void m2p2(const float2* B, float2 x, float2 y, float2 z, float2 e2, \
+                                                float2& ax, float2& ay, float2& az) {                 \
+      m2p2_p##P(B, x, y, z, e2, ax, ay, az);                                                          \
+    }                                                                                                 \
   };
 NB_WORD(0)
 NB_WORD(1)
@@ -62,7 +66,14 @@ struct WalkArgs {
 
 constexpr double kScale = 1.0 / 8388608.0;  // 2^-23
 
-template <typename T, int P, int WARPS, int MINB>
+// PK selects how a chunk of queued M2P cells is evaluated: every lane is a
+// sink and loops over the chunk's cells, whose coefficients are staged in
+// shared memory and read as broadcasts, one cell at a time (PK = false) or
+// two at a time in packed FP32 pairs (PK = true, FP32 only: the coefficients
+// of cells 2q and 2q + 1 are staged interleaved and each pair instruction
+// advances both expansions, halving the instructions issued per M2P; every
+// cell's result is bitwise the scalar one).  The autotuner picks.
+template <typename T, int P, int WARPS, int MINB, bool PK>
 __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   using V4 = typename Vec4<T>::type;
   constexpr int NBS = WOrd<P>::NBS;
@@ -110,6 +121,43 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     int qn = 0;  // queued M2P cells
     // evaluate the first nmp queued M2P cells for every sink of the group
     auto m2p_chunk = [&](int nmp) {
+      if constexpr (PK) {
+        // stage pairs: cell 2q in .x, cell 2q + 1 in .y (zeros past nmp)
+        const int npair = (nmp + 1) >> 1;
+        constexpr int C4 = NBS / 4;
+        const float4* gsrc = reinterpret_cast<const float4*>(w.coef);
+        float4* sdst = reinterpret_cast<float4*>(&s_coef[wid][0]);
+        for (int t = lane; t < npair * C4; t += 32) {
+          const int q = t / C4, r = t - q * C4;
+          const float4 c0 = gsrc[(int64_t)s_midx[wid][2 * q] * C4 + r];
+          const float4 c1 = 2 * q + 1 < nmp ? gsrc[(int64_t)s_midx[wid][2 * q + 1] * C4 + r]
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+          sdst[2 * (q * C4 + r)] = make_float4(c0.x, c1.x, c0.y, c1.y);
+          sdst[2 * (q * C4 + r) + 1] = make_float4(c0.z, c1.z, c0.w, c1.w);
+        }
+        __syncwarp();
+        if (act) {
+          float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+          const float2 x2 = make_float2(xi, xi), y2 = make_float2(yi, yi), z2 = make_float2(zi, zi);
+          const float2* cf = reinterpret_cast<const float2*>(&s_coef[wid][0]);
+          for (int q = 0; q < npair; q++) {
+            const float4 m0 = s_moff[wid][2 * q];
+            const bool two = 2 * q + 1 < nmp;
+            const float4 m1 = two ? s_moff[wid][2 * q + 1] : make_float4(0.f, 0.f, 0.f, 1.f);
+            const float2 sc = make_float2(m0.w, m1.w);
+            const float2 e2 = make_float2(s_meps[wid][2 * q], two ? s_meps[wid][2 * q + 1] : 1.f);
+            WOrd<P>::m2p2(&cf[q * NBS], __ffma2_rn(x2, sc, make_float2(m0.x, m1.x)),
+                          __ffma2_rn(y2, sc, make_float2(m0.y, m1.y)), __ffma2_rn(z2, sc, make_float2(m0.z, m1.z)),
+                          e2, px, py, pz);
+          }
+          kadd(ax, cx, px.x + px.y);
+          kadd(ay, cy, py.x + py.y);
+          kadd(az, cz, pz.x + pz.y);
+        }
+        n_m2p += nmp;
+        __syncwarp();
+        return;
+      }
       const int4* gsrc = reinterpret_cast<const int4*>(w.coef);
       int4* sdst = reinterpret_cast<int4*>(&s_coef[wid][0]);
       for (int t = lane; t < nmp * C16; t += 32) {
@@ -278,31 +326,40 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   }
 }
 
-template <typename T, int P, int WARPS, int MINB>
+template <typename T, int P, int WARPS, int MINB, bool PK>
 cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
   int occ = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB>,
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB, PK>,
                                                                  WARPS * 32, 0);
   if (e) return e;
   int grid = nsm * (occ > 0 ? occ : 1);
   if (grid > max_blocks) grid = max_blocks;
-  walk_kernel<T, P, WARPS, MINB><<<grid, WARPS * 32, 0, s>>>(a);
+  walk_kernel<T, P, WARPS, MINB, PK><<<grid, WARPS * 32, 0, s>>>(a);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
-// launch variants (warps per block, minimum resident blocks per SM); the
-// register budget per thread follows from them
+// launch variants (warps per block, minimum resident blocks per SM, M2P
+// form); the register budget per thread follows from the first two.  The
+// stack is sized for 8 warps per block.
 template <typename T, int P>
 cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
-  if (sizeof(T) == 8) return launch_walk<T, P, 4, 1>(a, nsm, max_blocks, s);
-  if (v == 0) return launch_walk<T, P, 8, 2>(a, nsm, max_blocks, s);
-  return launch_walk<T, P, 8, 3>(a, nsm, max_blocks, s);
+  if constexpr (sizeof(T) == 8) {
+    return launch_walk<T, P, 4, 1, false>(a, nsm, max_blocks, s);
+  } else {
+    switch (v) {
+      case 0: return launch_walk<T, P, 8, 2, false>(a, nsm, max_blocks, s);
+      case 1: return launch_walk<T, P, 8, 3, false>(a, nsm, max_blocks, s);
+      case 2: return launch_walk<T, P, 8, 2, true>(a, nsm, max_blocks, s);
+      default: return launch_walk<T, P, 4, 5, true>(a, nsm, max_blocks, s);
+    }
+  }
 }
-constexpr int kVariants = 2;
+constexpr int kVariants = 4;
 
 struct TuneEntry {
   int device, order, fp64, variant;
+  float ms[kVariants];  // the tuning run's time of each variant
 };
 std::mutex g_tune_mutex;
 std::vector<TuneEntry> g_tune;
@@ -311,10 +368,11 @@ std::vector<TuneEntry> g_tune;
 // variant on the real data and keeps the fastest; results do not depend on
 // the variant (each group's walk is the same computation).
 template <typename T, int P>
-cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
+cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
   const int fp = sizeof(T) == 8;
+  if (forced >= 0) return launch_variant<T, P>(fp ? 0 : forced, a, nsm, max_blocks, s);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const auto& t : g_tune)
@@ -322,7 +380,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t
   }
   if (fp) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune.push_back({dev, P, fp, 0});
+    g_tune.push_back({dev, P, fp, 0, {}});
     return launch_variant<T, P>(0, a, nsm, max_blocks, s);
   }
   cudaEvent_t e0, e1;
@@ -331,6 +389,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t
   if ((e = cudaEventCreate(&e1))) return e;
   float best = 1e30f;
   int bv = 0;
+  TuneEntry te{dev, P, fp, 0, {}};
   for (int v = 0; v < kVariants; v++) {
     if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
     if ((e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s))) return e;
@@ -340,6 +399,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t
     if ((e = cudaEventSynchronize(e1))) return e;
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
+    te.ms[v] = ms;
     if (ms < best) {
       best = ms;
       bv = v;
@@ -347,9 +407,10 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  te.variant = bv;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune.push_back({dev, P, fp, bv});
+    g_tune.push_back(te);
   }
   if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
   if ((e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s))) return e;
@@ -361,20 +422,27 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t
 // warps per block of the walk for a precision (stack slots are sized for the largest)
 int nb_walk_warps(bool fp64) { return fp64 ? 4 : 8; }
 
-// the variant the autotuner chose for (precision, order) on this device, or -1
-int nb_walk_variant(bool fp64, int order) {
+// the variant the autotuner chose for (precision, order) on this device, or
+// -1; ms (nullable, kWalkVariantsMax entries) receives each variant's time
+// in the tuning run (0 for variants not timed)
+int nb_walk_variant(bool fp64, int order, double* ms) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   for (const auto& t : g_tune)
-    if (t.device == dev && t.order == order && t.fp64 == (fp64 ? 1 : 0)) return t.variant;
+    if (t.device == dev && t.order == order && t.fp64 == (fp64 ? 1 : 0)) {
+      if (ms)
+        for (int v = 0; v < kVariants; v++) ms[v] = t.ms[v];
+      return t.variant;
+    }
   return -1;
 }
 
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src,
                     const void* eps2, const long long* thr, int n_direct, int le, int* stack,
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
-                    unsigned long long* counters, unsigned* status, int nsm, cudaStream_t s) {
+                    unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
+                    cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
 #define NB_WALK(TT, P)                                                             \
@@ -393,7 +461,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.acc = (TT*)acc;                                                              \
     a.counters = counters;                                                         \
     a.status = status;                                                             \
-    return run_walk<TT, P>(a, nsm, max_blocks, s);                                 \
+    return run_walk<TT, P>(a, nsm, max_blocks, forced_variant, s);                 \
   }
   if (fp64) {
     switch (order) {

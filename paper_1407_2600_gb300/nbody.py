@@ -26,6 +26,11 @@ NBODY_ERANGE = -7
 NBODY_MIXED = 0
 NBODY_FP64 = 1
 NBODY_FLAG_ASYNC = 1
+
+
+def NBODY_FLAG_WALK_VARIANT(v: int) -> int:
+    """flags bits selecting walk launch variant v instead of the autotuned one"""
+    return (v + 1) << 8
 EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_level": 5,
           "moments": 6, "groups": 7}
 
@@ -58,10 +63,13 @@ class Timing(C.Structure):
                 ("p2p", C.c_double), ("m2p", C.c_double), ("m2l", C.c_double),
                 ("ms_sort", C.c_double), ("ms_build", C.c_double), ("ms_upward", C.c_double),
                 ("ms_walk", C.c_double), ("ms_periodic", C.c_double),
-                ("adjoint_steps", C.c_int64), ("adjoint_reused", C.c_int64)]
+                ("adjoint_steps", C.c_int64), ("adjoint_reused", C.c_int64),
+                ("walk_variant", C.c_int64), ("walk_tune_ms", C.c_double * 8)]
 
     def asdict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["walk_tune_ms"] = list(self.walk_tune_ms)
+        return d
 
 
 class NbodyError(RuntimeError):

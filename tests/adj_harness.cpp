@@ -9,7 +9,19 @@
 #define __forceinline__ inline
 #define __restrict__
 static inline double nbody_rsqrt(double x) { return 1.0 / std::sqrt(x); }
+static inline float nbody_rsqrt(float x) { return 1.0f / std::sqrt(x); }
 using std::fma;
+// host stand-ins for the packed FP32 pair operations (per component, round
+// to nearest, as the device instructions are specified)
+struct float2 {
+  float x, y;
+};
+static inline float2 make_float2(float a, float b) { return float2{a, b}; }
+static inline float2 __ffma2_rn(float2 a, float2 b, float2 c) {
+  return float2{std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y)};
+}
+static inline float2 __fmul2_rn(float2 a, float2 b) { return float2{a.x * b.x, a.y * b.y}; }
+static inline float2 __fadd2_rn(float2 a, float2 b) { return float2{a.x + b.x, a.y + b.y}; }
 #include "../paper_1407_2600_gb300/csrc/m2p_gen.cuh"
 #include "../paper_1407_2600_gb300/csrc/adj_gen.cuh"
 
@@ -48,6 +60,22 @@ template <int P> struct K;
     static void m2madj(const double* nup, double x, double y, double z, double* nuc) { m2m_adj_acc_p##P(nup, x, y, z, nuc); } \
   };
 KD(0) KD(1) KD(2) KD(3) KD(4)
+
+template <int P>
+void fwd_scalar(const float* B, float x, float y, float z, float e, float& ax, float& ay, float& az);
+template <int P> struct K2;
+#define K2D(P)                                                                                               \
+  template <> void fwd_scalar<P>(const float* B, float x, float y, float z, float e, float& ax, float& ay,    \
+                                 float& az) {                                                               \
+    m2p_p##P<float>(B, x, y, z, e, ax, ay, az);                                                             \
+  }                                                                                                          \
+  template <> struct K2<P> {                                                                                 \
+    static void fwd2(const float2* B, float2 x, float2 y, float2 z, float2 e, float2& ax, float2& ay,        \
+                     float2& az) {                                                                           \
+      m2p2_p##P(B, x, y, z, e, ax, ay, az);                                                                  \
+    }                                                                                                        \
+  };
+K2D(0) K2D(1) K2D(2) K2D(3) K2D(4)
 
 template <int P> void run_m2p() {
   const int NM = (P + 1) * (P + 2) * (P + 3) / 6;
@@ -173,7 +201,35 @@ template <int PE> void run_field() {
   check("m2l_adj", l, r, 1.0 + std::fabs(l), 1e-12);
 }
 
+// the packed two-cell M2P gives, per half, the scalar FP32 M2P bit for bit
+template <int P>
+void run_m2p2() {
+  constexpr int NB = K<P>::NB;
+  float B0[NB], B1[NB];
+  float2 B2[NB];
+  for (int t = 0; t < NB; t++) {
+    B0[t] = (float)U();
+    B1[t] = (float)U();
+    B2[t] = make_float2(B0[t], B1[t]);
+  }
+  const float x0 = (float)(2 * U()), y0 = (float)(2 * U()), z0 = (float)(2 * U());
+  const float x1 = (float)(2 * U()), y1 = (float)(2 * U()), z1 = (float)(2 * U());
+  const float e0 = 0.01f, e1 = 0.02f;
+  float ax0 = 0.25f, ay0 = -0.5f, az0 = 0.125f, ax1 = 0.25f, ay1 = -0.5f, az1 = 0.125f;
+  float2 ax = make_float2(ax0, ax1), ay = make_float2(ay0, ay1), az = make_float2(az0, az1);
+  fwd_scalar<P>(B0, x0, y0, z0, e0, ax0, ay0, az0);
+  fwd_scalar<P>(B1, x1, y1, z1, e1, ax1, ay1, az1);
+  K2<P>::fwd2(B2, make_float2(x0, x1), make_float2(y0, y1), make_float2(z0, z1), make_float2(e0, e1), ax, ay, az);
+  if (ax.x != ax0 || ay.x != ay0 || az.x != az0 || ax.y != ax1 || ay.y != ay1 || az.y != az1) {
+    std::printf("FAIL m2p2_p%d differs from m2p_p%d\n", P, P);
+    std::exit(1);
+  }
+}
+
 int main() {
+  for (int rep = 0; rep < 50; rep++) {
+    run_m2p2<0>(); run_m2p2<1>(); run_m2p2<2>(); run_m2p2<3>(); run_m2p2<4>();
+  }
   for (int rep = 0; rep < 20; rep++) {
     run_m2p<0>(); run_m2p<1>(); run_m2p<2>(); run_m2p<3>(); run_m2p<4>();
     run_field<1>(); run_field<2>(); run_field<3>(); run_field<4>(); run_field<5>();

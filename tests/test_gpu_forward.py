@@ -131,6 +131,28 @@ def test_forces_vs_oracle_tree(cuda, name, gen, theta, order):
     assert abs(st["p2p"] - (ost["p2p"] + len(x))) <= 1e-9 * ost["p2p"] + 0.5  # GPU counts the self pair
 
 
+@pytest.mark.parametrize("name,gen,theta,order", [CASES[0], CASES[2], CASES[4]])
+def test_every_walk_variant_vs_oracle_tree(cuda, name, gen, theta, order):
+    """Each launch variant of the walk (sink-major and cell-major M2P, forced
+    through the params flags) meets the oracle bar and counts the same
+    interactions."""
+    nb = _nb()
+    x, eps = gen()
+    nd = 2 if order <= 2 else 4
+    ref, ost = oracle.tree_forces(x, None, oracle.tree_params(eps, theta, order, n_direct=nd, ewald=4),
+                                  return_stats=True)
+    outs = []
+    for v in range(4):
+        a, st = _gpu_forces(x, cuda, eps=eps, theta=theta, order=order, n_direct=nd,
+                            flags=nb.NBODY_FLAG_WALK_VARIANT(v))
+        rel = _rel(a, ref)
+        assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (v, np.median(rel))
+        assert st["m2p"] == ost["m2p"], v
+        outs.append(a)
+    for a in outs[1:]:
+        assert np.percentile(_rel(a, outs[0]), 99) <= 2e-5
+
+
 def test_forces_fp64_mode(cuda):
     x, eps = ics.config_small(2)
     a, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=4, precision=1)
