@@ -2,6 +2,10 @@
 // Reverse-mode (adjoint) kernels of the M2P, M2M, P2M and image-field expansions.
 #pragma once
 
+__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {
+  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+}
+
 template <typename T>
 __device__ __forceinline__ void m2p_adj_self_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
                                           T lx, T ly, T lz, T& ox, T& oy, T& oz) {
@@ -11,23 +15,45 @@ __device__ __forceinline__ void m2p_adj_self_p0(const T* __restrict__ B, T Rx, T
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
   const T m0 = T(1);
-  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0), H0x = T(0), H0y = T(0), H0z = T(0);
+  T S0;
   { const T b = B[0];
-    S0 = fma(b, m0, S0);
+    S0 = b;
   }
   const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));
-  T ax = T(0), ay = T(0), az = T(0);
+  T ax = ox, ay = oy, az = oz;
   { const T a1 = F1 * S0;  // F_{j+1} S_j
-    const T gl = fma(G0x, lx, fma(G0y, ly, G0z * lz));
-    const T c1 = fma(F2 * S0, rl, F1 * gl);  // R_k coefficient
-    const T c2 = F1 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G0x, fma(F0, H0x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G0y, fma(F0, H0y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G0z, fma(F0, H0z, az))));
+    const T c1 = F2 * S0 * rl;  // R_k coefficient
+    ax = fma(a1, lx, fma(Rx, c1, ax));
+    ay = fma(a1, ly, fma(Ry, c1, ay));
+    az = fma(a1, lz, fma(Rz, c1, az));
   }
-  ox += ax;
-  oy += ay;
-  oz += az;
+  ox = ax;
+  oy = ay;
+  oz = az;
+}
+
+__device__ __forceinline__ void m2p2_adj_self_p0(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz, float2 eps2, float2 lx, float2 ly, float2 lz, float2& ox, float2& oy, float2& oz) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = nbody_rsqrt2(s);
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 m0 = make_float2(1.0f, 1.0f);
+  float2 S0;
+  { const float2 b = B[0];
+    S0 = b;
+  }
+  const float2 rl = __ffma2_rn(Rx, lx, __ffma2_rn(Ry, ly, __fmul2_rn(Rz, lz)));
+  float2 ax = ox, ay = oy, az = oz;
+  { const float2 a1 = __fmul2_rn(F1, S0);
+    const float2 c1 = __fmul2_rn(__fmul2_rn(F2, S0), rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, ax));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, ay));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, az));
+  }
+  ox = ax;
+  oy = ay;
+  oz = az;
 }
 
 template <typename T>
@@ -68,45 +94,89 @@ __device__ __forceinline__ void m2p_adj_self_p1(const T* __restrict__ B, T Rx, T
   const T m1 = Rx;
   const T m2 = Ry;
   const T m3 = Rz;
-  T q0 = T(0);
-  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0), H0x = T(0), H0y = T(0), H0z = T(0);
-  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0), H1x = T(0), H1y = T(0), H1z = T(0);
+  T S0, S1, G1x, G1y, G1z;
   { const T b = B[0];
-    S0 = fma(b, m0, S0);
+    S0 = b;
   }
   { const T b = B[1];
-    S1 = fma(b, m1, S1);
-    G1x = fma(b, m0, G1x);
+    S1 = b * m1;
+    G1x = b;
   }
   { const T b = B[2];
     S1 = fma(b, m2, S1);
-    G1y = fma(b, m0, G1y);
+    G1y = b;
   }
   { const T b = B[3];
     S1 = fma(b, m3, S1);
-    G1z = fma(b, m0, G1z);
+    G1z = b;
   }
   const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));
-  T ax = T(0), ay = T(0), az = T(0);
+  T ax = ox, ay = oy, az = oz;
   { const T a1 = F1 * S0;  // F_{j+1} S_j
-    const T gl = fma(G0x, lx, fma(G0y, ly, G0z * lz));
-    const T c1 = fma(F2 * S0, rl, F1 * gl);  // R_k coefficient
-    const T c2 = F1 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G0x, fma(F0, H0x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G0y, fma(F0, H0y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G0z, fma(F0, H0z, az))));
+    const T c1 = F2 * S0 * rl;  // R_k coefficient
+    ax = fma(a1, lx, fma(Rx, c1, ax));
+    ay = fma(a1, ly, fma(Ry, c1, ay));
+    az = fma(a1, lz, fma(Rz, c1, az));
   }
   { const T a1 = F2 * S1;  // F_{j+1} S_j
     const T gl = fma(G1x, lx, fma(G1y, ly, G1z * lz));
     const T c1 = fma(F3 * S1, rl, F2 * gl);  // R_k coefficient
     const T c2 = F2 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, fma(F1, H1x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, fma(F1, H1y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, fma(F1, H1z, az))));
+    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, ax)));
+    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, ay)));
+    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, az)));
   }
-  ox += ax;
-  oy += ay;
-  oz += az;
+  ox = ax;
+  oy = ay;
+  oz = az;
+}
+
+__device__ __forceinline__ void m2p2_adj_self_p1(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz, float2 eps2, float2 lx, float2 ly, float2 lz, float2& ox, float2& oy, float2& oz) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = nbody_rsqrt2(s);
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 m0 = make_float2(1.0f, 1.0f);
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  float2 S0, S1, G1x, G1y, G1z;
+  { const float2 b = B[0];
+    S0 = b;
+  }
+  { const float2 b = B[1];
+    S1 = __fmul2_rn(b, m1);
+    G1x = b;
+  }
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
+  }
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  const float2 rl = __ffma2_rn(Rx, lx, __ffma2_rn(Ry, ly, __fmul2_rn(Rz, lz)));
+  float2 ax = ox, ay = oy, az = oz;
+  { const float2 a1 = __fmul2_rn(F1, S0);
+    const float2 c1 = __fmul2_rn(__fmul2_rn(F2, S0), rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, ax));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, ay));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, az));
+  }
+  { const float2 a1 = __fmul2_rn(F2, S1);
+    const float2 gl = __ffma2_rn(G1x, lx, __ffma2_rn(G1y, ly, __fmul2_rn(G1z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F3, S1), rl, __fmul2_rn(F2, gl));
+    const float2 c2 = __fmul2_rn(F2, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G1x, ax)));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G1y, ay)));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G1z, az)));
+  }
+  ox = ax;
+  oy = ay;
+  oz = az;
 }
 
 template <typename T>
@@ -173,52 +243,46 @@ __device__ __forceinline__ void m2p_adj_self_p2(const T* __restrict__ B, T Rx, T
   const T m7 = m2 * Ry_2;
   const T m8 = m3 * Ry;
   const T m9 = m3 * Rz_2;
-  T q0 = T(0);
-  T q1 = T(0);
-  T q2 = T(0);
-  T q3 = T(0);
-  q1 = fma(lx, m0, q1);
-  q2 = fma(ly, m0, q2);
-  q3 = fma(lz, m0, q3);
-  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0), H0x = T(0), H0y = T(0), H0z = T(0);
-  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0), H1x = T(0), H1y = T(0), H1z = T(0);
-  T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0), H2x = T(0), H2y = T(0), H2z = T(0);
+  T q1 = lx;
+  T q2 = ly;
+  T q3 = lz;
+  T S0, S1, G1x, G1y, G1z, S2, G2x, H2x, G2y, H2y, G2z, H2z;
   { const T b = B[0];
-    S0 = fma(b, m0, S0);
+    S0 = b;
   }
   { const T b = B[1];
-    S1 = fma(b, m0, S1);
+    S1 = b;
   }
   { const T b = B[2];
     S1 = fma(b, m1, S1);
-    G1x = fma(b, m0, G1x);
+    G1x = b;
   }
   { const T b = B[3];
     S1 = fma(b, m2, S1);
-    G1y = fma(b, m0, G1y);
+    G1y = b;
   }
   { const T b = B[4];
     S1 = fma(b, m3, S1);
-    G1z = fma(b, m0, G1z);
+    G1z = b;
   }
   { const T b = B[5];
-    S2 = fma(b, m4, S2);
-    G2x = fma(b, m1, G2x);
-    H2x = fma(b, q1, H2x);
+    S2 = b * m4;
+    G2x = b * m1;
+    H2x = b * q1;
   }
   { const T b = B[6];
     S2 = fma(b, m5, S2);
     G2x = fma(b, m2, G2x);
     H2x = fma(b, q2, H2x);
-    G2y = fma(b, m1, G2y);
-    H2y = fma(b, q1, H2y);
+    G2y = b * m1;
+    H2y = b * q1;
   }
   { const T b = B[7];
     S2 = fma(b, m6, S2);
     G2x = fma(b, m3, G2x);
     H2x = fma(b, q3, H2x);
-    G2z = fma(b, m1, G2z);
-    H2z = fma(b, q1, H2z);
+    G2z = b * m1;
+    H2z = b * q1;
   }
   { const T b = B[8];
     S2 = fma(b, m7, S2);
@@ -238,22 +302,20 @@ __device__ __forceinline__ void m2p_adj_self_p2(const T* __restrict__ B, T Rx, T
     H2z = fma(b, q3, H2z);
   }
   const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));
-  T ax = T(0), ay = T(0), az = T(0);
+  T ax = ox, ay = oy, az = oz;
   { const T a1 = F1 * S0;  // F_{j+1} S_j
-    const T gl = fma(G0x, lx, fma(G0y, ly, G0z * lz));
-    const T c1 = fma(F2 * S0, rl, F1 * gl);  // R_k coefficient
-    const T c2 = F1 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G0x, fma(F0, H0x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G0y, fma(F0, H0y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G0z, fma(F0, H0z, az))));
+    const T c1 = F2 * S0 * rl;  // R_k coefficient
+    ax = fma(a1, lx, fma(Rx, c1, ax));
+    ay = fma(a1, ly, fma(Ry, c1, ay));
+    az = fma(a1, lz, fma(Rz, c1, az));
   }
   { const T a1 = F2 * S1;  // F_{j+1} S_j
     const T gl = fma(G1x, lx, fma(G1y, ly, G1z * lz));
     const T c1 = fma(F3 * S1, rl, F2 * gl);  // R_k coefficient
     const T c2 = F2 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, fma(F1, H1x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, fma(F1, H1y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, fma(F1, H1z, az))));
+    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, ax)));
+    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, ay)));
+    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, az)));
   }
   { const T a1 = F3 * S2;  // F_{j+1} S_j
     const T gl = fma(G2x, lx, fma(G2y, ly, G2z * lz));
@@ -263,9 +325,117 @@ __device__ __forceinline__ void m2p_adj_self_p2(const T* __restrict__ B, T Rx, T
     ay = fma(a1, ly, fma(Ry, c1, fma(c2, G2y, fma(F2, H2y, ay))));
     az = fma(a1, lz, fma(Rz, c1, fma(c2, G2z, fma(F2, H2z, az))));
   }
-  ox += ax;
-  oy += ay;
-  oz += az;
+  ox = ax;
+  oy = ay;
+  oz = az;
+}
+
+__device__ __forceinline__ void m2p2_adj_self_p2(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz, float2 eps2, float2 lx, float2 ly, float2 lz, float2& ox, float2& oy, float2& oz) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = nbody_rsqrt2(s);
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 F4 = __fmul2_rn(F3, __fmul2_rn(make_float2(-7.0f, -7.0f), is));
+  const float2 Rx_2 = __fmul2_rn(Rx, make_float2(0.5f, 0.5f));
+  const float2 Ry_2 = __fmul2_rn(Ry, make_float2(0.5f, 0.5f));
+  const float2 Rz_2 = __fmul2_rn(Rz, make_float2(0.5f, 0.5f));
+  const float2 m0 = make_float2(1.0f, 1.0f);
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  const float2 m4 = __fmul2_rn(m1, Rx_2);
+  const float2 m5 = __fmul2_rn(m2, Rx);
+  const float2 m6 = __fmul2_rn(m3, Rx);
+  const float2 m7 = __fmul2_rn(m2, Ry_2);
+  const float2 m8 = __fmul2_rn(m3, Ry);
+  const float2 m9 = __fmul2_rn(m3, Rz_2);
+  float2 q1 = lx;
+  float2 q2 = ly;
+  float2 q3 = lz;
+  float2 S0, S1, G1x, G1y, G1z, S2, G2x, H2x, G2y, H2y, G2z, H2z;
+  { const float2 b = B[0];
+    S0 = b;
+  }
+  { const float2 b = B[1];
+    S1 = b;
+  }
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m1, S1);
+    G1x = b;
+  }
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
+  }
+  { const float2 b = B[4];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  { const float2 b = B[5];
+    S2 = __fmul2_rn(b, m4);
+    G2x = __fmul2_rn(b, m1);
+    H2x = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[6];
+    S2 = __ffma2_rn(b, m5, S2);
+    G2x = __ffma2_rn(b, m2, G2x);
+    H2x = __ffma2_rn(b, q2, H2x);
+    G2y = __fmul2_rn(b, m1);
+    H2y = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[7];
+    S2 = __ffma2_rn(b, m6, S2);
+    G2x = __ffma2_rn(b, m3, G2x);
+    H2x = __ffma2_rn(b, q3, H2x);
+    G2z = __fmul2_rn(b, m1);
+    H2z = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[8];
+    S2 = __ffma2_rn(b, m7, S2);
+    G2y = __ffma2_rn(b, m2, G2y);
+    H2y = __ffma2_rn(b, q2, H2y);
+  }
+  { const float2 b = B[9];
+    S2 = __ffma2_rn(b, m8, S2);
+    G2y = __ffma2_rn(b, m3, G2y);
+    H2y = __ffma2_rn(b, q3, H2y);
+    G2z = __ffma2_rn(b, m2, G2z);
+    H2z = __ffma2_rn(b, q2, H2z);
+  }
+  { const float2 b = B[10];
+    S2 = __ffma2_rn(b, m9, S2);
+    G2z = __ffma2_rn(b, m3, G2z);
+    H2z = __ffma2_rn(b, q3, H2z);
+  }
+  const float2 rl = __ffma2_rn(Rx, lx, __ffma2_rn(Ry, ly, __fmul2_rn(Rz, lz)));
+  float2 ax = ox, ay = oy, az = oz;
+  { const float2 a1 = __fmul2_rn(F1, S0);
+    const float2 c1 = __fmul2_rn(__fmul2_rn(F2, S0), rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, ax));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, ay));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, az));
+  }
+  { const float2 a1 = __fmul2_rn(F2, S1);
+    const float2 gl = __ffma2_rn(G1x, lx, __ffma2_rn(G1y, ly, __fmul2_rn(G1z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F3, S1), rl, __fmul2_rn(F2, gl));
+    const float2 c2 = __fmul2_rn(F2, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G1x, ax)));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G1y, ay)));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G1z, az)));
+  }
+  { const float2 a1 = __fmul2_rn(F3, S2);
+    const float2 gl = __ffma2_rn(G2x, lx, __ffma2_rn(G2y, ly, __fmul2_rn(G2z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F4, S2), rl, __fmul2_rn(F3, gl));
+    const float2 c2 = __fmul2_rn(F3, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G2x, __ffma2_rn(F2, H2x, ax))));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G2y, __ffma2_rn(F2, H2y, ay))));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G2z, __ffma2_rn(F2, H2z, az))));
+  }
+  ox = ax;
+  oy = ay;
+  oz = az;
 }
 
 template <typename T>
@@ -380,80 +550,67 @@ __device__ __forceinline__ void m2p_adj_self_p3(const T* __restrict__ B, T Rx, T
   const T m17 = m8 * Ry_2;
   const T m18 = m9 * Ry;
   const T m19 = m9 * Rz_3;
-  T q0 = T(0);
-  T q1 = T(0);
-  T q2 = T(0);
-  T q3 = T(0);
-  T q4 = T(0);
-  T q5 = T(0);
-  T q6 = T(0);
-  T q7 = T(0);
-  T q8 = T(0);
-  T q9 = T(0);
-  q1 = fma(lx, m0, q1);
-  q2 = fma(ly, m0, q2);
-  q3 = fma(lz, m0, q3);
-  q4 = fma(lx, m1, q4);
-  q5 = fma(lx, m2, q5);
+  T q1 = lx;
+  T q2 = ly;
+  T q3 = lz;
+  T q4 = lx * m1;
+  T q5 = lx * m2;
   q5 = fma(ly, m1, q5);
-  q6 = fma(lx, m3, q6);
+  T q6 = lx * m3;
   q6 = fma(lz, m1, q6);
-  q7 = fma(ly, m2, q7);
-  q8 = fma(ly, m3, q8);
+  T q7 = ly * m2;
+  T q8 = ly * m3;
   q8 = fma(lz, m2, q8);
-  q9 = fma(lz, m3, q9);
-  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0), H0x = T(0), H0y = T(0), H0z = T(0);
-  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0), H1x = T(0), H1y = T(0), H1z = T(0);
-  T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0), H2x = T(0), H2y = T(0), H2z = T(0);
-  T S3 = T(0), G3x = T(0), G3y = T(0), G3z = T(0), H3x = T(0), H3y = T(0), H3z = T(0);
+  T q9 = lz * m3;
+  T S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z, H2x, H2y, H2z, S3, G3x, H3x, G3y, H3y, G3z, H3z;
   { const T b = B[0];
-    S0 = fma(b, m0, S0);
+    S0 = b;
   }
   { const T b = B[1];
-    S1 = fma(b, m0, S1);
+    S1 = b;
   }
   { const T b = B[2];
     S1 = fma(b, m1, S1);
-    G1x = fma(b, m0, G1x);
+    G1x = b;
   }
   { const T b = B[3];
     S1 = fma(b, m2, S1);
-    G1y = fma(b, m0, G1y);
+    G1y = b;
   }
   { const T b = B[4];
     S1 = fma(b, m3, S1);
-    G1z = fma(b, m0, G1z);
+    G1z = b;
   }
   { const T b = B[5];
-    S2 = fma(b, m1, S2);
-    G2x = fma(b, m0, G2x);
+    S2 = b * m1;
+    G2x = b;
   }
   { const T b = B[6];
     S2 = fma(b, m2, S2);
-    G2y = fma(b, m0, G2y);
+    G2y = b;
   }
   { const T b = B[7];
     S2 = fma(b, m3, S2);
-    G2z = fma(b, m0, G2z);
+    G2z = b;
   }
   { const T b = B[8];
     S2 = fma(b, m4, S2);
     G2x = fma(b, m1, G2x);
-    H2x = fma(b, q1, H2x);
+    H2x = b * q1;
   }
   { const T b = B[9];
     S2 = fma(b, m5, S2);
     G2x = fma(b, m2, G2x);
     H2x = fma(b, q2, H2x);
     G2y = fma(b, m1, G2y);
-    H2y = fma(b, q1, H2y);
+    H2y = b * q1;
   }
   { const T b = B[10];
     S2 = fma(b, m6, S2);
     G2x = fma(b, m3, G2x);
     H2x = fma(b, q3, H2x);
     G2z = fma(b, m1, G2z);
-    H2z = fma(b, q1, H2z);
+    H2z = b * q1;
   }
   { const T b = B[11];
     S2 = fma(b, m7, S2);
@@ -473,23 +630,23 @@ __device__ __forceinline__ void m2p_adj_self_p3(const T* __restrict__ B, T Rx, T
     H2z = fma(b, q3, H2z);
   }
   { const T b = B[14];
-    S3 = fma(b, m10, S3);
-    G3x = fma(b, m4, G3x);
-    H3x = fma(b, q4, H3x);
+    S3 = b * m10;
+    G3x = b * m4;
+    H3x = b * q4;
   }
   { const T b = B[15];
     S3 = fma(b, m11, S3);
     G3x = fma(b, m5, G3x);
     H3x = fma(b, q5, H3x);
-    G3y = fma(b, m4, G3y);
-    H3y = fma(b, q4, H3y);
+    G3y = b * m4;
+    H3y = b * q4;
   }
   { const T b = B[16];
     S3 = fma(b, m12, S3);
     G3x = fma(b, m6, G3x);
     H3x = fma(b, q6, H3x);
-    G3z = fma(b, m4, G3z);
-    H3z = fma(b, q4, H3z);
+    G3z = b * m4;
+    H3z = b * q4;
   }
   { const T b = B[17];
     S3 = fma(b, m13, S3);
@@ -539,22 +696,20 @@ __device__ __forceinline__ void m2p_adj_self_p3(const T* __restrict__ B, T Rx, T
     H3z = fma(b, q9, H3z);
   }
   const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));
-  T ax = T(0), ay = T(0), az = T(0);
+  T ax = ox, ay = oy, az = oz;
   { const T a1 = F1 * S0;  // F_{j+1} S_j
-    const T gl = fma(G0x, lx, fma(G0y, ly, G0z * lz));
-    const T c1 = fma(F2 * S0, rl, F1 * gl);  // R_k coefficient
-    const T c2 = F1 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G0x, fma(F0, H0x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G0y, fma(F0, H0y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G0z, fma(F0, H0z, az))));
+    const T c1 = F2 * S0 * rl;  // R_k coefficient
+    ax = fma(a1, lx, fma(Rx, c1, ax));
+    ay = fma(a1, ly, fma(Ry, c1, ay));
+    az = fma(a1, lz, fma(Rz, c1, az));
   }
   { const T a1 = F2 * S1;  // F_{j+1} S_j
     const T gl = fma(G1x, lx, fma(G1y, ly, G1z * lz));
     const T c1 = fma(F3 * S1, rl, F2 * gl);  // R_k coefficient
     const T c2 = F2 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, fma(F1, H1x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, fma(F1, H1y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, fma(F1, H1z, az))));
+    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, ax)));
+    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, ay)));
+    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, az)));
   }
   { const T a1 = F3 * S2;  // F_{j+1} S_j
     const T gl = fma(G2x, lx, fma(G2y, ly, G2z * lz));
@@ -572,9 +727,226 @@ __device__ __forceinline__ void m2p_adj_self_p3(const T* __restrict__ B, T Rx, T
     ay = fma(a1, ly, fma(Ry, c1, fma(c2, G3y, fma(F3, H3y, ay))));
     az = fma(a1, lz, fma(Rz, c1, fma(c2, G3z, fma(F3, H3z, az))));
   }
-  ox += ax;
-  oy += ay;
-  oz += az;
+  ox = ax;
+  oy = ay;
+  oz = az;
+}
+
+__device__ __forceinline__ void m2p2_adj_self_p3(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz, float2 eps2, float2 lx, float2 ly, float2 lz, float2& ox, float2& oy, float2& oz) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = nbody_rsqrt2(s);
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 F4 = __fmul2_rn(F3, __fmul2_rn(make_float2(-7.0f, -7.0f), is));
+  const float2 F5 = __fmul2_rn(F4, __fmul2_rn(make_float2(-9.0f, -9.0f), is));
+  const float2 Rx_2 = __fmul2_rn(Rx, make_float2(0.5f, 0.5f));
+  const float2 Rx_3 = __fmul2_rn(Rx, make_float2(0.333333333f, 0.333333333f));
+  const float2 Ry_2 = __fmul2_rn(Ry, make_float2(0.5f, 0.5f));
+  const float2 Ry_3 = __fmul2_rn(Ry, make_float2(0.333333333f, 0.333333333f));
+  const float2 Rz_2 = __fmul2_rn(Rz, make_float2(0.5f, 0.5f));
+  const float2 Rz_3 = __fmul2_rn(Rz, make_float2(0.333333333f, 0.333333333f));
+  const float2 m0 = make_float2(1.0f, 1.0f);
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  const float2 m4 = __fmul2_rn(m1, Rx_2);
+  const float2 m5 = __fmul2_rn(m2, Rx);
+  const float2 m6 = __fmul2_rn(m3, Rx);
+  const float2 m7 = __fmul2_rn(m2, Ry_2);
+  const float2 m8 = __fmul2_rn(m3, Ry);
+  const float2 m9 = __fmul2_rn(m3, Rz_2);
+  const float2 m10 = __fmul2_rn(m4, Rx_3);
+  const float2 m11 = __fmul2_rn(m5, Rx_2);
+  const float2 m12 = __fmul2_rn(m6, Rx_2);
+  const float2 m13 = __fmul2_rn(m7, Rx);
+  const float2 m14 = __fmul2_rn(m8, Rx);
+  const float2 m15 = __fmul2_rn(m9, Rx);
+  const float2 m16 = __fmul2_rn(m7, Ry_3);
+  const float2 m17 = __fmul2_rn(m8, Ry_2);
+  const float2 m18 = __fmul2_rn(m9, Ry);
+  const float2 m19 = __fmul2_rn(m9, Rz_3);
+  float2 q1 = lx;
+  float2 q2 = ly;
+  float2 q3 = lz;
+  float2 q4 = __fmul2_rn(lx, m1);
+  float2 q5 = __fmul2_rn(lx, m2);
+  q5 = __ffma2_rn(ly, m1, q5);
+  float2 q6 = __fmul2_rn(lx, m3);
+  q6 = __ffma2_rn(lz, m1, q6);
+  float2 q7 = __fmul2_rn(ly, m2);
+  float2 q8 = __fmul2_rn(ly, m3);
+  q8 = __ffma2_rn(lz, m2, q8);
+  float2 q9 = __fmul2_rn(lz, m3);
+  float2 S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z, H2x, H2y, H2z, S3, G3x, H3x, G3y, H3y, G3z, H3z;
+  { const float2 b = B[0];
+    S0 = b;
+  }
+  { const float2 b = B[1];
+    S1 = b;
+  }
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m1, S1);
+    G1x = b;
+  }
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
+  }
+  { const float2 b = B[4];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  { const float2 b = B[5];
+    S2 = __fmul2_rn(b, m1);
+    G2x = b;
+  }
+  { const float2 b = B[6];
+    S2 = __ffma2_rn(b, m2, S2);
+    G2y = b;
+  }
+  { const float2 b = B[7];
+    S2 = __ffma2_rn(b, m3, S2);
+    G2z = b;
+  }
+  { const float2 b = B[8];
+    S2 = __ffma2_rn(b, m4, S2);
+    G2x = __ffma2_rn(b, m1, G2x);
+    H2x = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[9];
+    S2 = __ffma2_rn(b, m5, S2);
+    G2x = __ffma2_rn(b, m2, G2x);
+    H2x = __ffma2_rn(b, q2, H2x);
+    G2y = __ffma2_rn(b, m1, G2y);
+    H2y = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[10];
+    S2 = __ffma2_rn(b, m6, S2);
+    G2x = __ffma2_rn(b, m3, G2x);
+    H2x = __ffma2_rn(b, q3, H2x);
+    G2z = __ffma2_rn(b, m1, G2z);
+    H2z = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[11];
+    S2 = __ffma2_rn(b, m7, S2);
+    G2y = __ffma2_rn(b, m2, G2y);
+    H2y = __ffma2_rn(b, q2, H2y);
+  }
+  { const float2 b = B[12];
+    S2 = __ffma2_rn(b, m8, S2);
+    G2y = __ffma2_rn(b, m3, G2y);
+    H2y = __ffma2_rn(b, q3, H2y);
+    G2z = __ffma2_rn(b, m2, G2z);
+    H2z = __ffma2_rn(b, q2, H2z);
+  }
+  { const float2 b = B[13];
+    S2 = __ffma2_rn(b, m9, S2);
+    G2z = __ffma2_rn(b, m3, G2z);
+    H2z = __ffma2_rn(b, q3, H2z);
+  }
+  { const float2 b = B[14];
+    S3 = __fmul2_rn(b, m10);
+    G3x = __fmul2_rn(b, m4);
+    H3x = __fmul2_rn(b, q4);
+  }
+  { const float2 b = B[15];
+    S3 = __ffma2_rn(b, m11, S3);
+    G3x = __ffma2_rn(b, m5, G3x);
+    H3x = __ffma2_rn(b, q5, H3x);
+    G3y = __fmul2_rn(b, m4);
+    H3y = __fmul2_rn(b, q4);
+  }
+  { const float2 b = B[16];
+    S3 = __ffma2_rn(b, m12, S3);
+    G3x = __ffma2_rn(b, m6, G3x);
+    H3x = __ffma2_rn(b, q6, H3x);
+    G3z = __fmul2_rn(b, m4);
+    H3z = __fmul2_rn(b, q4);
+  }
+  { const float2 b = B[17];
+    S3 = __ffma2_rn(b, m13, S3);
+    G3x = __ffma2_rn(b, m7, G3x);
+    H3x = __ffma2_rn(b, q7, H3x);
+    G3y = __ffma2_rn(b, m5, G3y);
+    H3y = __ffma2_rn(b, q5, H3y);
+  }
+  { const float2 b = B[18];
+    S3 = __ffma2_rn(b, m14, S3);
+    G3x = __ffma2_rn(b, m8, G3x);
+    H3x = __ffma2_rn(b, q8, H3x);
+    G3y = __ffma2_rn(b, m6, G3y);
+    H3y = __ffma2_rn(b, q6, H3y);
+    G3z = __ffma2_rn(b, m5, G3z);
+    H3z = __ffma2_rn(b, q5, H3z);
+  }
+  { const float2 b = B[19];
+    S3 = __ffma2_rn(b, m15, S3);
+    G3x = __ffma2_rn(b, m9, G3x);
+    H3x = __ffma2_rn(b, q9, H3x);
+    G3z = __ffma2_rn(b, m6, G3z);
+    H3z = __ffma2_rn(b, q6, H3z);
+  }
+  { const float2 b = B[20];
+    S3 = __ffma2_rn(b, m16, S3);
+    G3y = __ffma2_rn(b, m7, G3y);
+    H3y = __ffma2_rn(b, q7, H3y);
+  }
+  { const float2 b = B[21];
+    S3 = __ffma2_rn(b, m17, S3);
+    G3y = __ffma2_rn(b, m8, G3y);
+    H3y = __ffma2_rn(b, q8, H3y);
+    G3z = __ffma2_rn(b, m7, G3z);
+    H3z = __ffma2_rn(b, q7, H3z);
+  }
+  { const float2 b = B[22];
+    S3 = __ffma2_rn(b, m18, S3);
+    G3y = __ffma2_rn(b, m9, G3y);
+    H3y = __ffma2_rn(b, q9, H3y);
+    G3z = __ffma2_rn(b, m8, G3z);
+    H3z = __ffma2_rn(b, q8, H3z);
+  }
+  { const float2 b = B[23];
+    S3 = __ffma2_rn(b, m19, S3);
+    G3z = __ffma2_rn(b, m9, G3z);
+    H3z = __ffma2_rn(b, q9, H3z);
+  }
+  const float2 rl = __ffma2_rn(Rx, lx, __ffma2_rn(Ry, ly, __fmul2_rn(Rz, lz)));
+  float2 ax = ox, ay = oy, az = oz;
+  { const float2 a1 = __fmul2_rn(F1, S0);
+    const float2 c1 = __fmul2_rn(__fmul2_rn(F2, S0), rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, ax));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, ay));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, az));
+  }
+  { const float2 a1 = __fmul2_rn(F2, S1);
+    const float2 gl = __ffma2_rn(G1x, lx, __ffma2_rn(G1y, ly, __fmul2_rn(G1z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F3, S1), rl, __fmul2_rn(F2, gl));
+    const float2 c2 = __fmul2_rn(F2, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G1x, ax)));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G1y, ay)));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G1z, az)));
+  }
+  { const float2 a1 = __fmul2_rn(F3, S2);
+    const float2 gl = __ffma2_rn(G2x, lx, __ffma2_rn(G2y, ly, __fmul2_rn(G2z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F4, S2), rl, __fmul2_rn(F3, gl));
+    const float2 c2 = __fmul2_rn(F3, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G2x, __ffma2_rn(F2, H2x, ax))));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G2y, __ffma2_rn(F2, H2y, ay))));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G2z, __ffma2_rn(F2, H2z, az))));
+  }
+  { const float2 a1 = __fmul2_rn(F4, S3);
+    const float2 gl = __ffma2_rn(G3x, lx, __ffma2_rn(G3y, ly, __fmul2_rn(G3z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F5, S3), rl, __fmul2_rn(F4, gl));
+    const float2 c2 = __fmul2_rn(F4, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G3x, __ffma2_rn(F3, H3x, ax))));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G3y, __ffma2_rn(F3, H3y, ay))));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G3z, __ffma2_rn(F3, H3z, az))));
+  }
+  ox = ax;
+  oy = ay;
+  oz = az;
 }
 
 template <typename T>
@@ -765,112 +1137,88 @@ __device__ __forceinline__ void m2p_adj_self_p4(const T* __restrict__ B, T Rx, T
   const T m32 = m18 * Ry_2;
   const T m33 = m19 * Ry;
   const T m34 = m19 * Rz_4;
-  T q0 = T(0);
-  T q1 = T(0);
-  T q2 = T(0);
-  T q3 = T(0);
-  T q4 = T(0);
-  T q5 = T(0);
-  T q6 = T(0);
-  T q7 = T(0);
-  T q8 = T(0);
-  T q9 = T(0);
-  T q10 = T(0);
-  T q11 = T(0);
-  T q12 = T(0);
-  T q13 = T(0);
-  T q14 = T(0);
-  T q15 = T(0);
-  T q16 = T(0);
-  T q17 = T(0);
-  T q18 = T(0);
-  T q19 = T(0);
-  q1 = fma(lx, m0, q1);
-  q2 = fma(ly, m0, q2);
-  q3 = fma(lz, m0, q3);
-  q4 = fma(lx, m1, q4);
-  q5 = fma(lx, m2, q5);
+  T q1 = lx;
+  T q2 = ly;
+  T q3 = lz;
+  T q4 = lx * m1;
+  T q5 = lx * m2;
   q5 = fma(ly, m1, q5);
-  q6 = fma(lx, m3, q6);
+  T q6 = lx * m3;
   q6 = fma(lz, m1, q6);
-  q7 = fma(ly, m2, q7);
-  q8 = fma(ly, m3, q8);
+  T q7 = ly * m2;
+  T q8 = ly * m3;
   q8 = fma(lz, m2, q8);
-  q9 = fma(lz, m3, q9);
-  q10 = fma(lx, m4, q10);
-  q11 = fma(lx, m5, q11);
+  T q9 = lz * m3;
+  T q10 = lx * m4;
+  T q11 = lx * m5;
   q11 = fma(ly, m4, q11);
-  q12 = fma(lx, m6, q12);
+  T q12 = lx * m6;
   q12 = fma(lz, m4, q12);
-  q13 = fma(lx, m7, q13);
+  T q13 = lx * m7;
   q13 = fma(ly, m5, q13);
-  q14 = fma(lx, m8, q14);
+  T q14 = lx * m8;
   q14 = fma(ly, m6, q14);
   q14 = fma(lz, m5, q14);
-  q15 = fma(lx, m9, q15);
+  T q15 = lx * m9;
   q15 = fma(lz, m6, q15);
-  q16 = fma(ly, m7, q16);
-  q17 = fma(ly, m8, q17);
+  T q16 = ly * m7;
+  T q17 = ly * m8;
   q17 = fma(lz, m7, q17);
-  q18 = fma(ly, m9, q18);
+  T q18 = ly * m9;
   q18 = fma(lz, m8, q18);
-  q19 = fma(lz, m9, q19);
-  T S0 = T(0), G0x = T(0), G0y = T(0), G0z = T(0), H0x = T(0), H0y = T(0), H0z = T(0);
-  T S1 = T(0), G1x = T(0), G1y = T(0), G1z = T(0), H1x = T(0), H1y = T(0), H1z = T(0);
-  T S2 = T(0), G2x = T(0), G2y = T(0), G2z = T(0), H2x = T(0), H2y = T(0), H2z = T(0);
-  T S3 = T(0), G3x = T(0), G3y = T(0), G3z = T(0), H3x = T(0), H3y = T(0), H3z = T(0);
-  T S4 = T(0), G4x = T(0), G4y = T(0), G4z = T(0), H4x = T(0), H4y = T(0), H4z = T(0);
+  T q19 = lz * m9;
+  T S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z, H2x, H2y, H2z, S3, G3x, H3x, G3y, H3y, G3z, H3z, S4, G4x, H4x, G4y, H4y, G4z, H4z;
   { const T b = B[0];
-    S0 = fma(b, m0, S0);
+    S0 = b;
   }
   { const T b = B[1];
-    S1 = fma(b, m0, S1);
+    S1 = b;
   }
   { const T b = B[2];
     S1 = fma(b, m1, S1);
-    G1x = fma(b, m0, G1x);
+    G1x = b;
   }
   { const T b = B[3];
     S1 = fma(b, m2, S1);
-    G1y = fma(b, m0, G1y);
+    G1y = b;
   }
   { const T b = B[4];
     S1 = fma(b, m3, S1);
-    G1z = fma(b, m0, G1z);
+    G1z = b;
   }
   { const T b = B[5];
-    S2 = fma(b, m0, S2);
+    S2 = b;
   }
   { const T b = B[6];
     S2 = fma(b, m1, S2);
-    G2x = fma(b, m0, G2x);
+    G2x = b;
   }
   { const T b = B[7];
     S2 = fma(b, m2, S2);
-    G2y = fma(b, m0, G2y);
+    G2y = b;
   }
   { const T b = B[8];
     S2 = fma(b, m3, S2);
-    G2z = fma(b, m0, G2z);
+    G2z = b;
   }
   { const T b = B[9];
     S2 = fma(b, m4, S2);
     G2x = fma(b, m1, G2x);
-    H2x = fma(b, q1, H2x);
+    H2x = b * q1;
   }
   { const T b = B[10];
     S2 = fma(b, m5, S2);
     G2x = fma(b, m2, G2x);
     H2x = fma(b, q2, H2x);
     G2y = fma(b, m1, G2y);
-    H2y = fma(b, q1, H2y);
+    H2y = b * q1;
   }
   { const T b = B[11];
     S2 = fma(b, m6, S2);
     G2x = fma(b, m3, G2x);
     H2x = fma(b, q3, H2x);
     G2z = fma(b, m1, G2z);
-    H2z = fma(b, q1, H2z);
+    H2z = b * q1;
   }
   { const T b = B[12];
     S2 = fma(b, m7, S2);
@@ -890,23 +1238,23 @@ __device__ __forceinline__ void m2p_adj_self_p4(const T* __restrict__ B, T Rx, T
     H2z = fma(b, q3, H2z);
   }
   { const T b = B[15];
-    S3 = fma(b, m4, S3);
-    G3x = fma(b, m1, G3x);
-    H3x = fma(b, q1, H3x);
+    S3 = b * m4;
+    G3x = b * m1;
+    H3x = b * q1;
   }
   { const T b = B[16];
     S3 = fma(b, m5, S3);
     G3x = fma(b, m2, G3x);
     H3x = fma(b, q2, H3x);
-    G3y = fma(b, m1, G3y);
-    H3y = fma(b, q1, H3y);
+    G3y = b * m1;
+    H3y = b * q1;
   }
   { const T b = B[17];
     S3 = fma(b, m6, S3);
     G3x = fma(b, m3, G3x);
     H3x = fma(b, q3, H3x);
-    G3z = fma(b, m1, G3z);
-    H3z = fma(b, q1, H3z);
+    G3z = b * m1;
+    H3z = b * q1;
   }
   { const T b = B[18];
     S3 = fma(b, m7, S3);
@@ -992,23 +1340,23 @@ __device__ __forceinline__ void m2p_adj_self_p4(const T* __restrict__ B, T Rx, T
     H3z = fma(b, q9, H3z);
   }
   { const T b = B[31];
-    S4 = fma(b, m20, S4);
-    G4x = fma(b, m10, G4x);
-    H4x = fma(b, q10, H4x);
+    S4 = b * m20;
+    G4x = b * m10;
+    H4x = b * q10;
   }
   { const T b = B[32];
     S4 = fma(b, m21, S4);
     G4x = fma(b, m11, G4x);
     H4x = fma(b, q11, H4x);
-    G4y = fma(b, m10, G4y);
-    H4y = fma(b, q10, H4y);
+    G4y = b * m10;
+    H4y = b * q10;
   }
   { const T b = B[33];
     S4 = fma(b, m22, S4);
     G4x = fma(b, m12, G4x);
     H4x = fma(b, q12, H4x);
-    G4z = fma(b, m10, G4z);
-    H4z = fma(b, q10, H4z);
+    G4z = b * m10;
+    H4z = b * q10;
   }
   { const T b = B[34];
     S4 = fma(b, m23, S4);
@@ -1097,22 +1445,20 @@ __device__ __forceinline__ void m2p_adj_self_p4(const T* __restrict__ B, T Rx, T
     H4z = fma(b, q19, H4z);
   }
   const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));
-  T ax = T(0), ay = T(0), az = T(0);
+  T ax = ox, ay = oy, az = oz;
   { const T a1 = F1 * S0;  // F_{j+1} S_j
-    const T gl = fma(G0x, lx, fma(G0y, ly, G0z * lz));
-    const T c1 = fma(F2 * S0, rl, F1 * gl);  // R_k coefficient
-    const T c2 = F1 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G0x, fma(F0, H0x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G0y, fma(F0, H0y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G0z, fma(F0, H0z, az))));
+    const T c1 = F2 * S0 * rl;  // R_k coefficient
+    ax = fma(a1, lx, fma(Rx, c1, ax));
+    ay = fma(a1, ly, fma(Ry, c1, ay));
+    az = fma(a1, lz, fma(Rz, c1, az));
   }
   { const T a1 = F2 * S1;  // F_{j+1} S_j
     const T gl = fma(G1x, lx, fma(G1y, ly, G1z * lz));
     const T c1 = fma(F3 * S1, rl, F2 * gl);  // R_k coefficient
     const T c2 = F2 * rl;  // G_{j,k} coefficient
-    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, fma(F1, H1x, ax))));
-    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, fma(F1, H1y, ay))));
-    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, fma(F1, H1z, az))));
+    ax = fma(a1, lx, fma(Rx, c1, fma(c2, G1x, ax)));
+    ay = fma(a1, ly, fma(Ry, c1, fma(c2, G1y, ay)));
+    az = fma(a1, lz, fma(Rz, c1, fma(c2, G1z, az)));
   }
   { const T a1 = F3 * S2;  // F_{j+1} S_j
     const T gl = fma(G2x, lx, fma(G2y, ly, G2z * lz));
@@ -1138,9 +1484,415 @@ __device__ __forceinline__ void m2p_adj_self_p4(const T* __restrict__ B, T Rx, T
     ay = fma(a1, ly, fma(Ry, c1, fma(c2, G4y, fma(F4, H4y, ay))));
     az = fma(a1, lz, fma(Rz, c1, fma(c2, G4z, fma(F4, H4z, az))));
   }
-  ox += ax;
-  oy += ay;
-  oz += az;
+  ox = ax;
+  oy = ay;
+  oz = az;
+}
+
+__device__ __forceinline__ void m2p2_adj_self_p4(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz, float2 eps2, float2 lx, float2 ly, float2 lz, float2& ox, float2& oy, float2& oz) {
+  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
+  const float2 F0 = nbody_rsqrt2(s);
+  const float2 is = __fmul2_rn(F0, F0);
+  const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
+  const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
+  const float2 F3 = __fmul2_rn(F2, __fmul2_rn(make_float2(-5.0f, -5.0f), is));
+  const float2 F4 = __fmul2_rn(F3, __fmul2_rn(make_float2(-7.0f, -7.0f), is));
+  const float2 F5 = __fmul2_rn(F4, __fmul2_rn(make_float2(-9.0f, -9.0f), is));
+  const float2 F6 = __fmul2_rn(F5, __fmul2_rn(make_float2(-11.0f, -11.0f), is));
+  const float2 Rx_2 = __fmul2_rn(Rx, make_float2(0.5f, 0.5f));
+  const float2 Rx_3 = __fmul2_rn(Rx, make_float2(0.333333333f, 0.333333333f));
+  const float2 Rx_4 = __fmul2_rn(Rx, make_float2(0.25f, 0.25f));
+  const float2 Ry_2 = __fmul2_rn(Ry, make_float2(0.5f, 0.5f));
+  const float2 Ry_3 = __fmul2_rn(Ry, make_float2(0.333333333f, 0.333333333f));
+  const float2 Ry_4 = __fmul2_rn(Ry, make_float2(0.25f, 0.25f));
+  const float2 Rz_2 = __fmul2_rn(Rz, make_float2(0.5f, 0.5f));
+  const float2 Rz_3 = __fmul2_rn(Rz, make_float2(0.333333333f, 0.333333333f));
+  const float2 Rz_4 = __fmul2_rn(Rz, make_float2(0.25f, 0.25f));
+  const float2 m0 = make_float2(1.0f, 1.0f);
+  const float2 m1 = Rx;
+  const float2 m2 = Ry;
+  const float2 m3 = Rz;
+  const float2 m4 = __fmul2_rn(m1, Rx_2);
+  const float2 m5 = __fmul2_rn(m2, Rx);
+  const float2 m6 = __fmul2_rn(m3, Rx);
+  const float2 m7 = __fmul2_rn(m2, Ry_2);
+  const float2 m8 = __fmul2_rn(m3, Ry);
+  const float2 m9 = __fmul2_rn(m3, Rz_2);
+  const float2 m10 = __fmul2_rn(m4, Rx_3);
+  const float2 m11 = __fmul2_rn(m5, Rx_2);
+  const float2 m12 = __fmul2_rn(m6, Rx_2);
+  const float2 m13 = __fmul2_rn(m7, Rx);
+  const float2 m14 = __fmul2_rn(m8, Rx);
+  const float2 m15 = __fmul2_rn(m9, Rx);
+  const float2 m16 = __fmul2_rn(m7, Ry_3);
+  const float2 m17 = __fmul2_rn(m8, Ry_2);
+  const float2 m18 = __fmul2_rn(m9, Ry);
+  const float2 m19 = __fmul2_rn(m9, Rz_3);
+  const float2 m20 = __fmul2_rn(m10, Rx_4);
+  const float2 m21 = __fmul2_rn(m11, Rx_3);
+  const float2 m22 = __fmul2_rn(m12, Rx_3);
+  const float2 m23 = __fmul2_rn(m13, Rx_2);
+  const float2 m24 = __fmul2_rn(m14, Rx_2);
+  const float2 m25 = __fmul2_rn(m15, Rx_2);
+  const float2 m26 = __fmul2_rn(m16, Rx);
+  const float2 m27 = __fmul2_rn(m17, Rx);
+  const float2 m28 = __fmul2_rn(m18, Rx);
+  const float2 m29 = __fmul2_rn(m19, Rx);
+  const float2 m30 = __fmul2_rn(m16, Ry_4);
+  const float2 m31 = __fmul2_rn(m17, Ry_3);
+  const float2 m32 = __fmul2_rn(m18, Ry_2);
+  const float2 m33 = __fmul2_rn(m19, Ry);
+  const float2 m34 = __fmul2_rn(m19, Rz_4);
+  float2 q1 = lx;
+  float2 q2 = ly;
+  float2 q3 = lz;
+  float2 q4 = __fmul2_rn(lx, m1);
+  float2 q5 = __fmul2_rn(lx, m2);
+  q5 = __ffma2_rn(ly, m1, q5);
+  float2 q6 = __fmul2_rn(lx, m3);
+  q6 = __ffma2_rn(lz, m1, q6);
+  float2 q7 = __fmul2_rn(ly, m2);
+  float2 q8 = __fmul2_rn(ly, m3);
+  q8 = __ffma2_rn(lz, m2, q8);
+  float2 q9 = __fmul2_rn(lz, m3);
+  float2 q10 = __fmul2_rn(lx, m4);
+  float2 q11 = __fmul2_rn(lx, m5);
+  q11 = __ffma2_rn(ly, m4, q11);
+  float2 q12 = __fmul2_rn(lx, m6);
+  q12 = __ffma2_rn(lz, m4, q12);
+  float2 q13 = __fmul2_rn(lx, m7);
+  q13 = __ffma2_rn(ly, m5, q13);
+  float2 q14 = __fmul2_rn(lx, m8);
+  q14 = __ffma2_rn(ly, m6, q14);
+  q14 = __ffma2_rn(lz, m5, q14);
+  float2 q15 = __fmul2_rn(lx, m9);
+  q15 = __ffma2_rn(lz, m6, q15);
+  float2 q16 = __fmul2_rn(ly, m7);
+  float2 q17 = __fmul2_rn(ly, m8);
+  q17 = __ffma2_rn(lz, m7, q17);
+  float2 q18 = __fmul2_rn(ly, m9);
+  q18 = __ffma2_rn(lz, m8, q18);
+  float2 q19 = __fmul2_rn(lz, m9);
+  float2 S0, S1, G1x, G1y, G1z, S2, G2x, G2y, G2z, H2x, H2y, H2z, S3, G3x, H3x, G3y, H3y, G3z, H3z, S4, G4x, H4x, G4y, H4y, G4z, H4z;
+  { const float2 b = B[0];
+    S0 = b;
+  }
+  { const float2 b = B[1];
+    S1 = b;
+  }
+  { const float2 b = B[2];
+    S1 = __ffma2_rn(b, m1, S1);
+    G1x = b;
+  }
+  { const float2 b = B[3];
+    S1 = __ffma2_rn(b, m2, S1);
+    G1y = b;
+  }
+  { const float2 b = B[4];
+    S1 = __ffma2_rn(b, m3, S1);
+    G1z = b;
+  }
+  { const float2 b = B[5];
+    S2 = b;
+  }
+  { const float2 b = B[6];
+    S2 = __ffma2_rn(b, m1, S2);
+    G2x = b;
+  }
+  { const float2 b = B[7];
+    S2 = __ffma2_rn(b, m2, S2);
+    G2y = b;
+  }
+  { const float2 b = B[8];
+    S2 = __ffma2_rn(b, m3, S2);
+    G2z = b;
+  }
+  { const float2 b = B[9];
+    S2 = __ffma2_rn(b, m4, S2);
+    G2x = __ffma2_rn(b, m1, G2x);
+    H2x = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[10];
+    S2 = __ffma2_rn(b, m5, S2);
+    G2x = __ffma2_rn(b, m2, G2x);
+    H2x = __ffma2_rn(b, q2, H2x);
+    G2y = __ffma2_rn(b, m1, G2y);
+    H2y = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[11];
+    S2 = __ffma2_rn(b, m6, S2);
+    G2x = __ffma2_rn(b, m3, G2x);
+    H2x = __ffma2_rn(b, q3, H2x);
+    G2z = __ffma2_rn(b, m1, G2z);
+    H2z = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[12];
+    S2 = __ffma2_rn(b, m7, S2);
+    G2y = __ffma2_rn(b, m2, G2y);
+    H2y = __ffma2_rn(b, q2, H2y);
+  }
+  { const float2 b = B[13];
+    S2 = __ffma2_rn(b, m8, S2);
+    G2y = __ffma2_rn(b, m3, G2y);
+    H2y = __ffma2_rn(b, q3, H2y);
+    G2z = __ffma2_rn(b, m2, G2z);
+    H2z = __ffma2_rn(b, q2, H2z);
+  }
+  { const float2 b = B[14];
+    S2 = __ffma2_rn(b, m9, S2);
+    G2z = __ffma2_rn(b, m3, G2z);
+    H2z = __ffma2_rn(b, q3, H2z);
+  }
+  { const float2 b = B[15];
+    S3 = __fmul2_rn(b, m4);
+    G3x = __fmul2_rn(b, m1);
+    H3x = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[16];
+    S3 = __ffma2_rn(b, m5, S3);
+    G3x = __ffma2_rn(b, m2, G3x);
+    H3x = __ffma2_rn(b, q2, H3x);
+    G3y = __fmul2_rn(b, m1);
+    H3y = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[17];
+    S3 = __ffma2_rn(b, m6, S3);
+    G3x = __ffma2_rn(b, m3, G3x);
+    H3x = __ffma2_rn(b, q3, H3x);
+    G3z = __fmul2_rn(b, m1);
+    H3z = __fmul2_rn(b, q1);
+  }
+  { const float2 b = B[18];
+    S3 = __ffma2_rn(b, m7, S3);
+    G3y = __ffma2_rn(b, m2, G3y);
+    H3y = __ffma2_rn(b, q2, H3y);
+  }
+  { const float2 b = B[19];
+    S3 = __ffma2_rn(b, m8, S3);
+    G3y = __ffma2_rn(b, m3, G3y);
+    H3y = __ffma2_rn(b, q3, H3y);
+    G3z = __ffma2_rn(b, m2, G3z);
+    H3z = __ffma2_rn(b, q2, H3z);
+  }
+  { const float2 b = B[20];
+    S3 = __ffma2_rn(b, m9, S3);
+    G3z = __ffma2_rn(b, m3, G3z);
+    H3z = __ffma2_rn(b, q3, H3z);
+  }
+  { const float2 b = B[21];
+    S3 = __ffma2_rn(b, m10, S3);
+    G3x = __ffma2_rn(b, m4, G3x);
+    H3x = __ffma2_rn(b, q4, H3x);
+  }
+  { const float2 b = B[22];
+    S3 = __ffma2_rn(b, m11, S3);
+    G3x = __ffma2_rn(b, m5, G3x);
+    H3x = __ffma2_rn(b, q5, H3x);
+    G3y = __ffma2_rn(b, m4, G3y);
+    H3y = __ffma2_rn(b, q4, H3y);
+  }
+  { const float2 b = B[23];
+    S3 = __ffma2_rn(b, m12, S3);
+    G3x = __ffma2_rn(b, m6, G3x);
+    H3x = __ffma2_rn(b, q6, H3x);
+    G3z = __ffma2_rn(b, m4, G3z);
+    H3z = __ffma2_rn(b, q4, H3z);
+  }
+  { const float2 b = B[24];
+    S3 = __ffma2_rn(b, m13, S3);
+    G3x = __ffma2_rn(b, m7, G3x);
+    H3x = __ffma2_rn(b, q7, H3x);
+    G3y = __ffma2_rn(b, m5, G3y);
+    H3y = __ffma2_rn(b, q5, H3y);
+  }
+  { const float2 b = B[25];
+    S3 = __ffma2_rn(b, m14, S3);
+    G3x = __ffma2_rn(b, m8, G3x);
+    H3x = __ffma2_rn(b, q8, H3x);
+    G3y = __ffma2_rn(b, m6, G3y);
+    H3y = __ffma2_rn(b, q6, H3y);
+    G3z = __ffma2_rn(b, m5, G3z);
+    H3z = __ffma2_rn(b, q5, H3z);
+  }
+  { const float2 b = B[26];
+    S3 = __ffma2_rn(b, m15, S3);
+    G3x = __ffma2_rn(b, m9, G3x);
+    H3x = __ffma2_rn(b, q9, H3x);
+    G3z = __ffma2_rn(b, m6, G3z);
+    H3z = __ffma2_rn(b, q6, H3z);
+  }
+  { const float2 b = B[27];
+    S3 = __ffma2_rn(b, m16, S3);
+    G3y = __ffma2_rn(b, m7, G3y);
+    H3y = __ffma2_rn(b, q7, H3y);
+  }
+  { const float2 b = B[28];
+    S3 = __ffma2_rn(b, m17, S3);
+    G3y = __ffma2_rn(b, m8, G3y);
+    H3y = __ffma2_rn(b, q8, H3y);
+    G3z = __ffma2_rn(b, m7, G3z);
+    H3z = __ffma2_rn(b, q7, H3z);
+  }
+  { const float2 b = B[29];
+    S3 = __ffma2_rn(b, m18, S3);
+    G3y = __ffma2_rn(b, m9, G3y);
+    H3y = __ffma2_rn(b, q9, H3y);
+    G3z = __ffma2_rn(b, m8, G3z);
+    H3z = __ffma2_rn(b, q8, H3z);
+  }
+  { const float2 b = B[30];
+    S3 = __ffma2_rn(b, m19, S3);
+    G3z = __ffma2_rn(b, m9, G3z);
+    H3z = __ffma2_rn(b, q9, H3z);
+  }
+  { const float2 b = B[31];
+    S4 = __fmul2_rn(b, m20);
+    G4x = __fmul2_rn(b, m10);
+    H4x = __fmul2_rn(b, q10);
+  }
+  { const float2 b = B[32];
+    S4 = __ffma2_rn(b, m21, S4);
+    G4x = __ffma2_rn(b, m11, G4x);
+    H4x = __ffma2_rn(b, q11, H4x);
+    G4y = __fmul2_rn(b, m10);
+    H4y = __fmul2_rn(b, q10);
+  }
+  { const float2 b = B[33];
+    S4 = __ffma2_rn(b, m22, S4);
+    G4x = __ffma2_rn(b, m12, G4x);
+    H4x = __ffma2_rn(b, q12, H4x);
+    G4z = __fmul2_rn(b, m10);
+    H4z = __fmul2_rn(b, q10);
+  }
+  { const float2 b = B[34];
+    S4 = __ffma2_rn(b, m23, S4);
+    G4x = __ffma2_rn(b, m13, G4x);
+    H4x = __ffma2_rn(b, q13, H4x);
+    G4y = __ffma2_rn(b, m11, G4y);
+    H4y = __ffma2_rn(b, q11, H4y);
+  }
+  { const float2 b = B[35];
+    S4 = __ffma2_rn(b, m24, S4);
+    G4x = __ffma2_rn(b, m14, G4x);
+    H4x = __ffma2_rn(b, q14, H4x);
+    G4y = __ffma2_rn(b, m12, G4y);
+    H4y = __ffma2_rn(b, q12, H4y);
+    G4z = __ffma2_rn(b, m11, G4z);
+    H4z = __ffma2_rn(b, q11, H4z);
+  }
+  { const float2 b = B[36];
+    S4 = __ffma2_rn(b, m25, S4);
+    G4x = __ffma2_rn(b, m15, G4x);
+    H4x = __ffma2_rn(b, q15, H4x);
+    G4z = __ffma2_rn(b, m12, G4z);
+    H4z = __ffma2_rn(b, q12, H4z);
+  }
+  { const float2 b = B[37];
+    S4 = __ffma2_rn(b, m26, S4);
+    G4x = __ffma2_rn(b, m16, G4x);
+    H4x = __ffma2_rn(b, q16, H4x);
+    G4y = __ffma2_rn(b, m13, G4y);
+    H4y = __ffma2_rn(b, q13, H4y);
+  }
+  { const float2 b = B[38];
+    S4 = __ffma2_rn(b, m27, S4);
+    G4x = __ffma2_rn(b, m17, G4x);
+    H4x = __ffma2_rn(b, q17, H4x);
+    G4y = __ffma2_rn(b, m14, G4y);
+    H4y = __ffma2_rn(b, q14, H4y);
+    G4z = __ffma2_rn(b, m13, G4z);
+    H4z = __ffma2_rn(b, q13, H4z);
+  }
+  { const float2 b = B[39];
+    S4 = __ffma2_rn(b, m28, S4);
+    G4x = __ffma2_rn(b, m18, G4x);
+    H4x = __ffma2_rn(b, q18, H4x);
+    G4y = __ffma2_rn(b, m15, G4y);
+    H4y = __ffma2_rn(b, q15, H4y);
+    G4z = __ffma2_rn(b, m14, G4z);
+    H4z = __ffma2_rn(b, q14, H4z);
+  }
+  { const float2 b = B[40];
+    S4 = __ffma2_rn(b, m29, S4);
+    G4x = __ffma2_rn(b, m19, G4x);
+    H4x = __ffma2_rn(b, q19, H4x);
+    G4z = __ffma2_rn(b, m15, G4z);
+    H4z = __ffma2_rn(b, q15, H4z);
+  }
+  { const float2 b = B[41];
+    S4 = __ffma2_rn(b, m30, S4);
+    G4y = __ffma2_rn(b, m16, G4y);
+    H4y = __ffma2_rn(b, q16, H4y);
+  }
+  { const float2 b = B[42];
+    S4 = __ffma2_rn(b, m31, S4);
+    G4y = __ffma2_rn(b, m17, G4y);
+    H4y = __ffma2_rn(b, q17, H4y);
+    G4z = __ffma2_rn(b, m16, G4z);
+    H4z = __ffma2_rn(b, q16, H4z);
+  }
+  { const float2 b = B[43];
+    S4 = __ffma2_rn(b, m32, S4);
+    G4y = __ffma2_rn(b, m18, G4y);
+    H4y = __ffma2_rn(b, q18, H4y);
+    G4z = __ffma2_rn(b, m17, G4z);
+    H4z = __ffma2_rn(b, q17, H4z);
+  }
+  { const float2 b = B[44];
+    S4 = __ffma2_rn(b, m33, S4);
+    G4y = __ffma2_rn(b, m19, G4y);
+    H4y = __ffma2_rn(b, q19, H4y);
+    G4z = __ffma2_rn(b, m18, G4z);
+    H4z = __ffma2_rn(b, q18, H4z);
+  }
+  { const float2 b = B[45];
+    S4 = __ffma2_rn(b, m34, S4);
+    G4z = __ffma2_rn(b, m19, G4z);
+    H4z = __ffma2_rn(b, q19, H4z);
+  }
+  const float2 rl = __ffma2_rn(Rx, lx, __ffma2_rn(Ry, ly, __fmul2_rn(Rz, lz)));
+  float2 ax = ox, ay = oy, az = oz;
+  { const float2 a1 = __fmul2_rn(F1, S0);
+    const float2 c1 = __fmul2_rn(__fmul2_rn(F2, S0), rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, ax));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, ay));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, az));
+  }
+  { const float2 a1 = __fmul2_rn(F2, S1);
+    const float2 gl = __ffma2_rn(G1x, lx, __ffma2_rn(G1y, ly, __fmul2_rn(G1z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F3, S1), rl, __fmul2_rn(F2, gl));
+    const float2 c2 = __fmul2_rn(F2, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G1x, ax)));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G1y, ay)));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G1z, az)));
+  }
+  { const float2 a1 = __fmul2_rn(F3, S2);
+    const float2 gl = __ffma2_rn(G2x, lx, __ffma2_rn(G2y, ly, __fmul2_rn(G2z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F4, S2), rl, __fmul2_rn(F3, gl));
+    const float2 c2 = __fmul2_rn(F3, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G2x, __ffma2_rn(F2, H2x, ax))));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G2y, __ffma2_rn(F2, H2y, ay))));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G2z, __ffma2_rn(F2, H2z, az))));
+  }
+  { const float2 a1 = __fmul2_rn(F4, S3);
+    const float2 gl = __ffma2_rn(G3x, lx, __ffma2_rn(G3y, ly, __fmul2_rn(G3z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F5, S3), rl, __fmul2_rn(F4, gl));
+    const float2 c2 = __fmul2_rn(F4, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G3x, __ffma2_rn(F3, H3x, ax))));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G3y, __ffma2_rn(F3, H3y, ay))));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G3z, __ffma2_rn(F3, H3z, az))));
+  }
+  { const float2 a1 = __fmul2_rn(F5, S4);
+    const float2 gl = __ffma2_rn(G4x, lx, __ffma2_rn(G4y, ly, __fmul2_rn(G4z, lz)));
+    const float2 c1 = __ffma2_rn(__fmul2_rn(F6, S4), rl, __fmul2_rn(F5, gl));
+    const float2 c2 = __fmul2_rn(F5, rl);
+    ax = __ffma2_rn(a1, lx, __ffma2_rn(Rx, c1, __ffma2_rn(c2, G4x, __ffma2_rn(F4, H4x, ax))));
+    ay = __ffma2_rn(a1, ly, __ffma2_rn(Ry, c1, __ffma2_rn(c2, G4y, __ffma2_rn(F4, H4y, ay))));
+    az = __ffma2_rn(a1, lz, __ffma2_rn(Rz, c1, __ffma2_rn(c2, G4z, __ffma2_rn(F4, H4z, az))));
+  }
+  ox = ax;
+  oy = ay;
+  oz = az;
 }
 
 template <typename T>

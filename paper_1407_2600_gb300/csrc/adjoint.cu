@@ -31,6 +31,11 @@ template <int P> struct AOrd;
                                                 T& oy, T& oz) {                                         \
       m2p_adj_self_p##P<T>(B, x, y, z, e2, lx, ly, lz, ox, oy, oz);                                     \
     }                                                                                                   \
+    static __device__ __forceinline__ void self2(const float2* B, float2 x, float2 y, float2 z, float2 e2,  \
+                                                 float2 lx, float2 ly, float2 lz, float2& ox, float2& oy,   \
+                                                 float2& oz) {                                              \
+      m2p2_adj_self_p##P(B, x, y, z, e2, lx, ly, lz, ox, oy, oz);                                       \
+    }                                                                                                   \
     template <typename T>                                                                               \
     static __device__ __forceinline__ void src(T x, T y, T z, T e2, T lx, T ly, T lz, T* nu) {          \
       m2p_adj_src_p##P<T>(x, y, z, e2, lx, ly, lz, nu);                                                 \
@@ -69,27 +74,105 @@ struct AdjArgs {
 
 constexpr double kScale = 1.0 / 8388608.0;
 
-template <typename T, int P, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
+// The walk of one group, shared by the two reverse-mode kernels: the same
+// traversal, classification and M2P queue as the forward walk, with the
+// interactions handed to callbacks.  on_m2p(nmp) consumes the first nmp
+// queued cells (s_midx, s_moff, s_meps); on_p2p(is_p2p, ca, cb, kx, ky, kz,
+// lvl) is called by every lane for the cells of one pop.  Returns false on a
+// stack overflow.
+template <typename T, typename OnM2P, typename OnP2P>
+__device__ __forceinline__ bool adj_walk_group(const DevTree& tr, int box, const int4 gb, const int4 gc, const int4 gd,
+                                               int le, const long long* thr, int n_direct, T eps2, int* stk,
+                                               int stack_cap, int lane, int* s_midx,
+                                               typename Vec4<T>::type* s_moff, T* s_meps, OnM2P on_m2p,
+                                               OnP2P on_p2p) {
   using V4 = typename Vec4<T>::type;
-  constexpr int NBS = AOrd<P>::NBS, NM = AOrd<P>::NM;
-  constexpr int C16 = NBS * (int)sizeof(T) / 16;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned ltmask = (1u << lane) - 1u;
+  const T scale = (T)kScale;
+  int qn = 0;
+  int top = 1;
+  if (lane == 0) stk[0] = box;
+  __syncwarp();
+  while (top > 0) {
+    const int nb = min(32, top);
+    const int base = top - nb;
+    top = base;
+    int c = -1;
+    int4 ca = make_int4(0, 0, 0, 0), cb = make_int4(0, 0, 0, 0);
+    if (lane < nb) {
+      c = stk[base + lane];
+      ca = tr.cA[c];
+      cb = tr.cB[c];
+    }
+    __syncwarp();
+    int cls = NB_CELL_NONE, kx = 0, ky = 0, kz = 0;
+    const int lvl = ca.w & 0xff, nch = ca.w >> 8;
+    if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, le, thr, n_direct, kx, ky, kz);
+    {
+      const int nc = (cls == NB_CELL_OPEN) ? nch : 0;
+      const int pre = warp_excl_scan(nc, lane);
+      const int tot = __shfl_sync(FULL, pre + nc, 31);
+      if (top + tot > stack_cap) return false;
+      for (int q = 0; q < nc; q++) stk[top + pre + q] = cb.z + q;
+      top += tot;
+      __syncwarp();
+    }
+    const unsigned mm = __ballot_sync(FULL, cls == NB_CELL_M2P);
+    if (mm) {
+      if (cls == NB_CELL_M2P) {
+        const int pos = qn + __popc(mm & ltmask);
+        const T sc = (T)(1 << lvl);
+        s_midx[pos] = c;
+        V4 mo;
+        mo.x = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
+        mo.y = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
+        mo.z = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
+        mo.w = sc;
+        s_moff[pos] = mo;
+        s_meps[pos] = eps2 * (sc * sc);
+      }
+      qn += __popc(mm);
+      if (qn >= 32) {
+        __syncwarp();
+        on_m2p(32);
+        if (lane < qn - 32) {
+          s_midx[lane] = s_midx[32 + lane];
+          s_moff[lane] = s_moff[32 + lane];
+          s_meps[lane] = s_meps[32 + lane];
+        }
+        qn -= 32;
+      }
+      __syncwarp();
+    }
+    on_p2p(cls == NB_CELL_P2P, ca, cb, kx, ky, kz, lvl);
+  }
+  if (qn > 0) on_m2p(qn);
+  return true;
+}
+
+// Sink side: per sink, the Hessian-vector products of every M2P expansion
+// its group uses (PK: two cells per packed FP32 pair instruction) and the
+// P2P tidal terms, both for the sink and, by a diagonal pairing over the
+// warp, for the source particles (one atomic per source and chunk).
+template <int P, int WARPS, int MINB, bool PK>
+__global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<float> w) {
+  using T = float;
+  using V4 = float4;
+  constexpr int NBS = AOrd<P>::NBS;
+  constexpr int C4 = NBS / 4;
   __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
   __shared__ V4 s_src[WARPS][32];
   __shared__ int s_jidx[WARPS][32];
-  // M2P queue (up to 31 carried + 32 new), as in the forward walk
   __shared__ V4 s_moff[WARPS][64];
   __shared__ T s_meps[WARPS][64];
   __shared__ int s_midx[WARPS][64];
   __shared__ int s_pfx[WARPS][32], s_pst[WARPS][32], s_plev[WARPS][32];
   __shared__ T s_poff[WARPS][32][3];
   __shared__ int4 s_pcen[WARPS][32];
-  __shared__ T s_sx[WARPS][32][3];
-  __shared__ T s_sl[WARPS][32][3];
 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
-  const unsigned ltmask = (1u << lane) - 1u;
   const DevTree& tr = w.tr;
   int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
   const T scale = (T)kScale;
@@ -112,205 +195,228 @@ __global__ void __launch_bounds__(WARPS * 32, 2) adj_walk_kernel(AdjArgs<T> w) {
       yi = o.y + (T)(la.y - gd.y) * scale;
       zi = o.z + (T)(la.z - gd.z) * scale;
       if (act) {
-        lx = (T)w.lam[i];
-        ly = (T)w.lam[tr.n + i];
-        lz = (T)w.lam[2 * tr.n + i];
+        lx = w.lam[i];
+        ly = w.lam[tr.n + i];
+        lz = w.lam[2 * tr.n + i];
       }
     }
-    s_sx[wid][lane][0] = xi;
-    s_sx[wid][lane][1] = yi;
-    s_sx[wid][lane][2] = zi;
-    s_sl[wid][lane][0] = lx;
-    s_sl[wid][lane][1] = ly;
-    s_sl[wid][lane][2] = lz;
     T mx = 0, my = 0, mz = 0;  // sink cotangent
-    int qn = 0;                // queued M2P cells
-    // the first nmp queued M2P cells: sink side (Hessian-vector products, in
-    // the cell unit, times 2^level) and source side (lane q owns cell q and
-    // sums its moment cotangents over the group's sinks)
-    auto m2p_chunk = [&](int nmp) {
-      const int4* gsrc = reinterpret_cast<const int4*>(w.coef);
-      int4* sdst = reinterpret_cast<int4*>(&s_coef[wid][0]);
-      for (int t = lane; t < nmp * C16; t += 32) {
-        const int q = t / C16, r = t - q * C16;
-        sdst[t] = gsrc[(int64_t)s_midx[wid][q] * C16 + r];
-      }
-      __syncwarp();
-      if (act) {
-        for (int q = 0; q < nmp; q++) {
-          const V4 mo = s_moff[wid][q];
-          T ox = 0, oy = 0, oz = 0;
-          AOrd<P>::template self<T>(&s_coef[wid][q * NBS], fma(xi, mo.w, mo.x), fma(yi, mo.w, mo.y),
-                                    fma(zi, mo.w, mo.z), s_meps[wid][q], lx, ly, lz, ox, oy, oz);
-          mx = fma(ox, mo.w, mx);
-          my = fma(oy, mo.w, my);
-          mz = fma(oz, mo.w, mz);
+    auto on_m2p = [&](int nmp) {
+      const float4* gsrc = reinterpret_cast<const float4*>(w.coef);
+      float4* sdst = reinterpret_cast<float4*>(&s_coef[wid][0]);
+      if constexpr (PK) {
+        const int npair = (nmp + 1) >> 1;
+        for (int t = lane; t < npair * C4; t += 32) {
+          const int q = t / C4, r = t - q * C4;
+          const float4 c0 = gsrc[(int64_t)s_midx[wid][2 * q] * C4 + r];
+          const float4 c1 = 2 * q + 1 < nmp ? gsrc[(int64_t)s_midx[wid][2 * q + 1] * C4 + r]
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+          sdst[2 * (q * C4 + r)] = make_float4(c0.x, c1.x, c0.y, c1.y);
+          sdst[2 * (q * C4 + r) + 1] = make_float4(c0.z, c1.z, c0.w, c1.w);
         }
-      }
-      if (lane < nmp) {
-        const V4 mo = s_moff[wid][lane];
-        const T e2 = s_meps[wid][lane];
-        T nu[NM];
-#pragma unroll
-        for (int t = 0; t < NM; t++) nu[t] = (T)0;
-        for (int sk = 0; sk < cnt; sk++)
-          AOrd<P>::template src<T>(fma(s_sx[wid][sk][0], mo.w, mo.x), fma(s_sx[wid][sk][1], mo.w, mo.y),
-                                   fma(s_sx[wid][sk][2], mo.w, mo.z), e2, s_sl[wid][sk][0], s_sl[wid][sk][1],
-                                   s_sl[wid][sk][2], nu);
-        float* dst = w.nuc + (int64_t)s_midx[wid][lane] * NM;
-#pragma unroll
-        for (int t = 0; t < NM; t++) atomicAdd(dst + t, (float)nu[t]);
+        __syncwarp();
+        if (act) {
+          const float2* cf = reinterpret_cast<const float2*>(&s_coef[wid][0]);
+          const float2 x2 = make_float2(xi, xi), y2 = make_float2(yi, yi), z2 = make_float2(zi, zi);
+          const float2 l2x = make_float2(lx, lx), l2y = make_float2(ly, ly), l2z = make_float2(lz, lz);
+          for (int q = 0; q < npair; q++) {
+            const float4 m0 = s_moff[wid][2 * q];
+            const bool two = 2 * q + 1 < nmp;
+            const float4 m1 = two ? s_moff[wid][2 * q + 1] : make_float4(0.f, 0.f, 0.f, 1.f);
+            const float2 sc = make_float2(m0.w, m1.w);
+            const float2 e2 = make_float2(s_meps[wid][2 * q], two ? s_meps[wid][2 * q + 1] : 1.f);
+            float2 ox = make_float2(0.f, 0.f), oy = ox, oz = ox;
+            AOrd<P>::self2(&cf[q * NBS], __ffma2_rn(x2, sc, make_float2(m0.x, m1.x)),
+                           __ffma2_rn(y2, sc, make_float2(m0.y, m1.y)), __ffma2_rn(z2, sc, make_float2(m0.z, m1.z)),
+                           e2, l2x, l2y, l2z, ox, oy, oz);
+            // back to box units: times 2^level of each cell
+            mx = fma(ox.x, m0.w, fma(ox.y, m1.w, mx));
+            my = fma(oy.x, m0.w, fma(oy.y, m1.w, my));
+            mz = fma(oz.x, m0.w, fma(oz.y, m1.w, mz));
+          }
+        }
+      } else {
+        for (int t = lane; t < nmp * C4; t += 32) {
+          const int q = t / C4, r = t - q * C4;
+          sdst[t] = gsrc[(int64_t)s_midx[wid][q] * C4 + r];
+        }
+        __syncwarp();
+        if (act) {
+          for (int q = 0; q < nmp; q++) {
+            const V4 mo = s_moff[wid][q];
+            T ox = 0, oy = 0, oz = 0;
+            AOrd<P>::template self<T>(&s_coef[wid][q * NBS], fma(xi, mo.w, mo.x), fma(yi, mo.w, mo.y),
+                                      fma(zi, mo.w, mo.z), s_meps[wid][q], lx, ly, lz, ox, oy, oz);
+            mx = fma(ox, mo.w, mx);
+            my = fma(oy, mo.w, my);
+            mz = fma(oz, mo.w, mz);
+          }
+        }
       }
       __syncwarp();
     };
-    int top = 1;
-    if (lane == 0) stk[0] = box;
-    __syncwarp();
-    bool overflow = false;
-    while (top > 0) {
-      const int nb = min(32, top);
-      const int base = top - nb;
-      top = base;
-      int c = -1;
-      int4 ca = make_int4(0, 0, 0, 0), cb = make_int4(0, 0, 0, 0);
-      if (lane < nb) {
-        c = stk[base + lane];
-        ca = tr.cA[c];
-        cb = tr.cB[c];
-      }
+    auto on_p2p = [&](bool mine, const int4 ca, const int4 cb, int kx, int ky, int kz, int lvl) {
+      const unsigned pm = __ballot_sync(FULL, mine);
+      if (!pm) return;
+      const int ncl = mine ? cb.y : 0;
+      const int pre = warp_excl_scan(ncl, lane);
+      const int total = __shfl_sync(FULL, pre + ncl, 31);
+      s_pfx[wid][lane] = pre;
+      s_pst[wid][lane] = cb.x;
+      s_plev[wid][lane] = lvl;
+      s_pcen[wid][lane] = ca;
+      s_poff[wid][lane][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
+      s_poff[wid][lane][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
+      s_poff[wid][lane][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
       __syncwarp();
-      int cls = NB_CELL_NONE, kx = 0, ky = 0, kz = 0;
-      const int lvl = ca.w & 0xff, nch = ca.w >> 8;
-      if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, kx, ky, kz);
-      {
-        const int nc = (cls == NB_CELL_OPEN) ? nch : 0;
-        const int pre = warp_excl_scan(nc, lane);
-        const int tot = __shfl_sync(FULL, pre + nc, 31);
-        if (top + tot > w.stack_cap) {
-          overflow = true;
-          break;
+      for (int b0 = 0; b0 < total; b0 += 32) {
+        const int t = b0 + lane;
+        int jsrc = -1;
+        if (t < total) {
+          int lo = 0, hi = 31;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_pfx[wid][mid] <= t) lo = mid; else hi = mid - 1;
+          }
+          const int q = lo;
+          const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
+          V4 v = w.src[j];
+          T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
+          if (s_plev[wid][q] < w.le) {
+            const int4 pc = s_pcen[wid][q];
+            int jx, jy, jz;
+            particle_image(tr.skeys[j], w.le, gd, jx, jy, jz);
+            ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
+            oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
+            oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;
+          }
+          v.x = v.x + ox;
+          v.y = v.y + oy;
+          v.z = v.z + oz;
+          s_src[wid][lane] = v;
+          jsrc = j;
         }
-        for (int q = 0; q < nc; q++) stk[top + pre + q] = cb.z + q;
-        top += tot;
+        s_jidx[wid][lane] = jsrc;
+        __syncwarp();
+        const int nn = min(32, total - b0);
+        // diagonal pairing: in round k lane l takes source (l+k) mod 32 and
+        // passes the source-side term to the lane that owns that source
+        T sx = 0, sy = 0, sz = 0;
+        for (int k = 0; k < 32; k++) {
+          const int q = (lane + k) & 31;
+          T wx = 0, wy = 0, wz = 0;
+          if (act && q < nn && s_jidx[wid][q] != i) {
+            const V4 sv = s_src[wid][q];
+            const T dx = sv.x - xi, dy = sv.y - yi, dz = sv.z - zi;
+            const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+            const T inv = nbody_rsqrt(r2);
+            const T f = (inv * inv) * inv;
+            const T g5 = f * (inv * inv) * (T)3;
+            const T rl = fma(dx, lx, fma(dy, ly, dz * lz));
+            const T a = sv.w * f, bb = sv.w * g5 * rl;
+            wx = fma(a, lx, -bb * dx);
+            wy = fma(a, ly, -bb * dy);
+            wz = fma(a, lz, -bb * dz);
+          }
+          mx -= wx;
+          my -= wy;
+          mz -= wz;
+          const int from = (lane - k) & 31;
+          sx += __shfl_sync(FULL, wx, from);
+          sy += __shfl_sync(FULL, wy, from);
+          sz += __shfl_sync(FULL, wz, from);
+        }
+        if (lane < nn) {
+          const int j = s_jidx[wid][lane];
+          atomicAdd(&w.mu[j], (double)sx);
+          atomicAdd(&w.mu[tr.n + j], (double)sy);
+          atomicAdd(&w.mu[2 * tr.n + j], (double)sz);
+        }
         __syncwarp();
       }
-      const unsigned mm = __ballot_sync(FULL, cls == NB_CELL_M2P);
-      if (mm) {
-        if (cls == NB_CELL_M2P) {
-          const int pos = qn + __popc(mm & ltmask);
-          const T sc = (T)(1 << lvl);
-          s_midx[wid][pos] = c;
-          V4 mo;
-          mo.x = -((T)(ca.x - kx * NB_PBOX - gd.x) * scale) * sc;
-          mo.y = -((T)(ca.y - ky * NB_PBOX - gd.y) * scale) * sc;
-          mo.z = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
-          mo.w = sc;
-          s_moff[wid][pos] = mo;
-          s_meps[wid][pos] = eps2 * (sc * sc);
-        }
-        qn += __popc(mm);
-        if (qn >= 32) {
-          __syncwarp();
-          m2p_chunk(32);
-          if (lane < qn - 32) {
-            s_midx[wid][lane] = s_midx[wid][32 + lane];
-            s_moff[wid][lane] = s_moff[wid][32 + lane];
-            s_meps[wid][lane] = s_meps[wid][32 + lane];
-          }
-          qn -= 32;
-        }
-        __syncwarp();
-      }
-      const unsigned pm = __ballot_sync(FULL, cls == NB_CELL_P2P);
-      if (pm) {
-        const int ncl = (cls == NB_CELL_P2P) ? cb.y : 0;
-        const int pre = warp_excl_scan(ncl, lane);
-        const int total = __shfl_sync(FULL, pre + ncl, 31);
-        s_pfx[wid][lane] = pre;
-        s_pst[wid][lane] = cb.x;
-        s_plev[wid][lane] = lvl;
-        s_pcen[wid][lane] = ca;
-        s_poff[wid][lane][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
-        s_poff[wid][lane][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
-        s_poff[wid][lane][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
-        __syncwarp();
-        for (int b0 = 0; b0 < total; b0 += 32) {
-          const int t = b0 + lane;
-          int jsrc = -1;
-          if (t < total) {
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-              const int mid = (lo + hi + 1) >> 1;
-              if (s_pfx[wid][mid] <= t) lo = mid; else hi = mid - 1;
-            }
-            const int q = lo;
-            const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
-            V4 v = w.src[j];
-            T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
-            if (s_plev[wid][q] < w.le) {
-              const int4 pc = s_pcen[wid][q];
-              int jx, jy, jz;
-              particle_image(tr.skeys[j], w.le, gd, jx, jy, jz);
-              ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
-              oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
-              oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;
-            }
-            v.x = v.x + ox;
-            v.y = v.y + oy;
-            v.z = v.z + oz;
-            s_src[wid][lane] = v;
-            jsrc = j;
-          }
-          s_jidx[wid][lane] = jsrc;
-          __syncwarp();
-          const int nn = min(32, total - b0);
-          // diagonal pairing: in round k lane l takes source (l+k) mod 32 and
-          // passes the source-side term to the lane that owns that source
-          T sx = 0, sy = 0, sz = 0;
-          for (int k = 0; k < 32; k++) {
-            const int q = (lane + k) & 31;
-            T wx = 0, wy = 0, wz = 0;
-            if (act && q < nn && s_jidx[wid][q] != i) {
-              const V4 s = s_src[wid][q];
-              const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-              const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-              const T inv = nbody_rsqrt(r2);
-              const T f = (inv * inv) * inv;
-              const T g5 = f * (inv * inv) * (T)3;
-              const T rl = fma(dx, lx, fma(dy, ly, dz * lz));
-              const T a = s.w * f, b = s.w * g5 * rl;
-              wx = fma(a, lx, -b * dx);
-              wy = fma(a, ly, -b * dy);
-              wz = fma(a, lz, -b * dz);
-            }
-            mx -= wx;
-            my -= wy;
-            mz -= wz;
-            const int from = (lane - k) & 31;
-            sx += __shfl_sync(FULL, wx, from);
-            sy += __shfl_sync(FULL, wy, from);
-            sz += __shfl_sync(FULL, wz, from);
-          }
-          if (lane < nn) {
-            const int j = s_jidx[wid][lane];
-            atomicAdd(&w.mu[j], (double)sx);
-            atomicAdd(&w.mu[tr.n + j], (double)sy);
-            atomicAdd(&w.mu[2 * tr.n + j], (double)sz);
-          }
-          __syncwarp();
-        }
-      }
-    }
-    if (overflow) {
+    };
+    const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, eps2, stk, w.stack_cap, lane,
+                                      s_midx[wid], s_moff[wid], s_meps[wid], on_m2p, on_p2p);
+    if (!ok) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
     }
-    if (qn > 0) m2p_chunk(qn);
     if (act) {
       atomicAdd(&w.mu[i], (double)mx);
       atomicAdd(&w.mu[tr.n + i], (double)my);
       atomicAdd(&w.mu[2 * tr.n + i], (double)mz);
     }
+  }
+}
+
+// Source side: the cotangents of the scaled moments of every cell a group
+// expands, summed over the group's sinks by the lane that owns the cell, added
+// to the cell with 16-byte vector atomics (stride NMP = NM rounded up to 4).
+template <int P, int WARPS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB) adj_src_kernel(AdjArgs<float> w) {
+  using T = float;
+  using V4 = float4;
+  constexpr int NM = AOrd<P>::NM, NMP = (NM + 3) & ~3;
+  __shared__ V4 s_moff[WARPS][64];
+  __shared__ T s_meps[WARPS][64];
+  __shared__ int s_midx[WARPS][64];
+  __shared__ V4 s_sx[WARPS][32];  // sink position (xyz) and, in w, unused
+  __shared__ V4 s_sl[WARPS][32];  // sink lambda
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const DevTree& tr = w.tr;
+  int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
+  const T scale = (T)kScale;
+
+  while (true) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(w.group_ctr, 1);
+    g = __shfl_sync(FULL, g, 0);
+    if (g >= tr.ngroup) break;
+    const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
+    const int cnt = ga.y, box = ga.z;
+    const T eps2 = w.eps2[box];
+    const bool act = lane < cnt;
+    const int i = ga.x + (act ? lane : 0);
+    {
+      V4 o = w.src[i];
+      int4 la = tr.cA[tr.sleaf[i]];
+      V4 x, l;
+      x.x = o.x + (T)(la.x - gd.x) * scale;
+      x.y = o.y + (T)(la.y - gd.y) * scale;
+      x.z = o.z + (T)(la.z - gd.z) * scale;
+      x.w = 0.f;
+      l.x = act ? w.lam[i] : 0.f;
+      l.y = act ? w.lam[tr.n + i] : 0.f;
+      l.z = act ? w.lam[2 * tr.n + i] : 0.f;
+      l.w = 0.f;
+      s_sx[wid][lane] = x;
+      s_sl[wid][lane] = l;
+    }
+    __syncwarp();
+    auto on_m2p = [&](int nmp) {
+      if (lane < nmp) {
+        const V4 mo = s_moff[wid][lane];
+        const T e2 = s_meps[wid][lane];
+        T nu[NMP];
+#pragma unroll
+        for (int t = 0; t < NMP; t++) nu[t] = (T)0;
+        for (int sk = 0; sk < cnt; sk++) {
+          const V4 x = s_sx[wid][sk], l = s_sl[wid][sk];
+          AOrd<P>::template src<T>(fma(x.x, mo.w, mo.x), fma(x.y, mo.w, mo.y), fma(x.z, mo.w, mo.z), e2, l.x,
+                                   l.y, l.z, nu);
+        }
+        float4* dst = reinterpret_cast<float4*>(w.nuc + (int64_t)s_midx[wid][lane] * NMP);
+#pragma unroll
+        for (int t = 0; t < NMP / 4; t++) atomicAdd(dst + t, make_float4(nu[4 * t], nu[4 * t + 1], nu[4 * t + 2], nu[4 * t + 3]));
+      }
+      __syncwarp();
+    };
+    auto on_p2p = [&](bool, const int4, const int4, int, int, int, int) {};
+    const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, eps2, stk, w.stack_cap, lane,
+                                      s_midx[wid], s_moff[wid], s_meps[wid], on_m2p, on_p2p);
+    if (!ok && lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
   }
 }
 
@@ -500,7 +606,7 @@ __global__ void adj_field_p2m_kernel(DevTree tr, int le, const double* __restric
 template <int P>
 __global__ void adj_unscale_kernel(int ncell, const int4* __restrict__ cA, const float* __restrict__ nuc,
                                    double* __restrict__ nu) {
-  constexpr int NM = AOrd<P>::NM;
+  constexpr int NM = AOrd<P>::NM, NMP = (NM + 3) & ~3;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
     const int lvl = cA[c].w & 0xff;
     int t = 0;
@@ -514,7 +620,7 @@ __global__ void adj_unscale_kernel(int ncell, const int4* __restrict__ cA, const
           for (int q = 2; q <= nx; q++) f *= q;
           for (int q = 2; q <= ny; q++) f *= q;
           for (int q = 2; q <= nz; q++) f *= q;
-          nu[(int64_t)c * NM + t] = (double)nuc[(int64_t)c * NM + t] * sc / f;
+          nu[(int64_t)c * NM + t] = (double)nuc[(int64_t)c * NMP + t] * sc / f;
         }
     }
   }
@@ -624,7 +730,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
     g_apar_done[dev] = true;
   }
   adj_prep_kernel<<<gridv(tr.n, 256), 256, 0, s>>>(tr.n, tr.perm, lam, B.lam_s, B.mu);
-  if ((e = cudaMemsetAsync(B.nuc, 0, sizeof(float) * (size_t)tr.ncell * NM, s))) return e;
+  if ((e = cudaMemsetAsync(B.nuc, 0, sizeof(float) * (size_t)tr.ncell * ((NM + 3) & ~3), s))) return e;
   if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;
   nb_launch_counter += 1;
   {
@@ -643,16 +749,21 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
     a.mu = B.mu;
     a.nuc = B.nuc;
     a.status = status;
-    constexpr int W = 4;
+    // source side, then (group counter reset) sink side
     int occ = 0;
-#define NB_ADJW(P)                                                                                         \
-  {                                                                                                        \
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adj_walk_kernel<float, P, W>, W * 32, 0))) \
-      return e;                                                                                            \
-    int grid = nsm * (occ > 0 ? occ : 1);                                                                  \
-    if (grid * W > max_blocks * 8) grid = max_blocks * 8 / W;                                              \
-    adj_walk_kernel<float, P, W><<<grid, W * 32, 0, s>>>(a);                                               \
-    break;                                                                                                 \
+#define NB_ADJ_GRID(KER, W)                                                                     \
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, KER, (W) * 32, 0))) return e;    \
+  grid = nsm * (occ > 0 ? occ : 1);                                                             \
+  if (grid * (W) > max_blocks * 8) grid = max_blocks * 8 / (W);
+#define NB_ADJW(P)                                                                               \
+  {                                                                                              \
+    int grid = 0;                                                                                \
+    NB_ADJ_GRID((adj_src_kernel<P, 4, 4>), 4)                                                    \
+    adj_src_kernel<P, 4, 4><<<grid, 128, 0, s>>>(a);                                             \
+    if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;                         \
+    NB_ADJ_GRID((adj_sink_kernel<P, 4, 3, true>), 4)                                             \
+    adj_sink_kernel<P, 4, 3, true><<<grid, 128, 0, s>>>(a);                                      \
+    break;                                                                                       \
   }
     switch (order) {
       case 0: NB_ADJW(0)
@@ -662,7 +773,8 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
       default: NB_ADJW(4)
     }
 #undef NB_ADJW
-    nb_launch_counter += 1;
+#undef NB_ADJ_GRID
+    nb_launch_counter += 2;
   }
   if ((e = cudaGetLastError())) return e;
   if (pe > 0) {

@@ -581,7 +581,7 @@ int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   const int nm = nb_adj_coef_nm(p.order);
   NB_CU(t->a_lam.ensure(12 * n));
   NB_CU(t->a_mu.ensure(24 * n));
-  NB_CU(t->a_nuc.ensure(4 * (int64_t)t->ncell * nm));
+  NB_CU(t->a_nuc.ensure(4 * (int64_t)t->ncell * ((nm + 3) & ~3)));
   NB_CU(t->a_nu.ensure(8 * (int64_t)t->ncell * nm));
   if (p.ewald_order > 0) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;

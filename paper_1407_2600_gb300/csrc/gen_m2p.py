@@ -421,45 +421,77 @@ def emit_m2p_adj_self(p):
     lam = ("lx", "ly", "lz")
     # q_c = sum_l lam_l mu_{c-e_l}, so that (H_j lam)_k = sum_a B_{j,a} q_{a-e_k}
     for i, c in enumerate(mon):
-        if sum(c) > p - 1:
+        if sum(c) > p - 1 or sum(c) == 0:
             continue
-        L.append("  T q%d = T(0);" % i)
-    for i, c in enumerate(mon):
-        if sum(c) > p - 1:
-            continue
+        first = True
         for d in range(3):
             if c[d] > 0:
                 cc = list(c)
                 cc[d] -= 1
-                L.append("  q%d = fma(%s, m%d, q%d);" % (i, lam[d], mi[tuple(cc)], i))
-    for j in range(p + 1):
-        L.append("  T S%d = T(0), G%dx = T(0), G%dy = T(0), G%dz = T(0), H%dx = T(0), H%dy = T(0), H%dz = T(0);"
-                 % ((j,) * 7))
+                mk = mi[tuple(cc)]
+                if first:
+                    L.append("  T q%d = %s;" % (i, lam[d] if mk == 0 else "%s * m%d" % (lam[d], mk)))
+                    first = False
+                else:
+                    L.append("  q%d = fma(%s, m%d, q%d);" % (i, lam[d], mk, i))
+    # accumulators start at their first term; terms of the unit monomial are
+    # plain additions; G_0 and H_0 vanish and are not formed
+    started = set()
+
+    def acc(name, mono, qv=False):
+        src = ("q%d" if qv else "m%d") % mono
+        if name not in started:
+            started.add(name)
+            return "    %s = %s;" % (name, "b" if (mono == 0 and not qv) else "b * %s" % src)
+        if mono == 0 and not qv:
+            return "    %s += b;" % name
+        return "    %s = fma(b, %s, %s);" % (name, src, name)
+
+    body = []
     for t, (j, a) in enumerate(sl):
+        body.append((t, j, a))
+    # declare every accumulator up front (first terms assign)
+    decl = []
+    for (t, j, a) in body:
+        for nm in ["S%d" % j] + ["G%d%s" % (j, c) for d, c in enumerate("xyz") if a[d] > 0] + \
+                  ["H%d%s" % (j, c) for d, c in enumerate("xyz") if a[d] > 0 and sum(a) > 1]:
+            if nm not in decl:
+                decl.append(nm)
+    L.append("  T %s;" % ", ".join(decl))
+    for (t, j, a) in body:
         L.append("  { const T b = B[%d];" % t)
-        L.append("    S%d = fma(b, m%d, S%d);" % (j, mi[a], j))
+        L.append(acc("S%d" % j, mi[a]))
         for d, ax in enumerate("xyz"):
             if a[d] > 0:
                 par = list(a)
                 par[d] -= 1
-                L.append("    G%d%s = fma(b, m%d, G%d%s);" % (j, ax, mi[tuple(par)], j, ax))
+                L.append(acc("G%d%s" % (j, ax), mi[tuple(par)]))
                 if sum(par) > 0:
-                    L.append("    H%d%s = fma(b, q%d, H%d%s);" % (j, ax, mi[tuple(par)], j, ax))
+                    L.append(acc("H%d%s" % (j, ax), mi[tuple(par)], qv=True))
         L.append("  }")
     L.append("  const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz));")
-    L.append("  T ax = T(0), ay = T(0), az = T(0);")
+    L.append("  T ax = ox, ay = oy, az = oz;")
     for j in range(p + 1):
+        hasG = ("G%dx" % j) in decl
+        hasH = ("H%dx" % j) in decl
         L.append("  { const T a1 = F%d * S%d;  // F_{j+1} S_j" % (j + 1, j))
-        L.append("    const T gl = fma(G%dx, lx, fma(G%dy, ly, G%dz * lz));" % (j, j, j))
-        L.append("    const T c1 = fma(F%d * S%d, rl, F%d * gl);  // R_k coefficient" % (j + 2, j, j + 1))
-        L.append("    const T c2 = F%d * rl;  // G_{j,k} coefficient" % (j + 1))
+        if hasG:
+            L.append("    const T gl = fma(G%dx, lx, fma(G%dy, ly, G%dz * lz));" % (j, j, j))
+            L.append("    const T c1 = fma(F%d * S%d, rl, F%d * gl);  // R_k coefficient" % (j + 2, j, j + 1))
+            L.append("    const T c2 = F%d * rl;  // G_{j,k} coefficient" % (j + 1))
+        else:
+            L.append("    const T c1 = F%d * S%d * rl;  // R_k coefficient" % (j + 2, j))
         for ax, Rv, lv in (("x", "Rx", "lx"), ("y", "Ry", "ly"), ("z", "Rz", "lz")):
-            L.append("    a%s = fma(a1, %s, fma(%s, c1, fma(c2, G%d%s, fma(F%d, H%d%s, a%s))));"
-                     % (ax, lv, Rv, j, ax, j, j, ax, ax))
+            e = "a%s" % ax
+            if hasH:
+                e = "fma(F%d, H%d%s, %s)" % (j, j, ax, e)
+            if hasG:
+                e = "fma(c2, G%d%s, %s)" % (j, ax, e)
+            L.append("    a%s = fma(a1, %s, fma(%s, c1, %s));" % (ax, lv, Rv, e))
         L.append("  }")
-    L.append("  ox += ax;")
-    L.append("  oy += ay;")
-    L.append("  oz += az;")
+    L.append("  ox = ax;")
+    L.append("  oy = ay;")
+    L.append("  oz = az;")
     L.append("}")
     return "\n".join(L)
 
@@ -657,12 +689,174 @@ def emit_field_adj(pe):
     return "\n".join(L)
 
 
+# ---- packed FP32 pairs from the scalar emitters -----------------------------------
+# The scalar emitters above write a small C subset: declarations and
+# assignments of T values built from fma(a, b, c), products a * b, constants
+# T(c), nbody_rsqrt(x), names and B[i] / nu[i] elements.  pack() rewrites such
+# a function for float2 operands, one pair instruction per scalar operation in
+# the same order, so each half of the result is bitwise the scalar FP32 one.
+def _flit(v):
+    """a float literal for the value of the decimal string v"""
+    t = "%.9g" % float(v)
+    if not any(ch in t for ch in ".en"):
+        t += ".0"
+    return t + "f"
+
+
+def _tokens(src):
+    import re
+    tok = re.compile(r"\s*(?:([A-Za-z_][A-Za-z0-9_]*)|([0-9][0-9.eE+\-]*)|(\+=|[()\[\],*=;{}+\-]))")
+    out, pos = [], 0
+    while pos < len(src):
+        m = tok.match(src, pos)
+        if not m or m.end() == pos:
+            if src[pos:].strip() == "":
+                break
+            raise ValueError("cannot tokenize: %r" % src[pos:])
+        out.append(m.group(1) or m.group(2) or m.group(3))
+        pos = m.end()
+    return out
+
+
+class _P:
+    def __init__(self, toks):
+        self.t, self.i = toks, 0
+
+    def peek(self):
+        return self.t[self.i] if self.i < len(self.t) else None
+
+    def take(self, want=None):
+        v = self.t[self.i]
+        if want is not None and v != want:
+            raise ValueError("expected %s got %s" % (want, v))
+        self.i += 1
+        return v
+
+    def expr(self):
+        e = self.unary()
+        while self.peek() == "*":
+            self.take()
+            e = "__fmul2_rn(%s, %s)" % (e, self.unary())
+        return e
+
+    def unary(self):
+        if self.peek() == "-":
+            self.take()
+            return "__fmul2_rn(make_float2(-1.0f, -1.0f), %s)" % self.unary()
+        return self.primary()
+
+    def number(self):
+        sign = ""
+        if self.peek() == "-":
+            self.take()
+            sign = "-"
+        return sign + _flit(self.take())
+
+    def primary(self):
+        v = self.take()
+        if v == "fma":
+            self.take("(")
+            a = self.expr()
+            self.take(",")
+            b = self.expr()
+            self.take(",")
+            c = self.expr()
+            self.take(")")
+            return "__ffma2_rn(%s, %s, %s)" % (a, b, c)
+        if v == "T":
+            self.take("(")
+            c = self.number()
+            self.take(")")
+            return "make_float2(%s, %s)" % (c, c)
+        if v == "nbody_rsqrt":
+            self.take("(")
+            a = self.expr()
+            self.take(")")
+            return "nbody_rsqrt2(%s)" % a
+        if v == "(":
+            e = self.expr()
+            self.take(")")
+            return e
+        if self.peek() == "[":
+            self.take("[")
+            k = self.take()
+            self.take("]")
+            return "%s[%s]" % (v, k)
+        if v[0].isdigit():
+            c = _flit(v)
+            return "make_float2(%s, %s)" % (c, c)
+        return v
+
+
+def _pack_decls(toks):
+    """T a = e, b, ...  ->  float2 a = e', b, ..."""
+    P = _P(toks)
+    parts = []
+    while P.peek() is not None:
+        name = P.take()
+        if P.peek() == "=":
+            P.take("=")
+            parts.append("%s = %s" % (name, P.expr()))
+        else:
+            parts.append(name)
+        if P.peek() == ",":
+            P.take()
+    return ", ".join(parts)
+
+
+def pack(code, name_from, name_to):
+    out = []
+    lines = code.split("\n")
+    i = 0
+    while lines[i].startswith("template"):
+        i += 1
+    sig = []
+    while True:
+        sig.append(lines[i])
+        if lines[i].rstrip().endswith("{"):
+            break
+        i += 1
+    sig = " ".join(x.strip() for x in sig)
+    sig = sig.replace(name_from, name_to).replace("const T*", "const float2*").replace("T*", "float2*")
+    sig = sig.replace("T&", "float2&").replace("(T ", "(float2 ").replace(", T ", ", float2 ")
+    out.append(sig)
+    for ln in lines[i + 1:]:
+        body = ln.split("//")[0].rstrip()
+        ind = body[: len(body) - len(body.lstrip())]
+        st = body.strip()
+        if st in ("", "}"):
+            out.append(body)
+            continue
+        pre = ""
+        if st.startswith("{ "):
+            pre, st = "{ ", st[2:]
+        assert st.endswith(";"), st
+        st = st[:-1]
+        if st.startswith("const T "):
+            out.append("%s%sconst float2 %s;" % (ind, pre, _pack_decls(_tokens(st[len("const T "):]))))
+        elif st.startswith("T "):
+            out.append("%s%sfloat2 %s;" % (ind, pre, _pack_decls(_tokens(st[2:]))))
+        elif "+=" in st:
+            lhs, rhs = st.split("+=")
+            out.append("%s%s%s = __fadd2_rn(%s, %s);" % (ind, pre, lhs.strip(), lhs.strip(), _P(_tokens(rhs)).expr()))
+        else:
+            lhs, rhs = st.split("=", 1)
+            out.append("%s%s%s = %s;" % (ind, pre, lhs.strip(), _P(_tokens(rhs)).expr()))
+    return "\n".join(out)
+
+
 def generate_adjoint():
     out = ["// Generated by gen_m2p.py -- do not edit by hand.",
            "// Reverse-mode (adjoint) kernels of the M2P, M2M, P2M and image-field expansions.",
            "#pragma once", ""]
+    out.append("__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {")
+    out.append("  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));")
+    out.append("}")
+    out.append("")
     for p in range(5):
         out.append(emit_m2p_adj_self(p))
+        out.append("")
+        out.append(pack(emit_m2p_adj_self(p), "m2p_adj_self_p%d" % p, "m2p2_adj_self_p%d" % p))
         out.append("")
         out.append(emit_m2p_adj_src(p))
         out.append("")

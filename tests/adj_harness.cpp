@@ -74,6 +74,14 @@ template <int P> struct K2;
                      float2& az) {                                                                           \
       m2p2_p##P(B, x, y, z, e, ax, ay, az);                                                                  \
     }                                                                                                        \
+    static void self1(const float* B, float x, float y, float z, float e, float lx, float ly, float lz,      \
+                      float& ox, float& oy, float& oz) {                                                    \
+      m2p_adj_self_p##P<float>(B, x, y, z, e, lx, ly, lz, ox, oy, oz);                                       \
+    }                                                                                                        \
+    static void self2(const float2* B, float2 x, float2 y, float2 z, float2 e, float2 lx, float2 ly,         \
+                      float2 lz, float2& ox, float2& oy, float2& oz) {                                      \
+      m2p2_adj_self_p##P(B, x, y, z, e, lx, ly, lz, ox, oy, oz);                                             \
+    }                                                                                                        \
   };
 K2D(0) K2D(1) K2D(2) K2D(3) K2D(4)
 
@@ -222,6 +230,18 @@ void run_m2p2() {
   K2<P>::fwd2(B2, make_float2(x0, x1), make_float2(y0, y1), make_float2(z0, z1), make_float2(e0, e1), ax, ay, az);
   if (ax.x != ax0 || ay.x != ay0 || az.x != az0 || ax.y != ax1 || ay.y != ay1 || az.y != az1) {
     std::printf("FAIL m2p2_p%d differs from m2p_p%d\n", P, P);
+    std::exit(1);
+  }
+  // the packed reverse-mode sink term likewise (two cells, one sink's lambda)
+  const float lx = (float)U(), ly = (float)U(), lz = (float)U();
+  float ox0 = 0.5f, oy0 = 0.25f, oz0 = -1.0f, ox1 = 0.5f, oy1 = 0.25f, oz1 = -1.0f;
+  float2 ox = make_float2(ox0, ox1), oy = make_float2(oy0, oy1), oz = make_float2(oz0, oz1);
+  K2<P>::self1(B0, x0, y0, z0, e0, lx, ly, lz, ox0, oy0, oz0);
+  K2<P>::self1(B1, x1, y1, z1, e1, lx, ly, lz, ox1, oy1, oz1);
+  K2<P>::self2(B2, make_float2(x0, x1), make_float2(y0, y1), make_float2(z0, z1), make_float2(e0, e1),
+               make_float2(lx, lx), make_float2(ly, ly), make_float2(lz, lz), ox, oy, oz);
+  if (ox.x != ox0 || oy.x != oy0 || oz.x != oz0 || ox.y != ox1 || oy.y != oy1 || oz.y != oz1) {
+    std::printf("FAIL m2p2_adj_self_p%d differs from m2p_adj_self_p%d\n", P, P);
     std::exit(1);
   }
 }
