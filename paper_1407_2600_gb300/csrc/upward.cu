@@ -60,6 +60,13 @@ __device__ __forceinline__ double mul_pow2(double x, int k) {
   return x * __longlong_as_double((long long)(1023 + k) << 52);
 }
 
+// order |n| of the moment at storage index t (orders are stored in sequence)
+__host__ __device__ constexpr int order_of(int t) {
+  int o = 0;
+  while ((o + 1) * (o + 2) * (o + 3) / 6 <= t) o++;
+  return o;
+}
+
 // Reduced coefficients in the cell's own length unit h = 2^-level: with
 // R' = R/h and eps' = eps/h the expansion terms are O(1) for every accepted
 // cell (R' >= 1/theta), so FP32 intermediates cannot overflow however deep the
@@ -69,12 +76,8 @@ template <int P, typename T>
 __device__ __forceinline__ void finish_cell(int c, int level, const double* M, T* __restrict__ coef) {
   constexpr int NM = Ord<P>::NM;
   double Ms[NM];
-  int t = 0;
 #pragma unroll
-  for (int o = 0; o <= P; o++) {
-#pragma unroll
-    for (int q = 0; q < (o + 1) * (o + 2) / 2; q++, t++) Ms[t] = mul_pow2(M[t], level * o);
-  }
+  for (int t = 0; t < NM; t++) Ms[t] = mul_pow2(M[t], level * order_of(t));
   double B[Ord<P>::NB];
   Ord<P>::reduce(Ms, B);
   T* dst = coef + (int64_t)c * Ord<P>::NBS;
@@ -138,7 +141,15 @@ leaf_moments_kernel(const uint32_t* __restrict__ order, const int* __restrict__ 
   }
 }
 
-// M2M of the parents of one level from their daughters (formed by earlier launches)
+// M2M of the parents of one level from their daughters (formed by earlier
+// launches).  A wide level gives each parent one thread, which shifts its
+// daughters one after another.  GB300's FP64 pipe takes a warp instruction
+// at a time however few lanes are active, so on a narrow level (near the
+// root, or the deep levels of a halo) that serial chain would set the time;
+// there a warp takes four parents, one lane per daughter shifts its moments
+// and the daughters' terms are summed across lanes.
+constexpr int kWideLevel = 12288;
+
 template <int P, typename T>
 __global__ void __launch_bounds__(128)
 level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __restrict__ r,
@@ -146,6 +157,49 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
                      T* __restrict__ coef) {
   constexpr int NM = Ord<P>::NM;
   const int lo = r[j], hi = r[j + 1];
+  if (hi - lo < kWideLevel) {
+    const int lane = threadIdx.x & 31, slot = lane >> 3, d = lane & 7;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int i0 = lo + 4 * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i0 < hi; i0 += 4 * nwarp) {
+      const int i = i0 + slot;
+      int b = -1, first = 0, nch = 0;
+      int4 pa = make_int4(0, 0, 0, 0);
+      if (i < hi) {
+        b = (int)order[i];
+        pa = cA[b];
+        first = cB[b].z;
+        nch = pa.w >> 8;
+      }
+      double M[NM];
+#pragma unroll
+      for (int t = 0; t < NM; t++) M[t] = 0.0;
+      if (d < nch) {
+        const int ch = first + d;
+        const int4 ca = cA[ch];
+        double Mc[NM];
+        const double* src = mom + (int64_t)ch * NM;
+#pragma unroll
+        for (int t = 0; t < NM; t++) Mc[t] = src[t];
+        Ord<P>::m2m(Mc, i2d_pow2(ca.x - pa.x, -23), i2d_pow2(ca.y - pa.y, -23), i2d_pow2(ca.z - pa.z, -23), M);
+      }
+      // sum over the eight daughter lanes of each parent (fixed order)
+#pragma unroll
+      for (int t = 0; t < NM; t++) {
+        double v = M[t];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        M[t] = v;
+      }
+      if (d == 0 && b >= 0) {
+        double* pd = mom + (int64_t)b * NM;
+#pragma unroll
+        for (int t = 0; t < NM; t++) pd[t] = M[t];
+        finish_cell<P, T>(b, pa.w & 0xff, M, coef);
+      }
+    }
+    return;
+  }
   for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
     const int b = (int)order[i];
     const int4 pa = cA[b];
@@ -260,7 +314,7 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int
   urange_kernel<<<1, 32, 0, s>>>(uhist, urange);
   nb_launch_counter += 1;
   const int g = gridc(ncell, 128);
-  const int gl = g < 152 * 8 ? g : 152 * 8;
+  const int gl = g < 152 * 4 ? g : 152 * 4;
 #define NB_UP(P, TT)                                                                                        \
   {                                                                                                         \
     leaf_moments_kernel<P, TT><<<g, 128, 0, s>>>(uorder, urange, cA, cB, spos, smass, n, mom, (TT*)coef);   \
