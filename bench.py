@@ -198,7 +198,7 @@ def run_gpu(args, rank, world, local_rank):
     n = len(x)
     pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
     mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
-    prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=4, ewald_grid=EWALD_GRID,
+    prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=4, ewald_grid=args.ewald_grid,
                     flags=nb.NBODY_FLAG_ASYNC)
     tree = nb.Tree(prm, pos)
     acc = tree.forces()
@@ -325,6 +325,10 @@ def run_gpu(args, rank, world, local_rank):
                        "forward = the same trajectory's KDK steps with checkpoint copies"}
         a = a_list[-1]
 
+    batched = None
+    if args.batched:
+        batched = run_batched(dev, max(2, args.steps // 2))
+
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -345,7 +349,7 @@ def run_gpu(args, rank, world, local_rank):
                                    "(2k-50k particles, c 5-15), L=250 Mpc/h, eps=spacing/30; one KDK step "
                                    "of dln a = 0.1 per step",
                        "n": n, "theta": THETA, "order": ORDER, "n_group": 32, "n_leaf": 16,
-                       "ewald_order": 4, "ewald_grid": EWALD_GRID, "precision": "FP32 interactions, "
+                       "ewald_order": 4, "ewald_grid": args.ewald_grid, "precision": "FP32 interactions, "
                        "FP64 positions/moments",
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "dp%d (independent realisations)" % world},
@@ -368,10 +372,70 @@ def run_gpu(args, rank, world, local_rank):
                                            "packed FP32x2 M2P, 8 x 2", "packed FP32x2 M2P, 4 x 5"]},
             "adjoint_forward_ratio": adj["ratio"] if adj else None,
             "adjoint": adj,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     tree.close()
     return 0
+
+
+def run_batched(dev, steps: int):
+    """Many independent small boxes in one tree build and one walk launch:
+    32 boxes of 48^3, 32 of 64^3 and 32 of 80^3 particles (28,311,552), each
+    its own periodic unit box with Zel'dovich initial conditions; theta 0.5,
+    quadrupole.  Times `steps` KDK steps (rebuild + forces + kicks + drift)
+    of the whole batch and one force evaluation."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    from paper_1407_2600_gb300 import ics
+    x, p, off, eps = ics.config_batched(1)
+    n = len(x)
+    pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
+    mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
+    del x, p
+    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=2, ewald_grid=4,
+                    flags=nb.NBODY_FLAG_ASYNC | nb.NBODY_FLAG_MAC_EDGE)
+    tree = nb.Tree(prm, pos, offsets=off.tolist(), eps=eps)
+    acc = tree.forces()
+    a = A_START
+    for _ in range(2):
+        a1 = a * math.exp(DLNA)
+        tree.kdk_step(mom, acc, a, a1)
+        a = a1
+    torch.cuda.synchronize()
+    tree.timing(reset=True)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    for _ in range(steps):
+        a1 = a * math.exp(DLNA)
+        tree.kdk_step(mom, acc, a, a1)
+        a = a1
+    e[1].record(stream)
+    e[2].record(stream)
+    tree.rebuild()
+    tree.forces(acc)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    rc = nb.nbody_check(tree.handle, nb._stream())
+    if rc != nb.NBODY_OK:
+        raise nb.NbodyError(rc, "batched steps")
+    tm = tree.timing(reset=True)
+    ms = e[0].elapsed_time(e[1]) / steps
+    fms = e[2].elapsed_time(e[3])
+    ev = max(tm["evaluations"], 1)
+    out = {"workload": "96 periodic boxes: 32 x 48^3 + 32 x 64^3 + 32 x 80^3 Zel'dovich (P~k^-2, rms 0.25 "
+                       "spacing, a=0.02), eps = spacing/30 per box; theta 0.5 (opening distance from the cell faces), "
+                       "quadrupole, groups within level-3 cells (ewald_grid 4); one tree build and one walk "
+                       "launch for all boxes",
+           "n": int(n), "nbox": 96, "steps": steps, "ms_per_kdk_step": ms, "updates_per_s": n / (ms * 1e-3),
+           "force_eval_ms": fms, "force_updates_per_s": n / (fms * 1e-3),
+           "phases_ms": {k: tm[k] / max(tm["builds"] if k in ("ms_sort", "ms_build", "ms_upward") else ev, 1)
+                         for k in ("ms_sort", "ms_build", "ms_upward", "ms_walk", "ms_periodic")},
+           "interactions_per_particle": {"p2p": tm["p2p"] / ev / n, "m2p": tm["m2p"] / ev / n},
+           "walk_variant": tm["walk_variant"], "graph_captured": False}
+    tree.close()
+    return out
 
 
 def main():
@@ -383,8 +447,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the 96-box batched workload")
     ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")
     ap.add_argument("--ng", type=int, default=NG, help="particles per axis (128 = the benchmark workload)")
+    ap.add_argument("--ewald-grid", type=int, default=EWALD_GRID,
+                    help="groups never straddle a cell of level ewald_grid - 1")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -57,7 +57,13 @@ enum {
 };
 
 enum { NBODY_MIXED = 0, NBODY_FP64 = 1 };
-enum { NBODY_FLAG_ASYNC = 1 };
+enum {
+  NBODY_FLAG_ASYNC = 1,
+  /* opening test with d measured from the cell's faces to the group box
+   * (box-to-box distance) instead of from the cell centre: a stricter test
+   * at the same theta (see nbody_params.theta) */
+  NBODY_FLAG_MAC_EDGE = 2
+};
 /* flags bits 8..11: walk launch variant + 1 to use instead of the autotuned
  * one (0 = autotune).  Mixed precision has variants 0..3 (one M2P per
  * instruction stream with 8 warps x 2 or 3 blocks per SM; two M2P at once in
@@ -69,7 +75,11 @@ enum { NBODY_FLAG_ASYNC = 1 };
 typedef struct {
   double eps;       /* Plummer softening length, box units (> 0); per-box
                        values may be given to nbody_build_tree_batched */
-  double theta;     /* opening angle of the multipole acceptance test */
+  double theta;     /* opening angle of the multipole acceptance test: a cell
+                       of side s is expanded for a group when s / d < theta,
+                       d the distance from the cell centre (or, with
+                       NBODY_FLAG_MAC_EDGE, from the cell's faces) to the
+                       group's bounding box, in integer units of 2^-23 */
   int order;        /* multipole order p of the cell expansions, 0..4 */
   int n_leaf;       /* cells with more particles are split (1..64) */
   int n_group;      /* sinks per group, 1..32 */

@@ -56,7 +56,7 @@ class TreeParams(C.Structure):
     _fields_ = [("eps", C.c_double), ("theta", C.c_double), ("order", C.c_int),
                 ("n_leaf", C.c_int), ("n_group", C.c_int), ("n_direct", C.c_int),
                 ("lmax", C.c_int), ("ewald", C.c_int), ("ew_level", C.c_int),
-                ("ew_grid", C.c_int)]
+                ("ew_grid", C.c_int), ("mac", C.c_int)]
 
 
 class EwaldCfg(C.Structure):
@@ -237,11 +237,13 @@ def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int = 64):
 
 
 def tree_params(eps, theta, order, n_leaf=16, n_group=32, n_direct=None, lmax=21, ewald=4,
-                ew_level=3, ew_grid=6) -> TreeParams:
+                ew_level=3, ew_grid=6, mac=0) -> TreeParams:
+    """mac 0: the opening test measures d from the cell centre to the group
+    box; mac 1: from the cell's faces (box to box)."""
     if n_direct is None:
         n_direct = 2 if order <= 2 else 4
     return TreeParams(eps, theta, order, n_leaf, n_group, n_direct, lmax, ewald, ew_level,
-                      ew_grid)
+                      ew_grid, mac)
 
 
 def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,

@@ -85,6 +85,8 @@ typedef struct {
                      per-group local expansion of the image field */
   int ew_level;   /* level of the fixed source cells of the image field */
   int ew_grid;    /* expansion points snap to the lattice 2^-ew_grid */
+  int mac;        /* distance d of the opening test: 0 from the cell centre to
+                     the group box, 1 from the cell's boundary to the group box */
 } or_tree_params;
 
 /* stats[0] = P2P pair interactions, stats[1] = M2P interactions,

@@ -347,7 +347,9 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
   for (int d = 0; d < 3; d++) {
     int64_t delta = 2 * centre_u(c->ix[d], c->level) - G->g2[d] - kimg[d] * PBOX;
     int64_t ad = delta < 0 ? -delta : delta;
-    int64_t dd = ad - G->w2[d];
+    /* d is measured from the cell centre, or (mac = 1) from the cell's
+       faces: the half side 2^(22 - level) in these units is taken off */
+    int64_t dd = ad - G->w2[d] - (p->mac ? ((int64_t)1 << (22 - c->level)) : 0);
     if (dd < 0) dd = 0;
     d2 += dd * dd;
   }

@@ -62,7 +62,7 @@ struct AdjArgs {
   const typename Vec4<T>::type* src;
   const T* eps2;
   long long thr[NB_NLEV];
-  int n_direct, le;
+  int n_direct, le, mac_edge;
   int* stack;
   int stack_cap;
   int* group_ctr;
@@ -82,7 +82,7 @@ constexpr double kScale = 1.0 / 8388608.0;
 // stack overflow.
 template <typename T, typename OnM2P, typename OnP2P>
 __device__ __forceinline__ bool adj_walk_group(const DevTree& tr, int box, const int4 gb, const int4 gc, const int4 gd,
-                                               int le, const long long* thr, int n_direct, T eps2, int* stk,
+                                               int le, const long long* thr, int n_direct, int mac_edge, T eps2, int* stk,
                                                int stack_cap, int lane, int* s_midx,
                                                typename Vec4<T>::type* s_moff, T* s_meps, OnM2P on_m2p,
                                                OnP2P on_p2p) {
@@ -108,7 +108,7 @@ __device__ __forceinline__ bool adj_walk_group(const DevTree& tr, int box, const
     __syncwarp();
     int cls = NB_CELL_NONE, kx = 0, ky = 0, kz = 0;
     const int lvl = ca.w & 0xff, nch = ca.w >> 8;
-    if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, le, thr, n_direct, kx, ky, kz);
+    if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, le, thr, n_direct, mac_edge, kx, ky, kz);
     {
       const int nc = (cls == NB_CELL_OPEN) ? nch : 0;
       const int pre = warp_excl_scan(nc, lane);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
         __syncwarp();
       }
     };
-    const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, eps2, stk, w.stack_cap, lane,
+    const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, eps2, stk, w.stack_cap, lane,
                                       s_midx[wid], s_moff[wid], s_meps[wid], on_m2p, on_p2p);
     if (!ok) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_src_kernel(AdjArgs<float
       __syncwarp();
     };
     auto on_p2p = [&](bool, const int4, const int4, int, int, int, int) {};
-    const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, eps2, stk, w.stack_cap, lane,
+    const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, eps2, stk, w.stack_cap, lane,
                                       s_midx[wid], s_moff[wid], s_meps[wid], on_m2p, on_p2p);
     if (!ok && lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
   }
@@ -714,7 +714,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
                           int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
-                          unsigned* status, int nsm, cudaStream_t s) {
+                          unsigned* status, int nsm, int mac_edge, cudaStream_t s) {
   if (fp64) return cudaErrorNotSupported;  // the reverse mode runs the mixed-precision walk
   if (pe > 4) return cudaErrorNotSupported;
   cudaError_t e;
@@ -741,6 +741,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
     a.eps2 = (const float*)eps2;
     for (int l = 0; l < NB_NLEV; l++) a.thr[l] = thr[l];
     a.n_direct = n_direct;
+    a.mac_edge = mac_edge;
     a.le = le;
     a.stack = stack;
     a.stack_cap = stack_cap;

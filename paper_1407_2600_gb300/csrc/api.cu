@@ -47,7 +47,7 @@ int nb_walk_warps(bool fp64);
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
-                    int forced_variant, cudaStream_t s);
+                    int forced_variant, int mac_edge, cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -65,7 +65,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
                           int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
-                          unsigned* status, int nsm, cudaStream_t s);
+                          unsigned* status, int nsm, int mac_edge, cudaStream_t s);
 cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                            const void* tab, void* lbuf, cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
@@ -555,7 +555,8 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
-                t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, s));
+                t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0,
+                s));
   NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
@@ -600,7 +601,7 @@ int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   NB_CU(nb_forces_vjp(tr, false, p.order, p.ewald_order, p.ewald_level, p.ewald_grid, t->coef.p, t->src.p,
                       t->eps2.p, t->thr, p.n_direct, t->stack.as<int>(), kStackCap, t->walk_blocks,
                       t->fm.as<double>(), t->tab32, t->lbuf.p, nb_field_stride(p.ewald_order), p.lmax, lam, out,
-                      B, t->status.as<unsigned>(), t->nsm, s));
+                      B, t->status.as<unsigned>(), t->nsm, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0, s));
   return NBODY_OK;
 }
 

@@ -55,6 +55,7 @@ struct WalkArgs {
   const T* eps2;  // per box
   long long thr[NB_NLEV];
   int n_direct;
+  int mac_edge;
   int le;
   int* stack;
   int stack_cap;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       int cls = NB_CELL_NONE;
       int kx = 0, ky = 0, kz = 0;
       const int lvl = ca.w & 0xff, nch = ca.w >> 8;
-      if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, kx, ky, kz);
+      if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, kx, ky, kz);
       // push daughters of opened cells
       {
         const int nc = (cls == 1) ? nch : 0;
@@ -442,7 +443,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     const void* eps2, const long long* thr, int n_direct, int le, int* stack,
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
                     unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
-                    cudaStream_t s) {
+                    int mac_edge, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
 #define NB_WALK(TT, P)                                                             \
@@ -454,6 +455,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.eps2 = (const TT*)eps2;                                                      \
     for (int l = 0; l < NB_NLEV; l++) a.thr[l] = thr[l];                           \
     a.n_direct = n_direct;                                                         \
+    a.mac_edge = mac_edge;                                                         \
     a.le = le;                                                                     \
     a.stack = stack;                                                               \
     a.stack_cap = stack_cap;                                                       \

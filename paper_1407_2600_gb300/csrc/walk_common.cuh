@@ -26,10 +26,11 @@ enum { NB_CELL_NONE = 0, NB_CELL_OPEN = 1, NB_CELL_M2P = 2, NB_CELL_P2P = 3 };
 
 // Image of a cell from its level-le ancestor (or the common image of its
 // level-le descendants) nearest the expansion point e; then the integer
-// acceptance test against the group box (centre g2, half-widths w2).
+// acceptance test against the group box (centre g2, half-widths w2), with
+// the distance taken from the cell centre or, with mac_edge, its faces.
 __device__ __forceinline__ int classify_cell(const int4 ca, const int4 cb, const int4 gb, const int4 gc,
                                              const int4 gd, int le, const long long* thr, int n_direct,
-                                             int& kx, int& ky, int& kz) {
+                                             int mac_edge, int& kx, int& ky, int& kz) {
   const int lvl = ca.w & 0xff, nch = ca.w >> 8;
   bool consistent = true;
   const int ix = ((ca.x >> (22 - lvl)) - 1) >> 1;
@@ -49,9 +50,11 @@ __device__ __forceinline__ int classify_cell(const int4 ca, const int4 cb, const
                  ky == img_shift(cell_c2(((iy + 1) << sh) - 1, le), gd.y) &&
                  kz == img_shift(cell_c2(((iz + 1) << sh) - 1, le), gd.z);
   }
-  const int dx = abs(ca.x - gb.x - kx * NB_PBOX) - gc.x;
-  const int dy = abs(ca.y - gb.y - ky * NB_PBOX) - gc.y;
-  const int dz = abs(ca.z - gb.z - kz * NB_PBOX) - gc.z;
+  // d from the cell centre, or (mac_edge) from its faces: less the half side
+  const int hs = mac_edge ? (1 << (22 - lvl)) : 0;
+  const int dx = abs(ca.x - gb.x - kx * NB_PBOX) - gc.x - hs;
+  const int dy = abs(ca.y - gb.y - ky * NB_PBOX) - gc.y - hs;
+  const int dz = abs(ca.z - gb.z - kz * NB_PBOX) - gc.z - hs;
   const long long ddx = dx > 0 ? dx : 0, ddy = dy > 0 ? dy : 0, ddz = dz > 0 ? dz : 0;
   const long long d2 = ddx * ddx + ddy * ddy + ddz * ddz;
   const bool accept = consistent && lvl >= 2 && d2 > thr[lvl];

@@ -136,6 +136,25 @@ def config_haloes(ng: int = 128, seed: int = 1, n_halo: int = 64, rms: float = 0
     return x, 1.0 / (30.0 * ng)
 
 
+def config_batched(seed: int = 1, sizes=(48,) * 32 + (64,) * 32 + (80,) * 32, rms: float = 0.25,
+                   a: float = 0.02):
+    """Independent periodic boxes of uneven sizes (default: 32 of 48^3, 32 of
+    64^3, 32 of 80^3 particles), each with its own seeded Zel'dovich field
+    (P(k) ~ k^-2, rms displacement `rms` spacing) at expansion factor a.
+    Returns the concatenated positions (N, 3) and growing-mode momenta
+    p = H0 a^(1/2) psi (N, 3), the box offsets (nbox + 1) and the per-box
+    softening eps = spacing/30."""
+    h0 = np.sqrt(8.0 * np.pi / 3.0)
+    xs, ps, eps = [], [], []
+    for b, ng in enumerate(sizes):
+        q, psi = zeldovich_particles(ng, -2.0, rms, seed * 1000 + b)
+        xs.append(np.mod(q + psi, 1.0))
+        ps.append(h0 * np.sqrt(a) * psi)
+        eps.append(1.0 / (30.0 * ng))
+    off = np.cumsum([0] + [len(x) for x in xs])
+    return np.concatenate(xs), np.concatenate(ps), off, eps
+
+
 def random_targets(n: int, k: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed + 7))
     return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)

@@ -26,6 +26,7 @@ NBODY_ERANGE = -7
 NBODY_MIXED = 0
 NBODY_FP64 = 1
 NBODY_FLAG_ASYNC = 1
+NBODY_FLAG_MAC_EDGE = 2
 
 
 def NBODY_FLAG_WALK_VARIANT(v: int) -> int:

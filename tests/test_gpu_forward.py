@@ -153,6 +153,22 @@ def test_every_walk_variant_vs_oracle_tree(cuda, name, gen, theta, order):
         assert np.percentile(_rel(a, outs[0]), 99) <= 2e-5
 
 
+@pytest.mark.parametrize("name,gen,theta,order", [CASES[0], CASES[2], CASES[3]])
+def test_edge_mac_vs_oracle_tree(cuda, name, gen, theta, order):
+    """The opening test measured from the cell faces: same interactions and
+    forces as the oracle with mac = 1."""
+    nb = _nb()
+    x, eps = gen()
+    nd = 2 if order <= 2 else 4
+    a, st = _gpu_forces(x, cuda, eps=eps, theta=theta, order=order, n_direct=nd, flags=nb.NBODY_FLAG_MAC_EDGE)
+    ref, ost = oracle.tree_forces(x, None, oracle.tree_params(eps, theta, order, n_direct=nd, ewald=4, mac=1),
+                                  return_stats=True)
+    rel = _rel(a, ref)
+    assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (np.median(rel), np.percentile(rel, 99))
+    assert st["m2p"] == ost["m2p"]
+    assert abs(st["p2p"] - (ost["p2p"] + len(x))) <= 1e-9 * ost["p2p"] + 0.5
+
+
 def test_forces_fp64_mode(cuda):
     x, eps = ics.config_small(2)
     a, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=4, precision=1)
@@ -172,6 +188,12 @@ def test_forces_vs_direct_ewald(cuda):
     a0, _ = _gpu_forces(x, cuda, eps=eps, theta=1e-3, order=2, n_direct=2)
     rel0 = _rel(a0, ad)
     assert np.median(rel0) <= 1e-4
+    # the small-box setting at quadrupole order, theta 0.5, with the
+    # face-distance opening test: median <= 1e-3, 99th percentile <= 1e-2
+    nb = _nb()
+    a2, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=2, n_direct=2, flags=nb.NBODY_FLAG_MAC_EDGE)
+    rel2 = _rel(a2, ad)
+    assert np.median(rel2) <= 1e-3 and np.percentile(rel2, 99) <= 1e-2, (np.median(rel2), np.percentile(rel2, 99))
 
 
 def test_lattice_zero_force(cuda):
