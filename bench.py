@@ -39,10 +39,11 @@ THETA = 0.6
 ORDER = 4
 EWALD_GRID = 5       # groups never straddle a level-4 cell (measured accuracy setting)
 FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FMA
-# DRAM traffic of one walk launch from the ncu capture summarised in
-# profiles/walk_kernel_haloes96.md, scaled to 2^21 particles; valid only while
-# the walk's sources are unchanged since that capture
-WALK_TRAFFIC = {"bytes": 124e6, "source_sha": "66456c7f86ad5907"}
+# DRAM traffic of one walk launch (packed variant, 8 warps x 2 blocks) from
+# the ncu capture summarised in profiles/walk_kernel_haloes96.md, scaled to
+# 2^21 particles; valid only while the walk's sources are unchanged since that
+# capture
+WALK_TRAFFIC = {"bytes": 120e6, "source_sha": "9d0a39b1ea0133a7"}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -73,7 +74,7 @@ def m2p_flops(order: int) -> int:
 def walk_source_sha() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("walk.cu", "m2p_gen.cuh", "common.cuh"):
+    for f in ("walk.cu", "walk_common.cuh", "m2p_gen.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1407_2600_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -325,6 +326,37 @@ def run_gpu(args, rank, world, local_rank):
                        "forward = the same trajectory's KDK steps with checkpoint copies"}
         a = a_list[-1]
 
+    # the same force evaluation with FP64 interactions (same tree, theta and
+    # order: the force error is the tree's, as in mixed precision)
+    fp64 = None
+    if args.fp64:
+        prm64 = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=4, ewald_grid=args.ewald_grid,
+                          precision=1, flags=nb.NBODY_FLAG_ASYNC)
+        t64 = nb.Tree(prm64, pos)
+        a64 = t64.forces()
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        t64.rebuild()
+        t64.forces(a64)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        rc = nb.nbody_check(t64.handle, nb._stream())
+        if rc != nb.NBODY_OK:
+            raise nb.NbodyError(rc, "FP64 force evaluation")
+        ms64 = d0.elapsed_time(d1)
+        t64.timing(reset=True)
+        tree.pos = pos
+        tree.rebuild()
+        a32 = tree.forces()
+        torch.cuda.synchronize()
+        dif = torch.linalg.norm(a32 - a64, dim=0) / torch.linalg.norm(a64, dim=0)
+        fp64 = {"force_eval_ms": ms64, "updates_per_s": n / (ms64 * 1e-3),
+                "mixed_over_fp64_speed": ms64 / force_ms,
+                "mixed_vs_fp64_rel_diff": {"median": float(dif.median()), "p99": float(torch.quantile(dif[:1 << 20], 0.99))},
+                "note": "precision=1: FP64 interactions and coefficients on the same tree (FP32 output)"}
+        t64.close()
+
     batched = None
     if args.batched:
         batched = run_batched(dev, max(2, args.steps // 2))
@@ -372,6 +404,7 @@ def run_gpu(args, rank, world, local_rank):
                                            "packed FP32x2 M2P, 8 x 2", "packed FP32x2 M2P, 4 x 5"]},
             "adjoint_forward_ratio": adj["ratio"] if adj else None,
             "adjoint": adj,
+            "fp64_tree": fp64,
             "batched": batched,
         }
         print(json.dumps(line), flush=True)
@@ -447,6 +480,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--fp64", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time one all-FP64 force evaluation of the same workload")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 96-box batched workload")
     ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")
