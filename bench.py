@@ -38,6 +38,7 @@ DLNA = 0.1
 THETA = 0.6
 ORDER = 4
 EWALD_GRID = 5       # groups never straddle a level-4 cell (measured accuracy setting)
+N_DIRECT = 8         # accepted cells with <= 8 particles summed directly (fastest of 4/8/12/16 measured)
 FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FMA
 # DRAM traffic of one walk launch (packed variant, 8 warps x 2 blocks) from
 # the ncu capture summarised in profiles/walk_kernel_haloes96.md, scaled to
@@ -145,7 +146,7 @@ def cpu_reference(x, eps, sample: int, seed: int):
     import oracle
     from paper_1407_2600_gb300 import ics
     n = len(x)
-    prm = oracle.tree_params(eps, THETA, ORDER, n_direct=4, ewald=4, ew_grid=EWALD_GRID)
+    prm = oracle.tree_params(eps, THETA, ORDER, n_direct=N_DIRECT, ewald=4, ew_grid=EWALD_GRID)
     oracle.phitilde_lattice(EWALD_GRID, 5)  # build the oracle's table outside the timing
     t0 = time.perf_counter()
     oracle.tree_forces(x, None, prm, targets=np.array([0], dtype=np.int64))
@@ -199,7 +200,7 @@ def run_gpu(args, rank, world, local_rank):
     n = len(x)
     pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
     mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
-    prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=4, ewald_grid=args.ewald_grid,
+    prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=args.n_direct, ewald_grid=args.ewald_grid,
                     flags=nb.NBODY_FLAG_ASYNC)
     tree = nb.Tree(prm, pos)
     acc = tree.forces()
@@ -330,7 +331,7 @@ def run_gpu(args, rank, world, local_rank):
     # order: the force error is the tree's, as in mixed precision)
     fp64 = None
     if args.fp64:
-        prm64 = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=4, ewald_grid=args.ewald_grid,
+        prm64 = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=args.n_direct, ewald_grid=args.ewald_grid,
                           precision=1, flags=nb.NBODY_FLAG_ASYNC)
         t64 = nb.Tree(prm64, pos)
         a64 = t64.forces()
@@ -381,6 +382,7 @@ def run_gpu(args, rank, world, local_rank):
                                    "(2k-50k particles, c 5-15), L=250 Mpc/h, eps=spacing/30; one KDK step "
                                    "of dln a = 0.1 per step",
                        "n": n, "theta": THETA, "order": ORDER, "n_group": 32, "n_leaf": 16,
+                       "n_direct": args.n_direct,
                        "ewald_order": 4, "ewald_grid": args.ewald_grid, "precision": "FP32 interactions, "
                        "FP64 positions/moments",
                        "l2": "inputs larger than L2 (no flush)",
@@ -486,6 +488,8 @@ def main():
                     help="also time the 96-box batched workload")
     ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")
     ap.add_argument("--ng", type=int, default=NG, help="particles per axis (128 = the benchmark workload)")
+    ap.add_argument("--n-direct", type=int, default=N_DIRECT,
+                    help="accepted cells with at most this many particles are summed directly")
     ap.add_argument("--ewald-grid", type=int, default=EWALD_GRID,
                     help="groups never straddle a cell of level ewald_grid - 1")
     args = ap.parse_args()

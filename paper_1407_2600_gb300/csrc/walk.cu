@@ -259,8 +259,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         s_poff[wid][lane][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
         s_poff[wid][lane][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
         __syncwarp();
-        for (int b0 = 0; b0 < total; b0 += 32) {
-          const int t = b0 + lane;
+        // source t of this pop's P2P cells at its image, relative to e; past
+        // the end a massless source at the origin
+        auto fetch = [&](int t) {
+          V4 v;
+          v.x = v.y = v.z = v.w = (T)0;
           if (t < total) {
             // last P2P lane q with pfx[q] <= t
             int lo = 0, hi = 31;
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             }
             const int q = lo;
             const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
-            V4 v = w.src[j];
+            v = w.src[j];
             T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
             if (s_plev[wid][q] < w.le) {
               // leaf above the image level: image per particle from its own
@@ -285,11 +288,51 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             v.x = v.x + ox;
             v.y = v.y + oy;
             v.z = v.z + oz;
+          }
+          return v;
+        };
+        // the next chunk's sources are fetched while this chunk is summed
+        V4 v = fetch(lane);
+        for (int b0 = 0; b0 < total; b0 += 32) {
+          if constexpr (PK) {
+            // pairs of sources interleaved: (x0, x1, y0, y1) then (z0, z1, m0, m1)
+            float* pa = reinterpret_cast<float*>(&s_src[wid][0]);
+            float* pb = reinterpret_cast<float*>(&s_src[wid][16]);
+            const int pr = lane >> 1, hf = lane & 1;
+            pa[4 * pr + hf] = v.x;
+            pa[4 * pr + 2 + hf] = v.y;
+            pb[4 * pr + hf] = v.z;
+            pb[4 * pr + 2 + hf] = v.w;
+          } else {
             s_src[wid][lane] = v;
           }
           __syncwarp();
           const int nn = min(32, total - b0);
-          if (act) {
+          const V4 vnext = fetch(b0 + 32 + lane);
+          if constexpr (PK) {
+            if (act) {
+              const float4* pa = reinterpret_cast<const float4*>(&s_src[wid][0]);
+              const float4* pb = reinterpret_cast<const float4*>(&s_src[wid][16]);
+              const float2 nx = make_float2(-xi, -xi), ny = make_float2(-yi, -yi), nz = make_float2(-zi, -zi);
+              const float2 e2 = make_float2(eps2, eps2);
+              float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+              for (int k = 0; k < ((nn + 1) >> 1); k++) {
+                const float4 a = pa[k], b = pb[k];
+                const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+                const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+                const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
+                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                const float2 inv = make_float2(nbody_rsqrt(r2.x), nbody_rsqrt(r2.y));
+                const float2 f = __fmul2_rn(__fmul2_rn(make_float2(b.z, b.w), __fmul2_rn(inv, inv)), inv);
+                px = __ffma2_rn(dx, f, px);
+                py = __ffma2_rn(dy, f, py);
+                pz = __ffma2_rn(dz, f, pz);
+              }
+              kadd(ax, cx, px.x + px.y);
+              kadd(ay, cy, py.x + py.y);
+              kadd(az, cz, pz.x + pz.y);
+            }
+          } else if (act) {
             T px = 0, py = 0, pz = 0;
             for (int k = 0; k < nn; k++) {
               const V4 s = s_src[wid][k];
@@ -306,6 +349,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             kadd(az, cz, pz);
           }
           __syncwarp();
+          v = vnext;
         }
         n_p2p += (unsigned long long)total;
       }
