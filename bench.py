@@ -361,6 +361,7 @@ def run_gpu(args, rank, world, local_rank):
     batched = None
     if args.batched:
         batched = run_batched(dev, max(2, args.steps // 2))
+    config3 = run_config3(dev) if args.config3 else None
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -408,10 +409,61 @@ def run_gpu(args, rank, world, local_rank):
             "adjoint": adj,
             "fp64_tree": fp64,
             "batched": batched,
+            "config3": config3,
         }
         print(json.dumps(line), flush=True)
     tree.close()
     return 0
+
+
+def run_config3(dev, ng: int = 512):
+    """Throughput at scale: ng^3 (default 512^3 = 134,217,728) particles, a
+    Zel'dovich box with P(k) ~ k^-1.5 (rms displacement 0.25 spacing at
+    a = 0.02, generated on the device), theta 0.7, hexadecapole, eps =
+    spacing/30; ten KDK steps from a = 0.02 to 0.05 (dln a = ln 2.5 / 10).
+    Reports particle updates/s per step and the phase times."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    from paper_1407_2600_gb300 import ics
+    pos, mom = ics.zeldovich_device(ng, -1.5, 0.25, 3, 0.02, dev)
+    n = pos.shape[1]
+    torch.cuda.synchronize()
+    prm = nb.params(eps=1.0 / (30.0 * ng), theta=0.7, order=4, n_direct=N_DIRECT, ewald_grid=EWALD_GRID,
+                    flags=nb.NBODY_FLAG_ASYNC)
+    tree = nb.Tree(prm, pos)
+    acc = tree.forces()
+    dlna = math.log(2.5) / 10
+    a = 0.02
+    torch.cuda.synchronize()
+    tree.timing(reset=True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        a1 = a * math.exp(dlna)
+        tree.kdk_step(mom, acc, a, a1)
+        a = a1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rc = nb.nbody_check(tree.handle, nb._stream())
+    if rc != nb.NBODY_OK:
+        raise nb.NbodyError(rc, "config-3 steps")
+    tm = tree.timing(reset=True)
+    ms = e0.elapsed_time(e1) / 10
+    ev = max(tm["evaluations"], 1)
+    walk_ms = tm["ms_walk"] / ev
+    flops = (tm["p2p"] * FP32_FLOPS_P2P + tm["m2p"] * m2p_flops(4)) / ev
+    out = {"workload": "%d^3 Zel'dovich (P~k^-1.5, rms 0.25 spacing at a=0.02, device-generated), L=1 Gpc/h, "
+                       "theta 0.7, p=4, eps=spacing/30; 10 KDK steps a=0.02->0.05" % ng,
+           "n": int(n), "ms_per_kdk_step": ms, "updates_per_s": n / (ms * 1e-3), "a_end": a,
+           "phases_ms": {k: tm[k] / max(tm["builds"] if k in ("ms_sort", "ms_build", "ms_upward") else ev, 1)
+                         for k in ("ms_sort", "ms_build", "ms_upward", "ms_walk", "ms_periodic")},
+           "interactions_per_particle": {"p2p": tm["p2p"] / ev / n, "m2p": tm["m2p"] / ev / n},
+           "walk_roofline": {"achieved_tflops": flops / (walk_ms * 1e-3) / 1e12,
+                             "frac": flops / (walk_ms * 1e-3) / 1e12 / fp32_peak_tflops(SM_MAX_MHZ)},
+           "device_mem_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
+    tree.close()
+    return out
 
 
 def run_batched(dev, steps: int):
@@ -484,6 +536,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--fp64", action=argparse.BooleanOptionalAction, default=True,
                     help="also time one all-FP64 force evaluation of the same workload")
+    ap.add_argument("--config3", action="store_true",
+                    help="also time ten KDK steps of the 512^3 scale workload (about a minute)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 96-box batched workload")
     ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")

@@ -155,6 +155,52 @@ def config_batched(seed: int = 1, sizes=(48,) * 32 + (64,) * 32 + (80,) * 32, rm
     return np.concatenate(xs), np.concatenate(ps), off, eps
 
 
+def zeldovich_device(ng: int, n_index: float, rms_spacing: float, seed: int, a: float, device):
+    """The Zel'dovich recipe of zeldovich_displacement for large grids,
+    generated on a CUDA device with torch (white noise from a seeded torch
+    generator, so a different realisation than the numpy one).  Returns
+    positions (3, ng^3) float64 wrapped to [0, 1) and growing-mode momenta
+    p = H0 a^(1/2) psi (3, ng^3) float32, particle order as lattice()."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    white = torch.randn((ng, ng, ng), dtype=torch.float64, device=device, generator=g)
+    dk = torch.fft.rfftn(white)
+    del white
+    kx = torch.fft.fftfreq(ng, d=1.0 / ng, dtype=torch.float64, device=device) * 2.0 * math.pi
+    kz = torch.fft.rfftfreq(ng, d=1.0 / ng, dtype=torch.float64, device=device) * 2.0 * math.pi
+    k2 = kx.view(-1, 1, 1) ** 2 + kx.view(1, -1, 1) ** 2 + kz.view(1, 1, -1) ** 2
+    kk = torch.sqrt(k2)
+    amp = torch.where((kk > 0) & (kk <= math.pi * ng), kk.clamp_min(1e-300) ** (n_index / 2.0),
+                      torch.zeros_like(kk))
+    del kk
+    if ng % 2 == 0:
+        amp[ng // 2, :, :] = 0.0
+        amp[:, ng // 2, :] = 0.0
+        amp[:, :, -1] = 0.0
+    dk = dk * amp / torch.where(k2 > 0, k2, torch.ones_like(k2))
+    del amp, k2
+    psi = torch.empty((3, ng ** 3), dtype=torch.float64, device=device)
+    shapes = ((-1, 1, 1), (1, -1, 1), (1, 1, -1))
+    for d in range(3):
+        kd = (kx if d < 2 else kz).view(*shapes[d])
+        psi[d] = torch.fft.irfftn(1j * kd * dk, s=(ng, ng, ng)).reshape(-1)
+    del dk
+    rms = float(torch.sqrt(torch.mean(torch.sum(psi * psi, dim=0))))
+    if rms > 0:
+        psi *= (rms_spacing / ng) / rms
+    q = (torch.arange(ng, dtype=torch.float64, device=device) + 0.5) / ng
+    pos = torch.empty_like(psi)
+    pos[0] = q.view(-1, 1, 1).expand(ng, ng, ng).reshape(-1)
+    pos[1] = q.view(1, -1, 1).expand(ng, ng, ng).reshape(-1)
+    pos[2] = q.view(1, 1, -1).expand(ng, ng, ng).reshape(-1)
+    pos = torch.remainder(pos + psi, 1.0)
+    pos[pos >= 1.0] = 0.0
+    h0 = math.sqrt(8.0 * math.pi / 3.0)
+    mom = (h0 * math.sqrt(a) * psi).float()
+    return pos.contiguous(), mom.contiguous()
+
+
 def random_targets(n: int, k: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed + 7))
     return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int64)
