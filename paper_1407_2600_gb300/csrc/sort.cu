@@ -96,6 +96,11 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
                 uint32_t* __restrict__ tile_ctr, unsigned* __restrict__ err) {
   __shared__ uint32_t s_cnt[kSortWarps][256];
   __shared__ uint32_t s_excl[256];
+  __shared__ uint32_t s_tstart[256];  // start of each digit in the tile's digit-sorted order
+  __shared__ uint32_t s_wsum[kSortWarps];
+  __shared__ uint64_t s_key[kTile];
+  __shared__ uint32_t s_val[kTile];
+  __shared__ uint8_t s_dig[kTile];
   __shared__ int s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
@@ -133,6 +138,18 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
       s_cnt[w][dd] = run;
       run += c;
     }
+    // exclusive scan of the tile's digit counts over the 256 digits
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; w++) wpre += s_wsum[w];
+    s_tstart[dd] = wpre + x - run;
     uint32_t* my = status + (int64_t)tile * 256 + dd;
     uint32_t prefix = 0;
     if (tile == 0) {
@@ -160,13 +177,24 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
     s_excl[dd] = base[dd] + prefix;
   }
   __syncthreads();
+  // stage the tile in digit order, then write each digit's run contiguously
 #pragma unroll
   for (int r = 0; r < kItems; r++) {
     if (d[r] < 256u) {
-      uint32_t dst = s_excl[d[r]] + s_cnt[warp][d[r]] + rk[r];
-      kout[dst] = k[r];
-      vout[dst] = v[r];
+      const uint32_t lp = s_tstart[d[r]] + s_cnt[warp][d[r]] + rk[r];
+      s_key[lp] = k[r];
+      s_val[lp] = v[r];
+      s_dig[lp] = (uint8_t)d[r];
     }
+  }
+  __syncthreads();
+  const int64_t t0 = (int64_t)tile * kTile;
+  const int cnt = (int)min((int64_t)kTile, n - t0);
+  for (int e = threadIdx.x; e < cnt; e += kSortThreads) {
+    const uint32_t dd = s_dig[e];
+    const uint32_t dst = s_excl[dd] + ((uint32_t)e - s_tstart[dd]);
+    kout[dst] = s_key[e];
+    vout[dst] = s_val[e];
   }
 }
 
