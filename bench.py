@@ -303,6 +303,8 @@ def run_gpu(args, rank, world, local_rank):
         g.manual_seed(17 + rank)
         lx = torch.randn((3, n), dtype=torch.float64, device=dev, generator=g)
         lp = torch.randn((3, n), dtype=torch.float32, device=dev, generator=g)
+        # warm-up: one reverse step (runs the reverse walk's autotuner)
+        tree.kdk_adjoint(pos.clone(), mom.clone(), a_list[0], a_list[1], lx, lp, acc0=acc.clone())
         torch.cuda.synchronize()
         tree.timing(reset=True)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]

@@ -14,6 +14,9 @@
 //    the level-3 cells and their particles.
 #include <math.h>
 
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "m2p_gen.cuh"
 #include "adj_gen.cuh"
@@ -710,6 +713,96 @@ struct AdjBuffers {
 int nb_adj_coef_nm(int order) { return (order + 1) * (order + 2) * (order + 3) / 6; }
 int nb_adj_lbar_stride(int pe) { return pe > 0 ? ((pe + 2) * (pe + 3) * (pe + 4) / 6 - 1) + 3 : 0; }
 
+namespace {
+
+template <typename K>
+int adj_grid(K kernel, int warps, int max_blocks, int nsm) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, warps * 32, 0) != cudaSuccess) occ = 1;
+  int grid = nsm * (occ > 0 ? occ : 1);
+  if (grid * warps > max_blocks * 8) grid = max_blocks * 8 / warps;
+  return grid;
+}
+
+// sink-side variants: packed or scalar Hessian-vector products, 4 warps per
+// block, 3 or 4 blocks per SM (the register budget follows)
+template <int P>
+cudaError_t launch_sink(int v, const AdjArgs<float>& a, int max_blocks, int nsm, cudaStream_t s) {
+  switch (v) {
+    case 0:
+      adj_sink_kernel<P, 4, 3, true><<<adj_grid(adj_sink_kernel<P, 4, 3, true>, 4, max_blocks, nsm), 128, 0, s>>>(a);
+      break;
+    case 1:
+      adj_sink_kernel<P, 4, 4, true><<<adj_grid(adj_sink_kernel<P, 4, 4, true>, 4, max_blocks, nsm), 128, 0, s>>>(a);
+      break;
+    case 2:
+      adj_sink_kernel<P, 4, 3, false><<<adj_grid(adj_sink_kernel<P, 4, 3, false>, 4, max_blocks, nsm), 128, 0, s>>>(a);
+      break;
+    default:
+      adj_sink_kernel<P, 4, 4, false><<<adj_grid(adj_sink_kernel<P, 4, 4, false>, 4, max_blocks, nsm), 128, 0, s>>>(a);
+      break;
+  }
+  nb_launch_counter += 1;
+  return cudaGetLastError();
+}
+constexpr int kSinkVariants = 4;
+std::mutex g_sink_mutex;
+struct SinkTune {
+  int device, order, variant;
+};
+std::vector<SinkTune> g_sink_tune;
+
+template <int P>
+cudaError_t launch_adj(const AdjArgs<float>& a, const AdjBuffers& B, const DevTree& tr, const float* lam,
+                       int max_blocks, int nsm, cudaStream_t s) {
+  cudaError_t e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int variant = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_sink_mutex);
+    for (const auto& t : g_sink_tune)
+      if (t.device == dev && t.order == P) variant = t.variant;
+  }
+  if (variant < 0) {
+    // time every variant on this call's data; each trial starts from a zero
+    // sink cotangent, which the final run below starts from again
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0))) return e;
+    if ((e = cudaEventCreate(&e1))) return e;
+    float best = 1e30f;
+    variant = 0;
+    for (int v = 0; v < kSinkVariants; v++) {
+      adj_prep_kernel<<<gridv(tr.n, 256), 256, 0, s>>>(tr.n, tr.perm, lam, B.lam_s, B.mu);
+      nb_launch_counter += 1;
+      if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;
+      cudaEventRecord(e0, s);
+      if ((e = launch_sink<P>(v, a, max_blocks, nsm, s))) return e;
+      cudaEventRecord(e1, s);
+      if ((e = cudaEventSynchronize(e1))) return e;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        variant = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lock(g_sink_mutex);
+    g_sink_tune.push_back({dev, P, variant});
+    adj_prep_kernel<<<gridv(tr.n, 256), 256, 0, s>>>(tr.n, tr.perm, lam, B.lam_s, B.mu);
+    nb_launch_counter += 1;
+  }
+  if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;
+  adj_src_kernel<P, 4, 4><<<adj_grid(adj_src_kernel<P, 4, 4>, 4, max_blocks, nsm), 128, 0, s>>>(a);
+  nb_launch_counter += 1;
+  if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;
+  return launch_sink<P>(variant, a, max_blocks, nsm, s);
+}
+
+}  // namespace
+
 cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int le, int lg, const void* coef,
                           const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
@@ -750,32 +843,16 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
     a.mu = B.mu;
     a.nuc = B.nuc;
     a.status = status;
-    // source side, then (group counter reset) sink side
-    int occ = 0;
-#define NB_ADJ_GRID(KER, W)                                                                     \
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, KER, (W) * 32, 0))) return e;    \
-  grid = nsm * (occ > 0 ? occ : 1);                                                             \
-  if (grid * (W) > max_blocks * 8) grid = max_blocks * 8 / (W);
-#define NB_ADJW(P)                                                                               \
-  {                                                                                              \
-    int grid = 0;                                                                                \
-    NB_ADJ_GRID((adj_src_kernel<P, 4, 4>), 4)                                                    \
-    adj_src_kernel<P, 4, 4><<<grid, 128, 0, s>>>(a);                                             \
-    if ((e = cudaMemsetAsync(B.group_ctr, 0, sizeof(int), s))) return e;                         \
-    NB_ADJ_GRID((adj_sink_kernel<P, 4, 3, true>), 4)                                             \
-    adj_sink_kernel<P, 4, 3, true><<<grid, 128, 0, s>>>(a);                                      \
-    break;                                                                                       \
-  }
+    // source side, then (group counter reset) sink side; the sink side's
+    // launch variant is autotuned on the first call per (device, order)
     switch (order) {
-      case 0: NB_ADJW(0)
-      case 1: NB_ADJW(1)
-      case 2: NB_ADJW(2)
-      case 3: NB_ADJW(3)
-      default: NB_ADJW(4)
+      case 0: e = launch_adj<0>(a, B, tr, lam, max_blocks, nsm, s); break;
+      case 1: e = launch_adj<1>(a, B, tr, lam, max_blocks, nsm, s); break;
+      case 2: e = launch_adj<2>(a, B, tr, lam, max_blocks, nsm, s); break;
+      case 3: e = launch_adj<3>(a, B, tr, lam, max_blocks, nsm, s); break;
+      default: e = launch_adj<4>(a, B, tr, lam, max_blocks, nsm, s); break;
     }
-#undef NB_ADJW
-#undef NB_ADJ_GRID
-    nb_launch_counter += 2;
+    if (e) return e;
   }
   if ((e = cudaGetLastError())) return e;
   if (pe > 0) {
