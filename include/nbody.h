@@ -115,6 +115,9 @@ typedef struct {
   float ms_upward;     /* moments */
   float ms_walk;       /* group walk with P2P and M2P */
   float ms_periodic;   /* image-field expansion and scatter to caller order */
+  uint64_t decision_hash; /* order-independent checksum of every (group, cell,
+                             decision) of the walk: equal trees and decisions
+                             give equal sums (finite-difference checks use it) */
 } nbody_stats;
 
 typedef struct nbody_tree nbody_tree;
@@ -152,6 +155,14 @@ int nbody_build_tree_batched(const nbody_params *params, int nbox, const int64_t
  *            only filled when the call synchronises)
  */
 int nbody_forces(nbody_tree *tree, float *acc_dev, nbody_stats *stats, nbody_stream_t stream);
+
+/*
+ * nbody_forces with FP64 output: acc_dev is 3*n FP64 (caller order,
+ * overwritten).  With precision NBODY_FP64 the accelerations are FP64
+ * throughout (for FP64 finite-difference checks of the reverse mode); with
+ * NBODY_MIXED they are the FP32 results widened.  Errors as nbody_forces.
+ */
+int nbody_forces64(nbody_tree *tree, double *acc_dev, nbody_stream_t stream);
 
 /*
  * One kick-drift-kick step in comoving coordinates (Einstein-de Sitter,
@@ -233,6 +244,7 @@ typedef struct {
   double ms_sort, ms_build, ms_upward, ms_walk, ms_periodic; /* summed device times */
   int64_t adjoint_steps;   /* nbody_kdk_adjoint(_acc) calls */
   int64_t adjoint_reused;  /* of which reused the previous call's J(x0)^T lam_ph */
+  uint64_t decision_hash;  /* sum (mod 2^64) of the evaluations' decision checksums */
   int64_t walk_variant;    /* walk launch variant the autotuner chose for this tree's
                               precision and order on this device (-1: not tuned yet) */
   double walk_tune_ms[8];  /* each variant's time in the tuning run (0: not timed) */

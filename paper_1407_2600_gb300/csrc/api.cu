@@ -70,7 +70,7 @@ cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg,
                            const void* tab, void* lbuf, cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
-                        cudaStream_t s);
+                        double* out64, cudaStream_t s);
 
 namespace {
 
@@ -327,7 +327,7 @@ __global__ void differ_kernel(int64_t n3, const unsigned long long* __restrict__
 }
 
 __global__ void accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ tot) {
-  if (threadIdx.x < 3) tot[threadIdx.x] += c[threadIdx.x];
+  if (threadIdx.x < 4) tot[threadIdx.x] += c[threadIdx.x];
 }
 
 __global__ void max_level_kernel(int ncell, const int4* __restrict__ cA, int* out) {
@@ -539,7 +539,7 @@ int field_impl(nbody_tree* t, cudaStream_t s) {
   return NBODY_OK;
 }
 
-int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
+int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullptr) {
   const nbody_params& p = t->prm;
   const bool fp64 = p.precision == NBODY_FP64;
   const int64_t n = t->n;
@@ -560,7 +560,7 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s) {
   NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
-                    t->lbuf.p, t->accw.p, acc, ctr + 2, s));
+                    t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, s));
   NB_CU(cudaEventRecord(fe[2], s));
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
   nb_launch_counter += 1;
@@ -692,6 +692,17 @@ int nbody_build_tree_batched(const nbody_params* params, int nbox, const int64_t
   return make_tree(params, nbox, offsets_host, eps_host, pos_dev, mass_dev, tree, (cudaStream_t)stream);
 }
 
+int nbody_forces64(nbody_tree* tree, double* acc_dev, nbody_stream_t stream) {
+  if (!tree || !acc_dev) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long l0 = nb_launch_counter;
+  int rc = forces_impl(tree, nullptr, s, acc_dev);
+  tree->launches += nb_launch_counter - l0;
+  if (rc) return rc;
+  if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  return read_status(tree, s);
+}
+
 int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_stream_t stream) {
   if (!tree || !acc_dev) return NBODY_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -703,11 +714,12 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_str
   rc = read_status(tree, s);
   if (stats) {
     memset(stats, 0, sizeof(*stats));
-    unsigned long long c[3] = {0, 0, 0};
+    unsigned long long c[4] = {0, 0, 0, 0};
     if (cudaMemcpy(c, tree->counters.p, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess) {
       stats->p2p = (double)c[0];
       stats->m2p = (double)c[1];
       stats->m2l = (double)c[2];
+      stats->decision_hash = c[3];
     }
     stats->ncells = tree->ncell;
     stats->ngroups = tree->ngroup;
@@ -1000,11 +1012,12 @@ int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
   out->adjoint_steps = t->adj_steps;
   out->adjoint_reused = t->adj_reused;
   if (t->tot.p) {
-    unsigned long long c[3] = {0, 0, 0};
+    unsigned long long c[4] = {0, 0, 0, 0};
     NB_CU(cudaMemcpy(c, t->tot.p, sizeof(c), cudaMemcpyDeviceToHost));
     out->p2p = (double)c[0];
     out->m2p = (double)c[1];
     out->m2l = (double)c[2];
+    out->decision_hash = c[3];
   }
   if (reset) {
     t->nb_log = 0;

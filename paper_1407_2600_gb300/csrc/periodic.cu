@@ -193,6 +193,7 @@ struct PerArgs {
   const T* accw;        // walk accelerations, key order
   float* out;           // caller order
   unsigned long long* counter;
+  double* out64;        // when set, FP64 output in caller order instead of out
 };
 
 __constant__ unsigned char c_par_mask[kNMMax];  // bit d set: multi-index odd in axis d
@@ -307,21 +308,27 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
     T az = a.accw[2 * tr.n + i] + fourpi3 * (mt * dz - vz);
     PE_<PE>::template l2p<T>(L, dx, dy, dz, ax, ay, az);
     const uint32_t j = tr.perm[i];
-    a.out[j] = (float)ax;
-    a.out[tr.n + j] = (float)ay;
-    a.out[2 * tr.n + j] = (float)az;
+    if (a.out64) {
+      a.out64[j] = (double)ax;
+      a.out64[tr.n + j] = (double)ay;
+      a.out64[2 * tr.n + j] = (double)az;
+    } else {
+      a.out[j] = (float)ax;
+      a.out[tr.n + j] = (float)ay;
+      a.out[2 * tr.n + j] = (float)az;
+    }
   }
 }
 
 // plain scatter when there are no periodic images
-template <typename T>
+template <typename T, typename O>
 __global__ void scatter_kernel(int64_t n, const uint32_t* __restrict__ perm, const T* __restrict__ accw,
-                               float* __restrict__ out) {
+                               O* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t j = perm[i];
-    out[j] = (float)accw[i];
-    out[n + j] = (float)accw[n + i];
-    out[2 * n + j] = (float)accw[2 * n + i];
+    out[j] = (O)accw[i];
+    out[n + j] = (O)accw[n + i];
+    out[2 * n + j] = (O)accw[2 * n + i];
   }
 }
 
@@ -438,10 +445,16 @@ int nb_field_stride(int pe) {
 
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
-                        cudaStream_t s) {
+                        double* out64, cudaStream_t s) {
   if (pe == 0) {
-    if (fp64) scatter_kernel<double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out);
-    else scatter_kernel<float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out);
+    if (out64) {
+      if (fp64) scatter_kernel<double, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out64);
+      else scatter_kernel<float, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out64);
+    } else if (fp64) {
+      scatter_kernel<double, float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out);
+    } else {
+      scatter_kernel<float, float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out);
+    }
     nb_launch_counter += 1;
     return cudaGetLastError();
   }
@@ -452,7 +465,7 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
 #define NB_PER(TT, PE)                                                                              \
   {                                                                                                 \
     PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
-                  (const TT*)accw, out, counter};                                                   \
+                  (const TT*)accw, out, counter, out64};                                            \
     field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     field_l2p_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     break;                                                                                          \
@@ -491,7 +504,7 @@ cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg,
 #define NB_LOC(TT, PE)                                                                              \
   {                                                                                                 \
     PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
-                  nullptr, nullptr, nullptr};                                                       \
+                  nullptr, nullptr, nullptr, nullptr};                                              \
     field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     break;                                                                                          \
   }

@@ -120,6 +120,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     T ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;
     unsigned long long n_p2p = 0, n_m2p = 0;
     int qn = 0;  // queued M2P cells
+    // checksum of this lane's (group, cell, decision, cell count) terms and of
+    // the group's membership (its sinks' input indices)
+    unsigned long long hsum = act ? decision_mix(g, -2 - (int)tr.perm[i], 0) : 0ull;
     // evaluate the first nmp queued M2P cells for every sink of the group
     auto m2p_chunk = [&](int nmp) {
       if constexpr (PK) {
@@ -201,7 +204,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       int cls = NB_CELL_NONE;
       int kx = 0, ky = 0, kz = 0;
       const int lvl = ca.w & 0xff, nch = ca.w >> 8;
-      if (lane < nb) cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, kx, ky, kz);
+      if (lane < nb) {
+        cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, kx, ky, kz);
+        hsum += decision_mix(g, c, cls | (cb.y << 2));
+      }
       // push daughters of opened cells
       {
         const int nc = (cls == 1) ? nch : 0;
@@ -368,6 +374,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       atomicAdd(&w.counters[0], n_p2p * (unsigned long long)cnt);
       atomicAdd(&w.counters[1], n_m2p * (unsigned long long)cnt);
     }
+    for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(FULL, hsum, o);
+    if (lane == 0) {
+      atomicAdd(&w.counters[3], hsum);
+    }
   }
 }
 
@@ -437,7 +447,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
   TuneEntry te{dev, P, fp, 0, {}};
   for (int v = 0; v < kVariants; v++) {
     if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
-    if ((e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s))) return e;
+    if ((e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), s))) return e;
     cudaEventRecord(e0, s);
     if ((e = launch_variant<T, P>(v, a, nsm, max_blocks, s))) return e;
     cudaEventRecord(e1, s);
@@ -458,7 +468,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
     g_tune.push_back(te);
   }
   if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
-  if ((e = cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), s))) return e;
+  if ((e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), s))) return e;
   return launch_variant<T, P>(bv, a, nsm, max_blocks, s);
 }
 

@@ -24,6 +24,18 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
 
 enum { NB_CELL_NONE = 0, NB_CELL_OPEN = 1, NB_CELL_M2P = 2, NB_CELL_P2P = 3 };
 
+// term of the order-independent checksum (a sum modulo 2^64) of every
+// (group, cell, decision) of a walk and of every group's members: any change
+// of the tree, the groups or an acceptance decision changes the sum with
+// overwhelming probability
+__device__ __forceinline__ unsigned long long decision_mix(int g, int c, int cls) {
+  unsigned long long h = (unsigned long long)(g + 1) * 0x9E3779B97F4A7C15ull;
+  h ^= (unsigned long long)(c + 1) * 0xC2B2AE3D27D4EB4Full;
+  h ^= (unsigned long long)cls * 0x165667B19E3779F9ull;
+  h ^= h >> 29;
+  return h * 0xBF58476D1CE4E5B9ull;
+}
+
 // Image of a cell from its level-le ancestor (or the common image of its
 // level-le descendants) nearest the expansion point e; then the integer
 // acceptance test against the group box (centre g2, half-widths w2), with

@@ -36,7 +36,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
           "moments": 6, "groups": 7}
 
 # every symbol include/nbody.h declares
-SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces",
+SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces", "nbody_forces64",
            "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
            "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
@@ -53,7 +53,8 @@ class Stats(C.Structure):
     _fields_ = [("p2p", C.c_double), ("m2p", C.c_double), ("m2l", C.c_double),
                 ("ncells", C.c_int64), ("ngroups", C.c_int64), ("max_level", C.c_int32),
                 ("nbox", C.c_int32), ("ms_sort", C.c_float), ("ms_build", C.c_float),
-                ("ms_upward", C.c_float), ("ms_walk", C.c_float), ("ms_periodic", C.c_float)]
+                ("ms_upward", C.c_float), ("ms_walk", C.c_float), ("ms_periodic", C.c_float),
+                ("decision_hash", C.c_uint64)]
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,7 +66,7 @@ class Timing(C.Structure):
                 ("ms_sort", C.c_double), ("ms_build", C.c_double), ("ms_upward", C.c_double),
                 ("ms_walk", C.c_double), ("ms_periodic", C.c_double),
                 ("adjoint_steps", C.c_int64), ("adjoint_reused", C.c_int64),
-                ("walk_variant", C.c_int64), ("walk_tune_ms", C.c_double * 8)]
+                ("decision_hash", C.c_uint64), ("walk_variant", C.c_int64), ("walk_tune_ms", C.c_double * 8)]
 
     def asdict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,6 +98,7 @@ def lib():
         L.nbody_build_tree_batched.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_int64),
                                                C.POINTER(C.c_double), _vp, _vp, C.POINTER(_vp), _vp]
         L.nbody_forces.argtypes = [_vp, _vp, C.POINTER(Stats), _vp]
+        L.nbody_forces64.argtypes = [_vp, _vp, _vp]
         L.nbody_kdk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp]
         L.nbody_kdk_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp]
         L.nbody_kdk_adjoint_acc.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp,
@@ -150,6 +152,10 @@ def nbody_build_tree_batched(params: Params, offsets, eps, pos_dev: int, mass_de
 
 def nbody_forces(tree: int, acc_dev: int, stats: Stats | None = None, stream: int | None = None) -> int:
     return lib().nbody_forces(tree, acc_dev, C.byref(stats) if stats is not None else None, stream)
+
+
+def nbody_forces64(tree: int, acc_dev: int, stream: int | None = None) -> int:
+    return lib().nbody_forces64(tree, acc_dev, stream)
 
 
 def nbody_kdk_step(tree: int, pos_dev: int, mom_dev: int, acc_dev: int, a0: float, a1: float,
@@ -263,6 +269,14 @@ class Tree:
         st = Stats() if stats else None
         _check(nbody_forces(self.handle, acc.data_ptr(), st, _stream()), "nbody_forces")
         return (acc, st.asdict()) if stats else acc
+
+    def forces64(self, acc=None):
+        """(3, n) float64 accelerations (nbody_forces64)."""
+        import torch
+        if acc is None:
+            acc = torch.empty((3, self.n), dtype=torch.float64, device=self.pos.device)
+        _check(nbody_forces64(self.handle, acc.data_ptr(), _stream()), "nbody_forces64")
+        return acc
 
     def kdk_step(self, mom, acc, a0, a1):
         _check(nbody_kdk_step(self.handle, self.pos.data_ptr(), mom.data_ptr(), acc.data_ptr(), a0, a1,

@@ -176,18 +176,20 @@ def test_trajectory_gradient_vs_finite_differences(cuda):
 
 
 def test_trajectory_gradient_vs_direct_sum_adjoint(cuda):
-    """The tree adjoint against the FP64 direct-sum adjoint (O1 dynamics); they
-    differ by the tree's force error, so the bound is the tree's accuracy."""
+    """The tree adjoint against the FP64 direct-sum adjoint (O1 dynamics) at
+    16^3 on the differentiable-trajectory schedule (16 KDK steps from a =
+    0.05 to 0.2, checkpoints every 4); they differ by the tree's force error,
+    so the bound is the tree's accuracy."""
     import torch
     import paper_1407_2600_gb300.nbody as nb
     from paper_1407_2600_gb300.autograd import trajectory_loss
     q, psi = ics.zeldovich_particles(16, -2.0, 0.25, 44)
-    a_init, a_end, S = 0.05, 0.1, 4
+    a_init, a_end, S = 0.05, 0.2, 16
     psi = psi / a_init
     a_list = [a_init * (a_end / a_init) ** (k / S) for k in range(S + 1)]
     eps = 1.0 / 480
     psi_t = _t(psi, cuda).requires_grad_(True)
-    L = trajectory_loss(psi_t, _t(q, cuda), _prm(eps, 0.4, 4), a_list, 16, every=2)
+    L = trajectory_loss(psi_t, _t(q, cuda), _prm(eps, 0.4, 4), a_list, 16, every=4)
     L.backward()
     g = psi_t.grad.cpu().numpy().T
     force = lambda xx: oracle.direct_forces(xx, None, eps, table_n1=64)
@@ -202,6 +204,7 @@ def test_trajectory_gradient_vs_direct_sum_adjoint(cuda):
     lx, lp = oracle.adjoint_kdk(xs, ps, a_list, gx, np.zeros_like(gx), None, eps, n1=64)
     gd = a_init * lx + oracle.H0 * a_init ** 1.5 * lp
     rel = np.linalg.norm(g - gd, axis=1) / np.linalg.norm(gd, axis=1)
+    print("tree vs direct-sum adjoint gradient: median %.2e p90 %.2e" % (np.median(rel), np.percentile(rel, 90)))
     assert np.median(rel) <= 5e-3, np.median(rel)
 
 
