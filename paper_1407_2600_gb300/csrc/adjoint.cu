@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
   constexpr int NBS = AOrd<P>::NBS;
   constexpr int C4 = NBS / 4;
   __shared__ __align__(16) T s_coef[WARPS][32 * NBS];
-  __shared__ V4 s_src[WARPS][32];
-  __shared__ int s_jidx[WARPS][32];
+  __shared__ V4 s_src[WARPS][64];
+  __shared__ int s_jidx[WARPS][64];
   __shared__ V4 s_moff[WARPS][64];
   __shared__ T s_meps[WARPS][64];
   __shared__ int s_midx[WARPS][64];
@@ -258,6 +258,45 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
       }
       __syncwarp();
     };
+    // P2P sources are queued (up to 31 carried + 32 new) and summed 32 at a
+    // time, so the diagonal pairing below runs on full chunks
+    int qp = 0;
+    auto p2p_chunk = [&](int nn) {
+      // diagonal pairing: in round k lane l takes source (l+k) mod 32 and
+      // passes the source-side term to the lane that owns that source
+      T sx = 0, sy = 0, sz = 0;
+      for (int k = 0; k < 32; k++) {
+        const int q = (lane + k) & 31;
+        T wx = 0, wy = 0, wz = 0;
+        if (act && q < nn && s_jidx[wid][q] != i) {
+          const V4 sv = s_src[wid][q];
+          const T dx = sv.x - xi, dy = sv.y - yi, dz = sv.z - zi;
+          const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+          const T inv = nbody_rsqrt(r2);
+          const T f = (inv * inv) * inv;
+          const T g5 = f * (inv * inv) * (T)3;
+          const T rl = fma(dx, lx, fma(dy, ly, dz * lz));
+          const T a = sv.w * f, bb = sv.w * g5 * rl;
+          wx = fma(a, lx, -bb * dx);
+          wy = fma(a, ly, -bb * dy);
+          wz = fma(a, lz, -bb * dz);
+        }
+        mx -= wx;
+        my -= wy;
+        mz -= wz;
+        const int from = (lane - k) & 31;
+        sx += __shfl_sync(FULL, wx, from);
+        sy += __shfl_sync(FULL, wy, from);
+        sz += __shfl_sync(FULL, wz, from);
+      }
+      if (lane < nn) {
+        const int j = s_jidx[wid][lane];
+        atomicAdd(&w.mu[j], (double)sx);
+        atomicAdd(&w.mu[tr.n + j], (double)sy);
+        atomicAdd(&w.mu[2 * tr.n + j], (double)sz);
+      }
+      __syncwarp();
+    };
     auto on_p2p = [&](bool mine, const int4 ca, const int4 cb, int kx, int ky, int kz, int lvl) {
       const unsigned pm = __ballot_sync(FULL, mine);
       if (!pm) return;
@@ -274,7 +313,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
       __syncwarp();
       for (int b0 = 0; b0 < total; b0 += 32) {
         const int t = b0 + lane;
-        int jsrc = -1;
         if (t < total) {
           int lo = 0, hi = 31;
           while (lo < hi) {
@@ -296,46 +334,20 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
           v.x = v.x + ox;
           v.y = v.y + oy;
           v.z = v.z + oz;
-          s_src[wid][lane] = v;
-          jsrc = j;
+          s_src[wid][qp + lane] = v;
+          s_jidx[wid][qp + lane] = j;
         }
-        s_jidx[wid][lane] = jsrc;
+        qp += min(32, total - b0);
         __syncwarp();
-        const int nn = min(32, total - b0);
-        // diagonal pairing: in round k lane l takes source (l+k) mod 32 and
-        // passes the source-side term to the lane that owns that source
-        T sx = 0, sy = 0, sz = 0;
-        for (int k = 0; k < 32; k++) {
-          const int q = (lane + k) & 31;
-          T wx = 0, wy = 0, wz = 0;
-          if (act && q < nn && s_jidx[wid][q] != i) {
-            const V4 sv = s_src[wid][q];
-            const T dx = sv.x - xi, dy = sv.y - yi, dz = sv.z - zi;
-            const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-            const T inv = nbody_rsqrt(r2);
-            const T f = (inv * inv) * inv;
-            const T g5 = f * (inv * inv) * (T)3;
-            const T rl = fma(dx, lx, fma(dy, ly, dz * lz));
-            const T a = sv.w * f, bb = sv.w * g5 * rl;
-            wx = fma(a, lx, -bb * dx);
-            wy = fma(a, ly, -bb * dy);
-            wz = fma(a, lz, -bb * dz);
+        if (qp >= 32) {
+          p2p_chunk(32);
+          if (lane < qp - 32) {
+            s_src[wid][lane] = s_src[wid][32 + lane];
+            s_jidx[wid][lane] = s_jidx[wid][32 + lane];
           }
-          mx -= wx;
-          my -= wy;
-          mz -= wz;
-          const int from = (lane - k) & 31;
-          sx += __shfl_sync(FULL, wx, from);
-          sy += __shfl_sync(FULL, wy, from);
-          sz += __shfl_sync(FULL, wz, from);
+          qp -= 32;
+          __syncwarp();
         }
-        if (lane < nn) {
-          const int j = s_jidx[wid][lane];
-          atomicAdd(&w.mu[j], (double)sx);
-          atomicAdd(&w.mu[tr.n + j], (double)sy);
-          atomicAdd(&w.mu[2 * tr.n + j], (double)sz);
-        }
-        __syncwarp();
       }
     };
     const bool ok = adj_walk_group<T>(tr, box, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, eps2, stk, w.stack_cap, lane,
@@ -344,6 +356,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
     }
+    if (qp > 0) p2p_chunk(qp);
     if (act) {
       atomicAdd(&w.mu[i], (double)mx);
       atomicAdd(&w.mu[tr.n + i], (double)my);

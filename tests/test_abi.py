@@ -48,6 +48,13 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
     rc, h = nb.nbody_build_tree(p, 10, 1, None)
     assert rc == nb.NBODY_EINVAL
     assert nb.nbody_forces(None, 0) == nb.NBODY_EINVAL
+    assert nb.nbody_forces64(None, 0) == nb.NBODY_EINVAL
+    assert nb.nbody_kdk_adjoint_acc(None, 0, 0, 0, 0.1, 0.2, 0, 0, 0, 0) == nb.NBODY_EINVAL
+    # flags: a walk variant beyond the table is rejected before any work
+    p = nb.nbody_default_params()
+    p.flags = nb.NBODY_FLAG_WALK_VARIANT(4)
+    rc, h = nb.nbody_build_tree(p, 10, 1, None)
+    assert rc == nb.NBODY_EINVAL and not h
 
 
 def test_generated_kernel_header_is_current():

@@ -259,3 +259,25 @@ def test_batched_boxes_match_single(cuda):
         ref = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.55, 4, ewald=4))
         rel = _rel(acc[off[b]:off[b + 1]], ref)
         assert np.median(rel) <= 1e-5, (b, np.median(rel))
+
+
+def test_decision_checksum(cuda):
+    """The walk's decision checksum is reproducible, equal between the mixed
+    and FP64 walks of one tree (same decisions), and changes when a particle
+    moves to another group."""
+    import torch
+    nb = _nb()
+    x, eps = ics.config_small(3)
+    sums = []
+    for prec in (0, 0, 1):
+        tree = nb.Tree(nb.params(eps=eps, theta=0.5, order=4, precision=prec), _pos(x, cuda))
+        _, st = tree.forces(stats=True)
+        sums.append(st["decision_hash"])
+        tree.close()
+    assert sums[0] == sums[1] == sums[2] != 0
+    y = x.copy()
+    y[0] = np.mod(y[0] + 0.37, 1.0)
+    tree = nb.Tree(nb.params(eps=eps, theta=0.5, order=4), _pos(y, cuda))
+    _, st = tree.forces(stats=True)
+    tree.close()
+    assert st["decision_hash"] != sums[0]
