@@ -190,6 +190,22 @@ def run_reference(args, rank, world):
     return 0
 
 
+def reduce_over_ranks(ms: float, n_local: int, steps: int, world: int, device):
+    """Whole-job throughput of independent per-rank boxes: the slowest rank's
+    timed region (max over ranks) and the particles of all ranks (sum).
+    Returns (t_max in ms, total particles, particle updates/s)."""
+    import torch
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        m = torch.tensor([n_local], dtype=torch.int64, device=device)
+        torch.distributed.all_reduce(m, op=torch.distributed.ReduceOp.SUM)
+        ms, n_all = float(t.item()), int(m.item())
+    else:
+        n_all = n_local
+    return ms, n_all, n_all * steps / (ms * 1e-3)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_1407_2600_gb300.nbody as nb
@@ -234,13 +250,7 @@ def run_gpu(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     tm = tree.timing(reset=True)
-    # max over ranks of the timed region
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n * args.steps / (t_max * 1e-3)
+    t_max, n_all, value = reduce_over_ranks(ms, n, args.steps, world, dev)
 
     # roofline of the dominant kernel (the walk), from the timed region
     evals = max(tm["evaluations"], 1)
@@ -287,7 +297,8 @@ def run_gpu(args, rank, world, local_rank):
             hacc.copy_(acc, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         t_e2e = time.perf_counter() - t0
-        e2e = {"value": world * n * k2 / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
+        _, _, e2e_rate = reduce_over_ranks(t_e2e * 1e3, n, k2, world, dev)
+        e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 48 * n,
                "d2h_bytes_per_step": 48 * n}
 
     # reverse mode: a checkpointed trajectory of S steps (checkpoints every 4)
