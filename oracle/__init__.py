@@ -107,13 +107,12 @@ def _d(a):
 
 
 def _soa(pos):
-    """(n,3) or (3,n) array -> contiguous FP64 SoA (3,n)."""
+    """(n, 3) array (one row per particle) -> contiguous FP64 SoA (3, n).
+    Only the (n, 3) layout is accepted, so that n = 3 is unambiguous."""
     p = np.asarray(pos, dtype=np.float64)
-    if p.ndim != 2:
-        raise ValueError("positions must be 2-D")
-    if p.shape[0] != 3 and p.shape[1] == 3:
-        p = p.T
-    return np.ascontiguousarray(p)
+    if p.ndim != 2 or p.shape[1] != 3:
+        raise ValueError("positions must have shape (n, 3)")
+    return np.ascontiguousarray(p.T)
 
 
 def ewald_cfg(alpha=2.0, rcut=None, h2max=None) -> EwaldCfg:

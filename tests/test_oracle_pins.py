@@ -144,7 +144,7 @@ def test_direct_plane_wave_linear_force():
 
 # ---- multipoles and tree ----------------------------------------------------------------
 def test_m2m_exact():
-    pts = RNG.uniform(0.1, 0.3, (3, 40))
+    pts = RNG.uniform(0.1, 0.3, (40, 3))
     m = RNG.uniform(0.5, 1.5, 40)
     c, cp = np.array([0.2, 0.2, 0.2]), np.array([0.25, 0.15, 0.2])
     for p in range(5):
@@ -175,17 +175,17 @@ def test_dtensor_finite_differences():
 
 def test_one_particle_cell_m2p_equals_p2p():
     c = np.array([0.5, 0.5, 0.5])
-    y = np.array([[0.51], [0.49], [0.505]])
+    y = np.array([[0.51, 0.49, 0.505]])  # one particle, (n, 3)
     x = np.array([0.8, 0.1, 0.6])
     eps = 0.01
-    r = y[:, 0] - x
+    r = y[0] - x
     p2p = 0.7 * r / (r @ r + eps * eps) ** 1.5
     for p in (2, 4):
         M = O.p2m(y, np.array([0.7]), c, p)
         a = O.m2p(M, p, x - c, eps)
         # the expansion about c converges to the softened particle force
         assert np.abs(a - p2p).max() <= 5e-3 * np.abs(p2p).max() * (0.02 / 0.6) ** (p - 1)
-    M = O.p2m(c[:, None], np.array([0.7]), c, 4)  # particle at the centre: exact
+    M = O.p2m(c[None, :], np.array([0.7]), c, 4)  # particle at the centre: exact
     assert np.abs(O.m2p(M, 4, x - c, eps) - 0.7 * (c - x) / ((c - x) @ (c - x) + eps * eps) ** 1.5).max() <= 1e-15
 
 
