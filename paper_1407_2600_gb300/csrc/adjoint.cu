@@ -606,9 +606,9 @@ __global__ void adj_field_p2m_kernel(DevTree tr, int le, const double* __restric
     double nl[NE];
 #pragma unroll
     for (int t = 0; t < NE; t++) nl[t] = nu[t];
-    const double cx = ldexp((double)cell_c2((int)compact3((uint64_t)cell), le), -23);
-    const double cy = ldexp((double)cell_c2((int)compact3((uint64_t)cell >> 1), le), -23);
-    const double cz = ldexp((double)cell_c2((int)compact3((uint64_t)cell >> 2), le), -23);
+    const double cx = i2d_pow2(cell_c2((int)compact3((uint64_t)cell), le), -23);
+    const double cy = i2d_pow2(cell_c2((int)compact3((uint64_t)cell >> 1), le), -23);
+    const double cz = i2d_pow2(cell_c2((int)compact3((uint64_t)cell >> 2), le), -23);
     double gx = 0, gy = 0, gz = 0;
     AFE<PE>::p2madj((double)tr.smass[j], tr.spos[j] - cx, tr.spos[tr.n + j] - cy, tr.spos[2 * tr.n + j] - cz, nl,
                     gx, gy, gz);
@@ -628,7 +628,7 @@ __global__ void adj_unscale_kernel(int ncell, const int4* __restrict__ cA, const
     int t = 0;
     for (int o = 0; o <= P; o++) {
       // nu_n = nu'_n (-1)^|n| / n! h^(-2-|n|), h = 2^-level
-      const double sc = ldexp(1.0, lvl * (2 + o)) * ((o & 1) ? -1.0 : 1.0);
+      const double sc = __longlong_as_double((long long)(1023 + lvl * (2 + o)) << 52) * ((o & 1) ? -1.0 : 1.0);
       for (int nx = o; nx >= 0; nx--)
         for (int ny = o - nx; ny >= 0; ny--, t++) {
           const int nz = o - nx - ny;
@@ -658,8 +658,7 @@ __global__ void adj_down_kernel(int ncell, int level, const int4* __restrict__ c
       nup[t] = nu[(int64_t)par * NM + t];
       nc[t] = nu[(int64_t)c * NM + t];
     }
-    AOrd<P>::m2madj(nup, ldexp((double)(a.x - pa.x), -23), ldexp((double)(a.y - pa.y), -23),
-                    ldexp((double)(a.z - pa.z), -23), nc);
+    AOrd<P>::m2madj(nup, i2d_pow2(a.x - pa.x, -23), i2d_pow2(a.y - pa.y, -23), i2d_pow2(a.z - pa.z, -23), nc);
 #pragma unroll
     for (int t = 0; t < NM; t++) nu[(int64_t)c * NM + t] = nc[t];
   }
@@ -675,8 +674,8 @@ __global__ void adj_p2m_kernel(DevTree tr, const double* __restrict__ nu, double
 #pragma unroll
     for (int t = 0; t < NM; t++) nl[t] = nu[(int64_t)leaf * NM + t];
     double gx = 0, gy = 0, gz = 0;
-    AOrd<P>::p2madj((double)tr.smass[j], tr.spos[j] - ldexp((double)a.x, -23), tr.spos[tr.n + j] - ldexp((double)a.y, -23),
-                    tr.spos[2 * tr.n + j] - ldexp((double)a.z, -23), nl, gx, gy, gz);
+    AOrd<P>::p2madj((double)tr.smass[j], tr.spos[j] - i2d_pow2(a.x, -23), tr.spos[tr.n + j] - i2d_pow2(a.y, -23),
+                    tr.spos[2 * tr.n + j] - i2d_pow2(a.z, -23), nl, gx, gy, gz);
     mu[j] += gx;
     mu[tr.n + j] += gy;
     mu[2 * tr.n + j] += gz;

@@ -37,6 +37,42 @@ __device__ __forceinline__ int64_t upper_pref(const uint64_t* __restrict__ k, in
   return lo;
 }
 
+// Galloping forms of the two searches for a prefix P that particle i itself
+// has: the ranges they look for are usually short, so probing i +- 1, 2, 4, ...
+// before bisecting touches a few nearby keys instead of O(log n) scattered ones.
+// first index in (i, hi) whose level-l prefix is > P (hi if none)
+__device__ __forceinline__ int64_t upper_pref_from(const uint64_t* __restrict__ k, int64_t i, int64_t hi,
+                                                   uint64_t P, int level) {
+  int64_t lo = i + 1, step = 1;
+  while (true) {
+    const int64_t probe = i + step;
+    if (probe >= hi) break;
+    if (prefix_of(k[probe], level) > P) {
+      hi = probe;
+      break;
+    }
+    lo = probe + 1;
+    step <<= 1;
+  }
+  return upper_pref(k, lo, hi, P, level);
+}
+// first index in [lo, i] whose level-l prefix is >= P (the start of P's range)
+__device__ __forceinline__ int64_t lower_pref_to(const uint64_t* __restrict__ k, int64_t lo, int64_t i,
+                                                 uint64_t P, int level) {
+  int64_t hi = i, step = 1;
+  while (true) {
+    const int64_t probe = i - step;
+    if (probe < lo) break;
+    if (prefix_of(k[probe], level) < P) {
+      lo = probe + 1;
+      break;
+    }
+    hi = probe;
+    step <<= 1;
+  }
+  return lower_pref(k, lo, hi + 1, P, level);
+}
+
 __device__ __forceinline__ int first_level(const uint64_t* __restrict__ k, int64_t i, int64_t bb) {
   if (i == bb) return 0;
   uint64_t x = k[i - 1] ^ k[i];
@@ -64,15 +100,15 @@ __global__ void count_cells_kernel(BuildArgs a, int* __restrict__ ccount, int8_t
       bool exists = true;
       if (l0 > 0) {
         uint64_t pp = prefix_of(k, l0 - 1);
-        int64_t lo = lower_pref(a.skeys, bb, i + 1, pp, l0 - 1);
-        int64_t hi = upper_pref(a.skeys, i, be, pp, l0 - 1);
+        int64_t lo = lower_pref_to(a.skeys, bb, i, pp, l0 - 1);
+        int64_t hi = upper_pref_from(a.skeys, i, be, pp, l0 - 1);
         exists = (hi - lo) > a.n_leaf;
       }
       if (exists) {
         int l = l0;
         while (true) {
           c++;
-          int64_t hi = upper_pref(a.skeys, i, be, prefix_of(k, l), l);
+          int64_t hi = upper_pref_from(a.skeys, i, be, prefix_of(k, l), l);
           if (hi - i > a.n_leaf && l < a.lmax) l++; else break;
         }
       }
@@ -97,7 +133,7 @@ __global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, c
     int p0 = coff[i];
     for (int t = 0; t < c; t++) {
       int l = l0 + t, p = p0 + t;
-      int64_t hi = upper_pref(a.skeys, i, be, prefix_of(k, l), l);
+      int64_t hi = upper_pref_from(a.skeys, i, be, prefix_of(k, l), l);
       plevel[p] = (uint8_t)l;
       pstart[p] = (int)i;
       pcount[p] = (int)(hi - i);
@@ -105,7 +141,7 @@ __global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, c
       if (t > 0) par = p - 1;
       else if (l == 0) par = -1;
       else {
-        int64_t s = lower_pref(a.skeys, bb, i + 1, prefix_of(k, l - 1), l - 1);
+        int64_t s = lower_pref_to(a.skeys, bb, i, prefix_of(k, l - 1), l - 1);
         par = coff[s] + (l - 1 - (int)l0in[s]);
       }
       pparent[p] = par;
@@ -219,7 +255,7 @@ __global__ void leaf_kernel(int ncell, const int4* __restrict__ cA, const int4* 
     int4 a = cA[b];
     if ((a.w >> 8) != 0) continue;  // not a leaf
     int4 r = cB[b];
-    double cx = ldexp((double)a.x, -23), cy = ldexp((double)a.y, -23), cz = ldexp((double)a.z, -23);
+    const double cx = i2d_pow2(a.x, -23), cy = i2d_pow2(a.y, -23), cz = i2d_pow2(a.z, -23);
     for (int j = r.x; j < r.x + r.y; j++) {
       sleaf[j] = b;
       typename Vec4<T>::type v;
@@ -239,7 +275,7 @@ __global__ void group_flag_kernel(BuildArgs a, int ls, int n_group, int* __restr
     int b = a.sbox[i];
     int64_t bb = a.off[b];
     uint64_t P = prefix_of(a.skeys[i], ls);
-    int64_t rs = lower_pref(a.skeys, bb, i + 1, P, ls);
+    int64_t rs = lower_pref_to(a.skeys, bb, i, P, ls);
     flag[i] = ((i - rs) % n_group) == 0 ? 1 : 0;
   }
 }

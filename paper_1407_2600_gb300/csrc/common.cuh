@@ -70,6 +70,17 @@ __device__ __forceinline__ uint32_t quant21(double x) {
   return (uint32_t)q;
 }
 
+// v * 2^e for |v| < 2^31, exact, on the integer pipe (GB300's FP64 pipe is
+// narrow, and int-to-double conversions run on it)
+__device__ __forceinline__ double i2d_pow2(int v, int e) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? 0x8000000000000000ULL : 0ULL;
+  const unsigned u = v < 0 ? (unsigned)(-(long long)v) : (unsigned)v;
+  const int msb = 31 - __clz(u);
+  const unsigned long long mant = ((unsigned long long)u << (52 - msb)) & 0x000fffffffffffffULL;
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + msb + e) << 52) | mant));
+}
+
 // ---- device-side tree description passed to kernels -------------------------
 struct DevTree {
   int64_t n;

@@ -38,18 +38,9 @@ NB_ORD(2)
 NB_ORD(3)
 NB_ORD(4)
 
-// Exact scalings by powers of two on the integer pipe: GB300's FP64 pipe is
-// narrow, and these run once per moment of every cell.
-// v * 2^e for |v| < 2^31 (exact)
-__device__ __forceinline__ double i2d_pow2(int v, int e) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = v < 0 ? 0x8000000000000000ULL : 0ULL;
-  const unsigned u = v < 0 ? (unsigned)(-(long long)v) : (unsigned)v;
-  const int msb = 31 - __clz(u);
-  const unsigned long long mant = ((unsigned long long)u << (52 - msb)) & 0x000fffffffffffffULL;
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + msb + e) << 52) | mant));
-}
-
+// Exact scalings by powers of two run on the integer pipe (i2d_pow2 in
+// common.cuh, mul_pow2 below): GB300's FP64 pipe is narrow, and these run
+// once per moment of every cell.
 // x * 2^k (exact unless the result under- or overflows); the exponent field
 // is adjusted directly when x and the result are normal numbers
 __device__ __forceinline__ double mul_pow2(double x, int k) {
