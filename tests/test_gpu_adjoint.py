@@ -259,3 +259,27 @@ def test_kdk_adjoint_chain_reuses_and_matches_unchained(cuda):
         a, b = a.cpu().numpy(), b.cpu().numpy()
         rms = np.sqrt(np.mean(b ** 2))
         assert np.abs(a - b).max() <= 1e-5 * rms, np.abs(a - b).max() / rms
+
+
+def test_batched_force_vjp_matches_single_boxes(cuda):
+    """The force VJP of a batched tree (three uneven boxes in one forest)
+    equals, box by box, the VJP of each box on its own."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    boxes = [ics.config_small(21)[0], ics.config_haloes(12, seed=6, n_halo=2, nmin=40, nmax=200)[0],
+             np.random.default_rng(8).uniform(0, 1, (777, 3))]
+    eps = [1.0 / 480, 1.0 / 360, 2e-3]
+    off = np.cumsum([0] + [len(b) for b in boxes])
+    rng = np.random.default_rng(4)
+    lam = rng.standard_normal((off[-1], 3)).astype(np.float32)
+    prm = _prm(1e-3, 0.55, 4)
+    tree = nb.Tree(prm, _t(np.concatenate(boxes), cuda), offsets=off.tolist(), eps=eps)
+    mu = tree.forces_vjp(_t(lam, cuda, torch.float32)).cpu().numpy().T
+    tree.close()
+    for b, xb in enumerate(boxes):
+        t1 = nb.Tree(_prm(eps[b], 0.55, 4), _t(xb, cuda))
+        m1 = t1.forces_vjp(_t(lam[off[b]:off[b + 1]], cuda, torch.float32)).cpu().numpy().T
+        t1.close()
+        got = mu[off[b]:off[b + 1]]
+        rms = np.sqrt(np.mean(m1 ** 2))
+        assert np.abs(got - m1).max() <= 1e-5 * rms, (b, np.abs(got - m1).max() / rms)
