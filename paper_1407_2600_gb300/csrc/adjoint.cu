@@ -779,9 +779,9 @@ cudaError_t launch_adj(const AdjArgs<float>& a, const AdjBuffers& B, const DevTr
   if (variant < 0) {
     // time every variant on this call's data; each trial starts from a zero
     // sink cotangent, which the final run below starts from again
-    cudaEvent_t e0, e1;
-    if ((e = cudaEventCreate(&e0))) return e;
-    if ((e = cudaEventCreate(&e1))) return e;
+    EventPair ev;
+    if ((e = ev.create())) return e;
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     float best = 1e30f;
     variant = 0;
     for (int v = 0; v < kSinkVariants; v++) {
@@ -799,8 +799,6 @@ cudaError_t launch_adj(const AdjArgs<float>& a, const AdjBuffers& B, const DevTr
         variant = v;
       }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lock(g_sink_mutex);
     g_sink_tune.push_back({dev, P, variant});
     adj_prep_kernel<<<gridv(tr.n, 256), 256, 0, s>>>(tr.n, tr.perm, lam, B.lam_s, B.mu);

@@ -81,6 +81,20 @@ __device__ __forceinline__ double i2d_pow2(int v, int e) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + msb + e) << 52) | mant));
 }
 
+// two timing events destroyed on every exit path (the launch autotuners)
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    return e;
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
 // ---- device-side tree description passed to kernels -------------------------
 struct DevTree {
   int64_t n;

@@ -438,10 +438,10 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
     g_tune.push_back({dev, P, fp, 0, {}});
     return launch_variant<T, P>(0, a, nsm, max_blocks, s);
   }
-  cudaEvent_t e0, e1;
+  EventPair ev;
   cudaError_t e;
-  if ((e = cudaEventCreate(&e0))) return e;
-  if ((e = cudaEventCreate(&e1))) return e;
+  if ((e = ev.create())) return e;
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   float best = 1e30f;
   int bv = 0;
   TuneEntry te{dev, P, fp, 0, {}};
@@ -460,8 +460,6 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
       bv = v;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   te.variant = bv;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
