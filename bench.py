@@ -484,7 +484,9 @@ def run_batched(dev, steps: int):
     32 boxes of 48^3, 32 of 64^3 and 32 of 80^3 particles (28,311,552), each
     its own periodic unit box with Zel'dovich initial conditions; theta 0.5,
     quadrupole.  Times `steps` KDK steps (rebuild + forces + kicks + drift)
-    of the whole batch and one force evaluation."""
+    of the whole batch and one force evaluation (rebuild + forces), both as
+    calls made one by one (each build reads its counts back) and as CUDA
+    graphs replayed on reserved capacities (no host round trip at all)."""
     import torch
     import paper_1407_2600_gb300.nbody as nb
     from paper_1407_2600_gb300 import ics
@@ -503,37 +505,84 @@ def run_batched(dev, steps: int):
         tree.kdk_step(mom, acc, a, a1)
         a = a1
     torch.cuda.synchronize()
+    tree.check()
     tree.timing(reset=True)
+    # the timed steps start from this state, once called one by one and once replayed
+    x0, p0, g0 = pos.clone(), mom.clone(), acc.clone()
+    a_list = [a * math.exp(DLNA * k) for k in range(steps + 1)]
+
+    def restore():
+        pos.copy_(x0)
+        mom.copy_(p0)
+        acc.copy_(g0)
+        torch.cuda.synchronize()
+
     stream = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     e[0].record(stream)
-    for _ in range(steps):
-        a1 = a * math.exp(DLNA)
-        tree.kdk_step(mom, acc, a, a1)
-        a = a1
+    for k in range(steps):
+        tree.kdk_step(mom, acc, a_list[k], a_list[k + 1])
     e[1].record(stream)
+    torch.cuda.synchronize()
+    tree.check()
+    x_e, p_e, g_e = pos.clone(), mom.clone(), acc.clone()
     e[2].record(stream)
     tree.rebuild()
     tree.forces(acc)
     e[3].record(stream)
     torch.cuda.synchronize()
-    rc = nb.nbody_check(tree.handle, nb._stream())
-    if rc != nb.NBODY_OK:
-        raise nb.NbodyError(rc, "batched steps")
+    tree.check()
     tm = tree.timing(reset=True)
     ms = e[0].elapsed_time(e[1]) / steps
     fms = e[2].elapsed_time(e[3])
     ev = max(tm["evaluations"], 1)
+    # the same steps captured on capacities fixed at 1.1x the counts of the
+    # starting state (an overflow would be reported by tree.check)
+    restore()
+    tree.rebuild()
+    caps = tree.reserve(0.1)
+    tree.forces(acc)
+    g_steps, g_force = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_steps):
+        for k in range(steps):
+            tree.kdk_step(mom, acc, a_list[k], a_list[k + 1])
+    with torch.cuda.graph(g_force):
+        tree.rebuild()
+        tree.forces(acc)
+    restore()
+    g_steps.replay()  # warm-up replay
+    g_force.replay()
+    torch.cuda.synchronize()
+    tree.check()
+    restore()
+    e[0].record(stream)
+    g_steps.replay()
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    tree.check()
+    same = bool(torch.equal(pos, x_e) and torch.equal(mom, p_e) and torch.equal(acc, g_e))
+    e[2].record(stream)
+    g_force.replay()
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    tree.check()
+    gms = e[0].elapsed_time(e[1]) / steps
+    gfms = e[2].elapsed_time(e[3])
     out = {"workload": "96 periodic boxes: 32 x 48^3 + 32 x 64^3 + 32 x 80^3 Zel'dovich (P~k^-2, rms 0.25 "
                        "spacing, a=0.02), eps = spacing/30 per box; theta 0.5 (opening distance from the cell faces), "
                        "quadrupole, groups within level-3 cells (ewald_grid 4); one tree build and one walk "
                        "launch for all boxes",
-           "n": int(n), "nbox": 96, "steps": steps, "ms_per_kdk_step": ms, "updates_per_s": n / (ms * 1e-3),
-           "force_eval_ms": fms, "force_updates_per_s": n / (fms * 1e-3),
+           "n": int(n), "nbox": 96, "steps": steps,
+           "graph_captured": True, "graph_state_equals_uncaptured": same,
+           "ms_per_kdk_step": gms, "updates_per_s": n / (gms * 1e-3),
+           "force_eval_ms": gfms, "force_updates_per_s": n / (gfms * 1e-3),
+           "reserved_capacity": {"cells": caps[0], "groups": caps[1]},
+           "uncaptured": {"ms_per_kdk_step": ms, "updates_per_s": n / (ms * 1e-3), "force_eval_ms": fms},
            "phases_ms": {k: tm[k] / max(tm["builds"] if k in ("ms_sort", "ms_build", "ms_upward") else ev, 1)
                          for k in ("ms_sort", "ms_build", "ms_upward", "ms_walk", "ms_periodic")},
            "interactions_per_particle": {"p2p": tm["p2p"] / ev / n, "m2p": tm["m2p"] / ev / n},
-           "walk_variant": tm["walk_variant"], "graph_captured": False}
+           "walk_variant": tm["walk_variant"]}
+    del g_steps, g_force
     tree.close()
     return out
 

@@ -306,6 +306,32 @@ int nbody_tree_lookup(const nbody_tree *tree, const uint64_t *keys_dev, int64_t 
 int nbody_sort_keys_noalloc(const double *pos_dev, int64_t n, uint64_t *keys_out_dev,
                             uint32_t *perm_out_dev, nbody_stream_t stream);
 
+/*
+ * Fixed capacities, for steps captured in a CUDA graph (the batched
+ * realisations of Sec. 2.1's "multiple realisations" run as one replayed
+ * graph).  By default every build reads its cell and group counts back to the
+ * host to size the cell buffers and launch grids, and stream capture cannot
+ * hold that read.  After nbody_reserve the cell and group buffers are sized
+ * once for max_cells and max_groups, builds keep their counts on the device
+ * (the kernels read them there; grids are sized for the capacities), and a
+ * build, nbody_forces and nbody_kdk_step enqueue no host synchronisation when
+ * NBODY_FLAG_ASYNC is set, so they can be captured.
+ *   max_cells, max_groups  capacities (both > 0); both 0 returns to counts
+ *                          read back per build
+ * A later build whose counts exceed a capacity writes no buffer past its end:
+ * it sets the overflow status, its counts become 0 and the evaluation that
+ * follows computes nothing (accelerations are left as they were); the next
+ * status read (nbody_check, or any call without NBODY_FLAG_ASYNC) returns
+ * NBODY_EOVERFLOW, and the caller reserves more and steps again from its own
+ * saved state.  The call synchronises the stream, reallocates, rebuilds the
+ * tree from the positions of its last build (which must still be valid) and
+ * returns that build's status (NBODY_EOVERFLOW if it does not fit).  The
+ * first nbody_forces after it (uncaptured) sizes the evaluation buffers and
+ * runs the walk autotuner, so make one before capturing.  Tree statistics and
+ * exports then read the counts from the device.
+ */
+int nbody_reserve(nbody_tree *tree, int64_t max_cells, int64_t max_groups, nbody_stream_t stream);
+
 /* Read and clear the tree's device status word (blocks on the stream). */
 int nbody_check(nbody_tree *tree, nbody_stream_t stream);
 void nbody_tree_free(nbody_tree *tree);

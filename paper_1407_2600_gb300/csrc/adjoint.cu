@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const DevTree& tr = w.tr;
+  const int ngroup = tr.cnt[1];
   int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
   const T scale = (T)kScale;
 
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
     int g = 0;
     if (lane == 0) g = atomicAdd(w.group_ctr, 1);
     g = __shfl_sync(FULL, g, 0);
-    if (g >= tr.ngroup) break;
+    if (g >= ngroup) break;
     const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
     const int cnt = ga.y, box = ga.z;
     const T eps2 = w.eps2[box];
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_src_kernel(AdjArgs<float
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const DevTree& tr = w.tr;
+  const int ngroup = tr.cnt[1];
   int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
   const T scale = (T)kScale;
 
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_src_kernel(AdjArgs<float
     int g = 0;
     if (lane == 0) g = atomicAdd(w.group_ctr, 1);
     g = __shfl_sync(FULL, g, 0);
-    if (g >= tr.ngroup) break;
+    if (g >= ngroup) break;
     const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
     const int cnt = ga.y, box = ga.z;
     const T eps2 = w.eps2[box];
@@ -491,9 +493,10 @@ __global__ void __launch_bounds__(128) adj_field_local_kernel(AFArgs<T> a) {
   constexpr int NL = AFE<PE>::NL;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
+  const int ngroup = tr.cnt[1];
   const T scale = (T)kScale;
   const T fourpi3 = (T)(4.0 * M_PI / 3.0);
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
     const int4 ga = tr.gA[g], gd = tr.gD[g];
     const bool act = lane < ga.y;
     const T* Lr = a.lbuf + (int64_t)gd.w * a.lstride;
@@ -549,10 +552,11 @@ __global__ void __launch_bounds__(128) adj_field_m2l_kernel(AFArgs<T> a) {
   constexpr int NL = AFE<PE>::NL, NE = AFE<PE>::NE, NP = AFE<PE>::NP;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
+  const int ngroup = tr.cnt[1];
   const int ncp = 1 << (3 * a.le);
   const int m = (1 << (a.lg - 1)) + 2;
   const int step = 1 << (23 - a.lg);
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
     const int4 ga = tr.gA[g];
     if (ga.w == 0) continue;
     const int4 gd = tr.gD[g];
@@ -620,9 +624,10 @@ __global__ void adj_field_p2m_kernel(DevTree tr, int le, const double* __restric
 
 // ---- moments: unscale, down the tree, onto the particles --------------------------------
 template <int P>
-__global__ void adj_unscale_kernel(int ncell, const int4* __restrict__ cA, const float* __restrict__ nuc,
-                                   double* __restrict__ nu) {
+__global__ void adj_unscale_kernel(const int* __restrict__ pncell, const int4* __restrict__ cA,
+                                   const float* __restrict__ nuc, double* __restrict__ nu) {
   constexpr int NM = AOrd<P>::NM, NMP = (NM + 3) & ~3;
+  const int ncell = *pncell;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
     const int lvl = cA[c].w & 0xff;
     int t = 0;
@@ -643,9 +648,10 @@ __global__ void adj_unscale_kernel(int ncell, const int4* __restrict__ cA, const
 }
 
 template <int P>
-__global__ void adj_down_kernel(int ncell, int level, const int4* __restrict__ cA, const int4* __restrict__ cB,
-                                double* __restrict__ nu) {
+__global__ void adj_down_kernel(const int* __restrict__ pncell, int level, const int4* __restrict__ cA,
+                                const int4* __restrict__ cB, double* __restrict__ nu) {
   constexpr int NM = AOrd<P>::NM;
+  const int ncell = *pncell;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
     const int4 a = cA[c];
     if ((a.w & 0xff) != level) continue;
@@ -667,6 +673,7 @@ __global__ void adj_down_kernel(int ncell, int level, const int4* __restrict__ c
 template <int P>
 __global__ void adj_p2m_kernel(DevTree tr, const double* __restrict__ nu, double* __restrict__ mu) {
   constexpr int NM = AOrd<P>::NM;
+  if (tr.cnt[0] <= 0) return;  // a build that overflowed its capacity formed no leaves
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < tr.n; j += (int64_t)gridDim.x * blockDim.x) {
     const int leaf = tr.sleaf[j];
     const int4 a = tr.cA[leaf];
@@ -894,9 +901,9 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
   }
 #define NB_ADJD(P)                                                                                   \
   {                                                                                                  \
-    adj_unscale_kernel<P><<<gridv(tr.ncell, 128), 128, 0, s>>>(tr.ncell, tr.cA, B.nuc, B.nu);         \
+    adj_unscale_kernel<P><<<gridv(tr.ncell, 128), 128, 0, s>>>(tr.cnt, tr.cA, B.nuc, B.nu);         \
     for (int l = 1; l <= max_level; l++)                                                             \
-      adj_down_kernel<P><<<gridv(tr.ncell, 128), 128, 0, s>>>(tr.ncell, l, tr.cA, tr.cB, B.nu);       \
+      adj_down_kernel<P><<<gridv(tr.ncell, 128), 128, 0, s>>>(tr.cnt, l, tr.cA, tr.cB, B.nu);       \
     adj_p2m_kernel<P><<<gridv(tr.n, 128), 128, 0, s>>>(tr, B.nu, B.mu);                               \
     break;                                                                                           \
   }

@@ -17,30 +17,32 @@ cudaError_t nb_gather(const double* pos, const float* mass, const uint32_t* perm
                       const int64_t* off, int64_t n, double* spos, float* smass, uint16_t* sbox, cudaStream_t s);
 cudaError_t nb_count_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int n_leaf,
                            int lmax, int* ccount, int8_t* l0, cudaStream_t s);
+cudaError_t nb_cap_check(int* cnt, int cell_cap, int group_cap, unsigned* err, cudaStream_t s);
 cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int n_leaf,
-                          int lmax, const int* ccount, const int* coff, const int8_t* l0, uint8_t* plevel,
-                          int* pstart, int* pcount, int* pparent, cudaStream_t s);
-cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const uint32_t* bfs2pre,
-                         int* pre2bfs, const uint8_t* plevel, const int* pstart, const int* pcount,
-                         const int* pparent, int4* cA, int4* cB, uint64_t* ckey, uint16_t* cbox, cudaStream_t s);
-cudaError_t nb_hash_build(int ncell, const uint64_t* ckey, const uint16_t* cbox, int* hval, uint64_t cap,
-                          unsigned* err, cudaStream_t s);
+                          int lmax, const int* ccount, const int* coff, const int8_t* l0, const int* pncell,
+                          uint8_t* plevel, int* pstart, int* pcount, int* pparent, cudaStream_t s);
+cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const int* pncell,
+                         const uint32_t* bfs2pre, int* pre2bfs, const uint8_t* plevel, const int* pstart,
+                         const int* pcount, const int* pparent, int4* cA, int4* cB, uint64_t* ckey, uint16_t* cbox,
+                         cudaStream_t s);
+cudaError_t nb_hash_build(int ncell, const int* pncell, const uint64_t* ckey, const uint16_t* cbox, int* hval,
+                          uint64_t cap, unsigned* err, cudaStream_t s);
 cudaError_t nb_hash_lookup(const uint64_t* q, int64_t nq, int box, const int* hval, const uint64_t* ckey,
                            const uint16_t* cbox, uint64_t cap, int* out, cudaStream_t s);
-cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* spos, const float* smass,
-                      int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s);
+cudaError_t nb_leaves(int ncell, const int* pncell, const int4* cA, const int4* cB, const double* spos,
+                      const float* smass, int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s);
 cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int ls,
                            int n_group, int* flag, cudaStream_t s);
-cudaError_t nb_group_runs(int ngroup, int4* gA, int4* gD, int* flag, int* excl, int* total, int* tmp,
-                          cudaStream_t s);
-cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, int ls,
-                          const int* flag, const int* gid, int* gstart, const double* spos, int4* gA, int4* gB,
-                          int4* gC, int4* gD, cudaStream_t s);
+cudaError_t nb_group_runs(int ngroup, const int* pngroup, int4* gA, int4* gD, int* flag, int* excl, int* total,
+                          int* tmp, cudaStream_t s);
+cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, const int* pngroup,
+                          int ls, const int* flag, const int* gid, int* gstart, const double* spos, int4* gA,
+                          int4* gB, int4* gC, int4* gD, cudaStream_t s);
 int nb_walk_variant(bool fp64, int order, double* ms);
 int nb_coef_stride(int order);
-cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int4* cB, const double* spos,
-                      const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey, uint32_t* uorder,
-                      uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s);
+cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const int4* cA, const int4* cB,
+                      const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
+                      uint32_t* uorder, uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s);
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, double* fm, cudaStream_t s);
 int nb_walk_warps(bool fp64);
@@ -119,7 +121,14 @@ struct nbody_tree {
   Buf hist, sstatus, tilectr, status;
   // build scratch
   Buf ccount, coff, l0, plevel, pstart, pcount, pparent, bfs2pre, pre2bfs, lvlhist, scantmp, totals;
-  // cells
+  // Cells and groups.  ncell / ngroup are the counts of the last build as the
+  // host knows them; cell_cap / group_cap size the buffers and launch grids.
+  // Without a reservation every build reads its counts back and the
+  // capacities equal them; with one (fixed_cap) builds never read back, the
+  // kernels take the counts from totals[0..1] on the device, and a count
+  // above its capacity sets the overflow status instead.
+  bool fixed_cap = false;
+  int cell_cap = 0, group_cap = 0;
   int ncell = 0, max_level = 0;
   Buf cA, cB, ckey, cbox, hval, mom, uorder, coef, ukey, urng;
   uint64_t hcap = 0;
@@ -182,10 +191,11 @@ struct nbody_tree {
     t.sbox = sbox.as<uint16_t>();
     t.spos = spos.as<double>();
     t.smass = smass.as<float>();
-    t.ncell = ncell;
+    t.cnt = totals.as<int>();
+    t.ncell = cell_cap;
     t.cA = cA.as<int4>();
     t.cB = cB.as<int4>();
-    t.ngroup = ngroup;
+    t.ngroup = group_cap;
     t.gA = gA.as<int4>();
     t.gB = gB.as<int4>();
     t.gC = gC.as<int4>();
@@ -353,6 +363,87 @@ int read_status(nbody_tree* t, cudaStream_t s) {
   return status_to_code(st);
 }
 
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// box offsets and per-box squared softening on the device; once per set-up
+int upload_boxes(nbody_tree* t, cudaStream_t s) {
+  NB_CU(t->off.ensure(8 * (t->nbox + 1)));
+  NB_CU(cudaMemcpyAsync(t->off.p, t->h_off.data(), 8 * (t->nbox + 1), cudaMemcpyHostToDevice, s));
+  NB_CU(t->eps2.ensure(12 * t->nbox + 64));
+  Buf tmp;
+  NB_CU(tmp.ensure(8 * t->nbox));
+  NB_CU(cudaMemcpyAsync(tmp.p, t->h_eps.data(), 8 * t->nbox, cudaMemcpyHostToDevice, s));
+  float* e32 = t->eps2.as<float>();
+  double* e64 = (double*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15));
+  eps2_kernel<<<gridn(t->nbox, 128), 128, 0, s>>>(t->nbox, tmp.as<double>(), e32, e64);
+  NB_CU(cudaGetLastError());
+  NB_CU(cudaStreamSynchronize(s));
+  tmp.release();
+  return NBODY_OK;
+}
+
+// buffers of cells and groups for the given capacities
+int size_cells(nbody_tree* t, int cell_cap, int group_cap) {
+  const nbody_params& p = t->prm;
+  const bool fp64 = p.precision == NBODY_FP64;
+  const int cs = nb_coef_stride(p.order);
+  const int nm = (p.order + 1) * (p.order + 2) * (p.order + 3) / 6;
+  const int64_t nc = cell_cap, ng = group_cap;
+  NB_CU(t->plevel.ensure(nc));
+  NB_CU(t->pstart.ensure(4 * nc));
+  NB_CU(t->pcount.ensure(4 * nc));
+  NB_CU(t->pparent.ensure(4 * nc));
+  NB_CU(t->bfs2pre.ensure(4 * nc));
+  NB_CU(t->pre2bfs.ensure(4 * nc));
+  NB_CU(t->cA.ensure(16 * nc));
+  NB_CU(t->cB.ensure(16 * nc));
+  NB_CU(t->ckey.ensure(8 * nc));
+  NB_CU(t->cbox.ensure(2 * nc));
+  NB_CU(t->mom.ensure(8 * nc * nm));
+  NB_CU(t->uorder.ensure(4 * nc));
+  NB_CU(t->coef.ensure((fp64 ? 8 : 4) * nc * cs));
+  NB_CU(t->ukey.ensure(nc));
+  NB_CU(t->urng.ensure(4 * (256 + 32)));
+  uint64_t hc = 1;
+  while (hc < 2 * (uint64_t)nc) hc <<= 1;
+  t->hcap = hc;
+  NB_CU(t->hval.ensure(4 * hc));
+  NB_CU(t->gstart.ensure(4 * ng));
+  NB_CU(t->gA.ensure(16 * ng));
+  NB_CU(t->gB.ensure(16 * ng));
+  NB_CU(t->gC.ensure(16 * ng));
+  NB_CU(t->gD.ensure(16 * ng));
+  // scratch of the sorts: the key sort's passes and the one-pass cell sorts
+  const int64_t tiles = nb_sort_tiles(t->n) + 1, ctiles = nb_sort_tiles(nc) + 1;
+  NB_CU(t->sstatus.ensure(4 * 256 * (tiles * 12 > ctiles ? tiles * 12 : ctiles)));
+  t->cell_cap = cell_cap;
+  t->group_cap = group_cap;
+  return NBODY_OK;
+}
+
+// counts of the last build as the host sees them (a read back when builds
+// run on reserved capacities and so do not make one)
+int host_counts(const nbody_tree* t, int* nc, int* ng) {
+  if (!t->fixed_cap) {
+    *nc = t->ncell;
+    *ng = t->ngroup;
+    return NBODY_OK;
+  }
+  int c[2] = {0, 0};
+  if (t->last_stream) NB_CU(cudaStreamSynchronize(t->last_stream));
+  NB_CU(cudaMemcpy(c, t->totals.p, sizeof(c), cudaMemcpyDeviceToHost));
+  *nc = c[0];
+  *ng = c[1];
+  return NBODY_OK;
+}
+
 int build_impl(nbody_tree* t, cudaStream_t s) {
   const nbody_params& p = t->prm;
   const int64_t n = t->n;
@@ -375,50 +466,39 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(t->gid.ensure(4 * n));
   NB_CU(t->scantmp.ensure(4 * (nb_scan_tmp_ints(n) + 16)));
   NB_CU(t->totals.ensure(64));
-  const int64_t tiles = nb_sort_tiles(n) + 1;
   NB_CU(t->hist.ensure(4 * 256 * 16));
-  NB_CU(t->sstatus.ensure(4 * 256 * tiles * 12));
   NB_CU(t->tilectr.ensure(4 * 16));
   NB_CU(t->lvlhist.ensure(4 * 256));
-  NB_CU(t->off.ensure(8 * (t->nbox + 1)));
-  NB_CU(cudaMemcpyAsync(t->off.p, t->h_off.data(), 8 * (t->nbox + 1), cudaMemcpyHostToDevice, s));
-  {
-    NB_CU(t->eps2.ensure(12 * t->nbox + 64));
-    Buf tmp;
-    NB_CU(tmp.ensure(8 * t->nbox));
-    NB_CU(cudaMemcpyAsync(tmp.p, t->h_eps.data(), 8 * t->nbox, cudaMemcpyHostToDevice, s));
-    float* e32 = t->eps2.as<float>();
-    double* e64 = (double*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15));
-    eps2_kernel<<<gridn(t->nbox, 128), 128, 0, s>>>(t->nbox, tmp.as<double>(), e32, e64);
-    NB_CU(cudaStreamSynchronize(s));
-    tmp.release();
-  }
+  if (!t->fixed_cap) NB_CU(t->sstatus.ensure(4 * 256 * (nb_sort_tiles(n) + 1) * 12));
+  // the keys start in whichever buffer makes the sort's last pass land in
+  // keys / vals, so every build (and a captured one) leaves them in place
+  const int np = nb_radix_passes(63, t->nbox);
+  Buf& kin = (np & 1) ? t->keys2 : t->keys;
+  Buf& vin = (np & 1) ? t->vals2 : t->vals;
   SortScratch sc;
-  sc.keys_alt = t->keys2.as<uint64_t>();
-  sc.vals_alt = t->vals2.as<uint32_t>();
+  sc.keys_alt = ((np & 1) ? t->keys : t->keys2).as<uint64_t>();
+  sc.vals_alt = ((np & 1) ? t->vals : t->vals2).as<uint32_t>();
   sc.hist = t->hist.as<uint32_t>();
   sc.status = t->sstatus.as<uint32_t>();
   sc.tile_ctr = t->tilectr.as<uint32_t>();
-  sc.tiles_cap = tiles;
+  sc.tiles_cap = (int64_t)(t->sstatus.cap / (4 * 256));
   sc.dstatus = t->status.as<unsigned>();
 
+  const bool timed = !capturing(s);
   cudaEvent_t* be = t->bev[t->nb_log % kRing];
   t->last_stream = s;
-  NB_CU(cudaEventRecord(be[0], s));
+  if (timed) NB_CU(cudaEventRecord(be[0], s));
   // A1 keys, A2 sort, A3 gather
   NB_CU(nb_launch_box_ids(t->off.as<int64_t>(), t->nbox, n, t->box_of.as<uint16_t>(), s));
-  NB_CU(nb_launch_keys(t->pos, n, 0, t->keys.as<uint64_t>(), t->vals.as<uint32_t>(), s));
+  NB_CU(nb_launch_keys(t->pos, n, 0, kin.as<uint64_t>(), vin.as<uint32_t>(), s));
   int alt = 0;
-  NB_CU(nb_radix_sort(t->keys.as<uint64_t>(), t->vals.as<uint32_t>(), n, 63, t->box_of.as<uint16_t>(), t->nbox,
-                      &sc, s, &alt));
-  if (alt) {
-    std::swap(t->keys, t->keys2);
-    std::swap(t->vals, t->vals2);
-  }
+  NB_CU(nb_radix_sort(kin.as<uint64_t>(), vin.as<uint32_t>(), n, 63, t->box_of.as<uint16_t>(), t->nbox, &sc, s,
+                      &alt));
+  if (alt != (np & 1)) return NBODY_ECUDA;
   NB_CU(nb_gather(t->pos, t->mass, t->vals.as<uint32_t>(), t->box_of.as<uint16_t>(), t->off.as<int64_t>(), n,
                   t->spos.as<double>(), t->smass.as<float>(), t->sbox.as<uint16_t>(), s));
-  NB_CU(cudaEventRecord(be[1], s));
-  // A4 tree: cells per particle, scan, groups flags + scan, read totals
+  if (timed) NB_CU(cudaEventRecord(be[1], s));
+  // A4 tree: cells per particle, scan, groups flags + scan, counts
   NB_CU(nb_count_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, p.n_leaf, p.lmax,
                        t->ccount.as<int>(), t->l0.as<int8_t>(), s));
   int* totals = t->totals.as<int>();
@@ -427,64 +507,44 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(nb_group_flags(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, ls, p.n_group,
                        t->gflag.as<int>(), s));
   NB_CU(nb_exclusive_scan_i32(t->gflag.as<int>(), t->gid.as<int>(), n, totals + 1, t->scantmp.as<int>(), s));
-  NB_CU(cudaMemcpyAsync(t->pinned, totals, 8, cudaMemcpyDeviceToHost, s));
-  NB_CU(cudaStreamSynchronize(s));
-  const int ncell = (int)((int*)t->pinned)[0];
-  const int ngroup = (int)((int*)t->pinned)[1];
-  if (ncell <= 0 || ngroup <= 0) return NBODY_EINVAL;
-  t->ncell = ncell;
-  t->ngroup = ngroup;
-  const int cs = nb_coef_stride(p.order);
-  const int nm = (p.order + 1) * (p.order + 2) * (p.order + 3) / 6;
-  NB_CU(t->plevel.ensure(ncell));
-  NB_CU(t->pstart.ensure(4 * (int64_t)ncell));
-  NB_CU(t->pcount.ensure(4 * (int64_t)ncell));
-  NB_CU(t->pparent.ensure(4 * (int64_t)ncell));
-  NB_CU(t->bfs2pre.ensure(4 * (int64_t)ncell));
-  NB_CU(t->pre2bfs.ensure(4 * (int64_t)ncell));
-  NB_CU(t->cA.ensure(16 * (int64_t)ncell));
-  NB_CU(t->cB.ensure(16 * (int64_t)ncell));
-  NB_CU(t->ckey.ensure(8 * (int64_t)ncell));
-  NB_CU(t->cbox.ensure(2 * (int64_t)ncell));
-  NB_CU(t->mom.ensure(8 * (int64_t)ncell * nm));
-  NB_CU(t->uorder.ensure(4 * (int64_t)ncell));
-  NB_CU(t->coef.ensure((fp64 ? 8 : 4) * (int64_t)ncell * cs));
-  uint64_t hc = 1;
-  while (hc < 2 * (uint64_t)ncell) hc <<= 1;
-  t->hcap = hc;
-  NB_CU(t->hval.ensure(4 * hc));
-  NB_CU(t->gstart.ensure(4 * (int64_t)ngroup));
-  NB_CU(t->gA.ensure(16 * (int64_t)ngroup));
-  NB_CU(t->gB.ensure(16 * (int64_t)ngroup));
-  NB_CU(t->gC.ensure(16 * (int64_t)ngroup));
-  NB_CU(t->gD.ensure(16 * (int64_t)ngroup));
-  if (nb_sort_tiles(ncell) + 1 > tiles) {
-    NB_CU(t->sstatus.ensure(4 * 256 * (nb_sort_tiles(ncell) + 1)));
+  if (!t->fixed_cap) {
+    NB_CU(cudaMemcpyAsync(t->pinned, totals, 8, cudaMemcpyDeviceToHost, s));
+    NB_CU(cudaStreamSynchronize(s));
+    const int ncell = (int)((int*)t->pinned)[0];
+    const int ngroup = (int)((int*)t->pinned)[1];
+    if (ncell <= 0 || ngroup <= 0) return NBODY_EINVAL;
+    t->ncell = ncell;
+    t->ngroup = ngroup;
+    int rc = size_cells(t, ncell, ngroup);
+    if (rc) return rc;
     sc.status = t->sstatus.as<uint32_t>();
-    sc.tiles_cap = nb_sort_tiles(ncell) + 1;
+    sc.tiles_cap = (int64_t)(t->sstatus.cap / (4 * 256));
+  } else {
+    NB_CU(nb_cap_check(totals, t->cell_cap, t->group_cap, t->status.as<unsigned>(), s));
+    // slots past the cell count take the largest level code and sort last
+    NB_CU(cudaMemsetAsync(t->plevel.p, 0xff, (size_t)t->cell_cap, s));
   }
+  const int nc = t->cell_cap, ng = t->group_cap;
   NB_CU(nb_emit_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, p.n_leaf, p.lmax,
-                      t->ccount.as<int>(), t->coff.as<int>(), t->l0.as<int8_t>(), t->plevel.as<uint8_t>(),
+                      t->ccount.as<int>(), t->coff.as<int>(), t->l0.as<int8_t>(), totals, t->plevel.as<uint8_t>(),
                       t->pstart.as<int>(), t->pcount.as<int>(), t->pparent.as<int>(), s));
-  NB_CU(nb_sort_digit8(t->plevel.as<uint8_t>(), ncell, t->bfs2pre.as<uint32_t>(), t->lvlhist.as<uint32_t>(), &sc, s));
-  NB_CU(nb_bfs_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), ncell, t->bfs2pre.as<uint32_t>(),
+  NB_CU(nb_sort_digit8(t->plevel.as<uint8_t>(), nc, t->bfs2pre.as<uint32_t>(), t->lvlhist.as<uint32_t>(), &sc, s));
+  NB_CU(nb_bfs_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), nc, totals, t->bfs2pre.as<uint32_t>(),
                      t->pre2bfs.as<int>(), t->plevel.as<uint8_t>(), t->pstart.as<int>(), t->pcount.as<int>(),
                      t->pparent.as<int>(), t->cA.as<int4>(), t->cB.as<int4>(), t->ckey.as<uint64_t>(),
                      t->cbox.as<uint16_t>(), s));
-  NB_CU(nb_hash_build(ncell, t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(), t->hval.as<int>(), hc,
+  NB_CU(nb_hash_build(nc, totals, t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(), t->hval.as<int>(), t->hcap,
                       t->status.as<unsigned>(), s));
-  NB_CU(nb_leaves(ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(), t->smass.as<float>(), n,
+  NB_CU(nb_leaves(nc, totals, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(), t->smass.as<float>(), n,
                   t->sleaf.as<int>(), t->src.p, fp64, s));
-  NB_CU(nb_group_info(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), n, ngroup, ls, t->gflag.as<int>(),
+  NB_CU(nb_group_info(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), n, ng, totals + 1, ls, t->gflag.as<int>(),
                       t->gid.as<int>(), t->gstart.as<int>(), t->spos.as<double>(), t->gA.as<int4>(), t->gB.as<int4>(),
                       t->gC.as<int4>(), t->gD.as<int4>(), s));
-  NB_CU(nb_group_runs(ngroup, t->gA.as<int4>(), t->gD.as<int4>(), t->gflag.as<int>(), t->gid.as<int>(),
+  NB_CU(nb_group_runs(ng, totals + 1, t->gA.as<int4>(), t->gD.as<int4>(), t->gflag.as<int>(), t->gid.as<int>(),
                       totals + 2, t->scantmp.as<int>(), s));
-  NB_CU(cudaEventRecord(be[2], s));
+  if (timed) NB_CU(cudaEventRecord(be[2], s));
   // A5 moments
-  NB_CU(t->ukey.ensure((int64_t)ncell));
-  NB_CU(t->urng.ensure(4 * (256 + 32)));
-  NB_CU(nb_upward(p.order, fp64, ncell, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
+  NB_CU(nb_upward(p.order, fp64, nc, totals, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
                   t->smass.as<float>(), n, t->mom.as<double>(), t->coef.p, t->ukey.as<uint8_t>(),
                   t->uorder.as<uint32_t>(), t->urng.as<uint32_t>(), t->urng.as<int>() + 256, &sc, s));
   if (p.ewald_order > 0) {
@@ -493,8 +553,10 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
     NB_CU(nb_field_moments(p.ewald_order, p.ewald_level, t->nbox, t->off.as<int64_t>(), t->keys.as<uint64_t>(),
                            t->spos.as<double>(), t->smass.as<float>(), n, t->fm.as<double>(), s));
   }
-  NB_CU(cudaEventRecord(be[3], s));
-  t->nb_log++;
+  if (timed) {
+    NB_CU(cudaEventRecord(be[3], s));
+    t->nb_log++;
+  }
   t->forces_valid = false;
   t->field_valid = false;
   return NBODY_OK;
@@ -520,7 +582,7 @@ int eval_prep(nbody_tree* t, cudaStream_t s) {
   }
   if (p.ewald_order > 0) {
     NB_CU(nb_phitilde_table(p.ewald_grid, p.ewald_order + 1, &t->tab64, &t->tab32, s));
-    NB_CU(t->lbuf.ensure((fp64 ? 8 : 4) * (int64_t)t->ngroup * nb_field_stride(p.ewald_order)));
+    NB_CU(t->lbuf.ensure((fp64 ? 8 : 4) * (int64_t)t->group_cap * nb_field_stride(p.ewald_order)));
   }
   return NBODY_OK;
 }
@@ -546,25 +608,27 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   NB_CU(t->accw.ensure((fp64 ? 24 : 12) * n));
   int rc = eval_prep(t, s);
   if (rc) return rc;
+  if (t->fixed_cap) NB_CU(nb_cap_check(t->totals.as<int>(), t->cell_cap, t->group_cap, t->status.as<unsigned>(), s));
   NB_CU(cudaMemsetAsync(t->counters.p, 0, 64, s));
   const void* eps2 = fp64 ? (const void*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15)) : t->eps2.p;
   cudaEvent_t* fe = t->fev[t->nf_log % kRing];
   t->last_stream = s;
-  NB_CU(cudaEventRecord(fe[0], s));
+  const bool timed = !capturing(s);
+  if (timed) NB_CU(cudaEventRecord(fe[0], s));
   DevTree tr = t->dev();
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
                 t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0,
                 s));
-  NB_CU(cudaEventRecord(fe[1], s));
+  if (timed) NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
                     t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, s));
-  NB_CU(cudaEventRecord(fe[2], s));
+  if (timed) NB_CU(cudaEventRecord(fe[2], s));
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
   nb_launch_counter += 1;
-  t->nf_log++;
+  if (timed) t->nf_log++;
   t->forces_valid = true;
   t->field_valid = true;
   return NBODY_OK;
@@ -582,13 +646,14 @@ int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   const int nm = nb_adj_coef_nm(p.order);
   NB_CU(t->a_lam.ensure(12 * n));
   NB_CU(t->a_mu.ensure(24 * n));
-  NB_CU(t->a_nuc.ensure(4 * (int64_t)t->ncell * ((nm + 3) & ~3)));
-  NB_CU(t->a_nu.ensure(8 * (int64_t)t->ncell * nm));
+  NB_CU(t->a_nuc.ensure(4 * (int64_t)t->cell_cap * ((nm + 3) & ~3)));
+  NB_CU(t->a_nu.ensure(8 * (int64_t)t->cell_cap * nm));
   if (p.ewald_order > 0) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
-    NB_CU(t->a_lbar.ensure(8 * (int64_t)t->ngroup * nb_adj_lbar_stride(p.ewald_order)));
+    NB_CU(t->a_lbar.ensure(8 * (int64_t)t->group_cap * nb_adj_lbar_stride(p.ewald_order)));
     NB_CU(t->a_nue.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
   }
+  if (t->fixed_cap) NB_CU(nb_cap_check(t->totals.as<int>(), t->cell_cap, t->group_cap, t->status.as<unsigned>(), s));
   AdjBuffers B;
   B.lam_s = t->a_lam.as<float>();
   B.mu = t->a_mu.as<double>();
@@ -638,16 +703,24 @@ int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, cons
     }
     t->events = true;
   }
+  std::vector<int64_t> off_new(offsets, offsets + nbox + 1);
+  std::vector<double> eps_new(nbox);
+  for (int b = 0; b < nbox; b++) eps_new[b] = eps_host ? eps_host[b] : params->eps;
+  // a rebuild with the same boxes enqueues no host synchronisation (so that
+  // it can be captured on reserved capacities)
+  const bool same_boxes = !fresh && t->off.p && t->nbox == nbox && t->h_off == off_new && t->h_eps == eps_new;
   t->prm = *params;
   t->nbox = nbox;
   t->n = n;
   t->pos = pos;
   t->mass = mass;
-  t->h_off.assign(offsets, offsets + nbox + 1);
-  t->h_eps.resize(nbox);
-  for (int b = 0; b < nbox; b++) t->h_eps[b] = eps_host ? eps_host[b] : params->eps;
+  t->h_off.swap(off_new);
+  t->h_eps.swap(eps_new);
   const long long l0 = nb_launch_counter;
-  rc = build_impl(t, s);
+  rc = same_boxes ? NBODY_OK : upload_boxes(t, s);
+  // parameters may have changed the per-cell sizes of reserved buffers
+  if (rc == NBODY_OK && t->fixed_cap) rc = size_cells(t, t->cell_cap, t->group_cap);
+  if (rc == NBODY_OK) rc = build_impl(t, s);
   t->launches += nb_launch_counter - l0;
   if (rc == NBODY_OK && !(params->flags & NBODY_FLAG_ASYNC)) rc = read_status(t, s);
   if (rc != NBODY_OK && fresh) {
@@ -721,13 +794,15 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_str
       stats->m2l = (double)c[2];
       stats->decision_hash = c[3];
     }
-    stats->ncells = tree->ncell;
-    stats->ngroups = tree->ngroup;
+    int nc = 0, ng = 0;
+    if (host_counts(tree, &nc, &ng) != NBODY_OK) nc = ng = 0;
+    stats->ncells = nc;
+    stats->ngroups = ng;
     stats->nbox = tree->nbox;
     int* ml = nullptr;
-    if (cudaMalloc(&ml, sizeof(int)) == cudaSuccess) {
+    if (nc > 0 && cudaMalloc(&ml, sizeof(int)) == cudaSuccess) {
       cudaMemsetAsync(ml, 0, sizeof(int), s);
-      max_level_kernel<<<gridn(tree->ncell, 256), 256, 0, s>>>(tree->ncell, tree->cA.as<int4>(), ml);
+      max_level_kernel<<<gridn(nc, 256), 256, 0, s>>>(nc, tree->cA.as<int4>(), ml);
       int v = 0;
       if (cudaMemcpyAsync(&v, ml, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
           cudaStreamSynchronize(s) == cudaSuccess)
@@ -876,12 +951,15 @@ int kdk_adjoint_impl(nbody_tree* t, const double* pos0, const float* mom0, const
     if ((rc = ensure_aux(t, s))) return rc;
     nbody_tree* x = t->aux;
     x->prm = t->prm;
-    x->nbox = t->nbox;
     x->n = t->n;
     x->pos = X1;
     x->mass = t->mass;
-    x->h_off = t->h_off;
-    x->h_eps = t->h_eps;
+    if (x->nbox != t->nbox || x->h_off != t->h_off || x->h_eps != t->h_eps || !x->off.p) {
+      x->nbox = t->nbox;
+      x->h_off = t->h_off;
+      x->h_eps = t->h_eps;
+      if ((rc = upload_boxes(x, s))) return rc;
+    }
     if ((rc = build_impl(x, s))) return rc;
     if ((rc = vjp_impl(x, lam_mom1, t->a_out.as<double>(), s))) return rc;
     MU1 = t->a_out.as<double>();
@@ -928,14 +1006,19 @@ int nbody_kdk_adjoint_acc(nbody_tree* t, const double* pos0, const float* mom0, 
 
 int64_t nbody_tree_count(const nbody_tree* t, int what) {
   if (!t) return NBODY_EINVAL;
+  int nc = 0, ng = 0;
+  if (what != NBODY_EXPORT_SORTED_KEYS && what != NBODY_EXPORT_PERM) {
+    int rc = host_counts(t, &nc, &ng);
+    if (rc) return rc;
+  }
   switch (what) {
     case NBODY_EXPORT_SORTED_KEYS:
     case NBODY_EXPORT_PERM: return t->n;
     case NBODY_EXPORT_CELL_KEYS:
     case NBODY_EXPORT_CELL_RANGE:
     case NBODY_EXPORT_CELL_LEVEL:
-    case NBODY_EXPORT_MOMENTS: return t->ncell;
-    case NBODY_EXPORT_GROUPS: return t->ngroup;
+    case NBODY_EXPORT_MOMENTS: return nc;
+    case NBODY_EXPORT_GROUPS: return ng;
     default: return NBODY_EINVAL;
   }
 }
@@ -944,24 +1027,26 @@ int nbody_tree_export(const nbody_tree* t, int what, void* dst, nbody_stream_t s
   if (!t || !dst) return NBODY_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int nm = (t->prm.order + 1) * (t->prm.order + 2) * (t->prm.order + 3) / 6;
+  int nc = 0, ng = 0;
+  int rc = host_counts(t, &nc, &ng);
+  if (rc) return rc;
   switch (what) {
     case NBODY_EXPORT_SORTED_KEYS:
       NB_CU(cudaMemcpyAsync(dst, t->keys.p, 8 * t->n, cudaMemcpyDeviceToDevice, s));
       break;
     case NBODY_EXPORT_PERM: NB_CU(cudaMemcpyAsync(dst, t->vals.p, 4 * t->n, cudaMemcpyDeviceToDevice, s)); break;
     case NBODY_EXPORT_CELL_KEYS:
-      NB_CU(cudaMemcpyAsync(dst, t->ckey.p, 8 * (int64_t)t->ncell, cudaMemcpyDeviceToDevice, s));
+      NB_CU(cudaMemcpyAsync(dst, t->ckey.p, 8 * (int64_t)nc, cudaMemcpyDeviceToDevice, s));
       break;
     case NBODY_EXPORT_CELL_RANGE:
     case NBODY_EXPORT_CELL_LEVEL:
-      export_cells_kernel<<<gridn(t->ncell, 256), 256, 0, s>>>(t->ncell, t->cA.as<int4>(), t->cB.as<int4>(), what,
-                                                                (int*)dst);
+      export_cells_kernel<<<gridn(nc, 256), 256, 0, s>>>(nc, t->cA.as<int4>(), t->cB.as<int4>(), what, (int*)dst);
       break;
     case NBODY_EXPORT_MOMENTS:
-      NB_CU(cudaMemcpyAsync(dst, t->mom.p, 8 * (int64_t)t->ncell * nm, cudaMemcpyDeviceToDevice, s));
+      NB_CU(cudaMemcpyAsync(dst, t->mom.p, 8 * (int64_t)nc * nm, cudaMemcpyDeviceToDevice, s));
       break;
     case NBODY_EXPORT_GROUPS:
-      export_groups_kernel<<<gridn(t->ngroup, 256), 256, 0, s>>>(t->ngroup, t->gA.as<int4>(), (int*)dst);
+      export_groups_kernel<<<gridn(ng, 256), 256, 0, s>>>(ng, t->gA.as<int4>(), (int*)dst);
       break;
     default: return NBODY_EINVAL;
   }
@@ -1028,6 +1113,37 @@ int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
     if (t->tot.p) NB_CU(cudaMemset(t->tot.p, 0, 64));
   }
   return NBODY_OK;
+}
+
+int nbody_reserve(nbody_tree* t, int64_t max_cells, int64_t max_groups, nbody_stream_t stream) {
+  if (!t || max_cells < 0 || max_groups < 0 || (max_cells == 0) != (max_groups == 0)) return NBODY_EINVAL;
+  if (max_cells > ((int64_t)1 << 30) || max_groups > ((int64_t)1 << 30)) return NBODY_EINVAL;
+  // a group holds at least one particle, and the group scans run in
+  // per-particle scratch
+  if (max_groups > t->n) max_groups = t->n;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long l0 = nb_launch_counter;
+  int rc = NBODY_OK;
+  if (max_cells == 0) {
+    t->fixed_cap = false;
+  } else {
+    NB_CU(cudaStreamSynchronize(s));
+    if (t->last_stream) NB_CU(cudaStreamSynchronize(t->last_stream));
+    if ((rc = size_cells(t, (int)max_cells, (int)max_groups))) return rc;
+    t->fixed_cap = true;
+  }
+  // the buffers may have moved: rebuild from the positions of the last build
+  rc = build_impl(t, s);
+  t->launches += nb_launch_counter - l0;
+  if (rc) return rc;
+  rc = read_status(t, s);
+  if (rc == NBODY_OK && t->fixed_cap) {
+    int nc = 0, ng = 0;
+    if ((rc = host_counts(t, &nc, &ng))) return rc;
+    t->ncell = nc;
+    t->ngroup = ng;
+  }
+  return rc;
 }
 
 int nbody_check(nbody_tree* t, nbody_stream_t stream) {

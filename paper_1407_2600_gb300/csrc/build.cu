@@ -119,9 +119,10 @@ __global__ void count_cells_kernel(BuildArgs a, int* __restrict__ ccount, int8_t
 }
 
 __global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, const int* __restrict__ coff,
-                                  const int8_t* __restrict__ l0in, uint8_t* __restrict__ plevel,
-                                  int* __restrict__ pstart, int* __restrict__ pcount,
-                                  int* __restrict__ pparent) {
+                                  const int8_t* __restrict__ l0in, const int* __restrict__ pncell,
+                                  uint8_t* __restrict__ plevel, int* __restrict__ pstart,
+                                  int* __restrict__ pcount, int* __restrict__ pparent) {
+  const int ncell = *pncell;  // 0 when the count exceeded the buffers' capacity
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     int c = ccount[i];
@@ -131,6 +132,7 @@ __global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, c
     int l0 = l0in[i];
     uint64_t k = a.skeys[i];
     int p0 = coff[i];
+    if (p0 + c > ncell) continue;
     for (int t = 0; t < c; t++) {
       int l = l0 + t, p = p0 + t;
       int64_t hi = upper_pref_from(a.skeys, i, be, prefix_of(k, l), l);
@@ -149,18 +151,20 @@ __global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, c
   }
 }
 
-__global__ void bfs_fill_kernel(BuildArgs a, int ncell, const uint32_t* __restrict__ bfs2pre,
+__global__ void bfs_fill_kernel(BuildArgs a, const int* __restrict__ pncell, const uint32_t* __restrict__ bfs2pre,
                                 int* __restrict__ pre2bfs) {
+  const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x)
     pre2bfs[bfs2pre[b]] = b;
 }
 
-__global__ void bfs_cells_kernel(BuildArgs a, int ncell, const uint32_t* __restrict__ bfs2pre,
+__global__ void bfs_cells_kernel(BuildArgs a, const int* __restrict__ pncell, const uint32_t* __restrict__ bfs2pre,
                                  const int* __restrict__ pre2bfs, const uint8_t* __restrict__ plevel,
                                  const int* __restrict__ pstart, const int* __restrict__ pcount,
                                  const int* __restrict__ pparent, int4* __restrict__ cA,
                                  int4* __restrict__ cB, uint64_t* __restrict__ ckey,
                                  uint16_t* __restrict__ cbox) {
+  const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
     int p = bfs2pre[b];
     int l = plevel[p];
@@ -176,7 +180,8 @@ __global__ void bfs_cells_kernel(BuildArgs a, int ncell, const uint32_t* __restr
 }
 
 // daughters of a cell are contiguous in breadth-first order
-__global__ void children_kernel(int ncell, int4* __restrict__ cB) {
+__global__ void children_kernel(const int* __restrict__ pncell, int4* __restrict__ cB) {
+  const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
     int par = cB[b].w;
     if (par < 0) continue;
@@ -184,7 +189,8 @@ __global__ void children_kernel(int ncell, int4* __restrict__ cB) {
   }
 }
 
-__global__ void nchild_kernel(int ncell, int4* __restrict__ cA, const int4* __restrict__ cB) {
+__global__ void nchild_kernel(const int* __restrict__ pncell, int4* __restrict__ cA, const int4* __restrict__ cB) {
+  const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
     int par = cB[b].w;
     if (par < 0) continue;
@@ -208,9 +214,10 @@ __device__ __forceinline__ uint64_t hmix(uint64_t k) {
 
 // slots hold cell indices (-1 = empty); a slot matches when the cell's key
 // and box equal the query
-__global__ void hash_insert_kernel(int ncell, const uint64_t* __restrict__ ckey,
+__global__ void hash_insert_kernel(const int* __restrict__ pncell, const uint64_t* __restrict__ ckey,
                                    const uint16_t* __restrict__ cbox, int* __restrict__ hval,
                                    uint64_t mask, unsigned* err) {
+  const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
     uint64_t h = hmix(ckey[b] ^ ((uint64_t)cbox[b] * 0x9e3779b97f4a7c15ull)) & mask;
     bool done = false;
@@ -248,9 +255,11 @@ __global__ void hash_lookup_kernel(const uint64_t* __restrict__ q, int64_t nq, i
 
 // ---- leaves: particle -> leaf and leaf-relative FP32/FP64 source records ----------
 template <typename T>
-__global__ void leaf_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ cB,
-                            const double* __restrict__ spos, const float* __restrict__ smass, int64_t n,
-                            int* __restrict__ sleaf, typename Vec4<T>::type* __restrict__ src) {
+__global__ void leaf_kernel(const int* __restrict__ pncell, const int4* __restrict__ cA,
+                            const int4* __restrict__ cB, const double* __restrict__ spos,
+                            const float* __restrict__ smass, int64_t n, int* __restrict__ sleaf,
+                            typename Vec4<T>::type* __restrict__ src) {
+  const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
     int4 a = cA[b];
     if ((a.w >> 8) != 0) continue;  // not a leaf
@@ -281,17 +290,20 @@ __global__ void group_flag_kernel(BuildArgs a, int ls, int n_group, int* __restr
 }
 
 __global__ void group_start_kernel(int64_t n, const int* __restrict__ flag, const int* __restrict__ gid,
-                                   int* __restrict__ gstart) {
+                                   const int* __restrict__ pngroup, int* __restrict__ gstart) {
+  const int ngroup = *pngroup;  // 0 when the count exceeded the buffers' capacity
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (flag[i]) gstart[gid[i]] = (int)i;
+    if (flag[i] && gid[i] < ngroup) gstart[gid[i]] = (int)i;
 }
 
 // one warp per group: count, box, integer bounding box and expansion point
-__global__ void group_info_kernel(BuildArgs a, int ngroup, int ls, const int* __restrict__ gstart,
-                                  const double* __restrict__ spos, int4* __restrict__ gA,
-                                  int4* __restrict__ gB, int4* __restrict__ gC, int4* __restrict__ gD) {
+__global__ void group_info_kernel(BuildArgs a, const int* __restrict__ pngroup, int ls,
+                                  const int* __restrict__ gstart, const double* __restrict__ spos,
+                                  int4* __restrict__ gA, int4* __restrict__ gB, int4* __restrict__ gC,
+                                  int4* __restrict__ gD) {
   const int lane = threadIdx.x & 31;
+  const int ngroup = *pngroup;
   for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup;
        g += (gridDim.x * blockDim.x) >> 5) {
     int s = gstart[g];
@@ -323,10 +335,16 @@ __global__ void group_info_kernel(BuildArgs a, int ngroup, int ls, const int* __
 }
 
 // groups sharing an expansion cell (same box, same level-(grid-1) cell) form
-// a run; gA.w = 1 marks a run's first group, gD.w receives the run index
-__global__ void run_flag_kernel(int ngroup, int4* __restrict__ gA, const int4* __restrict__ gD,
-                                int* __restrict__ flag) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x) {
+// a run; gA.w = 1 marks a run's first group, gD.w receives the run index.
+// The flags are scanned over the whole capacity, so slots past the count get 0.
+__global__ void run_flag_kernel(int cap, const int* __restrict__ pngroup, int4* __restrict__ gA,
+                                const int4* __restrict__ gD, int* __restrict__ flag) {
+  const int ngroup = *pngroup;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < cap; g += gridDim.x * blockDim.x) {
+    if (g >= ngroup) {
+      flag[g] = 0;
+      continue;
+    }
     bool first = g == 0;
     if (!first) {
       const int4 a = gD[g], b = gD[g - 1];
@@ -337,10 +355,26 @@ __global__ void run_flag_kernel(int ngroup, int4* __restrict__ gA, const int4* _
   }
 }
 
-__global__ void run_index_kernel(int ngroup, const int* __restrict__ flag, const int* __restrict__ excl,
-                                 int4* __restrict__ gD) {
+__global__ void run_index_kernel(const int* __restrict__ pngroup, const int* __restrict__ flag,
+                                 const int* __restrict__ excl, int4* __restrict__ gD) {
+  const int ngroup = *pngroup;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x)
     gD[g].w = excl[g] + flag[g] - 1;
+}
+
+// Counts of a build whose buffers were sized beforehand (a reserved capacity):
+// a count above its capacity sets the overflow status and both counts drop to
+// zero, so every later kernel of the build and of the evaluation does nothing
+// and no buffer is written past its end.  A built tree has at least one cell
+// and one group, so zero counts (an overflowed build) set the status again
+// when an evaluation checks them.
+__global__ void cap_check_kernel(int* __restrict__ cnt, int cell_cap, int group_cap, unsigned* __restrict__ err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (cnt[0] > cell_cap || cnt[1] > group_cap || cnt[0] <= 0 || cnt[1] <= 0) {
+    atomicOr(err, NB_ST_OVERFLOW);
+    cnt[0] = 0;
+    cnt[1] = 0;
+  }
 }
 
 __global__ void gather_kernel(const double* __restrict__ pos, const float* __restrict__ mass,
@@ -398,34 +432,42 @@ cudaError_t nb_count_cells(const uint64_t* skeys, const uint16_t* sbox, const in
   return cudaGetLastError();
 }
 
-cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n,
-                          int n_leaf, int lmax, const int* ccount, const int* coff, const int8_t* l0,
-                          uint8_t* plevel, int* pstart, int* pcount, int* pparent, cudaStream_t s) {
-  BuildArgs a{skeys, sbox, off, n, n_leaf, lmax};
-  emit_cells_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ccount, coff, l0, plevel, pstart, pcount, pparent);
+cudaError_t nb_cap_check(int* cnt, int cell_cap, int group_cap, unsigned* err, cudaStream_t s) {
+  cap_check_kernel<<<1, 32, 0, s>>>(cnt, cell_cap, group_cap, err);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
-cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const uint32_t* bfs2pre,
-                         int* pre2bfs, const uint8_t* plevel, const int* pstart, const int* pcount,
-                         const int* pparent, int4* cA, int4* cB, uint64_t* ckey, uint16_t* cbox,
-                         cudaStream_t s) {
+cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n,
+                          int n_leaf, int lmax, const int* ccount, const int* coff, const int8_t* l0,
+                          const int* pncell, uint8_t* plevel, int* pstart, int* pcount, int* pparent,
+                          cudaStream_t s) {
+  BuildArgs a{skeys, sbox, off, n, n_leaf, lmax};
+  emit_cells_kernel<<<gridn(n, 256), 256, 0, s>>>(a, ccount, coff, l0, pncell, plevel, pstart, pcount,
+                                                  pparent);
+  nb_launch_counter += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const int* pncell,
+                         const uint32_t* bfs2pre, int* pre2bfs, const uint8_t* plevel, const int* pstart,
+                         const int* pcount, const int* pparent, int4* cA, int4* cB, uint64_t* ckey,
+                         uint16_t* cbox, cudaStream_t s) {
   BuildArgs a{skeys, sbox, nullptr, 0, 0, 0};
-  bfs_fill_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, ncell, bfs2pre, pre2bfs);
-  bfs_cells_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, ncell, bfs2pre, pre2bfs, plevel, pstart, pcount,
+  bfs_fill_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, pncell, bfs2pre, pre2bfs);
+  bfs_cells_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, pncell, bfs2pre, pre2bfs, plevel, pstart, pcount,
                                                      pparent, cA, cB, ckey, cbox);
-  children_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, cB);
-  nchild_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, cA, cB);
+  children_kernel<<<gridn(ncell, 256), 256, 0, s>>>(pncell, cB);
+  nchild_kernel<<<gridn(ncell, 256), 256, 0, s>>>(pncell, cA, cB);
   nb_launch_counter += 4;
   return cudaGetLastError();
 }
 
-cudaError_t nb_hash_build(int ncell, const uint64_t* ckey, const uint16_t* cbox, int* hval, uint64_t cap,
-                          unsigned* err, cudaStream_t s) {
+cudaError_t nb_hash_build(int ncell, const int* pncell, const uint64_t* ckey, const uint16_t* cbox, int* hval,
+                          uint64_t cap, unsigned* err, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(hval, 0xff, sizeof(int) * cap, s);
   if (e) return e;
-  hash_insert_kernel<<<gridn(ncell, 256), 256, 0, s>>>(ncell, ckey, cbox, hval, cap - 1, err);
+  hash_insert_kernel<<<gridn(ncell, 256), 256, 0, s>>>(pncell, ckey, cbox, hval, cap - 1, err);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
@@ -437,25 +479,25 @@ cudaError_t nb_hash_lookup(const uint64_t* q, int64_t nq, int box, const int* hv
   return cudaGetLastError();
 }
 
-cudaError_t nb_leaves(int ncell, const int4* cA, const int4* cB, const double* spos, const float* smass,
-                      int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s) {
+cudaError_t nb_leaves(int ncell, const int* pncell, const int4* cA, const int4* cB, const double* spos,
+                      const float* smass, int64_t n, int* sleaf, void* src, bool fp64, cudaStream_t s) {
   if (fp64)
-    leaf_kernel<double><<<gridn(ncell, 128), 128, 0, s>>>(ncell, cA, cB, spos, smass, n, sleaf,
+    leaf_kernel<double><<<gridn(ncell, 128), 128, 0, s>>>(pncell, cA, cB, spos, smass, n, sleaf,
                                                           (dbl4*)src);
   else
-    leaf_kernel<float><<<gridn(ncell, 128), 128, 0, s>>>(ncell, cA, cB, spos, smass, n, sleaf,
+    leaf_kernel<float><<<gridn(ncell, 128), 128, 0, s>>>(pncell, cA, cB, spos, smass, n, sleaf,
                                                          (float4*)src);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
-cudaError_t nb_group_runs(int ngroup, int4* gA, int4* gD, int* flag, int* excl, int* total, int* tmp,
-                          cudaStream_t s) {
-  run_flag_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(ngroup, gA, gD, flag);
+cudaError_t nb_group_runs(int ngroup, const int* pngroup, int4* gA, int4* gD, int* flag, int* excl, int* total,
+                          int* tmp, cudaStream_t s) {
+  run_flag_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(ngroup, pngroup, gA, gD, flag);
   nb_launch_counter += 1;
   cudaError_t e = nb_exclusive_scan_i32(flag, excl, ngroup, total, tmp, s);
   if (e) return e;
-  run_index_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(ngroup, flag, excl, gD);
+  run_index_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(pngroup, flag, excl, gD);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
@@ -468,12 +510,12 @@ cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const in
   return cudaGetLastError();
 }
 
-cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, int ls,
-                          const int* flag, const int* gid, int* gstart, const double* spos, int4* gA,
+cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, const int* pngroup,
+                          int ls, const int* flag, const int* gid, int* gstart, const double* spos, int4* gA,
                           int4* gB, int4* gC, int4* gD, cudaStream_t s) {
   BuildArgs a{skeys, sbox, nullptr, n, 0, 0};
-  group_start_kernel<<<gridn(n, 256), 256, 0, s>>>(n, flag, gid, gstart);
-  group_info_kernel<<<gridn((int64_t)ngroup * 32, 256), 256, 0, s>>>(a, ngroup, ls, gstart, spos, gA, gB,
+  group_start_kernel<<<gridn(n, 256), 256, 0, s>>>(n, flag, gid, pngroup, gstart);
+  group_info_kernel<<<gridn((int64_t)ngroup * 32, 256), 256, 0, s>>>(a, pngroup, ls, gstart, spos, gA, gB,
                                                                       gC, gD);
   nb_launch_counter += 2;
   return cudaGetLastError();

@@ -105,6 +105,11 @@ struct DevTree {
   const uint16_t* sbox;    // box id per sorted particle
   const double* spos;      // 3n sorted positions (SoA)
   const float* smass;      // sorted masses
+  // ncell and ngroup are the capacities the launch grids and buffers are
+  // sized for; the counts of the last build are on the device (cnt[0] cells,
+  // cnt[1] groups, both <= the capacities) so that a build needs no read back
+  // to the host and a whole step can be captured in a CUDA graph
+  const int* cnt;
   int ncell;
   const int4* cA;          // c2x, c2y, c2z, level | nchild << 8
   const int4* cB;          // start, count, child, parent
@@ -132,9 +137,11 @@ struct SortScratch {
   uint32_t* hist;       // 16 passes x 256
   uint32_t* status;     // tiles x 256 x passes
   uint32_t* tile_ctr;   // passes
-  int64_t tiles_cap;
+  int64_t tiles_cap;    // rows of 256 status words available (tiles x passes)
   unsigned* dstatus;    // error word
 };
+// passes of nb_radix_sort; an odd count leaves the result in the alternate buffers
+int nb_radix_passes(int bit1, int nbox);
 cudaError_t nb_radix_sort(uint64_t* keys, uint32_t* vals, int64_t n, int bit1,
                           const uint16_t* box_of_orig, int nbox, SortScratch* sc, cudaStream_t s,
                           int* result_in_alt);

@@ -205,11 +205,12 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
   constexpr int NL = PE_<PE>::NL, NE = PE_<PE>::NE, NP = PE_<PE>::NP;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
+  const int ngroup = tr.cnt[1];
   const int ncp = 1 << (3 * a.le);
   const int m = (1 << (a.lg - 1)) + 2;
   const int step = 1 << (23 - a.lg);
   const T scale = (T)(1.0 / 8388608.0);
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
     const int4 ga = tr.gA[g];
     if (ga.w == 0) continue;  // not the first group of its run
     const int4 gd = tr.gD[g];
@@ -287,9 +288,10 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
   constexpr int NL = PE_<PE>::NL;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
+  const int ngroup = tr.cnt[1];
   const T scale = (T)(1.0 / 8388608.0);
   const T fourpi3 = (T)(4.0 * M_PI / 3.0);
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < tr.ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
     const int4 ga = tr.gA[g], gd = tr.gD[g];
     if (lane >= ga.y) continue;
     const T* Lr = a.lbuf + (int64_t)gd.w * a.lstride;

@@ -397,15 +397,16 @@ cudaError_t nb_launch_box_ids(const int64_t* off, int nbox, int64_t n, uint16_t*
   return cudaGetLastError();
 }
 
+int nb_radix_passes(int bit1, int nbox) { return (bit1 + 7) / 8 + (nbox > 1 ? (nbox > 256 ? 2 : 1) : 0); }
+
 cudaError_t nb_radix_sort(uint64_t* keys, uint32_t* vals, int64_t n, int bit1,
                           const uint16_t* box_of_orig, int nbox, SortScratch* sc, cudaStream_t s,
                           int* result_in_alt) {
   int nkp = (bit1 + 7) / 8;
-  int nbp = (box_of_orig && nbox > 1) ? (nbox > 256 ? 2 : 1) : 0;
-  int np = nkp + nbp;
+  int np = nb_radix_passes(bit1, box_of_orig ? nbox : 1);
   DigitFn dig{nkp, box_of_orig};
   int64_t tiles = nb_sort_tiles(n);
-  if (tiles > sc->tiles_cap || np > 16) return cudaErrorInvalidValue;
+  if (tiles * np > sc->tiles_cap || np > 16) return cudaErrorInvalidValue;
   cudaError_t e;
   if ((e = cudaMemsetAsync(sc->hist, 0, sizeof(uint32_t) * 256 * np, s))) return e;
   if ((e = cudaMemsetAsync(sc->status, 0, sizeof(uint32_t) * 256 * tiles * np, s))) return e;
@@ -524,7 +525,7 @@ extern "C" int nbody_sort_keys_noalloc(const double* pos_dev, int64_t n, uint64_
   ss.hist = sc->hist;
   ss.status = sc->status;
   ss.tile_ctr = sc->tile_ctr;
-  ss.tiles_cap = kNoAllocTiles;
+  ss.tiles_cap = kNoAllocPasses * kNoAllocTiles;
   ss.dstatus = &sc->err;
   int alt = 0;
   if (nb_radix_sort(keys_out_dev, perm_out_dev, n, 63, nullptr, 1, &ss, s, &alt) != cudaSuccess)

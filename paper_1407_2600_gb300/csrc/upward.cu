@@ -84,10 +84,16 @@ __device__ __forceinline__ void finish_cell(int c, int level, const double* M, T
 // this key, one launch forms all leaves (threads of a warp have similar
 // counts) and one launch per level forms that level's parents from their
 // finished daughters (similar daughter counts), so the FP64 work runs on
-// full warps and no thread waits for another.
-__global__ void upkey_kernel(int ncell, const int4* __restrict__ cA, const int4* __restrict__ cB,
-                             uint8_t* __restrict__ key) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
+// full warps and no thread waits for another.  Slots past the cell count (a
+// reserved capacity) get key 255, which no cell has and the schedule ignores.
+__global__ void upkey_kernel(int cap, const int* __restrict__ pncell, const int4* __restrict__ cA,
+                             const int4* __restrict__ cB, uint8_t* __restrict__ key) {
+  const int ncell = *pncell;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < cap; b += gridDim.x * blockDim.x) {
+    if (b >= ncell) {
+      key[b] = 255;
+      continue;
+    }
     const int4 a = cA[b];
     const int nch = a.w >> 8, lvl = a.w & 0xff;
     key[b] = nch == 0 ? (uint8_t)min(cB[b].y, 63) : (uint8_t)(64 + (NB_QBITS - lvl) * 8 + (nch - 1));
@@ -295,10 +301,10 @@ int nb_coef_stride(int order) {
   }
 }
 
-cudaError_t nb_upward(int order, bool fp64, int ncell, const int4* cA, const int4* cB, const double* spos,
-                      const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey, uint32_t* uorder,
-                      uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s) {
-  upkey_kernel<<<gridc(ncell, 256), 256, 0, s>>>(ncell, cA, cB, ukey);
+cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const int4* cA, const int4* cB,
+                      const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
+                      uint32_t* uorder, uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s) {
+  upkey_kernel<<<gridc(ncell, 256), 256, 0, s>>>(ncell, pncell, cA, cB, ukey);
   nb_launch_counter += 1;
   cudaError_t e = nb_sort_digit8(ukey, ncell, uorder, uhist, sc, s);
   if (e) return e;

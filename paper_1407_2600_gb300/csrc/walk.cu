@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   const unsigned FULL = 0xffffffffu;
   const unsigned ltmask = (1u << lane) - 1u;
   const DevTree& tr = w.tr;
+  const int ngroup = tr.cnt[1];
   int* stk = w.stack + ((int64_t)blockIdx.x * WARPS + wid) * w.stack_cap;
   const T scale = (T)kScale;
 
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     int g = 0;
     if (lane == 0) g = atomicAdd(w.group_ctr, 1);
     g = __shfl_sync(FULL, g, 0);
-    if (g >= tr.ngroup) break;
+    if (g >= ngroup) break;
     const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
     const int cnt = ga.y, box = ga.z;
     const T eps2 = w.eps2[box];
@@ -383,10 +384,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
 
 template <typename T, int P, int WARPS, int MINB, bool PK>
 cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
-  int occ = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB, PK>,
-                                                                 WARPS * 32, 0);
-  if (e) return e;
+  // resident blocks per SM, queried once per variant (and so never while a
+  // stream is being captured, after the first evaluation)
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB, PK>,
+                                                                   WARPS * 32, 0);
+    if (e) {
+      occ = 0;
+      return e;
+    }
+  }
   int grid = nsm * (occ > 0 ? occ : 1);
   if (grid > max_blocks) grid = max_blocks;
   walk_kernel<T, P, WARPS, MINB, PK><<<grid, WARPS * 32, 0, s>>>(a);

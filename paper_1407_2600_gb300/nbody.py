@@ -9,6 +9,7 @@ been built (``python -m paper_1407_2600_gb300.build`` or ``__graft_entry__.build
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from dataclasses import dataclass, field
 
@@ -38,7 +39,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 # every symbol include/nbody.h declares
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces", "nbody_forces64",
            "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
-           "nbody_tree_export", "nbody_tree_lookup", "nbody_check", "nbody_tree_free",
+           "nbody_tree_export", "nbody_tree_lookup", "nbody_reserve", "nbody_check", "nbody_tree_free",
            "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
 
 
@@ -108,6 +109,7 @@ def lib():
         L.nbody_tree_count.restype = C.c_int64
         L.nbody_tree_export.argtypes = [_vp, C.c_int, _vp, _vp]
         L.nbody_tree_lookup.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+        L.nbody_reserve.argtypes = [_vp, C.c_int64, C.c_int64, _vp]
         L.nbody_check.argtypes = [_vp, _vp]
         L.nbody_tree_free.argtypes = [_vp]
         L.nbody_tree_free.restype = None
@@ -191,6 +193,10 @@ def nbody_tree_export(tree: int, what: int, dst_dev: int, stream: int | None = N
 
 def nbody_tree_lookup(tree: int, keys_dev: int, nkeys: int, idx_dev: int, stream: int | None = None) -> int:
     return lib().nbody_tree_lookup(tree, keys_dev, nkeys, idx_dev, stream)
+
+
+def nbody_reserve(tree: int, max_cells: int, max_groups: int, stream: int | None = None) -> int:
+    return lib().nbody_reserve(tree, max_cells, max_groups, stream)
 
 
 def nbody_check(tree: int, stream: int | None = None) -> int:
@@ -314,6 +320,26 @@ class Tree:
                                          lx1.data_ptr(), lp1.data_ptr(), lx0.data_ptr(), lp0.data_ptr(),
                                          _stream()), "nbody_kdk_adjoint_acc")
         return lx0, lp0
+
+    def reserve(self, slack: float = 0.25, max_cells: int | None = None, max_groups: int | None = None):
+        """Fix the cell and group capacities (nbody_reserve) at the given
+        counts, or at the last build's counts times (1 + slack); slack < 0
+        returns to counts read back per build.  Returns (max_cells, max_groups)."""
+        if slack < 0:
+            _check(nbody_reserve(self.handle, 0, 0, _stream()), "nbody_reserve")
+            return 0, 0
+        nc = nbody_tree_count(self.handle, EXPORT["cell_keys"])
+        ng = nbody_tree_count(self.handle, EXPORT["groups"])
+        if nc < 0 or ng < 0:
+            _check(int(min(nc, ng)), "nbody_tree_count")
+        mc = int(max_cells) if max_cells is not None else int(math.ceil(nc * (1.0 + slack))) + 64
+        mg = int(max_groups) if max_groups is not None else int(math.ceil(ng * (1.0 + slack))) + 64
+        _check(nbody_reserve(self.handle, mc, mg, _stream()), "nbody_reserve")
+        return mc, mg
+
+    def check(self):
+        """Status of the calls made since the last read (nbody_check)."""
+        _check(nbody_check(self.handle, _stream()), "nbody_check")
 
     def timing(self, reset=True):
         t = Timing()

@@ -1,0 +1,124 @@
+"""Steps on reserved capacities and captured in a CUDA graph (the batched
+realisations, Sec. 2.1): builds that keep their counts on the device give
+bit-identical trees and forces, a captured sequence of KDK steps replays to
+the same state as the same steps called one by one, its final forces match
+the oracle tree, and capacities that are too small are reported as
+NBODY_EOVERFLOW without touching memory past the buffers."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_2600_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+SIZES = (16, 16, 24, 24, 32)
+
+
+def _setup(dev, flags=0, seed=3):
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    x, p, off, eps = ics.config_batched(seed, sizes=SIZES)
+    pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
+    mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
+    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=2, ewald_grid=4,
+                    flags=nb.NBODY_FLAG_MAC_EDGE | flags)
+    tree = nb.Tree(prm, pos, offsets=off.tolist(), eps=eps)
+    return tree, pos, mom, off, eps
+
+
+def test_reserved_capacity_builds_match_exact(cuda):
+    import torch
+    tree, pos, mom, off, eps = _setup(cuda)
+    acc0, st0 = tree.forces(stats=True)
+    keys0 = tree.export("cell_keys").clone()
+    groups0 = tree.export("groups").clone()
+    mc, mg = tree.reserve(0.25)
+    assert mc > st0["ncells"] and mg > st0["ngroups"]
+    acc1, st1 = tree.forces(stats=True)
+    assert st1["ncells"] == st0["ncells"] and st1["ngroups"] == st0["ngroups"]
+    assert st1["decision_hash"] == st0["decision_hash"]
+    assert torch.equal(tree.export("cell_keys"), keys0)
+    assert torch.equal(tree.export("groups"), groups0)
+    assert torch.equal(acc1, acc0)
+    # back to counts read per build
+    tree.reserve(-1)
+    acc2 = tree.forces()
+    assert torch.equal(acc2, acc0)
+    tree.close()
+
+
+def test_graph_captured_kdk_steps_match_eager_and_oracle(cuda):
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    steps, a0, dlna = 3, 0.02, 0.1
+    a_list = [a0 * math.exp(dlna * k) for k in range(steps + 1)]
+    # eager reference: counts read back per build
+    te, pe, me, off, eps = _setup(cuda)
+    ae = te.forces()
+    for k in range(steps):
+        te.kdk_step(me, ae, a_list[k], a_list[k + 1])
+    torch.cuda.synchronize()
+    # reserved capacities, asynchronous calls, captured
+    tg, pg, mg, _, _ = _setup(cuda, flags=nb.NBODY_FLAG_ASYNC)
+    ag = tg.forces()
+    tg.reserve(0.25)
+    tg.forces(ag)           # sizes the evaluation buffers on the reserved capacities
+    x_init, p_init, g_init = pg.clone(), mg.clone(), ag.clone()
+    torch.cuda.synchronize()
+    tg.check()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for k in range(steps):
+            tg.kdk_step(mg, ag, a_list[k], a_list[k + 1])
+    # capture records the steps without running them
+    assert torch.equal(pg, x_init) and torch.equal(mg, p_init)
+    graph.replay()
+    torch.cuda.synchronize()
+    tg.check()
+    assert torch.equal(pg, pe) and torch.equal(mg, me) and torch.equal(ag, ae)
+    # a second replay from the restored initial state gives the same state again
+    pg.copy_(x_init)
+    mg.copy_(p_init)
+    ag.copy_(g_init)
+    graph.replay()
+    torch.cuda.synchronize()
+    tg.check()
+    assert torch.equal(pg, pe) and torch.equal(mg, me) and torch.equal(ag, ae)
+    # the replayed forces at the final positions against the oracle tree
+    x = pg.cpu().numpy().T
+    acc = ag.cpu().numpy().T.astype(np.float64)
+    for b in (0, len(SIZES) - 1):
+        xb = x[off[b]:off[b + 1]]
+        tgt = ics.random_targets(len(xb), 128, 90 + b)
+        at = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.5, 2, n_direct=2, ewald=4, mac=1,
+                                                             ew_grid=4), targets=tgt)
+        a = acc[off[b] + tgt]
+        rt = np.linalg.norm(a - at, axis=1) / np.linalg.norm(at, axis=1)
+        assert np.median(rt) <= 1e-5, (b, np.median(rt))
+    del graph
+    te.close()
+    tg.close()
+
+
+def test_capacity_overflow_is_reported_and_recovers(cuda):
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    tree, pos, mom, off, eps = _setup(cuda)
+    acc0, st = tree.forces(stats=True)
+    nc, ng = st["ncells"], st["ngroups"]
+    for mc, mg in ((nc // 2, ng + 64), (nc + 64, ng // 2), (nc - 1, ng)):
+        with pytest.raises(nb.NbodyError) as ei:
+            tree.reserve(max_cells=mc, max_groups=mg)
+        assert ei.value.code == nb.NBODY_EOVERFLOW
+        # the overflowed build evaluates nothing and reports it again
+        acc = torch.zeros_like(acc0)
+        with pytest.raises(nb.NbodyError) as ei:
+            tree.forces(acc)
+        assert ei.value.code == nb.NBODY_EOVERFLOW
+    # exact capacities fit
+    tree.reserve(max_cells=nc, max_groups=ng)
+    assert torch.equal(tree.forces(), acc0)
+    tree.close()
