@@ -56,7 +56,7 @@ class TreeParams(C.Structure):
     _fields_ = [("eps", C.c_double), ("theta", C.c_double), ("order", C.c_int),
                 ("n_leaf", C.c_int), ("n_group", C.c_int), ("n_direct", C.c_int),
                 ("lmax", C.c_int), ("ewald", C.c_int), ("ew_level", C.c_int),
-                ("ew_grid", C.c_int), ("mac", C.c_int)]
+                ("ew_grid", C.c_int), ("mac", C.c_int), ("bg", C.c_int)]
 
 
 class EwaldCfg(C.Structure):
@@ -98,6 +98,8 @@ def _lib():
             L.or_m2m.argtypes = [_dp, _dp, _dp, C.c_int, _dp]
             L.or_dtensor.argtypes = [_dp, C.c_double, C.c_int, _dp]
             L.or_m2p.argtypes = [_dp, C.c_int, _dp, C.c_double, _dp]
+            L.or_m2p_orders.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_double, _dp]
+            L.or_cube_moments.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
             _LIB = L
     return _LIB
 
@@ -236,13 +238,14 @@ def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int = 64):
 
 
 def tree_params(eps, theta, order, n_leaf=16, n_group=32, n_direct=None, lmax=21, ewald=4,
-                ew_level=3, ew_grid=6, mac=0) -> TreeParams:
+                ew_level=3, ew_grid=6, mac=0, bg=0) -> TreeParams:
     """mac 0: the opening test measures d from the cell centre to the group
-    box; mac 1: from the cell's faces (box to box)."""
+    box; mac 1: from the cell's faces (box to box).  bg = q > order adds the
+    orders order+1..q of each expanded cell's uniform background share."""
     if n_direct is None:
         n_direct = 2 if order <= 2 else 4
     return TreeParams(eps, theta, order, n_leaf, n_group, n_direct, lmax, ewald, ew_level,
-                      ew_grid, mac)
+                      ew_grid, mac, bg)
 
 
 def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,
@@ -337,6 +340,22 @@ def m2p(M, p, R, eps):
     a = np.zeros(3)
     _lib().or_m2p(_d(M), p, _d(R), eps, _d(a))
     return a
+
+
+def m2p_orders(M, pmin, pmax, R, eps):
+    """Acceleration from the orders pmin..pmax of the moments M only."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    a = np.zeros(3)
+    _lib().or_m2p_orders(_d(M), pmin, pmax, _d(R), eps, _d(a))
+    return a
+
+
+def cube_moments(s, rho, p):
+    """Moments (|n| <= p) about its centre of a cube of side s, density rho."""
+    C_ = np.zeros(nmom(p))
+    _lib().or_cube_moments(s, rho, p, _d(C_))
+    return C_
 
 
 def multi_indices(p):

@@ -87,6 +87,12 @@ typedef struct {
   int ew_grid;    /* expansion points snap to the lattice 2^-ew_grid */
   int mac;        /* distance d of the opening test: 0 from the cell centre to
                      the group box, 1 from the cell's boundary to the group box */
+  int bg;         /* 0, or the highest order q (p < q <= 8) of the uniform
+                     background terms: every cell used through its expansion
+                     also gets the orders p+1..q of a cube of the mean density
+                     filling it, with the Newtonian kernel (the higher moments
+                     of the cell's uniform share, which dominate the expansion
+                     error of a near-uniform state) */
 } or_tree_params;
 
 /* stats[0] = P2P pair interactions, stats[1] = M2P interactions,
@@ -112,6 +118,10 @@ void or_m2m(const double *Mc, const double c[3], const double cp[3], int p, doub
 void or_dtensor(const double R[3], double eps, int pmax, double *D);
 /* acceleration at R from a cell with moments M (order p), softened */
 void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]);
+/* the same with only the orders pmin..pmax of M (pmax <= 8) */
+void or_m2p_orders(const double *M, int pmin, int pmax, const double R[3], double eps, double a[3]);
+/* moments (order <= p) of a cube of side s and density rho about its centre */
+void or_cube_moments(double s, double rho, int p, double *C);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,12 @@
  *           opened), and the MAC distance uses that image.
  *  M2P      a_k = sum_{|n|<=p} ((-1)^|n|/n!) M_n d^{n+e_k} g(R), R = x - c*,
  *           g = (|R|^2 + eps^2)^-1/2, moments about the geometric centre.
+ *  background (bg = q > p) a cell used through its expansion also adds the
+ *           orders p+1..q of a_k for the moments C_n of a cube of the mean
+ *           density (total mass / unit volume) filling the cell, with the
+ *           Newtonian kernel g = 1/|R|: the truncation error of the uniform
+ *           share of every cell, which is what subtracting the uniform
+ *           background from every cell (and summing it exactly) removes.
  *  P2P      a += m_j r / (|r|^2 + eps^2)^(3/2), r = x_j* - x_i, j != i.
  *  periodic a_E(r) = a_N(r) + (4 pi/3) r + C~(r) for any image r; the walk sums
  *           the Newton/Plummer part, the background term is summed exactly
@@ -119,15 +125,15 @@ void or_m2m(const double *Mc, const double c[3], const double cp[3], int p, doub
 /* d^m g, |m| <= pmax, g(R) = (|R|^2+eps^2)^-1/2, explicit Hermite-product form:
  *   d^m g = sum_{k <= m/2} prod_d [m_d! / (k_d! (m_d - 2k_d)! 2^k_d)] R^(m-2k) F_{|m|-|k|}
  *   F_j = 2^j f^(j)(s) = (-1)^j (2j-1)!! s^(-1/2-j),  s = |R|^2 + eps^2.
- * The term list is enumerated once (orders <= 6). */
-#define DT_PMAX 6
+ * The term list is enumerated once (orders <= 9). */
+#define DT_PMAX 9
 typedef struct {
   double cf;
   int e[3], j;
 } hterm;
-static hterm g_ht[1024];
-static int g_hbeg[128], g_hend[128];
-static int g_ml[128][3];
+static hterm g_ht[4096];
+static int g_hbeg[256], g_hend[256];
+static int g_ml[256][3];
 
 __attribute__((constructor)) static void hermite_init(void) {
   int nm = or_nmom(DT_PMAX), nt = 0;
@@ -175,18 +181,37 @@ void or_dtensor(const double R[3], double eps, int pmax, double *D) {
   }
 }
 
-void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]) {
-  double D[64];
-  or_dtensor(R, eps, p + 1, D);
-  int nm = or_nmom(p);
+void or_m2p_orders(const double *M, int pmin, int pmax, const double R[3], double eps, double a[3]) {
+  double D[256];
+  or_dtensor(R, eps, pmax + 1, D);
+  int nm = or_nmom(pmax);
   a[0] = a[1] = a[2] = 0.0;
-  for (int t = 0; t < nm; t++) {
+  for (int t = pmin > 0 ? or_nmom(pmin - 1) : 0; t < nm; t++) {
     int nx = g_ml[t][0], ny = g_ml[t][1], nz = g_ml[t][2];
     int o = nx + ny + nz;
     double C = ((o & 1) ? -1.0 : 1.0) * M[t] / (fact(nx) * fact(ny) * fact(nz));
     a[0] += C * D[mi_idx(nx + 1, ny, nz)];
     a[1] += C * D[mi_idx(nx, ny + 1, nz)];
     a[2] += C * D[mi_idx(nx, ny, nz + 1)];
+  }
+}
+
+void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]) {
+  or_m2p_orders(M, 0, p, R, eps, a);
+}
+
+/* Moments about its centre of a cube of side s filled with density rho:
+ * C_n = rho prod_d int_{-s/2}^{s/2} x^{n_d} dx, i.e. rho prod_d s^(n_d+1) /
+ * ((n_d+1) 2^n_d) for even n_d and 0 for odd n_d. */
+void or_cube_moments(double s, double rho, int p, double *C) {
+  int nm = or_nmom(p);
+  for (int t = 0; t < nm; t++) {
+    double v = rho;
+    for (int d = 0; d < 3; d++) {
+      int k = g_ml[t][d];
+      v *= (k & 1) ? 0.0 : ipow(s, k + 1) / ((double)(k + 1) * ipow(2.0, k));
+    }
+    C[t] = v;
   }
 }
 
@@ -295,6 +320,7 @@ typedef struct {
   const int64_t *ec_ix; /* 3 per cell */
   const double *ec_mom; /* nmom(p_E) per cell */
   const double *lat;    /* phi~ lattice, orders 0..p_E+1 */
+  double rho;           /* mean density: total mass over the unit box */
 } walkctx;
 
 typedef struct {
@@ -372,6 +398,14 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
     if (use_m2p) {
       double R[3] = {xi[0] - cs[0], xi[1] - cs[1], xi[2] - cs[2]};
       or_m2p(M, p->order, R, p->eps, a);
+      if (p->bg > p->order) {
+        /* the cell's share of the uniform background (a cube of the mean
+           density filling the cell) beyond order p, Newtonian kernel */
+        double C[256], ab[3];
+        or_cube_moments(ldexp(1.0, -c->level), w->rho, p->bg, C);
+        or_m2p_orders(C, p->order + 1, p->bg, R, 0.0, ab);
+        for (int d = 0; d < 3; d++) a[d] += ab[d];
+      }
       st->m2p += 1.0;
     } else {
       for (int64_t j = c->start; j < c->start + c->count; j++) {
@@ -511,7 +545,7 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
   if (p->order < 0 || p->order > 4 || p->lmax < 2 || p->lmax > QBITS || p->n_leaf < 1 ||
       p->n_group < 1 || p->n_direct > p->n_leaf || p->ewald < 0 || p->ewald > 5 ||
       (p->ewald > 0 && !tab) || p->ew_level < 1 || p->ew_level > 8 ||
-      p->ew_grid < p->ew_level + 1 || p->ew_grid > 10)
+      p->ew_grid < p->ew_level + 1 || p->ew_grid > 10 || p->bg < 0 || p->bg > 8)
     return -1;
   int64_t *perm = malloc(sizeof(int64_t) * n);
   uint64_t *skeys = malloc(sizeof(uint64_t) * n);
@@ -592,6 +626,8 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
   w.ec_ix = ec_ix;
   w.ec_mom = ec_mom;
   w.lat = tab;
+  w.rho = 0.0;
+  for (int64_t i = 0; i < n; i++) w.rho += Ms[i];
   for (int l = 0; l <= QBITS; l++) {
     double s = ldexp(1.0, 23 - l);
     w.T[l] = floor((s * s) / (p->theta * p->theta));

@@ -189,6 +189,68 @@ def test_one_particle_cell_m2p_equals_p2p():
     assert np.abs(O.m2p(M, 4, x - c, eps) - 0.7 * (c - x) / ((c - x) @ (c - x) + eps * eps) ** 1.5).max() <= 1e-15
 
 
+def _gauss_cube(s, k):
+    """Gauss-Legendre nodes and weights (k per axis) on the cube [-s/2, s/2]^3."""
+    t, w = np.polynomial.legendre.leggauss(k)
+    t = 0.5 * s * t
+    w = 0.5 * s * w
+    X, Y, Z = np.meshgrid(t, t, t, indexing="ij")
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1), W.ravel()
+
+
+def test_cube_moments_match_quadrature():
+    """Moments of a uniform cube against Gauss-Legendre quadrature (exact for
+    these polynomial degrees), for side and density not equal to 1."""
+    s, rho = 0.37, 2.5
+    y, w = _gauss_cube(s, 6)
+    C_ = O.cube_moments(s, rho, 8)
+    for t, (nx, ny, nz) in enumerate(O.multi_indices(8)):
+        q = rho * np.sum(w * y[:, 0] ** nx * y[:, 1] ** ny * y[:, 2] ** nz)
+        assert abs(C_[t] - q) <= 1e-14 * max(abs(q), rho * s ** 3 * (s / 2) ** (nx + ny + nz)), (nx, ny, nz)
+
+
+def test_cube_expansion_converges_to_cube_field():
+    """The Newtonian field of a uniform cube at an exterior point, by
+    high-order quadrature, against its multipole series from the cube's
+    moments: the error falls with every even order added (the odd orders
+    vanish), so the background terms of the tree have the right sign and
+    normalisation at each order."""
+    s, rho = 0.25, 1.3
+    y, w = _gauss_cube(s, 40)
+    C_ = O.cube_moments(s, rho, 8)
+    for R in (np.array([0.55, 0.21, 0.08]), np.array([0.4, 0.4, 0.35]), np.array([0.02, -0.61, 0.3])):
+        d = y - R
+        r = np.sqrt(np.sum(d * d, axis=1))
+        exact = rho * np.sum((w / r ** 3)[:, None] * d, axis=0)
+        errs = []
+        for q in (0, 2, 4, 6, 8):
+            a = O.m2p_orders(C_, 0, q, R, 0.0)
+            errs.append(np.linalg.norm(a - exact) / np.linalg.norm(exact))
+        # order 2 of a cube is isotropic and adds nothing to a Newtonian field
+        assert abs(errs[1] - errs[0]) <= 1e-12
+        assert errs[2] < 0.2 * errs[1] and errs[3] < 0.5 * errs[2] and errs[4] < 0.5 * errs[3], errs
+        # the series converges outside the cube's circumscribed sphere
+        assert errs[4] <= (math.sqrt(3.0) * s / 2 / np.linalg.norm(R)) ** 10, errs
+
+
+def test_background_terms_cancel_a_lattice():
+    """A perfect lattice feels no force.  The expansion error of the tree on
+    it is the truncation error of each cell's uniform share, which the
+    background terms remove: with them the residual force falls by more than
+    an order of magnitude (a sign or factor error would not)."""
+    ng = 16
+    x = ics.lattice(ng)
+    eps = 1.0 / (30 * ng)
+    tg = ics.random_targets(len(x), 128, 5)
+    scale = 4 * math.pi * 0.25 / ng  # force of a displacement of a quarter spacing
+    res = {}
+    for bg in (0, 4, 6):
+        tp = O.tree_params(eps, 0.5, 2, n_direct=2, ewald=4, mac=0, ew_grid=4, bg=bg)
+        res[bg] = np.median(np.linalg.norm(O.tree_forces(x, None, tp, targets=tg), axis=1)) / scale
+    assert res[4] <= 0.1 * res[0] and res[6] <= 1.1 * res[4], res
+
+
 def test_tree_topology_invariants():
     x, _ = ics.config_haloes(16, seed=4, n_halo=3, nmin=100, nmax=400)
     key, lev, st, ct = O.tree_cells(x, n_leaf=8)
