@@ -62,7 +62,15 @@ enum {
   /* opening test with d measured from the cell's faces to the group box
    * (box-to-box distance) instead of from the cell centre: a stricter test
    * at the same theta (see nbody_params.theta) */
-  NBODY_FLAG_MAC_EDGE = 2
+  NBODY_FLAG_MAC_EDGE = 2,
+  /* uniform-background terms (Sec. 2.1's background subtraction for
+   * near-uniform states): every cell used through its expansion also adds
+   * the next even order of the field of a cube of the box's mean density
+   * filling it (order 4 after expansions of order 0 and 2, order 6 after
+   * order 4; Newtonian kernel), i.e. the truncation error of the cell's
+   * uniform share, which dominates the expansion error when the density is
+   * nearly uniform.  Orders 1 and 3 reject the flag (NBODY_EINVAL). */
+  NBODY_FLAG_BACKGROUND = 4
 };
 /* flags bits 8..11: walk launch variant + 1 to use instead of the autotuned
  * one (0 = autotune).  Mixed precision has variants 0..3 (one M2P per

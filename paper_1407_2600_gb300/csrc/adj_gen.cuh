@@ -2,8 +2,191 @@
 // Reverse-mode (adjoint) kernels of the M2P, M2M, P2M and image-field expansions.
 #pragma once
 
-__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {
-  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+template <typename T>
+__device__ __forceinline__ void cube_bg_hvp_l4(T q, T Rx, T Ry, T Rz, T lx, T ly, T lz, T& ox, T& oy,
+                                             T& oz) {
+  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;
+  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));
+  const T ir = nbody_rsqrt(r2);
+  const T ir2 = ir * ir;
+  const T u = q * ir * ir2 * ir2 * ir2 * ir2 * ir2;
+  const T X0Y0Z2 = Z * Z;
+  const T X0Y1Z1 = Z * Y;
+  const T X0Y2Z0 = Y * Y;
+  const T X1Y0Z1 = Z * X;
+  const T X1Y1Z0 = Y * X;
+  const T X2Y0Z0 = X * X;
+  T w0 = T(0.21875) * X0Y0Z2;
+  w0 = fma(T(-0.21875), X0Y1Z1, w0);
+  w0 = fma(T(0.21875), X0Y2Z0, w0);
+  w0 = fma(T(-0.36458333333333331), X1Y0Z1, w0);
+  w0 = fma(T(-0.36458333333333331), X1Y1Z0, w0);
+  w0 = fma(T(0.072916666666666671), X2Y0Z0, w0);
+  T w1 = T(0.21875) * X0Y0Z2;
+  w1 = fma(T(-0.36458333333333331), X0Y1Z1, w1);
+  w1 = fma(T(0.072916666666666671), X0Y2Z0, w1);
+  w1 = fma(T(-0.21875), X1Y0Z1, w1);
+  w1 = fma(T(-0.36458333333333331), X1Y1Z0, w1);
+  w1 = fma(T(0.21875), X2Y0Z0, w1);
+  T w2 = T(0.072916666666666671) * X0Y0Z2;
+  w2 = fma(T(-0.36458333333333331), X0Y1Z1, w2);
+  w2 = fma(T(0.21875), X0Y2Z0, w2);
+  w2 = fma(T(-0.36458333333333331), X1Y0Z1, w2);
+  w2 = fma(T(-0.21875), X1Y1Z0, w2);
+  w2 = fma(T(0.21875), X2Y0Z0, w2);
+  T d00 = T(-0.36458333333333331) * Z;
+  d00 = fma(T(-0.36458333333333331), Y, d00);
+  d00 = fma(T(0.14583333333333334), X, d00);
+  T d01 = T(-0.21875) * Z;
+  d01 = fma(T(0.4375), Y, d01);
+  d01 = fma(T(-0.36458333333333331), X, d01);
+  T d02 = T(0.4375) * Z;
+  d02 = fma(T(-0.21875), Y, d02);
+  d02 = fma(T(-0.36458333333333331), X, d02);
+  T d10 = T(-0.21875) * Z;
+  d10 = fma(T(-0.36458333333333331), Y, d10);
+  d10 = fma(T(0.4375), X, d10);
+  T d11 = T(-0.36458333333333331) * Z;
+  d11 = fma(T(0.14583333333333334), Y, d11);
+  d11 = fma(T(-0.36458333333333331), X, d11);
+  T d12 = T(0.4375) * Z;
+  d12 = fma(T(-0.36458333333333331), Y, d12);
+  d12 = fma(T(-0.21875), X, d12);
+  T d20 = T(-0.36458333333333331) * Z;
+  d20 = fma(T(-0.21875), Y, d20);
+  d20 = fma(T(0.4375), X, d20);
+  T d21 = T(-0.36458333333333331) * Z;
+  d21 = fma(T(0.4375), Y, d21);
+  d21 = fma(T(-0.21875), X, d21);
+  T d22 = T(0.14583333333333334) * Z;
+  d22 = fma(T(-0.36458333333333331), Y, d22);
+  d22 = fma(T(-0.36458333333333331), X, d22);
+  const T t0 = T(2) * Rx * lx, t1 = T(2) * Ry * ly, t2 = T(2) * Rz * lz;
+  const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz)) * (T(-11) * ir2);
+  const T s0 = fma(d00, t0, fma(d01, t1, d02 * t2));
+  ox = fma(u, fma(w0, lx, Rx * fma(w0, rl, s0)), ox);
+  const T s1 = fma(d10, t0, fma(d11, t1, d12 * t2));
+  oy = fma(u, fma(w1, ly, Ry * fma(w1, rl, s1)), oy);
+  const T s2 = fma(d20, t0, fma(d21, t1, d22 * t2));
+  oz = fma(u, fma(w2, lz, Rz * fma(w2, rl, s2)), oz);
+}
+
+template <typename T>
+__device__ __forceinline__ void cube_bg_hvp_l6(T q, T Rx, T Ry, T Rz, T lx, T ly, T lz, T& ox, T& oy,
+                                             T& oz) {
+  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;
+  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));
+  const T ir = nbody_rsqrt(r2);
+  const T ir2 = ir * ir;
+  const T u = q * ir * ir2 * ir2 * ir2 * ir2 * ir2 * ir2 * ir2;
+  const T X0Y0Z2 = Z * Z;
+  const T X0Y1Z1 = Z * Y;
+  const T X0Y2Z0 = Y * Y;
+  const T X1Y0Z1 = Z * X;
+  const T X1Y1Z0 = Y * X;
+  const T X2Y0Z0 = X * X;
+  const T X0Y0Z3 = X0Y0Z2 * Z;
+  const T X0Y1Z2 = X0Y0Z2 * Y;
+  const T X0Y2Z1 = X0Y1Z1 * Y;
+  const T X0Y3Z0 = X0Y2Z0 * Y;
+  const T X1Y0Z2 = X0Y0Z2 * X;
+  const T X1Y1Z1 = X0Y1Z1 * X;
+  const T X1Y2Z0 = X0Y2Z0 * X;
+  const T X2Y0Z1 = X1Y0Z1 * X;
+  const T X2Y1Z0 = X1Y1Z0 * X;
+  const T X3Y0Z0 = X2Y0Z0 * X;
+  T w0 = T(-0.041666666666666664) * X0Y0Z3;
+  w0 = fma(T(0.390625), X0Y1Z2, w0);
+  w0 = fma(T(0.390625), X0Y2Z1, w0);
+  w0 = fma(T(-0.041666666666666664), X0Y3Z0, w0);
+  w0 = fma(T(0.078125), X1Y0Z2, w0);
+  w0 = fma(T(-1.5625), X1Y1Z1, w0);
+  w0 = fma(T(0.078125), X1Y2Z0, w0);
+  w0 = fma(T(0.109375), X2Y0Z1, w0);
+  w0 = fma(T(0.109375), X2Y1Z0, w0);
+  w0 = fma(T(-0.010416666666666666), X3Y0Z0, w0);
+  T w1 = T(-0.041666666666666664) * X0Y0Z3;
+  w1 = fma(T(0.078125), X0Y1Z2, w1);
+  w1 = fma(T(0.109375), X0Y2Z1, w1);
+  w1 = fma(T(-0.010416666666666666), X0Y3Z0, w1);
+  w1 = fma(T(0.390625), X1Y0Z2, w1);
+  w1 = fma(T(-1.5625), X1Y1Z1, w1);
+  w1 = fma(T(0.109375), X1Y2Z0, w1);
+  w1 = fma(T(0.390625), X2Y0Z1, w1);
+  w1 = fma(T(0.078125), X2Y1Z0, w1);
+  w1 = fma(T(-0.041666666666666664), X3Y0Z0, w1);
+  T w2 = T(-0.010416666666666666) * X0Y0Z3;
+  w2 = fma(T(0.109375), X0Y1Z2, w2);
+  w2 = fma(T(0.078125), X0Y2Z1, w2);
+  w2 = fma(T(-0.041666666666666664), X0Y3Z0, w2);
+  w2 = fma(T(0.109375), X1Y0Z2, w2);
+  w2 = fma(T(-1.5625), X1Y1Z1, w2);
+  w2 = fma(T(0.390625), X1Y2Z0, w2);
+  w2 = fma(T(0.078125), X2Y0Z1, w2);
+  w2 = fma(T(0.390625), X2Y1Z0, w2);
+  w2 = fma(T(-0.041666666666666664), X3Y0Z0, w2);
+  T d00 = T(0.078125) * X0Y0Z2;
+  d00 = fma(T(-1.5625), X0Y1Z1, d00);
+  d00 = fma(T(0.078125), X0Y2Z0, d00);
+  d00 = fma(T(0.21875), X1Y0Z1, d00);
+  d00 = fma(T(0.21875), X1Y1Z0, d00);
+  d00 = fma(T(-0.03125), X2Y0Z0, d00);
+  T d01 = T(0.390625) * X0Y0Z2;
+  d01 = fma(T(0.78125), X0Y1Z1, d01);
+  d01 = fma(T(-0.125), X0Y2Z0, d01);
+  d01 = fma(T(-1.5625), X1Y0Z1, d01);
+  d01 = fma(T(0.15625), X1Y1Z0, d01);
+  d01 = fma(T(0.109375), X2Y0Z0, d01);
+  T d02 = T(-0.125) * X0Y0Z2;
+  d02 = fma(T(0.78125), X0Y1Z1, d02);
+  d02 = fma(T(0.390625), X0Y2Z0, d02);
+  d02 = fma(T(0.15625), X1Y0Z1, d02);
+  d02 = fma(T(-1.5625), X1Y1Z0, d02);
+  d02 = fma(T(0.109375), X2Y0Z0, d02);
+  T d10 = T(0.390625) * X0Y0Z2;
+  d10 = fma(T(-1.5625), X0Y1Z1, d10);
+  d10 = fma(T(0.109375), X0Y2Z0, d10);
+  d10 = fma(T(0.78125), X1Y0Z1, d10);
+  d10 = fma(T(0.15625), X1Y1Z0, d10);
+  d10 = fma(T(-0.125), X2Y0Z0, d10);
+  T d11 = T(0.078125) * X0Y0Z2;
+  d11 = fma(T(0.21875), X0Y1Z1, d11);
+  d11 = fma(T(-0.03125), X0Y2Z0, d11);
+  d11 = fma(T(-1.5625), X1Y0Z1, d11);
+  d11 = fma(T(0.21875), X1Y1Z0, d11);
+  d11 = fma(T(0.078125), X2Y0Z0, d11);
+  T d12 = T(-0.125) * X0Y0Z2;
+  d12 = fma(T(0.15625), X0Y1Z1, d12);
+  d12 = fma(T(0.109375), X0Y2Z0, d12);
+  d12 = fma(T(0.78125), X1Y0Z1, d12);
+  d12 = fma(T(-1.5625), X1Y1Z0, d12);
+  d12 = fma(T(0.390625), X2Y0Z0, d12);
+  T d20 = T(0.109375) * X0Y0Z2;
+  d20 = fma(T(-1.5625), X0Y1Z1, d20);
+  d20 = fma(T(0.390625), X0Y2Z0, d20);
+  d20 = fma(T(0.15625), X1Y0Z1, d20);
+  d20 = fma(T(0.78125), X1Y1Z0, d20);
+  d20 = fma(T(-0.125), X2Y0Z0, d20);
+  T d21 = T(0.109375) * X0Y0Z2;
+  d21 = fma(T(0.15625), X0Y1Z1, d21);
+  d21 = fma(T(-0.125), X0Y2Z0, d21);
+  d21 = fma(T(-1.5625), X1Y0Z1, d21);
+  d21 = fma(T(0.78125), X1Y1Z0, d21);
+  d21 = fma(T(0.390625), X2Y0Z0, d21);
+  T d22 = T(-0.03125) * X0Y0Z2;
+  d22 = fma(T(0.21875), X0Y1Z1, d22);
+  d22 = fma(T(0.078125), X0Y2Z0, d22);
+  d22 = fma(T(0.21875), X1Y0Z1, d22);
+  d22 = fma(T(-1.5625), X1Y1Z0, d22);
+  d22 = fma(T(0.078125), X2Y0Z0, d22);
+  const T t0 = T(2) * Rx * lx, t1 = T(2) * Ry * ly, t2 = T(2) * Rz * lz;
+  const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz)) * (T(-15) * ir2);
+  const T s0 = fma(d00, t0, fma(d01, t1, d02 * t2));
+  ox = fma(u, fma(w0, lx, Rx * fma(w0, rl, s0)), ox);
+  const T s1 = fma(d10, t0, fma(d11, t1, d12 * t2));
+  oy = fma(u, fma(w1, ly, Ry * fma(w1, rl, s1)), oy);
+  const T s2 = fma(d20, t0, fma(d21, t1, d22 * t2));
+  oz = fma(u, fma(w2, lz, Rz * fma(w2, rl, s2)), oz);
 }
 
 template <typename T>

@@ -24,6 +24,10 @@
 
 namespace {
 
+template <int P> constexpr int kNBofP() {
+  return P == 0 ? kNB0 : P == 1 ? kNB1 : P == 2 ? kNB2 : P == 3 ? kNB3 : kNB4;
+}
+
 template <int P> struct AOrd;
 #define NB_AORD(P)                                                                                      \
   template <> struct AOrd<P> {                                                                          \
@@ -58,6 +62,25 @@ NB_AORD(2)
 NB_AORD(3)
 NB_AORD(4)
 
+// sink-side derivative of the uniform-background term (orders as in the walk);
+// the term does not depend on the source particles' positions
+template <int P> struct ABg {
+  static constexpr bool has = false;
+  template <typename T>
+  static __device__ __forceinline__ void hvp(T, T, T, T, T, T, T, T&, T&, T&) {}
+};
+#define NB_ABG(P, L)                                                                                   \
+  template <> struct ABg<P> {                                                                          \
+    static constexpr bool has = true;                                                                  \
+    template <typename T>                                                                              \
+    static __device__ __forceinline__ void hvp(T q, T x, T y, T z, T lx, T ly, T lz, T& ox, T& oy, T& oz) { \
+      cube_bg_hvp_l##L<T>(q, x, y, z, lx, ly, lz, ox, oy, oz);                                         \
+    }                                                                                                  \
+  };
+NB_ABG(0, 4)
+NB_ABG(2, 4)
+NB_ABG(4, 6)
+
 template <typename T>
 struct AdjArgs {
   DevTree tr;
@@ -65,7 +88,7 @@ struct AdjArgs {
   const typename Vec4<T>::type* src;
   const T* eps2;
   long long thr[NB_NLEV];
-  int n_direct, le, mac_edge;
+  int n_direct, le, mac_edge, bg;
   int* stack;
   int stack_cap;
   int* group_ctr;
@@ -230,9 +253,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
             const float2 sc = make_float2(m0.w, m1.w);
             const float2 e2 = make_float2(s_meps[wid][2 * q], two ? s_meps[wid][2 * q + 1] : 1.f);
             float2 ox = make_float2(0.f, 0.f), oy = ox, oz = ox;
-            AOrd<P>::self2(&cf[q * NBS], __ffma2_rn(x2, sc, make_float2(m0.x, m1.x)),
-                           __ffma2_rn(y2, sc, make_float2(m0.y, m1.y)), __ffma2_rn(z2, sc, make_float2(m0.z, m1.z)),
-                           e2, l2x, l2y, l2z, ox, oy, oz);
+            const float2 rx = __ffma2_rn(x2, sc, make_float2(m0.x, m1.x));
+            const float2 ry = __ffma2_rn(y2, sc, make_float2(m0.y, m1.y));
+            const float2 rz = __ffma2_rn(z2, sc, make_float2(m0.z, m1.z));
+            AOrd<P>::self2(&cf[q * NBS], rx, ry, rz, e2, l2x, l2y, l2z, ox, oy, oz);
+            if (ABg<P>::has && w.bg) {
+              const float2 qb = cf[q * NBS + kNBofP<P>()];
+              ABg<P>::template hvp<float>(qb.x, rx.x, ry.x, rz.x, lx, ly, lz, ox.x, oy.x, oz.x);
+              if (two) ABg<P>::template hvp<float>(qb.y, rx.y, ry.y, rz.y, lx, ly, lz, ox.y, oy.y, oz.y);
+            }
             // back to box units: times 2^level of each cell
             mx = fma(ox.x, m0.w, fma(ox.y, m1.w, mx));
             my = fma(oy.x, m0.w, fma(oy.y, m1.w, my));
@@ -249,8 +278,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
           for (int q = 0; q < nmp; q++) {
             const V4 mo = s_moff[wid][q];
             T ox = 0, oy = 0, oz = 0;
-            AOrd<P>::template self<T>(&s_coef[wid][q * NBS], fma(xi, mo.w, mo.x), fma(yi, mo.w, mo.y),
-                                      fma(zi, mo.w, mo.z), s_meps[wid][q], lx, ly, lz, ox, oy, oz);
+            const T rx = fma(xi, mo.w, mo.x), ry = fma(yi, mo.w, mo.y), rz = fma(zi, mo.w, mo.z);
+            AOrd<P>::template self<T>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q], lx, ly, lz, ox, oy, oz);
+            if (ABg<P>::has && w.bg)
+              ABg<P>::template hvp<T>(s_coef[wid][q * NBS + kNBofP<P>()], rx, ry, rz, lx, ly, lz, ox, oy, oz);
             mx = fma(ox, mo.w, mx);
             my = fma(oy, mo.w, my);
             mz = fma(oz, mo.w, mz);
@@ -824,7 +855,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
                           int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
-                          unsigned* status, int nsm, int mac_edge, cudaStream_t s) {
+                          unsigned* status, int nsm, int mac_edge, int bg, cudaStream_t s) {
   if (fp64) return cudaErrorNotSupported;  // the reverse mode runs the mixed-precision walk
   if (pe > 4) return cudaErrorNotSupported;
   cudaError_t e;
@@ -852,6 +883,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
     for (int l = 0; l < NB_NLEV; l++) a.thr[l] = thr[l];
     a.n_direct = n_direct;
     a.mac_edge = mac_edge;
+    a.bg = bg;
     a.le = le;
     a.stack = stack;
     a.stack_cap = stack_cap;

@@ -42,14 +42,16 @@ int nb_walk_variant(bool fp64, int order, double* ms);
 int nb_coef_stride(int order);
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const int4* cA, const int4* cB,
                       const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
-                      uint32_t* uorder, uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s);
+                      uint32_t* uorder, uint32_t* uhist, int* urange, const uint16_t* cbox, const double* rho,
+                      SortScratch* sc, cudaStream_t s);
+cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, cudaStream_t s);
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, double* fm, cudaStream_t s);
 int nb_walk_warps(bool fp64);
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
-                    int forced_variant, int mac_edge, cudaStream_t s);
+                    int forced_variant, int mac_edge, int bg, cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -67,7 +69,7 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           const void* src, const void* eps2, const long long* thr, int n_direct, int* stack,
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
                           int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
-                          unsigned* status, int nsm, int mac_edge, cudaStream_t s);
+                          unsigned* status, int nsm, int mac_edge, int bg, cudaStream_t s);
 cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                            const void* tab, void* lbuf, cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
@@ -137,6 +139,7 @@ struct nbody_tree {
   Buf gflag, gid, gstart, gA, gB, gC, gD;
   // image field
   Buf fm;
+  Buf rho;  // mean density per box (background terms)
   const double* tab64 = nullptr;
   const float* tab32 = nullptr;
   // walk
@@ -168,7 +171,7 @@ struct nbody_tree {
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
                   &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
-                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf,
+                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
                   &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq};
     for (Buf* b : all) b->release();
@@ -240,6 +243,7 @@ int validate(const nbody_params* p) {
   }
   if (p->precision != NBODY_MIXED && p->precision != NBODY_FP64) return NBODY_EINVAL;
   if (((p->flags >> 8) & 0xf) > 4) return NBODY_EINVAL;  // walk variant override 0..3
+  if ((p->flags & NBODY_FLAG_BACKGROUND) && (p->order == 1 || p->order == 3)) return NBODY_EINVAL;
   return NBODY_OK;
 }
 
@@ -543,10 +547,17 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(nb_group_runs(ng, totals + 1, t->gA.as<int4>(), t->gD.as<int4>(), t->gflag.as<int>(), t->gid.as<int>(),
                       totals + 2, t->scantmp.as<int>(), s));
   if (timed) NB_CU(cudaEventRecord(be[2], s));
-  // A5 moments
+  // A5 moments (with the background weights when asked for)
+  const double* rho = nullptr;
+  if (p.flags & NBODY_FLAG_BACKGROUND) {
+    NB_CU(t->rho.ensure(8 * (int64_t)t->nbox));
+    NB_CU(nb_box_mass(t->off.as<int64_t>(), t->smass.as<float>(), t->nbox, t->rho.as<double>(), s));
+    rho = t->rho.as<double>();
+  }
   NB_CU(nb_upward(p.order, fp64, nc, totals, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
                   t->smass.as<float>(), n, t->mom.as<double>(), t->coef.p, t->ukey.as<uint8_t>(),
-                  t->uorder.as<uint32_t>(), t->urng.as<uint32_t>(), t->urng.as<int>() + 256, &sc, s));
+                  t->uorder.as<uint32_t>(), t->urng.as<uint32_t>(), t->urng.as<int>() + 256,
+                  t->cbox.as<uint16_t>(), rho, &sc, s));
   if (p.ewald_order > 0) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
     NB_CU(t->fm.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
@@ -620,7 +631,7 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
                 t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0,
-                s));
+                (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0, s));
   if (timed) NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
@@ -666,7 +677,8 @@ int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   NB_CU(nb_forces_vjp(tr, false, p.order, p.ewald_order, p.ewald_level, p.ewald_grid, t->coef.p, t->src.p,
                       t->eps2.p, t->thr, p.n_direct, t->stack.as<int>(), kStackCap, t->walk_blocks,
                       t->fm.as<double>(), t->tab32, t->lbuf.p, nb_field_stride(p.ewald_order), p.lmax, lam, out,
-                      B, t->status.as<unsigned>(), t->nsm, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0, s));
+                      B, t->status.as<unsigned>(), t->nsm, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0,
+                      (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0, s));
   return NBODY_OK;
 }
 

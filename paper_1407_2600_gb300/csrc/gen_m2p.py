@@ -353,6 +353,204 @@ def emit_m2m(p):
     return "\n".join(L)
 
 
+# ---- uniform-background terms of an expanded cell ------------------------------------
+# A cell used through its expansion also gets the orders p < l <= l_bg of the
+# field of a cube of the mean density filling it (Newtonian kernel): the higher
+# moments of its uniform share, whose truncation dominates the expansion error
+# of near-uniform states.  In the cell's length unit (side 1) and for unit
+# density, the order-l potential term of the expansion is
+#     psi_l(R) = sum_{|n|=l} (c_n / n!) d^n (1/r),  c_n = prod_d m(n_d),
+#     m(k) = 1 / ((k+1) 2^k) for even k, 0 for odd k,
+# and the Hermite form of d^n (1/r) (eps = 0) makes r^(2l+1) psi_l = h(X, Y, Z)
+# a polynomial in X = Rx^2, Y = Ry^2, Z = Rz^2.  The field term is
+#     a_i = d_i psi_l = R_i w_i(X, Y, Z) / r^(2l+3),  w_i = 2 r^2 dh/dX_i - (2l+1) h,
+# scaled by q = rho h_cell (rho the mean density, h_cell the cell's side).
+def _padd(a, b, f=1):
+    from fractions import Fraction
+    out = dict(a)
+    for k, v in b.items():
+        out[k] = out.get(k, Fraction(0)) + f * v
+    return {k: v for k, v in out.items() if v != 0}
+
+
+def _pmul(a, b):
+    from fractions import Fraction
+    out = {}
+    for ka, va in a.items():
+        for kb, vb in b.items():
+            k = (ka[0] + kb[0], ka[1] + kb[1], ka[2] + kb[2])
+            out[k] = out.get(k, Fraction(0)) + va * vb
+    return {k: v for k, v in out.items() if v != 0}
+
+
+def _pdiff(a, d):
+    out = {}
+    for k, v in a.items():
+        if k[d] > 0:
+            kk = list(k)
+            kk[d] -= 1
+            out[tuple(kk)] = out.get(tuple(kk), 0) + v * k[d]
+    return {k: v for k, v in out.items() if v != 0}
+
+
+def bg_order(p):
+    """order of the background term added at expansion order p (0 = none)"""
+    return {0: 4, 2: 4, 4: 6}.get(p, 0)
+
+
+def bg_poly(l):
+    """h(X, Y, Z) = r^(2l+1) psi_l(R) as {(a, b, c): Fraction} for X^a Y^b Z^c"""
+    from fractions import Fraction
+
+    def mom(k):
+        return Fraction(0) if k % 2 else Fraction(1, (k + 1) * 2 ** k)
+
+    def dfact(j):  # (2j-1)!!
+        v = 1
+        for t in range(1, 2 * j, 2):
+            v *= t
+        return v
+
+    r2 = {(1, 0, 0): Fraction(1), (0, 1, 0): Fraction(1), (0, 0, 1): Fraction(1)}
+    h = {}
+    for n in multi(l):
+        if sum(n) != l:
+            continue
+        cn = mom(n[0]) * mom(n[1]) * mom(n[2])
+        if cn == 0:
+            continue
+        nf = math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2])
+        for k in product(*(range(n[d] // 2 + 1) for d in range(3))):
+            K = sum(k)
+            j = l - K
+            hc = Fraction(1)
+            for d in range(3):
+                hc *= Fraction(math.factorial(n[d]),
+                               math.factorial(k[d]) * math.factorial(n[d] - 2 * k[d]) * 2 ** k[d])
+            coef = cn / nf * hc * (-1) ** j * dfact(j)
+            term = {((n[0] - 2 * k[0]) // 2, (n[1] - 2 * k[1]) // 2, (n[2] - 2 * k[2]) // 2): coef}
+            for _ in range(K):
+                term = _pmul(term, r2)
+            h = _padd(h, term)
+    return h
+
+
+def _bg_parts(l):
+    h = bg_poly(l)
+    r2 = {(1, 0, 0): 1, (0, 1, 0): 1, (0, 0, 1): 1}
+    w = [_padd(_pmul({k: 2 * v for k, v in _pdiff(h, d).items()}, r2), h, -(2 * l + 1)) for d in range(3)]
+    return h, w
+
+
+def _emit_poly(L, name, poly, mono_name):
+    """name = sum_k c_k mono_k in the fma subset (first term assigns)"""
+    first = True
+    for k in sorted(poly):
+        c = "T(%.17g)" % float(poly[k])
+        mn = mono_name(k)
+        if first:
+            L.append("  T %s = %s;" % (name, c if mn is None else "%s * %s" % (c, mn)))
+            first = False
+        else:
+            L.append("  %s = fma(%s, %s, %s);" % (name, c, "T(1)" if mn is None else mn, name))
+    if first:
+        L.append("  T %s = T(0);" % name)
+
+
+def _emit_monomials(L, polys):
+    """declare every monomial X^a Y^b Z^c (degree >= 2) the polynomials use"""
+    need = set()
+    for p in polys:
+        need |= set(p)
+    names = {(0, 0, 0): None, (1, 0, 0): "X", (0, 1, 0): "Y", (0, 0, 1): "Z"}
+    for k in sorted(need, key=lambda k: (sum(k), k)):
+        if k in names:
+            continue
+        # build from a lower monomial times X, Y or Z
+        for d, v in enumerate("XYZ"):
+            if k[d] > 0:
+                par = list(k)
+                par[d] -= 1
+                par = tuple(par)
+                if par not in names:
+                    raise ValueError("monomial %s needs %s" % (k, par))
+                nm = "X%dY%dZ%d" % k
+                L.append("  const T %s = %s * %s;" % (nm, names[par], v) if names[par] else "  const T %s = %s;" % (nm, v))
+                names[k] = nm
+                break
+    return lambda k: names[k]
+
+
+def _close_monomials(polys):
+    """all lower monomials needed to build the ones the polynomials use"""
+    need = set()
+    for p in polys:
+        for k in p:
+            stack = [k]
+            while stack:
+                m = stack.pop()
+                if m in need:
+                    continue
+                need.add(m)
+                for d in range(3):
+                    if m[d] > 0:
+                        par = list(m)
+                        par[d] -= 1
+                        stack.append(tuple(par))
+                        break
+    return [{k: 1 for k in need}]
+
+
+def emit_bg(l):
+    h, w = _bg_parts(l)
+    L = ["template <typename T>",
+         "__device__ __forceinline__ void cube_bg_l%d(T q, T Rx, T Ry, T Rz, T& ax, T& ay, T& az) {" % l,
+         "  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;",
+         "  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));",
+         "  const T ir = nbody_rsqrt(r2);",
+         "  const T ir2 = ir * ir;"]
+    # u = q / r^(2l+3)
+    e = "ir"
+    for _ in range(l + 1):
+        e = "%s * ir2" % e if e != "ir" else "ir * ir2"
+    L.append("  const T u = q * %s;" % " * ".join(["ir"] + ["ir2"] * (l + 1)))
+    mono = _emit_monomials(L, _close_monomials(w))
+    for d in range(3):
+        _emit_poly(L, "w%d" % d, w[d], mono)
+    for d, (R, a) in enumerate((("Rx", "ax"), ("Ry", "ay"), ("Rz", "az"))):
+        L.append("  %s = fma(%s * u, w%d, %s);" % (a, R, d, a))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_bg_hvp(l):
+    """o += J lam, J_ij = d a_i / d R_j of the background term:
+    (J lam)_i = u [w_i lam_i + R_i sum_j 2 R_j (dw_i/dX_j) lam_j - (2l+3) R_i w_i (R.lam) / r^2]."""
+    h, w = _bg_parts(l)
+    D = [[_pdiff(w[i], j) for j in range(3)] for i in range(3)]
+    L = ["template <typename T>",
+         "__device__ __forceinline__ void cube_bg_hvp_l%d(T q, T Rx, T Ry, T Rz, T lx, T ly, T lz, T& ox, T& oy," % l,
+         "                                             T& oz) {",
+         "  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;",
+         "  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));",
+         "  const T ir = nbody_rsqrt(r2);",
+         "  const T ir2 = ir * ir;"]
+    L.append("  const T u = q * %s;" % " * ".join(["ir"] + ["ir2"] * (l + 1)))
+    mono = _emit_monomials(L, _close_monomials(w + [D[i][j] for i in range(3) for j in range(3)]))
+    for d in range(3):
+        _emit_poly(L, "w%d" % d, w[d], mono)
+    for i in range(3):
+        for j in range(3):
+            _emit_poly(L, "d%d%d" % (i, j), D[i][j], mono)
+    L.append("  const T t0 = T(2) * Rx * lx, t1 = T(2) * Ry * ly, t2 = T(2) * Rz * lz;")
+    L.append("  const T rl = fma(Rx, lx, fma(Ry, ly, Rz * lz)) * (T(%d) * ir2);" % (-(2 * l + 3)))
+    for i, (R, lv, o) in enumerate((("Rx", "lx", "ox"), ("Ry", "ly", "oy"), ("Rz", "lz", "oz"))):
+        L.append("  const T s%d = fma(d%d0, t0, fma(d%d1, t1, d%d2 * t2));" % (i, i, i, i))
+        L.append("  %s = fma(u, fma(w%d, %s, %s * fma(w%d, rl, s%d)), %s);" % (o, i, lv, R, i, i, o))
+    L.append("}")
+    return "\n".join(L)
+
+
 def generate():
     out = []
     out.append("// Generated by gen_m2p.py -- do not edit by hand.")
@@ -378,6 +576,15 @@ def generate():
     for pe in range(1, 6):
         out.append("constexpr int kNL%d = %d;  // local coefficients, image-field order %d" % (pe, len(multi(pe + 1)) - 1, pe))
         out.append(emit_m2l(pe))
+        out.append("")
+    out.append("__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {")
+    out.append("  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));")
+    out.append("}")
+    out.append("")
+    for l in (4, 6):
+        out.append(emit_bg(l))
+        out.append("")
+        out.append(pack(emit_bg(l), "cube_bg_l%d" % l, "cube_bg2_l%d" % l))
         out.append("")
     return "\n".join(out) + "\n"
 
@@ -849,10 +1056,9 @@ def generate_adjoint():
     out = ["// Generated by gen_m2p.py -- do not edit by hand.",
            "// Reverse-mode (adjoint) kernels of the M2P, M2M, P2M and image-field expansions.",
            "#pragma once", ""]
-    out.append("__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {")
-    out.append("  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));")
-    out.append("}")
-    out.append("")
+    for l in (4, 6):
+        out.append(emit_bg_hvp(l))
+        out.append("")
     for p in range(5):
         out.append(emit_m2p_adj_self(p))
         out.append("")

@@ -2156,3 +2156,193 @@ __device__ __forceinline__ void l2p_pe5(const T* __restrict__ Lc, T dx, T dy, T 
   az = fma(-q55, Lc[82], fma(-q54, Lc[81], fma(-q53, Lc[80], fma(-q52, Lc[79], fma(-q51, Lc[78], fma(-q50, Lc[77], fma(-q49, Lc[75], fma(-q48, Lc[74], fma(-q47, Lc[73], fma(-q46, Lc[72], fma(-q45, Lc[71], fma(-q44, Lc[69], fma(-q43, Lc[68], fma(-q42, Lc[67], fma(-q41, Lc[66], fma(-q40, Lc[64], fma(-q39, Lc[63], fma(-q38, Lc[62], fma(-q37, Lc[60], fma(-q36, Lc[59], fma(-q35, Lc[57], fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))))))))))))))))))))))))))))))))))))))));
 }
 
+__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {
+  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+}
+
+template <typename T>
+__device__ __forceinline__ void cube_bg_l4(T q, T Rx, T Ry, T Rz, T& ax, T& ay, T& az) {
+  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;
+  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));
+  const T ir = nbody_rsqrt(r2);
+  const T ir2 = ir * ir;
+  const T u = q * ir * ir2 * ir2 * ir2 * ir2 * ir2;
+  const T X0Y0Z2 = Z * Z;
+  const T X0Y1Z1 = Z * Y;
+  const T X0Y2Z0 = Y * Y;
+  const T X1Y0Z1 = Z * X;
+  const T X1Y1Z0 = Y * X;
+  const T X2Y0Z0 = X * X;
+  T w0 = T(0.21875) * X0Y0Z2;
+  w0 = fma(T(-0.21875), X0Y1Z1, w0);
+  w0 = fma(T(0.21875), X0Y2Z0, w0);
+  w0 = fma(T(-0.36458333333333331), X1Y0Z1, w0);
+  w0 = fma(T(-0.36458333333333331), X1Y1Z0, w0);
+  w0 = fma(T(0.072916666666666671), X2Y0Z0, w0);
+  T w1 = T(0.21875) * X0Y0Z2;
+  w1 = fma(T(-0.36458333333333331), X0Y1Z1, w1);
+  w1 = fma(T(0.072916666666666671), X0Y2Z0, w1);
+  w1 = fma(T(-0.21875), X1Y0Z1, w1);
+  w1 = fma(T(-0.36458333333333331), X1Y1Z0, w1);
+  w1 = fma(T(0.21875), X2Y0Z0, w1);
+  T w2 = T(0.072916666666666671) * X0Y0Z2;
+  w2 = fma(T(-0.36458333333333331), X0Y1Z1, w2);
+  w2 = fma(T(0.21875), X0Y2Z0, w2);
+  w2 = fma(T(-0.36458333333333331), X1Y0Z1, w2);
+  w2 = fma(T(-0.21875), X1Y1Z0, w2);
+  w2 = fma(T(0.21875), X2Y0Z0, w2);
+  ax = fma(Rx * u, w0, ax);
+  ay = fma(Ry * u, w1, ay);
+  az = fma(Rz * u, w2, az);
+}
+
+__device__ __forceinline__ void cube_bg2_l4(float2 q, float2 Rx, float2 Ry, float2 Rz, float2& ax, float2& ay, float2& az) {
+  const float2 X = __fmul2_rn(Rx, Rx), Y = __fmul2_rn(Ry, Ry), Z = __fmul2_rn(Rz, Rz);
+  const float2 r2 = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, Z));
+  const float2 ir = nbody_rsqrt2(r2);
+  const float2 ir2 = __fmul2_rn(ir, ir);
+  const float2 u = __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(q, ir), ir2), ir2), ir2), ir2), ir2);
+  const float2 X0Y0Z2 = __fmul2_rn(Z, Z);
+  const float2 X0Y1Z1 = __fmul2_rn(Z, Y);
+  const float2 X0Y2Z0 = __fmul2_rn(Y, Y);
+  const float2 X1Y0Z1 = __fmul2_rn(Z, X);
+  const float2 X1Y1Z0 = __fmul2_rn(Y, X);
+  const float2 X2Y0Z0 = __fmul2_rn(X, X);
+  float2 w0 = __fmul2_rn(make_float2(0.21875f, 0.21875f), X0Y0Z2);
+  w0 = __ffma2_rn(make_float2(-0.21875f, -0.21875f), X0Y1Z1, w0);
+  w0 = __ffma2_rn(make_float2(0.21875f, 0.21875f), X0Y2Z0, w0);
+  w0 = __ffma2_rn(make_float2(-0.364583333f, -0.364583333f), X1Y0Z1, w0);
+  w0 = __ffma2_rn(make_float2(-0.364583333f, -0.364583333f), X1Y1Z0, w0);
+  w0 = __ffma2_rn(make_float2(0.0729166667f, 0.0729166667f), X2Y0Z0, w0);
+  float2 w1 = __fmul2_rn(make_float2(0.21875f, 0.21875f), X0Y0Z2);
+  w1 = __ffma2_rn(make_float2(-0.364583333f, -0.364583333f), X0Y1Z1, w1);
+  w1 = __ffma2_rn(make_float2(0.0729166667f, 0.0729166667f), X0Y2Z0, w1);
+  w1 = __ffma2_rn(make_float2(-0.21875f, -0.21875f), X1Y0Z1, w1);
+  w1 = __ffma2_rn(make_float2(-0.364583333f, -0.364583333f), X1Y1Z0, w1);
+  w1 = __ffma2_rn(make_float2(0.21875f, 0.21875f), X2Y0Z0, w1);
+  float2 w2 = __fmul2_rn(make_float2(0.0729166667f, 0.0729166667f), X0Y0Z2);
+  w2 = __ffma2_rn(make_float2(-0.364583333f, -0.364583333f), X0Y1Z1, w2);
+  w2 = __ffma2_rn(make_float2(0.21875f, 0.21875f), X0Y2Z0, w2);
+  w2 = __ffma2_rn(make_float2(-0.364583333f, -0.364583333f), X1Y0Z1, w2);
+  w2 = __ffma2_rn(make_float2(-0.21875f, -0.21875f), X1Y1Z0, w2);
+  w2 = __ffma2_rn(make_float2(0.21875f, 0.21875f), X2Y0Z0, w2);
+  ax = __ffma2_rn(__fmul2_rn(Rx, u), w0, ax);
+  ay = __ffma2_rn(__fmul2_rn(Ry, u), w1, ay);
+  az = __ffma2_rn(__fmul2_rn(Rz, u), w2, az);
+}
+
+template <typename T>
+__device__ __forceinline__ void cube_bg_l6(T q, T Rx, T Ry, T Rz, T& ax, T& ay, T& az) {
+  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;
+  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));
+  const T ir = nbody_rsqrt(r2);
+  const T ir2 = ir * ir;
+  const T u = q * ir * ir2 * ir2 * ir2 * ir2 * ir2 * ir2 * ir2;
+  const T X0Y0Z2 = Z * Z;
+  const T X0Y1Z1 = Z * Y;
+  const T X0Y2Z0 = Y * Y;
+  const T X1Y0Z1 = Z * X;
+  const T X1Y1Z0 = Y * X;
+  const T X2Y0Z0 = X * X;
+  const T X0Y0Z3 = X0Y0Z2 * Z;
+  const T X0Y1Z2 = X0Y0Z2 * Y;
+  const T X0Y2Z1 = X0Y1Z1 * Y;
+  const T X0Y3Z0 = X0Y2Z0 * Y;
+  const T X1Y0Z2 = X0Y0Z2 * X;
+  const T X1Y1Z1 = X0Y1Z1 * X;
+  const T X1Y2Z0 = X0Y2Z0 * X;
+  const T X2Y0Z1 = X1Y0Z1 * X;
+  const T X2Y1Z0 = X1Y1Z0 * X;
+  const T X3Y0Z0 = X2Y0Z0 * X;
+  T w0 = T(-0.041666666666666664) * X0Y0Z3;
+  w0 = fma(T(0.390625), X0Y1Z2, w0);
+  w0 = fma(T(0.390625), X0Y2Z1, w0);
+  w0 = fma(T(-0.041666666666666664), X0Y3Z0, w0);
+  w0 = fma(T(0.078125), X1Y0Z2, w0);
+  w0 = fma(T(-1.5625), X1Y1Z1, w0);
+  w0 = fma(T(0.078125), X1Y2Z0, w0);
+  w0 = fma(T(0.109375), X2Y0Z1, w0);
+  w0 = fma(T(0.109375), X2Y1Z0, w0);
+  w0 = fma(T(-0.010416666666666666), X3Y0Z0, w0);
+  T w1 = T(-0.041666666666666664) * X0Y0Z3;
+  w1 = fma(T(0.078125), X0Y1Z2, w1);
+  w1 = fma(T(0.109375), X0Y2Z1, w1);
+  w1 = fma(T(-0.010416666666666666), X0Y3Z0, w1);
+  w1 = fma(T(0.390625), X1Y0Z2, w1);
+  w1 = fma(T(-1.5625), X1Y1Z1, w1);
+  w1 = fma(T(0.109375), X1Y2Z0, w1);
+  w1 = fma(T(0.390625), X2Y0Z1, w1);
+  w1 = fma(T(0.078125), X2Y1Z0, w1);
+  w1 = fma(T(-0.041666666666666664), X3Y0Z0, w1);
+  T w2 = T(-0.010416666666666666) * X0Y0Z3;
+  w2 = fma(T(0.109375), X0Y1Z2, w2);
+  w2 = fma(T(0.078125), X0Y2Z1, w2);
+  w2 = fma(T(-0.041666666666666664), X0Y3Z0, w2);
+  w2 = fma(T(0.109375), X1Y0Z2, w2);
+  w2 = fma(T(-1.5625), X1Y1Z1, w2);
+  w2 = fma(T(0.390625), X1Y2Z0, w2);
+  w2 = fma(T(0.078125), X2Y0Z1, w2);
+  w2 = fma(T(0.390625), X2Y1Z0, w2);
+  w2 = fma(T(-0.041666666666666664), X3Y0Z0, w2);
+  ax = fma(Rx * u, w0, ax);
+  ay = fma(Ry * u, w1, ay);
+  az = fma(Rz * u, w2, az);
+}
+
+__device__ __forceinline__ void cube_bg2_l6(float2 q, float2 Rx, float2 Ry, float2 Rz, float2& ax, float2& ay, float2& az) {
+  const float2 X = __fmul2_rn(Rx, Rx), Y = __fmul2_rn(Ry, Ry), Z = __fmul2_rn(Rz, Rz);
+  const float2 r2 = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, Z));
+  const float2 ir = nbody_rsqrt2(r2);
+  const float2 ir2 = __fmul2_rn(ir, ir);
+  const float2 u = __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(q, ir), ir2), ir2), ir2), ir2), ir2), ir2), ir2);
+  const float2 X0Y0Z2 = __fmul2_rn(Z, Z);
+  const float2 X0Y1Z1 = __fmul2_rn(Z, Y);
+  const float2 X0Y2Z0 = __fmul2_rn(Y, Y);
+  const float2 X1Y0Z1 = __fmul2_rn(Z, X);
+  const float2 X1Y1Z0 = __fmul2_rn(Y, X);
+  const float2 X2Y0Z0 = __fmul2_rn(X, X);
+  const float2 X0Y0Z3 = __fmul2_rn(X0Y0Z2, Z);
+  const float2 X0Y1Z2 = __fmul2_rn(X0Y0Z2, Y);
+  const float2 X0Y2Z1 = __fmul2_rn(X0Y1Z1, Y);
+  const float2 X0Y3Z0 = __fmul2_rn(X0Y2Z0, Y);
+  const float2 X1Y0Z2 = __fmul2_rn(X0Y0Z2, X);
+  const float2 X1Y1Z1 = __fmul2_rn(X0Y1Z1, X);
+  const float2 X1Y2Z0 = __fmul2_rn(X0Y2Z0, X);
+  const float2 X2Y0Z1 = __fmul2_rn(X1Y0Z1, X);
+  const float2 X2Y1Z0 = __fmul2_rn(X1Y1Z0, X);
+  const float2 X3Y0Z0 = __fmul2_rn(X2Y0Z0, X);
+  float2 w0 = __fmul2_rn(make_float2(-0.0416666667f, -0.0416666667f), X0Y0Z3);
+  w0 = __ffma2_rn(make_float2(0.390625f, 0.390625f), X0Y1Z2, w0);
+  w0 = __ffma2_rn(make_float2(0.390625f, 0.390625f), X0Y2Z1, w0);
+  w0 = __ffma2_rn(make_float2(-0.0416666667f, -0.0416666667f), X0Y3Z0, w0);
+  w0 = __ffma2_rn(make_float2(0.078125f, 0.078125f), X1Y0Z2, w0);
+  w0 = __ffma2_rn(make_float2(-1.5625f, -1.5625f), X1Y1Z1, w0);
+  w0 = __ffma2_rn(make_float2(0.078125f, 0.078125f), X1Y2Z0, w0);
+  w0 = __ffma2_rn(make_float2(0.109375f, 0.109375f), X2Y0Z1, w0);
+  w0 = __ffma2_rn(make_float2(0.109375f, 0.109375f), X2Y1Z0, w0);
+  w0 = __ffma2_rn(make_float2(-0.0104166667f, -0.0104166667f), X3Y0Z0, w0);
+  float2 w1 = __fmul2_rn(make_float2(-0.0416666667f, -0.0416666667f), X0Y0Z3);
+  w1 = __ffma2_rn(make_float2(0.078125f, 0.078125f), X0Y1Z2, w1);
+  w1 = __ffma2_rn(make_float2(0.109375f, 0.109375f), X0Y2Z1, w1);
+  w1 = __ffma2_rn(make_float2(-0.0104166667f, -0.0104166667f), X0Y3Z0, w1);
+  w1 = __ffma2_rn(make_float2(0.390625f, 0.390625f), X1Y0Z2, w1);
+  w1 = __ffma2_rn(make_float2(-1.5625f, -1.5625f), X1Y1Z1, w1);
+  w1 = __ffma2_rn(make_float2(0.109375f, 0.109375f), X1Y2Z0, w1);
+  w1 = __ffma2_rn(make_float2(0.390625f, 0.390625f), X2Y0Z1, w1);
+  w1 = __ffma2_rn(make_float2(0.078125f, 0.078125f), X2Y1Z0, w1);
+  w1 = __ffma2_rn(make_float2(-0.0416666667f, -0.0416666667f), X3Y0Z0, w1);
+  float2 w2 = __fmul2_rn(make_float2(-0.0104166667f, -0.0104166667f), X0Y0Z3);
+  w2 = __ffma2_rn(make_float2(0.109375f, 0.109375f), X0Y1Z2, w2);
+  w2 = __ffma2_rn(make_float2(0.078125f, 0.078125f), X0Y2Z1, w2);
+  w2 = __ffma2_rn(make_float2(-0.0416666667f, -0.0416666667f), X0Y3Z0, w2);
+  w2 = __ffma2_rn(make_float2(0.109375f, 0.109375f), X1Y0Z2, w2);
+  w2 = __ffma2_rn(make_float2(-1.5625f, -1.5625f), X1Y1Z1, w2);
+  w2 = __ffma2_rn(make_float2(0.390625f, 0.390625f), X1Y2Z0, w2);
+  w2 = __ffma2_rn(make_float2(0.078125f, 0.078125f), X2Y0Z1, w2);
+  w2 = __ffma2_rn(make_float2(0.390625f, 0.390625f), X2Y1Z0, w2);
+  w2 = __ffma2_rn(make_float2(-0.0416666667f, -0.0416666667f), X3Y0Z0, w2);
+  ax = __ffma2_rn(__fmul2_rn(Rx, u), w0, ax);
+  ay = __ffma2_rn(__fmul2_rn(Ry, u), w1, ay);
+  az = __ffma2_rn(__fmul2_rn(Rz, u), w2, az);
+}
+

@@ -63,8 +63,15 @@ __host__ __device__ constexpr int order_of(int t) {
 // cell (R' >= 1/theta), so FP32 intermediates cannot overflow however deep the
 // cell; a = h^-2 sum(...) is folded into the coefficients as B'' =
 // h^-2 B(M_n h^-|n|).  All scalings are exact powers of two.
+// The slot just past the coefficients (where the row has one) carries the
+// weight rho 2^-level of the cell's uniform-background term (0 without it).
+struct BgArgs {
+  const uint16_t* cbox;  // box of each cell
+  const double* rho;     // mean density of each box; nullptr: no background term
+};
+
 template <int P, typename T>
-__device__ __forceinline__ void finish_cell(int c, int level, const double* M, T* __restrict__ coef) {
+__device__ __forceinline__ void finish_cell(int c, int level, const double* M, T* __restrict__ coef, BgArgs bg) {
   constexpr int NM = Ord<P>::NM;
   double Ms[NM];
 #pragma unroll
@@ -76,6 +83,8 @@ __device__ __forceinline__ void finish_cell(int c, int level, const double* M, T
   for (int q = 0; q < Ord<P>::NB; q++) dst[q] = (T)mul_pow2(B[q], 2 * level);
 #pragma unroll
   for (int q = Ord<P>::NB; q < Ord<P>::NBS; q++) dst[q] = (T)0;
+  if constexpr (Ord<P>::NB < Ord<P>::NBS)
+    if (bg.rho) dst[Ord<P>::NB] = (T)mul_pow2(bg.rho[bg.cbox[c]], -level);
 }
 
 // Schedule of the upward pass.  Every cell gets an 8-bit key: leaves sort by
@@ -118,7 +127,7 @@ template <int P, typename T>
 __global__ void __launch_bounds__(128)
 leaf_moments_kernel(const uint32_t* __restrict__ order, const int* __restrict__ r, const int4* __restrict__ cA,
                     const int4* __restrict__ cB, const double* __restrict__ spos, const float* __restrict__ smass,
-                    int64_t n, double* __restrict__ mom, T* __restrict__ coef) {
+                    int64_t n, double* __restrict__ mom, T* __restrict__ coef, BgArgs bg) {
   constexpr int NM = Ord<P>::NM;
   const int nleaf = r[0];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nleaf; i += gridDim.x * blockDim.x) {
@@ -134,7 +143,7 @@ leaf_moments_kernel(const uint32_t* __restrict__ order, const int* __restrict__ 
     double* dst = mom + (int64_t)b * NM;
 #pragma unroll
     for (int t = 0; t < NM; t++) dst[t] = M[t];
-    finish_cell<P, T>(b, a.w & 0xff, M, coef);
+    finish_cell<P, T>(b, a.w & 0xff, M, coef, bg);
   }
 }
 
@@ -151,7 +160,7 @@ template <int P, typename T>
 __global__ void __launch_bounds__(128)
 level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __restrict__ r,
                      const int4* __restrict__ cA, const int4* __restrict__ cB, double* __restrict__ mom,
-                     T* __restrict__ coef) {
+                     T* __restrict__ coef, BgArgs bg) {
   constexpr int NM = Ord<P>::NM;
   const int lo = r[j], hi = r[j + 1];
   if (hi - lo < kWideLevel) {
@@ -192,7 +201,7 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
         double* pd = mom + (int64_t)b * NM;
 #pragma unroll
         for (int t = 0; t < NM; t++) pd[t] = M[t];
-        finish_cell<P, T>(b, pa.w & 0xff, M, coef);
+        finish_cell<P, T>(b, pa.w & 0xff, M, coef, bg);
       }
     }
     return;
@@ -215,7 +224,7 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
     double* pd = mom + (int64_t)b * NM;
 #pragma unroll
     for (int t = 0; t < NM; t++) pd[t] = M[t];
-    finish_cell<P, T>(b, pa.w & 0xff, M, coef);
+    finish_cell<P, T>(b, pa.w & 0xff, M, coef, bg);
   }
 }
 
@@ -282,6 +291,23 @@ field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __
   }
 }
 
+// mean density of each box (its mass over the unit volume), one block per box
+__global__ void __launch_bounds__(256) box_mass_kernel(const int64_t* __restrict__ off, const float* __restrict__ smass,
+                                                       double* __restrict__ rho) {
+  __shared__ double s_red[8];
+  const int box = blockIdx.x;
+  double m = 0.0;
+  for (int64_t j = off[box] + threadIdx.x; j < off[box + 1]; j += blockDim.x) m += (double)smass[j];
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_red[w];
+    rho[box] = t;
+  }
+}
+
 int gridc(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -290,6 +316,12 @@ int gridc(int64_t n, int threads) {
 }
 
 }  // namespace
+
+cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, cudaStream_t s) {
+  box_mass_kernel<<<nbox, 256, 0, s>>>(off, smass, rho);
+  nb_launch_counter += 1;
+  return cudaGetLastError();
+}
 
 int nb_coef_stride(int order) {
   switch (order) {
@@ -303,7 +335,9 @@ int nb_coef_stride(int order) {
 
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const int4* cA, const int4* cB,
                       const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
-                      uint32_t* uorder, uint32_t* uhist, int* urange, SortScratch* sc, cudaStream_t s) {
+                      uint32_t* uorder, uint32_t* uhist, int* urange, const uint16_t* cbox, const double* rho,
+                      SortScratch* sc, cudaStream_t s) {
+  const BgArgs bg{cbox, rho};
   upkey_kernel<<<gridc(ncell, 256), 256, 0, s>>>(ncell, pncell, cA, cB, ukey);
   nb_launch_counter += 1;
   cudaError_t e = nb_sort_digit8(ukey, ncell, uorder, uhist, sc, s);
@@ -314,9 +348,9 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const 
   const int gl = g < 152 * 4 ? g : 152 * 4;
 #define NB_UP(P, TT)                                                                                        \
   {                                                                                                         \
-    leaf_moments_kernel<P, TT><<<g, 128, 0, s>>>(uorder, urange, cA, cB, spos, smass, n, mom, (TT*)coef);   \
+    leaf_moments_kernel<P, TT><<<g, 128, 0, s>>>(uorder, urange, cA, cB, spos, smass, n, mom, (TT*)coef, bg); \
     for (int j = 0; j <= NB_QBITS; j++)                                                                     \
-      level_moments_kernel<P, TT><<<gl, 128, 0, s>>>(j, uorder, urange, cA, cB, mom, (TT*)coef);           \
+      level_moments_kernel<P, TT><<<gl, 128, 0, s>>>(j, uorder, urange, cA, cB, mom, (TT*)coef, bg);       \
   }
 #define NB_UPP(P) \
   if (fp64) NB_UP(P, double) else NB_UP(P, float)

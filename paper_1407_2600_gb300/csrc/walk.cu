@@ -20,6 +20,7 @@
 // whose level-l_E descendants share one image is accepted iff
 // d2 > floor(s^2/theta^2), s = 2^(23-l).
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -31,6 +32,7 @@ namespace {
 template <int P> struct WOrd;
 #define NB_WORD(P)                                                                                    \
   template <> struct WOrd<P> {                                                                        \
+    static constexpr int NB = kNB##P;                                                                 \
     static constexpr int NBS = (kNB##P + 3) & ~3;                                                     \
     template <typename T>                                                                             \
     static __device__ __forceinline__ void m2p(const T* B, T x, T y, T z, T e2, T& ax, T& ay, T& az) { \
@@ -47,6 +49,32 @@ NB_WORD(2)
 NB_WORD(3)
 NB_WORD(4)
 
+// Uniform-background term of an expanded cell: order 4 after expansions of
+// order 0 and 2, order 6 after order 4 (none at orders 1 and 3, whose
+// coefficient rows have no spare slot).  Its weight q = rho h_cell is stored
+// in the cell's coefficient row just past the expansion's coefficients.
+template <int P> struct WBg {
+  static constexpr bool has = false;
+  template <typename T>
+  static __device__ __forceinline__ void add(T, T, T, T, T&, T&, T&) {}
+  static __device__ __forceinline__ void add2(float2, float2, float2, float2, float2&, float2&, float2&) {}
+};
+#define NB_WBG(P, L)                                                                                        \
+  template <> struct WBg<P> {                                                                               \
+    static constexpr bool has = true;                                                                       \
+    template <typename T>                                                                                   \
+    static __device__ __forceinline__ void add(T q, T x, T y, T z, T& ax, T& ay, T& az) {                   \
+      cube_bg_l##L<T>(q, x, y, z, ax, ay, az);                                                              \
+    }                                                                                                       \
+    static __device__ __forceinline__ void add2(float2 q, float2 x, float2 y, float2 z, float2& ax, float2& ay, \
+                                                float2& az) {                                               \
+      cube_bg2_l##L(q, x, y, z, ax, ay, az);                                                                \
+    }                                                                                                       \
+  };
+NB_WBG(0, 4)
+NB_WBG(2, 4)
+NB_WBG(4, 6)
+
 template <typename T>
 struct WalkArgs {
   DevTree tr;
@@ -56,6 +84,7 @@ struct WalkArgs {
   long long thr[NB_NLEV];
   int n_direct;
   int mac_edge;
+  int bg;  // add the uniform-background term of every expanded cell
   int le;
   int* stack;
   int stack_cap;
@@ -145,16 +174,27 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           float2 px = make_float2(0.f, 0.f), py = px, pz = px;
           const float2 x2 = make_float2(xi, xi), y2 = make_float2(yi, yi), z2 = make_float2(zi, zi);
           const float2* cf = reinterpret_cast<const float2*>(&s_coef[wid][0]);
-          for (int q = 0; q < npair; q++) {
-            const float4 m0 = s_moff[wid][2 * q];
-            const bool two = 2 * q + 1 < nmp;
-            const float4 m1 = two ? s_moff[wid][2 * q + 1] : make_float4(0.f, 0.f, 0.f, 1.f);
-            const float2 sc = make_float2(m0.w, m1.w);
-            const float2 e2 = make_float2(s_meps[wid][2 * q], two ? s_meps[wid][2 * q + 1] : 1.f);
-            WOrd<P>::m2p2(&cf[q * NBS], __ffma2_rn(x2, sc, make_float2(m0.x, m1.x)),
-                          __ffma2_rn(y2, sc, make_float2(m0.y, m1.y)), __ffma2_rn(z2, sc, make_float2(m0.z, m1.z)),
-                          e2, px, py, pz);
-          }
+          auto pairs = [&](auto bgc) {
+            for (int q = 0; q < npair; q++) {
+              const float4 m0 = s_moff[wid][2 * q];
+              const bool two = 2 * q + 1 < nmp;
+              const float4 m1 = two ? s_moff[wid][2 * q + 1] : make_float4(0.f, 0.f, 0.f, 1.f);
+              const float2 sc = make_float2(m0.w, m1.w);
+              const float2 e2 = make_float2(s_meps[wid][2 * q], two ? s_meps[wid][2 * q + 1] : 1.f);
+              const float2 rx = __ffma2_rn(x2, sc, make_float2(m0.x, m1.x));
+              const float2 ry = __ffma2_rn(y2, sc, make_float2(m0.y, m1.y));
+              const float2 rz = __ffma2_rn(z2, sc, make_float2(m0.z, m1.z));
+              WOrd<P>::m2p2(&cf[q * NBS], rx, ry, rz, e2, px, py, pz);
+              // the padding cell of an odd chunk has weight 0 at R = (0, 0, 0) + offset 0: skip it
+              if constexpr (decltype(bgc)::value) {
+                const float2 qb = cf[q * NBS + WOrd<P>::NB];
+                WBg<P>::add2(two ? qb : make_float2(qb.x, 0.f), rx, ry, two ? rz : make_float2(rz.x, 1.f), px, py,
+                             pz);
+              }
+            }
+          };
+          if (WBg<P>::has && w.bg) pairs(std::true_type{});
+          else pairs(std::false_type{});
           kadd(ax, cx, px.x + px.y);
           kadd(ay, cy, py.x + py.y);
           kadd(az, cz, pz.x + pz.y);
@@ -174,11 +214,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         T px = 0, py = 0, pz = 0;
         // each M2P runs in its cell's unit (coordinates times 2^level,
         // coefficients pre-scaled): see the upward pass
-        for (int q = 0; q < nmp; q++) {
-          const V4 mo = s_moff[wid][q];
-          WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], fma(xi, mo.w, mo.x), fma(yi, mo.w, mo.y),
-                                   fma(zi, mo.w, mo.z), s_meps[wid][q], px, py, pz);
-        }
+        auto cells = [&](auto bgc) {
+          for (int q = 0; q < nmp; q++) {
+            const V4 mo = s_moff[wid][q];
+            const T rx = fma(xi, mo.w, mo.x), ry = fma(yi, mo.w, mo.y), rz = fma(zi, mo.w, mo.z);
+            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q], px, py, pz);
+            if constexpr (decltype(bgc)::value)
+              WBg<P>::template add<T>(s_coef[wid][q * NBS + WOrd<P>::NB], rx, ry, rz, px, py, pz);
+          }
+        };
+        if (WBg<P>::has && w.bg) cells(std::true_type{});
+        else cells(std::false_type{});
         kadd(ax, cx, px);
         kadd(ay, cy, py);
         kadd(az, cz, pz);
@@ -503,7 +549,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     const void* eps2, const long long* thr, int n_direct, int le, int* stack,
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
                     unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
-                    int mac_edge, cudaStream_t s) {
+                    int mac_edge, int bg, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
 #define NB_WALK(TT, P)                                                             \
@@ -516,6 +562,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     for (int l = 0; l < NB_NLEV; l++) a.thr[l] = thr[l];                           \
     a.n_direct = n_direct;                                                         \
     a.mac_edge = mac_edge;                                                         \
+    a.bg = bg;                                                                     \
     a.le = le;                                                                     \
     a.stack = stack;                                                               \
     a.stack_cap = stack_cap;                                                       \

@@ -28,6 +28,7 @@ NBODY_MIXED = 0
 NBODY_FP64 = 1
 NBODY_FLAG_ASYNC = 1
 NBODY_FLAG_MAC_EDGE = 2
+NBODY_FLAG_BACKGROUND = 4
 
 
 def NBODY_FLAG_WALK_VARIANT(v: int) -> int:

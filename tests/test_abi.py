@@ -56,6 +56,13 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
     p.flags = nb.NBODY_FLAG_WALK_VARIANT(4)
     rc, h = nb.nbody_build_tree(p, 10, 1, None)
     assert rc == nb.NBODY_EINVAL and not h
+    # background terms need a spare coefficient slot: not at orders 1 and 3
+    for order in (1, 3):
+        p = nb.nbody_default_params()
+        p.order = order
+        p.flags = nb.NBODY_FLAG_BACKGROUND
+        rc, h = nb.nbody_build_tree(p, 10, 1, None)
+        assert rc == nb.NBODY_EINVAL and not h
 
 
 def test_generated_kernel_header_is_current():

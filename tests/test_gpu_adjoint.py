@@ -36,23 +36,26 @@ def test_cic_loss_matches_oracle(cuda):
     assert np.abs(g.cpu().numpy().T - go).max() <= 1e-10 * np.abs(go).max()
 
 
-def _prm(eps, theta, order):
+def _prm(eps, theta, order, flags=0):
     import paper_1407_2600_gb300.nbody as nb
-    return nb.params(eps=eps, theta=theta, order=order, n_direct=2 if order <= 2 else 4)
+    return nb.params(eps=eps, theta=theta, order=order, n_direct=2 if order <= 2 else 4, flags=flags)
 
 
-@pytest.mark.parametrize("theta,order", [(0.5, 4), (0.6, 2)])
-def test_force_vjp_vs_finite_differences(cuda, theta, order):
+@pytest.mark.parametrize("theta,order,bg", [(0.5, 4, False), (0.6, 2, False), (0.5, 4, True), (0.5, 2, True)])
+def test_force_vjp_vs_finite_differences(cuda, theta, order, bg):
+    """With bg the uniform-background terms are on (their sink-side
+    derivative is part of the product)."""
     import torch
     import paper_1407_2600_gb300.nbody as nb
     x, eps = ics.config_haloes(16, seed=4, n_halo=2, nmin=200, nmax=400)
     n = len(x)
     rng = np.random.default_rng(11)
     lam = rng.standard_normal((n, 3))
-    tree = nb.Tree(_prm(eps, theta, order), _t(x, cuda))
+    tree = nb.Tree(_prm(eps, theta, order, nb.NBODY_FLAG_BACKGROUND if bg else 0), _t(x, cuda))
     mu = tree.forces_vjp(_t(lam.astype(np.float32), cuda, torch.float32)).cpu().numpy().T
     tree.close()
-    op = oracle.tree_params(eps, theta, order, n_direct=2 if order <= 2 else 4, ewald=4)
+    op = oracle.tree_params(eps, theta, order, n_direct=2 if order <= 2 else 4, ewald=4,
+                            bg={2: 4, 4: 6}[order] if bg else 0)
     lam32 = lam.astype(np.float32).astype(np.float64)
     h = 5e-9
     rms = np.sqrt(np.mean(mu ** 2))

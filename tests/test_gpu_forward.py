@@ -169,6 +169,60 @@ def test_edge_mac_vs_oracle_tree(cuda, name, gen, theta, order):
     assert abs(st["p2p"] - (ost["p2p"] + len(x))) <= 1e-9 * ost["p2p"] + 0.5
 
 
+BG_ORDER = {0: 4, 2: 4, 4: 6}
+
+
+@pytest.mark.parametrize("name,gen,theta,order", [CASES[0], CASES[1], CASES[2], CASES[4]])
+def test_background_terms_vs_oracle_tree(cuda, name, gen, theta, order):
+    """Uniform-background terms (the next even order of each expanded cell's
+    share of the mean density): same forces as the oracle with those terms,
+    and a visible change against the forces without them."""
+    nb = _nb()
+    x, eps = gen()
+    nd = 2 if order <= 2 else 4
+    a, st = _gpu_forces(x, cuda, eps=eps, theta=theta, order=order, n_direct=nd, flags=nb.NBODY_FLAG_BACKGROUND)
+    ref, ost = oracle.tree_forces(x, None, oracle.tree_params(eps, theta, order, n_direct=nd, ewald=4,
+                                                              bg=BG_ORDER[order]), return_stats=True)
+    rel = _rel(a, ref)
+    assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (np.median(rel), np.percentile(rel, 99))
+    assert st["m2p"] == ost["m2p"]
+    a0, _ = _gpu_forces(x, cuda, eps=eps, theta=theta, order=order, n_direct=nd)
+    ref0 = oracle.tree_forces(x, None, oracle.tree_params(eps, theta, order, n_direct=nd, ewald=4))
+    # the term's size in the oracle is reproduced on the GPU
+    d_gpu, d_or = a - a0, ref - ref0
+    size = np.linalg.norm(ref, axis=1)
+    scale = np.linalg.norm(d_or, axis=1).max()
+    if name.startswith("zeldovich"):  # near-uniform: the term is not negligible
+        assert scale > 1e-4 * np.median(size)
+    err = np.linalg.norm(d_gpu - d_or, axis=1)
+    assert np.all(err <= 0.02 * scale + 2e-5 * size), (err.max(), scale)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_background_terms_every_walk_variant(cuda, variant):
+    """The background term in the scalar and the packed-pair M2P paths."""
+    nb = _nb()
+    x, eps = ics.config_small(4)
+    ref = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.5, 2, n_direct=2, ewald=4, bg=4))
+    a, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=2, n_direct=2,
+                       flags=nb.NBODY_FLAG_BACKGROUND | nb.NBODY_FLAG_WALK_VARIANT(variant))
+    rel = _rel(a, ref)
+    assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (np.median(rel), np.percentile(rel, 99))
+
+
+def test_background_terms_cancel_lattice(cuda):
+    """On a perfect lattice (exact force 0) the background terms remove most
+    of the expansion error of the quadrupole tree."""
+    nb = _nb()
+    q = ics.lattice(32)
+    eps = 1.0 / (30 * 32)
+    a0, _ = _gpu_forces(q, cuda, eps=eps, theta=0.5, order=2, n_direct=2)
+    a1, _ = _gpu_forces(q, cuda, eps=eps, theta=0.5, order=2, n_direct=2, flags=nb.NBODY_FLAG_BACKGROUND)
+    m0 = np.median(np.linalg.norm(a0, axis=1))
+    m1 = np.median(np.linalg.norm(a1, axis=1))
+    assert m1 <= 0.1 * m0, (m0, m1)
+
+
 def test_forces_fp64_mode(cuda):
     x, eps = ics.config_small(2)
     a, _ = _gpu_forces(x, cuda, eps=eps, theta=0.5, order=4, precision=1)
