@@ -80,6 +80,44 @@ def walk_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def hbm_peak():
+    """(GB/s, source) of the HBM copy bandwidth the phases are measured against."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def phase_bytes(n, ncell, ngroup, order, nbox=1):
+    """Algorithmic DRAM bytes of one build's sort, build and upward phases and
+    of one evaluation's image-field phase: every array their kernels read or
+    write, counted once, per particle / cell / group (derivation in the design doc):
+      sort     box ids 2, keys 36, histograms 8, 24 per digit pass, sbox 8, gather 58
+      build    152 per particle + 194 per cell + 168 per group
+      upward   64 per particle + (91 + 16 nmom + 4 nbs) per cell
+      periodic 64 per particle (image-field L2P and the scatter to caller order)"""
+    npass = 8 + (0 if nbox == 1 else (1 if nbox <= 256 else 2))
+    nm = (order + 1) * (order + 2) * (order + 3) // 6
+    nbs = {0: 4, 1: 4, 2: 12, 3: 24, 4: 48}[order]
+    return {"ms_sort": n * (112 + 24 * npass), "ms_build": n * 152 + ncell * 194 + ngroup * 168,
+            "ms_upward": n * 64 + ncell * (91 + 16 * nm + 4 * nbs), "ms_periodic": n * 64}
+
+
+def phase_roofline(n, ncell, ngroup, order, phases, nbox=1):
+    peak, src = hbm_peak()
+    by = phase_bytes(n, ncell, ngroup, order, nbox)
+    bound = {"ms_sort": "hbm", "ms_build": "latency (prefix searches)", "ms_upward": "fp64 pipe",
+             "ms_periodic": "hbm"}
+    out = {}
+    for k, b in by.items():
+        gbs = b / (phases[k] * 1e-3) / 1e9
+        out[k[3:]] = {"bytes": b, "achieved_gbs": gbs, "frac": gbs / peak, "bound": bound[k]}
+    out["peak_gbs"] = peak
+    out["peak_source"] = src
+    return out
+
+
 def fp32_peak_tflops(mhz: float) -> float:
     return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
@@ -260,6 +298,8 @@ def run_gpu(args, rank, world, local_rank):
     achieved = flops / (walk_ms * 1e-3) / 1e12
     phases = {k: tm[k] / max(tm["builds"] if k in ("ms_sort", "ms_build", "ms_upward") else evals, 1)
               for k in ("ms_sort", "ms_build", "ms_upward", "ms_walk", "ms_periodic")}
+    phase_rf = phase_roofline(n, nb.nbody_tree_count(tree.handle, nb.EXPORT["cell_keys"]),
+                              nb.nbody_tree_count(tree.handle, nb.EXPORT["groups"]), ORDER, phases)
 
     # force evaluation alone (no kicks/drift, tree rebuilt each time)
     fe0, fe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -412,6 +452,7 @@ def run_gpu(args, rank, world, local_rank):
             "gpu_launches": tm["launches"] // 1,
             "clocks": ck,
             "phases_ms": phases,
+            "phase_roofline": phase_rf,
             "force_eval_ms": force_ms,
             "force_updates_per_s": n / (force_ms * 1e-3),
             "interactions_per_particle": {"p2p": tm["p2p"] / evals / n, "m2p": tm["m2p"] / evals / n},

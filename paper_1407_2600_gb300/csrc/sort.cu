@@ -89,6 +89,48 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
 }
 __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) { *(volatile uint32_t*)p = v; }
 
+// Decoupled look-back of one digit: the exclusive prefix of this tile from
+// the status words (flag | count) of the tiles before it.  The words of
+// kLookback predecessors are loaded at once, so a walk back over many tiles
+// that have published only their aggregates costs one memory latency per
+// kLookback tiles instead of one per tile.  A predecessor that has published
+// nothing yet is waited for (bounded: the wait sets NB_ST_TIMEOUT in *err and
+// gives up).
+constexpr int kLookback = 8;
+__device__ __forceinline__ uint32_t lookback(const uint32_t* __restrict__ status, int tile, int dd,
+                                             unsigned* __restrict__ err) {
+  uint32_t prefix = 0;
+  int t = tile - 1, spins = 0;
+  while (t >= 0) {
+    uint32_t sv[kLookback];
+#pragma unroll
+    for (int q = 0; q < kLookback; q++) sv[q] = t - q >= 0 ? ld_volatile(status + (int64_t)(t - q) * 256 + dd) : kFlagInc;
+    int used = kLookback;
+    bool done = false;
+#pragma unroll
+    for (int q = 0; q < kLookback; q++) {
+      if (done || used < kLookback) continue;
+      if ((sv[q] & ~kValMask) == 0u) {
+        used = q;  // not published yet: wait for it from here
+      } else {
+        prefix += sv[q] & kValMask;
+        if (sv[q] & kFlagInc) done = true;
+      }
+    }
+    if (done) break;
+    if (used < kLookback) {
+      t -= used;
+      if (++spins > NB_SPIN_LIMIT) {
+        atomicOr(err, NB_ST_TIMEOUT);
+        break;
+      }
+    } else {
+      t -= kLookback;
+    }
+  }
+  return prefix;
+}
+
 __global__ void __launch_bounds__(kSortThreads)
 onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                 uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, DigitFn dig,
@@ -156,21 +198,7 @@ onesweep_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ v
       st_volatile(my, kFlagInc | run);
     } else {
       st_volatile(my, kFlagAgg | run);
-      int t = tile - 1;
-      int spins = 0;
-      while (t >= 0) {
-        uint32_t sv = ld_volatile(status + (int64_t)t * 256 + dd);
-        if ((sv & ~kValMask) == 0u) {
-          if (++spins > NB_SPIN_LIMIT) {
-            atomicOr(err, NB_ST_TIMEOUT);
-            break;
-          }
-          continue;
-        }
-        prefix += sv & kValMask;
-        if (sv & kFlagInc) break;
-        t--;
-      }
+      prefix = lookback(status, tile, dd, err);
       __threadfence();
       st_volatile(my, kFlagInc | (prefix + run));
     }
@@ -244,20 +272,7 @@ digit_sweep_kernel(const uint8_t* __restrict__ digit, int64_t n, const uint32_t*
       st_volatile(my, kFlagInc | run);
     } else {
       st_volatile(my, kFlagAgg | run);
-      int t = tile - 1, spins = 0;
-      while (t >= 0) {
-        uint32_t sv = ld_volatile(status + (int64_t)t * 256 + dd);
-        if ((sv & ~kValMask) == 0u) {
-          if (++spins > NB_SPIN_LIMIT) {
-            atomicOr(err, NB_ST_TIMEOUT);
-            break;
-          }
-          continue;
-        }
-        prefix += sv & kValMask;
-        if (sv & kFlagInc) break;
-        t--;
-      }
+      prefix = lookback(status, tile, dd, err);
       __threadfence();
       st_volatile(my, kFlagInc | (prefix + run));
     }
