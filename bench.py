@@ -44,7 +44,7 @@ FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FM
 # the ncu capture summarised in profiles/walk_kernel_haloes96.md, scaled to
 # 2^21 particles; valid only while the walk's sources are unchanged since that
 # capture
-WALK_TRAFFIC = {"bytes": 107e6, "source_sha": "222f288132796c32"}
+WALK_TRAFFIC = {"bytes": 106e6, "source_sha": "2e8f5d91dec55cc2"}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
