@@ -545,6 +545,9 @@ def run_batched(dev, steps: int):
         a1 = a * math.exp(DLNA)
         tree.kdk_step(mom, acc, a, a1)
         a = a1
+    # walk tile sizes (sinks per group, direct-sum threshold) by the autotuner
+    tune = tree.autotune()
+    tree.forces(acc)
     torch.cuda.synchronize()
     tree.check()
     tree.timing(reset=True)
@@ -637,6 +640,7 @@ def run_batched(dev, steps: int):
                          for k in ("ms_sort", "ms_build", "ms_upward", "ms_walk", "ms_periodic")},
            "interactions_per_particle": {"p2p": tm["p2p"] / ev / n, "m2p": tm["m2p"] / ev / n},
            "walk_variant": tm["walk_variant"],
+           "tile_autotune": tune,
            "background_terms": {"force_eval_ms": bgms, "force_updates_per_s": n / (bgms * 1e-3),
                                 "note": "NBODY_FLAG_BACKGROUND: order-4 uniform-cube term of every expanded cell"}}
     tree.close()

@@ -340,6 +340,29 @@ int nbody_sort_keys_noalloc(const double *pos_dev, int64_t n, uint64_t *keys_out
  */
 int nbody_reserve(nbody_tree *tree, int64_t max_cells, int64_t max_groups, nbody_stream_t stream);
 
+/*
+ * Walk tile autotuner.  Times one rebuild + force evaluation of the tree's
+ * current positions for every candidate pair of tile sizes -- sinks per group
+ * n_group in {16, 24, 32} (the particles of a warp's shared interaction list)
+ * and direct-sum threshold n_direct in {2, 4, 8, 12} (accepted cells with at
+ * most that many particles are summed pairwise instead of through their
+ * expansion; candidates above n_leaf are skipped) -- keeps the fastest pair
+ * in the tree's parameters and rebuilds the tree with it.  Every candidate is
+ * the same force definition up to which accepted cells are summed directly
+ * (which only removes expansion error) and how sinks are grouped.
+ *   out  nullable: the timings and the choice
+ * Synchronises the stream; not allowed while capacities are reserved
+ * (NBODY_ENOTSUP) or while a stream is being captured.
+ */
+typedef struct {
+  int32_t ncand;           /* candidates timed */
+  int32_t n_group[12];
+  int32_t n_direct[12];
+  double ms[12];           /* rebuild + forces, CUDA events */
+  int32_t best;            /* index of the kept candidate */
+} nbody_tune;
+int nbody_autotune(nbody_tree *tree, nbody_tune *out, nbody_stream_t stream);
+
 /* Read and clear the tree's device status word (blocks on the stream). */
 int nbody_check(nbody_tree *tree, nbody_stream_t stream);
 void nbody_tree_free(nbody_tree *tree);

@@ -1158,6 +1158,57 @@ int nbody_reserve(nbody_tree* t, int64_t max_cells, int64_t max_groups, nbody_st
   return rc;
 }
 
+int nbody_autotune(nbody_tree* t, nbody_tune* out, nbody_stream_t stream) {
+  if (!t) return NBODY_EINVAL;
+  if (t->fixed_cap) return NBODY_ENOTSUP;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (capturing(s)) return NBODY_ENOTSUP;
+  const long long l0 = nb_launch_counter;
+  const nbody_params p0 = t->prm;
+  static const int kGroups[3] = {16, 24, 32};
+  static const int kDirect[4] = {2, 4, 8, 12};
+  nbody_tune r;
+  memset(&r, 0, sizeof(r));
+  r.best = -1;
+  Buf acc;
+  NB_CU(acc.ensure(12 * t->n));
+  EventPair ev;
+  NB_CU(ev.create());
+  int rc = NBODY_OK;
+  for (int gi = 0; gi < 3 && rc == NBODY_OK; gi++)
+    for (int di = 0; di < 4 && rc == NBODY_OK; di++) {
+      if (kDirect[di] > p0.n_leaf) continue;
+      t->prm.n_group = kGroups[gi];
+      t->prm.n_direct = kDirect[di];
+      // once untimed (buffers sized for this candidate), then timed
+      if ((rc = build_impl(t, s)) || (rc = forces_impl(t, acc.as<float>(), s))) break;
+      NB_CU(cudaEventRecord(ev.a, s));
+      if ((rc = build_impl(t, s)) || (rc = forces_impl(t, acc.as<float>(), s))) break;
+      NB_CU(cudaEventRecord(ev.b, s));
+      NB_CU(cudaEventSynchronize(ev.b));
+      if ((rc = read_status(t, s))) break;
+      float ms = 0.f;
+      NB_CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
+      const int k = r.ncand++;
+      r.n_group[k] = kGroups[gi];
+      r.n_direct[k] = kDirect[di];
+      r.ms[k] = ms;
+      if (r.best < 0 || ms < r.ms[r.best]) r.best = k;
+    }
+  t->prm = p0;
+  if (rc == NBODY_OK && r.best >= 0) {
+    t->prm.n_group = r.n_group[r.best];
+    t->prm.n_direct = r.n_direct[r.best];
+  }
+  // the tree as the caller will use it: rebuilt with the kept tile sizes
+  const int rb = build_impl(t, s);
+  t->launches += nb_launch_counter - l0;
+  if (rc == NBODY_OK) rc = rb;
+  if (rc == NBODY_OK) rc = read_status(t, s);
+  if (out) *out = r;
+  return rc;
+}
+
 int nbody_check(nbody_tree* t, nbody_stream_t stream) {
   if (!t) return NBODY_EINVAL;
   return read_status(t, (cudaStream_t)stream);

@@ -40,7 +40,8 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 # every symbol include/nbody.h declares
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces", "nbody_forces64",
            "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
-           "nbody_tree_export", "nbody_tree_lookup", "nbody_reserve", "nbody_check", "nbody_tree_free",
+           "nbody_tree_export", "nbody_tree_lookup", "nbody_reserve", "nbody_autotune", "nbody_check",
+           "nbody_tree_free",
            "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
 
 
@@ -74,6 +75,18 @@ class Timing(C.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["walk_tune_ms"] = list(self.walk_tune_ms)
         return d
+
+
+class Tune(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("n_group", C.c_int32 * 12), ("n_direct", C.c_int32 * 12),
+                ("ms", C.c_double * 12), ("best", C.c_int32)]
+
+    def asdict(self):
+        k = self.ncand
+        return {"candidates": [{"n_group": self.n_group[i], "n_direct": self.n_direct[i], "ms": self.ms[i]}
+                               for i in range(k)],
+                "n_group": self.n_group[self.best] if self.best >= 0 else None,
+                "n_direct": self.n_direct[self.best] if self.best >= 0 else None}
 
 
 class NbodyError(RuntimeError):
@@ -111,6 +124,7 @@ def lib():
         L.nbody_tree_export.argtypes = [_vp, C.c_int, _vp, _vp]
         L.nbody_tree_lookup.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
         L.nbody_reserve.argtypes = [_vp, C.c_int64, C.c_int64, _vp]
+        L.nbody_autotune.argtypes = [_vp, C.POINTER(Tune), _vp]
         L.nbody_check.argtypes = [_vp, _vp]
         L.nbody_tree_free.argtypes = [_vp]
         L.nbody_tree_free.restype = None
@@ -198,6 +212,10 @@ def nbody_tree_lookup(tree: int, keys_dev: int, nkeys: int, idx_dev: int, stream
 
 def nbody_reserve(tree: int, max_cells: int, max_groups: int, stream: int | None = None) -> int:
     return lib().nbody_reserve(tree, max_cells, max_groups, stream)
+
+
+def nbody_autotune(tree: int, out: Tune | None = None, stream: int | None = None) -> int:
+    return lib().nbody_autotune(tree, C.byref(out) if out is not None else None, stream)
 
 
 def nbody_check(tree: int, stream: int | None = None) -> int:
@@ -337,6 +355,17 @@ class Tree:
         mg = int(max_groups) if max_groups is not None else int(math.ceil(ng * (1.0 + slack))) + 64
         _check(nbody_reserve(self.handle, mc, mg, _stream()), "nbody_reserve")
         return mc, mg
+
+    def autotune(self):
+        """Pick the walk tile sizes (sinks per group, direct-sum threshold) by
+        timing (nbody_autotune); the tree's parameters and tree are updated.
+        Returns the timings and the choice."""
+        t = Tune()
+        _check(nbody_autotune(self.handle, t, _stream()), "nbody_autotune")
+        d = t.asdict()
+        self.params.n_group = d["n_group"]
+        self.params.n_direct = d["n_direct"]
+        return d
 
     def check(self):
         """Status of the calls made since the last read (nbody_check)."""

@@ -2,8 +2,9 @@
 realisations, Sec. 2.1): builds that keep their counts on the device give
 bit-identical trees and forces, a captured sequence of KDK steps replays to
 the same state as the same steps called one by one, its final forces match
-the oracle tree, and capacities that are too small are reported as
-NBODY_EOVERFLOW without touching memory past the buffers."""
+the oracle tree, capacities that are too small are reported as
+NBODY_EOVERFLOW without touching memory past the buffers, and the walk tile
+autotuner keeps the fastest of its candidates without changing the method."""
 import math
 
 import numpy as np
@@ -122,3 +123,35 @@ def test_capacity_overflow_is_reported_and_recovers(cuda):
     tree.reserve(max_cells=nc, max_groups=ng)
     assert torch.equal(tree.forces(), acc0)
     tree.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_the_method(cuda):
+    """The tile autotuner times every (sinks per group, direct-sum threshold)
+    candidate, keeps the fastest, and the tuned tree gives the forces of a
+    tree built with those sizes, which match the oracle with them."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    tree, pos, mom, off, eps = _setup(cuda)
+    res = tree.autotune()
+    cands = res["candidates"]
+    assert len(cands) == 12
+    best = min(cands, key=lambda c: c["ms"])
+    assert (res["n_group"], res["n_direct"]) == (best["n_group"], best["n_direct"])
+    acc = tree.forces()
+    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=res["n_direct"], n_group=res["n_group"],
+                    ewald_grid=4, flags=nb.NBODY_FLAG_MAC_EDGE)
+    fresh = nb.Tree(prm, pos, offsets=off.tolist(), eps=eps)
+    assert torch.equal(fresh.forces(), acc)
+    fresh.close()
+    x = pos.cpu().numpy().T
+    a = acc.cpu().numpy().T.astype(np.float64)
+    b = len(SIZES) - 1
+    xb = x[off[b]:off[b + 1]]
+    tgt = ics.random_targets(len(xb), 128, 77)
+    at = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.5, 2, n_direct=res["n_direct"],
+                                                         n_group=res["n_group"], ewald=4, mac=1, ew_grid=4),
+                            targets=tgt)
+    rt = np.linalg.norm(a[off[b] + tgt] - at, axis=1) / np.linalg.norm(at, axis=1)
+    assert np.median(rt) <= 1e-5, np.median(rt)
+    tree.close()
+
