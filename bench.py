@@ -95,13 +95,14 @@ def phase_bytes(n, ncell, ngroup, order, nbox=1):
     write, counted once, per particle / cell / group (derivation in the design doc):
       sort     box ids 2, keys 36, histograms 8, 24 per digit pass, sbox 8, gather 58
       build    152 per particle + 194 per cell + 168 per group
-      upward   64 per particle + (91 + 16 nmom + 4 nbs) per cell
+      upward   28 per particle + (91 + 16 nmom + 4 nbs) per cell (the image-field
+               source moments are the tree's level-3 moments, copied)
       periodic 64 per particle (image-field L2P and the scatter to caller order)"""
     npass = 8 + (0 if nbox == 1 else (1 if nbox <= 256 else 2))
     nm = (order + 1) * (order + 2) * (order + 3) // 6
     nbs = {0: 4, 1: 4, 2: 12, 3: 24, 4: 48}[order]
     return {"ms_sort": n * (112 + 24 * npass), "ms_build": n * 152 + ncell * 194 + ngroup * 168,
-            "ms_upward": n * 64 + ncell * (91 + 16 * nm + 4 * nbs), "ms_periodic": n * 64}
+            "ms_upward": n * 28 + ncell * (91 + 16 * nm + 4 * nbs), "ms_periodic": n * 64}
 
 
 def phase_roofline(n, ncell, ngroup, order, phases, nbox=1):

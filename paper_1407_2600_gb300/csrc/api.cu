@@ -46,7 +46,9 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const 
                       SortScratch* sc, cudaStream_t s);
 cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, cudaStream_t s);
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
-                             const double* spos, const float* smass, int64_t n, double* fm, cudaStream_t s);
+                             const double* spos, const float* smass, int64_t n, const int* hval,
+                             const uint64_t* ckey, const uint16_t* cbox, uint64_t hcap, const double* mom,
+                             int order, double* fm, cudaStream_t s);
 int nb_walk_warps(bool fp64);
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
@@ -562,7 +564,9 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
     NB_CU(t->fm.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
     NB_CU(nb_field_moments(p.ewald_order, p.ewald_level, t->nbox, t->off.as<int64_t>(), t->keys.as<uint64_t>(),
-                           t->spos.as<double>(), t->smass.as<float>(), n, t->fm.as<double>(), s));
+                           t->spos.as<double>(), t->smass.as<float>(), n, t->hval.as<int>(),
+                           t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(), t->hcap, t->mom.as<double>(), p.order,
+                           t->fm.as<double>(), s));
   }
   if (timed) {
     NB_CU(cudaEventRecord(be[3], s));

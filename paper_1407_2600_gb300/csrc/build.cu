@@ -203,15 +203,6 @@ __global__ void nchild_kernel(const int* __restrict__ pncell, int4* __restrict__
 }
 
 // ---- hash of cell keys (open addressing, linear probing) ------------------------
-__device__ __forceinline__ uint64_t hmix(uint64_t k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
-}
-
 // slots hold cell indices (-1 = empty); a slot matches when the cell's key
 // and box equal the query
 __global__ void hash_insert_kernel(const int* __restrict__ pncell, const uint64_t* __restrict__ ckey,
@@ -219,7 +210,7 @@ __global__ void hash_insert_kernel(const int* __restrict__ pncell, const uint64_
                                    uint64_t mask, unsigned* err) {
   const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
-    uint64_t h = hmix(ckey[b] ^ ((uint64_t)cbox[b] * 0x9e3779b97f4a7c15ull)) & mask;
+    uint64_t h = hslot(ckey[b], cbox[b], mask);
     bool done = false;
     for (uint64_t probe = 0; probe <= mask; probe++) {
       if (atomicCAS(&hval[h], -1, b) == -1) {
@@ -237,19 +228,7 @@ __global__ void hash_lookup_kernel(const uint64_t* __restrict__ q, int64_t nq, i
                                    const uint16_t* __restrict__ cbox, uint64_t mask, int* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t k = q[i];
-    uint64_t h = hmix(k ^ ((uint64_t)box * 0x9e3779b97f4a7c15ull)) & mask;
-    int r = -1;
-    for (uint64_t probe = 0; probe <= mask; probe++) {
-      int v = hval[h];
-      if (v < 0) break;
-      if (ckey[v] == k && cbox[v] == box) {
-        r = v;
-        break;
-      }
-      h = (h + 1) & mask;
-    }
-    out[i] = r;
+    out[i] = hash_find(hval, ckey, cbox, mask, q[i], box);
   }
 }
 

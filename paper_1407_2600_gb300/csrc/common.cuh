@@ -95,6 +95,32 @@ struct EventPair {
   }
 };
 
+// ---- key hash of the cells (open addressing, linear probing) ------------------
+__device__ __forceinline__ uint64_t hmix(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+__device__ __forceinline__ uint64_t hslot(uint64_t key, int box, uint64_t mask) {
+  return hmix(key ^ ((uint64_t)box * 0x9e3779b97f4a7c15ull)) & mask;
+}
+// the cell with this placeholder key in this box, or -1 (slots hold cell
+// indices, -1 = empty)
+__device__ __forceinline__ int hash_find(const int* __restrict__ hval, const uint64_t* __restrict__ ckey,
+                                         const uint16_t* __restrict__ cbox, uint64_t mask, uint64_t key, int box) {
+  uint64_t h = hslot(key, box, mask);
+  for (uint64_t probe = 0; probe <= mask; probe++) {
+    const int v = hval[h];
+    if (v < 0) return -1;
+    if (ckey[v] == key && cbox[v] == box) return v;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
 // ---- device-side tree description passed to kernels -------------------------
 struct DevTree {
   int64_t n;

@@ -228,16 +228,40 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
   }
 }
 
-// image-field source moments: one block per (box, level-le prefix)
+// Image-field source moments: one block per (box, level-le prefix).  When the
+// prefix is a cell of the tree and the tree's moments reach order PE, they are
+// the same moments (about the same centre, over the same particles): they are
+// copied; otherwise (a prefix inside a leaf, or a lower tree order) they are
+// formed from the prefix's particles.
+struct TreeMoments {
+  const int* hval;
+  const uint64_t* ckey;
+  const uint16_t* cbox;
+  uint64_t mask;
+  const double* mom;  // nullptr: always from the particles
+  int nm;             // moments per cell of the tree
+};
+
 template <int PE>
 __global__ void __launch_bounds__(256)
 field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __restrict__ skeys,
                      const double* __restrict__ spos, const float* __restrict__ smass, int64_t n,
-                     double* __restrict__ fm) {
+                     TreeMoments tm, double* __restrict__ fm) {
   constexpr int NM = (PE + 1) * (PE + 2) * (PE + 3) / 6;
   const int ncp = 1 << (3 * le);
   const int box = blockIdx.y;
   const int cell = blockIdx.x;
+  __shared__ int s_tc;
+  if (threadIdx.x == 0)
+    s_tc = (tm.mom && tm.nm >= NM) ? hash_find(tm.hval, tm.ckey, tm.cbox, tm.mask,
+                                               (1ull << (3 * le)) | (uint64_t)cell, box)
+                                   : -1;
+  __syncthreads();
+  if (s_tc >= 0) {
+    double* dst = fm + ((int64_t)box * ncp + cell) * NM;
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) dst[t] = tm.mom[(int64_t)s_tc * tm.nm + t];
+    return;
+  }
   __shared__ int64_t s_rng[2];
   __shared__ double s_red[8][NM];
   if (threadIdx.x == 0) {
@@ -368,14 +392,17 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const 
 }
 
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
-                             const double* spos, const float* smass, int64_t n, double* fm, cudaStream_t s) {
+                             const double* spos, const float* smass, int64_t n, const int* hval,
+                             const uint64_t* ckey, const uint16_t* cbox, uint64_t hcap, const double* mom,
+                             int order, double* fm, cudaStream_t s) {
   dim3 g(1u << (3 * le), nbox);
+  const TreeMoments tm{hval, ckey, cbox, hcap - 1, mom, (order + 1) * (order + 2) * (order + 3) / 6};
   switch (pe) {
-    case 1: field_moments_kernel<1><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
-    case 2: field_moments_kernel<2><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
-    case 3: field_moments_kernel<3><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
-    case 4: field_moments_kernel<4><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
-    default: field_moments_kernel<5><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, fm); break;
+    case 1: field_moments_kernel<1><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
+    case 2: field_moments_kernel<2><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
+    case 3: field_moments_kernel<3><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
+    case 4: field_moments_kernel<4><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
+    default: field_moments_kernel<5><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
   }
   nb_launch_counter += 1;
   return cudaGetLastError();
