@@ -12,7 +12,8 @@ Contents (each function cites the passage it follows):
 * ``tree_forces``    O2, FP64 CPU treecode with the same method definition as
   the GPU path (Sec. 2.1: keys, key-implied tree, multipoles, MAC, groups).
 * ``kick_factor`` / ``drift_factor`` / ``kdk_step``  O3, comoving leapfrog in an
-  Einstein-de Sitter background (Sec. 2.1 cites a symplectic integrator).
+  Einstein-de Sitter background (Sec. 2.1 cites a symplectic integrator);
+  ``assign_rungs`` / ``kdk_multistep``  its block-step (hierarchical) form.
 * ``cic_loss``       CIC density contrast and sum of squares, with gradient.
 * ``direct_vjp`` / ``adjoint_kdk``  O4, exact reverse mode of O1 + O3.
 """
@@ -395,6 +396,72 @@ def kdk_step(x, p, g0, a0, a1, force):
     g1 = force(x)
     p = p + kick_factor(ah, a1) * g1
     return x, p, g1
+
+
+# Hierarchical (block) steps: Sec. 2.1 cites the adaptive symplectic
+# integrator of Quinn et al. (1997), whose particles take power-of-two
+# fractions of the global step.  Reading used here: a global step in ln a is
+# cut into T = 2^rmax ticks; a particle on rung r takes steps of S = 2^(rmax-r)
+# ticks in kick-drift-kick form: at the tick where its step starts it is
+# kicked over the first half of that step, every tick all particles drift,
+# and at the tick where its step ends its acceleration is recomputed at the
+# new positions and it is kicked over the second half.  Rungs are fixed for
+# the global step.  With rmax = 0 this is kdk_step.
+def assign_rungs(g32, eps, eta, dlna, rmax):
+    """Rung of each particle: the smallest r in [0, rmax] with
+    (dlna / 2^r)^2 <= eta^2 H0^2 eps / |g|, i.e. 4^r >= q with
+    q = |g| dlna^2 / (eta^2 H0^2 eps) (rmax if none): the step in ln a at
+    which a particle moves about eta^2 eps under its acceleration.  g32 (n,3)
+    are the accelerations as float32 values; |g| and q are formed in FP64 in
+    the order written.  eps may be per particle."""
+    g = np.asarray(g32, dtype=np.float32).astype(np.float64)
+    s = np.sqrt((g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1]) + g[:, 2] * g[:, 2])
+    eps = np.broadcast_to(np.asarray(eps, dtype=np.float64), s.shape)
+    c = (dlna * dlna) / ((eta * eta) * (H0 * H0) * eps)
+    q = s * c
+    r = np.zeros(len(s), dtype=np.int64)
+    f = np.ones(len(s))
+    for _ in range(rmax):
+        up = f < q
+        r[up] += 1
+        f = np.where(up, f * 4.0, f)
+    return r
+
+
+def tick_a(a0, a1, rmax, j2):
+    """Expansion factor at half-tick j2 (tick j2/2) of the step a0 -> a1."""
+    T = 1 << rmax
+    L = math.log(a1 / a0)
+    return a0 * math.exp(L * j2 / (2 * T))
+
+
+def kdk_multistep(x, p, g, rung, a0, a1, rmax, force):
+    """One global step a0 -> a1 with block steps (see above).  x, p, g (n,3);
+    rung (n,) in [0, rmax]; force(x) -> (n,3).  Returns x, p, g with g the
+    accelerations at each particle's last force evaluation."""
+    T = 1 << rmax
+    rung = np.asarray(rung, dtype=np.int64)
+    S = np.left_shift(1, rmax - rung)
+    x, p, g = x.copy(), p.copy(), g.copy()
+    for k in range(T):
+        start = (k % S) == 0
+        for r in range(rmax + 1):
+            sel = start & (rung == r)
+            if sel.any():
+                st = 1 << (rmax - r)
+                p[sel] += kick_factor(tick_a(a0, a1, rmax, 2 * k), tick_a(a0, a1, rmax, 2 * k + st)) * g[sel]
+        x = np.mod(x + drift_factor(tick_a(a0, a1, rmax, 2 * k), tick_a(a0, a1, rmax, 2 * k + 2)) * p, 1.0)
+        end = ((k + 1) % S) == 0
+        if end.any():
+            gn = force(x)
+            g[end] = gn[end]
+            for r in range(rmax + 1):
+                sel = end & (rung == r)
+                if sel.any():
+                    st = 1 << (rmax - r)
+                    p[sel] += kick_factor(tick_a(a0, a1, rmax, 2 * (k + 1) - st),
+                                          tick_a(a0, a1, rmax, 2 * (k + 1))) * g[sel]
+    return x, p, g
 
 
 def zeldovich_state(q, psi, a):

@@ -251,6 +251,41 @@ def test_background_terms_cancel_a_lattice():
     assert res[4] <= 0.1 * res[0] and res[6] <= 1.1 * res[4], res
 
 
+def test_multistep_reduces_to_global_steps():
+    """Block steps: with one rung (rmax = 0) the step is kdk_step; with every
+    particle on the finest rung it is 2^rmax global steps on the tick grid;
+    under a constant uniform field every particle's momentum changes by
+    g K(a0, a1) whatever its rung (its kicks tile the step)."""
+    rng = np.random.default_rng(3)
+    x0 = rng.uniform(0, 1, (40, 3))
+    p0 = rng.standard_normal((40, 3)) * 0.01
+    force = lambda xx: -0.3 * (xx - 0.5)  # smooth position-dependent field
+    g0 = force(x0)
+    a0, a1 = 0.05, 0.07
+    x1, p1, g1 = O.kdk_multistep(x0, p0, g0, np.zeros(40, int), a0, a1, 0, force)
+    xr, pr, gr = O.kdk_step(x0, p0, g0, a0, a1, force)
+    assert np.abs(x1 - xr).max() <= 1e-14 and np.abs(p1 - pr).max() <= 1e-14
+    rmax = 2
+    x1, p1, g1 = O.kdk_multistep(x0, p0, g0, np.full(40, rmax), a0, a1, rmax, force)
+    xs, ps, gs = x0, p0, g0
+    for k in range(1 << rmax):
+        xs, ps, gs = O.kdk_step(xs, ps, gs, O.tick_a(a0, a1, rmax, 2 * k), O.tick_a(a0, a1, rmax, 2 * k + 2), force)
+    assert np.abs(x1 - xs).max() <= 1e-14 and np.abs(p1 - ps).max() <= 1e-14
+    gc = np.array([0.3, -0.2, 0.1])
+    const = lambda xx: np.broadcast_to(gc, xx.shape).copy()
+    rung = rng.integers(0, rmax + 1, 40)
+    x1, p1, g1 = O.kdk_multistep(x0, p0, const(x0), rung, a0, a1, rmax, const)
+    assert np.abs(p1 - (p0 + gc * O.kick_factor(a0, a1))).max() <= 1e-15
+    # rung assignment: 4^r >= q at the smallest r, capped
+    g = np.array([[1.0, 0, 0], [4.0, 0, 0], [4.001, 0, 0], [1e6, 0, 0]], dtype=np.float32)
+    c = 1.0 / ((0.5 ** 2) * O.H0 ** 2 * 1.0)
+    # q = |g| dlna^2 / (eta^2 H0^2 eps) with dlna = 1, eta = 0.5, eps = 1
+    r = O.assign_rungs(g, 1.0, 0.5, 1.0, 5)
+    q = np.array([1.0, 4.0, 4.001, 1e6]) * c
+    want = [min(5, int(np.ceil(np.log(v) / np.log(4.0) - 1e-12))) if v > 1 else 0 for v in q]
+    assert list(r) == want, (list(r), want)
+
+
 def test_tree_topology_invariants():
     x, _ = ics.config_haloes(16, seed=4, n_halo=3, nmin=100, nmax=400)
     key, lev, st, ct = O.tree_cells(x, n_leaf=8)
