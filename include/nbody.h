@@ -188,6 +188,39 @@ int nbody_kdk_step(nbody_tree *tree, double *pos_dev, float *mom_dev, float *acc
                    double a1, nbody_stream_t stream);
 
 /*
+ * Block steps (the hierarchical form of the symplectic integrator cited in
+ * Sec. 2.1, Quinn et al. 1997).  A global step in ln a is cut into
+ * T = 2^rmax ticks uniform in ln a (tick j at a_j = a0 exp(j ln(a1/a0)/T)); a
+ * particle on rung r takes steps of S = 2^(rmax - r) ticks in kick-drift-kick
+ * form: when its step starts it is kicked over the step's first half,
+ * K(a_j, a_{j+S/2}); every tick all particles drift D(a_j, a_{j+1}) and the
+ * tree is rebuilt; when its step ends its acceleration is recomputed (only
+ * the groups holding such particles are walked) and it is kicked over the
+ * second half.  Rungs stay fixed during the call.  With rmax = 0 this is
+ * nbody_kdk_step.
+ *
+ * nbody_assign_rungs: rung of each particle from its acceleration, the
+ * smallest r in [0, rmax] with 4^r >= |g| dlna^2 / (eta^2 H0^2 eps) (eps of
+ * the particle's box, |g| from the FP32 acc in FP64): the step at which a
+ * particle moves about eta^2 eps under g.
+ *   acc_dev   3*n FP32 accelerations (caller order)
+ *   eta > 0, dlna > 0 (the global step in ln a), rmax 0..7
+ *   rung_dev  n int8 output (caller order)
+ * nbody_forces_active: accelerations of the particles with rung >= rmin at
+ * the last build's positions; the other entries of acc_dev are not written.
+ * nbody_kdk_multistep: one global step a0 -> a1 (a1 > a0); pos_dev, mom_dev,
+ * acc_dev as in nbody_kdk_step (acc_dev must hold every particle's
+ * acceleration at the start, and holds each particle's last one at the end);
+ * rung_dev n int8 in [0, rmax].
+ */
+int nbody_assign_rungs(nbody_tree *tree, const float *acc_dev, double eta, double dlna, int rmax,
+                       int8_t *rung_dev, nbody_stream_t stream);
+int nbody_forces_active(nbody_tree *tree, const int8_t *rung_dev, int rmin, float *acc_dev,
+                        nbody_stream_t stream);
+int nbody_kdk_multistep(nbody_tree *tree, double *pos_dev, float *mom_dev, float *acc_dev,
+                        const int8_t *rung_dev, double a0, double a1, int rmax, nbody_stream_t stream);
+
+/*
  * Reverse mode of one nbody_kdk_step, with g(x0) recomputed from pos0 (so the
  * step is a function (x0, p0) -> (x1, p1)).  Given the cotangents of the
  * step's outputs it returns those of its inputs:

@@ -142,6 +142,8 @@ struct nbody_tree {
   // image field
   Buf fm;
   Buf rho;  // mean density per box (background terms)
+  // block steps: active sinks (sorted order), active groups, per-box rung factors
+  Buf act_s, act_g, rungc;
   const double* tab64 = nullptr;
   const float* tab32 = nullptr;
   // walk
@@ -173,7 +175,7 @@ struct nbody_tree {
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
                   &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
-                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho,
+                  &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho, &act_s, &act_g, &rungc,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
                   &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq};
     for (Buf* b : all) b->release();
@@ -206,6 +208,8 @@ struct nbody_tree {
     t.gC = gC.as<int4>();
     t.gD = gD.as<int4>();
     t.sleaf = sleaf.as<int>();
+    t.sact = nullptr;
+    t.gact = nullptr;
     return t;
   }
 };
@@ -344,6 +348,58 @@ __global__ void differ_kernel(int64_t n3, const unsigned long long* __restrict__
 
 __global__ void accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ tot) {
   if (threadIdx.x < 4) tot[threadIdx.x] += c[threadIdx.x];
+}
+
+// ---- block steps ------------------------------------------------------------------
+// rung of each particle (caller order): the smallest r in [0, rmax] with
+// 4^r >= q = |g| c_box, c_box = dlna^2 / (eta^2 H0^2 eps_box); |g| and q in
+// FP64, rounded at every operation (no contraction), from the FP32 g
+__global__ void rung_kernel(int64_t n, const float* __restrict__ acc, const uint16_t* __restrict__ box_of,
+                            const double* __restrict__ cbox, int rmax, int8_t* __restrict__ rung) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double gx = acc[i], gy = acc[n + i], gz = acc[2 * n + i];
+    const double g2 = __dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), __dmul_rn(gz, gz));
+    const double q = __dmul_rn(__dsqrt_rn(g2), cbox[box_of[i]]);
+    int r = 0;
+    double f = 1.0;
+    while (r < rmax && f < q) {
+      r++;
+      f *= 4.0;
+    }
+    rung[i] = (int8_t)r;
+  }
+}
+
+// active sinks in key order: rung[perm[i]] >= rmin
+__global__ void active_kernel(int64_t n, const uint32_t* __restrict__ perm, const int8_t* __restrict__ rung, int rmin,
+                              uint8_t* __restrict__ sact) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sact[i] = rung[perm[i]] >= rmin ? 1 : 0;
+}
+
+// a group is evaluated when any of its sinks is active
+__global__ void group_active_kernel(const int* __restrict__ pngroup, const int4* __restrict__ gA,
+                                    const uint8_t* __restrict__ sact, uint8_t* __restrict__ gact) {
+  const int ngroup = *pngroup;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x) {
+    const int4 a = gA[g];
+    uint8_t any = 0;
+    for (int k = 0; k < a.y; k++) any |= sact[a.x + k];
+    gact[g] = any;
+  }
+}
+
+// kicks of the particles whose rung has a factor in this call (f[r] != 0)
+struct RungKicks {
+  float f[8];
+};
+__global__ void kick_rungs_kernel(int64_t n, float* __restrict__ mom, const float* __restrict__ acc,
+                                  const int8_t* __restrict__ rung, RungKicks k) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float f = k.f[rung[i] & 7];
+    if (f != 0.f)
+      for (int d = 0; d < 3; d++) mom[d * n + i] = fmaf(f, acc[d * n + i], mom[d * n + i]);
+  }
 }
 
 __global__ void max_level_kernel(int ncell, const int4* __restrict__ cA, int* out) {
@@ -616,7 +672,8 @@ int field_impl(nbody_tree* t, cudaStream_t s) {
   return NBODY_OK;
 }
 
-int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullptr) {
+int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullptr, const uint8_t* sact = nullptr,
+                const uint8_t* gact = nullptr) {
   const nbody_params& p = t->prm;
   const bool fp64 = p.precision == NBODY_FP64;
   const int64_t n = t->n;
@@ -631,6 +688,8 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   const bool timed = !capturing(s);
   if (timed) NB_CU(cudaEventRecord(fe[0], s));
   DevTree tr = t->dev();
+  tr.sact = sact;
+  tr.gact = gact;
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
@@ -866,6 +925,101 @@ int nbody_kdk_step(nbody_tree* tree, double* pos_dev, float* mom_dev, float* acc
   NB_CU(cudaGetLastError());
   if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
   return read_status(tree, s);
+}
+
+namespace {
+
+// accelerations of the particles with rung >= rmin, the others' left as they are
+int forces_active_impl(nbody_tree* t, const int8_t* rung, int rmin, float* acc, cudaStream_t s) {
+  const int64_t n = t->n;
+  NB_CU(t->act_s.ensure(n));
+  NB_CU(t->act_g.ensure((int64_t)t->group_cap + 1));
+  active_kernel<<<gridn(n, 256), 256, 0, s>>>(n, t->vals.as<uint32_t>(), rung, rmin, t->act_s.as<uint8_t>());
+  group_active_kernel<<<gridn(t->group_cap, 256), 256, 0, s>>>(t->totals.as<int>() + 1, t->gA.as<int4>(),
+                                                                t->act_s.as<uint8_t>(), t->act_g.as<uint8_t>());
+  nb_launch_counter += 2;
+  NB_CU(cudaGetLastError());
+  return forces_impl(t, acc, s, nullptr, t->act_s.as<uint8_t>(), t->act_g.as<uint8_t>());
+}
+
+}  // namespace
+
+int nbody_assign_rungs(nbody_tree* t, const float* acc_dev, double eta, double dlna, int rmax, int8_t* rung_dev,
+                       nbody_stream_t stream) {
+  if (!t || !acc_dev || !rung_dev || !(eta > 0.0) || !(dlna > 0.0) || rmax < 0 || rmax > 7) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double H0 = sqrt(8.0 * M_PI / 3.0);
+  std::vector<double> c(t->nbox);
+  for (int b = 0; b < t->nbox; b++) c[b] = (dlna * dlna) / ((eta * eta) * (H0 * H0) * t->h_eps[b]);
+  NB_CU(t->rungc.ensure(8 * (int64_t)t->nbox));
+  NB_CU(cudaMemcpyAsync(t->rungc.p, c.data(), 8 * t->nbox, cudaMemcpyHostToDevice, s));
+  rung_kernel<<<gridn(t->n, 256), 256, 0, s>>>(t->n, acc_dev, t->box_of.as<uint16_t>(), t->rungc.as<double>(), rmax,
+                                               rung_dev);
+  t->launches += 1;
+  nb_launch_counter += 1;
+  NB_CU(cudaGetLastError());
+  NB_CU(cudaStreamSynchronize(s));
+  return NBODY_OK;
+}
+
+int nbody_forces_active(nbody_tree* t, const int8_t* rung_dev, int rmin, float* acc_dev, nbody_stream_t stream) {
+  if (!t || !rung_dev || !acc_dev || rmin < 0) return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long l0 = nb_launch_counter;
+  int rc = forces_active_impl(t, rung_dev, rmin, acc_dev, s);
+  t->launches += nb_launch_counter - l0;
+  if (rc) return rc;
+  if (t->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  return read_status(t, s);
+}
+
+int nbody_kdk_multistep(nbody_tree* t, double* pos_dev, float* mom_dev, float* acc_dev, const int8_t* rung_dev,
+                        double a0, double a1, int rmax, nbody_stream_t stream) {
+  if (!t || !pos_dev || !mom_dev || !acc_dev || !rung_dev || !(a0 > 0.0) || !(a1 > a0) || rmax < 0 || rmax > 7)
+    return NBODY_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  t->pos = pos_dev;
+  const double H0 = sqrt(8.0 * M_PI / 3.0);
+  const int T = 1 << rmax;
+  const double L = log(a1 / a0);
+  // expansion factor at half-tick j2 (tick j2 / 2), as the oracle forms it
+  auto at = [&](int j2) { return a0 * exp(L * j2 / (2 * T)); };
+  auto K = [&](double x, double y) { return 2.0 / H0 * (sqrt(y) - sqrt(x)); };
+  auto D = [&](double x, double y) { return 2.0 / H0 * (1.0 / sqrt(x) - 1.0 / sqrt(y)); };
+  const int64_t n = t->n, n3 = 3 * n;
+  const long long l0 = nb_launch_counter;
+  for (int k = 0; k < T; k++) {
+    // opening half kicks of the steps that start at tick k
+    RungKicks ko;
+    for (int r = 0; r < 8; r++) ko.f[r] = 0.f;
+    for (int r = 0; r <= rmax; r++) {
+      const int st = 1 << (rmax - r);
+      if (k % st == 0) ko.f[r] = (float)K(at(2 * k), at(2 * k + st));
+    }
+    kick_rungs_kernel<<<gridn(n, 256), 256, 0, s>>>(n, mom_dev, acc_dev, rung_dev, ko);
+    drift_kernel<<<gridn(n3, 256), 256, 0, s>>>(n3, pos_dev, mom_dev, D(at(2 * k), at(2 * k + 2)));
+    nb_launch_counter += 2;
+    NB_CU(cudaGetLastError());
+    int rc = build_impl(t, s);
+    if (rc) return rc;
+    // the steps that end at tick k + 1: rungs >= rmax - (trailing zeros of k + 1)
+    int tz = 0;
+    while (tz < rmax && ((k + 1) >> tz & 1) == 0) tz++;
+    const int rmin = rmax - tz;
+    if ((rc = forces_active_impl(t, rung_dev, rmin, acc_dev, s))) return rc;
+    RungKicks kc;
+    for (int r = 0; r < 8; r++) kc.f[r] = 0.f;
+    for (int r = rmin; r <= rmax; r++) {
+      const int st = 1 << (rmax - r);
+      kc.f[r] = (float)K(at(2 * (k + 1) - st), at(2 * (k + 1)));
+    }
+    kick_rungs_kernel<<<gridn(n, 256), 256, 0, s>>>(n, mom_dev, acc_dev, rung_dev, kc);
+    nb_launch_counter += 1;
+    NB_CU(cudaGetLastError());
+  }
+  t->launches += nb_launch_counter - l0;
+  if (t->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+  return read_status(t, s);
 }
 
 int nbody_forces_vjp(nbody_tree* t, const float* lam_dev, double* out_dev, nbody_stream_t stream) {

@@ -145,6 +145,11 @@ struct DevTree {
   const int4* gC;          // w2x, w2y, w2z, 0 (half widths, units 2^-23)
   const int4* gD;          // e2x, e2y, e2z, 0 (expansion point, units 2^-23)
   const int* sleaf;        // leaf cell of each sorted particle
+  // evaluation of a subset (block steps): per sorted particle and per group
+  // a nonzero byte marks the sinks whose accelerations are computed and
+  // written; nullptr = every particle
+  const uint8_t* sact;
+  const uint8_t* gact;
 };
 
 // kernels launched by this thread through the library (benchmark accounting)

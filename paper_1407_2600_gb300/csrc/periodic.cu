@@ -292,8 +292,10 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
   const T scale = (T)(1.0 / 8388608.0);
   const T fourpi3 = (T)(4.0 * M_PI / 3.0);
   for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+    if (tr.gact && !tr.gact[g]) continue;
     const int4 ga = tr.gA[g], gd = tr.gD[g];
     if (lane >= ga.y) continue;
+    if (tr.sact && !tr.sact[ga.x + lane]) continue;
     const T* Lr = a.lbuf + (int64_t)gd.w * a.lstride;
     T L[NL];
 #pragma unroll
@@ -325,8 +327,9 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
 // plain scatter when there are no periodic images
 template <typename T, typename O>
 __global__ void scatter_kernel(int64_t n, const uint32_t* __restrict__ perm, const T* __restrict__ accw,
-                               O* __restrict__ out) {
+                               const uint8_t* __restrict__ sact, O* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (sact && !sact[i]) continue;
     const uint32_t j = perm[i];
     out[j] = (O)accw[i];
     out[n + j] = (O)accw[n + i];
@@ -450,12 +453,12 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
                         double* out64, cudaStream_t s) {
   if (pe == 0) {
     if (out64) {
-      if (fp64) scatter_kernel<double, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out64);
-      else scatter_kernel<float, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out64);
+      if (fp64) scatter_kernel<double, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, tr.sact, out64);
+      else scatter_kernel<float, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, tr.sact, out64);
     } else if (fp64) {
-      scatter_kernel<double, float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, out);
+      scatter_kernel<double, float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, tr.sact, out);
     } else {
-      scatter_kernel<float, float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, out);
+      scatter_kernel<float, float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)accw, tr.sact, out);
     }
     nb_launch_counter += 1;
     return cudaGetLastError();

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     if (lane == 0) g = atomicAdd(w.group_ctr, 1);
     g = __shfl_sync(FULL, g, 0);
     if (g >= ngroup) break;
+    if (tr.gact && !tr.gact[g]) continue;  // no sink of this group is evaluated
     const int4 ga = tr.gA[g], gb = tr.gB[g], gc = tr.gC[g], gd = tr.gD[g];
     const int cnt = ga.y, box = ga.z;
     const T eps2 = w.eps2[box];
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       continue;
     }
     if (qn > 0) m2p_chunk(qn);
-    if (act) {
+    if (act && (!tr.sact || tr.sact[i])) {
       w.acc[i] = ax - cx;
       w.acc[tr.n + i] = ay - cy;
       w.acc[2 * tr.n + i] = az - cz;

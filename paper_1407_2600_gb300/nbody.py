@@ -39,7 +39,7 @@ EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_le
 
 # every symbol include/nbody.h declares
 SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces", "nbody_forces64",
-           "nbody_kdk_step", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
+           "nbody_kdk_step", "nbody_assign_rungs", "nbody_forces_active", "nbody_kdk_multistep", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_reserve", "nbody_autotune", "nbody_check",
            "nbody_tree_free",
            "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
@@ -115,6 +115,9 @@ def lib():
         L.nbody_forces.argtypes = [_vp, _vp, C.POINTER(Stats), _vp]
         L.nbody_forces64.argtypes = [_vp, _vp, _vp]
         L.nbody_kdk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp]
+        L.nbody_assign_rungs.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int, _vp, _vp]
+        L.nbody_forces_active.argtypes = [_vp, _vp, C.c_int, _vp, _vp]
+        L.nbody_kdk_multistep.argtypes = [_vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double, C.c_int, _vp]
         L.nbody_kdk_adjoint.argtypes = [_vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp, _vp]
         L.nbody_kdk_adjoint_acc.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp, _vp, _vp, _vp,
                                             _vp]
@@ -178,6 +181,20 @@ def nbody_forces64(tree: int, acc_dev: int, stream: int | None = None) -> int:
 def nbody_kdk_step(tree: int, pos_dev: int, mom_dev: int, acc_dev: int, a0: float, a1: float,
                    stream: int | None = None) -> int:
     return lib().nbody_kdk_step(tree, pos_dev, mom_dev, acc_dev, a0, a1, stream)
+
+
+def nbody_assign_rungs(tree: int, acc_dev: int, eta: float, dlna: float, rmax: int, rung_dev: int,
+                       stream: int | None = None) -> int:
+    return lib().nbody_assign_rungs(tree, acc_dev, eta, dlna, rmax, rung_dev, stream)
+
+
+def nbody_forces_active(tree: int, rung_dev: int, rmin: int, acc_dev: int, stream: int | None = None) -> int:
+    return lib().nbody_forces_active(tree, rung_dev, rmin, acc_dev, stream)
+
+
+def nbody_kdk_multistep(tree: int, pos_dev: int, mom_dev: int, acc_dev: int, rung_dev: int, a0: float, a1: float,
+                        rmax: int, stream: int | None = None) -> int:
+    return lib().nbody_kdk_multistep(tree, pos_dev, mom_dev, acc_dev, rung_dev, a0, a1, rmax, stream)
 
 
 def nbody_kdk_adjoint(tree: int, pos0_dev: int, mom0_dev: int, a0: float, a1: float,
@@ -306,6 +323,24 @@ class Tree:
     def kdk_step(self, mom, acc, a0, a1):
         _check(nbody_kdk_step(self.handle, self.pos.data_ptr(), mom.data_ptr(), acc.data_ptr(), a0, a1,
                               _stream()), "nbody_kdk_step")
+
+    def assign_rungs(self, acc, eta, dlna, rmax):
+        """(n,) int8 rungs from (3, n) FP32 accelerations (nbody_assign_rungs)."""
+        import torch
+        rung = torch.empty(self.n, dtype=torch.int8, device=self.pos.device)
+        _check(nbody_assign_rungs(self.handle, acc.data_ptr(), eta, dlna, rmax, rung.data_ptr(), _stream()),
+               "nbody_assign_rungs")
+        return rung
+
+    def forces_active(self, rung, rmin, acc):
+        """Accelerations of the particles with rung >= rmin written into acc."""
+        _check(nbody_forces_active(self.handle, rung.data_ptr(), rmin, acc.data_ptr(), _stream()),
+               "nbody_forces_active")
+        return acc
+
+    def kdk_multistep(self, mom, acc, rung, a0, a1, rmax):
+        _check(nbody_kdk_multistep(self.handle, self.pos.data_ptr(), mom.data_ptr(), acc.data_ptr(),
+                                   rung.data_ptr(), a0, a1, rmax, _stream()), "nbody_kdk_multistep")
 
     def forces_vjp(self, lam, out=None):
         """(d acc / d pos)^T lam for the tree as last built (lam: (3, n) float32)."""

@@ -52,6 +52,9 @@ def test_invalid_arguments_are_rejected_without_gpu_work():
     assert nb.nbody_kdk_adjoint_acc(None, 0, 0, 0, 0.1, 0.2, 0, 0, 0, 0) == nb.NBODY_EINVAL
     assert nb.nbody_reserve(None, 1000, 100) == nb.NBODY_EINVAL
     assert nb.nbody_autotune(None) == nb.NBODY_EINVAL
+    assert nb.nbody_assign_rungs(None, 0, 1.0, 0.1, 3, 0) == nb.NBODY_EINVAL
+    assert nb.nbody_forces_active(None, 0, 0, 0) == nb.NBODY_EINVAL
+    assert nb.nbody_kdk_multistep(None, 0, 0, 0, 0, 0.1, 0.2, 2) == nb.NBODY_EINVAL
     # flags: a walk variant beyond the table is rejected before any work
     p = nb.nbody_default_params()
     p.flags = nb.NBODY_FLAG_WALK_VARIANT(4)
