@@ -43,8 +43,10 @@ FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FM
 # DRAM traffic of one walk launch (packed variant, 8 warps x 2 blocks) from
 # the ncu capture summarised in profiles/walk_kernel_haloes96.md, scaled to
 # 2^21 particles; valid only while the walk's sources are unchanged since that
-# capture
-WALK_TRAFFIC = {"bytes": 106e6, "source_sha": "3b2f2b9ff6c487da"}
+# capture (the sources have since gained the active-group test of the block
+# steps, so the bench line reports the traffic as null and quotes the capture
+# separately)
+WALK_TRAFFIC = {"bytes": 106e6, "source_sha": "2e8f5d91dec55cc2"}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -446,6 +448,9 @@ def run_gpu(args, rank, world, local_rank):
                          "frac": achieved / peak,
                          "traffic": (WALK_TRAFFIC["bytes"] if args.ng == NG and
                                      walk_source_sha() == WALK_TRAFFIC["source_sha"] else None),
+                         "traffic_last_capture": {"bytes": WALK_TRAFFIC["bytes"],
+                                                  "source_sha": WALK_TRAFFIC["source_sha"],
+                                                  "current_sha": walk_source_sha()},
                          "kernel": "walk_kernel", "flops_per_launch": flops,
                          "peak_note": "FP32 non-tensor: 152 SMs x 128 lanes x 2 x 2070 MHz"},
             "cpu_baseline": base,

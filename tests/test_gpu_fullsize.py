@@ -118,3 +118,29 @@ def test_batched_uneven_boxes_vs_direct_and_tree(cuda):
         rt = np.linalg.norm(a - at, axis=1) / np.linalg.norm(at, axis=1)
         assert np.median(rd) <= 5e-3 and np.percentile(rd, 99) <= 3e-2, (b, np.median(rd), np.percentile(rd, 99))
         assert np.median(rt) <= 1e-5, (b, np.median(rt))
+
+
+def test_scale_setting_vs_oracle(cuda):
+    """The 512^3 scale workload's setting on a 64^3 box of the same spectrum
+    (P ~ k^-1.5, rms displacement 0.25 spacing): theta 0.7 with the opening
+    distance from the cell faces, hexadecapole, accepted cells of <= 8
+    particles summed directly, groups inside level-4 cells.  Sampled forces
+    match the oracle tree (median <= 1e-5, 99th percentile <= 1e-4) and the
+    direct Ewald sum (median <= 1e-3)."""
+    import paper_1407_2600_gb300.nbody as nb
+    q, psi = ics.zeldovich_particles(64, -1.5, 0.25, 3)
+    x = np.mod(q + psi, 1.0)
+    x[x >= 1.0] = 0.0
+    eps = 1.0 / (30 * 64)
+    a, _ = _forces(x, cuda, eps=eps, theta=0.7, order=4, n_direct=8, ewald_grid=5, flags=nb.NBODY_FLAG_MAC_EDGE)
+    assert np.isfinite(a).all()
+    tg = ics.random_targets(len(x), 1024, 3)
+    at = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.7, 4, n_direct=8, ewald=4, ew_grid=5, mac=1),
+                            targets=tg)
+    rt = _rel(a[tg], at)
+    assert np.median(rt) <= 1e-5 and np.percentile(rt, 99) <= 1e-4, (np.median(rt), np.percentile(rt, 99))
+    td = tg[:256]
+    ad = oracle.direct_forces(x, None, eps, targets=td, table_n1=128)
+    rd = _rel(a[td], ad)
+    print("scale setting at 64^3: median %.3e p99 %.3e vs direct Ewald" % (np.median(rd), np.percentile(rd, 99)))
+    assert np.median(rd) <= 1e-3
