@@ -14,7 +14,7 @@
  *
  * Conventions for every entry point:
  *   - Units: each box is the unit periodic cube; positions are FP64 in [0,1)
- *     (values outside are wrapped), G = 1, accelerations are in units of
+ *     (finite values outside are wrapped; NaN or Inf is NBODY_EINVAL), G = 1, accelerations are in units of
  *     G * (unit mass) / (box length)^2.  With masses summing to 1 per box the
  *     mean density is 1.
  *   - Layout: arrays are structure-of-arrays in the caller's particle order:
@@ -135,12 +135,16 @@ typedef struct nbody_tree nbody_tree;
  * gather into key order, oct-tree topology and key hash, sink groups, leaf
  * offsets and the cell moments (Sec. 2.1: keys imply the tree; cells carry
  * truncated multipole expansions).
- *   n        number of particles (>= 1, < 2^31)
+ *   n        number of particles (>= 1, < 2^30)
  *   pos_dev  3*n FP64 positions (SoA)
  *   mass_dev n FP32 masses, or NULL for equal masses 1/n
  *   tree     in: NULL or an existing handle to reuse (its buffers are kept
  *            when large enough); out: the handle
- * The tree keeps pointers to pos_dev and mass_dev.
+ * The tree keeps pointers to pos_dev and mass_dev.  A position or mass that
+ * is not finite (NaN, +-Inf) makes the build return NBODY_EINVAL (with
+ * NBODY_FLAG_ASYNC: the next nbody_check); a fresh handle is then not
+ * returned, a reused one holds a meaningless tree until the next build from
+ * finite positions.  Finite positions outside [0,1) are wrapped.
  */
 int nbody_build_tree(const nbody_params *params, int64_t n, const double *pos_dev,
                      const float *mass_dev, nbody_tree **tree, nbody_stream_t stream);
@@ -183,6 +187,9 @@ int nbody_forces64(nbody_tree *tree, double *acc_dev, nbody_stream_t stream);
  *   pos_dev  3*n FP64, updated in place (must be the tree's positions)
  *   mom_dev  3*n FP32 momenta, updated in place
  *   acc_dev  3*n FP32: in g(x0), out g(x1)
+ * A drifted position that is not finite (from a non-finite momentum or
+ * acceleration) makes the step's rebuild, and so the step, return
+ * NBODY_EINVAL.
  */
 int nbody_kdk_step(nbody_tree *tree, double *pos_dev, float *mom_dev, float *acc_dev, double a0,
                    double a1, nbody_stream_t stream);

@@ -14,7 +14,8 @@
 
 // launchers from the other translation units
 cudaError_t nb_gather(const double* pos, const float* mass, const uint32_t* perm, const uint16_t* box_of,
-                      const int64_t* off, int64_t n, double* spos, float* smass, uint16_t* sbox, cudaStream_t s);
+                      const int64_t* off, int64_t n, double* spos, float* smass, uint16_t* sbox, unsigned* status,
+                      cudaStream_t s);
 cudaError_t nb_count_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int n_leaf,
                            int lmax, int* ccount, int8_t* l0, cudaStream_t s);
 cudaError_t nb_cap_check(int* cnt, int cell_cap, int group_cap, unsigned* err, cudaStream_t s);
@@ -558,7 +559,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
                       &alt));
   if (alt != (np & 1)) return NBODY_ECUDA;
   NB_CU(nb_gather(t->pos, t->mass, t->vals.as<uint32_t>(), t->box_of.as<uint16_t>(), t->off.as<int64_t>(), n,
-                  t->spos.as<double>(), t->smass.as<float>(), t->sbox.as<uint16_t>(), s));
+                  t->spos.as<double>(), t->smass.as<float>(), t->sbox.as<uint16_t>(), t->status.as<unsigned>(), s));
   if (timed) NB_CU(cudaEventRecord(be[1], s));
   // A4 tree: cells per particle, scan, groups flags + scan, counts
   NB_CU(nb_count_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), t->off.as<int64_t>(), n, p.n_leaf, p.lmax,

@@ -356,24 +356,33 @@ __global__ void cap_check_kernel(int* __restrict__ cnt, int cell_cap, int group_
   }
 }
 
+// A position or mass that is not finite sets NB_ST_BADINPUT in `status` (the
+// build then returns NBODY_EINVAL); the rest of the build runs on, since every
+// index it derives from a position goes through the wrapped key.
 __global__ void gather_kernel(const double* __restrict__ pos, const float* __restrict__ mass,
                               const uint32_t* __restrict__ perm, const uint16_t* __restrict__ sbox,
                               const int64_t* __restrict__ off, int64_t n, double* __restrict__ spos,
-                              float* __restrict__ smass) {
+                              float* __restrict__ smass, unsigned* __restrict__ status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     uint32_t j = perm[i];
+    bool bad = false;
     for (int d = 0; d < 3; d++) {
       double x = pos[d * n + j];
+      bad |= !isfinite(x);
       x -= floor(x);  // wrap into [0,1)
       if (x >= 1.0) x = 0.0;
       spos[d * n + i] = x;
     }
-    if (mass) smass[i] = mass[j];
-    else {
+    if (mass) {
+      const float m = mass[j];
+      bad |= !isfinite(m);
+      smass[i] = m;
+    } else {
       int b = sbox[i];
       smass[i] = (float)(1.0 / (double)(off[b + 1] - off[b]));
     }
+    if (bad) atomicOr(status, NB_ST_BADINPUT);
   }
 }
 
@@ -396,9 +405,9 @@ int gridn(int64_t n, int threads) {
 // ---- host launchers --------------------------------------------------------
 cudaError_t nb_gather(const double* pos, const float* mass, const uint32_t* perm, const uint16_t* box_of,
                       const int64_t* off, int64_t n, double* spos, float* smass, uint16_t* sbox,
-                      cudaStream_t s) {
+                      unsigned* status, cudaStream_t s) {
   sbox_kernel<<<gridn(n, 256), 256, 0, s>>>(perm, box_of, n, sbox);
-  gather_kernel<<<gridn(n, 256), 256, 0, s>>>(pos, mass, perm, sbox, off, n, spos, smass);
+  gather_kernel<<<gridn(n, 256), 256, 0, s>>>(pos, mass, perm, sbox, off, n, spos, smass, status);
   nb_launch_counter += 2;
   return cudaGetLastError();
 }

@@ -378,3 +378,58 @@ def test_degenerate_inputs_vs_oracle(cuda, case):
         # no cell is expanded: what remains is the image field's order-4
         # local expansion (about 1e-5 of a unit mass's force at unit distance)
         assert np.abs(a - ad).max() <= 1e-4 * scale + 1e-5
+
+
+def test_non_finite_inputs_are_rejected(cuda):
+    """A NaN or infinite position or mass makes the build return
+    NBODY_EINVAL (no handle for a fresh tree), also through a rebuild of an
+    existing tree, through nbody_check with NBODY_FLAG_ASYNC, and through a
+    KDK step whose momenta are not finite; the same tree then rebuilds from
+    finite positions and gives the forces of a fresh tree."""
+    import torch
+    nb = _nb()
+    x, eps = ics.config_small(2)
+    good = _pos(x, cuda)
+    prm = nb.params(eps=eps, theta=0.5, order=4)
+    for bad_value in (float("nan"), float("inf"), -float("inf")):
+        bad = good.clone()
+        bad[1, 77] = bad_value
+        with pytest.raises(nb.NbodyError) as ei:
+            nb.Tree(prm, bad)
+        assert ei.value.code == nb.NBODY_EINVAL
+    mass = torch.full((len(x),), 1.0 / len(x), dtype=torch.float32, device=cuda)
+    mass[5] = float("nan")
+    with pytest.raises(nb.NbodyError) as ei:
+        nb.Tree(prm, good, mass=mass)
+    assert ei.value.code == nb.NBODY_EINVAL
+    # rebuild of an existing tree, then recovery
+    tree = nb.Tree(prm, good)
+    ref = tree.forces()
+    bad = good.clone()
+    bad[0, 3] = float("nan")
+    tree.pos = bad
+    with pytest.raises(nb.NbodyError) as ei:
+        tree.rebuild()
+    assert ei.value.code == nb.NBODY_EINVAL
+    tree.pos = good
+    tree.rebuild()
+    assert torch.equal(tree.forces(), ref)
+    # a KDK step with a non-finite momentum
+    pos = good.clone()
+    tree.pos = pos
+    tree.rebuild()
+    acc = tree.forces()
+    mom = torch.zeros((3, len(x)), dtype=torch.float32, device=cuda)
+    mom[2, 9] = float("inf")
+    with pytest.raises(nb.NbodyError) as ei:
+        tree.kdk_step(mom, acc, 0.05, 0.06)
+    assert ei.value.code == nb.NBODY_EINVAL
+    tree.close()
+    # deferred status
+    tree = nb.Tree(nb.params(eps=eps, theta=0.5, order=4, flags=nb.NBODY_FLAG_ASYNC), bad)
+    torch.cuda.synchronize()
+    with pytest.raises(nb.NbodyError) as ei:
+        tree.check()
+    assert ei.value.code == nb.NBODY_EINVAL
+    tree.check()  # the read clears the status
+    tree.close()
