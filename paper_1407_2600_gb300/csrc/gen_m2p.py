@@ -393,6 +393,15 @@ def _pdiff(a, d):
     return {k: v for k, v in out.items() if v != 0}
 
 
+def bg_flop_count(l):
+    """Flops (FMA = 2, multiply = 1, rsqrt = 1) of the order-l background term
+    as emitted by emit_bg; the walk adds it to an M2P whose scaled separation
+    it reuses, so these are the term's whole extra cost per M2P."""
+    import re
+    body = "\n".join(emit_bg(l).split("\n")[2:-1])
+    return 2 * body.count("fma(") + len(re.findall(r" \* ", body)) + body.count("nbody_rsqrt(")
+
+
 def bg_order(p):
     """order of the background term added at expansion order p (0 = none)"""
     return {0: 4, 2: 4, 4: 6}.get(p, 0)

@@ -120,23 +120,29 @@ def test_batched_uneven_boxes_vs_direct_and_tree(cuda):
         assert np.median(rt) <= 1e-5, (b, np.median(rt))
 
 
+def _scale_flags(nb):
+    """The scale workload's flags: face-distance opening test and the
+    uniform-background terms."""
+    return nb.NBODY_FLAG_MAC_EDGE | nb.NBODY_FLAG_BACKGROUND
+
+
 def test_scale_setting_vs_oracle(cuda):
     """The 512^3 scale workload's setting on a 64^3 box of the same spectrum
     (P ~ k^-1.5, rms displacement 0.25 spacing): theta 0.7 with the opening
-    distance from the cell faces, hexadecapole, accepted cells of <= 8
-    particles summed directly, groups inside level-4 cells.  Sampled forces
-    match the oracle tree (median <= 1e-5, 99th percentile <= 1e-4) and the
-    direct Ewald sum (median <= 1e-3)."""
+    distance from the cell faces and the uniform-background terms,
+    hexadecapole, accepted cells of <= 8 particles summed directly, groups
+    inside level-4 cells.  Sampled forces match the oracle tree (median <=
+    1e-5, 99th percentile <= 1e-4) and the direct Ewald sum (median <= 1e-3)."""
     import paper_1407_2600_gb300.nbody as nb
     q, psi = ics.zeldovich_particles(64, -1.5, 0.25, 3)
     x = np.mod(q + psi, 1.0)
     x[x >= 1.0] = 0.0
     eps = 1.0 / (30 * 64)
-    a, _ = _forces(x, cuda, eps=eps, theta=0.7, order=4, n_direct=8, ewald_grid=5, flags=nb.NBODY_FLAG_MAC_EDGE)
+    a, _ = _forces(x, cuda, eps=eps, theta=0.7, order=4, n_direct=8, ewald_grid=5, flags=_scale_flags(nb))
     assert np.isfinite(a).all()
     tg = ics.random_targets(len(x), 1024, 3)
-    at = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.7, 4, n_direct=8, ewald=4, ew_grid=5, mac=1),
-                            targets=tg)
+    at = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.7, 4, n_direct=8, ewald=4, ew_grid=5, mac=1,
+                                                        bg=6), targets=tg)
     rt = _rel(a[tg], at)
     assert np.median(rt) <= 1e-5 and np.percentile(rt, 99) <= 1e-4, (np.median(rt), np.percentile(rt, 99))
     td = tg[:256]
@@ -160,12 +166,12 @@ def _host_mem_available_gb():
 def test_scale_workload_fullsize_vs_oracle_tree(cuda):
     """The 512^3 scale workload at full size (134,217,728 particles, the
     numpy generator's realisation of its spectrum so that both sides see the
-    same input) in the benchmark's setting: theta 0.7 from the cell faces,
-    hexadecapole, accepted cells of <= 8 particles summed directly, groups
-    inside level-4 cells.  256 sampled forces against the oracle tree (same
-    discrete decisions; median <= 1e-5, 99th percentile <= 1e-4).  The
-    oracle's tree of all particles needs about 25 GB of host memory and a
-    minute or two of the host cores."""
+    same input) in the benchmark's setting: theta 0.7 from the cell faces
+    with the uniform-background terms, hexadecapole, accepted cells of <= 8
+    particles summed directly, groups inside level-4 cells.  256 sampled
+    forces against the oracle tree (same discrete decisions; median <= 1e-5,
+    99th percentile <= 1e-4).  The oracle's tree of all particles needs
+    about 25 GB of host memory and a minute or two of the host cores."""
     if _host_mem_available_gb() < 48.0:
         pytest.skip("the oracle tree of 512^3 particles needs about 25 GB of host memory")
     import torch
@@ -178,7 +184,7 @@ def test_scale_workload_fullsize_vs_oracle_tree(cuda):
     eps = 1.0 / (30 * ng)
     pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=cuda)
     prm = nb.params(eps=eps, theta=0.7, order=4, n_direct=8, ewald_grid=5,
-                    flags=nb.NBODY_FLAG_ASYNC | nb.NBODY_FLAG_MAC_EDGE)
+                    flags=nb.NBODY_FLAG_ASYNC | _scale_flags(nb))
     tree = nb.Tree(prm, pos)
     acc = tree.forces()
     torch.cuda.synchronize()
@@ -188,8 +194,8 @@ def test_scale_workload_fullsize_vs_oracle_tree(cuda):
     tree.close()
     del pos, acc
     assert np.isfinite(a).all()
-    at = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.7, 4, n_direct=8, ewald=4, ew_grid=5, mac=1),
-                            targets=tg)
+    at = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.7, 4, n_direct=8, ewald=4, ew_grid=5, mac=1,
+                                                        bg=6), targets=tg)
     rt = _rel(a, at)
     print("512^3 scale setting: GPU vs oracle tree median %.3e p99 %.3e" % (np.median(rt), np.percentile(rt, 99)))
     assert np.median(rt) <= 1e-5 and np.percentile(rt, 99) <= 1e-4, (np.median(rt), np.percentile(rt, 99))
