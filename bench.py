@@ -424,6 +424,7 @@ def run_gpu(args, rank, world, local_rank):
     batched = None
     if args.batched:
         batched = run_batched(dev, max(2, args.steps // 2))
+    block = run_block_steps(dev, x, p, eps, args) if args.block_steps else None
     config3 = run_config3(dev) if args.config3 else None
 
     base = None
@@ -476,11 +477,81 @@ def run_gpu(args, rank, world, local_rank):
             "adjoint": adj,
             "fp64_tree": fp64,
             "batched": batched,
+            "block_steps": block,
             "config3": config3,
         }
         print(json.dumps(line), flush=True)
     tree.close()
     return 0
+
+
+def run_block_steps(dev, x, p, eps, args, eta: float = 1.0, rmax: int = 3):
+    """Block steps (hierarchical KDK) on the benchmark workload: rungs from
+    the accelerations at a = A_START (the smallest r <= rmax with
+    4^r >= |g| dlna^2 / (eta^2 H0^2 eps)), then one global step of dlna =
+    DLNA in 2^rmax ticks: every tick drifts all particles and rebuilds the
+    tree, and the walk evaluates only the groups holding a particle whose
+    step ends.  Timed against the 2^rmax global KDK steps that would give
+    every particle the finest rung's step, from the same state.  Returns a
+    dict, or {"error": ...} (this is a side measurement: it must not cost the
+    benchmark line)."""
+    try:
+        import torch
+        import paper_1407_2600_gb300.nbody as nb
+        pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
+        mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
+        prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=args.n_direct, ewald_grid=args.ewald_grid,
+                        flags=nb.NBODY_FLAG_ASYNC)
+        tree = nb.Tree(prm, pos)
+        acc = tree.forces()
+        a0, a1 = A_START, A_START * math.exp(DLNA)
+        rung = tree.assign_rungs(acc, eta, DLNA, rmax)
+        counts = torch.bincount(rung.long(), minlength=rmax + 1).cpu().tolist()
+        n = len(x)
+        evals = sum(c << r for r, c in enumerate(counts))  # force evaluations per global step
+        x0, p0, g0 = pos.clone(), mom.clone(), acc.clone()
+
+        def restore():
+            pos.copy_(x0)
+            mom.copy_(p0)
+            acc.copy_(g0)
+            torch.cuda.synchronize()
+
+        stream = torch.cuda.current_stream()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        tree.kdk_multistep(mom, acc, rung, a0, a1, rmax)  # warm-up
+        torch.cuda.synchronize()
+        tree.check()
+        ms_block = []
+        for _ in range(3):
+            restore()
+            e[0].record(stream)
+            tree.kdk_multistep(mom, acc, rung, a0, a1, rmax)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            tree.check()
+            ms_block.append(e[0].elapsed_time(e[1]))
+        restore()
+        T = 1 << rmax
+        a_list = [a0 * math.exp(DLNA * k / T) for k in range(T + 1)]
+        e[2].record(stream)
+        for k in range(T):
+            tree.kdk_step(mom, acc, a_list[k], a_list[k + 1])
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        tree.check()
+        ms_fine = e[2].elapsed_time(e[3])
+        tree.close()
+        ms = float(np.median(ms_block))
+        return {"workload": "benchmark workload at a=%.2f, one global step dln a = %.2f in %d ticks" % (a0, DLNA, T),
+                "eta": eta, "rmax": rmax, "rung_counts": counts,
+                "force_evals_per_global_step": evals, "force_evals_all_finest": n * T,
+                "ms_block_step": ms, "ms_all_finest_steps": ms_fine,
+                "speedup_vs_all_finest": ms_fine / ms,
+                "force_updates_per_s": evals / (ms * 1e-3),
+                "note": "every tick rebuilds the whole tree; only groups with an ending step are walked"}
+    except Exception as exc:  # a side measurement never costs the benchmark line
+        return {"error": "%s: %s" % (type(exc).__name__, exc)}
 
 
 def run_config3(dev, ng: int = 512):
@@ -682,6 +753,8 @@ def main():
                     help="also time ten KDK steps of the 512^3 scale workload (about a minute)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the 96-box batched workload")
+    ap.add_argument("--block-steps", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time one global step of block (hierarchical) steps on the benchmark workload")
     ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")
     ap.add_argument("--ng", type=int, default=NG, help="particles per axis (128 = the benchmark workload)")
     ap.add_argument("--n-direct", type=int, default=N_DIRECT,
