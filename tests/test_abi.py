@@ -107,3 +107,51 @@ def test_reduced_m2p_matches_oracle_dtensor_form():
         acc = sum(R * F[j + 1] * S[j] + F[j] * Gd[j] for j in range(p + 1))
         ref = O.m2p(M, p, R, eps)
         assert np.abs(acc - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_more_invalid_arguments_are_rejected_without_gpu_work():
+    """Host-side fault injection: out-of-range parameters, malformed box
+    offsets, sizes beyond the limits and NULL handles or pointers are
+    rejected with NBODY_EINVAL (NBODY_ERANGE for the allocation-free sort's
+    size limit) before any CUDA call, so these run on a machine without a GPU.
+    The device address 1 stands in for a buffer that is never touched."""
+    import paper_1407_2600_gb300.nbody as nb
+    EINVAL = nb.NBODY_EINVAL
+    # every parameter outside its documented range
+    bad = [("theta", 0.0), ("theta", -0.5), ("eps", -1e-3), ("order", 5), ("order", -1), ("n_leaf", 0),
+           ("n_leaf", 65), ("n_group", 0), ("n_group", 33), ("n_direct", -1), ("lmax", 1), ("lmax", 22),
+           ("ewald_order", 6), ("ewald_grid", 3), ("ewald_grid", 9), ("ewald_level", 0), ("precision", 2)]
+    for name, value in bad:
+        p = nb.nbody_default_params()
+        setattr(p, name, value)
+        rc, h = nb.nbody_build_tree(p, 10, 1, None)
+        assert rc == EINVAL and not h, (name, value, rc)
+    p = nb.nbody_default_params()
+    # sizes: no particles, or at least 2^30 of them
+    for n in (0, -5, 1 << 30):
+        rc, h = nb.nbody_build_tree(p, n, 1, None)
+        assert rc == EINVAL and not h, n
+    # box offsets: an empty box, a first offset other than 0, no box, a
+    # non-positive softening
+    for off, eps in (([0, 5, 5], None), ([1, 5, 9], None), ([0], None), ([0, 4, 8], [1e-3, 0.0])):
+        rc, h = nb.nbody_build_tree_batched(p, off, eps, 1, None)
+        assert rc == EINVAL and not h, (off, eps)
+    rc, h = nb.nbody_build_tree_batched(p, [0, 4, 8], None, 0, None)  # NULL positions
+    assert rc == EINVAL and not h
+    # NULL tree handles
+    assert nb.nbody_tree_count(None, 0) == EINVAL
+    assert nb.nbody_tree_export(None, 0, 1) == EINVAL
+    assert nb.nbody_check(None) == EINVAL
+    assert nb.nbody_forces_vjp(None, 1, 1) == EINVAL
+    assert nb.nbody_kdk_step(None, 1, 1, 1, 0.1, 0.2) == EINVAL
+    assert nb.nbody_kdk_adjoint(None, 1, 1, 0.1, 0.2, 1, 1, 1, 1) == EINVAL
+    assert nb.nbody_timing_read(None, nb.Timing(), 0) == EINVAL
+    assert nb.nbody_tree_lookup(None, 1, 1, 1) == EINVAL
+    nb.nbody_tree_free(None)  # freeing nothing is allowed
+    # the CIC loss: grid sizes outside 2..1024, no particles, NULL pointers
+    for n, ng, pos in ((10, 1, 1), (10, 1025, 1), (0, 8, 1), (10, 8, 0)):
+        assert nb.nbody_cic_loss(pos, None, n, ng, 1, 1, None) == EINVAL, (n, ng, pos)
+    # the allocation-free sort: no particles or NULL outputs, and its size limit
+    assert nb.nbody_sort_keys_noalloc(1, 0, 1, 1) == EINVAL
+    assert nb.nbody_sort_keys_noalloc(1, 16, 0, 1) == EINVAL
+    assert nb.nbody_sort_keys_noalloc(1, (1 << 20) + 1, 1, 1) == nb.NBODY_ERANGE
