@@ -68,6 +68,53 @@ def zeldovich_particles(ng: int, n_index: float, rms_spacing: float, seed: int):
     return lattice(ng), zeldovich_displacement(ng, n_index, rms_spacing, seed)
 
 
+def lpt2_displacement(psi1: np.ndarray, ng: int) -> np.ndarray:
+    """Second-order Lagrangian displacement of a first-order field.
+
+    psi1 (ng^3, 3) on the lattice of `lattice` is the Zel'dovich displacement
+    -grad phi1.  Returns psi2 = grad phi2 (ng^3, 3), where phi2 solves
+    lap phi2 = sum over i < j of (phi1_ii phi1_jj - phi1_ij^2), all derivatives
+    spectral (first derivatives without the Nyquist component; the Nyquist
+    planes of phi2 zeroed, as those of the first-order field are).  In an
+    Einstein-de Sitter background the second-order positions and momenta
+    (p = a^2 dx/dt) at linear growth factor D (D = 1 where psi1 is given) are
+    x = q + D psi1 - (3/7) D^2 psi2 and p = H0 a^(1/2) D (psi1 - (6/7) D psi2);
+    see lpt2_state."""
+    k1 = np.fft.fftfreq(ng, d=1.0 / ng) * 2.0 * math.pi
+    kd = k1.copy()
+    if ng % 2 == 0:
+        kd[ng // 2] = 0.0
+    K = np.meshgrid(kd, kd, kd, indexing="ij")
+    P = [np.fft.fftn(psi1[:, d].reshape(ng, ng, ng)) for d in range(3)]
+    # phi1_ij = -d_j psi1_i, symmetrised (psi1 is a gradient field)
+    phi = {}
+    for i in range(3):
+        for j in range(i, 3):
+            phi[i, j] = np.real(np.fft.ifftn(-0.5j * (K[j] * P[i] + K[i] * P[j])))
+    src = (phi[0, 0] * phi[1, 1] + phi[0, 0] * phi[2, 2] + phi[1, 1] * phi[2, 2]
+           - phi[0, 1] ** 2 - phi[0, 2] ** 2 - phi[1, 2] ** 2)
+    Q = np.meshgrid(k1, k1, k1, indexing="ij")
+    k2 = Q[0] ** 2 + Q[1] ** 2 + Q[2] ** 2
+    phi2 = -np.fft.fftn(src) / np.where(k2 > 0, k2, 1.0)
+    phi2[k2 == 0] = 0.0
+    if ng % 2 == 0:  # Nyquist planes zeroed, as in the first-order field
+        phi2[ng // 2, :, :] = 0.0
+        phi2[:, ng // 2, :] = 0.0
+        phi2[:, :, ng // 2] = 0.0
+    return np.stack([np.real(np.fft.ifftn(1j * K[d] * phi2)).ravel() for d in range(3)], axis=1)
+
+
+def lpt2_state(q: np.ndarray, psi1: np.ndarray, psi2: np.ndarray, growth: float, a: float):
+    """Second-order positions (wrapped to [0,1)) and momenta p = a^2 dx/dt at
+    expansion factor a with linear growth factor `growth` in Einstein-de
+    Sitter (D proportional to a, second-order growth -(3/7) D^2)."""
+    h0 = math.sqrt(8.0 * math.pi / 3.0)
+    x = np.mod(q + growth * psi1 - (3.0 / 7.0) * growth ** 2 * psi2, 1.0)
+    x[x >= 1.0] = 0.0
+    p = h0 * math.sqrt(a) * growth * (psi1 - (6.0 / 7.0) * growth * psi2)
+    return x, p
+
+
 def nfw_radii(rng, count: int, c: float, r200: float) -> np.ndarray:
     """Radii drawn from the NFW enclosed-mass profile truncated at r200."""
     def mu(x):

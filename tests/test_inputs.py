@@ -98,3 +98,70 @@ def test_batched_boxes_layout_and_growing_mode():
         psi -= np.round(psi)  # displacements are far below half a box
         assert np.allclose(pb, h0 * math.sqrt(a) * psi, rtol=1e-12, atol=1e-15)
         assert abs(math.sqrt(np.mean(np.sum(psi * psi, axis=1))) - 0.25 / ng) <= 1e-9 / ng
+
+
+def _crossed_waves(ng, A, B):
+    q = ics.lattice(ng)
+    k = 2 * math.pi
+    psi1 = np.stack([A * np.sin(k * q[:, 0]), B * np.sin(k * q[:, 1]), 0 * q[:, 2]], axis=1)
+    return q, psi1
+
+
+def test_lpt2_crossed_waves_closed_form():
+    """psi1 = (A sin kx, B sin ky, 0): phi1 = (A cos kx + B cos ky)/k, the
+    source phi1_xx phi1_yy = A B k^2 cos kx cos ky, phi2 = -(A B / 2) cos kx
+    cos ky and psi2 = (A B k / 2)(sin kx cos ky, cos kx sin ky, 0)."""
+    ng, A, B = 16, 0.02, 0.013
+    q, psi1 = _crossed_waves(ng, A, B)
+    psi2 = ics.lpt2_displacement(psi1, ng)
+    k = 2 * math.pi
+    ref = np.stack([A * B * k / 2 * np.sin(k * q[:, 0]) * np.cos(k * q[:, 1]),
+                    A * B * k / 2 * np.cos(k * q[:, 0]) * np.sin(k * q[:, 1]), 0 * q[:, 2]], axis=1)
+    assert np.abs(psi2 - ref).max() <= 1e-12 * np.abs(ref).max()
+    # one plane wave has no second-order displacement
+    assert np.abs(ics.lpt2_displacement(_crossed_waves(ng, A, 0.0)[1], ng)).max() <= 1e-18
+
+
+def test_lpt2_of_a_random_field_is_curl_free():
+    ng = 24
+    psi1 = ics.zeldovich_displacement(ng, -2.0, 0.25, 9)
+    psi2 = ics.lpt2_displacement(psi1, ng)
+    assert np.abs(psi2).max() > 0
+    f = [np.fft.fftn(psi2[:, d].reshape(ng, ng, ng)) for d in range(3)]
+    k = np.fft.fftfreq(ng, d=1.0 / ng)
+    KX, KY, KZ = np.meshgrid(k, k, k, indexing="ij")
+    curl = [KY * f[2] - KZ * f[1], KZ * f[0] - KX * f[2], KX * f[1] - KY * f[0]]
+    scale = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2) * np.sqrt(sum(np.abs(c) ** 2 for c in f))
+    assert max(np.abs(c).max() for c in curl) <= 1e-10 * scale.max()
+
+
+def test_lpt2_follows_the_dynamics():
+    """Sign and the 3/7 of the second-order term, by the oracle's own
+    dynamics: crossed waves started from second-order positions and momenta
+    at a = 0.5 and stepped to a = 1 (oracle tree forces, KDK) stay on the
+    second-order prediction far more closely than on the first-order one
+    (the remaining difference is third order, lattice discreteness and the
+    integrator's error)."""
+    import oracle as O
+    ng, A, B = 16, 0.02, 0.013
+    q, psi1 = _crossed_waves(ng, A, B)
+    psi2 = ics.lpt2_displacement(psi1, ng)
+    ai, af, S = 0.5, 1.0, 6
+    x, p = ics.lpt2_state(q, psi1, psi2, ai, ai)  # D = a
+    op = O.tree_params(1e-4, 0.5, 4, ewald=4, ew_grid=4)
+    force = lambda xx: O.tree_forces(xx, None, op)
+    g = force(x)
+    a_list = [ai * (af / ai) ** (j / S) for j in range(S + 1)]
+    for j in range(S):
+        x, p, g = O.kdk_step(x, p, g, a_list[j], a_list[j + 1], force)
+
+    def rms_off(pred):
+        d = x - np.mod(pred, 1.0)
+        d -= np.round(d)
+        return math.sqrt(np.mean(np.sum(d * d, axis=1)))
+
+    e1 = rms_off(q + af * psi1)
+    e2 = rms_off(q + af * psi1 - 3.0 / 7.0 * af ** 2 * psi2)
+    assert e2 <= 0.1 * e1, (e1, e2)
+    # the wrong sign of the second-order term does worse than first order
+    assert rms_off(q + af * psi1 + 3.0 / 7.0 * af ** 2 * psi2) > e1
