@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <random>
+#include <string>
 #define __device__
 #define __forceinline__ inline
 #define __restrict__
@@ -246,7 +247,75 @@ void run_m2p2() {
   }
 }
 
-int main() {
+// uniform-background terms: the Hessian-vector products against central
+// differences of the forward terms, and the packed FP32 terms bit for bit per
+// lane against the scalar FP32 terms
+template <int L> struct BG;
+#define BGD(L)                                                                                       \
+  template <> struct BG<L> {                                                                          \
+    template <typename T> static void f(T q, T x, T y, T z, T& ax, T& ay, T& az) {                    \
+      cube_bg_l##L<T>(q, x, y, z, ax, ay, az);                                                        \
+    }                                                                                                 \
+    static void f2(float2 q, float2 x, float2 y, float2 z, float2& ax, float2& ay, float2& az) {      \
+      cube_bg2_l##L(q, x, y, z, ax, ay, az);                                                          \
+    }                                                                                                 \
+    static void hvp(double q, double x, double y, double z, double lx, double ly, double lz, double& ox, \
+                    double& oy, double& oz) {                                                         \
+      cube_bg_hvp_l##L<double>(q, x, y, z, lx, ly, lz, ox, oy, oz);                                   \
+    }                                                                                                 \
+  };
+BGD(4)
+BGD(6)
+
+template <int L> void run_bg() {
+  double R[3];
+  do {  // outside the unit cube's circumscribed sphere, where the series holds
+    for (int d = 0; d < 3; d++) R[d] = 3 * U();
+  } while (R[0] * R[0] + R[1] * R[1] + R[2] * R[2] < 1.0);
+  const double q = 1.0 + 0.5 * U(), lam[3] = {U(), U(), U()}, h = 1e-6;
+  double o[3] = {0, 0, 0}, ap[3] = {0, 0, 0}, am[3] = {0, 0, 0};
+  BG<L>::hvp(q, R[0], R[1], R[2], lam[0], lam[1], lam[2], o[0], o[1], o[2]);
+  BG<L>::template f<double>(q, R[0] + h * lam[0], R[1] + h * lam[1], R[2] + h * lam[2], ap[0], ap[1], ap[2]);
+  BG<L>::template f<double>(q, R[0] - h * lam[0], R[1] - h * lam[1], R[2] - h * lam[2], am[0], am[1], am[2]);
+  const double scale = std::fabs(o[0]) + std::fabs(o[1]) + std::fabs(o[2]);
+  for (int k = 0; k < 3; k++) check(L == 4 ? "bg_hvp_l4" : "bg_hvp_l6", o[k], (ap[k] - am[k]) / (2 * h), scale, 1e-6);
+  float x[2], y[2], z[2], qq[2] = {(float)(1.0 + 0.5 * U()), (float)(1.0 + 0.5 * U())};
+  for (int c = 0; c < 2; c++) {
+    do {
+      x[c] = (float)(3 * U());
+      y[c] = (float)(3 * U());
+      z[c] = (float)(3 * U());
+    } while (x[c] * x[c] + y[c] * y[c] + z[c] * z[c] < 1.0f);
+  }
+  float a[2][3] = {{0.25f, -0.5f, 0.125f}, {0.25f, -0.5f, 0.125f}};
+  for (int c = 0; c < 2; c++) BG<L>::template f<float>(qq[c], x[c], y[c], z[c], a[c][0], a[c][1], a[c][2]);
+  float2 ax = make_float2(0.25f, 0.25f), ay = make_float2(-0.5f, -0.5f), az = make_float2(0.125f, 0.125f);
+  BG<L>::f2(make_float2(qq[0], qq[1]), make_float2(x[0], x[1]), make_float2(y[0], y[1]), make_float2(z[0], z[1]),
+            ax, ay, az);
+  if (ax.x != a[0][0] || ay.x != a[0][1] || az.x != a[0][2] || ax.y != a[1][0] || ay.y != a[1][1] ||
+      az.y != a[1][2]) {
+    std::printf("FAIL cube_bg2_l%d differs from cube_bg_l%d\n", L, L);
+    std::exit(1);
+  }
+}
+
+int main(int argc, char** argv) {
+  if (argc > 1 && std::string(argv[1]) == "bg") {
+    // the background terms of a unit cube of unit density at the points read
+    // from stdin ("x y z" per line): order-4 and order-6 accelerations
+    double x, y, z;
+    while (std::scanf("%lf %lf %lf", &x, &y, &z) == 3) {
+      double a4[3] = {0, 0, 0}, a6[3] = {0, 0, 0};
+      cube_bg_l4<double>(1.0, x, y, z, a4[0], a4[1], a4[2]);
+      cube_bg_l6<double>(1.0, x, y, z, a6[0], a6[1], a6[2]);
+      std::printf("%.17g %.17g %.17g %.17g %.17g %.17g\n", a4[0], a4[1], a4[2], a6[0], a6[1], a6[2]);
+    }
+    return 0;
+  }
+  for (int rep = 0; rep < 50; rep++) {
+    run_bg<4>();
+    run_bg<6>();
+  }
   for (int rep = 0; rep < 50; rep++) {
     run_m2p2<0>(); run_m2p2<1>(); run_m2p2<2>(); run_m2p2<3>(); run_m2p2<4>();
   }
