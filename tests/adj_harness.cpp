@@ -299,7 +299,47 @@ template <int L> void run_bg() {
   }
 }
 
+// one case from stdin for a comparison with the oracle: "p k", then k lines
+// "m dx dy dz" (particles relative to the cell centre), then "Rx Ry Rz eps
+// sx sy sz"; prints the moments from p2m_acc, the acceleration of m2p on the
+// reduced moments at R, and the moments shifted by m2m_acc with s = c_child
+// - c_parent, one value per line
+template <int P> void run_io() {
+  const int NM = (P + 1) * (P + 2) * (P + 3) / 6;
+  int k = 0;
+  if (std::scanf("%d", &k) != 1) std::exit(2);
+  double M[NM], Mp[NM], B[K<P>::NB];
+  for (int t = 0; t < NM; t++) M[t] = Mp[t] = 0.0;
+  for (int i = 0; i < k; i++) {
+    double m, x, y, z;
+    if (std::scanf("%lf %lf %lf %lf", &m, &x, &y, &z) != 4) std::exit(2);
+    K<P>::p2m(m, x, y, z, M);
+  }
+  double R[3], eps, sh[3];
+  if (std::scanf("%lf %lf %lf %lf %lf %lf %lf", &R[0], &R[1], &R[2], &eps, &sh[0], &sh[1], &sh[2]) != 7) std::exit(2);
+  K<P>::red(M, B);
+  double a[3] = {0, 0, 0};
+  K<P>::fwd(B, R[0], R[1], R[2], eps * eps, a[0], a[1], a[2]);
+  K<P>::m2m(M, sh[0], sh[1], sh[2], Mp);
+  for (int t = 0; t < NM; t++) std::printf("%.17g\n", M[t]);
+  for (int d = 0; d < 3; d++) std::printf("%.17g\n", a[d]);
+  for (int t = 0; t < NM; t++) std::printf("%.17g\n", Mp[t]);
+}
+
 int main(int argc, char** argv) {
+  if (argc > 1 && std::string(argv[1]) == "io") {
+    int p = -1;
+    if (std::scanf("%d", &p) != 1) return 2;
+    switch (p) {
+      case 0: run_io<0>(); break;
+      case 1: run_io<1>(); break;
+      case 2: run_io<2>(); break;
+      case 3: run_io<3>(); break;
+      case 4: run_io<4>(); break;
+      default: return 2;
+    }
+    return 0;
+  }
   if (argc > 1 && std::string(argv[1]) == "bg") {
     // the background terms of a unit cube of unit density at the points read
     // from stdin ("x y z" per line): order-4 and order-6 accelerations

@@ -2,7 +2,8 @@
 tests/adj_harness.cpp compiles the generated headers as host code with
 T = double and checks every reverse-mode kernel against central finite
 differences of its forward kernel, or against the dot-product identity;
-the packed FP32x2 kernels against the scalar FP32 ones bit for bit; and the
+the packed FP32x2 kernels against the scalar FP32 ones bit for bit; the forward
+P2M, M2P and M2M kernels against the oracle; and the
 uniform-background terms against the oracle's expansion of a uniform cube."""
 import os
 import shutil
@@ -49,3 +50,34 @@ def test_background_terms_match_the_oracle_cube_expansion(harness):
         for k, l in enumerate((4, 6)):
             ref = O.m2p_orders(M, l, l, R, 0.0)
             assert np.abs(got[i, 3 * k:3 * k + 3] - ref).max() <= 1e-12 * np.abs(ref).max(), (l, R)
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
+def test_forward_expansion_kernels_match_the_oracle(harness, p):
+    """The walk's generated forward kernels compiled as host FP64 code: P2M
+    moments of a few particles, the M2P acceleration of their reduced
+    moments (softened) and the M2M shift to a parent centre equal the
+    oracle's p2m, m2p and m2m."""
+    import oracle as O
+    rng = np.random.default_rng(40 + p)
+    for case in range(4):
+        k = int(rng.integers(1, 12))
+        d = rng.uniform(-0.5, 0.5, (k, 3))
+        m = rng.uniform(0.5, 1.5, k)
+        R = rng.uniform(-3.0, 3.0, 3)
+        R *= (1.2 + 2.0 * rng.uniform()) / np.linalg.norm(R)
+        eps = float(rng.choice([0.0, 0.01, 0.2]))
+        sh = 0.25 * rng.choice([-1.0, 1.0], 3)
+        inp = ("%d\n%d\n" % (p, k) + "\n".join("%.17g %.17g %.17g %.17g" % (m[i], *d[i]) for i in range(k))
+               + "\n%.17g %.17g %.17g %.17g %.17g %.17g %.17g\n" % (*R, eps, *sh))
+        r = subprocess.run([harness, "io"], input=inp, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        v = np.array([float(x) for x in r.stdout.split()])
+        nm = O.nmom(p)
+        assert len(v) == 2 * nm + 3
+        Mo = O.p2m(d, m, np.zeros(3), p)
+        ao = O.m2p(Mo, p, R, eps)
+        Mpo = O.m2m(Mo, sh, np.zeros(3), p)
+        assert np.abs(v[:nm] - Mo).max() <= 1e-14 * np.abs(Mo).max()
+        assert np.abs(v[nm:nm + 3] - ao).max() <= 1e-13 * np.abs(ao).max()
+        assert np.abs(v[nm + 3:] - Mpo).max() <= 1e-14 * np.abs(Mpo).max()
