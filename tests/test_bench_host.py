@@ -1,0 +1,33 @@
+"""Host logic of the benchmark on the CPU: the clock record taken during
+the timed region, and the algorithmic byte counts the phases are measured
+against (the per-particle figures the design doc states)."""
+import bench
+
+
+def _line(sm, mx, hw="Not Active", hwt="Not Active", swt="Not Active", pcap="Not Active"):
+    return "0, %s, %s, 812.5, 0x0000000000000000, %s, %s, %s, %s" % (sm, mx, hw, hwt, swt, pcap)
+
+
+def test_clock_summary_median_max_and_reasons():
+    lines = [_line(2070, 2070), _line(1980, 2070, pcap="Active"), _line(2070, 2070), "garbage",
+             _line("[N/A]", 2070), "", _line(1500, 2070, swt="Active")]
+    c = bench.summarise_clocks(lines)
+    assert c["samples"] == 4
+    assert c["sm_mhz"] == 2025.0  # median of 2070, 1980, 2070, 1500
+    assert c["sm_max_mhz"] == 2070.0
+    assert c["reasons"] == ["sw_power_cap", "sw_thermal_slowdown"]
+    assert bench.summarise_clocks([_line(2070, 2070, hw="Active", hwt="Active")])["reasons"] == [
+        "hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.summarise_clocks(["garbage", ""]) is None
+
+
+def test_phase_bytes_per_particle():
+    n, nc, ng = 1 << 20, 1000, 100
+    b = bench.phase_bytes(n, nc, ng, 4)
+    assert b["ms_sort"] == 304 * n  # 8 digit passes of 24 B + 112 B
+    assert bench.phase_bytes(n, nc, ng, 4, nbox=96)["ms_sort"] == (304 + 24) * n
+    assert bench.phase_bytes(n, nc, ng, 4, nbox=300)["ms_sort"] == (304 + 48) * n
+    assert b["ms_build"] == 152 * n + 194 * nc + 168 * ng
+    assert b["ms_upward"] == 28 * n + 843 * nc  # 91 + 16 * 35 + 4 * 48 per cell at p = 4
+    assert b["ms_periodic"] == 64 * n
+    assert abs(bench.fp32_peak_tflops(2070.0) - 80.54784) < 1e-9
