@@ -9,6 +9,7 @@ cells), convergence of the tree to direct summation, the integrator's
 closed forms and linear growth, and the CIC loss gradient.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -51,12 +52,38 @@ def test_ewald_small_r_background_limit():
         assert np.abs(diff / r - 4 * math.pi / 3).max() <= 5 * h ** 2 * 10
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
 def test_madelung_constant():
-    # simple cubic lattice with neutralising background (Nijboer & de Wette):
-    # lim_{r->0} [psi(r) - 1/r] = -2.8372974794806 for the Coulomb-sign potential
+    # simple cubic lattice with neutralising background (literature value and
+    # citation in tests/golden/madelung_simple_cubic.txt): the Coulomb-sign
+    # regular part lim_{r->0} [psi(r) - 1/r] = -value, so for the oracle's
+    # gravitational-sign potential lim_{r->0} [phi_E(r) + 1/r] = +value
+    value = float(_golden_lines("madelung_simple_cubic.txt")[0][0])
     r = 1e-4 * np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0)
-    val = -(O.ewald_pot(r) + 1.0 / np.linalg.norm(r))
-    assert abs(val - (-2.8372974794806)) <= 1e-7
+    val = O.ewald_pot(r) + 1.0 / np.linalg.norm(r)
+    assert abs(val - value) <= 1e-7
+
+
+def test_oracle_matches_its_regression_fixture():
+    """tests/golden/oracle_direct8.txt (written by make_oracle_fixture.py
+    from the oracle alone): exact Ewald accelerations and the direct sum of
+    eight particles are reproduced; a change here is a change of the
+    oracle's arithmetic."""
+    rows = _golden_lines("oracle_direct8.txt")
+    ew = np.array([[float(v) for v in r[1:]] for r in rows if r[0] == "ewald"])
+    for row in ew:
+        a = O.ewald_acc(row[:3])
+        assert np.abs(a - row[3:]).max() <= 1e-12 * np.abs(row[3:]).max()
+    dr = np.array([[float(v) for v in r[1:]] for r in rows if r[0] == "direct"])
+    acc = O.direct_forces(dr[:, 1:4], dr[:, 0], 0.02, table_n1=None)
+    assert np.abs(acc - dr[:, 4:]).max() <= 1e-12 * np.abs(dr[:, 4:]).max()
 
 
 def test_phitilde_consistency_and_harmonic():
