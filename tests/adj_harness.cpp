@@ -326,7 +326,40 @@ template <int P> void run_io() {
   for (int t = 0; t < NM; t++) std::printf("%.17g\n", Mp[t]);
 }
 
+// one image-field case from stdin: NE source moments M (orders <= pe about
+// the source centre), NP derivatives D of phi~ at R0 (orders <= pe + 1), the
+// sink offset d from the expansion point; prints the L2P acceleration of the
+// M2L local expansion, one value per line
+template <int PE> void run_field_io() {
+  const int NE = (PE + 1) * (PE + 2) * (PE + 3) / 6, NP = (PE + 2) * (PE + 3) * (PE + 4) / 6;
+  double M[NE], D[NP], L[F<PE>::NL], d[3];
+  for (int t = 0; t < NE; t++)
+    if (std::scanf("%lf", &M[t]) != 1) std::exit(2);
+  for (int t = 0; t < NP; t++)
+    if (std::scanf("%lf", &D[t]) != 1) std::exit(2);
+  for (int k = 0; k < 3; k++)
+    if (std::scanf("%lf", &d[k]) != 1) std::exit(2);
+  for (int t = 0; t < F<PE>::NL; t++) L[t] = 0.0;
+  F<PE>::m2l(M, D, L);
+  double a[3] = {0, 0, 0};
+  F<PE>::l2p(L, d[0], d[1], d[2], a[0], a[1], a[2]);
+  for (int k = 0; k < 3; k++) std::printf("%.17g\n", a[k]);
+}
+
 int main(int argc, char** argv) {
+  if (argc > 1 && std::string(argv[1]) == "field") {
+    int pe = -1;
+    if (std::scanf("%d", &pe) != 1) return 2;
+    switch (pe) {
+      case 1: run_field_io<1>(); break;
+      case 2: run_field_io<2>(); break;
+      case 3: run_field_io<3>(); break;
+      case 4: run_field_io<4>(); break;
+      case 5: run_field_io<5>(); break;
+      default: return 2;
+    }
+    return 0;
+  }
   if (argc > 1 && std::string(argv[1]) == "io") {
     int p = -1;
     if (std::scanf("%d", &p) != 1) return 2;

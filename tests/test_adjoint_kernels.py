@@ -3,8 +3,10 @@ tests/adj_harness.cpp compiles the generated headers as host code with
 T = double and checks every reverse-mode kernel against central finite
 differences of its forward kernel, or against the dot-product identity;
 the packed FP32x2 kernels against the scalar FP32 ones bit for bit; the forward
-P2M, M2P and M2M kernels against the oracle; and the
-uniform-background terms against the oracle's expansion of a uniform cube."""
+P2M, M2P and M2M kernels against the oracle; the image field's M2L and L2P
+against the oracle's exact Ewald derivatives (convergence at their order);
+and the uniform-background terms against the oracle's expansion of a uniform
+cube."""
 import os
 import shutil
 import subprocess
@@ -81,3 +83,37 @@ def test_forward_expansion_kernels_match_the_oracle(harness, p):
         assert np.abs(v[:nm] - Mo).max() <= 1e-14 * np.abs(Mo).max()
         assert np.abs(v[nm:nm + 3] - ao).max() <= 1e-13 * np.abs(ao).max()
         assert np.abs(v[nm + 3:] - Mpo).max() <= 1e-14 * np.abs(Mpo).max()
+
+
+@pytest.mark.parametrize("pe", [1, 2, 3, 4, 5])
+def test_image_field_expansion_converges_at_its_order(harness, pe):
+    """The walk's generated image-field M2L and L2P, compiled as host FP64
+    code, for a unit point source at offset delta from its cell centre and a
+    sink at offset d from the expansion point, with the oracle's exact Ewald
+    derivatives of phi~ at R0 = e - c*: the result is the Taylor expansion of
+    -grad phi~(R0 + d - delta) to total order pe in the two offsets, so its
+    error against the oracle's exact value falls as h^(pe+1) when both
+    offsets scale with h.  A wrong coefficient of any order k <= pe would
+    leave an error falling only as h^k."""
+    import oracle as O
+    R0 = np.array([0.3, 0.2, -0.25])
+    u = np.array([0.6, -0.5, 0.62])
+    w = np.array([-0.3, 0.8, 0.52])
+    u /= np.linalg.norm(u)
+    w /= np.linalg.norm(w)
+    mi = O.multi_indices(pe)
+    D = O.phitilde_mi(R0, pe + 1)
+    errs = []
+    for h in (0.08, 0.04, 0.02):
+        delta, d = h * u, 0.7 * h * w
+        M = np.array([delta[0] ** n[0] * delta[1] ** n[1] * delta[2] ** n[2] for n in mi])
+        inp = ("%d\n" % pe + "\n".join("%.17g" % v for v in M) + "\n" + "\n".join("%.17g" % v for v in D)
+               + "\n%.17g %.17g %.17g\n" % tuple(d))
+        r = subprocess.run([harness, "field"], input=inp, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        a = np.array([float(x) for x in r.stdout.split()])
+        exact = -O.phitilde_mi(R0 + d - delta, 1)[1:4]
+        errs.append(np.linalg.norm(a - exact) / np.linalg.norm(exact))
+    assert errs[2] <= 0.02 * 0.3 ** (pe - 1)
+    for i in range(2):
+        assert errs[i] / errs[i + 1] >= 0.8 * 2 ** (pe + 1), (pe, errs)
