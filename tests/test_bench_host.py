@@ -31,3 +31,23 @@ def test_phase_bytes_per_particle():
     assert b["ms_upward"] == 28 * n + 843 * nc  # 91 + 16 * 35 + 4 * 48 per cell at p = 4
     assert b["ms_periodic"] == 64 * n
     assert abs(bench.fp32_peak_tflops(2070.0) - 80.54784) < 1e-9
+
+
+def test_reference_arm_line(capsys):
+    """bench.py --impl reference times the oracle on a bounded sample and
+    prints one JSON line with the keys the comparison needs; ranks other than
+    0 print nothing."""
+    import argparse
+    import json
+    args = argparse.Namespace(steps=1, warmup=0, gpus=1)
+    assert bench.run_reference(args, rank=1, world=2) == 0
+    assert capsys.readouterr().out == ""
+    assert bench.run_reference(args, rank=0, world=1) == 0
+    line = json.loads(capsys.readouterr().out.strip().split("\n")[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
