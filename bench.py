@@ -101,7 +101,7 @@ def hbm_peak():
 def phase_bytes(n, ncell, ngroup, order, nbox=1):
     """Algorithmic DRAM bytes of one build's sort, build and upward phases and
     of one evaluation's image-field phase: every array their kernels read or
-    write, counted once, per particle / cell / group (derivation in the design doc):
+    write, counted once, per particle / cell / group:
       sort     box ids 2, keys 36, histograms 8, 24 per digit pass, sbox 8, gather 58
       build    152 per particle + 194 per cell + 168 per group
       upward   28 per particle + (91 + 16 nmom + 4 nbs) per cell (the image-field

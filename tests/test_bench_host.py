@@ -1,6 +1,8 @@
 """Host logic of the benchmark on the CPU: the clock record taken during
-the timed region, and the algorithmic byte counts the phases are measured
-against (the per-particle figures the design doc states)."""
+the timed region, the algorithmic byte counts the phases are measured
+against (per particle: sort 304 B over 8 digit passes, 24 B per extra box
+pass; build 152 B plus 194 B per cell and 168 B per group; upward 28 B plus
+843 B per cell at p = 4; image field 64 B), and the reference arm's line."""
 import bench
 
 
