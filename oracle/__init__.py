@@ -225,16 +225,18 @@ def direct_forces(pos, mass=None, eps=0.0, targets=None, table_n1: int | None = 
     return acc.reshape(3, nt).T.copy()
 
 
-def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int = 64):
-    """(d a / d x)^T lam for O1 (all particles); lam and result are (n,3)."""
+def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int | None = 64):
+    """(d a / d x)^T lam for O1 (all particles); lam and result are (n,3).
+    ``n1=None`` takes grad C~ from the exact Ewald sum for every pair (slow);
+    otherwise from the tricubic table with ``n1`` intervals."""
     P = _soa(pos)
     n = P.shape[1]
     m = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
     L = _soa(lam)
     out = np.zeros(3 * n)
-    tab = ctilde_grad_table(n1)
-    _lib().or_direct_vjp(n, _d(P), None if m is None else _d(m), eps, _d(tab), n1, _d(L),
-                         _d(out))
+    tab = None if n1 is None else ctilde_grad_table(n1)
+    _lib().or_direct_vjp(n, _d(P), None if m is None else _d(m), eps, None if tab is None else _d(tab),
+                         n1 or 0, _d(L), _d(out))
     return out.reshape(3, n).T.copy()
 
 
@@ -517,7 +519,8 @@ def adjoint_kdk(x_list, p_list, a_list, lam_x, lam_p, mass, eps, n1=64):
     ``x_list[k], p_list[k]`` are the states at ``a_list[k]`` (k = 0..S); each
     step recomputes nothing (states given).  The force at step start is a
     function of x_k, so every step contributes two force VJPs.  Returns the
-    cotangents (lam_x0, lam_p0)."""
+    cotangents (lam_x0, lam_p0).  ``n1`` is passed to ``direct_vjp``
+    (None: exact Ewald derivatives)."""
     S = len(a_list) - 1
     lx = np.array(lam_x, dtype=np.float64)
     lp = np.array(lam_p, dtype=np.float64)

@@ -62,12 +62,16 @@ int or_direct_forces(int64_t n, const double *pos, const double *mass, double ep
 }
 
 /* out_j = sum_{i != j} grad K(r_ij) (m_i lam_j - m_j lam_i),
- * K(r) = a_P(r*) + (4 pi/3) r* + C~(r*), grad K symmetric and even in r. */
+ * K(r) = a_P(r*) + (4 pi/3) r* + C~(r*), grad K symmetric and even in r.
+ * grad C~ = -d_ij phi~ comes from the tricubic table gtab, or, with gtab
+ * NULL, from the exact Ewald derivatives of phi~ at r*. */
 int or_direct_vjp(int64_t n, const double *pos, const double *mass, double eps,
                   const double *gtab, int n1, const double *lam, double *out) {
   if (n <= 0) return 0;
   const double *X = pos, *Y = pos + n, *Z = pos + 2 * n;
   double e2 = eps * eps;
+  or_ewald_cfg cfg;
+  or_ewald_default(&cfg);
   static const int I2[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t j = 0; j < n; j++) {
@@ -82,7 +86,13 @@ int or_direct_vjp(int64_t n, const double *pos, const double *mass, double eps,
       double s = q2 + e2;
       double is3 = 1.0 / (s * sqrt(s)), is5 = is3 / s;
       double g6[6];
-      or_ctilde_grad_table_eval(gtab, n1, rs, g6);
+      if (gtab) {
+        or_ctilde_grad_table_eval(gtab, n1, rs, g6);
+      } else {
+        double d10[10]; /* multi-indices |m| <= 2; 4..9 = xx, xy, xz, yy, yz, zz */
+        or_phitilde_mi(rs, &cfg, 2, d10);
+        for (int t = 0; t < 6; t++) g6[t] = -d10[4 + t];
+      }
       double G[3][3];
       for (int t = 0; t < 6; t++) {
         int a = I2[t][0], b = I2[t][1];

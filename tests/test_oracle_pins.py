@@ -480,3 +480,86 @@ def test_direct_vjp_dot_product():
           O.direct_forces(x - h * v, None, eps, table_n1=64)) / (2 * h)
     jtw = O.direct_vjp(x, w, None, eps, n1=64)
     assert abs(np.sum(jv * w) - np.sum(v * jtw)) <= 1e-4 * abs(np.sum(jv * w))
+
+
+# ---- keys and sort, by hand -------------------------------------------------------------
+def test_morton_keys_hand_computed():
+    """Keys of hand-placed points, worked out by hand (no call to the oracle
+    to get them) in the layout the tree rests on: q_d = floor(x_d 2^21) mod
+    2^21, and bit b of q_x, q_y, q_z goes to key bit 3b, 3b+1, 3b+2.  A
+    swapped axis, an interleave off by one or a quantisation that rounds
+    instead of flooring fails one of these."""
+    u = 2.0 ** -21
+    cases = [
+        ((0.5, 0.0, 0.0), 1 << 60),                    # q_x = 2^20: bit 20 -> key bit 60
+        ((0.0, 0.5, 0.0), 1 << 61),                    # q_y = 2^20 -> key bit 61
+        ((0.0, 0.0, 0.5), 1 << 62),                    # q_z = 2^20 -> key bit 62
+        ((u, 0.0, 0.0), 1),                            # q_x = 1
+        ((0.0, 3 * u, 0.0), 0b10010),                  # q_y = 0b11: key bits 1 and 4
+        ((0.75, 0.25, 0.125), (1 << 60) | (1 << 58) | (1 << 57) | (1 << 56)),
+        # q_x = floor(3 - 2^-39) = 2 (bit 1 -> key bit 3); q_z = 0b101 (key bits 2, 8)
+        ((3 * u - 2.0 ** -60, 0.0, 5 * u), 8 + 4 + 256),
+        ((1.0, 0.0, 0.0), 0),                          # x = 1 wraps to 0
+        ((-u, 0.0, 0.0), 0x1249249249249249),          # q_x = 2^21 - 1: every x bit
+        ((0.0, 1.0 - u, 0.0), 0x2492492492492492),     # q_y = 2^21 - 1: every y bit
+        ((0.0, 0.0, 1.0 - 0.5 * u), 0x4924924924924924),  # q_z = floor(2^21 - 1/2)
+        ((1.0 - u, 1.0 - u, 1.0 - u), 0x7FFFFFFFFFFFFFFF),
+        ((2.25, -0.75, 0.0), (1 << 57) | (1 << 58)),   # wrapped: 0.25 and 0.25
+    ]
+    pts = np.array([c[0] for c in cases], dtype=np.float64)
+    want = np.array([c[1] for c in cases], dtype=np.uint64)
+    got = O.morton_keys(pts)
+    assert np.array_equal(got, want), [(i, hex(int(g)), hex(int(w))) for i, (g, w) in enumerate(zip(got, want))
+                                      if g != w]
+
+
+def test_sort_perm_hand_computed():
+    """Stable key order of a hand-written key list: equal keys keep their
+    input order."""
+    keys = np.array([5, 3, 5, 1, 3, 0x7FFFFFFFFFFFFFFF, 0, 3], dtype=np.uint64)
+    assert O.sort_perm(keys).tolist() == [6, 3, 1, 4, 7, 0, 2, 5]
+
+
+# ---- the reverse mode of a KDK trajectory -------------------------------------------------
+def test_adjoint_kdk_matches_central_differences():
+    """adjoint_kdk over three KDK steps of the direct Ewald forces against
+    FP64 central differences of the same trajectory (kdk_step driven by
+    direct_forces with the exact Ewald sum, g(x0) recomputed from x0).  The
+    functional is F = <w_x, x_S> + <w_p, p_S>, so its cotangents are
+    (w_x, w_p); <lam_x0, v> + <lam_p0, u> must equal dF along (v, u).  Which
+    state each force VJP uses and where K1, K2 and D enter all change the
+    result by far more than the 1e-6 allowed."""
+    rng = np.random.default_rng(77)
+    q = ics.lattice(3)                                  # 27 particles at (i + 1/2)/3
+    psi = 0.04 * rng.standard_normal(q.shape)
+    a_list = [0.1, 0.15, 0.22, 0.3]
+    eps = 0.05
+    x0, p0 = O.zeldovich_state(q, psi, a_list[0])
+    force = lambda x: O.direct_forces(x, None, eps, table_n1=None)
+
+    def run(x, p):
+        xs, ps = [x], [p]
+        g = force(x)
+        for k in range(len(a_list) - 1):
+            x, p, g = O.kdk_step(x, p, g, a_list[k], a_list[k + 1], force)
+            xs.append(x)
+            ps.append(p)
+        return xs, ps
+
+    xs, ps = run(x0, p0)
+    wx = rng.standard_normal(q.shape)
+    wp = rng.standard_normal(q.shape)
+    lx0, lp0 = O.adjoint_kdk(xs, ps, a_list, wx, wp, None, eps, n1=None)
+    h = 1e-6
+    for _ in range(3):
+        v = rng.standard_normal(q.shape)
+        u = rng.standard_normal(q.shape)
+        xp, pp = run(x0 + h * v, p0 + h * u)
+        xm, pm = run(x0 - h * v, p0 - h * u)
+        # unwrapped final positions: no particle crosses the box edge here
+        fd = (np.sum(wx * (xp[-1] - xm[-1])) + np.sum(wp * (pp[-1] - pm[-1]))) / (2 * h)
+        ad = np.sum(lx0 * v) + np.sum(lp0 * u)
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+    # the chaining matters: reversing with the VJPs at swapped states is far off
+    assert np.abs(lx0 - O.adjoint_kdk(xs[::-1][:1] + xs[1:], ps, a_list, wx, wp, None, eps,
+                                      n1=None)[0]).max() > 1e-4 * np.abs(lx0).max()
