@@ -8,7 +8,8 @@ module both sides use is the seeded input generator
 
 Contents (each function cites the passage it follows):
 
-* ``direct_forces``  O1, FP64 direct sum with Ewald images.
+* ``direct_forces``  O1, FP64 direct sum with Ewald images (Plummer or
+  Dehnen K1 softening, ``soft_factor``).
 * ``tree_forces``    O2, FP64 CPU treecode with the same method definition as
   the GPU path (Sec. 2.1: keys, key-implied tree, multipoles, MAC, groups).
 * ``kick_factor`` / ``drift_factor`` / ``kdk_step``  O3, comoving leapfrog in an
@@ -57,7 +58,8 @@ class TreeParams(C.Structure):
     _fields_ = [("eps", C.c_double), ("theta", C.c_double), ("order", C.c_int),
                 ("n_leaf", C.c_int), ("n_group", C.c_int), ("n_direct", C.c_int),
                 ("lmax", C.c_int), ("ewald", C.c_int), ("ew_level", C.c_int),
-                ("ew_grid", C.c_int), ("mac", C.c_int), ("bg", C.c_int)]
+                ("ew_grid", C.c_int), ("mac", C.c_int), ("bg", C.c_int), ("kernel", C.c_int),
+                ("dual", C.c_int)]
 
 
 class EwaldCfg(C.Structure):
@@ -86,6 +88,10 @@ def _lib():
             L.or_ctilde_grad_table_eval.argtypes = [_dp, C.c_int, _dp, _dp]
             L.or_direct_forces.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_int64, _i64p,
                                            _dp, C.c_int, _dp]
+            L.or_direct_forces_k.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_int, C.c_int64, _i64p,
+                                             _dp, C.c_int, _dp]
+            L.or_soft_factor.argtypes = [C.c_double, C.c_double, C.c_int]
+            L.or_soft_factor.restype = C.c_double
             L.or_direct_vjp.argtypes = [C.c_int64, _dp, _dp, C.c_double, _dp, C.c_int, _dp, _dp]
             L.or_tree_forces.argtypes = [C.c_int64, _dp, _dp, C.POINTER(TreeParams), _dp,
                                          C.c_int64, _i64p, _dp, _dp]
@@ -101,6 +107,8 @@ def _lib():
             L.or_m2p.argtypes = [_dp, C.c_int, _dp, C.c_double, _dp]
             L.or_m2p_orders.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_double, _dp]
             L.or_cube_moments.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
+            L.or_m2l.argtypes = [_dp, C.c_int, _dp, C.c_double, _dp]
+            L.or_l2p.argtypes = [_dp, C.c_int, _dp, _dp]
             _LIB = L
     return _LIB
 
@@ -206,8 +214,14 @@ def ctilde_grad_table(n1: int = 64) -> np.ndarray:
     return _TABLE_CACHE[key]
 
 
-def direct_forces(pos, mass=None, eps=0.0, targets=None, table_n1: int | None = 128):
-    """O1: a_i = sum_j m_j [a_E(r_ij) - a_N(r*_ij) + a_P(r*_ij)] (FP64).
+def soft_factor(r2, eps, kernel=0) -> float:
+    """f(r) of the pair acceleration m (x_j - x_i) f: kernel 0 Plummer, 1 Dehnen K1."""
+    return float(_lib().or_soft_factor(float(r2), float(eps), int(kernel)))
+
+
+def direct_forces(pos, mass=None, eps=0.0, targets=None, table_n1: int | None = 128, kernel: int = 0):
+    """O1: a_i = sum_j m_j [a_E(r_ij) - a_N(r*_ij) + a_S(r*_ij)] (FP64), a_S the
+    softened pair force of ``kernel`` (0 Plummer, 1 Dehnen K1).
 
     ``table_n1=None`` evaluates the exact Ewald sum for every pair (slow);
     otherwise C~ comes from the tricubic table with ``table_n1`` intervals.
@@ -219,9 +233,11 @@ def direct_forces(pos, mass=None, eps=0.0, targets=None, table_n1: int | None = 
     nt = n if tg is None else len(tg)
     acc = np.zeros(3 * nt)
     tab = None if table_n1 is None else ctilde_table(table_n1)
-    _lib().or_direct_forces(n, _d(P), None if m is None else _d(m), eps, nt,
-                            None if tg is None else tg.ctypes.data_as(_i64p),
-                            None if tab is None else _d(tab), table_n1 or 0, _d(acc))
+    rc = _lib().or_direct_forces_k(n, _d(P), None if m is None else _d(m), eps, kernel, nt,
+                                   None if tg is None else tg.ctypes.data_as(_i64p),
+                                   None if tab is None else _d(tab), table_n1 or 0, _d(acc))
+    if rc != 0:
+        raise ValueError("or_direct_forces_k rejected its parameters (%d)" % rc)
     return acc.reshape(3, nt).T.copy()
 
 
@@ -241,14 +257,17 @@ def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int | None = 64):
 
 
 def tree_params(eps, theta, order, n_leaf=16, n_group=32, n_direct=None, lmax=21, ewald=4,
-                ew_level=3, ew_grid=6, mac=0, bg=0) -> TreeParams:
+                ew_level=3, ew_grid=6, mac=0, bg=0, kernel=0, dual=0) -> TreeParams:
     """mac 0: the opening test measures d from the cell centre to the group
     box; mac 1: from the cell's faces (box to box).  bg = q > order adds the
-    orders order+1..q of each expanded cell's uniform background share."""
+    orders order+1..q of each expanded cell's uniform background share.
+    kernel 0: Plummer softening; 1: Dehnen K1 for direct pairs, Newtonian
+    cell expansions.  dual 1: well-separated cell-group pairs through a local
+    expansion of the group (or_m2l / or_l2p)."""
     if n_direct is None:
         n_direct = 2 if order <= 2 else 4
     return TreeParams(eps, theta, order, n_leaf, n_group, n_direct, lmax, ewald, ew_level,
-                      ew_grid, mac, bg)
+                      ew_grid, mac, bg, kernel, dual)
 
 
 def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,
@@ -260,7 +279,7 @@ def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
     nt = n if tg is None else len(tg)
     acc = np.zeros(3 * nt)
-    st = np.zeros(5)
+    st = np.zeros(7)
     tab = phitilde_lattice(params.ew_grid, params.ewald + 1) if params.ewald > 0 else None
     rc = _lib().or_tree_forces(n, _d(P), None if m is None else _d(m), C.byref(params),
                                None if tab is None else _d(tab), nt,
@@ -269,7 +288,8 @@ def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,
         raise ValueError("or_tree_forces rejected its parameters (%d)" % rc)
     a = acc.reshape(3, nt).T.copy()
     if return_stats:
-        return a, {"p2p": st[0], "m2p": st[1], "ewald": st[2], "cells": st[3], "groups": st[4]}
+        return a, {"p2p": st[0], "m2p": st[1], "ewald": st[2], "cells": st[3], "groups": st[4],
+                   "sinks": st[5], "m2l": st[6]}
     return a
 
 
@@ -351,6 +371,24 @@ def m2p_orders(M, pmin, pmax, R, eps):
     R = np.ascontiguousarray(R, dtype=np.float64)
     a = np.zeros(3)
     _lib().or_m2p_orders(_d(M), pmin, pmax, _d(R), eps, _d(a))
+    return a
+
+
+def m2l(M, p, R, eps):
+    """Local expansion coefficients (nmom(p + 1), index 0 unused) about z of a
+    cell's field, R = z - c (the dual form's cell-group interaction)."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    L = np.zeros(nmom(p + 1))
+    _lib().or_m2l(_d(M), p, _d(R), eps, _d(L))
+    return L
+
+
+def l2p(L, p, d):
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    a = np.zeros(3)
+    _lib().or_l2p(_d(L), p, _d(d), _d(a))
     return a
 
 

@@ -18,15 +18,31 @@ static const double PI = 3.14159265358979323846264338327950288;
 
 static inline double min_image(double d) { return d - floor(d + 0.5); }
 
+double or_soft_factor(double r2, double eps, int kernel) {
+  if (kernel == 1) {
+    double x2 = r2 / (eps * eps);
+    if (x2 < 1.0) return (175.0 / 16.0 - (147.0 / 8.0) * x2 + (135.0 / 16.0) * x2 * x2) / (eps * eps * eps);
+    return 1.0 / (r2 * sqrt(r2));
+  }
+  double s = r2 + eps * eps;
+  return 1.0 / (s * sqrt(s));
+}
+
 int or_direct_forces(int64_t n, const double *pos, const double *mass, double eps,
                      int64_t ntarget, const int64_t *targets, const double *ctab, int n1,
                      double *acc) {
+  return or_direct_forces_k(n, pos, mass, eps, 0, ntarget, targets, ctab, n1, acc);
+}
+
+int or_direct_forces_k(int64_t n, const double *pos, const double *mass, double eps, int kernel,
+                       int64_t ntarget, const int64_t *targets, const double *ctab, int n1,
+                       double *acc) {
   if (n <= 0) return 0;
+  if (kernel < 0 || kernel > 1) return -1;
   const double *X = pos, *Y = pos + n, *Z = pos + 2 * n;
   int64_t nt = targets ? ntarget : n;
   or_ewald_cfg cfg;
   or_ewald_default(&cfg);
-  double e2 = eps * eps;
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t t = 0; t < nt; t++) {
     int64_t i = targets ? targets[t] : t;
@@ -37,8 +53,7 @@ int or_direct_forces(int64_t n, const double *pos, const double *mass, double ep
       double r[3] = {X[i] - X[j], Y[i] - Y[j], Z[i] - Z[j]};
       double rs[3] = {min_image(r[0]), min_image(r[1]), min_image(r[2])};
       double q2 = rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2];
-      double s = q2 + e2;
-      double fp = 1.0 / (s * sqrt(s));
+      double fp = or_soft_factor(q2, eps, kernel);
       double k[3];
       if (ctab) {
         double ct[3];

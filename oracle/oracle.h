@@ -59,6 +59,18 @@ void or_ctilde_table_eval(const double *tab, int n1, const double r[3], double o
 int or_ctilde_grad_table_build(int n1, double *tab /* (n1+4)^3 * 6 */);
 void or_ctilde_grad_table_eval(const double *tab, int n1, const double r[3], double out[6]);
 
+/* ---- softening -------------------------------------------------------------
+ * Pair acceleration a_i = m_j (x_j - x_i) f(r) with r = |x_j - x_i|:
+ *   kernel 0, Plummer:  f = (r^2 + eps^2)^(-3/2)
+ *   kernel 1, Dehnen's compensating K1 kernel (the paper's choice): the field
+ *   of the density rho(r) = 105/(64 pi eps^3) (1 - x^2)(5 - 9 x^2), x = r/eps
+ *   < 1 (zero beyond), the quadratic F1 kernel 1 - x^2 times the factor that
+ *   makes its second moment vanish.  Its enclosed mass is
+ *   M(x) = (175/16) x^3 - (147/8) x^5 + (135/16) x^7 (M(1) = 1), so
+ *   f = M(x)/r^3 = (175/16 - (147/8) x^2 + (135/16) x^4)/eps^3 for r < eps
+ *   and f = 1/r^3 beyond. */
+double or_soft_factor(double r2, double eps, int kernel);
+
 /* ---- O1: direct summation with Ewald images --------------------------------
  * a_i = sum_{j != i} m_j [ a_E(r_ij) - a_N(r*_ij) + a_P(r*_ij) ]
  * (Plummer softening for the minimum-image pair only).  ctab == NULL uses the
@@ -67,6 +79,11 @@ void or_ctilde_grad_table_eval(const double *tab, int n1, const double r[3], dou
 int or_direct_forces(int64_t n, const double *pos, const double *mass, double eps,
                      int64_t ntarget, const int64_t *targets, const double *ctab,
                      int n1, double *acc);
+/* The same with the softening kernel of or_soft_factor for the minimum-image
+ * pair (kernel 0 is or_direct_forces). */
+int or_direct_forces_k(int64_t n, const double *pos, const double *mass, double eps, int kernel,
+                       int64_t ntarget, const int64_t *targets, const double *ctab, int n1,
+                       double *acc);
 /* Vector-Jacobian product of O1: given lam (3 x n SoA, cotangent of the
  * accelerations of all particles), out = (d a / d x)^T lam (3 x n SoA). */
 int or_direct_vjp(int64_t n, const double *pos, const double *mass, double eps,
@@ -93,10 +110,26 @@ typedef struct {
                      filling it, with the Newtonian kernel (the higher moments
                      of the cell's uniform share, which dominate the expansion
                      error of a near-uniform state) */
+  int kernel;     /* softening of direct pairs (or_soft_factor): 0 Plummer,
+                     1 Dehnen K1.  With K1, whose field is Newtonian beyond
+                     eps, cell expansions use the Newtonian kernel 1/|R| */
+  int dual;       /* 1: cell-group (dual) interactions.  An accepted cell C
+                     of side s_C whose centre lies farther than
+                     (s_C + s_G)/theta from the centre z of the group box
+                     (largest side s_G; integer units of 2^-23, threshold
+                     floor(S^2/theta^2) in IEEE double) is not expanded at
+                     every sink: its field joins a local (Taylor) expansion
+                     of the group about z, L_k = sum_n ((-1)^|n|/n!) M_n
+                     d^(n+k) g(z - c*), 1 <= |k|, |n| + |k| <= p + 1 (the
+                     M2P's derivative orders), evaluated once per sink,
+                     a_k = sum_{|m| <= p} (x - z)^m/m! L_(m + e_k).  Not with
+                     bg. */
 } or_tree_params;
 
 /* stats[0] = P2P pair interactions, stats[1] = M2P interactions,
- * stats[2] = Ewald (group, cell) terms, stats[3] = cells, stats[4] = groups */
+ * stats[2] = Ewald (group, cell) terms, stats[3] = cells, stats[4] = groups walked,
+ * stats[5] = sinks walked (every particle of a group that holds a target),
+ * stats[6] = cell-group local expansions (dual) */
 int or_tree_forces(int64_t n, const double *pos, const double *mass,
                    const or_tree_params *p, const double *tab, int64_t ntarget,
                    const int64_t *targets, double *acc, double *stats);
@@ -120,6 +153,11 @@ void or_dtensor(const double R[3], double eps, int pmax, double *D);
 void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]);
 /* the same with only the orders pmin..pmax of M (pmax <= 8) */
 void or_m2p_orders(const double *M, int pmin, int pmax, const double R[3], double eps, double a[3]);
+/* cell-group interaction of the dual form: L (nmom(p + 1) values, index 0
+ * unused) += the local expansion about z of a cell's field at R = z - c
+ * (orders |n| + |k| <= p + 1), and the acceleration at offset d from z */
+void or_m2l(const double *M, int p, const double R[3], double eps, double *L);
+void or_l2p(const double *L, int p, const double d[3], double a[3]);
 /* moments (order <= p) of a cube of side s and density rho about its centre */
 void or_cube_moments(double s, double rho, int p, double *C);
 

@@ -34,7 +34,10 @@
  *           Newtonian kernel g = 1/|R|: the truncation error of the uniform
  *           share of every cell, which is what subtracting the uniform
  *           background from every cell (and summing it exactly) removes.
- *  P2P      a += m_j r / (|r|^2 + eps^2)^(3/2), r = x_j* - x_i, j != i.
+ *  P2P      a += m_j r f(|r|), r = x_j* - x_i, j != i, f the softening of
+ *           or_soft_factor: Plummer (|r|^2 + eps^2)^(-3/2), or Dehnen's K1
+ *           kernel (kernel = 1), whose field is Newtonian beyond eps; with K1
+ *           the cell expansions use the Newtonian kernel (eps = 0 in M2P).
  *  periodic a_E(r) = a_N(r) + (4 pi/3) r + C~(r) for any image r; the walk sums
  *           the Newton/Plummer part, the background term is summed exactly
  *           and the image field sum_j m_j C~(x_i - x_j*) = -grad sum_j m_j
@@ -200,6 +203,41 @@ void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]) 
   or_m2p_orders(M, 0, p, R, eps, a);
 }
 
+/* Local expansion of a cell's field about z: with Psi(x) = sum_n
+ * ((-1)^|n|/n!) M_n d^n g(x - c) (a = grad Psi), L_k = d^k Psi(z) truncated
+ * to the derivative orders of the M2P: |n| + |k| <= p + 1. */
+void or_m2l(const double *M, int p, const double R[3], double eps, double *L) {
+  int P = p + 1;
+  double D[256];
+  or_dtensor(R, eps, P, D);
+  int nl = or_nmom(P), nm = or_nmom(p);
+  for (int t = 1; t < nl; t++) {
+    int k0 = g_ml[t][0], k1 = g_ml[t][1], k2 = g_ml[t][2];
+    int ok = k0 + k1 + k2;
+    for (int u = 0; u < nm; u++) {
+      int n0 = g_ml[u][0], n1 = g_ml[u][1], n2 = g_ml[u][2];
+      int on = n0 + n1 + n2;
+      if (on + ok > P) continue;
+      double cf = ((on & 1) ? -1.0 : 1.0) / (fact(n0) * fact(n1) * fact(n2));
+      L[t] += cf * M[u] * D[mi_idx(n0 + k0, n1 + k1, n2 + k2)];
+    }
+  }
+}
+
+/* a_k(z + d) = sum_{|m| <= p} d^m/m! L_(m + e_k): the gradient of the
+ * truncated Taylor series of Psi about z */
+void or_l2p(const double *L, int p, const double d[3], double a[3]) {
+  int nm = or_nmom(p);
+  a[0] = a[1] = a[2] = 0.0;
+  for (int u = 0; u < nm; u++) {
+    int m0 = g_ml[u][0], m1 = g_ml[u][1], m2 = g_ml[u][2];
+    double tay = ipow(d[0], m0) * ipow(d[1], m1) * ipow(d[2], m2) / (fact(m0) * fact(m1) * fact(m2));
+    a[0] += tay * L[mi_idx(m0 + 1, m1, m2)];
+    a[1] += tay * L[mi_idx(m0, m1 + 1, m2)];
+    a[2] += tay * L[mi_idx(m0, m1, m2 + 1)];
+  }
+}
+
 /* Moments about its centre of a cube of side s filled with density rho:
  * C_n = rho prod_d int_{-s/2}^{s/2} x^{n_d} dx, i.e. rho prod_d s^(n_d+1) /
  * ((n_d+1) 2^n_d) for even n_d and 0 for odd n_d. */
@@ -330,7 +368,7 @@ typedef struct {
 } tgroup;
 
 typedef struct {
-  double p2p, m2p, ew;
+  double p2p, m2p, ew, m2l;
 } wstats;
 
 static const int64_t PBOX = (int64_t)1 << 23; /* one box in units of 2^-23 */
@@ -364,7 +402,7 @@ static int cell_image(const walkctx *w, const tgroup *G, int level, const int64_
 static int64_t quant(double x);
 
 static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc /* 3 x count */,
-                     wstats *st) {
+                     double *Lg /* the group's local expansion (dual) */, wstats *st) {
   const tcell *c = &w->cells[ci];
   const or_tree_params *p = w->p;
   int64_t kimg[3];
@@ -382,22 +420,40 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
   int accept = consistent && c->level >= 2 && (double)d2 > w->T[c->level];
   int leaf = c->nchild == 0;
   if (!accept && !leaf) {
-    for (int k = 0; k < c->nchild; k++) walk_rec(w, G, c->child[k], acc, st);
+    for (int k = 0; k < c->nchild; k++) walk_rec(w, G, c->child[k], acc, Lg, st);
     return;
   }
   double cs[3];
   for (int d = 0; d < 3; d++) cs[d] = ldexp((double)centre_u(c->ix[d], c->level), -22) - (double)kimg[d];
   const double *M = w->mom + ci * w->nmom;
-  double e2 = p->eps * p->eps;
   int use_m2p = accept && c->count > p->n_direct;
   int le = p->ew_level;
+  if (use_m2p && p->dual) {
+    /* cell-group test: centre-to-centre distance against (s_C + s_G)/theta */
+    int64_t wmax = G->w2[0] > G->w2[1] ? G->w2[0] : G->w2[1];
+    if (G->w2[2] > wmax) wmax = G->w2[2];
+    int64_t S = ((int64_t)1 << (23 - c->level)) + 2 * wmax;
+    double T = floor((double)S * (double)S / (p->theta * p->theta));
+    int64_t dcc2 = 0;
+    for (int d = 0; d < 3; d++) {
+      int64_t delta = 2 * centre_u(c->ix[d], c->level) - G->g2[d] - kimg[d] * PBOX;
+      dcc2 += delta * delta;
+    }
+    if ((double)dcc2 > T) {
+      double R[3];
+      for (int d = 0; d < 3; d++) R[d] = ldexp((double)G->g2[d], -23) - cs[d];
+      or_m2l(M, p->order, R, p->kernel == 1 ? 0.0 : p->eps, Lg);
+      st->m2l += 1.0;
+      return;
+    }
+  }
   for (int64_t s = 0; s < G->count; s++) {
     int64_t i = G->start + s;
     double xi[3] = {w->X[i], w->Y[i], w->Z[i]};
     double a[3] = {0.0, 0.0, 0.0};
     if (use_m2p) {
       double R[3] = {xi[0] - cs[0], xi[1] - cs[1], xi[2] - cs[2]};
-      or_m2p(M, p->order, R, p->eps, a);
+      or_m2p(M, p->order, R, p->kernel == 1 ? 0.0 : p->eps, a);
       if (p->bg > p->order) {
         /* the cell's share of the uniform background (a cube of the mean
            density filling the cell) beyond order p, Newtonian kernel */
@@ -417,8 +473,7 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
         for (int d = 0; d < 3; d++) kj[d] = img_shift(2 * centre_u(jx[d], le), G->cell2[d]);
         double r[3] = {w->X[j] - (double)kj[0] - xi[0], w->Y[j] - (double)kj[1] - xi[1],
                        w->Z[j] - (double)kj[2] - xi[2]};
-        double q = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + e2;
-        double f = w->Mass[j] / (q * sqrt(q));
+        double f = w->Mass[j] * or_soft_factor(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], p->eps, p->kernel);
         a[0] += f * r[0];
         a[1] += f * r[1];
         a[2] += f * r[2];
@@ -545,7 +600,8 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
   if (p->order < 0 || p->order > 4 || p->lmax < 2 || p->lmax > QBITS || p->n_leaf < 1 ||
       p->n_group < 1 || p->n_direct > p->n_leaf || p->ewald < 0 || p->ewald > 5 ||
       (p->ewald > 0 && !tab) || p->ew_level < 1 || p->ew_level > 8 ||
-      p->ew_grid < p->ew_level + 1 || p->ew_grid > 10 || p->bg < 0 || p->bg > 8)
+      p->ew_grid < p->ew_level + 1 || p->ew_grid > 10 || p->bg < 0 || p->bg > 8 || p->kernel < 0 ||
+      p->kernel > 1 || p->dual < 0 || p->dual > 1 || (p->dual && p->bg > p->order))
     return -1;
   int64_t *perm = malloc(sizeof(int64_t) * n);
   uint64_t *skeys = malloc(sizeof(uint64_t) * n);
@@ -656,8 +712,8 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
     need[gid[where[orig]]] = 1;
   }
   double *sacc = calloc((size_t)(3 * n), sizeof(double));
-  double sp2p = 0.0, sm2p = 0.0, sew = 0.0, sgroups = 0.0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : sp2p, sm2p, sew, sgroups)
+  double sp2p = 0.0, sm2p = 0.0, sew = 0.0, sgroups = 0.0, ssinks = 0.0, sm2l = 0.0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : sp2p, sm2p, sew, sgroups, ssinks, sm2l)
   for (int64_t gi = 0; gi < ng; gi++) {
     if (!need[gi]) continue;
     tgroup G;
@@ -679,8 +735,19 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
       G.w2[d] = hi[d] - lo[d];
     }
     double *ga = calloc((size_t)(3 * G.count), sizeof(double));
-    wstats st = {0.0, 0.0, 0.0};
-    walk_rec(&w, &G, 0, ga, &st);
+    wstats st = {0.0, 0.0, 0.0, 0.0};
+    double Lg[128];
+    for (int t = 0; t < 128; t++) Lg[t] = 0.0;
+    walk_rec(&w, &G, 0, ga, Lg, &st);
+    if (p->dual && st.m2l > 0.0)
+      for (int64_t s = 0; s < G.count; s++) {
+        int64_t i = G.start + s;
+        double d[3] = {X[i] - ldexp((double)G.g2[0], -23), Y[i] - ldexp((double)G.g2[1], -23),
+                       Z[i] - ldexp((double)G.g2[2], -23)};
+        double a[3];
+        or_l2p(Lg, p->order, d, a);
+        for (int k = 0; k < 3; k++) ga[k * G.count + s] += a[k];
+      }
     if (p->ewald > 0) periodic_group(&w, &G, ga, &st);
     for (int64_t s = 0; s < G.count; s++)
       for (int d = 0; d < 3; d++) sacc[d * n + G.start + s] = ga[d * G.count + s];
@@ -689,6 +756,8 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
     sm2p += st.m2p;
     sew += st.ew;
     sgroups += 1.0;
+    ssinks += (double)G.count;
+    sm2l += st.m2l;
   }
   for (int64_t t = 0; t < nt; t++) {
     int64_t orig = targets ? targets[t] : t;
@@ -701,6 +770,8 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
     stats[2] = sew;
     stats[3] = (double)nc;
     stats[4] = sgroups;
+    stats[5] = ssinks;
+    stats[6] = sm2l;
   }
   free(sacc);
   free(where);

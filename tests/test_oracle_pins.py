@@ -563,3 +563,118 @@ def test_adjoint_kdk_matches_central_differences():
     # the chaining matters: reversing with the VJPs at swapped states is far off
     assert np.abs(lx0 - O.adjoint_kdk(xs[::-1][:1] + xs[1:], ps, a_list, wx, wp, None, eps,
                                       n1=None)[0]).max() > 1e-4 * np.abs(lx0).max()
+
+
+# ---- Dehnen's K1 softening kernel --------------------------------------------------------
+def _k1_density(x):
+    """The K1 kernel's density for eps = 1, written from its definition: the
+    quadratic kernel 1 - x^2 times (5 - 9 x^2), normalised to unit mass."""
+    return 105.0 / (64.0 * math.pi) * (1.0 - x * x) * (5.0 - 9.0 * x * x)
+
+
+def test_k1_kernel_mass_second_moment_and_newtonian_exterior():
+    """The oracle's K1 pair factor against quadrature of the kernel's density:
+    the enclosed mass M(x) = int_0^x 4 pi s^2 rho ds equals x^3 f(x) (Gauss's
+    law, eps = 1) at every radius, the total mass is 1, the second moment
+    int 4 pi s^4 rho ds vanishes (what makes the kernel compensating), the
+    field is exactly Newtonian from eps on, and the force is continuous with a
+    continuous slope at eps."""
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    for x in (0.1, 0.3, 0.5, 0.77, 0.95, 1.0):
+        s = 0.5 * x * (xg + 1.0)
+        m = 0.5 * x * np.sum(wg * 4.0 * math.pi * s * s * _k1_density(s))
+        assert abs(m - x ** 3 * O.soft_factor(x * x, 1.0, 1)) <= 1e-13, x
+    s = 0.5 * (xg + 1.0)
+    assert abs(0.5 * np.sum(wg * 4.0 * math.pi * s ** 2 * _k1_density(s)) - 1.0) <= 1e-13
+    assert abs(0.5 * np.sum(wg * 4.0 * math.pi * s ** 4 * _k1_density(s))) <= 1e-13
+    eps = 0.02
+    for r in (eps, 1.5 * eps, 0.3):
+        assert O.soft_factor(r * r, eps, 1) == 1.0 / (r * r * r)
+    h = 1e-6
+    g = lambda r: r * O.soft_factor(r * r, eps, 1)  # force magnitude per unit mass
+    assert abs(g(eps * (1 - h)) - g(eps)) <= 3 * h * g(eps)  # continuous: changes at first order in h
+    slope_in = (g(eps) - g(eps * (1 - h))) / (eps * h)
+    slope_out = (g(eps * (1 + h)) - g(eps)) / (eps * h)
+    assert abs(slope_in - slope_out) <= 1e-4 * abs(slope_out)
+
+
+def test_k1_direct_sum_is_newtonian_beyond_eps_and_tree_converges():
+    """With K1 softening the direct Ewald sum of particles farther apart than
+    eps equals the unsoftened one (Plummer with negligible eps); and the tree
+    with K1 pairs and Newtonian expansions converges to the K1 direct sum as
+    theta -> 0."""
+    rng = np.random.default_rng(5)
+    x = np.array([[0.2, 0.3, 0.4], [0.45, 0.31, 0.38], [0.8, 0.1, 0.9]])
+    a1 = O.direct_forces(x, None, 0.05, table_n1=None, kernel=1)
+    a0 = O.direct_forces(x, None, 1e-9, table_n1=None, kernel=0)
+    assert np.abs(a1 - a0).max() <= 1e-12 * np.abs(a0).max()
+    x, eps = ics.config_small(4)
+    eps = 4 * eps  # enough pairs inside eps to matter
+    ad = O.direct_forces(x, None, eps, table_n1=128, kernel=1)
+    ap = O.direct_forces(x, None, eps, table_n1=128, kernel=0)
+    assert np.median(np.linalg.norm(ad - ap, axis=1) / np.linalg.norm(ad, axis=1)) > 1e-4  # the kernels differ
+    at = O.tree_forces(x, None, O.tree_params(eps, 1e-3, 2, ewald=5, kernel=1))
+    rel = np.linalg.norm(at - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    assert np.median(rel) <= 1e-4, np.median(rel)
+
+
+# ---- the dual (cell-group) form -----------------------------------------------------------
+def test_m2l_at_the_expansion_point_is_m2p_and_converges_at_its_order():
+    """The local expansion of a cell's field about z, evaluated at z, is the
+    cell's M2P there (same derivative orders); for a point mass at the cell
+    centre it is the Taylor series of the softened force to order p in the
+    offset d, so its error falls as |d|^(p+1)."""
+    rng = np.random.default_rng(9)
+    c = np.array([0.3, 0.5, 0.45])
+    pts = c + 0.02 * rng.standard_normal((40, 3))
+    m = rng.uniform(0.5, 1.5, 40)
+    z = np.array([0.62, 0.41, 0.5])
+    eps = 0.003
+    for p in range(5):
+        M = O.p2m(pts, m, c, p)
+        L = O.m2l(M, p, z - c, eps)
+        a = O.l2p(L, p, np.zeros(3))
+        ref = O.m2p(M, p, z - c, eps)
+        assert np.abs(a - ref).max() <= 1e-13 * np.abs(ref).max(), p
+    M = np.zeros(O.nmom(4))
+    M[0] = 1.0
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    for p in (2, 4):
+        Mp = M[:O.nmom(p)]
+        L = O.m2l(Mp, p, z - c, eps)
+        errs = []
+        for h in (0.02, 0.01):
+            x = z + h * u
+            r = c - x
+            exact = r / (r @ r + eps * eps) ** 1.5
+            errs.append(np.linalg.norm(O.l2p(L, p, x - z) - exact))
+        assert 2 ** (p + 1) * 0.8 <= errs[0] / errs[1] <= 2 ** (p + 1) * 1.25, (p, errs)
+
+
+def test_dual_tree_accuracy_and_work():
+    """The dual form on a clustered box (48^3 Zel'dovich + NFW haloes, theta
+    0.6, hexadecapole): cell-group local expansions replace most M2P
+    interactions (fewer than half remain), the force error against the
+    direct Ewald sum stays within 25 % of the M2P tree's, and the dual tree
+    converges to the direct sum as theta falls."""
+    import bench
+    x, _, eps = bench.workload(3, 48)
+    tg = ics.random_targets(len(x), 128, 5)
+    ad = O.direct_forces(x, None, eps, targets=tg, table_n1=128)
+    med = {}
+    for dual in (0, 1):
+        a, st = O.tree_forces(x, None, O.tree_params(eps, 0.6, 4, n_direct=8, ewald=4, ew_grid=5, dual=dual),
+                              targets=tg, return_stats=True)
+        med[dual] = np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1))
+        if dual:
+            m2p_dual, m2l = st["m2p"], st["m2l"]
+        else:
+            m2p_plain = st["m2p"]
+    assert m2l > 0 and m2p_dual < 0.5 * m2p_plain, (m2p_dual, m2p_plain, m2l)
+    assert med[1] <= 1.25 * med[0], med
+    errs = []
+    for th in (0.4, 0.2):
+        a = O.tree_forces(x, None, O.tree_params(eps, th, 4, n_direct=8, ewald=5, ew_grid=5, dual=1), targets=tg)
+        errs.append(np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)))
+    assert errs[1] < errs[0] < med[1], (errs, med)
