@@ -70,7 +70,28 @@ enum {
    * order 4; Newtonian kernel), i.e. the truncation error of the cell's
    * uniform share, which dominates the expansion error when the density is
    * nearly uniform.  Orders 1 and 3 reject the flag (NBODY_EINVAL). */
-  NBODY_FLAG_BACKGROUND = 4
+  NBODY_FLAG_BACKGROUND = 4,
+  /* softening by Dehnen's compensating K1 kernel (the kernel Sec. 2.1 names)
+   * instead of Plummer's: a direct pair at r = |d| gets a = m d f(r) with
+   * f = 1/r^3 from r >= eps on (exactly Newtonian) and, for x = r/eps < 1,
+   * f = (175/16 - (147/8) x^2 + (135/16) x^4)/eps^3, the enclosed mass over
+   * r^3 of the density 105/(64 pi eps^3) (1 - x^2)(5 - 9 x^2) (the kernel
+   * 1 - x^2 with the factor that makes its second moment vanish).  Cell
+   * expansions then use the Newtonian kernel 1/|R|.  The reverse mode
+   * (nbody_forces_vjp, nbody_kdk_adjoint) returns NBODY_ENOTSUP with it. */
+  NBODY_FLAG_K1 = 8,
+  /* dual (cell-group) interactions, the source-sink form of the traversal in
+   * Sec. 2.1: an accepted cell C of side s_C whose centre lies farther than
+   * (s_C + s_G)/theta from the centre z of the group's bounding box (s_G its
+   * largest side; integer units of 2^-23, the threshold floor(S^2/theta^2)
+   * in IEEE double) is not expanded at every sink: one local expansion per
+   * (cell, group), L_k = sum_n ((-1)^|n|/n!) M_n d^(n+k) g(z - c*) with
+   * 1 <= |k| and |n| + |k| <= order + 1 (the derivative orders of the
+   * expansion at a sink), is accumulated per group and evaluated once per
+   * sink, a_k = sum_{|m| <= order} (x - z)^m / m! L_(m + e_k).  Orders 1..4,
+   * NBODY_MIXED, not with NBODY_FLAG_BACKGROUND (else NBODY_ENOTSUP); the
+   * reverse mode returns NBODY_ENOTSUP with it. */
+  NBODY_FLAG_DUAL = 16
 };
 /* flags bits 8..11: walk launch variant + 1 to use instead of the autotuned
  * one (0 = autotune).  Mixed precision has variants 0..3 (one M2P per
@@ -103,11 +124,20 @@ typedef struct {
   int precision;    /* NBODY_MIXED (FP32 interactions, FP64 positions and
                        moments) or NBODY_FP64 (FP64 throughout) */
   int flags;        /* NBODY_FLAG_* */
+  double box_len;   /* side L of the periodic box (0 or 1: the unit box).
+                       Positions are then in [0, L), eps is in the same
+                       length unit, and accelerations (force VJPs) come back
+                       as G m / L^2 (G m / L^3) for the caller's masses, G = 1:
+                       the tree works on x / L.  The comoving integrator and
+                       its adjoint work in box units and return NBODY_ENOTSUP
+                       for a tree with L != 1 (nbody_kdk_step,
+                       nbody_kdk_multistep, nbody_assign_rungs,
+                       nbody_forces_active, nbody_kdk_adjoint(_acc)). */
 } nbody_params;
 
 /* Fills the defaults: eps = 1/(30*128), theta = 0.6, order = 4, n_leaf = 16,
  * n_group = 32, n_direct = 4, lmax = 21, ewald_order = 4, ewald_level = 3,
- * ewald_grid = 6, precision = NBODY_MIXED, flags = 0. */
+ * ewald_grid = 6, precision = NBODY_MIXED, flags = 0, box_len = 1. */
 void nbody_default_params(nbody_params *p);
 
 typedef struct {
@@ -158,6 +188,23 @@ int nbody_build_tree(const nbody_params *params, int64_t n, const double *pos_de
 int nbody_build_tree_batched(const nbody_params *params, int nbox, const int64_t *offsets_host,
                              const double *eps_host, const double *pos_dev,
                              const float *mass_dev, nbody_tree **tree, nbody_stream_t stream);
+
+/*
+ * Build and evaluate in one call: nbox independent periodic boxes of
+ * possibly different sizes, as nbody_build_tree_batched followed by
+ * nbody_forces (the batched realisations of Sec. 1's "multiple
+ * realisations", each a periodic box of Sec. 2.1).
+ *   box_len_host  nbox host doubles, the side L_b of box b (NULL: params->box_len
+ *                 for every box); box b's positions are in [0, L_b) and
+ *                 eps_host[b] (NULL: params->eps) is in the same unit
+ *   acc_dev       3*n FP32 accelerations (caller order), G m / L_b^2 for the
+ *                 caller's masses (NULL masses: 1/n_b per box)
+ *   tree          as nbody_build_tree (NULL or a handle to reuse)
+ * Errors as nbody_build_tree_batched and nbody_forces.
+ */
+int nbody_forces_batched(const nbody_params *params, int nbox, const int64_t *offsets_host,
+                         const double *box_len_host, const double *eps_host, const double *pos_dev,
+                         const float *mass_dev, float *acc_dev, nbody_tree **tree, nbody_stream_t stream);
 
 /*
  * Accelerations of all particles of the tree (Sec. 2.1: grouped tree walk with
@@ -296,6 +343,7 @@ typedef struct {
   int64_t walk_variant;    /* walk launch variant the autotuner chose for this tree's
                               precision and order on this device (-1: not tuned yet) */
   double walk_tune_ms[8];  /* each variant's time in the tuning run (0: not timed) */
+  double m2l_dual;         /* cell-group expansions of the dual form (NBODY_FLAG_DUAL), summed */
 } nbody_timing;
 int nbody_timing_read(nbody_tree *tree, nbody_timing *out, int reset);
 
@@ -312,6 +360,24 @@ int nbody_timing_read(nbody_tree *tree, nbody_timing *out, int reset);
 int nbody_cic_loss(const double *pos_dev, const float *mass_dev, int64_t n, int ng, double *grid_dev,
                    double *loss_dev, double *grad_dev, nbody_stream_t stream);
 
+/*
+ * Ends of the differentiable trajectory that are not tree work: its
+ * Zel'dovich starting state and the transpose of that map (the comoving
+ * growing mode of the integrator above, D = a, H0^2 = 8 pi / 3).
+ * nbody_zeldovich_state: x = q + a psi wrapped into [0, 1),
+ *   p = H0 a^(3/2) psi rounded to FP32.
+ *   q_dev, psi_dev  3*n FP64 lattice positions and displacement field (SoA)
+ *   pos_dev         3*n FP64 out;  mom_dev 3*n FP32 out
+ * nbody_zeldovich_vjp: the gradient of a loss with respect to psi from the
+ * cotangents of (x, p): dpsi = a lam_x + H0 a^(3/2) lam_p.
+ *   lam_pos_dev 3*n FP64, lam_mom_dev 3*n FP32, dpsi_dev 3*n FP64 out
+ * Both: a > 0, n >= 1, else NBODY_EINVAL; asynchronous on the stream.
+ */
+int nbody_zeldovich_state(int64_t n, const double *q_dev, const double *psi_dev, double a, double *pos_dev,
+                          float *mom_dev, nbody_stream_t stream);
+int nbody_zeldovich_vjp(int64_t n, double a, const double *lam_pos_dev, const float *lam_mom_dev,
+                        double *dpsi_dev, nbody_stream_t stream);
+
 /* Tree inspection (tests).  what: */
 enum {
   NBODY_EXPORT_SORTED_KEYS = 1, /* uint64 per particle, key order */
@@ -320,7 +386,14 @@ enum {
   NBODY_EXPORT_CELL_RANGE = 4,  /* int32 pairs (first particle, count) per cell */
   NBODY_EXPORT_CELL_LEVEL = 5,  /* int32 per cell */
   NBODY_EXPORT_MOMENTS = 6,     /* FP64 moments per cell, (order+1)(order+2)(order+3)/6 each */
-  NBODY_EXPORT_GROUPS = 7       /* int32 pairs (first particle, count) per group */
+  NBODY_EXPORT_GROUPS = 7,      /* int32 pairs (first particle, count) per group */
+  /* FP64 derivatives d^n phi~ (|n| <= ewald_order + 1, in the moments'
+   * multi-index order) of the image-field potential phi~ = phi_E + 1/|r| +
+   * (2 pi/3)|r|^2 at the lattice nodes r = (i, j, k) 2^-ewald_grid,
+   * 0 <= i, j, k < 2^(ewald_grid-1) + 2, node-major with k fastest: the
+   * per-device table the image field reads (NBODY_EINVAL when
+   * ewald_order is 0) */
+  NBODY_EXPORT_IMAGE_TABLE = 8
 };
 /* Number of elements of an export (cells, particles, groups), or < 0. */
 int64_t nbody_tree_count(const nbody_tree *tree, int what);
@@ -339,7 +412,9 @@ int nbody_tree_lookup(const nbody_tree *tree, const uint64_t *keys_dev, int64_t 
  * counterpart; this is the keys + sort phase of nbody_build_tree run on
  * scratch held in a file-scope device array of the library instead of
  * allocated memory.
- *   pos_dev       3*n FP64 positions (SoA), read only
+ *   pos_dev       3*n FP64 positions (SoA), read only; finite values outside
+ *                 [0,1) are wrapped, a NaN or Inf coordinate makes the call
+ *                 return NBODY_EINVAL (the outputs are then meaningless)
  *   n             1 .. 2^20 particles; larger n returns NBODY_ERANGE
  *   keys_out_dev  n uint64: the Morton keys in ascending order (equal keys in
  *                 input order), caller-allocated

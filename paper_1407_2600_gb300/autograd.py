@@ -9,25 +9,18 @@ checkpoint and the steps are reversed with nbody_kdk_adjoint_acc (chained:
 each call reuses the previous call's reverse product at its end state); the
 loss's gradient with respect to psi is a0 lam_x0 + H0 a0^(3/2) lam_p0.
 
-All arithmetic of the path runs in the CUDA library; torch supplies device
-memory, the stream and the autograd plumbing (the linear initial-state map
-and the final chain rule are elementwise tensor expressions).
+All arithmetic of the path runs in the CUDA library (the initial-state map
+and its transpose too: nbody_zeldovich_state, nbody_zeldovich_vjp); torch
+supplies device memory, the stream and the autograd plumbing.
 """
 from __future__ import annotations
-
-import math
 
 import torch
 
 from . import nbody as nb
 
-H0 = math.sqrt(8.0 * math.pi / 3.0)
-
-
 def zeldovich_state(q, psi, a):
-    x = torch.remainder(q + a * psi, 1.0)
-    p = (H0 * a ** 1.5 * psi).float()
-    return x.contiguous(), p.contiguous()
+    return nb.zeldovich_state(q, psi, a)
 
 
 def forward_steps(tree, x, p, acc, a_list, every):
@@ -90,8 +83,7 @@ class Trajectory(torch.autograd.Function):
         lx = (ctx.gx * gL).contiguous()
         lp = torch.zeros_like(ctx.ckpt[0][1])
         lx, lp = reverse_steps(tree, ctx.ckpt, a, lx, lp)
-        a0 = a[0]
-        dpsi = a0 * lx + H0 * a0 ** 1.5 * lp.double()
+        dpsi = nb.zeldovich_vjp(a[0], lx, lp)
         tree.close()
         return dpsi, None, None, None, None, None
 

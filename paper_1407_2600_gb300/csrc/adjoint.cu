@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
           const V4 sv = s_src[wid][q];
           const T dx = sv.x - xi, dy = sv.y - yi, dz = sv.z - zi;
           const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-          const T inv = nbody_rsqrt(r2);
+          const T inv = nbody_rsqrt_pair(r2);
           const T f = (inv * inv) * inv;
           const T g5 = f * (inv * inv) * (T)3;
           const T rl = fma(dx, lx, fma(dy, ly, dz * lz));

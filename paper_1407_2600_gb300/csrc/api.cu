@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -39,12 +40,12 @@ cudaError_t nb_group_runs(int ngroup, const int* pngroup, int4* gA, int4* gD, in
 cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, const int* pngroup,
                           int ls, const int* flag, const int* gid, int* gstart, const double* spos, int4* gA,
                           int4* gB, int4* gC, int4* gD, cudaStream_t s);
-int nb_walk_variant(bool fp64, int order, double* ms);
+int nb_walk_variant(bool fp64, bool dual, int order, double* ms);
 int nb_coef_stride(int order);
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const int4* cA, const int4* cB,
                       const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
                       uint32_t* uorder, uint32_t* uhist, int* urange, const uint16_t* cbox, const double* rho,
-                      SortScratch* sc, cudaStream_t s);
+                      float* mom32, SortScratch* sc, cudaStream_t s);
 cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, cudaStream_t s);
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, const int* hval,
@@ -54,7 +55,8 @@ int nb_walk_warps(bool fp64);
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
-                    int forced_variant, int mac_edge, int bg, cudaStream_t s);
+                    int forced_variant, int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
+                    cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -116,7 +118,10 @@ struct nbody_tree {
   int nbox = 0;
   int64_t n = 0;
   std::vector<int64_t> h_off;
-  std::vector<double> h_eps;
+  std::vector<double> h_eps;  // per box, in box units (the caller's eps / L)
+  std::vector<double> h_len;  // per box side length L in the caller's units
+  bool scaled = false;        // some L != 1: the tree works on pos / L (upos)
+  Buf upos, lscale;           // scaled positions; per box 1/L, 1/L^2, 1/L^3 (FP64)
   const double* pos = nullptr;
   const float* mass = nullptr;
   int device = 0, nsm = 0;
@@ -136,6 +141,7 @@ struct nbody_tree {
   int cell_cap = 0, group_cap = 0;
   int ncell = 0, max_level = 0;
   Buf cA, cB, ckey, cbox, hval, mom, uorder, coef, ukey, urng;
+  Buf mom32;  // FP32 cell-unit moments for the dual form
   uint64_t hcap = 0;
   // groups
   int ngroup = 0;
@@ -178,7 +184,7 @@ struct nbody_tree {
                   &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho, &act_s, &act_g, &rungc,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
-                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq};
+                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     delete aux;
@@ -250,7 +256,14 @@ int validate(const nbody_params* p) {
   }
   if (p->precision != NBODY_MIXED && p->precision != NBODY_FP64) return NBODY_EINVAL;
   if (((p->flags >> 8) & 0xf) > 4) return NBODY_EINVAL;  // walk variant override 0..3
+  if (p->flags &
+      ~(NBODY_FLAG_ASYNC | NBODY_FLAG_MAC_EDGE | NBODY_FLAG_BACKGROUND | NBODY_FLAG_K1 | NBODY_FLAG_DUAL | (0xf << 8)))
+    return NBODY_EINVAL;  // unknown flag bits
+  if ((p->flags & NBODY_FLAG_DUAL) &&
+      (p->order < 1 || p->precision != NBODY_MIXED || (p->flags & NBODY_FLAG_BACKGROUND)))
+    return NBODY_ENOTSUP;
   if ((p->flags & NBODY_FLAG_BACKGROUND) && (p->order == 1 || p->order == 3)) return NBODY_EINVAL;
+  if (!(p->box_len >= 0.0) || p->box_len > 1e300) return NBODY_EINVAL;  // 0 = unit box
   return NBODY_OK;
 }
 
@@ -304,6 +317,24 @@ __global__ void eps2_kernel(int nbox, const double* __restrict__ eps, float* __r
   }
 }
 
+// out[d n + i] = in[d n + i] * f[b] for every particle i of box b (offsets
+// off) and d = 0..2: positions to box units (f = 1/L) and accelerations or
+// force VJPs back to the caller's length unit (f = 1/L^2, 1/L^3)
+template <typename T>
+__global__ void box_scale_kernel(const int64_t* __restrict__ off, int nbox, int64_t n,
+                                 const double* __restrict__ f, const T* in, T* out) {
+  for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
+    const int64_t lo = off[b], hi = off[b + 1];
+    const double fb = f[b];
+    for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      out[i] = (T)(in[i] * fb);
+      out[n + i] = (T)(in[n + i] * fb);
+      out[2 * n + i] = (T)(in[2 * n + i] * fb);
+    }
+  }
+}
+
 // elementwise pieces of the KDK adjoint
 __global__ void drift_from_kernel(int64_t n3, const double* __restrict__ x0, const float* __restrict__ p, double d,
                                   double* __restrict__ x1) {
@@ -348,7 +379,7 @@ __global__ void differ_kernel(int64_t n3, const unsigned long long* __restrict__
 }
 
 __global__ void accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ tot) {
-  if (threadIdx.x < 4) tot[threadIdx.x] += c[threadIdx.x];
+  if (threadIdx.x < 5) tot[threadIdx.x] += c[threadIdx.x];
 }
 
 // ---- block steps ------------------------------------------------------------------
@@ -447,8 +478,33 @@ int upload_boxes(nbody_tree* t, cudaStream_t s) {
   double* e64 = (double*)((char*)t->eps2.p + ((4 * t->nbox + 15) & ~15));
   eps2_kernel<<<gridn(t->nbox, 128), 128, 0, s>>>(t->nbox, tmp.as<double>(), e32, e64);
   NB_CU(cudaGetLastError());
+  if (t->scaled) {
+    std::vector<double> f(3 * t->nbox);
+    for (int b = 0; b < t->nbox; b++) {
+      const double il = 1.0 / t->h_len[b];
+      f[b] = il;
+      f[t->nbox + b] = il * il;
+      f[2 * t->nbox + b] = il * il * il;
+    }
+    NB_CU(t->lscale.ensure(8 * f.size()));
+    NB_CU(cudaMemcpyAsync(t->lscale.p, f.data(), 8 * f.size(), cudaMemcpyHostToDevice, s));
+  }
   NB_CU(cudaStreamSynchronize(s));
   tmp.release();
+  return NBODY_OK;
+}
+
+// arrays of the caller's (3, n) layout scaled per box by lscale[k * nbox + b]
+// (k = 0: 1/L, 1: 1/L^2, 2: 1/L^3); a no-op for unit boxes
+template <typename T>
+int scale_boxes(const nbody_tree* t, int k, const T* in, T* out, cudaStream_t s) {
+  if (!t->scaled) return NBODY_OK;
+  const int64_t per = (t->n + t->nbox - 1) / t->nbox;
+  dim3 g((unsigned)std::min<int64_t>((per + 255) / 256, 1024), (unsigned)std::min(t->nbox, 65535));
+  box_scale_kernel<T><<<g, 256, 0, s>>>(t->off.as<int64_t>(), t->nbox, t->n, t->lscale.as<double>() + k * t->nbox,
+                                        in, out);
+  nb_launch_counter += 1;
+  NB_CU(cudaGetLastError());
   return NBODY_OK;
 }
 
@@ -472,6 +528,7 @@ int size_cells(nbody_tree* t, int cell_cap, int group_cap) {
   NB_CU(t->mom.ensure(8 * nc * nm));
   NB_CU(t->uorder.ensure(4 * nc));
   NB_CU(t->coef.ensure((fp64 ? 8 : 4) * nc * cs));
+  if (p.flags & NBODY_FLAG_DUAL) NB_CU(t->mom32.ensure(4 * nc * kDualStride));
   NB_CU(t->ukey.ensure(nc));
   NB_CU(t->urng.ensure(4 * (256 + 32)));
   uint64_t hc = 1;
@@ -616,7 +673,8 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   NB_CU(nb_upward(p.order, fp64, nc, totals, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),
                   t->smass.as<float>(), n, t->mom.as<double>(), t->coef.p, t->ukey.as<uint8_t>(),
                   t->uorder.as<uint32_t>(), t->urng.as<uint32_t>(), t->urng.as<int>() + 256,
-                  t->cbox.as<uint16_t>(), rho, &sc, s));
+                  t->cbox.as<uint16_t>(), rho, (p.flags & NBODY_FLAG_DUAL) ? t->mom32.as<float>() : nullptr, &sc,
+                  s));
   if (p.ewald_order > 0) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
     NB_CU(t->fm.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
@@ -695,7 +753,8 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
                 t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
                 t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0,
-                (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0, s));
+                (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0, (p.flags & NBODY_FLAG_K1) ? 1 : 0,
+                (p.flags & NBODY_FLAG_DUAL) ? 1 : 0, p.theta, t->mom32.as<float>(), group_level(p), s));
   if (timed) NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
@@ -712,7 +771,8 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
 // out = (d acc / d pos)^T lam for the tree as last built (forces refreshed if needed)
 int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   const nbody_params& p = t->prm;
-  if (p.precision != NBODY_MIXED || p.ewald_order > 4) return NBODY_ENOTSUP;
+  if (p.precision != NBODY_MIXED || p.ewald_order > 4 || (p.flags & (NBODY_FLAG_K1 | NBODY_FLAG_DUAL)))
+    return NBODY_ENOTSUP;
   const int64_t n = t->n;
   if (!t->field_valid) {
     int rc = field_impl(t, s);
@@ -747,7 +807,7 @@ int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
 }
 
 int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, const double* eps_host,
-              const double* pos, const float* mass, nbody_tree** tree, cudaStream_t s) {
+              const double* len_host, const double* pos, const float* mass, nbody_tree** tree, cudaStream_t s) {
   if (!tree || !pos || !offsets || nbox < 1 || nbox > NB_MAX_NBOX) return NBODY_EINVAL;
   int rc = validate(params);
   if (rc) return rc;
@@ -759,6 +819,9 @@ int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, cons
   if (eps_host)
     for (int b = 0; b < nbox; b++)
       if (!(eps_host[b] > 0.0)) return NBODY_EINVAL;
+  if (len_host)
+    for (int b = 0; b < nbox; b++)
+      if (!(len_host[b] > 0.0) || len_host[b] > 1e300) return NBODY_EINVAL;
   nbody_tree* t = *tree;
   bool fresh = false;
   if (!t) {
@@ -780,20 +843,34 @@ int make_tree(const nbody_params* params, int nbox, const int64_t* offsets, cons
     t->events = true;
   }
   std::vector<int64_t> off_new(offsets, offsets + nbox + 1);
-  std::vector<double> eps_new(nbox);
-  for (int b = 0; b < nbox; b++) eps_new[b] = eps_host ? eps_host[b] : params->eps;
+  std::vector<double> eps_new(nbox), len_new(nbox);
+  bool scaled = false;
+  for (int b = 0; b < nbox; b++) {
+    len_new[b] = len_host ? len_host[b] : (params->box_len > 0.0 ? params->box_len : 1.0);
+    scaled |= len_new[b] != 1.0;
+    eps_new[b] = (eps_host ? eps_host[b] : params->eps) / len_new[b];
+  }
   // a rebuild with the same boxes enqueues no host synchronisation (so that
   // it can be captured on reserved capacities)
-  const bool same_boxes = !fresh && t->off.p && t->nbox == nbox && t->h_off == off_new && t->h_eps == eps_new;
+  const bool same_boxes = !fresh && t->off.p && t->nbox == nbox && t->h_off == off_new && t->h_eps == eps_new &&
+                          t->h_len == len_new;
   t->prm = *params;
   t->nbox = nbox;
   t->n = n;
   t->pos = pos;
   t->mass = mass;
+  t->scaled = scaled;
   t->h_off.swap(off_new);
   t->h_eps.swap(eps_new);
+  t->h_len.swap(len_new);
   const long long l0 = nb_launch_counter;
   rc = same_boxes ? NBODY_OK : upload_boxes(t, s);
+  if (rc == NBODY_OK && scaled) {
+    // the tree works in box units: its positions are the caller's / L
+    rc = t->upos.ensure(24 * n) == cudaSuccess ? scale_boxes<double>(t, 0, pos, t->upos.as<double>(), s)
+                                               : NBODY_ENOMEM;
+    t->pos = t->upos.as<double>();
+  }
   // parameters may have changed the per-cell sizes of reserved buffers
   if (rc == NBODY_OK && t->fixed_cap) rc = size_cells(t, t->cell_cap, t->group_cap);
   if (rc == NBODY_OK) rc = build_impl(t, s);
@@ -826,19 +903,30 @@ void nbody_default_params(nbody_params* p) {
   p->ewald_grid = 6;
   p->precision = NBODY_MIXED;
   p->flags = 0;
+  p->box_len = 1.0;
 }
 
 int nbody_build_tree(const nbody_params* params, int64_t n, const double* pos_dev, const float* mass_dev,
                      nbody_tree** tree, nbody_stream_t stream) {
   if (n <= 0) return NBODY_EINVAL;
   int64_t off[2] = {0, n};
-  return make_tree(params, 1, off, nullptr, pos_dev, mass_dev, tree, (cudaStream_t)stream);
+  return make_tree(params, 1, off, nullptr, nullptr, pos_dev, mass_dev, tree, (cudaStream_t)stream);
 }
 
 int nbody_build_tree_batched(const nbody_params* params, int nbox, const int64_t* offsets_host,
                              const double* eps_host, const double* pos_dev, const float* mass_dev,
                              nbody_tree** tree, nbody_stream_t stream) {
-  return make_tree(params, nbox, offsets_host, eps_host, pos_dev, mass_dev, tree, (cudaStream_t)stream);
+  return make_tree(params, nbox, offsets_host, eps_host, nullptr, pos_dev, mass_dev, tree, (cudaStream_t)stream);
+}
+
+int nbody_forces_batched(const nbody_params* params, int nbox, const int64_t* offsets_host,
+                         const double* box_len_host, const double* eps_host, const double* pos_dev,
+                         const float* mass_dev, float* acc_dev, nbody_tree** tree, nbody_stream_t stream) {
+  if (!acc_dev) return NBODY_EINVAL;
+  int rc = make_tree(params, nbox, offsets_host, eps_host, box_len_host, pos_dev, mass_dev, tree,
+                     (cudaStream_t)stream);
+  if (rc) return rc;
+  return nbody_forces(*tree, acc_dev, nullptr, stream);
 }
 
 int nbody_forces64(nbody_tree* tree, double* acc_dev, nbody_stream_t stream) {
@@ -846,6 +934,7 @@ int nbody_forces64(nbody_tree* tree, double* acc_dev, nbody_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const long long l0 = nb_launch_counter;
   int rc = forces_impl(tree, nullptr, s, acc_dev);
+  if (rc == NBODY_OK) rc = scale_boxes<double>(tree, 1, acc_dev, acc_dev, s);
   tree->launches += nb_launch_counter - l0;
   if (rc) return rc;
   if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
@@ -857,6 +946,7 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_str
   cudaStream_t s = (cudaStream_t)stream;
   const long long l0 = nb_launch_counter;
   int rc = forces_impl(tree, acc_dev, s);
+  if (rc == NBODY_OK) rc = scale_boxes<float>(tree, 1, acc_dev, acc_dev, s);
   tree->launches += nb_launch_counter - l0;
   if (rc) return rc;
   if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
@@ -903,6 +993,7 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_str
 int nbody_kdk_step(nbody_tree* tree, double* pos_dev, float* mom_dev, float* acc_dev, double a0, double a1,
                    nbody_stream_t stream) {
   if (!tree || !pos_dev || !mom_dev || !acc_dev || !(a0 > 0.0) || !(a1 > 0.0)) return NBODY_EINVAL;
+  if (tree->scaled) return NBODY_ENOTSUP;  // the integrator works in box units
   cudaStream_t s = (cudaStream_t)stream;
   tree->pos = pos_dev;
   const double H0 = sqrt(8.0 * M_PI / 3.0);
@@ -948,6 +1039,7 @@ int forces_active_impl(nbody_tree* t, const int8_t* rung, int rmin, float* acc, 
 int nbody_assign_rungs(nbody_tree* t, const float* acc_dev, double eta, double dlna, int rmax, int8_t* rung_dev,
                        nbody_stream_t stream) {
   if (!t || !acc_dev || !rung_dev || !(eta > 0.0) || !(dlna > 0.0) || rmax < 0 || rmax > 7) return NBODY_EINVAL;
+  if (t->scaled) return NBODY_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   const double H0 = sqrt(8.0 * M_PI / 3.0);
   std::vector<double> c(t->nbox);
@@ -965,6 +1057,7 @@ int nbody_assign_rungs(nbody_tree* t, const float* acc_dev, double eta, double d
 
 int nbody_forces_active(nbody_tree* t, const int8_t* rung_dev, int rmin, float* acc_dev, nbody_stream_t stream) {
   if (!t || !rung_dev || !acc_dev || rmin < 0) return NBODY_EINVAL;
+  if (t->scaled) return NBODY_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   const long long l0 = nb_launch_counter;
   int rc = forces_active_impl(t, rung_dev, rmin, acc_dev, s);
@@ -978,6 +1071,7 @@ int nbody_kdk_multistep(nbody_tree* t, double* pos_dev, float* mom_dev, float* a
                         double a0, double a1, int rmax, nbody_stream_t stream) {
   if (!t || !pos_dev || !mom_dev || !acc_dev || !rung_dev || !(a0 > 0.0) || !(a1 > a0) || rmax < 0 || rmax > 7)
     return NBODY_EINVAL;
+  if (t->scaled) return NBODY_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   t->pos = pos_dev;
   const double H0 = sqrt(8.0 * M_PI / 3.0);
@@ -1028,6 +1122,7 @@ int nbody_forces_vjp(nbody_tree* t, const float* lam_dev, double* out_dev, nbody
   cudaStream_t s = (cudaStream_t)stream;
   const long long l0 = nb_launch_counter;
   int rc = vjp_impl(t, lam_dev, out_dev, s);
+  if (rc == NBODY_OK) rc = scale_boxes<double>(t, 2, out_dev, out_dev, s);
   t->launches += nb_launch_counter - l0;
   if (rc) return rc;
   if (t->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
@@ -1062,6 +1157,7 @@ int kdk_adjoint_impl(nbody_tree* t, const double* pos0, const float* mom0, const
                      cudaStream_t s) {
   if (!t || !pos0 || !mom0 || !lam_pos1 || !lam_mom1 || !lam_pos0 || !lam_mom0 || !(a0 > 0.0) || !(a1 > 0.0))
     return NBODY_EINVAL;
+  if (t->scaled || (t->prm.flags & (NBODY_FLAG_K1 | NBODY_FLAG_DUAL))) return NBODY_ENOTSUP;
   if (t->prm.precision != NBODY_MIXED || t->prm.ewald_order > 4) return NBODY_ENOTSUP;
   const long long l0 = nb_launch_counter;
   const int64_t n = t->n, n3 = 3 * n;
@@ -1175,8 +1271,17 @@ int nbody_kdk_adjoint_acc(nbody_tree* t, const double* pos0, const float* mom0, 
                           (cudaStream_t)stream);
 }
 
+// size of the image-field lattice table of the tree's parameters (elements)
+static int64_t image_table_count(const nbody_params& p) {
+  if (p.ewald_order <= 0) return NBODY_EINVAL;
+  const int64_t m = (1 << (p.ewald_grid - 1)) + 2;
+  const int P = p.ewald_order + 1;
+  return m * m * m * ((P + 1) * (P + 2) * (P + 3) / 6);
+}
+
 int64_t nbody_tree_count(const nbody_tree* t, int what) {
   if (!t) return NBODY_EINVAL;
+  if (what == NBODY_EXPORT_IMAGE_TABLE) return image_table_count(t->prm);
   int nc = 0, ng = 0;
   if (what != NBODY_EXPORT_SORTED_KEYS && what != NBODY_EXPORT_PERM) {
     int rc = host_counts(t, &nc, &ng);
@@ -1197,6 +1302,16 @@ int64_t nbody_tree_count(const nbody_tree* t, int what) {
 int nbody_tree_export(const nbody_tree* t, int what, void* dst, nbody_stream_t stream) {
   if (!t || !dst) return NBODY_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (what == NBODY_EXPORT_IMAGE_TABLE) {
+    const int64_t cnt = image_table_count(t->prm);
+    if (cnt < 0) return (int)cnt;
+    const double* t64 = nullptr;
+    const float* t32 = nullptr;
+    NB_CU(nb_phitilde_table(t->prm.ewald_grid, t->prm.ewald_order + 1, &t64, &t32, s));
+    NB_CU(cudaMemcpyAsync(dst, t64, 8 * cnt, cudaMemcpyDeviceToDevice, s));
+    NB_CU(cudaStreamSynchronize(s));
+    return NBODY_OK;
+  }
   const int nm = (t->prm.order + 1) * (t->prm.order + 2) * (t->prm.order + 3) / 6;
   int nc = 0, ng = 0;
   int rc = host_counts(t, &nc, &ng);
@@ -1264,16 +1379,18 @@ int nbody_timing_read(nbody_tree* t, nbody_timing* out, int reset) {
   out->builds = nb;
   out->evaluations = nf;
   out->launches = t->launches;
-  out->walk_variant = nb_walk_variant(t->prm.precision == NBODY_FP64, t->prm.order, out->walk_tune_ms);
+  out->walk_variant = nb_walk_variant(t->prm.precision == NBODY_FP64, (t->prm.flags & NBODY_FLAG_DUAL) != 0,
+                                      t->prm.order, out->walk_tune_ms);
   out->adjoint_steps = t->adj_steps;
   out->adjoint_reused = t->adj_reused;
   if (t->tot.p) {
-    unsigned long long c[4] = {0, 0, 0, 0};
+    unsigned long long c[5] = {0, 0, 0, 0, 0};
     NB_CU(cudaMemcpy(c, t->tot.p, sizeof(c), cudaMemcpyDeviceToHost));
     out->p2p = (double)c[0];
     out->m2p = (double)c[1];
     out->m2l = (double)c[2];
     out->decision_hash = c[3];
+    out->m2l_dual = (double)c[4];
   }
   if (reset) {
     t->nb_log = 0;

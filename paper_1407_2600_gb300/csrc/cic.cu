@@ -67,6 +67,26 @@ __global__ void cic_grad_kernel(int64_t n, const double* __restrict__ pos, const
   }
 }
 
+// Zel'dovich state of the trajectory's start: x = q + a psi wrapped into
+// [0, 1), p = H0 a^(3/2) psi (growing mode of the comoving equations, D = a)
+__global__ void zeldovich_state_kernel(int64_t n3, const double* __restrict__ q, const double* __restrict__ psi,
+                                       double a, double pa, double* __restrict__ pos, float* __restrict__ mom) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double u = psi[i];
+    double x = __dadd_rn(q[i], __dmul_rn(a, u));  // rounded as written, no contraction
+    x -= floor(x);
+    pos[i] = x < 1.0 ? x : 0.0;
+    mom[i] = (float)(pa * u);
+  }
+}
+
+// its transpose: d psi = a lam_x + H0 a^(3/2) lam_p (the wrap has unit slope)
+__global__ void zeldovich_vjp_kernel(int64_t n3, double a, double pa, const double* __restrict__ lx,
+                                     const float* __restrict__ lp, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __dadd_rn(__dmul_rn(a, lx[i]), __dmul_rn(pa, (double)lp[i]));
+}
+
 int gridc(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -90,5 +110,25 @@ extern "C" int nbody_cic_loss(const double* pos_dev, const float* mass_dev, int6
     cic_grad_kernel<<<gridc(n, 256), 256, 0, s>>>(n, pos_dev, mass_dev, ng, grid_dev, grad_dev);
     nb_launch_counter += 1;
   }
+  return cudaGetLastError() == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
+}
+
+extern "C" int nbody_zeldovich_state(int64_t n, const double* q_dev, const double* psi_dev, double a,
+                                     double* pos_dev, float* mom_dev, nbody_stream_t stream) {
+  if (!q_dev || !psi_dev || !pos_dev || !mom_dev || n <= 0 || !(a > 0.0) || !(a < 1e300)) return NBODY_EINVAL;
+  const double pa = sqrt(8.0 * M_PI / 3.0) * a * sqrt(a);
+  zeldovich_state_kernel<<<gridc(3 * n, 256), 256, 0, (cudaStream_t)stream>>>(3 * n, q_dev, psi_dev, a, pa,
+                                                                               pos_dev, mom_dev);
+  nb_launch_counter += 1;
+  return cudaGetLastError() == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
+}
+
+extern "C" int nbody_zeldovich_vjp(int64_t n, double a, const double* lam_pos_dev, const float* lam_mom_dev,
+                                   double* dpsi_dev, nbody_stream_t stream) {
+  if (!lam_pos_dev || !lam_mom_dev || !dpsi_dev || n <= 0 || !(a > 0.0) || !(a < 1e300)) return NBODY_EINVAL;
+  const double pa = sqrt(8.0 * M_PI / 3.0) * a * sqrt(a);
+  zeldovich_vjp_kernel<<<gridc(3 * n, 256), 256, 0, (cudaStream_t)stream>>>(3 * n, a, pa, lam_pos_dev, lam_mom_dev,
+                                                                             dpsi_dev);
+  nb_launch_counter += 1;
   return cudaGetLastError() == cudaSuccess ? NBODY_OK : NBODY_ECUDA;
 }

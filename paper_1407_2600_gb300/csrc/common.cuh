@@ -12,6 +12,8 @@
 #define NB_MAX_NBOX 65535
 
 // device status bits (OR-ed into the tree's status word)
+// floats per cell of the FP32 cell-unit moments of the dual form (orders <= 4)
+constexpr int kDualStride = 36;
 #define NB_ST_OVERFLOW 1u
 #define NB_ST_TIMEOUT 2u
 #define NB_ST_BADINPUT 4u
@@ -19,8 +21,26 @@
 // bounded spin limit for decoupled look-back waits
 #define NB_SPIN_LIMIT (1 << 22)
 
-__device__ __forceinline__ float nbody_rsqrt(float x) { return rsqrtf(x); }
+// FP32 1/sqrt(s): the hardware approximation (good to about 2 ulp) refined
+// by one Newton-Raphson step r + r (1 - s r^2)/2 whose residual is formed
+// exactly, r^2 = p + p_lo being an exact FMA two-product, so that only the
+// final rounding is left.  Interaction terms of the walk inherit the
+// reciprocal's error several times over (r^3 for the monopole, r^11 at
+// hexadecapole order), and on near-uniform boxes far cells' terms cancel to
+// a force a thousand times smaller than their sum.  s > 0 and finite.
+__device__ __forceinline__ float nbody_rsqrt(float s) {
+  const float r = rsqrtf(s);
+  const float p = r * r;
+  const float plo = fmaf(r, r, -p);
+  const float e = fmaf(-s, plo, fmaf(-s, p, 1.0f));
+  return fmaf(0.5f * r, e, r);
+}
 __device__ __forceinline__ double nbody_rsqrt(double x) { return rsqrt(x); }
+// the hardware approximation alone, for particle-particle terms: each pair's
+// term is small next to the sum it joins, so the last ulp of 1/sqrt does not
+// show in the result, while one more instruction per pair would
+__device__ __forceinline__ float nbody_rsqrt_pair(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double nbody_rsqrt_pair(double x) { return rsqrt(x); }
 
 struct __align__(32) dbl4 {
   double x, y, z, w;

@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import math
 import os
+import re
 import sys
 from itertools import product
 
@@ -301,6 +302,97 @@ def emit_m2l(pe):
         L.append("  a%s = %s;" % (ax, expr))
     L.append("}")
     return "\n".join(L)
+
+
+def emit_dtensor(P):
+    """D[t] = d^t g(R) for |t| <= P, g = (|R|^2 + eps^2)^-1/2, by the
+    Cartesian recurrence on the radial ladder g_j = ((1/r) d/dr)^j g:
+    T^(j)_(n + e_a) = R_a T^(j+1)_n + n_a T^(j+1)_(n - e_a), T^(j)_0 = g_j."""
+    mP = multi(P)
+    mi = {m: i for i, m in enumerate(mP)}
+    L = []
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ void dtensor_p%d(T Rx, T Ry, T Rz, T eps2, T* __restrict__ D) {" % P)
+    L.append("  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));")
+    L.append("  const T g0_0 = nbody_rsqrt(s);")
+    L.append("  const T is = g0_0 * g0_0;")
+    for j in range(1, P + 1):
+        L.append("  const T g%d_0 = g%d_0 * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
+    R = "RxRyRz"
+    for t, n in enumerate(mP):
+        if t == 0:
+            continue
+        o = sum(n)
+        a = next(d for d in range(3) if n[d] > 0)
+        m1 = list(n)
+        m1[a] -= 1
+        d1 = mi[tuple(m1)]
+        d2 = None
+        if n[a] >= 2:
+            m2 = list(m1)
+            m2[a] -= 1
+            d2 = mi[tuple(m2)]
+        for j in range(P - o + 1):
+            e = "%s * g%d_%d" % (R[2 * a:2 * a + 2], j + 1, d1)
+            if d2 is not None:
+                e = "fma(T(%d), g%d_%d, %s)" % (n[a] - 1, j + 1, d2, e)
+            L.append("  const T g%d_%d = %s;" % (j, t, e))
+    for t in range(len(mP)):
+        L.append("  D[%d] = g0_%d;" % (t, t))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_m2l_red(p):
+    """The dual form's cell-group M2L, one local coefficient at a time:
+    v_t = sum_n (-1)^|n|/n! M_n D_(t+n), 1 <= |t|, |t| + |n| <= p + 1, each
+    handed to red(t - 1, |t|, v_t) as soon as it is formed (so that only
+    the moments, the derivatives and one coefficient are live).  M is read
+    through M[u] (an accessor)."""
+    P = p + 1
+    mP = multi(P)
+    mi = {m: i for i, m in enumerate(mP)}
+    me = multi(p)
+    L = []
+    L.append("template <typename T, typename MA, typename Red>")
+    L.append("__device__ __forceinline__ void m2l_red_p%d(const MA& M, const T* __restrict__ D, Red&& red) {" % p)
+    for t, m in enumerate(mP):
+        if t == 0:
+            continue
+        expr = None
+        for u, n in enumerate(me):
+            if sum(m) + sum(n) > P:
+                continue
+            c = (-1.0 if sum(n) % 2 else 1.0) / (math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2]))
+            k = mi[(m[0] + n[0], m[1] + n[1], m[2] + n[2])]
+            mm = "M[%d]" % u if c == 1.0 else ("(-M[%d])" % u if c == -1.0 else "(M[%d] * T(%.17g))" % (u, c))
+            expr = "%s * D[%d]" % (mm, k) if expr is None else "fma(%s, D[%d], %s)" % (mm, k, expr)
+        L.append("  red(%d, %d, %s);" % (t - 1, sum(m), expr))
+    L.append("}")
+    return "\n".join(L)
+
+
+def _code_flops(code):
+    """Flops of generated straight-line code: FMA = 2, a product = 1, rsqrt = 1."""
+    return 2 * code.count("fma(") + len(re.findall(r" \* ", code)) + code.count("nbody_rsqrt(")
+
+
+def m2l_dual_flop_count(p):
+    """Flops of one cell-group expansion of the dual form at order p: the
+    softened derivative tensor to order p + 1 (with its negation), the
+    generated contraction, and per local coefficient one product taking it to
+    the group's unit and one addition joining it to the group's sum."""
+    nl = len(multi(p + 1)) - 1
+    return _code_flops(emit_dtensor(p + 1)) + len(multi(p + 1)) + _code_flops(emit_m2l_red(p)) + 2 * nl
+
+
+def l2p_flop_count(p):
+    """Flops of the group's local expansion evaluated at one sink (the
+    image-field L2P of order p, the offset to the group's unit, the unit
+    factor and the sum into the acceleration)."""
+    code = emit_m2l(p)
+    code = code[code.index("l2p_pe"):]
+    return _code_flops(code) + 3 * 2 + 3 + 3 * 4
 
 
 def emit_p2m(p):
@@ -585,6 +677,11 @@ def generate():
     for pe in range(1, 6):
         out.append("constexpr int kNL%d = %d;  // local coefficients, image-field order %d" % (pe, len(multi(pe + 1)) - 1, pe))
         out.append(emit_m2l(pe))
+        out.append("")
+    for p in range(1, 5):
+        out.append(emit_dtensor(p + 1))
+        out.append("")
+        out.append(emit_m2l_red(p))
         out.append("")
     out.append("__device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {")
     out.append("  return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));")

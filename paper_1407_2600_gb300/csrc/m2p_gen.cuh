@@ -2156,6 +2156,530 @@ __device__ __forceinline__ void l2p_pe5(const T* __restrict__ Lc, T dx, T dy, T 
   az = fma(-q55, Lc[82], fma(-q54, Lc[81], fma(-q53, Lc[80], fma(-q52, Lc[79], fma(-q51, Lc[78], fma(-q50, Lc[77], fma(-q49, Lc[75], fma(-q48, Lc[74], fma(-q47, Lc[73], fma(-q46, Lc[72], fma(-q45, Lc[71], fma(-q44, Lc[69], fma(-q43, Lc[68], fma(-q42, Lc[67], fma(-q41, Lc[66], fma(-q40, Lc[64], fma(-q39, Lc[63], fma(-q38, Lc[62], fma(-q37, Lc[60], fma(-q36, Lc[59], fma(-q35, Lc[57], fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))))))))))))))))))))))))))))))))))))))));
 }
 
+template <typename T>
+__device__ __forceinline__ void dtensor_p2(T Rx, T Ry, T Rz, T eps2, T* __restrict__ D) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T g0_0 = nbody_rsqrt(s);
+  const T is = g0_0 * g0_0;
+  const T g1_0 = g0_0 * (T(-1) * is);
+  const T g2_0 = g1_0 * (T(-3) * is);
+  const T g0_1 = Rx * g1_0;
+  const T g1_1 = Rx * g2_0;
+  const T g0_2 = Ry * g1_0;
+  const T g1_2 = Ry * g2_0;
+  const T g0_3 = Rz * g1_0;
+  const T g1_3 = Rz * g2_0;
+  const T g0_4 = fma(T(1), g1_0, Rx * g1_1);
+  const T g0_5 = Rx * g1_2;
+  const T g0_6 = Rx * g1_3;
+  const T g0_7 = fma(T(1), g1_0, Ry * g1_2);
+  const T g0_8 = Ry * g1_3;
+  const T g0_9 = fma(T(1), g1_0, Rz * g1_3);
+  D[0] = g0_0;
+  D[1] = g0_1;
+  D[2] = g0_2;
+  D[3] = g0_3;
+  D[4] = g0_4;
+  D[5] = g0_5;
+  D[6] = g0_6;
+  D[7] = g0_7;
+  D[8] = g0_8;
+  D[9] = g0_9;
+}
+
+template <typename T, typename MA, typename Red>
+__device__ __forceinline__ void m2l_red_p1(const MA& M, const T* __restrict__ D, Red&& red) {
+  red(0, 1, fma((-M[3]), D[6], fma((-M[2]), D[5], fma((-M[1]), D[4], M[0] * D[1]))));
+  red(1, 1, fma((-M[3]), D[8], fma((-M[2]), D[7], fma((-M[1]), D[5], M[0] * D[2]))));
+  red(2, 1, fma((-M[3]), D[9], fma((-M[2]), D[8], fma((-M[1]), D[6], M[0] * D[3]))));
+  red(3, 2, M[0] * D[4]);
+  red(4, 2, M[0] * D[5]);
+  red(5, 2, M[0] * D[6]);
+  red(6, 2, M[0] * D[7]);
+  red(7, 2, M[0] * D[8]);
+  red(8, 2, M[0] * D[9]);
+}
+
+template <typename T>
+__device__ __forceinline__ void dtensor_p3(T Rx, T Ry, T Rz, T eps2, T* __restrict__ D) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T g0_0 = nbody_rsqrt(s);
+  const T is = g0_0 * g0_0;
+  const T g1_0 = g0_0 * (T(-1) * is);
+  const T g2_0 = g1_0 * (T(-3) * is);
+  const T g3_0 = g2_0 * (T(-5) * is);
+  const T g0_1 = Rx * g1_0;
+  const T g1_1 = Rx * g2_0;
+  const T g2_1 = Rx * g3_0;
+  const T g0_2 = Ry * g1_0;
+  const T g1_2 = Ry * g2_0;
+  const T g2_2 = Ry * g3_0;
+  const T g0_3 = Rz * g1_0;
+  const T g1_3 = Rz * g2_0;
+  const T g2_3 = Rz * g3_0;
+  const T g0_4 = fma(T(1), g1_0, Rx * g1_1);
+  const T g1_4 = fma(T(1), g2_0, Rx * g2_1);
+  const T g0_5 = Rx * g1_2;
+  const T g1_5 = Rx * g2_2;
+  const T g0_6 = Rx * g1_3;
+  const T g1_6 = Rx * g2_3;
+  const T g0_7 = fma(T(1), g1_0, Ry * g1_2);
+  const T g1_7 = fma(T(1), g2_0, Ry * g2_2);
+  const T g0_8 = Ry * g1_3;
+  const T g1_8 = Ry * g2_3;
+  const T g0_9 = fma(T(1), g1_0, Rz * g1_3);
+  const T g1_9 = fma(T(1), g2_0, Rz * g2_3);
+  const T g0_10 = fma(T(2), g1_1, Rx * g1_4);
+  const T g0_11 = fma(T(1), g1_2, Rx * g1_5);
+  const T g0_12 = fma(T(1), g1_3, Rx * g1_6);
+  const T g0_13 = Rx * g1_7;
+  const T g0_14 = Rx * g1_8;
+  const T g0_15 = Rx * g1_9;
+  const T g0_16 = fma(T(2), g1_2, Ry * g1_7);
+  const T g0_17 = fma(T(1), g1_3, Ry * g1_8);
+  const T g0_18 = Ry * g1_9;
+  const T g0_19 = fma(T(2), g1_3, Rz * g1_9);
+  D[0] = g0_0;
+  D[1] = g0_1;
+  D[2] = g0_2;
+  D[3] = g0_3;
+  D[4] = g0_4;
+  D[5] = g0_5;
+  D[6] = g0_6;
+  D[7] = g0_7;
+  D[8] = g0_8;
+  D[9] = g0_9;
+  D[10] = g0_10;
+  D[11] = g0_11;
+  D[12] = g0_12;
+  D[13] = g0_13;
+  D[14] = g0_14;
+  D[15] = g0_15;
+  D[16] = g0_16;
+  D[17] = g0_17;
+  D[18] = g0_18;
+  D[19] = g0_19;
+}
+
+template <typename T, typename MA, typename Red>
+__device__ __forceinline__ void m2l_red_p2(const MA& M, const T* __restrict__ D, Red&& red) {
+  red(0, 1, fma((M[9] * T(0.5)), D[15], fma(M[8], D[14], fma((M[7] * T(0.5)), D[13], fma(M[6], D[12], fma(M[5], D[11], fma((M[4] * T(0.5)), D[10], fma((-M[3]), D[6], fma((-M[2]), D[5], fma((-M[1]), D[4], M[0] * D[1]))))))))));
+  red(1, 1, fma((M[9] * T(0.5)), D[18], fma(M[8], D[17], fma((M[7] * T(0.5)), D[16], fma(M[6], D[14], fma(M[5], D[13], fma((M[4] * T(0.5)), D[11], fma((-M[3]), D[8], fma((-M[2]), D[7], fma((-M[1]), D[5], M[0] * D[2]))))))))));
+  red(2, 1, fma((M[9] * T(0.5)), D[19], fma(M[8], D[18], fma((M[7] * T(0.5)), D[17], fma(M[6], D[15], fma(M[5], D[14], fma((M[4] * T(0.5)), D[12], fma((-M[3]), D[9], fma((-M[2]), D[8], fma((-M[1]), D[6], M[0] * D[3]))))))))));
+  red(3, 2, fma((-M[3]), D[12], fma((-M[2]), D[11], fma((-M[1]), D[10], M[0] * D[4]))));
+  red(4, 2, fma((-M[3]), D[14], fma((-M[2]), D[13], fma((-M[1]), D[11], M[0] * D[5]))));
+  red(5, 2, fma((-M[3]), D[15], fma((-M[2]), D[14], fma((-M[1]), D[12], M[0] * D[6]))));
+  red(6, 2, fma((-M[3]), D[17], fma((-M[2]), D[16], fma((-M[1]), D[13], M[0] * D[7]))));
+  red(7, 2, fma((-M[3]), D[18], fma((-M[2]), D[17], fma((-M[1]), D[14], M[0] * D[8]))));
+  red(8, 2, fma((-M[3]), D[19], fma((-M[2]), D[18], fma((-M[1]), D[15], M[0] * D[9]))));
+  red(9, 3, M[0] * D[10]);
+  red(10, 3, M[0] * D[11]);
+  red(11, 3, M[0] * D[12]);
+  red(12, 3, M[0] * D[13]);
+  red(13, 3, M[0] * D[14]);
+  red(14, 3, M[0] * D[15]);
+  red(15, 3, M[0] * D[16]);
+  red(16, 3, M[0] * D[17]);
+  red(17, 3, M[0] * D[18]);
+  red(18, 3, M[0] * D[19]);
+}
+
+template <typename T>
+__device__ __forceinline__ void dtensor_p4(T Rx, T Ry, T Rz, T eps2, T* __restrict__ D) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T g0_0 = nbody_rsqrt(s);
+  const T is = g0_0 * g0_0;
+  const T g1_0 = g0_0 * (T(-1) * is);
+  const T g2_0 = g1_0 * (T(-3) * is);
+  const T g3_0 = g2_0 * (T(-5) * is);
+  const T g4_0 = g3_0 * (T(-7) * is);
+  const T g0_1 = Rx * g1_0;
+  const T g1_1 = Rx * g2_0;
+  const T g2_1 = Rx * g3_0;
+  const T g3_1 = Rx * g4_0;
+  const T g0_2 = Ry * g1_0;
+  const T g1_2 = Ry * g2_0;
+  const T g2_2 = Ry * g3_0;
+  const T g3_2 = Ry * g4_0;
+  const T g0_3 = Rz * g1_0;
+  const T g1_3 = Rz * g2_0;
+  const T g2_3 = Rz * g3_0;
+  const T g3_3 = Rz * g4_0;
+  const T g0_4 = fma(T(1), g1_0, Rx * g1_1);
+  const T g1_4 = fma(T(1), g2_0, Rx * g2_1);
+  const T g2_4 = fma(T(1), g3_0, Rx * g3_1);
+  const T g0_5 = Rx * g1_2;
+  const T g1_5 = Rx * g2_2;
+  const T g2_5 = Rx * g3_2;
+  const T g0_6 = Rx * g1_3;
+  const T g1_6 = Rx * g2_3;
+  const T g2_6 = Rx * g3_3;
+  const T g0_7 = fma(T(1), g1_0, Ry * g1_2);
+  const T g1_7 = fma(T(1), g2_0, Ry * g2_2);
+  const T g2_7 = fma(T(1), g3_0, Ry * g3_2);
+  const T g0_8 = Ry * g1_3;
+  const T g1_8 = Ry * g2_3;
+  const T g2_8 = Ry * g3_3;
+  const T g0_9 = fma(T(1), g1_0, Rz * g1_3);
+  const T g1_9 = fma(T(1), g2_0, Rz * g2_3);
+  const T g2_9 = fma(T(1), g3_0, Rz * g3_3);
+  const T g0_10 = fma(T(2), g1_1, Rx * g1_4);
+  const T g1_10 = fma(T(2), g2_1, Rx * g2_4);
+  const T g0_11 = fma(T(1), g1_2, Rx * g1_5);
+  const T g1_11 = fma(T(1), g2_2, Rx * g2_5);
+  const T g0_12 = fma(T(1), g1_3, Rx * g1_6);
+  const T g1_12 = fma(T(1), g2_3, Rx * g2_6);
+  const T g0_13 = Rx * g1_7;
+  const T g1_13 = Rx * g2_7;
+  const T g0_14 = Rx * g1_8;
+  const T g1_14 = Rx * g2_8;
+  const T g0_15 = Rx * g1_9;
+  const T g1_15 = Rx * g2_9;
+  const T g0_16 = fma(T(2), g1_2, Ry * g1_7);
+  const T g1_16 = fma(T(2), g2_2, Ry * g2_7);
+  const T g0_17 = fma(T(1), g1_3, Ry * g1_8);
+  const T g1_17 = fma(T(1), g2_3, Ry * g2_8);
+  const T g0_18 = Ry * g1_9;
+  const T g1_18 = Ry * g2_9;
+  const T g0_19 = fma(T(2), g1_3, Rz * g1_9);
+  const T g1_19 = fma(T(2), g2_3, Rz * g2_9);
+  const T g0_20 = fma(T(3), g1_4, Rx * g1_10);
+  const T g0_21 = fma(T(2), g1_5, Rx * g1_11);
+  const T g0_22 = fma(T(2), g1_6, Rx * g1_12);
+  const T g0_23 = fma(T(1), g1_7, Rx * g1_13);
+  const T g0_24 = fma(T(1), g1_8, Rx * g1_14);
+  const T g0_25 = fma(T(1), g1_9, Rx * g1_15);
+  const T g0_26 = Rx * g1_16;
+  const T g0_27 = Rx * g1_17;
+  const T g0_28 = Rx * g1_18;
+  const T g0_29 = Rx * g1_19;
+  const T g0_30 = fma(T(3), g1_7, Ry * g1_16);
+  const T g0_31 = fma(T(2), g1_8, Ry * g1_17);
+  const T g0_32 = fma(T(1), g1_9, Ry * g1_18);
+  const T g0_33 = Ry * g1_19;
+  const T g0_34 = fma(T(3), g1_9, Rz * g1_19);
+  D[0] = g0_0;
+  D[1] = g0_1;
+  D[2] = g0_2;
+  D[3] = g0_3;
+  D[4] = g0_4;
+  D[5] = g0_5;
+  D[6] = g0_6;
+  D[7] = g0_7;
+  D[8] = g0_8;
+  D[9] = g0_9;
+  D[10] = g0_10;
+  D[11] = g0_11;
+  D[12] = g0_12;
+  D[13] = g0_13;
+  D[14] = g0_14;
+  D[15] = g0_15;
+  D[16] = g0_16;
+  D[17] = g0_17;
+  D[18] = g0_18;
+  D[19] = g0_19;
+  D[20] = g0_20;
+  D[21] = g0_21;
+  D[22] = g0_22;
+  D[23] = g0_23;
+  D[24] = g0_24;
+  D[25] = g0_25;
+  D[26] = g0_26;
+  D[27] = g0_27;
+  D[28] = g0_28;
+  D[29] = g0_29;
+  D[30] = g0_30;
+  D[31] = g0_31;
+  D[32] = g0_32;
+  D[33] = g0_33;
+  D[34] = g0_34;
+}
+
+template <typename T, typename MA, typename Red>
+__device__ __forceinline__ void m2l_red_p3(const MA& M, const T* __restrict__ D, Red&& red) {
+  red(0, 1, fma((M[19] * T(-0.16666666666666666)), D[29], fma((M[18] * T(-0.5)), D[28], fma((M[17] * T(-0.5)), D[27], fma((M[16] * T(-0.16666666666666666)), D[26], fma((M[15] * T(-0.5)), D[25], fma((-M[14]), D[24], fma((M[13] * T(-0.5)), D[23], fma((M[12] * T(-0.5)), D[22], fma((M[11] * T(-0.5)), D[21], fma((M[10] * T(-0.16666666666666666)), D[20], fma((M[9] * T(0.5)), D[15], fma(M[8], D[14], fma((M[7] * T(0.5)), D[13], fma(M[6], D[12], fma(M[5], D[11], fma((M[4] * T(0.5)), D[10], fma((-M[3]), D[6], fma((-M[2]), D[5], fma((-M[1]), D[4], M[0] * D[1]))))))))))))))))))));
+  red(1, 1, fma((M[19] * T(-0.16666666666666666)), D[33], fma((M[18] * T(-0.5)), D[32], fma((M[17] * T(-0.5)), D[31], fma((M[16] * T(-0.16666666666666666)), D[30], fma((M[15] * T(-0.5)), D[28], fma((-M[14]), D[27], fma((M[13] * T(-0.5)), D[26], fma((M[12] * T(-0.5)), D[24], fma((M[11] * T(-0.5)), D[23], fma((M[10] * T(-0.16666666666666666)), D[21], fma((M[9] * T(0.5)), D[18], fma(M[8], D[17], fma((M[7] * T(0.5)), D[16], fma(M[6], D[14], fma(M[5], D[13], fma((M[4] * T(0.5)), D[11], fma((-M[3]), D[8], fma((-M[2]), D[7], fma((-M[1]), D[5], M[0] * D[2]))))))))))))))))))));
+  red(2, 1, fma((M[19] * T(-0.16666666666666666)), D[34], fma((M[18] * T(-0.5)), D[33], fma((M[17] * T(-0.5)), D[32], fma((M[16] * T(-0.16666666666666666)), D[31], fma((M[15] * T(-0.5)), D[29], fma((-M[14]), D[28], fma((M[13] * T(-0.5)), D[27], fma((M[12] * T(-0.5)), D[25], fma((M[11] * T(-0.5)), D[24], fma((M[10] * T(-0.16666666666666666)), D[22], fma((M[9] * T(0.5)), D[19], fma(M[8], D[18], fma((M[7] * T(0.5)), D[17], fma(M[6], D[15], fma(M[5], D[14], fma((M[4] * T(0.5)), D[12], fma((-M[3]), D[9], fma((-M[2]), D[8], fma((-M[1]), D[6], M[0] * D[3]))))))))))))))))))));
+  red(3, 2, fma((M[9] * T(0.5)), D[25], fma(M[8], D[24], fma((M[7] * T(0.5)), D[23], fma(M[6], D[22], fma(M[5], D[21], fma((M[4] * T(0.5)), D[20], fma((-M[3]), D[12], fma((-M[2]), D[11], fma((-M[1]), D[10], M[0] * D[4]))))))))));
+  red(4, 2, fma((M[9] * T(0.5)), D[28], fma(M[8], D[27], fma((M[7] * T(0.5)), D[26], fma(M[6], D[24], fma(M[5], D[23], fma((M[4] * T(0.5)), D[21], fma((-M[3]), D[14], fma((-M[2]), D[13], fma((-M[1]), D[11], M[0] * D[5]))))))))));
+  red(5, 2, fma((M[9] * T(0.5)), D[29], fma(M[8], D[28], fma((M[7] * T(0.5)), D[27], fma(M[6], D[25], fma(M[5], D[24], fma((M[4] * T(0.5)), D[22], fma((-M[3]), D[15], fma((-M[2]), D[14], fma((-M[1]), D[12], M[0] * D[6]))))))))));
+  red(6, 2, fma((M[9] * T(0.5)), D[32], fma(M[8], D[31], fma((M[7] * T(0.5)), D[30], fma(M[6], D[27], fma(M[5], D[26], fma((M[4] * T(0.5)), D[23], fma((-M[3]), D[17], fma((-M[2]), D[16], fma((-M[1]), D[13], M[0] * D[7]))))))))));
+  red(7, 2, fma((M[9] * T(0.5)), D[33], fma(M[8], D[32], fma((M[7] * T(0.5)), D[31], fma(M[6], D[28], fma(M[5], D[27], fma((M[4] * T(0.5)), D[24], fma((-M[3]), D[18], fma((-M[2]), D[17], fma((-M[1]), D[14], M[0] * D[8]))))))))));
+  red(8, 2, fma((M[9] * T(0.5)), D[34], fma(M[8], D[33], fma((M[7] * T(0.5)), D[32], fma(M[6], D[29], fma(M[5], D[28], fma((M[4] * T(0.5)), D[25], fma((-M[3]), D[19], fma((-M[2]), D[18], fma((-M[1]), D[15], M[0] * D[9]))))))))));
+  red(9, 3, fma((-M[3]), D[22], fma((-M[2]), D[21], fma((-M[1]), D[20], M[0] * D[10]))));
+  red(10, 3, fma((-M[3]), D[24], fma((-M[2]), D[23], fma((-M[1]), D[21], M[0] * D[11]))));
+  red(11, 3, fma((-M[3]), D[25], fma((-M[2]), D[24], fma((-M[1]), D[22], M[0] * D[12]))));
+  red(12, 3, fma((-M[3]), D[27], fma((-M[2]), D[26], fma((-M[1]), D[23], M[0] * D[13]))));
+  red(13, 3, fma((-M[3]), D[28], fma((-M[2]), D[27], fma((-M[1]), D[24], M[0] * D[14]))));
+  red(14, 3, fma((-M[3]), D[29], fma((-M[2]), D[28], fma((-M[1]), D[25], M[0] * D[15]))));
+  red(15, 3, fma((-M[3]), D[31], fma((-M[2]), D[30], fma((-M[1]), D[26], M[0] * D[16]))));
+  red(16, 3, fma((-M[3]), D[32], fma((-M[2]), D[31], fma((-M[1]), D[27], M[0] * D[17]))));
+  red(17, 3, fma((-M[3]), D[33], fma((-M[2]), D[32], fma((-M[1]), D[28], M[0] * D[18]))));
+  red(18, 3, fma((-M[3]), D[34], fma((-M[2]), D[33], fma((-M[1]), D[29], M[0] * D[19]))));
+  red(19, 4, M[0] * D[20]);
+  red(20, 4, M[0] * D[21]);
+  red(21, 4, M[0] * D[22]);
+  red(22, 4, M[0] * D[23]);
+  red(23, 4, M[0] * D[24]);
+  red(24, 4, M[0] * D[25]);
+  red(25, 4, M[0] * D[26]);
+  red(26, 4, M[0] * D[27]);
+  red(27, 4, M[0] * D[28]);
+  red(28, 4, M[0] * D[29]);
+  red(29, 4, M[0] * D[30]);
+  red(30, 4, M[0] * D[31]);
+  red(31, 4, M[0] * D[32]);
+  red(32, 4, M[0] * D[33]);
+  red(33, 4, M[0] * D[34]);
+}
+
+template <typename T>
+__device__ __forceinline__ void dtensor_p5(T Rx, T Ry, T Rz, T eps2, T* __restrict__ D) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T g0_0 = nbody_rsqrt(s);
+  const T is = g0_0 * g0_0;
+  const T g1_0 = g0_0 * (T(-1) * is);
+  const T g2_0 = g1_0 * (T(-3) * is);
+  const T g3_0 = g2_0 * (T(-5) * is);
+  const T g4_0 = g3_0 * (T(-7) * is);
+  const T g5_0 = g4_0 * (T(-9) * is);
+  const T g0_1 = Rx * g1_0;
+  const T g1_1 = Rx * g2_0;
+  const T g2_1 = Rx * g3_0;
+  const T g3_1 = Rx * g4_0;
+  const T g4_1 = Rx * g5_0;
+  const T g0_2 = Ry * g1_0;
+  const T g1_2 = Ry * g2_0;
+  const T g2_2 = Ry * g3_0;
+  const T g3_2 = Ry * g4_0;
+  const T g4_2 = Ry * g5_0;
+  const T g0_3 = Rz * g1_0;
+  const T g1_3 = Rz * g2_0;
+  const T g2_3 = Rz * g3_0;
+  const T g3_3 = Rz * g4_0;
+  const T g4_3 = Rz * g5_0;
+  const T g0_4 = fma(T(1), g1_0, Rx * g1_1);
+  const T g1_4 = fma(T(1), g2_0, Rx * g2_1);
+  const T g2_4 = fma(T(1), g3_0, Rx * g3_1);
+  const T g3_4 = fma(T(1), g4_0, Rx * g4_1);
+  const T g0_5 = Rx * g1_2;
+  const T g1_5 = Rx * g2_2;
+  const T g2_5 = Rx * g3_2;
+  const T g3_5 = Rx * g4_2;
+  const T g0_6 = Rx * g1_3;
+  const T g1_6 = Rx * g2_3;
+  const T g2_6 = Rx * g3_3;
+  const T g3_6 = Rx * g4_3;
+  const T g0_7 = fma(T(1), g1_0, Ry * g1_2);
+  const T g1_7 = fma(T(1), g2_0, Ry * g2_2);
+  const T g2_7 = fma(T(1), g3_0, Ry * g3_2);
+  const T g3_7 = fma(T(1), g4_0, Ry * g4_2);
+  const T g0_8 = Ry * g1_3;
+  const T g1_8 = Ry * g2_3;
+  const T g2_8 = Ry * g3_3;
+  const T g3_8 = Ry * g4_3;
+  const T g0_9 = fma(T(1), g1_0, Rz * g1_3);
+  const T g1_9 = fma(T(1), g2_0, Rz * g2_3);
+  const T g2_9 = fma(T(1), g3_0, Rz * g3_3);
+  const T g3_9 = fma(T(1), g4_0, Rz * g4_3);
+  const T g0_10 = fma(T(2), g1_1, Rx * g1_4);
+  const T g1_10 = fma(T(2), g2_1, Rx * g2_4);
+  const T g2_10 = fma(T(2), g3_1, Rx * g3_4);
+  const T g0_11 = fma(T(1), g1_2, Rx * g1_5);
+  const T g1_11 = fma(T(1), g2_2, Rx * g2_5);
+  const T g2_11 = fma(T(1), g3_2, Rx * g3_5);
+  const T g0_12 = fma(T(1), g1_3, Rx * g1_6);
+  const T g1_12 = fma(T(1), g2_3, Rx * g2_6);
+  const T g2_12 = fma(T(1), g3_3, Rx * g3_6);
+  const T g0_13 = Rx * g1_7;
+  const T g1_13 = Rx * g2_7;
+  const T g2_13 = Rx * g3_7;
+  const T g0_14 = Rx * g1_8;
+  const T g1_14 = Rx * g2_8;
+  const T g2_14 = Rx * g3_8;
+  const T g0_15 = Rx * g1_9;
+  const T g1_15 = Rx * g2_9;
+  const T g2_15 = Rx * g3_9;
+  const T g0_16 = fma(T(2), g1_2, Ry * g1_7);
+  const T g1_16 = fma(T(2), g2_2, Ry * g2_7);
+  const T g2_16 = fma(T(2), g3_2, Ry * g3_7);
+  const T g0_17 = fma(T(1), g1_3, Ry * g1_8);
+  const T g1_17 = fma(T(1), g2_3, Ry * g2_8);
+  const T g2_17 = fma(T(1), g3_3, Ry * g3_8);
+  const T g0_18 = Ry * g1_9;
+  const T g1_18 = Ry * g2_9;
+  const T g2_18 = Ry * g3_9;
+  const T g0_19 = fma(T(2), g1_3, Rz * g1_9);
+  const T g1_19 = fma(T(2), g2_3, Rz * g2_9);
+  const T g2_19 = fma(T(2), g3_3, Rz * g3_9);
+  const T g0_20 = fma(T(3), g1_4, Rx * g1_10);
+  const T g1_20 = fma(T(3), g2_4, Rx * g2_10);
+  const T g0_21 = fma(T(2), g1_5, Rx * g1_11);
+  const T g1_21 = fma(T(2), g2_5, Rx * g2_11);
+  const T g0_22 = fma(T(2), g1_6, Rx * g1_12);
+  const T g1_22 = fma(T(2), g2_6, Rx * g2_12);
+  const T g0_23 = fma(T(1), g1_7, Rx * g1_13);
+  const T g1_23 = fma(T(1), g2_7, Rx * g2_13);
+  const T g0_24 = fma(T(1), g1_8, Rx * g1_14);
+  const T g1_24 = fma(T(1), g2_8, Rx * g2_14);
+  const T g0_25 = fma(T(1), g1_9, Rx * g1_15);
+  const T g1_25 = fma(T(1), g2_9, Rx * g2_15);
+  const T g0_26 = Rx * g1_16;
+  const T g1_26 = Rx * g2_16;
+  const T g0_27 = Rx * g1_17;
+  const T g1_27 = Rx * g2_17;
+  const T g0_28 = Rx * g1_18;
+  const T g1_28 = Rx * g2_18;
+  const T g0_29 = Rx * g1_19;
+  const T g1_29 = Rx * g2_19;
+  const T g0_30 = fma(T(3), g1_7, Ry * g1_16);
+  const T g1_30 = fma(T(3), g2_7, Ry * g2_16);
+  const T g0_31 = fma(T(2), g1_8, Ry * g1_17);
+  const T g1_31 = fma(T(2), g2_8, Ry * g2_17);
+  const T g0_32 = fma(T(1), g1_9, Ry * g1_18);
+  const T g1_32 = fma(T(1), g2_9, Ry * g2_18);
+  const T g0_33 = Ry * g1_19;
+  const T g1_33 = Ry * g2_19;
+  const T g0_34 = fma(T(3), g1_9, Rz * g1_19);
+  const T g1_34 = fma(T(3), g2_9, Rz * g2_19);
+  const T g0_35 = fma(T(4), g1_10, Rx * g1_20);
+  const T g0_36 = fma(T(3), g1_11, Rx * g1_21);
+  const T g0_37 = fma(T(3), g1_12, Rx * g1_22);
+  const T g0_38 = fma(T(2), g1_13, Rx * g1_23);
+  const T g0_39 = fma(T(2), g1_14, Rx * g1_24);
+  const T g0_40 = fma(T(2), g1_15, Rx * g1_25);
+  const T g0_41 = fma(T(1), g1_16, Rx * g1_26);
+  const T g0_42 = fma(T(1), g1_17, Rx * g1_27);
+  const T g0_43 = fma(T(1), g1_18, Rx * g1_28);
+  const T g0_44 = fma(T(1), g1_19, Rx * g1_29);
+  const T g0_45 = Rx * g1_30;
+  const T g0_46 = Rx * g1_31;
+  const T g0_47 = Rx * g1_32;
+  const T g0_48 = Rx * g1_33;
+  const T g0_49 = Rx * g1_34;
+  const T g0_50 = fma(T(4), g1_16, Ry * g1_30);
+  const T g0_51 = fma(T(3), g1_17, Ry * g1_31);
+  const T g0_52 = fma(T(2), g1_18, Ry * g1_32);
+  const T g0_53 = fma(T(1), g1_19, Ry * g1_33);
+  const T g0_54 = Ry * g1_34;
+  const T g0_55 = fma(T(4), g1_19, Rz * g1_34);
+  D[0] = g0_0;
+  D[1] = g0_1;
+  D[2] = g0_2;
+  D[3] = g0_3;
+  D[4] = g0_4;
+  D[5] = g0_5;
+  D[6] = g0_6;
+  D[7] = g0_7;
+  D[8] = g0_8;
+  D[9] = g0_9;
+  D[10] = g0_10;
+  D[11] = g0_11;
+  D[12] = g0_12;
+  D[13] = g0_13;
+  D[14] = g0_14;
+  D[15] = g0_15;
+  D[16] = g0_16;
+  D[17] = g0_17;
+  D[18] = g0_18;
+  D[19] = g0_19;
+  D[20] = g0_20;
+  D[21] = g0_21;
+  D[22] = g0_22;
+  D[23] = g0_23;
+  D[24] = g0_24;
+  D[25] = g0_25;
+  D[26] = g0_26;
+  D[27] = g0_27;
+  D[28] = g0_28;
+  D[29] = g0_29;
+  D[30] = g0_30;
+  D[31] = g0_31;
+  D[32] = g0_32;
+  D[33] = g0_33;
+  D[34] = g0_34;
+  D[35] = g0_35;
+  D[36] = g0_36;
+  D[37] = g0_37;
+  D[38] = g0_38;
+  D[39] = g0_39;
+  D[40] = g0_40;
+  D[41] = g0_41;
+  D[42] = g0_42;
+  D[43] = g0_43;
+  D[44] = g0_44;
+  D[45] = g0_45;
+  D[46] = g0_46;
+  D[47] = g0_47;
+  D[48] = g0_48;
+  D[49] = g0_49;
+  D[50] = g0_50;
+  D[51] = g0_51;
+  D[52] = g0_52;
+  D[53] = g0_53;
+  D[54] = g0_54;
+  D[55] = g0_55;
+}
+
+template <typename T, typename MA, typename Red>
+__device__ __forceinline__ void m2l_red_p4(const MA& M, const T* __restrict__ D, Red&& red) {
+  red(0, 1, fma((M[34] * T(0.041666666666666664)), D[49], fma((M[33] * T(0.16666666666666666)), D[48], fma((M[32] * T(0.25)), D[47], fma((M[31] * T(0.16666666666666666)), D[46], fma((M[30] * T(0.041666666666666664)), D[45], fma((M[29] * T(0.16666666666666666)), D[44], fma((M[28] * T(0.5)), D[43], fma((M[27] * T(0.5)), D[42], fma((M[26] * T(0.16666666666666666)), D[41], fma((M[25] * T(0.25)), D[40], fma((M[24] * T(0.5)), D[39], fma((M[23] * T(0.25)), D[38], fma((M[22] * T(0.16666666666666666)), D[37], fma((M[21] * T(0.16666666666666666)), D[36], fma((M[20] * T(0.041666666666666664)), D[35], fma((M[19] * T(-0.16666666666666666)), D[29], fma((M[18] * T(-0.5)), D[28], fma((M[17] * T(-0.5)), D[27], fma((M[16] * T(-0.16666666666666666)), D[26], fma((M[15] * T(-0.5)), D[25], fma((-M[14]), D[24], fma((M[13] * T(-0.5)), D[23], fma((M[12] * T(-0.5)), D[22], fma((M[11] * T(-0.5)), D[21], fma((M[10] * T(-0.16666666666666666)), D[20], fma((M[9] * T(0.5)), D[15], fma(M[8], D[14], fma((M[7] * T(0.5)), D[13], fma(M[6], D[12], fma(M[5], D[11], fma((M[4] * T(0.5)), D[10], fma((-M[3]), D[6], fma((-M[2]), D[5], fma((-M[1]), D[4], M[0] * D[1])))))))))))))))))))))))))))))))))));
+  red(1, 1, fma((M[34] * T(0.041666666666666664)), D[54], fma((M[33] * T(0.16666666666666666)), D[53], fma((M[32] * T(0.25)), D[52], fma((M[31] * T(0.16666666666666666)), D[51], fma((M[30] * T(0.041666666666666664)), D[50], fma((M[29] * T(0.16666666666666666)), D[48], fma((M[28] * T(0.5)), D[47], fma((M[27] * T(0.5)), D[46], fma((M[26] * T(0.16666666666666666)), D[45], fma((M[25] * T(0.25)), D[43], fma((M[24] * T(0.5)), D[42], fma((M[23] * T(0.25)), D[41], fma((M[22] * T(0.16666666666666666)), D[39], fma((M[21] * T(0.16666666666666666)), D[38], fma((M[20] * T(0.041666666666666664)), D[36], fma((M[19] * T(-0.16666666666666666)), D[33], fma((M[18] * T(-0.5)), D[32], fma((M[17] * T(-0.5)), D[31], fma((M[16] * T(-0.16666666666666666)), D[30], fma((M[15] * T(-0.5)), D[28], fma((-M[14]), D[27], fma((M[13] * T(-0.5)), D[26], fma((M[12] * T(-0.5)), D[24], fma((M[11] * T(-0.5)), D[23], fma((M[10] * T(-0.16666666666666666)), D[21], fma((M[9] * T(0.5)), D[18], fma(M[8], D[17], fma((M[7] * T(0.5)), D[16], fma(M[6], D[14], fma(M[5], D[13], fma((M[4] * T(0.5)), D[11], fma((-M[3]), D[8], fma((-M[2]), D[7], fma((-M[1]), D[5], M[0] * D[2])))))))))))))))))))))))))))))))))));
+  red(2, 1, fma((M[34] * T(0.041666666666666664)), D[55], fma((M[33] * T(0.16666666666666666)), D[54], fma((M[32] * T(0.25)), D[53], fma((M[31] * T(0.16666666666666666)), D[52], fma((M[30] * T(0.041666666666666664)), D[51], fma((M[29] * T(0.16666666666666666)), D[49], fma((M[28] * T(0.5)), D[48], fma((M[27] * T(0.5)), D[47], fma((M[26] * T(0.16666666666666666)), D[46], fma((M[25] * T(0.25)), D[44], fma((M[24] * T(0.5)), D[43], fma((M[23] * T(0.25)), D[42], fma((M[22] * T(0.16666666666666666)), D[40], fma((M[21] * T(0.16666666666666666)), D[39], fma((M[20] * T(0.041666666666666664)), D[37], fma((M[19] * T(-0.16666666666666666)), D[34], fma((M[18] * T(-0.5)), D[33], fma((M[17] * T(-0.5)), D[32], fma((M[16] * T(-0.16666666666666666)), D[31], fma((M[15] * T(-0.5)), D[29], fma((-M[14]), D[28], fma((M[13] * T(-0.5)), D[27], fma((M[12] * T(-0.5)), D[25], fma((M[11] * T(-0.5)), D[24], fma((M[10] * T(-0.16666666666666666)), D[22], fma((M[9] * T(0.5)), D[19], fma(M[8], D[18], fma((M[7] * T(0.5)), D[17], fma(M[6], D[15], fma(M[5], D[14], fma((M[4] * T(0.5)), D[12], fma((-M[3]), D[9], fma((-M[2]), D[8], fma((-M[1]), D[6], M[0] * D[3])))))))))))))))))))))))))))))))))));
+  red(3, 2, fma((M[19] * T(-0.16666666666666666)), D[44], fma((M[18] * T(-0.5)), D[43], fma((M[17] * T(-0.5)), D[42], fma((M[16] * T(-0.16666666666666666)), D[41], fma((M[15] * T(-0.5)), D[40], fma((-M[14]), D[39], fma((M[13] * T(-0.5)), D[38], fma((M[12] * T(-0.5)), D[37], fma((M[11] * T(-0.5)), D[36], fma((M[10] * T(-0.16666666666666666)), D[35], fma((M[9] * T(0.5)), D[25], fma(M[8], D[24], fma((M[7] * T(0.5)), D[23], fma(M[6], D[22], fma(M[5], D[21], fma((M[4] * T(0.5)), D[20], fma((-M[3]), D[12], fma((-M[2]), D[11], fma((-M[1]), D[10], M[0] * D[4]))))))))))))))))))));
+  red(4, 2, fma((M[19] * T(-0.16666666666666666)), D[48], fma((M[18] * T(-0.5)), D[47], fma((M[17] * T(-0.5)), D[46], fma((M[16] * T(-0.16666666666666666)), D[45], fma((M[15] * T(-0.5)), D[43], fma((-M[14]), D[42], fma((M[13] * T(-0.5)), D[41], fma((M[12] * T(-0.5)), D[39], fma((M[11] * T(-0.5)), D[38], fma((M[10] * T(-0.16666666666666666)), D[36], fma((M[9] * T(0.5)), D[28], fma(M[8], D[27], fma((M[7] * T(0.5)), D[26], fma(M[6], D[24], fma(M[5], D[23], fma((M[4] * T(0.5)), D[21], fma((-M[3]), D[14], fma((-M[2]), D[13], fma((-M[1]), D[11], M[0] * D[5]))))))))))))))))))));
+  red(5, 2, fma((M[19] * T(-0.16666666666666666)), D[49], fma((M[18] * T(-0.5)), D[48], fma((M[17] * T(-0.5)), D[47], fma((M[16] * T(-0.16666666666666666)), D[46], fma((M[15] * T(-0.5)), D[44], fma((-M[14]), D[43], fma((M[13] * T(-0.5)), D[42], fma((M[12] * T(-0.5)), D[40], fma((M[11] * T(-0.5)), D[39], fma((M[10] * T(-0.16666666666666666)), D[37], fma((M[9] * T(0.5)), D[29], fma(M[8], D[28], fma((M[7] * T(0.5)), D[27], fma(M[6], D[25], fma(M[5], D[24], fma((M[4] * T(0.5)), D[22], fma((-M[3]), D[15], fma((-M[2]), D[14], fma((-M[1]), D[12], M[0] * D[6]))))))))))))))))))));
+  red(6, 2, fma((M[19] * T(-0.16666666666666666)), D[53], fma((M[18] * T(-0.5)), D[52], fma((M[17] * T(-0.5)), D[51], fma((M[16] * T(-0.16666666666666666)), D[50], fma((M[15] * T(-0.5)), D[47], fma((-M[14]), D[46], fma((M[13] * T(-0.5)), D[45], fma((M[12] * T(-0.5)), D[42], fma((M[11] * T(-0.5)), D[41], fma((M[10] * T(-0.16666666666666666)), D[38], fma((M[9] * T(0.5)), D[32], fma(M[8], D[31], fma((M[7] * T(0.5)), D[30], fma(M[6], D[27], fma(M[5], D[26], fma((M[4] * T(0.5)), D[23], fma((-M[3]), D[17], fma((-M[2]), D[16], fma((-M[1]), D[13], M[0] * D[7]))))))))))))))))))));
+  red(7, 2, fma((M[19] * T(-0.16666666666666666)), D[54], fma((M[18] * T(-0.5)), D[53], fma((M[17] * T(-0.5)), D[52], fma((M[16] * T(-0.16666666666666666)), D[51], fma((M[15] * T(-0.5)), D[48], fma((-M[14]), D[47], fma((M[13] * T(-0.5)), D[46], fma((M[12] * T(-0.5)), D[43], fma((M[11] * T(-0.5)), D[42], fma((M[10] * T(-0.16666666666666666)), D[39], fma((M[9] * T(0.5)), D[33], fma(M[8], D[32], fma((M[7] * T(0.5)), D[31], fma(M[6], D[28], fma(M[5], D[27], fma((M[4] * T(0.5)), D[24], fma((-M[3]), D[18], fma((-M[2]), D[17], fma((-M[1]), D[14], M[0] * D[8]))))))))))))))))))));
+  red(8, 2, fma((M[19] * T(-0.16666666666666666)), D[55], fma((M[18] * T(-0.5)), D[54], fma((M[17] * T(-0.5)), D[53], fma((M[16] * T(-0.16666666666666666)), D[52], fma((M[15] * T(-0.5)), D[49], fma((-M[14]), D[48], fma((M[13] * T(-0.5)), D[47], fma((M[12] * T(-0.5)), D[44], fma((M[11] * T(-0.5)), D[43], fma((M[10] * T(-0.16666666666666666)), D[40], fma((M[9] * T(0.5)), D[34], fma(M[8], D[33], fma((M[7] * T(0.5)), D[32], fma(M[6], D[29], fma(M[5], D[28], fma((M[4] * T(0.5)), D[25], fma((-M[3]), D[19], fma((-M[2]), D[18], fma((-M[1]), D[15], M[0] * D[9]))))))))))))))))))));
+  red(9, 3, fma((M[9] * T(0.5)), D[40], fma(M[8], D[39], fma((M[7] * T(0.5)), D[38], fma(M[6], D[37], fma(M[5], D[36], fma((M[4] * T(0.5)), D[35], fma((-M[3]), D[22], fma((-M[2]), D[21], fma((-M[1]), D[20], M[0] * D[10]))))))))));
+  red(10, 3, fma((M[9] * T(0.5)), D[43], fma(M[8], D[42], fma((M[7] * T(0.5)), D[41], fma(M[6], D[39], fma(M[5], D[38], fma((M[4] * T(0.5)), D[36], fma((-M[3]), D[24], fma((-M[2]), D[23], fma((-M[1]), D[21], M[0] * D[11]))))))))));
+  red(11, 3, fma((M[9] * T(0.5)), D[44], fma(M[8], D[43], fma((M[7] * T(0.5)), D[42], fma(M[6], D[40], fma(M[5], D[39], fma((M[4] * T(0.5)), D[37], fma((-M[3]), D[25], fma((-M[2]), D[24], fma((-M[1]), D[22], M[0] * D[12]))))))))));
+  red(12, 3, fma((M[9] * T(0.5)), D[47], fma(M[8], D[46], fma((M[7] * T(0.5)), D[45], fma(M[6], D[42], fma(M[5], D[41], fma((M[4] * T(0.5)), D[38], fma((-M[3]), D[27], fma((-M[2]), D[26], fma((-M[1]), D[23], M[0] * D[13]))))))))));
+  red(13, 3, fma((M[9] * T(0.5)), D[48], fma(M[8], D[47], fma((M[7] * T(0.5)), D[46], fma(M[6], D[43], fma(M[5], D[42], fma((M[4] * T(0.5)), D[39], fma((-M[3]), D[28], fma((-M[2]), D[27], fma((-M[1]), D[24], M[0] * D[14]))))))))));
+  red(14, 3, fma((M[9] * T(0.5)), D[49], fma(M[8], D[48], fma((M[7] * T(0.5)), D[47], fma(M[6], D[44], fma(M[5], D[43], fma((M[4] * T(0.5)), D[40], fma((-M[3]), D[29], fma((-M[2]), D[28], fma((-M[1]), D[25], M[0] * D[15]))))))))));
+  red(15, 3, fma((M[9] * T(0.5)), D[52], fma(M[8], D[51], fma((M[7] * T(0.5)), D[50], fma(M[6], D[46], fma(M[5], D[45], fma((M[4] * T(0.5)), D[41], fma((-M[3]), D[31], fma((-M[2]), D[30], fma((-M[1]), D[26], M[0] * D[16]))))))))));
+  red(16, 3, fma((M[9] * T(0.5)), D[53], fma(M[8], D[52], fma((M[7] * T(0.5)), D[51], fma(M[6], D[47], fma(M[5], D[46], fma((M[4] * T(0.5)), D[42], fma((-M[3]), D[32], fma((-M[2]), D[31], fma((-M[1]), D[27], M[0] * D[17]))))))))));
+  red(17, 3, fma((M[9] * T(0.5)), D[54], fma(M[8], D[53], fma((M[7] * T(0.5)), D[52], fma(M[6], D[48], fma(M[5], D[47], fma((M[4] * T(0.5)), D[43], fma((-M[3]), D[33], fma((-M[2]), D[32], fma((-M[1]), D[28], M[0] * D[18]))))))))));
+  red(18, 3, fma((M[9] * T(0.5)), D[55], fma(M[8], D[54], fma((M[7] * T(0.5)), D[53], fma(M[6], D[49], fma(M[5], D[48], fma((M[4] * T(0.5)), D[44], fma((-M[3]), D[34], fma((-M[2]), D[33], fma((-M[1]), D[29], M[0] * D[19]))))))))));
+  red(19, 4, fma((-M[3]), D[37], fma((-M[2]), D[36], fma((-M[1]), D[35], M[0] * D[20]))));
+  red(20, 4, fma((-M[3]), D[39], fma((-M[2]), D[38], fma((-M[1]), D[36], M[0] * D[21]))));
+  red(21, 4, fma((-M[3]), D[40], fma((-M[2]), D[39], fma((-M[1]), D[37], M[0] * D[22]))));
+  red(22, 4, fma((-M[3]), D[42], fma((-M[2]), D[41], fma((-M[1]), D[38], M[0] * D[23]))));
+  red(23, 4, fma((-M[3]), D[43], fma((-M[2]), D[42], fma((-M[1]), D[39], M[0] * D[24]))));
+  red(24, 4, fma((-M[3]), D[44], fma((-M[2]), D[43], fma((-M[1]), D[40], M[0] * D[25]))));
+  red(25, 4, fma((-M[3]), D[46], fma((-M[2]), D[45], fma((-M[1]), D[41], M[0] * D[26]))));
+  red(26, 4, fma((-M[3]), D[47], fma((-M[2]), D[46], fma((-M[1]), D[42], M[0] * D[27]))));
+  red(27, 4, fma((-M[3]), D[48], fma((-M[2]), D[47], fma((-M[1]), D[43], M[0] * D[28]))));
+  red(28, 4, fma((-M[3]), D[49], fma((-M[2]), D[48], fma((-M[1]), D[44], M[0] * D[29]))));
+  red(29, 4, fma((-M[3]), D[51], fma((-M[2]), D[50], fma((-M[1]), D[45], M[0] * D[30]))));
+  red(30, 4, fma((-M[3]), D[52], fma((-M[2]), D[51], fma((-M[1]), D[46], M[0] * D[31]))));
+  red(31, 4, fma((-M[3]), D[53], fma((-M[2]), D[52], fma((-M[1]), D[47], M[0] * D[32]))));
+  red(32, 4, fma((-M[3]), D[54], fma((-M[2]), D[53], fma((-M[1]), D[48], M[0] * D[33]))));
+  red(33, 4, fma((-M[3]), D[55], fma((-M[2]), D[54], fma((-M[1]), D[49], M[0] * D[34]))));
+  red(34, 5, M[0] * D[35]);
+  red(35, 5, M[0] * D[36]);
+  red(36, 5, M[0] * D[37]);
+  red(37, 5, M[0] * D[38]);
+  red(38, 5, M[0] * D[39]);
+  red(39, 5, M[0] * D[40]);
+  red(40, 5, M[0] * D[41]);
+  red(41, 5, M[0] * D[42]);
+  red(42, 5, M[0] * D[43]);
+  red(43, 5, M[0] * D[44]);
+  red(44, 5, M[0] * D[45]);
+  red(45, 5, M[0] * D[46]);
+  red(46, 5, M[0] * D[47]);
+  red(47, 5, M[0] * D[48]);
+  red(48, 5, M[0] * D[49]);
+  red(49, 5, M[0] * D[50]);
+  red(50, 5, M[0] * D[51]);
+  red(51, 5, M[0] * D[52]);
+  red(52, 5, M[0] * D[53]);
+  red(53, 5, M[0] * D[54]);
+  red(54, 5, M[0] * D[55]);
+}
+
 __device__ __forceinline__ float2 nbody_rsqrt2(float2 s) {
   return make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
 }

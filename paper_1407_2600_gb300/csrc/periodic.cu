@@ -15,8 +15,10 @@
 // order p_E + 1.
 //
 // phi~ derivatives at the lattice nodes are computed here in FP64 from the
-// Ewald sums, using the radial ladder d_i psi_l = -r_i psi_{l+1} of the screened
-// terms (psi = erfc(a r)/r) and of the smooth n = 0 remainder erf(a r)/r.
+// Ewald sums.  The Cartesian derivatives of each radial term come from the
+// McMurchie-Davidson recurrence on its "ladder" f_j = ((1/r) d/dr)^j f:
+// T^(j)_n = d^n f_j satisfies T^(j)_{n+e_a} = r_a T^(j+1)_n + n_a T^(j+1)_{n-e_a}
+// (Leibniz on d_a f_j = r_a f_{j+1}), started from T^(j)_0 = f_j.
 #include <math.h>
 
 #include <mutex>
@@ -29,70 +31,71 @@ namespace {
 
 constexpr int kPMax = 6;               // derivative orders in the table
 constexpr int kNMMax = 84;             // multi-indices of order <= 6
-constexpr double kAlpha = 2.0;
-constexpr double kRcut = 3.0;
-constexpr int kH2Max = 15;
+// Ewald split used to build the table: screening alpha, real-space cut-off
+// and reciprocal-space extent.  phi~ does not depend on the split; with these
+// the neglected real-space images (alpha r >= 8.1) and wave vectors
+// (|h|^2 > 27, weight e^(-pi^2 h^2 / alpha^2) < 2e-23) stay below 1e-14 of
+// the order-6 derivatives.
+constexpr double kAlpha = 2.5;
+constexpr double kRcut = 3.25;
+constexpr int kHMax = 5;
+constexpr int kH2Max = 27;
 
-struct HTerm {
-  double cf;
-  signed char e[3];
-  signed char j;
-};
-__constant__ HTerm c_hterm[600];
-__constant__ short c_hbeg[kNMMax + 1];
 __constant__ signed char c_mi[kNMMax][3];
+// recurrence plan per multi-index n (order >= 1): the axis a lowered, the
+// indices of n - e_a and n - 2 e_a (-1 if n_a < 2) and the order |n|
+__constant__ signed char c_rax[kNMMax];
+__constant__ short c_rd1[kNMMax], c_rd2[kNMMax];
+__constant__ signed char c_rord[kNMMax];
 
-__device__ void ladder_screened(double rho, int P, double* B) {
-  const double r2 = rho * rho;
-  const double ex = exp(-kAlpha * kAlpha * r2);
-  double pw = 1.0;
-  B[0] = erfc(kAlpha * rho) / rho;
-  for (int l = 1; l <= P; l++) {
-    pw *= 2.0 * kAlpha * kAlpha;
-    B[l] = ((2 * l - 1) * B[l - 1] + pw / (kAlpha * sqrt(M_PI)) * ex) / r2;
+// ladder of the screened image term f = erfc(alpha r)/r:
+//   f_j = -((2j - 1) f_{j-1} + (2 alpha/sqrt(pi)) (-2 alpha^2)^(j-1) e^(-alpha^2 r^2)) / r^2
+__device__ void screened_ladder(double r, int P, double* f) {
+  const double r2 = r * r;
+  const double ex = (2.0 * kAlpha / sqrt(M_PI)) * exp(-kAlpha * kAlpha * r2);
+  double w = 1.0;
+  f[0] = erfc(kAlpha * r) / r;
+  for (int j = 1; j <= P; j++) {
+    f[j] = -((2 * j - 1) * f[j - 1] + w * ex) / r2;
+    w *= -2.0 * kAlpha * kAlpha;
   }
 }
 
-// smooth ladder of erf(a r)/r
-__device__ void ladder_smooth(double r, int P, double* E) {
-  if (kAlpha * r > 1.0) {
-    double B[kPMax + 1];
-    ladder_screened(r, P, B);
-    double inv2 = 1.0 / (r * r), I = 1.0 / r;
-    for (int l = 0; l <= P; l++) {
-      E[l] = I - B[l];
-      I *= (2 * l + 1) * inv2;
+// ladder of the smooth n = 0 term u = erf(alpha r)/r: 1/r's ladder
+// (-1)^j (2j-1)!!/r^(2j+1) minus the screened one for alpha r >= 1, else its
+// power series u_j = (2 alpha/sqrt(pi)) (-2 alpha^2)^j
+//                    sum_k (-alpha^2 r^2)^k / (k! (2k + 2j + 1)).
+__device__ void smooth_ladder(double r, int P, double* u) {
+  if (kAlpha * r >= 1.0) {
+    screened_ladder(r, P, u);
+    double nj = 1.0 / r;
+    const double ir2 = 1.0 / (r * r);
+    for (int j = 0; j <= P; j++) {
+      u[j] = nj - u[j];
+      nj *= -(2 * j + 1) * ir2;
     }
     return;
   }
   const double x = -kAlpha * kAlpha * r * r;
-  double pref = 2.0 * kAlpha / sqrt(M_PI);
-  for (int l = 0; l <= P; l++) {
-    double t = 1.0, sum = 0.0;
-    for (int m = 0; m < 48; m++) {
-      sum += t / (2 * (l + m) + 1);
-      t *= x / (m + 1);
-    }
-    E[l] = pref * sum;
-    pref *= 2.0 * kAlpha * kAlpha;
+  double pre = 2.0 * kAlpha / sqrt(M_PI);
+  for (int j = 0; j <= P; j++) {
+    double sum = 0.0;
+    for (int k = 29; k >= 0; k--) sum = sum * x / (k + 1) + 1.0 / (2 * k + 2 * j + 1);
+    u[j] = pre * sum;
+    pre *= -2.0 * kAlpha * kAlpha;
   }
 }
 
-__device__ void add_radial(const double rho[3], const double* psi, double s, int nm, int P, double* out) {
-  double pw[3][kPMax + 1];
-  for (int d = 0; d < 3; d++) {
-    pw[d][0] = 1.0;
-    for (int e = 1; e <= P; e++) pw[d][e] = pw[d][e - 1] * rho[d];
+// out[n] += s d^n f(|r|) for |n| <= P from the ladder f[0..P]
+__device__ void add_cartesian(const double r[3], const double* f, double s, int P, int nm, double* out) {
+  double T[kPMax + 1][kNMMax];
+  for (int j = 0; j <= P; j++) T[j][0] = f[j];
+  for (int t = 1; t < nm; t++) {
+    const int a = c_rax[t], d1 = c_rd1[t], d2 = c_rd2[t], o = c_rord[t];
+    const double k = (double)(c_mi[t][a] - 1);
+    for (int j = 0; j + o <= P; j++) T[j][t] = r[a] * T[j + 1][d1] + (d2 >= 0 ? k * T[j + 1][d2] : 0.0);
   }
-  for (int t = 0; t < nm; t++) {
-    double v = 0.0;
-    for (int h = c_hbeg[t]; h < c_hbeg[t + 1]; h++) {
-      const HTerm q = c_hterm[h];
-      const double ps = (q.j & 1) ? -psi[q.j] : psi[q.j];
-      v += q.cf * pw[0][q.e[0]] * pw[1][q.e[1]] * pw[2][q.e[2]] * ps;
-    }
-    out[t] += s * v;
-  }
+  for (int t = 0; t < nm; t++) out[t] += s * T[0][t];
 }
 
 __global__ void phitilde_table_kernel(int lg, int P, int nm, double* __restrict__ tab) {
@@ -104,6 +107,8 @@ __global__ void phitilde_table_kernel(int lg, int P, int nm, double* __restrict_
     const double r[3] = {i * h, j * h, k * h};
     double out[kNMMax];
     for (int t = 0; t < nm; t++) out[t] = 0.0;
+    double f[kPMax + 1];
+    // real space: every image n != 0 within the cut-off, screened
     const int nmax = (int)ceil(kRcut) + 1;
     for (int nx = -nmax; nx <= nmax; nx++)
       for (int ny = -nmax; ny <= nmax; ny++)
@@ -112,36 +117,33 @@ __global__ void phitilde_table_kernel(int lg, int P, int nm, double* __restrict_
           const double rho[3] = {r[0] - nx, r[1] - ny, r[2] - nz};
           const double d = sqrt(rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2]);
           if (d >= kRcut) continue;
-          double B[kPMax + 1];
-          ladder_screened(d, P, B);
-          add_radial(rho, B, -1.0, nm, P, out);
+          screened_ladder(d, P, f);
+          add_cartesian(rho, f, -1.0, P, nm, out);
         }
-    {
-      const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-      double E[kPMax + 1];
-      ladder_smooth(d, P, E);
-      add_radial(r, E, 1.0, nm, P, out);
-    }
-    const int hm = 3;
-    for (int hx = -hm; hx <= hm; hx++)
-      for (int hy = -hm; hy <= hm; hy++)
-        for (int hz = -hm; hz <= hm; hz++) {
+    // the n = 0 source enters as erf(alpha r)/r (1/r is not part of phi~)
+    smooth_ladder(sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), P, f);
+    add_cartesian(r, f, 1.0, P, nm, out);
+    // reciprocal space: -(1/pi) sum_h e^(-pi^2 h^2/alpha^2)/h^2 cos(2 pi h.r);
+    // d^n cos(k.r) = k^n cos(k.r + |n| pi/2)
+    for (int hx = -kHMax; hx <= kHMax; hx++)
+      for (int hy = -kHMax; hy <= kHMax; hy++)
+        for (int hz = -kHMax; hz <= kHMax; hz++) {
           const int h2 = hx * hx + hy * hy + hz * hz;
           if (h2 == 0 || h2 > kH2Max) continue;
-          const double wgt = exp(-M_PI * M_PI * h2 / (kAlpha * kAlpha)) / h2;
+          const double wgt = -exp(-M_PI * M_PI * h2 / (kAlpha * kAlpha)) / (M_PI * h2);
           double sn, cs;
           sincos(2.0 * M_PI * (hx * r[0] + hy * r[1] + hz * r[2]), &sn, &cs);
+          const double kx = 2.0 * M_PI * hx, ky = 2.0 * M_PI * hy, kz = 2.0 * M_PI * hz;
           for (int t = 0; t < nm; t++) {
-            const int o = c_mi[t][0] + c_mi[t][1] + c_mi[t][2];
-            double hp = 1.0;
-            for (int q = 0; q < o; q++) hp *= 2.0 * M_PI;
-            for (int q = 0; q < c_mi[t][0]; q++) hp *= hx;
-            for (int q = 0; q < c_mi[t][1]; q++) hp *= hy;
-            for (int q = 0; q < c_mi[t][2]; q++) hp *= hz;
-            const double ph = (o & 3) == 0 ? cs : (o & 3) == 1 ? -sn : (o & 3) == 2 ? -cs : sn;
-            out[t] += -(1.0 / M_PI) * wgt * hp * ph;
+            double kn = wgt;
+            for (int q = 0; q < c_mi[t][0]; q++) kn *= kx;
+            for (int q = 0; q < c_mi[t][1]; q++) kn *= ky;
+            for (int q = 0; q < c_mi[t][2]; q++) kn *= kz;
+            const int o = (c_mi[t][0] + c_mi[t][1] + c_mi[t][2]) & 3;
+            out[t] += kn * (o == 0 ? cs : o == 1 ? -sn : o == 2 ? -cs : sn);
           }
         }
+    // the background and the split's constant: (2 pi/3)|r|^2 + pi/alpha^2
     out[0] += (2.0 * M_PI / 3.0) * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) + M_PI / (kAlpha * kAlpha);
     if (P >= 1)
       for (int d = 0; d < 3; d++) out[1 + d] += (4.0 * M_PI / 3.0) * r[d];
@@ -343,12 +345,6 @@ int mi_index(int nx, int ny, int nz) {
   return o * (o + 1) * (o + 2) / 6 + j * (j + 1) / 2 + nz;
 }
 
-double factd(int n) {
-  double f = 1.0;
-  for (int i = 2; i <= n; i++) f *= i;
-  return f;
-}
-
 struct TableCache {
   int device = -1, lg = 0, P = 0;
   double* d64 = nullptr;
@@ -357,47 +353,45 @@ struct TableCache {
 std::mutex g_tab_mutex;
 std::vector<TableCache> g_tabs;
 
+// multi-index tables of the table build and of the image field, per device
 cudaError_t upload_terms() {
   static bool done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && done[dev]) return cudaSuccess;
-  std::vector<HTerm> terms;
-  short beg[kNMMax + 1];
-  signed char mi[kNMMax][3];
+  signed char mi[kNMMax][3], rax[kNMMax], rord[kNMMax];
+  short rd1[kNMMax], rd2[kNMMax];
   unsigned char pm[kNMMax];
   for (int o = 0; o <= kPMax; o++)
     for (int nx = o; nx >= 0; nx--)
       for (int ny = o - nx; ny >= 0; ny--) {
-        int nz = o - nx - ny, t = mi_index(nx, ny, nz);
+        const int nz = o - nx - ny, t = mi_index(nx, ny, nz);
+        const int n[3] = {nx, ny, nz};
         mi[t][0] = (signed char)nx;
         mi[t][1] = (signed char)ny;
         mi[t][2] = (signed char)nz;
         pm[t] = (unsigned char)((nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2));
-      }
-  for (int t = 0; t < kNMMax; t++) {
-    beg[t] = (short)terms.size();
-    int m0 = mi[t][0], m1 = mi[t][1], m2 = mi[t][2];
-    for (int k0 = 0; 2 * k0 <= m0; k0++)
-      for (int k1 = 0; 2 * k1 <= m1; k1++)
-        for (int k2 = 0; 2 * k2 <= m2; k2++) {
-          HTerm h;
-          h.cf = factd(m0) / (factd(k0) * factd(m0 - 2 * k0) * ldexp(1.0, k0)) * factd(m1) /
-                 (factd(k1) * factd(m1 - 2 * k1) * ldexp(1.0, k1)) * factd(m2) /
-                 (factd(k2) * factd(m2 - 2 * k2) * ldexp(1.0, k2));
-          h.e[0] = (signed char)(m0 - 2 * k0);
-          h.e[1] = (signed char)(m1 - 2 * k1);
-          h.e[2] = (signed char)(m2 - 2 * k2);
-          h.j = (signed char)(m0 + m1 + m2 - k0 - k1 - k2);
-          terms.push_back(h);
+        rord[t] = (signed char)o;
+        rax[t] = 0;
+        rd1[t] = rd2[t] = -1;
+        if (o == 0) continue;
+        int a = 0;
+        while (n[a] == 0) a++;
+        int m1[3] = {n[0], n[1], n[2]};
+        m1[a] -= 1;
+        rax[t] = (signed char)a;
+        rd1[t] = (short)mi_index(m1[0], m1[1], m1[2]);
+        if (n[a] >= 2) {
+          m1[a] -= 1;
+          rd2[t] = (short)mi_index(m1[0], m1[1], m1[2]);
         }
-  }
-  beg[kNMMax] = (short)terms.size();
-  if (terms.size() > 600) return cudaErrorInvalidValue;
+      }
   cudaError_t e;
-  if ((e = cudaMemcpyToSymbol(c_hterm, terms.data(), sizeof(HTerm) * terms.size()))) return e;
-  if ((e = cudaMemcpyToSymbol(c_hbeg, beg, sizeof(beg)))) return e;
   if ((e = cudaMemcpyToSymbol(c_mi, mi, sizeof(mi)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_rax, rax, sizeof(rax)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_rd1, rd1, sizeof(rd1)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_rd2, rd2, sizeof(rd2)))) return e;
+  if ((e = cudaMemcpyToSymbol(c_rord, rord, sizeof(rord)))) return e;
   if ((e = cudaMemcpyToSymbol(c_par_mask, pm, sizeof(pm)))) return e;
   if (dev < 64) done[dev] = true;
   return cudaSuccess;

@@ -31,6 +31,23 @@ __global__ void keys_kernel(const double* __restrict__ pos, int64_t n, uint64_t*
   }
 }
 
+// keys_kernel for the allocation-free sort, which has no gather pass to
+// validate the positions: a coordinate that is not finite sets the
+// bad-input bit of *err (the build's gather does the same for its own path).
+__global__ void keys_checked_kernel(const double* __restrict__ pos, int64_t n, uint64_t* __restrict__ keys,
+                                    uint32_t* __restrict__ vals, unsigned* __restrict__ err) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = pos[i], y = pos[n + i], z = pos[2 * n + i];
+    bad |= !(isfinite(x) && isfinite(y) && isfinite(z));
+    uint32_t qx = quant21(x), qy = quant21(y), qz = quant21(z);
+    keys[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+    vals[i] = (uint32_t)i;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, NB_ST_BADINPUT);
+}
+
 __global__ void box_ids_kernel(const int64_t* __restrict__ off, int nbox, uint16_t* __restrict__ box_of) {
   for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
     int64_t s = off[b], e = off[b + 1];
@@ -533,7 +550,9 @@ extern "C" int nbody_sort_keys_noalloc(const double* pos_dev, int64_t n, uint64_
   // the array keeps the previous call's contents: the error word is cleared
   // here, the histograms, status words and tile counters by the sort itself
   if (cudaMemsetAsync(&sc->err, 0, sizeof(unsigned), s) != cudaSuccess) return NBODY_ECUDA;
-  if (nb_launch_keys(pos_dev, n, 0, keys_out_dev, perm_out_dev, s) != cudaSuccess) return NBODY_ECUDA;
+  keys_checked_kernel<<<grid_for(n, 256), 256, 0, s>>>(pos_dev, n, keys_out_dev, perm_out_dev, &sc->err);
+  nb_launch_counter += 1;
+  if (cudaGetLastError() != cudaSuccess) return NBODY_ECUDA;
   SortScratch ss;
   ss.keys_alt = sc->keys_alt;
   ss.vals_alt = sc->vals_alt;
@@ -550,6 +569,7 @@ extern "C" int nbody_sort_keys_noalloc(const double* pos_dev, int64_t n, uint64_
   if (cudaMemcpyAsync(&err, &sc->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return NBODY_ECUDA;
+  if (err & NB_ST_BADINPUT) return NBODY_EINVAL;
   if (err & NB_ST_TIMEOUT) return NBODY_ETIMEOUT;
   return NBODY_OK;
 }

@@ -68,6 +68,9 @@ __host__ __device__ constexpr int order_of(int t) {
 struct BgArgs {
   const uint16_t* cbox;  // box of each cell
   const double* rho;     // mean density of each box; nullptr: no background term
+  float* mom32;          // nullptr, or the cells' moments in their own unit
+                         // M_n h^-|n| in FP32 (kDualStride per cell), for
+                         // the cell-group local expansions of the dual form
 };
 
 template <int P, typename T>
@@ -85,6 +88,11 @@ __device__ __forceinline__ void finish_cell(int c, int level, const double* M, T
   for (int q = Ord<P>::NB; q < Ord<P>::NBS; q++) dst[q] = (T)0;
   if constexpr (Ord<P>::NB < Ord<P>::NBS)
     if (bg.rho) dst[Ord<P>::NB] = (T)mul_pow2(bg.rho[bg.cbox[c]], -level);
+  if (bg.mom32) {
+    float* m32 = bg.mom32 + (int64_t)c * kDualStride;
+#pragma unroll
+    for (int t = 0; t < NM; t++) m32[t] = (float)Ms[t];
+  }
 }
 
 // Schedule of the upward pass.  Every cell gets an 8-bit key: leaves sort by
@@ -360,8 +368,8 @@ int nb_coef_stride(int order) {
 cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const int4* cA, const int4* cB,
                       const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
                       uint32_t* uorder, uint32_t* uhist, int* urange, const uint16_t* cbox, const double* rho,
-                      SortScratch* sc, cudaStream_t s) {
-  const BgArgs bg{cbox, rho};
+                      float* mom32, SortScratch* sc, cudaStream_t s) {
+  const BgArgs bg{cbox, rho, mom32};
   upkey_kernel<<<gridc(ncell, 256), 256, 0, s>>>(ncell, pncell, cA, cB, ukey);
   nb_launch_counter += 1;
   cudaError_t e = nb_sort_digit8(ukey, ncell, uorder, uhist, sc, s);

@@ -75,6 +75,44 @@ NB_WBG(0, 4)
 NB_WBG(2, 4)
 NB_WBG(4, 6)
 
+// The dual form's cell-group expansion at order P: the softened kernel's
+// derivatives to order P + 1 and the M2L one local coefficient at a time
+// (m2l_red), the L2P of the image-field code (same truncation, same storage).
+template <int P> struct WDual {
+  static constexpr bool has = false;
+  static constexpr int NL = 1;
+  template <typename MA, typename Red>
+  static __device__ __forceinline__ void m2l(const MA&, float, float, float, float, Red&&) {}
+  static __device__ __forceinline__ void l2p(const float*, float, float, float, float&, float&, float&) {}
+};
+#define NB_WDUAL(P, Q)                                                                                   \
+  template <> struct WDual<P> {                                                                          \
+    static constexpr bool has = true;                                                                    \
+    static constexpr int NL = kNL##P;                                                                    \
+    template <typename MA, typename Red>                                                                 \
+    static __device__ __forceinline__ void m2l(const MA& M, float x, float y, float z, float e2, Red&& red) { \
+      float D[(Q + 1) * (Q + 2) * (Q + 3) / 6];                                                          \
+      dtensor_p##Q<float>(x, y, z, e2, D);                                                               \
+      _Pragma("unroll") for (int t = 0; t < (Q + 1) * (Q + 2) * (Q + 3) / 6; t++) D[t] = -D[t];          \
+      m2l_red_p##P<float>(M, D, red);                                                                    \
+    }                                                                                                    \
+    static __device__ __forceinline__ void l2p(const float* L, float x, float y, float z, float& ax, float& ay, \
+                                               float& az) {                                              \
+      l2p_pe##P<float>(L, x, y, z, ax, ay, az);                                                          \
+    }                                                                                                    \
+  };
+NB_WDUAL(1, 2)
+NB_WDUAL(2, 3)
+NB_WDUAL(3, 4)
+NB_WDUAL(4, 5)
+
+// moments of the cell a lane works on, staged in shared memory as [n][lane]
+struct LaneMoments {
+  const float* base;
+  int lane;
+  __device__ __forceinline__ float operator[](int u) const { return base[u * 32 + lane]; }
+};
+
 template <typename T>
 struct WalkArgs {
   DevTree tr;
@@ -85,6 +123,11 @@ struct WalkArgs {
   int n_direct;
   int mac_edge;
   int bg;  // add the uniform-background term of every expanded cell
+  int k1;  // Dehnen K1 softening of direct pairs, Newtonian expansions
+  int dual;        // cell-group local expansions for well-separated cells
+  double theta2;   // theta^2 of the cell-group test (IEEE double, as on the host)
+  const float* mom32;  // FP32 cell-unit moments (kDualStride per cell)
+  int lu;          // the groups' length unit 2^-lu (level of the cell no group straddles)
   int le;
   int* stack;
   int stack_cap;
@@ -103,7 +146,7 @@ constexpr double kScale = 1.0 / 8388608.0;  // 2^-23
 // of cells 2q and 2q + 1 are staged interleaved and each pair instruction
 // advances both expansions, halving the instructions issued per M2P; every
 // cell's result is bitwise the scalar one).  The autotuner picks.
-template <typename T, int P, int WARPS, int MINB, bool PK>
+template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK>
 __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   using V4 = typename Vec4<T>::type;
   constexpr int NBS = WOrd<P>::NBS;
@@ -115,6 +158,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   __shared__ V4 s_moff[WARPS][64];
   __shared__ int s_midx[WARPS][64];
   __shared__ T s_meps[WARPS][64];
+  __shared__ T s_b0[WARPS][32];  // monopole coefficient of the chunk's largest cells
+  // double-float sums of the largest cells' monopole terms, per lane (hi x3, lo x3)
+  __shared__ float s_df[WARPS][6][32];
+  // dual form: queue of (cell, R = (z - c*) 2^level, level - lu in .w,
+  // eps^2 4^level), the group's local coefficients (Kahan pairs) and the
+  // cell-group thresholds per level
+  __shared__ V4 s_loff[WARPS][64];
+  __shared__ int s_lidx[WARPS][64];
+  __shared__ T s_leps[WARPS][64];
+  __shared__ float s_L[WARPS][2][64];
+  __shared__ long long s_tl[WARPS][NB_NLEV];
   __shared__ int s_pfx[WARPS][32];
   __shared__ int s_pst[WARPS][32];
   __shared__ int s_plev[WARPS][32];
@@ -149,11 +203,105 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       zi = o.z + (T)(la.z - gd.z) * scale;
     }
     T ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;
-    unsigned long long n_p2p = 0, n_m2p = 0;
+    // double-float sum of the largest cells' monopole terms (FP32 walk only),
+    // kept in shared memory: it changes once per such cell
+    constexpr bool DF = std::is_same<T, float>::value;
+    if constexpr (DF)
+#pragma unroll
+      for (int k = 0; k < 6; k++) s_df[wid][k][lane] = 0.f;
+    unsigned long long n_p2p = 0, n_m2p = 0, n_m2l = 0;
     int qn = 0;  // queued M2P cells
+    int ln = 0;  // queued cell-group (M2L) cells
+    constexpr bool DUAL = DUALK && DF && WDual<P>::has;
+    if constexpr (DUAL) {
+      if (w.dual) {
+        s_L[wid][0][lane] = s_L[wid][0][lane + 32] = 0.f;
+        s_L[wid][1][lane] = s_L[wid][1][lane + 32] = 0.f;
+        if (lane < NB_NLEV) {
+          // (s_C + s_G)^2 / theta^2 with s_G the group box's largest side
+          const long long wmax = max(gc.x, max(gc.y, gc.z));
+          const long long S = (1ll << (23 - min(lane, 23))) + 2 * wmax;
+          s_tl[wid][lane] = (long long)floor((double)S * (double)S / w.theta2);
+        }
+        __syncwarp();
+      }
+    }
     // checksum of this lane's (group, cell, decision, cell count) terms and of
     // the group's membership (its sinks' input indices)
     unsigned long long hsum = act ? decision_mix(g, -2 - (int)tr.perm[i], 0) : 0ull;
+    // the largest queued cells' monopole terms, in double-float (their
+    // coefficient was taken out of the expansions of the chunk).  Done with
+    // the uniform-background terms, i.e. for the nearly uniform states
+    // where those terms cancel a thousandfold.
+    auto df_monopoles = [&](int nmp) {
+      if (!w.bg) return;
+      float sh[3], sl[3];
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        sh[k] = s_df[wid][k][lane];
+        sl[k] = s_df[wid][3 + k][lane];
+      }
+      for (int q = 0; q < nmp; q++) {
+        const V4 mo = s_moff[wid][q];
+        if (mo.w <= (T)kDfScale)
+          mono_df((float)xi, (float)yi, (float)zi, (float)mo.w, (float)mo.x, (float)mo.y, (float)mo.z,
+                  (float)s_meps[wid][q], (float)s_b0[wid][q], sh, sl);
+      }
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        s_df[wid][k][lane] = sh[k];
+        s_df[wid][3 + k][lane] = sl[k];
+      }
+    };
+    // dual form: lane q forms the local expansion about the group-box centre
+    // of queued cell q; the warp sums each coefficient over its lanes and the
+    // coefficient's owner lane (t mod 32) adds it to the group's, compensated
+    auto m2l_chunk = [&](int nml) {
+      if constexpr (DUAL) {
+        // the lanes' moments (nmom(P), in 16-byte pieces) staged as [n][lane];
+        // they fit the coefficient buffer: 4 ceil(nmom(P)/4) <= NBS
+        constexpr int NM4 = ((P + 1) * (P + 2) * (P + 3) / 6 + 3) / 4;
+        static_assert(4 * NM4 <= NBS, "dual staging exceeds the coefficient buffer");
+        float* sm = reinterpret_cast<float*>(&s_coef[wid][0]);
+        if (lane < nml) {
+          const float4* src = reinterpret_cast<const float4*>(w.mom32 + (int64_t)s_lidx[wid][lane] * kDualStride);
+#pragma unroll
+          for (int k = 0; k < NM4; k++) {
+            const float4 v = src[k];
+            sm[(4 * k) * 32 + lane] = v.x;
+            sm[(4 * k + 1) * 32 + lane] = v.y;
+            sm[(4 * k + 2) * 32 + lane] = v.z;
+            sm[(4 * k + 3) * 32 + lane] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4 * NM4; k++) sm[k * 32 + lane] = 0.f;
+        }
+        __syncwarp();
+        const V4 lo = s_loff[wid][lane < nml ? lane : 0];
+        const float e2 = (float)s_leps[wid][lane < nml ? lane : 0];
+        // 2^((level - lu)(o + 1)) takes coefficient order o to the group's unit
+        float f[7];
+        f[0] = __int_as_float((127 + (int)lo.w) << 23);  // 2^(level - lu), |level - lu| < 24
+        f[1] = f[0] * f[0];
+#pragma unroll
+        for (int o = 2; o < 7; o++) f[o] = f[o - 1] * f[0];
+        WDual<P>::m2l(LaneMoments{sm, lane}, (float)lo.x, (float)lo.y, (float)lo.z, e2, [&](int t, int o, float v) {
+          v *= f[o];
+#pragma unroll
+          for (int k = 16; k > 0; k >>= 1) v += __shfl_xor_sync(FULL, v, k);
+          if ((t & 31) == lane) {
+            const int h = t >> 5;
+            float sh = s_L[wid][0][lane + 32 * h], sc = s_L[wid][1][lane + 32 * h];
+            kadd(sh, sc, v);
+            s_L[wid][0][lane + 32 * h] = sh;
+            s_L[wid][1][lane + 32 * h] = sc;
+          }
+        });
+        n_m2l += nml;
+        __syncwarp();
+      }
+    };
     // evaluate the first nmp queued M2P cells for every sink of the group
     auto m2p_chunk = [&](int nmp) {
       if constexpr (PK) {
@@ -171,7 +319,17 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           sdst[2 * (q * C4 + r) + 1] = make_float4(c0.z, c1.z, c0.w, c1.w);
         }
         __syncwarp();
+        // the largest cells' monopoles are summed in double-float: out of the pair expansion
+        if (w.bg && lane < nmp && s_moff[wid][lane].w <= kDfScale) {
+          float* slot0 = &s_coef[wid][2 * (lane >> 1) * NBS + (lane & 1)];
+          s_b0[wid][lane] = *slot0;
+          *slot0 = 0.f;
+        }
+        __syncwarp();
         if (act) {
+          // each cell's term is formed from zero and added to the chunk sum
+          // once (the largest cells' monopoles, the terms that cancel most,
+          // are summed apart in double-float)
           float2 px = make_float2(0.f, 0.f), py = px, pz = px;
           const float2 x2 = make_float2(xi, xi), y2 = make_float2(yi, yi), z2 = make_float2(zi, zi);
           const float2* cf = reinterpret_cast<const float2*>(&s_coef[wid][0]);
@@ -185,17 +343,22 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
               const float2 rx = __ffma2_rn(x2, sc, make_float2(m0.x, m1.x));
               const float2 ry = __ffma2_rn(y2, sc, make_float2(m0.y, m1.y));
               const float2 rz = __ffma2_rn(z2, sc, make_float2(m0.z, m1.z));
-              WOrd<P>::m2p2(&cf[q * NBS], rx, ry, rz, e2, px, py, pz);
+              float2 tx = make_float2(0.f, 0.f), ty = tx, tz = tx;
+              WOrd<P>::m2p2(&cf[q * NBS], rx, ry, rz, e2, tx, ty, tz);
               // the padding cell of an odd chunk has weight 0 at R = (0, 0, 0) + offset 0: skip it
               if constexpr (decltype(bgc)::value) {
                 const float2 qb = cf[q * NBS + WOrd<P>::NB];
-                WBg<P>::add2(two ? qb : make_float2(qb.x, 0.f), rx, ry, two ? rz : make_float2(rz.x, 1.f), px, py,
-                             pz);
+                WBg<P>::add2(two ? qb : make_float2(qb.x, 0.f), rx, ry, two ? rz : make_float2(rz.x, 1.f), tx, ty,
+                             tz);
               }
+              px = __fadd2_rn(px, tx);
+              py = __fadd2_rn(py, ty);
+              pz = __fadd2_rn(pz, tz);
             }
           };
           if (WBg<P>::has && w.bg) pairs(std::true_type{});
           else pairs(std::false_type{});
+          df_monopoles(nmp);
           kadd(ax, cx, px.x + px.y);
           kadd(ay, cy, py.x + py.y);
           kadd(az, cz, pz.x + pz.y);
@@ -211,7 +374,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         sdst[t] = gsrc[(int64_t)s_midx[wid][q] * C16 + r];
       }
       __syncwarp();
+      if constexpr (DF) {
+        // the largest cells' monopoles are summed in double-float: out of the expansion
+        if (w.bg && lane < nmp && s_moff[wid][lane].w <= kDfScale) {
+          s_b0[wid][lane] = s_coef[wid][lane * NBS];
+          s_coef[wid][lane * NBS] = (T)0;
+        }
+        __syncwarp();
+      }
       if (act) {
+        // each cell's term is formed from zero and added to the chunk sum
+        // once (the largest cells' monopoles, the terms that cancel most,
+        // are summed apart in double-float)
         T px = 0, py = 0, pz = 0;
         // each M2P runs in its cell's unit (coordinates times 2^level,
         // coefficients pre-scaled): see the upward pass
@@ -219,13 +393,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           for (int q = 0; q < nmp; q++) {
             const V4 mo = s_moff[wid][q];
             const T rx = fma(xi, mo.w, mo.x), ry = fma(yi, mo.w, mo.y), rz = fma(zi, mo.w, mo.z);
-            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q], px, py, pz);
+            T tx = 0, ty = 0, tz = 0;
+            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q], tx, ty, tz);
             if constexpr (decltype(bgc)::value)
-              WBg<P>::template add<T>(s_coef[wid][q * NBS + WOrd<P>::NB], rx, ry, rz, px, py, pz);
+              WBg<P>::template add<T>(s_coef[wid][q * NBS + WOrd<P>::NB], rx, ry, rz, tx, ty, tz);
+            px += tx;
+            py += ty;
+            pz += tz;
           }
         };
         if (WBg<P>::has && w.bg) cells(std::true_type{});
         else cells(std::false_type{});
+        if constexpr (DF) df_monopoles(nmp);
         kadd(ax, cx, px);
         kadd(ay, cy, py);
         kadd(az, cz, pz);
@@ -254,7 +433,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       const int lvl = ca.w & 0xff, nch = ca.w >> 8;
       if (lane < nb) {
         cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, kx, ky, kz);
-        hsum += decision_mix(g, c, cls | (cb.y << 2));
+        if constexpr (DUAL) {
+          if (w.dual && cls == NB_CELL_M2P) {
+            // cell-group test: centre-to-centre distance against (s_C + s_G)/theta
+            const long long dx = ca.x - kx * NB_PBOX - gb.x, dy = ca.y - ky * NB_PBOX - gb.y,
+                            dz = ca.z - kz * NB_PBOX - gb.z;
+            if (dx * dx + dy * dy + dz * dz > s_tl[wid][lvl]) cls = NB_CELL_M2L;
+          }
+        }
+        hsum += decision_mix(g, c, cls | (cb.y << 3));
       }
       // push daughters of opened cells
       {
@@ -283,7 +470,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           mo.z = -((T)(ca.z - kz * NB_PBOX - gd.z) * scale) * sc;
           mo.w = sc;
           s_moff[wid][pos] = mo;
-          s_meps[wid][pos] = eps2 * (sc * sc);
+          s_meps[wid][pos] = w.k1 ? (T)0 : eps2 * (sc * sc);
         }
         qn += __popc(mm);
         if (qn >= 32) {
@@ -298,6 +485,36 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           qn -= 32;
         }
         __syncwarp();
+      }
+      if constexpr (DUAL) {
+        const unsigned lm = __ballot_sync(FULL, cls == NB_CELL_M2L);
+        if (lm) {
+          if (cls == NB_CELL_M2L) {
+            const int pos = ln + __popc(lm & ltmask);
+            s_lidx[wid][pos] = c;
+            // R = (z - c*) 2^level, z the group-box centre (exact scalings)
+            const T sc = (T)(1 << lvl);
+            V4 lo;
+            lo.x = ((T)(gb.x - (ca.x - kx * NB_PBOX)) * scale) * sc;
+            lo.y = ((T)(gb.y - (ca.y - ky * NB_PBOX)) * scale) * sc;
+            lo.z = ((T)(gb.z - (ca.z - kz * NB_PBOX)) * scale) * sc;
+            lo.w = (T)(lvl - w.lu);  // log2 of the group unit over the cell's
+            s_loff[wid][pos] = lo;
+            s_leps[wid][pos] = w.k1 ? (T)0 : eps2 * (sc * sc);
+          }
+          ln += __popc(lm);
+          if (ln >= 32) {
+            __syncwarp();
+            m2l_chunk(32);
+            if (lane < ln - 32) {
+              s_lidx[wid][lane] = s_lidx[wid][32 + lane];
+              s_loff[wid][lane] = s_loff[wid][32 + lane];
+              s_leps[wid][lane] = s_leps[wid][32 + lane];
+            }
+            ln -= 32;
+          }
+          __syncwarp();
+        }
       }
       // P2P chunks
       const unsigned pm = __ballot_sync(FULL, cls == 3);
@@ -363,45 +580,67 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           __syncwarp();
           const int nn = min(32, total - b0);
           const V4 vnext = fetch(b0 + 32 + lane);
-          if constexpr (PK) {
-            if (act) {
-              const float4* pa = reinterpret_cast<const float4*>(&s_src[wid][0]);
-              const float4* pb = reinterpret_cast<const float4*>(&s_src[wid][16]);
-              const float2 nx = make_float2(-xi, -xi), ny = make_float2(-yi, -yi), nz = make_float2(-zi, -zi);
-              const float2 e2 = make_float2(eps2, eps2);
-              float2 px = make_float2(0.f, 0.f), py = px, pz = px;
-              for (int k = 0; k < ((nn + 1) >> 1); k++) {
-                const float4 a = pa[k], b = pb[k];
-                const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
-                const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
-                const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
-                const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
-                const float2 inv = make_float2(nbody_rsqrt(r2.x), nbody_rsqrt(r2.y));
-                const float2 f = __fmul2_rn(__fmul2_rn(make_float2(b.z, b.w), __fmul2_rn(inv, inv)), inv);
-                px = __ffma2_rn(dx, f, px);
-                py = __ffma2_rn(dy, f, py);
-                pz = __ffma2_rn(dz, f, pz);
+          // pair factor f of a = m d f: Plummer (r^2 + eps^2)^(-3/2), or the
+          // K1 kernel, Newtonian from eps on and (175/16 - (147/8) x^2 +
+          // (135/16) x^4)/eps^3 inside (x = r/eps: the enclosed mass of its
+          // compensating density over r^3); the self pair has d = 0
+          auto pairs = [&](auto k1c) {
+            constexpr bool K1 = decltype(k1c)::value;
+            const T e2p = K1 ? (T)0 : eps2;
+            const T ie2 = K1 ? (T)1 / eps2 : (T)0;
+            const T ie3 = K1 ? ie2 * sqrt(ie2) : (T)0;
+            if constexpr (PK) {
+              if (act) {
+                const float4* pa = reinterpret_cast<const float4*>(&s_src[wid][0]);
+                const float4* pb = reinterpret_cast<const float4*>(&s_src[wid][16]);
+                const float2 nx = make_float2(-xi, -xi), ny = make_float2(-yi, -yi), nz = make_float2(-zi, -zi);
+                const float2 e2 = make_float2(e2p, e2p);
+                float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+                for (int k = 0; k < ((nn + 1) >> 1); k++) {
+                  const float4 a = pa[k], b = pb[k];
+                  const float2 dx = __fadd2_rn(make_float2(a.x, a.y), nx);
+                  const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ny);
+                  const float2 dz = __fadd2_rn(make_float2(b.x, b.y), nz);
+                  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+                  const float2 inv = make_float2(nbody_rsqrt_pair(r2.x), nbody_rsqrt_pair(r2.y));
+                  float2 f = __fmul2_rn(__fmul2_rn(make_float2(b.z, b.w), __fmul2_rn(inv, inv)), inv);
+                  if constexpr (K1) {
+                    const float x2a = r2.x * ie2, x2b = r2.y * ie2;
+                    if (x2a < 1.f) f.x = b.z * ie3 * fmaf(x2a, fmaf(x2a, 135.f / 16.f, -147.f / 8.f), 175.f / 16.f);
+                    if (x2b < 1.f) f.y = b.w * ie3 * fmaf(x2b, fmaf(x2b, 135.f / 16.f, -147.f / 8.f), 175.f / 16.f);
+                  }
+                  px = __ffma2_rn(dx, f, px);
+                  py = __ffma2_rn(dy, f, py);
+                  pz = __ffma2_rn(dz, f, pz);
+                }
+                kadd(ax, cx, px.x + px.y);
+                kadd(ay, cy, py.x + py.y);
+                kadd(az, cz, pz.x + pz.y);
               }
-              kadd(ax, cx, px.x + px.y);
-              kadd(ay, cy, py.x + py.y);
-              kadd(az, cz, pz.x + pz.y);
+            } else if (act) {
+              T px = 0, py = 0, pz = 0;
+              for (int k = 0; k < nn; k++) {
+                const V4 s = s_src[wid][k];
+                const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+                const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2p)));
+                const T inv = nbody_rsqrt_pair(r2);
+                T f = s.w * (inv * inv) * inv;
+                if constexpr (K1) {
+                  const T x2 = r2 * ie2;
+                  if (x2 < (T)1)
+                    f = s.w * ie3 * fma(x2, fma(x2, (T)(135.0 / 16.0), (T)(-147.0 / 8.0)), (T)(175.0 / 16.0));
+                }
+                px = fma(dx, f, px);
+                py = fma(dy, f, py);
+                pz = fma(dz, f, pz);
+              }
+              kadd(ax, cx, px);
+              kadd(ay, cy, py);
+              kadd(az, cz, pz);
             }
-          } else if (act) {
-            T px = 0, py = 0, pz = 0;
-            for (int k = 0; k < nn; k++) {
-              const V4 s = s_src[wid][k];
-              const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-              const T r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-              const T inv = nbody_rsqrt(r2);
-              const T f = s.w * (inv * inv) * inv;
-              px = fma(dx, f, px);
-              py = fma(dy, f, py);
-              pz = fma(dz, f, pz);
-            }
-            kadd(ax, cx, px);
-            kadd(ay, cy, py);
-            kadd(az, cz, pz);
-          }
+          };
+          if (w.k1) pairs(std::true_type{});
+          else pairs(std::false_type{});
           __syncwarp();
           v = vnext;
         }
@@ -413,14 +652,53 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       continue;
     }
     if (qn > 0) m2p_chunk(qn);
+    if constexpr (DUAL) {
+      if (w.dual) {
+        if (ln > 0) m2l_chunk(ln);
+        const bool any = __any_sync(FULL, n_m2l > 0);
+        if (any) {
+          // the group's local expansion at every sink: d = (x - z) in the
+          // group's unit 2^-lu; the coefficients were built from -d g, which
+          // the image-field L2P turns back (it subtracts)
+          float* Lf = reinterpret_cast<float*>(&s_coef[wid][0]);
+          Lf[lane] = s_L[wid][0][lane] - s_L[wid][1][lane];
+          if (lane + 32 < WDual<P>::NL) Lf[lane + 32] = s_L[wid][0][lane + 32] - s_L[wid][1][lane + 32];
+          __syncwarp();
+          if (act) {
+            const float u = (float)(1 << w.lu);
+            const float dxp = (xi - (T)(gb.x - gd.x) * scale) * u;
+            const float dyp = (yi - (T)(gb.y - gd.y) * scale) * u;
+            const float dzp = (zi - (T)(gb.z - gd.z) * scale) * u;
+            float bx = 0.f, by = 0.f, bz = 0.f;
+            WDual<P>::l2p(Lf, dxp, dyp, dzp, bx, by, bz);
+            kadd(ax, cx, bx * (u * u));
+            kadd(ay, cy, by * (u * u));
+            kadd(az, cz, bz * (u * u));
+          }
+          __syncwarp();
+        }
+      }
+    }
     if (act && (!tr.sact || tr.sact[i])) {
-      w.acc[i] = ax - cx;
-      w.acc[tr.n + i] = ay - cy;
-      w.acc[2 * tr.n + i] = az - cz;
+      if constexpr (DF) {
+        // (ax - cx) + (dsh + dsl), the large parts added error-free first
+        const T a3[3] = {ax, ay, az}, c3[3] = {cx, cy, cz};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          float h, e;
+          two_sum(s_df[wid][d][lane], a3[d], h, e);
+          w.acc[d * tr.n + i] = h + ((e + s_df[wid][3 + d][lane]) - c3[d]);
+        }
+      } else {
+        w.acc[i] = ax - cx;
+        w.acc[tr.n + i] = ay - cy;
+        w.acc[2 * tr.n + i] = az - cz;
+      }
     }
     if (lane == 0) {
       atomicAdd(&w.counters[0], n_p2p * (unsigned long long)cnt);
       atomicAdd(&w.counters[1], n_m2p * (unsigned long long)cnt);
+      if (n_m2l) atomicAdd(&w.counters[4], n_m2l);  // one per (cell, group)
     }
     for (int o = 16; o > 0; o >>= 1) hsum += __shfl_xor_sync(FULL, hsum, o);
     if (lane == 0) {
@@ -429,13 +707,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   }
 }
 
-template <typename T, int P, int WARPS, int MINB, bool PK>
+template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK>
 cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
   // resident blocks per SM, queried once per variant (and so never while a
   // stream is being captured, after the first evaluation)
   static int occ = 0;
   if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB, PK>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB, PK, DUALK>,
                                                                    WARPS * 32, 0);
     if (e) {
       occ = 0;
@@ -444,24 +722,36 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
   }
   int grid = nsm * (occ > 0 ? occ : 1);
   if (grid > max_blocks) grid = max_blocks;
-  walk_kernel<T, P, WARPS, MINB, PK><<<grid, WARPS * 32, 0, s>>>(a);
+  walk_kernel<T, P, WARPS, MINB, PK, DUALK><<<grid, WARPS * 32, 0, s>>>(a);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
 
 // launch variants (warps per block, minimum resident blocks per SM, M2P
-// form); the register budget per thread follows from the first two.  The
-// stack is sized for 8 warps per block.
+// form): 16 warps per SM in blocks of 8 or 4, so every variant has 128
+// registers per thread (none spills); with the dual form 8 or 12 warps per SM.
+// The stack is sized for 8 warps per block.
 template <typename T, int P>
 cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
-    return launch_walk<T, P, 4, 1, false>(a, nsm, max_blocks, s);
+    return launch_walk<T, P, 4, 1, false, false>(a, nsm, max_blocks, s);
   } else {
+    if constexpr (WDual<P>::has) {
+      if (a.dual) {
+        // the cell-group expansions need more registers: 8 or 12 warps per SM
+        switch (v) {
+          case 0: return launch_walk<T, P, 8, 1, false, true>(a, nsm, max_blocks, s);
+          case 1: return launch_walk<T, P, 4, 3, false, true>(a, nsm, max_blocks, s);
+          case 2: return launch_walk<T, P, 8, 1, true, true>(a, nsm, max_blocks, s);
+          default: return launch_walk<T, P, 4, 3, true, true>(a, nsm, max_blocks, s);
+        }
+      }
+    }
     switch (v) {
-      case 0: return launch_walk<T, P, 8, 2, false>(a, nsm, max_blocks, s);
-      case 1: return launch_walk<T, P, 8, 3, false>(a, nsm, max_blocks, s);
-      case 2: return launch_walk<T, P, 8, 2, true>(a, nsm, max_blocks, s);
-      default: return launch_walk<T, P, 4, 5, true>(a, nsm, max_blocks, s);
+      case 0: return launch_walk<T, P, 8, 2, false, false>(a, nsm, max_blocks, s);
+      case 1: return launch_walk<T, P, 4, 4, false, false>(a, nsm, max_blocks, s);
+      case 2: return launch_walk<T, P, 8, 2, true, false>(a, nsm, max_blocks, s);
+      default: return launch_walk<T, P, 4, 4, true, false>(a, nsm, max_blocks, s);
     }
   }
 }
@@ -481,14 +771,15 @@ template <typename T, int P>
 cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
-  const int fp = sizeof(T) == 8;
-  if (forced >= 0) return launch_variant<T, P>(fp ? 0 : forced, a, nsm, max_blocks, s);
+  // tuning key: 0 FP32, 1 FP64, 2 FP32 with the dual form
+  const int fp = sizeof(T) == 8 ? 1 : (a.dual ? 2 : 0);
+  if (forced >= 0) return launch_variant<T, P>(fp == 1 ? 0 : forced, a, nsm, max_blocks, s);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const auto& t : g_tune)
       if (t.device == dev && t.order == P && t.fp64 == fp) return launch_variant<T, P>(t.variant, a, nsm, max_blocks, s);
   }
-  if (fp) {
+  if (fp == 1) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tune.push_back({dev, P, fp, 0, {}});
     return launch_variant<T, P>(0, a, nsm, max_blocks, s);
@@ -533,12 +824,12 @@ int nb_walk_warps(bool fp64) { return fp64 ? 4 : 8; }
 // the variant the autotuner chose for (precision, order) on this device, or
 // -1; ms (nullable, kWalkVariantsMax entries) receives each variant's time
 // in the tuning run (0 for variants not timed)
-int nb_walk_variant(bool fp64, int order, double* ms) {
+int nb_walk_variant(bool fp64, bool dual, int order, double* ms) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   for (const auto& t : g_tune)
-    if (t.device == dev && t.order == order && t.fp64 == (fp64 ? 1 : 0)) {
+    if (t.device == dev && t.order == order && t.fp64 == (fp64 ? 1 : (dual ? 2 : 0))) {
       if (ms)
         for (int v = 0; v < kVariants; v++) ms[v] = t.ms[v];
       return t.variant;
@@ -550,7 +841,8 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     const void* eps2, const long long* thr, int n_direct, int le, int* stack,
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
                     unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
-                    int mac_edge, int bg, cudaStream_t s) {
+                    int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
+                    cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
 #define NB_WALK(TT, P)                                                             \
@@ -564,6 +856,11 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.n_direct = n_direct;                                                         \
     a.mac_edge = mac_edge;                                                         \
     a.bg = bg;                                                                     \
+    a.k1 = k1;                                                                     \
+    a.dual = dual;                                                                 \
+    a.theta2 = theta * theta;                                                      \
+    a.mom32 = mom32;                                                               \
+    a.lu = lu;                                                                     \
     a.le = le;                                                                     \
     a.stack = stack;                                                               \
     a.stack_cap = stack_cap;                                                       \

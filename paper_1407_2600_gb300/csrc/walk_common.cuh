@@ -12,6 +12,79 @@ __device__ __forceinline__ void kadd(T& s, T& c, T x) {
   s = t;
 }
 
+// kadd on both halves of an FP32 pair, in packed instructions
+__device__ __forceinline__ void kadd2(float2& s, float2& c, float2 x) {
+  const float2 y = __fadd2_rn(x, make_float2(-c.x, -c.y));
+  const float2 t = __fadd2_rn(s, y);
+  const float2 d = __fadd2_rn(t, make_float2(-s.x, -s.y));
+  c = __fadd2_rn(d, make_float2(-y.x, -y.y));
+  s = t;
+}
+
+// Error-free transformations of FP32 sums (Knuth's TwoSum; Dekker's
+// Fast2Sum for |a| >= |b|): s + e equals a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// Largest cells whose monopole term is formed in double-float arithmetic:
+// level <= kDfLevel (side >= 1/16 of the box).
+constexpr float kDfScale = 16.f;
+
+// The monopole term b0 R f(R), f = -(|R|^2 + eps^2)^(-3/2), of a cell's
+// expansion (R = x sc + o in the cell's unit, sc a power of two) in
+// double-float arithmetic -- every value an unevaluated sum hi + lo of two
+// FP32 numbers, sums and products made error-free by TwoSum and the FMA
+// two-product -- added to the double-float accumulators (sh, sl).  On a
+// nearly uniform box the largest cells' monopole terms are a thousand times
+// the force they add up to, and in plain FP32 their few-ulp rounding sets the
+// error of the result; this form leaves an error of order 2^-44 of each term.
+__device__ __forceinline__ void mono_df(float x, float y, float z, float sc, float ox, float oy, float oz, float e2,
+                                        float b0, float* sh, float* sl) {
+  float Rh[3], Rl[3];
+  two_sum(x * sc, ox, Rh[0], Rl[0]);  // x sc is exact
+  two_sum(y * sc, oy, Rh[1], Rl[1]);
+  two_sum(z * sc, oz, Rh[2], Rl[2]);
+  // s = |R|^2 + eps^2
+  float p[3], pe[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    p[d] = Rh[d] * Rh[d];
+    pe[d] = fmaf(Rh[d], Rh[d], -p[d]) + 2.f * Rh[d] * Rl[d];
+  }
+  float s1, t1, s2, t2, s3, t3;
+  two_sum(p[0], p[1], s1, t1);
+  two_sum(s1, p[2], s2, t2);
+  two_sum(s2, e2, s3, t3);
+  float shi, slo;
+  fast_two_sum(s3, ((t1 + t2) + t3) + ((pe[0] + pe[1]) + pe[2]), shi, slo);
+  // r = s^(-1/2): one Newton step from the hardware value, residual exact
+  const float r0 = rsqrtf(shi);
+  const float q = r0 * r0, ql = fmaf(r0, r0, -q);
+  float res = fmaf(-shi, q, 1.f);
+  res = fmaf(-shi, ql, res);
+  res = fmaf(-slo, q, res);  // 1 - s r0^2
+  // f = -r^3 = -r0^3 (1 + 3 res / 2), second order in res dropped (|res| < 1e-6)
+  const float c = r0 * q, cl = fmaf(r0, q, -c) + r0 * ql;
+  const float fh = -c, fl = -(cl + c * (1.5f * res));
+  const float u = b0 * fh, ul = fmaf(b0, fh, -u) + b0 * fl;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const float v = u * Rh[d];
+    const float vl = fmaf(u, Rh[d], -v) + (u * Rl[d] + ul * Rh[d]);
+    float h, e;
+    two_sum(sh[d], v, h, e);
+    sh[d] = h;
+    sl[d] += e + vl;
+  }
+}
+
 __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   int x = v;
 #pragma unroll
@@ -22,7 +95,7 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   return x - v;
 }
 
-enum { NB_CELL_NONE = 0, NB_CELL_OPEN = 1, NB_CELL_M2P = 2, NB_CELL_P2P = 3 };
+enum { NB_CELL_NONE = 0, NB_CELL_OPEN = 1, NB_CELL_M2P = 2, NB_CELL_P2P = 3, NB_CELL_M2L = 4 };
 
 // term of the order-independent checksum (a sum modulo 2^64) of every
 // (group, cell, decision) of a walk and of every group's members: any change

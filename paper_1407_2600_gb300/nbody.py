@@ -29,27 +29,31 @@ NBODY_FP64 = 1
 NBODY_FLAG_ASYNC = 1
 NBODY_FLAG_MAC_EDGE = 2
 NBODY_FLAG_BACKGROUND = 4
+NBODY_FLAG_K1 = 8
+NBODY_FLAG_DUAL = 16
 
 
 def NBODY_FLAG_WALK_VARIANT(v: int) -> int:
     """flags bits selecting walk launch variant v instead of the autotuned one"""
     return (v + 1) << 8
 EXPORT = {"sorted_keys": 1, "perm": 2, "cell_keys": 3, "cell_range": 4, "cell_level": 5,
-          "moments": 6, "groups": 7}
+          "moments": 6, "groups": 7, "image_table": 8}
 
 # every symbol include/nbody.h declares
-SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces", "nbody_forces64",
+SYMBOLS = ["nbody_default_params", "nbody_build_tree", "nbody_build_tree_batched", "nbody_forces_batched",
+           "nbody_forces", "nbody_forces64",
            "nbody_kdk_step", "nbody_assign_rungs", "nbody_forces_active", "nbody_kdk_multistep", "nbody_kdk_adjoint", "nbody_kdk_adjoint_acc", "nbody_forces_vjp", "nbody_tree_count",
            "nbody_tree_export", "nbody_tree_lookup", "nbody_reserve", "nbody_autotune", "nbody_check",
            "nbody_tree_free",
-           "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss"]
+           "nbody_strerror", "nbody_timing_read", "nbody_sort_keys_noalloc", "nbody_cic_loss",
+           "nbody_zeldovich_state", "nbody_zeldovich_vjp"]
 
 
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("theta", C.c_double), ("order", C.c_int), ("n_leaf", C.c_int),
                 ("n_group", C.c_int), ("n_direct", C.c_int), ("lmax", C.c_int),
                 ("ewald_order", C.c_int), ("ewald_level", C.c_int), ("ewald_grid", C.c_int),
-                ("precision", C.c_int), ("flags", C.c_int)]
+                ("precision", C.c_int), ("flags", C.c_int), ("box_len", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -69,7 +73,8 @@ class Timing(C.Structure):
                 ("ms_sort", C.c_double), ("ms_build", C.c_double), ("ms_upward", C.c_double),
                 ("ms_walk", C.c_double), ("ms_periodic", C.c_double),
                 ("adjoint_steps", C.c_int64), ("adjoint_reused", C.c_int64),
-                ("decision_hash", C.c_uint64), ("walk_variant", C.c_int64), ("walk_tune_ms", C.c_double * 8)]
+                ("decision_hash", C.c_uint64), ("walk_variant", C.c_int64), ("walk_tune_ms", C.c_double * 8),
+                ("m2l_dual", C.c_double)]
 
     def asdict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -112,6 +117,9 @@ def lib():
         L.nbody_build_tree.argtypes = [C.POINTER(Params), C.c_int64, _vp, _vp, C.POINTER(_vp), _vp]
         L.nbody_build_tree_batched.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_int64),
                                                C.POINTER(C.c_double), _vp, _vp, C.POINTER(_vp), _vp]
+        L.nbody_forces_batched.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_int64),
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double), _vp, _vp, _vp,
+                                           C.POINTER(_vp), _vp]
         L.nbody_forces.argtypes = [_vp, _vp, C.POINTER(Stats), _vp]
         L.nbody_forces64.argtypes = [_vp, _vp, _vp]
         L.nbody_kdk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp]
@@ -134,6 +142,8 @@ def lib():
         L.nbody_timing_read.argtypes = [_vp, C.POINTER(Timing), C.c_int]
         L.nbody_sort_keys_noalloc.argtypes = [_vp, C.c_int64, _vp, _vp, _vp]
         L.nbody_cic_loss.argtypes = [_vp, _vp, C.c_int64, C.c_int, _vp, _vp, _vp, _vp]
+        L.nbody_zeldovich_state.argtypes = [C.c_int64, _vp, _vp, C.c_double, _vp, _vp, _vp]
+        L.nbody_zeldovich_vjp.argtypes = [C.c_int64, C.c_double, _vp, _vp, _vp, _vp]
         L.nbody_strerror.argtypes = [C.c_int]
         L.nbody_strerror.restype = C.c_char_p
         _LIB = L
@@ -167,6 +177,18 @@ def nbody_build_tree_batched(params: Params, offsets, eps, pos_dev: int, mass_de
     h = _vp(tree)
     rc = lib().nbody_build_tree_batched(C.byref(params), nbox, off, ep, pos_dev, mass_dev,
                                         C.byref(h), stream)
+    return rc, h.value
+
+
+def nbody_forces_batched(params: Params, offsets, box_len, eps, pos_dev: int, mass_dev: int | None, acc_dev: int,
+                         tree=None, stream: int | None = None):
+    nbox = len(offsets) - 1
+    off = (C.c_int64 * (nbox + 1))(*[int(v) for v in offsets])
+    ln = None if box_len is None else (C.c_double * nbox)(*[float(v) for v in box_len])
+    ep = None if eps is None else (C.c_double * nbox)(*[float(v) for v in eps])
+    h = _vp(tree)
+    rc = lib().nbody_forces_batched(C.byref(params), nbox, off, ln, ep, pos_dev, mass_dev, acc_dev, C.byref(h),
+                                    stream)
     return rc, h.value
 
 
@@ -425,6 +447,8 @@ class Tree:
             t = torch.empty((cnt, 2), dtype=torch.int32, device=self.pos.device)
         elif what == "cell_level":
             t = torch.empty(cnt, dtype=torch.int32, device=self.pos.device)
+        elif what == "image_table":
+            t = torch.empty(cnt, dtype=torch.float64, device=self.pos.device)
         else:
             o = self.params.order
             t = torch.empty((cnt, (o + 1) * (o + 2) * (o + 3) // 6), dtype=torch.float64, device=self.pos.device)
@@ -448,6 +472,37 @@ class Tree:
             self.close()
         except Exception:
             pass
+
+
+def nbody_zeldovich_state(n: int, q_dev: int, psi_dev: int, a: float, pos_dev: int, mom_dev: int,
+                          stream: int | None = None) -> int:
+    return lib().nbody_zeldovich_state(n, q_dev, psi_dev, a, pos_dev, mom_dev, stream)
+
+
+def nbody_zeldovich_vjp(n: int, a: float, lam_pos_dev: int, lam_mom_dev: int, dpsi_dev: int,
+                        stream: int | None = None) -> int:
+    return lib().nbody_zeldovich_vjp(n, a, lam_pos_dev, lam_mom_dev, dpsi_dev, stream)
+
+
+def zeldovich_state(q, psi, a):
+    """(x, p) = (q + a psi wrapped, H0 a^(3/2) psi) from (3, n) FP64 CUDA tensors."""
+    import torch
+    q, psi = q.contiguous(), psi.contiguous()
+    x = torch.empty_like(q)
+    p = torch.empty(q.shape, dtype=torch.float32, device=q.device)
+    _check(nbody_zeldovich_state(q.shape[1], q.data_ptr(), psi.data_ptr(), a, x.data_ptr(), p.data_ptr(),
+                                 _stream()), "nbody_zeldovich_state")
+    return x, p
+
+
+def zeldovich_vjp(a, lam_x, lam_p):
+    """a lam_x + H0 a^(3/2) lam_p as a (3, n) FP64 CUDA tensor."""
+    import torch
+    lx, lp = lam_x.contiguous(), lam_p.contiguous().float()
+    out = torch.empty(lx.shape, dtype=torch.float64, device=lx.device)
+    _check(nbody_zeldovich_vjp(lx.shape[1], a, lx.data_ptr(), lp.data_ptr(), out.data_ptr(), _stream()),
+           "nbody_zeldovich_vjp")
+    return out
 
 
 def cic_loss(pos, ng, mass=None, grad=True):

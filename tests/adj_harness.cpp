@@ -346,7 +346,66 @@ template <int PE> void run_field_io() {
   for (int k = 0; k < 3; k++) std::printf("%.17g\n", a[k]);
 }
 
+// the dual form's cell-group interaction: moments (nmom(P)), R, eps and the
+// sink offset d read from stdin; prints the derivative tensor of g at R
+// (orders <= P + 1) and the acceleration at d of the local expansion about z
+template <int P> void dtens(double x, double y, double z, double e2, double* D);
+template <> void dtens<1>(double x, double y, double z, double e2, double* D) { dtensor_p2<double>(x, y, z, e2, D); }
+template <> void dtens<2>(double x, double y, double z, double e2, double* D) { dtensor_p3<double>(x, y, z, e2, D); }
+template <> void dtens<3>(double x, double y, double z, double e2, double* D) { dtensor_p4<double>(x, y, z, e2, D); }
+template <> void dtens<4>(double x, double y, double z, double e2, double* D) { dtensor_p5<double>(x, y, z, e2, D); }
+struct MAcc {
+  const double* m;
+  double operator[](int u) const { return m[u]; }
+};
+template <int P> void l2pd(const double* L, double x, double y, double z, double& ax, double& ay, double& az);
+#define DUAL_DISPATCH(P)                                                                         \
+  template <> void l2pd<P>(const double* L, double x, double y, double z, double& ax, double& ay, double& az) { \
+    l2p_pe##P<double>(L, x, y, z, ax, ay, az);                                                    \
+  }
+DUAL_DISPATCH(1)
+DUAL_DISPATCH(2)
+DUAL_DISPATCH(3)
+DUAL_DISPATCH(4)
+
+template <int P> void run_dual_io() {
+  const int NM = (P + 1) * (P + 2) * (P + 3) / 6, NP = (P + 2) * (P + 3) * (P + 4) / 6;
+  double M[35], R[3], eps, d[3], D[56], L[55];
+  for (int t = 0; t < NM; t++)
+    if (std::scanf("%lf", &M[t]) != 1) std::exit(2);
+  for (int k = 0; k < 3; k++)
+    if (std::scanf("%lf", &R[k]) != 1) std::exit(2);
+  if (std::scanf("%lf", &eps) != 1) std::exit(2);
+  for (int k = 0; k < 3; k++)
+    if (std::scanf("%lf", &d[k]) != 1) std::exit(2);
+  dtens<P>(R[0], R[1], R[2], eps * eps, D);
+  for (int t = 0; t < NP; t++) std::printf("%.17g\n", D[t]);
+  for (int t = 0; t < NP; t++) D[t] = -D[t];  // the image-field L2P subtracts: feed it -d g
+  for (int t = 0; t < NP - 1; t++) L[t] = 0.0;
+  const MAcc acc{M};
+  auto red = [&](int t, int, double v) { L[t] += v; };
+  if constexpr (P == 1) m2l_red_p1<double>(acc, D, red);
+  if constexpr (P == 2) m2l_red_p2<double>(acc, D, red);
+  if constexpr (P == 3) m2l_red_p3<double>(acc, D, red);
+  if constexpr (P == 4) m2l_red_p4<double>(acc, D, red);
+  double a[3] = {0, 0, 0};
+  l2pd<P>(L, d[0], d[1], d[2], a[0], a[1], a[2]);
+  for (int k = 0; k < 3; k++) std::printf("%.17g\n", a[k]);
+}
+
 int main(int argc, char** argv) {
+  if (argc > 1 && std::string(argv[1]) == "dual") {
+    int p = -1;
+    if (std::scanf("%d", &p) != 1) return 2;
+    switch (p) {
+      case 1: run_dual_io<1>(); break;
+      case 2: run_dual_io<2>(); break;
+      case 3: run_dual_io<3>(); break;
+      case 4: run_dual_io<4>(); break;
+      default: return 2;
+    }
+    return 0;
+  }
   if (argc > 1 && std::string(argv[1]) == "field") {
     int pe = -1;
     if (std::scanf("%d", &pe) != 1) return 2;

@@ -120,12 +120,21 @@ def test_more_invalid_arguments_are_rejected_without_gpu_work():
     # every parameter outside its documented range
     bad = [("theta", 0.0), ("theta", -0.5), ("eps", -1e-3), ("order", 5), ("order", -1), ("n_leaf", 0),
            ("n_leaf", 65), ("n_group", 0), ("n_group", 33), ("n_direct", -1), ("lmax", 1), ("lmax", 22),
-           ("ewald_order", 6), ("ewald_grid", 3), ("ewald_grid", 9), ("ewald_level", 0), ("precision", 2)]
+           ("ewald_order", 6), ("ewald_grid", 3), ("ewald_grid", 9), ("ewald_level", 0), ("precision", 2),
+           ("box_len", -1.0), ("box_len", float("nan")), ("box_len", float("inf")), ("flags", 32),
+           ("flags", 1 << 12)]
     for name, value in bad:
         p = nb.nbody_default_params()
         setattr(p, name, value)
         rc, h = nb.nbody_build_tree(p, 10, 1, None)
         assert rc == EINVAL and not h, (name, value, rc)
+    # combinations the dual form does not take: order 0, FP64, background terms
+    for name, value in (("order", 0), ("precision", 1), ("flags", nb.NBODY_FLAG_DUAL | nb.NBODY_FLAG_BACKGROUND)):
+        p = nb.nbody_default_params()
+        p.flags = nb.NBODY_FLAG_DUAL
+        setattr(p, name, value if name != "flags" else value)
+        rc, h = nb.nbody_build_tree(p, 10, 1, None)
+        assert rc == nb.NBODY_ENOTSUP and not h, (name, value, rc)
     p = nb.nbody_default_params()
     # sizes: no particles, or at least 2^30 of them
     for n in (0, -5, 1 << 30):
@@ -138,6 +147,12 @@ def test_more_invalid_arguments_are_rejected_without_gpu_work():
         assert rc == EINVAL and not h, (off, eps)
     rc, h = nb.nbody_build_tree_batched(p, [0, 4, 8], None, 0, None)  # NULL positions
     assert rc == EINVAL and not h
+    # build-and-evaluate: NULL accelerations, a non-positive box length
+    rc, h = nb.nbody_forces_batched(p, [0, 4, 8], None, None, 1, None, 0)
+    assert rc == EINVAL and not h
+    for ln in ([1.0, 0.0], [250.0, -1.0], [float("nan"), 1.0]):
+        rc, h = nb.nbody_forces_batched(p, [0, 4, 8], ln, None, 1, None, 1)
+        assert rc == EINVAL and not h, ln
     # NULL tree handles
     assert nb.nbody_tree_count(None, 0) == EINVAL
     assert nb.nbody_tree_export(None, 0, 1) == EINVAL

@@ -117,3 +117,34 @@ def test_image_field_expansion_converges_at_its_order(harness, pe):
     assert errs[2] <= 0.02 * 0.3 ** (pe - 1)
     for i in range(2):
         assert errs[i] / errs[i + 1] >= 0.8 * 2 ** (pe + 1), (pe, errs)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_dual_form_kernels_match_the_oracle(harness, p):
+    """The walk's generated derivative tensor of the softened kernel (by the
+    Cartesian recurrence) against the oracle's Hermite-product form, and its
+    generated cell-group M2L (one local coefficient at a time) followed by
+    the L2P against the oracle's or_m2l / or_l2p, in FP64 on the host."""
+    import oracle
+    rng = np.random.default_rng(40 + p)
+    for _ in range(6):
+        c = rng.uniform(-0.1, 0.1, 3)
+        pts = c + 0.05 * rng.standard_normal((12, 3))
+        M = oracle.p2m(pts, rng.uniform(0.5, 1.5, 12), c, p)
+        R = rng.uniform(0.4, 1.0, 3) * rng.choice([-1, 1], 3)
+        eps = 10 ** rng.uniform(-3, -1)
+        d = 0.1 * rng.standard_normal(3)
+        inp = "%d\n%s\n%s\n%.17g\n%s\n" % (p, " ".join("%.17g" % v for v in M), " ".join("%.17g" % v for v in R),
+                                          eps, " ".join("%.17g" % v for v in d))
+        r = subprocess.run([harness, "dual"], input=inp, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        out = np.array([float(v) for v in r.stdout.split()])
+        nd = oracle.nmom(p + 1)
+        D, a = out[:nd], out[nd:]
+        Dref = oracle.dtensor(R, eps, p + 1)
+        order = np.array([sum(m) for m in oracle.multi_indices(p + 1)])
+        for o in range(p + 2):
+            sc = np.abs(Dref[order == o]).max()
+            assert np.abs(D[order == o] - Dref[order == o]).max() <= 1e-13 * sc, (p, o)
+        aref = oracle.l2p(oracle.m2l(M, p, R, eps), p, d)
+        assert np.abs(a - aref).max() <= 1e-13 * np.abs(aref).max(), (p, a, aref)

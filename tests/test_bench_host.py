@@ -32,7 +32,22 @@ def test_phase_bytes_per_particle():
     assert b["ms_build"] == 152 * n + 194 * nc + 168 * ng
     assert b["ms_upward"] == 28 * n + 843 * nc  # 91 + 16 * 35 + 4 * 48 per cell at p = 4
     assert b["ms_periodic"] == 64 * n
-    assert abs(bench.fp32_peak_tflops(2070.0) - 80.54784) < 1e-9
+    assert abs(bench.fp32_peak_tflops(2070.0, 152) - 80.54784) < 1e-9
+    assert abs(bench.fp32_peak_tflops(2070.0, 148) - 80.54784 * 148 / 152) < 1e-9
+
+
+def test_accuracy_bar_flag():
+    assert bench.meets_bar({"median": 6.8e-4, "p99": 8.6e-3})
+    assert not bench.meets_bar({"median": 1.03e-3, "p99": 5e-3})
+    assert not bench.meets_bar({"median": 5e-4, "p99": 1.1e-2})
+    assert not bench.meets_bar(None)
+
+
+def test_line_summary_keeps_the_named_keys():
+    rec = {"a": 1, "b": {"c": 2}, "bulky": list(range(100))}
+    assert bench._summary(rec, ("a", "b", "missing")) == {"a": 1, "b": {"c": 2}, "missing": None}
+    assert bench._summary(None, ("a",)) is None
+    assert bench._summary({"error": "x"}, ("a",)) == {"error": "x"}
 
 
 def test_reference_arm_line(capsys):
@@ -50,6 +65,9 @@ def test_reference_arm_line(capsys):
     assert line["value"] > 0 and line["higher_is_better"] is True
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    # the step time is the sample's own wall time, so the run fits its clock
+    assert 0 < line["ms_per_step"] < 600e3
+    assert line["extrapolated_full_evaluation_updates_per_s"] > 0
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

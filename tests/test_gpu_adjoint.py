@@ -286,3 +286,26 @@ def test_batched_force_vjp_matches_single_boxes(cuda):
         got = mu[off[b]:off[b + 1]]
         rms = np.sqrt(np.mean(m1 ** 2))
         assert np.abs(got - m1).max() <= 1e-5 * rms, (b, np.abs(got - m1).max() / rms)
+
+
+def test_zeldovich_state_and_its_transpose(cuda):
+    """The trajectory's starting state x = q + a psi (wrapped), p = H0
+    a^(3/2) psi through the C ABI against the oracle's zeldovich_state, and
+    the transpose dpsi = a lam_x + H0 a^(3/2) lam_p against the same linear
+    map applied on the host (positions bit for bit, FP32 momenta within an
+    ulp, the transpose to FP64 rounding)."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    rng = np.random.default_rng(21)
+    q = ics.lattice(12)
+    psi = 0.3 * rng.standard_normal(q.shape)  # large enough to cross the box edge
+    a = 0.07
+    x, p = nb.zeldovich_state(_t(q, cuda), _t(psi, cuda), a)
+    xo, po = oracle.zeldovich_state(q, psi, a)
+    assert np.array_equal(x.cpu().numpy().T, xo)
+    assert np.abs(p.cpu().numpy().T - po).max() <= 2 * np.spacing(np.float32(np.abs(po).max()))
+    lx = rng.standard_normal(q.shape)
+    lp = rng.standard_normal(q.shape).astype(np.float32)
+    d = nb.zeldovich_vjp(a, _t(lx, cuda), _t(lp, cuda, torch.float32)).cpu().numpy().T
+    ref = a * lx + oracle.H0 * a ** 1.5 * lp.astype(np.float64)
+    assert np.abs(d - ref).max() <= 1e-14 * np.abs(ref).max()

@@ -84,7 +84,7 @@ def test_fullsize_error_vs_direct_ewald(cuda, cfg2, cfg2_direct):
     a, _ = _forces(x, cuda, eps=eps, theta=0.6, order=4, n_direct=8, ewald_grid=5)
     rel = _rel(a[tg], ad)
     print("theta=0.6 p=4 (benchmark setting): median %.3e p99 %.3e" % (np.median(rel), np.percentile(rel, 99)))
-    assert np.median(rel) <= 1e-3
+    assert np.median(rel) <= 1e-3 and np.percentile(rel, 99) <= 1e-2
     a, _ = _forces(x, cuda, eps=eps, theta=0.5, order=4, n_direct=4, ewald_grid=6)
     rel = _rel(a[tg], ad)
     print("theta=0.5 p=4: median %.3e p99 %.3e" % (np.median(rel), np.percentile(rel, 99)))
@@ -93,17 +93,19 @@ def test_fullsize_error_vs_direct_ewald(cuda, cfg2, cfg2_direct):
 
 def test_batched_uneven_boxes_vs_direct_and_tree(cuda):
     """Three uneven boxes of the batched workload (48^3, 64^3, 80^3) in one
-    build at its setting (theta 0.5, quadrupole, face-distance opening
-    test): per box, sampled forces against the oracle tree (median <= 1e-5)
-    and against the direct Ewald sum.  These near-uniform boxes (rms
-    displacement 0.25 spacing) reach a median of 2-3e-3 at quadrupole order
-    (the oracle gives the same), so the bound here is median <= 5e-3 and 99th
-    percentile <= 3e-2; at hexadecapole order they reach 1-2e-4."""
+    build at the benchmark's setting (theta 0.5, quadrupole, face-distance
+    opening test, uniform-background terms, accepted cells of <= 16
+    particles summed directly): per box, sampled forces against the oracle
+    tree (median <= 1e-5) and against the direct Ewald sum at the accuracy
+    bar (median <= 1e-3, 99th percentile <= 1e-2).  Without the background
+    terms and with the tuned direct-sum threshold of 2 these near-uniform
+    boxes (rms displacement 0.25 spacing) sit at 1-2.5e-3."""
     import torch
     import paper_1407_2600_gb300.nbody as nb
     x, p, off, eps = ics.config_batched(7, sizes=(48, 64, 80))
     pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=cuda)
-    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=2, ewald_grid=4, flags=nb.NBODY_FLAG_MAC_EDGE)
+    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=16, ewald_grid=4,
+                    flags=nb.NBODY_FLAG_MAC_EDGE | nb.NBODY_FLAG_BACKGROUND)
     tree = nb.Tree(prm, pos, offsets=off.tolist(), eps=eps)
     acc = tree.forces().cpu().numpy().T.astype(np.float64)
     tree.close()
@@ -111,12 +113,13 @@ def test_batched_uneven_boxes_vs_direct_and_tree(cuda):
         xb = x[off[b]:off[b + 1]]
         tg = ics.random_targets(len(xb), 256, 50 + b)
         ad = oracle.direct_forces(xb, None, eps[b], targets=tg, table_n1=128)
-        at = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.5, 2, n_direct=2, ewald=4, mac=1,
-                                                             ew_grid=4), targets=tg)
+        at = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.5, 2, n_direct=16, ewald=4, mac=1,
+                                                             ew_grid=4, bg=4), targets=tg)
         a = acc[off[b] + tg]
         rd = np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)
         rt = np.linalg.norm(a - at, axis=1) / np.linalg.norm(at, axis=1)
-        assert np.median(rd) <= 5e-3 and np.percentile(rd, 99) <= 3e-2, (b, np.median(rd), np.percentile(rd, 99))
+        print("box %d: median %.3e p99 %.3e vs direct Ewald" % (b, np.median(rd), np.percentile(rd, 99)))
+        assert np.median(rd) <= 1e-3 and np.percentile(rd, 99) <= 1e-2, (b, np.median(rd), np.percentile(rd, 99))
         assert np.median(rt) <= 1e-5, (b, np.median(rt))
 
 

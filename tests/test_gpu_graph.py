@@ -169,8 +169,8 @@ def test_fullsize_96_boxes_captured_force_vs_oracle(cuda):
     x, p, off, eps = ics.config_batched(1)
     assert off[-1] == 32 * (48 ** 3 + 64 ** 3 + 80 ** 3)
     pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=cuda)
-    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=2, ewald_grid=4,
-                    flags=nb.NBODY_FLAG_ASYNC | nb.NBODY_FLAG_MAC_EDGE)
+    prm = nb.params(eps=eps[0], theta=0.5, order=2, n_direct=16, ewald_grid=4,
+                    flags=nb.NBODY_FLAG_ASYNC | nb.NBODY_FLAG_MAC_EDGE | nb.NBODY_FLAG_BACKGROUND)
     tree = nb.Tree(prm, pos, offsets=off.tolist(), eps=eps)
     acc_e = tree.forces()
     torch.cuda.synchronize()
@@ -193,7 +193,7 @@ def test_fullsize_96_boxes_captured_force_vs_oracle(cuda):
     for b in (0, 40, 95):
         xb = x[off[b]:off[b + 1]]
         tgt = ics.random_targets(len(xb), 256, 300 + b)
-        at = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.5, 2, n_direct=2, ewald=4, mac=1,
-                                                             ew_grid=4), targets=tgt)
+        at = oracle.tree_forces(xb, None, oracle.tree_params(eps[b], 0.5, 2, n_direct=16, ewald=4, mac=1,
+                                                             ew_grid=4, bg=4), targets=tgt)
         rt = np.linalg.norm(a[off[b] + tgt] - at, axis=1) / np.linalg.norm(at, axis=1)
         assert np.median(rt) <= 1e-5, (b, np.median(rt))

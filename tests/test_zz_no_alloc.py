@@ -50,3 +50,27 @@ def test_noalloc_rejects_sizes_beyond_its_maximum(cuda):
     rc = nb.nbody_sort_keys_noalloc(pos.data_ptr(), (1 << 20) + 1, out.data_ptr(), out.data_ptr(), nb._stream())
     assert rc == nb.NBODY_ERANGE
     assert "maximum" in nb.nbody_strerror(rc)
+
+
+def test_noalloc_rejects_non_finite_positions(cuda):
+    """A NaN or infinite coordinate is reported as NBODY_EINVAL, as
+    nbody_build_tree reports it, and the next call on finite positions is
+    unaffected (the error word is cleared per call)."""
+    import torch
+    import paper_1407_2600_gb300.nbody as nb
+    n = 4097
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0.0, 1.0, (n, 3))
+    for bad in (np.nan, np.inf, -np.inf):
+        y = x.copy()
+        y[1234, 2] = bad
+        pos = torch.tensor(np.ascontiguousarray(y.T), dtype=torch.float64, device=cuda)
+        rc, _, _ = _noalloc(nb, pos, n, cuda)
+        assert rc == nb.NBODY_EINVAL, nb.nbody_strerror(rc)
+    pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=cuda)
+    rc, keys, perm = _noalloc(nb, pos, n, cuda)
+    assert rc == nb.NBODY_OK, nb.nbody_strerror(rc)
+    tree = nb.Tree(nb.params(eps=1e-3), pos)
+    assert torch.equal(keys, tree.export("sorted_keys"))
+    assert torch.equal(perm, tree.export("perm"))
+    tree.close()
