@@ -46,7 +46,8 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const 
                       const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
                       uint32_t* uorder, uint32_t* uhist, int* urange, const uint16_t* cbox, const double* rho,
                       float* mom32, SortScratch* sc, cudaStream_t s);
-cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, cudaStream_t s);
+cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, double* part,
+                        cudaStream_t s);
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, const int* hval,
                              const uint64_t* ckey, const uint16_t* cbox, uint64_t hcap, const double* mom,
@@ -666,8 +667,9 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
   // A5 moments (with the background weights when asked for)
   const double* rho = nullptr;
   if (p.flags & NBODY_FLAG_BACKGROUND) {
-    NB_CU(t->rho.ensure(8 * (int64_t)t->nbox));
-    NB_CU(nb_box_mass(t->off.as<int64_t>(), t->smass.as<float>(), t->nbox, t->rho.as<double>(), s));
+    NB_CU(t->rho.ensure(8 * (int64_t)t->nbox * 65));  // the densities, then 64 partial sums per box
+    NB_CU(nb_box_mass(t->off.as<int64_t>(), t->smass.as<float>(), t->nbox, t->rho.as<double>(),
+                      t->rho.as<double>() + t->nbox, s));
     rho = t->rho.as<double>();
   }
   NB_CU(nb_upward(p.order, fp64, nc, totals, t->cA.as<int4>(), t->cB.as<int4>(), t->spos.as<double>(),

@@ -323,21 +323,35 @@ field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __
   }
 }
 
-// mean density of each box (its mass over the unit volume), one block per box
-__global__ void __launch_bounds__(256) box_mass_kernel(const int64_t* __restrict__ off, const float* __restrict__ smass,
-                                                       double* __restrict__ rho) {
+// mean density of each box (its mass over the unit volume) in two fixed-order
+// stages, so that it is bitwise reproducible: kMassParts blocks per box sum
+// contiguous slices (FP64), then one warp per box sums the slices in order
+constexpr int kMassParts = 64;
+__global__ void __launch_bounds__(256) box_mass_part_kernel(const int64_t* __restrict__ off,
+                                                            const float* __restrict__ smass,
+                                                            double* __restrict__ part) {
   __shared__ double s_red[8];
-  const int box = blockIdx.x;
+  const int box = blockIdx.y, k = blockIdx.x;
+  const int64_t lo = off[box], n = off[box + 1] - lo;
+  const int64_t a = lo + n * k / kMassParts, b = lo + n * (k + 1) / kMassParts;
   double m = 0.0;
-  for (int64_t j = off[box] + threadIdx.x; j < off[box + 1]; j += blockDim.x) m += (double)smass[j];
+  for (int64_t j = a + threadIdx.x; j < b; j += blockDim.x) m += (double)smass[j];
   for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_red[w];
-    rho[box] = t;
+    part[(int64_t)box * kMassParts + k] = t;
   }
+}
+
+__global__ void box_mass_sum_kernel(int nbox, const double* __restrict__ part, double* __restrict__ rho) {
+  const int box = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (box >= nbox) return;
+  double m = part[(int64_t)box * kMassParts + lane] + part[(int64_t)box * kMassParts + 32 + lane];
+  for (int o = 16; o > 0; o >>= 1) m += __shfl_xor_sync(0xffffffffu, m, o);
+  if (lane == 0) rho[box] = m;
 }
 
 int gridc(int64_t n, int threads) {
@@ -349,9 +363,12 @@ int gridc(int64_t n, int threads) {
 
 }  // namespace
 
-cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, cudaStream_t s) {
-  box_mass_kernel<<<nbox, 256, 0, s>>>(off, smass, rho);
-  nb_launch_counter += 1;
+// part: kMassParts doubles of scratch per box
+cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double* rho, double* part,
+                        cudaStream_t s) {
+  box_mass_part_kernel<<<dim3(kMassParts, nbox), 256, 0, s>>>(off, smass, part);
+  box_mass_sum_kernel<<<(nbox + 3) / 4, 128, 0, s>>>(nbox, part, rho);
+  nb_launch_counter += 2;
   return cudaGetLastError();
 }
 

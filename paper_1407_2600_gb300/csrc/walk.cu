@@ -106,13 +106,6 @@ NB_WDUAL(2, 3)
 NB_WDUAL(3, 4)
 NB_WDUAL(4, 5)
 
-// moments of the cell a lane works on, staged in shared memory as [n][lane]
-struct LaneMoments {
-  const float* base;
-  int lane;
-  __device__ __forceinline__ float operator[](int u) const { return base[u * 32 + lane]; }
-};
-
 template <typename T>
 struct WalkArgs {
   DevTree tr;
@@ -254,52 +247,58 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       }
     };
     // dual form: lane q forms the local expansion about the group-box centre
-    // of queued cell q; the warp sums each coefficient over its lanes and the
-    // coefficient's owner lane (t mod 32) adds it to the group's, compensated
+    // of queued cell q (its moments in registers); each coefficient's lane
+    // values go to shared memory, and whenever the buffer holds ROWS of them
+    // lane r sums row r over the lanes and adds it to the group's, compensated
     auto m2l_chunk = [&](int nml) {
       if constexpr (DUAL) {
-        // the lanes' moments (nmom(P), in 16-byte pieces) staged as [n][lane];
-        // they fit the coefficient buffer: 4 ceil(nmom(P)/4) <= NBS
         constexpr int NM4 = ((P + 1) * (P + 2) * (P + 3) / 6 + 3) / 4;
-        static_assert(4 * NM4 <= NBS, "dual staging exceeds the coefficient buffer");
-        float* sm = reinterpret_cast<float*>(&s_coef[wid][0]);
-        if (lane < nml) {
-          const float4* src = reinterpret_cast<const float4*>(w.mom32 + (int64_t)s_lidx[wid][lane] * kDualStride);
+        // rows of lane values per pass through the coefficient buffer
+        constexpr int NL = WDual<P>::NL, ROWS = (32 * NBS) / 33 < NL ? (32 * NBS) / 33 : NL;
+        const int q = lane < nml ? lane : 0;
+        const float live = lane < nml ? 1.f : 0.f;
+        float Mr[4 * NM4];
+        {
+          const float4* src = reinterpret_cast<const float4*>(w.mom32 + (int64_t)s_lidx[wid][q] * kDualStride);
 #pragma unroll
           for (int k = 0; k < NM4; k++) {
             const float4 v = src[k];
-            sm[(4 * k) * 32 + lane] = v.x;
-            sm[(4 * k + 1) * 32 + lane] = v.y;
-            sm[(4 * k + 2) * 32 + lane] = v.z;
-            sm[(4 * k + 3) * 32 + lane] = v.w;
+            Mr[4 * k] = v.x * live;
+            Mr[4 * k + 1] = v.y * live;
+            Mr[4 * k + 2] = v.z * live;
+            Mr[4 * k + 3] = v.w * live;
           }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4 * NM4; k++) sm[k * 32 + lane] = 0.f;
         }
-        __syncwarp();
-        const V4 lo = s_loff[wid][lane < nml ? lane : 0];
-        const float e2 = (float)s_leps[wid][lane < nml ? lane : 0];
+        const V4 lo = s_loff[wid][q];
+        const float e2 = (float)s_leps[wid][q];
         // 2^((level - lu)(o + 1)) takes coefficient order o to the group's unit
         float f[7];
         f[0] = __int_as_float((127 + (int)lo.w) << 23);  // 2^(level - lu), |level - lu| < 24
         f[1] = f[0] * f[0];
 #pragma unroll
         for (int o = 2; o < 7; o++) f[o] = f[o - 1] * f[0];
-        WDual<P>::m2l(LaneMoments{sm, lane}, (float)lo.x, (float)lo.y, (float)lo.z, e2, [&](int t, int o, float v) {
-          v *= f[o];
-#pragma unroll
-          for (int k = 16; k > 0; k >>= 1) v += __shfl_xor_sync(FULL, v, k);
-          if ((t & 31) == lane) {
-            const int h = t >> 5;
-            float sh = s_L[wid][0][lane + 32 * h], sc = s_L[wid][1][lane + 32 * h];
-            kadd(sh, sc, v);
-            s_L[wid][0][lane + 32 * h] = sh;
-            s_L[wid][1][lane + 32 * h] = sc;
+        float* buf = reinterpret_cast<float*>(&s_coef[wid][0]);  // rows of 33: no bank conflicts
+        auto flush = [&](int t0, int rows) {
+          __syncwarp();
+          if (lane < rows) {
+            float sacc = 0.f, scmp = 0.f;
+            for (int j = 0; j < 32; j++) kadd(sacc, scmp, buf[lane * 33 + j]);
+            float sh = s_L[wid][0][t0 + lane], sc = s_L[wid][1][t0 + lane];
+            kadd(sh, sc, sacc - scmp);
+            s_L[wid][0][t0 + lane] = sh;
+            s_L[wid][1][t0 + lane] = sc;
           }
+          __syncwarp();
+        };
+        struct RegMoments {
+          const float* m;
+          __device__ __forceinline__ float operator[](int u) const { return m[u]; }
+        };
+        WDual<P>::m2l(RegMoments{Mr}, (float)lo.x, (float)lo.y, (float)lo.z, e2, [&](int t, int o, float v) {
+          buf[(t % ROWS) * 33 + lane] = v * f[o];
+          if (t % ROWS == ROWS - 1 || t == NL - 1) flush(t - t % ROWS, t % ROWS + 1);
         });
         n_m2l += nml;
-        __syncwarp();
       }
     };
     // evaluate the first nmp queued M2P cells for every sink of the group
@@ -416,7 +415,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     if (lane == 0) stk[0] = box;  // root of this box
     __syncwarp();
     bool overflow = false;
-    while (top > 0) {
+    // each chunk routine has one call site (the end of this loop), which
+    // keeps the kernel's instruction footprint small
+    while (true) {
       const int nb = min(32, top);
       const int base = top - nb;
       top = base;
@@ -473,17 +474,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           s_meps[wid][pos] = w.k1 ? (T)0 : eps2 * (sc * sc);
         }
         qn += __popc(mm);
-        if (qn >= 32) {
-          __syncwarp();
-          m2p_chunk(32);
-          // carry the remainder to the front of the queue
-          if (lane < qn - 32) {
-            s_midx[wid][lane] = s_midx[wid][32 + lane];
-            s_moff[wid][lane] = s_moff[wid][32 + lane];
-            s_meps[wid][lane] = s_meps[wid][32 + lane];
-          }
-          qn -= 32;
-        }
         __syncwarp();
       }
       if constexpr (DUAL) {
@@ -503,16 +493,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             s_leps[wid][pos] = w.k1 ? (T)0 : eps2 * (sc * sc);
           }
           ln += __popc(lm);
-          if (ln >= 32) {
-            __syncwarp();
-            m2l_chunk(32);
-            if (lane < ln - 32) {
-              s_lidx[wid][lane] = s_lidx[wid][32 + lane];
-              s_loff[wid][lane] = s_loff[wid][32 + lane];
-              s_leps[wid][lane] = s_leps[wid][32 + lane];
-            }
-            ln -= 32;
-          }
           __syncwarp();
         }
       }
@@ -646,15 +626,44 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         }
         n_p2p += (unsigned long long)total;
       }
+      // evaluate queued cells 32 at a time, and what is left once the stack
+      // is empty (up to two chunks then: the queue holds up to 63)
+      const bool fin = top == 0;
+      while (qn >= 32 || (fin && qn > 0)) {
+        const int k = min(qn, 32);
+        __syncwarp();
+        m2p_chunk(k);
+        // carry the remainder to the front of the queue
+        if (lane < qn - k) {
+          s_midx[wid][lane] = s_midx[wid][32 + lane];
+          s_moff[wid][lane] = s_moff[wid][32 + lane];
+          s_meps[wid][lane] = s_meps[wid][32 + lane];
+        }
+        qn -= k;
+        __syncwarp();
+      }
+      if constexpr (DUAL) {
+        while (ln >= 32 || (fin && ln > 0)) {
+          const int k = min(ln, 32);
+          __syncwarp();
+          m2l_chunk(k);
+          if (lane < ln - k) {
+            s_lidx[wid][lane] = s_lidx[wid][32 + lane];
+            s_loff[wid][lane] = s_loff[wid][32 + lane];
+            s_leps[wid][lane] = s_leps[wid][32 + lane];
+          }
+          ln -= k;
+          __syncwarp();
+        }
+      }
+      if (fin) break;
     }
     if (overflow) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
     }
-    if (qn > 0) m2p_chunk(qn);
     if constexpr (DUAL) {
       if (w.dual) {
-        if (ln > 0) m2l_chunk(ln);
         const bool any = __any_sync(FULL, n_m2l > 0);
         if (any) {
           // the group's local expansion at every sink: d = (x - z) in the
