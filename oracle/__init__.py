@@ -91,6 +91,14 @@ def _lib():
             L.or_direct_forces_k.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_int, C.c_int64, _i64p,
                                              _dp, C.c_int, _dp]
             L.or_soft_factor.argtypes = [C.c_double, C.c_double, C.c_int]
+            L.or_soft_pot.argtypes = [C.c_double, C.c_double, C.c_int]
+            L.or_soft_pot.restype = C.c_double
+            L.or_direct_pot.argtypes = [C.c_int64, _dp, _dp, C.c_double, C.c_int, C.c_int64, _i64p,
+                                        _dp, C.c_int, _dp]
+            L.or_phitilde_table_build.argtypes = [C.c_int, _dp]
+            L.or_phitilde_table_eval.argtypes = [_dp, C.c_int, _dp, _dp]
+            L.or_tree_forces_pot.argtypes = [C.c_int64, _dp, _dp, C.POINTER(TreeParams), _dp,
+                                             C.c_int64, _i64p, _dp, _dp, _dp]
             L.or_soft_factor.restype = C.c_double
             L.or_direct_vjp.argtypes = [C.c_int64, _dp, _dp, C.c_double, _dp, C.c_int, _dp, _dp]
             L.or_tree_forces.argtypes = [C.c_int64, _dp, _dp, C.POINTER(TreeParams), _dp,
@@ -241,6 +249,39 @@ def direct_forces(pos, mass=None, eps=0.0, targets=None, table_n1: int | None = 
     return acc.reshape(3, nt).T.copy()
 
 
+def soft_pot(r2, eps, kernel=0) -> float:
+    """Softened pair potential of unit masses (Plummer or K1)."""
+    return _lib().or_soft_pot(float(r2), float(eps), int(kernel))
+
+
+def phitilde_table(n1: int = 128) -> np.ndarray:
+    """Tricubic table of phi~ itself (one value per node)."""
+    tab = np.zeros((n1 + 4) ** 3)
+    rc = _lib().or_phitilde_table_build(n1, _d(tab))
+    if rc != 0:
+        raise ValueError("or_phitilde_table_build failed (%d)" % rc)
+    return tab
+
+
+def direct_pot(pos, mass=None, eps=0.0, targets=None, table_n1: int | None = 128, kernel: int = 0):
+    """O1's potential: the zero-mean Ewald potential of every other particle
+    (nearest image softened) plus each particle's own images and the
+    background; ``table_n1=None`` evaluates phi~ by the exact Ewald sum."""
+    P = _soa(pos)
+    n = P.shape[1]
+    m = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
+    tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    nt = n if tg is None else len(tg)
+    out = np.zeros(nt)
+    tab = None if table_n1 is None else phitilde_table(table_n1)
+    rc = _lib().or_direct_pot(n, _d(P), None if m is None else _d(m), eps, kernel, nt,
+                              None if tg is None else tg.ctypes.data_as(_i64p),
+                              None if tab is None else _d(tab), table_n1 or 0, _d(out))
+    if rc != 0:
+        raise ValueError("or_direct_pot rejected its parameters (%d)" % rc)
+    return out
+
+
 def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int | None = 64):
     """(d a / d x)^T lam for O1 (all particles); lam and result are (n,3).
     ``n1=None`` takes grad C~ from the exact Ewald sum for every pair (slow);
@@ -271,26 +312,32 @@ def tree_params(eps, theta, order, n_leaf=16, n_group=32, n_direct=None, lmax=21
 
 
 def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,
-                return_stats=False):
-    """O2: FP64 CPU treecode; returns (ntarget, 3) accelerations."""
+                return_stats=False, return_pot=False):
+    """O2: FP64 CPU treecode; returns (ntarget, 3) accelerations, then (with
+    return_pot) the (ntarget,) potential, then (with return_stats) the
+    interaction counts."""
     P = _soa(pos)
     n = P.shape[1]
     m = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
     tg = None if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
     nt = n if tg is None else len(tg)
     acc = np.zeros(3 * nt)
+    pot = np.zeros(nt) if return_pot else None
     st = np.zeros(7)
     tab = phitilde_lattice(params.ew_grid, params.ewald + 1) if params.ewald > 0 else None
-    rc = _lib().or_tree_forces(n, _d(P), None if m is None else _d(m), C.byref(params),
-                               None if tab is None else _d(tab), nt,
-                               None if tg is None else tg.ctypes.data_as(_i64p), _d(acc), _d(st))
+    rc = _lib().or_tree_forces_pot(n, _d(P), None if m is None else _d(m), C.byref(params),
+                                   None if tab is None else _d(tab), nt,
+                                   None if tg is None else tg.ctypes.data_as(_i64p), _d(acc),
+                                   None if pot is None else _d(pot), _d(st))
     if rc != 0:
         raise ValueError("or_tree_forces rejected its parameters (%d)" % rc)
-    a = acc.reshape(3, nt).T.copy()
+    out = [acc.reshape(3, nt).T.copy()]
+    if return_pot:
+        out.append(pot)
     if return_stats:
-        return a, {"p2p": st[0], "m2p": st[1], "ewald": st[2], "cells": st[3], "groups": st[4],
-                   "sinks": st[5], "m2l": st[6]}
-    return a
+        out.append({"p2p": st[0], "m2p": st[1], "ewald": st[2], "cells": st[3], "groups": st[4],
+                    "sinks": st[5], "m2l": st[6]})
+    return out[0] if len(out) == 1 else tuple(out)
 
 
 def tree_cells(pos, n_leaf=16, lmax=21):

@@ -28,6 +28,56 @@ double or_soft_factor(double r2, double eps, int kernel) {
   return 1.0 / (s * sqrt(s));
 }
 
+double or_soft_pot(double r2, double eps, int kernel) {
+  if (kernel == 1) {
+    double x2 = r2 / (eps * eps);
+    if (x2 < 1.0)
+      return -(105.0 / 32.0 - (175.0 / 32.0) * x2 + (147.0 / 32.0) * x2 * x2 - (45.0 / 32.0) * x2 * x2 * x2) / eps;
+    return -1.0 / sqrt(r2);
+  }
+  return -1.0 / sqrt(r2 + eps * eps);
+}
+
+/* phi_i = sum_{j != i} m_j [phi_E(r_ij) + 1/|r*| + s(r*)] + m_i phi~(0):
+ * the Ewald potential (zero-mean convention) with the nearest image softened
+ * (s the softened pair potential of or_soft_pot), plus each particle's
+ * interaction with its own images and the background.  phi_E + 1/|r| =
+ * phi~ - (2 pi/3)|r|^2 for the nearest image r*; phi~ from the exact Ewald
+ * sum (ptab NULL) or the tricubic table of or_phitilde_table_build. */
+int or_direct_pot(int64_t n, const double *pos, const double *mass, double eps, int kernel,
+                  int64_t ntarget, const int64_t *targets, const double *ptab, int n1, double *pot) {
+  if (n <= 0) return 0;
+  if (kernel < 0 || kernel > 1) return -1;
+  const double *X = pos, *Y = pos + n, *Z = pos + 2 * n;
+  int64_t nt = targets ? ntarget : n;
+  or_ewald_cfg cfg;
+  or_ewald_default(&cfg);
+  double zero[3] = {0.0, 0.0, 0.0}, d0[20];
+  or_phitilde(zero, &cfg, d0);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t t = 0; t < nt; t++) {
+    int64_t i = targets ? targets[t] : t;
+    double v = (mass ? mass[i] : 1.0 / (double)n) * d0[0];
+    for (int64_t j = 0; j < n; j++) {
+      if (j == i) continue;
+      double mj = mass ? mass[j] : 1.0 / (double)n;
+      double rs[3] = {min_image(X[i] - X[j]), min_image(Y[i] - Y[j]), min_image(Z[i] - Z[j])};
+      double q2 = rs[0] * rs[0] + rs[1] * rs[1] + rs[2] * rs[2];
+      double pt;
+      if (ptab) {
+        or_phitilde_table_eval(ptab, n1, rs, &pt);
+      } else {
+        double dd[20];
+        or_phitilde(rs, &cfg, dd);
+        pt = dd[0];
+      }
+      v += mj * (pt - (2.0 * PI / 3.0) * q2 + or_soft_pot(q2, eps, kernel));
+    }
+    pot[t] = v;
+  }
+  return 0;
+}
+
 int or_direct_forces(int64_t n, const double *pos, const double *mass, double eps,
                      int64_t ntarget, const int64_t *targets, const double *ctab, int n1,
                      double *acc) {

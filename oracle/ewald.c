@@ -425,6 +425,14 @@ void or_ctilde_table_eval(const double *tab, int n1, const double r[3], double o
   tricubic_eval(tab, n1, 3, CNT, r, out);
 }
 
+/* phi~ itself on the same nodes (one value per node; even in every axis) */
+int or_phitilde_table_build(int n1, double *tab) { return tricubic_build(n1, tab, 1, 0); }
+
+void or_phitilde_table_eval(const double *tab, int n1, const double r[3], double *out) {
+  static const int EVEN[1][3] = {{0, 0, 0}};
+  tricubic_eval(tab, n1, 1, EVEN, r, out);
+}
+
 /* grad C~ = -d_ij phi~ : store -d_ij (xx,xy,xz,yy,yz,zz) */
 int or_ctilde_grad_table_build(int n1, double *tab) {
   int rc = tricubic_build(n1, tab, 6, 4);

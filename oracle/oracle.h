@@ -70,6 +70,10 @@ void or_ctilde_grad_table_eval(const double *tab, int n1, const double r[3], dou
  *   f = M(x)/r^3 = (175/16 - (147/8) x^2 + (135/16) x^4)/eps^3 for r < eps
  *   and f = 1/r^3 beyond. */
 double or_soft_factor(double r2, double eps, int kernel);
+/* the softened pair potential (unit masses): Plummer -(r^2 + eps^2)^-1/2;
+ * K1 -(105/32 - (175/32) x^2 + (147/32) x^4 - (45/32) x^6)/eps inside eps
+ * (the integral of its force), -1/r beyond */
+double or_soft_pot(double r2, double eps, int kernel);
 
 /* ---- O1: direct summation with Ewald images --------------------------------
  * a_i = sum_{j != i} m_j [ a_E(r_ij) - a_N(r*_ij) + a_P(r*_ij) ]
@@ -84,6 +88,11 @@ int or_direct_forces(int64_t n, const double *pos, const double *mass, double ep
 int or_direct_forces_k(int64_t n, const double *pos, const double *mass, double eps, int kernel,
                        int64_t ntarget, const int64_t *targets, const double *ctab, int n1,
                        double *acc);
+/* O1's potential (see direct.c); ptab NULL: exact Ewald sum per pair */
+int or_direct_pot(int64_t n, const double *pos, const double *mass, double eps, int kernel,
+                  int64_t ntarget, const int64_t *targets, const double *ptab, int n1, double *pot);
+int or_phitilde_table_build(int n1, double *tab /* (n1+4)^3 */);
+void or_phitilde_table_eval(const double *tab, int n1, const double r[3], double *out);
 /* Vector-Jacobian product of O1: given lam (3 x n SoA, cotangent of the
  * accelerations of all particles), out = (d a / d x)^T lam (3 x n SoA). */
 int or_direct_vjp(int64_t n, const double *pos, const double *mass, double eps,
@@ -133,6 +142,13 @@ typedef struct {
 int or_tree_forces(int64_t n, const double *pos, const double *mass,
                    const or_tree_params *p, const double *tab, int64_t ntarget,
                    const int64_t *targets, double *acc, double *stats);
+/* the same with the potential (pot nullable, ntarget values): the tree's
+ * -Psi of every interaction (P2P softened, expansions -sum c_n M_n d^n g,
+ * the dual form's cells as M2P), the image field's phi~ series and the
+ * background's -(2 pi/3) sum m |x - x*|^2 (needs ewald = 0 or >= 2) */
+int or_tree_forces_pot(int64_t n, const double *pos, const double *mass,
+                       const or_tree_params *p, const double *tab, int64_t ntarget,
+                       const int64_t *targets, double *acc, double *pot, double *stats);
 
 /* Tree topology export for structural parity: cell placeholder keys
  * (1 << 3l | prefix), particle ranges, in breadth-first (level, key) order.

@@ -199,6 +199,20 @@ void or_m2p_orders(const double *M, int pmin, int pmax, const double R[3], doubl
   }
 }
 
+/* Psi(R) = sum_{pmin <= |n| <= pmax} ((-1)^|n|/n!) M_n d^n g(R): the
+ * expansion's potential up to sign (a = grad Psi, potential -Psi) */
+double or_m2p_pot_orders(const double *M, int pmin, int pmax, const double R[3], double eps) {
+  double D[256];
+  or_dtensor(R, eps, pmax, D);
+  int nm = or_nmom(pmax);
+  double v = 0.0;
+  for (int t = pmin > 0 ? or_nmom(pmin - 1) : 0; t < nm; t++) {
+    int nx = g_ml[t][0], ny = g_ml[t][1], nz = g_ml[t][2];
+    v += ((nx + ny + nz) & 1 ? -1.0 : 1.0) * M[t] / (fact(nx) * fact(ny) * fact(nz)) * D[t];
+  }
+  return v;
+}
+
 void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]) {
   or_m2p_orders(M, 0, p, R, eps, a);
 }
@@ -402,7 +416,8 @@ static int cell_image(const walkctx *w, const tgroup *G, int level, const int64_
 static int64_t quant(double x);
 
 static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc /* 3 x count */,
-                     double *Lg /* the group's local expansion (dual) */, wstats *st) {
+                     double *Lg /* the group's local expansion (dual) */, double *pot /* nullable */,
+                     wstats *st) {
   const tcell *c = &w->cells[ci];
   const or_tree_params *p = w->p;
   int64_t kimg[3];
@@ -420,7 +435,7 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
   int accept = consistent && c->level >= 2 && (double)d2 > w->T[c->level];
   int leaf = c->nchild == 0;
   if (!accept && !leaf) {
-    for (int k = 0; k < c->nchild; k++) walk_rec(w, G, c->child[k], acc, Lg, st);
+    for (int k = 0; k < c->nchild; k++) walk_rec(w, G, c->child[k], acc, Lg, pot, st);
     return;
   }
   double cs[3];
@@ -444,6 +459,13 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
       for (int d = 0; d < 3; d++) R[d] = ldexp((double)G->g2[d], -23) - cs[d];
       or_m2l(M, p->order, R, p->kernel == 1 ? 0.0 : p->eps, Lg);
       st->m2l += 1.0;
+      if (!pot) return;
+      /* the potential is the M2P form's (below) also for such cells */
+      for (int64_t s = 0; s < G->count; s++) {
+        int64_t i = G->start + s;
+        double Rs[3] = {w->X[i] - cs[0], w->Y[i] - cs[1], w->Z[i] - cs[2]};
+        pot[s] -= or_m2p_pot_orders(M, 0, p->order, Rs, p->kernel == 1 ? 0.0 : p->eps);
+      }
       return;
     }
   }
@@ -454,6 +476,7 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
     if (use_m2p) {
       double R[3] = {xi[0] - cs[0], xi[1] - cs[1], xi[2] - cs[2]};
       or_m2p(M, p->order, R, p->kernel == 1 ? 0.0 : p->eps, a);
+      if (pot) pot[s] -= or_m2p_pot_orders(M, 0, p->order, R, p->kernel == 1 ? 0.0 : p->eps);
       if (p->bg > p->order) {
         /* the cell's share of the uniform background (a cube of the mean
            density filling the cell) beyond order p, Newtonian kernel */
@@ -461,6 +484,7 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
         or_cube_moments(ldexp(1.0, -c->level), w->rho, p->bg, C);
         or_m2p_orders(C, p->order + 1, p->bg, R, 0.0, ab);
         for (int d = 0; d < 3; d++) a[d] += ab[d];
+        if (pot) pot[s] -= or_m2p_pot_orders(C, p->order + 1, p->bg, R, 0.0);
       }
       st->m2p += 1.0;
     } else {
@@ -473,7 +497,9 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
         for (int d = 0; d < 3; d++) kj[d] = img_shift(2 * centre_u(jx[d], le), G->cell2[d]);
         double r[3] = {w->X[j] - (double)kj[0] - xi[0], w->Y[j] - (double)kj[1] - xi[1],
                        w->Z[j] - (double)kj[2] - xi[2]};
-        double f = w->Mass[j] * or_soft_factor(r[0] * r[0] + r[1] * r[1] + r[2] * r[2], p->eps, p->kernel);
+        double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        double f = w->Mass[j] * or_soft_factor(r2, p->eps, p->kernel);
+        if (pot) pot[s] += w->Mass[j] * or_soft_pot(r2, p->eps, p->kernel);
         a[0] += f * r[0];
         a[1] += f * r[1];
         a[2] += f * r[2];
@@ -487,7 +513,7 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
 }
 
 /* per-group image field: local expansion about e from the level-ew_level cells */
-static void periodic_group(const walkctx *w, const tgroup *G, double *acc, wstats *st) {
+static void periodic_group(const walkctx *w, const tgroup *G, double *acc, double *pot, wstats *st) {
   const or_tree_params *p = w->p;
   int pe = p->ewald, P = pe + 1, le = p->ew_level;
   int nl = or_nmom(P), ne = or_nmom(pe);
@@ -495,7 +521,7 @@ static void periodic_group(const walkctx *w, const tgroup *G, double *acc, wstat
   const int64_t *e2 = G->cell2; /* expansion point: centre of the group's cell */
   double e[3];
   for (int d = 0; d < 3; d++) e[d] = ldexp((double)e2[d], -23);
-  double L[128], Dv[128], V[3] = {0.0, 0.0, 0.0}, Mt = 0.0;
+  double L[128], Dv[128], V[3] = {0.0, 0.0, 0.0}, Mt = 0.0, W = 0.0;
   for (int t = 0; t < nl; t++) L[t] = 0.0;
   for (int64_t ci = 0; ci < w->nec; ci++) {
     const int64_t *ix = w->ec_ix + 3 * ci;
@@ -509,7 +535,7 @@ static void periodic_group(const walkctx *w, const tgroup *G, double *acc, wstat
       cst[d] = ldexp((double)c2, -23) - (double)k[d];
     }
     or_phitilde_lattice_get(w->lat, p->ew_grid, P, ir, Dv);
-    for (int t = 1; t < nl; t++) {
+    for (int t = pot ? 0 : 1; t < nl; t++) {
       int m0 = g_ml[t][0], m1 = g_ml[t][1], m2 = g_ml[t][2];
       int om = m0 + m1 + m2;
       for (int u = 0; u < ne; u++) {
@@ -525,6 +551,13 @@ static void periodic_group(const walkctx *w, const tgroup *G, double *acc, wstat
     V[1] += mc * (cst[1] - e[1]) + M[mi_idx(0, 1, 0)];
     V[2] += mc * (cst[2] - e[2]) + M[mi_idx(0, 0, 1)];
     Mt += mc;
+    if (pot) {
+      /* sum over the cell of m |x_j* - e|^2, about its centre r = c* - e */
+      double r[3] = {cst[0] - e[0], cst[1] - e[1], cst[2] - e[2]};
+      W += mc * (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) +
+           2.0 * (r[0] * M[mi_idx(1, 0, 0)] + r[1] * M[mi_idx(0, 1, 0)] + r[2] * M[mi_idx(0, 0, 1)]) +
+           M[mi_idx(2, 0, 0)] + M[mi_idx(0, 2, 0)] + M[mi_idx(0, 0, 2)];
+    }
     st->ew += 1.0;
   }
   for (int64_t s = 0; s < G->count; s++) {
@@ -543,6 +576,18 @@ static void periodic_group(const walkctx *w, const tgroup *G, double *acc, wstat
     acc[s] += a[0];
     acc[G->count + s] += a[1];
     acc[2 * G->count + s] += a[2];
+    if (pot) {
+      /* -(2 pi/3) sum_j m_j |x - x_j*|^2 + sum_j m_j phi~(x - x_j*), the latter
+         as the truncated Taylor series of the local expansion about e */
+      double v = -(2.0 * PI / 3.0) *
+                 (Mt * (dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]) -
+                  2.0 * (dd[0] * V[0] + dd[1] * V[1] + dd[2] * V[2]) + W);
+      for (int t = 0; t < nl; t++) {
+        int m0 = g_ml[t][0], m1 = g_ml[t][1], m2 = g_ml[t][2];
+        v += ipow(dd[0], m0) * ipow(dd[1], m1) * ipow(dd[2], m2) / (fact(m0) * fact(m1) * fact(m2)) * L[t];
+      }
+      pot[s] += v;
+    }
   }
 }
 
@@ -596,7 +641,14 @@ int64_t or_tree_cells(int64_t n, const double *pos, int n_leaf, int lmax, int64_
 int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tree_params *p,
                    const double *tab, int64_t ntarget, const int64_t *targets, double *acc,
                    double *stats) {
+  return or_tree_forces_pot(n, pos, mass, p, tab, ntarget, targets, acc, NULL, stats);
+}
+
+int or_tree_forces_pot(int64_t n, const double *pos, const double *mass, const or_tree_params *p,
+                       const double *tab, int64_t ntarget, const int64_t *targets, double *acc,
+                       double *pot, double *stats) {
   if (n <= 0) return 0;
+  if (pot && p->ewald > 0 && p->ewald < 2) return -1; /* the background potential needs second moments */
   if (p->order < 0 || p->order > 4 || p->lmax < 2 || p->lmax > QBITS || p->n_leaf < 1 ||
       p->n_group < 1 || p->n_direct > p->n_leaf || p->ewald < 0 || p->ewald > 5 ||
       (p->ewald > 0 && !tab) || p->ew_level < 1 || p->ew_level > 8 ||
@@ -712,6 +764,7 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
     need[gid[where[orig]]] = 1;
   }
   double *sacc = calloc((size_t)(3 * n), sizeof(double));
+  double *spot = pot ? calloc((size_t)n, sizeof(double)) : NULL;
   double sp2p = 0.0, sm2p = 0.0, sew = 0.0, sgroups = 0.0, ssinks = 0.0, sm2l = 0.0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : sp2p, sm2p, sew, sgroups, ssinks, sm2l)
   for (int64_t gi = 0; gi < ng; gi++) {
@@ -735,10 +788,11 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
       G.w2[d] = hi[d] - lo[d];
     }
     double *ga = calloc((size_t)(3 * G.count), sizeof(double));
+    double *gp = spot ? calloc((size_t)G.count, sizeof(double)) : NULL;
     wstats st = {0.0, 0.0, 0.0, 0.0};
     double Lg[128];
     for (int t = 0; t < 128; t++) Lg[t] = 0.0;
-    walk_rec(&w, &G, 0, ga, Lg, &st);
+    walk_rec(&w, &G, 0, ga, Lg, gp, &st);
     if (p->dual && st.m2l > 0.0)
       for (int64_t s = 0; s < G.count; s++) {
         int64_t i = G.start + s;
@@ -748,9 +802,12 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
         or_l2p(Lg, p->order, d, a);
         for (int k = 0; k < 3; k++) ga[k * G.count + s] += a[k];
       }
-    if (p->ewald > 0) periodic_group(&w, &G, ga, &st);
+    if (p->ewald > 0) periodic_group(&w, &G, ga, gp, &st);
     for (int64_t s = 0; s < G.count; s++)
       for (int d = 0; d < 3; d++) sacc[d * n + G.start + s] = ga[d * G.count + s];
+    if (gp)
+      for (int64_t s = 0; s < G.count; s++) spot[G.start + s] = gp[s];
+    free(gp);
     free(ga);
     sp2p += st.p2p;
     sm2p += st.m2p;
@@ -763,7 +820,9 @@ int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tr
     int64_t orig = targets ? targets[t] : t;
     int64_t sidx = where[orig];
     for (int d = 0; d < 3; d++) acc[d * nt + t] = sacc[d * n + sidx];
+    if (pot) pot[t] = spot[sidx];
   }
+  free(spot);
   if (stats) {
     stats[0] = sp2p;
     stats[1] = sm2p;

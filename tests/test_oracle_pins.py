@@ -678,3 +678,132 @@ def test_dual_tree_accuracy_and_work():
         a = O.tree_forces(x, None, O.tree_params(eps, th, 4, n_direct=8, ewald=5, ew_grid=5, dual=1), targets=tg)
         errs.append(np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)))
     assert errs[1] < errs[0] < med[1], (errs, med)
+
+
+# ---- potentials ---------------------------------------------------------------------------
+def test_soft_pot_from_the_densities_and_the_force():
+    """The softened pair potentials against their definitions elsewhere: the
+    K1 potential is the potential of its density by quadrature,
+    phi(r) = -M(r)/r - int_r^eps 4 pi s rho(s) ds (eps = 1), so phi(0) =
+    -105/32; both kernels give -1/r beyond the support (Plummer
+    asymptotically), and each potential's radial slope is r times the pair
+    factor of the force (finite differences)."""
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    for r in (1e-9, 0.2, 0.5, 0.8, 0.99):
+        s = 0.5 * r * (xg + 1.0)
+        mass = 0.5 * r * np.sum(wg * 4.0 * math.pi * s * s * _k1_density(s))
+        s = r + 0.5 * (1.0 - r) * (xg + 1.0)
+        outer = 0.5 * (1.0 - r) * np.sum(wg * 4.0 * math.pi * s * _k1_density(s))
+        assert abs(O.soft_pot(r * r, 1.0, 1) - (-mass / r - outer)) <= 1e-12, r
+    assert abs(O.soft_pot(0.0, 1.0, 1) + 105.0 / 32.0) <= 1e-14
+    eps = 0.02
+    for r in (eps, 2 * eps, 0.3):
+        assert O.soft_pot(r * r, eps, 1) == -1.0 / r
+    assert abs(O.soft_pot(1.0, 1e-4, 0) + 1.0) <= 1e-8
+    h = 1e-6
+    for k in (0, 1):
+        for r in (0.3 * eps, 0.9 * eps, 1.7 * eps):
+            slope = (O.soft_pot((r + h * eps) ** 2, eps, k) - O.soft_pot((r - h * eps) ** 2, eps, k)) / (2 * h * eps)
+            assert abs(slope - r * O.soft_factor(r * r, eps, k)) <= 1e-7 * abs(slope), (k, r)
+
+
+def _lattice(k):
+    g = (np.arange(k) + 0.5) / k
+    return np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+
+
+def test_direct_pot_madelung_lattice_and_two_particles():
+    """The direct potential of a simple cubic lattice of k^3 equal masses
+    (total mass 1) is the single-particle periodic potential of a box of side
+    1/k: phi = m k xi with xi the Madelung constant of the golden fixture
+    (exact Ewald sum and the tricubic phi~ table).  For two particles with
+    negligible softening it is m_2 phi_E(r_12) + m_1 xi, phi_E the Ewald
+    potential (zero-mean convention) evaluated by its own routine."""
+    xi = float(_golden_lines("madelung_simple_cubic.txt")[0][0])
+    for k in (4, 5):
+        x = _lattice(k)
+        n = len(x)
+        want = xi * k / n
+        assert np.abs(O.direct_pot(x, None, 1e-9, table_n1=None) - want).max() <= 1e-9 * want
+        assert np.abs(O.direct_pot(x, None, 1e-9, table_n1=128) - want).max() <= 1e-7 * want
+    x = np.array([[0.1, 0.2, 0.3], [0.55, 0.05, 0.9]])
+    m = np.array([0.7, 1.9])
+    pot = O.direct_pot(x, m, 0.0, table_n1=None)
+    r = x[0] - x[1]
+    assert abs(pot[0] - (m[1] * O.ewald_pot(r) + m[0] * xi)) <= 1e-9
+    assert abs(pot[1] - (m[0] * O.ewald_pot(-r) + m[1] * xi)) <= 1e-9
+
+
+def test_direct_pot_gradient_is_minus_the_direct_force():
+    """phi_i depends on x_i only through its pairs (its own images and the
+    background give a constant), so -d phi_i / d x_i is the direct sum's
+    acceleration (central differences, exact Ewald sums, Plummer and K1)."""
+    rng = np.random.default_rng(21)
+    x = rng.random((10, 3))
+    m = rng.uniform(0.5, 1.5, 10)
+    h = 1e-5
+    for kern, eps in ((0, 0.01), (1, 0.3)):
+        acc = O.direct_forces(x, m, eps, table_n1=None, kernel=kern)
+        for i in (0, 3, 7):
+            for d in range(3):
+                xp, xm = x.copy(), x.copy()
+                xp[i, d] += h
+                xm[i, d] -= h
+                fd = -(O.direct_pot(xp, m, eps, targets=[i], table_n1=None, kernel=kern)[0] -
+                       O.direct_pot(xm, m, eps, targets=[i], table_n1=None, kernel=kern)[0]) / (2 * h)
+                assert abs(fd - acc[i, d]) <= 1e-6 * np.abs(acc[i]).max(), (kern, i, d, fd, acc[i, d])
+
+
+def test_tree_pot_converges_to_direct_and_its_gradient_is_its_force():
+    """The tree's potential converges to the direct one as theta falls
+    (order 4), with and without K1 and the dual form; and at a massless probe
+    (which moves no moment) minus the central-difference gradient of the
+    tree's potential is the tree's own acceleration whenever the opening
+    decisions are the same at both ends: the expansions, the image field's
+    series and the background term are each the gradient of their potential
+    form, so a dropped or mis-signed term of either shows here."""
+    rng = np.random.default_rng(22)
+    x = rng.random((1200, 3))
+    eps = 1e-3
+    pd = O.direct_pot(x, None, eps, table_n1=128)
+    rms = np.sqrt(np.mean(pd ** 2))
+    errs = []
+    for th in (0.6, 0.4, 0.25):
+        _, p = O.tree_forces(x, None, O.tree_params(eps, th, 4, ewald=4), return_pot=True)
+        errs.append(np.median(np.abs(p - pd)) / rms)
+    assert errs[0] > errs[1] > errs[2] and errs[2] <= 2e-5, errs
+    for extra in ({"kernel": 1}, {"dual": 1}, {"mac": 1, "bg": 6}):
+        pk = O.direct_pot(x, None, eps, table_n1=128, kernel=extra.get("kernel", 0))
+        _, p = O.tree_forces(x, None, O.tree_params(eps, 0.25, 4, ewald=4, **extra), return_pot=True)
+        assert np.median(np.abs(p - pk)) / rms <= 5e-5, extra
+    # massless probe
+    m = np.full(len(x) + 1, 1.0 / len(x))
+    m[-1] = 0.0
+    y = np.array([0.437, 0.611, 0.282])
+    h = 1e-6
+    checked = 0
+    for prm in (O.tree_params(eps, 0.6, 4, ewald=4), O.tree_params(eps, 0.5, 2, ewald=3, mac=1, bg=4),
+                O.tree_params(eps, 0.6, 3, ewald=5, kernel=1)):
+        a0, _ = O.tree_forces(np.vstack([x, y]), m, prm, targets=[len(x)], return_pot=True)
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = h
+            _, pp, sp = O.tree_forces(np.vstack([x, y + e]), m, prm, targets=[len(x)], return_pot=True,
+                                      return_stats=True)
+            _, pm, sm = O.tree_forces(np.vstack([x, y - e]), m, prm, targets=[len(x)], return_pot=True,
+                                      return_stats=True)
+            if sp != sm:
+                continue
+            fd = -(pp[0] - pm[0]) / (2 * h)
+            assert abs(fd - a0[0, d]) <= 1e-6 * np.abs(a0[0]).max(), (d, fd, a0[0, d])
+            checked += 1
+    assert checked >= 6
+
+
+def test_tree_pot_rejects_a_first_order_image_field():
+    """The background's potential needs the level-l_E cells' second moments,
+    which an order-1 image field does not carry."""
+    x = np.random.default_rng(2).random((100, 3))
+    with pytest.raises(ValueError):
+        O.tree_forces(x, None, O.tree_params(1e-3, 0.5, 2, ewald=1), return_pot=True)
+    O.tree_forces(x, None, O.tree_params(1e-3, 0.5, 2, ewald=1))  # forces alone are fine
