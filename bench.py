@@ -41,12 +41,11 @@ EWALD_GRID = 5       # groups never straddle a level-4 cell (measured accuracy s
 N_DIRECT = 8         # accepted cells with <= 8 particles summed directly (fastest of 4/8/12/16 measured)
 FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FMA
 # DRAM traffic of one walk launch (packed variant, 8 warps x 2 blocks) from
-# the ncu capture summarised in profiles/walk_kernel_haloes96.md, scaled to
-# 2^21 particles; valid only while the walk's sources are unchanged since that
-# capture (the sources have since gained the active-group test of the block
-# steps, so the bench line reports the traffic as null and quotes the capture
-# separately)
-WALK_TRAFFIC = {"bytes": 106e6, "source_sha": "2e8f5d91dec55cc2"}
+# the ncu capture summarised in profiles/walk_kernel_haloes96.md (96^3:
+# 42.7 MB read + 1.6 MB written), scaled by the particle count to 2^21
+# particles (x 2.370); reported only while the walk's sources are the ones
+# captured (hash of walk.cu, walk_common.cuh, m2p_gen.cuh, common.cuh)
+WALK_TRAFFIC = {"bytes": 105e6, "source_sha": "4124360064afd5ea"}
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 # accuracy of the timed settings against the FP64 direct Ewald sum, from the
@@ -306,8 +305,11 @@ def run_gpu(args, rank, world, local_rank):
     n = len(x)
     pos = torch.tensor(np.ascontiguousarray(x.T), dtype=torch.float64, device=dev)
     mom = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float32, device=dev)
+    fl = nb.NBODY_FLAG_ASYNC
+    if args.walk_variant is not None:  # a fixed launch variant instead of the autotuner's pick (profiling)
+        fl |= nb.NBODY_FLAG_WALK_VARIANT(args.walk_variant)
     prm = nb.params(eps=eps, theta=THETA, order=ORDER, n_direct=args.n_direct, ewald_grid=args.ewald_grid,
-                    flags=nb.NBODY_FLAG_ASYNC)
+                    flags=fl)
     tree = nb.Tree(prm, pos)
     acc = tree.forces()
     a = A_START
@@ -931,6 +933,8 @@ def main():
                     help="also time one global step of block (hierarchical) steps on the benchmark workload")
     ap.add_argument("--adjoint-steps", type=int, default=8, help="trajectory length of the reverse-mode timing")
     ap.add_argument("--ng", type=int, default=NG, help="particles per axis (128 = the benchmark workload)")
+    ap.add_argument("--walk-variant", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="fixed walk launch variant for the timed steps (default: the autotuner's)")
     ap.add_argument("--n-direct", type=int, default=N_DIRECT,
                     help="accepted cells with at most this many particles are summed directly")
     ap.add_argument("--ewald-grid", type=int, default=EWALD_GRID,

@@ -210,10 +210,26 @@ int nbody_forces_batched(const nbody_params *params, int nbox, const int64_t *of
  * Accelerations of all particles of the tree (Sec. 2.1: grouped tree walk with
  * the acceptance test, multipole and direct interactions, periodic images).
  *   acc_dev  3*n FP32 (SoA, caller order), overwritten
+ *   pot_dev  NULL, or n FP32 (caller order), overwritten with the potential
+ *            of the same evaluation: the periodic potential in the zero-mean
+ *            convention (the uniform neutralising background included),
+ *            G = 1, in the caller's units (mass / length); each particle's
+ *            own images and background count, its softened self pair does
+ *            not.  Every interaction contributes its potential form: a
+ *            direct pair -m (r^2 + eps^2)^-1/2 (Plummer) or the K1 kernel's
+ *            -m (105/32 - 175/32 x^2 + 147/32 x^4 - 45/32 x^6)/eps inside
+ *            eps; an accepted cell -sum_n ((-1)^|n|/n!) M_n d^n g, also
+ *            under NBODY_FLAG_DUAL (the potential is the expansion form's;
+ *            the accelerations stay the dual form's); the image field its
+ *            local expansion's series; the background -(2 pi/3) sum m |x -
+ *            x*|^2.  The potential comes from a second, scalar variant of the
+ *            walk, so asking for it costs one walk or more.
+ *            NBODY_ENOTSUP with ewald_order 1 (the background's potential
+ *            needs the image cells' second moments).
  *   stats    NULL or filled with counts and phase times (phase times are
  *            only filled when the call synchronises)
  */
-int nbody_forces(nbody_tree *tree, float *acc_dev, nbody_stats *stats, nbody_stream_t stream);
+int nbody_forces(nbody_tree *tree, float *acc_dev, float *pot_dev, nbody_stats *stats, nbody_stream_t stream);
 
 /*
  * nbody_forces with FP64 output: acc_dev is 3*n FP64 (caller order,

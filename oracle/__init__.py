@@ -114,6 +114,8 @@ def _lib():
             L.or_dtensor.argtypes = [_dp, C.c_double, C.c_int, _dp]
             L.or_m2p.argtypes = [_dp, C.c_int, _dp, C.c_double, _dp]
             L.or_m2p_orders.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_double, _dp]
+            L.or_m2p_pot_orders.argtypes = [_dp, C.c_int, C.c_int, _dp, C.c_double]
+            L.or_m2p_pot_orders.restype = C.c_double
             L.or_cube_moments.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
             L.or_m2l.argtypes = [_dp, C.c_int, _dp, C.c_double, _dp]
             L.or_l2p.argtypes = [_dp, C.c_int, _dp, _dp]
@@ -419,6 +421,13 @@ def m2p_orders(M, pmin, pmax, R, eps):
     a = np.zeros(3)
     _lib().or_m2p_orders(_d(M), pmin, pmax, _d(R), eps, _d(a))
     return a
+
+
+def m2p_pot(M, pmin, pmax, R, eps) -> float:
+    """Psi of the orders pmin..pmax of moments M at R (a = grad Psi)."""
+    Mv = np.ascontiguousarray(M, dtype=np.float64)
+    Rv = np.ascontiguousarray(R, dtype=np.float64)
+    return _lib().or_m2p_pot_orders(_d(Mv), pmin, pmax, _d(Rv), eps)
 
 
 def m2l(M, p, R, eps):

@@ -169,6 +169,9 @@ void or_dtensor(const double R[3], double eps, int pmax, double *D);
 void or_m2p(const double *M, int p, const double R[3], double eps, double a[3]);
 /* the same with only the orders pmin..pmax of M (pmax <= 8) */
 void or_m2p_orders(const double *M, int pmin, int pmax, const double R[3], double eps, double a[3]);
+/* its potential form Psi = sum_{pmin <= |n| <= pmax} ((-1)^|n|/n!) M_n d^n g(R)
+ * (a = grad Psi; the potential is -Psi) */
+double or_m2p_pot_orders(const double *M, int pmin, int pmax, const double R[3], double eps);
 /* cell-group interaction of the dual form: L (nmom(p + 1) values, index 0
  * unused) += the local expansion about z of a cell's field at R = z - c
  * (orders |n| + |k| <= p + 1), and the acceleration at offset d from z */

@@ -57,7 +57,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
                     int forced_variant, int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
-                    cudaStream_t s);
+                    void* pot, cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -80,7 +80,7 @@ cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg,
                            const void* tab, void* lbuf, cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
-                        double* out64, cudaStream_t s);
+                        double* out64, const void* potw, float* pout, cudaStream_t s);
 
 namespace {
 
@@ -156,6 +156,7 @@ struct nbody_tree {
   const float* tab32 = nullptr;
   // walk
   Buf eps2, stack, gctr, accw, counters, lbuf;
+  Buf potw;  // the walk's potential (key order), when one is asked for
   // reverse mode
   Buf a_lam, a_mu, a_nuc, a_nu, a_lbar, a_nue, a_x0, a_x1, a_ph, a_g, a_lg, a_lx, a_lp, a_out;
   // the KDK adjoint's kept product J(x0)^T lam_ph with its x0 and lam_p0
@@ -185,7 +186,7 @@ struct nbody_tree {
                   &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho, &act_s, &act_g, &rungc,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
-                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32};
+                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32, &potw};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     delete aux;
@@ -319,20 +320,18 @@ __global__ void eps2_kernel(int nbox, const double* __restrict__ eps, float* __r
 }
 
 // out[d n + i] = in[d n + i] * f[b] for every particle i of box b (offsets
-// off) and d = 0..2: positions to box units (f = 1/L) and accelerations or
-// force VJPs back to the caller's length unit (f = 1/L^2, 1/L^3)
+// off) and d < nc: positions to box units (f = 1/L) and accelerations,
+// potentials or force VJPs back to the caller's length unit (f = 1/L^2, 1/L,
+// 1/L^3)
 template <typename T>
 __global__ void box_scale_kernel(const int64_t* __restrict__ off, int nbox, int64_t n,
-                                 const double* __restrict__ f, const T* in, T* out) {
+                                 const double* __restrict__ f, const T* in, T* out, int nc) {
   for (int b = blockIdx.y; b < nbox; b += gridDim.y) {
     const int64_t lo = off[b], hi = off[b + 1];
     const double fb = f[b];
     for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      out[i] = (T)(in[i] * fb);
-      out[n + i] = (T)(in[n + i] * fb);
-      out[2 * n + i] = (T)(in[2 * n + i] * fb);
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+      for (int d = 0; d < nc; d++) out[d * n + i] = (T)(in[d * n + i] * fb);
   }
 }
 
@@ -498,12 +497,12 @@ int upload_boxes(nbody_tree* t, cudaStream_t s) {
 // arrays of the caller's (3, n) layout scaled per box by lscale[k * nbox + b]
 // (k = 0: 1/L, 1: 1/L^2, 2: 1/L^3); a no-op for unit boxes
 template <typename T>
-int scale_boxes(const nbody_tree* t, int k, const T* in, T* out, cudaStream_t s) {
+int scale_boxes(const nbody_tree* t, int k, const T* in, T* out, cudaStream_t s, int nc = 3) {
   if (!t->scaled) return NBODY_OK;
   const int64_t per = (t->n + t->nbox - 1) / t->nbox;
   dim3 g((unsigned)std::min<int64_t>((per + 255) / 256, 1024), (unsigned)std::min(t->nbox, 65535));
   box_scale_kernel<T><<<g, 256, 0, s>>>(t->off.as<int64_t>(), t->nbox, t->n, t->lscale.as<double>() + k * t->nbox,
-                                        in, out);
+                                        in, out, nc);
   nb_launch_counter += 1;
   NB_CU(cudaGetLastError());
   return NBODY_OK;
@@ -734,11 +733,12 @@ int field_impl(nbody_tree* t, cudaStream_t s) {
 }
 
 int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullptr, const uint8_t* sact = nullptr,
-                const uint8_t* gact = nullptr) {
+                const uint8_t* gact = nullptr, float* pot = nullptr) {
   const nbody_params& p = t->prm;
   const bool fp64 = p.precision == NBODY_FP64;
   const int64_t n = t->n;
   NB_CU(t->accw.ensure((fp64 ? 24 : 12) * n));
+  if (pot) NB_CU(t->potw.ensure((fp64 ? 8 : 4) * n));
   int rc = eval_prep(t, s);
   if (rc) return rc;
   if (t->fixed_cap) NB_CU(nb_cap_check(t->totals.as<int>(), t->cell_cap, t->group_cap, t->status.as<unsigned>(), s));
@@ -752,15 +752,25 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   tr.sact = sact;
   tr.gact = gact;
   unsigned long long* ctr = t->counters.as<unsigned long long>();
-  NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
-                t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
-                t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1, (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0,
-                (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0, (p.flags & NBODY_FLAG_K1) ? 1 : 0,
-                (p.flags & NBODY_FLAG_DUAL) ? 1 : 0, p.theta, t->mom32.as<float>(), group_level(p), s));
+  const bool dual = (p.flags & NBODY_FLAG_DUAL) != 0;
+  // with a potential: the potential variant of the walk (accelerations too);
+  // with the dual form it gives the potential only, and the dual walk then
+  // writes the accelerations (the potential of every accepted cell is its
+  // expansion's, as in the oracle)
+  for (int pass = pot ? 0 : 1; pass < 2; pass++) {
+    if (pass == 1 && pot && !dual) break;
+    if (pass == 1 && pot) NB_CU(cudaMemsetAsync(t->counters.p, 0, 64, s));
+    NB_CU(nb_walk(tr, fp64, p.order, t->coef.p, t->src.p, eps2, t->thr, p.n_direct, image_level(p),
+                  t->stack.as<int>(), kStackCap, t->walk_blocks, t->gctr.as<int>(), t->accw.p, ctr,
+                  t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1,
+                  (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0, (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0,
+                  (p.flags & NBODY_FLAG_K1) ? 1 : 0, dual ? 1 : 0, p.theta, t->mom32.as<float>(), group_level(p),
+                  pass == 0 ? t->potw.p : nullptr, s));
+  }
   if (timed) NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
-                    t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, s));
+                    t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, pot ? t->potw.p : nullptr, pot, s));
   if (timed) NB_CU(cudaEventRecord(fe[2], s));
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
   nb_launch_counter += 1;
@@ -928,7 +938,7 @@ int nbody_forces_batched(const nbody_params* params, int nbox, const int64_t* of
   int rc = make_tree(params, nbox, offsets_host, eps_host, box_len_host, pos_dev, mass_dev, tree,
                      (cudaStream_t)stream);
   if (rc) return rc;
-  return nbody_forces(*tree, acc_dev, nullptr, stream);
+  return nbody_forces(*tree, acc_dev, nullptr, nullptr, stream);
 }
 
 int nbody_forces64(nbody_tree* tree, double* acc_dev, nbody_stream_t stream) {
@@ -943,12 +953,15 @@ int nbody_forces64(nbody_tree* tree, double* acc_dev, nbody_stream_t stream) {
   return read_status(tree, s);
 }
 
-int nbody_forces(nbody_tree* tree, float* acc_dev, nbody_stats* stats, nbody_stream_t stream) {
+int nbody_forces(nbody_tree* tree, float* acc_dev, float* pot_dev, nbody_stats* stats, nbody_stream_t stream) {
   if (!tree || !acc_dev) return NBODY_EINVAL;
+  // the background's potential needs the image cells' second moments
+  if (pot_dev && tree->prm.ewald_order == 1) return NBODY_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
   const long long l0 = nb_launch_counter;
-  int rc = forces_impl(tree, acc_dev, s);
+  int rc = forces_impl(tree, acc_dev, s, nullptr, nullptr, nullptr, pot_dev);
   if (rc == NBODY_OK) rc = scale_boxes<float>(tree, 1, acc_dev, acc_dev, s);
+  if (rc == NBODY_OK && pot_dev) rc = scale_boxes<float>(tree, 0, pot_dev, pot_dev, s, 1);
   tree->launches += nb_launch_counter - l0;
   if (rc) return rc;
   if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;

@@ -153,6 +153,48 @@ def emit_m2p(p):
     return "\n".join(L)
 
 
+def emit_m2pot(p):
+    """The expansion's potential form phi(R) = sum_j F_j S_j(R) (the walk's
+    potential is -phi), from the same stored coefficients as m2p_p<p>."""
+    mon = multi(p)
+    mi = {m: i for i, m in enumerate(mon)}
+    sl = slots(p)
+    L = []
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ T m2pot_p%d(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2) {" % p)
+    L.append("  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));")
+    L.append("  const T F0 = nbody_rsqrt(s);")
+    L.append("  const T is = F0 * F0;")
+    for j in range(1, p + 1):
+        L.append("  const T F%d = F%d * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
+    for d, R in enumerate(("Rx", "Ry", "Rz")):
+        for k in range(2, p + 1):
+            L.append("  const T %s_%d = %s * T(%.17g);" % (R, k, R, 1.0 / k))
+    for i, m in enumerate(mon):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                pi = mi[tuple(par)]
+                R = ("Rx", "Ry", "Rz")[d]
+                fac = R if m[d] == 1 else "%s_%d" % (R, m[d])
+                L.append("  const T m%d = %s;" % (i, fac if pi == 0 else "m%d * %s" % (pi, fac)))
+                break
+    for j in range(p + 1):
+        L.append("  T S%d = T(0);" % j)
+    for t, (j, a) in enumerate(sl):
+        ai = mi[a]
+        L.append("  S%d = %s;" % (j, "S%d + B[%d]" % (j, t) if ai == 0 else "fma(B[%d], m%d, S%d)" % (t, ai, j)))
+    e = "F0 * S0"
+    for j in range(1, p + 1):
+        e = "fma(F%d, S%d, %s)" % (j, j, e)
+    L.append("  return %s;" % e)
+    L.append("}")
+    return "\n".join(L)
+
+
 def emit_m2p2(p):
     """The M2P of two cells at once for one sink, in packed FP32 pairs (the
     .x and .y halves are the two cells; B holds the two cells' coefficients
@@ -624,6 +666,61 @@ def emit_bg(l):
     return "\n".join(L)
 
 
+def emit_bgpot(l):
+    """The background term's potential form q h / r^(2l+1) (its gradient is
+    cube_bg_l<l>'s acceleration)."""
+    h, _ = _bg_parts(l)
+    L = ["template <typename T>",
+         "__device__ __forceinline__ T cube_bgpot_l%d(T q, T Rx, T Ry, T Rz) {" % l,
+         "  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;",
+         "  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));",
+         "  const T ir = nbody_rsqrt(r2);",
+         "  const T ir2 = ir * ir;"]
+    mono = _emit_monomials(L, _close_monomials([h]))
+    _emit_poly(L, "hv", h, mono)
+    L.append("  return q * hv * (%s);" % " * ".join(["ir"] + ["ir2"] * l))
+    L.append("}")
+    return "\n".join(L)
+
+
+def emit_l2pot(pe):
+    """Image-field potential: L_0 = sum_n (-1)^|n|/n! M_n d^n phi~(R0) per
+    cell (m2l0_pe), and the series L_0 + sum_{1 <= |m| <= pe+1} d^m/m! L_m
+    at offset d from the expansion point (l2pot_pe), whose gradient is minus
+    l2p_pe's acceleration."""
+    me = multi(pe)
+    L = ["template <typename T>",
+         "__device__ __forceinline__ T m2l0_pe%d(const T* __restrict__ M, const T* __restrict__ D) {" % pe]
+    e = "T(0)"
+    for u, n in enumerate(me):
+        c = (-1.0 if sum(n) % 2 else 1.0) / (math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2]))
+        e = "fma(M[%d] * T(%.17g), D[%d], %s)" % (u, c, u, e) if c not in (1.0, -1.0) else \
+            "fma(%sM[%d], D[%d], %s)" % ("-" if c < 0 else "", u, u, e)
+    L.append("  return %s;" % e)
+    L.append("}")
+    mP = multi(pe + 1)
+    mmi = {m: i for i, m in enumerate(mP)}
+    L.append("template <typename T>")
+    L.append("__device__ __forceinline__ T l2pot_pe%d(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {" % pe)
+    L.append("  const T q0 = T(1);")
+    for i, m in enumerate(mP):
+        if i == 0:
+            continue
+        for d in range(3):
+            if m[d] > 0:
+                par = list(m)
+                par[d] -= 1
+                L.append("  const T q%d = q%d * (%s * T(%.17g));" % (i, mmi[tuple(par)], "dxdydz"[2 * d:2 * d + 2],
+                                                                    1.0 / m[d]))
+                break
+    e = "L0"
+    for i in range(1, len(mP)):
+        e = "fma(q%d, Lc[%d], %s)" % (i, i - 1, e)
+    L.append("  return %s;" % e)
+    L.append("}")
+    return "\n".join(L)
+
+
 def emit_bg_hvp(l):
     """o += J lam, J_ij = d a_i / d R_j of the background term:
     (J lam)_i = u [w_i lam_i + R_i sum_j 2 R_j (dw_i/dX_j) lam_j - (2l+3) R_i w_i (R.lam) / r^2]."""
@@ -665,6 +762,8 @@ def generate():
     for p in range(5):
         out.append(emit_m2p(p))
         out.append("")
+        out.append(emit_m2pot(p))
+        out.append("")
         out.append(emit_m2p2(p))
         out.append("")
         out.append(emit_reduce(p))
@@ -678,6 +777,8 @@ def generate():
         out.append("constexpr int kNL%d = %d;  // local coefficients, image-field order %d" % (pe, len(multi(pe + 1)) - 1, pe))
         out.append(emit_m2l(pe))
         out.append("")
+        out.append(emit_l2pot(pe))
+        out.append("")
     for p in range(1, 5):
         out.append(emit_dtensor(p + 1))
         out.append("")
@@ -689,6 +790,8 @@ def generate():
     out.append("")
     for l in (4, 6):
         out.append(emit_bg(l))
+        out.append("")
+        out.append(emit_bgpot(l))
         out.append("")
         out.append(pack(emit_bg(l), "cube_bg_l%d" % l, "cube_bg2_l%d" % l))
         out.append("")

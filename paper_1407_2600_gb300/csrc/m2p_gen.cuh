@@ -31,6 +31,16 @@ __device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz
   az = fma(Rz, t, az);
 }
 
+template <typename T>
+__device__ __forceinline__ T m2pot_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  T S0 = T(0);
+  S0 = S0 + B[0];
+  return F0 * S0;
+}
+
 __device__ __forceinline__ void m2p2_p0(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
                                        float2 eps2, float2& ax, float2& ay, float2& az) {
   const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
@@ -85,6 +95,24 @@ __device__ __forceinline__ void m2p_p1(const T* __restrict__ B, T Rx, T Ry, T Rz
   ax = fma(Rx, t, fma(F1, G1x, ax));
   ay = fma(Ry, t, fma(F1, G1y, ay));
   az = fma(Rz, t, fma(F1, G1z, az));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2pot_p1(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  T S0 = T(0);
+  T S1 = T(0);
+  S0 = S0 + B[0];
+  S1 = fma(B[1], m1, S1);
+  S1 = fma(B[2], m2, S1);
+  S1 = fma(B[3], m3, S1);
+  return fma(F1, S1, F0 * S0);
 }
 
 __device__ __forceinline__ void m2p2_p1(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
@@ -203,6 +231,42 @@ __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz
   ax = fma(Rx, t, fma(F1, G1x, fma(F2, G2x, ax)));
   ay = fma(Ry, t, fma(F1, G1y, fma(F2, G2y, ay)));
   az = fma(Rz, t, fma(F1, G1z, fma(F2, G2z, az)));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2pot_p2(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T Rx_2 = Rx * T(0.5);
+  const T Ry_2 = Ry * T(0.5);
+  const T Rz_2 = Rz * T(0.5);
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  const T m4 = m1 * Rx_2;
+  const T m5 = m2 * Rx;
+  const T m6 = m3 * Rx;
+  const T m7 = m2 * Ry_2;
+  const T m8 = m3 * Ry;
+  const T m9 = m3 * Rz_2;
+  T S0 = T(0);
+  T S1 = T(0);
+  T S2 = T(0);
+  S0 = S0 + B[0];
+  S1 = S1 + B[1];
+  S1 = fma(B[2], m1, S1);
+  S1 = fma(B[3], m2, S1);
+  S1 = fma(B[4], m3, S1);
+  S2 = fma(B[5], m4, S2);
+  S2 = fma(B[6], m5, S2);
+  S2 = fma(B[7], m6, S2);
+  S2 = fma(B[8], m7, S2);
+  S2 = fma(B[9], m8, S2);
+  S2 = fma(B[10], m9, S2);
+  return fma(F2, S2, fma(F1, S1, F0 * S0));
 }
 
 __device__ __forceinline__ void m2p2_p2(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
@@ -445,6 +509,70 @@ __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz
   ax = fma(Rx, t, fma(F1, G1x, fma(F2, G2x, fma(F3, G3x, ax))));
   ay = fma(Ry, t, fma(F1, G1y, fma(F2, G2y, fma(F3, G3y, ay))));
   az = fma(Rz, t, fma(F1, G1z, fma(F2, G2z, fma(F3, G3z, az))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2pot_p3(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T F3 = F2 * (T(-5) * is);
+  const T Rx_2 = Rx * T(0.5);
+  const T Rx_3 = Rx * T(0.33333333333333331);
+  const T Ry_2 = Ry * T(0.5);
+  const T Ry_3 = Ry * T(0.33333333333333331);
+  const T Rz_2 = Rz * T(0.5);
+  const T Rz_3 = Rz * T(0.33333333333333331);
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  const T m4 = m1 * Rx_2;
+  const T m5 = m2 * Rx;
+  const T m6 = m3 * Rx;
+  const T m7 = m2 * Ry_2;
+  const T m8 = m3 * Ry;
+  const T m9 = m3 * Rz_2;
+  const T m10 = m4 * Rx_3;
+  const T m11 = m5 * Rx_2;
+  const T m12 = m6 * Rx_2;
+  const T m13 = m7 * Rx;
+  const T m14 = m8 * Rx;
+  const T m15 = m9 * Rx;
+  const T m16 = m7 * Ry_3;
+  const T m17 = m8 * Ry_2;
+  const T m18 = m9 * Ry;
+  const T m19 = m9 * Rz_3;
+  T S0 = T(0);
+  T S1 = T(0);
+  T S2 = T(0);
+  T S3 = T(0);
+  S0 = S0 + B[0];
+  S1 = S1 + B[1];
+  S1 = fma(B[2], m1, S1);
+  S1 = fma(B[3], m2, S1);
+  S1 = fma(B[4], m3, S1);
+  S2 = fma(B[5], m1, S2);
+  S2 = fma(B[6], m2, S2);
+  S2 = fma(B[7], m3, S2);
+  S2 = fma(B[8], m4, S2);
+  S2 = fma(B[9], m5, S2);
+  S2 = fma(B[10], m6, S2);
+  S2 = fma(B[11], m7, S2);
+  S2 = fma(B[12], m8, S2);
+  S2 = fma(B[13], m9, S2);
+  S3 = fma(B[14], m10, S3);
+  S3 = fma(B[15], m11, S3);
+  S3 = fma(B[16], m12, S3);
+  S3 = fma(B[17], m13, S3);
+  S3 = fma(B[18], m14, S3);
+  S3 = fma(B[19], m15, S3);
+  S3 = fma(B[20], m16, S3);
+  S3 = fma(B[21], m17, S3);
+  S3 = fma(B[22], m18, S3);
+  S3 = fma(B[23], m19, S3);
+  return fma(F3, S3, fma(F2, S2, fma(F1, S1, F0 * S0)));
 }
 
 __device__ __forceinline__ void m2p2_p3(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
@@ -901,6 +1029,112 @@ __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz
   ax = fma(Rx, t, fma(F1, G1x, fma(F2, G2x, fma(F3, G3x, fma(F4, G4x, ax)))));
   ay = fma(Ry, t, fma(F1, G1y, fma(F2, G2y, fma(F3, G3y, fma(F4, G4y, ay)))));
   az = fma(Rz, t, fma(F1, G1z, fma(F2, G2z, fma(F3, G3z, fma(F4, G4z, az)))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2pot_p4(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2) {
+  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
+  const T F0 = nbody_rsqrt(s);
+  const T is = F0 * F0;
+  const T F1 = F0 * (T(-1) * is);
+  const T F2 = F1 * (T(-3) * is);
+  const T F3 = F2 * (T(-5) * is);
+  const T F4 = F3 * (T(-7) * is);
+  const T Rx_2 = Rx * T(0.5);
+  const T Rx_3 = Rx * T(0.33333333333333331);
+  const T Rx_4 = Rx * T(0.25);
+  const T Ry_2 = Ry * T(0.5);
+  const T Ry_3 = Ry * T(0.33333333333333331);
+  const T Ry_4 = Ry * T(0.25);
+  const T Rz_2 = Rz * T(0.5);
+  const T Rz_3 = Rz * T(0.33333333333333331);
+  const T Rz_4 = Rz * T(0.25);
+  const T m1 = Rx;
+  const T m2 = Ry;
+  const T m3 = Rz;
+  const T m4 = m1 * Rx_2;
+  const T m5 = m2 * Rx;
+  const T m6 = m3 * Rx;
+  const T m7 = m2 * Ry_2;
+  const T m8 = m3 * Ry;
+  const T m9 = m3 * Rz_2;
+  const T m10 = m4 * Rx_3;
+  const T m11 = m5 * Rx_2;
+  const T m12 = m6 * Rx_2;
+  const T m13 = m7 * Rx;
+  const T m14 = m8 * Rx;
+  const T m15 = m9 * Rx;
+  const T m16 = m7 * Ry_3;
+  const T m17 = m8 * Ry_2;
+  const T m18 = m9 * Ry;
+  const T m19 = m9 * Rz_3;
+  const T m20 = m10 * Rx_4;
+  const T m21 = m11 * Rx_3;
+  const T m22 = m12 * Rx_3;
+  const T m23 = m13 * Rx_2;
+  const T m24 = m14 * Rx_2;
+  const T m25 = m15 * Rx_2;
+  const T m26 = m16 * Rx;
+  const T m27 = m17 * Rx;
+  const T m28 = m18 * Rx;
+  const T m29 = m19 * Rx;
+  const T m30 = m16 * Ry_4;
+  const T m31 = m17 * Ry_3;
+  const T m32 = m18 * Ry_2;
+  const T m33 = m19 * Ry;
+  const T m34 = m19 * Rz_4;
+  T S0 = T(0);
+  T S1 = T(0);
+  T S2 = T(0);
+  T S3 = T(0);
+  T S4 = T(0);
+  S0 = S0 + B[0];
+  S1 = S1 + B[1];
+  S1 = fma(B[2], m1, S1);
+  S1 = fma(B[3], m2, S1);
+  S1 = fma(B[4], m3, S1);
+  S2 = S2 + B[5];
+  S2 = fma(B[6], m1, S2);
+  S2 = fma(B[7], m2, S2);
+  S2 = fma(B[8], m3, S2);
+  S2 = fma(B[9], m4, S2);
+  S2 = fma(B[10], m5, S2);
+  S2 = fma(B[11], m6, S2);
+  S2 = fma(B[12], m7, S2);
+  S2 = fma(B[13], m8, S2);
+  S2 = fma(B[14], m9, S2);
+  S3 = fma(B[15], m4, S3);
+  S3 = fma(B[16], m5, S3);
+  S3 = fma(B[17], m6, S3);
+  S3 = fma(B[18], m7, S3);
+  S3 = fma(B[19], m8, S3);
+  S3 = fma(B[20], m9, S3);
+  S3 = fma(B[21], m10, S3);
+  S3 = fma(B[22], m11, S3);
+  S3 = fma(B[23], m12, S3);
+  S3 = fma(B[24], m13, S3);
+  S3 = fma(B[25], m14, S3);
+  S3 = fma(B[26], m15, S3);
+  S3 = fma(B[27], m16, S3);
+  S3 = fma(B[28], m17, S3);
+  S3 = fma(B[29], m18, S3);
+  S3 = fma(B[30], m19, S3);
+  S4 = fma(B[31], m20, S4);
+  S4 = fma(B[32], m21, S4);
+  S4 = fma(B[33], m22, S4);
+  S4 = fma(B[34], m23, S4);
+  S4 = fma(B[35], m24, S4);
+  S4 = fma(B[36], m25, S4);
+  S4 = fma(B[37], m26, S4);
+  S4 = fma(B[38], m27, S4);
+  S4 = fma(B[39], m28, S4);
+  S4 = fma(B[40], m29, S4);
+  S4 = fma(B[41], m30, S4);
+  S4 = fma(B[42], m31, S4);
+  S4 = fma(B[43], m32, S4);
+  S4 = fma(B[44], m33, S4);
+  S4 = fma(B[45], m34, S4);
+  return fma(F4, S4, fma(F3, S3, fma(F2, S2, fma(F1, S1, F0 * S0))));
 }
 
 __device__ __forceinline__ void m2p2_p4(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
@@ -1792,6 +2026,25 @@ __device__ __forceinline__ void l2p_pe1(const T* __restrict__ Lc, T dx, T dy, T 
   az = fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))));
 }
 
+template <typename T>
+__device__ __forceinline__ T m2l0_pe1(const T* __restrict__ M, const T* __restrict__ D) {
+  return fma(-M[3], D[3], fma(-M[2], D[2], fma(-M[1], D[1], fma(M[0], D[0], T(0)))));
+}
+template <typename T>
+__device__ __forceinline__ T l2pot_pe1(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  return fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0)))))))));
+}
+
 constexpr int kNL2 = 19;  // local coefficients, image-field order 2
 template <typename T>
 __device__ __forceinline__ void m2l_pe2(const T* __restrict__ M, const T* __restrict__ D, T* __restrict__ Lc) {
@@ -1832,6 +2085,35 @@ __device__ __forceinline__ void l2p_pe2(const T* __restrict__ Lc, T dx, T dy, T 
   ax = fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))));
   ay = fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))));
   az = fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2l0_pe2(const T* __restrict__ M, const T* __restrict__ D) {
+  return fma(M[9] * T(0.5), D[9], fma(M[8], D[8], fma(M[7] * T(0.5), D[7], fma(M[6], D[6], fma(M[5], D[5], fma(M[4] * T(0.5), D[4], fma(-M[3], D[3], fma(-M[2], D[2], fma(-M[1], D[1], fma(M[0], D[0], T(0)))))))))));
+}
+template <typename T>
+__device__ __forceinline__ T l2pot_pe2(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  return fma(q19, Lc[18], fma(q18, Lc[17], fma(q17, Lc[16], fma(q16, Lc[15], fma(q15, Lc[14], fma(q14, Lc[13], fma(q13, Lc[12], fma(q12, Lc[11], fma(q11, Lc[10], fma(q10, Lc[9], fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0)))))))))))))))))));
 }
 
 constexpr int kNL3 = 34;  // local coefficients, image-field order 3
@@ -1899,6 +2181,50 @@ __device__ __forceinline__ void l2p_pe3(const T* __restrict__ Lc, T dx, T dy, T 
   ax = fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))))))))))))));
   ay = fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))))))))))))));
   az = fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2l0_pe3(const T* __restrict__ M, const T* __restrict__ D) {
+  return fma(M[19] * T(-0.16666666666666666), D[19], fma(M[18] * T(-0.5), D[18], fma(M[17] * T(-0.5), D[17], fma(M[16] * T(-0.16666666666666666), D[16], fma(M[15] * T(-0.5), D[15], fma(-M[14], D[14], fma(M[13] * T(-0.5), D[13], fma(M[12] * T(-0.5), D[12], fma(M[11] * T(-0.5), D[11], fma(M[10] * T(-0.16666666666666666), D[10], fma(M[9] * T(0.5), D[9], fma(M[8], D[8], fma(M[7] * T(0.5), D[7], fma(M[6], D[6], fma(M[5], D[5], fma(M[4] * T(0.5), D[4], fma(-M[3], D[3], fma(-M[2], D[2], fma(-M[1], D[1], fma(M[0], D[0], T(0)))))))))))))))))))));
+}
+template <typename T>
+__device__ __forceinline__ T l2pot_pe3(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  return fma(q34, Lc[33], fma(q33, Lc[32], fma(q32, Lc[31], fma(q31, Lc[30], fma(q30, Lc[29], fma(q29, Lc[28], fma(q28, Lc[27], fma(q27, Lc[26], fma(q26, Lc[25], fma(q25, Lc[24], fma(q24, Lc[23], fma(q23, Lc[22], fma(q22, Lc[21], fma(q21, Lc[20], fma(q20, Lc[19], fma(q19, Lc[18], fma(q18, Lc[17], fma(q17, Lc[16], fma(q16, Lc[15], fma(q15, Lc[14], fma(q14, Lc[13], fma(q13, Lc[12], fma(q12, Lc[11], fma(q11, Lc[10], fma(q10, Lc[9], fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0))))))))))))))))))))))))))))))))));
 }
 
 constexpr int kNL4 = 55;  // local coefficients, image-field order 4
@@ -2002,6 +2328,71 @@ __device__ __forceinline__ void l2p_pe4(const T* __restrict__ Lc, T dx, T dy, T 
   ax = fma(-q34, Lc[48], fma(-q33, Lc[47], fma(-q32, Lc[46], fma(-q31, Lc[45], fma(-q30, Lc[44], fma(-q29, Lc[43], fma(-q28, Lc[42], fma(-q27, Lc[41], fma(-q26, Lc[40], fma(-q25, Lc[39], fma(-q24, Lc[38], fma(-q23, Lc[37], fma(-q22, Lc[36], fma(-q21, Lc[35], fma(-q20, Lc[34], fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax)))))))))))))))))))))))))))))))))));
   ay = fma(-q34, Lc[53], fma(-q33, Lc[52], fma(-q32, Lc[51], fma(-q31, Lc[50], fma(-q30, Lc[49], fma(-q29, Lc[47], fma(-q28, Lc[46], fma(-q27, Lc[45], fma(-q26, Lc[44], fma(-q25, Lc[42], fma(-q24, Lc[41], fma(-q23, Lc[40], fma(-q22, Lc[38], fma(-q21, Lc[37], fma(-q20, Lc[35], fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay)))))))))))))))))))))))))))))))))));
   az = fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az)))))))))))))))))))))))))))))))))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2l0_pe4(const T* __restrict__ M, const T* __restrict__ D) {
+  return fma(M[34] * T(0.041666666666666664), D[34], fma(M[33] * T(0.16666666666666666), D[33], fma(M[32] * T(0.25), D[32], fma(M[31] * T(0.16666666666666666), D[31], fma(M[30] * T(0.041666666666666664), D[30], fma(M[29] * T(0.16666666666666666), D[29], fma(M[28] * T(0.5), D[28], fma(M[27] * T(0.5), D[27], fma(M[26] * T(0.16666666666666666), D[26], fma(M[25] * T(0.25), D[25], fma(M[24] * T(0.5), D[24], fma(M[23] * T(0.25), D[23], fma(M[22] * T(0.16666666666666666), D[22], fma(M[21] * T(0.16666666666666666), D[21], fma(M[20] * T(0.041666666666666664), D[20], fma(M[19] * T(-0.16666666666666666), D[19], fma(M[18] * T(-0.5), D[18], fma(M[17] * T(-0.5), D[17], fma(M[16] * T(-0.16666666666666666), D[16], fma(M[15] * T(-0.5), D[15], fma(-M[14], D[14], fma(M[13] * T(-0.5), D[13], fma(M[12] * T(-0.5), D[12], fma(M[11] * T(-0.5), D[11], fma(M[10] * T(-0.16666666666666666), D[10], fma(M[9] * T(0.5), D[9], fma(M[8], D[8], fma(M[7] * T(0.5), D[7], fma(M[6], D[6], fma(M[5], D[5], fma(M[4] * T(0.5), D[4], fma(-M[3], D[3], fma(-M[2], D[2], fma(-M[1], D[1], fma(M[0], D[0], T(0))))))))))))))))))))))))))))))))))));
+}
+template <typename T>
+__device__ __forceinline__ T l2pot_pe4(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  const T q35 = q20 * (dx * T(0.20000000000000001));
+  const T q36 = q21 * (dx * T(0.25));
+  const T q37 = q22 * (dx * T(0.25));
+  const T q38 = q23 * (dx * T(0.33333333333333331));
+  const T q39 = q24 * (dx * T(0.33333333333333331));
+  const T q40 = q25 * (dx * T(0.33333333333333331));
+  const T q41 = q26 * (dx * T(0.5));
+  const T q42 = q27 * (dx * T(0.5));
+  const T q43 = q28 * (dx * T(0.5));
+  const T q44 = q29 * (dx * T(0.5));
+  const T q45 = q30 * (dx * T(1));
+  const T q46 = q31 * (dx * T(1));
+  const T q47 = q32 * (dx * T(1));
+  const T q48 = q33 * (dx * T(1));
+  const T q49 = q34 * (dx * T(1));
+  const T q50 = q30 * (dy * T(0.20000000000000001));
+  const T q51 = q31 * (dy * T(0.25));
+  const T q52 = q32 * (dy * T(0.33333333333333331));
+  const T q53 = q33 * (dy * T(0.5));
+  const T q54 = q34 * (dy * T(1));
+  const T q55 = q34 * (dz * T(0.20000000000000001));
+  return fma(q55, Lc[54], fma(q54, Lc[53], fma(q53, Lc[52], fma(q52, Lc[51], fma(q51, Lc[50], fma(q50, Lc[49], fma(q49, Lc[48], fma(q48, Lc[47], fma(q47, Lc[46], fma(q46, Lc[45], fma(q45, Lc[44], fma(q44, Lc[43], fma(q43, Lc[42], fma(q42, Lc[41], fma(q41, Lc[40], fma(q40, Lc[39], fma(q39, Lc[38], fma(q38, Lc[37], fma(q37, Lc[36], fma(q36, Lc[35], fma(q35, Lc[34], fma(q34, Lc[33], fma(q33, Lc[32], fma(q32, Lc[31], fma(q31, Lc[30], fma(q30, Lc[29], fma(q29, Lc[28], fma(q28, Lc[27], fma(q27, Lc[26], fma(q26, Lc[25], fma(q25, Lc[24], fma(q24, Lc[23], fma(q23, Lc[22], fma(q22, Lc[21], fma(q21, Lc[20], fma(q20, Lc[19], fma(q19, Lc[18], fma(q18, Lc[17], fma(q17, Lc[16], fma(q16, Lc[15], fma(q15, Lc[14], fma(q14, Lc[13], fma(q13, Lc[12], fma(q12, Lc[11], fma(q11, Lc[10], fma(q10, Lc[9], fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0)))))))))))))))))))))))))))))))))))))))))))))))))))))));
 }
 
 constexpr int kNL5 = 83;  // local coefficients, image-field order 5
@@ -2154,6 +2545,99 @@ __device__ __forceinline__ void l2p_pe5(const T* __restrict__ Lc, T dx, T dy, T 
   ax = fma(-q55, Lc[75], fma(-q54, Lc[74], fma(-q53, Lc[73], fma(-q52, Lc[72], fma(-q51, Lc[71], fma(-q50, Lc[70], fma(-q49, Lc[69], fma(-q48, Lc[68], fma(-q47, Lc[67], fma(-q46, Lc[66], fma(-q45, Lc[65], fma(-q44, Lc[64], fma(-q43, Lc[63], fma(-q42, Lc[62], fma(-q41, Lc[61], fma(-q40, Lc[60], fma(-q39, Lc[59], fma(-q38, Lc[58], fma(-q37, Lc[57], fma(-q36, Lc[56], fma(-q35, Lc[55], fma(-q34, Lc[48], fma(-q33, Lc[47], fma(-q32, Lc[46], fma(-q31, Lc[45], fma(-q30, Lc[44], fma(-q29, Lc[43], fma(-q28, Lc[42], fma(-q27, Lc[41], fma(-q26, Lc[40], fma(-q25, Lc[39], fma(-q24, Lc[38], fma(-q23, Lc[37], fma(-q22, Lc[36], fma(-q21, Lc[35], fma(-q20, Lc[34], fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))))))))))))))))))))))))))))))))))))))))))))))))));
   ay = fma(-q55, Lc[81], fma(-q54, Lc[80], fma(-q53, Lc[79], fma(-q52, Lc[78], fma(-q51, Lc[77], fma(-q50, Lc[76], fma(-q49, Lc[74], fma(-q48, Lc[73], fma(-q47, Lc[72], fma(-q46, Lc[71], fma(-q45, Lc[70], fma(-q44, Lc[68], fma(-q43, Lc[67], fma(-q42, Lc[66], fma(-q41, Lc[65], fma(-q40, Lc[63], fma(-q39, Lc[62], fma(-q38, Lc[61], fma(-q37, Lc[59], fma(-q36, Lc[58], fma(-q35, Lc[56], fma(-q34, Lc[53], fma(-q33, Lc[52], fma(-q32, Lc[51], fma(-q31, Lc[50], fma(-q30, Lc[49], fma(-q29, Lc[47], fma(-q28, Lc[46], fma(-q27, Lc[45], fma(-q26, Lc[44], fma(-q25, Lc[42], fma(-q24, Lc[41], fma(-q23, Lc[40], fma(-q22, Lc[38], fma(-q21, Lc[37], fma(-q20, Lc[35], fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))))))))))))))))))))))))))))))))))))))))))))))))));
   az = fma(-q55, Lc[82], fma(-q54, Lc[81], fma(-q53, Lc[80], fma(-q52, Lc[79], fma(-q51, Lc[78], fma(-q50, Lc[77], fma(-q49, Lc[75], fma(-q48, Lc[74], fma(-q47, Lc[73], fma(-q46, Lc[72], fma(-q45, Lc[71], fma(-q44, Lc[69], fma(-q43, Lc[68], fma(-q42, Lc[67], fma(-q41, Lc[66], fma(-q40, Lc[64], fma(-q39, Lc[63], fma(-q38, Lc[62], fma(-q37, Lc[60], fma(-q36, Lc[59], fma(-q35, Lc[57], fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2l0_pe5(const T* __restrict__ M, const T* __restrict__ D) {
+  return fma(M[55] * T(-0.0083333333333333332), D[55], fma(M[54] * T(-0.041666666666666664), D[54], fma(M[53] * T(-0.083333333333333329), D[53], fma(M[52] * T(-0.083333333333333329), D[52], fma(M[51] * T(-0.041666666666666664), D[51], fma(M[50] * T(-0.0083333333333333332), D[50], fma(M[49] * T(-0.041666666666666664), D[49], fma(M[48] * T(-0.16666666666666666), D[48], fma(M[47] * T(-0.25), D[47], fma(M[46] * T(-0.16666666666666666), D[46], fma(M[45] * T(-0.041666666666666664), D[45], fma(M[44] * T(-0.083333333333333329), D[44], fma(M[43] * T(-0.25), D[43], fma(M[42] * T(-0.25), D[42], fma(M[41] * T(-0.083333333333333329), D[41], fma(M[40] * T(-0.083333333333333329), D[40], fma(M[39] * T(-0.16666666666666666), D[39], fma(M[38] * T(-0.083333333333333329), D[38], fma(M[37] * T(-0.041666666666666664), D[37], fma(M[36] * T(-0.041666666666666664), D[36], fma(M[35] * T(-0.0083333333333333332), D[35], fma(M[34] * T(0.041666666666666664), D[34], fma(M[33] * T(0.16666666666666666), D[33], fma(M[32] * T(0.25), D[32], fma(M[31] * T(0.16666666666666666), D[31], fma(M[30] * T(0.041666666666666664), D[30], fma(M[29] * T(0.16666666666666666), D[29], fma(M[28] * T(0.5), D[28], fma(M[27] * T(0.5), D[27], fma(M[26] * T(0.16666666666666666), D[26], fma(M[25] * T(0.25), D[25], fma(M[24] * T(0.5), D[24], fma(M[23] * T(0.25), D[23], fma(M[22] * T(0.16666666666666666), D[22], fma(M[21] * T(0.16666666666666666), D[21], fma(M[20] * T(0.041666666666666664), D[20], fma(M[19] * T(-0.16666666666666666), D[19], fma(M[18] * T(-0.5), D[18], fma(M[17] * T(-0.5), D[17], fma(M[16] * T(-0.16666666666666666), D[16], fma(M[15] * T(-0.5), D[15], fma(-M[14], D[14], fma(M[13] * T(-0.5), D[13], fma(M[12] * T(-0.5), D[12], fma(M[11] * T(-0.5), D[11], fma(M[10] * T(-0.16666666666666666), D[10], fma(M[9] * T(0.5), D[9], fma(M[8], D[8], fma(M[7] * T(0.5), D[7], fma(M[6], D[6], fma(M[5], D[5], fma(M[4] * T(0.5), D[4], fma(-M[3], D[3], fma(-M[2], D[2], fma(-M[1], D[1], fma(M[0], D[0], T(0)))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+}
+template <typename T>
+__device__ __forceinline__ T l2pot_pe5(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  const T q35 = q20 * (dx * T(0.20000000000000001));
+  const T q36 = q21 * (dx * T(0.25));
+  const T q37 = q22 * (dx * T(0.25));
+  const T q38 = q23 * (dx * T(0.33333333333333331));
+  const T q39 = q24 * (dx * T(0.33333333333333331));
+  const T q40 = q25 * (dx * T(0.33333333333333331));
+  const T q41 = q26 * (dx * T(0.5));
+  const T q42 = q27 * (dx * T(0.5));
+  const T q43 = q28 * (dx * T(0.5));
+  const T q44 = q29 * (dx * T(0.5));
+  const T q45 = q30 * (dx * T(1));
+  const T q46 = q31 * (dx * T(1));
+  const T q47 = q32 * (dx * T(1));
+  const T q48 = q33 * (dx * T(1));
+  const T q49 = q34 * (dx * T(1));
+  const T q50 = q30 * (dy * T(0.20000000000000001));
+  const T q51 = q31 * (dy * T(0.25));
+  const T q52 = q32 * (dy * T(0.33333333333333331));
+  const T q53 = q33 * (dy * T(0.5));
+  const T q54 = q34 * (dy * T(1));
+  const T q55 = q34 * (dz * T(0.20000000000000001));
+  const T q56 = q35 * (dx * T(0.16666666666666666));
+  const T q57 = q36 * (dx * T(0.20000000000000001));
+  const T q58 = q37 * (dx * T(0.20000000000000001));
+  const T q59 = q38 * (dx * T(0.25));
+  const T q60 = q39 * (dx * T(0.25));
+  const T q61 = q40 * (dx * T(0.25));
+  const T q62 = q41 * (dx * T(0.33333333333333331));
+  const T q63 = q42 * (dx * T(0.33333333333333331));
+  const T q64 = q43 * (dx * T(0.33333333333333331));
+  const T q65 = q44 * (dx * T(0.33333333333333331));
+  const T q66 = q45 * (dx * T(0.5));
+  const T q67 = q46 * (dx * T(0.5));
+  const T q68 = q47 * (dx * T(0.5));
+  const T q69 = q48 * (dx * T(0.5));
+  const T q70 = q49 * (dx * T(0.5));
+  const T q71 = q50 * (dx * T(1));
+  const T q72 = q51 * (dx * T(1));
+  const T q73 = q52 * (dx * T(1));
+  const T q74 = q53 * (dx * T(1));
+  const T q75 = q54 * (dx * T(1));
+  const T q76 = q55 * (dx * T(1));
+  const T q77 = q50 * (dy * T(0.16666666666666666));
+  const T q78 = q51 * (dy * T(0.20000000000000001));
+  const T q79 = q52 * (dy * T(0.25));
+  const T q80 = q53 * (dy * T(0.33333333333333331));
+  const T q81 = q54 * (dy * T(0.5));
+  const T q82 = q55 * (dy * T(1));
+  const T q83 = q55 * (dz * T(0.16666666666666666));
+  return fma(q83, Lc[82], fma(q82, Lc[81], fma(q81, Lc[80], fma(q80, Lc[79], fma(q79, Lc[78], fma(q78, Lc[77], fma(q77, Lc[76], fma(q76, Lc[75], fma(q75, Lc[74], fma(q74, Lc[73], fma(q73, Lc[72], fma(q72, Lc[71], fma(q71, Lc[70], fma(q70, Lc[69], fma(q69, Lc[68], fma(q68, Lc[67], fma(q67, Lc[66], fma(q66, Lc[65], fma(q65, Lc[64], fma(q64, Lc[63], fma(q63, Lc[62], fma(q62, Lc[61], fma(q61, Lc[60], fma(q60, Lc[59], fma(q59, Lc[58], fma(q58, Lc[57], fma(q57, Lc[56], fma(q56, Lc[55], fma(q55, Lc[54], fma(q54, Lc[53], fma(q53, Lc[52], fma(q52, Lc[51], fma(q51, Lc[50], fma(q50, Lc[49], fma(q49, Lc[48], fma(q48, Lc[47], fma(q47, Lc[46], fma(q46, Lc[45], fma(q45, Lc[44], fma(q44, Lc[43], fma(q43, Lc[42], fma(q42, Lc[41], fma(q41, Lc[40], fma(q40, Lc[39], fma(q39, Lc[38], fma(q38, Lc[37], fma(q37, Lc[36], fma(q36, Lc[35], fma(q35, Lc[34], fma(q34, Lc[33], fma(q33, Lc[32], fma(q32, Lc[31], fma(q31, Lc[30], fma(q30, Lc[29], fma(q29, Lc[28], fma(q28, Lc[27], fma(q27, Lc[26], fma(q26, Lc[25], fma(q25, Lc[24], fma(q24, Lc[23], fma(q23, Lc[22], fma(q22, Lc[21], fma(q21, Lc[20], fma(q20, Lc[19], fma(q19, Lc[18], fma(q18, Lc[17], fma(q17, Lc[16], fma(q16, Lc[15], fma(q15, Lc[14], fma(q14, Lc[13], fma(q13, Lc[12], fma(q12, Lc[11], fma(q11, Lc[10], fma(q10, Lc[9], fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0)))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))));
 }
 
 template <typename T>
@@ -2720,6 +3204,27 @@ __device__ __forceinline__ void cube_bg_l4(T q, T Rx, T Ry, T Rz, T& ax, T& ay, 
   az = fma(Rz * u, w2, az);
 }
 
+template <typename T>
+__device__ __forceinline__ T cube_bgpot_l4(T q, T Rx, T Ry, T Rz) {
+  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;
+  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));
+  const T ir = nbody_rsqrt(r2);
+  const T ir2 = ir * ir;
+  const T X0Y0Z2 = Z * Z;
+  const T X0Y1Z1 = Z * Y;
+  const T X0Y2Z0 = Y * Y;
+  const T X1Y0Z1 = Z * X;
+  const T X1Y1Z0 = Y * X;
+  const T X2Y0Z0 = X * X;
+  T hv = T(-0.014583333333333334) * X0Y0Z2;
+  hv = fma(T(0.043749999999999997), X0Y1Z1, hv);
+  hv = fma(T(-0.014583333333333334), X0Y2Z0, hv);
+  hv = fma(T(0.043749999999999997), X1Y0Z1, hv);
+  hv = fma(T(0.043749999999999997), X1Y1Z0, hv);
+  hv = fma(T(-0.014583333333333334), X2Y0Z0, hv);
+  return q * hv * (ir * ir2 * ir2 * ir2 * ir2);
+}
+
 __device__ __forceinline__ void cube_bg2_l4(float2 q, float2 Rx, float2 Ry, float2 Rz, float2& ax, float2& ay, float2& az) {
   const float2 X = __fmul2_rn(Rx, Rx), Y = __fmul2_rn(Ry, Ry), Z = __fmul2_rn(Rz, Rz);
   const float2 r2 = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, Z));
@@ -2811,6 +3316,41 @@ __device__ __forceinline__ void cube_bg_l6(T q, T Rx, T Ry, T Rz, T& ax, T& ay, 
   ax = fma(Rx * u, w0, ax);
   ay = fma(Ry * u, w1, ay);
   az = fma(Rz * u, w2, az);
+}
+
+template <typename T>
+__device__ __forceinline__ T cube_bgpot_l6(T q, T Rx, T Ry, T Rz) {
+  const T X = Rx * Rx, Y = Ry * Ry, Z = Rz * Rz;
+  const T r2 = fma(Rx, Rx, fma(Ry, Ry, Z));
+  const T ir = nbody_rsqrt(r2);
+  const T ir2 = ir * ir;
+  const T X0Y0Z2 = Z * Z;
+  const T X0Y1Z1 = Z * Y;
+  const T X0Y2Z0 = Y * Y;
+  const T X1Y0Z1 = Z * X;
+  const T X1Y1Z0 = Y * X;
+  const T X2Y0Z0 = X * X;
+  const T X0Y0Z3 = X0Y0Z2 * Z;
+  const T X0Y1Z2 = X0Y0Z2 * Y;
+  const T X0Y2Z1 = X0Y1Z1 * Y;
+  const T X0Y3Z0 = X0Y2Z0 * Y;
+  const T X1Y0Z2 = X0Y0Z2 * X;
+  const T X1Y1Z1 = X0Y1Z1 * X;
+  const T X1Y2Z0 = X0Y2Z0 * X;
+  const T X2Y0Z1 = X1Y0Z1 * X;
+  const T X2Y1Z0 = X1Y1Z0 * X;
+  const T X3Y0Z0 = X2Y0Z0 * X;
+  T hv = T(0.001488095238095238) * X0Y0Z3;
+  hv = fma(T(-0.011160714285714286), X0Y1Z2, hv);
+  hv = fma(T(-0.011160714285714286), X0Y2Z1, hv);
+  hv = fma(T(0.001488095238095238), X0Y3Z0, hv);
+  hv = fma(T(-0.011160714285714286), X1Y0Z2, hv);
+  hv = fma(T(0.13392857142857142), X1Y1Z1, hv);
+  hv = fma(T(-0.011160714285714286), X1Y2Z0, hv);
+  hv = fma(T(-0.011160714285714286), X2Y0Z1, hv);
+  hv = fma(T(-0.011160714285714286), X2Y1Z0, hv);
+  hv = fma(T(0.001488095238095238), X3Y0Z0, hv);
+  return q * hv * (ir * ir2 * ir2 * ir2 * ir2 * ir2 * ir2);
 }
 
 __device__ __forceinline__ void cube_bg2_l6(float2 q, float2 Rx, float2 Ry, float2 Rz, float2& ax, float2& ay, float2& az) {

@@ -176,6 +176,14 @@ template <int PE> struct PE_;
     static __device__ __forceinline__ void l2p(const T* L, T x, T y, T z, T& ax, T& ay, T& az) { \
       l2p_pe##PE<T>(L, x, y, z, ax, ay, az);                                             \
     }                                                                                    \
+    template <typename T>                                                                \
+    static __device__ __forceinline__ T l0(const T* M, const T* D) {                     \
+      return m2l0_pe##PE<T>(M, D);                                                       \
+    }                                                                                    \
+    template <typename T>                                                                \
+    static __device__ __forceinline__ T pot(T L0, const T* L, T x, T y, T z) {           \
+      return l2pot_pe##PE<T>(L0, L, x, y, z);                                            \
+    }                                                                                    \
   };
 NB_PE(1)
 NB_PE(2)
@@ -196,6 +204,8 @@ struct PerArgs {
   float* out;           // caller order
   unsigned long long* counter;
   double* out64;        // when set, FP64 output in caller order instead of out
+  const T* potw;        // walk potential, key order, or null (no potential)
+  float* pout;          // potential, caller order
 };
 
 __constant__ unsigned char c_par_mask[kNMMax];  // bit d set: multi-index odd in axis d
@@ -221,6 +231,7 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
 #pragma unroll
     for (int t = 0; t < NL; t++) L[t] = (T)0;
     T vx = 0, vy = 0, vz = 0, mt = 0;
+    T l0 = 0, wq = 0;  // potential only: L_0 and sum m |x* - e|^2
     unsigned long long nused = 0;
     for (int cell = lane; cell < ncp; cell += 32) {
       const double* Mc = a.fm + ((int64_t)box * ncp + cell) * NE;
@@ -250,6 +261,15 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
       vy += M[0] * ((T)oy * scale) + M[2];
       vz += M[0] * ((T)oz * scale) + M[3];
       mt += M[0];
+      if constexpr (PE >= 2) {
+        if (a.potw) {
+          // L_0, and the cell's sum of m |x* - e|^2 about its centre r = c* - e
+          l0 += PE_<PE>::template l0<T>(M, D);
+          const T rx = (T)ox * scale, ry = (T)oy * scale, rz = (T)oz * scale;
+          wq += M[0] * fma(rx, rx, fma(ry, ry, rz * rz)) + (T)2 * fma(rx, M[1], fma(ry, M[2], rz * M[3])) +
+                (M[4] + M[7] + M[9]);
+        }
+      }
     }
 #pragma unroll
     for (int t = 0; t < NL; t++) {
@@ -263,6 +283,10 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
       vz += __shfl_xor_sync(0xffffffffu, vz, o);
       mt += __shfl_xor_sync(0xffffffffu, mt, o);
       nused += __shfl_xor_sync(0xffffffffu, nused, o);
+      if (a.potw) {
+        l0 += __shfl_xor_sync(0xffffffffu, l0, o);
+        wq += __shfl_xor_sync(0xffffffffu, wq, o);
+      }
     }
     T* dst = a.lbuf + (int64_t)gd.w * a.lstride;
     for (int t = lane; t < NL; t += 32) {
@@ -277,6 +301,8 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
       dst[NL + 1] = vy;
       dst[NL + 2] = vz;
       dst[NL + 3] = mt;
+      dst[NL + 4] = l0;
+      dst[NL + 5] = wq;
       if (a.counter) atomicAdd(a.counter, nused);
     }
   }
@@ -314,6 +340,13 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
     T az = a.accw[2 * tr.n + i] + fourpi3 * (mt * dz - vz);
     PE_<PE>::template l2p<T>(L, dx, dy, dz, ax, ay, az);
     const uint32_t j = tr.perm[i];
+    if (a.potw) {
+      // walk + image series + the background's -(2 pi/3) sum m |x - x*|^2
+      const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      const T bgq = fma(mt, d2, fma((T)-2, fma(dx, vx, fma(dy, vy, dz * vz)), Lr[NL + 5]));
+      a.pout[j] = (float)(a.potw[i] + PE_<PE>::template pot<T>(Lr[NL + 4], L, dx, dy, dz) -
+                          (T)(2.0 * M_PI / 3.0) * bgq);
+    }
     if (a.out64) {
       a.out64[j] = (double)ax;
       a.out64[tr.n + j] = (double)ay;
@@ -337,6 +370,14 @@ __global__ void scatter_kernel(int64_t n, const uint32_t* __restrict__ perm, con
     out[n + j] = (O)accw[n + i];
     out[2 * n + j] = (O)accw[2 * n + i];
   }
+}
+
+// potential to the caller's order when there are no periodic images
+template <typename T>
+__global__ void scatter_pot_kernel(int64_t n, const uint32_t* __restrict__ perm, const T* __restrict__ potw,
+                                   float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[perm[i]] = (float)potw[i];
 }
 
 // ---- host side: term tables and cached device tables ------------------------------
@@ -437,14 +478,20 @@ cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t
   return cudaSuccess;
 }
 
+// per run of groups: L (nl), V (3), M_total, and for the potential L_0 and W
 int nb_field_stride(int pe) {
   const int nl = (pe + 2) * (pe + 3) * (pe + 4) / 6 - 1;
-  return (nl + 4 + 3) & ~3;
+  return (nl + 6 + 3) & ~3;
 }
 
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
-                        double* out64, cudaStream_t s) {
+                        double* out64, const void* potw, float* pout, cudaStream_t s) {
+  if (pe == 0 && potw) {
+    if (fp64) scatter_pot_kernel<double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)potw, pout);
+    else scatter_pot_kernel<float><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const float*)potw, pout);
+    nb_launch_counter += 1;
+  }
   if (pe == 0) {
     if (out64) {
       if (fp64) scatter_kernel<double, double><<<1024, 256, 0, s>>>(tr.n, tr.perm, (const double*)accw, tr.sact, out64);
@@ -464,7 +511,7 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
 #define NB_PER(TT, PE)                                                                              \
   {                                                                                                 \
     PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
-                  (const TT*)accw, out, counter, out64};                                            \
+                  (const TT*)accw, out, counter, out64, (const TT*)potw, pout};                     \
     field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     field_l2p_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     break;                                                                                          \
@@ -503,7 +550,7 @@ cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg,
 #define NB_LOC(TT, PE)                                                                              \
   {                                                                                                 \
     PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
-                  nullptr, nullptr, nullptr, nullptr};                                              \
+                  nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};                            \
     field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     break;                                                                                          \
   }

@@ -42,6 +42,10 @@ template <int P> struct WOrd;
                                                 float2& ax, float2& ay, float2& az) {                 \
       m2p2_p##P(B, x, y, z, e2, ax, ay, az);                                                          \
     }                                                                                                 \
+    template <typename T>                                                                             \
+    static __device__ __forceinline__ T pot(const T* B, T x, T y, T z, T e2) {                        \
+      return m2pot_p##P<T>(B, x, y, z, e2);                                                           \
+    }                                                                                                 \
   };
 NB_WORD(0)
 NB_WORD(1)
@@ -58,6 +62,8 @@ template <int P> struct WBg {
   template <typename T>
   static __device__ __forceinline__ void add(T, T, T, T, T&, T&, T&) {}
   static __device__ __forceinline__ void add2(float2, float2, float2, float2, float2&, float2&, float2&) {}
+  template <typename T>
+  static __device__ __forceinline__ T pot(T, T, T, T) { return T(0); }
 };
 #define NB_WBG(P, L)                                                                                        \
   template <> struct WBg<P> {                                                                               \
@@ -69,6 +75,10 @@ template <int P> struct WBg {
     static __device__ __forceinline__ void add2(float2 q, float2 x, float2 y, float2 z, float2& ax, float2& ay, \
                                                 float2& az) {                                               \
       cube_bg2_l##L(q, x, y, z, ax, ay, az);                                                                \
+    }                                                                                                       \
+    template <typename T>                                                                                   \
+    static __device__ __forceinline__ T pot(T q, T x, T y, T z) {                                           \
+      return cube_bgpot_l##L<T>(q, x, y, z);                                                                \
     }                                                                                                       \
   };
 NB_WBG(0, 4)
@@ -126,6 +136,7 @@ struct WalkArgs {
   int stack_cap;
   int* group_ctr;
   T* acc;  // 3n, key order
+  T* pot;  // n, key order, or null: the potential variant (see below) writes it
   unsigned long long* counters;  // [0] p2p, [1] m2p
   unsigned* status;
 };
@@ -139,8 +150,15 @@ constexpr double kScale = 1.0 / 8388608.0;  // 2^-23
 // of cells 2q and 2q + 1 are staged interleaved and each pair instruction
 // advances both expansions, halving the instructions issued per M2P; every
 // cell's result is bitwise the scalar one).  The autotuner picks.
-template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK>
+//
+// POTK adds the potential (scalar form only, not with the dual form): every
+// interaction's potential form alongside its acceleration, -Psi with Psi =
+// sum_j F_j S_j for an expansion (divided by its cell scale), the background
+// term's q h / r^(2l+1), and m (r^2 + eps^2)^-1/2 (or the K1 kernel's
+// potential) for a direct pair other than the sink itself.
+template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK, bool POTK = false>
 __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
+  static_assert(!POTK || (!PK && !DUALK), "the potential variant is scalar and without the dual form");
   using V4 = typename Vec4<T>::type;
   constexpr int NBS = WOrd<P>::NBS;
   constexpr int C16 = NBS * (int)sizeof(T) / 16;  // 16-byte pieces per cell's coefficients
@@ -167,6 +185,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   __shared__ int s_plev[WARPS][32];
   __shared__ T s_poff[WARPS][32][3];
   __shared__ int4 s_pcen[WARPS][32];
+  __shared__ int s_sj[WARPS][POTK ? 32 : 1];  // the staged sources' indices (the sink's own pair is skipped)
 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
@@ -196,6 +215,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       zi = o.z + (T)(la.z - gd.z) * scale;
     }
     T ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;
+    T ps = 0, pc = 0;  // Psi (the potential is -Psi), Kahan pair
     // double-float sum of the largest cells' monopole terms (FP32 walk only),
     // kept in shared memory: it changes once per such cell
     constexpr bool DF = std::is_same<T, float>::value;
@@ -385,7 +405,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         // each cell's term is formed from zero and added to the chunk sum
         // once (the largest cells' monopoles, the terms that cancel most,
         // are summed apart in double-float)
-        T px = 0, py = 0, pz = 0;
+        T px = 0, py = 0, pz = 0, pp = 0;
         // each M2P runs in its cell's unit (coordinates times 2^level,
         // coefficients pre-scaled): see the upward pass
         auto cells = [&](auto bgc) {
@@ -399,6 +419,15 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             px += tx;
             py += ty;
             pz += tz;
+            if constexpr (POTK) {
+              // Psi in the cell's unit is 2^level times the true one
+              T tp = WOrd<P>::template pot<T>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q]);
+              if constexpr (decltype(bgc)::value)
+                tp += WBg<P>::template pot<T>(s_coef[wid][q * NBS + WOrd<P>::NB], rx, ry, rz);
+              if (DF && w.bg && mo.w <= (T)kDfScale)  // the monopole taken out of the expansion
+                tp += s_b0[wid][q] * nbody_rsqrt(fma(rx, rx, fma(ry, ry, fma(rz, rz, s_meps[wid][q]))));
+              pp = fma(tp, (T)1 / mo.w, pp);
+            }
           }
         };
         if (WBg<P>::has && w.bg) cells(std::true_type{});
@@ -407,6 +436,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         kadd(ax, cx, px);
         kadd(ay, cy, py);
         kadd(az, cz, pz);
+        if constexpr (POTK) kadd(ps, pc, pp);
       }
       n_m2p += nmp;
       __syncwarp();
@@ -512,9 +542,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         __syncwarp();
         // source t of this pop's P2P cells at its image, relative to e; past
         // the end a massless source at the origin
-        auto fetch = [&](int t) {
+        auto fetch = [&](int t, int& jo) {
           V4 v;
           v.x = v.y = v.z = v.w = (T)0;
+          jo = -1;
           if (t < total) {
             // last P2P lane q with pfx[q] <= t
             int lo = 0, hi = 31;
@@ -524,6 +555,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             }
             const int q = lo;
             const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
+            jo = j;
             v = w.src[j];
             T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
             if (s_plev[wid][q] < w.le) {
@@ -543,7 +575,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           return v;
         };
         // the next chunk's sources are fetched while this chunk is summed
-        V4 v = fetch(lane);
+        int jv = -1, jnext = -1;
+        V4 v = fetch(lane, jv);
         for (int b0 = 0; b0 < total; b0 += 32) {
           if constexpr (PK) {
             // pairs of sources interleaved: (x0, x1, y0, y1) then (z0, z1, m0, m1)
@@ -556,10 +589,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             pb[4 * pr + 2 + hf] = v.w;
           } else {
             s_src[wid][lane] = v;
+            if constexpr (POTK) s_sj[wid][lane] = jv;
           }
           __syncwarp();
           const int nn = min(32, total - b0);
-          const V4 vnext = fetch(b0 + 32 + lane);
+          const V4 vnext = fetch(b0 + 32 + lane, jnext);
           // pair factor f of a = m d f: Plummer (r^2 + eps^2)^(-3/2), or the
           // K1 kernel, Newtonian from eps on and (175/16 - (147/8) x^2 +
           // (135/16) x^4)/eps^3 inside (x = r/eps: the enclosed mass of its
@@ -598,7 +632,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
                 kadd(az, cz, pz.x + pz.y);
               }
             } else if (act) {
-              T px = 0, py = 0, pz = 0;
+              T px = 0, py = 0, pz = 0, pp = 0;
               for (int k = 0; k < nn; k++) {
                 const V4 s = s_src[wid][k];
                 const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
@@ -613,16 +647,30 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
                 px = fma(dx, f, px);
                 py = fma(dy, f, py);
                 pz = fma(dz, f, pz);
+                if constexpr (POTK) {
+                  // m (r^2 + eps^2)^-1/2, or K1's m (105/32 - 175/32 x^2 + 147/32 x^4 - 45/32 x^6)/eps inside eps
+                  T u = s.w * inv;
+                  if constexpr (K1) {
+                    const T x2 = r2 * ie2;
+                    if (x2 < (T)1)
+                      u = s.w * sqrt(ie2) *
+                          fma(x2, fma(x2, fma(x2, (T)(-45.0 / 32.0), (T)(147.0 / 32.0)), (T)(-175.0 / 32.0)),
+                              (T)(105.0 / 32.0));
+                  }
+                  if (s_sj[wid][k] != i) pp += u;
+                }
               }
               kadd(ax, cx, px);
               kadd(ay, cy, py);
               kadd(az, cz, pz);
+              if constexpr (POTK) kadd(ps, pc, pp);
             }
           };
           if (w.k1) pairs(std::true_type{});
           else pairs(std::false_type{});
           __syncwarp();
           v = vnext;
+          jv = jnext;
         }
         n_p2p += (unsigned long long)total;
       }
@@ -703,6 +751,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         w.acc[tr.n + i] = ay - cy;
         w.acc[2 * tr.n + i] = az - cz;
       }
+      if constexpr (POTK) w.pot[i] = -(ps - pc);
     }
     if (lane == 0) {
       atomicAdd(&w.counters[0], n_p2p * (unsigned long long)cnt);
@@ -716,14 +765,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   }
 }
 
-template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK>
+template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK, bool POTK = false>
 cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
   // resident blocks per SM, queried once per variant (and so never while a
   // stream is being captured, after the first evaluation)
   static int occ = 0;
   if (occ == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, walk_kernel<T, P, WARPS, MINB, PK, DUALK>,
-                                                                   WARPS * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, walk_kernel<T, P, WARPS, MINB, PK, DUALK, POTK>, WARPS * 32, 0);
     if (e) {
       occ = 0;
       return e;
@@ -731,7 +780,7 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
   }
   int grid = nsm * (occ > 0 ? occ : 1);
   if (grid > max_blocks) grid = max_blocks;
-  walk_kernel<T, P, WARPS, MINB, PK, DUALK><<<grid, WARPS * 32, 0, s>>>(a);
+  walk_kernel<T, P, WARPS, MINB, PK, DUALK, POTK><<<grid, WARPS * 32, 0, s>>>(a);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
@@ -742,6 +791,11 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
 // The stack is sized for 8 warps per block.
 template <typename T, int P>
 cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
+  // the potential: one scalar variant per precision (never with the dual form)
+  if (a.pot) {
+    if constexpr (sizeof(T) == 8) return launch_walk<T, P, 4, 1, false, false, true>(a, nsm, max_blocks, s);
+    else return launch_walk<T, P, 8, 1, false, false, true>(a, nsm, max_blocks, s);
+  }
   if constexpr (sizeof(T) == 8) {
     return launch_walk<T, P, 4, 1, false, false>(a, nsm, max_blocks, s);
   } else {
@@ -782,7 +836,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
   cudaGetDevice(&dev);
   // tuning key: 0 FP32, 1 FP64, 2 FP32 with the dual form
   const int fp = sizeof(T) == 8 ? 1 : (a.dual ? 2 : 0);
-  if (forced >= 0) return launch_variant<T, P>(fp == 1 ? 0 : forced, a, nsm, max_blocks, s);
+  if (forced >= 0 || a.pot) return launch_variant<T, P>(fp == 1 || forced < 0 ? 0 : forced, a, nsm, max_blocks, s);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     for (const auto& t : g_tune)
@@ -851,7 +905,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
                     unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
                     int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
-                    cudaStream_t s) {
+                    void* pot, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
 #define NB_WALK(TT, P)                                                             \
@@ -875,6 +929,8 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.stack_cap = stack_cap;                                                       \
     a.group_ctr = group_ctr;                                                       \
     a.acc = (TT*)acc;                                                              \
+    a.pot = (TT*)pot;                                                              \
+    if (pot) a.dual = 0;                                                           \
     a.counters = counters;                                                         \
     a.status = status;                                                             \
     return run_walk<TT, P>(a, nsm, max_blocks, forced_variant, s);                 \

@@ -120,7 +120,7 @@ def lib():
         L.nbody_forces_batched.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_int64),
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), _vp, _vp, _vp,
                                            C.POINTER(_vp), _vp]
-        L.nbody_forces.argtypes = [_vp, _vp, C.POINTER(Stats), _vp]
+        L.nbody_forces.argtypes = [_vp, _vp, _vp, C.POINTER(Stats), _vp]
         L.nbody_forces64.argtypes = [_vp, _vp, _vp]
         L.nbody_kdk_step.argtypes = [_vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp]
         L.nbody_assign_rungs.argtypes = [_vp, _vp, C.c_double, C.c_double, C.c_int, _vp, _vp]
@@ -192,8 +192,9 @@ def nbody_forces_batched(params: Params, offsets, box_len, eps, pos_dev: int, ma
     return rc, h.value
 
 
-def nbody_forces(tree: int, acc_dev: int, stats: Stats | None = None, stream: int | None = None) -> int:
-    return lib().nbody_forces(tree, acc_dev, C.byref(stats) if stats is not None else None, stream)
+def nbody_forces(tree: int, acc_dev: int, pot_dev: int | None = None, stats: Stats | None = None,
+                 stream: int | None = None) -> int:
+    return lib().nbody_forces(tree, acc_dev, pot_dev, C.byref(stats) if stats is not None else None, stream)
 
 
 def nbody_forces64(tree: int, acc_dev: int, stream: int | None = None) -> int:
@@ -326,13 +327,21 @@ class Tree:
             self.handle = h
         _check(rc, "nbody_build_tree")
 
-    def forces(self, acc=None, stats=False):
+    def forces(self, acc=None, stats=False, pot=None):
+        """(3, n) float32 accelerations; with pot=True (or an (n,) float32
+        tensor to fill) also the potential: returns (acc, pot[, stats])."""
         import torch
         if acc is None:
             acc = torch.empty((3, self.n), dtype=torch.float32, device=self.pos.device)
+        if pot is True:
+            pot = torch.empty(self.n, dtype=torch.float32, device=self.pos.device)
         st = Stats() if stats else None
-        _check(nbody_forces(self.handle, acc.data_ptr(), st, _stream()), "nbody_forces")
-        return (acc, st.asdict()) if stats else acc
+        _check(nbody_forces(self.handle, acc.data_ptr(), None if pot is None else pot.data_ptr(), st, _stream()),
+               "nbody_forces")
+        out = (acc,) if pot is None else (acc, pot)
+        if stats:
+            out = out + (st.asdict(),)
+        return out[0] if len(out) == 1 else out
 
     def forces64(self, acc=None):
         """(3, n) float64 accelerations (nbody_forces64)."""

@@ -58,6 +58,7 @@ template <int P> struct K;
       p2m_adj_p##P(m, x, y, z, nu, gx, gy, gz);                                                        \
     }                                                                                                  \
     static void m2m(const double* Mc, double x, double y, double z, double* Mp) { m2m_acc_p##P(Mc, x, y, z, Mp); } \
+    static double pot(const double* B, double x, double y, double z, double e) { return m2pot_p##P<double>(B, x, y, z, e); } \
     static void m2madj(const double* nup, double x, double y, double z, double* nuc) { m2m_adj_acc_p##P(nup, x, y, z, nuc); } \
   };
 KD(0) KD(1) KD(2) KD(3) KD(4)
@@ -175,6 +176,10 @@ template <int PE> struct F;
       l2p_adj_pe##PE<double>(x, y, z, lx, ly, lz, Lb);                                                \
     }                                                                                                 \
     static void madj(const double* Lb, const double* D, double* nu) { m2l_adj_pe##PE<double>(Lb, D, nu); } \
+    static double l0(const double* M, const double* D) { return m2l0_pe##PE<double>(M, D); }            \
+    static double pot(double L0, const double* L, double x, double y, double z) {                      \
+      return l2pot_pe##PE<double>(L0, L, x, y, z);                                                    \
+    }                                                                                                 \
   };
 FD(1) FD(2) FD(3) FD(4) FD(5)
 
@@ -324,6 +329,7 @@ template <int P> void run_io() {
   for (int t = 0; t < NM; t++) std::printf("%.17g\n", M[t]);
   for (int d = 0; d < 3; d++) std::printf("%.17g\n", a[d]);
   for (int t = 0; t < NM; t++) std::printf("%.17g\n", Mp[t]);
+  std::printf("%.17g\n", K<P>::pot(B, R[0], R[1], R[2], eps * eps));
 }
 
 // one image-field case from stdin: NE source moments M (orders <= pe about
@@ -344,6 +350,7 @@ template <int PE> void run_field_io() {
   double a[3] = {0, 0, 0};
   F<PE>::l2p(L, d[0], d[1], d[2], a[0], a[1], a[2]);
   for (int k = 0; k < 3; k++) std::printf("%.17g\n", a[k]);
+  std::printf("%.17g\n", F<PE>::pot(F<PE>::l0(M, D), L, d[0], d[1], d[2]));
 }
 
 // the dual form's cell-group interaction: moments (nmom(P)), R, eps and the
@@ -440,7 +447,8 @@ int main(int argc, char** argv) {
       double a4[3] = {0, 0, 0}, a6[3] = {0, 0, 0};
       cube_bg_l4<double>(1.0, x, y, z, a4[0], a4[1], a4[2]);
       cube_bg_l6<double>(1.0, x, y, z, a6[0], a6[1], a6[2]);
-      std::printf("%.17g %.17g %.17g %.17g %.17g %.17g\n", a4[0], a4[1], a4[2], a6[0], a6[1], a6[2]);
+      std::printf("%.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g\n", a4[0], a4[1], a4[2], a6[0], a6[1], a6[2],
+                  cube_bgpot_l4<double>(1.0, x, y, z), cube_bgpot_l6<double>(1.0, x, y, z));
     }
     return 0;
   }

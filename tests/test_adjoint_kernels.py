@@ -46,12 +46,15 @@ def test_background_terms_match_the_oracle_cube_expansion(harness):
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     got = np.array([[float(v) for v in line.split()] for line in r.stdout.strip().split("\n")])
-    assert got.shape == (len(pts), 6)
+    assert got.shape == (len(pts), 8)
     M = O.cube_moments(1.0, 1.0, 6)
     for i, R in enumerate(pts):
         for k, l in enumerate((4, 6)):
             ref = O.m2p_orders(M, l, l, R, 0.0)
             assert np.abs(got[i, 3 * k:3 * k + 3] - ref).max() <= 1e-12 * np.abs(ref).max(), (l, R)
+            pref = O.m2p_pot(M, l, l, R, 0.0)  # the potential forms
+            # (scale: the term's size |a| |R|, as the angular factor can nearly vanish)
+            assert abs(got[i, 6 + k] - pref) <= 1e-12 * max(abs(pref), np.abs(ref).max() * np.linalg.norm(R)), (l, R)
 
 
 @pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
@@ -76,13 +79,16 @@ def test_forward_expansion_kernels_match_the_oracle(harness, p):
         assert r.returncode == 0, r.stderr
         v = np.array([float(x) for x in r.stdout.split()])
         nm = O.nmom(p)
-        assert len(v) == 2 * nm + 3
+        assert len(v) == 2 * nm + 4
         Mo = O.p2m(d, m, np.zeros(3), p)
         ao = O.m2p(Mo, p, R, eps)
         Mpo = O.m2m(Mo, sh, np.zeros(3), p)
+        po = O.m2p_pot(Mo, 0, p, R, eps)
         assert np.abs(v[:nm] - Mo).max() <= 1e-14 * np.abs(Mo).max()
         assert np.abs(v[nm:nm + 3] - ao).max() <= 1e-13 * np.abs(ao).max()
-        assert np.abs(v[nm + 3:] - Mpo).max() <= 1e-14 * np.abs(Mpo).max()
+        assert np.abs(v[nm + 3:2 * nm + 3] - Mpo).max() <= 1e-14 * np.abs(Mpo).max()
+        # the potential form (m2pot) from the same coefficients
+        assert abs(v[-1] - po) <= 1e-13 * abs(po)
 
 
 @pytest.mark.parametrize("pe", [1, 2, 3, 4, 5])
@@ -103,20 +109,27 @@ def test_image_field_expansion_converges_at_its_order(harness, pe):
     w /= np.linalg.norm(w)
     mi = O.multi_indices(pe)
     D = O.phitilde_mi(R0, pe + 1)
-    errs = []
-    for h in (0.08, 0.04, 0.02):
+    errs, perrs = [], []
+    for h in (0.08, 0.04, 0.02, 0.01):
         delta, d = h * u, 0.7 * h * w
         M = np.array([delta[0] ** n[0] * delta[1] ** n[1] * delta[2] ** n[2] for n in mi])
         inp = ("%d\n" % pe + "\n".join("%.17g" % v for v in M) + "\n" + "\n".join("%.17g" % v for v in D)
                + "\n%.17g %.17g %.17g\n" % tuple(d))
         r = subprocess.run([harness, "field"], input=inp, capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
-        a = np.array([float(x) for x in r.stdout.split()])
+        v = np.array([float(x) for x in r.stdout.split()])
+        a = v[:3]
         exact = -O.phitilde_mi(R0 + d - delta, 1)[1:4]
         errs.append(np.linalg.norm(a - exact) / np.linalg.norm(exact))
+        # the potential series (m2l0 + l2pot) against phi~ itself: the same
+        # order (the order-(pe+1) moment term it lacks is the same at every sink)
+        perrs.append(abs(v[3] - O.phitilde_mi(R0 + d - delta, 0)[0]))
     assert errs[2] <= 0.02 * 0.3 ** (pe - 1)
     for i in range(2):
         assert errs[i] / errs[i + 1] >= 0.8 * 2 ** (pe + 1), (pe, errs)
+    # (the potential's two leading error orders nearly cancel at the larger
+    # offsets for some pe: its rate is checked on the two smallest)
+    assert perrs[2] / perrs[3] >= 0.75 * 2 ** (pe + 1), (pe, perrs)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
