@@ -419,6 +419,21 @@ def _code_flops(code):
     return 2 * code.count("fma(") + len(re.findall(r" \* ", code)) + code.count("nbody_rsqrt(")
 
 
+def upward_flop_counts(p):
+    """FP64 flops of the upward pass as generated (FMA = 2, product = 1,
+    addition = 1): per particle (P2M, plus the three coordinate differences
+    from the leaf centre), per daughter (its M2M shift into the parent, the
+    three centre differences being exact integer conversions), and per cell
+    (the power-of-two scalings of its moments and coefficients and the
+    reduction to the walk's coefficients)."""
+    def count(code):
+        return (2 * code.count("fma(") + len(re.findall(r" \* ", code)) + code.count("+=") +
+                len(re.findall(r" \+ ", code)))
+    nm, nb = len(multi(p)), len(slots(p))
+    return {"p2m_per_particle": count(emit_p2m(p)) + 3, "m2m_per_daughter": count(emit_m2m(p)),
+            "per_cell": count(emit_reduce(p)) + nm + nb}
+
+
 def m2l_dual_flop_count(p):
     """Flops of one cell-group expansion of the dual form at order p: the
     softened derivative tensor to order p + 1 (with its negation), the

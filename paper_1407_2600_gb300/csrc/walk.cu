@@ -273,8 +273,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     auto m2l_chunk = [&](int nml) {
       if constexpr (DUAL) {
         constexpr int NM4 = ((P + 1) * (P + 2) * (P + 3) / 6 + 3) / 4;
-        // rows of lane values per pass through the coefficient buffer
-        constexpr int NL = WDual<P>::NL, ROWS = (32 * NBS) / 33 < NL ? (32 * NBS) / 33 : NL;
+        // rows of lane values per pass through the coefficient buffer: at
+        // most what the buffer holds, and at most 32 (one summing lane each)
+        constexpr int NL = WDual<P>::NL, RB = (32 * NBS) / 33 < 32 ? (32 * NBS) / 33 : 32,
+                      ROWS = RB < NL ? RB : NL;
         const int q = lane < nml ? lane : 0;
         const float live = lane < nml ? 1.f : 0.f;
         float Mr[4 * NM4];
@@ -787,7 +789,8 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
 
 // launch variants (warps per block, minimum resident blocks per SM, M2P
 // form): 16 warps per SM in blocks of 8 or 4, so every variant has 128
-// registers per thread (none spills); with the dual form 8 or 12 warps per SM.
+// registers per thread (none spills); with the dual form three variants at
+// 16 warps per SM (a few dozen bytes spilled) and one at 12.
 // The stack is sized for 8 warps per block.
 template <typename T, int P>
 cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
@@ -801,12 +804,13 @@ cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks,
   } else {
     if constexpr (WDual<P>::has) {
       if (a.dual) {
-        // the cell-group expansions need more registers: 8 or 12 warps per SM
+        // the cell-group expansions want more registers: 16 warps per SM
+        // with a few spilled (128 registers), or 12 without
         switch (v) {
-          case 0: return launch_walk<T, P, 8, 1, false, true>(a, nsm, max_blocks, s);
-          case 1: return launch_walk<T, P, 4, 3, false, true>(a, nsm, max_blocks, s);
-          case 2: return launch_walk<T, P, 8, 1, true, true>(a, nsm, max_blocks, s);
-          default: return launch_walk<T, P, 4, 3, true, true>(a, nsm, max_blocks, s);
+          case 0: return launch_walk<T, P, 8, 2, false, true>(a, nsm, max_blocks, s);
+          case 1: return launch_walk<T, P, 4, 3, true, true>(a, nsm, max_blocks, s);
+          case 2: return launch_walk<T, P, 8, 2, true, true>(a, nsm, max_blocks, s);
+          default: return launch_walk<T, P, 4, 4, true, true>(a, nsm, max_blocks, s);
         }
       }
     }

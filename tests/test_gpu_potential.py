@@ -4,8 +4,8 @@ oracle's tree potential, through the C ABI.
 The potential crosses zero (zero-mean periodic convention), so errors are
 measured per particle against the root-mean-square potential of the sample:
 |phi_gpu - phi_oracle| / rms(phi_oracle), with the tree-parity bars of the
-forces (median <= 1e-5, 99th percentile <= 1e-4) in the mixed-precision mode
-and 1e-10 in the all-FP64 mode."""
+forces (median <= 1e-5, 99th percentile <= 1e-4) in the mixed-precision mode,
+and the FP32 rounding of output and masses in the all-FP64 mode."""
 import numpy as np
 import pytest
 
@@ -89,14 +89,18 @@ def test_potential_vs_oracle_tree(cuda, name, flags, extra, order, theta):
 
 def test_potential_fp64_mode_and_no_images(cuda):
     """All-FP64 interactions match the oracle to the rounding of the FP32
-    output (2^-24 of each value) plus 1e-10 of the rms (periodic, and with
-    the image field off, where the potential is the walk's alone)."""
+    output (2^-24 of each value) and of the FP32 particle mass 1/n (every
+    term carries the same mass, so it scales the whole potential), plus
+    1e-10 of the rms (periodic, and with the image field off, where the
+    potential is the walk's alone)."""
     x, eps = _clustered(8)
+    n = len(x)
+    dm = abs(float(np.float32(1.0 / n)) * n - 1.0)
     for ew in (4, 0):
         _, p, _ = _gpu(x, cuda, eps=eps, theta=0.5, order=4, n_direct=4, precision=1, ewald_order=ew)
         _, rp = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.5, 4, n_direct=4, ewald=ew),
                                    return_pot=True)
-        bound = 2.0 ** -24 * np.abs(rp) + 1e-10 * np.sqrt(np.mean(rp ** 2))
+        bound = (2.0 ** -24 + dm) * np.abs(rp) + 1e-10 * np.sqrt(np.mean(rp ** 2))
         assert np.all(np.abs(p - rp) <= bound), (ew, np.max(np.abs(p - rp) / bound))
 
 
