@@ -57,7 +57,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
                     int forced_variant, int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
-                    void* pot, cudaStream_t s);
+                    const NbDualBufs* db, void* pot, cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -157,6 +157,10 @@ struct nbody_tree {
   // walk
   Buf eps2, stack, gctr, accw, counters, lbuf;
   Buf potw;  // the walk's potential (key order), when one is asked for
+  // the dual form's cell-group pair chunks (lc_cap chunks of 32 pairs)
+  Buf lc_cell, lc_img, lc_head, lc_first, lc_ctr, lc_L;
+  int64_t lc_cap = 0;
+  bool lc_grew = false;  // the last status read grew the pool
   // reverse mode
   Buf a_lam, a_mu, a_nuc, a_nu, a_lbar, a_nue, a_x0, a_x1, a_ph, a_g, a_lg, a_lx, a_lp, a_out;
   // the KDK adjoint's kept product J(x0)^T lam_ph with its x0 and lam_p0
@@ -186,7 +190,8 @@ struct nbody_tree {
                   &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho, &act_s, &act_g, &rungc,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
-                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32, &potw};
+                  &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32, &potw,
+                  &lc_cell, &lc_img, &lc_head, &lc_first, &lc_ctr, &lc_L};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     delete aux;
@@ -449,13 +454,35 @@ int gridn(int64_t n, int threads) {
   return (int)g;
 }
 
+// After an overflow: if the dual form's last walk asked for more pair chunks
+// than its pool holds, size the pool for that many (and a quarter more) so
+// that the next evaluation fits; true when it grew.
+bool dual_regrow(nbody_tree* t, cudaStream_t s) {
+  if (!(t->prm.flags & NBODY_FLAG_DUAL) || !t->lc_ctr.p) return false;
+  int need = 0;
+  if (cudaMemcpyAsync(&need, t->lc_ctr.p, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if ((int64_t)need <= t->lc_cap) return false;
+  t->lc_cap = (int64_t)need + need / 4 + 1024;
+  return true;
+}
+
+// the status word of the calls since the last read (and on an overflow the
+// dual form's pair pool sized for the next evaluation)
 int read_status(nbody_tree* t, cudaStream_t s) {
   unsigned st = 0;
   NB_CU(cudaMemcpyAsync(&st, t->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   NB_CU(cudaStreamSynchronize(s));
   NB_CU(cudaMemsetAsync(t->status.p, 0, sizeof(unsigned), s));
-  return status_to_code(st);
+  const int rc = status_to_code(st);
+  t->lc_grew = rc == NBODY_EOVERFLOW && dual_regrow(t, s);
+  return rc;
 }
+
+
 
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
@@ -753,6 +780,22 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   tr.gact = gact;
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   const bool dual = (p.flags & NBODY_FLAG_DUAL) != 0;
+  NbDualBufs db{};
+  if (dual) {
+    // chunks of 32 cell-group pairs: 32 per group to begin with (1024 pairs;
+    // the benchmark workload averages under 600), grown when a walk asks for
+    // more (dual_regrow)
+    if (t->lc_cap == 0) t->lc_cap = std::max<int64_t>(1024, (int64_t)t->group_cap * 32);
+    const int64_t cap = t->lc_cap;
+    NB_CU(t->lc_cell.ensure(4 * 32 * cap));
+    NB_CU(t->lc_img.ensure(4 * 32 * cap));
+    NB_CU(t->lc_head.ensure(16 * cap));
+    NB_CU(t->lc_L.ensure(4 * (int64_t)kDualLStride * cap));
+    NB_CU(t->lc_first.ensure(4 * (int64_t)t->group_cap + 64));
+    NB_CU(t->lc_ctr.ensure(64));
+    db = NbDualBufs{t->lc_cell.as<int>(), t->lc_img.as<int>(), t->lc_head.as<int4>(), t->lc_first.as<int>(),
+                    t->lc_ctr.as<int>(), t->lc_L.as<float>(), (int)cap};
+  }
   // with a potential: the potential variant of the walk (accelerations too);
   // with the dual form it gives the potential only, and the dual walk then
   // writes the accelerations (the potential of every accepted cell is its
@@ -765,7 +808,7 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
                   t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1,
                   (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0, (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0,
                   (p.flags & NBODY_FLAG_K1) ? 1 : 0, dual ? 1 : 0, p.theta, t->mom32.as<float>(), group_level(p),
-                  pass == 0 ? t->potw.p : nullptr, s));
+                  dual ? &db : nullptr, pass == 0 ? t->potw.p : nullptr, s));
   }
   if (timed) NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
@@ -958,14 +1001,20 @@ int nbody_forces(nbody_tree* tree, float* acc_dev, float* pot_dev, nbody_stats* 
   // the background's potential needs the image cells' second moments
   if (pot_dev && tree->prm.ewald_order == 1) return NBODY_ENOTSUP;
   cudaStream_t s = (cudaStream_t)stream;
-  const long long l0 = nb_launch_counter;
-  int rc = forces_impl(tree, acc_dev, s, nullptr, nullptr, nullptr, pot_dev);
-  if (rc == NBODY_OK) rc = scale_boxes<float>(tree, 1, acc_dev, acc_dev, s);
-  if (rc == NBODY_OK && pot_dev) rc = scale_boxes<float>(tree, 0, pot_dev, pot_dev, s, 1);
-  tree->launches += nb_launch_counter - l0;
-  if (rc) return rc;
-  if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
-  rc = read_status(tree, s);
+  int rc = NBODY_OK;
+  // a walk of the dual form that outgrew its pair pool is redone once with a
+  // pool of the size it asked for (when the call synchronises)
+  for (int attempt = 0; attempt < 2; attempt++) {
+    const long long l0 = nb_launch_counter;
+    rc = forces_impl(tree, acc_dev, s, nullptr, nullptr, nullptr, pot_dev);
+    if (rc == NBODY_OK) rc = scale_boxes<float>(tree, 1, acc_dev, acc_dev, s);
+    if (rc == NBODY_OK && pot_dev) rc = scale_boxes<float>(tree, 0, pot_dev, pot_dev, s, 1);
+    tree->launches += nb_launch_counter - l0;
+    if (rc) return rc;
+    if (tree->prm.flags & NBODY_FLAG_ASYNC) return NBODY_OK;
+    rc = read_status(tree, s);
+    if (rc != NBODY_EOVERFLOW || capturing(s) || !tree->lc_grew) break;
+  }
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     unsigned long long c[4] = {0, 0, 0, 0};

@@ -172,6 +172,21 @@ struct DevTree {
   const uint8_t* gact;
 };
 
+// The dual form's cell-group pairs: the walk emits each group's pairs in
+// chunks of up to 32 (one group per chunk, linked in the walk's order), a
+// separate pass forms each chunk's summed local expansion, and a third sums
+// a group's chunks in list order and evaluates the expansion at its sinks.
+struct NbDualBufs {
+  int* cell;      // cap x 32 source cells
+  int* img;       // cap x 32 image shifts, (kx + 1) | (ky + 1) << 2 | (kz + 1) << 4
+  int4* head;     // cap: group, pair count, next chunk of the group (-1), 0
+  int* first;     // per group: its first chunk, or -1
+  int* ctr;       // chunks asked for (can exceed cap: the overflow is reported)
+  float* L;       // cap x kDualLStride: each chunk's local coefficients, group unit
+  int cap;
+};
+constexpr int kDualLStride = 56;  // local coefficients per chunk (orders 1..5)
+
 // kernels launched by this thread through the library (benchmark accounting)
 extern thread_local long long nb_launch_counter;
 

@@ -129,8 +129,7 @@ struct WalkArgs {
   int k1;  // Dehnen K1 softening of direct pairs, Newtonian expansions
   int dual;        // cell-group local expansions for well-separated cells
   double theta2;   // theta^2 of the cell-group test (IEEE double, as on the host)
-  const float* mom32;  // FP32 cell-unit moments (kDualStride per cell)
-  int lu;          // the groups' length unit 2^-lu (level of the cell no group straddles)
+  NbDualBufs db;   // where the walk emits its cell-group pairs
   int le;
   int* stack;
   int stack_cap;
@@ -172,14 +171,11 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   __shared__ T s_b0[WARPS][32];  // monopole coefficient of the chunk's largest cells
   // double-float sums of the largest cells' monopole terms, per lane (hi x3, lo x3)
   __shared__ float s_df[WARPS][6][32];
-  // dual form: queue of (cell, R = (z - c*) 2^level, level - lu in .w,
-  // eps^2 4^level), the group's local coefficients (Kahan pairs) and the
+  // dual form: queue of cell-group pairs (cell, image shift code) and the
   // cell-group thresholds per level
-  __shared__ V4 s_loff[WARPS][64];
-  __shared__ int s_lidx[WARPS][64];
-  __shared__ T s_leps[WARPS][64];
-  __shared__ float s_L[WARPS][2][64];
-  __shared__ long long s_tl[WARPS][NB_NLEV];
+  __shared__ int s_lidx[WARPS][DUALK ? 64 : 1];
+  __shared__ int s_limg[WARPS][DUALK ? 64 : 1];
+  __shared__ long long s_tl[WARPS][DUALK ? NB_NLEV : 1];
   __shared__ int s_pfx[WARPS][32];
   __shared__ int s_pst[WARPS][32];
   __shared__ int s_plev[WARPS][32];
@@ -226,10 +222,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     int qn = 0;  // queued M2P cells
     int ln = 0;  // queued cell-group (M2L) cells
     constexpr bool DUAL = DUALK && DF && WDual<P>::has;
+    int lprev = -1;  // this group's last emitted chunk of cell-group pairs
     if constexpr (DUAL) {
       if (w.dual) {
-        s_L[wid][0][lane] = s_L[wid][0][lane + 32] = 0.f;
-        s_L[wid][1][lane] = s_L[wid][1][lane + 32] = 0.f;
         if (lane < NB_NLEV) {
           // (s_C + s_G)^2 / theta^2 with s_G the group box's largest side
           const long long wmax = max(gc.x, max(gc.y, gc.z));
@@ -266,60 +261,27 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         s_df[wid][3 + k][lane] = sl[k];
       }
     };
-    // dual form: lane q forms the local expansion about the group-box centre
-    // of queued cell q (its moments in registers); each coefficient's lane
-    // values go to shared memory, and whenever the buffer holds ROWS of them
-    // lane r sums row r over the lanes and adds it to the group's, compensated
+    // dual form: the first nml queued cell-group pairs become one chunk of
+    // the group's pair list (a separate pass forms their local expansions)
     auto m2l_chunk = [&](int nml) {
       if constexpr (DUAL) {
-        constexpr int NM4 = ((P + 1) * (P + 2) * (P + 3) / 6 + 3) / 4;
-        // rows of lane values per pass through the coefficient buffer: at
-        // most what the buffer holds, and at most 32 (one summing lane each)
-        constexpr int NL = WDual<P>::NL, RB = (32 * NBS) / 33 < 32 ? (32 * NBS) / 33 : 32,
-                      ROWS = RB < NL ? RB : NL;
-        const int q = lane < nml ? lane : 0;
-        const float live = lane < nml ? 1.f : 0.f;
-        float Mr[4 * NM4];
-        {
-          const float4* src = reinterpret_cast<const float4*>(w.mom32 + (int64_t)s_lidx[wid][q] * kDualStride);
-#pragma unroll
-          for (int k = 0; k < NM4; k++) {
-            const float4 v = src[k];
-            Mr[4 * k] = v.x * live;
-            Mr[4 * k + 1] = v.y * live;
-            Mr[4 * k + 2] = v.z * live;
-            Mr[4 * k + 3] = v.w * live;
+        int cidx = 0;
+        if (lane == 0) cidx = atomicAdd(w.db.ctr, 1);
+        cidx = __shfl_sync(FULL, cidx, 0);
+        if (cidx < w.db.cap) {
+          if (lane < nml) {
+            w.db.cell[(int64_t)cidx * 32 + lane] = s_lidx[wid][lane];
+            w.db.img[(int64_t)cidx * 32 + lane] = s_limg[wid][lane];
           }
+          if (lane == 0) {
+            w.db.head[cidx] = make_int4(g, nml, -1, 0);
+            if (lprev < 0) w.db.first[g] = cidx;
+            else w.db.head[lprev].z = cidx;
+          }
+          lprev = cidx;
+        } else if (lane == 0) {
+          atomicOr(w.status, NB_ST_OVERFLOW);  // the pool is too small: the caller grows it
         }
-        const V4 lo = s_loff[wid][q];
-        const float e2 = (float)s_leps[wid][q];
-        // 2^((level - lu)(o + 1)) takes coefficient order o to the group's unit
-        float f[7];
-        f[0] = __int_as_float((127 + (int)lo.w) << 23);  // 2^(level - lu), |level - lu| < 24
-        f[1] = f[0] * f[0];
-#pragma unroll
-        for (int o = 2; o < 7; o++) f[o] = f[o - 1] * f[0];
-        float* buf = reinterpret_cast<float*>(&s_coef[wid][0]);  // rows of 33: no bank conflicts
-        auto flush = [&](int t0, int rows) {
-          __syncwarp();
-          if (lane < rows) {
-            float sacc = 0.f, scmp = 0.f;
-            for (int j = 0; j < 32; j++) kadd(sacc, scmp, buf[lane * 33 + j]);
-            float sh = s_L[wid][0][t0 + lane], sc = s_L[wid][1][t0 + lane];
-            kadd(sh, sc, sacc - scmp);
-            s_L[wid][0][t0 + lane] = sh;
-            s_L[wid][1][t0 + lane] = sc;
-          }
-          __syncwarp();
-        };
-        struct RegMoments {
-          const float* m;
-          __device__ __forceinline__ float operator[](int u) const { return m[u]; }
-        };
-        WDual<P>::m2l(RegMoments{Mr}, (float)lo.x, (float)lo.y, (float)lo.z, e2, [&](int t, int o, float v) {
-          buf[(t % ROWS) * 33 + lane] = v * f[o];
-          if (t % ROWS == ROWS - 1 || t == NL - 1) flush(t - t % ROWS, t % ROWS + 1);
-        });
         n_m2l += nml;
       }
     };
@@ -514,15 +476,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           if (cls == NB_CELL_M2L) {
             const int pos = ln + __popc(lm & ltmask);
             s_lidx[wid][pos] = c;
-            // R = (z - c*) 2^level, z the group-box centre (exact scalings)
-            const T sc = (T)(1 << lvl);
-            V4 lo;
-            lo.x = ((T)(gb.x - (ca.x - kx * NB_PBOX)) * scale) * sc;
-            lo.y = ((T)(gb.y - (ca.y - ky * NB_PBOX)) * scale) * sc;
-            lo.z = ((T)(gb.z - (ca.z - kz * NB_PBOX)) * scale) * sc;
-            lo.w = (T)(lvl - w.lu);  // log2 of the group unit over the cell's
-            s_loff[wid][pos] = lo;
-            s_leps[wid][pos] = w.k1 ? (T)0 : eps2 * (sc * sc);
+            s_limg[wid][pos] = (kx + 1) | ((ky + 1) << 2) | ((kz + 1) << 4);
           }
           ln += __popc(lm);
           __syncwarp();
@@ -634,7 +588,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
                 kadd(az, cz, pz.x + pz.y);
               }
             } else if (act) {
-              T px = 0, py = 0, pz = 0, pp = 0;
+              T px = 0, py = 0, pz = 0;
+              [[maybe_unused]] T pp = 0;
               for (int k = 0; k < nn; k++) {
                 const V4 s = s_src[wid][k];
                 const T dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
@@ -699,8 +654,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           m2l_chunk(k);
           if (lane < ln - k) {
             s_lidx[wid][lane] = s_lidx[wid][32 + lane];
-            s_loff[wid][lane] = s_loff[wid][32 + lane];
-            s_leps[wid][lane] = s_leps[wid][32 + lane];
+            s_limg[wid][lane] = s_limg[wid][32 + lane];
           }
           ln -= k;
           __syncwarp();
@@ -711,32 +665,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     if (overflow) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
-    }
-    if constexpr (DUAL) {
-      if (w.dual) {
-        const bool any = __any_sync(FULL, n_m2l > 0);
-        if (any) {
-          // the group's local expansion at every sink: d = (x - z) in the
-          // group's unit 2^-lu; the coefficients were built from -d g, which
-          // the image-field L2P turns back (it subtracts)
-          float* Lf = reinterpret_cast<float*>(&s_coef[wid][0]);
-          Lf[lane] = s_L[wid][0][lane] - s_L[wid][1][lane];
-          if (lane + 32 < WDual<P>::NL) Lf[lane + 32] = s_L[wid][0][lane + 32] - s_L[wid][1][lane + 32];
-          __syncwarp();
-          if (act) {
-            const float u = (float)(1 << w.lu);
-            const float dxp = (xi - (T)(gb.x - gd.x) * scale) * u;
-            const float dyp = (yi - (T)(gb.y - gd.y) * scale) * u;
-            const float dzp = (zi - (T)(gb.z - gd.z) * scale) * u;
-            float bx = 0.f, by = 0.f, bz = 0.f;
-            WDual<P>::l2p(Lf, dxp, dyp, dzp, bx, by, bz);
-            kadd(ax, cx, bx * (u * u));
-            kadd(ay, cy, by * (u * u));
-            kadd(az, cz, bz * (u * u));
-          }
-          __syncwarp();
-        }
-      }
     }
     if (act && (!tr.sact || tr.sact[i])) {
       if constexpr (DF) {
@@ -767,6 +695,148 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   }
 }
 
+// ---- the dual form's cell-group expansions ----------------------------------------
+struct DualArgs {
+  DevTree tr;
+  NbDualBufs db;
+  const float* mom32;  // FP32 cell-unit moments (kDualStride per cell)
+  const float* eps2;   // per box
+  int k1;
+  int lu;              // the groups' length unit 2^-lu (level of the cell no group straddles)
+  float* acc;          // 3n, key order (the walk's accelerations; the expansions are added)
+};
+
+// One warp per chunk of cell-group pairs, lane per pair: the cell's local
+// expansion about the group-box centre z at R = (z - c*) 2^level (its unit;
+// derivatives by the Cartesian recurrence), each coefficient taken to the
+// group's unit (x 2^((level - lu)(|k| + 1))) and written to shared memory;
+// whenever 32 coefficients are buffered, lane r sums coefficient r over the
+// lanes (compensated) and stores the chunk's sum.
+template <int P>
+__global__ void __launch_bounds__(256) dual_m2l_kernel(DualArgs a) {
+  constexpr int NL = WDual<P>::NL;
+  constexpr int NM4 = ((P + 1) * (P + 2) * (P + 3) / 6 + 3) / 4;
+  __shared__ float s_buf[8][32 * 33];  // rows of 33: no bank conflicts
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const DevTree& tr = a.tr;
+  const int nchunk = min(*a.db.ctr, a.db.cap);
+  const float scale = 1.f / 8388608.f;  // 2^-23
+  float* buf = s_buf[wid];
+  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunk; c += (gridDim.x * blockDim.x) >> 5) {
+    const int4 hd = a.db.head[c];
+    const int g = hd.x, nml = hd.y;
+    const int4 gb = tr.gB[g];
+    const int box = tr.gA[g].z;
+    const int q = lane < nml ? lane : 0;
+    const float live = lane < nml ? 1.f : 0.f;
+    const int cell = a.db.cell[(int64_t)c * 32 + q];
+    const int code = a.db.img[(int64_t)c * 32 + q];
+    const int kx = (code & 3) - 1, ky = ((code >> 2) & 3) - 1, kz = ((code >> 4) & 3) - 1;
+    const int4 ca = tr.cA[cell];
+    const int lvl = ca.w & 0xff;
+    const float sc = (float)(1 << lvl);
+    const float rx = ((float)(gb.x - (ca.x - kx * NB_PBOX)) * scale) * sc;
+    const float ry = ((float)(gb.y - (ca.y - ky * NB_PBOX)) * scale) * sc;
+    const float rz = ((float)(gb.z - (ca.z - kz * NB_PBOX)) * scale) * sc;
+    const float e2 = a.k1 ? 0.f : a.eps2[box] * (sc * sc);
+    float Mr[4 * NM4];
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.mom32 + (int64_t)cell * kDualStride);
+#pragma unroll
+      for (int k = 0; k < NM4; k++) {
+        const float4 v = src[k];
+        Mr[4 * k] = v.x * live;
+        Mr[4 * k + 1] = v.y * live;
+        Mr[4 * k + 2] = v.z * live;
+        Mr[4 * k + 3] = v.w * live;
+      }
+    }
+    // 2^((level - lu)(o + 1)) takes coefficient order o to the group's unit
+    float f[7];
+    f[0] = __int_as_float((127 + lvl - a.lu) << 23);  // |level - lu| < 24
+    f[1] = f[0] * f[0];
+#pragma unroll
+    for (int o = 2; o < 7; o++) f[o] = f[o - 1] * f[0];
+    float* Lout = a.db.L + (int64_t)c * kDualLStride;
+    auto flush = [&](int t0, int rows) {
+      __syncwarp();
+      if (lane < rows) {
+        float sacc = 0.f, scmp = 0.f;
+        for (int j = 0; j < 32; j++) kadd(sacc, scmp, buf[lane * 33 + j]);
+        Lout[t0 + lane] = sacc - scmp;
+      }
+      __syncwarp();
+    };
+    struct RegMoments {
+      const float* m;
+      __device__ __forceinline__ float operator[](int u) const { return m[u]; }
+    };
+    WDual<P>::m2l(RegMoments{Mr}, rx, ry, rz, e2, [&](int t, int o, float v) {
+      buf[(t & 31) * 33 + lane] = v * f[o];
+      if ((t & 31) == 31 || t == NL - 1) flush(t & ~31, (t & 31) + 1);
+    });
+  }
+}
+
+// One warp per group with cell-group pairs: lane t sums coefficients t and
+// t + 32 over the group's chunks in list order (compensated), then every
+// sink evaluates the expansion at d = (x - z) 2^lu and adds u^2 times it to
+// its acceleration (the coefficients were built from -d g, which the
+// image-field L2P turns back: it subtracts).
+template <int P>
+__global__ void __launch_bounds__(256) dual_l2p_kernel(DualArgs a) {
+  constexpr int NL = WDual<P>::NL;
+  __shared__ float s_L[8][64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const DevTree& tr = a.tr;
+  const int ngroup = tr.cnt[1];
+  const double scale = 1.0 / 8388608.0;
+  const float u = (float)(1 << a.lu);
+  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+    int c = a.db.first[g];
+    if (c < 0) continue;
+    float h0 = 0.f, c0 = 0.f, h1 = 0.f, c1 = 0.f;
+    int guard = 0;
+    while (c >= 0 && c < a.db.cap && guard++ < (1 << 24)) {
+      const float* Lc = a.db.L + (int64_t)c * kDualLStride;
+      kadd(h0, c0, Lc[lane]);
+      if (lane + 32 < NL) kadd(h1, c1, Lc[lane + 32]);
+      c = a.db.head[c].z;
+    }
+    s_L[wid][lane] = h0 - c0;
+    s_L[wid][lane + 32] = h1 - c1;
+    __syncwarp();
+    const int4 ga = tr.gA[g], gb = tr.gB[g];
+    if (lane < ga.y) {
+      const int64_t i = ga.x + lane;
+      if (!tr.sact || tr.sact[i]) {
+        const float dx = (float)((tr.spos[i] - gb.x * scale)) * u;
+        const float dy = (float)((tr.spos[tr.n + i] - gb.y * scale)) * u;
+        const float dz = (float)((tr.spos[2 * tr.n + i] - gb.z * scale)) * u;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        WDual<P>::l2p(s_L[wid], dx, dy, dz, bx, by, bz);
+        a.acc[i] += bx * (u * u);
+        a.acc[tr.n + i] += by * (u * u);
+        a.acc[2 * tr.n + i] += bz * (u * u);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int P>
+cudaError_t launch_dual(const DualArgs& a, int nsm, cudaStream_t s) {
+  if constexpr (WDual<P>::has) {
+    dual_m2l_kernel<P><<<nsm * 8, 256, 0, s>>>(a);
+    int grid = (int)(((int64_t)a.tr.ngroup * 32 + 255) / 256);
+    if (grid > nsm * 16) grid = nsm * 16;
+    if (grid < 1) grid = 1;
+    dual_l2p_kernel<P><<<grid, 256, 0, s>>>(a);
+    nb_launch_counter += 2;
+  }
+  return cudaGetLastError();
+}
+
 template <typename T, int P, int WARPS, int MINB, bool PK, bool DUALK, bool POTK = false>
 cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
   // resident blocks per SM, queried once per variant (and so never while a
@@ -789,8 +859,8 @@ cudaError_t launch_walk(const WalkArgs<T>& a, int nsm, int max_blocks, cudaStrea
 
 // launch variants (warps per block, minimum resident blocks per SM, M2P
 // form): 16 warps per SM in blocks of 8 or 4, so every variant has 128
-// registers per thread (none spills); with the dual form three variants at
-// 16 warps per SM (a few dozen bytes spilled) and one at 12.
+// registers per thread (none spills); the same shapes with the dual form,
+// whose walk only queues the cell-group pairs.
 // The stack is sized for 8 warps per block.
 template <typename T, int P>
 cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks, cudaStream_t s) {
@@ -804,11 +874,10 @@ cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks,
   } else {
     if constexpr (WDual<P>::has) {
       if (a.dual) {
-        // the cell-group expansions want more registers: 16 warps per SM
-        // with a few spilled (128 registers), or 12 without
+        // the cell-group pairs are only queued here: the same shapes as below
         switch (v) {
           case 0: return launch_walk<T, P, 8, 2, false, true>(a, nsm, max_blocks, s);
-          case 1: return launch_walk<T, P, 4, 3, true, true>(a, nsm, max_blocks, s);
+          case 1: return launch_walk<T, P, 4, 4, false, true>(a, nsm, max_blocks, s);
           case 2: return launch_walk<T, P, 8, 2, true, true>(a, nsm, max_blocks, s);
           default: return launch_walk<T, P, 4, 4, true, true>(a, nsm, max_blocks, s);
         }
@@ -823,6 +892,15 @@ cudaError_t launch_variant(int v, const WalkArgs<T>& a, int nsm, int max_blocks,
   }
 }
 constexpr int kVariants = 4;
+
+// an empty pair list for every group before a walk of the dual form
+template <typename T>
+cudaError_t reset_dual(const WalkArgs<T>& a, cudaStream_t s) {
+  if (!a.dual || !a.db.ctr) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.db.ctr, 0, sizeof(int), s);
+  if (e) return e;
+  return cudaMemsetAsync(a.db.first, 0xff, sizeof(int) * (size_t)a.tr.ngroup, s);
+}
 
 struct TuneEntry {
   int device, order, fp64, variant;
@@ -861,6 +939,7 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
   for (int v = 0; v < kVariants; v++) {
     if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
     if ((e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), s))) return e;
+    if ((e = reset_dual(a, s))) return e;
     cudaEventRecord(e0, s);
     if ((e = launch_variant<T, P>(v, a, nsm, max_blocks, s))) return e;
     cudaEventRecord(e1, s);
@@ -880,7 +959,21 @@ cudaError_t run_walk(const WalkArgs<T>& a, int nsm, int max_blocks, int forced, 
   }
   if ((e = cudaMemsetAsync(a.group_ctr, 0, sizeof(int), s))) return e;
   if ((e = cudaMemsetAsync(a.counters, 0, 4 * sizeof(unsigned long long), s))) return e;
+  if ((e = reset_dual(a, s))) return e;
   return launch_variant<T, P>(bv, a, nsm, max_blocks, s);
+}
+
+// after a walk of the dual form: the cell-group expansions and their L2P
+template <typename T, int P>
+cudaError_t finish_dual(const WalkArgs<T>& a, const float* mom32, const void* eps2, int k1, int lu, int nsm,
+                        cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (a.dual && !a.pot) {
+      DualArgs d{a.tr, a.db, mom32, (const float*)eps2, k1, lu, a.acc};
+      return launch_dual<P>(d, nsm, s);
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -909,9 +1002,10 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
                     unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
                     int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
-                    void* pot, cudaStream_t s) {
+                    const NbDualBufs* db, void* pot, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
+  if (dual && !pot && !db) return cudaErrorInvalidValue;
 #define NB_WALK(TT, P)                                                             \
   {                                                                                \
     WalkArgs<TT> a;                                                                \
@@ -926,8 +1020,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.k1 = k1;                                                                     \
     a.dual = dual;                                                                 \
     a.theta2 = theta * theta;                                                      \
-    a.mom32 = mom32;                                                               \
-    a.lu = lu;                                                                     \
+    a.db = db ? *db : NbDualBufs{};                                                \
     a.le = le;                                                                     \
     a.stack = stack;                                                               \
     a.stack_cap = stack_cap;                                                       \
@@ -937,7 +1030,9 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     if (pot) a.dual = 0;                                                           \
     a.counters = counters;                                                         \
     a.status = status;                                                             \
-    return run_walk<TT, P>(a, nsm, max_blocks, forced_variant, s);                 \
+    if ((e = reset_dual(a, s))) return e;                                          \
+    if ((e = run_walk<TT, P>(a, nsm, max_blocks, forced_variant, s))) return e;    \
+    return finish_dual<TT, P>(a, mom32, eps2, k1, lu, nsm, s);                     \
   }
   if (fp64) {
     switch (order) {

@@ -558,3 +558,29 @@ def test_dual_form_vs_oracle_tree(cuda, order, variant):
     assert ost["m2l"] > 0 and st["m2p"] == ost["m2p"], (st["m2p"], ost["m2p"], ost["m2l"])
     plain = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.5, order, n_direct=4, ewald=4))
     assert np.median(_rel(plain, ref)) <= 2e-3
+
+
+def test_dual_pair_pool_grows(cuda):
+    """The dual form's cell-group pairs go to a pool sized for 1024 pairs per
+    group; at theta 0.3 a clustered box asks for about 1250, so the first
+    synchronous evaluation outgrows it, is redone with a pool of the size
+    asked for, and still equals the oracle's dual form.  With the deferred
+    status read the overflow is reported by nbody_check instead, and the
+    next evaluation fits."""
+    import torch
+    nb = _nb()
+    x, eps = ics.config_haloes(32, seed=2, n_halo=8, nmin=200, nmax=3000)
+    tg = ics.random_targets(len(x), 512, 12)
+    ref = oracle.tree_forces(x, None, oracle.tree_params(eps, 0.3, 4, n_direct=4, ewald=4, dual=1), targets=tg)
+    a, _ = _gpu_forces(x, cuda, eps=eps, theta=0.3, order=4, n_direct=4, flags=nb.NBODY_FLAG_DUAL)
+    rel = _rel(a[tg], ref)
+    assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (np.median(rel), np.percentile(rel, 99))
+    tree = nb.Tree(nb.params(eps=eps, theta=0.3, order=4, n_direct=4,
+                             flags=nb.NBODY_FLAG_DUAL | nb.NBODY_FLAG_ASYNC), _pos(x, cuda))
+    acc = tree.forces()
+    assert nb.nbody_check(tree.handle, nb._stream()) == nb.NBODY_EOVERFLOW
+    acc = tree.forces()
+    assert nb.nbody_check(tree.handle, nb._stream()) == nb.NBODY_OK
+    rel = _rel(acc.cpu().numpy().T.astype(np.float64)[tg], ref)
+    tree.close()
+    assert np.median(rel) <= 1e-5 and np.percentile(rel, 99) <= 1e-4, (np.median(rel), np.percentile(rel, 99))
