@@ -59,7 +59,7 @@ class TreeParams(C.Structure):
                 ("n_leaf", C.c_int), ("n_group", C.c_int), ("n_direct", C.c_int),
                 ("lmax", C.c_int), ("ewald", C.c_int), ("ew_level", C.c_int),
                 ("ew_grid", C.c_int), ("mac", C.c_int), ("bg", C.c_int), ("kernel", C.c_int),
-                ("dual", C.c_int)]
+                ("dual", C.c_int), ("replicas", C.c_int)]
 
 
 class EwaldCfg(C.Structure):
@@ -118,6 +118,7 @@ def _lib():
             L.or_m2p_pot_orders.restype = C.c_double
             L.or_cube_moments.argtypes = [C.c_double, C.c_double, C.c_int, _dp]
             L.or_m2l.argtypes = [_dp, C.c_int, _dp, C.c_double, _dp]
+            L.or_lattice_tensor.argtypes = [C.c_int, C.c_int, _dp]
             L.or_l2p.argtypes = [_dp, C.c_int, _dp, _dp]
             _LIB = L
     return _LIB
@@ -300,17 +301,19 @@ def direct_vjp(pos, lam, mass=None, eps=0.0, n1: int | None = 64):
 
 
 def tree_params(eps, theta, order, n_leaf=16, n_group=32, n_direct=None, lmax=21, ewald=4,
-                ew_level=3, ew_grid=6, mac=0, bg=0, kernel=0, dual=0) -> TreeParams:
+                ew_level=3, ew_grid=6, mac=0, bg=0, kernel=0, dual=0, replicas=0) -> TreeParams:
     """mac 0: the opening test measures d from the cell centre to the group
     box; mac 1: from the cell's faces (box to box).  bg = q > order adds the
     orders order+1..q of each expanded cell's uniform background share.
     kernel 0: Plummer softening; 1: Dehnen K1 for direct pairs, Newtonian
     cell expansions.  dual 1: well-separated cell-group pairs through a local
-    expansion of the group (or_m2l / or_l2p)."""
+    expansion of the group (or_m2l / or_l2p).  replicas W = 1 or 2 (with
+    ewald 0): periodic images by the (2W+1)^3 near replicas walked
+    explicitly and an order-8 far-lattice expansion about the box centre."""
     if n_direct is None:
         n_direct = 2 if order <= 2 else 4
     return TreeParams(eps, theta, order, n_leaf, n_group, n_direct, lmax, ewald, ew_level,
-                      ew_grid, mac, bg, kernel, dual)
+                      ew_grid, mac, bg, kernel, dual, replicas)
 
 
 def tree_forces(pos, mass=None, params: TreeParams | None = None, targets=None,
@@ -421,6 +424,14 @@ def m2p_orders(M, pmin, pmax, R, eps):
     a = np.zeros(3)
     _lib().or_m2p_orders(_d(M), pmin, pmax, _d(R), eps, _d(a))
     return a
+
+
+def lattice_tensor(P: int = 8, W: int = 2) -> np.ndarray:
+    """d^m Phi_F(0), |m| <= P: the far-lattice potential (the images beyond
+    |n|_inf <= W, with the uniform background)."""
+    T = np.zeros(nmom(P))
+    _lib().or_lattice_tensor(P, W, _d(T))
+    return T
 
 
 def m2p_pot(M, pmin, pmax, R, eps) -> float:

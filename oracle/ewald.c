@@ -46,7 +46,7 @@ static void bseq(double rho, double alpha, int lmax, double *B) {
 /* smooth ladder E_l of erf(a r)/r, E_0 = erf(a r)/r, d_i E_l = -r_i E_{l+1} */
 static void eseq(double r, double alpha, int lmax, double *E) {
   if (alpha * r > 1.0) {
-    double Bv[8];
+    double Bv[16];
     bseq(r, alpha, lmax, Bv);
     double inv2 = 1.0 / (r * r);
     double I = 1.0 / r;
@@ -195,23 +195,23 @@ double or_ewald_pot(const double r[3], const or_ewald_cfg *c) {
   return phi + PI / (alpha * alpha);
 }
 
-/* ---- phi~ derivatives of any order <= 7 ----------------------------------
+/* ---- phi~ derivatives of any order <= 9 ----------------------------------
  * For a radial function with ladder psi_l (d_i psi_l = -r_i psi_{l+1}),
  *   d^m psi = sum_{k <= m/2} prod_d [m_d!/(k_d!(m_d-2k_d)! 2^k_d)] r^(m-2k) (-1)^(|m|-|k|) psi_{|m|-|k|},
  * and d^m cos(2 pi h.r) = (2 pi)^|m| h^m cos(2 pi h.r + |m| pi/2). */
-#define PX 7
+#define PX 9
 static int ml_idx(int nx, int ny, int nz) {
   int o = nx + ny + nz, j = ny + nz;
   return o * (o + 1) * (o + 2) / 6 + j * (j + 1) / 2 + nz;
 }
 static int nmomP(int p) { return (p + 1) * (p + 2) * (p + 3) / 6; }
-static int e_ml[128][3];
+static int e_ml[256][3];
 typedef struct {
   double cf;
   int e[3], j;
 } eterm;
 static eterm e_ht[2048];
-static int e_hb[128], e_he[128];
+static int e_hb[256], e_he[256];
 static double factd(int n) {
   double f = 1.0;
   for (int i = 2; i <= n; i++) f *= i;

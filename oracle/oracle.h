@@ -42,7 +42,7 @@ double or_ewald_pot(const double r[3], const or_ewald_cfg *c);
  * (xxx,xxy,xxz,xyy,xyz,xzz,yyy,yyz,yzz,zzz). */
 void or_phitilde(const double r[3], const or_ewald_cfg *c, double out[20]);
 
-/* All derivatives d^m phi~ with |m| <= P (P <= 7), in multi-index order
+/* All derivatives d^m phi~ with |m| <= P (P <= 9), in multi-index order
  * (order-major; within an order nx descending, then ny descending). */
 void or_phitilde_mi(const double r[3], const or_ewald_cfg *c, int P, double *out);
 /* Exact phi~ derivatives (|m| <= P) at the lattice nodes (i,j,k) 2^-lg with
@@ -133,7 +133,26 @@ typedef struct {
                      M2P's derivative orders), evaluated once per sink,
                      a_k = sum_{|m| <= p} (x - z)^m/m! L_(m + e_k).  Not with
                      bg. */
+  int replicas;   /* W = 1 or 2: periodic images by explicit near replicas
+                     and a far-lattice expansion (needs ewald = 0).  The walk
+                     visits every cell at each of the (2W+1)^3 images n,
+                     |n|_inf <= W, of the box (the acceptance test per image;
+                     cells of any level may be accepted), and the images
+                     beyond them act
+                     through one local expansion of order 8 about the box
+                     centre c0: L_k = sum_n ((-1)^|n|/n!) M_n T_(k+n),
+                     |k| + |n| <= 8, M the box's moments about c0, T the
+                     derivatives at 0 of the far-lattice potential
+                     (or_lattice_tensor); a = -sum_{|u| <= 7} d^u/u!
+                     L_(u + e_k), potential sum_{|k| <= 8} d^k/k! L_k,
+                     d = x - c0. */
 } or_tree_params;
+
+/* T_m = d^m Phi_F(0), |m| <= P (P <= 9): the far-lattice potential
+ * Phi_F(r) = phi~(r) - (2 pi/3)|r|^2 + sum_{0 < |n|_inf <= W} 1/|r - n|,
+ * the periodic potential of a unit mass with the uniform background, less
+ * the near images' -1/|r - n|, |n|_inf <= W (multi-index order) */
+void or_lattice_tensor(int P, int W, double *T);
 
 /* stats[0] = P2P pair interactions, stats[1] = M2P interactions,
  * stats[2] = Ewald (group, cell) terms, stats[3] = cells, stats[4] = groups walked,

@@ -417,11 +417,15 @@ static int64_t quant(double x);
 
 static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc /* 3 x count */,
                      double *Lg /* the group's local expansion (dual) */, double *pot /* nullable */,
-                     wstats *st) {
+                     wstats *st, const int64_t *kfix /* replicas: the image (c - k), else NULL */) {
   const tcell *c = &w->cells[ci];
   const or_tree_params *p = w->p;
   int64_t kimg[3];
-  int consistent = cell_image(w, G, c->level, c->ix, kimg);
+  int consistent = 1;
+  if (kfix)
+    for (int d = 0; d < 3; d++) kimg[d] = kfix[d];
+  else
+    consistent = cell_image(w, G, c->level, c->ix, kimg);
   int64_t d2 = 0;
   for (int d = 0; d < 3; d++) {
     int64_t delta = 2 * centre_u(c->ix[d], c->level) - G->g2[d] - kimg[d] * PBOX;
@@ -432,10 +436,11 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
     if (dd < 0) dd = 0;
     d2 += dd * dd;
   }
-  int accept = consistent && c->level >= 2 && (double)d2 > w->T[c->level];
+  /* levels 0-1 are always opened, except with replicas (any level may be accepted) */
+  int accept = consistent && c->level >= (kfix ? 0 : 2) && (double)d2 > w->T[c->level];
   int leaf = c->nchild == 0;
   if (!accept && !leaf) {
-    for (int k = 0; k < c->nchild; k++) walk_rec(w, G, c->child[k], acc, Lg, pot, st);
+    for (int k = 0; k < c->nchild; k++) walk_rec(w, G, c->child[k], acc, Lg, pot, st, kfix);
     return;
   }
   double cs[3];
@@ -489,12 +494,18 @@ static void walk_rec(const walkctx *w, const tgroup *G, int64_t ci, double *acc 
       st->m2p += 1.0;
     } else {
       for (int64_t j = c->start; j < c->start + c->count; j++) {
-        if (j == i) continue;
-        /* per-particle image from its level-ew_level ancestor */
-        int64_t jx[3] = {quant(w->X[j]) >> (QBITS - le), quant(w->Y[j]) >> (QBITS - le),
-                         quant(w->Z[j]) >> (QBITS - le)};
         int64_t kj[3];
-        for (int d = 0; d < 3; d++) kj[d] = img_shift(2 * centre_u(jx[d], le), G->cell2[d]);
+        if (kfix) {
+          /* replicas: the whole cell at its image; only the sink itself in the central box is skipped */
+          if (j == i && kfix[0] == 0 && kfix[1] == 0 && kfix[2] == 0) continue;
+          for (int d = 0; d < 3; d++) kj[d] = kfix[d];
+        } else {
+          if (j == i) continue;
+          /* per-particle image from its level-ew_level ancestor */
+          int64_t jx[3] = {quant(w->X[j]) >> (QBITS - le), quant(w->Y[j]) >> (QBITS - le),
+                           quant(w->Z[j]) >> (QBITS - le)};
+          for (int d = 0; d < 3; d++) kj[d] = img_shift(2 * centre_u(jx[d], le), G->cell2[d]);
+        }
         double r[3] = {w->X[j] - (double)kj[0] - xi[0], w->Y[j] - (double)kj[1] - xi[1],
                        w->Z[j] - (double)kj[2] - xi[2]};
         double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
@@ -638,6 +649,28 @@ int64_t or_tree_cells(int64_t n, const double *pos, int n_leaf, int lmax, int64_
   return nc;
 }
 
+#define LAT_P 8 /* order of the far-lattice expansion */
+
+void or_lattice_tensor(int P, int W, double *T) {
+  or_ewald_cfg cfg;
+  or_ewald_default(&cfg);
+  double zero[3] = {0.0, 0.0, 0.0}, D[256];
+  int nm = or_nmom(P);
+  or_phitilde_mi(zero, &cfg, P, T);
+  /* the background's -(2 pi/3)|r|^2 */
+  T[mi_idx(2, 0, 0)] -= 4.0 * PI / 3.0;
+  T[mi_idx(0, 2, 0)] -= 4.0 * PI / 3.0;
+  T[mi_idx(0, 0, 2)] -= 4.0 * PI / 3.0;
+  /* the near images' +1/|r - n|, 0 < |n|_inf <= W (derivatives at r = 0: R = -n) */
+  const int S1 = 2 * W + 1;
+  for (int r = 0; r < S1 * S1 * S1; r++) {
+    double R[3] = {-(double)(r % S1 - W), -(double)((r / S1) % S1 - W), -(double)(r / (S1 * S1) - W)};
+    if (R[0] == 0.0 && R[1] == 0.0 && R[2] == 0.0) continue;
+    or_dtensor(R, 0.0, P, D);
+    for (int t = 0; t < nm; t++) T[t] += D[t];
+  }
+}
+
 int or_tree_forces(int64_t n, const double *pos, const double *mass, const or_tree_params *p,
                    const double *tab, int64_t ntarget, const int64_t *targets, double *acc,
                    double *stats) {
@@ -653,7 +686,8 @@ int or_tree_forces_pot(int64_t n, const double *pos, const double *mass, const o
       p->n_group < 1 || p->n_direct > p->n_leaf || p->ewald < 0 || p->ewald > 5 ||
       (p->ewald > 0 && !tab) || p->ew_level < 1 || p->ew_level > 8 ||
       p->ew_grid < p->ew_level + 1 || p->ew_grid > 10 || p->bg < 0 || p->bg > 8 || p->kernel < 0 ||
-      p->kernel > 1 || p->dual < 0 || p->dual > 1 || (p->dual && p->bg > p->order))
+      p->kernel > 1 || p->dual < 0 || p->dual > 1 || (p->dual && p->bg > p->order) || p->replicas < 0 ||
+      p->replicas > 2 || (p->replicas && p->ewald != 0))
     return -1;
   int64_t *perm = malloc(sizeof(int64_t) * n);
   uint64_t *skeys = malloc(sizeof(uint64_t) * n);
@@ -740,6 +774,27 @@ int or_tree_forces_pot(int64_t n, const double *pos, const double *mass, const o
     double s = ldexp(1.0, 23 - l);
     w.T[l] = floor((s * s) / (p->theta * p->theta));
   }
+  /* far lattice (replicas): box moments about c0, the lattice tensor, L */
+  double Lfar[256];
+  for (int t = 0; t < 256; t++) Lfar[t] = 0.0;
+  if (p->replicas) {
+    int nl = or_nmom(LAT_P);
+    double Mb[256], T[256];
+    double c0[3] = {0.5, 0.5, 0.5};
+    or_p2m(n, S, Ms, c0, LAT_P, Mb);
+    or_lattice_tensor(LAT_P, p->replicas, T);
+    for (int t = 0; t < nl; t++) {
+      int k0 = g_ml[t][0], k1 = g_ml[t][1], k2 = g_ml[t][2];
+      int ok = k0 + k1 + k2;
+      for (int u = 0; u < nl; u++) {
+        int n0 = g_ml[u][0], n1 = g_ml[u][1], n2 = g_ml[u][2];
+        int on = n0 + n1 + n2;
+        if (on + ok > LAT_P) continue;
+        double cf = ((on & 1) ? -1.0 : 1.0) / (fact(n0) * fact(n1) * fact(n2));
+        Lfar[t] += cf * Mb[u] * T[mi_idx(n0 + k0, n1 + k1, n2 + k2)];
+      }
+    }
+  }
   /* groups: runs of <= n_group consecutive particles inside one level-ls cell */
   int ls = p->ew_grid - 1;
   int64_t *gstart = malloc(sizeof(int64_t) * (n + 1));
@@ -792,7 +847,16 @@ int or_tree_forces_pot(int64_t n, const double *pos, const double *mass, const o
     wstats st = {0.0, 0.0, 0.0, 0.0};
     double Lg[128];
     for (int t = 0; t < 128; t++) Lg[t] = 0.0;
-    walk_rec(&w, &G, 0, ga, Lg, gp, &st);
+    if (p->replicas) {
+      /* the near replicas |n|_inf <= W, each a walk from the root at image n (k = -n) */
+      const int W = p->replicas, S1 = 2 * W + 1;
+      for (int r = 0; r < S1 * S1 * S1; r++) {
+        int64_t kf[3] = {-(r % S1 - W), -((r / S1) % S1 - W), -(r / (S1 * S1) - W)};
+        walk_rec(&w, &G, 0, ga, Lg, gp, &st, kf);
+      }
+    } else {
+      walk_rec(&w, &G, 0, ga, Lg, gp, &st, NULL);
+    }
     if (p->dual && st.m2l > 0.0)
       for (int64_t s = 0; s < G.count; s++) {
         int64_t i = G.start + s;
@@ -803,6 +867,23 @@ int or_tree_forces_pot(int64_t n, const double *pos, const double *mass, const o
         for (int k = 0; k < 3; k++) ga[k * G.count + s] += a[k];
       }
     if (p->ewald > 0) periodic_group(&w, &G, ga, gp, &st);
+    if (p->replicas) {
+      /* the far lattice: local expansion of order LAT_P about the box centre */
+      for (int64_t s = 0; s < G.count; s++) {
+        int64_t i = G.start + s;
+        double d[3] = {X[i] - 0.5, Y[i] - 0.5, Z[i] - 0.5};
+        double a[3], v = 0.0;
+        or_l2p(Lfar, LAT_P - 1, d, a);
+        for (int k = 0; k < 3; k++) ga[k * G.count + s] -= a[k];
+        if (gp) {
+          for (int t = 0; t < or_nmom(LAT_P); t++) {
+            int m0 = g_ml[t][0], m1 = g_ml[t][1], m2 = g_ml[t][2];
+            v += ipow(d[0], m0) * ipow(d[1], m1) * ipow(d[2], m2) / (fact(m0) * fact(m1) * fact(m2)) * Lfar[t];
+          }
+          gp[s] += v;
+        }
+      }
+    }
     for (int64_t s = 0; s < G.count; s++)
       for (int d = 0; d < 3; d++) sacc[d * n + G.start + s] = ga[d * G.count + s];
     if (gp)
