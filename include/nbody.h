@@ -91,14 +91,29 @@ enum {
    * sink, a_k = sum_{|m| <= order} (x - z)^m / m! L_(m + e_k).  Orders 1..4,
    * NBODY_MIXED, not with NBODY_FLAG_BACKGROUND (else NBODY_ENOTSUP); the
    * reverse mode returns NBODY_ENOTSUP with it. */
-  NBODY_FLAG_DUAL = 16
+  NBODY_FLAG_DUAL = 16,
+  /* periodic images by near replicas and a far-lattice expansion (Sec.
+   * 2.1's periodic boundary conditions: a multipole local expansion of order
+   * p = 8).  The walk visits every cell at each of the 125 images n,
+   * |n|_inf <= 2, of the box (the acceptance test per image; cells of any
+   * level may be accepted), and the images beyond act through one local
+   * expansion about the box centre c0 of order 8: L_k = sum_n ((-1)^|n|/n!)
+   * M_n T_(k+n), |k| + |n| <= 8, with the box's moments M about c0 and T the
+   * derivatives at 0 of the periodic potential of a unit mass with the
+   * uniform background less its near images' -1/|r - n|; every sink adds
+   * a = -sum_{|u| <= 7} d^u/u! L_(u + e_k), d = x - c0.  Against the exact
+   * Ewald sum the far lattice errs by about 3e-7 (median, forces).  Needs
+   * ewald_order = 0 (else NBODY_EINVAL); ewald_grid - 1 is then the level
+   * of the cells no group straddles.  Fewer than 2^25 cells; the reverse
+   * mode returns NBODY_ENOTSUP with it. */
+  NBODY_FLAG_REPLICAS = 32
 };
 /* flags bits 8..11: walk launch variant + 1 to use instead of the autotuned
  * one (0 = autotune).  Mixed precision has variants 0..3 (one M2P per
- * instruction stream with 8 warps x 2 or 3 blocks per SM; two M2P at once in
- * packed FP32 pairs with 8 x 2 or 4 x 5); FP64 has only variant 0.
- * Every variant computes the same interactions; results differ by the
- * summation order only. */
+ * instruction stream with 8 warps x 2 or 4 x 4 blocks per SM; two M2P at
+ * once in packed FP32 pairs, 8 x 2 or 4 x 4; with NBODY_FLAG_DUAL the second
+ * is packed with 4 x 3); FP64 has only variant 0.  Every variant computes
+ * the same interactions; results differ by the summation order only. */
 #define NBODY_FLAG_WALK_VARIANT(v) (((v) + 1) << 8)
 
 typedef struct {

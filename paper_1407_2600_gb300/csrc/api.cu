@@ -57,7 +57,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
                     int* group_ctr, void* acc, unsigned long long* counters, unsigned* status, int nsm,
                     int forced_variant, int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
-                    const NbDualBufs* db, void* pot, cudaStream_t s);
+                    const NbDualBufs* db, void* pot, int repl, cudaStream_t s);
 cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t32, cudaStream_t s);
 int nb_field_stride(int pe);
 struct AdjBuffers {
@@ -78,6 +78,9 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           unsigned* status, int nsm, int mac_edge, int bg, cudaStream_t s);
 cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                            const void* tab, void* lbuf, cudaStream_t s);
+cudaError_t nb_lattice(const DevTree& tr, bool fp64, int W, const void* accw, float* out, double* out64,
+                       const void* potw, float* pout, double* part, double* mom, double* Ld, void* Lt,
+                       cudaStream_t s);
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         double* out64, const void* potw, float* pout, cudaStream_t s);
@@ -159,6 +162,8 @@ struct nbody_tree {
   Buf potw;  // the walk's potential (key order), when one is asked for
   // the dual form's cell-group pair chunks (lc_cap chunks of 32 pairs)
   Buf lc_cell, lc_img, lc_head, lc_first, lc_ctr, lc_L;
+  // the near-replica scheme's far lattice: moment slices, box moments, local expansions
+  Buf lat_part, lat_mom, lat_Ld, lat_Lt;
   int64_t lc_cap = 0;
   bool lc_grew = false;  // the last status read grew the pool
   // reverse mode
@@ -191,7 +196,8 @@ struct nbody_tree {
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho, &act_s, &act_g, &rungc,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
                   &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32, &potw,
-                  &lc_cell, &lc_img, &lc_head, &lc_first, &lc_ctr, &lc_L};
+                  &lc_cell, &lc_img, &lc_head, &lc_first, &lc_ctr, &lc_L, &lat_part, &lat_mom, &lat_Ld,
+                  &lat_Lt};
     for (Buf* b : all) b->release();
     if (pinned) cudaFreeHost(pinned);
     delete aux;
@@ -264,8 +270,13 @@ int validate(const nbody_params* p) {
   if (p->precision != NBODY_MIXED && p->precision != NBODY_FP64) return NBODY_EINVAL;
   if (((p->flags >> 8) & 0xf) > 4) return NBODY_EINVAL;  // walk variant override 0..3
   if (p->flags &
-      ~(NBODY_FLAG_ASYNC | NBODY_FLAG_MAC_EDGE | NBODY_FLAG_BACKGROUND | NBODY_FLAG_K1 | NBODY_FLAG_DUAL | (0xf << 8)))
+      ~(NBODY_FLAG_ASYNC | NBODY_FLAG_MAC_EDGE | NBODY_FLAG_BACKGROUND | NBODY_FLAG_K1 | NBODY_FLAG_DUAL |
+        NBODY_FLAG_REPLICAS | (0xf << 8)))
     return NBODY_EINVAL;  // unknown flag bits
+  if (p->flags & NBODY_FLAG_REPLICAS) {
+    // the near replicas replace the image field; ewald_grid still places the groups
+    if (p->ewald_order != 0 || p->ewald_grid < 2 || p->ewald_grid > 8) return NBODY_EINVAL;
+  }
   if ((p->flags & NBODY_FLAG_DUAL) &&
       (p->order < 1 || p->precision != NBODY_MIXED || (p->flags & NBODY_FLAG_BACKGROUND)))
     return NBODY_ENOTSUP;
@@ -276,7 +287,9 @@ int validate(const nbody_params* p) {
 
 // image level used by the walk even without periodic images
 int image_level(const nbody_params& p) { return p.ewald_order > 0 ? p.ewald_level : 3; }
-int group_level(const nbody_params& p) { return p.ewald_order > 0 ? p.ewald_grid - 1 : 5; }
+int group_level(const nbody_params& p) {
+  return (p.ewald_order > 0 || (p.flags & NBODY_FLAG_REPLICAS)) ? p.ewald_grid - 1 : 5;
+}
 
 __global__ void kick_kernel(int64_t n3, float* __restrict__ mom, const float* __restrict__ acc, float k) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x)
@@ -780,6 +793,15 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
   tr.gact = gact;
   unsigned long long* ctr = t->counters.as<unsigned long long>();
   const bool dual = (p.flags & NBODY_FLAG_DUAL) != 0;
+  const int repl = (p.flags & NBODY_FLAG_REPLICAS) ? 2 : 0;
+  if (repl) {
+    // the walk's stack entries hold the image above 25 bits of cell index
+    if (t->cell_cap >= (1 << 25)) return NBODY_ENOTSUP;
+    NB_CU(t->lat_part.ensure(8 * 512 * 165 * (int64_t)t->nbox));
+    NB_CU(t->lat_mom.ensure(8 * 165 * (int64_t)t->nbox));
+    NB_CU(t->lat_Ld.ensure(8 * 165 * (int64_t)t->nbox));
+    NB_CU(t->lat_Lt.ensure((fp64 ? 8 : 4) * 165 * (int64_t)t->nbox));
+  }
   NbDualBufs db{};
   if (dual) {
     // chunks of 32 cell-group pairs: 32 per group to begin with (1024 pairs;
@@ -808,12 +830,16 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
                   t->status.as<unsigned>(), t->nsm, ((p.flags >> 8) & 0xf) - 1,
                   (p.flags & NBODY_FLAG_MAC_EDGE) ? 1 : 0, (p.flags & NBODY_FLAG_BACKGROUND) ? 1 : 0,
                   (p.flags & NBODY_FLAG_K1) ? 1 : 0, dual ? 1 : 0, p.theta, t->mom32.as<float>(), group_level(p),
-                  dual ? &db : nullptr, pass == 0 ? t->potw.p : nullptr, s));
+                  dual ? &db : nullptr, pass == 0 ? t->potw.p : nullptr, repl, s));
   }
   if (timed) NB_CU(cudaEventRecord(fe[1], s));
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
-  NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
-                    t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, pot ? t->potw.p : nullptr, pot, s));
+  if (repl)
+    NB_CU(nb_lattice(tr, fp64, repl, t->accw.p, acc, acc64, pot ? t->potw.p : nullptr, pot, t->lat_part.as<double>(),
+                     t->lat_mom.as<double>(), t->lat_Ld.as<double>(), t->lat_Lt.p, s));
+  else
+    NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
+                      t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, pot ? t->potw.p : nullptr, pot, s));
   if (timed) NB_CU(cudaEventRecord(fe[2], s));
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());
   nb_launch_counter += 1;
@@ -826,7 +852,8 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
 // out = (d acc / d pos)^T lam for the tree as last built (forces refreshed if needed)
 int vjp_impl(nbody_tree* t, const float* lam, double* out, cudaStream_t s) {
   const nbody_params& p = t->prm;
-  if (p.precision != NBODY_MIXED || p.ewald_order > 4 || (p.flags & (NBODY_FLAG_K1 | NBODY_FLAG_DUAL)))
+  if (p.precision != NBODY_MIXED || p.ewald_order > 4 ||
+      (p.flags & (NBODY_FLAG_K1 | NBODY_FLAG_DUAL | NBODY_FLAG_REPLICAS)))
     return NBODY_ENOTSUP;
   const int64_t n = t->n;
   if (!t->field_valid) {
@@ -1221,7 +1248,7 @@ int kdk_adjoint_impl(nbody_tree* t, const double* pos0, const float* mom0, const
                      cudaStream_t s) {
   if (!t || !pos0 || !mom0 || !lam_pos1 || !lam_mom1 || !lam_pos0 || !lam_mom0 || !(a0 > 0.0) || !(a1 > 0.0))
     return NBODY_EINVAL;
-  if (t->scaled || (t->prm.flags & (NBODY_FLAG_K1 | NBODY_FLAG_DUAL))) return NBODY_ENOTSUP;
+  if (t->scaled || (t->prm.flags & (NBODY_FLAG_K1 | NBODY_FLAG_DUAL | NBODY_FLAG_REPLICAS))) return NBODY_ENOTSUP;
   if (t->prm.precision != NBODY_MIXED || t->prm.ewald_order > 4) return NBODY_ENOTSUP;
   const long long l0 = nb_launch_counter;
   const int64_t n = t->n, n3 = 3 * n;

@@ -178,7 +178,7 @@ struct DevTree {
 // a group's chunks in list order and evaluates the expansion at its sinks.
 struct NbDualBufs {
   int* cell;      // cap x 32 source cells
-  int* img;       // cap x 32 image shifts, (kx + 1) | (ky + 1) << 2 | (kz + 1) << 4
+  int* img;       // cap x 32 image shifts, (kx + 2) | (ky + 2) << 3 | (kz + 2) << 6
   int4* head;     // cap: group, pair count, next chunk of the group (-1), 0
   int* first;     // per group: its first chunk, or -1
   int* ctr;       // chunks asked for (can exceed cap: the overflow is reported)

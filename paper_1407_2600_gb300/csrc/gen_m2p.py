@@ -284,9 +284,10 @@ def emit_reduce(p):
     return "\n".join(L)
 
 
-def emit_m2l(pe):
+def emit_m2l(pe, with_m2l=True):
     """Image-field local expansion about the expansion point e:
-    L_m += sum_n (-1)^|n|/n! M_n d^{m+n} phi~(R0), 1 <= |m| <= pe+1, |m|+|n| <= pe+1."""
+    L_m += sum_n (-1)^|n|/n! M_n d^{m+n} phi~(R0), 1 <= |m| <= pe+1, |m|+|n| <= pe+1
+    (m2l_pe), and its evaluation (l2p_pe); with_m2l False emits the latter only."""
     P = pe + 1
     mP = multi(P)
     mi = {m: i for i, m in enumerate(mP)}
@@ -315,6 +316,8 @@ def emit_m2l(pe):
                 expr = "fma(M[%d] * T(%.17g), D[%d], %s)" % (u, c, k, expr)
         L.append("  Lc[%d] = %s;" % (t - 1, expr))
     L.append("}")
+    if not with_m2l:
+        L = []
     # L2P
     L.append("template <typename T>")
     L.append("__device__ __forceinline__ void l2p_pe%d(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {" % pe)
@@ -698,6 +701,21 @@ def emit_bgpot(l):
     return "\n".join(L)
 
 
+def emit_m2l0(p):
+    """m2l0_p<p>(M, D) = sum_{|n| <= p} (-1)^|n|/n! M_n D_n (the local
+    expansion's constant term from moments to order p)."""
+    me = multi(p)
+    L = ["template <typename T>",
+         "__device__ __forceinline__ T m2l0_p%d(const T* __restrict__ M, const T* __restrict__ D) {" % p,
+         "  T v = T(0);"]
+    for u, n in enumerate(me):
+        c = (-1.0 if sum(n) % 2 else 1.0) / (math.factorial(n[0]) * math.factorial(n[1]) * math.factorial(n[2]))
+        L.append("  v = fma(M[%d] * T(%.17g), D[%d], v);" % (u, c, u))
+    L.append("  return v;")
+    L.append("}")
+    return "\n".join(L)
+
+
 def emit_l2pot(pe):
     """Image-field potential: L_0 = sum_n (-1)^|n|/n! M_n d^n phi~(R0) per
     cell (m2l0_pe), and the series L_0 + sum_{1 <= |m| <= pe+1} d^m/m! L_m
@@ -794,6 +812,15 @@ def generate():
         out.append("")
         out.append(emit_l2pot(pe))
         out.append("")
+    # the far lattice of the near-replica scheme: its evaluation at order 7
+    # (coefficients to order 8) and the constant term from order-8 moments
+    out.append("constexpr int kNL7 = %d;  // far-lattice local coefficients (orders 1..8)" % (len(multi(8)) - 1))
+    out.append(emit_m2l(7, with_m2l=False))
+    out.append("")
+    out.append("\n".join(emit_l2pot(7).split("\n")[emit_l2pot(7).split("\n").index("template <typename T>", 1):]))
+    out.append("")
+    out.append(emit_m2l0(8))
+    out.append("")
     for p in range(1, 5):
         out.append(emit_dtensor(p + 1))
         out.append("")

@@ -2640,6 +2640,476 @@ __device__ __forceinline__ T l2pot_pe5(T L0, const T* __restrict__ Lc, T dx, T d
   return fma(q83, Lc[82], fma(q82, Lc[81], fma(q81, Lc[80], fma(q80, Lc[79], fma(q79, Lc[78], fma(q78, Lc[77], fma(q77, Lc[76], fma(q76, Lc[75], fma(q75, Lc[74], fma(q74, Lc[73], fma(q73, Lc[72], fma(q72, Lc[71], fma(q71, Lc[70], fma(q70, Lc[69], fma(q69, Lc[68], fma(q68, Lc[67], fma(q67, Lc[66], fma(q66, Lc[65], fma(q65, Lc[64], fma(q64, Lc[63], fma(q63, Lc[62], fma(q62, Lc[61], fma(q61, Lc[60], fma(q60, Lc[59], fma(q59, Lc[58], fma(q58, Lc[57], fma(q57, Lc[56], fma(q56, Lc[55], fma(q55, Lc[54], fma(q54, Lc[53], fma(q53, Lc[52], fma(q52, Lc[51], fma(q51, Lc[50], fma(q50, Lc[49], fma(q49, Lc[48], fma(q48, Lc[47], fma(q47, Lc[46], fma(q46, Lc[45], fma(q45, Lc[44], fma(q44, Lc[43], fma(q43, Lc[42], fma(q42, Lc[41], fma(q41, Lc[40], fma(q40, Lc[39], fma(q39, Lc[38], fma(q38, Lc[37], fma(q37, Lc[36], fma(q36, Lc[35], fma(q35, Lc[34], fma(q34, Lc[33], fma(q33, Lc[32], fma(q32, Lc[31], fma(q31, Lc[30], fma(q30, Lc[29], fma(q29, Lc[28], fma(q28, Lc[27], fma(q27, Lc[26], fma(q26, Lc[25], fma(q25, Lc[24], fma(q24, Lc[23], fma(q23, Lc[22], fma(q22, Lc[21], fma(q21, Lc[20], fma(q20, Lc[19], fma(q19, Lc[18], fma(q18, Lc[17], fma(q17, Lc[16], fma(q16, Lc[15], fma(q15, Lc[14], fma(q14, Lc[13], fma(q13, Lc[12], fma(q12, Lc[11], fma(q11, Lc[10], fma(q10, Lc[9], fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0)))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))));
 }
 
+constexpr int kNL7 = 164;  // far-lattice local coefficients (orders 1..8)
+template <typename T>
+__device__ __forceinline__ void l2p_pe7(const T* __restrict__ Lc, T dx, T dy, T dz, T& ax, T& ay, T& az) {
+  // a_k -= sum_{|n|<=7} d^n/n! L_{n+e_k}
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  const T q35 = q20 * (dx * T(0.20000000000000001));
+  const T q36 = q21 * (dx * T(0.25));
+  const T q37 = q22 * (dx * T(0.25));
+  const T q38 = q23 * (dx * T(0.33333333333333331));
+  const T q39 = q24 * (dx * T(0.33333333333333331));
+  const T q40 = q25 * (dx * T(0.33333333333333331));
+  const T q41 = q26 * (dx * T(0.5));
+  const T q42 = q27 * (dx * T(0.5));
+  const T q43 = q28 * (dx * T(0.5));
+  const T q44 = q29 * (dx * T(0.5));
+  const T q45 = q30 * (dx * T(1));
+  const T q46 = q31 * (dx * T(1));
+  const T q47 = q32 * (dx * T(1));
+  const T q48 = q33 * (dx * T(1));
+  const T q49 = q34 * (dx * T(1));
+  const T q50 = q30 * (dy * T(0.20000000000000001));
+  const T q51 = q31 * (dy * T(0.25));
+  const T q52 = q32 * (dy * T(0.33333333333333331));
+  const T q53 = q33 * (dy * T(0.5));
+  const T q54 = q34 * (dy * T(1));
+  const T q55 = q34 * (dz * T(0.20000000000000001));
+  const T q56 = q35 * (dx * T(0.16666666666666666));
+  const T q57 = q36 * (dx * T(0.20000000000000001));
+  const T q58 = q37 * (dx * T(0.20000000000000001));
+  const T q59 = q38 * (dx * T(0.25));
+  const T q60 = q39 * (dx * T(0.25));
+  const T q61 = q40 * (dx * T(0.25));
+  const T q62 = q41 * (dx * T(0.33333333333333331));
+  const T q63 = q42 * (dx * T(0.33333333333333331));
+  const T q64 = q43 * (dx * T(0.33333333333333331));
+  const T q65 = q44 * (dx * T(0.33333333333333331));
+  const T q66 = q45 * (dx * T(0.5));
+  const T q67 = q46 * (dx * T(0.5));
+  const T q68 = q47 * (dx * T(0.5));
+  const T q69 = q48 * (dx * T(0.5));
+  const T q70 = q49 * (dx * T(0.5));
+  const T q71 = q50 * (dx * T(1));
+  const T q72 = q51 * (dx * T(1));
+  const T q73 = q52 * (dx * T(1));
+  const T q74 = q53 * (dx * T(1));
+  const T q75 = q54 * (dx * T(1));
+  const T q76 = q55 * (dx * T(1));
+  const T q77 = q50 * (dy * T(0.16666666666666666));
+  const T q78 = q51 * (dy * T(0.20000000000000001));
+  const T q79 = q52 * (dy * T(0.25));
+  const T q80 = q53 * (dy * T(0.33333333333333331));
+  const T q81 = q54 * (dy * T(0.5));
+  const T q82 = q55 * (dy * T(1));
+  const T q83 = q55 * (dz * T(0.16666666666666666));
+  const T q84 = q56 * (dx * T(0.14285714285714285));
+  const T q85 = q57 * (dx * T(0.16666666666666666));
+  const T q86 = q58 * (dx * T(0.16666666666666666));
+  const T q87 = q59 * (dx * T(0.20000000000000001));
+  const T q88 = q60 * (dx * T(0.20000000000000001));
+  const T q89 = q61 * (dx * T(0.20000000000000001));
+  const T q90 = q62 * (dx * T(0.25));
+  const T q91 = q63 * (dx * T(0.25));
+  const T q92 = q64 * (dx * T(0.25));
+  const T q93 = q65 * (dx * T(0.25));
+  const T q94 = q66 * (dx * T(0.33333333333333331));
+  const T q95 = q67 * (dx * T(0.33333333333333331));
+  const T q96 = q68 * (dx * T(0.33333333333333331));
+  const T q97 = q69 * (dx * T(0.33333333333333331));
+  const T q98 = q70 * (dx * T(0.33333333333333331));
+  const T q99 = q71 * (dx * T(0.5));
+  const T q100 = q72 * (dx * T(0.5));
+  const T q101 = q73 * (dx * T(0.5));
+  const T q102 = q74 * (dx * T(0.5));
+  const T q103 = q75 * (dx * T(0.5));
+  const T q104 = q76 * (dx * T(0.5));
+  const T q105 = q77 * (dx * T(1));
+  const T q106 = q78 * (dx * T(1));
+  const T q107 = q79 * (dx * T(1));
+  const T q108 = q80 * (dx * T(1));
+  const T q109 = q81 * (dx * T(1));
+  const T q110 = q82 * (dx * T(1));
+  const T q111 = q83 * (dx * T(1));
+  const T q112 = q77 * (dy * T(0.14285714285714285));
+  const T q113 = q78 * (dy * T(0.16666666666666666));
+  const T q114 = q79 * (dy * T(0.20000000000000001));
+  const T q115 = q80 * (dy * T(0.25));
+  const T q116 = q81 * (dy * T(0.33333333333333331));
+  const T q117 = q82 * (dy * T(0.5));
+  const T q118 = q83 * (dy * T(1));
+  const T q119 = q83 * (dz * T(0.14285714285714285));
+  ax = fma(-q119, Lc[154], fma(-q118, Lc[153], fma(-q117, Lc[152], fma(-q116, Lc[151], fma(-q115, Lc[150], fma(-q114, Lc[149], fma(-q113, Lc[148], fma(-q112, Lc[147], fma(-q111, Lc[146], fma(-q110, Lc[145], fma(-q109, Lc[144], fma(-q108, Lc[143], fma(-q107, Lc[142], fma(-q106, Lc[141], fma(-q105, Lc[140], fma(-q104, Lc[139], fma(-q103, Lc[138], fma(-q102, Lc[137], fma(-q101, Lc[136], fma(-q100, Lc[135], fma(-q99, Lc[134], fma(-q98, Lc[133], fma(-q97, Lc[132], fma(-q96, Lc[131], fma(-q95, Lc[130], fma(-q94, Lc[129], fma(-q93, Lc[128], fma(-q92, Lc[127], fma(-q91, Lc[126], fma(-q90, Lc[125], fma(-q89, Lc[124], fma(-q88, Lc[123], fma(-q87, Lc[122], fma(-q86, Lc[121], fma(-q85, Lc[120], fma(-q84, Lc[119], fma(-q83, Lc[110], fma(-q82, Lc[109], fma(-q81, Lc[108], fma(-q80, Lc[107], fma(-q79, Lc[106], fma(-q78, Lc[105], fma(-q77, Lc[104], fma(-q76, Lc[103], fma(-q75, Lc[102], fma(-q74, Lc[101], fma(-q73, Lc[100], fma(-q72, Lc[99], fma(-q71, Lc[98], fma(-q70, Lc[97], fma(-q69, Lc[96], fma(-q68, Lc[95], fma(-q67, Lc[94], fma(-q66, Lc[93], fma(-q65, Lc[92], fma(-q64, Lc[91], fma(-q63, Lc[90], fma(-q62, Lc[89], fma(-q61, Lc[88], fma(-q60, Lc[87], fma(-q59, Lc[86], fma(-q58, Lc[85], fma(-q57, Lc[84], fma(-q56, Lc[83], fma(-q55, Lc[75], fma(-q54, Lc[74], fma(-q53, Lc[73], fma(-q52, Lc[72], fma(-q51, Lc[71], fma(-q50, Lc[70], fma(-q49, Lc[69], fma(-q48, Lc[68], fma(-q47, Lc[67], fma(-q46, Lc[66], fma(-q45, Lc[65], fma(-q44, Lc[64], fma(-q43, Lc[63], fma(-q42, Lc[62], fma(-q41, Lc[61], fma(-q40, Lc[60], fma(-q39, Lc[59], fma(-q38, Lc[58], fma(-q37, Lc[57], fma(-q36, Lc[56], fma(-q35, Lc[55], fma(-q34, Lc[48], fma(-q33, Lc[47], fma(-q32, Lc[46], fma(-q31, Lc[45], fma(-q30, Lc[44], fma(-q29, Lc[43], fma(-q28, Lc[42], fma(-q27, Lc[41], fma(-q26, Lc[40], fma(-q25, Lc[39], fma(-q24, Lc[38], fma(-q23, Lc[37], fma(-q22, Lc[36], fma(-q21, Lc[35], fma(-q20, Lc[34], fma(-q19, Lc[28], fma(-q18, Lc[27], fma(-q17, Lc[26], fma(-q16, Lc[25], fma(-q15, Lc[24], fma(-q14, Lc[23], fma(-q13, Lc[22], fma(-q12, Lc[21], fma(-q11, Lc[20], fma(-q10, Lc[19], fma(-q9, Lc[14], fma(-q8, Lc[13], fma(-q7, Lc[12], fma(-q6, Lc[11], fma(-q5, Lc[10], fma(-q4, Lc[9], fma(-q3, Lc[5], fma(-q2, Lc[4], fma(-q1, Lc[3], fma(-q0, Lc[0], ax))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  ay = fma(-q119, Lc[162], fma(-q118, Lc[161], fma(-q117, Lc[160], fma(-q116, Lc[159], fma(-q115, Lc[158], fma(-q114, Lc[157], fma(-q113, Lc[156], fma(-q112, Lc[155], fma(-q111, Lc[153], fma(-q110, Lc[152], fma(-q109, Lc[151], fma(-q108, Lc[150], fma(-q107, Lc[149], fma(-q106, Lc[148], fma(-q105, Lc[147], fma(-q104, Lc[145], fma(-q103, Lc[144], fma(-q102, Lc[143], fma(-q101, Lc[142], fma(-q100, Lc[141], fma(-q99, Lc[140], fma(-q98, Lc[138], fma(-q97, Lc[137], fma(-q96, Lc[136], fma(-q95, Lc[135], fma(-q94, Lc[134], fma(-q93, Lc[132], fma(-q92, Lc[131], fma(-q91, Lc[130], fma(-q90, Lc[129], fma(-q89, Lc[127], fma(-q88, Lc[126], fma(-q87, Lc[125], fma(-q86, Lc[123], fma(-q85, Lc[122], fma(-q84, Lc[120], fma(-q83, Lc[117], fma(-q82, Lc[116], fma(-q81, Lc[115], fma(-q80, Lc[114], fma(-q79, Lc[113], fma(-q78, Lc[112], fma(-q77, Lc[111], fma(-q76, Lc[109], fma(-q75, Lc[108], fma(-q74, Lc[107], fma(-q73, Lc[106], fma(-q72, Lc[105], fma(-q71, Lc[104], fma(-q70, Lc[102], fma(-q69, Lc[101], fma(-q68, Lc[100], fma(-q67, Lc[99], fma(-q66, Lc[98], fma(-q65, Lc[96], fma(-q64, Lc[95], fma(-q63, Lc[94], fma(-q62, Lc[93], fma(-q61, Lc[91], fma(-q60, Lc[90], fma(-q59, Lc[89], fma(-q58, Lc[87], fma(-q57, Lc[86], fma(-q56, Lc[84], fma(-q55, Lc[81], fma(-q54, Lc[80], fma(-q53, Lc[79], fma(-q52, Lc[78], fma(-q51, Lc[77], fma(-q50, Lc[76], fma(-q49, Lc[74], fma(-q48, Lc[73], fma(-q47, Lc[72], fma(-q46, Lc[71], fma(-q45, Lc[70], fma(-q44, Lc[68], fma(-q43, Lc[67], fma(-q42, Lc[66], fma(-q41, Lc[65], fma(-q40, Lc[63], fma(-q39, Lc[62], fma(-q38, Lc[61], fma(-q37, Lc[59], fma(-q36, Lc[58], fma(-q35, Lc[56], fma(-q34, Lc[53], fma(-q33, Lc[52], fma(-q32, Lc[51], fma(-q31, Lc[50], fma(-q30, Lc[49], fma(-q29, Lc[47], fma(-q28, Lc[46], fma(-q27, Lc[45], fma(-q26, Lc[44], fma(-q25, Lc[42], fma(-q24, Lc[41], fma(-q23, Lc[40], fma(-q22, Lc[38], fma(-q21, Lc[37], fma(-q20, Lc[35], fma(-q19, Lc[32], fma(-q18, Lc[31], fma(-q17, Lc[30], fma(-q16, Lc[29], fma(-q15, Lc[27], fma(-q14, Lc[26], fma(-q13, Lc[25], fma(-q12, Lc[23], fma(-q11, Lc[22], fma(-q10, Lc[20], fma(-q9, Lc[17], fma(-q8, Lc[16], fma(-q7, Lc[15], fma(-q6, Lc[13], fma(-q5, Lc[12], fma(-q4, Lc[10], fma(-q3, Lc[7], fma(-q2, Lc[6], fma(-q1, Lc[4], fma(-q0, Lc[1], ay))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+  az = fma(-q119, Lc[163], fma(-q118, Lc[162], fma(-q117, Lc[161], fma(-q116, Lc[160], fma(-q115, Lc[159], fma(-q114, Lc[158], fma(-q113, Lc[157], fma(-q112, Lc[156], fma(-q111, Lc[154], fma(-q110, Lc[153], fma(-q109, Lc[152], fma(-q108, Lc[151], fma(-q107, Lc[150], fma(-q106, Lc[149], fma(-q105, Lc[148], fma(-q104, Lc[146], fma(-q103, Lc[145], fma(-q102, Lc[144], fma(-q101, Lc[143], fma(-q100, Lc[142], fma(-q99, Lc[141], fma(-q98, Lc[139], fma(-q97, Lc[138], fma(-q96, Lc[137], fma(-q95, Lc[136], fma(-q94, Lc[135], fma(-q93, Lc[133], fma(-q92, Lc[132], fma(-q91, Lc[131], fma(-q90, Lc[130], fma(-q89, Lc[128], fma(-q88, Lc[127], fma(-q87, Lc[126], fma(-q86, Lc[124], fma(-q85, Lc[123], fma(-q84, Lc[121], fma(-q83, Lc[118], fma(-q82, Lc[117], fma(-q81, Lc[116], fma(-q80, Lc[115], fma(-q79, Lc[114], fma(-q78, Lc[113], fma(-q77, Lc[112], fma(-q76, Lc[110], fma(-q75, Lc[109], fma(-q74, Lc[108], fma(-q73, Lc[107], fma(-q72, Lc[106], fma(-q71, Lc[105], fma(-q70, Lc[103], fma(-q69, Lc[102], fma(-q68, Lc[101], fma(-q67, Lc[100], fma(-q66, Lc[99], fma(-q65, Lc[97], fma(-q64, Lc[96], fma(-q63, Lc[95], fma(-q62, Lc[94], fma(-q61, Lc[92], fma(-q60, Lc[91], fma(-q59, Lc[90], fma(-q58, Lc[88], fma(-q57, Lc[87], fma(-q56, Lc[85], fma(-q55, Lc[82], fma(-q54, Lc[81], fma(-q53, Lc[80], fma(-q52, Lc[79], fma(-q51, Lc[78], fma(-q50, Lc[77], fma(-q49, Lc[75], fma(-q48, Lc[74], fma(-q47, Lc[73], fma(-q46, Lc[72], fma(-q45, Lc[71], fma(-q44, Lc[69], fma(-q43, Lc[68], fma(-q42, Lc[67], fma(-q41, Lc[66], fma(-q40, Lc[64], fma(-q39, Lc[63], fma(-q38, Lc[62], fma(-q37, Lc[60], fma(-q36, Lc[59], fma(-q35, Lc[57], fma(-q34, Lc[54], fma(-q33, Lc[53], fma(-q32, Lc[52], fma(-q31, Lc[51], fma(-q30, Lc[50], fma(-q29, Lc[48], fma(-q28, Lc[47], fma(-q27, Lc[46], fma(-q26, Lc[45], fma(-q25, Lc[43], fma(-q24, Lc[42], fma(-q23, Lc[41], fma(-q22, Lc[39], fma(-q21, Lc[38], fma(-q20, Lc[36], fma(-q19, Lc[33], fma(-q18, Lc[32], fma(-q17, Lc[31], fma(-q16, Lc[30], fma(-q15, Lc[28], fma(-q14, Lc[27], fma(-q13, Lc[26], fma(-q12, Lc[24], fma(-q11, Lc[23], fma(-q10, Lc[21], fma(-q9, Lc[18], fma(-q8, Lc[17], fma(-q7, Lc[16], fma(-q6, Lc[14], fma(-q5, Lc[13], fma(-q4, Lc[11], fma(-q3, Lc[8], fma(-q2, Lc[7], fma(-q1, Lc[5], fma(-q0, Lc[2], az))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+}
+
+template <typename T>
+__device__ __forceinline__ T l2pot_pe7(T L0, const T* __restrict__ Lc, T dx, T dy, T dz) {
+  const T q0 = T(1);
+  const T q1 = q0 * (dx * T(1));
+  const T q2 = q0 * (dy * T(1));
+  const T q3 = q0 * (dz * T(1));
+  const T q4 = q1 * (dx * T(0.5));
+  const T q5 = q2 * (dx * T(1));
+  const T q6 = q3 * (dx * T(1));
+  const T q7 = q2 * (dy * T(0.5));
+  const T q8 = q3 * (dy * T(1));
+  const T q9 = q3 * (dz * T(0.5));
+  const T q10 = q4 * (dx * T(0.33333333333333331));
+  const T q11 = q5 * (dx * T(0.5));
+  const T q12 = q6 * (dx * T(0.5));
+  const T q13 = q7 * (dx * T(1));
+  const T q14 = q8 * (dx * T(1));
+  const T q15 = q9 * (dx * T(1));
+  const T q16 = q7 * (dy * T(0.33333333333333331));
+  const T q17 = q8 * (dy * T(0.5));
+  const T q18 = q9 * (dy * T(1));
+  const T q19 = q9 * (dz * T(0.33333333333333331));
+  const T q20 = q10 * (dx * T(0.25));
+  const T q21 = q11 * (dx * T(0.33333333333333331));
+  const T q22 = q12 * (dx * T(0.33333333333333331));
+  const T q23 = q13 * (dx * T(0.5));
+  const T q24 = q14 * (dx * T(0.5));
+  const T q25 = q15 * (dx * T(0.5));
+  const T q26 = q16 * (dx * T(1));
+  const T q27 = q17 * (dx * T(1));
+  const T q28 = q18 * (dx * T(1));
+  const T q29 = q19 * (dx * T(1));
+  const T q30 = q16 * (dy * T(0.25));
+  const T q31 = q17 * (dy * T(0.33333333333333331));
+  const T q32 = q18 * (dy * T(0.5));
+  const T q33 = q19 * (dy * T(1));
+  const T q34 = q19 * (dz * T(0.25));
+  const T q35 = q20 * (dx * T(0.20000000000000001));
+  const T q36 = q21 * (dx * T(0.25));
+  const T q37 = q22 * (dx * T(0.25));
+  const T q38 = q23 * (dx * T(0.33333333333333331));
+  const T q39 = q24 * (dx * T(0.33333333333333331));
+  const T q40 = q25 * (dx * T(0.33333333333333331));
+  const T q41 = q26 * (dx * T(0.5));
+  const T q42 = q27 * (dx * T(0.5));
+  const T q43 = q28 * (dx * T(0.5));
+  const T q44 = q29 * (dx * T(0.5));
+  const T q45 = q30 * (dx * T(1));
+  const T q46 = q31 * (dx * T(1));
+  const T q47 = q32 * (dx * T(1));
+  const T q48 = q33 * (dx * T(1));
+  const T q49 = q34 * (dx * T(1));
+  const T q50 = q30 * (dy * T(0.20000000000000001));
+  const T q51 = q31 * (dy * T(0.25));
+  const T q52 = q32 * (dy * T(0.33333333333333331));
+  const T q53 = q33 * (dy * T(0.5));
+  const T q54 = q34 * (dy * T(1));
+  const T q55 = q34 * (dz * T(0.20000000000000001));
+  const T q56 = q35 * (dx * T(0.16666666666666666));
+  const T q57 = q36 * (dx * T(0.20000000000000001));
+  const T q58 = q37 * (dx * T(0.20000000000000001));
+  const T q59 = q38 * (dx * T(0.25));
+  const T q60 = q39 * (dx * T(0.25));
+  const T q61 = q40 * (dx * T(0.25));
+  const T q62 = q41 * (dx * T(0.33333333333333331));
+  const T q63 = q42 * (dx * T(0.33333333333333331));
+  const T q64 = q43 * (dx * T(0.33333333333333331));
+  const T q65 = q44 * (dx * T(0.33333333333333331));
+  const T q66 = q45 * (dx * T(0.5));
+  const T q67 = q46 * (dx * T(0.5));
+  const T q68 = q47 * (dx * T(0.5));
+  const T q69 = q48 * (dx * T(0.5));
+  const T q70 = q49 * (dx * T(0.5));
+  const T q71 = q50 * (dx * T(1));
+  const T q72 = q51 * (dx * T(1));
+  const T q73 = q52 * (dx * T(1));
+  const T q74 = q53 * (dx * T(1));
+  const T q75 = q54 * (dx * T(1));
+  const T q76 = q55 * (dx * T(1));
+  const T q77 = q50 * (dy * T(0.16666666666666666));
+  const T q78 = q51 * (dy * T(0.20000000000000001));
+  const T q79 = q52 * (dy * T(0.25));
+  const T q80 = q53 * (dy * T(0.33333333333333331));
+  const T q81 = q54 * (dy * T(0.5));
+  const T q82 = q55 * (dy * T(1));
+  const T q83 = q55 * (dz * T(0.16666666666666666));
+  const T q84 = q56 * (dx * T(0.14285714285714285));
+  const T q85 = q57 * (dx * T(0.16666666666666666));
+  const T q86 = q58 * (dx * T(0.16666666666666666));
+  const T q87 = q59 * (dx * T(0.20000000000000001));
+  const T q88 = q60 * (dx * T(0.20000000000000001));
+  const T q89 = q61 * (dx * T(0.20000000000000001));
+  const T q90 = q62 * (dx * T(0.25));
+  const T q91 = q63 * (dx * T(0.25));
+  const T q92 = q64 * (dx * T(0.25));
+  const T q93 = q65 * (dx * T(0.25));
+  const T q94 = q66 * (dx * T(0.33333333333333331));
+  const T q95 = q67 * (dx * T(0.33333333333333331));
+  const T q96 = q68 * (dx * T(0.33333333333333331));
+  const T q97 = q69 * (dx * T(0.33333333333333331));
+  const T q98 = q70 * (dx * T(0.33333333333333331));
+  const T q99 = q71 * (dx * T(0.5));
+  const T q100 = q72 * (dx * T(0.5));
+  const T q101 = q73 * (dx * T(0.5));
+  const T q102 = q74 * (dx * T(0.5));
+  const T q103 = q75 * (dx * T(0.5));
+  const T q104 = q76 * (dx * T(0.5));
+  const T q105 = q77 * (dx * T(1));
+  const T q106 = q78 * (dx * T(1));
+  const T q107 = q79 * (dx * T(1));
+  const T q108 = q80 * (dx * T(1));
+  const T q109 = q81 * (dx * T(1));
+  const T q110 = q82 * (dx * T(1));
+  const T q111 = q83 * (dx * T(1));
+  const T q112 = q77 * (dy * T(0.14285714285714285));
+  const T q113 = q78 * (dy * T(0.16666666666666666));
+  const T q114 = q79 * (dy * T(0.20000000000000001));
+  const T q115 = q80 * (dy * T(0.25));
+  const T q116 = q81 * (dy * T(0.33333333333333331));
+  const T q117 = q82 * (dy * T(0.5));
+  const T q118 = q83 * (dy * T(1));
+  const T q119 = q83 * (dz * T(0.14285714285714285));
+  const T q120 = q84 * (dx * T(0.125));
+  const T q121 = q85 * (dx * T(0.14285714285714285));
+  const T q122 = q86 * (dx * T(0.14285714285714285));
+  const T q123 = q87 * (dx * T(0.16666666666666666));
+  const T q124 = q88 * (dx * T(0.16666666666666666));
+  const T q125 = q89 * (dx * T(0.16666666666666666));
+  const T q126 = q90 * (dx * T(0.20000000000000001));
+  const T q127 = q91 * (dx * T(0.20000000000000001));
+  const T q128 = q92 * (dx * T(0.20000000000000001));
+  const T q129 = q93 * (dx * T(0.20000000000000001));
+  const T q130 = q94 * (dx * T(0.25));
+  const T q131 = q95 * (dx * T(0.25));
+  const T q132 = q96 * (dx * T(0.25));
+  const T q133 = q97 * (dx * T(0.25));
+  const T q134 = q98 * (dx * T(0.25));
+  const T q135 = q99 * (dx * T(0.33333333333333331));
+  const T q136 = q100 * (dx * T(0.33333333333333331));
+  const T q137 = q101 * (dx * T(0.33333333333333331));
+  const T q138 = q102 * (dx * T(0.33333333333333331));
+  const T q139 = q103 * (dx * T(0.33333333333333331));
+  const T q140 = q104 * (dx * T(0.33333333333333331));
+  const T q141 = q105 * (dx * T(0.5));
+  const T q142 = q106 * (dx * T(0.5));
+  const T q143 = q107 * (dx * T(0.5));
+  const T q144 = q108 * (dx * T(0.5));
+  const T q145 = q109 * (dx * T(0.5));
+  const T q146 = q110 * (dx * T(0.5));
+  const T q147 = q111 * (dx * T(0.5));
+  const T q148 = q112 * (dx * T(1));
+  const T q149 = q113 * (dx * T(1));
+  const T q150 = q114 * (dx * T(1));
+  const T q151 = q115 * (dx * T(1));
+  const T q152 = q116 * (dx * T(1));
+  const T q153 = q117 * (dx * T(1));
+  const T q154 = q118 * (dx * T(1));
+  const T q155 = q119 * (dx * T(1));
+  const T q156 = q112 * (dy * T(0.125));
+  const T q157 = q113 * (dy * T(0.14285714285714285));
+  const T q158 = q114 * (dy * T(0.16666666666666666));
+  const T q159 = q115 * (dy * T(0.20000000000000001));
+  const T q160 = q116 * (dy * T(0.25));
+  const T q161 = q117 * (dy * T(0.33333333333333331));
+  const T q162 = q118 * (dy * T(0.5));
+  const T q163 = q119 * (dy * T(1));
+  const T q164 = q119 * (dz * T(0.125));
+  return fma(q164, Lc[163], fma(q163, Lc[162], fma(q162, Lc[161], fma(q161, Lc[160], fma(q160, Lc[159], fma(q159, Lc[158], fma(q158, Lc[157], fma(q157, Lc[156], fma(q156, Lc[155], fma(q155, Lc[154], fma(q154, Lc[153], fma(q153, Lc[152], fma(q152, Lc[151], fma(q151, Lc[150], fma(q150, Lc[149], fma(q149, Lc[148], fma(q148, Lc[147], fma(q147, Lc[146], fma(q146, Lc[145], fma(q145, Lc[144], fma(q144, Lc[143], fma(q143, Lc[142], fma(q142, Lc[141], fma(q141, Lc[140], fma(q140, Lc[139], fma(q139, Lc[138], fma(q138, Lc[137], fma(q137, Lc[136], fma(q136, Lc[135], fma(q135, Lc[134], fma(q134, Lc[133], fma(q133, Lc[132], fma(q132, Lc[131], fma(q131, Lc[130], fma(q130, Lc[129], fma(q129, Lc[128], fma(q128, Lc[127], fma(q127, Lc[126], fma(q126, Lc[125], fma(q125, Lc[124], fma(q124, Lc[123], fma(q123, Lc[122], fma(q122, Lc[121], fma(q121, Lc[120], fma(q120, Lc[119], fma(q119, Lc[118], fma(q118, Lc[117], fma(q117, Lc[116], fma(q116, Lc[115], fma(q115, Lc[114], fma(q114, Lc[113], fma(q113, Lc[112], fma(q112, Lc[111], fma(q111, Lc[110], fma(q110, Lc[109], fma(q109, Lc[108], fma(q108, Lc[107], fma(q107, Lc[106], fma(q106, Lc[105], fma(q105, Lc[104], fma(q104, Lc[103], fma(q103, Lc[102], fma(q102, Lc[101], fma(q101, Lc[100], fma(q100, Lc[99], fma(q99, Lc[98], fma(q98, Lc[97], fma(q97, Lc[96], fma(q96, Lc[95], fma(q95, Lc[94], fma(q94, Lc[93], fma(q93, Lc[92], fma(q92, Lc[91], fma(q91, Lc[90], fma(q90, Lc[89], fma(q89, Lc[88], fma(q88, Lc[87], fma(q87, Lc[86], fma(q86, Lc[85], fma(q85, Lc[84], fma(q84, Lc[83], fma(q83, Lc[82], fma(q82, Lc[81], fma(q81, Lc[80], fma(q80, Lc[79], fma(q79, Lc[78], fma(q78, Lc[77], fma(q77, Lc[76], fma(q76, Lc[75], fma(q75, Lc[74], fma(q74, Lc[73], fma(q73, Lc[72], fma(q72, Lc[71], fma(q71, Lc[70], fma(q70, Lc[69], fma(q69, Lc[68], fma(q68, Lc[67], fma(q67, Lc[66], fma(q66, Lc[65], fma(q65, Lc[64], fma(q64, Lc[63], fma(q63, Lc[62], fma(q62, Lc[61], fma(q61, Lc[60], fma(q60, Lc[59], fma(q59, Lc[58], fma(q58, Lc[57], fma(q57, Lc[56], fma(q56, Lc[55], fma(q55, Lc[54], fma(q54, Lc[53], fma(q53, Lc[52], fma(q52, Lc[51], fma(q51, Lc[50], fma(q50, Lc[49], fma(q49, Lc[48], fma(q48, Lc[47], fma(q47, Lc[46], fma(q46, Lc[45], fma(q45, Lc[44], fma(q44, Lc[43], fma(q43, Lc[42], fma(q42, Lc[41], fma(q41, Lc[40], fma(q40, Lc[39], fma(q39, Lc[38], fma(q38, Lc[37], fma(q37, Lc[36], fma(q36, Lc[35], fma(q35, Lc[34], fma(q34, Lc[33], fma(q33, Lc[32], fma(q32, Lc[31], fma(q31, Lc[30], fma(q30, Lc[29], fma(q29, Lc[28], fma(q28, Lc[27], fma(q27, Lc[26], fma(q26, Lc[25], fma(q25, Lc[24], fma(q24, Lc[23], fma(q23, Lc[22], fma(q22, Lc[21], fma(q21, Lc[20], fma(q20, Lc[19], fma(q19, Lc[18], fma(q18, Lc[17], fma(q17, Lc[16], fma(q16, Lc[15], fma(q15, Lc[14], fma(q14, Lc[13], fma(q13, Lc[12], fma(q12, Lc[11], fma(q11, Lc[10], fma(q10, Lc[9], fma(q9, Lc[8], fma(q8, Lc[7], fma(q7, Lc[6], fma(q6, Lc[5], fma(q5, Lc[4], fma(q4, Lc[3], fma(q3, Lc[2], fma(q2, Lc[1], fma(q1, Lc[0], L0))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))))));
+}
+
+template <typename T>
+__device__ __forceinline__ T m2l0_p8(const T* __restrict__ M, const T* __restrict__ D) {
+  T v = T(0);
+  v = fma(M[0] * T(1), D[0], v);
+  v = fma(M[1] * T(-1), D[1], v);
+  v = fma(M[2] * T(-1), D[2], v);
+  v = fma(M[3] * T(-1), D[3], v);
+  v = fma(M[4] * T(0.5), D[4], v);
+  v = fma(M[5] * T(1), D[5], v);
+  v = fma(M[6] * T(1), D[6], v);
+  v = fma(M[7] * T(0.5), D[7], v);
+  v = fma(M[8] * T(1), D[8], v);
+  v = fma(M[9] * T(0.5), D[9], v);
+  v = fma(M[10] * T(-0.16666666666666666), D[10], v);
+  v = fma(M[11] * T(-0.5), D[11], v);
+  v = fma(M[12] * T(-0.5), D[12], v);
+  v = fma(M[13] * T(-0.5), D[13], v);
+  v = fma(M[14] * T(-1), D[14], v);
+  v = fma(M[15] * T(-0.5), D[15], v);
+  v = fma(M[16] * T(-0.16666666666666666), D[16], v);
+  v = fma(M[17] * T(-0.5), D[17], v);
+  v = fma(M[18] * T(-0.5), D[18], v);
+  v = fma(M[19] * T(-0.16666666666666666), D[19], v);
+  v = fma(M[20] * T(0.041666666666666664), D[20], v);
+  v = fma(M[21] * T(0.16666666666666666), D[21], v);
+  v = fma(M[22] * T(0.16666666666666666), D[22], v);
+  v = fma(M[23] * T(0.25), D[23], v);
+  v = fma(M[24] * T(0.5), D[24], v);
+  v = fma(M[25] * T(0.25), D[25], v);
+  v = fma(M[26] * T(0.16666666666666666), D[26], v);
+  v = fma(M[27] * T(0.5), D[27], v);
+  v = fma(M[28] * T(0.5), D[28], v);
+  v = fma(M[29] * T(0.16666666666666666), D[29], v);
+  v = fma(M[30] * T(0.041666666666666664), D[30], v);
+  v = fma(M[31] * T(0.16666666666666666), D[31], v);
+  v = fma(M[32] * T(0.25), D[32], v);
+  v = fma(M[33] * T(0.16666666666666666), D[33], v);
+  v = fma(M[34] * T(0.041666666666666664), D[34], v);
+  v = fma(M[35] * T(-0.0083333333333333332), D[35], v);
+  v = fma(M[36] * T(-0.041666666666666664), D[36], v);
+  v = fma(M[37] * T(-0.041666666666666664), D[37], v);
+  v = fma(M[38] * T(-0.083333333333333329), D[38], v);
+  v = fma(M[39] * T(-0.16666666666666666), D[39], v);
+  v = fma(M[40] * T(-0.083333333333333329), D[40], v);
+  v = fma(M[41] * T(-0.083333333333333329), D[41], v);
+  v = fma(M[42] * T(-0.25), D[42], v);
+  v = fma(M[43] * T(-0.25), D[43], v);
+  v = fma(M[44] * T(-0.083333333333333329), D[44], v);
+  v = fma(M[45] * T(-0.041666666666666664), D[45], v);
+  v = fma(M[46] * T(-0.16666666666666666), D[46], v);
+  v = fma(M[47] * T(-0.25), D[47], v);
+  v = fma(M[48] * T(-0.16666666666666666), D[48], v);
+  v = fma(M[49] * T(-0.041666666666666664), D[49], v);
+  v = fma(M[50] * T(-0.0083333333333333332), D[50], v);
+  v = fma(M[51] * T(-0.041666666666666664), D[51], v);
+  v = fma(M[52] * T(-0.083333333333333329), D[52], v);
+  v = fma(M[53] * T(-0.083333333333333329), D[53], v);
+  v = fma(M[54] * T(-0.041666666666666664), D[54], v);
+  v = fma(M[55] * T(-0.0083333333333333332), D[55], v);
+  v = fma(M[56] * T(0.0013888888888888889), D[56], v);
+  v = fma(M[57] * T(0.0083333333333333332), D[57], v);
+  v = fma(M[58] * T(0.0083333333333333332), D[58], v);
+  v = fma(M[59] * T(0.020833333333333332), D[59], v);
+  v = fma(M[60] * T(0.041666666666666664), D[60], v);
+  v = fma(M[61] * T(0.020833333333333332), D[61], v);
+  v = fma(M[62] * T(0.027777777777777776), D[62], v);
+  v = fma(M[63] * T(0.083333333333333329), D[63], v);
+  v = fma(M[64] * T(0.083333333333333329), D[64], v);
+  v = fma(M[65] * T(0.027777777777777776), D[65], v);
+  v = fma(M[66] * T(0.020833333333333332), D[66], v);
+  v = fma(M[67] * T(0.083333333333333329), D[67], v);
+  v = fma(M[68] * T(0.125), D[68], v);
+  v = fma(M[69] * T(0.083333333333333329), D[69], v);
+  v = fma(M[70] * T(0.020833333333333332), D[70], v);
+  v = fma(M[71] * T(0.0083333333333333332), D[71], v);
+  v = fma(M[72] * T(0.041666666666666664), D[72], v);
+  v = fma(M[73] * T(0.083333333333333329), D[73], v);
+  v = fma(M[74] * T(0.083333333333333329), D[74], v);
+  v = fma(M[75] * T(0.041666666666666664), D[75], v);
+  v = fma(M[76] * T(0.0083333333333333332), D[76], v);
+  v = fma(M[77] * T(0.0013888888888888889), D[77], v);
+  v = fma(M[78] * T(0.0083333333333333332), D[78], v);
+  v = fma(M[79] * T(0.020833333333333332), D[79], v);
+  v = fma(M[80] * T(0.027777777777777776), D[80], v);
+  v = fma(M[81] * T(0.020833333333333332), D[81], v);
+  v = fma(M[82] * T(0.0083333333333333332), D[82], v);
+  v = fma(M[83] * T(0.0013888888888888889), D[83], v);
+  v = fma(M[84] * T(-0.00019841269841269841), D[84], v);
+  v = fma(M[85] * T(-0.0013888888888888889), D[85], v);
+  v = fma(M[86] * T(-0.0013888888888888889), D[86], v);
+  v = fma(M[87] * T(-0.0041666666666666666), D[87], v);
+  v = fma(M[88] * T(-0.0083333333333333332), D[88], v);
+  v = fma(M[89] * T(-0.0041666666666666666), D[89], v);
+  v = fma(M[90] * T(-0.0069444444444444441), D[90], v);
+  v = fma(M[91] * T(-0.020833333333333332), D[91], v);
+  v = fma(M[92] * T(-0.020833333333333332), D[92], v);
+  v = fma(M[93] * T(-0.0069444444444444441), D[93], v);
+  v = fma(M[94] * T(-0.0069444444444444441), D[94], v);
+  v = fma(M[95] * T(-0.027777777777777776), D[95], v);
+  v = fma(M[96] * T(-0.041666666666666664), D[96], v);
+  v = fma(M[97] * T(-0.027777777777777776), D[97], v);
+  v = fma(M[98] * T(-0.0069444444444444441), D[98], v);
+  v = fma(M[99] * T(-0.0041666666666666666), D[99], v);
+  v = fma(M[100] * T(-0.020833333333333332), D[100], v);
+  v = fma(M[101] * T(-0.041666666666666664), D[101], v);
+  v = fma(M[102] * T(-0.041666666666666664), D[102], v);
+  v = fma(M[103] * T(-0.020833333333333332), D[103], v);
+  v = fma(M[104] * T(-0.0041666666666666666), D[104], v);
+  v = fma(M[105] * T(-0.0013888888888888889), D[105], v);
+  v = fma(M[106] * T(-0.0083333333333333332), D[106], v);
+  v = fma(M[107] * T(-0.020833333333333332), D[107], v);
+  v = fma(M[108] * T(-0.027777777777777776), D[108], v);
+  v = fma(M[109] * T(-0.020833333333333332), D[109], v);
+  v = fma(M[110] * T(-0.0083333333333333332), D[110], v);
+  v = fma(M[111] * T(-0.0013888888888888889), D[111], v);
+  v = fma(M[112] * T(-0.00019841269841269841), D[112], v);
+  v = fma(M[113] * T(-0.0013888888888888889), D[113], v);
+  v = fma(M[114] * T(-0.0041666666666666666), D[114], v);
+  v = fma(M[115] * T(-0.0069444444444444441), D[115], v);
+  v = fma(M[116] * T(-0.0069444444444444441), D[116], v);
+  v = fma(M[117] * T(-0.0041666666666666666), D[117], v);
+  v = fma(M[118] * T(-0.0013888888888888889), D[118], v);
+  v = fma(M[119] * T(-0.00019841269841269841), D[119], v);
+  v = fma(M[120] * T(2.4801587301587302e-05), D[120], v);
+  v = fma(M[121] * T(0.00019841269841269841), D[121], v);
+  v = fma(M[122] * T(0.00019841269841269841), D[122], v);
+  v = fma(M[123] * T(0.00069444444444444447), D[123], v);
+  v = fma(M[124] * T(0.0013888888888888889), D[124], v);
+  v = fma(M[125] * T(0.00069444444444444447), D[125], v);
+  v = fma(M[126] * T(0.0013888888888888889), D[126], v);
+  v = fma(M[127] * T(0.0041666666666666666), D[127], v);
+  v = fma(M[128] * T(0.0041666666666666666), D[128], v);
+  v = fma(M[129] * T(0.0013888888888888889), D[129], v);
+  v = fma(M[130] * T(0.001736111111111111), D[130], v);
+  v = fma(M[131] * T(0.0069444444444444441), D[131], v);
+  v = fma(M[132] * T(0.010416666666666666), D[132], v);
+  v = fma(M[133] * T(0.0069444444444444441), D[133], v);
+  v = fma(M[134] * T(0.001736111111111111), D[134], v);
+  v = fma(M[135] * T(0.0013888888888888889), D[135], v);
+  v = fma(M[136] * T(0.0069444444444444441), D[136], v);
+  v = fma(M[137] * T(0.013888888888888888), D[137], v);
+  v = fma(M[138] * T(0.013888888888888888), D[138], v);
+  v = fma(M[139] * T(0.0069444444444444441), D[139], v);
+  v = fma(M[140] * T(0.0013888888888888889), D[140], v);
+  v = fma(M[141] * T(0.00069444444444444447), D[141], v);
+  v = fma(M[142] * T(0.0041666666666666666), D[142], v);
+  v = fma(M[143] * T(0.010416666666666666), D[143], v);
+  v = fma(M[144] * T(0.013888888888888888), D[144], v);
+  v = fma(M[145] * T(0.010416666666666666), D[145], v);
+  v = fma(M[146] * T(0.0041666666666666666), D[146], v);
+  v = fma(M[147] * T(0.00069444444444444447), D[147], v);
+  v = fma(M[148] * T(0.00019841269841269841), D[148], v);
+  v = fma(M[149] * T(0.0013888888888888889), D[149], v);
+  v = fma(M[150] * T(0.0041666666666666666), D[150], v);
+  v = fma(M[151] * T(0.0069444444444444441), D[151], v);
+  v = fma(M[152] * T(0.0069444444444444441), D[152], v);
+  v = fma(M[153] * T(0.0041666666666666666), D[153], v);
+  v = fma(M[154] * T(0.0013888888888888889), D[154], v);
+  v = fma(M[155] * T(0.00019841269841269841), D[155], v);
+  v = fma(M[156] * T(2.4801587301587302e-05), D[156], v);
+  v = fma(M[157] * T(0.00019841269841269841), D[157], v);
+  v = fma(M[158] * T(0.00069444444444444447), D[158], v);
+  v = fma(M[159] * T(0.0013888888888888889), D[159], v);
+  v = fma(M[160] * T(0.001736111111111111), D[160], v);
+  v = fma(M[161] * T(0.0013888888888888889), D[161], v);
+  v = fma(M[162] * T(0.00069444444444444447), D[162], v);
+  v = fma(M[163] * T(0.00019841269841269841), D[163], v);
+  v = fma(M[164] * T(2.4801587301587302e-05), D[164], v);
+  return v;
+}
+
 template <typename T>
 __device__ __forceinline__ void dtensor_p2(T Rx, T Ry, T Rz, T eps2, T* __restrict__ D) {
   const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));

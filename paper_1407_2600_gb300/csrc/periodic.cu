@@ -29,8 +29,9 @@
 
 namespace {
 
-constexpr int kPMax = 6;               // derivative orders in the table
-constexpr int kNMMax = 84;             // multi-indices of order <= 6
+constexpr int kPMax = 6;               // derivative orders in the lattice table
+constexpr int kPFar = 8;               // orders of the far-lattice tensor (near-replica scheme)
+constexpr int kNMMax = 165;            // multi-indices of order <= 8
 // Ewald split used to build the table: screening alpha, real-space cut-off
 // and reciprocal-space extent.  phi~ does not depend on the split; with these
 // the neglected real-space images (alpha r >= 8.1) and wave vectors
@@ -86,9 +87,11 @@ __device__ void smooth_ladder(double r, int P, double* u) {
   }
 }
 
-// out[n] += s d^n f(|r|) for |n| <= P from the ladder f[0..P]
+// out[n] += s d^n f(|r|) for |n| <= P <= PM from the ladder f[0..P]
+template <int PM>
 __device__ void add_cartesian(const double r[3], const double* f, double s, int P, int nm, double* out) {
-  double T[kPMax + 1][kNMMax];
+  constexpr int NM = (PM + 1) * (PM + 2) * (PM + 3) / 6;
+  double T[PM + 1][NM];
   for (int j = 0; j <= P; j++) T[j][0] = f[j];
   for (int t = 1; t < nm; t++) {
     const int a = c_rax[t], d1 = c_rd1[t], d2 = c_rd2[t], o = c_rord[t];
@@ -98,16 +101,18 @@ __device__ void add_cartesian(const double r[3], const double* f, double s, int 
   for (int t = 0; t < nm; t++) out[t] += s * T[0][t];
 }
 
+template <int PM>
 __global__ void phitilde_table_kernel(int lg, int P, int nm, double* __restrict__ tab) {
+  constexpr int NM = (PM + 1) * (PM + 2) * (PM + 3) / 6;
   const int m = (1 << (lg - 1)) + 2;
   const int total = m * m * m;
   const double h = ldexp(1.0, -lg);
   for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < total; id += gridDim.x * blockDim.x) {
     const int i = id / (m * m), j = (id / m) % m, k = id % m;
     const double r[3] = {i * h, j * h, k * h};
-    double out[kNMMax];
+    double out[NM];
     for (int t = 0; t < nm; t++) out[t] = 0.0;
-    double f[kPMax + 1];
+    double f[PM + 1];
     // real space: every image n != 0 within the cut-off, screened
     const int nmax = (int)ceil(kRcut) + 1;
     for (int nx = -nmax; nx <= nmax; nx++)
@@ -118,11 +123,11 @@ __global__ void phitilde_table_kernel(int lg, int P, int nm, double* __restrict_
           const double d = sqrt(rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2]);
           if (d >= kRcut) continue;
           screened_ladder(d, P, f);
-          add_cartesian(rho, f, -1.0, P, nm, out);
+          add_cartesian<PM>(rho, f, -1.0, P, nm, out);
         }
     // the n = 0 source enters as erf(alpha r)/r (1/r is not part of phi~)
     smooth_ladder(sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]), P, f);
-    add_cartesian(r, f, 1.0, P, nm, out);
+    add_cartesian<PM>(r, f, 1.0, P, nm, out);
     // reciprocal space: -(1/pi) sum_h e^(-pi^2 h^2/alpha^2)/h^2 cos(2 pi h.r);
     // d^n cos(k.r) = k^n cos(k.r + |n| pi/2)
     for (int hx = -kHMax; hx <= kHMax; hx++)
@@ -380,6 +385,154 @@ __global__ void scatter_pot_kernel(int64_t n, const uint32_t* __restrict__ perm,
     out[perm[i]] = (float)potw[i];
 }
 
+// ---- the near-replica scheme's far lattice --------------------------------------------
+// The walk covers the images |n|_inf <= W of every source; the images beyond
+// act through one local expansion of order 8 about the box centre c0:
+// L_k = sum_n ((-1)^|n|/n!) M_n T_(k+n), |k| + |n| <= 8, with the box's
+// moments M about c0 and T = d^m Phi_F(0), Phi_F the periodic potential of a
+// unit mass with the uniform background less its near images' -1/|r - n|.
+constexpr int kNF = 165;       // multi-indices of order <= 8
+constexpr int kLatParts = 512;  // slices per box of the moment sums
+constexpr int kLatTile = 128;  // particles per shared-memory tile
+
+// compensated (Kahan) addition of v to the pair (s, c)
+__device__ __forceinline__ void kadd_t(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ int mi_idx_dev(int nx, int ny, int nz) {
+  const int o = nx + ny + nz, j = ny + nz;
+  return o * (o + 1) * (o + 2) / 6 + j * (j + 1) / 2 + nz;
+}
+
+// T = phi~'s derivatives at 0 (node0), the background's -(2 pi/3)|r|^2, and
+// the near images' +1/|r - n| (ladder f_j = (-1)^j (2j-1)!! / r^(2j+1) at R = -n)
+__global__ void lattice_tensor_kernel(const double* __restrict__ node0, int W, double* __restrict__ T) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double out[kNF];
+  for (int t = 0; t < kNF; t++) out[t] = node0[t];
+  out[4] -= 4.0 * M_PI / 3.0;
+  out[7] -= 4.0 * M_PI / 3.0;
+  out[9] -= 4.0 * M_PI / 3.0;
+  double f[kPFar + 1];
+  for (int nx = -W; nx <= W; nx++)
+    for (int ny = -W; ny <= W; ny++)
+      for (int nz = -W; nz <= W; nz++) {
+        if (nx == 0 && ny == 0 && nz == 0) continue;
+        const double R[3] = {(double)-nx, (double)-ny, (double)-nz};
+        const double r2 = R[0] * R[0] + R[1] * R[1] + R[2] * R[2];
+        f[0] = 1.0 / sqrt(r2);
+        for (int j = 1; j <= kPFar; j++) f[j] = -(2 * j - 1) * f[j - 1] / r2;
+        add_cartesian<kPFar>(R, f, 1.0, kPFar, kNF, out);
+      }
+  for (int t = 0; t < kNF; t++) T[t] = out[t];
+}
+
+// partial moments about c0 of slice blockIdx.x of box blockIdx.y; thread t
+// (< 165) owns M_t and sums m x^a y^b z^c over tiles of particles whose
+// coordinate powers are staged in shared memory.  T = float (the mixed
+// precision mode) forms the terms in FP32 and sums them with compensation;
+// T = double in FP64.
+template <typename T>
+__global__ void __launch_bounds__(192) lattice_moments_part_kernel(const int64_t* __restrict__ off, int64_t n,
+                                                                  const double* __restrict__ spos,
+                                                                  const float* __restrict__ smass,
+                                                                  double* __restrict__ part) {
+  __shared__ T s_p[3][kLatTile][kPFar + 1];
+  __shared__ T s_m[kLatTile];
+  const int b = blockIdx.y, pp = blockIdx.x, t = threadIdx.x;
+  const int64_t lo = off[b], cnt = off[b + 1] - lo;
+  const int64_t s0 = lo + cnt * pp / kLatParts, s1 = lo + cnt * (pp + 1) / kLatParts;
+  const int a0 = t < kNF ? c_mi[t][0] : 0, a1 = t < kNF ? c_mi[t][1] : 0, a2 = t < kNF ? c_mi[t][2] : 0;
+  T acc = 0, cmp = 0;
+  for (int64_t i0 = s0; i0 < s1; i0 += kLatTile) {
+    const int nt = (int)min((int64_t)kLatTile, s1 - i0);
+    for (int k = t; k < nt; k += blockDim.x) {
+      const int64_t i = i0 + k;
+      s_m[k] = (T)smass[i];
+      for (int d = 0; d < 3; d++) {
+        const T x = (T)(spos[d * n + i] - 0.5);
+        T w = 1;
+        for (int e = 0; e <= kPFar; e++) {
+          s_p[d][k][e] = w;
+          w *= x;
+        }
+      }
+    }
+    __syncthreads();
+    if (t < kNF) {
+      if constexpr (sizeof(T) == 4) {
+        for (int k = 0; k < nt; k++) kadd_t(acc, cmp, (s_m[k] * s_p[0][k][a0]) * (s_p[1][k][a1] * s_p[2][k][a2]));
+      } else {
+        for (int k = 0; k < nt; k++) acc = fma(s_m[k] * s_p[0][k][a0], s_p[1][k][a1] * s_p[2][k][a2], acc);
+      }
+    }
+    __syncthreads();
+  }
+  if (t < kNF) part[((int64_t)b * kLatParts + pp) * kNF + t] = (double)acc - (double)cmp;
+}
+
+// box moments (slices summed in order: reproducible), then the local
+// expansion about c0, in FP64 and in the walk's precision
+template <typename T>
+__global__ void lattice_m2l_kernel(const double* __restrict__ part, const double* __restrict__ Tf,
+                                   double* __restrict__ M, double* __restrict__ Ld, T* __restrict__ Lt) {
+  __shared__ double s_M[kNF];
+  const int b = blockIdx.x, t = threadIdx.x;
+  if (t < kNF) {
+    double v = 0.0;
+    for (int pp = 0; pp < kLatParts; pp++) v += part[((int64_t)b * kLatParts + pp) * kNF + t];
+    s_M[t] = v;
+    M[(int64_t)b * kNF + t] = v;
+  }
+  __syncthreads();
+  if (t < kNF) {
+    const int k0 = c_mi[t][0], k1 = c_mi[t][1], k2 = c_mi[t][2], ok = k0 + k1 + k2;
+    double v = 0.0;
+    for (int u = 0; u < kNF; u++) {
+      const int n0 = c_mi[u][0], n1 = c_mi[u][1], n2 = c_mi[u][2], on = n0 + n1 + n2;
+      if (on + ok > kPFar) continue;
+      double fac = 1.0;
+      for (int q = 2; q <= n0; q++) fac *= q;
+      for (int q = 2; q <= n1; q++) fac *= q;
+      for (int q = 2; q <= n2; q++) fac *= q;
+      v += ((on & 1) ? -s_M[u] : s_M[u]) / fac * Tf[mi_idx_dev(n0 + k0, n1 + k1, n2 + k2)];
+    }
+    Ld[(int64_t)b * kNF + t] = v;
+    Lt[(int64_t)b * kNF + t] = (T)v;
+  }
+}
+
+// walk accelerations + the far lattice (a -= sum_{|u| <= 7} d^u/u! L_(u+e_k),
+// d = x - c0), scattered to the caller's order; with the potential, the
+// walk's plus sum_{|k| <= 8} d^k/k! L_k
+template <typename T, bool POT>
+__global__ void lattice_l2p_kernel(DevTree tr, const T* __restrict__ Lt, const T* __restrict__ accw,
+                                   float* __restrict__ out, double* __restrict__ out64, const T* __restrict__ potw,
+                                   float* __restrict__ pout) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tr.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (tr.sact && !tr.sact[i]) continue;
+    const T* L = Lt + (int64_t)tr.sbox[i] * kNF;
+    const T dx = (T)(tr.spos[i] - 0.5), dy = (T)(tr.spos[tr.n + i] - 0.5), dz = (T)(tr.spos[2 * tr.n + i] - 0.5);
+    T ax = accw[i], ay = accw[tr.n + i], az = accw[2 * tr.n + i];
+    l2p_pe7<T>(L + 1, dx, dy, dz, ax, ay, az);
+    const uint32_t j = tr.perm[i];
+    if (out64) {
+      out64[j] = (double)ax;
+      out64[tr.n + j] = (double)ay;
+      out64[2 * tr.n + j] = (double)az;
+    } else {
+      out[j] = (float)ax;
+      out[tr.n + j] = (float)ay;
+      out[2 * tr.n + j] = (float)az;
+    }
+    if constexpr (POT) pout[j] = (float)(potw[i] + l2pot_pe7<T>(L[0], L + 1, dx, dy, dz));
+  }
+}
+
 // ---- host side: term tables and cached device tables ------------------------------
 int mi_index(int nx, int ny, int nz) {
   int o = nx + ny + nz, j = ny + nz;
@@ -403,7 +556,7 @@ cudaError_t upload_terms() {
   signed char mi[kNMMax][3], rax[kNMMax], rord[kNMMax];
   short rd1[kNMMax], rd2[kNMMax];
   unsigned char pm[kNMMax];
-  for (int o = 0; o <= kPMax; o++)
+  for (int o = 0; o <= kPFar; o++)
     for (int nx = o; nx >= 0; nx--)
       for (int ny = o - nx; ny >= 0; ny--) {
         const int nz = o - nx - ny, t = mi_index(nx, ny, nz);
@@ -467,7 +620,7 @@ cudaError_t nb_phitilde_table(int lg, int P, const double** t64, const float** t
     return e;
   }
   const int nodes = m * m * m;
-  phitilde_table_kernel<<<(nodes + 63) / 64, 64, 0, s>>>(lg, P, nm, c.d64);
+  phitilde_table_kernel<kPMax><<<(nodes + 63) / 64, 64, 0, s>>>(lg, P, nm, c.d64);
   to_float_kernel<<<(int)((total + 255) / 256 > 4096 ? 4096 : (total + 255) / 256), 256, 0, s>>>(c.d64, c.d32,
                                                                                                  total);
   if ((e = cudaGetLastError())) return e;
@@ -573,5 +726,87 @@ cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg,
   }
 #undef NB_LOC
   nb_launch_counter += 1;
+  return cudaGetLastError();
+}
+
+namespace {
+struct LatticeCache {
+  int device = -1, W = 0;
+  double* T = nullptr;
+};
+std::mutex g_lat_mutex;
+std::vector<LatticeCache> g_lats;
+}  // namespace
+
+// The far-lattice tensor for shell width W on the current device (built
+// once: the order-8 derivatives of phi~ at 0, then the near images and the
+// background taken out; cached until exit)
+cudaError_t nb_lattice_tensor(int W, const double** out, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(g_lat_mutex);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e) return e;
+  for (auto& c : g_lats)
+    if (c.device == dev && c.W == W) {
+      *out = c.T;
+      return cudaSuccess;
+    }
+  if ((e = upload_terms())) return e;
+  const int lg = 2, m = (1 << (lg - 1)) + 2, nodes = m * m * m;
+  double* tab = nullptr;
+  LatticeCache c;
+  c.device = dev;
+  c.W = W;
+  if ((e = cudaMalloc(&tab, sizeof(double) * nodes * kNF))) return e;
+  if ((e = cudaMalloc(&c.T, sizeof(double) * kNF))) {
+    cudaFree(tab);
+    return e;
+  }
+  phitilde_table_kernel<kPFar><<<1, 64, 0, s>>>(lg, kPFar, kNF, tab);  // node 0 is r = 0
+  lattice_tensor_kernel<<<1, 32, 0, s>>>(tab, W, c.T);
+  if (!(e = cudaGetLastError())) e = cudaStreamSynchronize(s);
+  cudaFree(tab);
+  if (e) {
+    cudaFree(c.T);
+    return e;
+  }
+  g_lats.push_back(c);
+  *out = c.T;
+  return cudaSuccess;
+}
+
+// Far lattice of the near-replica scheme after a walk: box moments (two
+// fixed-order stages), the local expansion per box, and its evaluation at
+// every particle added to the walk's accelerations on the way to the
+// caller's order.  part: nbox * 512 * 165 doubles; mom, Ld: nbox * 165
+// doubles; Lt: nbox * 165 in the walk's precision.
+cudaError_t nb_lattice(const DevTree& tr, bool fp64, int W, const void* accw, float* out, double* out64,
+                       const void* potw, float* pout, double* part, double* mom, double* Ld, void* Lt,
+                       cudaStream_t s) {
+  const double* T = nullptr;
+  cudaError_t e = nb_lattice_tensor(W, &T, s);
+  if (e) return e;
+  if (fp64)
+    lattice_moments_part_kernel<double><<<dim3(kLatParts, tr.nbox), 192, 0, s>>>(tr.off, tr.n, tr.spos, tr.smass, part);
+  else
+    lattice_moments_part_kernel<float><<<dim3(kLatParts, tr.nbox), 192, 0, s>>>(tr.off, tr.n, tr.spos, tr.smass, part);
+  int grid = (int)((tr.n + 255) / 256);
+  if (grid > 152 * 32) grid = 152 * 32;
+#define NB_LAT_L2P(TT)                                                                                 \
+  if (potw)                                                                                            \
+    lattice_l2p_kernel<TT, true><<<grid, 256, 0, s>>>(tr, (const TT*)Lt, (const TT*)accw, out, out64,  \
+                                                      (const TT*)potw, pout);                          \
+  else                                                                                                 \
+    lattice_l2p_kernel<TT, false><<<grid, 256, 0, s>>>(tr, (const TT*)Lt, (const TT*)accw, out, out64, \
+                                                       nullptr, nullptr);
+  if (fp64) {
+    lattice_m2l_kernel<double><<<tr.nbox, 192, 0, s>>>(part, T, mom, Ld, (double*)Lt);
+    NB_LAT_L2P(double)
+  } else {
+    lattice_m2l_kernel<float><<<tr.nbox, 192, 0, s>>>(part, T, mom, Ld, (float*)Lt);
+    NB_LAT_L2P(float)
+  }
+#undef NB_LAT_L2P
+  nb_launch_counter += 3;
   return cudaGetLastError();
 }

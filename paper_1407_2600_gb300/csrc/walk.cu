@@ -127,6 +127,7 @@ struct WalkArgs {
   int mac_edge;
   int bg;  // add the uniform-background term of every expanded cell
   int k1;  // Dehnen K1 softening of direct pairs, Newtonian expansions
+  int repl;        // near-replica scheme: W (images |n|_inf <= W walked explicitly), else 0
   int dual;        // cell-group local expansions for well-separated cells
   double theta2;   // theta^2 of the cell-group test (IEEE double, as on the host)
   NbDualBufs db;   // where the walk emits its cell-group pairs
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
   __shared__ T s_poff[WARPS][32][3];
   __shared__ int4 s_pcen[WARPS][32];
   __shared__ int s_sj[WARPS][POTK ? 32 : 1];  // the staged sources' indices (the sink's own pair is skipped)
+  __shared__ int s_pctr[WARPS][POTK ? 32 : 1];  // replicas: the P2P cell is at the central image
 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
@@ -406,7 +408,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       __syncwarp();
     };
     int top = 1;
-    if (lane == 0) stk[0] = box;  // root of this box
+    if (w.repl) {
+      // the root at every near image, |n|_inf <= W
+      const int S1 = 2 * w.repl + 1;
+      top = S1 * S1 * S1;
+      for (int r = lane; r < top; r += 32) stk[r] = (int)((unsigned)box | ((unsigned)r << kReplShift));
+    } else if (lane == 0) {
+      stk[0] = box;  // root of this box
+    }
     __syncwarp();
     bool overflow = false;
     // each chunk routine has one call site (the end of this loop), which
@@ -416,9 +425,12 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       const int base = top - nb;
       top = base;
       int c = -1;
+      unsigned code = 0;  // replicas: the image of this entry's subtree
       int4 ca = make_int4(0, 0, 0, 0), cb = make_int4(0, 0, 0, 0);
       if (lane < nb) {
-        c = stk[base + lane];
+        const unsigned e = (unsigned)stk[base + lane];
+        c = (int)(e & kReplCellMask);
+        code = e >> kReplShift;
         ca = tr.cA[c];
         cb = tr.cB[c];
       }
@@ -427,7 +439,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       int kx = 0, ky = 0, kz = 0;
       const int lvl = ca.w & 0xff, nch = ca.w >> 8;
       if (lane < nb) {
-        cls = classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, kx, ky, kz);
+        cls = w.repl ? classify_cell_at(ca, cb, gb, gc, w.thr, w.n_direct, w.mac_edge, code, w.repl, kx, ky, kz)
+                     : classify_cell(ca, cb, gb, gc, gd, w.le, w.thr, w.n_direct, w.mac_edge, kx, ky, kz);
         if constexpr (DUAL) {
           if (w.dual && cls == NB_CELL_M2P) {
             // cell-group test: centre-to-centre distance against (s_C + s_G)/theta
@@ -436,9 +449,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             if (dx * dx + dy * dy + dz * dz > s_tl[wid][lvl]) cls = NB_CELL_M2L;
           }
         }
-        hsum += decision_mix(g, c, cls | (cb.y << 3));
+        hsum += decision_mix(g, (int)((unsigned)c | (code << kReplShift)), cls | (cb.y << 3));
       }
-      // push daughters of opened cells
+      // push daughters of opened cells (at the same image)
       {
         const int nc = (cls == 1) ? nch : 0;
         const int pre = warp_excl_scan(nc, lane);
@@ -447,7 +460,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           overflow = true;
           break;
         }
-        for (int q = 0; q < nc; q++) stk[top + pre + q] = cb.z + q;
+        for (int q = 0; q < nc; q++) stk[top + pre + q] = (int)((unsigned)(cb.z + q) | (code << kReplShift));
         top += tot;
         __syncwarp();
       }
@@ -476,7 +489,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           if (cls == NB_CELL_M2L) {
             const int pos = ln + __popc(lm & ltmask);
             s_lidx[wid][pos] = c;
-            s_limg[wid][pos] = (kx + 1) | ((ky + 1) << 2) | ((kz + 1) << 4);
+            s_limg[wid][pos] = (kx + 2) | ((ky + 2) << 3) | ((kz + 2) << 6);
           }
           ln += __popc(lm);
           __syncwarp();
@@ -492,6 +505,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         s_pst[wid][lane] = cb.x;
         s_plev[wid][lane] = lvl;
         s_pcen[wid][lane] = ca;
+        if constexpr (POTK) s_pctr[wid][lane] = kx == 0 && ky == 0 && kz == 0;
         s_poff[wid][lane][0] = (T)(ca.x - kx * NB_PBOX - gd.x) * scale;
         s_poff[wid][lane][1] = (T)(ca.y - ky * NB_PBOX - gd.y) * scale;
         s_poff[wid][lane][2] = (T)(ca.z - kz * NB_PBOX - gd.z) * scale;
@@ -511,10 +525,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             }
             const int q = lo;
             const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
-            jo = j;
+            if constexpr (POTK) jo = (!w.repl || s_pctr[wid][q]) ? j : -1;  // a replica's pair is never the self pair
             v = w.src[j];
             T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
-            if (s_plev[wid][q] < w.le) {
+            if (!w.repl && s_plev[wid][q] < w.le) {
               // leaf above the image level: image per particle from its own
               // level-l_E ancestor
               const int4 pc = s_pcen[wid][q];
@@ -731,7 +745,7 @@ __global__ void __launch_bounds__(256) dual_m2l_kernel(DualArgs a) {
     const float live = lane < nml ? 1.f : 0.f;
     const int cell = a.db.cell[(int64_t)c * 32 + q];
     const int code = a.db.img[(int64_t)c * 32 + q];
-    const int kx = (code & 3) - 1, ky = ((code >> 2) & 3) - 1, kz = ((code >> 4) & 3) - 1;
+    const int kx = (code & 7) - 2, ky = ((code >> 3) & 7) - 2, kz = ((code >> 6) & 7) - 2;
     const int4 ca = tr.cA[cell];
     const int lvl = ca.w & 0xff;
     const float sc = (float)(1 << lvl);
@@ -1002,7 +1016,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
                     int stack_cap, int max_blocks, int* group_ctr, void* acc,
                     unsigned long long* counters, unsigned* status, int nsm, int forced_variant,
                     int mac_edge, int bg, int k1, int dual, double theta, const float* mom32, int lu,
-                    const NbDualBufs* db, void* pot, cudaStream_t s) {
+                    const NbDualBufs* db, void* pot, int repl, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(group_ctr, 0, sizeof(int), s);
   if (e) return e;
   if (dual && !pot && !db) return cudaErrorInvalidValue;
@@ -1021,6 +1035,7 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
     a.dual = dual;                                                                 \
     a.theta2 = theta * theta;                                                      \
     a.db = db ? *db : NbDualBufs{};                                                \
+    a.repl = repl;                                                                 \
     a.le = le;                                                                     \
     a.stack = stack;                                                               \
     a.stack_cap = stack_cap;                                                       \

@@ -148,6 +148,33 @@ __device__ __forceinline__ int classify_cell(const int4 ca, const int4 cb, const
   return NB_CELL_OPEN;
 }
 
+// Near-replica scheme: the walk's stack entries carry the image n of the
+// whole subtree, |n|_inf <= W, as code (nx + W) + S (ny + W) + S^2 (nz + W),
+// S = 2W + 1, above the cell index.
+constexpr int kReplShift = 25;
+constexpr unsigned kReplCellMask = (1u << kReplShift) - 1u;
+
+// classify_cell at a given image (k = -n): no consistency condition, and
+// cells of any level may be accepted
+__device__ __forceinline__ int classify_cell_at(const int4 ca, const int4 cb, const int4 gb, const int4 gc,
+                                                const long long* thr, int n_direct, int mac_edge, unsigned code,
+                                                int W, int& kx, int& ky, int& kz) {
+  const int lvl = ca.w & 0xff, nch = ca.w >> 8, S = 2 * W + 1;
+  kx = W - (int)(code % S);
+  ky = W - (int)((code / S) % S);
+  kz = W - (int)(code / (S * S));
+  const int hs = mac_edge ? (1 << (22 - lvl)) : 0;
+  const int dx = abs(ca.x - gb.x - kx * NB_PBOX) - gc.x - hs;
+  const int dy = abs(ca.y - gb.y - ky * NB_PBOX) - gc.y - hs;
+  const int dz = abs(ca.z - gb.z - kz * NB_PBOX) - gc.z - hs;
+  const long long ddx = dx > 0 ? dx : 0, ddy = dy > 0 ? dy : 0, ddz = dz > 0 ? dz : 0;
+  const long long d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+  const bool accept = d2 > thr[lvl];
+  if (accept && cb.y > n_direct) return NB_CELL_M2P;
+  if (accept || nch == 0) return NB_CELL_P2P;
+  return NB_CELL_OPEN;
+}
+
 // Image of one source particle of a leaf above level le, from its own
 // level-le ancestor key prefix.
 __device__ __forceinline__ void particle_image(uint64_t key, int le, const int4 gd, int& kx, int& ky, int& kz) {

@@ -31,6 +31,7 @@ NBODY_FLAG_MAC_EDGE = 2
 NBODY_FLAG_BACKGROUND = 4
 NBODY_FLAG_K1 = 8
 NBODY_FLAG_DUAL = 16
+NBODY_FLAG_REPLICAS = 32
 
 
 def NBODY_FLAG_WALK_VARIANT(v: int) -> int:

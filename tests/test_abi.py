@@ -121,7 +121,7 @@ def test_more_invalid_arguments_are_rejected_without_gpu_work():
     bad = [("theta", 0.0), ("theta", -0.5), ("eps", -1e-3), ("order", 5), ("order", -1), ("n_leaf", 0),
            ("n_leaf", 65), ("n_group", 0), ("n_group", 33), ("n_direct", -1), ("lmax", 1), ("lmax", 22),
            ("ewald_order", 6), ("ewald_grid", 3), ("ewald_grid", 9), ("ewald_level", 0), ("precision", 2),
-           ("box_len", -1.0), ("box_len", float("nan")), ("box_len", float("inf")), ("flags", 32),
+           ("box_len", -1.0), ("box_len", float("nan")), ("box_len", float("inf")), ("flags", 64),
            ("flags", 1 << 12)]
     for name, value in bad:
         p = nb.nbody_default_params()
@@ -170,3 +170,17 @@ def test_more_invalid_arguments_are_rejected_without_gpu_work():
     assert nb.nbody_sort_keys_noalloc(1, 0, 1, 1) == EINVAL
     assert nb.nbody_sort_keys_noalloc(1, 16, 0, 1) == EINVAL
     assert nb.nbody_sort_keys_noalloc(1, (1 << 20) + 1, 1, 1) == nb.NBODY_ERANGE
+
+
+def test_replicas_need_no_image_field():
+    """The near-replica scheme replaces the image field: with ewald_order > 0
+    the parameters are rejected before any CUDA call."""
+    import paper_1407_2600_gb300.nbody as nb
+    p = nb.nbody_default_params()
+    p.flags = nb.NBODY_FLAG_REPLICAS
+    rc, h = nb.nbody_build_tree(p, 10, 1, None)
+    assert rc == nb.NBODY_EINVAL and not h
+    p.ewald_order = 0
+    p.ewald_grid = 9
+    rc, h = nb.nbody_build_tree(p, 10, 1, None)
+    assert rc == nb.NBODY_EINVAL and not h
