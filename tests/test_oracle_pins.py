@@ -130,12 +130,19 @@ def test_direct_lattice_zero_and_momentum():
 
 
 def test_direct_table_matches_exact_ewald():
+    """The tricubic C~ table against the exact Ewald sum: its error falls as
+    h^4 (about 16x per halving of the spacing) and is 3e-9 at the default
+    128 intervals, six orders below the 1e-3 accuracy bar it is used to
+    measure."""
     x, eps = ics.config_small(2)
     tg = ics.random_targets(len(x), 24, 2)
     a_ex = O.direct_forces(x, None, eps, targets=tg, table_n1=None)
-    a_tb = O.direct_forces(x, None, eps, targets=tg, table_n1=64)
-    rel = np.linalg.norm(a_ex - a_tb, axis=1) / np.linalg.norm(a_ex, axis=1)
-    assert rel.max() <= 1e-6
+    err = {}
+    for n1 in (64, 128):
+        a_tb = O.direct_forces(x, None, eps, targets=tg, table_n1=n1)
+        err[n1] = (np.linalg.norm(a_ex - a_tb, axis=1) / np.linalg.norm(a_ex, axis=1)).max()
+    assert err[128] <= 1e-8 and err[64] <= 1e-7, err
+    assert err[64] >= 6 * err[128], err
 
 
 def test_direct_pair_matches_definition():
