@@ -104,11 +104,13 @@ def emit_m2p(p):
     mi = {m: i for i, m in enumerate(mon)}
     sl = slots(p)
     L = []
-    L.append("template <typename T>")
+    L.append("// REF: the reciprocal square root refined (near-uniform boxes), else the")
+    L.append("// hardware approximation alone")
+    L.append("template <typename T, bool REF = true>")
     L.append("__device__ __forceinline__ void m2p_p%d(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2," % p)
     L.append("                                     T& ax, T& ay, T& az) {")
     L.append("  const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));")
-    L.append("  const T F0 = nbody_rsqrt(s);")
+    L.append("  const T F0 = REF ? nbody_rsqrt(s) : nbody_rsqrt_pair(s);")
     L.append("  const T is = F0 * F0;")
     for j in range(1, p + 2):
         L.append("  const T F%d = F%d * (T(%d) * is);" % (j, j - 1, -(2 * j - 1)))
@@ -204,10 +206,12 @@ def emit_m2p2(p):
     mi = {m: i for i, m in enumerate(mon)}
     sl = slots(p)
     L = []
+    L.append("template <bool REF = true>")
     L.append("__device__ __forceinline__ void m2p2_p%d(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz," % p)
     L.append("                                       float2 eps2, float2& ax, float2& ay, float2& az) {")
     L.append("  const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));")
-    L.append("  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));")
+    L.append("  const float2 F0 = REF ? make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y))")
+    L.append("                        : make_float2(nbody_rsqrt_pair(s.x), nbody_rsqrt_pair(s.y));")
     L.append("  const float2 is = __fmul2_rn(F0, F0);")
     for j in range(1, p + 2):
         c = -(2 * j - 1)

@@ -13,11 +13,13 @@ constexpr int kM2PFlops3 = 192;  // flops per M2P (FMA = 2, rsqrt = 1)
 constexpr int kNB4 = 46;  // reduced coefficients at order 4
 constexpr int kM2PFlops4 = 342;  // flops per M2P (FMA = 2, rsqrt = 1)
 
-template <typename T>
+// REF: the reciprocal square root refined (near-uniform boxes), else the
+// hardware approximation alone
+template <typename T, bool REF = true>
 __device__ __forceinline__ void m2p_p0(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
                                      T& ax, T& ay, T& az) {
   const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
-  const T F0 = nbody_rsqrt(s);
+  const T F0 = REF ? nbody_rsqrt(s) : nbody_rsqrt_pair(s);
   const T is = F0 * F0;
   const T F1 = F0 * (T(-1) * is);
   const T m0 = T(1);
@@ -41,10 +43,12 @@ __device__ __forceinline__ T m2pot_p0(const T* __restrict__ B, T Rx, T Ry, T Rz,
   return F0 * S0;
 }
 
+template <bool REF = true>
 __device__ __forceinline__ void m2p2_p0(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
                                        float2 eps2, float2& ax, float2& ay, float2& az) {
   const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
-  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 F0 = REF ? make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y))
+                        : make_float2(nbody_rsqrt_pair(s.x), nbody_rsqrt_pair(s.y));
   const float2 is = __fmul2_rn(F0, F0);
   const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
   float2 S0;
@@ -61,11 +65,13 @@ __device__ __forceinline__ void reduce_moments_p0(const double* __restrict__ M, 
   B[0] = 1 * M[0];
 }
 
-template <typename T>
+// REF: the reciprocal square root refined (near-uniform boxes), else the
+// hardware approximation alone
+template <typename T, bool REF = true>
 __device__ __forceinline__ void m2p_p1(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
                                      T& ax, T& ay, T& az) {
   const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
-  const T F0 = nbody_rsqrt(s);
+  const T F0 = REF ? nbody_rsqrt(s) : nbody_rsqrt_pair(s);
   const T is = F0 * F0;
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
@@ -115,10 +121,12 @@ __device__ __forceinline__ T m2pot_p1(const T* __restrict__ B, T Rx, T Ry, T Rz,
   return fma(F1, S1, F0 * S0);
 }
 
+template <bool REF = true>
 __device__ __forceinline__ void m2p2_p1(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
                                        float2 eps2, float2& ax, float2& ay, float2& az) {
   const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
-  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 F0 = REF ? make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y))
+                        : make_float2(nbody_rsqrt_pair(s.x), nbody_rsqrt_pair(s.y));
   const float2 is = __fmul2_rn(F0, F0);
   const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
   const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
@@ -155,11 +163,13 @@ __device__ __forceinline__ void reduce_moments_p1(const double* __restrict__ M, 
   B[3] = -1 * M[3];
 }
 
-template <typename T>
+// REF: the reciprocal square root refined (near-uniform boxes), else the
+// hardware approximation alone
+template <typename T, bool REF = true>
 __device__ __forceinline__ void m2p_p2(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
                                      T& ax, T& ay, T& az) {
   const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
-  const T F0 = nbody_rsqrt(s);
+  const T F0 = REF ? nbody_rsqrt(s) : nbody_rsqrt_pair(s);
   const T is = F0 * F0;
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
@@ -269,10 +279,12 @@ __device__ __forceinline__ T m2pot_p2(const T* __restrict__ B, T Rx, T Ry, T Rz,
   return fma(F2, S2, fma(F1, S1, F0 * S0));
 }
 
+template <bool REF = true>
 __device__ __forceinline__ void m2p2_p2(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
                                        float2 eps2, float2& ax, float2& ay, float2& az) {
   const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
-  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 F0 = REF ? make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y))
+                        : make_float2(nbody_rsqrt_pair(s.x), nbody_rsqrt_pair(s.y));
   const float2 is = __fmul2_rn(F0, F0);
   const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
   const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
@@ -357,11 +369,13 @@ __device__ __forceinline__ void reduce_moments_p2(const double* __restrict__ M, 
   B[10] = 1 * M[9];
 }
 
-template <typename T>
+// REF: the reciprocal square root refined (near-uniform boxes), else the
+// hardware approximation alone
+template <typename T, bool REF = true>
 __device__ __forceinline__ void m2p_p3(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
                                      T& ax, T& ay, T& az) {
   const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
-  const T F0 = nbody_rsqrt(s);
+  const T F0 = REF ? nbody_rsqrt(s) : nbody_rsqrt_pair(s);
   const T is = F0 * F0;
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
@@ -575,10 +589,12 @@ __device__ __forceinline__ T m2pot_p3(const T* __restrict__ B, T Rx, T Ry, T Rz,
   return fma(F3, S3, fma(F2, S2, fma(F1, S1, F0 * S0)));
 }
 
+template <bool REF = true>
 __device__ __forceinline__ void m2p2_p3(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
                                        float2 eps2, float2& ax, float2& ay, float2& az) {
   const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
-  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 F0 = REF ? make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y))
+                        : make_float2(nbody_rsqrt_pair(s.x), nbody_rsqrt_pair(s.y));
   const float2 is = __fmul2_rn(F0, F0);
   const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
   const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));
@@ -751,11 +767,13 @@ __device__ __forceinline__ void reduce_moments_p3(const double* __restrict__ M, 
   B[23] = -1 * M[19];
 }
 
-template <typename T>
+// REF: the reciprocal square root refined (near-uniform boxes), else the
+// hardware approximation alone
+template <typename T, bool REF = true>
 __device__ __forceinline__ void m2p_p4(const T* __restrict__ B, T Rx, T Ry, T Rz, T eps2,
                                      T& ax, T& ay, T& az) {
   const T s = fma(Rx, Rx, fma(Ry, Ry, fma(Rz, Rz, eps2)));
-  const T F0 = nbody_rsqrt(s);
+  const T F0 = REF ? nbody_rsqrt(s) : nbody_rsqrt_pair(s);
   const T is = F0 * F0;
   const T F1 = F0 * (T(-1) * is);
   const T F2 = F1 * (T(-3) * is);
@@ -1137,10 +1155,12 @@ __device__ __forceinline__ T m2pot_p4(const T* __restrict__ B, T Rx, T Ry, T Rz,
   return fma(F4, S4, fma(F3, S3, fma(F2, S2, fma(F1, S1, F0 * S0))));
 }
 
+template <bool REF = true>
 __device__ __forceinline__ void m2p2_p4(const float2* __restrict__ B, float2 Rx, float2 Ry, float2 Rz,
                                        float2 eps2, float2& ax, float2& ay, float2& az) {
   const float2 s = __ffma2_rn(Rx, Rx, __ffma2_rn(Ry, Ry, __ffma2_rn(Rz, Rz, eps2)));
-  const float2 F0 = make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y));
+  const float2 F0 = REF ? make_float2(nbody_rsqrt(s.x), nbody_rsqrt(s.y))
+                        : make_float2(nbody_rsqrt_pair(s.x), nbody_rsqrt_pair(s.y));
   const float2 is = __fmul2_rn(F0, F0);
   const float2 F1 = __fmul2_rn(F0, __fmul2_rn(make_float2(-1.0f, -1.0f), is));
   const float2 F2 = __fmul2_rn(F1, __fmul2_rn(make_float2(-3.0f, -3.0f), is));

@@ -34,13 +34,14 @@ template <int P> struct WOrd;
   template <> struct WOrd<P> {                                                                        \
     static constexpr int NB = kNB##P;                                                                 \
     static constexpr int NBS = (kNB##P + 3) & ~3;                                                     \
-    template <typename T>                                                                             \
+    template <typename T, bool REF = true>                                                            \
     static __device__ __forceinline__ void m2p(const T* B, T x, T y, T z, T e2, T& ax, T& ay, T& az) { \
-      m2p_p##P<T>(B, x, y, z, e2, ax, ay, az);                                                        \
+      m2p_p##P<T, REF>(B, x, y, z, e2, ax, ay, az);                                                   \
     }                                                                                                 \
+    template <bool REF = true>                                                                        \
     static __device__ __forceinline__ void m2p2(const float2* B, float2 x, float2 y, float2 z, float2 e2, \
                                                 float2& ax, float2& ay, float2& az) {                 \
-      m2p2_p##P(B, x, y, z, e2, ax, ay, az);                                                          \
+      m2p2_p##P<REF>(B, x, y, z, e2, ax, ay, az);                                                     \
     }                                                                                                 \
     template <typename T>                                                                             \
     static __device__ __forceinline__ T pot(const T* B, T x, T y, T z, T e2) {                        \
@@ -329,7 +330,9 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
               const float2 ry = __ffma2_rn(y2, sc, make_float2(m0.y, m1.y));
               const float2 rz = __ffma2_rn(z2, sc, make_float2(m0.z, m1.z));
               float2 tx = make_float2(0.f, 0.f), ty = tx, tz = tx;
-              WOrd<P>::m2p2(&cf[q * NBS], rx, ry, rz, e2, tx, ty, tz);
+              // the refined reciprocal square root where it matters: near-uniform
+              // boxes, i.e. with the uniform-background terms
+              WOrd<P>::template m2p2<decltype(bgc)::value>(&cf[q * NBS], rx, ry, rz, e2, tx, ty, tz);
               // the padding cell of an odd chunk has weight 0 at R = (0, 0, 0) + offset 0: skip it
               if constexpr (decltype(bgc)::value) {
                 const float2 qb = cf[q * NBS + WOrd<P>::NB];
@@ -379,7 +382,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             const V4 mo = s_moff[wid][q];
             const T rx = fma(xi, mo.w, mo.x), ry = fma(yi, mo.w, mo.y), rz = fma(zi, mo.w, mo.z);
             T tx = 0, ty = 0, tz = 0;
-            WOrd<P>::template m2p<T>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q], tx, ty, tz);
+            WOrd<P>::template m2p<T, decltype(bgc)::value>(&s_coef[wid][q * NBS], rx, ry, rz, s_meps[wid][q], tx,
+                                                           ty, tz);
             if constexpr (decltype(bgc)::value)
               WBg<P>::template add<T>(s_coef[wid][q * NBS + WOrd<P>::NB], rx, ry, rz, tx, ty, tz);
             px += tx;

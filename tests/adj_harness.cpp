@@ -11,6 +11,8 @@
 #define __restrict__
 static inline double nbody_rsqrt(double x) { return 1.0 / std::sqrt(x); }
 static inline float nbody_rsqrt(float x) { return 1.0f / std::sqrt(x); }
+static inline double nbody_rsqrt_pair(double x) { return 1.0 / std::sqrt(x); }
+static inline float nbody_rsqrt_pair(float x) { return 1.0f / std::sqrt(x); }
 using std::fma;
 // host stand-ins for the packed FP32 pair operations (per component, round
 // to nearest, as the device instructions are specified)
