@@ -577,19 +577,20 @@ __global__ void __launch_bounds__(128) adj_field_local_kernel(AFArgs<T> a) {
   }
 }
 
-// per run (first group), lane = level-le cell: transposed M2L onto the cells
+// per run (warps step through the list of runs), lane = level-le cell:
+// transposed M2L onto the cells
 template <typename T, int PE>
 __global__ void __launch_bounds__(128) adj_field_m2l_kernel(AFArgs<T> a) {
   constexpr int NL = AFE<PE>::NL, NE = AFE<PE>::NE, NP = AFE<PE>::NP;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
-  const int ngroup = tr.cnt[1];
+  const int nrun = tr.cnt[2];
   const int ncp = 1 << (3 * a.le);
   const int m = (1 << (a.lg - 1)) + 2;
   const int step = 1 << (23 - a.lg);
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrun; r += (gridDim.x * blockDim.x) >> 5) {
+    const int g = tr.runhead[r];
     const int4 ga = tr.gA[g];
-    if (ga.w == 0) continue;
     const int4 gd = tr.gD[g];
     const int box = ga.z;
     const double* Lbr = a.lbar + (int64_t)gd.w * a.bstride;

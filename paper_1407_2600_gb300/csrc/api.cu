@@ -36,7 +36,7 @@ cudaError_t nb_leaves(int ncell, const int* pncell, const int4* cA, const int4* 
 cudaError_t nb_group_flags(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int ls,
                            int n_group, int* flag, cudaStream_t s);
 cudaError_t nb_group_runs(int ngroup, const int* pngroup, int4* gA, int4* gD, int* flag, int* excl, int* total,
-                          int* tmp, cudaStream_t s);
+                          int* tmp, int* runhead, cudaStream_t s);
 cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ngroup, const int* pngroup,
                           int ls, const int* flag, const int* gid, int* gstart, const double* spos, int4* gA,
                           int4* gB, int4* gC, int4* gD, cudaStream_t s);
@@ -51,7 +51,7 @@ cudaError_t nb_box_mass(const int64_t* off, const float* smass, int nbox, double
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, const int* hval,
                              const uint64_t* ckey, const uint16_t* cbox, uint64_t hcap, const double* mom,
-                             int order, double* fm, cudaStream_t s);
+                             int order, double* fm, float* fm32, cudaStream_t s);
 int nb_walk_warps(bool fp64);
 cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, const void* src, const void* eps2,
                     const long long* thr, int n_direct, int le, int* stack, int stack_cap, int max_blocks,
@@ -76,12 +76,12 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
                           int stack_cap, int max_blocks, const double* fm, const void* tab, const void* lbuf,
                           int lstride, int max_level, const float* lam, double* out, const AdjBuffers& B,
                           unsigned* status, int nsm, int mac_edge, int bg, cudaStream_t s);
-cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm, const float* fm32,
                            const void* tab, void* lbuf, cudaStream_t s);
 cudaError_t nb_lattice(const DevTree& tr, bool fp64, int W, const void* accw, float* out, double* out64,
                        const void* potw, float* pout, double* part, double* mom, double* Ld, void* Lt,
                        cudaStream_t s);
-cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm, const float* fm32,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         double* out64, const void* potw, float* pout, cudaStream_t s);
 
@@ -149,7 +149,7 @@ struct nbody_tree {
   uint64_t hcap = 0;
   // groups
   int ngroup = 0;
-  Buf gflag, gid, gstart, gA, gB, gC, gD;
+  Buf gflag, gid, gstart, gA, gB, gC, gD, runhead;
   // image field
   Buf fm;
   Buf rho;  // mean density per box (background terms)
@@ -192,7 +192,7 @@ struct nbody_tree {
     Buf* all[] = {&off, &box_of, &keys, &vals, &keys2, &vals2, &sbox, &spos, &smass, &src, &sleaf,
                   &hist, &sstatus, &tilectr, &status, &ccount, &coff, &l0, &plevel, &pstart, &pcount,
                   &pparent, &bfs2pre, &pre2bfs, &lvlhist, &scantmp, &totals, &cA, &cB, &ckey, &cbox,
-                  &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &fm,
+                  &hval, &mom, &uorder, &coef, &ukey, &urng, &gflag, &gid, &gstart, &gA, &gB, &gC, &gD, &runhead, &fm,
                   &eps2, &stack, &gctr, &accw, &counters, &tot, &lbuf, &rho, &act_s, &act_g, &rungc,
                   &a_lam, &a_mu, &a_nuc, &a_nu, &a_lbar, &a_nue, &a_x0, &a_x1, &a_ph, &a_g, &a_lg,
                   &a_lx, &a_lp, &a_out, &a_xc, &a_lc, &a_muc, &a_eq, &upos, &lscale, &mom32, &potw,
@@ -227,6 +227,7 @@ struct nbody_tree {
     t.gB = gB.as<int4>();
     t.gC = gC.as<int4>();
     t.gD = gD.as<int4>();
+    t.runhead = runhead.as<int>();
     t.sleaf = sleaf.as<int>();
     t.sact = nullptr;
     t.gact = nullptr;
@@ -287,6 +288,13 @@ int validate(const nbody_params* p) {
 
 // image level used by the walk even without periodic images
 int image_level(const nbody_params& p) { return p.ewald_order > 0 ? p.ewald_level : 3; }
+
+// the FP32 copy of the image field's source moments, stored after the FP64 ones
+float* fm32_of(const nbody_tree* t) {
+  const nbody_params& p = t->prm;
+  const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
+  return (float*)(t->fm.as<double>() + (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne);
+}
 int group_level(const nbody_params& p) {
   return (p.ewald_order > 0 || (p.flags & NBODY_FLAG_REPLICAS)) ? p.ewald_grid - 1 : 5;
 }
@@ -580,6 +588,7 @@ int size_cells(nbody_tree* t, int cell_cap, int group_cap) {
   NB_CU(t->gB.ensure(16 * ng));
   NB_CU(t->gC.ensure(16 * ng));
   NB_CU(t->gD.ensure(16 * ng));
+  NB_CU(t->runhead.ensure(4 * ng));
   // scratch of the sorts: the key sort's passes and the one-pass cell sorts
   const int64_t tiles = nb_sort_tiles(t->n) + 1, ctiles = nb_sort_tiles(nc) + 1;
   NB_CU(t->sstatus.ensure(4 * 256 * (tiles * 12 > ctiles ? tiles * 12 : ctiles)));
@@ -701,7 +710,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
                       t->gid.as<int>(), t->gstart.as<int>(), t->spos.as<double>(), t->gA.as<int4>(), t->gB.as<int4>(),
                       t->gC.as<int4>(), t->gD.as<int4>(), s));
   NB_CU(nb_group_runs(ng, totals + 1, t->gA.as<int4>(), t->gD.as<int4>(), t->gflag.as<int>(), t->gid.as<int>(),
-                      totals + 2, t->scantmp.as<int>(), s));
+                      totals + 2, t->scantmp.as<int>(), t->runhead.as<int>(), s));
   if (timed) NB_CU(cudaEventRecord(be[2], s));
   // A5 moments (with the background weights when asked for)
   const double* rho = nullptr;
@@ -718,11 +727,12 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
                   s));
   if (p.ewald_order > 0) {
     const int ne = (p.ewald_order + 1) * (p.ewald_order + 2) * (p.ewald_order + 3) / 6;
-    NB_CU(t->fm.ensure(8 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
+    // FP64 moments, then their FP32 copy
+    NB_CU(t->fm.ensure(12 * (int64_t)t->nbox * (1 << (3 * p.ewald_level)) * ne));
     NB_CU(nb_field_moments(p.ewald_order, p.ewald_level, t->nbox, t->off.as<int64_t>(), t->keys.as<uint64_t>(),
                            t->spos.as<double>(), t->smass.as<float>(), n, t->hval.as<int>(),
                            t->ckey.as<uint64_t>(), t->cbox.as<uint16_t>(), t->hcap, t->mom.as<double>(), p.order,
-                           t->fm.as<double>(), s));
+                           t->fm.as<double>(), fm32_of(t), s));
   }
   if (timed) {
     NB_CU(cudaEventRecord(be[3], s));
@@ -767,7 +777,7 @@ int field_impl(nbody_tree* t, cudaStream_t s) {
   const void* tab = fp64 ? (const void*)t->tab64 : (const void*)t->tab32;
   if (p.ewald_order > 0)
     NB_CU(nb_field_local(t->dev(), fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p,
-                         t->fm.as<double>(), tab, t->lbuf.p, s));
+                         t->fm.as<double>(), fm32_of(t), tab, t->lbuf.p, s));
   t->field_valid = true;
   return NBODY_OK;
 }
@@ -838,7 +848,7 @@ int forces_impl(nbody_tree* t, float* acc, cudaStream_t s, double* acc64 = nullp
     NB_CU(nb_lattice(tr, fp64, repl, t->accw.p, acc, acc64, pot ? t->potw.p : nullptr, pot, t->lat_part.as<double>(),
                      t->lat_mom.as<double>(), t->lat_Ld.as<double>(), t->lat_Lt.p, s));
   else
-    NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), tab,
+    NB_CU(nb_periodic(tr, fp64, p.ewald_order, p.ewald_level, p.ewald_grid, t->src.p, t->fm.as<double>(), fm32_of(t), tab,
                       t->lbuf.p, t->accw.p, acc, ctr + 2, acc64, pot ? t->potw.p : nullptr, pot, s));
   if (timed) NB_CU(cudaEventRecord(fe[2], s));
   accumulate_kernel<<<1, 32, 0, s>>>(ctr, t->tot.as<unsigned long long>());

@@ -314,7 +314,8 @@ __global__ void group_info_kernel(BuildArgs a, const int* __restrict__ pngroup, 
 }
 
 // groups sharing an expansion cell (same box, same level-(grid-1) cell) form
-// a run; gA.w = 1 marks a run's first group, gD.w receives the run index.
+// a run; gA.w = 1 marks a run's first group, gD.w receives the run index and
+// runhead[run] the run's first group.
 // The flags are scanned over the whole capacity, so slots past the count get 0.
 __global__ void run_flag_kernel(int cap, const int* __restrict__ pngroup, int4* __restrict__ gA,
                                 const int4* __restrict__ gD, int* __restrict__ flag) {
@@ -335,10 +336,12 @@ __global__ void run_flag_kernel(int cap, const int* __restrict__ pngroup, int4* 
 }
 
 __global__ void run_index_kernel(const int* __restrict__ pngroup, const int* __restrict__ flag,
-                                 const int* __restrict__ excl, int4* __restrict__ gD) {
+                                 const int* __restrict__ excl, int4* __restrict__ gD, int* __restrict__ runhead) {
   const int ngroup = *pngroup;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x)
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x) {
     gD[g].w = excl[g] + flag[g] - 1;
+    if (flag[g]) runhead[excl[g]] = g;
+  }
 }
 
 // Counts of a build whose buffers were sized beforehand (a reserved capacity):
@@ -480,12 +483,12 @@ cudaError_t nb_leaves(int ncell, const int* pncell, const int4* cA, const int4* 
 }
 
 cudaError_t nb_group_runs(int ngroup, const int* pngroup, int4* gA, int4* gD, int* flag, int* excl, int* total,
-                          int* tmp, cudaStream_t s) {
+                          int* tmp, int* runhead, cudaStream_t s) {
   run_flag_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(ngroup, pngroup, gA, gD, flag);
   nb_launch_counter += 1;
   cudaError_t e = nb_exclusive_scan_i32(flag, excl, ngroup, total, tmp, s);
   if (e) return e;
-  run_index_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(pngroup, flag, excl, gD);
+  run_index_kernel<<<gridn(ngroup, 256), 256, 0, s>>>(pngroup, flag, excl, gD, runhead);
   nb_launch_counter += 1;
   return cudaGetLastError();
 }

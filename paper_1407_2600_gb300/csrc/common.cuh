@@ -21,6 +21,18 @@ constexpr int kDualStride = 36;
 // bounded spin limit for decoupled look-back waits
 #define NB_SPIN_LIMIT (1 << 22)
 
+// The hardware's approximate 1/sqrt(s) with subnormal inputs flushed to zero
+// (PTX rsqrt.approx.ftz.f32).  Every argument here is at least eps^2 or a
+// sum of squares of order one in a cell's unit, far above the subnormal
+// range, so the flush never changes a result; it spares the instructions
+// that the subnormal-preserving form adds around each reciprocal root.  An
+// argument of zero gives +inf either way.
+__device__ __forceinline__ float nb_rsqrt_ftz(float s) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+  return r;
+}
+
 // FP32 1/sqrt(s): the hardware approximation (good to about 2 ulp) refined
 // by one Newton-Raphson step r + r (1 - s r^2)/2 whose residual is formed
 // exactly, r^2 = p + p_lo being an exact FMA two-product, so that only the
@@ -29,7 +41,7 @@ constexpr int kDualStride = 36;
 // hexadecapole order), and on near-uniform boxes far cells' terms cancel to
 // a force a thousand times smaller than their sum.  s > 0 and finite.
 __device__ __forceinline__ float nbody_rsqrt(float s) {
-  const float r = rsqrtf(s);
+  const float r = nb_rsqrt_ftz(s);
   const float p = r * r;
   const float plo = fmaf(r, r, -p);
   const float e = fmaf(-s, plo, fmaf(-s, p, 1.0f));
@@ -39,7 +51,7 @@ __device__ __forceinline__ double nbody_rsqrt(double x) { return rsqrt(x); }
 // the hardware approximation alone, for particle-particle terms: each pair's
 // term is small next to the sum it joins, so the last ulp of 1/sqrt does not
 // show in the result, while one more instruction per pair would
-__device__ __forceinline__ float nbody_rsqrt_pair(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float nbody_rsqrt_pair(float x) { return nb_rsqrt_ftz(x); }
 __device__ __forceinline__ double nbody_rsqrt_pair(double x) { return rsqrt(x); }
 
 struct __align__(32) dbl4 {
@@ -163,7 +175,8 @@ struct DevTree {
   const int4* gA;          // start, count, box, 0
   const int4* gB;          // g2x, g2y, g2z, 0 (box centre, units 2^-23)
   const int4* gC;          // w2x, w2y, w2z, 0 (half widths, units 2^-23)
-  const int4* gD;          // e2x, e2y, e2z, 0 (expansion point, units 2^-23)
+  const int4* gD;          // e2x, e2y, e2z, run (expansion point, units 2^-23)
+  const int* runhead;      // first group of each run of groups sharing e (cnt[2] runs)
   const int* sleaf;        // leaf cell of each sorted particle
   // evaluation of a subset (block steps): per sorted particle and per group
   // a nonzero byte marks the sinks whose accelerations are computed and

@@ -201,6 +201,7 @@ struct PerArgs {
   DevTree tr;
   const typename Vec4<T>::type* src;
   const double* fm;     // field moments (FP64), (box, cell, NE)
+  const float* fm32;    // the same in FP32 (read by the FP32 M2L)
   const T* tab;         // phi~ table, nodes x NP
   int le, lg, pe;
   T* lbuf;              // per run: L (NL), V (3), M_total
@@ -217,19 +218,21 @@ __constant__ unsigned char c_par_mask[kNMMax];  // bit d set: multi-index odd in
 
 // One warp per run of groups sharing an expansion point e: the local
 // expansion of the image field, the background term's V and the total mass.
+// The warps step through the list of runs (not the groups), so that every
+// resident warp has a run to work on.
 template <typename T, int PE>
 __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
   constexpr int NL = PE_<PE>::NL, NE = PE_<PE>::NE, NP = PE_<PE>::NP;
   const int lane = threadIdx.x & 31;
   const DevTree& tr = a.tr;
-  const int ngroup = tr.cnt[1];
+  const int nrun = tr.cnt[2];
   const int ncp = 1 << (3 * a.le);
   const int m = (1 << (a.lg - 1)) + 2;
   const int step = 1 << (23 - a.lg);
   const T scale = (T)(1.0 / 8388608.0);
-  for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrun; r += (gridDim.x * blockDim.x) >> 5) {
+    const int g = tr.runhead[r];
     const int4 ga = tr.gA[g];
-    if (ga.w == 0) continue;  // not the first group of its run
     const int4 gd = tr.gD[g];
     const int box = ga.z;
     T L[NL];
@@ -239,12 +242,19 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
     T l0 = 0, wq = 0;  // potential only: L_0 and sum m |x* - e|^2
     unsigned long long nused = 0;
     for (int cell = lane; cell < ncp; cell += 32) {
-      const double* Mc = a.fm + ((int64_t)box * ncp + cell) * NE;
-      if (Mc[0] == 0.0) continue;
-      nused++;
       T M[NE];
+      if constexpr (sizeof(T) == 4) {
+        const float* Mc = a.fm32 + ((int64_t)box * ncp + cell) * NE;
+        if (Mc[0] == 0.f) continue;
 #pragma unroll
-      for (int t = 0; t < NE; t++) M[t] = (T)Mc[t];
+        for (int t = 0; t < NE; t++) M[t] = Mc[t];
+      } else {
+        const double* Mc = a.fm + ((int64_t)box * ncp + cell) * NE;
+        if (Mc[0] == 0.0) continue;
+#pragma unroll
+        for (int t = 0; t < NE; t++) M[t] = Mc[t];
+      }
+      nused++;
       const int cx2 = cell_c2((int)compact3((uint64_t)cell), a.le);
       const int cy2 = cell_c2((int)compact3((uint64_t)cell >> 1), a.le);
       const int cz2 = cell_c2((int)compact3((uint64_t)cell >> 2), a.le);
@@ -638,6 +648,7 @@ int nb_field_stride(int pe) {
 }
 
 cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+                        const float* fm32,
                         const void* tab, void* lbuf, const void* accw, float* out, unsigned long long* counter,
                         double* out64, const void* potw, float* pout, cudaStream_t s) {
   if (pe == 0 && potw) {
@@ -663,7 +674,7 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
   const int ls = nb_field_stride(pe);
 #define NB_PER(TT, PE)                                                                              \
   {                                                                                                 \
-    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
+    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, fm32, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
                   (const TT*)accw, out, counter, out64, (const TT*)potw, pout};                     \
     field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     field_l2p_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
@@ -694,6 +705,7 @@ cudaError_t nb_periodic(const DevTree& tr, bool fp64, int pe, int le, int lg, co
 // Local expansions of the image field only (one per run of groups), for the
 // reverse mode, which needs them without evaluating the forces.
 cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg, const void* src, const double* fm,
+                           const float* fm32,
                            const void* tab, void* lbuf, cudaStream_t s) {
   if (pe == 0) return cudaSuccess;
   int grid = (int)(((int64_t)tr.ngroup * 32 + 127) / 128);
@@ -702,7 +714,7 @@ cudaError_t nb_field_local(const DevTree& tr, bool fp64, int pe, int le, int lg,
   const int ls = nb_field_stride(pe);
 #define NB_LOC(TT, PE)                                                                              \
   {                                                                                                 \
-    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
+    PerArgs<TT> a{tr, (const typename Vec4<TT>::type*)src, fm, fm32, (const TT*)tab, le, lg, pe, (TT*)lbuf, ls, \
                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};                            \
     field_m2l_kernel<TT, PE><<<grid, 128, 0, s>>>(a);                                               \
     break;                                                                                          \

@@ -240,7 +240,9 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
 // prefix is a cell of the tree and the tree's moments reach order PE, they are
 // the same moments (about the same centre, over the same particles): they are
 // copied; otherwise (a prefix inside a leaf, or a lower tree order) they are
-// formed from the prefix's particles.
+// formed from the prefix's particles.  An FP32 copy (fm32, same layout) feeds
+// the mixed-precision image-field M2L, which would otherwise convert every
+// moment from FP64 once per run on GB300's narrow FP64 pipe.
 struct TreeMoments {
   const int* hval;
   const uint64_t* ckey;
@@ -254,7 +256,7 @@ template <int PE>
 __global__ void __launch_bounds__(256)
 field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __restrict__ skeys,
                      const double* __restrict__ spos, const float* __restrict__ smass, int64_t n,
-                     TreeMoments tm, double* __restrict__ fm) {
+                     TreeMoments tm, double* __restrict__ fm, float* __restrict__ fm32) {
   constexpr int NM = (PE + 1) * (PE + 2) * (PE + 3) / 6;
   const int ncp = 1 << (3 * le);
   const int box = blockIdx.y;
@@ -267,7 +269,12 @@ field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __
   __syncthreads();
   if (s_tc >= 0) {
     double* dst = fm + ((int64_t)box * ncp + cell) * NM;
-    for (int t = threadIdx.x; t < NM; t += blockDim.x) dst[t] = tm.mom[(int64_t)s_tc * tm.nm + t];
+    float* d32 = fm32 + ((int64_t)box * ncp + cell) * NM;
+    for (int t = threadIdx.x; t < NM; t += blockDim.x) {
+      const double v = tm.mom[(int64_t)s_tc * tm.nm + t];
+      dst[t] = v;
+      d32[t] = (float)v;
+    }
     return;
   }
   __shared__ int64_t s_rng[2];
@@ -316,10 +323,12 @@ field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __
   }
   __syncthreads();
   double* dst = fm + ((int64_t)box * ncp + cell) * NM;
+  float* d32 = fm32 + ((int64_t)box * ncp + cell) * NM;
   for (int t = threadIdx.x; t < NM; t += blockDim.x) {
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += s_red[w][t];
     dst[t] = v;
+    d32[t] = (float)v;
   }
 }
 
@@ -419,15 +428,15 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const 
 cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const uint64_t* skeys,
                              const double* spos, const float* smass, int64_t n, const int* hval,
                              const uint64_t* ckey, const uint16_t* cbox, uint64_t hcap, const double* mom,
-                             int order, double* fm, cudaStream_t s) {
+                             int order, double* fm, float* fm32, cudaStream_t s) {
   dim3 g(1u << (3 * le), nbox);
   const TreeMoments tm{hval, ckey, cbox, hcap - 1, mom, (order + 1) * (order + 2) * (order + 3) / 6};
   switch (pe) {
-    case 1: field_moments_kernel<1><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
-    case 2: field_moments_kernel<2><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
-    case 3: field_moments_kernel<3><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
-    case 4: field_moments_kernel<4><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
-    default: field_moments_kernel<5><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm); break;
+    case 1: field_moments_kernel<1><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm, fm32); break;
+    case 2: field_moments_kernel<2><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm, fm32); break;
+    case 3: field_moments_kernel<3><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm, fm32); break;
+    case 4: field_moments_kernel<4><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm, fm32); break;
+    default: field_moments_kernel<5><<<g, 256, 0, s>>>(le, off, skeys, spos, smass, n, tm, fm, fm32); break;
   }
   nb_launch_counter += 1;
   return cudaGetLastError();

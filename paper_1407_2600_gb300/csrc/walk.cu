@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       for (int k = 0; k < 6; k++) s_df[wid][k][lane] = 0.f;
     unsigned long long n_p2p = 0, n_m2p = 0, n_m2l = 0;
     int qn = 0;  // queued M2P cells
+    int pcar = 0;  // P2P sources staged but not yet summed (carried to the next pop)
     int ln = 0;  // queued cell-group (M2L) cells
     constexpr bool DUAL = DUALK && DF && WDual<P>::has;
     int lprev = -1;  // this group's last emitted chunk of cell-group pairs
@@ -499,9 +500,13 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           __syncwarp();
         }
       }
-      // P2P chunks
+      // P2P chunks.  This pop's sources join the ones carried over from
+      // earlier pops (already staged at positions 0..pcar-1 of s_src), and
+      // until the stack is empty only full chunks of 32 are summed, so that
+      // nearly every chunk is full; the rest stays staged for the next pop.
+      const bool fin = top == 0;
       const unsigned pm = __ballot_sync(FULL, cls == 3);
-      if (pm) {
+      if (pm || (fin && pcar > 0)) {
         const int ncl = (cls == 3) ? cb.y : 0;
         const int pre = warp_excl_scan(ncl, lane);
         const int total = __shfl_sync(FULL, pre + ncl, 31);
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           V4 v;
           v.x = v.y = v.z = v.w = (T)0;
           jo = -1;
-          if (t < total) {
+          if (t >= 0 && t < total) {
             // last P2P lane q with pfx[q] <= t
             int lo = 0, hi = 31;
             while (lo < hi) {
@@ -548,26 +553,33 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
           }
           return v;
         };
-        // the next chunk's sources are fetched while this chunk is summed
+        // combined position k = b0 + lane: the carried sources, then source
+        // k - pcar of this pop; the next chunk's sources are fetched while
+        // this chunk is summed
+        const int pc0 = pcar, avail = pc0 + total;
+        pcar = fin ? 0 : (avail & 31);
         int jv = -1, jnext = -1;
-        V4 v = fetch(lane, jv);
-        for (int b0 = 0; b0 < total; b0 += 32) {
-          if constexpr (PK) {
-            // pairs of sources interleaved: (x0, x1, y0, y1) then (z0, z1, m0, m1)
-            float* pa = reinterpret_cast<float*>(&s_src[wid][0]);
-            float* pb = reinterpret_cast<float*>(&s_src[wid][16]);
-            const int pr = lane >> 1, hf = lane & 1;
-            pa[4 * pr + hf] = v.x;
-            pa[4 * pr + 2 + hf] = v.y;
-            pb[4 * pr + hf] = v.z;
-            pb[4 * pr + 2 + hf] = v.w;
-          } else {
-            s_src[wid][lane] = v;
-            if constexpr (POTK) s_sj[wid][lane] = jv;
+        V4 v = fetch(lane - pc0, jv);
+        for (int b0 = 0; b0 < avail; b0 += 32) {
+          if (b0 > 0 || lane >= pc0) {  // a carried source stays where it is
+            if constexpr (PK) {
+              // pairs of sources interleaved: (x0, x1, y0, y1) then (z0, z1, m0, m1)
+              float* pa = reinterpret_cast<float*>(&s_src[wid][0]);
+              float* pb = reinterpret_cast<float*>(&s_src[wid][16]);
+              const int pr = lane >> 1, hf = lane & 1;
+              pa[4 * pr + hf] = v.x;
+              pa[4 * pr + 2 + hf] = v.y;
+              pb[4 * pr + hf] = v.z;
+              pb[4 * pr + 2 + hf] = v.w;
+            } else {
+              s_src[wid][lane] = v;
+              if constexpr (POTK) s_sj[wid][lane] = jv;
+            }
           }
           __syncwarp();
-          const int nn = min(32, total - b0);
-          const V4 vnext = fetch(b0 + 32 + lane, jnext);
+          const int nn = min(32, avail - b0);
+          if (nn < 32 && !fin) break;  // a partial chunk waits for the next pop's sources
+          const V4 vnext = fetch(b0 + 32 + lane - pc0, jnext);
           // pair factor f of a = m d f: Plummer (r^2 + eps^2)^(-3/2), or the
           // K1 kernel, Newtonian from eps on and (175/16 - (147/8) x^2 +
           // (135/16) x^4)/eps^3 inside (x = r/eps: the enclosed mass of its
@@ -651,7 +663,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       }
       // evaluate queued cells 32 at a time, and what is left once the stack
       // is empty (up to two chunks then: the queue holds up to 63)
-      const bool fin = top == 0;
       while (qn >= 32 || (fin && qn > 0)) {
         const int k = min(qn, 32);
         __syncwarp();
@@ -740,15 +751,31 @@ __global__ void __launch_bounds__(256) dual_m2l_kernel(DualArgs a) {
   const int nchunk = min(*a.db.ctr, a.db.cap);
   const float scale = 1.f / 8388608.f;  // 2^-23
   float* buf = s_buf[wid];
-  for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunk; c += (gridDim.x * blockDim.x) >> 5) {
-    const int4 hd = a.db.head[c];
+  const int stride = (gridDim.x * blockDim.x) >> 5;
+  // the next chunk's header and pair slots are loaded while this chunk is
+  // formed (slots past the chunk's count are read but not used)
+  int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int4 hd_n = make_int4(0, 0, 0, 0);
+  int cell_n = 0, code_n = 0;
+  if (c < nchunk) {
+    hd_n = a.db.head[c];
+    cell_n = a.db.cell[(int64_t)c * 32 + lane];
+    code_n = a.db.img[(int64_t)c * 32 + lane];
+  }
+  for (; c < nchunk; c += stride) {
+    const int4 hd = hd_n;
     const int g = hd.x, nml = hd.y;
+    const float live = lane < nml ? 1.f : 0.f;
+    // a slot past the count takes pair 0's cell (always valid), weight 0
+    const int cell = __shfl_sync(0xffffffffu, cell_n, lane < nml ? lane : 0);
+    const int code = __shfl_sync(0xffffffffu, code_n, lane < nml ? lane : 0);
+    if (c + stride < nchunk) {
+      hd_n = a.db.head[c + stride];
+      cell_n = a.db.cell[(int64_t)(c + stride) * 32 + lane];
+      code_n = a.db.img[(int64_t)(c + stride) * 32 + lane];
+    }
     const int4 gb = tr.gB[g];
     const int box = tr.gA[g].z;
-    const int q = lane < nml ? lane : 0;
-    const float live = lane < nml ? 1.f : 0.f;
-    const int cell = a.db.cell[(int64_t)c * 32 + q];
-    const int code = a.db.img[(int64_t)c * 32 + q];
     const int kx = (code & 7) - 2, ky = ((code >> 3) & 7) - 2, kz = ((code >> 6) & 7) - 2;
     const int4 ca = tr.cA[cell];
     const int lvl = ca.w & 0xff;

@@ -65,7 +65,7 @@ __device__ __forceinline__ void mono_df(float x, float y, float z, float sc, flo
   float shi, slo;
   fast_two_sum(s3, ((t1 + t2) + t3) + ((pe[0] + pe[1]) + pe[2]), shi, slo);
   // r = s^(-1/2): one Newton step from the hardware value, residual exact
-  const float r0 = rsqrtf(shi);
+  const float r0 = nb_rsqrt_ftz(shi);
   const float q = r0 * r0, ql = fmaf(r0, r0, -q);
   float res = fmaf(-shi, q, 1.f);
   res = fmaf(-shi, ql, res);
