@@ -85,6 +85,16 @@ __device__ __forceinline__ void mono_df(float x, float y, float z, float sc, flo
   }
 }
 
+// 16-byte asynchronous copy from global to shared memory (PTX cp.async,
+// cached in L1 and L2); both addresses 16-byte aligned.  The copies a thread
+// issued are complete and visible to it after cp_async_wait_all.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ int warp_excl_scan(int v, int lane) {
   int x = v;
 #pragma unroll
