@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnbody.so")
+# the debug build: every NB_IN bounds check compiled in (tests only)
+BUILD_DBG = os.path.join(HERE, "_build_dbg")
+LIB_DBG = os.path.join(HERE, "libnbody_dbg.so")
 UNITS = ["sort.cu", "build.cu", "upward.cu", "walk.cu", "periodic.cu", "adjoint.cu", "cic.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -42,8 +45,11 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > mt for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug_bounds: bool = False) -> str:
+    """Compile the library (``debug_bounds``: the bounds-checked debug library
+    libnbody_dbg.so, objects under _build_dbg) and return its path."""
+    build_dir, lib_path = (BUILD_DBG, LIB_DBG) if debug_bounds else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "nbody.h"))
     exe = nvcc()
@@ -51,10 +57,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     objs = []
     for u in UNITS:
         src = os.path.join(CSRC, u)
-        obj = os.path.join(BUILD, u.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, u.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            extra = ["-Xptxas", "-v"] if ptxas_info else []
+            extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DNB_DEBUG_BOUNDS"] if debug_bounds else [])
             jobs.append([exe] + _flags(extra) + ["-c", src, "-o", obj])
 
     def run(cmd):
@@ -68,14 +74,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     sys.stderr.write(r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         cmd = [exe] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -128,8 +128,8 @@ __device__ __forceinline__ bool adj_walk_group(const DevTree& tr, int box, const
     int4 ca = make_int4(0, 0, 0, 0), cb = make_int4(0, 0, 0, 0);
     if (lane < nb) {
       c = stk[base + lane];
-      ca = tr.cA[c];
-      cb = tr.cB[c];
+      ca = tr.cA[NB_IDX(c, tr.cnt[0], 601)];
+      cb = tr.cB[NB_IDX(c, tr.cnt[0], 601)];
     }
     __syncwarp();
     int cls = NB_CELL_NONE, kx = 0, ky = 0, kz = 0;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
         sy += __shfl_sync(FULL, wy, from);
         sz += __shfl_sync(FULL, wz, from);
       }
-      if (lane < nn) {
+      if (lane < nn && NB_IN(s_jidx[wid][lane], tr.n, 602)) {
         const int j = s_jidx[wid][lane];
         atomicAdd(&w.mu[j], (double)sx);
         atomicAdd(&w.mu[tr.n + j], (double)sy);
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
             if (s_pfx[wid][mid] <= t) lo = mid; else hi = mid - 1;
           }
           const int q = lo;
-          const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
+          const int j = NB_IDX(s_pst[wid][q] + (t - s_pfx[wid][q]), (int)tr.n, 603);
           V4 v = w.src[j];
           T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
           if (s_plev[wid][q] < w.le) {
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_sink_kernel(AdjArgs<floa
       continue;
     }
     if (qp > 0) p2p_chunk(qp);
-    if (act) {
+    if (act && NB_IN(i, tr.n, 604)) {
       atomicAdd(&w.mu[i], (double)mx);
       atomicAdd(&w.mu[tr.n + i], (double)my);
       atomicAdd(&w.mu[2 * tr.n + i], (double)mz);
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) adj_src_kernel(AdjArgs<float
           AOrd<P>::template src<T>(fma(x.x, mo.w, mo.x), fma(x.y, mo.w, mo.y), fma(x.z, mo.w, mo.z), e2, l.x,
                                    l.y, l.z, nu);
         }
-        float4* dst = reinterpret_cast<float4*>(w.nuc + (int64_t)s_midx[wid][lane] * NMP);
+        float4* dst = reinterpret_cast<float4*>(w.nuc + (int64_t)NB_IDX(s_midx[wid][lane], tr.cnt[0], 605) * NMP);
 #pragma unroll
         for (int t = 0; t < NMP / 4; t++) atomicAdd(dst + t, make_float4(nu[4 * t], nu[4 * t + 1], nu[4 * t + 2], nu[4 * t + 3]));
       }
@@ -953,3 +953,6 @@ cudaError_t nb_forces_vjp(const DevTree& tr, bool fp64, int order, int pe, int l
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
+
+// fault word of the debug build's bounds checks in this unit (debug build only)
+NB_DBG_EXPORT(adjoint)

@@ -143,7 +143,7 @@ __global__ void emit_cells_kernel(BuildArgs a, const int* __restrict__ ccount, c
       if (t > 0) par = p - 1;
       else if (l == 0) par = -1;
       else {
-        int64_t s = lower_pref_to(a.skeys, bb, i, prefix_of(k, l - 1), l - 1);
+        int64_t s = NB_IDX(lower_pref_to(a.skeys, bb, i, prefix_of(k, l - 1), l - 1), a.n, 301);
         par = coff[s] + (l - 1 - (int)l0in[s]);
       }
       pparent[p] = par;
@@ -155,7 +155,7 @@ __global__ void bfs_fill_kernel(BuildArgs a, const int* __restrict__ pncell, con
                                 int* __restrict__ pre2bfs) {
   const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x)
-    pre2bfs[bfs2pre[b]] = b;
+    if (NB_IN(bfs2pre[b], ncell, 303)) pre2bfs[bfs2pre[b]] = b;
 }
 
 __global__ void bfs_cells_kernel(BuildArgs a, const int* __restrict__ pncell, const uint32_t* __restrict__ bfs2pre,
@@ -166,14 +166,14 @@ __global__ void bfs_cells_kernel(BuildArgs a, const int* __restrict__ pncell, co
                                  uint16_t* __restrict__ cbox) {
   const int ncell = *pncell;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
-    int p = bfs2pre[b];
+    int p = NB_IDX((int)bfs2pre[b], ncell, 304);
     int l = plevel[p];
-    int s = pstart[p];
+    int s = NB_IDX(pstart[p], (int)a.n, 305);
     uint64_t pre = prefix_of(a.skeys[s], l);
     int ix = (int)compact3(pre), iy = (int)compact3(pre >> 1), iz = (int)compact3(pre >> 2);
     cA[b] = make_int4(cell_c2(ix, l), cell_c2(iy, l), cell_c2(iz, l), l);
     int par = pparent[p];
-    cB[b] = make_int4(s, pcount[p], 0, par >= 0 ? pre2bfs[par] : -1);
+    cB[b] = make_int4(s, pcount[p], 0, par >= 0 ? pre2bfs[NB_IDX(par, ncell, 302)] : -1);
     ckey[b] = (1ull << (3 * l)) | pre;
     cbox[b] = a.sbox[s];
   }
@@ -185,7 +185,7 @@ __global__ void children_kernel(const int* __restrict__ pncell, int4* __restrict
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ncell; b += gridDim.x * blockDim.x) {
     int par = cB[b].w;
     if (par < 0) continue;
-    if (b == 0 || cB[b - 1].w != par) cB[par].z = b;  // first daughter
+    if ((b == 0 || cB[b - 1].w != par) && NB_IN(par, ncell, 306)) cB[par].z = b;  // first daughter
   }
 }
 
@@ -195,7 +195,7 @@ __global__ void nchild_kernel(const int* __restrict__ pncell, int4* __restrict__
     int par = cB[b].w;
     if (par < 0) continue;
     bool last = (b == ncell - 1) || (cB[b + 1].w != par);
-    if (last) {
+    if (last && NB_IN(par, ncell, 307)) {
       int nch = b - cB[par].z + 1;
       cA[par].w = (cA[par].w & 0xff) | (nch << 8);
     }
@@ -245,6 +245,7 @@ __global__ void leaf_kernel(const int* __restrict__ pncell, const int4* __restri
     int4 r = cB[b];
     const double cx = i2d_pow2(a.x, -23), cy = i2d_pow2(a.y, -23), cz = i2d_pow2(a.z, -23);
     for (int j = r.x; j < r.x + r.y; j++) {
+      if (!NB_IN(j, n, 309)) break;
       sleaf[j] = b;
       typename Vec4<T>::type v;
       v.x = (T)(spos[j] - cx);
@@ -273,7 +274,7 @@ __global__ void group_start_kernel(int64_t n, const int* __restrict__ flag, cons
   const int ngroup = *pngroup;  // 0 when the count exceeded the buffers' capacity
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (flag[i] && gid[i] < ngroup) gstart[gid[i]] = (int)i;
+    if (flag[i] && gid[i] < ngroup && NB_IN(gid[i], ngroup, 310)) gstart[gid[i]] = (int)i;
 }
 
 // one warp per group: count, box, integer bounding box and expansion point
@@ -289,7 +290,7 @@ __global__ void group_info_kernel(BuildArgs a, const int* __restrict__ pngroup, 
     int e = (g + 1 < ngroup) ? gstart[g + 1] : (int)a.n;
     int cnt = e - s;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    if (lane < cnt) {
+    if (lane < cnt && NB_IN(s + lane, a.n, 311)) {
       int i = s + lane;
       for (int d = 0; d < 3; d++) {
         int q = (int)quant21(spos[d * a.n + i]);
@@ -302,7 +303,7 @@ __global__ void group_info_kernel(BuildArgs a, const int* __restrict__ pngroup, 
         lo[d] = min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
         hi[d] = max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
       }
-    if (lane == 0) {
+    if (lane == 0 && NB_IN(s, a.n, 311)) {
       uint64_t P = prefix_of(a.skeys[s], ls);
       int ix = (int)compact3(P), iy = (int)compact3(P >> 1), iz = (int)compact3(P >> 2);
       gA[g] = make_int4(s, cnt, a.sbox[s], 0);
@@ -340,7 +341,7 @@ __global__ void run_index_kernel(const int* __restrict__ pngroup, const int* __r
   const int ngroup = *pngroup;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += gridDim.x * blockDim.x) {
     gD[g].w = excl[g] + flag[g] - 1;
-    if (flag[g]) runhead[excl[g]] = g;
+    if (flag[g] && NB_IN(excl[g], ngroup, 312)) runhead[excl[g]] = g;
   }
 }
 
@@ -368,7 +369,7 @@ __global__ void gather_kernel(const double* __restrict__ pos, const float* __res
                               float* __restrict__ smass, unsigned* __restrict__ status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t j = perm[i];
+    uint32_t j = NB_IDX(perm[i], (uint32_t)n, 313);
     bool bad = false;
     for (int d = 0; d < 3; d++) {
       double x = pos[d * n + j];
@@ -393,7 +394,7 @@ __global__ void sbox_kernel(const uint32_t* __restrict__ perm, const uint16_t* _
                             int64_t n, uint16_t* __restrict__ sbox) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    sbox[i] = box_of[perm[i]];
+    sbox[i] = box_of[NB_IDX(perm[i], (uint32_t)n, 314)];
 }
 
 int gridn(int64_t n, int threads) {
@@ -511,3 +512,6 @@ cudaError_t nb_group_info(const uint64_t* skeys, const uint16_t* sbox, int64_t n
   nb_launch_counter += 2;
   return cudaGetLastError();
 }
+
+// fault word of the debug build's bounds checks in this unit (debug build only)
+NB_DBG_EXPORT(build)

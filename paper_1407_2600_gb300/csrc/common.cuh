@@ -11,6 +11,40 @@
 #define NB_PBOX (1 << 23)      // one box in integer units of 2^-23
 #define NB_MAX_NBOX 65535
 
+// Bounds checks of the debug build (compiled with -DNB_DEBUG_BOUNDS into
+// libnbody_dbg.so; the product library is built without them).
+// NB_IN(i, n, site) is true when 0 <= i < n.  Otherwise it records the first
+// failing check of this translation unit, (site << 48) | (i & (2^48 - 1)), in
+// the unit's fault word and returns false, and the caller skips the access,
+// so that a bad index is reported instead of read or written.  Each unit
+// exports its word through nbody_dbg_fault_<unit> (NB_DBG_EXPORT); without
+// NB_DEBUG_BOUNDS the check is the constant true and compiles away.
+#ifdef NB_DEBUG_BOUNDS
+static __device__ unsigned long long nb_dbg_fault;
+__device__ __forceinline__ bool nb_in(long long i, long long n, unsigned site) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&nb_dbg_fault, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)i & 0xffffffffffffull));
+  return false;
+}
+#define NB_IN(i, n, site) nb_in((long long)(i), (long long)(n), (unsigned)(site))
+// an index to read at: i when the check passes, else 0 (n > 0 wherever used)
+#define NB_IDX(i, n, site) (NB_IN(i, n, site) ? (i) : 0)
+// fault word of this unit to *out (0: no check failed); reset clears it
+#define NB_DBG_EXPORT(unit)                                                                   \
+  extern "C" int nbody_dbg_fault_##unit(unsigned long long* out, int reset) {                \
+    cudaError_t e = cudaMemcpyFromSymbol(out, nb_dbg_fault, sizeof(unsigned long long));     \
+    if (e == cudaSuccess && reset) {                                                          \
+      const unsigned long long z = 0;                                                         \
+      e = cudaMemcpyToSymbol(nb_dbg_fault, &z, sizeof(z));                                    \
+    }                                                                                         \
+    return (int)e;                                                                            \
+  }
+#else
+#define NB_IN(i, n, site) true
+#define NB_IDX(i, n, site) (i)
+#define NB_DBG_EXPORT(unit)
+#endif
+
 // device status bits (OR-ed into the tree's status word)
 // floats per cell of the FP32 cell-unit moments of the dual form (orders <= 4)
 constexpr int kDualStride = 36;

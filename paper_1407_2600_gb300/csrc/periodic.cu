@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
   const int step = 1 << (23 - a.lg);
   const T scale = (T)(1.0 / 8388608.0);
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrun; r += (gridDim.x * blockDim.x) >> 5) {
-    const int g = tr.runhead[r];
+    const int g = NB_IDX(tr.runhead[r], tr.cnt[1], 501);
     const int4 ga = tr.gA[g];
     const int4 gd = tr.gD[g];
     const int box = ga.z;
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
       // R0 = e - c* on the lattice
       const int irx = -ox / step, iry = -oy / step, irz = -oz / step;
       const int neg = (irx < 0 ? 1 : 0) | (iry < 0 ? 2 : 0) | (irz < 0 ? 4 : 0);
-      const int node = (abs(irx) * m + abs(iry)) * m + abs(irz);
+      const int node = NB_IDX((abs(irx) * m + abs(iry)) * m + abs(irz), m * m * m, 502);
       const T* src = a.tab + (int64_t)node * NP;
       T D[NP];
 #pragma unroll
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(128) field_m2l_kernel(PerArgs<T> a) {
         wq += __shfl_xor_sync(0xffffffffu, wq, o);
       }
     }
-    T* dst = a.lbuf + (int64_t)gd.w * a.lstride;
+    T* dst = a.lbuf + (int64_t)NB_IDX(gd.w, tr.ngroup, 503) * a.lstride;
     for (int t = lane; t < NL; t += 32) {
       T v = L[0];
 #pragma unroll
@@ -337,16 +337,16 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
   for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ngroup; g += (gridDim.x * blockDim.x) >> 5) {
     if (tr.gact && !tr.gact[g]) continue;
     const int4 ga = tr.gA[g], gd = tr.gD[g];
-    if (lane >= ga.y) continue;
+    if (lane >= ga.y || !NB_IN(ga.x + lane, tr.n, 504)) continue;
     if (tr.sact && !tr.sact[ga.x + lane]) continue;
-    const T* Lr = a.lbuf + (int64_t)gd.w * a.lstride;
+    const T* Lr = a.lbuf + (int64_t)NB_IDX(gd.w, tr.ngroup, 503) * a.lstride;
     T L[NL];
 #pragma unroll
     for (int t = 0; t < NL; t++) L[t] = Lr[t];
     const T vx = Lr[NL], vy = Lr[NL + 1], vz = Lr[NL + 2], mt = Lr[NL + 3];
     const int i = ga.x + lane;
     const V4 o4 = a.src[i];
-    const int4 la = tr.cA[tr.sleaf[i]];
+    const int4 la = tr.cA[NB_IDX(tr.sleaf[i], tr.cnt[0], 505)];
     const T dx = o4.x + (T)(la.x - gd.x) * scale;
     const T dy = o4.y + (T)(la.y - gd.y) * scale;
     const T dz = o4.z + (T)(la.z - gd.z) * scale;
@@ -355,6 +355,7 @@ __global__ void __launch_bounds__(128) field_l2p_kernel(PerArgs<T> a) {
     T az = a.accw[2 * tr.n + i] + fourpi3 * (mt * dz - vz);
     PE_<PE>::template l2p<T>(L, dx, dy, dz, ax, ay, az);
     const uint32_t j = tr.perm[i];
+    if (!NB_IN(j, tr.n, 506)) continue;
     if (a.potw) {
       // walk + image series + the background's -(2 pi/3) sum m |x - x*|^2
       const T d2 = fma(dx, dx, fma(dy, dy, dz * dz));
@@ -381,6 +382,7 @@ __global__ void scatter_kernel(int64_t n, const uint32_t* __restrict__ perm, con
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (sact && !sact[i]) continue;
     const uint32_t j = perm[i];
+    if (!NB_IN(j, n, 507)) continue;
     out[j] = (O)accw[i];
     out[n + j] = (O)accw[n + i];
     out[2 * n + j] = (O)accw[2 * n + i];
@@ -392,7 +394,7 @@ template <typename T>
 __global__ void scatter_pot_kernel(int64_t n, const uint32_t* __restrict__ perm, const T* __restrict__ potw,
                                    float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[perm[i]] = (float)potw[i];
+    if (NB_IN(perm[i], n, 507)) out[perm[i]] = (float)potw[i];
 }
 
 // ---- the near-replica scheme's far lattice --------------------------------------------
@@ -525,11 +527,12 @@ __global__ void lattice_l2p_kernel(DevTree tr, const T* __restrict__ Lt, const T
                                    float* __restrict__ pout) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tr.n; i += (int64_t)gridDim.x * blockDim.x) {
     if (tr.sact && !tr.sact[i]) continue;
-    const T* L = Lt + (int64_t)tr.sbox[i] * kNF;
+    const T* L = Lt + (int64_t)NB_IDX((int)tr.sbox[i], tr.nbox, 508) * kNF;
     const T dx = (T)(tr.spos[i] - 0.5), dy = (T)(tr.spos[tr.n + i] - 0.5), dz = (T)(tr.spos[2 * tr.n + i] - 0.5);
     T ax = accw[i], ay = accw[tr.n + i], az = accw[2 * tr.n + i];
     l2p_pe7<T>(L + 1, dx, dy, dz, ax, ay, az);
     const uint32_t j = tr.perm[i];
+    if (!NB_IN(j, tr.n, 506)) continue;
     if (out64) {
       out64[j] = (double)ax;
       out64[tr.n + j] = (double)ay;
@@ -822,3 +825,6 @@ cudaError_t nb_lattice(const DevTree& tr, bool fp64, int W, const void* accw, fl
   nb_launch_counter += 3;
   return cudaGetLastError();
 }
+
+// fault word of the debug build's bounds checks in this unit (debug build only)
+NB_DBG_EXPORT(periodic)

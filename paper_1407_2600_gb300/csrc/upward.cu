@@ -71,6 +71,7 @@ struct BgArgs {
   float* mom32;          // nullptr, or the cells' moments in their own unit
                          // M_n h^-|n| in FP32 (kDualStride per cell), for
                          // the cell-group local expansions of the dual form
+  const int* pncell;     // the build's cell count (bounds of the debug build)
 };
 
 template <int P, typename T>
@@ -139,15 +140,17 @@ leaf_moments_kernel(const uint32_t* __restrict__ order, const int* __restrict__ 
   constexpr int NM = Ord<P>::NM;
   const int nleaf = r[0];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nleaf; i += gridDim.x * blockDim.x) {
-    const int b = (int)order[i];
+    const int b = NB_IDX((int)order[i], *bg.pncell, 401);
     const int4 a = cA[b];
     const int4 rg = cB[b];
     double M[NM];
 #pragma unroll
     for (int t = 0; t < NM; t++) M[t] = 0.0;
     const double cx = i2d_pow2(a.x, -23), cy = i2d_pow2(a.y, -23), cz = i2d_pow2(a.z, -23);
-    for (int j = rg.x; j < rg.x + rg.y; j++)
+    for (int j = rg.x; j < rg.x + rg.y; j++) {
+      if (!NB_IN(j, n, 402)) break;
       Ord<P>::p2m((double)smass[j], spos[j] - cx, spos[n + j] - cy, spos[2 * n + j] - cz, M);
+    }
     double* dst = mom + (int64_t)b * NM;
 #pragma unroll
     for (int t = 0; t < NM; t++) dst[t] = M[t];
@@ -179,7 +182,7 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
       int b = -1, first = 0, nch = 0;
       int4 pa = make_int4(0, 0, 0, 0);
       if (i < hi) {
-        b = (int)order[i];
+        b = NB_IDX((int)order[i], *bg.pncell, 403);
         pa = cA[b];
         first = cB[b].z;
         nch = pa.w >> 8;
@@ -188,7 +191,7 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
 #pragma unroll
       for (int t = 0; t < NM; t++) M[t] = 0.0;
       if (d < nch) {
-        const int ch = first + d;
+        const int ch = NB_IDX(first + d, *bg.pncell, 404);
         const int4 ca = cA[ch];
         double Mc[NM];
         const double* src = mom + (int64_t)ch * NM;
@@ -215,13 +218,14 @@ level_moments_kernel(int j, const uint32_t* __restrict__ order, const int* __res
     return;
   }
   for (int i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += gridDim.x * blockDim.x) {
-    const int b = (int)order[i];
+    const int b = NB_IDX((int)order[i], *bg.pncell, 403);
     const int4 pa = cA[b];
     const int first = cB[b].z, nch = pa.w >> 8;
     double M[NM];
 #pragma unroll
     for (int t = 0; t < NM; t++) M[t] = 0.0;
     for (int ch = first; ch < first + nch; ch++) {
+      if (!NB_IN(ch, *bg.pncell, 404)) break;
       const int4 ca = cA[ch];
       double Mc[NM];
       const double* src = mom + (int64_t)ch * NM;
@@ -307,6 +311,7 @@ field_moments_kernel(int le, const int64_t* __restrict__ off, const uint64_t* __
 #pragma unroll
   for (int t = 0; t < NM; t++) M[t] = 0.0;
   for (int64_t j = s_rng[0] + threadIdx.x; j < s_rng[1]; j += blockDim.x) {
+    if (!NB_IN(j, n, 405)) break;
     double m = smass[j], dx = spos[j] - cx, dy = spos[n + j] - cy, dz = spos[2 * n + j] - cz;
     if constexpr (PE == 1) p2m_acc_p1(m, dx, dy, dz, M);
     if constexpr (PE == 2) p2m_acc_p2(m, dx, dy, dz, M);
@@ -395,7 +400,7 @@ cudaError_t nb_upward(int order, bool fp64, int ncell, const int* pncell, const 
                       const double* spos, const float* smass, int64_t n, double* mom, void* coef, uint8_t* ukey,
                       uint32_t* uorder, uint32_t* uhist, int* urange, const uint16_t* cbox, const double* rho,
                       float* mom32, SortScratch* sc, cudaStream_t s) {
-  const BgArgs bg{cbox, rho, mom32};
+  const BgArgs bg{cbox, rho, mom32, pncell};
   upkey_kernel<<<gridc(ncell, 256), 256, 0, s>>>(ncell, pncell, cA, cB, ukey);
   nb_launch_counter += 1;
   cudaError_t e = nb_sort_digit8(ukey, ncell, uorder, uhist, sc, s);
@@ -441,3 +446,6 @@ cudaError_t nb_field_moments(int pe, int le, int nbox, const int64_t* off, const
   nb_launch_counter += 1;
   return cudaGetLastError();
 }
+
+// fault word of the debug build's bounds checks in this unit (debug build only)
+NB_DBG_EXPORT(upward)

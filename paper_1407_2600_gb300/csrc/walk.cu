@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
     const int i = ga.x + (act ? lane : 0);
     T xi, yi, zi;
     {
-      V4 o = w.src[i];
-      int4 la = tr.cA[tr.sleaf[i]];
+      V4 o = w.src[NB_IDX(i, tr.n, 101)];
+      int4 la = tr.cA[NB_IDX(tr.sleaf[NB_IDX(i, tr.n, 101)], tr.cnt[0], 102)];
       xi = o.x + (T)(la.x - gd.x) * scale;
       yi = o.y + (T)(la.y - gd.y) * scale;
       zi = o.z + (T)(la.z - gd.z) * scale;
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         float4* sdst = reinterpret_cast<float4*>(&s_coef[wid][0]);
         for (int t = lane; t < npair * C4; t += 32) {
           const int q = t / C4, r = t - q * C4;
-          const float4 c0 = gsrc[(int64_t)s_midx[wid][2 * q] * C4 + r];
-          const float4 c1 = 2 * q + 1 < nmp ? gsrc[(int64_t)s_midx[wid][2 * q + 1] * C4 + r]
+          const float4 c0 = gsrc[(int64_t)NB_IDX(s_midx[wid][2 * q], tr.cnt[0], 105) * C4 + r];
+          const float4 c1 = 2 * q + 1 < nmp ? gsrc[(int64_t)NB_IDX(s_midx[wid][2 * q + 1], tr.cnt[0], 105) * C4 + r]
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
           sdst[2 * (q * C4 + r)] = make_float4(c0.x, c1.x, c0.y, c1.y);
           sdst[2 * (q * C4 + r) + 1] = make_float4(c0.z, c1.z, c0.w, c1.w);
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       int4* sdst = reinterpret_cast<int4*>(&s_coef[wid][0]);
       for (int t = lane; t < nmp * C16; t += 32) {
         const int q = t / C16, r = t - q * C16;
-        sdst[t] = gsrc[(int64_t)s_midx[wid][q] * C16 + r];
+        sdst[t] = gsrc[(int64_t)NB_IDX(s_midx[wid][q], tr.cnt[0], 105) * C16 + r];
       }
       __syncwarp();
       if constexpr (DF) {
@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
         const unsigned e = (unsigned)stk[top - nb2 + lane];
         const int c2 = (int)(e & kReplCellMask);
         s_ne[wid][lane] = e;
-        cp_async16(&s_nA[wid][lane], &tr.cA[c2]);
-        cp_async16(&s_nB[wid][lane], &tr.cB[c2]);
+        cp_async16(&s_nA[wid][lane], &tr.cA[NB_IDX(c2, tr.cnt[0], 104)]);
+        cp_async16(&s_nB[wid][lane], &tr.cB[NB_IDX(c2, tr.cnt[0], 104)]);
       }
       cp_async_commit();
     };
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       // queue the accepted cells; evaluate whenever 32 are queued
       const unsigned mm = __ballot_sync(FULL, cls == NB_CELL_M2P);
       if (mm) {
-        if (cls == NB_CELL_M2P) {
+        if (cls == NB_CELL_M2P && NB_IN(qn + __popc(mm & ltmask), 64, 106)) {
           const int pos = qn + __popc(mm & ltmask);
           s_midx[wid][pos] = c;
           // -(c* - e) 2^level and eps^2 4^level: the cell's unit (exact scalings)
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       if constexpr (DUAL) {
         const unsigned lm = __ballot_sync(FULL, cls == NB_CELL_M2L);
         if (lm) {
-          if (cls == NB_CELL_M2L) {
+          if (cls == NB_CELL_M2L && NB_IN(ln + __popc(lm & ltmask), 64, 107)) {
             const int pos = ln + __popc(lm & ltmask);
             s_lidx[wid][pos] = c;
             s_limg[wid][pos] = (kx + 2) | ((ky + 2) << 3) | ((kz + 2) << 6);
@@ -556,14 +556,14 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
             const int q = lo;
             const int j = s_pst[wid][q] + (t - s_pfx[wid][q]);
             if constexpr (POTK) jo = (!w.repl || s_pctr[wid][q]) ? j : -1;  // a replica's pair is never the self pair
-            v = w.src[j];
+            v = w.src[NB_IDX(j, tr.n, 103)];
             T ox = s_poff[wid][q][0], oy = s_poff[wid][q][1], oz = s_poff[wid][q][2];
             if (!w.repl && s_plev[wid][q] < w.le) {
               // leaf above the image level: image per particle from its own
               // level-l_E ancestor
               const int4 pc = s_pcen[wid][q];
               int jx, jy, jz;
-              particle_image(tr.skeys[j], w.le, gd, jx, jy, jz);
+              particle_image(tr.skeys[NB_IDX(j, tr.n, 103)], w.le, gd, jx, jy, jz);
               ox = (T)(pc.x - jx * NB_PBOX - gd.x) * scale;
               oy = (T)(pc.y - jy * NB_PBOX - gd.y) * scale;
               oz = (T)(pc.z - jz * NB_PBOX - gd.z) * scale;
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB) walk_kernel(WalkArgs<T> w) {
       if (lane == 0) atomicOr(w.status, NB_ST_OVERFLOW);
       continue;
     }
-    if (act && (!tr.sact || tr.sact[i])) {
+    if (act && NB_IN(i, tr.n, 108) && (!tr.sact || tr.sact[i])) {
       if constexpr (DF) {
         // (ax - cx) + (dsh + dsl), the large parts added error-free first
         const T a3[3] = {ax, ay, az}, c3[3] = {cx, cy, cz};
@@ -797,10 +797,10 @@ __global__ void __launch_bounds__(256) dual_m2l_kernel(DualArgs a) {
       cell_n = a.db.cell[(int64_t)(c + stride) * 32 + lane];
       code_n = a.db.img[(int64_t)(c + stride) * 32 + lane];
     }
-    const int4 gb = tr.gB[g];
-    const int box = tr.gA[g].z;
+    const int4 gb = tr.gB[NB_IDX(g, tr.cnt[1], 111)];
+    const int box = tr.gA[NB_IDX(g, tr.cnt[1], 111)].z;
     const int kx = (code & 7) - 2, ky = ((code >> 3) & 7) - 2, kz = ((code >> 6) & 7) - 2;
-    const int4 ca = tr.cA[cell];
+    const int4 ca = tr.cA[NB_IDX(cell, tr.cnt[0], 110)];
     const int lvl = ca.w & 0xff;
     const float sc = (float)(1 << lvl);
     const float rx = ((float)(gb.x - (ca.x - kx * NB_PBOX)) * scale) * sc;
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(256) dual_m2l_kernel(DualArgs a) {
     const float e2 = a.k1 ? 0.f : a.eps2[box] * (sc * sc);
     float Mr[4 * NM4];
     {
-      const float4* src = reinterpret_cast<const float4*>(a.mom32 + (int64_t)cell * kDualStride);
+      const float4* src = reinterpret_cast<const float4*>(a.mom32 + (int64_t)NB_IDX(cell, tr.cnt[0], 110) * kDualStride);
 #pragma unroll
       for (int k = 0; k < NM4; k++) {
         const float4 v = src[k];
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(256) dual_l2p_kernel(DualArgs a) {
     s_L[wid][lane + 32] = h1 - c1;
     __syncwarp();
     const int4 ga = tr.gA[g], gb = tr.gB[g];
-    if (lane < ga.y) {
+    if (lane < ga.y && NB_IN(ga.x + lane, tr.n, 112)) {
       const int64_t i = ga.x + lane;
       if (!tr.sact || tr.sact[i]) {
         const float dx = (float)((tr.spos[i] - gb.x * scale)) * u;
@@ -1122,3 +1122,6 @@ cudaError_t nb_walk(const DevTree& tr, bool fp64, int order, const void* coef, c
   }
 #undef NB_WALK
 }
+
+// fault word of the debug build's bounds checks in this unit (debug build only)
+NB_DBG_EXPORT(walk)

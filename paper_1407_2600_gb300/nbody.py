@@ -14,7 +14,9 @@ import os
 from dataclasses import dataclass, field
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libnbody.so")
+# NBODY_LIBRARY names another build of the same library (the tests' bounds-
+# checked debug build); by default the product library beside this file
+LIB_PATH = os.environ.get("NBODY_LIBRARY") or os.path.join(HERE, "libnbody.so")
 
 NBODY_OK = 0
 NBODY_EINVAL = -1
