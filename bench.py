@@ -44,11 +44,11 @@ FP32_FLOPS_P2P = 19  # dx,dy,dz (3 FADD), r^2+eps^2 (3 FMA), rsqrt, 3 FMUL, 3 FM
 # summarised in profiles/ (96^3, packed variant with 8 warps x 2 blocks),
 # scaled by the particle count to 2^21 particles (x 2.370): in the dual form
 # the walk kernel, the cell-group expansion kernel and their evaluation
-# (143.9 + 234.3 + 160.8 MB); in the M2P form the walk kernel (44.4 MB,
+# (143.4 + 233.8 + 160.8 MB); in the M2P form the walk kernel (44.4 MB,
 # captured on earlier sources).  Reported only while the walk's sources are
 # the ones captured (hash of walk.cu, walk_common.cuh, m2p_gen.cuh,
 # common.cuh).
-WALK_TRAFFIC = {"dual": {"bytes": 1.277e9, "source_sha": "29e003ab3a78b5ae"},
+WALK_TRAFFIC = {"dual": {"bytes": 1.275e9, "source_sha": "70ff0906ff041c4c"},
                 "m2p": {"bytes": 105e6, "source_sha": "4124360064afd5ea"}}
 FP32_LANES_PER_SM = 128
 FP64_FMA_PER_SM_CLK = 2  # GB300's nominal FP64 rate (1.25 TFLOP/s) over 152 SMs at 2070 MHz

@@ -23,7 +23,7 @@ cudaError_t nb_cap_check(int* cnt, int cell_cap, int group_cap, unsigned* err, c
 cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int64_t* off, int64_t n, int n_leaf,
                           int lmax, const int* ccount, const int* coff, const int8_t* l0, const int* pncell,
                           uint8_t* plevel, int* pstart, int* pcount, int* pparent, cudaStream_t s);
-cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const int* pncell,
+cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ncell, const int* pncell,
                          const uint32_t* bfs2pre, int* pre2bfs, const uint8_t* plevel, const int* pstart,
                          const int* pcount, const int* pparent, int4* cA, int4* cB, uint64_t* ckey, uint16_t* cbox,
                          cudaStream_t s);
@@ -698,7 +698,7 @@ int build_impl(nbody_tree* t, cudaStream_t s) {
                       t->ccount.as<int>(), t->coff.as<int>(), t->l0.as<int8_t>(), totals, t->plevel.as<uint8_t>(),
                       t->pstart.as<int>(), t->pcount.as<int>(), t->pparent.as<int>(), s));
   NB_CU(nb_sort_digit8(t->plevel.as<uint8_t>(), nc, t->bfs2pre.as<uint32_t>(), t->lvlhist.as<uint32_t>(), &sc, s));
-  NB_CU(nb_bfs_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), nc, totals, t->bfs2pre.as<uint32_t>(),
+  NB_CU(nb_bfs_cells(t->keys.as<uint64_t>(), t->sbox.as<uint16_t>(), n, nc, totals, t->bfs2pre.as<uint32_t>(),
                      t->pre2bfs.as<int>(), t->plevel.as<uint8_t>(), t->pstart.as<int>(), t->pcount.as<int>(),
                      t->pparent.as<int>(), t->cA.as<int4>(), t->cB.as<int4>(), t->ckey.as<uint64_t>(),
                      t->cbox.as<uint16_t>(), s));

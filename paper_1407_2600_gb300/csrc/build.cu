@@ -441,11 +441,11 @@ cudaError_t nb_emit_cells(const uint64_t* skeys, const uint16_t* sbox, const int
   return cudaGetLastError();
 }
 
-cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int ncell, const int* pncell,
+cudaError_t nb_bfs_cells(const uint64_t* skeys, const uint16_t* sbox, int64_t n, int ncell, const int* pncell,
                          const uint32_t* bfs2pre, int* pre2bfs, const uint8_t* plevel, const int* pstart,
                          const int* pcount, const int* pparent, int4* cA, int4* cB, uint64_t* ckey,
                          uint16_t* cbox, cudaStream_t s) {
-  BuildArgs a{skeys, sbox, nullptr, 0, 0, 0};
+  BuildArgs a{skeys, sbox, nullptr, n, 0, 0};
   bfs_fill_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, pncell, bfs2pre, pre2bfs);
   bfs_cells_kernel<<<gridn(ncell, 256), 256, 0, s>>>(a, pncell, bfs2pre, pre2bfs, plevel, pstart, pcount,
                                                      pparent, cA, cB, ckey, cbox);

@@ -28,9 +28,10 @@ pytestmark = pytest.mark.gpu
 UNITS = ("sort", "build", "upward", "walk", "periodic", "adjoint")
 
 
-def run_cases(dev: str) -> dict:
+def run_cases(dev: str, after=None) -> dict:
     """Small cases of every path; arrays keyed by case (the library is the
-    one paper_1407_2600_gb300.nbody loads)."""
+    one paper_1407_2600_gb300.nbody loads).  after(name), when given, runs
+    after each case (the child reads the fault words there)."""
     import torch
     import paper_1407_2600_gb300.nbody as nb
 
@@ -40,6 +41,12 @@ def run_cases(dev: str) -> dict:
     x, eps = ics.config_haloes(16, seed=5, n_halo=3, nmin=100, nmax=600)
     n = len(x)
     out = {}
+
+    def done(name):
+        torch.cuda.synchronize()
+        if after is not None:
+            after(name)
+
     settings = {
         "m2p": dict(theta=0.6, order=4),
         "dual": dict(theta=0.6, order=4, flags=nb.NBODY_FLAG_DUAL),
@@ -55,17 +62,25 @@ def run_cases(dev: str) -> dict:
         else:
             out[name] = tree.forces().cpu().numpy()
         tree.close()
+        done(name)
     # the potential beside the forces
     tree = nb.Tree(nb.params(eps=eps, theta=0.5, order=4), t(x))
     acc, pot = tree.forces(pot=True)
+    out["pot_acc"] = acc.cpu().numpy()
     out["pot"] = pot.cpu().numpy()
+    tree.close()
+    done("pot")
     # one KDK step, then the reverse mode of the force
+    tree = nb.Tree(nb.params(eps=eps, theta=0.5, order=4), t(x))
+    acc = tree.forces()
     mom = torch.zeros((3, n), dtype=torch.float32, device=dev)
     tree.kdk_step(mom, acc, 0.05, 0.06)
     out["kdk_pos"] = tree.pos.cpu().numpy()
+    done("kdk")
     lam = np.random.default_rng(3).standard_normal((n, 3)).astype(np.float32)
     out["vjp"] = tree.forces_vjp(t(lam, torch.float32)).cpu().numpy()
     tree.close()
+    done("vjp")
     # batched boxes of uneven sizes
     boxes = [ics.config_small(7)[0], np.random.default_rng(8).uniform(0, 1, (999, 3))]
     off = np.cumsum([0] + [len(b) for b in boxes])
@@ -73,6 +88,7 @@ def run_cases(dev: str) -> dict:
                    eps=[1.0 / 480, 2e-3])
     out["batched"] = tree.forces().cpu().numpy()
     tree.close()
+    done("batched")
     # the allocation-free sort
     keys = torch.empty(n, dtype=torch.int64, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
@@ -80,7 +96,7 @@ def run_cases(dev: str) -> dict:
     rc = nb.nbody_sort_keys_noalloc(pos.data_ptr(), n, keys.data_ptr(), perm.data_ptr(), nb._stream())
     assert rc == nb.NBODY_OK, nb.nbody_strerror(rc)
     out["noalloc_perm"] = perm.cpu().numpy()
-    torch.cuda.synchronize()
+    done("noalloc")
     return out
 
 
@@ -91,18 +107,23 @@ sys.path.insert(0, sys.argv[1])
 spec = importlib.util.spec_from_file_location("zbounds", sys.argv[2])
 m = importlib.util.module_from_spec(spec)
 spec.loader.exec_module(m)
-out = m.run_cases("cuda:0")
-np.savez(sys.argv[3], **out)
 import paper_1407_2600_gb300.nbody as nb
 L = nb.lib()
 faults = {}
-for u in m.UNITS:
-    f = getattr(L, "nbody_dbg_fault_" + u)
-    f.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
-    v = ctypes.c_ulonglong(0)
-    rc = f(ctypes.byref(v), 1)
-    faults[u] = [int(rc), int(v.value)]
-print("FAULTS " + json.dumps(faults))
+def after(name):
+    for u in m.UNITS:
+        f = getattr(L, "nbody_dbg_fault_" + u)
+        f.argtypes = [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
+        v = ctypes.c_ulonglong(0)
+        rc = f(ctypes.byref(v), 1)
+        if rc or v.value:
+            faults.setdefault(name, {})[u] = [int(rc), int(v.value)]
+    print("CASE " + name + " " + json.dumps(faults.get(name, {})), flush=True)
+try:
+    out = m.run_cases("cuda:0", after)
+    np.savez(sys.argv[3], **out)
+finally:
+    print("FAULTS " + json.dumps(faults), flush=True)
 """
 
 
@@ -114,14 +135,13 @@ def test_debug_bounds_build_every_path(cuda, tmp_path):
     env = dict(os.environ, NBODY_LIBRARY=dbg)
     r = subprocess.run([sys.executable, "-c", _CHILD, root, os.path.abspath(__file__), npz], env=env,
                        capture_output=True, text=True, timeout=900)
+    lines = [s for s in r.stdout.splitlines() if s.startswith("FAULTS ")]
+    faults = json.loads(lines[-1][len("FAULTS "):]) if lines else {}
+    # a nonzero word is (site << 48) | index of the first failed check
+    failed = ["case %s, unit %s: rc %d, site %d, index %d" % (case, u, rc, word >> 48, word & ((1 << 48) - 1))
+              for case, units in faults.items() for u, (rc, word) in units.items() if rc or word]
+    assert not failed, failed
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
-    line = [s for s in r.stdout.splitlines() if s.startswith("FAULTS ")][-1]
-    faults = json.loads(line[len("FAULTS "):])
-    assert set(faults) == set(UNITS)
-    for u, (rc, word) in faults.items():
-        assert rc == 0, (u, rc)
-        # a nonzero word is (site << 48) | index of the first failed check
-        assert word == 0, "bounds check failed in %s: site %d, index %d" % (u, word >> 48, word & ((1 << 48) - 1))
     got = dict(np.load(npz))
     ref = run_cases(str(cuda))
     assert set(got) == set(ref)
