@@ -66,7 +66,7 @@ ERR_BENCH = {"median": 7.2e-4, "p99": 1.20e-2, "targets": 4096, "p99_abs_over_rm
 ERR_BENCH_DUAL = {"median": 8.3e-4, "p99": 1.34e-2, "targets": 4096, "p99_abs_over_rms": 3.1e-4}
 ERR_CONFIG3 = {"median": 3.7e-4, "p99": 1.6e-3, "targets": 256}
 FORMS = {"m2p": "M2P: every accepted cell expanded at every sink",
-         "dual": "dual: cells far from a group through one local expansion of the group (cell-group M2L, L2P)"}
+         "dual": "dual: far cells through one local expansion per group (cell-group M2L, L2P)"}
 
 
 def workload(seed: int, ng: int = NG):
@@ -311,7 +311,7 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "extrapolated_full_evaluation_updates_per_s": float(np.median([r["extrapolated_rate"] for r in res])),
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_sig(line)), flush=True)
     return 0
 
 
@@ -534,8 +534,8 @@ def run_gpu(args, rank, world, local_rank):
         try:
             det = cpu_reference(x, eps, 128, 7)
             base = {"value": det["extrapolated_rate"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                    "sample": "FP64 CPU oracle tree: one build of all %d particles plus the walk of the groups "
-                              "of %d random targets (%d sinks, %.1f s), scaled to a whole evaluation"
+                    "sample": "FP64 CPU oracle tree: build of all %d particles + walk of the groups of %d "
+                              "random targets (%d sinks, %.1f s), scaled to one evaluation"
                               % (n, det["targets"], det["sinks"], det["t_call_s"])}
         except Exception as exc:  # the oracle is optional on a box without a compiler
             base = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -546,8 +546,8 @@ def run_gpu(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": ("%d^3" % args.ng) + " Zel'dovich (P~k^-2, rms 0.6 spacing, a=0.02) + 64 NFW haloes "
-                                   "(2k-50k particles, c 5-15), L=250 Mpc/h, eps=spacing/30; one KDK step "
-                                   "of dln a = 0.1 per step",
+                                   "(2k-50k particles, c 5-15), L=250 Mpc/h, eps=spacing/30; KDK steps "
+                                   "of dln a = 0.1",
                        "n": n, "theta": THETA, "order": ORDER, "n_group": 32, "n_leaf": 16,
                        "n_direct": args.n_direct, "form": FORMS[args.form],
                        "ewald_order": 4, "ewald_grid": args.ewald_grid, "precision": "FP32 interactions, "
@@ -559,7 +559,7 @@ def run_gpu(args, rank, world, local_rank):
                          "traffic": (WALK_TRAFFIC[args.form]["bytes"] if args.ng == NG and
                                      walk_source_sha() == WALK_TRAFFIC[args.form]["source_sha"] else None),
                          "kernel": ("walk_kernel + dual_m2l_kernel + dual_l2p_kernel" if dual_main else "walk_kernel"), "flops_per_launch": flops, "sm_count": sms,
-                         "peak_note": "FP32 non-tensor, derived: %d SMs x 128 lanes x 2 x 2070 MHz" % sms},
+                         "peak_note": "FP32 non-tensor: %d SMs x 128 lanes x 2 x 2070 MHz" % sms},
             "cpu_baseline": base,
             "e2e": e2e,
             "gpu_launches": tm["launches"] // 1,
@@ -568,17 +568,15 @@ def run_gpu(args, rank, world, local_rank):
             "phases_ms": {k[3:]: round(v, 4) for k, v in phases.items()},
             "phase_roofline": dict({k: round(v["frac"], 4) for k, v in phase_rf.items() if isinstance(v, dict)},
                                    upward_fp64=round(phase_rf["upward"]["fp64_frac"], 4)),
-            "force_eval_ms": force_ms,
             "force_updates_per_s": n / (force_ms * 1e-3),
             "interactions_per_particle": {"p2p": tm["p2p"] / evals / n, "m2p": tm["m2p"] / evals / n},
-            "walk_variant": tm["walk_variant"],
             "adjoint_forward_ratio": adj["ratio"] if adj else None,
-            "other_form": _summary(other, ("form", "force_updates_per_s", "speed_vs_headline_form", "walk_frac",
+            "other_form": _summary(other, ("form", "force_updates_per_s", "walk_frac",
                                            "meets_accuracy_bar")),
             "fp64_tree": None if fp64 is None else {"force_eval_ms": fp64["force_eval_ms"],
                                                     "mixed_over_fp64_speed": fp64["mixed_over_fp64_speed"],
                                                     "rel_diff": fp64["mixed_vs_fp64_rel_diff"]},
-            "batched": _summary(batched, ("updates_per_s", "force_updates_per_s", "meets_accuracy_bar",
+            "batched": _summary(batched, ("updates_per_s", "meets_accuracy_bar",
                                           "graph_state_equals_uncaptured", "tuned_force_updates_per_s")),
             "block_steps": _summary(block, ("speedup_vs_all_finest", "force_updates_per_s")),
             "config3": _summary(config3, ("updates_per_s", "ms_per_kdk_step", "phases_ms", "walk_frac",
@@ -601,7 +599,8 @@ def run_gpu(args, rank, world, local_rank):
                 json.dump(detail, f, indent=1)
         except OSError:
             line["detail_file"] = None
-        print(json.dumps(line), flush=True)
+        head = {k: line[k] for k in ("value", "ms_per_step")}
+        print(json.dumps(dict(_sig(line), **head)), flush=True)
     tree.close()
     return 0
 
@@ -666,6 +665,18 @@ def l2p_flops(order: int) -> int:
     sys.path.insert(0, os.path.join(ROOT, "paper_1407_2600_gb300", "csrc"))
     import gen_m2p
     return gen_m2p.l2p_flop_count(order)
+
+
+def _sig(o, digits: int = 5):
+    """The line's floats to `digits` significant digits (keeps the line short
+    enough for log tails; the detail file keeps full precision)."""
+    if isinstance(o, float):
+        return o if o == 0.0 or not math.isfinite(o) else float("%.*g" % (digits, o))
+    if isinstance(o, dict):
+        return {k: _sig(v, digits) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_sig(v, digits) for v in o]
+    return o
 
 
 def _summary(rec, keys):
