@@ -186,10 +186,10 @@ def with_bar(err) -> dict:
     return dict(err, meets_accuracy_bar=meets_bar(err), **{"p99_le_1e-2": err["p99"] <= 1e-2})
 
 
-def detail_path() -> str:
-    """Where the full per-leg records go (the printed line keeps the summary)."""
-    d = os.path.join(ROOT, "gpurun_out")
-    return os.path.join(d if os.path.isdir(d) else ROOT, "bench_detail.json")
+def detail_path(args) -> str:
+    """Where the full per-leg records go (the printed line keeps the summary):
+    --detail-file, relative to the repository root unless absolute."""
+    return os.path.join(ROOT, args.detail_file)
 
 
 class ClockSampler:
@@ -581,7 +581,7 @@ def run_gpu(args, rank, world, local_rank):
             "block_steps": _summary(block, ("speedup_vs_all_finest", "force_updates_per_s")),
             "config3": _summary(config3, ("updates_per_s", "ms_per_kdk_step", "phases_ms", "walk_frac",
                                           "meets_accuracy_bar")),
-            "detail_file": os.path.relpath(detail_path(), ROOT),
+            "detail_file": os.path.relpath(detail_path(args), ROOT),
         }
         detail = {"phase_roofline": phase_rf, "walk_autotune": {
                       "variant": tm["walk_variant"], "tuning_ms": tm["walk_tune_ms"][:4],
@@ -595,7 +595,7 @@ def run_gpu(args, rank, world, local_rank):
                   "adjoint": adj, "fp64_tree": fp64, "other_form": other, "batched": batched, "block_steps": block,
                   "config3": config3}
         try:
-            with open(detail_path(), "w") as f:
+            with open(detail_path(args), "w") as f:
                 json.dump(detail, f, indent=1)
         except OSError:
             line["detail_file"] = None
@@ -1002,6 +1002,8 @@ def main():
                     help="also time one all-FP64 force evaluation of the same workload")
     ap.add_argument("--config3", action=argparse.BooleanOptionalAction, default=True,
                     help="also time ten KDK steps of the 512^3 scale workload (about half a minute)")
+    ap.add_argument("--detail-file", default="bench_detail.json",
+                    help="where the full per-leg records are written (JSON)")
     ap.add_argument("--form", default="dual", choices=sorted(FORMS),
                     help="walk form of the timed steps: m2p (every accepted cell expanded at every sink) or dual "
                          "(far cells through one local expansion per group)")
