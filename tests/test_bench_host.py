@@ -72,3 +72,16 @@ def test_reference_arm_line(capsys):
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_line_rounding_keeps_structure_and_five_digits():
+    """The printed line's floats go to five significant digits; integers,
+    strings, booleans, None and the nesting are kept."""
+    import bench
+    rec = {"a": 153861860.76649404, "b": [0.000123456789, 7], "c": {"d": True, "e": None, "f": "x"},
+           "g": 0.0, "h": float("inf")}
+    out = bench._sig(rec)
+    assert out["a"] == 153860000.0
+    assert out["b"] == [0.00012346, 7]
+    assert out["c"] == {"d": True, "e": None, "f": "x"}
+    assert out["g"] == 0.0 and out["h"] == float("inf")
